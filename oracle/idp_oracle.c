@@ -1,0 +1,1284 @@
+/*
+ * idp_oracle.c -- plain, slow FP64 CPU oracle of the IDP-limited LGL-DGSEM
+ * right-hand side and SSP-RK3 step for the 2D Euler equations on a 2:1
+ * quadtree (Bolm, Rueda-Ramirez, Kuzmin, Gassner, arXiv 2607.06045).
+ *
+ * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the CPU
+ * baseline of the benchmark may load this library. It shares no code with the
+ * CUDA path.
+ *
+ * Structure, in the paper's order:
+ *   - reference operators: LGL nodes and weights (Sec. 2.1), the Lagrange
+ *     basis and its derivative, Qbar = diag(w) D, Bbar, Sbar = 2 Qbar - Bbar
+ *     (Sec. 2.1, volume integral);
+ *   - local mortar weights by subcell overlap (Eq. local_weights, App. A);
+ *   - the high-order residual in the form of Eq. evolutionformula, and the
+ *     high-order subcell fluxes of Eq. fluxdifferencingform;
+ *   - the low-order residual written literally in the global graph form of
+ *     Eq. LowOrderScheme_globalIndices with the c/d coefficients of Sec. 2.1
+ *     and, at mortars, Eq. c_nonconforming;
+ *   - bar states (Sec. 2.2, IDP property), bounds (Eqs. Bounds_Positivity,
+ *     Bounds_Barstates), FCT volume limiting and mortar limiting (Sec. 2.3);
+ *   - the IDP time step (Eq. timestep_restriction) and SSP-RK3.
+ *
+ * Readings where the paper is silent (numbered as in the design notes):
+ *   R1 Ranocha's entropy-conserving, kinetic-energy-preserving volume flux;
+ *   R2 logarithmic mean with the Ismail-Roe series below u = 1e-4;
+ *   R3 Davis wave speed lambda = max(|v_n,L| + c_L, |v_n,R| + c_R);
+ *   R4 ghost states for the boundary kinds;
+ *   R5 L2 mortar: interpolate, LLF on the small faces, project back
+ *      (LGL-weighted adjoint of interpolation, or exact L2 projection);
+ *   R6 the node itself is one of its bar states;
+ *   R7 Zalesak limiting of density;
+ *   R8 closed-form largest admissible factor for pressure, Gamma = 2d = 4;
+ *   R9 mortar factor after the volume correction with budget n_i;
+ *   R10 dt evaluated once per step;  R11 low-order CFL variant;
+ *   R12 mass-/length-weighted mean limiting factors;
+ *   R13 violation tolerance 1e-13 relative;
+ *   R15 volume density antidiffusion below 1e-14 relative is not
+ *      density-limited, and the mortar step aims at bounds relaxed by 1e-14
+ *      relative, so that rounding noise (exactly cancelling high- and
+ *      low-order fluxes, e.g. at the end nodes of a mortar, at a node the
+ *      volume step left on its bound) cannot switch a factor between 0 and 1;
+ *   R16 a mortar whose interpolated large-side states are not admissible
+ *      uses its low-order flux (alpha_S = 1), as the paper reports for
+ *      interpolation near vacuum (Sec. 3.2).
+ * Every bound interval is widened to contain the low-order value, which in
+ * exact arithmetic it already does (Eq. convex_combination).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NPMAX 9
+#define NSTAT 16
+#define TOL 1e-14   /* R15: relative bound relaxation inside the limiter */
+
+/* ------------------------------------------------------------------------ */
+/* context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+enum { F_CONF = 0, F_BND = 1, F_MORT_LARGE = 2, F_MORT_SMALL = 3 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_DIRICHLET = 2, BC_OUTFLOW = 3, BC_DMR = 4 };
+
+typedef struct {
+    int j;          /* neighbour global node index, or -1-g for ghost g */
+    double cx, cy;  /* c_(i,j) */
+} orc_nb;
+
+typedef struct {
+    int N, np, proj;
+    double gamma;
+    double xi[NPMAX], w[NPMAX];
+    double D[NPMAX][NPMAX], S[NPMAX][NPMAX];
+    double wt[NPMAX][2 * NPMAX];   /* local weights, reference units */
+    double Iint[2 * NPMAX][NPMAX]; /* interpolation large -> small nodes */
+    double P[NPMAX][2 * NPMAX];    /* projection small -> large */
+
+    /* mesh */
+    int nx0, ny0;
+    double x0, y0, x1, y1;
+    int bc[4];
+    double bc_prim[4][4], dmr_post[4], dmr_pre[4];
+    int K;
+    int *lev, *ix, *iy;
+    double *dx, *dy, *xc, *yc;
+    int *ftype;   /* [K][4] */
+    int *fnbr;    /* [K][4] neighbour element or mortar id */
+    int *fpos;    /* [K][4] small element position 0 lower / 1 upper */
+    int M;
+    int *mort;    /* [M][5]: dir(0 x,1 y), large, large_is_low(1 if large on -side), small_lo, small_hi */
+
+    /* global node graph */
+    int nn;       /* K*np*np */
+    int *nb_off;  /* [nn+1] */
+    orc_nb *nb;
+    int ng;       /* ghost count */
+    int *g_elem, *g_side, *g_t;  /* ghost owner element, side, face index */
+    int *ghost_of;                /* [K][4][np] ghost index or -1 */
+    int *mcount;  /* number of mortars incident on node */
+} orc_ctx;
+
+/* ------------------------------------------------------------------------ */
+/* reference operators (Sec. 2.1)                                           */
+/* ------------------------------------------------------------------------ */
+
+/* Legendre P_n and its first two derivatives by the three-term recurrence. */
+static void legendre(int n, double x, double *P, double *dP, double *d2P) {
+    double p0 = 1.0, p1 = x;
+    if (n == 0) { *P = 1.0; *dP = 0.0; *d2P = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        double p2 = ((2.0 * k + 1.0) * x * p1 - k * p0) / (k + 1.0);
+        p0 = p1; p1 = p2;
+    }
+    *P = p1;
+    /* derivatives for |x| < 1 from (x^2-1) P_n' = n (x P_n - P_{n-1}) and the
+       Legendre equation (1-x^2) P'' - 2x P' + n(n+1) P = 0 */
+    *dP = n * (x * p1 - p0) / (x * x - 1.0);
+    *d2P = (2.0 * x * (*dP) - n * (n + 1.0) * p1) / (1.0 - x * x);
+}
+
+/* LGL nodes: -1, the roots of P_N' (Newton from Chebyshev-Lobatto guesses), +1;
+   weights w = 2 / (N (N+1) P_N(x)^2). */
+void orc_lgl(int N, double *xi, double *w) {
+    xi[0] = -1.0; xi[N] = 1.0;
+    for (int k = 1; k < N; ++k) {
+        double x = -cos(M_PI * k / N);
+        for (int it = 0; it < 100; ++it) {
+            double P, dP, d2P;
+            legendre(N, x, &P, &dP, &d2P);
+            double dxn = dP / d2P;
+            x -= dxn;
+            if (fabs(dxn) < 1e-16) break;
+        }
+        xi[k] = x;
+    }
+    for (int k = 0; k <= N; ++k) {
+        double P = 1.0;   /* |P_N(+-1)| = 1 */
+        if (k > 0 && k < N) { double dP, d2P; legendre(N, xi[k], &P, &dP, &d2P); }
+        w[k] = 2.0 / (N * (N + 1.0) * P * P);
+    }
+}
+
+/* Lagrange basis phi_j(x) on the nodes xi (product definition). */
+static double lagrange(int np, const double *xi, int j, double x) {
+    double v = 1.0;
+    for (int m = 0; m < np; ++m)
+        if (m != j) v *= (x - xi[m]) / (xi[j] - xi[m]);
+    return v;
+}
+
+/* phi_j'(x) by the product rule. */
+static double lagrange_deriv(int np, const double *xi, int j, double x) {
+    double s = 0.0;
+    for (int m = 0; m < np; ++m) {
+        if (m == j) continue;
+        double t = 1.0 / (xi[j] - xi[m]);
+        for (int l = 0; l < np; ++l)
+            if (l != j && l != m) t *= (x - xi[l]) / (xi[j] - xi[l]);
+        s += t;
+    }
+    return s;
+}
+
+/* Gauss-Legendre nodes by Newton on P_n (used only for exact L2 projection). */
+static void gauss(int n, double *x, double *w) {
+    for (int k = 0; k < n; ++k) {
+        double t = -cos(M_PI * (k + 0.75) / (n + 0.5));
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = t;
+            for (int m = 1; m < n; ++m) { double p2 = ((2.0 * m + 1.0) * t * p1 - m * p0) / (m + 1.0); p0 = p1; p1 = p2; }
+            double dp = n * (t * p1 - p0) / (t * t - 1.0);
+            double d = p1 / dp; t -= d;
+            if (fabs(d) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = t;
+        for (int m = 1; m < n; ++m) { double p2 = ((2.0 * m + 1.0) * t * p1 - m * p0) / (m + 1.0); p0 = p1; p1 = p2; }
+        double dp = n * (t * p1 - p0) / (t * t - 1.0);
+        x[k] = t; w[k] = 2.0 / ((1.0 - t * t) * dp * dp);
+    }
+}
+
+/* Solve A X = B (n x n, m right-hand sides) by Gaussian elimination with
+   partial pivoting; A and B are overwritten. */
+static void solve(int n, int m, double *A, double *B) {
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r) if (fabs(A[r * n + c]) > fabs(A[piv * n + c])) piv = r;
+        if (piv != c) {
+            for (int k = 0; k < n; ++k) { double t = A[c * n + k]; A[c * n + k] = A[piv * n + k]; A[piv * n + k] = t; }
+            for (int k = 0; k < m; ++k) { double t = B[c * m + k]; B[c * m + k] = B[piv * m + k]; B[piv * m + k] = t; }
+        }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = A[r * n + c] / A[c * n + c];
+            for (int k = 0; k < n; ++k) A[r * n + k] -= f * A[c * n + k];
+            for (int k = 0; k < m; ++k) B[r * m + k] -= f * B[c * m + k];
+        }
+    }
+    for (int r = 0; r < n; ++r) for (int k = 0; k < m; ++k) B[r * m + k] /= A[r * n + r];
+}
+
+/* Operators for degree N: Sbar, local weights, mortar interpolation and
+   projection (proj 0: LGL-weighted adjoint of interpolation; 1: exact L2). */
+void orc_operators(int N, int proj, double *xi, double *w, double *D, double *S,
+                   double *wt, double *Iint, double *P) {
+    int np = N + 1;
+    orc_lgl(N, xi, w);
+    /* D_ij = phi_j'(xi_i), Qbar = diag(w) D, Bbar = diag(-1,0..0,1) */
+    for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j) {
+            D[i * np + j] = lagrange_deriv(np, xi, j, xi[i]);
+            double Q = w[i] * D[i * np + j];
+            double B = (i == j) ? (i == 0 ? -1.0 : (i == N ? 1.0 : 0.0)) : 0.0;
+            S[i * np + j] = 2.0 * Q - B;
+        }
+    /* local weights (App. A): overlap length of the LGL subcell of large node
+       k and of small node (e, l), the small subcells being half as wide */
+    for (int k = 0; k < np; ++k) {
+        double aL = -1.0, aU;
+        for (int m = 0; m < k; ++m) aL += w[m];
+        aU = aL + w[k];
+        for (int e = 0; e < 2; ++e) {
+            for (int l = 0; l < np; ++l) {
+                double bL = (e == 0 ? -1.0 : 0.0), bU;
+                for (int m = 0; m < l; ++m) bL += 0.5 * w[m];
+                bU = bL + 0.5 * w[l];
+                double lo = aL > bL ? aL : bL, hi = aU < bU ? aU : bU;
+                /* subcells that only touch at a point (b_U = b_L in exact
+                   arithmetic) do not overlap: rounding-level overlaps are 0 */
+                wt[k * 2 * np + e * np + l] = hi - lo > 1e-13 ? hi - lo : 0.0;
+            }
+        }
+    }
+    /* interpolation to the small-face nodes s = (xi_l -/+ 1)/2 */
+    for (int e = 0; e < 2; ++e)
+        for (int l = 0; l < np; ++l) {
+            double s = 0.5 * (xi[l] + (e == 0 ? -1.0 : 1.0));
+            for (int k = 0; k < np; ++k) Iint[(e * np + l) * np + k] = lagrange(np, xi, k, s);
+        }
+    if (proj == 0) {
+        for (int k = 0; k < np; ++k)
+            for (int e = 0; e < 2; ++e)
+                for (int l = 0; l < np; ++l)
+                    P[k * 2 * np + e * np + l] = 0.5 * w[l] * Iint[(e * np + l) * np + k] / w[k];
+    } else {
+        /* exact L2 projection with Gauss quadrature of 2N+2 points per half */
+        int ng = 2 * np;
+        double gx[2 * NPMAX], gw[2 * NPMAX];
+        gauss(ng, gx, gw);
+        double Mm[NPMAX * NPMAX], Bm[NPMAX * 2 * NPMAX];
+        memset(Mm, 0, sizeof Mm); memset(Bm, 0, sizeof Bm);
+        for (int q = 0; q < ng; ++q)
+            for (int a = 0; a < np; ++a)
+                for (int b = 0; b < np; ++b)
+                    Mm[a * np + b] += gw[q] * lagrange(np, xi, a, gx[q]) * lagrange(np, xi, b, gx[q]);
+        for (int e = 0; e < 2; ++e)
+            for (int q = 0; q < ng; ++q) {
+                double s = 0.5 * (gx[q] + (e == 0 ? -1.0 : 1.0));   /* point on the large face */
+                for (int k = 0; k < np; ++k)
+                    for (int l = 0; l < np; ++l)
+                        Bm[k * 2 * np + e * np + l] += 0.5 * gw[q] * lagrange(np, xi, k, s) * lagrange(np, xi, l, gx[q]);
+            }
+        solve(np, 2 * np, Mm, Bm);
+        /* P multiplies small-face nodal fluxes and gives large-face nodal
+           values; the large element weights them by w_k */
+        for (int k = 0; k < np; ++k)
+            for (int c = 0; c < 2 * np; ++c) P[k * 2 * np + c] = Bm[k * 2 * np + c];
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Euler physics                                                            */
+/* ------------------------------------------------------------------------ */
+
+static double pressure(double g, const double *u) {
+    return (g - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0]);
+}
+
+/* physical flux f(u) . n for a unit normal n = (nx, ny) */
+static void flux_n(double g, const double *u, double nx, double ny, double *f) {
+    double v1 = u[1] / u[0], v2 = u[2] / u[0], p = pressure(g, u);
+    double vn = v1 * nx + v2 * ny;
+    f[0] = u[0] * vn;
+    f[1] = u[1] * vn + p * nx;
+    f[2] = u[2] * vn + p * ny;
+    f[3] = (u[3] + p) * vn;
+}
+
+/* R3: Davis estimate of the maximum wave speed along n */
+static double lambda_max(double g, const double *a, const double *b, double nx, double ny) {
+    double va = (a[1] * nx + a[2] * ny) / a[0], vb = (b[1] * nx + b[2] * ny) / b[0];
+    double ca = sqrt(g * pressure(g, a) / a[0]), cb = sqrt(g * pressure(g, b) / b[0]);
+    double la = fabs(va) + ca, lb = fabs(vb) + cb;
+    return la > lb ? la : lb;
+}
+
+/* local Lax-Friedrichs (Rusanov) flux along a unit normal */
+void orc_llf(double g, const double *uL, const double *uR, double nx, double ny, double *f) {
+    double fL[4], fR[4];
+    flux_n(g, uL, nx, ny, fL);
+    flux_n(g, uR, nx, ny, fR);
+    double lam = lambda_max(g, uL, uR, nx, ny);
+    for (int v = 0; v < 4; ++v) f[v] = 0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]);
+}
+
+/* R2: logarithmic mean (a - b) / ln(a / b) in the Ismail-Roe form
+   (a + b) / (2 F), F = ln(zeta) / (2 f), zeta = a / b, f = (zeta-1)/(zeta+1),
+   with the series F = 1 + u/3 + u^2/5 + u^3/7, u = f^2, for u < 1e-4 */
+double orc_logmean(double a, double b) {
+    double f = (a - b) / (a + b), u = f * f;
+    if (u < 1e-4) return (a + b) / (2.0 * (1.0 + u / 3.0 + u * u / 5.0 + u * u * u / 7.0));
+    return (a - b) / log(a / b);
+}
+
+/* R1: Ranocha's EC/KEP two-point flux along the unit axis d (0 x, 1 y) */
+void orc_ranocha(double g, const double *uL, const double *uR, int d, double *f) {
+    double rL = uL[0], rR = uR[0];
+    double v1L = uL[1] / rL, v2L = uL[2] / rL, v1R = uR[1] / rR, v2R = uR[2] / rR;
+    double pL = pressure(g, uL), pR = pressure(g, uR);
+    double rho_ln = orc_logmean(rL, rR);
+    double inv_beta = 1.0 / orc_logmean(rL / pL, rR / pR);   /* 1/{rho/p}_ln */
+    double v1a = 0.5 * (v1L + v1R), v2a = 0.5 * (v2L + v2R), pa = 0.5 * (pL + pR);
+    double vnL = d == 0 ? v1L : v2L, vnR = d == 0 ? v1R : v2R, vna = 0.5 * (vnL + vnR);
+    double fr = rho_ln * vna;
+    f[0] = fr;
+    f[1] = fr * v1a + (d == 0 ? pa : 0.0);
+    f[2] = fr * v2a + (d == 1 ? pa : 0.0);
+    f[3] = fr * (0.5 * (v1L * v1R + v2L * v2R) + inv_beta / (g - 1.0)) + 0.5 * (pL * vnR + pR * vnL);
+}
+
+/* ------------------------------------------------------------------------ */
+/* mesh connectivity (naive: sorted leaf keys and binary search)            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct { int64_t key; int e; } leafkey;
+static int cmp_key(const void *a, const void *b) {
+    int64_t x = ((const leafkey *)a)->key, y = ((const leafkey *)b)->key;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+static int64_t mkkey(int l, int64_t x, int64_t y) { return ((int64_t)l << 58) | (x << 29) | y; }
+static int find_leaf(const leafkey *t, int K, int l, int64_t x, int64_t y) {
+    leafkey q; q.key = mkkey(l, x, y);
+    const leafkey *r = bsearch(&q, t, K, sizeof(leafkey), cmp_key);
+    return r ? r->e : -1;
+}
+
+void orc_destroy(orc_ctx *c) {
+    if (!c) return;
+    free(c->lev); free(c->ix); free(c->iy); free(c->dx); free(c->dy); free(c->xc); free(c->yc);
+    free(c->ftype); free(c->fnbr); free(c->fpos); free(c->mort);
+    free(c->nb_off); free(c->nb); free(c->g_elem); free(c->g_side); free(c->g_t); free(c->mcount); free(c->ghost_of);
+    free(c);
+}
+
+static int gidx(const orc_ctx *c, int e, int i, int j) { return (e * c->np + j) * c->np + i; }
+
+/* face node t of side s -> local (i, j) */
+static void face_node(int np, int s, int t, int *i, int *j) {
+    switch (s) {
+    case 0: *i = 0; *j = t; break;
+    case 1: *i = np - 1; *j = t; break;
+    case 2: *i = t; *j = 0; break;
+    default: *i = t; *j = np - 1; break;
+    }
+}
+
+/* outward unit normal of side s */
+static void side_normal(int s, double *nx, double *ny) {
+    *nx = (s == 0) ? -1.0 : (s == 1 ? 1.0 : 0.0);
+    *ny = (s == 2) ? -1.0 : (s == 3 ? 1.0 : 0.0);
+}
+
+static void push_nb(orc_nb **buf, int *n, int *cap, int j, double cx, double cy) {
+    if (*n == *cap) { *cap = *cap ? 2 * *cap : 1024; *buf = realloc(*buf, sizeof(orc_nb) * (*cap)); }
+    (*buf)[*n].j = j; (*buf)[*n].cx = cx; (*buf)[*n].cy = cy; ++*n;
+}
+
+orc_ctx *orc_create(int N, double gamma, int proj, int nx0, int ny0, double x0, double y0,
+                    double x1, double y1, int K, const int8_t *level, const int32_t *ix,
+                    const int32_t *iy, const int32_t *bc, const double *bc_prim,
+                    const double *dmr_post, const double *dmr_pre, int *err) {
+    *err = 0;
+    if (N < 1 || N + 1 > NPMAX || K < 1) { *err = 1; return NULL; }
+    orc_ctx *c = calloc(1, sizeof(orc_ctx));
+    c->N = N; c->np = N + 1; c->gamma = gamma; c->proj = proj;
+    /* the operator routine writes dense np-strided arrays: repack to NPMAX strides */
+    {
+        double D[NPMAX * NPMAX], S[NPMAX * NPMAX], wt[NPMAX * 2 * NPMAX], I[2 * NPMAX * NPMAX], P[NPMAX * 2 * NPMAX];
+        double xi[NPMAX], w[NPMAX];
+        orc_operators(N, proj, xi, w, D, S, wt, I, P);
+        int np = N + 1;
+        for (int a = 0; a < np; ++a) { c->xi[a] = xi[a]; c->w[a] = w[a]; }
+        for (int a = 0; a < np; ++a) for (int b = 0; b < np; ++b) { c->D[a][b] = D[a * np + b]; c->S[a][b] = S[a * np + b]; }
+        for (int a = 0; a < np; ++a) for (int b = 0; b < 2 * np; ++b) { c->wt[a][b] = wt[a * 2 * np + b]; c->P[a][b] = P[a * 2 * np + b]; }
+        for (int a = 0; a < 2 * np; ++a) for (int b = 0; b < np; ++b) c->Iint[a][b] = I[a * np + b];
+    }
+    c->nx0 = nx0; c->ny0 = ny0; c->x0 = x0; c->y0 = y0; c->x1 = x1; c->y1 = y1;
+    for (int s = 0; s < 4; ++s) { c->bc[s] = bc[s]; for (int v = 0; v < 4; ++v) c->bc_prim[s][v] = bc_prim[4 * s + v]; }
+    for (int v = 0; v < 4; ++v) { c->dmr_post[v] = dmr_post[v]; c->dmr_pre[v] = dmr_pre[v]; }
+    c->K = K;
+    c->lev = malloc(sizeof(int) * K); c->ix = malloc(sizeof(int) * K); c->iy = malloc(sizeof(int) * K);
+    c->dx = malloc(sizeof(double) * K); c->dy = malloc(sizeof(double) * K);
+    c->xc = malloc(sizeof(double) * K); c->yc = malloc(sizeof(double) * K);
+    leafkey *tab = malloc(sizeof(leafkey) * K);
+    for (int e = 0; e < K; ++e) {
+        c->lev[e] = level[e]; c->ix[e] = ix[e]; c->iy[e] = iy[e];
+        double n = (double)(1 << level[e]);
+        c->dx[e] = (x1 - x0) / (nx0 * n); c->dy[e] = (y1 - y0) / (ny0 * n);
+        c->xc[e] = x0 + (ix[e] + 0.5) * c->dx[e]; c->yc[e] = y0 + (iy[e] + 0.5) * c->dy[e];
+        tab[e].key = mkkey(level[e], ix[e], iy[e]); tab[e].e = e;
+    }
+    qsort(tab, K, sizeof(leafkey), cmp_key);
+    c->ftype = malloc(sizeof(int) * 4 * K); c->fnbr = malloc(sizeof(int) * 4 * K); c->fpos = malloc(sizeof(int) * 4 * K);
+    c->mort = malloc(sizeof(int) * 5 * 4 * K);
+    c->M = 0;
+    for (int e = 0; e < K; ++e) for (int s = 0; s < 4; ++s) c->fpos[4 * e + s] = -1;
+    /* pass 1: conforming, boundary and large-side mortar faces */
+    for (int e = 0; e < K && !*err; ++e) {
+        int l = c->lev[e];
+        int64_t nxl = (int64_t)nx0 << l, nyl = (int64_t)ny0 << l;
+        for (int s = 0; s < 4; ++s) {
+            int dir = s / 2;
+            int64_t qx = ix[e] + (s == 0 ? -1 : (s == 1 ? 1 : 0));
+            int64_t qy = iy[e] + (s == 2 ? -1 : (s == 3 ? 1 : 0));
+            int out = (qx < 0 || qx >= nxl || qy < 0 || qy >= nyl);
+            if (out && bc[s] != BC_PERIODIC) { c->ftype[4 * e + s] = F_BND; c->fnbr[4 * e + s] = -1; continue; }
+            qx = (qx + nxl) % nxl; qy = (qy + nyl) % nyl;
+            int nb = find_leaf(tab, K, l, qx, qy);
+            if (nb >= 0) { c->ftype[4 * e + s] = F_CONF; c->fnbr[4 * e + s] = nb; continue; }
+            if (l > 0 && find_leaf(tab, K, l - 1, qx >> 1, qy >> 1) >= 0) {
+                c->ftype[4 * e + s] = F_MORT_SMALL; c->fnbr[4 * e + s] = -1; continue;  /* filled in pass 2 */
+            }
+            /* two finer neighbours across the face */
+            int64_t fx0, fy0, fx1, fy1;
+            if (dir == 0) { fx0 = fx1 = 2 * qx + (s == 0 ? 1 : 0); fy0 = 2 * qy; fy1 = 2 * qy + 1; }
+            else { fy0 = fy1 = 2 * qy + (s == 2 ? 1 : 0); fx0 = 2 * qx; fx1 = 2 * qx + 1; }
+            int a = find_leaf(tab, K, l + 1, fx0, fy0), b = find_leaf(tab, K, l + 1, fx1, fy1);
+            if (a < 0 || b < 0) { *err = 2; break; }   /* not 2:1 balanced, or a gap */
+            int m = c->M++;
+            c->mort[5 * m + 0] = dir; c->mort[5 * m + 1] = e;
+            c->mort[5 * m + 2] = (s == 1 || s == 3) ? 1 : 0;  /* large on the low side */
+            c->mort[5 * m + 3] = a; c->mort[5 * m + 4] = b;
+            c->ftype[4 * e + s] = F_MORT_LARGE; c->fnbr[4 * e + s] = m;
+        }
+    }
+    free(tab);
+    if (*err) { orc_destroy(c); return NULL; }
+    /* pass 2: small-side mortar faces */
+    for (int m = 0; m < c->M; ++m) {
+        int dir = c->mort[5 * m], low = c->mort[5 * m + 2];
+        int s_small = dir == 0 ? (low ? 0 : 1) : (low ? 2 : 3);
+        for (int p = 0; p < 2; ++p) {
+            int e = c->mort[5 * m + 3 + p];
+            c->ftype[4 * e + s_small] = F_MORT_SMALL; c->fnbr[4 * e + s_small] = m; c->fpos[4 * e + s_small] = p;
+        }
+    }
+    for (int e = 0; e < K; ++e) for (int s = 0; s < 4; ++s)
+        if (c->ftype[4 * e + s] == F_MORT_SMALL && c->fnbr[4 * e + s] < 0) { *err = 2; orc_destroy(c); return NULL; }
+
+    /* global node graph with c_(i,j) (Sec. 2.1 and Eq. c_nonconforming) */
+    int np = c->np;
+    c->nn = K * np * np;
+    c->nb_off = malloc(sizeof(int) * (c->nn + 1));
+    c->mcount = calloc(c->nn, sizeof(int));
+    c->g_elem = malloc(sizeof(int) * 4 * np * K); c->g_side = malloc(sizeof(int) * 4 * np * K); c->g_t = malloc(sizeof(int) * 4 * np * K);
+    c->ng = 0;
+    int cap = 0, cnt = 0;
+    orc_nb *buf = NULL;
+    /* ghost numbering first */
+    int *ghost_of = malloc(sizeof(int) * 4 * np * K);
+    for (int e = 0; e < K; ++e) for (int s = 0; s < 4; ++s) for (int t = 0; t < np; ++t) {
+        int q = (4 * e + s) * np + t;
+        ghost_of[q] = -1;
+        if (c->ftype[4 * e + s] == F_BND) {
+            ghost_of[q] = c->ng; c->g_elem[c->ng] = e; c->g_side[c->ng] = s; c->g_t[c->ng] = t; c->ng++;
+        }
+    }
+    for (int e = 0; e < K; ++e) {
+        for (int j = 0; j < np; ++j) for (int i = 0; i < np; ++i) {
+            int g = gidx(c, e, i, j);
+            c->nb_off[g] = cnt;
+            double cxv = c->w[j] * c->dy[e] / 4.0, cyv = c->w[i] * c->dx[e] / 4.0;
+            if (i > 0) push_nb(&buf, &cnt, &cap, gidx(c, e, i - 1, j), -cxv, 0.0);
+            if (i < np - 1) push_nb(&buf, &cnt, &cap, gidx(c, e, i + 1, j), cxv, 0.0);
+            if (j > 0) push_nb(&buf, &cnt, &cap, gidx(c, e, i, j - 1), 0.0, -cyv);
+            if (j < np - 1) push_nb(&buf, &cnt, &cap, gidx(c, e, i, j + 1), 0.0, cyv);
+            for (int s = 0; s < 4; ++s) {
+                int on = (s == 0 && i == 0) || (s == 1 && i == np - 1) || (s == 2 && j == 0) || (s == 3 && j == np - 1);
+                if (!on) continue;
+                int t = s < 2 ? j : i;
+                double nx, ny; side_normal(s, &nx, &ny);
+                double half = (s < 2 ? c->dy[e] : c->dx[e]) / 2.0;   /* face Jacobian */
+                int ft = c->ftype[4 * e + s];
+                if (ft == F_CONF) {
+                    int f = c->fnbr[4 * e + s], fi, fj;
+                    face_node(np, s ^ 1, t, &fi, &fj);
+                    double cc = c->w[t] * half / 2.0;
+                    push_nb(&buf, &cnt, &cap, gidx(c, f, fi, fj), cc * nx, cc * ny);
+                } else if (ft == F_BND) {
+                    double cc = c->w[t] * half / 2.0;
+                    push_nb(&buf, &cnt, &cap, -1 - ghost_of[(4 * e + s) * np + t], cc * nx, cc * ny);
+                } else {
+                    int m = c->fnbr[4 * e + s];
+                    c->mcount[g]++;
+                    int dir = c->mort[5 * m], low = c->mort[5 * m + 2];
+                    int large = c->mort[5 * m + 1];
+                    double halfL = (dir == 0 ? c->dy[large] : c->dx[large]) / 2.0;
+                    if (ft == F_MORT_LARGE) {
+                        int s_small = dir == 0 ? (low ? 0 : 1) : (low ? 2 : 3);
+                        for (int p = 0; p < 2; ++p) {
+                            int es = c->mort[5 * m + 3 + p];
+                            for (int l = 0; l < np; ++l) {
+                                double wt = c->wt[t][p * np + l];
+                                if (wt <= 0.0) continue;
+                                int si, sj; face_node(np, s_small, l, &si, &sj);
+                                double cc = wt * halfL / 2.0;
+                                push_nb(&buf, &cnt, &cap, gidx(c, es, si, sj), cc * nx, cc * ny);
+                            }
+                        }
+                    } else {
+                        int p = c->fpos[4 * e + s];
+                        int s_large = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2);
+                        for (int k = 0; k < np; ++k) {
+                            double wt = c->wt[k][p * np + t];
+                            if (wt <= 0.0) continue;
+                            int li, lj; face_node(np, s_large, k, &li, &lj);
+                            double cc = wt * halfL / 2.0;
+                            push_nb(&buf, &cnt, &cap, gidx(c, large, li, lj), cc * nx, cc * ny);
+                        }
+                    }
+                }
+            }
+        }
+    }
+    c->nb_off[c->nn] = cnt;
+    c->nb = buf;
+    c->ghost_of = ghost_of;
+    return c;
+}
+
+int orc_n_mortars(const orc_ctx *c) { return c->M; }
+void orc_mortars(const orc_ctx *c, int32_t *out) { for (int k = 0; k < 5 * c->M; ++k) out[k] = c->mort[k]; }
+void orc_faces(const orc_ctx *c, int32_t *ftype, int32_t *fnbr) {
+    for (int k = 0; k < 4 * c->K; ++k) { ftype[k] = c->ftype[k]; fnbr[k] = c->fnbr[k]; }
+}
+int orc_graph_size(const orc_ctx *c) { return c->nb_off[c->nn]; }
+void orc_graph(const orc_ctx *c, int32_t *off, int32_t *nbj, double *cx, double *cy) {
+    for (int g = 0; g <= c->nn; ++g) off[g] = c->nb_off[g];
+    for (int k = 0; k < c->nb_off[c->nn]; ++k) { nbj[k] = c->nb[k].j; cx[k] = c->nb[k].cx; cy[k] = c->nb[k].cy; }
+}
+
+/* ------------------------------------------------------------------------ */
+/* states, ghosts                                                           */
+/* ------------------------------------------------------------------------ */
+
+static void get_u(const orc_ctx *c, const double *u, int g, double *q) {
+    for (int v = 0; v < 4; ++v) q[v] = u[(size_t)v * c->nn + g];
+}
+
+static void prim_to_cons(double gm, const double *w, double *q) {
+    q[0] = w[0]; q[1] = w[0] * w[1]; q[2] = w[0] * w[2];
+    q[3] = w[3] / (gm - 1.0) + 0.5 * w[0] * (w[1] * w[1] + w[2] * w[2]);
+}
+
+/* R4: ghost state across boundary side s of element e at face node t */
+static void ghost_state(const orc_ctx *c, const double *u, int e, int s, int t, double time, double *q) {
+    int i, j; face_node(c->np, s, t, &i, &j);
+    double in[4]; get_u(c, u, gidx(c, e, i, j), in);
+    double nx, ny; side_normal(s, &nx, &ny);
+    int kind = c->bc[s];
+    double x = c->xc[e] + 0.5 * c->dx[e] * c->xi[i];
+    if (kind == BC_DMR) {
+        if (s == 0) kind = BC_DIRICHLET + 100;        /* post-shock inflow */
+        else if (s == 1) kind = BC_OUTFLOW;
+        else if (s == 2) kind = (x < 1.0 / 6.0) ? BC_DIRICHLET + 100 : BC_WALL;
+        else kind = (x < 1.0 / 6.0 + (c->y1 + 20.0 * time) / sqrt(3.0)) ? BC_DIRICHLET + 100 : BC_DIRICHLET + 200;
+    }
+    if (kind == BC_WALL) {
+        double mn = in[1] * nx + in[2] * ny;
+        q[0] = in[0]; q[1] = in[1] - 2.0 * mn * nx; q[2] = in[2] - 2.0 * mn * ny; q[3] = in[3];
+    } else if (kind == BC_DIRICHLET) {
+        prim_to_cons(c->gamma, c->bc_prim[s], q);
+    } else if (kind == BC_DIRICHLET + 100) {
+        prim_to_cons(c->gamma, c->dmr_post, q);
+    } else if (kind == BC_DIRICHLET + 200) {
+        prim_to_cons(c->gamma, c->dmr_pre, q);
+    } else {
+        for (int v = 0; v < 4; ++v) q[v] = in[v];
+    }
+}
+
+static double *make_ghosts(const orc_ctx *c, const double *u, double time) {
+    double *gh = malloc(sizeof(double) * 4 * (c->ng + 1));
+    for (int k = 0; k < c->ng; ++k) ghost_state(c, u, c->g_elem[k], c->g_side[k], c->g_t[k], time, gh + 4 * k);
+    return gh;
+}
+
+static void node_or_ghost(const orc_ctx *c, const double *u, const double *gh, int j, double *q) {
+    if (j >= 0) get_u(c, u, j, q);
+    else for (int v = 0; v < 4; ++v) q[v] = gh[4 * (-1 - j) + v];
+}
+
+static double mass(const orc_ctx *c, int g) {
+    int np = c->np, e = g / (np * np), r = g % (np * np), i = r % np, j = r / np;
+    return c->dx[e] * c->dy[e] / 4.0 * c->w[i] * c->w[j];
+}
+
+/* Mortar m: global node indices of its 3np nodes (large side first, then
+   the lower and the upper small element) and the outward, mass-weighted
+   low-order sparse fluxes of Eq. interfaceflux_local for each of them. */
+static void mortar_nodes(const orc_ctx *c, int m, int *gnode) {
+    int np = c->np;
+    int dir = c->mort[5 * m], L = c->mort[5 * m + 1], low = c->mort[5 * m + 2];
+    int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
+    for (int k = 0; k < np; ++k) { int li, lj; face_node(np, sL, k, &li, &lj); gnode[k] = gidx(c, L, li, lj); }
+    for (int p = 0; p < 2; ++p) {
+        int es = c->mort[5 * m + 3 + p];
+        for (int l = 0; l < np; ++l) { int si, sj; face_node(np, sS, l, &si, &sj); gnode[np + p * np + l] = gidx(c, es, si, sj); }
+    }
+}
+
+static void mortar_low(const orc_ctx *c, const double *u, int m, double Flo[][4]) {
+    int np = c->np;
+    double gm = c->gamma;
+    int dir = c->mort[5 * m], L = c->mort[5 * m + 1], low = c->mort[5 * m + 2];
+    int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2);
+    double nxL, nyL; side_normal(sL, &nxL, &nyL);
+    double halfL = (dir == 0 ? c->dy[L] : c->dx[L]) / 2.0;
+    int gnode[3 * NPMAX];
+    mortar_nodes(c, m, gnode);
+    for (int q = 0; q < 3 * np; ++q) for (int v = 0; v < 4; ++v) Flo[q][v] = 0.0;
+    for (int k = 0; k < np; ++k)
+        for (int p = 0; p < 2; ++p)
+            for (int l = 0; l < np; ++l) {
+                double wt = c->wt[k][p * np + l] * halfL;
+                if (wt <= 0.0) continue;
+                double ui[4], uj[4], fi[4], fj[4];
+                get_u(c, u, gnode[k], ui); get_u(c, u, gnode[np + p * np + l], uj);
+                flux_n(gm, ui, nxL, nyL, fi); flux_n(gm, uj, nxL, nyL, fj);
+                double lam = lambda_max(gm, ui, uj, nxL, nyL);
+                for (int v = 0; v < 4; ++v) {
+                    Flo[k][v] += 0.5 * wt * ((fi[v] + fj[v]) - lam * (uj[v] - ui[v]));
+                    Flo[np + p * np + l][v] += 0.5 * wt * (-(fi[v] + fj[v]) - lam * (ui[v] - uj[v]));
+                }
+            }
+}
+
+/* ------------------------------------------------------------------------ */
+/* high-order DG residual (Eq. evolutionformula) and subcell fluxes          */
+/* ------------------------------------------------------------------------ */
+
+/* Surface fluxes of every element side, as J-weighted numerical fluxes in the
+   +x (+y) direction, f_hat = (face length / 2) * flux, per face node: sf[e][s][t][v].
+   Mortars use R5: interpolate, LLF on the small faces, project back. R16: a
+   mortar whose interpolated large-side states are not admissible (rho <= 0
+   or p <= 0) has no high-order flux; it uses its low-order sparse flux and
+   is flagged in mbad (if given). */
+static double *surface_fluxes_b(const orc_ctx *c, const double *u, const double *gh, char *mbad);
+static double *surface_fluxes(const orc_ctx *c, const double *u, const double *gh) {
+    return surface_fluxes_b(c, u, gh, NULL);
+}
+static double *surface_fluxes_b(const orc_ctx *c, const double *u, const double *gh, char *mbad) {
+    int np = c->np, K = c->K;
+    double *sf = calloc((size_t)K * 4 * np * 4, sizeof(double));
+    double g = c->gamma;
+    for (int e = 0; e < K; ++e)
+        for (int s = 0; s < 4; ++s) {
+            int ft = c->ftype[4 * e + s];
+            if (ft == F_MORT_LARGE || ft == F_MORT_SMALL) continue;
+            double ax = s < 2 ? 1.0 : 0.0, ay = 1.0 - ax, half = (s < 2 ? c->dy[e] : c->dx[e]) / 2.0;
+            for (int t = 0; t < np; ++t) {
+                int i, j; face_node(np, s, t, &i, &j);
+                double in[4], out[4], f[4];
+                get_u(c, u, gidx(c, e, i, j), in);
+                if (ft == F_CONF) {
+                    int fi, fj; face_node(np, s ^ 1, t, &fi, &fj);
+                    get_u(c, u, gidx(c, c->fnbr[4 * e + s], fi, fj), out);
+                } else {
+                    int q = c->ghost_of[(4 * e + s) * np + t];
+                    for (int v = 0; v < 4; ++v) out[v] = gh[4 * q + v];
+                }
+                /* left/bottom state first */
+                if (s == 0 || s == 2) orc_llf(g, out, in, ax, ay, f); else orc_llf(g, in, out, ax, ay, f);
+                for (int v = 0; v < 4; ++v) sf[((size_t)(4 * e + s) * np + t) * 4 + v] = half * f[v];
+            }
+        }
+    for (int m = 0; m < c->M; ++m) {
+        int dir = c->mort[5 * m], L = c->mort[5 * m + 1], low = c->mort[5 * m + 2];
+        int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
+        double ax = dir == 0 ? 1.0 : 0.0, ay = 1.0 - ax;
+        double halfL = (dir == 0 ? c->dy[L] : c->dx[L]) / 2.0, halfS = halfL / 2.0;
+        double fst[2 * NPMAX][4];
+        int bad = 0;
+        for (int p = 0; p < 2 && !bad; ++p)
+            for (int l = 0; l < np; ++l) {
+                double ui[4] = {0, 0, 0, 0};
+                for (int k = 0; k < np; ++k) {
+                    int li, lj; face_node(np, sL, k, &li, &lj);
+                    double q[4]; get_u(c, u, gidx(c, L, li, lj), q);
+                    for (int v = 0; v < 4; ++v) ui[v] += c->Iint[p * np + l][k] * q[v];
+                }
+                if (!(ui[0] > 0.0) || !(pressure(g, ui) > 0.0)) { bad = 1; break; }
+            }
+        if (mbad) mbad[m] = (char)bad;
+        if (bad) {
+            double Flo[3 * NPMAX][4];
+            mortar_low(c, u, m, Flo);
+            for (int k = 0; k < np; ++k)
+                for (int v = 0; v < 4; ++v)
+                    sf[((size_t)(4 * L + sL) * np + k) * 4 + v] = (low ? 1.0 : -1.0) * Flo[k][v] / c->w[k];
+            for (int p = 0; p < 2; ++p) {
+                int es = c->mort[5 * m + 3 + p];
+                for (int l = 0; l < np; ++l)
+                    for (int v = 0; v < 4; ++v)
+                        sf[((size_t)(4 * es + sS) * np + l) * 4 + v] = (low ? -1.0 : 1.0) * Flo[np + p * np + l][v] / c->w[l];
+            }
+            continue;
+        }
+        for (int p = 0; p < 2; ++p) {
+            int es = c->mort[5 * m + 3 + p];
+            for (int l = 0; l < np; ++l) {
+                double ui[4] = {0, 0, 0, 0}, us[4], f[4];
+                for (int k = 0; k < np; ++k) {
+                    int li, lj; face_node(np, sL, k, &li, &lj);
+                    double q[4]; get_u(c, u, gidx(c, L, li, lj), q);
+                    for (int v = 0; v < 4; ++v) ui[v] += c->Iint[p * np + l][k] * q[v];
+                }
+                int si, sj; face_node(np, sS, l, &si, &sj);
+                get_u(c, u, gidx(c, es, si, sj), us);
+                if (low) orc_llf(g, ui, us, ax, ay, f); else orc_llf(g, us, ui, ax, ay, f);
+                for (int v = 0; v < 4; ++v) { fst[p * np + l][v] = f[v]; sf[((size_t)(4 * es + sS) * np + l) * 4 + v] = halfS * f[v]; }
+            }
+        }
+        for (int k = 0; k < np; ++k)
+            for (int v = 0; v < 4; ++v) {
+                double acc = 0.0;
+                for (int q = 0; q < 2 * np; ++q) acc += c->P[k][q] * fst[q][v];
+                sf[((size_t)(4 * L + sL) * np + k) * 4 + v] = halfL * acc;
+            }
+    }
+    return sf;
+}
+
+/* mass-weighted high-order residual J w_i w_j du/dt (Eq. evolutionformula) */
+static void dg_residual(const orc_ctx *c, const double *u, const double *sf, double *res) {
+    int np = c->np, N = c->N;
+    double g = c->gamma;
+    for (int e = 0; e < c->K; ++e)
+        for (int j = 0; j < np; ++j)
+            for (int i = 0; i < np; ++i) {
+                double ui[4], uk[4], f[4], F1[4] = {0, 0, 0, 0}, F2[4] = {0, 0, 0, 0};
+                get_u(c, u, gidx(c, e, i, j), ui);
+                for (int k = 0; k < np; ++k) {
+                    get_u(c, u, gidx(c, e, k, j), uk);
+                    orc_ranocha(g, ui, uk, 0, f);
+                    for (int v = 0; v < 4; ++v) F1[v] -= c->S[i][k] * (c->dy[e] / 2.0) * f[v];
+                    get_u(c, u, gidx(c, e, i, k), uk);
+                    orc_ranocha(g, ui, uk, 1, f);
+                    for (int v = 0; v < 4; ++v) F2[v] -= c->S[j][k] * (c->dx[e] / 2.0) * f[v];
+                }
+                for (int v = 0; v < 4; ++v) {
+                    double a = F1[v], b = F2[v];
+                    if (i == 0) a += sf[((size_t)(4 * e + 0) * np + j) * 4 + v];
+                    if (i == N) a -= sf[((size_t)(4 * e + 1) * np + j) * 4 + v];
+                    if (j == 0) b += sf[((size_t)(4 * e + 2) * np + i) * 4 + v];
+                    if (j == N) b -= sf[((size_t)(4 * e + 3) * np + i) * 4 + v];
+                    res[(size_t)v * c->nn + gidx(c, e, i, j)] = c->w[j] * a + c->w[i] * b;
+                }
+            }
+}
+
+/* high-order subcell flux between nodes (l=a) and a+1 of a row/column
+   (Eq. fluxdifferencingform), d = 0 for x rows (row index r = j), 1 for y */
+static void dg_subcell_flux(const orc_ctx *c, const double *u, int e, int d, int r, int a, double *fh) {
+    int np = c->np;
+    double f[4], ul[4], uk[4];
+    for (int v = 0; v < 4; ++v) fh[v] = 0.0;
+    double half = (d == 0 ? c->dy[e] : c->dx[e]) / 2.0;
+    for (int l = 0; l <= a; ++l)
+        for (int k = 0; k < np; ++k) {
+            get_u(c, u, d == 0 ? gidx(c, e, l, r) : gidx(c, e, r, l), ul);
+            get_u(c, u, d == 0 ? gidx(c, e, k, r) : gidx(c, e, r, k), uk);
+            orc_ranocha(c->gamma, ul, uk, d, f);
+            for (int v = 0; v < 4; ++v) fh[v] += c->S[l][k] * half * f[v];
+        }
+}
+
+/* ------------------------------------------------------------------------ */
+/* low-order residual in global form (Eq. LowOrderScheme_globalIndices)     */
+/* ------------------------------------------------------------------------ */
+
+static void fv_residual(const orc_ctx *c, const double *u, const double *gh, double *res, double *dsum) {
+    double g = c->gamma;
+    for (int i = 0; i < c->nn; ++i) {
+        double ui[4], uj[4], acc[4] = {0, 0, 0, 0}, s2d = 0.0;
+        get_u(c, u, i, ui);
+        for (int k = c->nb_off[i]; k < c->nb_off[i + 1]; ++k) {
+            const orc_nb *b = &c->nb[k];
+            node_or_ghost(c, u, gh, b->j, uj);
+            double nrm = sqrt(b->cx * b->cx + b->cy * b->cy);
+            double fx[4], fy[4];
+            flux_n(g, uj, 1.0, 0.0, fx);
+            flux_n(g, uj, 0.0, 1.0, fy);
+            double lam = lambda_max(g, ui, uj, b->cx / nrm, b->cy / nrm);
+            double d = nrm * lam;
+            for (int v = 0; v < 4; ++v) acc[v] += -(b->cx * fx[v] + b->cy * fy[v]) + d * (uj[v] - ui[v]);
+            s2d += 2.0 * d;
+        }
+        for (int v = 0; v < 4; ++v) res[(size_t)v * c->nn + i] = acc[v];
+        if (dsum) dsum[i] = s2d;
+    }
+}
+
+/* IDP time step (Eq. timestep_restriction) or, for rule 1, the low-order CFL
+   estimate (R11): min over nodes and directions of (w_i dx/2) / (|v| + c). */
+double orc_dt(const orc_ctx *c, const double *u, double time, double cfl, int rule) {
+    double best = INFINITY;
+    if (rule == 0) {
+        double *gh = make_ghosts(c, u, time);
+        double *res = malloc(sizeof(double) * 4 * c->nn), *ds = malloc(sizeof(double) * c->nn);
+        fv_residual(c, u, gh, res, ds);
+        for (int i = 0; i < c->nn; ++i) { double t = mass(c, i) / ds[i]; if (t < best) best = t; }
+        free(gh); free(res); free(ds);
+    } else {
+        int np = c->np;
+        for (int i = 0; i < c->nn; ++i) {
+            double q[4]; get_u(c, u, i, q);
+            int e = i / (np * np), r = i % (np * np), a = r % np, b = r / np;
+            double p = pressure(c->gamma, q), cs = sqrt(c->gamma * p / q[0]);
+            double tx = c->w[a] * c->dx[e] / 2.0 / (fabs(q[1] / q[0]) + cs);
+            double ty = c->w[b] * c->dy[e] / 2.0 / (fabs(q[2] / q[0]) + cs);
+            if (tx < best) best = tx;
+            if (ty < best) best = ty;
+        }
+    }
+    return cfl * best;
+}
+
+/* ------------------------------------------------------------------------ */
+/* limiting (Sec. 2.3)                                                       */
+/* ------------------------------------------------------------------------ */
+
+/* R8: largest theta in [0, hi] such that v = u0 + theta a has rho > 0 and
+   g(theta) = (gamma-1)(rho E - |m|^2/2) - pmin rho >= 0 (equivalently
+   p >= pmin); the admissible set is convex, so the feasible thetas are an
+   interval [0, theta*]. */
+double orc_theta(double gm, const double *u0, const double *a, double pmin, double hi) {
+    if (!(hi > 0.0)) return 0.0;
+    double c0 = (gm - 1.0) * (u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2])) - pmin * u0[0];
+    if (!(c0 > 0.0) || !(u0[0] > 0.0)) return 0.0;
+    double c1 = (gm - 1.0) * (u0[0] * a[3] + a[0] * u0[3] - (u0[1] * a[1] + u0[2] * a[2])) - pmin * a[0];
+    double c2 = (gm - 1.0) * (a[0] * a[3] - 0.5 * (a[1] * a[1] + a[2] * a[2]));
+    double rho_hi = u0[0] + hi * a[0];
+    double g_hi = c0 + hi * (c1 + hi * c2);
+    if (rho_hi > 0.0 && g_hi >= 0.0) return hi;
+    /* smallest positive root of c0 + c1 t + c2 t^2 (c0 > 0) */
+    double root = INFINITY;
+    if (c2 == 0.0) {
+        if (c1 < 0.0) root = -c0 / c1;
+    } else {
+        double disc = c1 * c1 - 4.0 * c2 * c0;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            double q = -0.5 * (c1 + (c1 >= 0.0 ? sq : -sq));
+            double r1 = q / c2, r2 = c0 / q;
+            if (r1 > 0.0 && r1 < root) root = r1;
+            if (r2 > 0.0 && r2 < root) root = r2;
+        }
+    }
+    /* aim a relative 1e-12 inside the root so that rounding in the root and
+       in the directly evaluated pressure does not cross the bound */
+    double th = root < hi ? root * (1.0 - 1e-12) : hi;
+    if (a[0] < 0.0) {
+        double tr = -u0[0] / a[0];   /* density reaches zero */
+        if (th >= tr) th = 0.5 * tr;
+    }
+    if (!(th > 0.0)) return 0.0;
+    /* verification in FP64 against the directly evaluated pressure (R13
+       tolerance): at most four halvings, then zero */
+    for (int it = 0; it < 4; ++it) {
+        double v[4];
+        for (int k = 0; k < 4; ++k) v[k] = u0[k] + th * a[k];
+        if (v[0] > 0.0 && pressure(gm, v) >= pmin * (1.0 - 1e-13)) return th;
+        th *= 0.5;
+    }
+    return 0.0;
+}
+
+/* optional per-mortar factor output (l_S) for inspection by the tests */
+static double *g_mortar_ell = NULL;
+void orc_set_mortar_ell_out(double *p) { g_mortar_ell = p; }
+static double *g_mortar_dbg = NULL;   /* [M][3np][16]: node, lr, th, u0[4], av[4], rmin, rmax, pmin, n */
+void orc_set_mortar_dbg_out(double *p) { g_mortar_dbg = p; }
+static double *g_node_dbg = NULL;     /* [nn][8]: rho_FV, rmin, rmax, pmin, rho_vol, lmin, R+, R- */
+void orc_set_node_dbg_out(double *p) { g_node_dbg = p; }
+
+/* statistics slots */
+enum { ST_AVOL_M = 0, ST_M, ST_NVOL, ST_AMORT_L, ST_L, ST_NMORT, ST_VRHO, ST_VP, ST_NONPOS, ST_DTX, ST_MINRHO, ST_MINP };
+
+/* One limited forward-Euler stage: on return res holds the mass-weighted
+   limited residual m_i du_i/dt and, if utilde != NULL, utilde the limited
+   stage state u + dt/m * res written in the FCT form
+   u_FV + dt/m (sum l G) + dt/m (sum_S l_S H_S).
+   limiting: 0 none, 1 positivity, 2 local (bar-state density bounds). */
+int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int limiting,
+              double beta, double *res_out, double *utilde, double *stats) {
+    int np = c->np, nn = c->nn, K = c->K, N = c->N;
+    double gm = c->gamma;
+    double *gh = make_ghosts(c, u, time);
+    char *mbad = calloc(c->M + 1, 1);
+    double *sf = surface_fluxes_b(c, u, gh, mbad);
+    double *rdg = malloc(sizeof(double) * 4 * nn);
+    dg_residual(c, u, sf, rdg);
+    if (dt == 0.0 || limiting == 0) {
+        free(mbad);
+        for (int k = 0; k < 4 * nn; ++k) res_out[k] = rdg[k];
+        if (utilde) for (int i = 0; i < nn; ++i) for (int v = 0; v < 4; ++v)
+            utilde[(size_t)v * nn + i] = u[(size_t)v * nn + i] + dt / mass(c, i) * rdg[(size_t)v * nn + i];
+        free(gh); free(sf); free(rdg);
+        return 0;
+    }
+    double *rfv = malloc(sizeof(double) * 4 * nn), *ds = malloc(sizeof(double) * nn);
+    fv_residual(c, u, gh, rfv, ds);
+    /* low-order update */
+    double *ufv = malloc(sizeof(double) * 4 * nn);
+    for (int i = 0; i < nn; ++i) {
+        double m = mass(c, i);
+        for (int v = 0; v < 4; ++v) ufv[(size_t)v * nn + i] = u[(size_t)v * nn + i] + dt / m * rfv[(size_t)v * nn + i];
+        if (dt * ds[i] / m > 1.0 && stats) stats[ST_DTX] += 1;
+    }
+    /* bounds (R6 and Eqs. Bounds_Positivity, Bounds_Barstates) */
+    double *rmin = malloc(sizeof(double) * nn), *rmax = malloc(sizeof(double) * nn), *pmin = malloc(sizeof(double) * nn);
+    for (int i = 0; i < nn; ++i) {
+        double ui[4], uj[4], q[4];
+        get_u(c, u, i, ui);
+        for (int v = 0; v < 4; ++v) q[v] = ufv[(size_t)v * nn + i];
+        double lo = ui[0], hi = ui[0];
+        for (int k = c->nb_off[i]; k < c->nb_off[i + 1]; ++k) {
+            const orc_nb *b = &c->nb[k];
+            node_or_ghost(c, u, gh, b->j, uj);
+            double nrm = sqrt(b->cx * b->cx + b->cy * b->cy);
+            double d = nrm * lambda_max(gm, ui, uj, b->cx / nrm, b->cy / nrm);
+            double fi[4], fj[4], fiy[4], fjy[4];
+            flux_n(gm, ui, 1.0, 0.0, fi); flux_n(gm, ui, 0.0, 1.0, fiy);
+            flux_n(gm, uj, 1.0, 0.0, fj); flux_n(gm, uj, 0.0, 1.0, fjy);
+            double cdf = b->cx * (fj[0] - fi[0]) + b->cy * (fjy[0] - fiy[0]);
+            double rb = 0.5 * (ui[0] + uj[0]) - cdf / (2.0 * d);
+            if (rb < lo) lo = rb;
+            if (rb > hi) hi = rb;
+        }
+        if (limiting == 2) {
+            rmin[i] = lo > beta * q[0] ? lo : beta * q[0];
+            rmax[i] = hi;
+        } else {
+            rmin[i] = beta * q[0];
+            rmax[i] = INFINITY;
+        }
+        if (q[0] < rmin[i]) rmin[i] = q[0];
+        if (q[0] > rmax[i]) rmax[i] = q[0];
+        pmin[i] = beta * pressure(gm, q);
+    }
+    /* antidiffusive fluxes at interior subcell interfaces: A = F_DG - F_FV in
+       the +x (+y) direction, mass-weighted; node a gets -l A, node a+1 +l A */
+    int nif = K * 2 * np * N;
+    double *A = malloc(sizeof(double) * 4 * nif);
+    for (int e = 0; e < K; ++e)
+        for (int d = 0; d < 2; ++d)
+            for (int r = 0; r < np; ++r)
+                for (int a = 0; a < N; ++a) {
+                    int id = ((e * 2 + d) * np + r) * N + a;
+                    int gl = d == 0 ? gidx(c, e, a, r) : gidx(c, e, r, a);
+                    int gr = d == 0 ? gidx(c, e, a + 1, r) : gidx(c, e, r, a + 1);
+                    double fh[4], ul[4], ur[4], fl[4], fr[4];
+                    dg_subcell_flux(c, u, e, d, r, a, fh);
+                    get_u(c, u, gl, ul); get_u(c, u, gr, ur);
+                    double cc = c->w[r] * (d == 0 ? c->dy[e] : c->dx[e]) / 4.0;
+                    flux_n(gm, ul, d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0, fl);
+                    flux_n(gm, ur, d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0, fr);
+                    double lam = lambda_max(gm, ul, ur, d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0);
+                    for (int v = 0; v < 4; ++v) {
+                        double ffv = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
+                        A[4 * id + v] = c->w[r] * fh[v] - ffv;
+                    }
+                }
+    /* R15: an interface whose density antidiffusion changes neither end
+       node's density by more than TOL relative is exempt from the density
+       limiter (the mortar step below works on bounds relaxed by TOL) */
+    double *tolr = malloc(sizeof(double) * nn);
+    for (int i = 0; i < nn; ++i) tolr[i] = TOL * fabs(ufv[i]);
+    char *exempt = malloc(nif);
+    for (int e = 0; e < K; ++e)
+        for (int d = 0; d < 2; ++d)
+            for (int r = 0; r < np; ++r)
+                for (int a = 0; a < N; ++a) {
+                    int id = ((e * 2 + d) * np + r) * N + a;
+                    int gl = d == 0 ? gidx(c, e, a, r) : gidx(c, e, r, a);
+                    int gr = d == 0 ? gidx(c, e, a + 1, r) : gidx(c, e, r, a + 1);
+                    double Ar = fabs(A[4 * id]);
+                    exempt[id] = (dt / mass(c, gl) * Ar <= tolr[gl]) && (dt / mass(c, gr) * Ar <= tolr[gr]);
+                }
+    /* R7: Zalesak factors for density */
+    double *Rp = malloc(sizeof(double) * nn), *Rm = malloc(sizeof(double) * nn);
+    for (int i = 0; i < nn; ++i) {
+        int e = i / (np * np), rr = i % (np * np), a = rr % np, b = rr / np;
+        double Pp = 0.0, Pm = 0.0;
+        for (int d = 0; d < 2; ++d) {
+            int pos = d == 0 ? a : b, row = d == 0 ? b : a;
+            if (pos > 0) {
+                int id = ((e * 2 + d) * np + row) * N + pos - 1;
+                double G = A[4 * id];
+                if (!exempt[id]) { Pp += G > 0 ? G : 0; Pm += G < 0 ? G : 0; }
+            }
+            if (pos < N) {
+                int id = ((e * 2 + d) * np + row) * N + pos;
+                double G = -A[4 * id];
+                if (!exempt[id]) { Pp += G > 0 ? G : 0; Pm += G < 0 ? G : 0; }
+            }
+        }
+        double m = mass(c, i), rfv = ufv[i];
+        double Qp = m / dt * (rmax[i] - rfv), Qm = m / dt * (rmin[i] - rfv);
+        Rp[i] = (Pp > 0.0) ? (Qp / Pp < 1.0 ? Qp / Pp : 1.0) : 1.0;
+        Rm[i] = (Pm < 0.0) ? (Qm / Pm < 1.0 ? Qm / Pm : 1.0) : 1.0;
+        if (Rp[i] < 0.0) Rp[i] = 0.0;
+        if (Rm[i] < 0.0) Rm[i] = 0.0;
+    }
+    /* R8: per interface, largest factor keeping p >= pmin at both end points
+       for the Gamma-scaled single-interface update (Gamma = 2d = 4) */
+    const double Gam = 4.0;
+    double *ell = malloc(sizeof(double) * nif);
+    double *lmin = malloc(sizeof(double) * nn);
+    for (int i = 0; i < nn; ++i) lmin[i] = 1.0;
+    for (int e = 0; e < K; ++e)
+        for (int d = 0; d < 2; ++d)
+            for (int r = 0; r < np; ++r)
+                for (int a = 0; a < N; ++a) {
+                    int id = ((e * 2 + d) * np + r) * N + a;
+                    int gl = d == 0 ? gidx(c, e, a, r) : gidx(c, e, r, a);
+                    int gr = d == 0 ? gidx(c, e, a + 1, r) : gidx(c, e, r, a + 1);
+                    double Ar = A[4 * id];
+                    /* node gl receives G = -A, node gr receives G = +A */
+                    double lr = exempt[id] ? 1.0
+                              : (-Ar > 0.0) ? (Rp[gl] < Rm[gr] ? Rp[gl] : Rm[gr]) : (Rm[gl] < Rp[gr] ? Rm[gl] : Rp[gr]);
+                    double u0[4], av[4], th_l, th_r;
+                    double ml = mass(c, gl), mr = mass(c, gr);
+                    for (int v = 0; v < 4; ++v) { u0[v] = ufv[(size_t)v * nn + gl]; av[v] = -Gam * dt / ml * A[4 * id + v]; }
+                    th_l = orc_theta(gm, u0, av, pmin[gl], lr);
+                    for (int v = 0; v < 4; ++v) { u0[v] = ufv[(size_t)v * nn + gr]; av[v] = Gam * dt / mr * A[4 * id + v]; }
+                    th_r = orc_theta(gm, u0, av, pmin[gr], lr);
+                    double l = th_l < th_r ? th_l : th_r;
+                    ell[id] = l;
+                    if (l < lmin[gl]) lmin[gl] = l;
+                    if (l < lmin[gr]) lmin[gr] = l;
+                }
+    /* volume-corrected state u_vol = u_FV + dt/m sum l G and its residual */
+    double *uvol = malloc(sizeof(double) * 4 * nn), *acc = calloc(4 * (size_t)nn, sizeof(double));
+    for (int i = 0; i < nn; ++i) {
+        int e = i / (np * np), rr = i % (np * np), a = rr % np, b = rr / np;
+        double s[4] = {0, 0, 0, 0};
+        /* sum over the node's interfaces in a fixed order: x-left, x-right, y-bottom, y-top */
+        for (int d = 0; d < 2; ++d) {
+            int pos = d == 0 ? a : b, row = d == 0 ? b : a;
+            if (pos > 0) { int id = ((e * 2 + d) * np + row) * N + pos - 1; for (int v = 0; v < 4; ++v) s[v] += ell[id] * A[4 * id + v]; }
+            if (pos < N) { int id = ((e * 2 + d) * np + row) * N + pos; for (int v = 0; v < 4; ++v) s[v] -= ell[id] * A[4 * id + v]; }
+        }
+        double m = mass(c, i);
+        for (int v = 0; v < 4; ++v) {
+            acc[(size_t)v * nn + i] = s[v];
+            uvol[(size_t)v * nn + i] = ufv[(size_t)v * nn + i] + dt / m * s[v];
+        }
+        if (stats) {
+            stats[ST_AVOL_M] += m * (1.0 - lmin[i]);
+            stats[ST_M] += m;
+            if (lmin[i] < 1.0) stats[ST_NVOL] += 1;
+        }
+    }
+    if (g_node_dbg)
+        for (int i = 0; i < nn; ++i) {
+            double *o = g_node_dbg + (size_t)i * 8;
+            o[0] = ufv[i]; o[1] = rmin[i]; o[2] = rmax[i]; o[3] = pmin[i]; o[4] = uvol[i]; o[5] = lmin[i]; o[6] = Rp[i]; o[7] = Rm[i];
+        }
+    /* R9: mortar limiting after the volume correction. Per mortar node, the
+       high-order (R5) and low-order (Eq. interfaceflux_local) outward fluxes;
+       H = -(F_L2 - F_lo) is the antidiffusive contribution. */
+    double *corr = calloc(4 * (size_t)nn, sizeof(double));
+    for (int m = 0; m < c->M; ++m) {
+        int dir = c->mort[5 * m], L = c->mort[5 * m + 1], low = c->mort[5 * m + 2];
+        int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
+        double nxL, nyL; side_normal(sL, &nxL, &nyL);
+        double halfL = (dir == 0 ? c->dy[L] : c->dx[L]) / 2.0;
+        int gnode[3 * NPMAX];
+        double H[3 * NPMAX][4];
+        mortar_nodes(c, m, gnode);
+        /* low-order sparse fluxes, outward for each side */
+        double Flo[3 * NPMAX][4];
+        mortar_low(c, u, m, Flo);
+        /* high-order outward fluxes from the surface fluxes (signs: +x-direction
+           J-weighted fluxes sf; the element on the low side loses it) */
+        for (int k = 0; k < np; ++k) {
+            double sgn = low ? 1.0 : -1.0;
+            for (int v = 0; v < 4; ++v) {
+                double FL2 = sgn * c->w[k] * sf[((size_t)(4 * L + sL) * np + k) * 4 + v];
+                H[k][v] = -(FL2 - Flo[k][v]);
+            }
+        }
+        for (int p = 0; p < 2; ++p) {
+            int es = c->mort[5 * m + 3 + p];
+            double sgn = low ? -1.0 : 1.0;
+            for (int l = 0; l < np; ++l)
+                for (int v = 0; v < 4; ++v) {
+                    double FL2 = sgn * c->w[l] * sf[((size_t)(4 * es + sS) * np + l) * 4 + v];
+                    H[np + p * np + l][v] = -(FL2 - Flo[np + p * np + l][v]);
+                }
+        }
+        double lS = 1.0;
+        if (mbad[m]) {
+            /* R16: no admissible high-order flux, pure low order */
+            for (int q = 0; q < 3 * np; ++q) for (int v = 0; v < 4; ++v) H[q][v] = 0.0;
+            lS = 0.0;
+        }
+        for (int q = 0; q < 3 * np && !mbad[m]; ++q) {
+            int i = gnode[q];
+            double mi = mass(c, i), ni = (double)c->mcount[i];
+            double u0[4], av[4];
+            for (int v = 0; v < 4; ++v) { u0[v] = uvol[(size_t)v * nn + i]; av[v] = ni * dt / mi * H[q][v]; }
+            double lr = 1.0;
+            if (av[0] > 0.0) { double t = (rmax[i] + tolr[i] - u0[0]) / av[0]; if (t < lr) lr = t; }
+            else if (av[0] < 0.0) { double t = (rmin[i] - tolr[i] - u0[0]) / av[0]; if (t < lr) lr = t; }
+            if (lr < 0.0) lr = 0.0;
+            double th = orc_theta(gm, u0, av, pmin[i] - TOL * fabs(pmin[i]), lr);
+            if (th < lS) lS = th;
+            if (g_mortar_dbg) {
+                double *o = g_mortar_dbg + ((size_t)m * 3 * np + q) * 16;
+                o[0] = i; o[1] = lr; o[2] = th;
+                for (int v = 0; v < 4; ++v) { o[3 + v] = u0[v]; o[7 + v] = av[v]; }
+                o[11] = rmin[i]; o[12] = rmax[i]; o[13] = pmin[i]; o[14] = ni;
+            }
+        }
+        for (int q = 0; q < 3 * np; ++q) {
+            int i = gnode[q];
+            for (int v = 0; v < 4; ++v) corr[(size_t)v * nn + i] += lS * H[q][v];
+        }
+        if (g_mortar_ell) g_mortar_ell[m] = lS;
+        if (stats) {
+            stats[ST_AMORT_L] += 2.0 * halfL * (1.0 - lS);
+            stats[ST_L] += 2.0 * halfL;
+            if (lS < 1.0) stats[ST_NMORT] += 1;
+        }
+    }
+    /* limited residual and stage state; violations (R13) */
+    for (int i = 0; i < nn; ++i) {
+        double m = mass(c, i), q[4];
+        for (int v = 0; v < 4; ++v) {
+            res_out[(size_t)v * nn + i] = rfv[(size_t)v * nn + i] + acc[(size_t)v * nn + i] + corr[(size_t)v * nn + i];
+            q[v] = uvol[(size_t)v * nn + i] + dt / m * corr[(size_t)v * nn + i];
+            if (utilde) utilde[(size_t)v * nn + i] = q[v];
+        }
+        if (stats) {
+            double p = pressure(gm, q);
+            if (q[0] < rmin[i] - 1e-13 * fabs(rmin[i]) || q[0] > rmax[i] + 1e-13 * fabs(rmax[i])) stats[ST_VRHO] += 1;
+            if (p < pmin[i] - 1e-13 * fabs(pmin[i])) stats[ST_VP] += 1;
+            if (!(q[0] > 0.0) || !(p > 0.0)) stats[ST_NONPOS] += 1;
+            if (q[0] < stats[ST_MINRHO]) stats[ST_MINRHO] = q[0];
+            if (p < stats[ST_MINP]) stats[ST_MINP] = p;
+        }
+    }
+    free(mbad); free(gh); free(sf); free(rdg); free(rfv); free(ds); free(ufv); free(rmin); free(rmax); free(pmin);
+    free(A); free(Rp); free(Rm); free(tolr); free(exempt); free(ell); free(lmin); free(uvol); free(acc); free(corr);
+    return 0;
+}
+
+void orc_stats_init(double *stats) {
+    for (int k = 0; k < NSTAT; ++k) stats[k] = 0.0;
+    stats[ST_MINRHO] = INFINITY; stats[ST_MINP] = INFINITY;
+}
+
+/* residual per unit mass: rhs = res / m */
+int orc_rhs(const orc_ctx *c, const double *u, double time, double dt, int limiting, double beta,
+            double *rhs, double *stats) {
+    int rc = orc_stage(c, u, time, dt, limiting, beta, rhs, NULL, stats);
+    for (int i = 0; i < c->nn; ++i) {
+        double m = mass(c, i);
+        for (int v = 0; v < 4; ++v) rhs[(size_t)v * c->nn + i] /= m;
+    }
+    return rc;
+}
+
+/* SSP-RK3 (Shu-Osher) steps with dt recomputed from u^n every step (R10).
+   dt_hist receives each step's dt. */
+int orc_step(const orc_ctx *c, double *u, int nsteps, double *time, double cfl, int dt_rule,
+             int limiting, double beta, double *dt_hist, double *stats) {
+    size_t n = 4 * (size_t)c->nn;
+    double *u1 = malloc(sizeof(double) * n), *u2 = malloc(sizeof(double) * n), *ut = malloc(sizeof(double) * n);
+    double *res = malloc(sizeof(double) * n);
+    for (int s = 0; s < nsteps; ++s) {
+        double dt = orc_dt(c, u, *time, cfl, dt_rule);
+        if (dt_hist) dt_hist[s] = dt;
+        orc_stage(c, u, *time, dt, limiting, beta, res, ut, stats);
+        for (size_t k = 0; k < n; ++k) u1[k] = ut[k];
+        orc_stage(c, u1, *time + dt, dt, limiting, beta, res, ut, stats);
+        for (size_t k = 0; k < n; ++k) u2[k] = 0.75 * u[k] + 0.25 * ut[k];
+        orc_stage(c, u2, *time + 0.5 * dt, dt, limiting, beta, res, ut, stats);
+        for (size_t k = 0; k < n; ++k) u[k] = u[k] / 3.0 + 2.0 / 3.0 * ut[k];
+        *time += dt;
+    }
+    free(u1); free(u2); free(ut); free(res);
+    return 0;
+}
+
+/* discrete integrals sum_i m_i u_i (conservation) */
+void orc_integrals(const orc_ctx *c, const double *u, double *out) {
+    for (int v = 0; v < 4; ++v) {
+        double s = 0.0;
+        for (int i = 0; i < c->nn; ++i) s += mass(c, i) * u[(size_t)v * c->nn + i];
+        out[v] = s;
+    }
+}
+
+/* --- pieces exposed for the pins --------------------------------------- */
+
+/* high-order residual from the subcell fluxes (Eq. fluxdifferencingform) */
+void orc_dg_residual_fd(const orc_ctx *c, const double *u, double time, double *res) {
+    int np = c->np, N = c->N;
+    double *gh = make_ghosts(c, u, time);
+    double *sf = surface_fluxes(c, u, gh);
+    for (int e = 0; e < c->K; ++e)
+        for (int j = 0; j < np; ++j)
+            for (int i = 0; i < np; ++i) {
+                double fl[4], fr[4], fb[4], ft[4];
+                for (int v = 0; v < 4; ++v) {
+                    fl[v] = sf[((size_t)(4 * e + 0) * np + j) * 4 + v];
+                    fr[v] = sf[((size_t)(4 * e + 1) * np + j) * 4 + v];
+                    fb[v] = sf[((size_t)(4 * e + 2) * np + i) * 4 + v];
+                    ft[v] = sf[((size_t)(4 * e + 3) * np + i) * 4 + v];
+                }
+                if (i > 0) dg_subcell_flux(c, u, e, 0, j, i - 1, fl);
+                if (i < N) dg_subcell_flux(c, u, e, 0, j, i, fr);
+                if (j > 0) dg_subcell_flux(c, u, e, 1, i, j - 1, fb);
+                if (j < N) dg_subcell_flux(c, u, e, 1, i, j, ft);
+                for (int v = 0; v < 4; ++v)
+                    res[(size_t)v * c->nn + gidx(c, e, i, j)] = c->w[j] * (fl[v] - fr[v]) + c->w[i] * (fb[v] - ft[v]);
+            }
+    free(gh); free(sf);
+}
+
+/* low-order residual (mass-weighted) and sum_j 2 d_ij per node */
+void orc_fv_residual(const orc_ctx *c, const double *u, double time, double *res, double *dsum) {
+    double *gh = make_ghosts(c, u, time);
+    fv_residual(c, u, gh, res, dsum);
+    free(gh);
+}
+
+/* high-order residual (mass-weighted, Eq. evolutionformula) */
+void orc_dg_residual(const orc_ctx *c, const double *u, double time, double *res) {
+    double *gh = make_ghosts(c, u, time);
+    double *sf = surface_fluxes(c, u, gh);
+    dg_residual(c, u, sf, res);
+    free(gh); free(sf);
+}
+
+/* node masses */
+void orc_masses(const orc_ctx *c, double *m) { for (int i = 0; i < c->nn; ++i) m[i] = mass(c, i); }
+
+/* single-mortar low-order fluxes for a pin: large-side states uL[np][4],
+   small states us[2np][4]; outputs outward mass-weighted fluxes Flo[3np][4]
+   (large first) with unit face half-length, normal +x, large on the left. */
+void orc_mortar_sparse(int N, double g, const double *uL, const double *us, double *Flo) {
+    double xi[NPMAX], w[NPMAX], D[NPMAX * NPMAX], S[NPMAX * NPMAX], wt[NPMAX * 2 * NPMAX], I[2 * NPMAX * NPMAX], P[NPMAX * 2 * NPMAX];
+    int np = N + 1;
+    orc_operators(N, 0, xi, w, D, S, wt, I, P);
+    for (int k = 0; k < 12 * NPMAX; ++k) Flo[k] = 0.0;
+    for (int k = 0; k < np; ++k)
+        for (int q = 0; q < 2 * np; ++q) {
+            double ww = wt[k * 2 * np + q];
+            if (ww <= 0.0) continue;
+            double fi[4], fj[4];
+            flux_n(g, uL + 4 * k, 1.0, 0.0, fi); flux_n(g, us + 4 * q, 1.0, 0.0, fj);
+            double lam = lambda_max(g, uL + 4 * k, us + 4 * q, 1.0, 0.0);
+            for (int v = 0; v < 4; ++v) {
+                Flo[4 * k + v] += 0.5 * ww * ((fi[v] + fj[v]) - lam * (us[4 * q + v] - uL[4 * k + v]));
+                Flo[4 * (np + q) + v] += 0.5 * ww * (-(fi[v] + fj[v]) - lam * (uL[4 * k + v] - us[4 * q + v]));
+            }
+        }
+}
