@@ -1,0 +1,217 @@
+/*
+ * idp_dgsem.h -- C ABI of the B300 (sm_103a) implementation of the
+ * right-hand side and SSP Runge-Kutta step of the invariant-domain-preserving
+ * (IDP) LGL-DGSEM for the 2D compressible Euler equations on 2:1-balanced
+ * Cartesian quadtrees with hanging nodes (Bolm, Rueda-Ramirez, Kuzmin,
+ * Gassner, arXiv 2607.06045).
+ *
+ * The problem statement follows the paper: a conservation law on a domain
+ * with an initial condition and boundary conditions (Sec. 2, Eq.
+ * conservationlaw), a quadtree whose leaves are the elements (Sec. 3.1) and
+ * whose face neighbours differ by at most one level (Sec. 2.2), a polynomial
+ * degree N and the ratio of specific heats gamma (Sec. 3).
+ *
+ * Conventions shared by every entry point:
+ *  - All functions return an idp_status; none aborts, traps or prints, and no
+ *    C++ exception crosses the interface.
+ *  - State arrays are caller-owned DEVICE pointers to contiguous FP64 data in
+ *    the layout u[4][K][N+1][N+1]: variable (rho, rho v1, rho v2, E), then
+ *    element in the caller's leaf order (batched contexts concatenate the
+ *    simulations along K), then node j (y) and node i (x, fastest), the local
+ *    node ordering of Sec. 2.1. u must be 8-byte aligned.
+ *  - `stream` is a cudaStream_t passed as void* (NULL: the legacy default
+ *    stream). Work is enqueued asynchronously on it; conditions detected on
+ *    the device (invalid input state, bound violations) are reported by the
+ *    next synchronising call: idp_dgsem_step, idp_dgsem_step_host,
+ *    idp_dgsem_sync or idp_dgsem_limiter_stats.
+ *  - One context is used by one stream at a time; calls that overlap on the
+ *    GPU through the same context race on its scratch buffers.
+ */
+#ifndef IDP_DGSEM_H
+#define IDP_DGSEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IDP_OK = 0,
+    IDP_E_ARG = 1,        /* invalid argument (NULL pointer, N out of range, bad option) */
+    IDP_E_MESH = 2,       /* leaves overlap, leave a gap, lie outside the grid or are not 2:1 */
+    IDP_E_CUDA = 3,       /* a CUDA runtime call failed */
+    IDP_E_STATE = 4,      /* input state has rho <= 0, p <= 0 or a non-finite entry */
+    IDP_E_DT = 5,         /* no admissible time step (e.g. zero wave speed everywhere) */
+    IDP_E_NUMERIC = 6,    /* a limited stage left a bound violated beyond tolerance */
+    IDP_E_TIMEOUT = 7,    /* reserved for bounded device waits */
+    IDP_E_UNSUPPORTED = 8 /* option combination not built */
+} idp_status;
+
+/* Boundary kinds per domain side (Sec. 3.5 describes the double Mach
+ * reflection boundaries in words; ghost states are used in the LLF flux and
+ * in the bar states):
+ *  PERIODIC  the opposite side (both sides of a direction must be periodic);
+ *  WALL      reflecting slip wall: ghost = interior state with the normal
+ *            momentum mirrored;
+ *  DIRICHLET ghost = bc_prim[side] (rho, v1, v2, p);
+ *  OUTFLOW   ghost = interior state;
+ *  DMR       double Mach reflection: side -x post-shock Dirichlet, +x
+ *            outflow, -y post-shock Dirichlet for x < 1/6 and wall
+ *            otherwise, +y post-shock for x < 1/6 + (y1 + 20 t)/sqrt(3) and
+ *            pre-shock otherwise (states dmr_post and dmr_pre). */
+typedef enum {
+    IDP_BC_PERIODIC = 0,
+    IDP_BC_WALL = 1,
+    IDP_BC_DIRICHLET = 2,
+    IDP_BC_OUTFLOW = 3,
+    IDP_BC_DMR = 4
+} idp_bc;
+
+/* A quadtree mesh: an nx0 x ny0 level-0 grid over [x0,x1] x [y0,y1]; leaf e
+ * has level level[e] and integer position (ix[e], iy[e]) on the level-l grid
+ * of (nx0 2^l) x (ny0 2^l) cells. All arrays are HOST memory owned by the
+ * caller and copied at create time. */
+typedef struct {
+    int32_t nx0, ny0;
+    double x0, y0, x1, y1;
+    int32_t n_leaves;
+    const int8_t *level;
+    const int32_t *ix;
+    const int32_t *iy;
+    int32_t bc[4];          /* idp_bc for sides -x, +x, -y, +y */
+    double bc_prim[4][4];   /* DIRICHLET primitive state per side */
+    double dmr_post[4];     /* DMR post-shock primitive state */
+    double dmr_pre[4];      /* DMR pre-shock primitive state */
+} idp_mesh_desc;
+
+/* Method options (Sec. 2.3 and Sec. 3):
+ *  precision  0: all arithmetic FP64; 1: FP32 form -- node primitives, two-
+ *             point volume fluxes, subcell and face fluxes in FP32; bounds,
+ *             limiter solves, blending, stage update and all sums in FP64.
+ *  limiting   0: none (high-order DG); 1: positivity limiting
+ *             (Eq. Bounds_Positivity); 2: local limiting -- bar-state density
+ *             bounds (Eq. Bounds_Barstates, density part) plus positivity.
+ *  bounds     0: bar-state bounds (the only kind built).
+ *  dt_rule    0: IDP restriction (Eq. timestep_restriction); 1: low-order
+ *             CFL estimate (Eq. CFLcondition_lowordermethod).
+ *  beta       positivity factor of Eq. Bounds_Positivity (paper: 0.1).
+ *  cfl        dt = cfl * (rule's limit).
+ *  mortar_projection  0: LGL-weighted adjoint of the interpolation; 1: exact
+ *             L2 projection (default) for the high-order mortar flux.
+ *  elems_per_block  0: autotune; else elements per thread block.
+ *  collect_stats    1: accumulate limiter statistics (idp_limiter_stats). */
+typedef struct {
+    int32_t precision;
+    int32_t limiting;
+    int32_t bounds;
+    int32_t dt_rule;
+    double beta;
+    double cfl;
+    int32_t mortar_projection;
+    int32_t elems_per_block;
+    int32_t collect_stats;
+    int32_t reserved;
+} idp_options;
+
+/* Limiter statistics accumulated over the stages since the previous call of
+ * idp_dgsem_limiter_stats (Sec. 3: weighted averages of the limiting factors
+ * alpha = 1 - l over elements and over mortars). */
+typedef struct {
+    double alpha_volume_mean;   /* mass-weighted mean of 1 - min_k l_ik over nodes */
+    double alpha_mortar_mean;   /* face-length-weighted mean of alpha_S over mortars */
+    int64_t n_stages;
+    int64_t n_volume_active;    /* node-stages with alpha > 0 */
+    int64_t n_mortar_active;    /* mortar-stages with alpha_S > 0 */
+    int64_t n_mortar_fallback;  /* mortar-stages whose interpolated states were inadmissible */
+    int64_t n_viol_density;     /* node-stages outside [rho_min, rho_max] beyond 1e-13 relative */
+    int64_t n_viol_pressure;    /* node-stages with p < p_min beyond 1e-13 relative */
+    int64_t n_nonpositive;      /* node-stages with rho <= 0 or p <= 0 */
+    int64_t n_dt_exceed;        /* node-stages with dt sum_j 2 d_ij / m_i > 1 */
+    double min_rho, min_p;      /* over limited stage states */
+} idp_limiter_stats;
+
+typedef struct idp_ctx idp_ctx;
+
+/* Fill *o with the defaults: FP64, local limiting, bar-state bounds, IDP dt,
+ * beta 0.1, cfl 0.5, exact L2 projection, autotuned blocks, stats on. */
+idp_status idp_options_default(idp_options *o);
+
+/* Build a context for one mesh (the paper's Sec. 2.1-2.3): validates the leaves
+ * (IDP_E_MESH when they overlap, leave a gap or are not 2:1 face-balanced),
+ * builds the conforming-face, boundary and mortar lists, the LGL operators
+ * (nodes, weights, Sbar = 2 Qbar - Bbar), the local mortar weights
+ * (Eq. local_weights) and the mortar interpolation/projection, and uploads
+ * them to the current CUDA device. 1 <= N <= 7. opts may be NULL (defaults).
+ * On success *ctx owns all device tables and scratch; free with
+ * idp_dgsem_destroy. */
+idp_status idp_dgsem_create(const idp_mesh_desc *mesh, int32_t N, double gamma,
+                            const idp_options *opts, idp_ctx **ctx);
+
+/* As idp_dgsem_create for n_sims independent meshes that are advanced
+ * together; their elements are concatenated in the given order and every
+ * simulation keeps its own time step and time. */
+idp_status idp_dgsem_create_batch(const idp_mesh_desc *meshes, int32_t n_sims, int32_t N,
+                                  double gamma, const idp_options *opts, idp_ctx **ctx);
+
+/* Sizes: total elements, mortars, simulations; sim_elem_offsets (host,
+ * n_sims + 1 entries, may be NULL) receives the first element of each
+ * simulation. */
+idp_status idp_dgsem_layout(const idp_ctx *ctx, int64_t *n_elems, int64_t *n_mortars,
+                            int32_t *n_sims, int64_t *sim_elem_offsets);
+
+/* Right-hand side at time t (Eq. evolutionformula with the limited fluxes of
+ * Sec. 2.3). dt == 0: the unlimited high-order DG right-hand side du/dt.
+ * dt > 0: the limited forward-Euler increment (u_lim - u)/dt of one
+ * FCT stage, u_lim = u_FV + dt/m (sum of limited antidiffusive fluxes),
+ * which depends on dt because the limiter bounds do (Sec. 3.2). The same dt
+ * is used for every simulation of a batch. u and rhs: device, layout above,
+ * must not alias. */
+idp_status idp_dgsem_rhs(idp_ctx *ctx, const double *u, double t, double dt, double *rhs,
+                         void *stream);
+
+/* Time step of each simulation for state u at time t under the context's
+ * dt_rule and cfl; dt_host receives n_sims values (synchronises the stream). */
+idp_status idp_dgsem_dt(idp_ctx *ctx, const double *u, const double *t_host, double *dt_host,
+                        void *stream);
+
+/* n_steps SSP-RK3 steps (Shu-Osher form, Sec. 3) in place on the device
+ * state u. Each step computes its own dt from u^n (dt_rule, cfl). t_host
+ * (n_sims values, in/out) holds each simulation's time; dt_last_host (may be
+ * NULL) receives the last dt per simulation. Synchronises the stream at the
+ * end and returns IDP_E_STATE or IDP_E_NUMERIC if the device flagged an
+ * invalid state or a bound violation. */
+idp_status idp_dgsem_step(idp_ctx *ctx, double *u, int32_t n_steps, double *t_host,
+                          double *dt_last_host, void *stream);
+
+/* As idp_dgsem_step for a HOST state array: copies u_host to the device,
+ * steps, and copies the result back (u_host should be page-locked for
+ * asynchronous copies). */
+idp_status idp_dgsem_step_host(idp_ctx *ctx, double *u_host, int32_t n_steps, double *t_host,
+                               double *dt_last_host, void *stream);
+
+/* Discrete integrals sum_i m_i u_i per simulation and variable (the
+ * conserved totals of Eq. conservationProperty), out_host[n_sims][4], summed
+ * in a fixed order (deterministic). Synchronises the stream. */
+idp_status idp_dgsem_integrals(idp_ctx *ctx, const double *u, double *out_host, void *stream);
+
+/* Read and reset the accumulated limiter statistics (synchronises). */
+idp_status idp_dgsem_limiter_stats(idp_ctx *ctx, idp_limiter_stats *out, void *stream);
+
+/* Synchronise the stream and report any device-flagged condition. */
+idp_status idp_dgsem_sync(idp_ctx *ctx, void *stream);
+
+void idp_dgsem_destroy(idp_ctx *ctx);
+
+const char *idp_status_str(idp_status s);
+
+/* The CUDA error behind the calling thread's most recent IDP_E_CUDA: the
+ * failing step and cudaGetErrorString text ("" if none). Diagnostics only;
+ * the string is owned by the library. */
+const char *idp_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDP_DGSEM_H */

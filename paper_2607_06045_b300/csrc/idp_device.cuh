@@ -1,0 +1,277 @@
+// idp_device.cuh -- device data structures and point functions of the IDP
+// LGL-DGSEM right-hand side (arXiv 2607.06045, Sec. 2) for sm_103a.
+//
+// Arithmetic types: every routine is templated on the flux type FT (double
+// for the FP64 path, float for the FP32 form). Bounds, limiter solves,
+// blending and sums always use double.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+namespace idp {
+
+constexpr int NPMAX = 8;          // N <= 7
+constexpr double kTol = 1e-14;    // limiter relaxation / exemption (reading R15)
+constexpr double kViolTol = 1e-13;  // violation tolerance (reading R13)
+
+// Face kinds of an element side (-x, +x, -y, +y).
+enum : int { FT_CONF = 0, FT_BND = 1, FT_MLARGE = 2, FT_MSLO = 3, FT_MSHI = 4 };
+// Boundary kinds (idp_bc)
+enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_DIRICHLET = 2, BC_OUTFLOW = 3, BC_DMR = 4 };
+// status bits
+enum : unsigned { ST_BAD_INPUT = 1u, ST_VIOLATION = 2u, ST_NONFINITE = 4u };
+
+// Element geometry: x = left edge, y = bottom edge, z = dx, w = dy.
+struct __align__(32) Geo {
+    double x, y, z, w;
+};
+
+// Reference operators for NP = N + 1 nodes (Sec. 2.1, App. A).
+struct Ops {
+    double xi[NPMAX];                // LGL nodes
+    double w[NPMAX];                 // LGL weights
+    double S[NPMAX][NPMAX];          // Sbar = 2 Qbar - Bbar
+    double wt[NPMAX][2 * NPMAX];     // local mortar weights (reference units)
+    double I[2 * NPMAX][NPMAX];      // interpolation large -> small-face nodes
+    double P[NPMAX][2 * NPMAX];      // projection small-face fluxes -> large
+};
+
+// Per simulation: boundary data (ghost states as conserved variables).
+struct SimInfo {
+    int32_t bc[4];
+    int32_t pad[4];
+    double bc_cons[4][4];
+    double dmr_post[4];
+    double dmr_pre[4];
+    double y1;
+    double pad2;
+};
+
+// Limiter statistics accumulators (device).
+struct StatsAcc {
+    double alpha_vol_m, mass, alpha_mort_len, len;
+    unsigned long long n_vol, n_mort, n_fallback, n_vrho, n_vp, n_nonpos, n_dtx, n_stages;
+    unsigned long long min_rho_bits, min_p_bits;   // positive doubles as ordered bits
+};
+
+struct MeshDev {
+    int K, M, n_sims, n_mnodes;
+    const Geo *geom;          // per element: x_left, y_bottom, dx, dy
+    const int32_t *sim;       // per element
+    const int4 *fnbr;         // per element and side: neighbour element / mortar id / -1
+    const uchar4 *ftype;      // per element and side: FT_*
+    const int32_t *m_large;   // per mortar
+    const int2 *m_small;      // per mortar: lower, upper small element
+    const int32_t *m_info;    // per mortar: dir | (large_is_low << 1)
+    const SimInfo *siminfo;
+    const int32_t *mn_node;   // unique mortar nodes: global node index
+    const int2 *mn_slot;      // their (first, second or -1) slot
+};
+
+// Per-mortar-node scratch ("slots", index m * 3NP + q, large nodes first,
+// then the lower and upper small element's face nodes).
+struct SlotsDev {
+    int S;                    // M * 3NP
+    double *chi, *clo;        // [4][S] high/low-order contribution to m du/dt
+    double *rbmin, *rbmax;    // bar-state density min/max over cross-mortar pairs
+    double *dsum;             // sum_j 2 d_ij over cross-mortar pairs
+    double *uvol, *un;        // [4][S] state after the volume step / at step start
+    double *rmin, *rmax, *pmin, *tol, *mass;
+    float *nmort;             // n_i
+    int32_t *bad;             // per mortar: interpolated state inadmissible
+    double *ell;              // per mortar l_S
+};
+
+// ---------------------------------------------------------------------------
+// point functions
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double pressure_d(double g, double r, double m1, double m2, double E) {
+    return (g - 1.0) * (E - 0.5 * (m1 * m1 + m2 * m2) / r);
+}
+
+// Logarithmic mean {a}_ln = (a - b)/(ln a - ln b) from per-node logarithms,
+// with the Ismail-Roe series (a + b)/(2 F(u)), u = ((a-b)/(a+b))^2, for small u.
+template <typename FT> struct LogMean;
+
+template <> struct LogMean<double> {
+    __device__ __forceinline__ static double mean(double a, double b, double la, double lb) {
+        double d = a - b, s = a + b;
+        if (d * d < 1e-4 * (s * s)) {
+            double u = (d * d) / (s * s);
+            double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
+            return s / (2.0 * F);
+        }
+        return d / (la - lb);
+    }
+    // 1 / {a}_ln
+    __device__ __forceinline__ static double inv_mean(double a, double b, double la, double lb) {
+        double d = a - b, s = a + b;
+        if (d * d < 1e-4 * (s * s)) {
+            double u = (d * d) / (s * s);
+            double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
+            return (2.0 * F) / s;
+        }
+        return (la - lb) / d;
+    }
+};
+
+template <> struct LogMean<float> {
+    // FP32 form: ln(a/b) per pair keeps the relative error near 1e-7 even for
+    // near-vacuum magnitudes; the series takes over below u = 1e-2.
+    __device__ __forceinline__ static float mean(float a, float b, float, float) {
+        float d = a - b, s = a + b;
+        if (d * d < 1e-2f * (s * s)) {
+            float u = (d * d) / (s * s);
+            float F = 1.0f + u * (1.0f / 3.0f + u * (1.0f / 5.0f + u * (1.0f / 7.0f)));
+            return s / (2.0f * F);
+        }
+        return d / logf(a / b);
+    }
+    __device__ __forceinline__ static float inv_mean(float a, float b, float, float) {
+        float d = a - b, s = a + b;
+        if (d * d < 1e-2f * (s * s)) {
+            float u = (d * d) / (s * s);
+            float F = 1.0f + u * (1.0f / 3.0f + u * (1.0f / 5.0f + u * (1.0f / 7.0f)));
+            return (2.0f * F) / s;
+        }
+        return logf(a / b) / d;
+    }
+};
+
+// Node primitives in the flux type.
+template <typename FT> struct Prim {
+    FT rho, v1, v2, p, c, E, lr, lb, beta;
+};
+
+// Ranocha's entropy-conserving, kinetic-energy-preserving two-point flux
+// along axis d (reading R1; the paper names it in Sec. 3).
+template <typename FT>
+__device__ __forceinline__ void ranocha(const Prim<FT> &a, const Prim<FT> &b, int d, FT ginv1, FT f[4]) {
+    FT rho_ln = LogMean<FT>::mean(a.rho, b.rho, a.lr, b.lr);
+    FT ibeta = LogMean<FT>::inv_mean(a.beta, b.beta, a.lb, b.lb);   // 1/{rho/p}_ln
+    FT v1m = FT(0.5) * (a.v1 + b.v1), v2m = FT(0.5) * (a.v2 + b.v2), pm = FT(0.5) * (a.p + b.p);
+    FT vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
+    FT fr = rho_ln * (FT(0.5) * (vna + vnb));
+    f[0] = fr;
+    f[1] = fr * v1m + (d == 0 ? pm : FT(0));
+    f[2] = fr * v2m + (d == 1 ? pm : FT(0));
+    f[3] = fr * (FT(0.5) * (a.v1 * b.v1 + a.v2 * b.v2) + ibeta * ginv1) + FT(0.5) * (a.p * vnb + b.p * vna);
+}
+
+// Physical flux along axis d from conserved momentum/energy and primitives.
+template <typename FT>
+__device__ __forceinline__ void phys_flux(FT m1, FT m2, FT E, FT p, FT vn, int d, FT f[4]) {
+    f[0] = (d == 0 ? m1 : m2);
+    f[1] = m1 * vn + (d == 0 ? p : FT(0));
+    f[2] = m2 * vn + (d == 1 ? p : FT(0));
+    f[3] = (E + p) * vn;
+}
+
+// Primitive state from a conserved state (double input).
+template <typename FT>
+__device__ __forceinline__ Prim<FT> make_prim(double g, double r, double m1, double m2, double E, bool logs) {
+    Prim<FT> q;
+    double v1 = m1 / r, v2 = m2 / r;
+    double p = (g - 1.0) * (E - 0.5 * (m1 * v1 + m2 * v2));
+    q.rho = (FT)r; q.v1 = (FT)v1; q.v2 = (FT)v2; q.p = (FT)p; q.E = (FT)E;
+    q.c = sqrt((FT)g * q.p / q.rho);
+    q.beta = q.rho / q.p;
+    if (logs) { q.lr = log(q.rho); q.lb = log(q.beta); } else { q.lr = q.lb = FT(0); }
+    return q;
+}
+
+// Local Lax-Friedrichs flux along axis d with the Davis wave speed (R3);
+// returns lambda.
+template <typename FT>
+__device__ __forceinline__ FT llf(const double uL[4], const double uR[4], double g, int d, FT f[4]) {
+    Prim<FT> a = make_prim<FT>(g, uL[0], uL[1], uL[2], uL[3], false);
+    Prim<FT> b = make_prim<FT>(g, uR[0], uR[1], uR[2], uR[3], false);
+    FT vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
+    FT la = fabs(vna) + a.c, lb = fabs(vnb) + b.c;
+    FT lam = la > lb ? la : lb;
+    FT fa[4], fb[4];
+    phys_flux<FT>((FT)uL[1], (FT)uL[2], (FT)uL[3], a.p, vna, d, fa);
+    phys_flux<FT>((FT)uR[1], (FT)uR[2], (FT)uR[3], b.p, vnb, d, fb);
+    for (int v = 0; v < 4; ++v) f[v] = FT(0.5) * (fa[v] + fb[v]) - FT(0.5) * lam * ((FT)uR[v] - (FT)uL[v]);
+    return lam;
+}
+
+// Reading R8: largest theta in [0, hi] such that u0 + theta a has rho > 0 and
+// p >= pmin; the admissible set is convex so the feasible thetas form an
+// interval [0, theta*]. g(theta) = (gamma-1)(rho E - |m|^2/2) - pmin rho.
+__device__ __forceinline__ double theta_max(double g, const double u0[4], const double a[4], double pmin, double hi) {
+    if (!(hi > 0.0)) return 0.0;
+    double c0 = (g - 1.0) * (u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2])) - pmin * u0[0];
+    if (!(c0 > 0.0) || !(u0[0] > 0.0)) return 0.0;
+    double c1 = (g - 1.0) * (u0[0] * a[3] + a[0] * u0[3] - (u0[1] * a[1] + u0[2] * a[2])) - pmin * a[0];
+    double c2 = (g - 1.0) * (a[0] * a[3] - 0.5 * (a[1] * a[1] + a[2] * a[2]));
+    double rho_hi = u0[0] + hi * a[0];
+    double g_hi = c0 + hi * (c1 + hi * c2);
+    if (rho_hi > 0.0 && g_hi >= 0.0) return hi;
+    double root = INFINITY;
+    if (c2 == 0.0) {
+        if (c1 < 0.0) root = -c0 / c1;
+    } else {
+        double disc = c1 * c1 - 4.0 * c2 * c0;
+        if (disc >= 0.0) {
+            double sq = sqrt(disc);
+            double q = -0.5 * (c1 + (c1 >= 0.0 ? sq : -sq));
+            double r1 = q / c2, r2 = c0 / q;
+            if (r1 > 0.0 && r1 < root) root = r1;
+            if (r2 > 0.0 && r2 < root) root = r2;
+        }
+    }
+    double th = root < hi ? root * (1.0 - 1e-12) : hi;
+    if (a[0] < 0.0) {
+        double tr = -u0[0] / a[0];
+        if (th >= tr) th = 0.5 * tr;
+    }
+    if (!(th > 0.0)) return 0.0;
+    for (int it = 0; it < 4; ++it) {
+        double v0 = u0[0] + th * a[0], v1 = u0[1] + th * a[1], v2 = u0[2] + th * a[2], v3 = u0[3] + th * a[3];
+        if (v0 > 0.0 && pressure_d(g, v0, v1, v2, v3) >= pmin * (1.0 - 1e-13)) return th;
+        th *= 0.5;
+    }
+    return 0.0;
+}
+
+// Ghost state across boundary side s (reading R4). in: interior conserved
+// state at the face node, x: its x coordinate, t: time.
+__device__ __forceinline__ void ghost_state(const SimInfo &si, int s, const double in[4], double x, double t,
+                                            double gst[4]) {
+    int kind = si.bc[s];
+    const double *dir = nullptr;
+    if (kind == BC_DMR) {
+        if (s == 0) dir = si.dmr_post;
+        else if (s == 1) kind = BC_OUTFLOW;
+        else if (s == 2) { if (x < 1.0 / 6.0) dir = si.dmr_post; else kind = BC_WALL; }
+        else dir = (x < 1.0 / 6.0 + (si.y1 + 20.0 * t) / sqrt(3.0)) ? si.dmr_post : si.dmr_pre;
+        if (dir) kind = BC_DIRICHLET;
+    } else if (kind == BC_DIRICHLET) {
+        dir = si.bc_cons[s];
+    }
+    if (kind == BC_WALL) {
+        double nx = s == 0 ? -1.0 : (s == 1 ? 1.0 : 0.0), ny = s == 2 ? -1.0 : (s == 3 ? 1.0 : 0.0);
+        double mn = in[1] * nx + in[2] * ny;
+        gst[0] = in[0]; gst[1] = in[1] - 2.0 * mn * nx; gst[2] = in[2] - 2.0 * mn * ny; gst[3] = in[3];
+    } else if (kind == BC_DIRICHLET) {
+        for (int v = 0; v < 4; ++v) gst[v] = dir[v];
+    } else {
+        for (int v = 0; v < 4; ++v) gst[v] = in[v];
+    }
+}
+
+// local face-node coordinates (i, j) of face index t on side s
+template <int NP>
+__device__ __forceinline__ int face_node(int s, int t) {
+    int i = s == 0 ? 0 : (s == 1 ? NP - 1 : t);
+    int j = s == 2 ? 0 : (s == 3 ? NP - 1 : t);
+    return j * NP + i;
+}
+
+__device__ __forceinline__ unsigned long long dbits(double x) { return (unsigned long long)__double_as_longlong(x); }
+
+}  // namespace idp

@@ -1,0 +1,904 @@
+// idp_host.cu -- host runtime of the IDP LGL-DGSEM library: reference
+// operators, quadtree mesh builder and validation, device tables, stage
+// sequencing with CUDA graphs, the elements-per-block autotuner and the C ABI
+// declared in include/idp_dgsem.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/idp_dgsem.h"
+#include "idp_launch.cuh"
+
+using namespace idp;
+
+// ---------------------------------------------------------------------------
+// reference operators (Sec. 2.1, App. A)
+// ---------------------------------------------------------------------------
+namespace {
+
+// Legendre P_n(x) and P_{n-1}(x) by the three-term recurrence.
+void legendre_pair(int n, double x, double &pn, double &pnm1) {
+    double a = 1.0, b = x;
+    if (n == 0) { pn = 1.0; pnm1 = 0.0; return; }
+    for (int k = 1; k < n; ++k) {
+        double c = ((2.0 * k + 1.0) * x * b - k * a) / (k + 1.0);
+        a = b;
+        b = c;
+    }
+    pn = b;
+    pnm1 = a;
+}
+
+// LGL nodes: the roots of q = P_{N+1} - P_{N-1}, which vanishes at +-1 and at
+// the roots of P_N' (since (2N+1)(x^2-1) P_N' = N(N+1)(P_{N+1} - P_{N-1})),
+// found by Newton with q' = (2N+1) P_N; weights 2 / (N (N+1) P_N^2).
+void lgl_nodes(int N, double *x, double *w) {
+    x[0] = -1.0;
+    x[N] = 1.0;
+    for (int k = 1; k < N; ++k) {
+        double t = -std::cos(M_PI * k / N);
+        for (int it = 0; it < 200; ++it) {
+            double pNp1, pN, pNm1, tmp;
+            legendre_pair(N + 1, t, pNp1, pN);
+            legendre_pair(N - 1, t, pNm1, tmp);
+            double q = pNp1 - pNm1, dq = (2.0 * N + 1.0) * pN;
+            double step = q / dq;
+            t -= step;
+            if (std::fabs(step) < 1e-17) break;
+        }
+        x[k] = t;
+    }
+    for (int k = 0; k <= N; ++k) {
+        double pN, pNm1;
+        legendre_pair(N, x[k], pN, pNm1);
+        w[k] = 2.0 / (N * (N + 1.0) * pN * pN);
+    }
+}
+
+// Barycentric weights and Lagrange basis values at s.
+void bary_weights(int np, const double *x, double *lam) {
+    for (int j = 0; j < np; ++j) {
+        double p = 1.0;
+        for (int k = 0; k < np; ++k)
+            if (k != j) p *= (x[j] - x[k]);
+        lam[j] = 1.0 / p;
+    }
+}
+
+void bary_basis(int np, const double *x, const double *lam, double s, double *phi) {
+    for (int j = 0; j < np; ++j)
+        if (s == x[j]) {
+            for (int k = 0; k < np; ++k) phi[k] = k == j ? 1.0 : 0.0;
+            return;
+        }
+    double den = 0.0;
+    for (int j = 0; j < np; ++j) den += lam[j] / (s - x[j]);
+    for (int j = 0; j < np; ++j) phi[j] = lam[j] / (s - x[j]) / den;
+}
+
+// Gauss-Jordan inverse of a small dense matrix (row-major), in place.
+bool invert(int n, double *A) {
+    std::vector<double> I(n * n, 0.0);
+    for (int i = 0; i < n; ++i) I[i * n + i] = 1.0;
+    for (int c = 0; c < n; ++c) {
+        int p = c;
+        for (int r = c + 1; r < n; ++r)
+            if (std::fabs(A[r * n + c]) > std::fabs(A[p * n + c])) p = r;
+        if (A[p * n + c] == 0.0) return false;
+        for (int k = 0; k < n; ++k) { std::swap(A[c * n + k], A[p * n + k]); std::swap(I[c * n + k], I[p * n + k]); }
+        double d = A[c * n + c];
+        for (int k = 0; k < n; ++k) { A[c * n + k] /= d; I[c * n + k] /= d; }
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            double f = A[r * n + c];
+            for (int k = 0; k < n; ++k) { A[r * n + k] -= f * A[c * n + k]; I[r * n + k] -= f * I[c * n + k]; }
+        }
+    }
+    std::memcpy(A, I.data(), sizeof(double) * n * n);
+    return true;
+}
+
+void build_ops(int N, int proj, Ops &o) {
+    std::memset(&o, 0, sizeof(o));
+    const int np = N + 1;
+    double x[NPMAX], w[NPMAX], lam[NPMAX];
+    lgl_nodes(N, x, w);
+    bary_weights(np, x, lam);
+    for (int i = 0; i < np; ++i) { o.xi[i] = x[i]; o.w[i] = w[i]; }
+    // D_ij = phi_j'(x_i) in barycentric form; Sbar = 2 diag(w) D - B
+    for (int i = 0; i < np; ++i) {
+        double diag = 0.0;
+        double D[NPMAX];
+        for (int j = 0; j < np; ++j) {
+            if (j == i) continue;
+            D[j] = (lam[j] / lam[i]) / (x[i] - x[j]);
+            diag -= D[j];
+        }
+        D[i] = diag;
+        for (int j = 0; j < np; ++j) {
+            double B = (i == j) ? (i == 0 ? -1.0 : (i == N ? 1.0 : 0.0)) : 0.0;
+            o.S[i][j] = 2.0 * w[i] * D[j] - B;
+        }
+    }
+    // local mortar weights: overlap of LGL subcells (App. A); subcells that
+    // touch only at a point do not overlap
+    double bl[NPMAX + 1], bs[2 * NPMAX + 1];
+    bl[0] = -1.0;
+    for (int k = 0; k < np; ++k) bl[k + 1] = bl[k] + w[k];
+    bs[0] = -1.0;
+    for (int e = 0; e < 2; ++e)
+        for (int l = 0; l < np; ++l) bs[e * np + l + 1] = (l == 0 ? (e == 0 ? -1.0 : 0.0) : bs[e * np + l]) + 0.5 * w[l];
+    for (int k = 0; k < np; ++k)
+        for (int e = 0; e < 2; ++e)
+            for (int l = 0; l < np; ++l) {
+                double lo0 = l == 0 ? (e == 0 ? -1.0 : 0.0) : bs[e * np + l];
+                double hi0 = bs[e * np + l + 1];
+                double lo = std::max(bl[k], lo0), hi = std::min(bl[k + 1], hi0);
+                o.wt[k][e * np + l] = (hi - lo > 1e-12) ? hi - lo : 0.0;
+            }
+    // interpolation to the small-face nodes s = (x_l -/+ 1) / 2
+    for (int e = 0; e < 2; ++e)
+        for (int l = 0; l < np; ++l) {
+            double phi[NPMAX];
+            bary_basis(np, x, lam, 0.5 * (x[l] + (e == 0 ? -1.0 : 1.0)), phi);
+            for (int k = 0; k < np; ++k) o.I[e * np + l][k] = phi[k];
+        }
+    if (proj == 0) {
+        for (int k = 0; k < np; ++k)
+            for (int c = 0; c < 2 * np; ++c) o.P[k][c] = 0.5 * w[c % np] * o.I[c][k] / w[k];
+    } else {
+        // exact L2 projection: M = (V V^T)^{-1} with V the orthonormal
+        // Legendre-Vandermonde matrix; P = M^{-1} B with
+        // B_{k,(e,l)} = int_half phi_k psi_l = 1/2 sum_m I_e[m][k] M[m][l]
+        std::vector<double> V(np * np), Minv(np * np, 0.0), M(np * np);
+        for (int i = 0; i < np; ++i)
+            for (int n = 0; n < np; ++n) {
+                double pn, pm;
+                legendre_pair(n, x[i], pn, pm);
+                V[i * np + n] = std::sqrt((2.0 * n + 1.0) / 2.0) * pn;
+            }
+        for (int i = 0; i < np; ++i)
+            for (int j = 0; j < np; ++j) {
+                double s = 0.0;
+                for (int n = 0; n < np; ++n) s += V[i * np + n] * V[j * np + n];
+                Minv[i * np + j] = s;
+            }
+        M = Minv;
+        invert(np, M.data());
+        for (int k = 0; k < np; ++k)
+            for (int e = 0; e < 2; ++e)
+                for (int l = 0; l < np; ++l) {
+                    double acc = 0.0;
+                    for (int j = 0; j < np; ++j) {
+                        double Bjl = 0.0;
+                        for (int m = 0; m < np; ++m) Bjl += 0.5 * o.I[e * np + m][j] * M[m * np + l];
+                        acc += Minv[k * np + j] * Bjl;
+                    }
+                    o.P[k][e * np + l] = acc;
+                }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// mesh
+// ---------------------------------------------------------------------------
+
+struct HostMesh {
+    std::vector<Geo> geom;
+    std::vector<int32_t> sim;
+    std::vector<int4> fnbr;
+    std::vector<uchar4> ftype;
+    std::vector<int32_t> m_large, m_info;
+    std::vector<int2> m_small;
+    std::vector<SimInfo> siminfo;
+    std::vector<long long> sim_off;
+};
+
+inline uint64_t leaf_key(int l, int64_t x, int64_t y) { return ((uint64_t)l << 58) | ((uint64_t)x << 29) | (uint64_t)y; }
+
+void prim_to_cons(double g, const double *p, double *q) {
+    q[0] = p[0];
+    q[1] = p[0] * p[1];
+    q[2] = p[0] * p[2];
+    q[3] = p[3] / (g - 1.0) + 0.5 * p[0] * (p[1] * p[1] + p[2] * p[2]);
+}
+
+idp_status build_mesh(const idp_mesh_desc &d, double gamma, int simid, HostMesh &H) {
+    if (d.nx0 < 1 || d.ny0 < 1 || d.n_leaves < 1 || !d.level || !d.ix || !d.iy) return IDP_E_ARG;
+    if (!(d.x1 > d.x0) || !(d.y1 > d.y0)) return IDP_E_ARG;
+    for (int s = 0; s < 4; ++s)
+        if (d.bc[s] < IDP_BC_PERIODIC || d.bc[s] > IDP_BC_DMR) return IDP_E_ARG;
+    if ((d.bc[0] == IDP_BC_PERIODIC) != (d.bc[1] == IDP_BC_PERIODIC)) return IDP_E_ARG;
+    if ((d.bc[2] == IDP_BC_PERIODIC) != (d.bc[3] == IDP_BC_PERIODIC)) return IDP_E_ARG;
+    const int K = d.n_leaves, base = (int)H.geom.size(), mbase = (int)H.m_large.size();
+    int Lmax = 0;
+    for (int e = 0; e < K; ++e) {
+        int l = d.level[e];
+        if (l < 0 || l > 24) return IDP_E_MESH;
+        Lmax = std::max(Lmax, l);
+    }
+    if (((int64_t)d.nx0 << Lmax) >= (1LL << 28) || ((int64_t)d.ny0 << Lmax) >= (1LL << 28)) return IDP_E_ARG;
+    std::unordered_map<uint64_t, int> tab;
+    tab.reserve((size_t)K * 2);
+    unsigned __int128 area = 0;
+    for (int e = 0; e < K; ++e) {
+        int l = d.level[e];
+        int64_t nx = (int64_t)d.nx0 << l, ny = (int64_t)d.ny0 << l;
+        if (d.ix[e] < 0 || d.iy[e] < 0 || d.ix[e] >= nx || d.iy[e] >= ny) return IDP_E_MESH;
+        if (!tab.emplace(leaf_key(l, d.ix[e], d.iy[e]), e).second) return IDP_E_MESH;   // duplicate
+        area += (unsigned __int128)1 << (2 * (Lmax - l));
+    }
+    if (area != ((unsigned __int128)d.nx0 * d.ny0) << (2 * Lmax)) return IDP_E_MESH;   // gap or overlap
+    for (int e = 0; e < K; ++e) {   // no leaf may contain another
+        int64_t x = d.ix[e], y = d.iy[e];
+        for (int l = d.level[e] - 1; l >= 0; --l) {
+            x >>= 1; y >>= 1;
+            if (tab.count(leaf_key(l, x, y))) return IDP_E_MESH;
+        }
+    }
+    auto find = [&](int l, int64_t x, int64_t y) {
+        auto it = tab.find(leaf_key(l, x, y));
+        return it == tab.end() ? -1 : it->second;
+    };
+    for (int e = 0; e < K; ++e) {
+        int l = d.level[e];
+        double dx = (d.x1 - d.x0) / ((double)d.nx0 * (double)(1LL << l));
+        double dy = (d.y1 - d.y0) / ((double)d.ny0 * (double)(1LL << l));
+        Geo g;
+        g.x = d.x0 + d.ix[e] * dx; g.y = d.y0 + d.iy[e] * dy; g.z = dx; g.w = dy;
+        H.geom.push_back(g);
+        H.sim.push_back(simid);
+        H.fnbr.push_back(make_int4(-1, -1, -1, -1));
+        H.ftype.push_back(make_uchar4(FT_BND, FT_BND, FT_BND, FT_BND));
+    }
+    std::vector<char> pending((size_t)K * 4, 0);
+    for (int e = 0; e < K; ++e) {
+        int l = d.level[e];
+        int64_t nxl = (int64_t)d.nx0 << l, nyl = (int64_t)d.ny0 << l;
+        for (int s = 0; s < 4; ++s) {
+            int64_t qx = d.ix[e] + (s == 0 ? -1 : (s == 1 ? 1 : 0));
+            int64_t qy = d.iy[e] + (s == 2 ? -1 : (s == 3 ? 1 : 0));
+            bool outside = qx < 0 || qx >= nxl || qy < 0 || qy >= nyl;
+            int kind = FT_BND, nb = -1;
+            if (!outside || d.bc[s] == IDP_BC_PERIODIC) {
+                qx = (qx + nxl) % nxl;
+                qy = (qy + nyl) % nyl;
+                int f = find(l, qx, qy);
+                if (f >= 0) { kind = FT_CONF; nb = base + f; }
+                else if (l > 0 && find(l - 1, qx >> 1, qy >> 1) >= 0) { pending[(size_t)e * 4 + s] = 1; continue; }
+                else {
+                    int64_t ax, ay, bx, by;
+                    if (s < 2) { ax = bx = 2 * qx + (s == 0 ? 1 : 0); ay = 2 * qy; by = 2 * qy + 1; }
+                    else { ay = by = 2 * qy + (s == 2 ? 1 : 0); ax = 2 * qx; bx = 2 * qx + 1; }
+                    int a = find(l + 1, ax, ay), b = find(l + 1, bx, by);
+                    if (a < 0 || b < 0) return IDP_E_MESH;   // not 2:1 balanced
+                    int m = (int)H.m_large.size();
+                    int low = (s == 1 || s == 3) ? 1 : 0;
+                    H.m_large.push_back(base + e);
+                    H.m_small.push_back(make_int2(base + a, base + b));
+                    H.m_info.push_back((s >> 1) | (low << 1));
+                    kind = FT_MLARGE;
+                    nb = m;
+                }
+            }
+            int4 &n4 = H.fnbr[base + e];
+            uchar4 &t4 = H.ftype[base + e];
+            (s == 0 ? n4.x : s == 1 ? n4.y : s == 2 ? n4.z : n4.w) = nb;
+            (s == 0 ? t4.x : s == 1 ? t4.y : s == 2 ? t4.z : t4.w) = (unsigned char)kind;
+        }
+    }
+    for (int m = mbase; m < (int)H.m_large.size(); ++m) {
+        int dir = H.m_info[m] & 1, low = (H.m_info[m] >> 1) & 1;
+        int s_small = dir == 0 ? (low ? 0 : 1) : (low ? 2 : 3);
+        for (int p = 0; p < 2; ++p) {
+            int es = p == 0 ? H.m_small[m].x : H.m_small[m].y;
+            if (!pending[(size_t)(es - base) * 4 + s_small]) return IDP_E_MESH;
+            pending[(size_t)(es - base) * 4 + s_small] = 0;
+            int4 &n4 = H.fnbr[es];
+            uchar4 &t4 = H.ftype[es];
+            (s_small == 0 ? n4.x : s_small == 1 ? n4.y : s_small == 2 ? n4.z : n4.w) = m;
+            (s_small == 0 ? t4.x : s_small == 1 ? t4.y : s_small == 2 ? t4.z : t4.w) =
+                (unsigned char)(p == 0 ? FT_MSLO : FT_MSHI);
+        }
+    }
+    for (size_t k = 0; k < pending.size(); ++k)
+        if (pending[k]) return IDP_E_MESH;
+    SimInfo si;
+    std::memset(&si, 0, sizeof(si));
+    for (int s = 0; s < 4; ++s) {
+        si.bc[s] = d.bc[s];
+        prim_to_cons(gamma, d.bc_prim[s], si.bc_cons[s]);
+    }
+    prim_to_cons(gamma, d.dmr_post, si.dmr_post);
+    prim_to_cons(gamma, d.dmr_pre, si.dmr_pre);
+    si.y1 = d.y1;
+    H.siminfo.push_back(si);
+    return IDP_OK;
+}
+
+template <typename T>
+cudaError_t upload(T **dptr, const std::vector<T> &h) {
+    *dptr = nullptr;
+    if (h.empty()) return cudaSuccess;
+    cudaError_t e = cudaMalloc((void **)dptr, sizeof(T) * h.size());
+    if (e != cudaSuccess) return e;
+    return cudaMemcpy(*dptr, h.data(), sizeof(T) * h.size(), cudaMemcpyHostToDevice);
+}
+
+Launchers get_launchers(int np) {
+    switch (np) {
+    case 2: return launchers_np2();
+    case 3: return launchers_np3();
+    case 4: return launchers_np4();
+    case 5: return launchers_np5();
+    case 6: return launchers_np6();
+    case 7: return launchers_np7();
+    default: return launchers_np8();
+    }
+}
+
+std::mutex g_tune_mu;
+thread_local char g_last_error[256] = "";
+
+// Record the first failing CUDA call of an entry point (diagnostics only).
+cudaError_t note(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) std::snprintf(g_last_error, sizeof(g_last_error), "%s: %s", what, cudaGetErrorString(e));
+    return e;
+}
+std::map<long long, std::pair<int, int>> g_tune_cache;   // key -> (epb, persistent)
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+
+struct idp_ctx {
+    int N = 0, NP = 0, n_sims = 0;
+    double gamma = 1.4;
+    idp_options opt;
+    int num_sms = 0;
+    long long K = 0, M = 0;
+    int n_mnodes = 0;
+    std::vector<long long> sim_off;
+    Launchers L;
+    MeshDev mesh;
+    SlotsDev slots;
+    Ops *d_ops = nullptr;
+    Geo *d_geom = nullptr;
+    int32_t *d_sim = nullptr, *d_mlarge = nullptr, *d_minfo = nullptr, *d_mnnode = nullptr;
+    int4 *d_fnbr = nullptr;
+    uchar4 *d_ftype = nullptr;
+    int2 *d_msmall = nullptr, *d_mnslot = nullptr;
+    SimInfo *d_siminfo = nullptr;
+    void *d_slot_block = nullptr;
+    double *d_buf1 = nullptr, *d_buf2 = nullptr, *d_hostbuf = nullptr;
+    unsigned long long *d_dtmin = nullptr;
+    double *d_tsim = nullptr, *d_dtlast = nullptr;
+    unsigned *d_status = nullptr;
+    StatsAcc *d_stats = nullptr;
+    double *d_part = nullptr, *d_intout = nullptr;
+    long long *d_off = nullptr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    int epb = 0, persistent = 0, bps = 1;
+    bool tuned = false;
+    cudaGraphExec_t graph = nullptr;
+    const double *graph_u = nullptr;
+    long long n_stages = 0;
+};
+
+namespace {
+
+size_t KN(const idp_ctx *c) { return (size_t)c->K * c->NP * c->NP; }
+
+int element_grid(const idp_ctx *c, int epb, int persistent, int bps) {
+    long long blocks = (c->K + epb - 1) / epb;
+    if (persistent) blocks = std::min<long long>(blocks, (long long)c->num_sms * std::max(bps, 1));
+    return (int)std::max<long long>(blocks, 1);
+}
+
+StageArgs base_args(idp_ctx *c) {
+    StageArgs A;
+    std::memset(&A, 0, sizeof(A));
+    A.limiting = c->opt.limiting;
+    A.collect = c->opt.collect_stats;
+    A.dtmin = c->d_dtmin;
+    A.cfl = c->opt.cfl;
+    A.t_sim = c->d_tsim;
+    A.beta = c->opt.beta;
+    A.gamma = c->gamma;
+    A.ops = c->d_ops;
+    A.status = c->d_status;
+    A.stats = c->d_stats;
+    return A;
+}
+
+// one stage: mortar fluxes (unless already current), element pass, mortar limiting
+void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux) {
+    const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
+    if (c->M > 0 && need_mortar_flux) c->L.mortar_flux(gm, st, c->mesh, c->slots, A.u, c->gamma, c->d_ops);
+    c->L.element(c->opt.precision, c->epb, element_grid(c, c->epb, c->persistent, c->bps), st, c->mesh, c->slots, A);
+    bool dgmode = (A.mode == 0 && A.dt == 0.0) || A.limiting == 0;
+    if (c->M > 0 && !dgmode) {
+        c->L.mortar_limit(gm, st, c->mesh, c->slots, A);
+        int ga = std::max(1, std::min((c->n_mnodes + 255) / 256, c->num_sms * 8));
+        c->L.mortar_apply(ga, st, c->mesh, c->slots, A);
+    }
+}
+
+void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) {
+    k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
+    if (c->M > 0 && mortar_flux && c->opt.dt_rule == 0) {
+        const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
+        c->L.mortar_flux(gm, st, c->mesh, c->slots, u, c->gamma, c->d_ops);
+    }
+    int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
+    c->L.dt(g, st, c->mesh, c->slots, u, c->gamma, c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin, c->d_status);
+}
+
+// one SSP-RK3 step on u (in place), using the ctx stage buffers
+void enqueue_step(idp_ctx *c, cudaStream_t st, double *u) {
+    enqueue_dt(c, st, u, true);
+    StageArgs A = base_args(c);
+    A.mode = 1;
+    A.un = u;
+    // stage 1: u1 = ut(u)
+    A.u = u; A.out = c->d_buf1; A.comb = 0; A.tstage = 0.0;
+    enqueue_stage(c, st, A, c->opt.dt_rule != 0);
+    // stage 2: u2 = 3/4 u + 1/4 ut(u1)
+    A.u = c->d_buf1; A.out = c->d_buf2; A.comb = 1; A.tstage = 1.0;
+    enqueue_stage(c, st, A, true);
+    // stage 3: u3 = u/3 + 2/3 ut(u2), in place
+    A.u = c->d_buf2; A.out = u; A.comb = 2; A.tstage = 0.5;
+    enqueue_stage(c, st, A, true);
+    k_time_advance<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_tsim, c->d_dtmin, c->opt.cfl, c->d_dtlast,
+                                                           c->n_sims);
+}
+
+idp_status check_cuda(cudaError_t e) { return note(e, "launch") == cudaSuccess ? IDP_OK : IDP_E_CUDA; }
+
+// Choose elements per block and grid mode by timing the element pass (rhs
+// mode, output to a scratch buffer) on the given state; cached per degree,
+// precision, SM count and mesh-size bucket.
+idp_status autotune(idp_ctx *c, const double *u, cudaStream_t st, double dt) {
+    if (c->tuned) return IDP_OK;
+    long long bucket = 0;
+    for (long long k = c->K; k > 1; k >>= 1) ++bucket;
+    long long key = ((long long)c->NP << 48) | ((long long)c->opt.precision << 40) | ((long long)c->num_sms << 16) | bucket;
+    if (c->opt.elems_per_block > 0) {
+        int bps = 1;
+        if (c->L.element_prepare(c->opt.precision, c->opt.elems_per_block, &bps) != cudaSuccess || bps < 1)
+            return IDP_E_ARG;
+        c->epb = c->opt.elems_per_block; c->bps = bps; c->persistent = 0; c->tuned = true;
+        return IDP_OK;
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            int bps = 1;
+            if (c->L.element_prepare(c->opt.precision, it->second.first, &bps) == cudaSuccess) {
+                c->epb = it->second.first; c->persistent = it->second.second; c->bps = bps; c->tuned = true;
+                return IDP_OK;
+            }
+        }
+    }
+    StageArgs A = base_args(c);
+    A.mode = 0; A.u = u; A.out = c->d_buf1; A.dt = dt; A.t = 0.0; A.collect = 0;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    int best_epb = 0, best_pers = 0, best_bps = 1;
+    for (int ci = 0; ci < kNumEpb; ++ci) {
+        int epb = kEpbChoices[ci], bps = 0;
+        if (c->L.element_prepare(c->opt.precision, epb, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+        if ((long long)epb > 4 * c->K && epb > 1) continue;
+        for (int pers = 0; pers < 2; ++pers) {
+            int grid = element_grid(c, epb, pers, bps);
+            c->L.element(c->opt.precision, epb, grid, st, c->mesh, c->slots, A);   // warm-up
+            if (cudaGetLastError() != cudaSuccess) continue;                       // not launchable
+            cudaEventRecord(e0, st);
+            for (int r = 0; r < 3; ++r) c->L.element(c->opt.precision, epb, grid, st, c->mesh, c->slots, A);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return IDP_E_CUDA; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_epb = epb; best_pers = pers; best_bps = bps; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (!best_epb) return IDP_E_CUDA;
+    c->epb = best_epb; c->persistent = best_pers; c->bps = best_bps; c->tuned = true;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = {best_epb, best_pers};
+    return check_cuda(cudaGetLastError());
+}
+
+// Device-flagged conditions are reported once: the word is cleared after reading.
+idp_status read_status(idp_ctx *c) {
+    unsigned st = 0;
+    if (cudaMemcpy(&st, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return IDP_E_CUDA;
+    if (st && cudaMemset(c->d_status, 0, sizeof(unsigned)) != cudaSuccess) return IDP_E_CUDA;
+    if (st & ST_BAD_INPUT) return IDP_E_STATE;
+    if (st & ST_VIOLATION) return IDP_E_NUMERIC;
+    return IDP_OK;
+}
+
+void reset_stats(idp_ctx *c, cudaStream_t st) {
+    StatsAcc z;
+    std::memset(&z, 0, sizeof(z));
+    z.min_rho_bits = 0x7FF0000000000000ull;
+    z.min_p_bits = 0x7FF0000000000000ull;
+    cudaMemcpyAsync(c->d_stats, &z, sizeof(z), cudaMemcpyHostToDevice, st);
+    cudaStreamSynchronize(st);
+}
+
+idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double gamma, const idp_options *opts,
+                       idp_ctx **out) {
+    if (!out) return IDP_E_ARG;
+    *out = nullptr;
+    if (!meshes || n_sims < 1 || N < 1 || N > NPMAX - 1 || !(gamma > 1.0)) return IDP_E_ARG;
+    idp_options o;
+    idp_options_default(&o);
+    if (opts) o = *opts;
+    if (o.precision < 0 || o.precision > 1 || o.limiting < 0 || o.limiting > 2 || o.dt_rule < 0 || o.dt_rule > 1 ||
+        !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0) || o.mortar_projection < 0 || o.mortar_projection > 1)
+        return IDP_E_ARG;
+    if (o.bounds != 0) return IDP_E_UNSUPPORTED;
+    if (o.elems_per_block != 0 && o.elems_per_block != 1 && o.elems_per_block != 2 && o.elems_per_block != 4 &&
+        o.elems_per_block != 8 && o.elems_per_block != 16)
+        return IDP_E_ARG;
+    HostMesh H;
+    H.sim_off.push_back(0);
+    for (int s = 0; s < n_sims; ++s) {
+        idp_status r = build_mesh(meshes[s], gamma, s, H);
+        if (r != IDP_OK) return r;
+        H.sim_off.push_back((long long)H.geom.size());
+    }
+    idp_ctx *c = new (std::nothrow) idp_ctx();
+    if (!c) return IDP_E_ARG;
+    c->N = N; c->NP = N + 1; c->n_sims = n_sims; c->gamma = gamma; c->opt = o;
+    c->K = (long long)H.geom.size(); c->M = (long long)H.m_large.size();
+    c->sim_off = H.sim_off;
+    c->L = get_launchers(c->NP);
+    int dev = 0;
+    cudaError_t ce = cudaGetDevice(&dev);
+    if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (ce != cudaSuccess) { note(ce, "device query"); delete c; return IDP_E_CUDA; }
+    Ops ops;
+    build_ops(N, o.mortar_projection, ops);
+    // unique mortar nodes, slots ordered by mortar id
+    const int NP = c->NP, NN = NP * NP, Q = 3 * NP;
+    std::vector<std::pair<long long, int>> ns;
+    ns.reserve((size_t)c->M * Q);
+    for (long long m = 0; m < c->M; ++m) {
+        int dir = H.m_info[m] & 1, low = (H.m_info[m] >> 1) & 1;
+        int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
+        for (int q = 0; q < Q; ++q) {
+            int e, s, t;
+            if (q < NP) { e = H.m_large[m]; s = sL; t = q; }
+            else { e = ((q - NP) / NP == 0) ? H.m_small[m].x : H.m_small[m].y; s = sS; t = (q - NP) % NP; }
+            int i = s == 0 ? 0 : (s == 1 ? NP - 1 : t), j = s == 2 ? 0 : (s == 3 ? NP - 1 : t);
+            ns.push_back({(long long)e * NN + j * NP + i, (int)(m * Q + q)});
+        }
+    }
+    std::sort(ns.begin(), ns.end());
+    std::vector<int32_t> mn_node;
+    std::vector<int2> mn_slot;
+    for (size_t k = 0; k < ns.size();) {
+        size_t k2 = k;
+        while (k2 < ns.size() && ns[k2].first == ns[k].first) ++k2;
+        if (k2 - k > 2) { delete c; return IDP_E_MESH; }
+        mn_node.push_back((int32_t)ns[k].first);
+        mn_slot.push_back(make_int2(ns[k].second, k2 - k == 2 ? ns[k + 1].second : -1));
+        k = k2;
+    }
+    c->n_mnodes = (int)mn_node.size();
+    bool ok = true;
+    int step_no = 0;
+    auto chk = [&](cudaError_t e) { ++step_no; if (e != cudaSuccess) { ok = false; char w[32]; std::snprintf(w, 32, "create step %d", step_no); note(e, w); } };
+    chk(cudaMalloc(&c->d_ops, sizeof(Ops)));
+    if (ok) chk(cudaMemcpy(c->d_ops, &ops, sizeof(Ops), cudaMemcpyHostToDevice));
+    if (ok) chk(upload(&c->d_geom, H.geom));
+    if (ok) chk(upload(&c->d_sim, H.sim));
+    if (ok) chk(upload(&c->d_fnbr, H.fnbr));
+    if (ok) chk(upload(&c->d_ftype, H.ftype));
+    if (ok) chk(upload(&c->d_mlarge, H.m_large));
+    if (ok) chk(upload(&c->d_msmall, H.m_small));
+    if (ok) chk(upload(&c->d_minfo, H.m_info));
+    if (ok) chk(upload(&c->d_siminfo, H.siminfo));
+    if (ok) chk(upload(&c->d_mnnode, mn_node));
+    if (ok) chk(upload(&c->d_mnslot, mn_slot));
+    // slots: one block of device memory
+    const size_t S = (size_t)c->M * Q, MM = (size_t)std::max<long long>(c->M, 1), SS = std::max<size_t>(S, 1);
+    size_t bytes = sizeof(double) * (SS * (4 + 4 + 3 + 4 + 4 + 5)) + sizeof(float) * SS + sizeof(int32_t) * MM +
+                   sizeof(double) * MM + 16 * 256;   // 15 sub-arrays, each padded to 256 B
+    if (ok) chk(cudaMalloc(&c->d_slot_block, bytes));
+    if (ok) chk(cudaMemset(c->d_slot_block, 0, bytes));
+    if (ok) {
+        char *p = (char *)c->d_slot_block;
+        auto take = [&](size_t nb) { char *r = p; p += (nb + 255) & ~size_t(255); return (void *)r; };
+        SlotsDev &sl = c->slots;
+        sl.S = (int)S;
+        sl.chi = (double *)take(sizeof(double) * 4 * SS);
+        sl.clo = (double *)take(sizeof(double) * 4 * SS);
+        sl.rbmin = (double *)take(sizeof(double) * SS);
+        sl.rbmax = (double *)take(sizeof(double) * SS);
+        sl.dsum = (double *)take(sizeof(double) * SS);
+        sl.uvol = (double *)take(sizeof(double) * 4 * SS);
+        sl.un = (double *)take(sizeof(double) * 4 * SS);
+        sl.rmin = (double *)take(sizeof(double) * SS);
+        sl.rmax = (double *)take(sizeof(double) * SS);
+        sl.pmin = (double *)take(sizeof(double) * SS);
+        sl.tol = (double *)take(sizeof(double) * SS);
+        sl.mass = (double *)take(sizeof(double) * SS);
+        sl.nmort = (float *)take(sizeof(float) * SS);
+        sl.bad = (int32_t *)take(sizeof(int32_t) * MM);
+        sl.ell = (double *)take(sizeof(double) * MM);
+        if ((size_t)(p - (char *)c->d_slot_block) > bytes) { ok = false; note(cudaErrorMemoryAllocation, "slot layout"); }
+    }
+    const size_t kn = KN(c);
+    if (ok) chk(cudaMalloc(&c->d_buf1, sizeof(double) * 4 * kn));
+    if (ok) chk(cudaMalloc(&c->d_buf2, sizeof(double) * 4 * kn));
+    if (ok) chk(cudaMalloc(&c->d_dtmin, sizeof(unsigned long long) * n_sims));
+    if (ok) chk(cudaMalloc(&c->d_tsim, sizeof(double) * n_sims));
+    if (ok) chk(cudaMalloc(&c->d_dtlast, sizeof(double) * n_sims));
+    if (ok) chk(cudaMalloc(&c->d_status, sizeof(unsigned)));
+    if (ok) chk(cudaMemset(c->d_status, 0, sizeof(unsigned)));
+    if (ok) chk(cudaMalloc(&c->d_stats, sizeof(StatsAcc)));
+    if (ok) chk(cudaMalloc(&c->d_part, sizeof(double) * 4 * (size_t)c->K));
+    if (ok) chk(cudaMalloc(&c->d_intout, sizeof(double) * 4 * n_sims));
+    if (ok) chk(upload(&c->d_off, c->sim_off));
+    if (ok) chk(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    if (ok) chk(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
+    if (ok) chk(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
+    if (!ok) { idp_dgsem_destroy(c); return IDP_E_CUDA; }
+    MeshDev &md = c->mesh;
+    md.K = (int)c->K; md.M = (int)c->M; md.n_sims = n_sims; md.n_mnodes = c->n_mnodes;
+    md.geom = c->d_geom; md.sim = c->d_sim; md.fnbr = c->d_fnbr; md.ftype = c->d_ftype;
+    md.m_large = c->d_mlarge; md.m_small = c->d_msmall; md.m_info = c->d_minfo; md.siminfo = c->d_siminfo;
+    md.mn_node = c->d_mnnode; md.mn_slot = c->d_mnslot;
+    reset_stats(c, c->stream);
+    std::vector<double> tz(n_sims, 0.0);
+    cudaMemcpy(c->d_tsim, tz.data(), sizeof(double) * n_sims, cudaMemcpyHostToDevice);
+    if (note(cudaDeviceSynchronize(), "create sync") != cudaSuccess) { idp_dgsem_destroy(c); return IDP_E_CUDA; }
+    *out = c;
+    return IDP_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *idp_last_cuda_error(void) { return g_last_error; }
+
+const char *idp_status_str(idp_status s) {
+    switch (s) {
+    case IDP_OK: return "ok";
+    case IDP_E_ARG: return "invalid argument";
+    case IDP_E_MESH: return "invalid mesh (overlap, gap, out of range or not 2:1 balanced)";
+    case IDP_E_CUDA: return "CUDA runtime error";
+    case IDP_E_STATE: return "invalid state (rho <= 0, p <= 0 or non-finite)";
+    case IDP_E_DT: return "no admissible time step";
+    case IDP_E_NUMERIC: return "bound violation after limiting";
+    case IDP_E_TIMEOUT: return "device wait timed out";
+    case IDP_E_UNSUPPORTED: return "option not supported";
+    }
+    return "unknown status";
+}
+
+idp_status idp_options_default(idp_options *o) {
+    if (!o) return IDP_E_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->precision = 0;
+    o->limiting = 2;
+    o->bounds = 0;
+    o->dt_rule = 0;
+    o->beta = 0.1;
+    o->cfl = 0.5;
+    o->mortar_projection = 1;
+    o->elems_per_block = 0;
+    o->collect_stats = 1;
+    return IDP_OK;
+}
+
+idp_status idp_dgsem_create(const idp_mesh_desc *mesh, int32_t N, double gamma, const idp_options *opts,
+                            idp_ctx **ctx) {
+    try {
+        return create_impl(mesh, 1, N, gamma, opts, ctx);
+    } catch (...) {
+        return IDP_E_ARG;
+    }
+}
+
+idp_status idp_dgsem_create_batch(const idp_mesh_desc *meshes, int32_t n_sims, int32_t N, double gamma,
+                                  const idp_options *opts, idp_ctx **ctx) {
+    try {
+        return create_impl(meshes, n_sims, N, gamma, opts, ctx);
+    } catch (...) {
+        return IDP_E_ARG;
+    }
+}
+
+idp_status idp_dgsem_layout(const idp_ctx *c, int64_t *n_elems, int64_t *n_mortars, int32_t *n_sims,
+                            int64_t *sim_elem_offsets) {
+    if (!c) return IDP_E_ARG;
+    if (n_elems) *n_elems = c->K;
+    if (n_mortars) *n_mortars = c->M;
+    if (n_sims) *n_sims = c->n_sims;
+    if (sim_elem_offsets)
+        for (int s = 0; s <= c->n_sims; ++s) sim_elem_offsets[s] = c->sim_off[s];
+    return IDP_OK;
+}
+
+idp_status idp_dgsem_rhs(idp_ctx *c, const double *u, double t, double dt, double *rhs, void *stream) {
+    if (!c || !u || !rhs || u == rhs || !(dt >= 0.0) || !std::isfinite(dt)) return IDP_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    idp_status r = autotune(c, u, st, dt);
+    if (r != IDP_OK) return r;
+    StageArgs A = base_args(c);
+    A.mode = 0; A.u = u; A.out = rhs; A.dt = dt; A.t = t;
+    enqueue_stage(c, st, A, true);
+    if (dt > 0.0 && c->opt.limiting > 0) c->n_stages += 1;
+    return check_cuda(cudaGetLastError());
+}
+
+idp_status idp_dgsem_dt(idp_ctx *c, const double *u, const double *t_host, double *dt_host, void *stream) {
+    if (!c || !u || !dt_host) return IDP_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<double> tz(c->n_sims, 0.0);
+    if (t_host) for (int s = 0; s < c->n_sims; ++s) tz[s] = t_host[s];
+    if (cudaMemcpyAsync(c->d_tsim, tz.data(), sizeof(double) * c->n_sims, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return IDP_E_CUDA;
+    enqueue_dt(c, st, u, true);
+    std::vector<unsigned long long> b(c->n_sims);
+    if (cudaMemcpyAsync(b.data(), c->d_dtmin, sizeof(unsigned long long) * c->n_sims, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return IDP_E_CUDA;
+    for (int s = 0; s < c->n_sims; ++s) {
+        double v;
+        std::memcpy(&v, &b[s], sizeof(double));
+        if (!(v > 0.0) || !std::isfinite(v)) return IDP_E_DT;
+        dt_host[s] = c->opt.cfl * v;
+    }
+    return read_status(c);
+}
+
+idp_status idp_dgsem_step(idp_ctx *c, double *u, int32_t n_steps, double *t_host, double *dt_last_host,
+                          void *stream) {
+    if (!c || !u || n_steps < 0 || !t_host) return IDP_E_ARG;
+    cudaStream_t ust = (cudaStream_t)stream;
+    cudaStream_t st = c->stream;
+    // order after the caller's stream
+    if (cudaEventRecord(c->ev_in, ust) != cudaSuccess || cudaStreamWaitEvent(st, c->ev_in, 0) != cudaSuccess)
+        return IDP_E_CUDA;
+    if (cudaMemcpyAsync(c->d_tsim, t_host, sizeof(double) * c->n_sims, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return IDP_E_CUDA;
+    if (!c->tuned) {
+        // tune on u with its own IDP step
+        enqueue_dt(c, st, u, true);
+        std::vector<unsigned long long> b(c->n_sims);
+        cudaMemcpyAsync(b.data(), c->d_dtmin, sizeof(unsigned long long) * c->n_sims, cudaMemcpyDeviceToHost, st);
+        if (cudaStreamSynchronize(st) != cudaSuccess) return IDP_E_CUDA;
+        double v;
+        std::memcpy(&v, &b[0], sizeof(double));
+        idp_status r = autotune(c, u, st, std::isfinite(v) ? c->opt.cfl * v : 0.0);
+        if (r != IDP_OK) return r;
+    }
+    if (n_steps > 0) {
+        if (c->graph == nullptr || c->graph_u != u) {
+            if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+            cudaGraph_t g;
+            if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return IDP_E_CUDA;
+            enqueue_step(c, st, u);
+            if (cudaStreamEndCapture(st, &g) != cudaSuccess) return IDP_E_CUDA;
+            cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) { c->graph = nullptr; return IDP_E_CUDA; }
+            c->graph_u = u;
+        }
+        for (int k = 0; k < n_steps; ++k)
+            if (cudaGraphLaunch(c->graph, st) != cudaSuccess) return IDP_E_CUDA;
+        c->n_stages += 3LL * n_steps;
+    }
+    cudaMemcpyAsync(t_host, c->d_tsim, sizeof(double) * c->n_sims, cudaMemcpyDeviceToHost, st);
+    if (dt_last_host && n_steps > 0)
+        cudaMemcpyAsync(dt_last_host, c->d_dtlast, sizeof(double) * c->n_sims, cudaMemcpyDeviceToHost, st);
+    cudaEventRecord(c->ev_out, st);
+    cudaStreamWaitEvent(ust, c->ev_out, 0);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return IDP_E_CUDA;
+    return read_status(c);
+}
+
+idp_status idp_dgsem_step_host(idp_ctx *c, double *u_host, int32_t n_steps, double *t_host, double *dt_last_host,
+                               void *stream) {
+    if (!c || !u_host) return IDP_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    size_t bytes = sizeof(double) * 4 * KN(c);
+    if (!c->d_hostbuf && cudaMalloc(&c->d_hostbuf, bytes) != cudaSuccess) return IDP_E_CUDA;
+    if (cudaMemcpyAsync(c->d_hostbuf, u_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return IDP_E_CUDA;
+    idp_status r = idp_dgsem_step(c, c->d_hostbuf, n_steps, t_host, dt_last_host, stream);
+    if (r != IDP_OK && r != IDP_E_NUMERIC) return r;
+    if (cudaMemcpyAsync(u_host, c->d_hostbuf, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return IDP_E_CUDA;
+    return r;
+}
+
+idp_status idp_dgsem_integrals(idp_ctx *c, const double *u, double *out_host, void *stream) {
+    if (!c || !u || !out_host) return IDP_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    int g = (int)std::max<long long>(1, std::min<long long>((c->K + 255) / 256, (long long)c->num_sms * 8));
+    c->L.integrals(g, st, c->mesh, u, c->d_ops, c->d_part);
+    k_sum_segments<<<c->n_sims, 256, 0, st>>>(c->d_part, (int)c->K, c->d_off, c->d_intout);
+    if (cudaMemcpyAsync(out_host, c->d_intout, sizeof(double) * 4 * c->n_sims, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return IDP_E_CUDA;
+    return IDP_OK;
+}
+
+idp_status idp_dgsem_limiter_stats(idp_ctx *c, idp_limiter_stats *out, void *stream) {
+    if (!c || !out) return IDP_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    StatsAcc a;
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess ||
+        cudaMemcpy(&a, c->d_stats, sizeof(a), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return IDP_E_CUDA;
+    std::memset(out, 0, sizeof(*out));
+    out->alpha_volume_mean = a.mass > 0 ? a.alpha_vol_m / a.mass : 0.0;
+    out->alpha_mortar_mean = a.len > 0 ? a.alpha_mort_len / a.len : 0.0;
+    out->n_stages = c->n_stages;
+    out->n_volume_active = (int64_t)a.n_vol;
+    out->n_mortar_active = (int64_t)a.n_mort;
+    out->n_mortar_fallback = (int64_t)a.n_fallback;
+    out->n_viol_density = (int64_t)a.n_vrho;
+    out->n_viol_pressure = (int64_t)a.n_vp;
+    out->n_nonpositive = (int64_t)a.n_nonpos;
+    out->n_dt_exceed = (int64_t)a.n_dtx;
+    std::memcpy(&out->min_rho, &a.min_rho_bits, sizeof(double));
+    std::memcpy(&out->min_p, &a.min_p_bits, sizeof(double));
+    c->n_stages = 0;
+    reset_stats(c, c->stream);
+    return read_status(c);
+}
+
+idp_status idp_dgsem_sync(idp_ctx *c, void *stream) {
+    if (!c) return IDP_E_ARG;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return IDP_E_CUDA;
+    return read_status(c);
+}
+
+void idp_dgsem_destroy(idp_ctx *c) {
+    if (!c) return;
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    void *ptrs[] = {c->d_ops, c->d_geom, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+                    c->d_msmall, c->d_mnslot, c->d_siminfo, c->d_slot_block, c->d_buf1, c->d_buf2, c->d_hostbuf,
+                    c->d_dtmin, c->d_tsim, c->d_dtlast, c->d_status, c->d_stats, c->d_part, c->d_intout, c->d_off};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (c->ev_in) cudaEventDestroy(c->ev_in);
+    if (c->ev_out) cudaEventDestroy(c->ev_out);
+    if (c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,38 @@
+// idp_launch.cuh -- per-degree kernel launchers. Each polynomial degree is
+// compiled in its own translation unit (k_inst.cu with IDP_NP = N + 1); the
+// host selects the table for its N at create time.
+#pragma once
+
+#include "idp_mortar.cuh"
+
+namespace idp {
+
+constexpr int kEpbChoices[] = {1, 2, 4, 8, 16};
+constexpr int kNumEpb = 5;
+
+struct Launchers {
+    int np;
+    // element pass: fp32 selects the FP32 form; epb = elements per block
+    size_t (*element_smem)(int fp32, int epb);
+    int (*element_threads)(int epb);
+    cudaError_t (*element_prepare)(int fp32, int epb, int *blocks_per_sm);
+    void (*element)(int fp32, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
+                    const StageArgs &a);
+    void (*mortar_flux)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
+                        double gamma, const Ops *ops);
+    void (*mortar_limit)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
+    void (*mortar_apply)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
+    void (*dt)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma,
+               int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status);
+    void (*integrals)(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part);
+};
+
+Launchers launchers_np2();
+Launchers launchers_np3();
+Launchers launchers_np4();
+Launchers launchers_np5();
+Launchers launchers_np6();
+Launchers launchers_np7();
+Launchers launchers_np8();
+
+}  // namespace idp

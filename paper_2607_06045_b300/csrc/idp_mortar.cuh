@@ -1,0 +1,333 @@
+// idp_mortar.cuh -- face-list kernels at nonconforming interfaces and the
+// per-step reductions of the IDP LGL-DGSEM (arXiv 2607.06045).
+//
+//  k_mortar_flux   per mortar (one warp): high-order L2 mortar flux (Sec. 2.3,
+//                  interpolate, LLF on the two small faces, project back) and
+//                  the sparse low-order IDP mortar flux (Eq. interfaceflux_local)
+//                  with its bar states and graph-viscosity sums.
+//  k_mortar_limit  per mortar (one warp): one factor l_S per mortar after the
+//                  volume correction, each node's correction budget scaled by
+//                  its number of mortars n_i (Sec. 2.3, mortar limiting).
+//  k_mortar_apply  per mortar node: apply the limited corrections in mortar
+//                  order and finish the stage.
+//  k_dt            IDP time step (Eq. timestep_restriction) or the low-order
+//                  CFL estimate (Eq. CFLcondition_lowordermethod), per simulation.
+#pragma once
+
+#include "idp_element.cuh"
+
+namespace idp {
+
+constexpr int MORTARS_PER_BLOCK = 4;   // one warp per mortar
+
+template <int NP>
+__global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
+k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, const Ops *ops) {
+    constexpr int NN = NP * NP, Q = 3 * NP;
+    __shared__ double s_u[MORTARS_PER_BLOCK][Q][4];
+    __shared__ double s_ui[MORTARS_PER_BLOCK][2 * NP][4];
+    __shared__ double s_f[MORTARS_PER_BLOCK][2 * NP][4];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = blockIdx.x * MORTARS_PER_BLOCK + warp;
+    if (m >= mesh.M) return;
+    const size_t KN = (size_t)mesh.K * NN;
+    const int info = mesh.m_info[m], dir = info & 1, low = (info >> 1) & 1;
+    const int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
+    const int L = mesh.m_large[m];
+    const int2 sm2 = mesh.m_small[m];
+    const Geo geoL = mesh.geom[L];
+    const double halfL = dir == 0 ? 0.5 * geoL.w : 0.5 * geoL.z, halfS = 0.5 * halfL;
+    const double sg = low ? 1.0 : -1.0;   // large side's outward normal along +dir
+    const double g = gamma;
+    int gnode = -1;
+    if (lane < Q) {
+        if (lane < NP) gnode = L * NN + face_node<NP>(sL, lane);
+        else {
+            int p = (lane - NP) / NP, l = (lane - NP) % NP;
+            gnode = (p == 0 ? sm2.x : sm2.y) * NN + face_node<NP>(sS, l);
+        }
+        for (int v = 0; v < 4; ++v) s_u[warp][lane][v] = u[v * KN + gnode];
+    }
+    __syncwarp();
+    // interpolation of the large trace to the small-face nodes, admissibility
+    bool badl = false;
+    if (lane < 2 * NP) {
+        double acc[4] = {0, 0, 0, 0};
+        for (int k = 0; k < NP; ++k) {
+            double c = ops->I[lane][k];
+            for (int v = 0; v < 4; ++v) acc[v] += c * s_u[warp][k][v];
+        }
+        for (int v = 0; v < 4; ++v) s_ui[warp][lane][v] = acc[v];
+        badl = !(acc[0] > 0.0) || !(pressure_d(g, acc[0], acc[1], acc[2], acc[3]) > 0.0);
+    }
+    const bool bad = __any_sync(0xffffffffu, badl);
+    __syncwarp();
+    // LLF on the small faces (left/bottom state first)
+    if (!bad && lane < 2 * NP) {
+        double f[4];
+        const double *ui = s_ui[warp][lane], *us = s_u[warp][NP + lane];
+        if (low) llf<double>(ui, us, g, dir, f); else llf<double>(us, ui, g, dir, f);
+        for (int v = 0; v < 4; ++v) s_f[warp][lane][v] = f[v];
+    }
+    __syncwarp();
+    // node quantities
+    if (lane < Q) {
+        const int q = lane;
+        double chi[4] = {0, 0, 0, 0}, clo[4] = {0, 0, 0, 0};
+        if (!bad) {
+            if (q < NP) {
+                double acc[4] = {0, 0, 0, 0};
+                for (int r = 0; r < 2 * NP; ++r) {
+                    double c = ops->P[q][r];
+                    for (int v = 0; v < 4; ++v) acc[v] += c * s_f[warp][r][v];
+                }
+                for (int v = 0; v < 4; ++v) chi[v] = -sg * ops->w[q] * (halfL * acc[v]);
+            } else {
+                int l = (q - NP) % NP;
+                for (int v = 0; v < 4; ++v) chi[v] = sg * ops->w[l] * (halfS * s_f[warp][q - NP][v]);
+            }
+        }
+        // sparse low-order flux, bar states and 2 d sums over the nonzero local weights
+        double lo = INFINITY, hi = -INFINITY, ds = 0.0;
+        const int kb = q < NP ? q : 0, ke = q < NP ? q + 1 : NP;
+        const int rb = q < NP ? 0 : q - NP, re = q < NP ? 2 * NP : q - NP + 1;
+        for (int k = kb; k < ke; ++k)
+            for (int r = rb; r < re; ++r) {
+                double wt = ops->wt[k][r] * halfL;
+                if (wt <= 0.0) continue;
+                const double *a = s_u[warp][k], *b = s_u[warp][NP + r];
+                double va = a[1 + dir] / a[0], vb = b[1 + dir] / b[0];
+                double pa = pressure_d(g, a[0], a[1], a[2], a[3]), pb = pressure_d(g, b[0], b[1], b[2], b[3]);
+                double la = fabs(va) + sqrt(g * pa / a[0]), lb = fabs(vb) + sqrt(g * pb / b[0]);
+                double lam = la > lb ? la : lb;
+                double fa[4], fb[4];
+                phys_flux<double>(a[1], a[2], a[3], pa, va, dir, fa);
+                phys_flux<double>(b[1], b[2], b[3], pb, vb, dir, fb);
+                for (int v = 0; v < 4; ++v) {
+                    double term = 0.5 * wt * ((sg * fa[v] + sg * fb[v]) - lam * (b[v] - a[v]));
+                    clo[v] += q < NP ? -term : term;
+                }
+                double rbv = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) / (2.0 * lam);
+                lo = fmin(lo, rbv);
+                hi = fmax(hi, rbv);
+                ds += 2.0 * (wt / 2.0) * lam;
+            }
+        if (bad)
+            for (int v = 0; v < 4; ++v) chi[v] = clo[v];
+        const int s = m * Q + q;
+        for (int v = 0; v < 4; ++v) { sl.chi[(size_t)v * sl.S + s] = chi[v]; sl.clo[(size_t)v * sl.S + s] = clo[v]; }
+        sl.rbmin[s] = lo; sl.rbmax[s] = hi; sl.dsum[s] = ds;
+    }
+    if (lane == 0) sl.bad[m] = bad ? 1 : 0;
+}
+
+template <int NP>
+__global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
+k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
+    constexpr int Q = 3 * NP;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m = blockIdx.x * MORTARS_PER_BLOCK + warp;
+    if (m >= mesh.M) return;
+    const int L = mesh.m_large[m];
+    const int sim = mesh.sim[L];
+    const double dt = stage_dt(A, sim);
+    const bool bad = sl.bad[m] != 0;
+    double th = 1.0;
+    if (!bad && lane < Q) {
+        const int s = m * Q + lane;
+        double u0[4], av[4];
+        const double mi = sl.mass[s], ni = (double)sl.nmort[s];
+        for (int v = 0; v < 4; ++v) {
+            u0[v] = sl.uvol[(size_t)v * sl.S + s];
+            av[v] = ni * dt / mi * (sl.chi[(size_t)v * sl.S + s] - sl.clo[(size_t)v * sl.S + s]);
+        }
+        double lr = 1.0;
+        double tl = sl.tol[s];
+        if (av[0] > 0.0) { double t = (sl.rmax[s] + tl - u0[0]) / av[0]; if (t < lr) lr = t; }
+        else if (av[0] < 0.0) { double t = (sl.rmin[s] - tl - u0[0]) / av[0]; if (t < lr) lr = t; }
+        if (lr < 0.0) lr = 0.0;
+        double pm = sl.pmin[s];
+        th = theta_max(A.gamma, u0, av, pm - kTol * fabs(pm), lr);
+    }
+    for (int o = 16; o > 0; o >>= 1) th = fmin(th, __shfl_down_sync(0xffffffffu, th, o));
+    if (lane == 0) {
+        double lS = bad ? 0.0 : th;
+        sl.ell[m] = lS;
+        if (A.collect) {
+            const int info = mesh.m_info[m], dir = info & 1;
+            const Geo geo = mesh.geom[L];
+            double len = dir == 0 ? geo.w : geo.z;
+            atomicAdd(&A.stats->alpha_mort_len, len * (1.0 - lS));
+            atomicAdd(&A.stats->len, len);
+            if (lS < 1.0) atomicAdd(&A.stats->n_mort, 1ull);
+            if (bad) atomicAdd(&A.stats->n_fallback, 1ull);
+        }
+    }
+}
+
+template <int NP>
+__global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
+    constexpr int NN = NP * NP, Q = 3 * NP;
+    const size_t KN = (size_t)mesh.K * NN;
+    double st_rmin = INFINITY, st_pmin = INFINITY;
+    unsigned long long vr = 0, vp = 0, np_ = 0;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mesh.n_mnodes; k += gridDim.x * blockDim.x) {
+        const int gnode = mesh.mn_node[k];
+        const int2 ss = mesh.mn_slot[k];
+        const int s0 = ss.x;
+        const int e = gnode / NN;
+        const double dt = stage_dt(A, mesh.sim[e]);
+        const double mi = sl.mass[s0];
+        double corr[4] = {0, 0, 0, 0};
+        for (int c = 0; c < 2; ++c) {
+            int s = c == 0 ? ss.x : ss.y;
+            if (s < 0) continue;
+            double l = sl.ell[s / Q];
+            for (int v = 0; v < 4; ++v) corr[v] += l * (sl.chi[(size_t)v * sl.S + s] - sl.clo[(size_t)v * sl.S + s]);
+        }
+        double ut[4];
+        for (int v = 0; v < 4; ++v) {
+            double uv = sl.uvol[(size_t)v * sl.S + s0];
+            ut[v] = uv + dt / mi * corr[v];
+            if (A.mode == 0) {
+                A.out[v * KN + gnode] = (sl.un[(size_t)v * sl.S + s0] + corr[v]) / mi;
+            } else {
+                double o = ut[v];
+                double un = sl.un[(size_t)v * sl.S + s0];
+                if (A.comb == 1) o = 0.75 * un + 0.25 * ut[v];
+                else if (A.comb == 2) o = un / 3.0 + 2.0 / 3.0 * ut[v];
+                A.out[v * KN + gnode] = o;
+            }
+        }
+        if (A.collect) {
+            double p = pressure_d(A.gamma, ut[0], ut[1], ut[2], ut[3]);
+            double rmin = sl.rmin[s0], rmax = sl.rmax[s0], pmin = sl.pmin[s0];
+            if (ut[0] < rmin - kViolTol * fabs(rmin) || ut[0] > rmax + kViolTol * fabs(rmax)) vr++;
+            if (p < pmin - kViolTol * fabs(pmin)) vp++;
+            if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
+            st_rmin = fmin(st_rmin, ut[0]);
+            st_pmin = fmin(st_pmin, p);
+        }
+    }
+    if (A.collect) block_stats(A, 0.0, 0.0, 0ull, vr, vp, np_, 0ull, st_rmin, st_pmin);
+    if ((vr | vp | np_) != 0ull) atomicOr(A.status, ST_VIOLATION);
+}
+
+// Time step: per node m_i / sum_j 2 d_ij (rule 0) or min over directions of
+// (w_i h / 2) / (|v| + c) (rule 1); minimum per simulation as ordered bits.
+template <int NP>
+__global__ void k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int rule,
+                     const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status) {
+    constexpr int NN = NP * NP, N = NP - 1;
+    const size_t KN = (size_t)mesh.K * NN;
+    const double g = gamma;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < KN; k += (size_t)gridDim.x * blockDim.x) {
+        const int e = (int)(k / NN), n = (int)(k % NN), i = n % NP, j = n / NP;
+        const Geo geo = mesh.geom[e];
+        const int sim = mesh.sim[e];
+        double ui[4] = {u[k], u[KN + k], u[2 * KN + k], u[3 * KN + k]};
+        double pi_ = pressure_d(g, ui[0], ui[1], ui[2], ui[3]);
+        if (!(ui[0] > 0.0) || !(pi_ > 0.0)) { atomicOr(status, ST_BAD_INPUT); continue; }
+        double ci = sqrt(g * pi_ / ui[0]);
+        double val;
+        if (rule == 1) {
+            double tx = ops->w[i] * geo.z / 2.0 / (fabs(ui[1] / ui[0]) + ci);
+            double ty = ops->w[j] * geo.w / 2.0 / (fabs(ui[2] / ui[0]) + ci);
+            val = fmin(tx, ty);
+        } else {
+            double ds = 0.0;
+            const uchar4 ftv = mesh.ftype[e];
+            const int4 nb4 = mesh.fnbr[e];
+            for (int d = 0; d < 2; ++d) {
+                int pos = d == 0 ? i : j, row = d == 0 ? j : i;
+                double cc = ops->w[row] * (d == 0 ? geo.w : geo.z) / 4.0;
+                double vi = ui[1 + d] / ui[0], li = fabs(vi) + ci;
+                for (int side = 0; side < 2; ++side) {
+                    bool interior = side == 0 ? pos > 0 : pos < N;
+                    if (interior) {
+                        int on = d == 0 ? n + (side == 0 ? -1 : 1) : n + (side == 0 ? -NP : NP);
+                        size_t ko = (size_t)e * NN + on;
+                        double uo[4] = {u[ko], u[KN + ko], u[2 * KN + ko], u[3 * KN + ko]};
+                        double po = pressure_d(g, uo[0], uo[1], uo[2], uo[3]);
+                        double lo = fabs(uo[1 + d] / uo[0]) + sqrt(g * po / uo[0]);
+                        ds += 2.0 * cc * (li > lo ? li : lo);
+                    } else {
+                        int s = 2 * d + side;
+                        int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
+                        int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
+                        if (ft == FT_CONF || ft == FT_BND) {
+                            double uo[4];
+                            if (ft == FT_CONF) {
+                                size_t ko = (size_t)nb * NN + face_node<NP>(s ^ 1, row);
+                                for (int v = 0; v < 4; ++v) uo[v] = u[v * KN + ko];
+                            } else {
+                                // ghost state at the step's start time
+                                double xn = geo.x + 0.5 * geo.z * (1.0 + ops->xi[i]);
+                                ghost_state(mesh.siminfo[sim], s, ui, xn, t_sim[sim], uo);
+                            }
+                            double po = pressure_d(g, uo[0], uo[1], uo[2], uo[3]);
+                            double lo = fabs(uo[1 + d] / uo[0]) + sqrt(g * po / uo[0]);
+                            ds += 2.0 * cc * (li > lo ? li : lo);
+                        } else {
+                            ds += sl.dsum[slot_of<NP>(ft, nb, row)];
+                        }
+                    }
+                }
+            }
+            double mi = geo.z * geo.w / 4.0 * ops->w[i] * ops->w[j];
+            val = mi / ds;
+        }
+        if (val > 0.0) atomicMin(&dtmin[sim], dbits(val));
+    }
+}
+
+static __global__ void k_dt_init(unsigned long long *dtmin, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) dtmin[k] = dbits(INFINITY);
+}
+
+static __global__ void k_time_advance(double *t_sim, const unsigned long long *dtmin, double cfl, double *dt_last, int n) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) {
+        double dt = cfl * __longlong_as_double((long long)dtmin[k]);
+        t_sim[k] += dt;
+        dt_last[k] = dt;
+    }
+}
+
+// sum_i m_i u_i per element (fixed order over its nodes)
+template <int NP>
+__global__ void k_elem_integrals(MeshDev mesh, const double *__restrict__ u, const Ops *ops, double *part) {
+    constexpr int NN = NP * NP;
+    const size_t KN = (size_t)mesh.K * NN;
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < mesh.K; e += gridDim.x * blockDim.x) {
+        Geo geo = mesh.geom[e];
+        double J = geo.z * geo.w / 4.0;
+        for (int v = 0; v < 4; ++v) {
+            double s = 0.0;
+            for (int n = 0; n < NN; ++n) s += J * ops->w[n % NP] * ops->w[n / NP] * u[v * KN + (size_t)e * NN + n];
+            part[(size_t)v * mesh.K + e] = s;
+        }
+    }
+}
+
+// per simulation: fixed-order tree sum of the element partials in [off[s], off[s+1])
+static __global__ void k_sum_segments(const double *part, int K, const long long *off, double *out) {
+    __shared__ double red[4][256];
+    const int s = blockIdx.x;
+    const long long b = off[s], e = off[s + 1];
+    double acc[4] = {0, 0, 0, 0};
+    for (long long k = b + threadIdx.x; k < e; k += blockDim.x)
+        for (int v = 0; v < 4; ++v) acc[v] += part[(size_t)v * K + k];
+    for (int v = 0; v < 4; ++v) red[v][threadIdx.x] = acc[v];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int v = 0; v < 4; ++v) red[v][threadIdx.x] += red[v][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int v = 0; v < 4; ++v) out[4 * s + v] = red[v][0];
+}
+
+}  // namespace idp

@@ -1,0 +1,105 @@
+// k_inst.cu -- instantiates the kernels of one polynomial degree (IDP_NP =
+// N + 1, set on the compiler command line) and exposes them as a launcher
+// table.
+#include "idp_launch.cuh"
+
+#ifndef IDP_NP
+#error "IDP_NP must be defined"
+#endif
+
+#define IDP_CAT2(a, b) a##b
+#define IDP_CAT(a, b) IDP_CAT2(a, b)
+
+namespace idp {
+namespace {
+
+constexpr int NP = IDP_NP;
+
+template <typename FT, int EPB>
+void el_launch(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
+    size_t smem = sizeof(ElemSm<NP, FT>) * EPB;
+    k_element<NP, FT, EPB><<<grid, ElemLaunch<NP, EPB>::threads, smem, st>>>(m, s, a);
+}
+
+template <typename FT, int EPB>
+cudaError_t el_prepare(int *bps) {
+    size_t smem = sizeof(ElemSm<NP, FT>) * EPB;
+    cudaError_t e = cudaFuncSetAttribute(k_element<NP, FT, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_element<NP, FT, EPB>,
+                                                         ElemLaunch<NP, EPB>::threads, smem);
+}
+
+size_t element_smem(int fp32, int epb) {
+    return (fp32 ? sizeof(ElemSm<NP, float>) : sizeof(ElemSm<NP, double>)) * (size_t)epb;
+}
+
+int element_threads(int epb) {
+    switch (epb) {
+    case 1: return ElemLaunch<NP, 1>::threads;
+    case 2: return ElemLaunch<NP, 2>::threads;
+    case 4: return ElemLaunch<NP, 4>::threads;
+    case 8: return ElemLaunch<NP, 8>::threads;
+    default: return ElemLaunch<NP, 16>::threads;
+    }
+}
+
+#define IDP_EPB_SWITCH(FN, ...)                                                               \
+    switch (epb) {                                                                            \
+    case 1: return fp32 ? FN<float, 1>(__VA_ARGS__) : FN<double, 1>(__VA_ARGS__);             \
+    case 2: return fp32 ? FN<float, 2>(__VA_ARGS__) : FN<double, 2>(__VA_ARGS__);             \
+    case 4: return fp32 ? FN<float, 4>(__VA_ARGS__) : FN<double, 4>(__VA_ARGS__);             \
+    case 8: return fp32 ? FN<float, 8>(__VA_ARGS__) : FN<double, 8>(__VA_ARGS__);             \
+    default: return fp32 ? FN<float, 16>(__VA_ARGS__) : FN<double, 16>(__VA_ARGS__);          \
+    }
+
+cudaError_t element_prepare(int fp32, int epb, int *bps) {
+    if (ElemLaunch<NP, 16>::threads > 1024 && epb == 16) return cudaErrorInvalidConfiguration;
+    IDP_EPB_SWITCH(el_prepare, bps)
+}
+
+void element(int fp32, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
+    IDP_EPB_SWITCH(el_launch, grid, st, m, s, a)
+}
+
+void mortar_flux(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma,
+                 const Ops *ops) {
+    k_mortar_flux<NP><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gamma, ops);
+}
+
+void mortar_limit(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
+    k_mortar_limit<NP><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, a);
+}
+
+void mortar_apply(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
+    k_mortar_apply<NP><<<grid, 256, 0, st>>>(m, s, a);
+}
+
+void dt(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma, int rule,
+        const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status) {
+    k_dt<NP><<<grid, 256, 0, st>>>(m, s, u, gamma, rule, ops, t_sim, dtmin, status);
+}
+
+void integrals(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part) {
+    k_elem_integrals<NP><<<grid, 256, 0, st>>>(m, u, ops, part);
+}
+
+}  // namespace
+
+Launchers IDP_CAT(launchers_np, IDP_NP)() {
+    Launchers L;
+    L.np = NP;
+    L.element_smem = element_smem;
+    L.element_threads = element_threads;
+    L.element_prepare = element_prepare;
+    L.element = element;
+    L.mortar_flux = mortar_flux;
+    L.mortar_limit = mortar_limit;
+    L.mortar_apply = mortar_apply;
+    L.dt = dt;
+    L.integrals = integrals;
+    return L;
+}
+
+}  // namespace idp

@@ -1,0 +1,238 @@
+"""Python binding of libidpdgsem.so (argument marshalling only).
+
+Mirrors the C ABI of include/idp_dgsem.h: the same entry-point names, with
+device arrays passed as torch CUDA tensors (FP64, contiguous, layout
+u[4][K][N+1][N+1]) and the stream taken from torch's current stream unless
+given. Every computation runs in the library's CUDA kernels; there is no
+fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libidpdgsem.so")
+
+IDP_OK, IDP_E_ARG, IDP_E_MESH, IDP_E_CUDA, IDP_E_STATE, IDP_E_DT, IDP_E_NUMERIC, IDP_E_TIMEOUT, IDP_E_UNSUPPORTED = range(9)
+
+
+class MeshDesc(C.Structure):
+    _fields_ = [("nx0", C.c_int32), ("ny0", C.c_int32),
+                ("x0", C.c_double), ("y0", C.c_double), ("x1", C.c_double), ("y1", C.c_double),
+                ("n_leaves", C.c_int32),
+                ("level", C.POINTER(C.c_int8)), ("ix", C.POINTER(C.c_int32)), ("iy", C.POINTER(C.c_int32)),
+                ("bc", C.c_int32 * 4), ("bc_prim", (C.c_double * 4) * 4),
+                ("dmr_post", C.c_double * 4), ("dmr_pre", C.c_double * 4)]
+
+
+class Options(C.Structure):
+    _fields_ = [("precision", C.c_int32), ("limiting", C.c_int32), ("bounds", C.c_int32), ("dt_rule", C.c_int32),
+                ("beta", C.c_double), ("cfl", C.c_double), ("mortar_projection", C.c_int32),
+                ("elems_per_block", C.c_int32), ("collect_stats", C.c_int32), ("reserved", C.c_int32)]
+
+
+class LimiterStats(C.Structure):
+    _fields_ = [("alpha_volume_mean", C.c_double), ("alpha_mortar_mean", C.c_double),
+                ("n_stages", C.c_int64), ("n_volume_active", C.c_int64), ("n_mortar_active", C.c_int64),
+                ("n_mortar_fallback", C.c_int64), ("n_viol_density", C.c_int64), ("n_viol_pressure", C.c_int64),
+                ("n_nonpositive", C.c_int64), ("n_dt_exceed", C.c_int64),
+                ("min_rho", C.c_double), ("min_p", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", "idp_dgsem_layout",
+           "idp_dgsem_rhs", "idp_dgsem_dt", "idp_dgsem_step", "idp_dgsem_step_host", "idp_dgsem_integrals",
+           "idp_dgsem_limiter_stats", "idp_dgsem_sync", "idp_dgsem_destroy", "idp_status_str",
+           "idp_last_cuda_error"]
+
+
+def lib():
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: run `python -m paper_2607_06045_b300.build`")
+        L = C.CDLL(LIB_PATH)
+        vp, dp = C.c_void_p, C.POINTER(C.c_double)
+        L.idp_status_str.restype = C.c_char_p
+        L.idp_status_str.argtypes = [C.c_int]
+        L.idp_last_cuda_error.restype = C.c_char_p
+        L.idp_last_cuda_error.argtypes = []
+        L.idp_options_default.argtypes = [C.POINTER(Options)]
+        L.idp_dgsem_create.argtypes = [C.POINTER(MeshDesc), C.c_int32, C.c_double, C.POINTER(Options), C.POINTER(vp)]
+        L.idp_dgsem_create_batch.argtypes = [C.POINTER(MeshDesc), C.c_int32, C.c_int32, C.c_double,
+                                             C.POINTER(Options), C.POINTER(vp)]
+        L.idp_dgsem_layout.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
+                                       C.POINTER(C.c_int64)]
+        L.idp_dgsem_rhs.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp]
+        L.idp_dgsem_dt.argtypes = [vp, vp, dp, dp, vp]
+        L.idp_dgsem_step.argtypes = [vp, vp, C.c_int32, dp, dp, vp]
+        L.idp_dgsem_step_host.argtypes = [vp, vp, C.c_int32, dp, dp, vp]
+        L.idp_dgsem_integrals.argtypes = [vp, vp, dp, vp]
+        L.idp_dgsem_limiter_stats.argtypes = [vp, C.POINTER(LimiterStats), vp]
+        L.idp_dgsem_sync.argtypes = [vp, vp]
+        L.idp_dgsem_destroy.argtypes = [vp]
+        L.idp_dgsem_destroy.restype = None
+        for f in EXPORTS:
+            if f not in ("idp_dgsem_destroy", "idp_status_str", "idp_last_cuda_error"):
+                getattr(L, f).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+class IdpError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        msg = f"{where}: {lib().idp_status_str(code).decode()} (status {code})"
+        if code == IDP_E_CUDA:
+            msg += f" [{lib().idp_last_cuda_error().decode()}]"
+        super().__init__(msg)
+
+
+def _check(code, where):
+    if code != IDP_OK:
+        raise IdpError(code, where)
+
+
+def options(**kw) -> Options:
+    o = Options()
+    lib().idp_options_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def mesh_desc(mesh) -> tuple:
+    """MeshDesc for a workloads.Mesh plus the arrays it points into."""
+    lev = np.ascontiguousarray(mesh.level, dtype=np.int8)
+    ix = np.ascontiguousarray(mesh.ix, dtype=np.int32)
+    iy = np.ascontiguousarray(mesh.iy, dtype=np.int32)
+    d = MeshDesc()
+    d.nx0, d.ny0 = int(mesh.nx0), int(mesh.ny0)
+    d.x0, d.y0, d.x1, d.y1 = (float(v) for v in mesh.box)
+    d.n_leaves = int(lev.shape[0])
+    d.level = lev.ctypes.data_as(C.POINTER(C.c_int8))
+    d.ix = ix.ctypes.data_as(C.POINTER(C.c_int32))
+    d.iy = iy.ctypes.data_as(C.POINTER(C.c_int32))
+    for s in range(4):
+        d.bc[s] = int(mesh.bc[s])
+        for v in range(4):
+            d.bc_prim[s][v] = float(np.asarray(mesh.bc_prim)[s][v])
+    for v in range(4):
+        d.dmr_post[v] = float(mesh.dmr_post[v])
+        d.dmr_pre[v] = float(mesh.dmr_pre[v])
+    return d, (lev, ix, iy)
+
+
+def _ptr(t):
+    import torch
+    assert t.is_cuda and t.dtype == torch.float64 and t.is_contiguous(), "FP64 contiguous CUDA tensor expected"
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is not None:
+        return C.c_void_p(stream)
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+class Context:
+    """idp_dgsem context for one mesh (or a batch of meshes)."""
+
+    def __init__(self, meshes, N: int, gamma: float = 1.4, opts: Optional[Options] = None, **kw):
+        if opts is None:
+            opts = options(**kw)
+        self.N, self.np, self.gamma, self.opts = N, N + 1, gamma, opts
+        single = not isinstance(meshes, (list, tuple))
+        ml = [meshes] if single else list(meshes)
+        descs, self._keep = [], []
+        for m in ml:
+            d, keep = mesh_desc(m)
+            descs.append(d)
+            self._keep.append(keep)
+        arr = (MeshDesc * len(descs))(*descs)
+        h = C.c_void_p()
+        if single:
+            rc = lib().idp_dgsem_create(C.byref(arr[0]), N, gamma, C.byref(opts), C.byref(h))
+        else:
+            rc = lib().idp_dgsem_create_batch(arr, len(descs), N, gamma, C.byref(opts), C.byref(h))
+        _check(rc, "idp_dgsem_create")
+        self._h = h
+        K, M, S = C.c_int64(), C.c_int64(), C.c_int32()
+        _check(lib().idp_dgsem_layout(h, C.byref(K), C.byref(M), C.byref(S), None), "idp_dgsem_layout")
+        self.K, self.M, self.n_sims = K.value, M.value, S.value
+        off = (C.c_int64 * (self.n_sims + 1))()
+        lib().idp_dgsem_layout(h, None, None, None, off)
+        self.sim_offsets = np.array(off[:], dtype=np.int64)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().idp_dgsem_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (4, self.K, self.np, self.np)
+
+    def idp_dgsem_rhs(self, u, t, dt, out, stream=None):
+        _check(lib().idp_dgsem_rhs(self._h, _ptr(u), float(t), float(dt), _ptr(out), _stream(stream)), "idp_dgsem_rhs")
+
+    def idp_dgsem_dt(self, u, t=None, stream=None):
+        th = np.zeros(self.n_sims) if t is None else np.ascontiguousarray(np.broadcast_to(t, self.n_sims), dtype=np.float64)
+        out = np.zeros(self.n_sims)
+        dp = C.POINTER(C.c_double)
+        _check(lib().idp_dgsem_dt(self._h, _ptr(u), th.ctypes.data_as(dp), out.ctypes.data_as(dp), _stream(stream)),
+               "idp_dgsem_dt")
+        return out
+
+    def idp_dgsem_step(self, u, n_steps, t, stream=None, check=True):
+        """Advance u in place; t: per-sim times (array, updated in place). Returns (status, dt_last)."""
+        dp = C.POINTER(C.c_double)
+        dtl = np.zeros(self.n_sims)
+        rc = lib().idp_dgsem_step(self._h, _ptr(u), int(n_steps), t.ctypes.data_as(dp), dtl.ctypes.data_as(dp),
+                                  _stream(stream))
+        if check:
+            _check(rc, "idp_dgsem_step")
+        return rc, dtl
+
+    def idp_dgsem_step_host(self, u_host, n_steps, t, stream=None, check=True):
+        """u_host: a (pinned) CPU torch tensor or numpy array, updated in place."""
+        dp = C.POINTER(C.c_double)
+        dtl = np.zeros(self.n_sims)
+        ptr = C.c_void_p(u_host.data_ptr()) if hasattr(u_host, "data_ptr") else u_host.ctypes.data_as(C.c_void_p)
+        rc = lib().idp_dgsem_step_host(self._h, ptr, int(n_steps), t.ctypes.data_as(dp), dtl.ctypes.data_as(dp),
+                                       _stream(stream))
+        if check:
+            _check(rc, "idp_dgsem_step_host")
+        return rc, dtl
+
+    def idp_dgsem_integrals(self, u, stream=None):
+        out = np.zeros((self.n_sims, 4))
+        _check(lib().idp_dgsem_integrals(self._h, _ptr(u), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                         _stream(stream)), "idp_dgsem_integrals")
+        return out
+
+    def idp_dgsem_limiter_stats(self, stream=None, check=False):
+        st = LimiterStats()
+        rc = lib().idp_dgsem_limiter_stats(self._h, C.byref(st), _stream(stream))
+        if check:
+            _check(rc, "idp_dgsem_limiter_stats")
+        return rc, st.as_dict()
+
+    def idp_dgsem_sync(self, stream=None):
+        return lib().idp_dgsem_sync(self._h, _stream(stream))

@@ -1,0 +1,242 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 CPU oracle on
+the same seeded inputs.
+
+Tolerances (FP64 path): per right-hand side 1e-12 relative to the residual
+scale max|u_v| / dt_idp (the change of u over one IDP step, see
+conftest.rhs_scale); after 100 SSP-RK3 steps 1e-10 relative to max|u_v|.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_err, rhs_scale
+from paper_2607_06045_b300 import build, idp
+from paper_2607_06045_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    yield
+
+
+def dev(u):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(u)).cuda()
+
+
+def gpu_rhs(ctx, u, t, dt):
+    import torch
+    ud = dev(u)
+    out = torch.empty_like(ud)
+    ctx.idp_dgsem_rhs(ud, t, dt, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def check_rhs(mesh, N, u, limiting, t=0.0, cfl=0.5, gamma=1.4, tol=1e-12, precision=0, **kw):
+    o = oracle.Oracle(mesh, N, gamma=gamma)
+    ctx = idp.Context(mesh, N, gamma=gamma, limiting=limiting, precision=precision, **kw)
+    dt_idp = o.dt(u, t, cfl=1.0)
+    scale = rhs_scale(u, dt_idp)
+    r_o = o.rhs(u, t=t, dt=0.0)
+    r_g = gpu_rhs(ctx, u, t, 0.0)
+    e0 = rel_err(r_g, r_o, scale)
+    assert e0 <= tol, ("dg", e0)
+    if limiting:
+        dt = cfl * dt_idp
+        r_o = o.rhs(u, t=t, dt=dt, limiting=limiting)
+        r_g = gpu_rhs(ctx, u, t, dt)
+        e1 = rel_err(r_g, r_o, scale)
+        assert e1 <= tol, ("limited", e1)
+    ctx.close()
+
+
+@pytest.mark.parametrize("limiting", [1, 2])
+def test_cfg1_rhs(limiting):
+    m = W.cfg1_mesh()
+    check_rhs(m, 3, W.cfg1_state(m, 3), limiting)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
+def test_degrees_rough_state(N):
+    m = W.box_refined_mesh(5, 4, (0.0, 0.0, 1.25, 1.0), (0.3, 0.3, 0.8, 0.7))
+    u = W.random_state(m, N, seed=N, rho_range=(0.2, 3.0), p_range=(0.2, 3.0), vmax=1.0)
+    check_rhs(m, N, u, 2)
+
+
+@pytest.mark.parametrize("N", [3, 4, 7])
+def test_degrees_smooth_state_positivity(N):
+    m = W.box_refined_mesh(6, 6, (0.0, 0.0, 1.0, 1.0), (0.2, 0.2, 0.6, 0.5))
+    check_rhs(m, N, W.smooth_random_state(m, N, seed=10 + N), 1)
+
+
+@pytest.mark.parametrize("bc", [W.BC_WALL, W.BC_DIRICHLET, W.BC_OUTFLOW])
+def test_boundaries(bc):
+    m = W.box_refined_mesh(5, 3, (0.0, 0.0, 2.0, 1.0), (0.5, 0.3, 1.5, 0.7), bc=(bc,) * 4)
+    m.bc_prim = np.array([[1.2, 0.3, -0.1, 1.1], [0.9, 0.1, 0.2, 0.8], [1.0, -0.2, 0.3, 1.0], [1.1, 0.0, 0.0, 0.9]])
+    u = W.random_state(m, 3, seed=7 + bc)
+    check_rhs(m, 3, u, 2)
+
+
+def test_dmr_boundaries():
+    m = W.box_refined_mesh(16, 4, (0.0, 0.0, 4.0, 1.0), (0.0, 0.0, 1.0, 0.5), bc=(W.BC_DMR,) * 4)
+    m.dmr_post = W.DMR_POST.copy()
+    m.dmr_pre = W.DMR_PRE.copy()
+    u = W.cfg2_state(m, 3)
+    for t in (0.0, 0.05):
+        check_rhs(m, 3, u, 2, t=t)
+
+
+def test_dt_parity():
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    o = oracle.Oracle(m, 3)
+    for rule in (0, 1):
+        ctx = idp.Context(m, 3, dt_rule=rule, cfl=0.7)
+        d = ctx.idp_dgsem_dt(dev(u))[0]
+        assert abs(d - o.dt(u, cfl=0.7, rule=rule)) <= 1e-13 * d
+        ctx.close()
+
+
+@pytest.mark.parametrize("limiting", [1, 2])
+def test_cfg1_100_steps(limiting):
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    o = oracle.Oracle(m, 3)
+    u_o, t_o, dts, st = o.step(u, 100, cfl=0.5, limiting=limiting)
+    ctx = idp.Context(m, 3, limiting=limiting, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    ctx.idp_dgsem_step(ud, 100, t)
+    u_g = ud.cpu().numpy()
+    scale = np.abs(u_o).reshape(4, -1).max(axis=1)
+    err = (np.abs(u_g - u_o).reshape(4, -1).max(axis=1) / scale).max()
+    assert err <= 1e-10, err
+    assert abs(t[0] - t_o) <= 1e-12 * t_o
+    rc, s = ctx.idp_dgsem_limiter_stats()
+    assert rc == idp.IDP_OK
+    assert s["n_viol_density"] == 0 and s["n_viol_pressure"] == 0 and s["n_nonpositive"] == 0
+    assert s["n_stages"] == 300
+    ctx.close()
+
+
+def test_epb_invariance():
+    import torch
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    dt = oracle.Oracle(m, 3).dt(u, cfl=0.5)
+    outs = []
+    for epb in (1, 2, 4, 8, 16):
+        ctx = idp.Context(m, 3, elems_per_block=epb)
+        outs.append(gpu_rhs(ctx, u, 0.0, dt))
+        ctx.close()
+    for o in outs[1:]:
+        assert np.array_equal(o, outs[0])
+
+
+def test_batched_matches_individual():
+    ms = [W.cfg1_mesh(), W.box_refined_mesh(6, 4, (0.0, 0.0, 1.5, 1.0), (0.2, 0.2, 0.9, 0.6)),
+          W.uniform_mesh(5, 5, bc=(W.BC_OUTFLOW,) * 4)]
+    us = [W.cfg1_state(ms[0], 3), W.smooth_random_state(ms[1], 3, seed=3), W.random_state(ms[2], 3, seed=4)]
+    ctx = idp.Context(ms, 3, cfl=0.5)
+    ub = W.concat_states(us)
+    ud = dev(ub)
+    t = np.zeros(3)
+    ctx.idp_dgsem_step(ud, 5, t)
+    u_g = ud.cpu().numpy()
+    off = ctx.sim_offsets
+    for s in range(3):
+        o = oracle.Oracle(ms[s], 3)
+        u_o, t_o, _, _ = o.step(us[s], 5, cfl=0.5)
+        part = u_g[:, off[s]:off[s + 1]]
+        scale = np.abs(u_o).reshape(4, -1).max(axis=1)
+        err = (np.abs(part - u_o).reshape(4, -1).max(axis=1) / scale).max()
+        assert err <= 1e-11, (s, err)
+        assert abs(t[s] - t_o) <= 1e-12 * t_o
+    ctx.close()
+
+
+def test_conservation_and_free_stream():
+    import torch
+    m = W.cfg1_mesh()
+    sh = (m.n_elems, 4, 4)
+    uf = W.conserved(1.3 * np.ones(sh), 0.4 * np.ones(sh), -0.7 * np.ones(sh), 2.0 * np.ones(sh), 1.4)
+    ctx = idp.Context(m, 3)
+    r = gpu_rhs(ctx, uf, 0.0, 0.0)
+    mm = oracle.Oracle(m, 3).masses()
+    assert np.abs(r).max() < 1e-12 * 3.0 / mm.min()
+    u = W.cfg1_state(m, 3)
+    ud = dev(u)
+    I0 = ctx.idp_dgsem_integrals(ud)[0]
+    t = np.zeros(1)
+    ctx.idp_dgsem_step(ud, 50, t)
+    I1 = ctx.idp_dgsem_integrals(ud)[0]
+    scale = (mm[None] * np.abs(u)).reshape(4, -1).sum(axis=1)
+    assert (np.abs(I1 - I0) / scale).max() <= 1e-13
+    ctx.close()
+
+
+def test_invalid_state_reported():
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    u[0, 5, 1, 1] = -1.0
+    ctx = idp.Context(m, 3)
+    ud = dev(u)
+    t = np.zeros(1)
+    rc, _ = ctx.idp_dgsem_step(ud, 1, t, check=False)
+    assert rc == idp.IDP_E_STATE
+    ctx.close()
+
+
+def test_step_host_equals_device():
+    import torch
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    ctx = idp.Context(m, 3)
+    ud = dev(u)
+    t1 = np.zeros(1)
+    ctx.idp_dgsem_step(ud, 3, t1)
+    uh = torch.from_numpy(u.copy()).pin_memory()
+    t2 = np.zeros(1)
+    ctx.idp_dgsem_step_host(uh, 3, t2)
+    assert np.array_equal(uh.numpy(), ud.cpu().numpy())
+    assert t1[0] == t2[0]
+    ctx.close()
+
+
+def test_cfg2_full_size_rhs():
+    """Full-size DMR workload (about 60k elements) in the benchmark's launch
+    configuration: the limited right-hand side on every node."""
+    m = W.cfg2_mesh()
+    u = W.cfg2_state(m, 3)
+    check_rhs(m, 3, u, 2)
+
+
+def test_fp32_form_error_cfg3():
+    """FP32 form (flux arithmetic in FP32, limiter and sums in FP64) against the
+    FP64 oracle: density L1 error and zero positivity violations."""
+    m = W.cfg1_mesh()
+    for N in (4, 7):
+        u = W.cfg1_state(m, N)
+        o = oracle.Oracle(m, N)
+        nst = 20
+        u_o, t_o, _, _ = o.step(u, nst, cfl=0.5)
+        ctx = idp.Context(m, N, precision=1, cfl=0.5)
+        ud = dev(u)
+        t = np.zeros(1)
+        ctx.idp_dgsem_step(ud, nst, t)
+        u_g = ud.cpu().numpy()
+        mm = o.masses()
+        l1 = (mm * np.abs(u_g[0] - u_o[0])).sum() / (mm * np.abs(u_o[0])).sum()
+        assert l1 <= 1e-5, (N, l1)
+        rc, s = ctx.idp_dgsem_limiter_stats()
+        assert s["n_nonpositive"] == 0 and s["n_viol_pressure"] == 0
+        ctx.close()
