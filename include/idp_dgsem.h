@@ -198,6 +198,25 @@ idp_status idp_dgsem_integrals(idp_ctx *ctx, const double *u, double *out_host, 
 /* Read and reset the accumulated limiter statistics (synchronises). */
 idp_status idp_dgsem_limiter_stats(idp_ctx *ctx, idp_limiter_stats *out, void *stream);
 
+/* Measurement support (the paper has no counterpart). mode 1: each step's
+ * CUDA-graph launch is bracketed by CUDA events on the step's stream; mode 2:
+ * steps are launched kernel by kernel (no graph) with events around the step
+ * and around each element-pass launch; mode 0: off. In modes 1 and 2
+ * idp_dgsem_step synchronises after every step to accumulate the durations.
+ * idp_dgsem_profile_read returns the accumulated element-pass milliseconds
+ * and launches, and step milliseconds and steps (any pointer may be NULL;
+ * reset != 0 clears them). */
+idp_status idp_dgsem_profile(idp_ctx *ctx, int32_t mode);
+idp_status idp_dgsem_profile_read(idp_ctx *ctx, double *element_ms, int64_t *element_launches,
+                                  double *step_ms, int64_t *steps, int32_t reset);
+
+/* Pipe-throughput probe used as the roofline denominator (no counterpart in
+ * the paper): runs short kernels on the current device and stream and writes
+ * out[0] FP64 TFLOP/s (DFMA, 2 flops each), out[1] FP32 TFLOP/s (FFMA),
+ * out[2..4] the cost of one FP64 division, square root and logarithm
+ * (CUDA's routines, each plus one add) in DFMA-equivalents. Synchronises. */
+idp_status idp_probe_pipes(double *out, void *stream);
+
 /* Synchronise the stream and report any device-flagged condition. */
 idp_status idp_dgsem_sync(idp_ctx *ctx, void *stream);
 

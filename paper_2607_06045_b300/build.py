@@ -51,6 +51,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     os.makedirs(BUILD, exist_ok=True)
     tasks = [(os.path.join(CSRC, "k_inst.cu"), os.path.join(BUILD, f"k_np{n}.o"), [f"-DIDP_NP={n}"]) for n in NPS]
     tasks.append((os.path.join(CSRC, "idp_host.cu"), os.path.join(BUILD, "idp_host.o"), []))
+    tasks.append((os.path.join(CSRC, "k_probe.cu"), os.path.join(BUILD, "k_probe.o"), []))
     jobs = jobs or min(len(tasks), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(_compile, tasks))

@@ -395,6 +395,12 @@ struct idp_ctx {
     cudaGraphExec_t graph = nullptr;
     const double *graph_u = nullptr;
     long long n_stages = 0;
+    // optional timing: 1 step spans around the graph launches; 2 steps
+    // launched without the graph, with element-pass events
+    int prof = 0;
+    cudaEvent_t pev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+    double prof_ms = 0.0, prof_step_ms = 0.0;
+    long long prof_n = 0, prof_steps = 0;
 };
 
 namespace {
@@ -423,11 +429,15 @@ StageArgs base_args(idp_ctx *c) {
     return A;
 }
 
-// one stage: mortar fluxes (unless already current), element pass, mortar limiting
-void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux) {
+// one stage: mortar fluxes (unless already current), element pass, mortar
+// limiting; ev0/ev1 (optional) bracket the element pass
+void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux,
+                   cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
     const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
     if (c->M > 0 && need_mortar_flux) c->L.mortar_flux(gm, st, c->mesh, c->slots, A.u, c->gamma, c->d_ops);
+    if (ev0) cudaEventRecord(ev0, st);
     c->L.element(c->opt.precision, c->epb, element_grid(c, c->epb, c->persistent, c->bps), st, c->mesh, c->slots, A);
+    if (ev1) cudaEventRecord(ev1, st);
     bool dgmode = (A.mode == 0 && A.dt == 0.0) || A.limiting == 0;
     if (c->M > 0 && !dgmode) {
         c->L.mortar_limit(gm, st, c->mesh, c->slots, A);
@@ -453,14 +463,15 @@ void enqueue_step(idp_ctx *c, cudaStream_t st, double *u) {
     A.mode = 1;
     A.un = u;
     // stage 1: u1 = ut(u)
+    cudaEvent_t *ev = c->prof == 2 ? c->pev : nullptr;
     A.u = u; A.out = c->d_buf1; A.comb = 0; A.tstage = 0.0;
-    enqueue_stage(c, st, A, c->opt.dt_rule != 0);
+    enqueue_stage(c, st, A, c->opt.dt_rule != 0, ev ? ev[0] : nullptr, ev ? ev[1] : nullptr);
     // stage 2: u2 = 3/4 u + 1/4 ut(u1)
     A.u = c->d_buf1; A.out = c->d_buf2; A.comb = 1; A.tstage = 1.0;
-    enqueue_stage(c, st, A, true);
+    enqueue_stage(c, st, A, true, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr);
     // stage 3: u3 = u/3 + 2/3 ut(u2), in place
     A.u = c->d_buf2; A.out = u; A.comb = 2; A.tstage = 0.5;
-    enqueue_stage(c, st, A, true);
+    enqueue_stage(c, st, A, true, ev ? ev[4] : nullptr, ev ? ev[5] : nullptr);
     k_time_advance<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_tsim, c->d_dtmin, c->opt.cfl, c->d_dtlast,
                                                            c->n_sims);
 }
@@ -784,9 +795,12 @@ idp_status idp_dgsem_step(idp_ctx *c, double *u, int32_t n_steps, double *t_host
                           void *stream) {
     if (!c || !u || n_steps < 0 || !t_host) return IDP_E_ARG;
     cudaStream_t ust = (cudaStream_t)stream;
-    cudaStream_t st = c->stream;
-    // order after the caller's stream
-    if (cudaEventRecord(c->ev_in, ust) != cudaSuccess || cudaStreamWaitEvent(st, c->ev_in, 0) != cudaSuccess)
+    // steps run on the caller's stream; the legacy default stream cannot be
+    // captured into a graph, so then the context's own stream is used,
+    // ordered after the caller's
+    const bool own = ust == nullptr;
+    cudaStream_t st = own ? c->stream : ust;
+    if (own && (cudaEventRecord(c->ev_in, ust) != cudaSuccess || cudaStreamWaitEvent(st, c->ev_in, 0) != cudaSuccess))
         return IDP_E_CUDA;
     if (cudaMemcpyAsync(c->d_tsim, t_host, sizeof(double) * c->n_sims, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return IDP_E_CUDA;
@@ -801,8 +815,26 @@ idp_status idp_dgsem_step(idp_ctx *c, double *u, int32_t n_steps, double *t_host
         idp_status r = autotune(c, u, st, std::isfinite(v) ? c->opt.cfl * v : 0.0);
         if (r != IDP_OK) return r;
     }
-    if (n_steps > 0) {
-        if (c->graph == nullptr || c->graph_u != u) {
+    if (n_steps > 0 && c->prof == 2) {
+        for (int k = 0; k < n_steps; ++k) {
+            cudaEventRecord(c->pev[6], st);
+            enqueue_step(c, st, u);
+            cudaEventRecord(c->pev[7], st);
+            if (note(cudaStreamSynchronize(st), "step") != cudaSuccess) return IDP_E_CUDA;
+            float ms = 0.f;
+            for (int s = 0; s < 3; ++s) {
+                if (note(cudaEventElapsedTime(&ms, c->pev[2 * s], c->pev[2 * s + 1]), "profile") != cudaSuccess)
+                    return IDP_E_CUDA;
+                c->prof_ms += ms;
+                c->prof_n += 1;
+            }
+            if (note(cudaEventElapsedTime(&ms, c->pev[6], c->pev[7]), "profile") != cudaSuccess) return IDP_E_CUDA;
+            c->prof_step_ms += ms;
+            c->prof_steps += 1;
+        }
+        c->n_stages += 3LL * n_steps;
+    } else if (n_steps > 0) {
+        if (c->graph == nullptr || c->graph_u != u) {   // re-captured when u changes
             if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
             cudaGraph_t g;
             if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return IDP_E_CUDA;
@@ -813,16 +845,28 @@ idp_status idp_dgsem_step(idp_ctx *c, double *u, int32_t n_steps, double *t_host
             if (e != cudaSuccess) { c->graph = nullptr; return IDP_E_CUDA; }
             c->graph_u = u;
         }
-        for (int k = 0; k < n_steps; ++k)
-            if (cudaGraphLaunch(c->graph, st) != cudaSuccess) return IDP_E_CUDA;
+        for (int k = 0; k < n_steps; ++k) {
+            if (c->prof) cudaEventRecord(c->pev[6], st);
+            if (note(cudaGraphLaunch(c->graph, st), "graph launch") != cudaSuccess) return IDP_E_CUDA;
+            if (c->prof) {
+                cudaEventRecord(c->pev[7], st);
+                if (note(cudaStreamSynchronize(st), "step") != cudaSuccess) return IDP_E_CUDA;
+                float ms = 0.f;
+                if (note(cudaEventElapsedTime(&ms, c->pev[6], c->pev[7]), "profile") != cudaSuccess) return IDP_E_CUDA;
+                c->prof_step_ms += ms;
+                c->prof_steps += 1;
+            }
+        }
         c->n_stages += 3LL * n_steps;
     }
     cudaMemcpyAsync(t_host, c->d_tsim, sizeof(double) * c->n_sims, cudaMemcpyDeviceToHost, st);
     if (dt_last_host && n_steps > 0)
         cudaMemcpyAsync(dt_last_host, c->d_dtlast, sizeof(double) * c->n_sims, cudaMemcpyDeviceToHost, st);
-    cudaEventRecord(c->ev_out, st);
-    cudaStreamWaitEvent(ust, c->ev_out, 0);
-    if (cudaStreamSynchronize(st) != cudaSuccess) return IDP_E_CUDA;
+    if (own) {
+        cudaEventRecord(c->ev_out, st);
+        cudaStreamWaitEvent(ust, c->ev_out, 0);
+    }
+    if (note(cudaStreamSynchronize(st), "step sync") != cudaSuccess) return IDP_E_CUDA;
     return read_status(c);
 }
 
@@ -879,6 +923,26 @@ idp_status idp_dgsem_limiter_stats(idp_ctx *c, idp_limiter_stats *out, void *str
     return read_status(c);
 }
 
+idp_status idp_dgsem_profile(idp_ctx *c, int32_t mode) {
+    if (!c || mode < 0 || mode > 2) return IDP_E_ARG;
+    if (mode && !c->pev[0])
+        for (int k = 0; k < 8; ++k)
+            if (note(cudaEventCreate(&c->pev[k]), "profile events") != cudaSuccess) return IDP_E_CUDA;
+    c->prof = mode;
+    return IDP_OK;
+}
+
+idp_status idp_dgsem_profile_read(idp_ctx *c, double *element_ms, int64_t *element_launches, double *step_ms,
+                                  int64_t *steps, int32_t reset) {
+    if (!c) return IDP_E_ARG;
+    if (element_ms) *element_ms = c->prof_ms;
+    if (element_launches) *element_launches = c->prof_n;
+    if (step_ms) *step_ms = c->prof_step_ms;
+    if (steps) *steps = c->prof_steps;
+    if (reset) { c->prof_ms = 0.0; c->prof_n = 0; c->prof_step_ms = 0.0; c->prof_steps = 0; }
+    return IDP_OK;
+}
+
 idp_status idp_dgsem_sync(idp_ctx *c, void *stream) {
     if (!c) return IDP_E_ARG;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
@@ -897,6 +961,8 @@ void idp_dgsem_destroy(idp_ctx *c) {
         if (p) cudaFree(p);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
     if (c->ev_out) cudaEventDestroy(c->ev_out);
+    for (int k = 0; k < 8; ++k)
+        if (c->pev[k]) cudaEventDestroy(c->pev[k]);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

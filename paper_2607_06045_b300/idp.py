@@ -51,7 +51,7 @@ _lib = None
 EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", "idp_dgsem_layout",
            "idp_dgsem_rhs", "idp_dgsem_dt", "idp_dgsem_step", "idp_dgsem_step_host", "idp_dgsem_integrals",
            "idp_dgsem_limiter_stats", "idp_dgsem_sync", "idp_dgsem_destroy", "idp_status_str",
-           "idp_last_cuda_error"]
+           "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_probe_pipes"]
 
 
 def lib():
@@ -80,6 +80,9 @@ def lib():
         L.idp_dgsem_limiter_stats.argtypes = [vp, C.POINTER(LimiterStats), vp]
         L.idp_dgsem_sync.argtypes = [vp, vp]
         L.idp_dgsem_destroy.argtypes = [vp]
+        L.idp_dgsem_profile.argtypes = [vp, C.c_int32]
+        L.idp_dgsem_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64), dp, C.POINTER(C.c_int64), C.c_int32]
+        L.idp_probe_pipes.argtypes = [dp, vp]
         L.idp_dgsem_destroy.restype = None
         for f in EXPORTS:
             if f not in ("idp_dgsem_destroy", "idp_status_str", "idp_last_cuda_error"):
@@ -100,6 +103,13 @@ class IdpError(RuntimeError):
 def _check(code, where):
     if code != IDP_OK:
         raise IdpError(code, where)
+
+
+def idp_probe_pipes(stream=None):
+    """[FP64 TFLOP/s, FP32 TFLOP/s, div, sqrt, log cost in DFMA-equivalents]."""
+    out = (C.c_double * 5)()
+    _check(lib().idp_probe_pipes(out, _stream(stream)), "idp_probe_pipes")
+    return list(out)
 
 
 def options(**kw) -> Options:
@@ -233,6 +243,26 @@ class Context:
         if check:
             _check(rc, "idp_dgsem_limiter_stats")
         return rc, st.as_dict()
+
+    def idp_dgsem_profile(self, mode=1):
+        """0 off; 1 step spans around graph launches; 2 kernel-by-kernel steps with element-pass events."""
+        _check(lib().idp_dgsem_profile(self._h, int(mode)), "idp_dgsem_profile")
+
+    def idp_dgsem_profile_read(self, reset=True):
+        """(element-pass ms, element launches, step ms, steps) accumulated since the last reset."""
+        ms, n, sms, ns = C.c_double(), C.c_int64(), C.c_double(), C.c_int64()
+        _check(lib().idp_dgsem_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(sms), C.byref(ns),
+                                            1 if reset else 0), "idp_dgsem_profile_read")
+        return ms.value, n.value, sms.value, ns.value
+
+    def launches_per_step(self):
+        """Kernels one SSP-RK3 step launches (mirrors the step sequence)."""
+        M = self.M > 0
+        lim = self.opts.limiting > 0
+        n = 1 + (1 if (M and self.opts.dt_rule == 0) else 0) + 1          # dt init, mortar flux, dt
+        n += (1 if (M and self.opts.dt_rule != 0) else 0) + 1 + (2 if (M and lim) else 0)   # stage 1
+        n += 2 * ((1 if M else 0) + 1 + (2 if (M and lim) else 0))          # stages 2, 3
+        return n + 1                                                        # time advance
 
     def idp_dgsem_sync(self, stream=None):
         return lib().idp_dgsem_sync(self._h, _stream(stream))

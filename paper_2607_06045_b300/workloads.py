@@ -244,7 +244,7 @@ DMR_POST = np.array([8.0, 8.25 * math.cos(math.pi / 6), -8.25 * math.sin(math.pi
 DMR_PRE = np.array([1.4, 0.0, 0.0, 1.0])
 
 
-def cfg2_mesh(seed=0, target=(54000, 66000), max_extra=3):
+def cfg2_mesh(seed=0, target=(54000, 66000), max_extra=3, nx0=256, ny0=64):
     """[0,4] x [0,1], 256 x 64 base grid, up to three extra levels where a
     density-jump indicator fires across the 60 degree Mach-10 shock, balanced
     2:1; the indicator threshold is bisected until K lies in ``target``.
@@ -252,7 +252,7 @@ def cfg2_mesh(seed=0, target=(54000, 66000), max_extra=3):
     The indicator compares the density of a smoothed shock profile (width
     0.05) between each leaf and its face neighbours; a seeded jitter of 1e-3 in
     the threshold breaks ties between equal jumps."""
-    nx0, ny0, box = 256, 64, (0.0, 0.0, 4.0, 1.0)
+    box = (0.0, 0.0, 4.0, 1.0)
     rng = np.random.default_rng(seed)
     jitter = 1.0 + 1e-3 * rng.standard_normal()
     L = max_extra
@@ -292,6 +292,12 @@ def cfg2_mesh(seed=0, target=(54000, 66000), max_extra=3):
     m.dmr_post = DMR_POST.copy()
     m.dmr_pre = DMR_PRE.copy()
     return m
+
+
+def cfg2_sample_mesh(seed=0):
+    """A 1/16-size instance of the same DMR workload (64 x 16 base grid, the
+    same three-level shock refinement, K in [3400, 4100]) for CPU timing."""
+    return cfg2_mesh(seed=seed, target=(3400, 4100), nx0=64, ny0=16)
 
 
 def cfg2_state(mesh: Mesh, N: int, gamma=1.4):
