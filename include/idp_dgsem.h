@@ -217,6 +217,30 @@ idp_status idp_dgsem_profile_read(idp_ctx *ctx, double *element_ms, int64_t *ele
  * (CUDA's routines, each plus one add) in DFMA-equivalents. Synchronises. */
 idp_status idp_probe_pipes(double *out, void *stream);
 
+/* Largest element count accepted by idp_integrals_noalloc. */
+#define IDP_NOALLOC_MAX_ELEMS (1 << 19)
+
+/* Conservation totals without any device allocation (the paper has no
+ * counterpart). For callers that may not call cudaMalloc: one recording a
+ * CUDA graph, a framework that forbids allocations after start-up, or a host
+ * callback. Computes out[s][v] = sum over the elements e in
+ * [sim_elem_offsets[s], sim_elem_offsets[s+1]) of sum_ij (elem_area[e] / 4)
+ * w_i w_j u[v][e][j][i], the same totals as idp_dgsem_integrals, with no
+ * context. All pointers are caller-owned DEVICE memory: u (layout as above,
+ * n_elems elements, degree N), elem_area (n_elems values dx * dy),
+ * sim_elem_offsets (n_sims + 1 values) and out (4 * n_sims values). The
+ * per-element partial sums go to a fixed array of 4 * IDP_NOALLOC_MAX_ELEMS
+ * doubles (16 MiB) that the library keeps on every device it is used on
+ * until the process exits; n_elems above IDP_NOALLOC_MAX_ELEMS returns
+ * IDP_E_ARG. The first call on a device looks up that array's device address
+ * (once per device, with the device current): make it before any stream
+ * capture. All calls share the array, so calls that overlap on the GPU race;
+ * each call overwrites the partials it reads, nothing carries over between
+ * calls. Asynchronous on `stream`; calls no allocating routine. */
+idp_status idp_integrals_noalloc(const double *u, const double *elem_area, int64_t n_elems, int32_t N,
+                                 const int64_t *sim_elem_offsets, int32_t n_sims, double *out,
+                                 void *stream);
+
 /* Synchronise the stream and report any device-flagged condition. */
 idp_status idp_dgsem_sync(idp_ctx *ctx, void *stream);
 

@@ -52,6 +52,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     tasks = [(os.path.join(CSRC, "k_inst.cu"), os.path.join(BUILD, f"k_np{n}.o"), [f"-DIDP_NP={n}"]) for n in NPS]
     tasks.append((os.path.join(CSRC, "idp_host.cu"), os.path.join(BUILD, "idp_host.o"), []))
     tasks.append((os.path.join(CSRC, "k_probe.cu"), os.path.join(BUILD, "k_probe.o"), []))
+    tasks.append((os.path.join(CSRC, "k_noalloc.cu"), os.path.join(BUILD, "k_noalloc.o"), []))
     jobs = jobs or min(len(tasks), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(_compile, tasks))

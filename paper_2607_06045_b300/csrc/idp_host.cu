@@ -358,6 +358,14 @@ std::map<long long, std::pair<int, int>> g_tune_cache;   // key -> (epb, persist
 
 }  // namespace
 
+namespace idp {
+// LGL quadrature weights for degree N (used by the allocation-free integrals)
+void host_lgl_weights(int N, double *w) {
+    double x[NPMAX];
+    lgl_nodes(N, x, w);
+}
+}  // namespace idp
+
 // ---------------------------------------------------------------------------
 // context
 // ---------------------------------------------------------------------------

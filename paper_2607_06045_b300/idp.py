@@ -51,7 +51,8 @@ _lib = None
 EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", "idp_dgsem_layout",
            "idp_dgsem_rhs", "idp_dgsem_dt", "idp_dgsem_step", "idp_dgsem_step_host", "idp_dgsem_integrals",
            "idp_dgsem_limiter_stats", "idp_dgsem_sync", "idp_dgsem_destroy", "idp_status_str",
-           "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_probe_pipes"]
+           "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_probe_pipes",
+           "idp_integrals_noalloc"]
 
 
 def lib():
@@ -83,6 +84,7 @@ def lib():
         L.idp_dgsem_profile.argtypes = [vp, C.c_int32]
         L.idp_dgsem_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64), dp, C.POINTER(C.c_int64), C.c_int32]
         L.idp_probe_pipes.argtypes = [dp, vp]
+        L.idp_integrals_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.c_int32, vp, vp]
         L.idp_dgsem_destroy.restype = None
         for f in EXPORTS:
             if f not in ("idp_dgsem_destroy", "idp_status_str", "idp_last_cuda_error"):
@@ -110,6 +112,21 @@ def idp_probe_pipes(stream=None):
     out = (C.c_double * 5)()
     _check(lib().idp_probe_pipes(out, _stream(stream)), "idp_probe_pipes")
     return list(out)
+
+
+NOALLOC_MAX_ELEMS = 1 << 19
+
+
+def idp_integrals_noalloc(u, elem_area, N, sim_offsets, out, stream=None):
+    """Allocation-free conservation totals; every argument is a caller-owned
+    CUDA tensor (u FP64 [4][K][N+1][N+1], elem_area FP64 [K], sim_offsets
+    int64 [n_sims+1], out FP64 [n_sims][4]). Returns the status code."""
+    import torch
+    assert elem_area.is_cuda and elem_area.dtype == torch.float64 and sim_offsets.dtype == torch.int64
+    assert out.is_cuda and out.dtype == torch.float64
+    return lib().idp_integrals_noalloc(_ptr(u), C.c_void_p(elem_area.data_ptr()), int(elem_area.shape[0]), int(N),
+                                       C.c_void_p(sim_offsets.data_ptr()), int(sim_offsets.shape[0] - 1),
+                                       C.c_void_p(out.data_ptr()), _stream(stream))
 
 
 def options(**kw) -> Options:
