@@ -92,66 +92,56 @@ __device__ __forceinline__ double pressure_d(double g, double r, double m1, doub
     return (g - 1.0) * (E - 0.5 * (m1 * m1 + m2 * m2) / r);
 }
 
-// Logarithmic mean {a}_ln = (a - b)/(ln a - ln b) from per-node logarithms,
-// with the Ismail-Roe series (a + b)/(2 F(u)), u = ((a-b)/(a+b))^2, for small u.
-template <typename FT> struct LogMean;
-
-template <> struct LogMean<double> {
-    __device__ __forceinline__ static double mean(double a, double b, double la, double lb) {
-        double d = a - b, s = a + b;
-        if (d * d < 1e-4 * (s * s)) {
-            double u = (d * d) / (s * s);
-            double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
-            return s / (2.0 * F);
-        }
-        return d / (la - lb);
-    }
-    // 1 / {a}_ln
-    __device__ __forceinline__ static double inv_mean(double a, double b, double la, double lb) {
-        double d = a - b, s = a + b;
-        if (d * d < 1e-4 * (s * s)) {
-            double u = (d * d) / (s * s);
-            double F = 1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0)));
-            return (2.0 * F) / s;
-        }
-        return (la - lb) / d;
-    }
-};
-
-template <> struct LogMean<float> {
-    // FP32 form: ln(a/b) per pair keeps the relative error near 1e-7 even for
-    // near-vacuum magnitudes; the series takes over below u = 1e-2.
-    __device__ __forceinline__ static float mean(float a, float b, float, float) {
-        float d = a - b, s = a + b;
-        if (d * d < 1e-2f * (s * s)) {
-            float u = (d * d) / (s * s);
-            float F = 1.0f + u * (1.0f / 3.0f + u * (1.0f / 5.0f + u * (1.0f / 7.0f)));
-            return s / (2.0f * F);
-        }
-        return d / logf(a / b);
-    }
-    __device__ __forceinline__ static float inv_mean(float a, float b, float, float) {
-        float d = a - b, s = a + b;
-        if (d * d < 1e-2f * (s * s)) {
-            float u = (d * d) / (s * s);
-            float F = 1.0f + u * (1.0f / 3.0f + u * (1.0f / 5.0f + u * (1.0f / 7.0f)));
-            return (2.0f * F) / s;
-        }
-        return logf(a / b) / d;
-    }
-};
-
 // Node primitives in the flux type.
 template <typename FT> struct Prim {
     FT rho, v1, v2, p, c, E, lr, lb, beta;
 };
 
+// Logarithmic means of Ranocha's flux with one division per pair: the
+// density mean {rho}_ln and the inverse mean 1/{rho/p}_ln. For each mean the
+// far branch is (a-b)/(ln a - ln b) from per-node logarithms (FP64) or
+// ln(a/b) (FP32); for u = ((a-b)/(a+b))^2 below 1e-4 (FP64) or 1e-2 (FP32)
+// the Ismail-Roe series (a+b)/(2 F(u)), F = 1 + u/3 + u^2/5 + u^3/7, with
+// 1/F from the inverted series 1 - u/3 - 4u^2/45 - 44u^3/945. The two
+// denominators share one reciprocal.
+template <typename FT>
+__device__ __forceinline__ void log_means(const Prim<FT> &a, const Prim<FT> &b, FT &rho_ln, FT &ibeta) {
+    constexpr bool dbl = sizeof(FT) == 8;
+    const FT thr = dbl ? FT(1e-4) : FT(1e-2);
+    FT dr = a.rho - b.rho, sr = a.rho + b.rho;
+    FT db = a.beta - b.beta, sb = a.beta + b.beta;
+    bool nr = dr * dr < thr * (sr * sr), nb = db * db < thr * (sb * sb);
+    FT lr, lb;
+    if (dbl) { lr = a.lr - b.lr; lb = a.lb - b.lb; }
+    else {
+        lr = nr ? FT(0) : (FT)logf((float)(a.rho / b.rho));
+        lb = nb ? FT(0) : (FT)logf((float)(a.beta / b.beta));
+    }
+    FT Xr = nr ? sr : lr, Xb = nb ? sb : db;
+    FT R = FT(1) / (Xr * Xb);
+    FT ixr = Xb * R, ixb = Xr * R;   // 1/Xr, 1/Xb
+    if (nr) {
+        FT f = dr * ixr, u = f * f;
+        FT invF = FT(1) - u * (FT(1.0 / 3.0) + u * (FT(4.0 / 45.0) + u * FT(44.0 / 945.0)));
+        rho_ln = FT(0.5) * sr * invF;
+    } else {
+        rho_ln = dr * ixr;
+    }
+    if (nb) {
+        FT f = db * ixb, u = f * f;
+        FT F = FT(1) + u * (FT(1.0 / 3.0) + u * (FT(1.0 / 5.0) + u * FT(1.0 / 7.0)));
+        ibeta = FT(2) * F * ixb;
+    } else {
+        ibeta = lb * ixb;
+    }
+}
+
 // Ranocha's entropy-conserving, kinetic-energy-preserving two-point flux
 // along axis d (reading R1; the paper names it in Sec. 3).
 template <typename FT>
 __device__ __forceinline__ void ranocha(const Prim<FT> &a, const Prim<FT> &b, int d, FT ginv1, FT f[4]) {
-    FT rho_ln = LogMean<FT>::mean(a.rho, b.rho, a.lr, b.lr);
-    FT ibeta = LogMean<FT>::inv_mean(a.beta, b.beta, a.lb, b.lb);   // 1/{rho/p}_ln
+    FT rho_ln, ibeta;
+    log_means<FT>(a, b, rho_ln, ibeta);
     FT v1m = FT(0.5) * (a.v1 + b.v1), v2m = FT(0.5) * (a.v2 + b.v2), pm = FT(0.5) * (a.p + b.p);
     FT vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
     FT fr = rho_ln * (FT(0.5) * (vna + vnb));
@@ -170,17 +160,52 @@ __device__ __forceinline__ void phys_flux(FT m1, FT m2, FT E, FT p, FT vn, int d
     f[3] = (E + p) * vn;
 }
 
-// Primitive state from a conserved state (double input).
+// Primitive state from a conserved state (double input). The pressure is
+// always formed in FP64 (E - |m|^2 / 2 rho cancels at high Mach numbers) with
+// one reciprocal of rho; with full = true also beta = rho / p and, in the
+// FP64 path, ln rho and ln beta = ln rho - ln p. The velocity, pressure and
+// sound speed use explicitly rounded operations so that every element that
+// forms them for the same node gets the same bits.
 template <typename FT>
-__device__ __forceinline__ Prim<FT> make_prim(double g, double r, double m1, double m2, double E, bool logs) {
+__device__ __forceinline__ Prim<FT> make_prim(double g, double r, double m1, double m2, double E, bool full) {
     Prim<FT> q;
-    double v1 = m1 / r, v2 = m2 / r;
-    double p = (g - 1.0) * (E - 0.5 * (m1 * v1 + m2 * v2));
+    double ri = __drcp_rn(r);
+    double v1 = __dmul_rn(m1, ri), v2 = __dmul_rn(m2, ri);
+    double ke = __dmul_rn(0.5, __dadd_rn(__dmul_rn(m1, v1), __dmul_rn(m2, v2)));
+    double p = __dmul_rn(g - 1.0, __dadd_rn(E, -ke));
     q.rho = (FT)r; q.v1 = (FT)v1; q.v2 = (FT)v2; q.p = (FT)p; q.E = (FT)E;
-    q.c = sqrt((FT)g * q.p / q.rho);
-    q.beta = q.rho / q.p;
-    if (logs) { q.lr = log(q.rho); q.lb = log(q.beta); } else { q.lr = q.lb = FT(0); }
+    q.lr = q.lb = FT(0);
+    if (sizeof(FT) == 8) {
+        q.c = (FT)__dsqrt_rn(__dmul_rn(__dmul_rn(g, p), ri));
+        if (full) {
+            q.beta = (FT)(r / p);
+            double lr = log(r);
+            q.lr = (FT)lr;
+            q.lb = (FT)(lr - log(p));
+        } else {
+            q.beta = FT(0);
+        }
+    } else {
+        float pf = (float)p, rf = (float)r;
+        q.c = (FT)__fsqrt_rn(__fdiv_rn(__fmul_rn((float)g, pf), rf));
+        q.beta = full ? (FT)__fdiv_rn(rf, pf) : FT(0);
+    }
     return q;
+}
+
+// Local Lax-Friedrichs flux along axis d from conserved states and their
+// primitives (Davis wave speed, R3); returns lambda.
+template <typename FT>
+__device__ __forceinline__ FT llf_prim(const double uL[4], const Prim<FT> &a, const double uR[4], const Prim<FT> &b,
+                                       int d, FT f[4]) {
+    FT vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
+    FT la = fabs(vna) + a.c, lb = fabs(vnb) + b.c;
+    FT lam = la > lb ? la : lb;
+    FT fa[4], fb[4];
+    phys_flux<FT>((FT)uL[1], (FT)uL[2], (FT)uL[3], a.p, vna, d, fa);
+    phys_flux<FT>((FT)uR[1], (FT)uR[2], (FT)uR[3], b.p, vnb, d, fb);
+    for (int v = 0; v < 4; ++v) f[v] = FT(0.5) * (fa[v] + fb[v]) - FT(0.5) * lam * ((FT)uR[v] - (FT)uL[v]);
+    return lam;
 }
 
 // Local Lax-Friedrichs flux along axis d with the Davis wave speed (R3);
@@ -199,13 +224,45 @@ __device__ __forceinline__ FT llf(const double uL[4], const double uR[4], double
     return lam;
 }
 
+// g(0) = (gamma-1)(rho E - |m|^2/2) - pmin rho of a state (one per node).
+__device__ __forceinline__ double g_zero(double g, const double u0[4], double pmin) {
+    return (g - 1.0) * (u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2])) - pmin * u0[0];
+}
+
+// Certifies in FP32 that theta = hi is admissible (rho > 0 and g(hi) >= 0 in
+// exact arithmetic): every product and sum below is bounded by 15 unit
+// roundings of the sum S of the absolute terms, so g_f32 > 2e-6 S implies
+// g(hi) > 0; the FP64 evaluation of the same decision then agrees. Returns
+// false when it cannot decide (near the bound, or magnitudes outside FP32).
+__device__ __forceinline__ bool admissible_f32(double g, const double u0[4], const double a[4], double pmin,
+                                               double c0, double hi) {
+    if (!(c0 > 0.0) || !(u0[0] > 0.0) || !(hi > 0.0)) return false;
+    float r0 = (float)u0[0], m1 = (float)u0[1], m2 = (float)u0[2], E0 = (float)u0[3];
+    float ar = (float)a[0], am1 = (float)a[1], am2 = (float)a[2], aE = (float)a[3];
+    float gm = (float)(g - 1.0), pm = (float)pmin, h = (float)hi, c0f = (float)c0;
+    float t1 = r0 * aE, t2 = ar * E0, t3 = m1 * am1, t4 = m2 * am2, t5 = pm * ar;
+    float c1 = gm * (t1 + t2 - t3 - t4) - t5;
+    float s1 = gm * (fabsf(t1) + fabsf(t2) + fabsf(t3) + fabsf(t4)) + fabsf(t5);
+    float q1 = ar * aE, q2 = am1 * am1 + am2 * am2;
+    float c2 = gm * (q1 - 0.5f * q2);
+    float s2 = gm * (fabsf(q1) + 0.5f * q2);
+    float S = fabsf(c0f) + h * (s1 + h * s2);
+    if (!(S > 1e-30f) || !(S < 1e30f)) return false;
+    float gh = c0f + h * (c1 + h * c2);
+    if (!(gh > 2e-6f * S)) return false;
+    float rh = r0 + h * ar;
+    return rh > 2e-6f * (r0 + h * fabsf(ar));
+}
+
 // Reading R8: largest theta in [0, hi] such that u0 + theta a has rho > 0 and
 // p >= pmin; the admissible set is convex so the feasible thetas form an
-// interval [0, theta*]. g(theta) = (gamma-1)(rho E - |m|^2/2) - pmin rho.
-__device__ __forceinline__ double theta_max(double g, const double u0[4], const double a[4], double pmin, double hi) {
+// interval [0, theta*]. g(theta) = (gamma-1)(rho E - |m|^2/2) - pmin rho, with
+// c0 = g(0) precomputed by g_zero.
+__device__ __forceinline__ double theta_max(double g, const double u0[4], const double a[4], double pmin,
+                                            double c0, double hi) {
     if (!(hi > 0.0)) return 0.0;
-    double c0 = (g - 1.0) * (u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2])) - pmin * u0[0];
     if (!(c0 > 0.0) || !(u0[0] > 0.0)) return 0.0;
+    if (admissible_f32(g, u0, a, pmin, c0, hi)) return hi;
     double c1 = (g - 1.0) * (u0[0] * a[3] + a[0] * u0[3] - (u0[1] * a[1] + u0[2] * a[2])) - pmin * a[0];
     double c2 = (g - 1.0) * (a[0] * a[3] - 0.5 * (a[1] * a[1] + a[2] * a[2]));
     double rho_hi = u0[0] + hi * a[0];

@@ -55,10 +55,12 @@ struct ElemSm {
     double outs[4][NP][4];   // outside state (conforming neighbour or ghost)
     double fbar[4][NP];      // bar-state density across the face
     double f2d[4][NP];       // 2 d_ij across the face
-    double Fdg[NIF][4];      // mass-weighted high-order subcell flux w_r * fhat
+    double Fdg[NIF][4];      // mass-weighted high-order subcell flux w_r * fhat; after P4 the
+                             // antidiffusive flux A = Fdg - Ffv
     double Ffv[NIF][4];      // mass-weighted low-order subcell flux
     double ibar[NIF], i2d[NIF], ell[NIF];
     double rmin[NN], rmax[NN], pmin[NN], tol[NN], Rp[NN], Rm[NN];
+    double dtm[NN], c0[NN];  // dt / m_i and g(0) of the pressure solve at u_FV
     FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
     FT pair[2][NP][NPAIR][4];
 };
@@ -160,10 +162,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             size_t gi = (size_t)e * NN + n;
             double r = A.u[gi], m1 = A.u[KN + gi], m2 = A.u[2 * KN + gi], E = A.u[3 * KN + gi];
             S.u[0][n] = r; S.u[1][n] = m1; S.u[2][n] = m2; S.u[3][n] = E;
-            double p = pressure_d(g, r, m1, m2, E);
-            if (!(r > 0.0) || !(p > 0.0) || !isfinite(E) || !isfinite(m1) || !isfinite(m2))
-                atomicOr(A.status, ST_BAD_INPUT);
             Prim<FT> q = make_prim<FT>(g, r, m1, m2, E, true);
+            if (!(r > 0.0) || !(q.p > FT(0)) || !isfinite(E) || !isfinite(m1) || !isfinite(m2))
+                atomicOr(A.status, ST_BAD_INPUT);
             S.pr[0][n] = q.rho; S.pr[1][n] = q.v1; S.pr[2][n] = q.v2; S.pr[3][n] = q.p; S.pr[4][n] = q.c;
             S.pr[5][n] = q.E; S.pr[6][n] = q.lr; S.pr[7][n] = q.lb; S.pr[8][n] = q.beta;
         }
@@ -217,14 +218,17 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             int d = s >> 1, n = face_node<NP>(s, t);
             double in[4] = {S.u[0][n], S.u[1][n], S.u[2][n], S.u[3][n]};
             double out[4] = {S.outs[s][t][0], S.outs[s][t][1], S.outs[s][t][2], S.outs[s][t][3]};
+            Prim<FT> pi = load_prim<NP, FT>(S, n);
+            Prim<FT> po = make_prim<FT>(g, out[0], out[1], out[2], out[3], false);
             FT f[4];
-            FT lam = (s == 0 || s == 2) ? llf<FT>(out, in, g, d, f) : llf<FT>(in, out, g, d, f);
+            FT lam = (s == 0 || s == 2) ? llf_prim<FT>(out, po, in, pi, d, f) : llf_prim<FT>(in, pi, out, po, d, f);
             Geo geo = mesh.geom[e];
             double half = d == 0 ? 0.5 * geo.w : 0.5 * geo.z;
             for (int v = 0; v < 4; ++v) S.face[s][t][v] = half * (double)f[v];
             double sg = (s == 1 || s == 3) ? 1.0 : -1.0;
             double ld = (double)lam;
-            S.fbar[s][t] = 0.5 * (in[0] + out[0]) - sg * (out[1 + d] - in[1 + d]) / (2.0 * ld);
+            double i2l = (double)(FT(0.5) / lam);
+            S.fbar[s][t] = 0.5 * (in[0] + out[0]) - sg * (out[1 + d] - in[1 + d]) * i2l;
             S.f2d[s][t] = 2.0 * (s_w[t] * half / 2.0) * ld;
         }
         if (!dgmode_rhs && limited) {
@@ -247,8 +251,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 for (int v = 0; v < 4; ++v)
                     S.Ffv[id][v] = (double)(ccf * (fa[v] + fb[v]) - ccf * lam * ((FT)S.u[v][nb] - (FT)S.u[v][na]));
                 double ld = (double)lam;
+                double i2l = (double)(FT(0.5) / lam);
                 S.i2d[id] = 2.0 * cc * ld;
-                S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) / (2.0 * ld);
+                S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * i2l;
             }
         }
         __syncthreads();
@@ -314,16 +319,20 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     }
                 }
                 double q[4];
-                for (int v = 0; v < 4; ++v) { S.lfv[v][n] = L[v]; q[v] = S.u[v][n] + dt / mi * L[v]; S.ufv[v][n] = q[v]; }
+                double dtm = dt / mi;
+                S.dtm[n] = dtm;
+                for (int v = 0; v < 4; ++v) { S.lfv[v][n] = L[v]; q[v] = S.u[v][n] + dtm * L[v]; S.ufv[v][n] = q[v]; }
                 double rmin, rmax;
                 if (A.limiting == 2) { rmin = fmax(lo, A.beta * q[0]); rmax = hi; }
                 else { rmin = A.beta * q[0]; rmax = INFINITY; }
                 if (q[0] < rmin) rmin = q[0];
                 if (q[0] > rmax) rmax = q[0];
                 S.rmin[n] = rmin; S.rmax[n] = rmax;
-                S.pmin[n] = A.beta * pressure_d(g, q[0], q[1], q[2], q[3]);
+                double pm = A.beta * pressure_d(g, q[0], q[1], q[2], q[3]);
+                S.pmin[n] = pm;
+                S.c0[n] = g_zero(g, q, pm);
                 S.tol[n] = kTol * fabs(q[0]);
-                if (A.collect && dt * ds / mi > 1.0) atomicAdd(&A.stats->n_dtx, 1ull);
+                if (A.collect && dtm * ds > 1.0) atomicAdd(&A.stats->n_dtx, 1ull);
             }
         }
         __syncthreads();
@@ -381,15 +390,14 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
         }
 
         // ---------------- P3: Zalesak factors for density (R7) -------------
+        // R+ = min(1, Q+/P+) with Q+ = (m/dt)(rho_max - rho_FV), written with
+        // dt/m so that only an active bound costs a division
         for (int k = tid; k < EPB * NN; k += NT) {
             int le = k / NN, n = k - le * NN, e = e0 + le;
             if (e >= mesh.K) continue;
             SM &S = sm[le];
             int i = n % NP, j = n / NP;
-            Geo geo = mesh.geom[e];
-            double dt = stage_dt(A, mesh.sim[e]);
-            double J = geo.z * geo.w / 4.0;
-            double mi = J * s_w[i] * s_w[j];
+            double dtm = S.dtm[n];
             double Pp = 0.0, Pm = 0.0;
             for (int d = 0; d < 2; ++d) {
                 int pos = d == 0 ? i : j, row = d == 0 ? j : i;
@@ -399,8 +407,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     int id = ifid<NP>(d, row, a);
                     double Ar = S.Fdg[id][0] - S.Ffv[id][0];
                     int nl = nodeid<NP>(d, row, a), nr = nodeid<NP>(d, row, a + 1);
-                    double ml = J * s_w[nl % NP] * s_w[nl / NP], mr = J * s_w[nr % NP] * s_w[nr / NP];
-                    bool ex = (dt / ml * fabs(Ar) <= S.tol[nl]) && (dt / mr * fabs(Ar) <= S.tol[nr]);
+                    double aa = fabs(Ar);
+                    bool ex = (S.dtm[nl] * aa <= S.tol[nl]) && (S.dtm[nr] * aa <= S.tol[nr]);
                     if (ex) continue;
                     double G = side == 0 ? Ar : -Ar;
                     Pp += G > 0 ? G : 0.0;
@@ -408,9 +416,10 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 }
             }
             double rfv = S.ufv[0][n];
-            double Qp = mi / dt * (S.rmax[n] - rfv), Qm = mi / dt * (S.rmin[n] - rfv);
-            double Rp = (Pp > 0.0) ? (Qp / Pp < 1.0 ? Qp / Pp : 1.0) : 1.0;
-            double Rm = (Pm < 0.0) ? (Qm / Pm < 1.0 ? Qm / Pm : 1.0) : 1.0;
+            double qp = S.rmax[n] - rfv, qm = S.rmin[n] - rfv;   // Q / (m/dt)
+            double pp = dtm * Pp, pmm = dtm * Pm;
+            double Rp = (pp > qp) ? qp / pp : 1.0;
+            double Rm = (pmm < qm) ? qm / pmm : 1.0;
             S.Rp[n] = Rp < 0.0 ? 0.0 : Rp;
             S.Rm[n] = Rm < 0.0 ? 0.0 : Rm;
         }
@@ -422,23 +431,22 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             if (e >= mesh.K) continue;
             int d = id / (NP * N), r = (id / N) % NP, a = id % N;
             SM &S = sm[le];
-            Geo geo = mesh.geom[e];
-            double dt = stage_dt(A, mesh.sim[e]);
-            double J = geo.z * geo.w / 4.0;
             int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
-            double ml = J * s_w[nl % NP] * s_w[nl / NP], mr = J * s_w[nr % NP] * s_w[nr / NP];
             double Av[4];
             for (int v = 0; v < 4; ++v) Av[v] = S.Fdg[id][v] - S.Ffv[id][v];
             double Ar = Av[0];
-            bool ex = (dt / ml * fabs(Ar) <= S.tol[nl]) && (dt / mr * fabs(Ar) <= S.tol[nr]);
+            double aa = fabs(Ar);
+            bool ex = (S.dtm[nl] * aa <= S.tol[nl]) && (S.dtm[nr] * aa <= S.tol[nr]);
             double lr = ex ? 1.0
                            : (-Ar > 0.0) ? fmin(S.Rp[nl], S.Rm[nr]) : fmin(S.Rm[nl], S.Rp[nr]);
             double u0[4], av[4];
-            for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nl]; av[v] = -4.0 * dt / ml * Av[v]; }
-            double thl = theta_max(g, u0, av, S.pmin[nl], lr);
-            for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nr]; av[v] = 4.0 * dt / mr * Av[v]; }
-            double thr = theta_max(g, u0, av, S.pmin[nr], lr);
-            S.ell[id] = thl < thr ? thl : thr;
+            double sl_ = -4.0 * S.dtm[nl], sr_ = 4.0 * S.dtm[nr];
+            for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nl]; av[v] = sl_ * Av[v]; }
+            double thl = theta_max(g, u0, av, S.pmin[nl], S.c0[nl], lr);
+            for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nr]; av[v] = sr_ * Av[v]; }
+            double thr = theta_max(g, u0, av, S.pmin[nr], S.c0[nr], thl);
+            S.ell[id] = thr;   // min(theta_l, theta_r): theta_r is searched in [0, theta_l]
+            for (int v = 0; v < 4; ++v) S.Fdg[id][v] = Av[v];
         }
         __syncthreads();
 
@@ -453,29 +461,30 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 int i = n % NP, j = n / NP;
                 Geo geo = mesh.geom[e];
                 int sim = mesh.sim[e];
-                double dt = stage_dt(A, sim);
                 double mi = geo.z * geo.w / 4.0 * s_w[i] * s_w[j];
+                double dtm = S.dtm[n];
                 double sacc[4] = {0, 0, 0, 0}, lmin = 1.0;
                 for (int d = 0; d < 2; ++d) {
                     int pos = d == 0 ? i : j, row = d == 0 ? j : i;
                     if (pos > 0) {
                         int id = ifid<NP>(d, row, pos - 1);
                         double l = S.ell[id];
-                        for (int v = 0; v < 4; ++v) sacc[v] += l * (S.Fdg[id][v] - S.Ffv[id][v]);
+                        for (int v = 0; v < 4; ++v) sacc[v] += l * S.Fdg[id][v];
                         lmin = fmin(lmin, l);
                     }
                     if (pos < N) {
                         int id = ifid<NP>(d, row, pos);
                         double l = S.ell[id];
-                        for (int v = 0; v < 4; ++v) sacc[v] -= l * (S.Fdg[id][v] - S.Ffv[id][v]);
+                        for (int v = 0; v < 4; ++v) sacc[v] -= l * S.Fdg[id][v];
                         lmin = fmin(lmin, l);
                     }
                 }
                 double uvol[4], resv[4];
                 for (int v = 0; v < 4; ++v) {
-                    uvol[v] = S.ufv[v][n] + dt / mi * sacc[v];
+                    uvol[v] = S.ufv[v][n] + dtm * sacc[v];
                     resv[v] = S.lfv[v][n] + sacc[v];
                 }
+                (void)sim;
                 size_t gi = (size_t)e * NN + n;
                 // mortar hand-off
                 uchar4 ftv = mesh.ftype[e];
@@ -514,13 +523,15 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     st_m += mi;
                     st_act += lmin < 1.0;
                     if (nmort == 0) {
-                        double p = pressure_d(g, uvol[0], uvol[1], uvol[2], uvol[3]);
+                        // rho p = (gamma-1)(rho E - |m|^2/2): checks without division
+                        double rp = (g - 1.0) * (uvol[0] * uvol[3] - 0.5 * (uvol[1] * uvol[1] + uvol[2] * uvol[2]));
+                        double pmn = S.pmin[n];
                         if (uvol[0] < S.rmin[n] - kViolTol * fabs(S.rmin[n]) ||
                             uvol[0] > S.rmax[n] + kViolTol * fabs(S.rmax[n])) st_vr++;
-                        if (p < S.pmin[n] - kViolTol * fabs(S.pmin[n])) st_vp++;
-                        if (!(uvol[0] > 0.0) || !(p > 0.0)) st_np++;
+                        if (rp < (pmn - kViolTol * fabs(pmn)) * uvol[0]) st_vp++;
+                        if (!(uvol[0] > 0.0) || !(rp > 0.0)) st_np++;
                         st_rmin = fmin(st_rmin, uvol[0]);
-                        st_pmin = fmin(st_pmin, p);
+                        if (lmin < 1.0) st_pmin = fmin(st_pmin, rp / uvol[0]);
                     }
                 }
             }

@@ -25,6 +25,7 @@ __global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
 k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, const Ops *ops) {
     constexpr int NN = NP * NP, Q = 3 * NP;
     __shared__ double s_u[MORTARS_PER_BLOCK][Q][4];
+    __shared__ double s_pr[MORTARS_PER_BLOCK][Q][3];     // normal velocity, p, c
     __shared__ double s_ui[MORTARS_PER_BLOCK][2 * NP][4];
     __shared__ double s_f[MORTARS_PER_BLOCK][2 * NP][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -39,18 +40,24 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
     const double halfL = dir == 0 ? 0.5 * geoL.w : 0.5 * geoL.z, halfS = 0.5 * halfL;
     const double sg = low ? 1.0 : -1.0;   // large side's outward normal along +dir
     const double g = gamma;
-    int gnode = -1;
     if (lane < Q) {
+        int gnode;
         if (lane < NP) gnode = L * NN + face_node<NP>(sL, lane);
         else {
             int p = (lane - NP) / NP, l = (lane - NP) % NP;
             gnode = (p == 0 ? sm2.x : sm2.y) * NN + face_node<NP>(sS, l);
         }
-        for (int v = 0; v < 4; ++v) s_u[warp][lane][v] = u[v * KN + gnode];
+        double q[4];
+        for (int v = 0; v < 4; ++v) { q[v] = u[v * KN + gnode]; s_u[warp][lane][v] = q[v]; }
+        Prim<double> pr = make_prim<double>(g, q[0], q[1], q[2], q[3], false);
+        s_pr[warp][lane][0] = dir == 0 ? pr.v1 : pr.v2;
+        s_pr[warp][lane][1] = pr.p;
+        s_pr[warp][lane][2] = pr.c;
     }
     __syncwarp();
     // interpolation of the large trace to the small-face nodes, admissibility
     bool badl = false;
+    Prim<double> pint;
     if (lane < 2 * NP) {
         double acc[4] = {0, 0, 0, 0};
         for (int k = 0; k < NP; ++k) {
@@ -58,19 +65,24 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
             for (int v = 0; v < 4; ++v) acc[v] += c * s_u[warp][k][v];
         }
         for (int v = 0; v < 4; ++v) s_ui[warp][lane][v] = acc[v];
-        badl = !(acc[0] > 0.0) || !(pressure_d(g, acc[0], acc[1], acc[2], acc[3]) > 0.0);
+        // rho p > 0 without a division, then the primitives
+        badl = !(acc[0] > 0.0) || !(acc[0] * acc[3] - 0.5 * (acc[1] * acc[1] + acc[2] * acc[2]) > 0.0);
+        if (!badl) pint = make_prim<double>(g, acc[0], acc[1], acc[2], acc[3], false);
     }
     const bool bad = __any_sync(0xffffffffu, badl);
-    __syncwarp();
     // LLF on the small faces (left/bottom state first)
     if (!bad && lane < 2 * NP) {
         double f[4];
         const double *ui = s_ui[warp][lane], *us = s_u[warp][NP + lane];
-        if (low) llf<double>(ui, us, g, dir, f); else llf<double>(us, ui, g, dir, f);
+        Prim<double> ps;
+        ps.v1 = dir == 0 ? s_pr[warp][NP + lane][0] : 0.0;
+        ps.v2 = dir == 1 ? s_pr[warp][NP + lane][0] : 0.0;
+        ps.p = s_pr[warp][NP + lane][1];
+        ps.c = s_pr[warp][NP + lane][2];
+        if (low) llf_prim<double>(ui, pint, us, ps, dir, f); else llf_prim<double>(us, ps, ui, pint, dir, f);
         for (int v = 0; v < 4; ++v) s_f[warp][lane][v] = f[v];
     }
     __syncwarp();
-    // node quantities
     if (lane < Q) {
         const int q = lane;
         double chi[4] = {0, 0, 0, 0}, clo[4] = {0, 0, 0, 0};
@@ -87,7 +99,8 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
                 for (int v = 0; v < 4; ++v) chi[v] = sg * ops->w[l] * (halfS * s_f[warp][q - NP][v]);
             }
         }
-        // sparse low-order flux, bar states and 2 d sums over the nonzero local weights
+        // sparse low-order flux (Eq. interfaceflux_local), bar states and
+        // 2 d sums over the nonzero local weights
         double lo = INFINITY, hi = -INFINITY, ds = 0.0;
         const int kb = q < NP ? q : 0, ke = q < NP ? q + 1 : NP;
         const int rb = q < NP ? 0 : q - NP, re = q < NP ? 2 * NP : q - NP + 1;
@@ -96,18 +109,17 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
                 double wt = ops->wt[k][r] * halfL;
                 if (wt <= 0.0) continue;
                 const double *a = s_u[warp][k], *b = s_u[warp][NP + r];
-                double va = a[1 + dir] / a[0], vb = b[1 + dir] / b[0];
-                double pa = pressure_d(g, a[0], a[1], a[2], a[3]), pb = pressure_d(g, b[0], b[1], b[2], b[3]);
-                double la = fabs(va) + sqrt(g * pa / a[0]), lb = fabs(vb) + sqrt(g * pb / b[0]);
+                const double *pa = s_pr[warp][k], *pb = s_pr[warp][NP + r];
+                double la = fabs(pa[0]) + pa[2], lb = fabs(pb[0]) + pb[2];
                 double lam = la > lb ? la : lb;
                 double fa[4], fb[4];
-                phys_flux<double>(a[1], a[2], a[3], pa, va, dir, fa);
-                phys_flux<double>(b[1], b[2], b[3], pb, vb, dir, fb);
+                phys_flux<double>(a[1], a[2], a[3], pa[1], pa[0], dir, fa);
+                phys_flux<double>(b[1], b[2], b[3], pb[1], pb[0], dir, fb);
                 for (int v = 0; v < 4; ++v) {
                     double term = 0.5 * wt * ((sg * fa[v] + sg * fb[v]) - lam * (b[v] - a[v]));
                     clo[v] += q < NP ? -term : term;
                 }
-                double rbv = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) / (2.0 * lam);
+                double rbv = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) * (0.5 / lam);
                 lo = fmin(lo, rbv);
                 hi = fmax(hi, rbv);
                 ds += 2.0 * (wt / 2.0) * lam;
@@ -146,8 +158,8 @@ k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
         if (av[0] > 0.0) { double t = (sl.rmax[s] + tl - u0[0]) / av[0]; if (t < lr) lr = t; }
         else if (av[0] < 0.0) { double t = (sl.rmin[s] - tl - u0[0]) / av[0]; if (t < lr) lr = t; }
         if (lr < 0.0) lr = 0.0;
-        double pm = sl.pmin[s];
-        th = theta_max(A.gamma, u0, av, pm - kTol * fabs(pm), lr);
+        double pm = sl.pmin[s] - kTol * fabs(sl.pmin[s]);
+        th = theta_max(A.gamma, u0, av, pm, g_zero(A.gamma, u0, pm), lr);
     }
     for (int o = 16; o > 0; o >>= 1) th = fmin(th, __shfl_down_sync(0xffffffffu, th, o));
     if (lane == 0) {
@@ -215,69 +227,90 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
 
 // Time step: per node m_i / sum_j 2 d_ij (rule 0) or min over directions of
 // (w_i h / 2) / (|v| + c) (rule 1); minimum per simulation as ordered bits.
-template <int NP>
-__global__ void k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int rule,
-                     const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status) {
-    constexpr int NN = NP * NP, N = NP - 1;
+// One block holds EPB elements, one thread per node; each node's wave speeds
+// |v_x| + c and |v_y| + c are formed once and shared through shared memory.
+template <int NP, int EPB>
+__global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads)
+k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int rule, const Ops *ops,
+     const double *t_sim, unsigned long long *dtmin, unsigned *status) {
+    constexpr int NN = NP * NP, N = NP - 1, NT = ElemLaunch<NP, EPB>::threads;
+    __shared__ double s_l[EPB][2][NN];
     const size_t KN = (size_t)mesh.K * NN;
     const double g = gamma;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < KN; k += (size_t)gridDim.x * blockDim.x) {
-        const int e = (int)(k / NN), n = (int)(k % NN), i = n % NP, j = n / NP;
-        const Geo geo = mesh.geom[e];
-        const int sim = mesh.sim[e];
-        double ui[4] = {u[k], u[KN + k], u[2 * KN + k], u[3 * KN + k]};
-        double pi_ = pressure_d(g, ui[0], ui[1], ui[2], ui[3]);
-        if (!(ui[0] > 0.0) || !(pi_ > 0.0)) { atomicOr(status, ST_BAD_INPUT); continue; }
-        double ci = sqrt(g * pi_ / ui[0]);
-        double val;
-        if (rule == 1) {
-            double tx = ops->w[i] * geo.z / 2.0 / (fabs(ui[1] / ui[0]) + ci);
-            double ty = ops->w[j] * geo.w / 2.0 / (fabs(ui[2] / ui[0]) + ci);
-            val = fmin(tx, ty);
-        } else {
-            double ds = 0.0;
-            const uchar4 ftv = mesh.ftype[e];
-            const int4 nb4 = mesh.fnbr[e];
-            for (int d = 0; d < 2; ++d) {
-                int pos = d == 0 ? i : j, row = d == 0 ? j : i;
-                double cc = ops->w[row] * (d == 0 ? geo.w : geo.z) / 4.0;
-                double vi = ui[1 + d] / ui[0], li = fabs(vi) + ci;
-                for (int side = 0; side < 2; ++side) {
-                    bool interior = side == 0 ? pos > 0 : pos < N;
-                    if (interior) {
-                        int on = d == 0 ? n + (side == 0 ? -1 : 1) : n + (side == 0 ? -NP : NP);
-                        size_t ko = (size_t)e * NN + on;
-                        double uo[4] = {u[ko], u[KN + ko], u[2 * KN + ko], u[3 * KN + ko]};
-                        double po = pressure_d(g, uo[0], uo[1], uo[2], uo[3]);
-                        double lo = fabs(uo[1 + d] / uo[0]) + sqrt(g * po / uo[0]);
-                        ds += 2.0 * cc * (li > lo ? li : lo);
-                    } else {
-                        int s = 2 * d + side;
-                        int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
-                        int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
-                        if (ft == FT_CONF || ft == FT_BND) {
-                            double uo[4];
-                            if (ft == FT_CONF) {
-                                size_t ko = (size_t)nb * NN + face_node<NP>(s ^ 1, row);
-                                for (int v = 0; v < 4; ++v) uo[v] = u[v * KN + ko];
-                            } else {
-                                // ghost state at the step's start time
-                                double xn = geo.x + 0.5 * geo.z * (1.0 + ops->xi[i]);
-                                ghost_state(mesh.siminfo[sim], s, ui, xn, t_sim[sim], uo);
-                            }
-                            double po = pressure_d(g, uo[0], uo[1], uo[2], uo[3]);
-                            double lo = fabs(uo[1 + d] / uo[0]) + sqrt(g * po / uo[0]);
+    for (int e0 = blockIdx.x * EPB; e0 < mesh.K; e0 += gridDim.x * EPB) {
+        for (int k = threadIdx.x; k < EPB * NN; k += NT) {
+            int le = k / NN, n = k - le * NN, e = e0 + le;
+            if (e >= mesh.K) continue;
+            size_t gi = (size_t)e * NN + n;
+            Prim<double> q = make_prim<double>(g, u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi], false);
+            if (!(q.rho > 0.0) || !(q.p > 0.0)) atomicOr(status, ST_BAD_INPUT);
+            s_l[le][0][n] = fabs(q.v1) + q.c;
+            s_l[le][1][n] = fabs(q.v2) + q.c;
+        }
+        __syncthreads();
+        double best = INFINITY;
+        int bsim = -1;
+        for (int k = threadIdx.x; k < EPB * NN; k += NT) {
+            int le = k / NN, n = k - le * NN, e = e0 + le;
+            if (e >= mesh.K) continue;
+            int i = n % NP, j = n / NP;
+            const Geo geo = mesh.geom[e];
+            const int sim = mesh.sim[e];
+            double val;
+            if (rule == 1) {
+                val = fmin(ops->w[i] * geo.z / 2.0 / s_l[le][0][n], ops->w[j] * geo.w / 2.0 / s_l[le][1][n]);
+            } else {
+                double ds = 0.0;
+                const uchar4 ftv = mesh.ftype[e];
+                const int4 nb4 = mesh.fnbr[e];
+                for (int d = 0; d < 2; ++d) {
+                    int pos = d == 0 ? i : j, row = d == 0 ? j : i;
+                    double cc = ops->w[row] * (d == 0 ? geo.w : geo.z) / 4.0;
+                    double li = s_l[le][d][n];
+                    for (int side = 0; side < 2; ++side) {
+                        bool interior = side == 0 ? pos > 0 : pos < N;
+                        if (interior) {
+                            int on = d == 0 ? n + (side == 0 ? -1 : 1) : n + (side == 0 ? -NP : NP);
+                            double lo = s_l[le][d][on];
                             ds += 2.0 * cc * (li > lo ? li : lo);
                         } else {
-                            ds += sl.dsum[slot_of<NP>(ft, nb, row)];
+                            int s = 2 * d + side;
+                            int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
+                            int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
+                            if (ft == FT_CONF || ft == FT_BND) {
+                                double uo[4];
+                                if (ft == FT_CONF) {
+                                    size_t ko = (size_t)nb * NN + face_node<NP>(s ^ 1, row);
+                                    for (int v = 0; v < 4; ++v) uo[v] = u[v * KN + ko];
+                                } else {
+                                    size_t gi = (size_t)e * NN + n;
+                                    double ui[4] = {u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi]};
+                                    double xn = geo.x + 0.5 * geo.z * (1.0 + ops->xi[i]);
+                                    ghost_state(mesh.siminfo[sim], s, ui, xn, t_sim[sim], uo);
+                                }
+                                Prim<double> po = make_prim<double>(g, uo[0], uo[1], uo[2], uo[3], false);
+                                double lo = fabs(d == 0 ? po.v1 : po.v2) + po.c;
+                                ds += 2.0 * cc * (li > lo ? li : lo);
+                            } else {
+                                ds += sl.dsum[slot_of<NP>(ft, nb, row)];
+                            }
                         }
                     }
                 }
+                double mi = geo.z * geo.w / 4.0 * ops->w[i] * ops->w[j];
+                val = mi / ds;
             }
-            double mi = geo.z * geo.w / 4.0 * ops->w[i] * ops->w[j];
-            val = mi / ds;
+            // one atomic per thread and simulation run (elements of a block
+            // almost always share the simulation)
+            if (sim != bsim) {
+                if (bsim >= 0 && best < INFINITY) atomicMin(&dtmin[bsim], dbits(best));
+                bsim = sim;
+                best = INFINITY;
+            }
+            if (val > 0.0 && val < best) best = val;
         }
-        if (val > 0.0) atomicMin(&dtmin[sim], dbits(val));
+        if (bsim >= 0 && best < INFINITY) atomicMin(&dtmin[bsim], dbits(best));
+        __syncthreads();
     }
 }
 

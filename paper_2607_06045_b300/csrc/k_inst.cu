@@ -78,7 +78,10 @@ void mortar_apply(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s
 
 void dt(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma, int rule,
         const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status) {
-    k_dt<NP><<<grid, 256, 0, st>>>(m, s, u, gamma, rule, ops, t_sim, dtmin, status);
+    constexpr int EPB = NP * NP >= 64 ? 2 : (NP * NP >= 25 ? 4 : 8);
+    int blocks = (m.K + EPB - 1) / EPB;
+    k_dt<NP, EPB><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim, dtmin, status);
+    (void)grid;
 }
 
 void integrals(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part) {

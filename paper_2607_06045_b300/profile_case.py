@@ -1,0 +1,44 @@
+"""Small driver for profiler captures: builds one workload and runs a few
+SSP-RK3 steps through the C ABI (no timing, no oracle).
+
+  python -m paper_2607_06045_b300.profile_case --workload dmr --steps 3
+"""
+import argparse
+import sys
+
+import numpy as np
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="dmr", choices=["dmr", "cfg1", "cfg5", "batched"])
+    ap.add_argument("--precision", type=int, default=0)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--N", type=int, default=3)
+    ap.add_argument("--epb", type=int, default=0, help="elements per block (0: autotune)")
+    a = ap.parse_args(argv)
+    import torch
+    from paper_2607_06045_b300 import build, idp
+    from paper_2607_06045_b300 import workloads as W
+    build.build()
+    if a.workload == "dmr":
+        meshes = W.cfg2_mesh(); u = W.cfg2_state(meshes, a.N)
+    elif a.workload == "cfg1":
+        meshes = W.cfg1_mesh(); u = W.cfg1_state(meshes, a.N)
+    elif a.workload == "cfg5":
+        meshes, c = W.cfg5_mesh(); u = W.cfg5_state(meshes, a.N, c)
+    else:
+        meshes = W.cfg4_meshes(256, seed=0)
+        rng = np.random.default_rng(1)
+        u = W.concat_states([W.cfg4_state(m, a.N, rng) for m in meshes])
+    ctx = idp.Context(meshes, a.N, precision=a.precision, limiting=2, cfl=0.5, elems_per_block=a.epb)
+    ud = torch.from_numpy(u).cuda()
+    t = np.zeros(ctx.n_sims)
+    stream = torch.cuda.Stream()
+    ctx.idp_dgsem_step(ud, a.steps, t, stream=stream.cuda_stream)
+    torch.cuda.synchronize()
+    print(f"ok: {a.workload} K={ctx.K} M={ctx.M} steps={a.steps} t={t[:3]}")
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
