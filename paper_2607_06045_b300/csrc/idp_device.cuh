@@ -32,6 +32,7 @@ struct __align__(32) Geo {
 struct Ops {
     double xi[NPMAX];                // LGL nodes
     double w[NPMAX];                 // LGL weights
+    double iw[NPMAX];                // 1 / w
     double S[NPMAX][NPMAX];          // Sbar = 2 Qbar - Bbar
     double wt[NPMAX][2 * NPMAX];     // local mortar weights (reference units)
     double I[2 * NPMAX][NPMAX];      // interpolation large -> small-face nodes
@@ -193,6 +194,31 @@ __device__ __forceinline__ Prim<FT> make_prim(double g, double r, double m1, dou
     return q;
 }
 
+// FP32 primitives of the FP32 form. When E - |m|^2/2rho keeps at least half
+// of E (no cancellation) the pressure is formed in FP32 (relative error below
+// 1e-6, positive for sure); otherwise in FP64 as above.
+__device__ __forceinline__ Prim<float> make_prim_f32(double g, double r, double m1, double m2, double E, bool full,
+                                                     float &m1o, float &m2o) {
+    float rf = (float)r, m1f = (float)m1, m2f = (float)m2, Ef = (float)E;
+    float rif = __frcp_rn(rf);
+    float v1 = __fmul_rn(m1f, rif), v2 = __fmul_rn(m2f, rif);
+    float kef = __fmul_rn(0.5f, __fadd_rn(__fmul_rn(m1f, v1), __fmul_rn(m2f, v2)));
+    float pef = __fadd_rn(Ef, -kef);
+    Prim<float> q;
+    if (rf > 0.0f && Ef > 0.0f && pef >= 0.5f * Ef) {
+        q.rho = rf; q.v1 = v1; q.v2 = v2; q.E = Ef;
+        q.p = __fmul_rn((float)(g - 1.0), pef);
+        q.lr = q.lb = 0.0f;
+        q.c = __fsqrt_rn(__fmul_rn(__fmul_rn((float)g, q.p), rif));
+        q.beta = full ? __fmul_rn(rf, __frcp_rn(q.p)) : 0.0f;
+    } else {
+        q = make_prim<float>(g, r, m1, m2, E, full);
+    }
+    m1o = m1f;
+    m2o = m2f;
+    return q;
+}
+
 // Local Lax-Friedrichs flux along axis d from conserved states and their
 // primitives (Davis wave speed, R3); returns lambda.
 template <typename FT>
@@ -224,22 +250,26 @@ __device__ __forceinline__ FT llf(const double uL[4], const double uR[4], double
     return lam;
 }
 
-// g(0) = (gamma-1)(rho E - |m|^2/2) - pmin rho of a state (one per node).
-__device__ __forceinline__ double g_zero(double g, const double u0[4], double pmin) {
-    return (g - 1.0) * (u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2])) - pmin * u0[0];
+// g(0) = gm (rho E - |m|^2/2) - pm rho of a state. With gm = gamma - 1 and
+// pm = p_min this is rho (p - p_min); the element pass uses the same form
+// scaled by rho_FV (gm = (gamma-1) rho_FV, pm = p_min rho_FV), whose roots are
+// the same and which needs no division.
+__device__ __forceinline__ double g_zero(double gm, const double u0[4], double pm) {
+    return gm * (u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2])) - pm * u0[0];
 }
 
 // Certifies in FP32 that theta = hi is admissible (rho > 0 and g(hi) >= 0 in
-// exact arithmetic): every product and sum below is bounded by 15 unit
-// roundings of the sum S of the absolute terms, so g_f32 > 2e-6 S implies
-// g(hi) > 0; the FP64 evaluation of the same decision then agrees. Returns
-// false when it cannot decide (near the bound, or magnitudes outside FP32).
-__device__ __forceinline__ bool admissible_f32(double g, const double u0[4], const double a[4], double pmin,
-                                               double c0, double hi) {
-    if (!(c0 > 0.0) || !(u0[0] > 0.0) || !(hi > 0.0)) return false;
-    float r0 = (float)u0[0], m1 = (float)u0[1], m2 = (float)u0[2], E0 = (float)u0[3];
-    float ar = (float)a[0], am1 = (float)a[1], am2 = (float)a[2], aE = (float)a[3];
-    float gm = (float)(g - 1.0), pm = (float)pmin, h = (float)hi, c0f = (float)c0;
+// exact arithmetic) from FP32 inputs that carry at most three roundings each:
+// every product and sum below then stays within 17 unit roundings of the sum
+// S of the absolute terms, so g_f32 > 4e-6 S implies g(hi) > 0 with a
+// fourfold margin, and the FP64 evaluation of the same decision agrees.
+// Returns false when it cannot decide (near the bound, or magnitudes outside
+// the FP32 range).
+__device__ __forceinline__ bool admissible_f32(float gm, const float u0[4], const float a[4], float pm, float c0f,
+                                               float h) {
+    if (!(c0f > 0.0f) || !(u0[0] > 0.0f) || !(h > 0.0f)) return false;
+    float r0 = u0[0], m1 = u0[1], m2 = u0[2], E0 = u0[3];
+    float ar = a[0], am1 = a[1], am2 = a[2], aE = a[3];
     float t1 = r0 * aE, t2 = ar * E0, t3 = m1 * am1, t4 = m2 * am2, t5 = pm * ar;
     float c1 = gm * (t1 + t2 - t3 - t4) - t5;
     float s1 = gm * (fabsf(t1) + fabsf(t2) + fabsf(t3) + fabsf(t4)) + fabsf(t5);
@@ -249,22 +279,31 @@ __device__ __forceinline__ bool admissible_f32(double g, const double u0[4], con
     float S = fabsf(c0f) + h * (s1 + h * s2);
     if (!(S > 1e-30f) || !(S < 1e30f)) return false;
     float gh = c0f + h * (c1 + h * c2);
-    if (!(gh > 2e-6f * S)) return false;
+    if (!(gh > 4e-6f * S)) return false;
     float rh = r0 + h * ar;
-    return rh > 2e-6f * (r0 + h * fabsf(ar));
+    return rh > 4e-6f * (r0 + h * fabsf(ar));
+}
+
+__device__ __forceinline__ bool admissible_f32(double gm, const double u0[4], const double a[4], double pm,
+                                               double c0, double hi) {
+    if (!(c0 > 0.0) || !(u0[0] > 0.0) || !(hi > 0.0)) return false;
+    float uf[4] = {(float)u0[0], (float)u0[1], (float)u0[2], (float)u0[3]};
+    float af[4] = {(float)a[0], (float)a[1], (float)a[2], (float)a[3]};
+    return admissible_f32((float)gm, uf, af, (float)pm, (float)c0, (float)hi);
 }
 
 // Reading R8: largest theta in [0, hi] such that u0 + theta a has rho > 0 and
-// p >= pmin; the admissible set is convex so the feasible thetas form an
-// interval [0, theta*]. g(theta) = (gamma-1)(rho E - |m|^2/2) - pmin rho, with
-// c0 = g(0) precomputed by g_zero.
-__device__ __forceinline__ double theta_max(double g, const double u0[4], const double a[4], double pmin,
+// p >= p_min; the admissible set is convex so the feasible thetas form an
+// interval [0, theta*]. g(theta) = gm (rho E - |m|^2/2) - pm rho with
+// (gm, pm) = (gamma-1, p_min) or both scaled by the same positive factor
+// (see g_zero); c0 = g(0). p_min = pm / (gm / (gamma - 1)).
+__device__ __forceinline__ double theta_max(double g, const double u0[4], const double a[4], double gm, double pm,
                                             double c0, double hi) {
     if (!(hi > 0.0)) return 0.0;
     if (!(c0 > 0.0) || !(u0[0] > 0.0)) return 0.0;
-    if (admissible_f32(g, u0, a, pmin, c0, hi)) return hi;
-    double c1 = (g - 1.0) * (u0[0] * a[3] + a[0] * u0[3] - (u0[1] * a[1] + u0[2] * a[2])) - pmin * a[0];
-    double c2 = (g - 1.0) * (a[0] * a[3] - 0.5 * (a[1] * a[1] + a[2] * a[2]));
+    if (admissible_f32(gm, u0, a, pm, c0, hi)) return hi;
+    double c1 = gm * (u0[0] * a[3] + a[0] * u0[3] - (u0[1] * a[1] + u0[2] * a[2])) - pm * a[0];
+    double c2 = gm * (a[0] * a[3] - 0.5 * (a[1] * a[1] + a[2] * a[2]));
     double rho_hi = u0[0] + hi * a[0];
     double g_hi = c0 + hi * (c1 + hi * c2);
     if (rho_hi > 0.0 && g_hi >= 0.0) return hi;
@@ -287,6 +326,7 @@ __device__ __forceinline__ double theta_max(double g, const double u0[4], const 
         if (th >= tr) th = 0.5 * tr;
     }
     if (!(th > 0.0)) return 0.0;
+    const double pmin = pm * (g - 1.0) / gm;
     for (int it = 0; it < 4; ++it) {
         double v0 = u0[0] + th * a[0], v1 = u0[1] + th * a[1], v2 = u0[2] + th * a[2], v3 = u0[3] + th * a[3];
         if (v0 > 0.0 && pressure_d(g, v0, v1, v2, v3) >= pmin * (1.0 - 1e-13)) return th;

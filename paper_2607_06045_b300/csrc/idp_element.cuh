@@ -55,14 +55,27 @@ struct ElemSm {
     double outs[4][NP][4];   // outside state (conforming neighbour or ghost)
     double fbar[4][NP];      // bar-state density across the face
     double f2d[4][NP];       // 2 d_ij across the face
-    double Fdg[NIF][4];      // mass-weighted high-order subcell flux w_r * fhat; after P4 the
-                             // antidiffusive flux A = Fdg - Ffv
-    double Ffv[NIF][4];      // mass-weighted low-order subcell flux
+    FT Fdg[NIF][4];          // mass-weighted high-order subcell flux w_r * fhat (flux type)
+    FT Ffv[NIF][4];          // mass-weighted low-order subcell flux (flux type)
+    double Fv[NIF][4];       // the low-order subcell flux in FP64, for the residual sums
     double ibar[NIF], i2d[NIF], ell[NIF];
-    double rmin[NN], rmax[NN], pmin[NN], tol[NN], Rp[NN], Rm[NN];
-    double dtm[NN], c0[NN];  // dt / m_i and g(0) of the pressure solve at u_FV
+    double rmin[NN], rmax[NN], tol[NN], Rp[NN], Rm[NN];
+    // pressure solve at u_FV in the form scaled by rho_FV: gm = (gamma-1) rho_FV,
+    // pm = p_min rho_FV = beta (gamma-1)(rho E - |m|^2/2), c0 = g(0)
+    double dtm[NN], gms[NN], pms[NN], c0[NN];
+    float ufvf[4][NN];       // FP32 copies for the certified admissibility check
+    float dtmf[NN], gmsf[NN], pmsf[NN], c0f[NN];
+    unsigned char ex[NIF];   // density antidiffusion below the tolerance (R15)
+    float uf[4][NN];         // FP32 state (FP32 form)
+    double invA;             // 1 / (dx dy)
     FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
-    FT pair[2][NP][NPAIR][4];
+    union {
+        FT pair[2][NP][NPAIR][4];   // two-point fluxes (dead after the Sbar contraction)
+        struct {
+            double Ad[NIF][4];       // antidiffusive flux A = Fdg - Ffv in FP64
+            float Af[NIF][4];        // and in FP32
+        } a;
+    } un;
 };
 
 template <int NP>
@@ -140,20 +153,21 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
     using SM = ElemSm<NP, FT>;
     constexpr int NN = NP * NP, N = NP - 1, NPAIR = SM::NPAIR, NIF = SM::NIF;
     constexpr int NT = ElemLaunch<NP, EPB>::threads;
+    constexpr bool F32 = sizeof(FT) == 4;
     extern __shared__ __align__(16) unsigned char smraw[];
     SM *sm = reinterpret_cast<SM *>(smraw);
-    __shared__ double s_w[NP], s_S[NP][NP];
+    __shared__ double s_w[NP], s_iw[NP], s_S[NP][NP];
 
     const int tid = threadIdx.x;
-    if (tid < NP) s_w[tid] = A.ops->w[tid];
+    if (tid < NP) { s_w[tid] = A.ops->w[tid]; s_iw[tid] = A.ops->iw[tid]; }
     if (tid < NN) s_S[tid / NP][tid % NP] = A.ops->S[tid / NP][tid % NP];
     const double g = A.gamma;
     const FT ginv1 = FT(1.0 / (g - 1.0));
     const size_t KN = (size_t)mesh.K * NN;
     const bool limited = A.limiting > 0;
+    const bool dgmode = (A.mode == 0 && A.dt == 0.0) || !limited;
 
     for (int e0 = blockIdx.x * EPB; e0 < mesh.K; e0 += gridDim.x * EPB) {
-        const bool dgmode_rhs = (A.mode == 0 && A.dt == 0.0);
         // ---------------- P0: states, primitives, outside traces -------------
         for (int k = tid; k < EPB * NN; k += NT) {
             int le = k / NN, n = k - le * NN, e = e0 + le;
@@ -162,11 +176,19 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             size_t gi = (size_t)e * NN + n;
             double r = A.u[gi], m1 = A.u[KN + gi], m2 = A.u[2 * KN + gi], E = A.u[3 * KN + gi];
             S.u[0][n] = r; S.u[1][n] = m1; S.u[2][n] = m2; S.u[3][n] = E;
-            Prim<FT> q = make_prim<FT>(g, r, m1, m2, E, true);
+            Prim<FT> q;
+            if constexpr (F32) {
+                float m1f, m2f;
+                q = make_prim_f32(g, r, m1, m2, E, true, m1f, m2f);
+                S.uf[0][n] = q.rho; S.uf[1][n] = m1f; S.uf[2][n] = m2f; S.uf[3][n] = q.E;
+            } else {
+                q = make_prim<FT>(g, r, m1, m2, E, true);
+            }
             if (!(r > 0.0) || !(q.p > FT(0)) || !isfinite(E) || !isfinite(m1) || !isfinite(m2))
                 atomicOr(A.status, ST_BAD_INPUT);
             S.pr[0][n] = q.rho; S.pr[1][n] = q.v1; S.pr[2][n] = q.v2; S.pr[3][n] = q.p; S.pr[4][n] = q.c;
             S.pr[5][n] = q.E; S.pr[6][n] = q.lr; S.pr[7][n] = q.lb; S.pr[8][n] = q.beta;
+            if (n == 0) { Geo geo = mesh.geom[e]; S.invA = 1.0 / (geo.z * geo.w); }
         }
         for (int k = tid; k < EPB * 4 * NP; k += NT) {
             int le = k / (4 * NP), s = (k / NP) % 4, t = k % NP, e = e0 + le;
@@ -206,7 +228,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             Prim<FT> pa = load_prim<NP, FT>(S, nodeid<NP>(d, r, a)), pb = load_prim<NP, FT>(S, nodeid<NP>(d, r, b));
             FT f[4];
             ranocha<FT>(pa, pb, d, ginv1, f);
-            for (int v = 0; v < 4; ++v) S.pair[d][r][pi][v] = f[v];
+            for (int v = 0; v < 4; ++v) S.un.pair[d][r][pi][v] = f[v];
         }
         for (int k = tid; k < EPB * 4 * NP; k += NT) {
             int le = k / (4 * NP), s = (k / NP) % 4, t = k % NP, e = e0 + le;
@@ -219,7 +241,13 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             double in[4] = {S.u[0][n], S.u[1][n], S.u[2][n], S.u[3][n]};
             double out[4] = {S.outs[s][t][0], S.outs[s][t][1], S.outs[s][t][2], S.outs[s][t][3]};
             Prim<FT> pi = load_prim<NP, FT>(S, n);
-            Prim<FT> po = make_prim<FT>(g, out[0], out[1], out[2], out[3], false);
+            Prim<FT> po;
+            if constexpr (F32) {
+                float m1f, m2f;
+                po = make_prim_f32(g, out[0], out[1], out[2], out[3], false, m1f, m2f);
+            } else {
+                po = make_prim<FT>(g, out[0], out[1], out[2], out[3], false);
+            }
             FT f[4];
             FT lam = (s == 0 || s == 2) ? llf_prim<FT>(out, po, in, pi, d, f) : llf_prim<FT>(in, pi, out, po, d, f);
             Geo geo = mesh.geom[e];
@@ -231,7 +259,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             S.fbar[s][t] = 0.5 * (in[0] + out[0]) - sg * (out[1 + d] - in[1 + d]) * i2l;
             S.f2d[s][t] = 2.0 * (s_w[t] * half / 2.0) * ld;
         }
-        if (!dgmode_rhs && limited) {
+        if (!dgmode) {
             for (int k = tid; k < EPB * NIF; k += NT) {
                 int le = k / NIF, id = k - le * NIF, e = e0 + le;
                 if (e >= mesh.K) continue;
@@ -242,14 +270,22 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 FT vna = d == 0 ? pa.v1 : pa.v2, vnb = d == 0 ? pb.v1 : pb.v2;
                 FT la = fabs(vna) + pa.c, lb = fabs(vnb) + pb.c;
                 FT lam = la > lb ? la : lb;
+                FT ua[4], ub[4];
+                for (int v = 0; v < 4; ++v) {
+                    ua[v] = F32 ? (FT)S.uf[v][na] : (FT)S.u[v][na];
+                    ub[v] = F32 ? (FT)S.uf[v][nb] : (FT)S.u[v][nb];
+                }
                 FT fa[4], fb[4];
-                phys_flux<FT>((FT)S.u[1][na], (FT)S.u[2][na], (FT)S.u[3][na], pa.p, vna, d, fa);
-                phys_flux<FT>((FT)S.u[1][nb], (FT)S.u[2][nb], (FT)S.u[3][nb], pb.p, vnb, d, fb);
+                phys_flux<FT>(ua[1], ua[2], ua[3], pa.p, vna, d, fa);
+                phys_flux<FT>(ub[1], ub[2], ub[3], pb.p, vnb, d, fb);
                 Geo geo = mesh.geom[e];
                 double cc = s_w[r] * (d == 0 ? geo.w : geo.z) / 4.0;
                 FT ccf = (FT)cc;
-                for (int v = 0; v < 4; ++v)
-                    S.Ffv[id][v] = (double)(ccf * (fa[v] + fb[v]) - ccf * lam * ((FT)S.u[v][nb] - (FT)S.u[v][na]));
+                for (int v = 0; v < 4; ++v) {
+                    FT fv = ccf * (fa[v] + fb[v]) - ccf * lam * (ub[v] - ua[v]);
+                    S.Ffv[id][v] = fv;
+                    S.Fv[id][v] = (double)fv;
+                }
                 double ld = (double)lam;
                 double i2l = (double)(FT(0.5) / lam);
                 S.i2d[id] = 2.0 * cc * ld;
@@ -269,22 +305,21 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 for (int kk = a + 1; kk < NP; ++kk) {
                     FT sv = (FT)s_S[l][kk];
                     int pi = PairTab<NP>::idx(l, kk);
-                    for (int v = 0; v < 4; ++v) acc[v] += sv * S.pair[d][r][pi][v];
+                    for (int v = 0; v < 4; ++v) acc[v] += sv * S.un.pair[d][r][pi][v];
                 }
             Geo geo = mesh.geom[e];
-            double half = d == 0 ? 0.5 * geo.w : 0.5 * geo.z;
-            for (int v = 0; v < 4; ++v) S.Fdg[id][v] = s_w[r] * half * (double)acc[v];
+            FT wh = (FT)(s_w[r] * (d == 0 ? 0.5 * geo.w : 0.5 * geo.z));
+            for (int v = 0; v < 4; ++v) S.Fdg[id][v] = wh * acc[v];
         }
-        if (!dgmode_rhs && limited) {
+        if (!dgmode) {
             for (int k = tid; k < EPB * NN; k += NT) {
                 int le = k / NN, n = k - le * NN, e = e0 + le;
                 if (e >= mesh.K) continue;
                 SM &S = sm[le];
                 int i = n % NP, j = n / NP;
-                Geo geo = mesh.geom[e];
                 int sim = mesh.sim[e];
                 double dt = stage_dt(A, sim);
-                double mi = geo.z * geo.w / 4.0 * s_w[i] * s_w[j];
+                double dtm = dt * (4.0 * S.invA) * s_iw[i] * s_iw[j];
                 double L[4] = {0, 0, 0, 0};
                 double lo = S.u[0][n], hi = S.u[0][n], ds = 0.0;
                 uchar4 ftv = mesh.ftype[e];
@@ -297,7 +332,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         if (interior) {
                             int id = ifid<NP>(d, row, side == 0 ? pos - 1 : pos);
                             double sgn = side == 0 ? 1.0 : -1.0;
-                            for (int v = 0; v < 4; ++v) L[v] += sgn * S.Ffv[id][v];
+                            for (int v = 0; v < 4; ++v) L[v] += sgn * S.Fv[id][v];
                             lo = fmin(lo, S.ibar[id]); hi = fmax(hi, S.ibar[id]);
                             ds += S.i2d[id];
                         } else {
@@ -319,25 +354,31 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     }
                 }
                 double q[4];
-                double dtm = dt / mi;
                 S.dtm[n] = dtm;
-                for (int v = 0; v < 4; ++v) { S.lfv[v][n] = L[v]; q[v] = S.u[v][n] + dtm * L[v]; S.ufv[v][n] = q[v]; }
+                for (int v = 0; v < 4; ++v) {
+                    S.lfv[v][n] = L[v];
+                    q[v] = S.u[v][n] + dtm * L[v];
+                    S.ufv[v][n] = q[v];
+                    S.ufvf[v][n] = (float)q[v];
+                }
                 double rmin, rmax;
                 if (A.limiting == 2) { rmin = fmax(lo, A.beta * q[0]); rmax = hi; }
                 else { rmin = A.beta * q[0]; rmax = INFINITY; }
                 if (q[0] < rmin) rmin = q[0];
                 if (q[0] > rmax) rmax = q[0];
                 S.rmin[n] = rmin; S.rmax[n] = rmax;
-                double pm = A.beta * pressure_d(g, q[0], q[1], q[2], q[3]);
-                S.pmin[n] = pm;
-                S.c0[n] = g_zero(g, q, pm);
+                double rp = (g - 1.0) * (q[0] * q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]));   // rho p
+                double gms = (g - 1.0) * q[0], pms = A.beta * rp;
+                double c0 = g_zero(gms, q, pms);
+                S.gms[n] = gms; S.pms[n] = pms; S.c0[n] = c0;
                 S.tol[n] = kTol * fabs(q[0]);
+                S.dtmf[n] = (float)dtm; S.gmsf[n] = (float)gms; S.pmsf[n] = (float)pms; S.c0f[n] = (float)c0;
                 if (A.collect && dtm * ds > 1.0) atomicAdd(&A.stats->n_dtx, 1ull);
             }
         }
         __syncthreads();
 
-        if (dgmode_rhs || !limited) {
+        if (dgmode) {
             // ------------- unlimited high-order residual (Eq. evolutionformula)
             for (int k = tid; k < EPB * NN; k += NT) {
                 int le = k / NN, n = k - le * NN, e = e0 + le;
@@ -357,7 +398,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         double sgn = side == 0 ? 1.0 : -1.0;
                         if (interior) {
                             int id = ifid<NP>(d, row, side == 0 ? pos - 1 : pos);
-                            for (int v = 0; v < 4; ++v) L[v] += sgn * S.Fdg[id][v];
+                            for (int v = 0; v < 4; ++v) L[v] += sgn * (double)S.Fdg[id][v];
                         } else {
                             int s = 2 * d + side;
                             int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
@@ -380,7 +421,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         double ut = S.u[v][n] + dt / mi * L[v];
                         double o = ut;
                         if (A.comb == 1) o = 0.75 * A.un[v * KN + gi] + 0.25 * ut;
-                        else if (A.comb == 2) o = A.un[v * KN + gi] / 3.0 + 2.0 / 3.0 * ut;
+                        else if (A.comb == 2) o = A.un[v * KN + gi] * (1.0 / 3.0) + 2.0 / 3.0 * ut;
                         A.out[v * KN + gi] = o;
                     }
                 }
@@ -388,6 +429,23 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             __syncthreads();
             continue;
         }
+
+        // ---------------- P2b: antidiffusive fluxes A = Fdg - Ffv ------------
+        for (int k = tid; k < EPB * NIF; k += NT) {
+            int le = k / NIF, id = k - le * NIF;
+            if (e0 + le >= mesh.K) continue;
+            SM &S = sm[le];
+            int d = id / (NP * N), r = (id / N) % NP, a = id % N;
+            for (int v = 0; v < 4; ++v) {
+                FT fd = S.Fdg[id][v], ff = S.Ffv[id][v];
+                S.un.a.Ad[id][v] = (double)fd - S.Fv[id][v];
+                S.un.a.Af[id][v] = (float)(fd - ff);
+            }
+            int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
+            double aa = fabs(S.un.a.Ad[id][0]);
+            S.ex[id] = (S.dtm[nl] * aa <= S.tol[nl]) && (S.dtm[nr] * aa <= S.tol[nr]);
+        }
+        __syncthreads();
 
         // ---------------- P3: Zalesak factors for density (R7) -------------
         // R+ = min(1, Q+/P+) with Q+ = (m/dt)(rho_max - rho_FV), written with
@@ -405,11 +463,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if (side == 0 ? pos == 0 : pos == N) continue;
                     int a = side == 0 ? pos - 1 : pos;
                     int id = ifid<NP>(d, row, a);
-                    double Ar = S.Fdg[id][0] - S.Ffv[id][0];
-                    int nl = nodeid<NP>(d, row, a), nr = nodeid<NP>(d, row, a + 1);
-                    double aa = fabs(Ar);
-                    bool ex = (S.dtm[nl] * aa <= S.tol[nl]) && (S.dtm[nr] * aa <= S.tol[nr]);
-                    if (ex) continue;
+                    if (S.ex[id]) continue;
+                    double Ar = S.un.a.Ad[id][0];
                     double G = side == 0 ? Ar : -Ar;
                     Pp += G > 0 ? G : 0.0;
                     Pm += G < 0 ? G : 0.0;
@@ -432,21 +487,26 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             int d = id / (NP * N), r = (id / N) % NP, a = id % N;
             SM &S = sm[le];
             int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
-            double Av[4];
-            for (int v = 0; v < 4; ++v) Av[v] = S.Fdg[id][v] - S.Ffv[id][v];
-            double Ar = Av[0];
-            double aa = fabs(Ar);
-            bool ex = (S.dtm[nl] * aa <= S.tol[nl]) && (S.dtm[nr] * aa <= S.tol[nr]);
-            double lr = ex ? 1.0
+            double Ar = S.un.a.Ad[id][0];
+            double lr = S.ex[id] ? 1.0
                            : (-Ar > 0.0) ? fmin(S.Rp[nl], S.Rm[nr]) : fmin(S.Rm[nl], S.Rp[nr]);
-            double u0[4], av[4];
-            double sl_ = -4.0 * S.dtm[nl], sr_ = 4.0 * S.dtm[nr];
-            for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nl]; av[v] = sl_ * Av[v]; }
-            double thl = theta_max(g, u0, av, S.pmin[nl], S.c0[nl], lr);
-            for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nr]; av[v] = sr_ * Av[v]; }
-            double thr = theta_max(g, u0, av, S.pmin[nr], S.c0[nr], thl);
-            S.ell[id] = thr;   // min(theta_l, theta_r): theta_r is searched in [0, theta_l]
-            for (int v = 0; v < 4; ++v) S.Fdg[id][v] = Av[v];
+            double th = lr;
+            // left end point: Gamma-scaled increment -4 dt/m A; right: +4 dt/m A
+            for (int side = 0; side < 2 && th > 0.0; ++side) {
+                int nd = side == 0 ? nl : nr;
+                float sgf = side == 0 ? -4.0f : 4.0f;
+                float u0f[4], af[4];
+                float sdf = sgf * S.dtmf[nd];
+                for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.un.a.Af[id][v]; }
+                if (admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], (float)th) && S.c0[nd] > 0.0 &&
+                    S.ufv[0][nd] > 0.0)
+                    continue;   // the whole interval [0, th] is admissible
+                double u0[4], av[4];
+                double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
+                for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.un.a.Ad[id][v]; }
+                th = theta_max(g, u0, av, S.gms[nd], S.pms[nd], S.c0[nd], th);
+            }
+            S.ell[id] = th;   // min over both end points (each searched below the previous)
         }
         __syncthreads();
 
@@ -460,7 +520,6 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 SM &S = sm[le];
                 int i = n % NP, j = n / NP;
                 Geo geo = mesh.geom[e];
-                int sim = mesh.sim[e];
                 double mi = geo.z * geo.w / 4.0 * s_w[i] * s_w[j];
                 double dtm = S.dtm[n];
                 double sacc[4] = {0, 0, 0, 0}, lmin = 1.0;
@@ -469,22 +528,20 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if (pos > 0) {
                         int id = ifid<NP>(d, row, pos - 1);
                         double l = S.ell[id];
-                        for (int v = 0; v < 4; ++v) sacc[v] += l * S.Fdg[id][v];
+                        for (int v = 0; v < 4; ++v) sacc[v] += l * S.un.a.Ad[id][v];
                         lmin = fmin(lmin, l);
                     }
                     if (pos < N) {
                         int id = ifid<NP>(d, row, pos);
                         double l = S.ell[id];
-                        for (int v = 0; v < 4; ++v) sacc[v] -= l * S.Fdg[id][v];
+                        for (int v = 0; v < 4; ++v) sacc[v] -= l * S.un.a.Ad[id][v];
                         lmin = fmin(lmin, l);
                     }
                 }
-                double uvol[4], resv[4];
-                for (int v = 0; v < 4; ++v) {
-                    uvol[v] = S.ufv[v][n] + dtm * sacc[v];
-                    resv[v] = S.lfv[v][n] + sacc[v];
-                }
-                (void)sim;
+                double uvol[4], resv[4] = {0, 0, 0, 0};
+                for (int v = 0; v < 4; ++v) uvol[v] = S.ufv[v][n] + dtm * sacc[v];
+                if (A.mode == 0)
+                    for (int v = 0; v < 4; ++v) resv[v] = S.lfv[v][n] + sacc[v];
                 size_t gi = (size_t)e * NN + n;
                 // mortar hand-off
                 uchar4 ftv = mesh.ftype[e];
@@ -505,7 +562,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         // rhs mode keeps the mass-weighted residual, step mode u^n
                         sl.un[(size_t)v * sl.S + q] = A.mode == 0 ? resv[v] : (A.comb != 0 ? A.un[v * KN + gi] : 0.0);
                     }
-                    sl.rmin[q] = S.rmin[n]; sl.rmax[q] = S.rmax[n]; sl.pmin[q] = S.pmin[n];
+                    sl.rmin[q] = S.rmin[n]; sl.rmax[q] = S.rmax[n]; sl.pmin[q] = S.pms[n] / S.ufv[0][n];
                     sl.tol[q] = S.tol[n]; sl.mass[q] = mi; sl.nmort[q] = (float)nmort;
                 }
                 if (A.mode == 0) {
@@ -514,7 +571,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     for (int v = 0; v < 4; ++v) {
                         double o = uvol[v];
                         if (A.comb == 1) o = 0.75 * A.un[v * KN + gi] + 0.25 * uvol[v];
-                        else if (A.comb == 2) o = A.un[v * KN + gi] / 3.0 + 2.0 / 3.0 * uvol[v];
+                        else if (A.comb == 2) o = A.un[v * KN + gi] * (1.0 / 3.0) + 2.0 / 3.0 * uvol[v];
                         A.out[v * KN + gi] = o;
                     }
                 }
@@ -525,10 +582,10 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if (nmort == 0) {
                         // rho p = (gamma-1)(rho E - |m|^2/2): checks without division
                         double rp = (g - 1.0) * (uvol[0] * uvol[3] - 0.5 * (uvol[1] * uvol[1] + uvol[2] * uvol[2]));
-                        double pmn = S.pmin[n];
+                        // p >= p_min  <=>  rho p rho_FV >= (p_min rho_FV) rho
                         if (uvol[0] < S.rmin[n] - kViolTol * fabs(S.rmin[n]) ||
                             uvol[0] > S.rmax[n] + kViolTol * fabs(S.rmax[n])) st_vr++;
-                        if (rp < (pmn - kViolTol * fabs(pmn)) * uvol[0]) st_vp++;
+                        if (rp * S.ufv[0][n] < S.pms[n] * (1.0 - kViolTol) * uvol[0]) st_vp++;
                         if (!(uvol[0] > 0.0) || !(rp > 0.0)) st_np++;
                         st_rmin = fmin(st_rmin, uvol[0]);
                         if (lmin < 1.0) st_pmin = fmin(st_pmin, rp / uvol[0]);

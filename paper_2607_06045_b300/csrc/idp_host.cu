@@ -113,7 +113,7 @@ void build_ops(int N, int proj, Ops &o) {
     double x[NPMAX], w[NPMAX], lam[NPMAX];
     lgl_nodes(N, x, w);
     bary_weights(np, x, lam);
-    for (int i = 0; i < np; ++i) { o.xi[i] = x[i]; o.w[i] = w[i]; }
+    for (int i = 0; i < np; ++i) { o.xi[i] = x[i]; o.w[i] = w[i]; o.iw[i] = 1.0 / w[i]; }
     // D_ij = phi_j'(x_i) in barycentric form; Sbar = 2 diag(w) D - B
     for (int i = 0; i < np; ++i) {
         double diag = 0.0;

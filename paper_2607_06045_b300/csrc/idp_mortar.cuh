@@ -159,7 +159,7 @@ k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
         else if (av[0] < 0.0) { double t = (sl.rmin[s] - tl - u0[0]) / av[0]; if (t < lr) lr = t; }
         if (lr < 0.0) lr = 0.0;
         double pm = sl.pmin[s] - kTol * fabs(sl.pmin[s]);
-        th = theta_max(A.gamma, u0, av, pm, g_zero(A.gamma, u0, pm), lr);
+        th = theta_max(A.gamma, u0, av, A.gamma - 1.0, pm, g_zero(A.gamma - 1.0, u0, pm), lr);
     }
     for (int o = 16; o > 0; o >>= 1) th = fmin(th, __shfl_down_sync(0xffffffffu, th, o));
     if (lane == 0) {
@@ -207,7 +207,7 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double o = ut[v];
                 double un = sl.un[(size_t)v * sl.S + s0];
                 if (A.comb == 1) o = 0.75 * un + 0.25 * ut[v];
-                else if (A.comb == 2) o = un / 3.0 + 2.0 / 3.0 * ut[v];
+                else if (A.comb == 2) o = un * (1.0 / 3.0) + 2.0 / 3.0 * ut[v];
                 A.out[v * KN + gnode] = o;
             }
         }
@@ -300,8 +300,6 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int 
                 double mi = geo.z * geo.w / 4.0 * ops->w[i] * ops->w[j];
                 val = mi / ds;
             }
-            // one atomic per thread and simulation run (elements of a block
-            // almost always share the simulation)
             if (sim != bsim) {
                 if (bsim >= 0 && best < INFINITY) atomicMin(&dtmin[bsim], dbits(best));
                 bsim = sim;
@@ -309,7 +307,16 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int 
             }
             if (val > 0.0 && val < best) best = val;
         }
-        if (bsim >= 0 && best < INFINITY) atomicMin(&dtmin[bsim], dbits(best));
+        // warp minimum among the lanes that share lane 0's simulation, then
+        // one atomic per warp (other simulations: one atomic per lane)
+        {
+            int s0 = __shfl_sync(0xffffffffu, bsim, 0);
+            bool same = bsim == s0;
+            double bw = same ? best : INFINITY;
+            for (int o = 16; o > 0; o >>= 1) bw = fmin(bw, __shfl_down_sync(0xffffffffu, bw, o));
+            if ((threadIdx.x & 31) == 0 && s0 >= 0 && bw < INFINITY) atomicMin(&dtmin[s0], dbits(bw));
+            if (!same && bsim >= 0 && best < INFINITY) atomicMin(&dtmin[bsim], dbits(best));
+        }
         __syncthreads();
     }
 }
