@@ -442,7 +442,7 @@ StageArgs base_args(idp_ctx *c) {
 void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux,
                    cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
     const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
-    if (c->M > 0 && need_mortar_flux) c->L.mortar_flux(gm, st, c->mesh, c->slots, A.u, c->gamma, c->d_ops);
+    if (c->M > 0 && need_mortar_flux) c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, A.u, c->gamma, c->d_ops);
     if (ev0) cudaEventRecord(ev0, st);
     c->L.element(c->opt.precision, c->epb, element_grid(c, c->epb, c->persistent, c->bps), st, c->mesh, c->slots, A);
     if (ev1) cudaEventRecord(ev1, st);
@@ -458,10 +458,11 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) 
     k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
     if (c->M > 0 && mortar_flux && c->opt.dt_rule == 0) {
         const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
-        c->L.mortar_flux(gm, st, c->mesh, c->slots, u, c->gamma, c->d_ops);
+        c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, u, c->gamma, c->d_ops);
     }
     int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
-    c->L.dt(g, st, c->mesh, c->slots, u, c->gamma, c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin, c->d_status);
+    c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, c->gamma, c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
+            c->d_status);
 }
 
 // one SSP-RK3 step on u (in place), using the ctx stage buffers

@@ -18,12 +18,13 @@ struct Launchers {
     cudaError_t (*element_prepare)(int fp32, int epb, int *blocks_per_sm);
     void (*element)(int fp32, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
                     const StageArgs &a);
-    void (*mortar_flux)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
+    void (*mortar_flux)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
                         double gamma, const Ops *ops);
     void (*mortar_limit)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
     void (*mortar_apply)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
-    void (*dt)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma,
-               int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status);
+    void (*dt)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
+               double gamma, int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin,
+               unsigned *status);
     void (*integrals)(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part);
 };
 

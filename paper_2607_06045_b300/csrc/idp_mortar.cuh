@@ -20,14 +20,26 @@ namespace idp {
 
 constexpr int MORTARS_PER_BLOCK = 4;   // one warp per mortar
 
-template <int NP>
+// FT: flux arithmetic type (FP32 in the FP32 form). Interpolation, the
+// admissibility test, bar states and all sums are FP64.
+template <int NP, typename FT>
+__device__ __forceinline__ Prim<FT> mortar_prim(double g, const double *q) {
+    if constexpr (sizeof(FT) == 4) {
+        float a, b;
+        return make_prim_f32(g, q[0], q[1], q[2], q[3], false, a, b);
+    } else {
+        return make_prim<FT>(g, q[0], q[1], q[2], q[3], false);
+    }
+}
+
+template <int NP, typename FT>
 __global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
 k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, const Ops *ops) {
     constexpr int NN = NP * NP, Q = 3 * NP;
     __shared__ double s_u[MORTARS_PER_BLOCK][Q][4];
-    __shared__ double s_pr[MORTARS_PER_BLOCK][Q][3];     // normal velocity, p, c
+    __shared__ FT s_pr[MORTARS_PER_BLOCK][Q][3];     // normal velocity, p, c
     __shared__ double s_ui[MORTARS_PER_BLOCK][2 * NP][4];
-    __shared__ double s_f[MORTARS_PER_BLOCK][2 * NP][4];
+    __shared__ FT s_f[MORTARS_PER_BLOCK][2 * NP][4];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = blockIdx.x * MORTARS_PER_BLOCK + warp;
     if (m >= mesh.M) return;
@@ -39,6 +51,7 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
     const Geo geoL = mesh.geom[L];
     const double halfL = dir == 0 ? 0.5 * geoL.w : 0.5 * geoL.z, halfS = 0.5 * halfL;
     const double sg = low ? 1.0 : -1.0;   // large side's outward normal along +dir
+    const FT sgf = (FT)sg;
     const double g = gamma;
     if (lane < Q) {
         int gnode;
@@ -49,7 +62,7 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
         }
         double q[4];
         for (int v = 0; v < 4; ++v) { q[v] = u[v * KN + gnode]; s_u[warp][lane][v] = q[v]; }
-        Prim<double> pr = make_prim<double>(g, q[0], q[1], q[2], q[3], false);
+        Prim<FT> pr = mortar_prim<NP, FT>(g, q);
         s_pr[warp][lane][0] = dir == 0 ? pr.v1 : pr.v2;
         s_pr[warp][lane][1] = pr.p;
         s_pr[warp][lane][2] = pr.c;
@@ -57,7 +70,7 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
     __syncwarp();
     // interpolation of the large trace to the small-face nodes, admissibility
     bool badl = false;
-    Prim<double> pint;
+    Prim<FT> pint;
     if (lane < 2 * NP) {
         double acc[4] = {0, 0, 0, 0};
         for (int k = 0; k < NP; ++k) {
@@ -67,19 +80,19 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
         for (int v = 0; v < 4; ++v) s_ui[warp][lane][v] = acc[v];
         // rho p > 0 without a division, then the primitives
         badl = !(acc[0] > 0.0) || !(acc[0] * acc[3] - 0.5 * (acc[1] * acc[1] + acc[2] * acc[2]) > 0.0);
-        if (!badl) pint = make_prim<double>(g, acc[0], acc[1], acc[2], acc[3], false);
+        if (!badl) pint = mortar_prim<NP, FT>(g, acc);
     }
     const bool bad = __any_sync(0xffffffffu, badl);
     // LLF on the small faces (left/bottom state first)
     if (!bad && lane < 2 * NP) {
-        double f[4];
+        FT f[4];
         const double *ui = s_ui[warp][lane], *us = s_u[warp][NP + lane];
-        Prim<double> ps;
-        ps.v1 = dir == 0 ? s_pr[warp][NP + lane][0] : 0.0;
-        ps.v2 = dir == 1 ? s_pr[warp][NP + lane][0] : 0.0;
+        Prim<FT> ps;
+        ps.v1 = dir == 0 ? s_pr[warp][NP + lane][0] : FT(0);
+        ps.v2 = dir == 1 ? s_pr[warp][NP + lane][0] : FT(0);
         ps.p = s_pr[warp][NP + lane][1];
         ps.c = s_pr[warp][NP + lane][2];
-        if (low) llf_prim<double>(ui, pint, us, ps, dir, f); else llf_prim<double>(us, ps, ui, pint, dir, f);
+        if (low) llf_prim<FT>(ui, pint, us, ps, dir, f); else llf_prim<FT>(us, ps, ui, pint, dir, f);
         for (int v = 0; v < 4; ++v) s_f[warp][lane][v] = f[v];
     }
     __syncwarp();
@@ -88,15 +101,17 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
         double chi[4] = {0, 0, 0, 0}, clo[4] = {0, 0, 0, 0};
         if (!bad) {
             if (q < NP) {
+                // projection summed in FP64: conservation across the mortar
+                // holds to FP64 rounding whatever the flux type
                 double acc[4] = {0, 0, 0, 0};
                 for (int r = 0; r < 2 * NP; ++r) {
                     double c = ops->P[q][r];
-                    for (int v = 0; v < 4; ++v) acc[v] += c * s_f[warp][r][v];
+                    for (int v = 0; v < 4; ++v) acc[v] += c * (double)s_f[warp][r][v];
                 }
                 for (int v = 0; v < 4; ++v) chi[v] = -sg * ops->w[q] * (halfL * acc[v]);
             } else {
                 int l = (q - NP) % NP;
-                for (int v = 0; v < 4; ++v) chi[v] = sg * ops->w[l] * (halfS * s_f[warp][q - NP][v]);
+                for (int v = 0; v < 4; ++v) chi[v] = sg * ops->w[l] * (halfS * (double)s_f[warp][q - NP][v]);
             }
         }
         // sparse low-order flux (Eq. interfaceflux_local), bar states and
@@ -109,20 +124,22 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
                 double wt = ops->wt[k][r] * halfL;
                 if (wt <= 0.0) continue;
                 const double *a = s_u[warp][k], *b = s_u[warp][NP + r];
-                const double *pa = s_pr[warp][k], *pb = s_pr[warp][NP + r];
-                double la = fabs(pa[0]) + pa[2], lb = fabs(pb[0]) + pb[2];
-                double lam = la > lb ? la : lb;
-                double fa[4], fb[4];
-                phys_flux<double>(a[1], a[2], a[3], pa[1], pa[0], dir, fa);
-                phys_flux<double>(b[1], b[2], b[3], pb[1], pb[0], dir, fb);
+                const FT *pa = s_pr[warp][k], *pb = s_pr[warp][NP + r];
+                FT la = fabs(pa[0]) + pa[2], lb = fabs(pb[0]) + pb[2];
+                FT lam = la > lb ? la : lb;
+                FT fa[4], fb[4];
+                phys_flux<FT>((FT)a[1], (FT)a[2], (FT)a[3], pa[1], pa[0], dir, fa);
+                phys_flux<FT>((FT)b[1], (FT)b[2], (FT)b[3], pb[1], pb[0], dir, fb);
+                FT hw = (FT)(0.5 * wt);
                 for (int v = 0; v < 4; ++v) {
-                    double term = 0.5 * wt * ((sg * fa[v] + sg * fb[v]) - lam * (b[v] - a[v]));
-                    clo[v] += q < NP ? -term : term;
+                    FT term = hw * ((sgf * fa[v] + sgf * fb[v]) - lam * ((FT)b[v] - (FT)a[v]));
+                    clo[v] += q < NP ? -(double)term : (double)term;
                 }
-                double rbv = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) * (0.5 / lam);
+                double ld = (double)lam;
+                double rbv = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) * (double)(FT(0.5) / lam);
                 lo = fmin(lo, rbv);
                 hi = fmax(hi, rbv);
-                ds += 2.0 * (wt / 2.0) * lam;
+                ds += 2.0 * (wt / 2.0) * ld;
             }
         if (bad)
             for (int v = 0; v < 4; ++v) chi[v] = clo[v];
@@ -229,12 +246,15 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
 // (w_i h / 2) / (|v| + c) (rule 1); minimum per simulation as ordered bits.
 // One block holds EPB elements, one thread per node; each node's wave speeds
 // |v_x| + c and |v_y| + c are formed once and shared through shared memory.
-template <int NP, int EPB>
+// In the FP32 form (FT = float) the wave speeds, sums and the quotient are
+// FP32 and the result is scaled by (1 - 4e-6), more than the FP32 rounding of
+// these few operations, so the step never exceeds the FP64 limit.
+template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads)
 k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int rule, const Ops *ops,
      const double *t_sim, unsigned long long *dtmin, unsigned *status) {
     constexpr int NN = NP * NP, N = NP - 1, NT = ElemLaunch<NP, EPB>::threads;
-    __shared__ double s_l[EPB][2][NN];
+    __shared__ FT s_l[EPB][2][NN];
     const size_t KN = (size_t)mesh.K * NN;
     const double g = gamma;
     for (int e0 = blockIdx.x * EPB; e0 < mesh.K; e0 += gridDim.x * EPB) {
@@ -242,8 +262,9 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int 
             int le = k / NN, n = k - le * NN, e = e0 + le;
             if (e >= mesh.K) continue;
             size_t gi = (size_t)e * NN + n;
-            Prim<double> q = make_prim<double>(g, u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi], false);
-            if (!(q.rho > 0.0) || !(q.p > 0.0)) atomicOr(status, ST_BAD_INPUT);
+            double qd[4] = {u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi]};
+            Prim<FT> q = mortar_prim<NP, FT>(g, qd);
+            if (!(qd[0] > 0.0) || !(q.p > FT(0))) atomicOr(status, ST_BAD_INPUT);
             s_l[le][0][n] = fabs(q.v1) + q.c;
             s_l[le][1][n] = fabs(q.v2) + q.c;
         }
@@ -258,21 +279,25 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int 
             const int sim = mesh.sim[e];
             double val;
             if (rule == 1) {
-                val = fmin(ops->w[i] * geo.z / 2.0 / s_l[le][0][n], ops->w[j] * geo.w / 2.0 / s_l[le][1][n]);
+                if constexpr (sizeof(FT) == 4)
+                    val = (double)fminf((float)(ops->w[i] * geo.z / 2.0) / s_l[le][0][n],
+                                        (float)(ops->w[j] * geo.w / 2.0) / s_l[le][1][n]) * (1.0 - 4e-6);
+                else
+                    val = fmin(ops->w[i] * geo.z / 2.0 / s_l[le][0][n], ops->w[j] * geo.w / 2.0 / s_l[le][1][n]);
             } else {
-                double ds = 0.0;
+                FT ds = FT(0);
                 const uchar4 ftv = mesh.ftype[e];
                 const int4 nb4 = mesh.fnbr[e];
                 for (int d = 0; d < 2; ++d) {
                     int pos = d == 0 ? i : j, row = d == 0 ? j : i;
-                    double cc = ops->w[row] * (d == 0 ? geo.w : geo.z) / 4.0;
-                    double li = s_l[le][d][n];
+                    FT cc = (FT)(ops->w[row] * (d == 0 ? geo.w : geo.z) / 4.0);
+                    FT li = s_l[le][d][n];
                     for (int side = 0; side < 2; ++side) {
                         bool interior = side == 0 ? pos > 0 : pos < N;
                         if (interior) {
                             int on = d == 0 ? n + (side == 0 ? -1 : 1) : n + (side == 0 ? -NP : NP);
-                            double lo = s_l[le][d][on];
-                            ds += 2.0 * cc * (li > lo ? li : lo);
+                            FT lo = s_l[le][d][on];
+                            ds += FT(2) * cc * (li > lo ? li : lo);
                         } else {
                             int s = 2 * d + side;
                             int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
@@ -288,17 +313,18 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int 
                                     double xn = geo.x + 0.5 * geo.z * (1.0 + ops->xi[i]);
                                     ghost_state(mesh.siminfo[sim], s, ui, xn, t_sim[sim], uo);
                                 }
-                                Prim<double> po = make_prim<double>(g, uo[0], uo[1], uo[2], uo[3], false);
-                                double lo = fabs(d == 0 ? po.v1 : po.v2) + po.c;
-                                ds += 2.0 * cc * (li > lo ? li : lo);
+                                Prim<FT> po = mortar_prim<NP, FT>(g, uo);
+                                FT lo = fabs(d == 0 ? po.v1 : po.v2) + po.c;
+                                ds += FT(2) * cc * (li > lo ? li : lo);
                             } else {
-                                ds += sl.dsum[slot_of<NP>(ft, nb, row)];
+                                ds += (FT)sl.dsum[slot_of<NP>(ft, nb, row)];
                             }
                         }
                     }
                 }
                 double mi = geo.z * geo.w / 4.0 * ops->w[i] * ops->w[j];
-                val = mi / ds;
+                if constexpr (sizeof(FT) == 4) val = (double)((float)mi / ds) * (1.0 - 4e-6);
+                else val = mi / ds;
             }
             if (sim != bsim) {
                 if (bsim >= 0 && best < INFINITY) atomicMin(&dtmin[bsim], dbits(best));

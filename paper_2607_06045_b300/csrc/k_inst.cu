@@ -63,9 +63,10 @@ void element(int fp32, int epb, int grid, cudaStream_t st, const MeshDev &m, con
     IDP_EPB_SWITCH(el_launch, grid, st, m, s, a)
 }
 
-void mortar_flux(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma,
-                 const Ops *ops) {
-    k_mortar_flux<NP><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gamma, ops);
+void mortar_flux(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
+                 double gamma, const Ops *ops) {
+    if (fp32) k_mortar_flux<NP, float><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gamma, ops);
+    else k_mortar_flux<NP, double><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gamma, ops);
 }
 
 void mortar_limit(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
@@ -76,11 +77,16 @@ void mortar_apply(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s
     k_mortar_apply<NP><<<grid, 256, 0, st>>>(m, s, a);
 }
 
-void dt(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma, int rule,
-        const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status) {
+void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma,
+        int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status) {
     constexpr int EPB = NP * NP >= 64 ? 2 : (NP * NP >= 25 ? 4 : 8);
     int blocks = (m.K + EPB - 1) / EPB;
-    k_dt<NP, EPB><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim, dtmin, status);
+    if (fp32)
+        k_dt<NP, EPB, float><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
+                                                                             dtmin, status);
+    else
+        k_dt<NP, EPB, double><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
+                                                                              dtmin, status);
     (void)grid;
 }
 
