@@ -10,6 +10,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "idp_bits.cuh"
+
 namespace idp {
 
 constexpr int NPMAX = 8;          // N <= 7
@@ -196,10 +198,12 @@ __device__ __forceinline__ Prim<FT> make_prim(double g, double r, double m1, dou
 
 // FP32 primitives of the FP32 form. When E - |m|^2/2rho keeps at least half
 // of E (no cancellation) the pressure is formed in FP32 (relative error below
-// 1e-6, positive for sure); otherwise in FP64 as above.
+// 1e-6, positive for sure); otherwise in FP64 as above. The state is rounded
+// to FP32 on the integer pipe (d2f); the same function serves every element
+// that reads the node, so they all get the same bits.
 __device__ __forceinline__ Prim<float> make_prim_f32(double g, double r, double m1, double m2, double E, bool full,
                                                      float &m1o, float &m2o) {
-    float rf = (float)r, m1f = (float)m1, m2f = (float)m2, Ef = (float)E;
+    float rf = d2f(r), m1f = d2f(m1), m2f = d2f(m2), Ef = d2f(E);
     float rif = __frcp_rn(rf);
     float v1 = __fmul_rn(m1f, rif), v2 = __fmul_rn(m2f, rif);
     float kef = __fmul_rn(0.5f, __fadd_rn(__fmul_rn(m1f, v1), __fmul_rn(m2f, v2)));
@@ -207,9 +211,9 @@ __device__ __forceinline__ Prim<float> make_prim_f32(double g, double r, double 
     Prim<float> q;
     if (rf > 0.0f && Ef > 0.0f && pef >= 0.5f * Ef) {
         q.rho = rf; q.v1 = v1; q.v2 = v2; q.E = Ef;
-        q.p = __fmul_rn((float)(g - 1.0), pef);
+        q.p = __fmul_rn(d2f(g - 1.0), pef);
         q.lr = q.lb = 0.0f;
-        q.c = __fsqrt_rn(__fmul_rn(__fmul_rn((float)g, q.p), rif));
+        q.c = __fsqrt_rn(__fmul_rn(__fmul_rn(d2f(g), q.p), rif));
         q.beta = full ? __fmul_rn(rf, __frcp_rn(q.p)) : 0.0f;
     } else {
         q = make_prim<float>(g, r, m1, m2, E, full);
@@ -219,18 +223,29 @@ __device__ __forceinline__ Prim<float> make_prim_f32(double g, double r, double 
     return q;
 }
 
-// Local Lax-Friedrichs flux along axis d from conserved states and their
-// primitives (Davis wave speed, R3); returns lambda.
+// Conserved-state component in the flux type (FP32 via the integer pipe).
 template <typename FT>
-__device__ __forceinline__ FT llf_prim(const double uL[4], const Prim<FT> &a, const double uR[4], const Prim<FT> &b,
-                                       int d, FT f[4]) {
+__device__ __forceinline__ FT to_ft(double x) {
+    if constexpr (sizeof(FT) == 4) return d2f(x);
+    else return x;
+}
+template <typename FT>
+__device__ __forceinline__ FT to_ft(float x) { return (FT)x; }
+
+// Local Lax-Friedrichs flux along axis d from conserved states (double, or
+// float in the FP32 form) and their primitives (Davis wave speed, R3);
+// returns lambda.
+template <typename FT, typename ST>
+__device__ __forceinline__ FT llf_prim(const ST uL[4], const Prim<FT> &a, const ST uR[4], const Prim<FT> &b, int d,
+                                       FT f[4]) {
     FT vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
     FT la = fabs(vna) + a.c, lb = fabs(vnb) + b.c;
     FT lam = la > lb ? la : lb;
-    FT fa[4], fb[4];
-    phys_flux<FT>((FT)uL[1], (FT)uL[2], (FT)uL[3], a.p, vna, d, fa);
-    phys_flux<FT>((FT)uR[1], (FT)uR[2], (FT)uR[3], b.p, vnb, d, fb);
-    for (int v = 0; v < 4; ++v) f[v] = FT(0.5) * (fa[v] + fb[v]) - FT(0.5) * lam * ((FT)uR[v] - (FT)uL[v]);
+    FT fa[4], fb[4], ul[4], ur[4];
+    for (int v = 0; v < 4; ++v) { ul[v] = to_ft<FT>(uL[v]); ur[v] = to_ft<FT>(uR[v]); }
+    phys_flux<FT>(ul[1], ul[2], ul[3], a.p, vna, d, fa);
+    phys_flux<FT>(ur[1], ur[2], ur[3], b.p, vnb, d, fb);
+    for (int v = 0; v < 4; ++v) f[v] = FT(0.5) * (fa[v] + fb[v]) - FT(0.5) * lam * (ur[v] - ul[v]);
     return lam;
 }
 
@@ -262,9 +277,10 @@ __device__ __forceinline__ double g_zero(double gm, const double u0[4], double p
 // exact arithmetic) from FP32 inputs that carry at most three roundings each:
 // every product and sum below then stays within 17 unit roundings of the sum
 // S of the absolute terms, so g_f32 > 4e-6 S implies g(hi) > 0 with a
-// fourfold margin, and the FP64 evaluation of the same decision agrees.
-// Returns false when it cannot decide (near the bound, or magnitudes outside
-// the FP32 range).
+// fourfold margin, and the FP64 evaluation of the same decision agrees. When
+// h is theta rounded to FP32, g(theta) - g(h) is below 2 unit roundings of S,
+// well inside the margin, so theta itself is certified. Returns false when it
+// cannot decide (near the bound, or magnitudes outside the FP32 range).
 __device__ __forceinline__ bool admissible_f32(float gm, const float u0[4], const float a[4], float pm, float c0f,
                                                float h) {
     if (!(c0f > 0.0f) || !(u0[0] > 0.0f) || !(h > 0.0f)) return false;
@@ -287,9 +303,9 @@ __device__ __forceinline__ bool admissible_f32(float gm, const float u0[4], cons
 __device__ __forceinline__ bool admissible_f32(double gm, const double u0[4], const double a[4], double pm,
                                                double c0, double hi) {
     if (!(c0 > 0.0) || !(u0[0] > 0.0) || !(hi > 0.0)) return false;
-    float uf[4] = {(float)u0[0], (float)u0[1], (float)u0[2], (float)u0[3]};
-    float af[4] = {(float)a[0], (float)a[1], (float)a[2], (float)a[3]};
-    return admissible_f32((float)gm, uf, af, (float)pm, (float)c0, (float)hi);
+    float uf[4] = {d2f(u0[0]), d2f(u0[1]), d2f(u0[2]), d2f(u0[3])};
+    float af[4] = {d2f(a[0]), d2f(a[1]), d2f(a[2]), d2f(a[3])};
+    return admissible_f32(d2f(gm), uf, af, d2f(pm), d2f(c0), d2f(hi));
 }
 
 // Reading R8: largest theta in [0, hi] such that u0 + theta a has rho > 0 and

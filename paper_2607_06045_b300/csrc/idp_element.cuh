@@ -48,26 +48,32 @@ __device__ __forceinline__ double stage_time(const StageArgs &A, int sim, double
 template <int NP, typename FT>
 struct ElemSm {
     static constexpr int NN = NP * NP, N = NP - 1, NPAIR = NP * (NP - 1) / 2, NIF = 2 * NP * (NP - 1);
+    static constexpr bool F32 = sizeof(FT) == 4;
     double u[4][NN];
     double ufv[4][NN];
     double lfv[4][NN];
-    double face[4][NP][4];   // J-weighted numerical flux along +x/+y (conforming, boundary)
+    double face[4][NP][4];   // (w_t |face|/2) * numerical flux along +x/+y (conforming, boundary)
     double outs[4][NP][4];   // outside state (conforming neighbour or ghost)
     double fbar[4][NP];      // bar-state density across the face
-    double f2d[4][NP];       // 2 d_ij across the face
+    FT f2d[4][NP];           // 2 d_ij across the face (time-step check)
     FT Fdg[NIF][4];          // mass-weighted high-order subcell flux w_r * fhat (flux type)
-    FT Ffv[NIF][4];          // mass-weighted low-order subcell flux (flux type)
+    FT Ffv[F32 ? NIF : 1][4];  // FP32 form: the low-order subcell flux in FP32
     double Fv[NIF][4];       // the low-order subcell flux in FP64, for the residual sums
-    double ibar[NIF], i2d[NIF], ell[NIF];
+    double ibar[NIF], ell[NIF];
+    FT i2d[NIF];
     double rmin[NN], rmax[NN], tol[NN], Rp[NN], Rm[NN];
     // pressure solve at u_FV in the form scaled by rho_FV: gm = (gamma-1) rho_FV,
     // pm = p_min rho_FV = beta (gamma-1)(rho E - |m|^2/2), c0 = g(0)
     double dtm[NN], gms[NN], pms[NN], c0[NN];
     float ufvf[4][NN];       // FP32 copies for the certified admissibility check
     float dtmf[NN], gmsf[NN], pmsf[NN], c0f[NN];
+    float tqf[NN];           // FP32 form: exemption threshold kTol |rho_FV| m / dt
     unsigned char ex[NIF];   // density antidiffusion below the tolerance (R15)
     float uf[4][NN];         // FP32 state (FP32 form)
-    double invA;             // 1 / (dx dy)
+    // per-element constants: 1/(dx dy), dx dy / 4, stage dt, 4 dt / (dx dy),
+    // half and quarter edge lengths (and FP32 copies), (dx dy / 4) / dt
+    double invA, A4, dt, dt4A, hx, hy, qx, qy;
+    float hxf, hyf, qxf, qyf, idtmf;
     FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
     union {
         FT pair[2][NP][NPAIR][4];   // two-point fluxes (dead after the Sbar contraction)
@@ -156,13 +162,22 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
     constexpr bool F32 = sizeof(FT) == 4;
     extern __shared__ __align__(16) unsigned char smraw[];
     SM *sm = reinterpret_cast<SM *>(smraw);
-    __shared__ double s_w[NP], s_iw[NP], s_S[NP][NP];
+    // reference tables: w, 1/w, Sbar, w_i w_j, 1/(w_i w_j) and FP32 copies
+    __shared__ double s_w[NP], s_S[NP][NP], s_ww[NN], s_iww[NN];
+    __shared__ float s_wf[NP], s_Sf[NP][NP], s_wwf[NN];
 
     const int tid = threadIdx.x;
-    if (tid < NP) { s_w[tid] = A.ops->w[tid]; s_iw[tid] = A.ops->iw[tid]; }
-    if (tid < NN) s_S[tid / NP][tid % NP] = A.ops->S[tid / NP][tid % NP];
+    if (tid < NP) { s_w[tid] = A.ops->w[tid]; s_wf[tid] = d2f(A.ops->w[tid]); }
+    if (tid < NN) {
+        const int i = tid % NP, j = tid / NP;
+        s_S[j][i] = A.ops->S[j][i];
+        s_Sf[j][i] = d2f(A.ops->S[j][i]);
+        s_ww[tid] = A.ops->w[i] * A.ops->w[j];
+        s_iww[tid] = A.ops->iw[i] * A.ops->iw[j];
+        s_wwf[tid] = d2f(s_ww[tid]);
+    }
     const double g = A.gamma;
-    const FT ginv1 = FT(1.0 / (g - 1.0));
+    const FT ginv1 = to_ft<FT>(1.0 / (g - 1.0));
     const size_t KN = (size_t)mesh.K * NN;
     const bool limited = A.limiting > 0;
     const bool dgmode = (A.mode == 0 && A.dt == 0.0) || !limited;
@@ -177,18 +192,32 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             double r = A.u[gi], m1 = A.u[KN + gi], m2 = A.u[2 * KN + gi], E = A.u[3 * KN + gi];
             S.u[0][n] = r; S.u[1][n] = m1; S.u[2][n] = m2; S.u[3][n] = E;
             Prim<FT> q;
+            bool okp;
             if constexpr (F32) {
                 float m1f, m2f;
                 q = make_prim_f32(g, r, m1, m2, E, true, m1f, m2f);
                 S.uf[0][n] = q.rho; S.uf[1][n] = m1f; S.uf[2][n] = m2f; S.uf[3][n] = q.E;
+                okp = q.p > 0.0f;
             } else {
                 q = make_prim<FT>(g, r, m1, m2, E, true);
+                okp = dpos(q.p);
             }
-            if (!(r > 0.0) || !(q.p > FT(0)) || !isfinite(E) || !isfinite(m1) || !isfinite(m2))
-                atomicOr(A.status, ST_BAD_INPUT);
+            if (!(okp && dpos(r) && dfinite(m1) && dfinite(m2) && dfinite(E))) atomicOr(A.status, ST_BAD_INPUT);
             S.pr[0][n] = q.rho; S.pr[1][n] = q.v1; S.pr[2][n] = q.v2; S.pr[3][n] = q.p; S.pr[4][n] = q.c;
             S.pr[5][n] = q.E; S.pr[6][n] = q.lr; S.pr[7][n] = q.lb; S.pr[8][n] = q.beta;
-            if (n == 0) { Geo geo = mesh.geom[e]; S.invA = 1.0 / (geo.z * geo.w); }
+            if (n == 0) {
+                Geo geo = mesh.geom[e];
+                double area = geo.z * geo.w, dt = stage_dt(A, mesh.sim[e]);
+                S.invA = 1.0 / area;
+                S.A4 = 0.25 * area;
+                S.dt = dt;
+                S.dt4A = dt * (4.0 * S.invA);
+                S.hx = 0.5 * geo.z; S.hy = 0.5 * geo.w; S.qx = 0.25 * geo.z; S.qy = 0.25 * geo.w;
+                if constexpr (F32) {
+                    S.hxf = d2f(S.hx); S.hyf = d2f(S.hy); S.qxf = d2f(S.qx); S.qyf = d2f(S.qy);
+                    S.idtmf = dt > 0.0 ? d2f(S.A4 / dt) : 0.0f;
+                }
+            }
         }
         for (int k = tid; k < EPB * 4 * NP; k += NT) {
             int le = k / (4 * NP), s = (k / NP) % 4, t = k % NP, e = e0 + le;
@@ -238,26 +267,35 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             if (ft != FT_CONF && ft != FT_BND) continue;
             SM &S = sm[le];
             int d = s >> 1, n = face_node<NP>(s, t);
-            double in[4] = {S.u[0][n], S.u[1][n], S.u[2][n], S.u[3][n]};
-            double out[4] = {S.outs[s][t][0], S.outs[s][t][1], S.outs[s][t][2], S.outs[s][t][3]};
+            const double *out = S.outs[s][t];
             Prim<FT> pi = load_prim<NP, FT>(S, n);
-            Prim<FT> po;
+            FT f[4], lam;
+            double i2l;
+            // left/bottom state first, so that both elements of a face form
+            // the same bits
             if constexpr (F32) {
                 float m1f, m2f;
-                po = make_prim_f32(g, out[0], out[1], out[2], out[3], false, m1f, m2f);
+                Prim<float> po = make_prim_f32(g, out[0], out[1], out[2], out[3], false, m1f, m2f);
+                float ui[4] = {S.uf[0][n], S.uf[1][n], S.uf[2][n], S.uf[3][n]};
+                float uo[4] = {po.rho, m1f, m2f, po.E};
+                lam = (s == 0 || s == 2) ? llf_prim<float, float>(uo, po, ui, pi, d, f)
+                                         : llf_prim<float, float>(ui, pi, uo, po, d, f);
+                float whf = s_wf[t] * (d == 0 ? S.hyf : S.hxf);
+                for (int v = 0; v < 4; ++v) S.face[s][t][v] = f2d(whf * f[v]);
+                S.f2d[s][t] = whf * lam;
+                i2l = f2d(0.5f / lam);
             } else {
-                po = make_prim<FT>(g, out[0], out[1], out[2], out[3], false);
+                Prim<FT> po = make_prim<FT>(g, out[0], out[1], out[2], out[3], false);
+                double ui[4] = {S.u[0][n], S.u[1][n], S.u[2][n], S.u[3][n]};
+                lam = (s == 0 || s == 2) ? llf_prim<FT, double>(out, po, ui, pi, d, f)
+                                         : llf_prim<FT, double>(ui, pi, out, po, d, f);
+                double wh = s_w[t] * (d == 0 ? S.hy : S.hx);
+                for (int v = 0; v < 4; ++v) S.face[s][t][v] = wh * f[v];
+                S.f2d[s][t] = wh * lam;
+                i2l = 0.5 / lam;
             }
-            FT f[4];
-            FT lam = (s == 0 || s == 2) ? llf_prim<FT>(out, po, in, pi, d, f) : llf_prim<FT>(in, pi, out, po, d, f);
-            Geo geo = mesh.geom[e];
-            double half = d == 0 ? 0.5 * geo.w : 0.5 * geo.z;
-            for (int v = 0; v < 4; ++v) S.face[s][t][v] = half * (double)f[v];
             double sg = (s == 1 || s == 3) ? 1.0 : -1.0;
-            double ld = (double)lam;
-            double i2l = (double)(FT(0.5) / lam);
-            S.fbar[s][t] = 0.5 * (in[0] + out[0]) - sg * (out[1 + d] - in[1 + d]) * i2l;
-            S.f2d[s][t] = 2.0 * (s_w[t] * half / 2.0) * ld;
+            S.fbar[s][t] = 0.5 * (S.u[0][n] + out[0]) - sg * (out[1 + d] - S.u[1 + d][n]) * i2l;
         }
         if (!dgmode) {
             for (int k = tid; k < EPB * NIF; k += NT) {
@@ -272,23 +310,24 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 FT lam = la > lb ? la : lb;
                 FT ua[4], ub[4];
                 for (int v = 0; v < 4; ++v) {
-                    ua[v] = F32 ? (FT)S.uf[v][na] : (FT)S.u[v][na];
-                    ub[v] = F32 ? (FT)S.uf[v][nb] : (FT)S.u[v][nb];
+                    if constexpr (F32) { ua[v] = S.uf[v][na]; ub[v] = S.uf[v][nb]; }
+                    else { ua[v] = S.u[v][na]; ub[v] = S.u[v][nb]; }
                 }
                 FT fa[4], fb[4];
                 phys_flux<FT>(ua[1], ua[2], ua[3], pa.p, vna, d, fa);
                 phys_flux<FT>(ub[1], ub[2], ub[3], pb.p, vnb, d, fb);
-                Geo geo = mesh.geom[e];
-                double cc = s_w[r] * (d == 0 ? geo.w : geo.z) / 4.0;
-                FT ccf = (FT)cc;
+                FT cc;
+                if constexpr (F32) cc = s_wf[r] * (d == 0 ? S.qyf : S.qxf);
+                else cc = s_w[r] * (d == 0 ? S.qy : S.qx);
                 for (int v = 0; v < 4; ++v) {
-                    FT fv = ccf * (fa[v] + fb[v]) - ccf * lam * (ub[v] - ua[v]);
-                    S.Ffv[id][v] = fv;
-                    S.Fv[id][v] = (double)fv;
+                    FT fv = cc * (fa[v] + fb[v]) - cc * lam * (ub[v] - ua[v]);
+                    if constexpr (F32) { S.Ffv[id][v] = fv; S.Fv[id][v] = f2d(fv); }
+                    else S.Fv[id][v] = fv;
                 }
-                double ld = (double)lam;
-                double i2l = (double)(FT(0.5) / lam);
-                S.i2d[id] = 2.0 * cc * ld;
+                S.i2d[id] = FT(2) * cc * lam;
+                double i2l;
+                if constexpr (F32) i2l = f2d(0.5f / lam);
+                else i2l = 0.5 / lam;
                 S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * i2l;
             }
         }
@@ -303,12 +342,15 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             FT acc[4] = {FT(0), FT(0), FT(0), FT(0)};
             for (int l = 0; l <= a; ++l)
                 for (int kk = a + 1; kk < NP; ++kk) {
-                    FT sv = (FT)s_S[l][kk];
+                    FT sv;
+                    if constexpr (F32) sv = s_Sf[l][kk];
+                    else sv = s_S[l][kk];
                     int pi = PairTab<NP>::idx(l, kk);
                     for (int v = 0; v < 4; ++v) acc[v] += sv * S.un.pair[d][r][pi][v];
                 }
-            Geo geo = mesh.geom[e];
-            FT wh = (FT)(s_w[r] * (d == 0 ? 0.5 * geo.w : 0.5 * geo.z));
+            FT wh;
+            if constexpr (F32) wh = s_wf[r] * (d == 0 ? S.hyf : S.hxf);
+            else wh = s_w[r] * (d == 0 ? S.hy : S.hx);
             for (int v = 0; v < 4; ++v) S.Fdg[id][v] = wh * acc[v];
         }
         if (!dgmode) {
@@ -317,11 +359,10 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if (e >= mesh.K) continue;
                 SM &S = sm[le];
                 int i = n % NP, j = n / NP;
-                int sim = mesh.sim[e];
-                double dt = stage_dt(A, sim);
-                double dtm = dt * (4.0 * S.invA) * s_iw[i] * s_iw[j];
+                double dtm = S.dt4A * s_iww[n];
                 double L[4] = {0, 0, 0, 0};
-                double lo = S.u[0][n], hi = S.u[0][n], ds = 0.0;
+                long long klo = okey(S.u[0][n]), khi = klo;
+                FT ds = FT(0);
                 uchar4 ftv = mesh.ftype[e];
                 int4 nb4 = mesh.fnbr[e];
                 // x direction: left then right; y: bottom then top
@@ -329,26 +370,29 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     int pos = d == 0 ? i : j, row = d == 0 ? j : i;
                     for (int side = 0; side < 2; ++side) {
                         bool interior = side == 0 ? pos > 0 : pos < N;
+                        double sgn = side == 0 ? 1.0 : -1.0;
+                        long long kb;
                         if (interior) {
                             int id = ifid<NP>(d, row, side == 0 ? pos - 1 : pos);
-                            double sgn = side == 0 ? 1.0 : -1.0;
                             for (int v = 0; v < 4; ++v) L[v] += sgn * S.Fv[id][v];
-                            lo = fmin(lo, S.ibar[id]); hi = fmax(hi, S.ibar[id]);
+                            kb = okey(S.ibar[id]);
+                            klo = kb < klo ? kb : klo; khi = kb > khi ? kb : khi;
                             ds += S.i2d[id];
                         } else {
                             int s = 2 * d + side;
                             int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
                             if (ft == FT_CONF || ft == FT_BND) {
-                                double sgn = side == 0 ? 1.0 : -1.0;
-                                for (int v = 0; v < 4; ++v) L[v] += sgn * (s_w[row] * S.face[s][row][v]);
-                                lo = fmin(lo, S.fbar[s][row]); hi = fmax(hi, S.fbar[s][row]);
+                                for (int v = 0; v < 4; ++v) L[v] += sgn * S.face[s][row][v];
+                                kb = okey(S.fbar[s][row]);
+                                klo = kb < klo ? kb : klo; khi = kb > khi ? kb : khi;
                                 ds += S.f2d[s][row];
                             } else {
                                 int m = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
                                 int q = slot_of<NP>(ft, m, row);
                                 for (int v = 0; v < 4; ++v) L[v] += sl.clo[(size_t)v * sl.S + q];
-                                lo = fmin(lo, sl.rbmin[q]); hi = fmax(hi, sl.rbmax[q]);
-                                ds += sl.dsum[q];
+                                kb = okey(sl.rbmin[q]); klo = kb < klo ? kb : klo;
+                                kb = okey(sl.rbmax[q]); khi = kb > khi ? kb : khi;
+                                ds += to_ft<FT>(sl.dsum[q]);
                             }
                         }
                     }
@@ -359,21 +403,38 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     S.lfv[v][n] = L[v];
                     q[v] = S.u[v][n] + dtm * L[v];
                     S.ufv[v][n] = q[v];
-                    S.ufvf[v][n] = (float)q[v];
+                    S.ufvf[v][n] = d2f(q[v]);
                 }
-                double rmin, rmax;
-                if (A.limiting == 2) { rmin = fmax(lo, A.beta * q[0]); rmax = hi; }
-                else { rmin = A.beta * q[0]; rmax = INFINITY; }
-                if (q[0] < rmin) rmin = q[0];
-                if (q[0] > rmax) rmax = q[0];
-                S.rmin[n] = rmin; S.rmax[n] = rmax;
-                double rp = (g - 1.0) * (q[0] * q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]));   // rho p
+                // bounds (R6): every interval contains rho_FV
+                const long long kq = okey(q[0]);
+                long long kmn, kmx;
+                if (A.limiting == 2) {
+                    long long kb = okey(A.beta * q[0]);
+                    kmn = kb > klo ? kb : klo;
+                    kmx = khi;
+                } else {
+                    kmn = okey(A.beta * q[0]);
+                    kmx = okey(INFINITY);
+                }
+                kmn = kq < kmn ? kq : kmn;
+                kmx = kq > kmx ? kq : kmx;
+                S.rmin[n] = okey_value(kmn);
+                S.rmax[n] = okey_value(kmx);
+                // rho p = (gamma-1) X, X = rho E - |m|^2/2; the scaled pressure
+                // solve: gm = (gamma-1) rho, pm = beta rho p, c0 = gm X - pm rho
+                double X = q[0] * q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]);
+                double rp = (g - 1.0) * X;
                 double gms = (g - 1.0) * q[0], pms = A.beta * rp;
-                double c0 = g_zero(gms, q, pms);
+                double c0 = gms * X - pms * q[0];
                 S.gms[n] = gms; S.pms[n] = pms; S.c0[n] = c0;
-                S.tol[n] = kTol * fabs(q[0]);
-                S.dtmf[n] = (float)dtm; S.gmsf[n] = (float)gms; S.pmsf[n] = (float)pms; S.c0f[n] = (float)c0;
-                if (A.collect && dtm * ds > 1.0) atomicAdd(&A.stats->n_dtx, 1ull);
+                S.dtmf[n] = d2f(dtm); S.gmsf[n] = d2f(gms); S.pmsf[n] = d2f(pms); S.c0f[n] = d2f(c0);
+                if constexpr (F32) {
+                    S.tqf[n] = 1e-14f * fabsf(S.ufvf[0][n]) * (S.idtmf * s_wwf[n]);
+                    if (A.collect && S.dtmf[n] * ds > 1.0f) atomicAdd(&A.stats->n_dtx, 1ull);
+                } else {
+                    S.tol[n] = kTol * fabs(q[0]);
+                    if (A.collect && nn_lt(1.0, dtm * ds)) atomicAdd(&A.stats->n_dtx, 1ull);
+                }
             }
         }
         __syncthreads();
@@ -385,9 +446,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if (e >= mesh.K) continue;
                 SM &S = sm[le];
                 int i = n % NP, j = n / NP;
-                Geo geo = mesh.geom[e];
-                int sim = mesh.sim[e];
-                double mi = geo.z * geo.w / 4.0 * s_w[i] * s_w[j];
+                double mi = S.A4 * s_ww[n];
                 double L[4] = {0, 0, 0, 0};
                 uchar4 ftv = mesh.ftype[e];
                 int4 nb4 = mesh.fnbr[e];
@@ -398,12 +457,17 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         double sgn = side == 0 ? 1.0 : -1.0;
                         if (interior) {
                             int id = ifid<NP>(d, row, side == 0 ? pos - 1 : pos);
-                            for (int v = 0; v < 4; ++v) L[v] += sgn * (double)S.Fdg[id][v];
+                            for (int v = 0; v < 4; ++v) {
+                                double fd;
+                                if constexpr (F32) fd = f2d(S.Fdg[id][v]);
+                                else fd = S.Fdg[id][v];
+                                L[v] += sgn * fd;
+                            }
                         } else {
                             int s = 2 * d + side;
                             int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
                             if (ft == FT_CONF || ft == FT_BND) {
-                                for (int v = 0; v < 4; ++v) L[v] += sgn * (s_w[row] * S.face[s][row][v]);
+                                for (int v = 0; v < 4; ++v) L[v] += sgn * S.face[s][row][v];
                             } else {
                                 int m = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
                                 int q = slot_of<NP>(ft, m, row);
@@ -416,7 +480,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if (A.mode == 0) {
                     for (int v = 0; v < 4; ++v) A.out[v * KN + gi] = L[v] / mi;
                 } else {
-                    double dt = stage_dt(A, sim);
+                    double dt = S.dt;
                     for (int v = 0; v < 4; ++v) {
                         double ut = S.u[v][n] + dt / mi * L[v];
                         double o = ut;
@@ -431,19 +495,31 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
         }
 
         // ---------------- P2b: antidiffusive fluxes A = Fdg - Ffv ------------
+        // In the FP32 form the difference is taken in FP32 and carried to
+        // FP64 exactly; both nodes of the interface use the same value, so the
+        // limited update stays conservative.
         for (int k = tid; k < EPB * NIF; k += NT) {
             int le = k / NIF, id = k - le * NIF;
             if (e0 + le >= mesh.K) continue;
             SM &S = sm[le];
             int d = id / (NP * N), r = (id / N) % NP, a = id % N;
-            for (int v = 0; v < 4; ++v) {
-                FT fd = S.Fdg[id][v], ff = S.Ffv[id][v];
-                S.un.a.Ad[id][v] = (double)fd - S.Fv[id][v];
-                S.un.a.Af[id][v] = (float)(fd - ff);
-            }
             int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
-            double aa = fabs(S.un.a.Ad[id][0]);
-            S.ex[id] = (S.dtm[nl] * aa <= S.tol[nl]) && (S.dtm[nr] * aa <= S.tol[nr]);
+            if constexpr (F32) {
+                for (int v = 0; v < 4; ++v) {
+                    float df = S.Fdg[id][v] - S.Ffv[id][v];
+                    S.un.a.Af[id][v] = df;
+                    S.un.a.Ad[id][v] = f2d(df);
+                }
+                S.ex[id] = fabsf(S.un.a.Af[id][0]) <= fminf(S.tqf[nl], S.tqf[nr]);
+            } else {
+                for (int v = 0; v < 4; ++v) {
+                    double dd = S.Fdg[id][v] - S.Fv[id][v];
+                    S.un.a.Ad[id][v] = dd;
+                    S.un.a.Af[id][v] = d2f(dd);
+                }
+                double aa = fabs(S.un.a.Ad[id][0]);
+                S.ex[id] = !nn_lt(S.tol[nl], S.dtm[nl] * aa) && !nn_lt(S.tol[nr], S.dtm[nr] * aa);
+            }
         }
         __syncthreads();
 
@@ -466,17 +542,18 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if (S.ex[id]) continue;
                     double Ar = S.un.a.Ad[id][0];
                     double G = side == 0 ? Ar : -Ar;
-                    Pp += G > 0 ? G : 0.0;
-                    Pm += G < 0 ? G : 0.0;
+                    // one add into the sum that matches the sign of G
+                    const bool pos_g = __double_as_longlong(G) > 0;
+                    double acc = pos_g ? Pp : Pm;
+                    acc += G;
+                    if (pos_g) Pp = acc; else Pm = acc;
                 }
             }
             double rfv = S.ufv[0][n];
-            double qp = S.rmax[n] - rfv, qm = S.rmin[n] - rfv;   // Q / (m/dt)
-            double pp = dtm * Pp, pmm = dtm * Pm;
-            double Rp = (pp > qp) ? qp / pp : 1.0;
-            double Rm = (pmm < qm) ? qm / pmm : 1.0;
-            S.Rp[n] = Rp < 0.0 ? 0.0 : Rp;
-            S.Rm[n] = Rm < 0.0 ? 0.0 : Rm;
+            double qp = S.rmax[n] - rfv, qm = S.rmin[n] - rfv;   // Q / (m/dt): qp >= 0 >= qm
+            double pp = dtm * Pp, pmm = dtm * Pm;                // pp >= 0 >= pmm
+            S.Rp[n] = nn_lt(qp, pp) ? qp / pp : 1.0;
+            S.Rm[n] = nn_lt(qm, pmm) ? qm / pmm : 1.0;
         }
         __syncthreads();
 
@@ -489,17 +566,17 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
             double Ar = S.un.a.Ad[id][0];
             double lr = S.ex[id] ? 1.0
-                           : (-Ar > 0.0) ? fmin(S.Rp[nl], S.Rm[nr]) : fmin(S.Rm[nl], S.Rp[nr]);
+                                 : dneg(Ar) ? nn_min(S.Rp[nl], S.Rm[nr]) : nn_min(S.Rm[nl], S.Rp[nr]);
             double th = lr;
             // left end point: Gamma-scaled increment -4 dt/m A; right: +4 dt/m A
-            for (int side = 0; side < 2 && th > 0.0; ++side) {
+            for (int side = 0; side < 2 && __double_as_longlong(th) > 0; ++side) {
                 int nd = side == 0 ? nl : nr;
                 float sgf = side == 0 ? -4.0f : 4.0f;
                 float u0f[4], af[4];
                 float sdf = sgf * S.dtmf[nd];
                 for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.un.a.Af[id][v]; }
-                if (admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], (float)th) && S.c0[nd] > 0.0 &&
-                    S.ufv[0][nd] > 0.0)
+                // a certified FP32 yes implies c0 > 0 and rho_FV > 0
+                if (admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], d2f(th)))
                     continue;   // the whole interval [0, th] is admissible
                 double u0[4], av[4];
                 double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
@@ -519,8 +596,6 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if (e >= mesh.K) continue;
                 SM &S = sm[le];
                 int i = n % NP, j = n / NP;
-                Geo geo = mesh.geom[e];
-                double mi = geo.z * geo.w / 4.0 * s_w[i] * s_w[j];
                 double dtm = S.dtm[n];
                 double sacc[4] = {0, 0, 0, 0}, lmin = 1.0;
                 for (int d = 0; d < 2; ++d) {
@@ -529,13 +604,13 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         int id = ifid<NP>(d, row, pos - 1);
                         double l = S.ell[id];
                         for (int v = 0; v < 4; ++v) sacc[v] += l * S.un.a.Ad[id][v];
-                        lmin = fmin(lmin, l);
+                        lmin = nn_min(lmin, l);
                     }
                     if (pos < N) {
                         int id = ifid<NP>(d, row, pos);
                         double l = S.ell[id];
                         for (int v = 0; v < 4; ++v) sacc[v] -= l * S.un.a.Ad[id][v];
-                        lmin = fmin(lmin, l);
+                        lmin = nn_min(lmin, l);
                     }
                 }
                 double uvol[4], resv[4] = {0, 0, 0, 0};
@@ -552,20 +627,27 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if (i == N && ftv.y >= FT_MLARGE) sides[nmort++] = 1;
                 if (j == 0 && ftv.z >= FT_MLARGE) sides[nmort++] = 2;
                 if (j == N && ftv.w >= FT_MLARGE) sides[nmort++] = 3;
-                for (int c = 0; c < nmort; ++c) {
-                    int s = sides[c];
-                    int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
-                    int m = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
-                    int q = slot_of<NP>(ft, m, s < 2 ? j : i);
-                    for (int v = 0; v < 4; ++v) {
-                        sl.uvol[(size_t)v * sl.S + q] = uvol[v];
-                        // rhs mode keeps the mass-weighted residual, step mode u^n
-                        sl.un[(size_t)v * sl.S + q] = A.mode == 0 ? resv[v] : (A.comb != 0 ? A.un[v * KN + gi] : 0.0);
+                if (nmort) {
+                    const double mi = S.A4 * s_ww[n];
+                    const double pmin_n = S.pms[n] / S.ufv[0][n];
+                    const double tol_n = kTol * fabs(S.ufv[0][n]);
+                    for (int c = 0; c < nmort; ++c) {
+                        int s = sides[c];
+                        int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
+                        int m = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
+                        int q = slot_of<NP>(ft, m, s < 2 ? j : i);
+                        for (int v = 0; v < 4; ++v) {
+                            sl.uvol[(size_t)v * sl.S + q] = uvol[v];
+                            // rhs mode keeps the mass-weighted residual, step mode u^n
+                            sl.un[(size_t)v * sl.S + q] =
+                                A.mode == 0 ? resv[v] : (A.comb != 0 ? A.un[v * KN + gi] : 0.0);
+                        }
+                        sl.rmin[q] = S.rmin[n]; sl.rmax[q] = S.rmax[n]; sl.pmin[q] = pmin_n;
+                        sl.tol[q] = tol_n; sl.mass[q] = mi; sl.nmort[q] = (float)nmort;
                     }
-                    sl.rmin[q] = S.rmin[n]; sl.rmax[q] = S.rmax[n]; sl.pmin[q] = S.pms[n] / S.ufv[0][n];
-                    sl.tol[q] = S.tol[n]; sl.mass[q] = mi; sl.nmort[q] = (float)nmort;
                 }
                 if (A.mode == 0) {
+                    const double mi = S.A4 * s_ww[n];
                     for (int v = 0; v < 4; ++v) A.out[v * KN + gi] = resv[v] / mi;
                 } else {
                     for (int v = 0; v < 4; ++v) {
@@ -576,19 +658,20 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     }
                 }
                 if (A.collect) {
-                    st_am += mi * (1.0 - lmin);
-                    st_m += mi;
-                    st_act += lmin < 1.0;
+                    if (n == 0) st_m += 4.0 * S.A4;   // element area = sum of its node masses
+                    const bool act = nn_lt(lmin, 1.0);
+                    if (act) { st_am += S.A4 * s_ww[n] * (1.0 - lmin); st_act++; }
                     if (nmort == 0) {
-                        // rho p = (gamma-1)(rho E - |m|^2/2): checks without division
-                        double rp = (g - 1.0) * (uvol[0] * uvol[3] - 0.5 * (uvol[1] * uvol[1] + uvol[2] * uvol[2]));
+                        // rho p = (gamma-1)(rho E - |m|^2/2): checks without division;
                         // p >= p_min  <=>  rho p rho_FV >= (p_min rho_FV) rho
-                        if (uvol[0] < S.rmin[n] - kViolTol * fabs(S.rmin[n]) ||
-                            uvol[0] > S.rmax[n] + kViolTol * fabs(S.rmax[n])) st_vr++;
-                        if (rp * S.ufv[0][n] < S.pms[n] * (1.0 - kViolTol) * uvol[0]) st_vp++;
-                        if (!(uvol[0] > 0.0) || !(rp > 0.0)) st_np++;
-                        st_rmin = fmin(st_rmin, uvol[0]);
-                        if (lmin < 1.0) st_pmin = fmin(st_pmin, rp / uvol[0]);
+                        double rp = (g - 1.0) * (uvol[0] * uvol[3] - 0.5 * (uvol[1] * uvol[1] + uvol[2] * uvol[2]));
+                        const double rmn = S.rmin[n], rmx = S.rmax[n];
+                        if (dlt(uvol[0], rmn - kViolTol * fabs(rmn)) || dlt(rmx + kViolTol * fabs(rmx), uvol[0]))
+                            st_vr++;
+                        if (dlt(rp * S.ufv[0][n], S.pms[n] * (1.0 - kViolTol) * uvol[0])) st_vp++;
+                        if (!dpos(uvol[0]) || !dpos(rp)) st_np++;
+                        st_rmin = dmin(st_rmin, uvol[0]);
+                        if (act) st_pmin = dmin(st_pmin, rp / uvol[0]);
                     }
                 }
             }
