@@ -39,6 +39,13 @@ struct Ops {
     double wt[NPMAX][2 * NPMAX];     // local mortar weights (reference units)
     double I[2 * NPMAX][NPMAX];      // interpolation large -> small-face nodes
     double P[NPMAX][2 * NPMAX];      // projection small-face fluxes -> large
+    // nonzero local weights as a pair list (large node k, small-face node r),
+    // k-major with r ascending, and per mortar slot (large nodes first, then
+    // the small-face nodes) the pairs that touch it, in the same order
+    int npair;
+    int pk[3 * NPMAX], pr[3 * NPMAX];
+    int slot_n[3 * NPMAX];
+    int slot_p[3 * NPMAX][2 * NPMAX];
 };
 
 // Per simulation: boundary data (ghost states as conserved variables).
@@ -91,8 +98,21 @@ struct SlotsDev {
 // point functions
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ double pressure_d(double g, double r, double m1, double m2, double E) {
-    return (g - 1.0) * (E - 0.5 * (m1 * m1 + m2 * m2) / r);
+// Ideal-gas constants, formed once on the host: gamma, gamma - 1,
+// 1 / (gamma - 1) and their FP32 copies.
+struct Gas {
+    double g, gm1, ginv1;
+    float gf, gm1f, ginv1f;
+};
+inline Gas make_gas(double gamma) {
+    Gas G;
+    G.g = gamma; G.gm1 = gamma - 1.0; G.ginv1 = 1.0 / (gamma - 1.0);
+    G.gf = (float)G.g; G.gm1f = (float)G.gm1; G.ginv1f = (float)G.ginv1;
+    return G;
+}
+
+__device__ __forceinline__ double pressure_d(double gm1, double r, double m1, double m2, double E) {
+    return gm1 * (E - 0.5 * (m1 * m1 + m2 * m2) / r);
 }
 
 // Node primitives in the flux type.
@@ -170,12 +190,13 @@ __device__ __forceinline__ void phys_flux(FT m1, FT m2, FT E, FT p, FT vn, int d
 // sound speed use explicitly rounded operations so that every element that
 // forms them for the same node gets the same bits.
 template <typename FT>
-__device__ __forceinline__ Prim<FT> make_prim(double g, double r, double m1, double m2, double E, bool full) {
+__device__ __forceinline__ Prim<FT> make_prim(const Gas &G, double r, double m1, double m2, double E, bool full) {
+    const double g = G.g;
     Prim<FT> q;
     double ri = __drcp_rn(r);
     double v1 = __dmul_rn(m1, ri), v2 = __dmul_rn(m2, ri);
     double ke = __dmul_rn(0.5, __dadd_rn(__dmul_rn(m1, v1), __dmul_rn(m2, v2)));
-    double p = __dmul_rn(g - 1.0, __dadd_rn(E, -ke));
+    double p = __dmul_rn(G.gm1, __dadd_rn(E, -ke));
     q.rho = (FT)r; q.v1 = (FT)v1; q.v2 = (FT)v2; q.p = (FT)p; q.E = (FT)E;
     q.lr = q.lb = FT(0);
     if (sizeof(FT) == 8) {
@@ -190,7 +211,7 @@ __device__ __forceinline__ Prim<FT> make_prim(double g, double r, double m1, dou
         }
     } else {
         float pf = (float)p, rf = (float)r;
-        q.c = (FT)__fsqrt_rn(__fdiv_rn(__fmul_rn((float)g, pf), rf));
+        q.c = (FT)__fsqrt_rn(__fdiv_rn(__fmul_rn(G.gf, pf), rf));
         q.beta = full ? (FT)__fdiv_rn(rf, pf) : FT(0);
     }
     return q;
@@ -201,7 +222,7 @@ __device__ __forceinline__ Prim<FT> make_prim(double g, double r, double m1, dou
 // 1e-6, positive for sure); otherwise in FP64 as above. The state is rounded
 // to FP32 on the integer pipe (d2f); the same function serves every element
 // that reads the node, so they all get the same bits.
-__device__ __forceinline__ Prim<float> make_prim_f32(double g, double r, double m1, double m2, double E, bool full,
+__device__ __forceinline__ Prim<float> make_prim_f32(const Gas &G, double r, double m1, double m2, double E, bool full,
                                                      float &m1o, float &m2o) {
     float rf = d2f(r), m1f = d2f(m1), m2f = d2f(m2), Ef = d2f(E);
     float rif = __frcp_rn(rf);
@@ -211,12 +232,12 @@ __device__ __forceinline__ Prim<float> make_prim_f32(double g, double r, double 
     Prim<float> q;
     if (rf > 0.0f && Ef > 0.0f && pef >= 0.5f * Ef) {
         q.rho = rf; q.v1 = v1; q.v2 = v2; q.E = Ef;
-        q.p = __fmul_rn(d2f(g - 1.0), pef);
+        q.p = __fmul_rn(G.gm1f, pef);
         q.lr = q.lb = 0.0f;
-        q.c = __fsqrt_rn(__fmul_rn(__fmul_rn(d2f(g), q.p), rif));
+        q.c = __fsqrt_rn(__fmul_rn(__fmul_rn(G.gf, q.p), rif));
         q.beta = full ? __fmul_rn(rf, __frcp_rn(q.p)) : 0.0f;
     } else {
-        q = make_prim<float>(g, r, m1, m2, E, full);
+        q = make_prim<float>(G, r, m1, m2, E, full);
     }
     m1o = m1f;
     m2o = m2f;
@@ -246,22 +267,6 @@ __device__ __forceinline__ FT llf_prim(const ST uL[4], const Prim<FT> &a, const 
     phys_flux<FT>(ul[1], ul[2], ul[3], a.p, vna, d, fa);
     phys_flux<FT>(ur[1], ur[2], ur[3], b.p, vnb, d, fb);
     for (int v = 0; v < 4; ++v) f[v] = FT(0.5) * (fa[v] + fb[v]) - FT(0.5) * lam * (ur[v] - ul[v]);
-    return lam;
-}
-
-// Local Lax-Friedrichs flux along axis d with the Davis wave speed (R3);
-// returns lambda.
-template <typename FT>
-__device__ __forceinline__ FT llf(const double uL[4], const double uR[4], double g, int d, FT f[4]) {
-    Prim<FT> a = make_prim<FT>(g, uL[0], uL[1], uL[2], uL[3], false);
-    Prim<FT> b = make_prim<FT>(g, uR[0], uR[1], uR[2], uR[3], false);
-    FT vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
-    FT la = fabs(vna) + a.c, lb = fabs(vnb) + b.c;
-    FT lam = la > lb ? la : lb;
-    FT fa[4], fb[4];
-    phys_flux<FT>((FT)uL[1], (FT)uL[2], (FT)uL[3], a.p, vna, d, fa);
-    phys_flux<FT>((FT)uR[1], (FT)uR[2], (FT)uR[3], b.p, vnb, d, fb);
-    for (int v = 0; v < 4; ++v) f[v] = FT(0.5) * (fa[v] + fb[v]) - FT(0.5) * lam * ((FT)uR[v] - (FT)uL[v]);
     return lam;
 }
 
@@ -312,8 +317,8 @@ __device__ __forceinline__ bool admissible_f32(double gm, const double u0[4], co
 // p >= p_min; the admissible set is convex so the feasible thetas form an
 // interval [0, theta*]. g(theta) = gm (rho E - |m|^2/2) - pm rho with
 // (gm, pm) = (gamma-1, p_min) or both scaled by the same positive factor
-// (see g_zero); c0 = g(0). p_min = pm / (gm / (gamma - 1)).
-__device__ __forceinline__ double theta_max(double g, const double u0[4], const double a[4], double gm, double pm,
+// (see g_zero); c0 = g(0); gm1 = gamma - 1, so p_min = pm gm1 / gm.
+__device__ __forceinline__ double theta_max(double gm1, const double u0[4], const double a[4], double gm, double pm,
                                             double c0, double hi) {
     if (!(hi > 0.0)) return 0.0;
     if (!(c0 > 0.0) || !(u0[0] > 0.0)) return 0.0;
@@ -342,10 +347,10 @@ __device__ __forceinline__ double theta_max(double g, const double u0[4], const 
         if (th >= tr) th = 0.5 * tr;
     }
     if (!(th > 0.0)) return 0.0;
-    const double pmin = pm * (g - 1.0) / gm;
+    const double pmin = pm * gm1 / gm;
     for (int it = 0; it < 4; ++it) {
         double v0 = u0[0] + th * a[0], v1 = u0[1] + th * a[1], v2 = u0[2] + th * a[2], v3 = u0[3] + th * a[3];
-        if (v0 > 0.0 && pressure_d(g, v0, v1, v2, v3) >= pmin * (1.0 - 1e-13)) return th;
+        if (v0 > 0.0 && pressure_d(gm1, v0, v1, v2, v3) >= pmin * (1.0 - 1e-13)) return th;
         th *= 0.5;
     }
     return 0.0;

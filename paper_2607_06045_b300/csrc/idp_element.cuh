@@ -32,7 +32,8 @@ struct StageArgs {
     double t;             // rhs mode time
     const double *t_sim;  // step mode per-sim time
     double tstage;        // step mode: stage time = t_sim + tstage * dt
-    double beta, gamma;
+    double beta;
+    Gas gas;
     const Ops *ops;
     unsigned *status;
     StatsAcc *stats;
@@ -54,7 +55,8 @@ struct ElemSm {
     double lfv[4][NN];
     double face[4][NP][4];   // (w_t |face|/2) * numerical flux along +x/+y (conforming, boundary)
     double outs[4][NP][4];   // outside state (conforming neighbour or ghost)
-    double fbar[4][NP];      // bar-state density across the face
+    double fbar[4][NP];      // bar-state density across the face (mortar sides: the minimum)
+    double fbar2[4][NP];     // mortar sides: the maximum (conforming: = fbar)
     FT f2d[4][NP];           // 2 d_ij across the face (time-step check)
     FT Fdg[NIF][4];          // mass-weighted high-order subcell flux w_r * fhat (flux type)
     FT Ffv[F32 ? NIF : 1][4];  // FP32 form: the low-order subcell flux in FP32
@@ -120,30 +122,45 @@ __device__ __forceinline__ int slot_of(int ft, int m, int t) {
     return m * 3 * NP + role * NP + t;
 }
 
-__device__ __forceinline__ void block_stats(const StageArgs &A, double am, double mm, unsigned long long nact,
-                                            unsigned long long nvr, unsigned long long nvp, unsigned long long nnp,
-                                            unsigned long long ndx, double rmin_, double pmin_) {
-    // warp reduction then one atomic per warp
+// Per-warp reduction of the limiter statistics, then one atomic per warp and
+// field. Counts reduce as integers, the alpha sum in FP32 (a diagnostic
+// mean), the minimum density on the integer order of positive doubles, and
+// the minimum pressure over limited nodes as a ratio rho p / rho compared
+// without division; FP64 arithmetic only runs in warps that hold a limited
+// node.
+__device__ __forceinline__ void block_stats(const StageArgs &A, float am, unsigned nact, unsigned nvr, unsigned nvp,
+                                            unsigned nnp, double rmin_, double pn, double pd) {
+    const unsigned FULL = 0xffffffffu;
+    nact = __reduce_add_sync(FULL, nact);
+    nvr = __reduce_add_sync(FULL, nvr);
+    nvp = __reduce_add_sync(FULL, nvp);
+    nnp = __reduce_add_sync(FULL, nnp);
+    for (int o = 16; o > 0; o >>= 1) am += __shfl_down_sync(FULL, am, o);
+    // positive doubles (and +inf) order like their bits
+    unsigned long long rk = dbits(rmin_);
     for (int o = 16; o > 0; o >>= 1) {
-        am += __shfl_down_sync(0xffffffffu, am, o);
-        mm += __shfl_down_sync(0xffffffffu, mm, o);
-        nact += __shfl_down_sync(0xffffffffu, nact, o);
-        nvr += __shfl_down_sync(0xffffffffu, nvr, o);
-        nvp += __shfl_down_sync(0xffffffffu, nvp, o);
-        nnp += __shfl_down_sync(0xffffffffu, nnp, o);
-        ndx += __shfl_down_sync(0xffffffffu, ndx, o);
-        rmin_ = fmin(rmin_, __shfl_down_sync(0xffffffffu, rmin_, o));
-        pmin_ = fmin(pmin_, __shfl_down_sync(0xffffffffu, pmin_, o));
+        unsigned long long ok = __shfl_down_sync(FULL, rk, o);
+        rk = ok < rk ? ok : rk;
+    }
+    const bool anyp = __any_sync(FULL, __double_as_longlong(pd) > 0);
+    if (anyp) {
+        for (int o = 16; o > 0; o >>= 1) {
+            double qn = __shfl_down_sync(FULL, pn, o), qd = __shfl_down_sync(FULL, pd, o);
+            const bool have = __double_as_longlong(pd) > 0, other = __double_as_longlong(qd) > 0;
+            if (other && (!have || dlt(qn * pd, pn * qd))) { pn = qn; pd = qd; }
+        }
     }
     if ((threadIdx.x & 31) == 0) {
-        if (mm > 0.0) { atomicAdd(&A.stats->alpha_vol_m, am); atomicAdd(&A.stats->mass, mm); }
-        if (nact) atomicAdd(&A.stats->n_vol, nact);
-        if (nvr) atomicAdd(&A.stats->n_vrho, nvr);
-        if (nvp) atomicAdd(&A.stats->n_vp, nvp);
-        if (nnp) atomicAdd(&A.stats->n_nonpos, nnp);
-        if (ndx) atomicAdd(&A.stats->n_dtx, ndx);
-        if (rmin_ > 0.0 && rmin_ < INFINITY) atomicMin(&A.stats->min_rho_bits, dbits(rmin_));
-        if (pmin_ > 0.0 && pmin_ < INFINITY) atomicMin(&A.stats->min_p_bits, dbits(pmin_));
+        if (am > 0.0f) atomicAdd(&A.stats->alpha_vol_m, (double)am);
+        if (nact) atomicAdd(&A.stats->n_vol, (unsigned long long)nact);
+        if (nvr) atomicAdd(&A.stats->n_vrho, (unsigned long long)nvr);
+        if (nvp) atomicAdd(&A.stats->n_vp, (unsigned long long)nvp);
+        if (nnp) atomicAdd(&A.stats->n_nonpos, (unsigned long long)nnp);
+        if (rk > 0ull && rk < 0x7FF0000000000000ull) atomicMin(&A.stats->min_rho_bits, rk);
+        if (anyp && __double_as_longlong(pd) > 0) {
+            double pmin_ = pn / pd;
+            if (dpos(pmin_)) atomicMin(&A.stats->min_p_bits, dbits(pmin_));
+        }
     }
 }
 
@@ -176,8 +193,11 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
         s_iww[tid] = A.ops->iw[i] * A.ops->iw[j];
         s_wwf[tid] = d2f(s_ww[tid]);
     }
-    const double g = A.gamma;
-    const FT ginv1 = to_ft<FT>(1.0 / (g - 1.0));
+    const Gas &G = A.gas;
+    const double gm1 = G.gm1;
+    FT ginv1;
+    if constexpr (F32) ginv1 = G.ginv1f;
+    else ginv1 = G.ginv1;
     const size_t KN = (size_t)mesh.K * NN;
     const bool limited = A.limiting > 0;
     const bool dgmode = (A.mode == 0 && A.dt == 0.0) || !limited;
@@ -195,11 +215,11 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             bool okp;
             if constexpr (F32) {
                 float m1f, m2f;
-                q = make_prim_f32(g, r, m1, m2, E, true, m1f, m2f);
+                q = make_prim_f32(G, r, m1, m2, E, true, m1f, m2f);
                 S.uf[0][n] = q.rho; S.uf[1][n] = m1f; S.uf[2][n] = m2f; S.uf[3][n] = q.E;
                 okp = q.p > 0.0f;
             } else {
-                q = make_prim<FT>(g, r, m1, m2, E, true);
+                q = make_prim<FT>(G, r, m1, m2, E, true);
                 okp = dpos(q.p);
             }
             if (!(okp && dpos(r) && dfinite(m1) && dfinite(m2) && dfinite(E))) atomicOr(A.status, ST_BAD_INPUT);
@@ -264,8 +284,24 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             if (e >= mesh.K) continue;
             uchar4 ftv = mesh.ftype[e];
             int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
-            if (ft != FT_CONF && ft != FT_BND) continue;
             SM &S = sm[le];
+            if (ft != FT_CONF && ft != FT_BND) {
+                // mortar side: its contribution to m du/dt (high-order in the
+                // unlimited residual, else low-order), bar-state range and 2d
+                // sum, stored with the sign convention of the conforming faces
+                int4 nb4 = mesh.fnbr[e];
+                int m = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
+                int q = slot_of<NP>(ft, m, t);
+                const double *src = dgmode ? sl.chi : sl.clo;
+                const double sgn = (s & 1) ? -1.0 : 1.0;
+                for (int v = 0; v < 4; ++v) S.face[s][t][v] = sgn * src[(size_t)v * sl.S + q];
+                if (!dgmode) {
+                    S.fbar[s][t] = sl.rbmin[q];
+                    S.fbar2[s][t] = sl.rbmax[q];
+                    S.f2d[s][t] = to_ft<FT>(sl.dsum[q]);
+                }
+                continue;
+            }
             int d = s >> 1, n = face_node<NP>(s, t);
             const double *out = S.outs[s][t];
             Prim<FT> pi = load_prim<NP, FT>(S, n);
@@ -275,7 +311,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             // the same bits
             if constexpr (F32) {
                 float m1f, m2f;
-                Prim<float> po = make_prim_f32(g, out[0], out[1], out[2], out[3], false, m1f, m2f);
+                Prim<float> po = make_prim_f32(G, out[0], out[1], out[2], out[3], false, m1f, m2f);
                 float ui[4] = {S.uf[0][n], S.uf[1][n], S.uf[2][n], S.uf[3][n]};
                 float uo[4] = {po.rho, m1f, m2f, po.E};
                 lam = (s == 0 || s == 2) ? llf_prim<float, float>(uo, po, ui, pi, d, f)
@@ -285,7 +321,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 S.f2d[s][t] = whf * lam;
                 i2l = f2d(0.5f / lam);
             } else {
-                Prim<FT> po = make_prim<FT>(g, out[0], out[1], out[2], out[3], false);
+                Prim<FT> po = make_prim<FT>(G, out[0], out[1], out[2], out[3], false);
                 double ui[4] = {S.u[0][n], S.u[1][n], S.u[2][n], S.u[3][n]};
                 lam = (s == 0 || s == 2) ? llf_prim<FT, double>(out, po, ui, pi, d, f)
                                          : llf_prim<FT, double>(ui, pi, out, po, d, f);
@@ -295,7 +331,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 i2l = 0.5 / lam;
             }
             double sg = (s == 1 || s == 3) ? 1.0 : -1.0;
-            S.fbar[s][t] = 0.5 * (S.u[0][n] + out[0]) - sg * (out[1 + d] - S.u[1 + d][n]) * i2l;
+            double fb = 0.5 * (S.u[0][n] + out[0]) - sg * (out[1 + d] - S.u[1 + d][n]) * i2l;
+            S.fbar[s][t] = fb;
+            S.fbar2[s][t] = fb;
         }
         if (!dgmode) {
             for (int k = tid; k < EPB * NIF; k += NT) {
@@ -363,38 +401,31 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double L[4] = {0, 0, 0, 0};
                 long long klo = okey(S.u[0][n]), khi = klo;
                 FT ds = FT(0);
-                uchar4 ftv = mesh.ftype[e];
-                int4 nb4 = mesh.fnbr[e];
-                // x direction: left then right; y: bottom then top
+                // x direction: left then right; y: bottom then top. Interior
+                // subcell interfaces and element faces (conforming, boundary or
+                // mortar) are read through one path so that the warp does not
+                // split between them.
+#pragma unroll
                 for (int d = 0; d < 2; ++d) {
                     int pos = d == 0 ? i : j, row = d == 0 ? j : i;
+#pragma unroll
                     for (int side = 0; side < 2; ++side) {
-                        bool interior = side == 0 ? pos > 0 : pos < N;
-                        double sgn = side == 0 ? 1.0 : -1.0;
-                        long long kb;
-                        if (interior) {
-                            int id = ifid<NP>(d, row, side == 0 ? pos - 1 : pos);
-                            for (int v = 0; v < 4; ++v) L[v] += sgn * S.Fv[id][v];
-                            kb = okey(S.ibar[id]);
-                            klo = kb < klo ? kb : klo; khi = kb > khi ? kb : khi;
-                            ds += S.i2d[id];
-                        } else {
-                            int s = 2 * d + side;
-                            int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
-                            if (ft == FT_CONF || ft == FT_BND) {
-                                for (int v = 0; v < 4; ++v) L[v] += sgn * S.face[s][row][v];
-                                kb = okey(S.fbar[s][row]);
-                                klo = kb < klo ? kb : klo; khi = kb > khi ? kb : khi;
-                                ds += S.f2d[s][row];
-                            } else {
-                                int m = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
-                                int q = slot_of<NP>(ft, m, row);
-                                for (int v = 0; v < 4; ++v) L[v] += sl.clo[(size_t)v * sl.S + q];
-                                kb = okey(sl.rbmin[q]); klo = kb < klo ? kb : klo;
-                                kb = okey(sl.rbmax[q]); khi = kb > khi ? kb : khi;
-                                ds += to_ft<FT>(sl.dsum[q]);
-                            }
+                        const bool interior = side == 0 ? pos > 0 : pos < N;
+                        const int id = ifid<NP>(d, row, side == 0 ? (interior ? pos - 1 : 0) : (interior ? pos : 0));
+                        const int s = 2 * d + side;
+                        const double *fl = interior ? S.Fv[id] : S.face[s][row];
+                        const double blo = interior ? S.ibar[id] : S.fbar[s][row];
+                        const double bhi = interior ? S.ibar[id] : S.fbar2[s][row];
+                        const FT dsv = interior ? S.i2d[id] : S.f2d[s][row];
+                        for (int v = 0; v < 4; ++v) {
+                            if (side == 0) L[v] += fl[v];
+                            else L[v] -= fl[v];
                         }
+                        long long kb = okey(blo);
+                        klo = kb < klo ? kb : klo;
+                        kb = okey(bhi);
+                        khi = kb > khi ? kb : khi;
+                        ds += dsv;
                     }
                 }
                 double q[4];
@@ -423,8 +454,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 // rho p = (gamma-1) X, X = rho E - |m|^2/2; the scaled pressure
                 // solve: gm = (gamma-1) rho, pm = beta rho p, c0 = gm X - pm rho
                 double X = q[0] * q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]);
-                double rp = (g - 1.0) * X;
-                double gms = (g - 1.0) * q[0], pms = A.beta * rp;
+                double rp = gm1 * X;
+                double gms = gm1 * q[0], pms = A.beta * rp;
                 double c0 = gms * X - pms * q[0];
                 S.gms[n] = gms; S.pms[n] = pms; S.c0[n] = c0;
                 S.dtmf[n] = d2f(dtm); S.gmsf[n] = d2f(gms); S.pmsf[n] = d2f(pms); S.c0f[n] = d2f(c0);
@@ -446,43 +477,36 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if (e >= mesh.K) continue;
                 SM &S = sm[le];
                 int i = n % NP, j = n / NP;
-                double mi = S.A4 * s_ww[n];
                 double L[4] = {0, 0, 0, 0};
-                uchar4 ftv = mesh.ftype[e];
-                int4 nb4 = mesh.fnbr[e];
+#pragma unroll
                 for (int d = 0; d < 2; ++d) {
                     int pos = d == 0 ? i : j, row = d == 0 ? j : i;
+#pragma unroll
                     for (int side = 0; side < 2; ++side) {
-                        bool interior = side == 0 ? pos > 0 : pos < N;
-                        double sgn = side == 0 ? 1.0 : -1.0;
-                        if (interior) {
-                            int id = ifid<NP>(d, row, side == 0 ? pos - 1 : pos);
-                            for (int v = 0; v < 4; ++v) {
-                                double fd;
+                        const bool interior = side == 0 ? pos > 0 : pos < N;
+                        const int id = ifid<NP>(d, row, side == 0 ? (interior ? pos - 1 : 0) : (interior ? pos : 0));
+                        const int s = 2 * d + side;
+                        for (int v = 0; v < 4; ++v) {
+                            double fd;
+                            if (interior) {
                                 if constexpr (F32) fd = f2d(S.Fdg[id][v]);
                                 else fd = S.Fdg[id][v];
-                                L[v] += sgn * fd;
-                            }
-                        } else {
-                            int s = 2 * d + side;
-                            int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
-                            if (ft == FT_CONF || ft == FT_BND) {
-                                for (int v = 0; v < 4; ++v) L[v] += sgn * S.face[s][row][v];
                             } else {
-                                int m = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
-                                int q = slot_of<NP>(ft, m, row);
-                                for (int v = 0; v < 4; ++v) L[v] += sl.chi[(size_t)v * sl.S + q];
+                                fd = S.face[s][row][v];
                             }
+                            if (side == 0) L[v] += fd;
+                            else L[v] -= fd;
                         }
                     }
                 }
                 size_t gi = (size_t)e * NN + n;
                 if (A.mode == 0) {
-                    for (int v = 0; v < 4; ++v) A.out[v * KN + gi] = L[v] / mi;
+                    const double imi = (4.0 * S.invA) * s_iww[n];   // 1 / m_i
+                    for (int v = 0; v < 4; ++v) A.out[v * KN + gi] = L[v] * imi;
                 } else {
-                    double dt = S.dt;
+                    const double dtm = S.dt4A * s_iww[n];           // dt / m_i
                     for (int v = 0; v < 4; ++v) {
-                        double ut = S.u[v][n] + dt / mi * L[v];
+                        double ut = S.u[v][n] + dtm * L[v];
                         double o = ut;
                         if (A.comb == 1) o = 0.75 * A.un[v * KN + gi] + 0.25 * ut;
                         else if (A.comb == 2) o = A.un[v * KN + gi] * (1.0 / 3.0) + 2.0 / 3.0 * ut;
@@ -552,8 +576,10 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             double rfv = S.ufv[0][n];
             double qp = S.rmax[n] - rfv, qm = S.rmin[n] - rfv;   // Q / (m/dt): qp >= 0 >= qm
             double pp = dtm * Pp, pmm = dtm * Pm;                // pp >= 0 >= pmm
-            S.Rp[n] = nn_lt(qp, pp) ? qp / pp : 1.0;
-            S.Rm[n] = nn_lt(qm, pmm) ? qm / pmm : 1.0;
+            // R = Q / P where P exceeds Q; Q = 0 (a node on its bound) gives 0
+            // without a division
+            S.Rp[n] = nn_lt(qp, pp) ? (__double_as_longlong(qp) > 0 ? qp / pp : 0.0) : 1.0;
+            S.Rm[n] = nn_lt(qm, pmm) ? (dneg(qm) ? qm / pmm : 0.0) : 1.0;
         }
         __syncthreads();
 
@@ -581,7 +607,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double u0[4], av[4];
                 double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
                 for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.un.a.Ad[id][v]; }
-                th = theta_max(g, u0, av, S.gms[nd], S.pms[nd], S.c0[nd], th);
+                th = theta_max(gm1, u0, av, S.gms[nd], S.pms[nd], S.c0[nd], th);
             }
             S.ell[id] = th;   // min over both end points (each searched below the previous)
         }
@@ -589,8 +615,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
 
         // ---------------- P5: blend, outputs, mortar hand-off, stats --------
         {
-            double st_am = 0.0, st_m = 0.0, st_rmin = INFINITY, st_pmin = INFINITY;
-            unsigned long long st_act = 0, st_vr = 0, st_vp = 0, st_np = 0;
+            float st_am = 0.0f;
+            double st_rmin = INFINITY, st_pn = 0.0, st_pd = 0.0;
+            unsigned st_act = 0, st_vr = 0, st_vp = 0, st_np = 0;
             for (int k = tid; k < EPB * NN; k += NT) {
                 int le = k / NN, n = k - le * NN, e = e0 + le;
                 if (e >= mesh.K) continue;
@@ -658,25 +685,30 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     }
                 }
                 if (A.collect) {
-                    if (n == 0) st_m += 4.0 * S.A4;   // element area = sum of its node masses
+                    // alpha weighted by the node mass; the host divides by the
+                    // mesh area times the number of limited stages
                     const bool act = nn_lt(lmin, 1.0);
-                    if (act) { st_am += S.A4 * s_ww[n] * (1.0 - lmin); st_act++; }
+                    if (act) { st_am += d2f(S.A4) * s_wwf[n] * (1.0f - d2f(lmin)); st_act++; }
                     if (nmort == 0) {
                         // rho p = (gamma-1)(rho E - |m|^2/2): checks without division;
                         // p >= p_min  <=>  rho p rho_FV >= (p_min rho_FV) rho
-                        double rp = (g - 1.0) * (uvol[0] * uvol[3] - 0.5 * (uvol[1] * uvol[1] + uvol[2] * uvol[2]));
+                        double rp = gm1 * (uvol[0] * uvol[3] - 0.5 * (uvol[1] * uvol[1] + uvol[2] * uvol[2]));
                         const double rmn = S.rmin[n], rmx = S.rmax[n];
                         if (dlt(uvol[0], rmn - kViolTol * fabs(rmn)) || dlt(rmx + kViolTol * fabs(rmx), uvol[0]))
                             st_vr++;
                         if (dlt(rp * S.ufv[0][n], S.pms[n] * (1.0 - kViolTol) * uvol[0])) st_vp++;
                         if (!dpos(uvol[0]) || !dpos(rp)) st_np++;
                         st_rmin = dmin(st_rmin, uvol[0]);
-                        if (act) st_pmin = dmin(st_pmin, rp / uvol[0]);
+                        // minimum p = rho p / rho over limited nodes, kept as a ratio
+                        if (act && dpos(uvol[0]) &&
+                            (!(__double_as_longlong(st_pd) > 0) || dlt(rp * st_pd, st_pn * uvol[0]))) {
+                            st_pn = rp; st_pd = uvol[0];
+                        }
                     }
                 }
             }
-            if (A.collect) block_stats(A, st_am, st_m, st_act, st_vr, st_vp, st_np, 0ull, st_rmin, st_pmin);
-            if ((st_vr | st_vp | st_np) != 0ull) atomicOr(A.status, ST_VIOLATION);
+            if (A.collect) block_stats(A, st_am, st_act, st_vr, st_vp, st_np, st_rmin, st_pn, st_pd);
+            if ((st_vr | st_vp | st_np) != 0u) atomicOr(A.status, ST_VIOLATION);
         }
         __syncthreads();
     }

@@ -145,6 +145,15 @@ void build_ops(int N, int proj, Ops &o) {
                 double lo = std::max(bl[k], lo0), hi = std::min(bl[k + 1], hi0);
                 o.wt[k][e * np + l] = (hi - lo > 1e-12) ? hi - lo : 0.0;
             }
+    o.npair = 0;
+    for (int k = 0; k < np; ++k)
+        for (int r = 0; r < 2 * np; ++r)
+            if (o.wt[k][r] > 0.0) {
+                const int p = o.npair++;
+                o.pk[p] = k; o.pr[p] = r;
+                o.slot_p[k][o.slot_n[k]++] = p;
+                o.slot_p[np + r][o.slot_n[np + r]++] = p;
+            }
     // interpolation to the small-face nodes s = (x_l -/+ 1) / 2
     for (int e = 0; e < 2; ++e)
         for (int l = 0; l < np; ++l) {
@@ -403,6 +412,7 @@ struct idp_ctx {
     cudaGraphExec_t graph = nullptr;
     const double *graph_u = nullptr;
     long long n_stages = 0;
+    double total_area = 0.0;   // sum of element areas (all simulations)
     // optional timing: 1 step spans around the graph launches; 2 steps
     // launched without the graph, with element-pass events
     int prof = 0;
@@ -430,7 +440,7 @@ StageArgs base_args(idp_ctx *c) {
     A.cfl = c->opt.cfl;
     A.t_sim = c->d_tsim;
     A.beta = c->opt.beta;
-    A.gamma = c->gamma;
+    A.gas = make_gas(c->gamma);
     A.ops = c->d_ops;
     A.status = c->d_status;
     A.stats = c->d_stats;
@@ -442,7 +452,7 @@ StageArgs base_args(idp_ctx *c) {
 void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux,
                    cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
     const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
-    if (c->M > 0 && need_mortar_flux) c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, A.u, c->gamma, c->d_ops);
+    if (c->M > 0 && need_mortar_flux) c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, A.u, A.gas, c->d_ops);
     if (ev0) cudaEventRecord(ev0, st);
     c->L.element(c->opt.precision, c->epb, element_grid(c, c->epb, c->persistent, c->bps), st, c->mesh, c->slots, A);
     if (ev1) cudaEventRecord(ev1, st);
@@ -458,10 +468,10 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) 
     k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
     if (c->M > 0 && mortar_flux && c->opt.dt_rule == 0) {
         const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
-        c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, u, c->gamma, c->d_ops);
+        c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, u, make_gas(c->gamma), c->d_ops);
     }
     int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
-    c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, c->gamma, c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
+    c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, make_gas(c->gamma), c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
             c->d_status);
 }
 
@@ -592,6 +602,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     c->N = N; c->NP = N + 1; c->n_sims = n_sims; c->gamma = gamma; c->opt = o;
     c->K = (long long)H.geom.size(); c->M = (long long)H.m_large.size();
     c->sim_off = H.sim_off;
+    for (const Geo &g : H.geom) c->total_area += g.z * g.w;
     c->L = get_launchers(c->NP);
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -915,7 +926,10 @@ idp_status idp_dgsem_limiter_stats(idp_ctx *c, idp_limiter_stats *out, void *str
         cudaMemcpy(&a, c->d_stats, sizeof(a), cudaMemcpyDeviceToHost) != cudaSuccess)
         return IDP_E_CUDA;
     std::memset(out, 0, sizeof(*out));
-    out->alpha_volume_mean = a.mass > 0 ? a.alpha_vol_m / a.mass : 0.0;
+    // every limited stage visits every node once: the mass sum is the mesh
+    // area times the number of limited stages
+    const double mass = c->total_area * (double)c->n_stages;
+    out->alpha_volume_mean = mass > 0 ? a.alpha_vol_m / mass : 0.0;
     out->alpha_mortar_mean = a.len > 0 ? a.alpha_mort_len / a.len : 0.0;
     out->n_stages = c->n_stages;
     out->n_volume_active = (int64_t)a.n_vol;

@@ -19,11 +19,11 @@ struct Launchers {
     void (*element)(int fp32, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
                     const StageArgs &a);
     void (*mortar_flux)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
-                        double gamma, const Ops *ops);
+                        const Gas &gas, const Ops *ops);
     void (*mortar_limit)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
     void (*mortar_apply)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
     void (*dt)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
-               double gamma, int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin,
+               const Gas &gas, int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin,
                unsigned *status);
     void (*integrals)(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part);
 };

@@ -23,7 +23,7 @@ constexpr int MORTARS_PER_BLOCK = 4;   // one warp per mortar
 // FT: flux arithmetic type (FP32 in the FP32 form). Interpolation, the
 // admissibility test, bar states and all sums are FP64.
 template <int NP, typename FT>
-__device__ __forceinline__ Prim<FT> mortar_prim(double g, const double *q) {
+__device__ __forceinline__ Prim<FT> mortar_prim(const Gas &g, const double *q) {
     if constexpr (sizeof(FT) == 4) {
         float a, b;
         return make_prim_f32(g, q[0], q[1], q[2], q[3], false, a, b);
@@ -32,17 +32,26 @@ __device__ __forceinline__ Prim<FT> mortar_prim(double g, const double *q) {
     }
 }
 
+// One warp per mortar. Lanes take (node, variable) items for the
+// interpolation and the projection, one small-face node each for the LLF
+// fluxes, and one nonzero local weight each for the sparse low-order flux:
+// every pair term is formed once and summed into both of its slots in a
+// fixed order.
 template <int NP, typename FT>
 __global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
-k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, const Ops *ops) {
-    constexpr int NN = NP * NP, Q = 3 * NP;
-    __shared__ double s_u[MORTARS_PER_BLOCK][Q][4];
-    __shared__ FT s_pr[MORTARS_PER_BLOCK][Q][3];     // normal velocity, p, c
-    __shared__ double s_ui[MORTARS_PER_BLOCK][2 * NP][4];
-    __shared__ FT s_f[MORTARS_PER_BLOCK][2 * NP][4];
+k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, const Ops *ops) {
+    constexpr int NN = NP * NP, Q = 3 * NP, NI = 2 * NP, MP = 3 * NP, W = MORTARS_PER_BLOCK;
+    __shared__ double s_u[W][Q][4];      // traces: large side, then the two small faces
+    __shared__ FT s_uf[W][Q][4];         // the same in the flux type
+    __shared__ FT s_pr[W][Q][3];         // normal velocity, p, c
+    __shared__ double s_ui[W][NI][4];    // large trace interpolated to the small-face nodes
+    __shared__ FT s_f[W][NI][4];         // LLF flux on the small faces
+    __shared__ double s_term[W][MP][4];  // sparse low-order pair terms
+    __shared__ double s_rb[W][MP];       // their bar-state densities
+    __shared__ FT s_d2[W][MP];           // and 2 d
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.x * MORTARS_PER_BLOCK + warp;
-    if (m >= mesh.M) return;
+    const int m = blockIdx.x * W + warp;
+    if (m >= mesh.M) return;   // uniform per warp
     const size_t KN = (size_t)mesh.K * NN;
     const int info = mesh.m_info[m], dir = info & 1, low = (info >> 1) & 1;
     const int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
@@ -51,8 +60,9 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
     const Geo geoL = mesh.geom[L];
     const double halfL = dir == 0 ? 0.5 * geoL.w : 0.5 * geoL.z, halfS = 0.5 * halfL;
     const double sg = low ? 1.0 : -1.0;   // large side's outward normal along +dir
-    const FT sgf = (FT)sg;
-    const double g = gamma;
+    const Gas &g = gas;
+    constexpr bool F32 = sizeof(FT) == 4;
+    // traces and their primitives
     if (lane < Q) {
         int gnode;
         if (lane < NP) gnode = L * NN + face_node<NP>(sL, lane);
@@ -62,90 +72,135 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double ga
         }
         double q[4];
         for (int v = 0; v < 4; ++v) { q[v] = u[v * KN + gnode]; s_u[warp][lane][v] = q[v]; }
-        Prim<FT> pr = mortar_prim<NP, FT>(g, q);
+        Prim<FT> pr;
+        if constexpr (F32) {
+            float m1f, m2f;
+            pr = make_prim_f32(g, q[0], q[1], q[2], q[3], false, m1f, m2f);
+            s_uf[warp][lane][0] = pr.rho; s_uf[warp][lane][1] = m1f; s_uf[warp][lane][2] = m2f;
+            s_uf[warp][lane][3] = pr.E;
+        } else {
+            pr = make_prim<FT>(g, q[0], q[1], q[2], q[3], false);
+            for (int v = 0; v < 4; ++v) s_uf[warp][lane][v] = q[v];
+        }
         s_pr[warp][lane][0] = dir == 0 ? pr.v1 : pr.v2;
         s_pr[warp][lane][1] = pr.p;
         s_pr[warp][lane][2] = pr.c;
     }
     __syncwarp();
-    // interpolation of the large trace to the small-face nodes, admissibility
+    // interpolation of the large trace to the small-face nodes (FP64)
+    for (int it = lane; it < NI * 4; it += 32) {
+        const int r = it >> 2, v = it & 3;
+        double acc = 0.0;
+        for (int k = 0; k < NP; ++k) acc += ops->I[r][k] * s_u[warp][k][v];
+        s_ui[warp][r][v] = acc;
+    }
+    // sparse low-order pair terms (Eq. interfaceflux_local) with their bar
+    // states and 2 d; term enters the large slot with -, the small with +
+    const int npair = ops->npair;
+    if (lane < npair) {
+        const int k = ops->pk[lane], r = ops->pr[lane];
+        const double wt = ops->wt[k][r] * halfL;
+        const double *a = s_u[warp][k], *b = s_u[warp][NP + r];
+        const FT *af = s_uf[warp][k], *bf = s_uf[warp][NP + r];
+        const FT *pa = s_pr[warp][k], *pb = s_pr[warp][NP + r];
+        FT la = fabs(pa[0]) + pa[2], lb = fabs(pb[0]) + pb[2];
+        FT lam = la > lb ? la : lb;
+        FT fa[4], fb[4];
+        phys_flux<FT>(af[1], af[2], af[3], pa[1], pa[0], dir, fa);
+        phys_flux<FT>(bf[1], bf[2], bf[3], pb[1], pb[0], dir, fb);
+        const FT sgf = low ? FT(1) : FT(-1);
+        FT hw, i2l_f;
+        double i2l;
+        if constexpr (F32) { hw = d2f(0.5 * wt); i2l_f = 0.5f / lam; i2l = f2d(i2l_f); }
+        else { hw = 0.5 * wt; i2l = 0.5 / lam; }
+        for (int v = 0; v < 4; ++v) {
+            FT term = hw * ((sgf * fa[v] + sgf * fb[v]) - lam * (bf[v] - af[v]));
+            if constexpr (F32) s_term[warp][lane][v] = f2d(term);
+            else s_term[warp][lane][v] = term;
+        }
+        s_rb[warp][lane] = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) * i2l;
+        FT wtf;
+        if constexpr (F32) wtf = d2f(wt);
+        else wtf = wt;
+        s_d2[warp][lane] = wtf * lam;
+    }
+    __syncwarp();
+    // admissibility of the interpolated states; LLF on the small faces
+    // (left/bottom state first)
     bool badl = false;
     Prim<FT> pint;
-    if (lane < 2 * NP) {
-        double acc[4] = {0, 0, 0, 0};
-        for (int k = 0; k < NP; ++k) {
-            double c = ops->I[lane][k];
-            for (int v = 0; v < 4; ++v) acc[v] += c * s_u[warp][k][v];
-        }
-        for (int v = 0; v < 4; ++v) s_ui[warp][lane][v] = acc[v];
-        // rho p > 0 without a division, then the primitives
-        badl = !(acc[0] > 0.0) || !(acc[0] * acc[3] - 0.5 * (acc[1] * acc[1] + acc[2] * acc[2]) > 0.0);
+    if (lane < NI) {
+        const double *acc = s_ui[warp][lane];
+        // rho > 0 and rho p > 0, without a division
+        badl = !dpos(acc[0]) || !dpos(acc[0] * acc[3] - 0.5 * (acc[1] * acc[1] + acc[2] * acc[2]));
         if (!badl) pint = mortar_prim<NP, FT>(g, acc);
     }
     const bool bad = __any_sync(0xffffffffu, badl);
-    // LLF on the small faces (left/bottom state first)
-    if (!bad && lane < 2 * NP) {
+    if (!bad && lane < NI) {
         FT f[4];
-        const double *ui = s_ui[warp][lane], *us = s_u[warp][NP + lane];
         Prim<FT> ps;
         ps.v1 = dir == 0 ? s_pr[warp][NP + lane][0] : FT(0);
         ps.v2 = dir == 1 ? s_pr[warp][NP + lane][0] : FT(0);
         ps.p = s_pr[warp][NP + lane][1];
         ps.c = s_pr[warp][NP + lane][2];
-        if (low) llf_prim<FT>(ui, pint, us, ps, dir, f); else llf_prim<FT>(us, ps, ui, pint, dir, f);
+        const FT *us = s_uf[warp][NP + lane];
+        FT ui[4];
+        for (int v = 0; v < 4; ++v) ui[v] = to_ft<FT>(s_ui[warp][lane][v]);
+        if (low) llf_prim<FT, FT>(ui, pint, us, ps, dir, f);
+        else llf_prim<FT, FT>(us, ps, ui, pint, dir, f);
         for (int v = 0; v < 4; ++v) s_f[warp][lane][v] = f[v];
     }
     __syncwarp();
-    if (lane < Q) {
-        const int q = lane;
-        double chi[4] = {0, 0, 0, 0}, clo[4] = {0, 0, 0, 0};
+    // per (slot, variable): high-order contribution (projection summed in
+    // FP64, so conservation across the mortar holds to FP64 rounding whatever
+    // the flux type) and the sparse low-order sum
+    for (int it = lane; it < Q * 4; it += 32) {
+        const int q = it >> 2, v = it & 3;
+        double chi = 0.0, clo = 0.0;
+        const int np_q = ops->slot_n[q];
+        for (int t = 0; t < np_q; ++t) clo += s_term[warp][ops->slot_p[q][t]][v];
+        if (q < NP) clo = -clo;
         if (!bad) {
             if (q < NP) {
-                // projection summed in FP64: conservation across the mortar
-                // holds to FP64 rounding whatever the flux type
-                double acc[4] = {0, 0, 0, 0};
-                for (int r = 0; r < 2 * NP; ++r) {
-                    double c = ops->P[q][r];
-                    for (int v = 0; v < 4; ++v) acc[v] += c * (double)s_f[warp][r][v];
+                double acc = 0.0;
+                for (int r = 0; r < NI; ++r) {
+                    double fr;
+                    if constexpr (F32) fr = f2d(s_f[warp][r][v]);
+                    else fr = s_f[warp][r][v];
+                    acc += ops->P[q][r] * fr;
                 }
-                for (int v = 0; v < 4; ++v) chi[v] = -sg * ops->w[q] * (halfL * acc[v]);
+                chi = -sg * ops->w[q] * (halfL * acc);
             } else {
-                int l = (q - NP) % NP;
-                for (int v = 0; v < 4; ++v) chi[v] = sg * ops->w[l] * (halfS * (double)s_f[warp][q - NP][v]);
+                const int l = (q - NP) % NP;
+                double fr;
+                if constexpr (F32) fr = f2d(s_f[warp][q - NP][v]);
+                else fr = s_f[warp][q - NP][v];
+                chi = sg * ops->w[l] * (halfS * fr);
             }
+        } else {
+            chi = clo;
         }
-        // sparse low-order flux (Eq. interfaceflux_local), bar states and
-        // 2 d sums over the nonzero local weights
-        double lo = INFINITY, hi = -INFINITY, ds = 0.0;
-        const int kb = q < NP ? q : 0, ke = q < NP ? q + 1 : NP;
-        const int rb = q < NP ? 0 : q - NP, re = q < NP ? 2 * NP : q - NP + 1;
-        for (int k = kb; k < ke; ++k)
-            for (int r = rb; r < re; ++r) {
-                double wt = ops->wt[k][r] * halfL;
-                if (wt <= 0.0) continue;
-                const double *a = s_u[warp][k], *b = s_u[warp][NP + r];
-                const FT *pa = s_pr[warp][k], *pb = s_pr[warp][NP + r];
-                FT la = fabs(pa[0]) + pa[2], lb = fabs(pb[0]) + pb[2];
-                FT lam = la > lb ? la : lb;
-                FT fa[4], fb[4];
-                phys_flux<FT>((FT)a[1], (FT)a[2], (FT)a[3], pa[1], pa[0], dir, fa);
-                phys_flux<FT>((FT)b[1], (FT)b[2], (FT)b[3], pb[1], pb[0], dir, fb);
-                FT hw = (FT)(0.5 * wt);
-                for (int v = 0; v < 4; ++v) {
-                    FT term = hw * ((sgf * fa[v] + sgf * fb[v]) - lam * ((FT)b[v] - (FT)a[v]));
-                    clo[v] += q < NP ? -(double)term : (double)term;
-                }
-                double ld = (double)lam;
-                double rbv = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) * (double)(FT(0.5) / lam);
-                lo = fmin(lo, rbv);
-                hi = fmax(hi, rbv);
-                ds += 2.0 * (wt / 2.0) * ld;
-            }
-        if (bad)
-            for (int v = 0; v < 4; ++v) chi[v] = clo[v];
-        const int s = m * Q + q;
-        for (int v = 0; v < 4; ++v) { sl.chi[(size_t)v * sl.S + s] = chi[v]; sl.clo[(size_t)v * sl.S + s] = clo[v]; }
-        sl.rbmin[s] = lo; sl.rbmax[s] = hi; sl.dsum[s] = ds;
+        const size_t si = (size_t)v * sl.S + (size_t)m * Q + q;
+        sl.chi[si] = chi;
+        sl.clo[si] = clo;
+    }
+    // per slot: bar-state range and 2 d sum over its pairs
+    if (lane < Q) {
+        long long klo = okey(INFINITY), khi = okey(-INFINITY);
+        FT ds = FT(0);
+        const int np_q = ops->slot_n[lane];
+        for (int t = 0; t < np_q; ++t) {
+            const int p = ops->slot_p[lane][t];
+            const long long kb = okey(s_rb[warp][p]);
+            klo = kb < klo ? kb : klo;
+            khi = kb > khi ? kb : khi;
+            ds += s_d2[warp][p];
+        }
+        const int si = m * Q + lane;
+        sl.rbmin[si] = okey_value(klo);
+        sl.rbmax[si] = okey_value(khi);
+        if constexpr (F32) sl.dsum[si] = f2d(ds);
+        else sl.dsum[si] = ds;
     }
     if (lane == 0) sl.bad[m] = bad ? 1 : 0;
 }
@@ -176,7 +231,7 @@ k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
         else if (av[0] < 0.0) { double t = (sl.rmin[s] - tl - u0[0]) / av[0]; if (t < lr) lr = t; }
         if (lr < 0.0) lr = 0.0;
         double pm = sl.pmin[s] - kTol * fabs(sl.pmin[s]);
-        th = theta_max(A.gamma, u0, av, A.gamma - 1.0, pm, g_zero(A.gamma - 1.0, u0, pm), lr);
+        th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
     }
     for (int o = 16; o > 0; o >>= 1) th = fmin(th, __shfl_down_sync(0xffffffffu, th, o));
     if (lane == 0) {
@@ -198,8 +253,8 @@ template <int NP>
 __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
     constexpr int NN = NP * NP, Q = 3 * NP;
     const size_t KN = (size_t)mesh.K * NN;
-    double st_rmin = INFINITY, st_pmin = INFINITY;
-    unsigned long long vr = 0, vp = 0, np_ = 0;
+    double st_rmin = INFINITY, st_pmin = 0.0, st_one = 0.0;   // min p as the ratio st_pmin / st_one
+    unsigned vr = 0, vp = 0, np_ = 0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mesh.n_mnodes; k += gridDim.x * blockDim.x) {
         const int gnode = mesh.mn_node[k];
         const int2 ss = mesh.mn_slot[k];
@@ -229,17 +284,17 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
             }
         }
         if (A.collect) {
-            double p = pressure_d(A.gamma, ut[0], ut[1], ut[2], ut[3]);
+            double p = pressure_d(A.gas.gm1, ut[0], ut[1], ut[2], ut[3]);
             double rmin = sl.rmin[s0], rmax = sl.rmax[s0], pmin = sl.pmin[s0];
             if (ut[0] < rmin - kViolTol * fabs(rmin) || ut[0] > rmax + kViolTol * fabs(rmax)) vr++;
             if (p < pmin - kViolTol * fabs(pmin)) vp++;
             if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
-            st_rmin = fmin(st_rmin, ut[0]);
-            st_pmin = fmin(st_pmin, p);
+            st_rmin = dmin(st_rmin, ut[0]);
+            if (st_one == 0.0 || dlt(p, st_pmin)) { st_pmin = p; st_one = 1.0; }
         }
     }
-    if (A.collect) block_stats(A, 0.0, 0.0, 0ull, vr, vp, np_, 0ull, st_rmin, st_pmin);
-    if ((vr | vp | np_) != 0ull) atomicOr(A.status, ST_VIOLATION);
+    if (A.collect) block_stats(A, 0.0f, 0u, vr, vp, np_, st_rmin, st_pmin, st_one);
+    if ((vr | vp | np_) != 0u) atomicOr(A.status, ST_VIOLATION);
 }
 
 // Time step: per node m_i / sum_j 2 d_ij (rule 0) or min over directions of
@@ -251,12 +306,12 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
 // these few operations, so the step never exceeds the FP64 limit.
 template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads)
-k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, double gamma, int rule, const Ops *ops,
+k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule, const Ops *ops,
      const double *t_sim, unsigned long long *dtmin, unsigned *status) {
     constexpr int NN = NP * NP, N = NP - 1, NT = ElemLaunch<NP, EPB>::threads;
     __shared__ FT s_l[EPB][2][NN];
     const size_t KN = (size_t)mesh.K * NN;
-    const double g = gamma;
+    const Gas &g = gas;
     for (int e0 = blockIdx.x * EPB; e0 < mesh.K; e0 += gridDim.x * EPB) {
         for (int k = threadIdx.x; k < EPB * NN; k += NT) {
             int le = k / NN, n = k - le * NN, e = e0 + le;

@@ -64,9 +64,9 @@ void element(int fp32, int epb, int grid, cudaStream_t st, const MeshDev &m, con
 }
 
 void mortar_flux(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
-                 double gamma, const Ops *ops) {
-    if (fp32) k_mortar_flux<NP, float><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gamma, ops);
-    else k_mortar_flux<NP, double><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gamma, ops);
+                 const Gas &gas, const Ops *ops) {
+    if (fp32) k_mortar_flux<NP, float><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gas, ops);
+    else k_mortar_flux<NP, double><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gas, ops);
 }
 
 void mortar_limit(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
@@ -77,7 +77,7 @@ void mortar_apply(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s
     k_mortar_apply<NP><<<grid, 256, 0, st>>>(m, s, a);
 }
 
-void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, double gamma,
+void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, const Gas &gamma,
         int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status) {
     constexpr int EPB = NP * NP >= 64 ? 2 : (NP * NP >= 25 ? 4 : 8);
     int blocks = (m.K + EPB - 1) / EPB;
