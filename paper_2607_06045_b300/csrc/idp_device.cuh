@@ -30,6 +30,13 @@ struct __align__(32) Geo {
     double x, y, z, w;
 };
 
+// Per-element constants formed once on the host: 4 / (dx dy), dx dy / 4,
+// half and quarter edge lengths, and FP32 copies.
+struct __align__(16) GeoC {
+    double iA4, A4, hx, hy, qx, qy;
+    float hxf, hyf, qxf, qyf, A4f, pad;
+};
+
 // Reference operators for NP = N + 1 nodes (Sec. 2.1, App. A).
 struct Ops {
     double xi[NPMAX];                // LGL nodes
@@ -69,6 +76,7 @@ struct StatsAcc {
 struct MeshDev {
     int K, M, n_sims, n_mnodes;
     const Geo *geom;          // per element: x_left, y_bottom, dx, dy
+    const GeoC *geoc;         // per element: derived constants
     const int32_t *sim;       // per element
     const int4 *fnbr;         // per element and side: neighbour element / mortar id / -1
     const uchar4 *ftype;      // per element and side: FT_*
@@ -88,7 +96,8 @@ struct SlotsDev {
     double *rbmin, *rbmax;    // bar-state density min/max over cross-mortar pairs
     double *dsum;             // sum_j 2 d_ij over cross-mortar pairs
     double *uvol, *un;        // [4][S] state after the volume step / at step start
-    double *rmin, *rmax, *pmin, *tol, *mass;
+    double *rmin, *rmax, *pmin, *tol, *mass;   // pmin: p_min rho_FV (divided by rfv where used)
+    double *rfv;              // rho_FV
     float *nmort;             // n_i
     int32_t *bad;             // per mortar: interpolated state inadmissible
     double *ell;              // per mortar l_S

@@ -72,9 +72,9 @@ struct ElemSm {
     float tqf[NN];           // FP32 form: exemption threshold kTol |rho_FV| m / dt
     unsigned char ex[NIF];   // density antidiffusion below the tolerance (R15)
     float uf[4][NN];         // FP32 state (FP32 form)
-    // per-element constants: 1/(dx dy), dx dy / 4, stage dt, 4 dt / (dx dy),
+    // per-element constants: 4/(dx dy), dx dy / 4, stage dt, 4 dt / (dx dy),
     // half and quarter edge lengths (and FP32 copies), (dx dy / 4) / dt
-    double invA, A4, dt, dt4A, hx, hy, qx, qy;
+    double iA4, A4, dt, dt4A, hx, hy, qx, qy;
     float hxf, hyf, qxf, qyf, idtmf;
     FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
     union {
@@ -226,16 +226,19 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             S.pr[0][n] = q.rho; S.pr[1][n] = q.v1; S.pr[2][n] = q.v2; S.pr[3][n] = q.p; S.pr[4][n] = q.c;
             S.pr[5][n] = q.E; S.pr[6][n] = q.lr; S.pr[7][n] = q.lb; S.pr[8][n] = q.beta;
             if (n == 0) {
-                Geo geo = mesh.geom[e];
-                double area = geo.z * geo.w, dt = stage_dt(A, mesh.sim[e]);
-                S.invA = 1.0 / area;
-                S.A4 = 0.25 * area;
+                // one lane per element: copies of host-formed constants (a
+                // division here would cost every warp, which holds one such
+                // lane per element)
+                const GeoC gc = mesh.geoc[e];
+                const double dt = stage_dt(A, mesh.sim[e]);
+                S.iA4 = gc.iA4; S.A4 = gc.A4;
                 S.dt = dt;
-                S.dt4A = dt * (4.0 * S.invA);
-                S.hx = 0.5 * geo.z; S.hy = 0.5 * geo.w; S.qx = 0.25 * geo.z; S.qy = 0.25 * geo.w;
+                S.dt4A = dt * gc.iA4;
+                S.hx = gc.hx; S.hy = gc.hy; S.qx = gc.qx; S.qy = gc.qy;
                 if constexpr (F32) {
-                    S.hxf = d2f(S.hx); S.hyf = d2f(S.hy); S.qxf = d2f(S.qx); S.qyf = d2f(S.qy);
-                    S.idtmf = dt > 0.0 ? d2f(S.A4 / dt) : 0.0f;
+                    S.hxf = gc.hxf; S.hyf = gc.hyf; S.qxf = gc.qxf; S.qyf = gc.qyf;
+                    const float dtf = d2f(dt);
+                    S.idtmf = dtf > 0.0f ? gc.A4f / dtf : 0.0f;
                 }
             }
         }
@@ -501,7 +504,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 }
                 size_t gi = (size_t)e * NN + n;
                 if (A.mode == 0) {
-                    const double imi = (4.0 * S.invA) * s_iww[n];   // 1 / m_i
+                    const double imi = S.iA4 * s_iww[n];   // 1 / m_i
                     for (int v = 0; v < 4; ++v) A.out[v * KN + gi] = L[v] * imi;
                 } else {
                     const double dtm = S.dt4A * s_iww[n];           // dt / m_i
@@ -577,9 +580,22 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             double qp = S.rmax[n] - rfv, qm = S.rmin[n] - rfv;   // Q / (m/dt): qp >= 0 >= qm
             double pp = dtm * Pp, pmm = dtm * Pm;                // pp >= 0 >= pmm
             // R = Q / P where P exceeds Q; Q = 0 (a node on its bound) gives 0
-            // without a division
-            S.Rp[n] = nn_lt(qp, pp) ? (__double_as_longlong(qp) > 0 ? qp / pp : 0.0) : 1.0;
-            S.Rm[n] = nn_lt(qm, pmm) ? (dneg(qm) ? qm / pmm : 0.0) : 1.0;
+            // without a division. The FP32 form takes the quotient in FP32,
+            // scaled down by 2^-21 (more than the three roundings of the
+            // operands and the quotient), so R never exceeds the exact Q / P.
+            double Rp = 1.0, Rm = 1.0;
+            if (nn_lt(qp, pp)) {
+                if (__double_as_longlong(qp) <= 0) Rp = 0.0;
+                else if constexpr (F32) Rp = f2d(d2f(qp) / d2f(pp) * (1.0f - 0x1p-21f));
+                else Rp = qp / pp;
+            }
+            if (nn_lt(qm, pmm)) {
+                if (!dneg(qm)) Rm = 0.0;
+                else if constexpr (F32) Rm = f2d(d2f(qm) / d2f(pmm) * (1.0f - 0x1p-21f));
+                else Rm = qm / pmm;
+            }
+            S.Rp[n] = Rp;
+            S.Rm[n] = Rm;
         }
         __syncthreads();
 
@@ -656,7 +672,6 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if (j == N && ftv.w >= FT_MLARGE) sides[nmort++] = 3;
                 if (nmort) {
                     const double mi = S.A4 * s_ww[n];
-                    const double pmin_n = S.pms[n] / S.ufv[0][n];
                     const double tol_n = kTol * fabs(S.ufv[0][n]);
                     for (int c = 0; c < nmort; ++c) {
                         int s = sides[c];
@@ -669,7 +684,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                             sl.un[(size_t)v * sl.S + q] =
                                 A.mode == 0 ? resv[v] : (A.comb != 0 ? A.un[v * KN + gi] : 0.0);
                         }
-                        sl.rmin[q] = S.rmin[n]; sl.rmax[q] = S.rmax[n]; sl.pmin[q] = pmin_n;
+                        sl.rmin[q] = S.rmin[n]; sl.rmax[q] = S.rmax[n];
+                        sl.pmin[q] = S.pms[n]; sl.rfv[q] = S.ufv[0][n];
                         sl.tol[q] = tol_n; sl.mass[q] = mi; sl.nmort[q] = (float)nmort;
                     }
                 }

@@ -392,6 +392,7 @@ struct idp_ctx {
     SlotsDev slots;
     Ops *d_ops = nullptr;
     Geo *d_geom = nullptr;
+    GeoC *d_geoc = nullptr;
     int32_t *d_sim = nullptr, *d_mlarge = nullptr, *d_minfo = nullptr, *d_mnnode = nullptr;
     int4 *d_fnbr = nullptr;
     uchar4 *d_ftype = nullptr;
@@ -643,6 +644,18 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     chk(cudaMalloc(&c->d_ops, sizeof(Ops)));
     if (ok) chk(cudaMemcpy(c->d_ops, &ops, sizeof(Ops), cudaMemcpyHostToDevice));
     if (ok) chk(upload(&c->d_geom, H.geom));
+    {
+        std::vector<GeoC> gcv(H.geom.size());
+        for (size_t e = 0; e < H.geom.size(); ++e) {
+            const Geo &g = H.geom[e];
+            GeoC &q = gcv[e];
+            std::memset(&q, 0, sizeof(q));
+            q.iA4 = 4.0 / (g.z * g.w); q.A4 = 0.25 * (g.z * g.w);
+            q.hx = 0.5 * g.z; q.hy = 0.5 * g.w; q.qx = 0.25 * g.z; q.qy = 0.25 * g.w;
+            q.hxf = (float)q.hx; q.hyf = (float)q.hy; q.qxf = (float)q.qx; q.qyf = (float)q.qy; q.A4f = (float)q.A4;
+        }
+        if (ok) chk(upload(&c->d_geoc, gcv));
+    }
     if (ok) chk(upload(&c->d_sim, H.sim));
     if (ok) chk(upload(&c->d_fnbr, H.fnbr));
     if (ok) chk(upload(&c->d_ftype, H.ftype));
@@ -654,8 +667,8 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(upload(&c->d_mnslot, mn_slot));
     // slots: one block of device memory
     const size_t S = (size_t)c->M * Q, MM = (size_t)std::max<long long>(c->M, 1), SS = std::max<size_t>(S, 1);
-    size_t bytes = sizeof(double) * (SS * (4 + 4 + 3 + 4 + 4 + 5)) + sizeof(float) * SS + sizeof(int32_t) * MM +
-                   sizeof(double) * MM + 16 * 256;   // 15 sub-arrays, each padded to 256 B
+    size_t bytes = sizeof(double) * (SS * (4 + 4 + 3 + 4 + 4 + 6)) + sizeof(float) * SS + sizeof(int32_t) * MM +
+                   sizeof(double) * MM + 17 * 256;   // 16 sub-arrays, each padded to 256 B
     if (ok) chk(cudaMalloc(&c->d_slot_block, bytes));
     if (ok) chk(cudaMemset(c->d_slot_block, 0, bytes));
     if (ok) {
@@ -675,6 +688,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
         sl.pmin = (double *)take(sizeof(double) * SS);
         sl.tol = (double *)take(sizeof(double) * SS);
         sl.mass = (double *)take(sizeof(double) * SS);
+        sl.rfv = (double *)take(sizeof(double) * SS);
         sl.nmort = (float *)take(sizeof(float) * SS);
         sl.bad = (int32_t *)take(sizeof(int32_t) * MM);
         sl.ell = (double *)take(sizeof(double) * MM);
@@ -698,7 +712,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (!ok) { idp_dgsem_destroy(c); return IDP_E_CUDA; }
     MeshDev &md = c->mesh;
     md.K = (int)c->K; md.M = (int)c->M; md.n_sims = n_sims; md.n_mnodes = c->n_mnodes;
-    md.geom = c->d_geom; md.sim = c->d_sim; md.fnbr = c->d_fnbr; md.ftype = c->d_ftype;
+    md.geom = c->d_geom; md.geoc = c->d_geoc; md.sim = c->d_sim; md.fnbr = c->d_fnbr; md.ftype = c->d_ftype;
     md.m_large = c->d_mlarge; md.m_small = c->d_msmall; md.m_info = c->d_minfo; md.siminfo = c->d_siminfo;
     md.mn_node = c->d_mnnode; md.mn_slot = c->d_mnslot;
     reset_stats(c, c->stream);
@@ -977,7 +991,7 @@ void idp_dgsem_destroy(idp_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    void *ptrs[] = {c->d_ops, c->d_geom, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+    void *ptrs[] = {c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
                     c->d_msmall, c->d_mnslot, c->d_siminfo, c->d_slot_block, c->d_buf1, c->d_buf2, c->d_hostbuf,
                     c->d_dtmin, c->d_tsim, c->d_dtlast, c->d_status, c->d_stats, c->d_part, c->d_intout, c->d_off};
     for (void *p : ptrs)

@@ -230,7 +230,8 @@ k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
         if (av[0] > 0.0) { double t = (sl.rmax[s] + tl - u0[0]) / av[0]; if (t < lr) lr = t; }
         else if (av[0] < 0.0) { double t = (sl.rmin[s] - tl - u0[0]) / av[0]; if (t < lr) lr = t; }
         if (lr < 0.0) lr = 0.0;
-        double pm = sl.pmin[s] - kTol * fabs(sl.pmin[s]);
+        const double pmin = sl.pmin[s] / sl.rfv[s];
+        double pm = pmin - kTol * fabs(pmin);
         th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
     }
     for (int o = 16; o > 0; o >>= 1) th = fmin(th, __shfl_down_sync(0xffffffffu, th, o));
@@ -285,7 +286,7 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
         }
         if (A.collect) {
             double p = pressure_d(A.gas.gm1, ut[0], ut[1], ut[2], ut[3]);
-            double rmin = sl.rmin[s0], rmax = sl.rmax[s0], pmin = sl.pmin[s0];
+            double rmin = sl.rmin[s0], rmax = sl.rmax[s0], pmin = sl.pmin[s0] / sl.rfv[s0];
             if (ut[0] < rmin - kViolTol * fabs(rmin) || ut[0] > rmax + kViolTol * fabs(rmax)) vr++;
             if (p < pmin - kViolTol * fabs(pmin)) vp++;
             if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
