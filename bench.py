@@ -4,20 +4,22 @@ One benchmark step is one SSP-RK3 step of the whole hot path (time step,
 three limited stages, each with mortar fluxes, the element pass and mortar
 limiting) over the workload's state, which is resident in HBM. The default
 workload is the double-Mach-reflection mesh (256 x 64 base, up to three
-extra levels along the shock, about 60k elements, N = 3, FP64, local
+extra levels along the shock, 60,139 elements, N = 3, FP64, local
 limiting). The same JSON line also carries the FP32 form on that workload and
 the batched workload (256 simulations, FP32 form).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
 --impl reference times the CPU oracle (the reference arm of this build) on a
-1/16-size instance of the same DMR workload.
+1/16-size instance of the same DMR workload. Under torchrun every rank runs
+its own replica of the workload (no data-path collective); the reported value
+aggregates all ranks over the slowest rank's time.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
-import math
 import os
 import subprocess
 import sys
@@ -33,18 +35,53 @@ if ROOT not in sys.path:
 METRIC = "IDP-DGSEM DOF-updates/s per RK stage (FP64 vs FP32 form, batched); % roofline"
 UNIT = "DOF-updates/s"
 L2_BYTES = 126 * 2 ** 20
+# B300: 148 SMs, each retiring 2 FP64 fused multiply-adds per clock (the
+# nominal 1.25 TFLOP/s FP64 rate at the maximum SM clock).
+SMS, DFMA_PER_CLK_SM = 148, 2
+DMR_CONFIG = {"workload": "double Mach reflection, [0,4]x[0,1], 256x64 base + 3 levels along the shock",
+              "elements": 60139, "N": 3, "dofs": 962224, "limiting": "local + positivity", "cfl": 0.5,
+              "step": "one SSP-RK3 step (3 stages + dt)"}
 
 
 def rank_env():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)), int(os.environ.get("WORLD_SIZE", 1))
 
 
+def dist_helpers(dist, device, sync=None):
+    """Barrier (with device synchronisation on both sides) and max over ranks;
+    plain local operations without a process group."""
+    def barrier_sync():
+        if sync:
+            sync()
+        if dist is not None:
+            dist.barrier()
+        if sync:
+            sync()
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        import torch
+        t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    return barrier_sync, max_over_ranks
+
+
+def aggregate_rate(units_per_rank, world, max_time):
+    """Whole-job throughput: units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / max_time
+
+
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling (SM clock, limit and throttle reasons) around the
+    timed region; start() returns once the first sample has arrived."""
 
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
 
     def __init__(self, gpu_index):
         self.gpu = gpu_index
@@ -60,19 +97,15 @@ class Clocks:
                                          stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 5.0 and os.path.getsize(self.path) == 0:
+            time.sleep(0.02)
 
-    def stop(self):
-        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
-        if self.proc is None:
-            return out
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
+    @classmethod
+    def parse(cls, lines):
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in open(self.path):
+        for line in lines:
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -81,13 +114,25 @@ class Clocks:
                 mx.append(float(f[2]))
             except ValueError:
                 continue
-            for k, nm in enumerate(names):
+            for k, nm in enumerate(cls.NAMES):
                 if f[5 + k].lower() == "active":
                     reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        with open(self.path) as fh:
+            out = self.parse(fh.readlines())
         os.unlink(self.path)
-        if sm:
-            out = {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(mx)), "reasons": sorted(reasons),
-                   "samples": len(sm)}
         return out
 
 
@@ -103,7 +148,23 @@ def build_workload(name):
     raise ValueError(name)
 
 
-def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn, clocks=None):
+def recorded_traffic():
+    """DRAM bytes per element-pass launch from the committed ncu record, if the
+    element-pass sources are unchanged since it was taken (else None)."""
+    path = os.path.join(ROOT, "profiles", "traffic_k_element_dmr.json")
+    try:
+        rec = json.load(open(path))
+        h = hashlib.sha256()
+        for f in rec["sources"]:
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None
+        return rec["dram_bytes_read"] + rec["dram_bytes_write"]
+    except (OSError, KeyError, ValueError):
+        return None
+
+
+def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn):
     """Per-step CUDA-event timing on the launching stream, L2 flushed between
     steps. Pass 1 (the headline): CUDA-graph steps bracketed by events. Pass 2:
     the same number of steps launched kernel by kernel with events around each
@@ -117,20 +178,16 @@ def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn, clocks=None):
         ctx.idp_dgsem_profile(mode)
         ctx.idp_dgsem_profile_read(reset=True)
         sync_fn()
-        if clocks and mode == 1:
-            clocks.start()
         for _ in range(steps):
             with torch.cuda.stream(stream):
                 flush.zero_()          # L2 flush, outside the timed span
             ctx.idp_dgsem_step(u_dev, 1, t, stream=stream.cuda_stream)
         sync_fn()
-        if clocks and mode == 1:
-            ck = clocks.stop()
         out.append(ctx.idp_dgsem_profile_read(reset=True))
     ctx.idp_dgsem_profile(0)
     (_, _, step_ms, nst), (el_ms, el_n, _, _) = out
     assert nst == steps
-    return step_ms * 1e-3, el_ms, el_n, (ck if clocks else None)
+    return step_ms * 1e-3, el_ms, el_n
 
 
 def run_ours(args):
@@ -140,42 +197,35 @@ def run_ours(args):
     dist = None
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+        dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     build.build()
     stream = torch.cuda.Stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
-
-    def barrier_sync():
-        torch.cuda.synchronize()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-
-    def max_over_ranks(x):
-        if dist is None:
-            return x
-        tt = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        return float(tt.item())
+    barrier_sync, max_over_ranks = dist_helpers(dist, "cuda", torch.cuda.synchronize)
 
     probe = idp.idp_probe_pipes(stream.cuda_stream)
-    fp64_tflops, fp32_tflops, w_div, w_sqrt, w_log = probe
+    fp64_probe, fp32_probe, w_div, w_sqrt, w_log = probe
 
     meshes, u0 = build_workload("dmr")
     nodes = u0.shape[1] * u0.shape[2] * u0.shape[3]
     results = {}
+    clocks = Clocks(local)
     for prec in (0, 1):
         ctx = idp.Context(meshes[0], 3, precision=prec, limiting=2, cfl=0.5)
         u_dev = torch.from_numpy(u0).cuda()
-        clocks = Clocks(local) if prec == 0 else None
         barrier_sync()
-        tot, el_ms, el_n, ck = time_steps(ctx, u_dev, args.steps, args.warmup, flush, stream, barrier_sync, clocks)
+        if prec == 0:
+            clocks.start()
+        tot, el_ms, el_n = time_steps(ctx, u_dev, args.steps, args.warmup, flush, stream, barrier_sync)
+        if prec == 0:
+            ck = clocks.stop()
         tot = max_over_ranks(tot)
         rc, st = ctx.idp_dgsem_limiter_stats()
-        results[prec] = dict(time=tot, el_ms=el_ms, el_n=el_n, clocks=ck, stats=st, ctx=ctx,
-                             launches=ctx.launches_per_step() * args.steps, epb=None)
+        results[prec] = dict(time=tot, el_ms=el_ms, el_n=el_n, stats=st, ctx=ctx,
+                             launches=ctx.launches_per_step() * args.steps)
         if prec == 0:
+            results["clocks"] = ck
             # end to end through the host-buffer entry point (pinned host state)
             uh = torch.from_numpy(u0.copy()).pin_memory()
             th = np.zeros(1)
@@ -194,24 +244,28 @@ def run_ours(args):
     bctx = idp.Context(bm, 3, precision=1, limiting=2, cfl=0.5)
     ubd = torch.from_numpy(ub).cuda()
     del ub
-    bsteps = max(3, args.steps // 2)
+    bsteps = max(3, args.steps // 4)
     barrier_sync()
-    btot, bel_ms, bel_n, _ = time_steps(bctx, ubd, bsteps, max(3, args.warmup // 2), flush, stream, barrier_sync)
+    btot, _, _ = time_steps(bctx, ubd, bsteps, max(3, args.warmup // 2), flush, stream, barrier_sync)
     btot = max_over_ranks(btot)
     brc, bst = bctx.idp_dgsem_limiter_stats()
 
     if rank != 0:
-        if dist is not None:
-            dist.barrier()
+        barrier_sync()
         return
     r64, r32 = results[0], results[1]
-    value = world * nodes * 3 * args.steps / r64["time"]
+    ck = results["clocks"]
+    value = aggregate_rate(nodes * 3 * args.steps, world, r64["time"])
+    sm_mhz = ck["sm_max_mhz"] or 2032.0
+    peak = SMS * DFMA_PER_CLK_SM * 2 * sm_mhz * 1e6 * 1e-12
     w = (w_div, w_sqrt, w_log)
     f64 = roofline.element_flops(3, 0, *w)
     el_avg = r64["el_ms"] * 1e-3 / max(r64["el_n"], 1)
     achieved = f64 * nodes / el_avg * 1e-12
     f32 = roofline.element_flops(3, 1, *w)
     el32 = r32["el_ms"] * 1e-3 / max(r32["el_n"], 1)
+    ach32 = f32 * nodes / el32 * 1e-12
+    bval = aggregate_rate(bnodes * 3 * bsteps, world, btot)
     line = {
         "metric": METRIC,
         "value": value,
@@ -225,45 +279,47 @@ def run_ours(args):
         "vs_baseline": None,
         "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": "double Mach reflection, [0,4]x[0,1], 256x64 base + 3 levels along the shock",
-                   "elements": int(u0.shape[1]), "N": 3, "dofs": int(nodes), "limiting": "local + positivity",
-                   "cfl": 0.5, "precision": "fp64", "step": "one SSP-RK3 step (3 stages + dt)",
-                   "l2": "flushed between steps (256 MiB write)", "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "alu", "kernel": "k_element (element pass)",
-                     "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
-                     "frac": achieved / fp64_tflops,
-                     "peak_source": "FP64 DFMA rate measured in this run (idp_probe_pipes)",
-                     "flops_per_node_stage": f64, "weights_dfma_eq": {"div": w_div, "sqrt": w_sqrt, "log": w_log},
-                     "launch_ms": el_avg * 1e3, "traffic": None},
-        "e2e": {"value": world * nodes * 3 * args.steps / results["e2e"], "unit": UNIT,
+        "config": dict(DMR_CONFIG, precision="fp64", l2="flushed between steps (256 MiB write)",
+                       parallelism=f"replicas x{world}"),
+        "roofline": {"bound": "alu", "kernel": "k_element (element pass, FP64 path)",
+                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                     "peak_source": f"derived: {SMS} SMs x {DFMA_PER_CLK_SM} FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz",
+                     "peak_probe": fp64_probe,
+                     "flops_per_node_stage": f64,
+                     "weights_dfma_eq": {"div": w_div, "sqrt": w_sqrt, "log": w_log},
+                     "launch_ms": el_avg * 1e3,
+                     "traffic": recorded_traffic()},
+        "e2e": {"value": aggregate_rate(nodes * 3 * args.steps, world, results["e2e"]), "unit": UNIT,
                 "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(u0.nbytes)},
         "gpu_launches": int(r64["launches"]),
-        "clocks": r64["clocks"],
+        "clocks": ck,
         "stats": {k: r64["stats"][k] for k in ("alpha_volume_mean", "alpha_mortar_mean", "n_viol_density",
                                                "n_viol_pressure", "n_nonpositive")},
         "forms": {
-            "fp32_form": {"value": world * nodes * 3 * args.steps / r32["time"], "unit": UNIT,
+            "fp32_form": {"value": aggregate_rate(nodes * 3 * args.steps, world, r32["time"]), "unit": UNIT,
                           "ms_per_step": r32["time"] / args.steps * 1e3,
                           "speedup_vs_fp64": r64["time"] / r32["time"],
-                          "roofline": {"bound": "alu", "achieved": f32 * nodes / el32 * 1e-12, "peak": fp64_tflops,
-                                       "frac": f32 * nodes / el32 * 1e-12 / fp64_tflops, "unit": "TFLOP/s",
-                                       "launch_ms": el32 * 1e3},
-                          "gpu_launches": int(r32["launches"])},
-            "batched_fp32": {"value": world * bnodes * 3 * bsteps / btot, "unit": UNIT,
+                          "roofline": {"bound": "alu", "achieved": ach32, "peak": peak, "frac": ach32 / peak,
+                                       "unit": "TFLOP/s", "launch_ms": el32 * 1e3,
+                                       "flops_per_node_stage": f32},
+                          "gpu_launches": int(r32["launches"]),
+                          "stats": {k: r32["stats"][k] for k in ("alpha_volume_mean", "n_viol_density",
+                                                                 "n_viol_pressure", "n_nonpositive")}},
+            "batched_fp32": {"value": bval, "unit": UNIT,
                              "workload": "256 simulations, 8..128 base, 0-2 levels on seeded patches, N=3, "
                                          "four-quadrant Riemann data, FP32 form",
                              "elements": int(bctx.K), "dofs": int(bnodes), "steps": bsteps,
-                             "speedup_vs_fp64": (bnodes * 3 * bsteps / btot) / (nodes * 3 * args.steps / r64["time"]),
+                             "speedup_vs_fp64": bval / value,
                              "gpu_launches": int(bctx.launches_per_step() * bsteps),
-                             "n_nonpositive": bst["n_nonpositive"]},
+                             "stats": {k: bst[k] for k in ("alpha_volume_mean", "n_viol_density",
+                                                           "n_viol_pressure", "n_nonpositive")}},
         },
-        "probe": {"fp64_tflops": fp64_tflops, "fp32_tflops": fp32_tflops},
+        "probe": {"fp64_tflops": fp64_probe, "fp32_tflops": fp32_probe},
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_full()
     print(json.dumps(line), flush=True)
-    if dist is not None:
-        dist.barrier()
+    barrier_sync()
 
 
 def cpu_baseline_full():
@@ -301,13 +357,13 @@ def run_reference(args):
         u, t, _, _ = o.step(u, 1, t=t, cfl=0.5, limiting=2)
     dt = time.perf_counter() - t0
     value = nodes * 3 * args.steps / dt
-    sample = f"1/16-size DMR instance (64x16 base, {m.n_elems} elements, {nodes} DOFs), one SSP-RK3 step per bench step"
+    sample = (f"1/16-size instance of the DMR workload (64x16 base, {m.n_elems} elements, {nodes} DOFs), "
+              f"one SSP-RK3 step per bench step, single-threaded C oracle")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": "double Mach reflection (1/16-size instance of the 256x64 + 3 levels mesh)",
-                       "N": 3, "limiting": "local + positivity", "cfl": 0.5},
+            "config": dict(DMR_CONFIG, precision="fp64", parallelism="single host thread"),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -316,7 +372,7 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
