@@ -46,44 +46,66 @@ __device__ __forceinline__ double stage_time(const StageArgs &A, int sim, double
     return A.mode == 0 ? A.t : A.t_sim[sim] + A.tstage * dt;
 }
 
+// Shared memory of one element. Arrays whose lifetimes (in phases P0..P5 of
+// k_element) do not overlap share storage: the P0-P1 primitives and traces
+// with the P2-P5 node data, the P1-P2 fluxes and bar states with the P2b-P5
+// antidiffusive fluxes, the P1-P2b subcell fluxes with the P3-P5 factors, and
+// the state (read for the last time by its own node in P2) with that node's
+// low-order residual.
 template <int NP, typename FT>
 struct ElemSm {
     static constexpr int NN = NP * NP, N = NP - 1, NPAIR = NP * (NP - 1) / 2, NIF = 2 * NP * (NP - 1);
     static constexpr bool F32 = sizeof(FT) == 4;
-    double u[4][NN];
-    double ufv[4][NN];
-    double lfv[4][NN];
-    double face[4][NP][4];   // (w_t |face|/2) * numerical flux along +x/+y (conforming, boundary)
-    double outs[4][NP][4];   // outside state (conforming neighbour or ghost)
-    double fbar[4][NP];      // bar-state density across the face (mortar sides: the minimum)
-    double fbar2[4][NP];     // mortar sides: the maximum (conforming: = fbar)
-    FT f2d[4][NP];           // 2 d_ij across the face (time-step check)
-    FT Fdg[NIF][4];          // mass-weighted high-order subcell flux w_r * fhat (flux type)
-    FT Ffv[F32 ? NIF : 1][4];  // FP32 form: the low-order subcell flux in FP32
-    double Fv[NIF][4];       // the low-order subcell flux in FP64, for the residual sums
-    double ibar[NIF], ell[NIF];
-    FT i2d[NIF];
-    double rmin[NN], rmax[NN], tol[NN], Rp[NN], Rm[NN];
-    // pressure solve at u_FV in the form scaled by rho_FV: gm = (gamma-1) rho_FV,
-    // pm = p_min rho_FV = beta (gamma-1)(rho E - |m|^2/2), c0 = g(0)
-    double dtm[NN], gms[NN], pms[NN], c0[NN];
-    float ufvf[4][NN];       // FP32 copies for the certified admissibility check
-    float dtmf[NN], gmsf[NN], pmsf[NN], c0f[NN];
-    float tqf[NN];           // FP32 form: exemption threshold kTol |rho_FV| m / dt
-    unsigned char ex[NIF];   // density antidiffusion below the tolerance (R15)
-    float uf[4][NN];         // FP32 state (FP32 form)
+    union {
+        struct {                 // P0 - P1
+            FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
+            float uf[F32 ? 4 : 1][NN];   // FP32 state (FP32 form)
+            double outs[4][NP][4];   // outside state (conforming neighbour or ghost)
+        };
+        struct {                 // P2 - P5
+            double dtm[NN], ufv[4][NN], rmin[NN], rmax[NN], tol[NN];
+            // pressure solve at u_FV in the form scaled by rho_FV: gm = (gamma-1) rho_FV,
+            // pm = p_min rho_FV = beta (gamma-1)(rho E - |m|^2/2), c0 = g(0)
+            double gms[NN], pms[NN], c0[NN];
+            float ufvf[4][NN];       // FP32 copies for the certified admissibility check
+            float dtmf[NN], gmsf[NN], pmsf[NN], c0f[NN];
+            float tqf[NN];           // FP32 form: exemption threshold kTol |rho_FV| m / dt
+        };
+    };
+    union {
+        struct {                 // P1 - P2
+            FT pair[2][NP][NPAIR][4];   // two-point fluxes
+            double face[4][NP][4];   // (w_t |face|/2) * numerical flux along +x/+y
+            double fbar[4][NP];      // bar-state density across the face (mortar sides: the minimum)
+            double fbar2[4][NP];     // mortar sides: the maximum (conforming: = fbar)
+            FT f2d[4][NP];           // 2 d_ij across the face (time-step check)
+            double ibar[NIF];        // bar-state density across interior subcell interfaces
+            FT i2d[NIF];
+        };
+        struct {                 // P2b - P5
+            double Ad[NIF][4];       // antidiffusive flux A = Fdg - Ffv in FP64
+            float Af[NIF][4];        // and in FP32
+            unsigned char ex[NIF];   // density antidiffusion below the tolerance (R15)
+        };
+    };
+    union {
+        struct {                 // P1 - P2b
+            FT Ffv[F32 ? NIF : 1][4];  // FP32 form: the low-order subcell flux in FP32
+            double Fv[NIF][4];       // the low-order subcell flux in FP64, for the residual sums
+            FT Fdg[NIF][4];          // mass-weighted high-order subcell flux w_r * fhat (flux type)
+        };
+        struct {                 // P3 - P5
+            double Rp[NN], Rm[NN], ell[NIF];
+        };
+    };
+    union {
+        double u[4][NN];         // P0 - P2 (in P2 each node reads only its own entries)
+        double lfv[4][NN];       // P2 - P5: low-order residual (rhs mode)
+    };
     // per-element constants: 4/(dx dy), dx dy / 4, stage dt, 4 dt / (dx dy),
     // half and quarter edge lengths (and FP32 copies), (dx dy / 4) / dt
     double iA4, A4, dt, dt4A, hx, hy, qx, qy;
     float hxf, hyf, qxf, qyf, idtmf;
-    FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
-    union {
-        FT pair[2][NP][NPAIR][4];   // two-point fluxes (dead after the Sbar contraction)
-        struct {
-            double Ad[NIF][4];       // antidiffusive flux A = Fdg - Ffv in FP64
-            float Af[NIF][4];        // and in FP32
-        } a;
-    } un;
 };
 
 template <int NP>
@@ -280,7 +302,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             Prim<FT> pa = load_prim<NP, FT>(S, nodeid<NP>(d, r, a)), pb = load_prim<NP, FT>(S, nodeid<NP>(d, r, b));
             FT f[4];
             ranocha<FT>(pa, pb, d, ginv1, f);
-            for (int v = 0; v < 4; ++v) S.un.pair[d][r][pi][v] = f[v];
+            for (int v = 0; v < 4; ++v) S.pair[d][r][pi][v] = f[v];
         }
         for (int k = tid; k < EPB * 4 * NP; k += NT) {
             int le = k / (4 * NP), s = (k / NP) % 4, t = k % NP, e = e0 + le;
@@ -387,7 +409,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if constexpr (F32) sv = s_Sf[l][kk];
                     else sv = s_S[l][kk];
                     int pi = PairTab<NP>::idx(l, kk);
-                    for (int v = 0; v < 4; ++v) acc[v] += sv * S.un.pair[d][r][pi][v];
+                    for (int v = 0; v < 4; ++v) acc[v] += sv * S.pair[d][r][pi][v];
                 }
             FT wh;
             if constexpr (F32) wh = s_wf[r] * (d == 0 ? S.hyf : S.hxf);
@@ -433,9 +455,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 }
                 double q[4];
                 S.dtm[n] = dtm;
+                for (int v = 0; v < 4; ++v) q[v] = S.u[v][n] + dtm * L[v];
                 for (int v = 0; v < 4; ++v) {
-                    S.lfv[v][n] = L[v];
-                    q[v] = S.u[v][n] + dtm * L[v];
+                    S.lfv[v][n] = L[v];   // shares storage with u[v][n], read above
                     S.ufv[v][n] = q[v];
                     S.ufvf[v][n] = d2f(q[v]);
                 }
@@ -534,17 +556,17 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             if constexpr (F32) {
                 for (int v = 0; v < 4; ++v) {
                     float df = S.Fdg[id][v] - S.Ffv[id][v];
-                    S.un.a.Af[id][v] = df;
-                    S.un.a.Ad[id][v] = f2d(df);
+                    S.Af[id][v] = df;
+                    S.Ad[id][v] = f2d(df);
                 }
-                S.ex[id] = fabsf(S.un.a.Af[id][0]) <= fminf(S.tqf[nl], S.tqf[nr]);
+                S.ex[id] = fabsf(S.Af[id][0]) <= fminf(S.tqf[nl], S.tqf[nr]);
             } else {
                 for (int v = 0; v < 4; ++v) {
                     double dd = S.Fdg[id][v] - S.Fv[id][v];
-                    S.un.a.Ad[id][v] = dd;
-                    S.un.a.Af[id][v] = d2f(dd);
+                    S.Ad[id][v] = dd;
+                    S.Af[id][v] = d2f(dd);
                 }
-                double aa = fabs(S.un.a.Ad[id][0]);
+                double aa = fabs(S.Ad[id][0]);
                 S.ex[id] = !nn_lt(S.tol[nl], S.dtm[nl] * aa) && !nn_lt(S.tol[nr], S.dtm[nr] * aa);
             }
         }
@@ -567,7 +589,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     int a = side == 0 ? pos - 1 : pos;
                     int id = ifid<NP>(d, row, a);
                     if (S.ex[id]) continue;
-                    double Ar = S.un.a.Ad[id][0];
+                    double Ar = S.Ad[id][0];
                     double G = side == 0 ? Ar : -Ar;
                     // one add into the sum that matches the sign of G
                     const bool pos_g = __double_as_longlong(G) > 0;
@@ -606,7 +628,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             int d = id / (NP * N), r = (id / N) % NP, a = id % N;
             SM &S = sm[le];
             int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
-            double Ar = S.un.a.Ad[id][0];
+            double Ar = S.Ad[id][0];
             double lr = S.ex[id] ? 1.0
                                  : dneg(Ar) ? nn_min(S.Rp[nl], S.Rm[nr]) : nn_min(S.Rm[nl], S.Rp[nr]);
             double th = lr;
@@ -616,13 +638,13 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 float sgf = side == 0 ? -4.0f : 4.0f;
                 float u0f[4], af[4];
                 float sdf = sgf * S.dtmf[nd];
-                for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.un.a.Af[id][v]; }
+                for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.Af[id][v]; }
                 // a certified FP32 yes implies c0 > 0 and rho_FV > 0
                 if (admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], d2f(th)))
                     continue;   // the whole interval [0, th] is admissible
                 double u0[4], av[4];
                 double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
-                for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.un.a.Ad[id][v]; }
+                for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.Ad[id][v]; }
                 th = theta_max(gm1, u0, av, S.gms[nd], S.pms[nd], S.c0[nd], th);
             }
             S.ell[id] = th;   // min over both end points (each searched below the previous)
@@ -646,13 +668,13 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if (pos > 0) {
                         int id = ifid<NP>(d, row, pos - 1);
                         double l = S.ell[id];
-                        for (int v = 0; v < 4; ++v) sacc[v] += l * S.un.a.Ad[id][v];
+                        for (int v = 0; v < 4; ++v) sacc[v] += l * S.Ad[id][v];
                         lmin = nn_min(lmin, l);
                     }
                     if (pos < N) {
                         int id = ifid<NP>(d, row, pos);
                         double l = S.ell[id];
-                        for (int v = 0; v < 4; ++v) sacc[v] -= l * S.un.a.Ad[id][v];
+                        for (int v = 0; v < 4; ++v) sacc[v] -= l * S.Ad[id][v];
                         lmin = nn_min(lmin, l);
                     }
                 }
