@@ -210,12 +210,21 @@ idp_status idp_dgsem_profile(idp_ctx *ctx, int32_t mode);
 idp_status idp_dgsem_profile_read(idp_ctx *ctx, double *element_ms, int64_t *element_launches,
                                   double *step_ms, int64_t *steps, int32_t reset);
 
-/* Pipe-throughput probe used as the roofline denominator (no counterpart in
- * the paper): runs short kernels on the current device and stream and writes
- * out[0] FP64 TFLOP/s (DFMA, 2 flops each), out[1] FP32 TFLOP/s (FFMA),
- * out[2..4] the cost of one FP64 division, square root and logarithm
- * (CUDA's routines, each plus one add) in DFMA-equivalents. Synchronises. */
+/* Pipe-throughput probe used for the roofline (no counterpart in the paper):
+ * runs short kernels on the current device and stream and writes out[0] FP64
+ * TFLOP/s (DFMA, 2 flops each), out[1] FP32 TFLOP/s (FFMA), out[2..4] the
+ * cost of one FP64 reciprocal, square root and logarithm as the FP64 flux
+ * arithmetic forms them (each plus one add) in DFMA-equivalents.
+ * Synchronises. */
 idp_status idp_probe_pipes(double *out, void *stream);
+
+/* Test hook (no counterpart in the paper): y[i] = f(x[i]) for i < n with the
+ * FP64 routines of the flux arithmetic, f = 1/x (fn 0), sqrt(x) (fn 1) or
+ * ln(x) (fn 2); x and y are caller-owned device arrays of n doubles; inputs
+ * are meant to be positive, finite and normal. Runs on the given stream and
+ * synchronises it. IDP_E_ARG for fn outside 0..2, n < 0 or null pointers with
+ * n > 0; IDP_E_CUDA on a CUDA failure. */
+idp_status idp_eval_math(int32_t fn, const double *x, double *y, int64_t n, void *stream);
 
 /* Largest element count accepted by idp_integrals_noalloc. */
 #define IDP_NOALLOC_MAX_ELEMS (1 << 19)

@@ -11,6 +11,7 @@
 #include <stdint.h>
 
 #include "idp_bits.cuh"
+#include "idp_fastmath.cuh"
 
 namespace idp {
 
@@ -53,6 +54,7 @@ struct Ops {
     int pk[3 * NPMAX], pr[3 * NPMAX];
     int slot_n[3 * NPMAX];
     int slot_p[3 * NPMAX][2 * NPMAX];
+    LogTab lg;                       // table of the FP64 logarithm
 };
 
 // Per simulation: boundary data (ghost states as conserved variables).
@@ -112,9 +114,11 @@ struct SlotsDev {
 struct Gas {
     double g, gm1, ginv1;
     float gf, gm1f, ginv1f;
+    const LogTab *lg;   // device table of fast_log
 };
-inline Gas make_gas(double gamma) {
+inline Gas make_gas(double gamma, const LogTab *lg) {
     Gas G;
+    G.lg = lg;
     G.g = gamma; G.gm1 = gamma - 1.0; G.ginv1 = 1.0 / (gamma - 1.0);
     G.gf = (float)G.g; G.gm1f = (float)G.gm1; G.ginv1f = (float)G.ginv1;
     return G;
@@ -150,7 +154,9 @@ __device__ __forceinline__ void log_means(const Prim<FT> &a, const Prim<FT> &b, 
         lb = nb ? FT(0) : (FT)logf((float)(a.beta / b.beta));
     }
     FT Xr = nr ? sr : lr, Xb = nb ? sb : db;
-    FT R = FT(1) / (Xr * Xb);
+    FT R;
+    if constexpr (dbl) R = fast_rcp(Xr * Xb);
+    else R = FT(1) / (Xr * Xb);
     FT ixr = Xb * R, ixb = Xr * R;   // 1/Xr, 1/Xb
     if (nr) {
         FT f = dr * ixr, u = f * f;
@@ -202,19 +208,19 @@ template <typename FT>
 __device__ __forceinline__ Prim<FT> make_prim(const Gas &G, double r, double m1, double m2, double E, bool full) {
     const double g = G.g;
     Prim<FT> q;
-    double ri = __drcp_rn(r);
+    double ri = fast_rcp(r);
     double v1 = __dmul_rn(m1, ri), v2 = __dmul_rn(m2, ri);
     double ke = __dmul_rn(0.5, __dadd_rn(__dmul_rn(m1, v1), __dmul_rn(m2, v2)));
     double p = __dmul_rn(G.gm1, __dadd_rn(E, -ke));
     q.rho = (FT)r; q.v1 = (FT)v1; q.v2 = (FT)v2; q.p = (FT)p; q.E = (FT)E;
     q.lr = q.lb = FT(0);
     if (sizeof(FT) == 8) {
-        q.c = (FT)__dsqrt_rn(__dmul_rn(__dmul_rn(g, p), ri));
+        q.c = (FT)fast_sqrt(__dmul_rn(__dmul_rn(g, p), ri));
         if (full) {
-            q.beta = (FT)(r / p);
-            double lr = log(r);
+            q.beta = (FT)__dmul_rn(r, fast_rcp(p));
+            double lr = fast_log(r, G.lg);
             q.lr = (FT)lr;
-            q.lb = (FT)(lr - log(p));
+            q.lb = (FT)(lr - fast_log(p, G.lg));
         } else {
             q.beta = FT(0);
         }

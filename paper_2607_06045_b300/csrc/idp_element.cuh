@@ -353,7 +353,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double wh = s_w[t] * (d == 0 ? S.hy : S.hx);
                 for (int v = 0; v < 4; ++v) S.face[s][t][v] = wh * f[v];
                 S.f2d[s][t] = wh * lam;
-                i2l = 0.5 / lam;
+                i2l = 0.5 * fast_rcp(lam);
             }
             double sg = (s == 1 || s == 3) ? 1.0 : -1.0;
             double fb = 0.5 * (S.u[0][n] + out[0]) - sg * (out[1 + d] - S.u[1 + d][n]) * i2l;
@@ -390,7 +390,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 S.i2d[id] = FT(2) * cc * lam;
                 double i2l;
                 if constexpr (F32) i2l = f2d(0.5f / lam);
-                else i2l = 0.5 / lam;
+                else i2l = 0.5 * fast_rcp(lam);
                 S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * i2l;
             }
         }

@@ -107,8 +107,29 @@ bool invert(int n, double *A) {
     return true;
 }
 
+// Table of the FP64 logarithm (Tang's method): 1 / F_j and ln F_j as head +
+// tail for F_j = 1 + j/128, and ln 2 with a 42-bit head; formed in long double.
+void host_log_table_impl(LogTab &T) {
+    for (int j = 0; j < kLogTab; ++j) {
+        const long double F = 1.0L + (long double)j / kLogTab;
+        T.inv[j] = (double)(1.0L / F);
+        const long double l = logl(F);
+        T.hi[j] = (double)l;
+        T.lo[j] = (double)(l - (long double)T.hi[j]);
+    }
+    const long double ln2 = logl(2.0L);
+    double h = (double)ln2;
+    uint64_t b;
+    std::memcpy(&b, &h, sizeof(b));
+    b &= ~((uint64_t(1) << 11) - 1);   // keep 42 significant bits
+    std::memcpy(&h, &b, sizeof(b));
+    T.ln2_hi = h;
+    T.ln2_lo = (double)(ln2 - (long double)h);
+}
+
 void build_ops(int N, int proj, Ops &o) {
     std::memset(&o, 0, sizeof(o));
+    host_log_table_impl(o.lg);
     const int np = N + 1;
     double x[NPMAX], w[NPMAX], lam[NPMAX];
     lgl_nodes(N, x, w);
@@ -368,6 +389,9 @@ std::map<long long, std::pair<int, int>> g_tune_cache;   // key -> (epb, persist
 }  // namespace
 
 namespace idp {
+// table of the FP64 logarithm (used by the probes and the test hook)
+void host_log_table(LogTab &T) { host_log_table_impl(T); }
+
 // LGL quadrature weights for degree N (used by the allocation-free integrals)
 void host_lgl_weights(int N, double *w) {
     double x[NPMAX];
@@ -441,7 +465,7 @@ StageArgs base_args(idp_ctx *c) {
     A.cfl = c->opt.cfl;
     A.t_sim = c->d_tsim;
     A.beta = c->opt.beta;
-    A.gas = make_gas(c->gamma);
+    A.gas = make_gas(c->gamma, &c->d_ops->lg);
     A.ops = c->d_ops;
     A.status = c->d_status;
     A.stats = c->d_stats;
@@ -469,10 +493,10 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) 
     k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
     if (c->M > 0 && mortar_flux && c->opt.dt_rule == 0) {
         const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
-        c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, u, make_gas(c->gamma), c->d_ops);
+        c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->d_ops);
     }
     int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
-    c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, make_gas(c->gamma), c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
+    c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
             c->d_status);
 }
 

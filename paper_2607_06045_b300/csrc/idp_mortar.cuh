@@ -112,7 +112,7 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
         FT hw, i2l_f;
         double i2l;
         if constexpr (F32) { hw = d2f(0.5 * wt); i2l_f = 0.5f / lam; i2l = f2d(i2l_f); }
-        else { hw = 0.5 * wt; i2l = 0.5 / lam; }
+        else { hw = 0.5 * wt; i2l = 0.5 * fast_rcp(lam); }
         for (int v = 0; v < 4; ++v) {
             FT term = hw * ((sgf * fa[v] + sgf * fb[v]) - lam * (bf[v] - af[v]));
             if constexpr (F32) s_term[warp][lane][v] = f2d(term);

@@ -51,7 +51,7 @@ _lib = None
 EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", "idp_dgsem_layout",
            "idp_dgsem_rhs", "idp_dgsem_dt", "idp_dgsem_step", "idp_dgsem_step_host", "idp_dgsem_integrals",
            "idp_dgsem_limiter_stats", "idp_dgsem_sync", "idp_dgsem_destroy", "idp_status_str",
-           "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_probe_pipes",
+           "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_probe_pipes", "idp_eval_math",
            "idp_integrals_noalloc"]
 
 
@@ -84,6 +84,7 @@ def lib():
         L.idp_dgsem_profile.argtypes = [vp, C.c_int32]
         L.idp_dgsem_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64), dp, C.POINTER(C.c_int64), C.c_int32]
         L.idp_probe_pipes.argtypes = [dp, vp]
+        L.idp_eval_math.argtypes = [C.c_int32, vp, vp, C.c_int64, vp]
         L.idp_integrals_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.c_int32, vp, vp]
         L.idp_dgsem_destroy.restype = None
         for f in EXPORTS:
@@ -112,6 +113,14 @@ def idp_probe_pipes(stream=None):
     out = (C.c_double * 5)()
     _check(lib().idp_probe_pipes(out, _stream(stream)), "idp_probe_pipes")
     return list(out)
+
+
+def idp_eval_math(fn, x, y, stream=None):
+    """y = f(x) elementwise on CUDA FP64 tensors with the library's FP64 routines
+    (fn 0: 1/x, 1: sqrt, 2: ln)."""
+    assert x.is_cuda and y.is_cuda and x.dtype == y.dtype and x.numel() == y.numel()
+    _check(lib().idp_eval_math(int(fn), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(),
+                               _stream(stream)), "idp_eval_math")
 
 
 NOALLOC_MAX_ELEMS = 1 << 19
