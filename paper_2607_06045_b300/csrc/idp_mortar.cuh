@@ -300,17 +300,23 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
 
 // Time step: per node m_i / sum_j 2 d_ij (rule 0) or min over directions of
 // (w_i h / 2) / (|v| + c) (rule 1); minimum per simulation as ordered bits.
-// One block holds EPB elements, one thread per node; each node's wave speeds
-// |v_x| + c and |v_y| + c are formed once and shared through shared memory.
-// In the FP32 form (FT = float) the wave speeds, sums and the quotient are
-// FP32 and the result is scaled by (1 - 4e-6), more than the FP32 rounding of
-// these few operations, so the step never exceeds the FP64 limit.
+// One block holds EPB elements, one thread per node. Three uniform passes:
+// each node's wave speeds |v_x| + c and |v_y| + c; per face node the outside
+// wave speed along the face normal (conforming neighbour or ghost state) or
+// the mortar's 2d sum; then the per-node sums. In the FP32 form (FT = float)
+// the wave speeds, sums and the quotient are FP32 and the result is scaled by
+// (1 - 4e-6), more than the FP32 rounding of these few operations, so the
+// step never exceeds the FP64 limit.
 template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads)
 k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule, const Ops *ops,
      const double *t_sim, unsigned long long *dtmin, unsigned *status) {
     constexpr int NN = NP * NP, N = NP - 1, NT = ElemLaunch<NP, EPB>::threads;
-    __shared__ FT s_l[EPB][2][NN];
+    constexpr bool F32 = sizeof(FT) == 4;
+    __shared__ FT s_l[EPB][2][NN];       // |v_x| + c, |v_y| + c per node
+    __shared__ FT s_o[EPB][4][NP];       // outside wave speed, or 2d sum of a mortar side
+    __shared__ double s_w[NP];
+    if (threadIdx.x < NP) s_w[threadIdx.x] = ops->w[threadIdx.x];
     const size_t KN = (size_t)mesh.K * NN;
     const Gas &g = gas;
     for (int e0 = blockIdx.x * EPB; e0 < mesh.K; e0 += gridDim.x * EPB) {
@@ -320,84 +326,102 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
             size_t gi = (size_t)e * NN + n;
             double qd[4] = {u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi]};
             Prim<FT> q = mortar_prim<NP, FT>(g, qd);
-            if (!(qd[0] > 0.0) || !(q.p > FT(0))) atomicOr(status, ST_BAD_INPUT);
+            bool okp;
+            if constexpr (F32) okp = q.p > 0.0f;
+            else okp = dpos(q.p);
+            if (!dpos(qd[0]) || !okp) atomicOr(status, ST_BAD_INPUT);
             s_l[le][0][n] = fabs(q.v1) + q.c;
             s_l[le][1][n] = fabs(q.v2) + q.c;
         }
+        if (rule == 0) {
+            for (int k = threadIdx.x; k < EPB * 4 * NP; k += NT) {
+                int le = k / (4 * NP), s = (k / NP) % 4, t = k % NP, e = e0 + le;
+                if (e >= mesh.K) continue;
+                const uchar4 ftv = mesh.ftype[e];
+                const int4 nb4 = mesh.fnbr[e];
+                const int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
+                const int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
+                if (ft == FT_CONF || ft == FT_BND) {
+                    double uo[4];
+                    if (ft == FT_CONF) {
+                        size_t ko = (size_t)nb * NN + face_node<NP>(s ^ 1, t);
+                        for (int v = 0; v < 4; ++v) uo[v] = u[v * KN + ko];
+                    } else {
+                        const int n = face_node<NP>(s, t), i = n % NP, sim = mesh.sim[e];
+                        const Geo geo = mesh.geom[e];
+                        size_t gi = (size_t)e * NN + n;
+                        double ui[4] = {u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi]};
+                        double xn = geo.x + 0.5 * geo.z * (1.0 + ops->xi[i]);
+                        ghost_state(mesh.siminfo[sim], s, ui, xn, t_sim[sim], uo);
+                    }
+                    Prim<FT> po = mortar_prim<NP, FT>(g, uo);
+                    s_o[le][s][t] = fabs((s >> 1) == 0 ? po.v1 : po.v2) + po.c;
+                } else {
+                    s_o[le][s][t] = to_ft<FT>(sl.dsum[slot_of<NP>(ft, nb, t)]);
+                }
+            }
+        }
         __syncthreads();
-        double best = INFINITY;
+        unsigned long long best = dbits(INFINITY);
         int bsim = -1;
         for (int k = threadIdx.x; k < EPB * NN; k += NT) {
             int le = k / NN, n = k - le * NN, e = e0 + le;
             if (e >= mesh.K) continue;
-            int i = n % NP, j = n / NP;
-            const Geo geo = mesh.geom[e];
+            const int i = n % NP, j = n / NP;
+            const GeoC gc = mesh.geoc[e];
             const int sim = mesh.sim[e];
             double val;
             if (rule == 1) {
-                if constexpr (sizeof(FT) == 4)
-                    val = (double)fminf((float)(ops->w[i] * geo.z / 2.0) / s_l[le][0][n],
-                                        (float)(ops->w[j] * geo.w / 2.0) / s_l[le][1][n]) * (1.0 - 4e-6);
+                if constexpr (F32)
+                    val = f2d(fminf(d2f(s_w[i] * gc.hx) / s_l[le][0][n], d2f(s_w[j] * gc.hy) / s_l[le][1][n]) *
+                              (1.0f - 4e-6f));
                 else
-                    val = fmin(ops->w[i] * geo.z / 2.0 / s_l[le][0][n], ops->w[j] * geo.w / 2.0 / s_l[le][1][n]);
+                    val = fmin(s_w[i] * gc.hx * fast_rcp(s_l[le][0][n]), s_w[j] * gc.hy * fast_rcp(s_l[le][1][n]));
             } else {
-                FT ds = FT(0);
                 const uchar4 ftv = mesh.ftype[e];
-                const int4 nb4 = mesh.fnbr[e];
+                FT ds = FT(0);
+#pragma unroll
                 for (int d = 0; d < 2; ++d) {
-                    int pos = d == 0 ? i : j, row = d == 0 ? j : i;
-                    FT cc = (FT)(ops->w[row] * (d == 0 ? geo.w : geo.z) / 4.0);
-                    FT li = s_l[le][d][n];
+                    const int pos = d == 0 ? i : j, row = d == 0 ? j : i;
+                    FT cc2;   // 2 c_ij = w_row |face| / 2
+                    if constexpr (F32) cc2 = d2f(s_w[row]) * (d == 0 ? gc.hyf : gc.hxf);
+                    else cc2 = s_w[row] * (d == 0 ? gc.hy : gc.hx);
+                    const FT li = s_l[le][d][n];
+#pragma unroll
                     for (int side = 0; side < 2; ++side) {
-                        bool interior = side == 0 ? pos > 0 : pos < N;
-                        if (interior) {
-                            int on = d == 0 ? n + (side == 0 ? -1 : 1) : n + (side == 0 ? -NP : NP);
-                            FT lo = s_l[le][d][on];
-                            ds += FT(2) * cc * (li > lo ? li : lo);
-                        } else {
-                            int s = 2 * d + side;
-                            int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
-                            int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
-                            if (ft == FT_CONF || ft == FT_BND) {
-                                double uo[4];
-                                if (ft == FT_CONF) {
-                                    size_t ko = (size_t)nb * NN + face_node<NP>(s ^ 1, row);
-                                    for (int v = 0; v < 4; ++v) uo[v] = u[v * KN + ko];
-                                } else {
-                                    size_t gi = (size_t)e * NN + n;
-                                    double ui[4] = {u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi]};
-                                    double xn = geo.x + 0.5 * geo.z * (1.0 + ops->xi[i]);
-                                    ghost_state(mesh.siminfo[sim], s, ui, xn, t_sim[sim], uo);
-                                }
-                                Prim<FT> po = mortar_prim<NP, FT>(g, uo);
-                                FT lo = fabs(d == 0 ? po.v1 : po.v2) + po.c;
-                                ds += FT(2) * cc * (li > lo ? li : lo);
-                            } else {
-                                ds += (FT)sl.dsum[slot_of<NP>(ft, nb, row)];
-                            }
-                        }
+                        const bool interior = side == 0 ? pos > 0 : pos < N;
+                        const int s = 2 * d + side;
+                        const int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
+                        const int on = d == 0 ? n + (side == 0 ? -1 : 1) : n + (side == 0 ? -NP : NP);
+                        const FT lo = interior ? s_l[le][d][interior ? on : n] : s_o[le][s][row];
+                        const bool mort = !interior && ft != FT_CONF && ft != FT_BND;
+                        ds += mort ? lo : cc2 * (li > lo ? li : lo);
                     }
                 }
-                double mi = geo.z * geo.w / 4.0 * ops->w[i] * ops->w[j];
-                if constexpr (sizeof(FT) == 4) val = (double)((float)mi / ds) * (1.0 - 4e-6);
-                else val = mi / ds;
+                if constexpr (F32) val = f2d(gc.A4f * d2f(s_w[i] * s_w[j]) / ds * (1.0f - 4e-6f));
+                else val = gc.A4 * (s_w[i] * s_w[j]) * fast_rcp(ds);
             }
+            // positive doubles order like their bits
+            const unsigned long long vb = dbits(val);
             if (sim != bsim) {
-                if (bsim >= 0 && best < INFINITY) atomicMin(&dtmin[bsim], dbits(best));
+                if (bsim >= 0 && best < dbits(INFINITY)) atomicMin(&dtmin[bsim], best);
                 bsim = sim;
-                best = INFINITY;
+                best = dbits(INFINITY);
             }
-            if (val > 0.0 && val < best) best = val;
+            if (dpos(val) && vb < best) best = vb;
         }
         // warp minimum among the lanes that share lane 0's simulation, then
         // one atomic per warp (other simulations: one atomic per lane)
         {
-            int s0 = __shfl_sync(0xffffffffu, bsim, 0);
-            bool same = bsim == s0;
-            double bw = same ? best : INFINITY;
-            for (int o = 16; o > 0; o >>= 1) bw = fmin(bw, __shfl_down_sync(0xffffffffu, bw, o));
-            if ((threadIdx.x & 31) == 0 && s0 >= 0 && bw < INFINITY) atomicMin(&dtmin[s0], dbits(bw));
-            if (!same && bsim >= 0 && best < INFINITY) atomicMin(&dtmin[bsim], dbits(best));
+            const int s0 = __shfl_sync(0xffffffffu, bsim, 0);
+            const bool same = bsim == s0;
+            unsigned long long bw = same ? best : dbits(INFINITY);
+            for (int o = 16; o > 0; o >>= 1) {
+                const unsigned long long ob = __shfl_down_sync(0xffffffffu, bw, o);
+                bw = ob < bw ? ob : bw;
+            }
+            if ((threadIdx.x & 31) == 0 && s0 >= 0 && bw < dbits(INFINITY)) atomicMin(&dtmin[s0], bw);
+            if (!same && bsim >= 0 && best < dbits(INFINITY)) atomicMin(&dtmin[bsim], best);
         }
         __syncthreads();
     }
