@@ -147,11 +147,10 @@ __device__ __forceinline__ int slot_of(int ft, int m, int t) {
 // Per-warp reduction of the limiter statistics, then one atomic per warp and
 // field. Counts reduce as integers, the alpha sum in FP32 (a diagnostic
 // mean), the minimum density on the integer order of positive doubles, and
-// the minimum pressure over limited nodes as a ratio rho p / rho compared
-// without division; FP64 arithmetic only runs in warps that hold a limited
-// node.
+// the minimum pressure (a diagnostic, FP32) as a ratio compared without
+// division.
 __device__ __forceinline__ void block_stats(const StageArgs &A, float am, unsigned nact, unsigned nvr, unsigned nvp,
-                                            unsigned nnp, double rmin_, double pn, double pd) {
+                                            unsigned nnp, double rmin_, float pn, float pd) {
     const unsigned FULL = 0xffffffffu;
     nact = __reduce_add_sync(FULL, nact);
     nvr = __reduce_add_sync(FULL, nvr);
@@ -164,12 +163,12 @@ __device__ __forceinline__ void block_stats(const StageArgs &A, float am, unsign
         unsigned long long ok = __shfl_down_sync(FULL, rk, o);
         rk = ok < rk ? ok : rk;
     }
-    const bool anyp = __any_sync(FULL, __double_as_longlong(pd) > 0);
+    const bool anyp = __any_sync(FULL, pd > 0.0f);
     if (anyp) {
         for (int o = 16; o > 0; o >>= 1) {
-            double qn = __shfl_down_sync(FULL, pn, o), qd = __shfl_down_sync(FULL, pd, o);
-            const bool have = __double_as_longlong(pd) > 0, other = __double_as_longlong(qd) > 0;
-            if (other && (!have || dlt(qn * pd, pn * qd))) { pn = qn; pd = qd; }
+            float qn = __shfl_down_sync(FULL, pn, o), qd = __shfl_down_sync(FULL, pd, o);
+            const bool have = pd > 0.0f, other = qd > 0.0f;
+            if (other && (!have || qn * pd < pn * qd)) { pn = qn; pd = qd; }
         }
     }
     if ((threadIdx.x & 31) == 0) {
@@ -179,8 +178,8 @@ __device__ __forceinline__ void block_stats(const StageArgs &A, float am, unsign
         if (nvp) atomicAdd(&A.stats->n_vp, (unsigned long long)nvp);
         if (nnp) atomicAdd(&A.stats->n_nonpos, (unsigned long long)nnp);
         if (rk > 0ull && rk < 0x7FF0000000000000ull) atomicMin(&A.stats->min_rho_bits, rk);
-        if (anyp && __double_as_longlong(pd) > 0) {
-            double pmin_ = pn / pd;
+        if (anyp && pd > 0.0f) {
+            const double pmin_ = f2d(pn / pd);
             if (dpos(pmin_)) atomicMin(&A.stats->min_p_bits, dbits(pmin_));
         }
     }
@@ -443,7 +442,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         const double bhi = interior ? S.ibar[id] : S.fbar2[s][row];
                         const FT dsv = interior ? S.i2d[id] : S.f2d[s][row];
                         for (int v = 0; v < 4; ++v) {
-                            if (side == 0) L[v] += fl[v];
+                            if (d == 0 && side == 0) L[v] = fl[v];
+                            else if (side == 0) L[v] += fl[v];
                             else L[v] -= fl[v];
                         }
                         long long kb = okey(blo);
@@ -653,8 +653,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
 
         // ---------------- P5: blend, outputs, mortar hand-off, stats --------
         {
-            float st_am = 0.0f;
-            double st_rmin = INFINITY, st_pn = 0.0, st_pd = 0.0;
+            float st_am = 0.0f, st_pn = 0.0f, st_pd = 0.0f;
+            double st_rmin = INFINITY;
             unsigned st_act = 0, st_vr = 0, st_vp = 0, st_np = 0;
             for (int k = tid; k < EPB * NN; k += NT) {
                 int le = k / NN, n = k - le * NN, e = e0 + le;
@@ -728,20 +728,30 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     const bool act = nn_lt(lmin, 1.0);
                     if (act) { st_am += d2f(S.A4) * s_wwf[n] * (1.0f - d2f(lmin)); st_act++; }
                     if (nmort == 0) {
-                        // rho p = (gamma-1)(rho E - |m|^2/2): checks without division;
-                        // p >= p_min  <=>  rho p rho_FV >= (p_min rho_FV) rho
-                        double rp = gm1 * (uvol[0] * uvol[3] - 0.5 * (uvol[1] * uvol[1] + uvol[2] * uvol[2]));
                         const double rmn = S.rmin[n], rmx = S.rmax[n];
                         if (dlt(uvol[0], rmn - kViolTol * fabs(rmn)) || dlt(rmx + kViolTol * fabs(rmx), uvol[0]))
                             st_vr++;
-                        if (dlt(rp * S.ufv[0][n], S.pms[n] * (1.0 - kViolTol) * uvol[0])) st_vp++;
-                        if (!dpos(uvol[0]) || !dpos(rp)) st_np++;
                         st_rmin = dmin(st_rmin, uvol[0]);
-                        // minimum p = rho p / rho over limited nodes, kept as a ratio
-                        if (act && dpos(uvol[0]) &&
-                            (!(__double_as_longlong(st_pd) > 0) || dlt(rp * st_pd, st_pn * uvol[0]))) {
-                            st_pn = rp; st_pd = uvol[0];
+                        // p >= p_min  <=>  (gamma-1)(rho E - |m|^2/2) rho_FV >= (p_min rho_FV) rho,
+                        // first certified in FP32: with inputs rounded once, the
+                        // FP32 difference stays within 9 unit roundings of the
+                        // sum S of the absolute terms, so a difference above
+                        // 4e-6 S proves it (and p > 0) exactly; else FP64
+                        const float u0 = d2f(uvol[0]), u1 = d2f(uvol[1]), u2 = d2f(uvol[2]), u3 = d2f(uvol[3]);
+                        const float t1 = u0 * u3, t2 = 0.5f * (u1 * u1 + u2 * u2);
+                        const float gr = G.gm1f * S.ufvf[0][n];
+                        const float lhs = gr * (t1 - t2), rhs = S.pmsf[n] * u0;
+                        const float Sab = gr * (fabsf(t1) + t2) + fabsf(rhs);
+                        const bool cert = dpos(uvol[0]) && Sab > 1e-30f && Sab < 1e30f && lhs - rhs > 4e-6f * Sab;
+                        float pmin_n = u0 > 0.0f ? (G.gm1f * (t1 - t2)) / (u0 * u0) : 0.0f;   // statistic only
+                        if (!cert) {
+                            const double rp = gm1 * (uvol[0] * uvol[3] - 0.5 * (uvol[1] * uvol[1] + uvol[2] * uvol[2]));
+                            if (dlt(rp * S.ufv[0][n], S.pms[n] * (1.0 - kViolTol) * uvol[0])) st_vp++;
+                            if (!dpos(uvol[0]) || !dpos(rp)) st_np++;
+                            pmin_n = dpos(uvol[0]) ? d2f(rp) / u0 : 0.0f;
                         }
+                        // minimum p over limited nodes (FP32 statistic)
+                        if (act && pmin_n > 0.0f && !(st_pd > 0.0f && st_pn <= pmin_n)) { st_pn = pmin_n; st_pd = 1.0f; }
                     }
                 }
             }

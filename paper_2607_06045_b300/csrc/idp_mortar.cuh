@@ -254,7 +254,8 @@ template <int NP>
 __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
     constexpr int NN = NP * NP, Q = 3 * NP;
     const size_t KN = (size_t)mesh.K * NN;
-    double st_rmin = INFINITY, st_pmin = 0.0, st_one = 0.0;   // min p as the ratio st_pmin / st_one
+    double st_rmin = INFINITY;
+    float st_pmin = 0.0f, st_one = 0.0f;   // minimum p (FP32 statistic) as the ratio st_pmin / st_one
     unsigned vr = 0, vp = 0, np_ = 0;
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mesh.n_mnodes; k += gridDim.x * blockDim.x) {
         const int gnode = mesh.mn_node[k];
@@ -291,7 +292,8 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
             if (p < pmin - kViolTol * fabs(pmin)) vp++;
             if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
             st_rmin = dmin(st_rmin, ut[0]);
-            if (st_one == 0.0 || dlt(p, st_pmin)) { st_pmin = p; st_one = 1.0; }
+            const float pf = d2f(p);
+            if (pf > 0.0f && (st_one == 0.0f || pf < st_pmin)) { st_pmin = pf; st_one = 1.0f; }
         }
     }
     if (A.collect) block_stats(A, 0.0f, 0u, vr, vp, np_, st_rmin, st_pmin, st_one);
