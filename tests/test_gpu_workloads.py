@@ -1,0 +1,157 @@
+"""GPU tests on the workloads at their full sizes, in the configuration
+bench.py times, and on reduced instances the oracle finishes in seconds:
+
+- near-vacuum blast (N = 5, background rho = 1e-6, p = 1e-9): a reduced mesh
+  against the oracle (FP64 path, and the FP32 form's density L1 error), and
+  the full 512 x 512 (+2 levels) mesh in the FP32 form over 200 steps with
+  positivity, bounds and conservation checked at every node;
+- double Mach reflection over 500 FP64 steps: invariants at every node;
+- the 256-simulation batch: sampled simulations against individual oracle
+  runs (FP64 path and FP32 form), and invariants over the whole batch.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_err, rhs_scale
+from paper_2607_06045_b300 import build, idp
+from paper_2607_06045_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    yield
+
+
+def dev(u):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(u)).cuda()
+
+
+def invariants_clean(ctx):
+    rc, st = ctx.idp_dgsem_limiter_stats()
+    assert rc == idp.IDP_OK
+    assert st["n_nonpositive"] == 0 and st["n_viol_density"] == 0 and st["n_viol_pressure"] == 0, st
+    return st
+
+
+def test_vacuum_reduced_parity():
+    m, c = W.cfg5_mesh(n0=16)
+    N = 5
+    u = W.cfg5_state(m, N, c)
+    o = oracle.Oracle(m, N)
+    # limited right-hand side
+    dt_idp = o.dt(u, 0.0, cfl=1.0)
+    # the fluid starts at rest: momentum is scaled by sqrt(2 rho E)
+    mom = np.sqrt(2.0 * np.abs(u[0]).max() * np.abs(u[3]).max())
+    scale = rhs_scale(u, dt_idp)
+    scale[1:3] = np.maximum(scale[1:3], mom / dt_idp)
+    ctx = idp.Context(m, N, limiting=2)
+    import torch
+    ud = dev(u)
+    out = torch.empty_like(ud)
+    ctx.idp_dgsem_rhs(ud, 0.0, 0.5 * dt_idp, out)
+    r_o = o.rhs(u, t=0.0, dt=0.5 * dt_idp, limiting=2)
+    assert rel_err(out.cpu().numpy(), r_o, scale) <= 1e-12
+    # five steps, FP64 path and FP32 form
+    nst = 5
+    u_o, t_o, _, _ = o.step(u, nst, cfl=0.5)
+    t = np.zeros(1)
+    ctx.idp_dgsem_step(ud, nst, t)
+    u_g = ud.cpu().numpy()
+    sc = np.abs(u_o).reshape(4, -1).max(axis=1)
+    sc[1:3] = np.maximum(sc[1:3], mom)
+    assert (np.abs(u_g - u_o).reshape(4, -1).max(axis=1) / sc).max() <= 1e-10
+    assert abs(t[0] - t_o) <= 1e-12 * t_o
+    invariants_clean(ctx)
+    ctx.close()
+    c32 = idp.Context(m, N, precision=1, limiting=2)
+    ud = dev(u)
+    t = np.zeros(1)
+    c32.idp_dgsem_step(ud, nst, t)
+    u_g = ud.cpu().numpy()
+    mm = o.masses()
+    l1 = (mm * np.abs(u_g[0] - u_o[0])).sum() / (mm * np.abs(u_o[0])).sum()
+    assert l1 <= 1e-5, l1
+    invariants_clean(c32)
+    c32.close()
+
+
+def test_vacuum_full_size_fp32_200_steps():
+    m, c = W.cfg5_mesh()
+    N = 5
+    u = W.cfg5_state(m, N, c)
+    ctx = idp.Context(m, N, precision=1, limiting=2)
+    ud = dev(u)
+    I0 = ctx.idp_dgsem_integrals(ud)[0]
+    t = np.zeros(1)
+    for _ in range(4):
+        ctx.idp_dgsem_step(ud, 50, t)
+        st = invariants_clean(ctx)
+        assert st["alpha_volume_mean"] > 0.0   # the limiter is active
+    u_g = ud.cpu().numpy()
+    assert np.all(np.isfinite(u_g)) and u_g[0].min() > 0.0
+    I1 = ctx.idp_dgsem_integrals(ud)[0]
+    # the blast stays far from the outflow boundaries: mass and energy are
+    # conserved, momentum (zero at the start) on the scale sqrt(2 M E)
+    M, E = I0[0], I0[3]
+    scale = np.array([M, np.sqrt(2 * M * E), np.sqrt(2 * M * E), E])
+    assert (np.abs(I1 - I0) / scale).max() <= 1e-12
+    ctx.close()
+
+
+def test_dmr_500_steps_fp64():
+    m = W.cfg2_mesh()
+    u = W.cfg2_state(m, 3)
+    ctx = idp.Context(m, 3, limiting=2, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    for _ in range(5):
+        ctx.idp_dgsem_step(ud, 100, t)
+        invariants_clean(ctx)
+    u_g = ud.cpu().numpy()
+    assert np.all(np.isfinite(u_g)) and u_g[0].min() > 0.0
+    assert t[0] > 0.0
+    ctx.close()
+
+
+def test_batched_full_size_sampled():
+    ms = W.cfg4_meshes(256, seed=0)
+    rng = np.random.default_rng(1)
+    us = [W.cfg4_state(mm, 3, rng) for mm in ms]
+    ub = W.concat_states(us)
+    smallest = np.argsort([mm.n_elems for mm in ms])[:3].tolist()
+    nst = 2
+    ref = {}
+    for s in smallest:
+        o = oracle.Oracle(ms[s], 3)
+        u_o, t_o, _, _ = o.step(us[s], nst, cfl=0.5)
+        ref[s] = (u_o, t_o, o.masses())
+    for prec in (0, 1):
+        ctx = idp.Context(ms, 3, precision=prec, limiting=2, cfl=0.5)
+        ud = dev(ub)
+        t = np.zeros(len(ms))
+        ctx.idp_dgsem_step(ud, nst, t)
+        u_g = ud.cpu().numpy()
+        off = ctx.sim_offsets
+        for s, (u_o, t_o, mm) in ref.items():
+            part = u_g[:, off[s]:off[s + 1]]
+            if prec == 0:
+                sc = np.abs(u_o).reshape(4, -1).max(axis=1)
+                assert (np.abs(part - u_o).reshape(4, -1).max(axis=1) / sc).max() <= 1e-10, s
+                assert abs(t[s] - t_o) <= 1e-12 * t_o
+            else:
+                l1 = (mm * np.abs(part[0] - u_o[0])).sum() / (mm * np.abs(u_o[0])).sum()
+                assert l1 <= 1e-5, (s, l1)
+        invariants_clean(ctx)
+        # the whole batch runs on to 50 steps with the invariants intact
+        ctx.idp_dgsem_step(ud, 48, t)
+        invariants_clean(ctx)
+        assert np.all(np.isfinite(ud.cpu().numpy()))
+        ctx.close()
