@@ -164,6 +164,44 @@ def recorded_traffic():
         return None
 
 
+def node_masses(mesh, N):
+    """m_i = (dx dy / 4) w_i w_j per node, [K][N+1][N+1] (LGL weights)."""
+    from numpy.polynomial import legendre as Lg
+    x = np.sort(np.concatenate(([-1.0, 1.0], np.real(Lg.legroots(Lg.legder([0] * N + [1]))))))
+    w = 2.0 / (N * (N + 1) * Lg.legval(x, [0] * N + [1]) ** 2)
+    x0, y0, x1, y1 = mesh.box
+    dx = (x1 - x0) / mesh.nx0 / 2.0 ** mesh.level
+    dy = (y1 - y0) / mesh.ny0 / 2.0 ** mesh.level
+    return (dx * dy / 4.0)[:, None, None] * w[None, :, None] * w[None, None, :]
+
+
+def l1_per_field(u, ref, m):
+    """sum m |u - ref| / sum m |ref| per conserved field (rho, rho v1, rho v2, E)."""
+    return {f: float((m * np.abs(u[v] - ref[v])).sum() / max((m * np.abs(ref[v])).sum(), 1e-300))
+            for v, f in enumerate(("rho", "rho_v1", "rho_v2", "E"))}
+
+
+def kernel_rooflines(work, kern, steps, step_time, peak_tflops, hbm_gbs):
+    """Per kernel: measured ms per launch, share of the kernel time, roofline
+    time max(flops / FP64 peak, bytes / HBM) and its fraction of the measured
+    time; and the step's roofline fraction (sum of the kernels' roofline times
+    over the measured step time)."""
+    out, tot, roof_step = {}, sum(ms for ms, n in kern.values()), 0.0
+    for name, (ms, n) in kern.items():
+        if n == 0:
+            continue
+        t = ms * 1e-3 / n
+        d = {"ms_per_launch": t * 1e3, "launches_per_step": n / steps, "share": ms / tot}
+        if name in work:
+            fl, by = work[name]
+            ta, tb = fl / (peak_tflops * 1e12), by / (hbm_gbs * 1e9)
+            d.update({"bound": "alu" if ta >= tb else "hbm", "roofline_ms": max(ta, tb) * 1e3,
+                      "frac": max(ta, tb) / t})
+            roof_step += max(ta, tb) * n / steps
+        out[name] = d
+    return out, {"roofline_ms": roof_step * 1e3, "measured_ms": step_time * 1e3, "frac": roof_step / step_time}
+
+
 def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn):
     """Per-step CUDA-event timing on the launching stream, L2 flushed between
     steps. Pass 1 (the headline): CUDA-graph steps bracketed by events. Pass 2:
@@ -183,11 +221,12 @@ def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn):
                 flush.zero_()          # L2 flush, outside the timed span
             ctx.idp_dgsem_step(u_dev, 1, t, stream=stream.cuda_stream)
         sync_fn()
-        out.append(ctx.idp_dgsem_profile_read(reset=True))
+        kern = ctx.idp_dgsem_profile_kernels(reset=False)
+        out.append(ctx.idp_dgsem_profile_read(reset=True) + ((kern,) if mode == 2 else ()))
     ctx.idp_dgsem_profile(0)
-    (_, _, step_ms, nst), (el_ms, el_n, _, _) = out
+    (_, _, step_ms, nst), (el_ms, el_n, _, _, kern) = out
     assert nst == steps
-    return step_ms * 1e-3, el_ms, el_n
+    return step_ms * 1e-3, el_ms, el_n, kern
 
 
 def run_ours(args):
@@ -217,13 +256,13 @@ def run_ours(args):
         barrier_sync()
         if prec == 0:
             clocks.start()
-        tot, el_ms, el_n = time_steps(ctx, u_dev, args.steps, args.warmup, flush, stream, barrier_sync)
+        tot, el_ms, el_n, kern = time_steps(ctx, u_dev, args.steps, args.warmup, flush, stream, barrier_sync)
         if prec == 0:
             ck = clocks.stop()
         tot = max_over_ranks(tot)
         rc, st = ctx.idp_dgsem_limiter_stats()
-        results[prec] = dict(time=tot, el_ms=el_ms, el_n=el_n, stats=st, ctx=ctx,
-                             launches=ctx.launches_per_step() * args.steps)
+        results[prec] = dict(time=tot, el_ms=el_ms, el_n=el_n, stats=st, ctx=ctx, kern=kern,
+                             launches=ctx.launches_per_step() * args.steps, u_end=u_dev.cpu().numpy())
         if prec == 0:
             results["clocks"] = ck
             # end to end through the host-buffer entry point (pinned host state)
@@ -246,7 +285,7 @@ def run_ours(args):
     del ub
     bsteps = max(3, args.steps // 4)
     barrier_sync()
-    btot, _, _ = time_steps(bctx, ubd, bsteps, max(3, args.warmup // 2), flush, stream, barrier_sync)
+    btot, _, _, _ = time_steps(bctx, ubd, bsteps, max(3, args.warmup // 2), flush, stream, barrier_sync)
     btot = max_over_ranks(btot)
     brc, bst = bctx.idp_dgsem_limiter_stats()
 
@@ -266,6 +305,16 @@ def run_ours(args):
     el32 = r32["el_ms"] * 1e-3 / max(r32["el_n"], 1)
     ach32 = f32 * nodes / el32 * 1e-12
     bval = aggregate_rate(bnodes * 3 * bsteps, world, btot)
+    hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
+    K, M = r64["ctx"].K, r64["ctx"].M
+    kr64, st64 = kernel_rooflines(roofline.kernel_work(3, 0, K, M, 12 * M, *w), r64["kern"], args.steps,
+                                  r64["time"] / args.steps, peak, hbm)
+    kr32, st32 = kernel_rooflines(roofline.kernel_work(3, 1, K, M, 12 * M, *w), r32["kern"], args.steps,
+                                  r32["time"] / args.steps, peak, hbm)
+    # FP32 form against the FP64 path after the same number of steps from the
+    # same state (the FP64 path matches the FP64 oracle to 1e-10 over 100 steps)
+    l1 = l1_per_field(r32["u_end"], r64["u_end"], node_masses(meshes[0], 3))
     line = {
         "metric": METRIC,
         "value": value,
@@ -292,6 +341,8 @@ def run_ours(args):
         "e2e": {"value": aggregate_rate(nodes * 3 * args.steps, world, results["e2e"]), "unit": UNIT,
                 "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(u0.nbytes)},
         "gpu_launches": int(r64["launches"]),
+        "kernels": kr64,
+        "step_roofline": dict(st64, peaks={"fp64_tflops": peak, "hbm_gbs": hbm}),
         "clocks": ck,
         "stats": {k: r64["stats"][k] for k in ("alpha_volume_mean", "alpha_mortar_mean", "n_viol_density",
                                                "n_viol_pressure", "n_nonpositive")},
@@ -303,6 +354,9 @@ def run_ours(args):
                                        "unit": "TFLOP/s", "launch_ms": el32 * 1e3,
                                        "flops_per_node_stage": f32},
                           "gpu_launches": int(r32["launches"]),
+                          "kernels": kr32,
+                          "step_roofline": st32,
+                          "l1_vs_fp64": dict(l1, steps=args.warmup + 2 * args.steps),
                           "stats": {k: r32["stats"][k] for k in ("alpha_volume_mean", "n_viol_density",
                                                                  "n_viol_pressure", "n_nonpositive")}},
             "batched_fp32": {"value": bval, "unit": UNIT,

@@ -198,17 +198,33 @@ idp_status idp_dgsem_integrals(idp_ctx *ctx, const double *u, double *out_host, 
 /* Read and reset the accumulated limiter statistics (synchronises). */
 idp_status idp_dgsem_limiter_stats(idp_ctx *ctx, idp_limiter_stats *out, void *stream);
 
+/* Kernel kinds of one SSP-RK3 step, for idp_dgsem_profile_kernels. */
+enum {
+    IDP_K_DT_INIT = 0,      /* reset of the per-simulation time-step minimum */
+    IDP_K_MORTAR_FLUX = 1,  /* mortar fluxes (L2 and sparse IDP), bar states */
+    IDP_K_DT = 2,           /* IDP time step */
+    IDP_K_ELEMENT = 3,      /* element pass: volume, faces, low order, limiting, stage */
+    IDP_K_MORTAR_LIMIT = 4, /* one limiting factor per mortar */
+    IDP_K_MORTAR_APPLY = 5, /* limited mortar corrections, stage at mortar nodes */
+    IDP_K_TIME_ADVANCE = 6, /* per-simulation time */
+    IDP_NKERNELS = 7
+};
+
 /* Measurement support (the paper has no counterpart). mode 1: each step's
  * CUDA-graph launch is bracketed by CUDA events on the step's stream; mode 2:
  * steps are launched kernel by kernel (no graph) with events around the step
- * and around each element-pass launch; mode 0: off. In modes 1 and 2
+ * and around every kernel launch; mode 0: off. In modes 1 and 2
  * idp_dgsem_step synchronises after every step to accumulate the durations.
  * idp_dgsem_profile_read returns the accumulated element-pass milliseconds
  * and launches, and step milliseconds and steps (any pointer may be NULL;
- * reset != 0 clears them). */
+ * reset != 0 clears them). idp_dgsem_profile_kernels writes, for each kernel
+ * kind k < IDP_NKERNELS, the accumulated milliseconds ms[k] and launches
+ * launches[k] of mode 2 (caller arrays of IDP_NKERNELS entries, either may be
+ * NULL; reset != 0 clears them). */
 idp_status idp_dgsem_profile(idp_ctx *ctx, int32_t mode);
 idp_status idp_dgsem_profile_read(idp_ctx *ctx, double *element_ms, int64_t *element_launches,
                                   double *step_ms, int64_t *steps, int32_t reset);
+idp_status idp_dgsem_profile_kernels(idp_ctx *ctx, double *ms, int64_t *launches, int32_t reset);
 
 /* Pipe-throughput probe used for the roofline (no counterpart in the paper):
  * runs short kernels on the current device and stream and writes out[0] FP64

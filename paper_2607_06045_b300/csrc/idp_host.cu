@@ -442,8 +442,15 @@ struct idp_ctx {
     // launched without the graph, with element-pass events
     int prof = 0;
     cudaEvent_t pev[8] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
-    double prof_ms = 0.0, prof_step_ms = 0.0;
-    long long prof_n = 0, prof_steps = 0;
+    double prof_step_ms = 0.0;
+    long long prof_steps = 0;
+    // mode 2: events around every kernel launch of a step, by kind
+    static constexpr int kMaxKev = 32;
+    cudaEvent_t kev[kMaxKev][2] = {};
+    int kev_kind[kMaxKev] = {};
+    int kev_n = 0;
+    double kms[IDP_NKERNELS] = {};
+    long long kcnt[IDP_NKERNELS] = {};
 };
 
 namespace {
@@ -472,32 +479,70 @@ StageArgs base_args(idp_ctx *c) {
     return A;
 }
 
+// Profiling mode 2: CUDA events before and after a launch, by kernel kind
+// (kt_begin returns the event slot, or -1 when not profiling).
+int kt_begin(idp_ctx *c, cudaStream_t st, int kind) {
+    if (c->prof != 2 || c->kev_n >= idp_ctx::kMaxKev) return -1;
+    const int k = c->kev_n++;
+    c->kev_kind[k] = kind;
+    cudaEventRecord(c->kev[k][0], st);
+    return k;
+}
+void kt_end(idp_ctx *c, cudaStream_t st, int k) {
+    if (k >= 0) cudaEventRecord(c->kev[k][1], st);
+}
+// after the step's stream has synchronised
+cudaError_t kt_collect(idp_ctx *c) {
+    for (int k = 0; k < c->kev_n; ++k) {
+        float ms = 0.f;
+        cudaError_t e = cudaEventElapsedTime(&ms, c->kev[k][0], c->kev[k][1]);
+        if (e != cudaSuccess) return e;
+        c->kms[c->kev_kind[k]] += ms;
+        c->kcnt[c->kev_kind[k]] += 1;
+    }
+    c->kev_n = 0;
+    return cudaSuccess;
+}
+
 // one stage: mortar fluxes (unless already current), element pass, mortar
-// limiting; ev0/ev1 (optional) bracket the element pass
-void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux,
-                   cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
+// limiting
+void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux) {
     const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
-    if (c->M > 0 && need_mortar_flux) c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, A.u, A.gas, c->d_ops);
-    if (ev0) cudaEventRecord(ev0, st);
+    if (c->M > 0 && need_mortar_flux) {
+        int k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
+        c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, A.u, A.gas, c->d_ops);
+        kt_end(c, st, k);
+    }
+    int k = kt_begin(c, st, IDP_K_ELEMENT);
     c->L.element(c->opt.precision, c->epb, element_grid(c, c->epb, c->persistent, c->bps), st, c->mesh, c->slots, A);
-    if (ev1) cudaEventRecord(ev1, st);
+    kt_end(c, st, k);
     bool dgmode = (A.mode == 0 && A.dt == 0.0) || A.limiting == 0;
     if (c->M > 0 && !dgmode) {
+        k = kt_begin(c, st, IDP_K_MORTAR_LIMIT);
         c->L.mortar_limit(gm, st, c->mesh, c->slots, A);
+        kt_end(c, st, k);
         int ga = std::max(1, std::min((c->n_mnodes + 255) / 256, c->num_sms * 8));
+        k = kt_begin(c, st, IDP_K_MORTAR_APPLY);
         c->L.mortar_apply(ga, st, c->mesh, c->slots, A);
+        kt_end(c, st, k);
     }
 }
 
 void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) {
+    int k = kt_begin(c, st, IDP_K_DT_INIT);
     k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
+    kt_end(c, st, k);
     if (c->M > 0 && mortar_flux && c->opt.dt_rule == 0) {
         const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
+        k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
         c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->d_ops);
+        kt_end(c, st, k);
     }
     int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
+    k = kt_begin(c, st, IDP_K_DT);
     c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
             c->d_status);
+    kt_end(c, st, k);
 }
 
 // one SSP-RK3 step on u (in place), using the ctx stage buffers
@@ -507,17 +552,18 @@ void enqueue_step(idp_ctx *c, cudaStream_t st, double *u) {
     A.mode = 1;
     A.un = u;
     // stage 1: u1 = ut(u)
-    cudaEvent_t *ev = c->prof == 2 ? c->pev : nullptr;
     A.u = u; A.out = c->d_buf1; A.comb = 0; A.tstage = 0.0;
-    enqueue_stage(c, st, A, c->opt.dt_rule != 0, ev ? ev[0] : nullptr, ev ? ev[1] : nullptr);
+    enqueue_stage(c, st, A, c->opt.dt_rule != 0);
     // stage 2: u2 = 3/4 u + 1/4 ut(u1)
     A.u = c->d_buf1; A.out = c->d_buf2; A.comb = 1; A.tstage = 1.0;
-    enqueue_stage(c, st, A, true, ev ? ev[2] : nullptr, ev ? ev[3] : nullptr);
+    enqueue_stage(c, st, A, true);
     // stage 3: u3 = u/3 + 2/3 ut(u2), in place
     A.u = c->d_buf2; A.out = u; A.comb = 2; A.tstage = 0.5;
-    enqueue_stage(c, st, A, true, ev ? ev[4] : nullptr, ev ? ev[5] : nullptr);
+    enqueue_stage(c, st, A, true);
+    const int k = kt_begin(c, st, IDP_K_TIME_ADVANCE);
     k_time_advance<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_tsim, c->d_dtmin, c->opt.cfl, c->d_dtlast,
                                                            c->n_sims);
+    kt_end(c, st, k);
 }
 
 idp_status check_cuda(cudaError_t e) { return note(e, "launch") == cudaSuccess ? IDP_OK : IDP_E_CUDA; }
@@ -879,13 +925,8 @@ idp_status idp_dgsem_step(idp_ctx *c, double *u, int32_t n_steps, double *t_host
             enqueue_step(c, st, u);
             cudaEventRecord(c->pev[7], st);
             if (note(cudaStreamSynchronize(st), "step") != cudaSuccess) return IDP_E_CUDA;
+            if (note(kt_collect(c), "profile") != cudaSuccess) return IDP_E_CUDA;
             float ms = 0.f;
-            for (int s = 0; s < 3; ++s) {
-                if (note(cudaEventElapsedTime(&ms, c->pev[2 * s], c->pev[2 * s + 1]), "profile") != cudaSuccess)
-                    return IDP_E_CUDA;
-                c->prof_ms += ms;
-                c->prof_n += 1;
-            }
             if (note(cudaEventElapsedTime(&ms, c->pev[6], c->pev[7]), "profile") != cudaSuccess) return IDP_E_CUDA;
             c->prof_step_ms += ms;
             c->prof_steps += 1;
@@ -986,9 +1027,14 @@ idp_status idp_dgsem_limiter_stats(idp_ctx *c, idp_limiter_stats *out, void *str
 
 idp_status idp_dgsem_profile(idp_ctx *c, int32_t mode) {
     if (!c || mode < 0 || mode > 2) return IDP_E_ARG;
-    if (mode && !c->pev[0])
+    if (mode && !c->pev[0]) {
         for (int k = 0; k < 8; ++k)
             if (note(cudaEventCreate(&c->pev[k]), "profile events") != cudaSuccess) return IDP_E_CUDA;
+        for (int k = 0; k < idp_ctx::kMaxKev; ++k)
+            for (int b = 0; b < 2; ++b)
+                if (note(cudaEventCreate(&c->kev[k][b]), "profile events") != cudaSuccess) return IDP_E_CUDA;
+    }
+    c->kev_n = 0;
     c->prof = mode;
     return IDP_OK;
 }
@@ -996,11 +1042,24 @@ idp_status idp_dgsem_profile(idp_ctx *c, int32_t mode) {
 idp_status idp_dgsem_profile_read(idp_ctx *c, double *element_ms, int64_t *element_launches, double *step_ms,
                                   int64_t *steps, int32_t reset) {
     if (!c) return IDP_E_ARG;
-    if (element_ms) *element_ms = c->prof_ms;
-    if (element_launches) *element_launches = c->prof_n;
+    if (element_ms) *element_ms = c->kms[IDP_K_ELEMENT];
+    if (element_launches) *element_launches = c->kcnt[IDP_K_ELEMENT];
     if (step_ms) *step_ms = c->prof_step_ms;
     if (steps) *steps = c->prof_steps;
-    if (reset) { c->prof_ms = 0.0; c->prof_n = 0; c->prof_step_ms = 0.0; c->prof_steps = 0; }
+    if (reset) {
+        for (int k = 0; k < IDP_NKERNELS; ++k) { c->kms[k] = 0.0; c->kcnt[k] = 0; }
+        c->prof_step_ms = 0.0; c->prof_steps = 0;
+    }
+    return IDP_OK;
+}
+
+idp_status idp_dgsem_profile_kernels(idp_ctx *c, double *ms, int64_t *launches, int32_t reset) {
+    if (!c) return IDP_E_ARG;
+    for (int k = 0; k < IDP_NKERNELS; ++k) {
+        if (ms) ms[k] = c->kms[k];
+        if (launches) launches[k] = c->kcnt[k];
+        if (reset) { c->kms[k] = 0.0; c->kcnt[k] = 0; }
+    }
     return IDP_OK;
 }
 
@@ -1024,6 +1083,9 @@ void idp_dgsem_destroy(idp_ctx *c) {
     if (c->ev_out) cudaEventDestroy(c->ev_out);
     for (int k = 0; k < 8; ++k)
         if (c->pev[k]) cudaEventDestroy(c->pev[k]);
+    for (int k = 0; k < idp_ctx::kMaxKev; ++k)
+        for (int b = 0; b < 2; ++b)
+            if (c->kev[k][b]) cudaEventDestroy(c->kev[k][b]);
     if (c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -51,7 +51,8 @@ _lib = None
 EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", "idp_dgsem_layout",
            "idp_dgsem_rhs", "idp_dgsem_dt", "idp_dgsem_step", "idp_dgsem_step_host", "idp_dgsem_integrals",
            "idp_dgsem_limiter_stats", "idp_dgsem_sync", "idp_dgsem_destroy", "idp_status_str",
-           "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_probe_pipes", "idp_eval_math",
+           "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_dgsem_profile_kernels",
+           "idp_probe_pipes", "idp_eval_math",
            "idp_integrals_noalloc"]
 
 
@@ -83,6 +84,7 @@ def lib():
         L.idp_dgsem_destroy.argtypes = [vp]
         L.idp_dgsem_profile.argtypes = [vp, C.c_int32]
         L.idp_dgsem_profile_read.argtypes = [vp, dp, C.POINTER(C.c_int64), dp, C.POINTER(C.c_int64), C.c_int32]
+        L.idp_dgsem_profile_kernels.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int32]
         L.idp_probe_pipes.argtypes = [dp, vp]
         L.idp_eval_math.argtypes = [C.c_int32, vp, vp, C.c_int64, vp]
         L.idp_integrals_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.c_int32, vp, vp]
@@ -122,6 +124,9 @@ def idp_eval_math(fn, x, y, stream=None):
     _check(lib().idp_eval_math(int(fn), C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()), x.numel(),
                                _stream(stream)), "idp_eval_math")
 
+
+# kernel kinds of one step, in the order of the IDP_K_* constants
+KERNELS = ["dt_init", "mortar_flux", "dt", "element", "mortar_limit", "mortar_apply", "time_advance"]
 
 NOALLOC_MAX_ELEMS = 1 << 19
 
@@ -280,6 +285,13 @@ class Context:
         _check(lib().idp_dgsem_profile_read(self._h, C.byref(ms), C.byref(n), C.byref(sms), C.byref(ns),
                                             1 if reset else 0), "idp_dgsem_profile_read")
         return ms.value, n.value, sms.value, ns.value
+
+    def idp_dgsem_profile_kernels(self, reset=False):
+        """{kernel kind: (ms, launches)} accumulated in profiling mode 2."""
+        ms = (C.c_double * len(KERNELS))()
+        n = (C.c_int64 * len(KERNELS))()
+        _check(lib().idp_dgsem_profile_kernels(self._h, ms, n, 1 if reset else 0), "idp_dgsem_profile_kernels")
+        return {k: (ms[i], n[i]) for i, k in enumerate(KERNELS)}
 
     def launches_per_step(self):
         """Kernels one SSP-RK3 step launches (mirrors the step sequence)."""

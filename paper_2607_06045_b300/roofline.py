@@ -7,11 +7,12 @@ per node and stage against 6.5 TB/s) is two orders of magnitude below it.
 Work is counted in FP64 pipe instructions that the method's formulas need, for
 an interior node of the limited scheme at N = 3 (counts scale with N as the
 pair and interface counts below): an add, multiply, compare, min/max or fused
-multiply-add is one instruction; a division, square root or logarithm costs
-the number of DFMA-equivalents that idp_probe_pipes measures for CUDA's FP64
-routine. Each instruction counts as 2 DFMA-equivalent flops, the unit of the
-measured peak. In the FP32 form the flux arithmetic runs in FP32 and only the
-FP64 instructions (including the FP64<->FP32 conversions the form needs) are
+multiply-add is one instruction; a reciprocal ("div"), square root or
+logarithm costs the number of DFMA-equivalents that idp_probe_pipes measures
+for the routine the FP64 flux arithmetic uses (Newton-Raphson reciprocal,
+Goldschmidt square root, Tang's logarithm). Each instruction counts as 2
+DFMA-equivalent flops, the unit of the peak. In the FP32 form the flux
+arithmetic runs in FP32 and only the FP64 instructions the form needs are
 counted. Conforming face fluxes are counted once per face.
 """
 from __future__ import annotations
@@ -43,32 +44,33 @@ def element_ops_per_node(N: int, precision: int = 0) -> dict:
     """FP64 work per node and stage of the limited element pass, by row."""
     NP = N + 1
     ifn = 2.0 * N / NP            # interior subcell interfaces per node
+    ends = 2.0 * ifn              # interface end points per node
     facen = 2.0 / NP              # face-node flux evaluations per node (one per face)
     pairs = float(N)              # two-point fluxes per node (symmetric, once per pair)
     sbar = N * (N + 1) * (N + 2) / 6.0   # (pair, interface) contributions per row
     fp64 = precision == 0
     r = {}
-    # a1 node preparation: 1/rho, v, p, c, beta, ln rho, ln p (FP32 form: the
-    # four conversions of the state)
-    r["a1_node_prep"] = Ops(inst=9, div=2, sqrt=1, log=2) if fp64 else Ops(inst=6)
-    # a2 two-point fluxes: two log means sharing one division, Ranocha's flux
+    # a1 node preparation: 1/rho, v, p, c, beta, ln rho, ln p (the FP32 form
+    # forms them in FP32)
+    r["a1_node_prep"] = Ops(inst=10, div=2, sqrt=1, log=2) if fp64 else Ops()
+    # a2 two-point fluxes: two log means sharing one reciprocal, Ranocha's flux
     r["a2_pair_fluxes"] = pairs * Ops(inst=40, div=1) if fp64 else Ops()
     # a2 Sbar contraction (one FMA per contribution and variable) and scaling
-    r["a2_sbar_contraction"] = (Ops(inst=2 * sbar * 4 / NP) if fp64 else Ops()) + ifn * Ops(inst=5 if fp64 else 2)
-    # a3 low-order subcell flux, graph viscosity, bar state, 2d
-    r["a3_fv_subcell"] = ifn * (Ops(inst=36, div=1) if fp64 else Ops(inst=15))
-    # a4 conforming/boundary LLF flux of the face node, its bar state and 2d
-    r["a4_face_flux"] = facen * (Ops(inst=42, div=2, sqrt=1) if fp64 else Ops(inst=29))
-    # a6/a7 low-order update, bar-state/positivity bounds, scaled pressure
-    # solve coefficients, tolerance, dt check (+ FP32 copies in the FP32 form)
-    r["a6_a7_update_bounds"] = Ops(inst=55 if fp64 else 63)
-    # a8 antidiffusive fluxes and exemption (per interface), Zalesak factors
-    r["a8_zalesak"] = ifn * Ops(inst=9 if fp64 else 13) + Ops(inst=26)
-    # a8 pressure: per interface the admissibility of the full correction at
-    # both end points, certified in FP32 (FP64 only when undecided)
-    r["a8_pressure"] = ifn * Ops(inst=6)
-    # a10 blend, stage combination, statistics
-    r["a10_blend_stage"] = Ops(inst=45)
+    r["a2_sbar_contraction"] = (Ops(inst=2 * sbar * 4 / NP) + ifn * Ops(inst=5)) if fp64 else Ops()
+    # a3 low-order subcell flux, graph viscosity and 2d (flux type), bar state (FP64)
+    r["a3_fv_subcell"] = ifn * (Ops(inst=35, div=1) if fp64 else Ops(inst=4))
+    # a4 conforming/boundary LLF flux of the face node (flux type), bar state (FP64)
+    r["a4_face_flux"] = facen * (Ops(inst=49, div=2, sqrt=1) if fp64 else Ops(inst=5))
+    # a6/a7 low-order update (residual sums from the first term), bounds,
+    # pressure-solve coefficients
+    r["a6_a7_update_bounds"] = Ops(inst=27 + (1 if fp64 else 0))
+    # a8 antidiffusive fluxes and exemption (FP64 path), Zalesak sums and factors
+    r["a8_zalesak"] = (ifn * Ops(inst=4) if fp64 else Ops()) + ends * Ops(inst=1) + Ops(inst=4)
+    # a8 pressure: the admissibility of the full correction at both end
+    # points is certified in FP32 (the FP64 solve is rare)
+    r["a8_pressure"] = Ops()
+    # a10 blend, stage combination (2/3 of the stages), statistics thresholds
+    r["a10_blend_stage"] = Ops(inst=ends * 4 + 4 + 8 * 2.0 / 3.0 + 2)
     total = Ops()
     for v in r.values():
         total = total + v
@@ -85,3 +87,68 @@ def element_flops(N: int, precision: int, w_div: float, w_sqrt: float, w_log: fl
 # two of three stages (64/3 B), write u^(s+1) (32 B); face traces and mesh
 # tables are re-reads of data already counted.
 BYTES_PER_NODE_STAGE = 32.0 + 64.0 / 3.0 + 32.0
+
+
+# ---------------------------------------------------------------------------
+# The other kernels of a step: algorithmic FP64 work and HBM bytes per unit
+# (node, mortar or mortar node), at degree N. Counts follow the kernels'
+# formulas in the same units as above; the FP32 form counts only its FP64
+# instructions (its FP32 work is far below the FP32 peak).
+# ---------------------------------------------------------------------------
+
+def _prim(precision: int) -> Ops:
+    """Primitives and wave speed of one state (1/rho, v, p, c)."""
+    return Ops(inst=7, div=1, sqrt=1) if precision == 0 else Ops()
+
+
+def dt_ops_per_node(N: int, precision: int = 0) -> Ops:
+    """k_dt: own wave speeds, the outside wave speed of each face node (one
+    per node on average at one face node per element side and node row), the
+    2d sum and m / sum."""
+    NP = N + 1
+    facen = 4.0 * NP / (NP * NP)
+    o = _prim(precision) + facen * _prim(precision)
+    if precision == 0:
+        o = o + Ops(inst=8 + 2, div=1)
+    return o
+
+
+def mortar_flux_ops_per_mortar(N: int, precision: int = 0) -> Ops:
+    """k_mortar_flux: trace primitives, interpolation (FP64), admissibility,
+    LLF on the small faces, the sparse pair terms with bar states, the
+    projection (FP64 sums) and the slot sums."""
+    NP = N + 1
+    npair = 3 * NP - 1
+    o = Ops(inst=8 * NP * NP)                      # interpolation 2NP x 4 x NP
+    o = o + Ops(inst=6 * 2 * NP)                   # admissibility of the interpolated states
+    o = o + Ops(inst=8 * NP * NP + 12 * NP)        # projection and scaling
+    o = o + Ops(inst=2 * NP * 4 * 3)               # small-face contributions
+    o = o + Ops(inst=npair * (5 + 8))              # bar states and slot sums
+    if precision == 0:
+        o = o + 3 * NP * _prim(0) + 2 * NP * (_prim(0) + Ops(inst=24)) + npair * Ops(inst=22, div=1)
+    return o
+
+
+def mortar_limit_ops_per_slot(precision: int = 0) -> Ops:
+    """k_mortar_limit: correction, density factor, pressure factor."""
+    return Ops(inst=30, div=3)
+
+
+def mortar_apply_ops_per_node(precision: int = 0) -> Ops:
+    """k_mortar_apply: limited corrections, stage combination, checks."""
+    return Ops(inst=35, div=2)
+
+
+def kernel_work(N: int, precision: int, K: int, M: int, n_mnodes: int, w_div: float, w_sqrt: float,
+                w_log: float) -> dict:
+    """Per launch: (FP64 DFMA-equivalent flops, HBM bytes) of each kernel."""
+    nodes = K * (N + 1) ** 2
+    Q = 3 * (N + 1)
+    w = (w_div, w_sqrt, w_log)
+    return {
+        "element": (element_flops(N, precision, *w) * nodes, BYTES_PER_NODE_STAGE * nodes),
+        "dt": (2.0 * dt_ops_per_node(N, precision).dfma_eq(*w) * nodes, 32.0 * nodes),
+        "mortar_flux": (2.0 * mortar_flux_ops_per_mortar(N, precision).dfma_eq(*w) * M, (96.0 + 264.0) * (N + 1) * M),
+        "mortar_limit": (2.0 * mortar_limit_ops_per_slot(precision).dfma_eq(*w) * Q * M, 112.0 * Q * M),
+        "mortar_apply": (2.0 * mortar_apply_ops_per_node(precision).dfma_eq(*w) * n_mnodes, 136.0 * n_mnodes),
+    }
