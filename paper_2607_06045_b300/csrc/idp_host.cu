@@ -438,6 +438,7 @@ struct idp_ctx {
     const double *graph_u = nullptr;
     long long n_stages = 0;
     double total_area = 0.0;   // sum of element areas (all simulations)
+    double total_mortar_len = 0.0;   // sum of the large faces' lengths over the mortars
     // optional timing: 1 step spans around the graph launches; 2 steps
     // launched without the graph, with element-pass events
     int prof = 0;
@@ -521,7 +522,7 @@ void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mo
         k = kt_begin(c, st, IDP_K_MORTAR_LIMIT);
         c->L.mortar_limit(gm, st, c->mesh, c->slots, A);
         kt_end(c, st, k);
-        int ga = std::max(1, std::min((c->n_mnodes + 255) / 256, c->num_sms * 8));
+        int ga = std::max(1, std::min((c->n_mnodes + 63) / 64, c->num_sms * 32));
         k = kt_begin(c, st, IDP_K_MORTAR_APPLY);
         c->L.mortar_apply(ga, st, c->mesh, c->slots, A);
         kt_end(c, st, k);
@@ -674,6 +675,10 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     c->K = (long long)H.geom.size(); c->M = (long long)H.m_large.size();
     c->sim_off = H.sim_off;
     for (const Geo &g : H.geom) c->total_area += g.z * g.w;
+    for (size_t m = 0; m < H.m_large.size(); ++m) {
+        const Geo &g = H.geom[H.m_large[m]];
+        c->total_mortar_len += (H.m_info[m] & 1) == 0 ? g.w : g.z;
+    }
     c->L = get_launchers(c->NP);
     int dev = 0;
     cudaError_t ce = cudaGetDevice(&dev);
@@ -1009,7 +1014,10 @@ idp_status idp_dgsem_limiter_stats(idp_ctx *c, idp_limiter_stats *out, void *str
     // area times the number of limited stages
     const double mass = c->total_area * (double)c->n_stages;
     out->alpha_volume_mean = mass > 0 ? a.alpha_vol_m / mass : 0.0;
-    out->alpha_mortar_mean = a.len > 0 ? a.alpha_mort_len / a.len : 0.0;
+    // every limited stage limits every mortar once: the length sum is the
+    // total mortar length times the number of limited stages
+    const double mlen = c->total_mortar_len * (double)c->n_stages;
+    out->alpha_mortar_mean = mlen > 0 ? a.alpha_mort_len / mlen : 0.0;
     out->n_stages = c->n_stages;
     out->n_volume_active = (int64_t)a.n_vol;
     out->n_mortar_active = (int64_t)a.n_mort;

@@ -205,53 +205,79 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
     if (lane == 0) sl.bad[m] = bad ? 1 : 0;
 }
 
+// Mortar limiting: one thread per mortar slot, 128 / (3 (N+1)) mortars per
+// block; the factor of a mortar is the minimum over its slots (shared-memory
+// minimum on the bits of the non-negative factors).
 template <int NP>
-__global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
+struct MortarLimitLaunch {
+    static constexpr int Q = 3 * NP, threads = 128, mpb = threads / Q;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(128)
 k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
-    constexpr int Q = 3 * NP;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.x * MORTARS_PER_BLOCK + warp;
-    if (m >= mesh.M) return;
-    const int L = mesh.m_large[m];
-    const int sim = mesh.sim[L];
-    const double dt = stage_dt(A, sim);
-    const bool bad = sl.bad[m] != 0;
-    double th = 1.0;
-    if (!bad && lane < Q) {
-        const int s = m * Q + lane;
+    using ML = MortarLimitLaunch<NP>;
+    constexpr int Q = ML::Q, MPB = ML::mpb;
+    __shared__ unsigned long long s_min[MPB];
+    const int lm = threadIdx.x / Q, q = threadIdx.x - lm * Q;
+    const int m = blockIdx.x * MPB + lm;
+    if (threadIdx.x < MPB) s_min[threadIdx.x] = dbits(1.0);
+    __syncthreads();
+    if (lm < MPB && m < mesh.M && sl.bad[m] == 0) {
+        const int L = mesh.m_large[m];
+        const double dt = stage_dt(A, mesh.sim[L]);
+        const int s = m * Q + q;
         double u0[4], av[4];
-        const double mi = sl.mass[s], ni = (double)sl.nmort[s];
+        const double f = (double)sl.nmort[s] * dt * fast_rcp(sl.mass[s]);   // n_i dt / m_i
         for (int v = 0; v < 4; ++v) {
             u0[v] = sl.uvol[(size_t)v * sl.S + s];
-            av[v] = ni * dt / mi * (sl.chi[(size_t)v * sl.S + s] - sl.clo[(size_t)v * sl.S + s]);
+            av[v] = f * (sl.chi[(size_t)v * sl.S + s] - sl.clo[(size_t)v * sl.S + s]);
         }
         double lr = 1.0;
-        double tl = sl.tol[s];
-        if (av[0] > 0.0) { double t = (sl.rmax[s] + tl - u0[0]) / av[0]; if (t < lr) lr = t; }
-        else if (av[0] < 0.0) { double t = (sl.rmin[s] - tl - u0[0]) / av[0]; if (t < lr) lr = t; }
-        if (lr < 0.0) lr = 0.0;
-        const double pmin = sl.pmin[s] / sl.rfv[s];
-        double pm = pmin - kTol * fabs(pmin);
-        th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
+        const double tl = sl.tol[s];
+        if (dpos(av[0])) { double t = (sl.rmax[s] + tl - u0[0]) * fast_rcp(av[0]); if (dlt(t, lr)) lr = t; }
+        else if (dneg(av[0])) { double t = (sl.rmin[s] - tl - u0[0]) * fast_rcp(av[0]); if (dlt(t, lr)) lr = t; }
+        if (!dpos(lr)) lr = 0.0;
+        const double pmin = sl.pmin[s] * fast_rcp(sl.rfv[s]);
+        const double pm = pmin - kTol * fabs(pmin);
+        const double th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
+        atomicMin(&s_min[lm], dbits(dpos(th) ? th : 0.0));
     }
-    for (int o = 16; o > 0; o >>= 1) th = fmin(th, __shfl_down_sync(0xffffffffu, th, o));
-    if (lane == 0) {
-        double lS = bad ? 0.0 : th;
-        sl.ell[m] = lS;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        float am = 0.0f;
+        unsigned nm = 0, nf = 0;
+        for (int j = threadIdx.x; j < MPB; j += 32) {
+            const int mm = blockIdx.x * MPB + j;
+            if (mm >= mesh.M) continue;
+            const bool bad = sl.bad[mm] != 0;
+            const double lS = bad ? 0.0 : __longlong_as_double((long long)s_min[j]);
+            sl.ell[mm] = lS;
+            if (A.collect) {
+                const int info = mesh.m_info[mm], dir = info & 1;
+                const GeoC gc = mesh.geoc[mesh.m_large[mm]];
+                am += d2f(2.0 * (dir == 0 ? gc.hy : gc.hx)) * (1.0f - d2f(lS));   // face length (1 - l_S)
+                nm += nn_lt(lS, 1.0);
+                nf += bad;
+            }
+        }
         if (A.collect) {
-            const int info = mesh.m_info[m], dir = info & 1;
-            const Geo geo = mesh.geom[L];
-            double len = dir == 0 ? geo.w : geo.z;
-            atomicAdd(&A.stats->alpha_mort_len, len * (1.0 - lS));
-            atomicAdd(&A.stats->len, len);
-            if (lS < 1.0) atomicAdd(&A.stats->n_mort, 1ull);
-            if (bad) atomicAdd(&A.stats->n_fallback, 1ull);
+            for (int o = 16; o > 0; o >>= 1) am += __shfl_down_sync(0xffffffffu, am, o);
+            nm = __reduce_add_sync(0xffffffffu, nm);
+            nf = __reduce_add_sync(0xffffffffu, nf);
+            if (threadIdx.x == 0) {
+                if (am > 0.0f) atomicAdd(&A.stats->alpha_mort_len, (double)am);
+                if (nm) atomicAdd(&A.stats->n_mort, (unsigned long long)nm);
+                if (nf) atomicAdd(&A.stats->n_fallback, (unsigned long long)nf);
+            }
         }
     }
 }
 
+// Limited mortar corrections at the mortar nodes (corner nodes of two
+// mortars in mortar order) and the stage combination there.
 template <int NP>
-__global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
+__global__ void __launch_bounds__(64) k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
     constexpr int NN = NP * NP, Q = 3 * NP;
     const size_t KN = (size_t)mesh.K * NN;
     double st_rmin = INFINITY;
@@ -263,7 +289,7 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
         const int s0 = ss.x;
         const int e = gnode / NN;
         const double dt = stage_dt(A, mesh.sim[e]);
-        const double mi = sl.mass[s0];
+        const double imi = fast_rcp(sl.mass[s0]);
         double corr[4] = {0, 0, 0, 0};
         for (int c = 0; c < 2; ++c) {
             int s = c == 0 ? ss.x : ss.y;
@@ -272,11 +298,12 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
             for (int v = 0; v < 4; ++v) corr[v] += l * (sl.chi[(size_t)v * sl.S + s] - sl.clo[(size_t)v * sl.S + s]);
         }
         double ut[4];
+        const double dtm = dt * imi;
         for (int v = 0; v < 4; ++v) {
             double uv = sl.uvol[(size_t)v * sl.S + s0];
-            ut[v] = uv + dt / mi * corr[v];
+            ut[v] = uv + dtm * corr[v];
             if (A.mode == 0) {
-                A.out[v * KN + gnode] = (sl.un[(size_t)v * sl.S + s0] + corr[v]) / mi;
+                A.out[v * KN + gnode] = (sl.un[(size_t)v * sl.S + s0] + corr[v]) * imi;
             } else {
                 double o = ut[v];
                 double un = sl.un[(size_t)v * sl.S + s0];
@@ -286,13 +313,15 @@ __global__ void k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
             }
         }
         if (A.collect) {
-            double p = pressure_d(A.gas.gm1, ut[0], ut[1], ut[2], ut[3]);
-            double rmin = sl.rmin[s0], rmax = sl.rmax[s0], pmin = sl.pmin[s0] / sl.rfv[s0];
-            if (ut[0] < rmin - kViolTol * fabs(rmin) || ut[0] > rmax + kViolTol * fabs(rmax)) vr++;
-            if (p < pmin - kViolTol * fabs(pmin)) vp++;
-            if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
+            // rho p = (gamma-1)(rho E - |m|^2/2) against p_min rho, without division
+            const double rp = A.gas.gm1 * (ut[0] * ut[3] - 0.5 * (ut[1] * ut[1] + ut[2] * ut[2]));
+            const double pmin = sl.pmin[s0] * fast_rcp(sl.rfv[s0]);
+            const double rmin = sl.rmin[s0], rmax = sl.rmax[s0];
+            if (dlt(ut[0], rmin - kViolTol * fabs(rmin)) || dlt(rmax + kViolTol * fabs(rmax), ut[0])) vr++;
+            if (dlt(rp, (pmin - kViolTol * fabs(pmin)) * ut[0])) vp++;
+            if (!dpos(ut[0]) || !dpos(rp)) np_++;
             st_rmin = dmin(st_rmin, ut[0]);
-            const float pf = d2f(p);
+            const float pf = dpos(ut[0]) ? d2f(rp) / d2f(ut[0]) : 0.0f;
             if (pf > 0.0f && (st_one == 0.0f || pf < st_pmin)) { st_pmin = pf; st_one = 1.0f; }
         }
     }

@@ -70,11 +70,13 @@ void mortar_flux(int fp32, int grid, cudaStream_t st, const MeshDev &m, const Sl
 }
 
 void mortar_limit(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
-    k_mortar_limit<NP><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, a);
+    using ML = MortarLimitLaunch<NP>;
+    (void)grid;
+    k_mortar_limit<NP><<<(m.M + ML::mpb - 1) / ML::mpb, ML::threads, 0, st>>>(m, s, a);
 }
 
 void mortar_apply(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
-    k_mortar_apply<NP><<<grid, 256, 0, st>>>(m, s, a);
+    k_mortar_apply<NP><<<grid, 64, 0, st>>>(m, s, a);
 }
 
 void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, const Gas &gamma,
