@@ -63,10 +63,13 @@ struct ElemSm {
             double outs[4][NP][4];   // outside state (conforming neighbour or ghost)
         };
         struct {                 // P2 - P5
-            double dtm[NN], ufv[4][NN], rmin[NN], rmax[NN], tol[NN];
+            double dtm[NN], ufv[4][NN], rmin[NN], rmax[NN];
+            double tol[F32 ? 1 : NN];    // FP64 path: kTol |rho_FV|
             // pressure solve at u_FV in the form scaled by rho_FV: gm = (gamma-1) rho_FV,
-            // pm = p_min rho_FV = beta (gamma-1)(rho E - |m|^2/2), c0 = g(0)
-            double gms[NN], pms[NN], c0[NN];
+            // pm = p_min rho_FV = beta (gamma-1)(rho E - |m|^2/2), c0 = g(0); the
+            // FP32 form keeps pm only and forms gm and c0 where the FP64 solve runs
+            double pms[NN];
+            double gms[F32 ? 1 : NN], c0[F32 ? 1 : NN];
             float ufvf[4][NN];       // FP32 copies for the certified admissibility check
             float dtmf[NN], gmsf[NN], pmsf[NN], c0f[NN];
             float tqf[NN];           // FP32 form: exemption threshold kTol |rho_FV| m / dt
@@ -91,7 +94,7 @@ struct ElemSm {
     union {
         struct {                 // P1 - P2b
             FT Ffv[F32 ? NIF : 1][4];  // FP32 form: the low-order subcell flux in FP32
-            double Fv[NIF][4];       // the low-order subcell flux in FP64, for the residual sums
+            double Fv[F32 ? 1 : NIF][4];  // FP64 path: the low-order subcell flux
             FT Fdg[NIF][4];          // mass-weighted high-order subcell flux w_r * fhat (flux type)
         };
         struct {                 // P3 - P5
@@ -189,10 +192,17 @@ template <int NP, int EPB>
 struct ElemLaunch {
     // threads per block: one per node, rounded up to whole warps
     static constexpr int threads = ((EPB * NP * NP + 31) / 32) * 32;
+    // FP32 form: ask for 640 resident threads per SM (at most 102 registers
+    // each), so that one block's FP64 phases overlap others' FP32 phases
+    static constexpr int min_blocks_f32 = 640 / threads > 0 ? 640 / threads : 1;
+    // FP64 path: 512 resident threads per SM (at most 128 registers each)
+    static constexpr int min_blocks_f64 = 512 / threads > 0 ? 512 / threads : 1;
 };
 
 template <int NP, typename FT, int EPB>
-__global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads)
+__global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads,
+                                  sizeof(FT) == 4 ? ElemLaunch<NP, EPB>::min_blocks_f32
+                                                  : ElemLaunch<NP, EPB>::min_blocks_f64)
 k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
     using SM = ElemSm<NP, FT>;
     constexpr int NN = NP * NP, N = NP - 1, NPAIR = SM::NPAIR, NIF = SM::NIF;
@@ -383,7 +393,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 else cc = s_w[r] * (d == 0 ? S.qy : S.qx);
                 for (int v = 0; v < 4; ++v) {
                     FT fv = cc * (fa[v] + fb[v]) - cc * lam * (ub[v] - ua[v]);
-                    if constexpr (F32) { S.Ffv[id][v] = fv; S.Fv[id][v] = f2d(fv); }
+                    if constexpr (F32) S.Ffv[id][v] = fv;
                     else S.Fv[id][v] = fv;
                 }
                 S.i2d[id] = FT(2) * cc * lam;
@@ -437,7 +447,17 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         const bool interior = side == 0 ? pos > 0 : pos < N;
                         const int id = ifid<NP>(d, row, side == 0 ? (interior ? pos - 1 : 0) : (interior ? pos : 0));
                         const int s = 2 * d + side;
-                        const double *fl = interior ? S.Fv[id] : S.face[s][row];
+                        double fl[4];
+                        if constexpr (F32) {
+                            // FP32 subcell flux carried to FP64 exactly (integer pipe)
+                            for (int v = 0; v < 4; ++v) {
+                                const double fi = f2d(S.Ffv[id][v]), ff = S.face[s][row][v];
+                                fl[v] = interior ? fi : ff;
+                            }
+                        } else {
+                            const double *src = interior ? S.Fv[id] : S.face[s][row];
+                            for (int v = 0; v < 4; ++v) fl[v] = src[v];
+                        }
                         const double blo = interior ? S.ibar[id] : S.fbar[s][row];
                         const double bhi = interior ? S.ibar[id] : S.fbar2[s][row];
                         const FT dsv = interior ? S.i2d[id] : S.f2d[s][row];
@@ -482,13 +502,14 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double rp = gm1 * X;
                 double gms = gm1 * q[0], pms = A.beta * rp;
                 double c0 = gms * X - pms * q[0];
-                S.gms[n] = gms; S.pms[n] = pms; S.c0[n] = c0;
+                S.pms[n] = pms;
+                if constexpr (!F32) { S.gms[n] = gms; S.c0[n] = c0; }
                 S.dtmf[n] = d2f(dtm); S.gmsf[n] = d2f(gms); S.pmsf[n] = d2f(pms); S.c0f[n] = d2f(c0);
                 if constexpr (F32) {
                     S.tqf[n] = 1e-14f * fabsf(S.ufvf[0][n]) * (S.idtmf * s_wwf[n]);
                     if (A.collect && S.dtmf[n] * ds > 1.0f) atomicAdd(&A.stats->n_dtx, 1ull);
                 } else {
-                    S.tol[n] = kTol * fabs(q[0]);
+                    if constexpr (!F32) S.tol[n] = kTol * fabs(q[0]);
                     if (A.collect && nn_lt(1.0, dtm * ds)) atomicAdd(&A.stats->n_dtx, 1ull);
                 }
             }
@@ -645,7 +666,15 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double u0[4], av[4];
                 double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
                 for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.Ad[id][v]; }
-                th = theta_max(gm1, u0, av, S.gms[nd], S.pms[nd], S.c0[nd], th);
+                double gmsn, c0n;
+                if constexpr (F32) {
+                    gmsn = gm1 * u0[0];
+                    const double X = u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2]);
+                    c0n = gmsn * X - S.pms[nd] * u0[0];
+                } else {
+                    gmsn = S.gms[nd]; c0n = S.c0[nd];
+                }
+                th = theta_max(gm1, u0, av, gmsn, S.pms[nd], c0n, th);
             }
             S.ell[id] = th;   // min over both end points (each searched below the previous)
         }
@@ -661,6 +690,12 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if (e >= mesh.K) continue;
                 SM &S = sm[le];
                 int i = n % NP, j = n / NP;
+                const size_t gi = (size_t)e * NN + n;
+                // the step-start state is read first so that its latency
+                // overlaps the blend
+                double unv[4] = {0.0, 0.0, 0.0, 0.0};
+                if (A.mode == 1 && A.comb != 0)
+                    for (int v = 0; v < 4; ++v) unv[v] = __ldg(A.un + v * KN + gi);
                 double dtm = S.dtm[n];
                 double sacc[4] = {0, 0, 0, 0}, lmin = 1.0;
                 for (int d = 0; d < 2; ++d) {
@@ -682,7 +717,6 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 for (int v = 0; v < 4; ++v) uvol[v] = S.ufv[v][n] + dtm * sacc[v];
                 if (A.mode == 0)
                     for (int v = 0; v < 4; ++v) resv[v] = S.lfv[v][n] + sacc[v];
-                size_t gi = (size_t)e * NN + n;
                 // mortar hand-off
                 uchar4 ftv = mesh.ftype[e];
                 int4 nb4 = mesh.fnbr[e];
@@ -703,8 +737,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         for (int v = 0; v < 4; ++v) {
                             sl.uvol[(size_t)v * sl.S + q] = uvol[v];
                             // rhs mode keeps the mass-weighted residual, step mode u^n
-                            sl.un[(size_t)v * sl.S + q] =
-                                A.mode == 0 ? resv[v] : (A.comb != 0 ? A.un[v * KN + gi] : 0.0);
+                            sl.un[(size_t)v * sl.S + q] = A.mode == 0 ? resv[v] : unv[v];
                         }
                         sl.rmin[q] = S.rmin[n]; sl.rmax[q] = S.rmax[n];
                         sl.pmin[q] = S.pms[n]; sl.rfv[q] = S.ufv[0][n];
@@ -717,8 +750,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 } else {
                     for (int v = 0; v < 4; ++v) {
                         double o = uvol[v];
-                        if (A.comb == 1) o = 0.75 * A.un[v * KN + gi] + 0.25 * uvol[v];
-                        else if (A.comb == 2) o = A.un[v * KN + gi] * (1.0 / 3.0) + 2.0 / 3.0 * uvol[v];
+                        if (A.comb == 1) o = 0.75 * unv[v] + 0.25 * uvol[v];
+                        else if (A.comb == 2) o = unv[v] * (1.0 / 3.0) + 2.0 / 3.0 * uvol[v];
                         A.out[v * KN + gi] = o;
                     }
                 }
