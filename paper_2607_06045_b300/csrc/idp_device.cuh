@@ -232,11 +232,14 @@ __device__ __forceinline__ Prim<FT> make_prim(const Gas &G, double r, double m1,
     return q;
 }
 
-// FP32 primitives of the FP32 form. When E - |m|^2/2rho keeps at least half
-// of E (no cancellation) the pressure is formed in FP32 (relative error below
-// 1e-6, positive for sure); otherwise in FP64 as above. The state is rounded
-// to FP32 on the integer pipe (d2f); the same function serves every element
-// that reads the node, so they all get the same bits.
+// FP32 primitives of the FP32 form. When E - |m|^2/2rho keeps at least an
+// eighth of E the pressure is formed in FP32: with the state rounded once,
+// the kinetic energy carries at most 4 unit roundings and E one half, so the
+// FP32 pressure is within (0.5 + 4 * 7/8) * 8 + 0.5 = 32.5 unit roundings
+// (2e-6) of the pressure of the rounded state and positive for sure;
+// otherwise it is formed in FP64 as above. The state is rounded to FP32 on
+// the integer pipe (d2f); the same function serves every element that reads
+// the node, so they all get the same bits.
 __device__ __forceinline__ Prim<float> make_prim_f32(const Gas &G, double r, double m1, double m2, double E, bool full,
                                                      float &m1o, float &m2o) {
     float rf = d2f(r), m1f = d2f(m1), m2f = d2f(m2), Ef = d2f(E);
@@ -245,7 +248,7 @@ __device__ __forceinline__ Prim<float> make_prim_f32(const Gas &G, double r, dou
     float kef = __fmul_rn(0.5f, __fadd_rn(__fmul_rn(m1f, v1), __fmul_rn(m2f, v2)));
     float pef = __fadd_rn(Ef, -kef);
     Prim<float> q;
-    if (rf > 0.0f && Ef > 0.0f && pef >= 0.5f * Ef) {
+    if (rf > 0.0f && Ef > 0.0f && pef >= 0.125f * Ef) {
         q.rho = rf; q.v1 = v1; q.v2 = v2; q.E = Ef;
         q.p = __fmul_rn(G.gm1f, pef);
         q.lr = q.lb = 0.0f;
