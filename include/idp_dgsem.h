@@ -100,7 +100,11 @@ typedef struct {
  *  mortar_projection  0: LGL-weighted adjoint of the interpolation; 1: exact
  *             L2 projection (default) for the high-order mortar flux.
  *  elems_per_block  0: autotune; else elements per thread block.
- *  collect_stats    1: accumulate limiter statistics (idp_limiter_stats). */
+ *  collect_stats    1: accumulate limiter statistics (idp_limiter_stats).
+ *  grid_mode  element-pass grid: 0 chosen by the autotuner (or one block per
+ *             element batch when elems_per_block is set), 1 one block per
+ *             element batch, 2 persistent (a grid of resident blocks that
+ *             loops over the batches). */
 typedef struct {
     int32_t precision;
     int32_t limiting;
@@ -111,7 +115,7 @@ typedef struct {
     int32_t mortar_projection;
     int32_t elems_per_block;
     int32_t collect_stats;
-    int32_t reserved;
+    int32_t grid_mode;
 } idp_options;
 
 /* Limiter statistics accumulated over the stages since the previous call of

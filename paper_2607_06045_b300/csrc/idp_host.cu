@@ -576,12 +576,14 @@ idp_status autotune(idp_ctx *c, const double *u, cudaStream_t st, double dt) {
     if (c->tuned) return IDP_OK;
     long long bucket = 0;
     for (long long k = c->K; k > 1; k >>= 1) ++bucket;
-    long long key = ((long long)c->NP << 48) | ((long long)c->opt.precision << 40) | ((long long)c->num_sms << 16) | bucket;
+    long long key = ((long long)c->NP << 48) | ((long long)c->opt.precision << 40) |
+                    ((long long)c->opt.grid_mode << 36) | ((long long)c->num_sms << 16) | bucket;
     if (c->opt.elems_per_block > 0) {
         int bps = 1;
         if (c->L.element_prepare(c->opt.precision, c->opt.elems_per_block, &bps) != cudaSuccess || bps < 1)
             return IDP_E_ARG;
-        c->epb = c->opt.elems_per_block; c->bps = bps; c->persistent = 0; c->tuned = true;
+        c->epb = c->opt.elems_per_block; c->bps = bps; c->persistent = c->opt.grid_mode == 2 ? 1 : 0;
+        c->tuned = true;
         return IDP_OK;
     }
     {
@@ -607,6 +609,7 @@ idp_status autotune(idp_ctx *c, const double *u, cudaStream_t st, double dt) {
         if (c->L.element_prepare(c->opt.precision, epb, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
         if ((long long)epb > 4 * c->K && epb > 1) continue;
         for (int pers = 0; pers < 2; ++pers) {
+            if ((c->opt.grid_mode == 1 && pers == 1) || (c->opt.grid_mode == 2 && pers == 0)) continue;
             int grid = element_grid(c, epb, pers, bps);
             c->L.element(c->opt.precision, epb, grid, st, c->mesh, c->slots, A);   // warm-up
             if (cudaGetLastError() != cudaSuccess) continue;                       // not launchable
@@ -662,6 +665,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (o.elems_per_block != 0 && o.elems_per_block != 1 && o.elems_per_block != 2 && o.elems_per_block != 4 &&
         o.elems_per_block != 8 && o.elems_per_block != 16)
         return IDP_E_ARG;
+    if (o.grid_mode < 0 || o.grid_mode > 2) return IDP_E_ARG;
     HostMesh H;
     H.sim_off.push_back(0);
     for (int s = 0; s < n_sims; ++s) {

@@ -90,11 +90,20 @@ def test_rejects_bad_arguments():
     assert _create(m, bounds=1) == idp.IDP_E_UNSUPPORTED
     mb = W.uniform_mesh(2, 2, bc=(W.BC_PERIODIC, W.BC_WALL, W.BC_PERIODIC, W.BC_PERIODIC))
     assert _create(mb) == idp.IDP_E_ARG
+    assert _create(m, grid_mode=3) == idp.IDP_E_ARG
     L = idp.lib()
     assert L.idp_eval_math(3, None, None, 1, None) == idp.IDP_E_ARG
     assert L.idp_eval_math(0, None, None, -1, None) == idp.IDP_E_ARG
     assert L.idp_eval_math(0, None, None, 4, None) == idp.IDP_E_ARG
     assert L.idp_eval_math(2, None, None, 0, None) == idp.IDP_OK
+
+
+def test_rejects_empty_mesh():
+    import ctypes as C
+    d, keep = idp.mesh_desc(W.uniform_mesh(2, 2))
+    d.n_leaves = 0
+    h = C.c_void_p()
+    assert idp.lib().idp_dgsem_create(C.byref(d), 3, 1.4, C.byref(idp.options()), C.byref(h)) == idp.IDP_E_ARG
 
 
 def test_valid_mesh_without_gpu_is_a_cuda_error():

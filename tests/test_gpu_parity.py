@@ -240,3 +240,43 @@ def test_fp32_form_error_cfg3():
         rc, s = ctx.idp_dgsem_limiter_stats()
         assert s["n_nonpositive"] == 0 and s["n_viol_pressure"] == 0
         ctx.close()
+
+
+def test_ragged_tails_every_launch_shape():
+    """An element count that no block size divides (a 7 x 5 base with a refined
+    box): every elements-per-block choice, one block per batch and persistent
+    grids give the same bits, and the FP64 path matches the oracle."""
+    m = W.box_refined_mesh(7, 5, (0.0, 0.0, 1.4, 1.0), (0.3, 0.2, 0.9, 0.7))
+    assert m.n_elems % 2 == 1
+    u = W.smooth_random_state(m, 3, seed=11)
+    o = oracle.Oracle(m, 3)
+    dt = o.dt(u, cfl=0.5)
+    r_o = o.rhs(u, t=0.0, dt=dt, limiting=2)
+    scale = rhs_scale(u, o.dt(u, cfl=1.0))
+    for prec in (0, 1):
+        outs = []
+        for epb in (1, 2, 4, 8, 16):
+            for gm in (1, 2):
+                ctx = idp.Context(m, 3, precision=prec, elems_per_block=epb, grid_mode=gm)
+                outs.append(gpu_rhs(ctx, u, 0.0, dt))
+                ctx.close()
+        for r in outs[1:]:
+            assert np.array_equal(r, outs[0])
+        if prec == 0:
+            assert rel_err(outs[0], r_o, scale) <= 1e-12
+
+
+def test_single_element_periodic():
+    """One element whose four faces are its own neighbours (periodic 1 x 1)."""
+    m = W.uniform_mesh(1, 1)
+    u = W.smooth_random_state(m, 4, seed=5)
+    check_rhs(m, 4, u, 2)
+    o = oracle.Oracle(m, 4)
+    u_o, t_o, _, _ = o.step(u, 10, cfl=0.5)
+    ctx = idp.Context(m, 4, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    ctx.idp_dgsem_step(ud, 10, t)
+    sc = np.abs(u_o).reshape(4, -1).max(axis=1)
+    assert (np.abs(ud.cpu().numpy() - u_o).reshape(4, -1).max(axis=1) / sc).max() <= 1e-10
+    ctx.close()
