@@ -56,6 +56,8 @@ def lib():
         L.orc_llf.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double, dp]
         L.orc_theta.restype = C.c_double
         L.orc_theta.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double]
+        L.orc_indicator.restype = C.c_double
+        L.orc_indicator.argtypes = [C.c_int, dp, dp]
         L.orc_n_mortars.restype = C.c_int
         L.orc_n_mortars.argtypes = [C.c_void_p]
         L.orc_mortars.argtypes = [C.c_void_p, ip]
@@ -134,6 +136,16 @@ def theta(u0, a, pmin, hi, gamma=1.4):
     a = np.ascontiguousarray(a, dtype=np.float64)
     return lib().orc_theta(gamma, _d(u0), _d(a), float(pmin), float(hi))
 
+
+
+def indicator(N, p):
+    """Shock indicator alpha in [0, 1] of one element from its nodal pressures
+    p[j][i] (y index j, x index i) at the LGL nodes of degree N (reading R20:
+    Hennemann et al.'s modal energy indicator, used by the combined limiting
+    of Sec. 3.5)."""
+    xi, _ = lgl(N)
+    pp = np.ascontiguousarray(p, dtype=np.float64).reshape(-1)
+    return float(lib().orc_indicator(N, xi.ctypes.data_as(C.POINTER(C.c_double)), pp.ctypes.data_as(C.POINTER(C.c_double))))
 
 def mortar_sparse(N, uL, us, gamma=1.4):
     uL = np.ascontiguousarray(uL, dtype=np.float64)

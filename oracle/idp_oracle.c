@@ -838,6 +838,59 @@ double orc_dt(const orc_ctx *c, const double *u, double time, double cfl, int ru
 }
 
 /* ------------------------------------------------------------------------ */
+/* shock indicator of the combined limiting (Sec. 3.5, Eq.                   */
+/* combination_posLim_local): the modal-energy indicator of Hennemann et al.  */
+/* applied to the pressure (reading R20)                                      */
+/* ------------------------------------------------------------------------ */
+
+/* alpha in [0, 1] from the nodal pressures p[j * np + i] of one element at
+   the LGL nodes xi of degree N. The pressure is expanded in the orthonormal
+   Legendre tensor basis, m = V^{-1} P V^{-T}; with e1 the energy of the modes
+   with max(k, l) = N, e2 that of max(k, l) = N - 1 and e0 the rest, the
+   energy fraction is E = max(e1 / (e0 + e1 + e2), e2 / (e0 + e2)); alpha is
+   the logistic map 1 / (1 + exp(-(s / T)(E - T))) with the threshold
+   T = 0.5 10^(-1.8 (N+1)^(1/4)) and s = ln((1 - 1e-4) / 1e-4), snapped to 0
+   or 1 within 1e-3 of them. */
+double orc_indicator(int N, const double *xi, const double *p) {
+    int np = N + 1;
+    double V[NPMAX * NPMAX], Vc[NPMAX * NPMAX], X[NPMAX * NPMAX], Xt[NPMAX * NPMAX];
+    for (int i = 0; i < np; ++i)
+        for (int k = 0; k < np; ++k) {
+            double Pk, dP, d2P;
+            legendre(k, xi[i], &Pk, &dP, &d2P);
+            V[i * np + k] = sqrt((2.0 * k + 1.0) / 2.0) * Pk;
+        }
+    /* X = V^{-1} P with P[i][j] = p(x_i, y_j) */
+    for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j) X[i * np + j] = p[j * np + i];
+    memcpy(Vc, V, sizeof(double) * np * np);
+    solve(np, np, Vc, X);
+    /* M^T = V^{-1} X^T, so Xt[l][k] = M[k][l] */
+    for (int k = 0; k < np; ++k)
+        for (int j = 0; j < np; ++j) Xt[j * np + k] = X[k * np + j];
+    memcpy(Vc, V, sizeof(double) * np * np);
+    solve(np, np, Vc, Xt);
+    double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+    for (int l = 0; l < np; ++l)
+        for (int k = 0; k < np; ++k) {
+            double m2 = Xt[l * np + k] * Xt[l * np + k];
+            int top = k > l ? k : l;
+            if (top == N) e1 += m2;
+            else if (top == N - 1) e2 += m2;
+            else e0 += m2;
+        }
+    double E = 0.0;
+    if (e0 + e1 + e2 > 0.0) E = e1 / (e0 + e1 + e2);
+    if (e0 + e2 > 0.0 && e2 / (e0 + e2) > E) E = e2 / (e0 + e2);
+    double T = 0.5 * pow(10.0, -1.8 * pow(N + 1.0, 0.25));
+    double sh = log((1.0 - 1e-4) / 1e-4);
+    double a = 1.0 / (1.0 + exp(-sh / T * (E - T)));
+    if (a < 1e-3) a = 0.0;
+    if (a > 1.0 - 1e-3) a = 1.0;
+    return a;
+}
+
+/* ------------------------------------------------------------------------ */
 /* limiting (Sec. 2.3)                                                       */
 /* ------------------------------------------------------------------------ */
 
@@ -902,7 +955,11 @@ enum { ST_AVOL_M = 0, ST_M, ST_NVOL, ST_AMORT_L, ST_L, ST_NMORT, ST_VRHO, ST_VP,
    limited residual m_i du_i/dt and, if utilde != NULL, utilde the limited
    stage state u + dt/m * res written in the FCT form
    u_FV + dt/m (sum l G) + dt/m (sum_S l_S H_S).
-   limiting: 0 none, 1 positivity, 2 local (bar-state density bounds). */
+   limiting: 0 none, 1 positivity, 2 local (bar-state density bounds),
+   3 combined: per interface and per mortar the factor
+   l = (1 - a) l_positivity + a l_local with a the shock indicator of the
+   element (of the mortar: the largest of its three elements), Sec. 3.5
+   Eq. combination_posLim_local. */
 int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int limiting,
               double beta, double *res_out, double *utilde, double *stats) {
     int np = c->np, nn = c->nn, K = c->K, N = c->N;
@@ -931,6 +988,17 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     }
     /* bounds (R6 and Eqs. Bounds_Positivity, Bounds_Barstates) */
     double *rmin = malloc(sizeof(double) * nn), *rmax = malloc(sizeof(double) * nn), *pmin = malloc(sizeof(double) * nn);
+    /* combined limiting: the positivity bounds beside the local ones, and
+       the indicator per element */
+    const int comb = limiting == 3;
+    double *rmin2 = malloc(sizeof(double) * nn), *rmax2 = malloc(sizeof(double) * nn);
+    double *aind = calloc((size_t)K, sizeof(double));
+    if (comb)
+        for (int e = 0; e < K; ++e) {
+            double pe[NPMAX * NPMAX], q[4];
+            for (int n = 0; n < np * np; ++n) { get_u(c, u, e * np * np + n, q); pe[n] = pressure(gm, q); }
+            aind[e] = orc_indicator(N, c->xi, pe);
+        }
     for (int i = 0; i < nn; ++i) {
         double ui[4], uj[4], q[4];
         get_u(c, u, i, ui);
@@ -949,7 +1017,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
             if (rb < lo) lo = rb;
             if (rb > hi) hi = rb;
         }
-        if (limiting == 2) {
+        if (limiting >= 2) {
             rmin[i] = lo > beta * q[0] ? lo : beta * q[0];
             rmax[i] = hi;
         } else {
@@ -958,6 +1026,9 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
         }
         if (q[0] < rmin[i]) rmin[i] = q[0];
         if (q[0] > rmax[i]) rmax[i] = q[0];
+        rmin2[i] = beta * q[0];
+        rmax2[i] = INFINITY;
+        if (q[0] < rmin2[i]) rmin2[i] = q[0];
         pmin[i] = beta * pressure(gm, q);
     }
     /* antidiffusive fluxes at interior subcell interfaces: A = F_DG - F_FV in
@@ -1001,6 +1072,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
                 }
     /* R7: Zalesak factors for density */
     double *Rp = malloc(sizeof(double) * nn), *Rm = malloc(sizeof(double) * nn);
+    double *Rp2 = malloc(sizeof(double) * nn), *Rm2 = malloc(sizeof(double) * nn);
     for (int i = 0; i < nn; ++i) {
         int e = i / (np * np), rr = i % (np * np), a = rr % np, b = rr / np;
         double Pp = 0.0, Pm = 0.0;
@@ -1023,6 +1095,11 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
         Rm[i] = (Pm < 0.0) ? (Qm / Pm < 1.0 ? Qm / Pm : 1.0) : 1.0;
         if (Rp[i] < 0.0) Rp[i] = 0.0;
         if (Rm[i] < 0.0) Rm[i] = 0.0;
+        double Qp2 = m / dt * (rmax2[i] - rfv), Qm2 = m / dt * (rmin2[i] - rfv);
+        Rp2[i] = (Pp > 0.0) ? (Qp2 / Pp < 1.0 ? Qp2 / Pp : 1.0) : 1.0;
+        Rm2[i] = (Pm < 0.0) ? (Qm2 / Pm < 1.0 ? Qm2 / Pm : 1.0) : 1.0;
+        if (Rp2[i] < 0.0) Rp2[i] = 0.0;
+        if (Rm2[i] < 0.0) Rm2[i] = 0.0;
     }
     /* R8: per interface, largest factor keeping p >= pmin at both end points
        for the Gamma-scaled single-interface update (Gamma = 2d = 4) */
@@ -1048,6 +1125,18 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
                     for (int v = 0; v < 4; ++v) { u0[v] = ufv[(size_t)v * nn + gr]; av[v] = Gam * dt / mr * A[4 * id + v]; }
                     th_r = orc_theta(gm, u0, av, pmin[gr], lr);
                     double l = th_l < th_r ? th_l : th_r;
+                    if (comb) {
+                        /* positivity-only factor of the same interface, blended */
+                        double lr2 = exempt[id] ? 1.0
+                                   : (-Ar > 0.0) ? (Rp2[gl] < Rm2[gr] ? Rp2[gl] : Rm2[gr])
+                                                 : (Rm2[gl] < Rp2[gr] ? Rm2[gl] : Rp2[gr]);
+                        for (int v = 0; v < 4; ++v) { u0[v] = ufv[(size_t)v * nn + gl]; av[v] = -Gam * dt / ml * A[4 * id + v]; }
+                        double t2l = orc_theta(gm, u0, av, pmin[gl], lr2);
+                        for (int v = 0; v < 4; ++v) { u0[v] = ufv[(size_t)v * nn + gr]; av[v] = Gam * dt / mr * A[4 * id + v]; }
+                        double t2r = orc_theta(gm, u0, av, pmin[gr], lr2);
+                        double l2 = t2l < t2r ? t2l : t2r;
+                        l = (1.0 - aind[e]) * l2 + aind[e] * l;
+                    }
                     ell[id] = l;
                     if (l < lmin[gl]) lmin[gl] = l;
                     if (l < lmin[gr]) lmin[gr] = l;
@@ -1112,7 +1201,12 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
                     H[np + p * np + l][v] = -(FL2 - Flo[np + p * np + l][v]);
                 }
         }
-        double lS = 1.0;
+        double lS = 1.0, lS2 = 1.0;
+        double am = 0.0;
+        if (comb) {
+            am = aind[L];
+            for (int p2 = 0; p2 < 2; ++p2) if (aind[c->mort[5 * m + 3 + p2]] > am) am = aind[c->mort[5 * m + 3 + p2]];
+        }
         if (mbad[m]) {
             /* R16: no admissible high-order flux, pure low order */
             for (int q = 0; q < 3 * np; ++q) for (int v = 0; v < 4; ++v) H[q][v] = 0.0;
@@ -1129,6 +1223,13 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
             if (lr < 0.0) lr = 0.0;
             double th = orc_theta(gm, u0, av, pmin[i] - TOL * fabs(pmin[i]), lr);
             if (th < lS) lS = th;
+            if (comb) {
+                double lr2 = 1.0;
+                if (av[0] < 0.0) { double t = (rmin2[i] - tolr[i] - u0[0]) / av[0]; if (t < lr2) lr2 = t; }
+                if (lr2 < 0.0) lr2 = 0.0;
+                double th2 = orc_theta(gm, u0, av, pmin[i] - TOL * fabs(pmin[i]), lr2);
+                if (th2 < lS2) lS2 = th2;
+            }
             if (g_mortar_dbg) {
                 double *o = g_mortar_dbg + ((size_t)m * 3 * np + q) * 16;
                 o[0] = i; o[1] = lr; o[2] = th;
@@ -1136,6 +1237,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
                 o[11] = rmin[i]; o[12] = rmax[i]; o[13] = pmin[i]; o[14] = ni;
             }
         }
+        if (comb && !mbad[m]) lS = (1.0 - am) * lS2 + am * lS;
         for (int q = 0; q < 3 * np; ++q) {
             int i = gnode[q];
             for (int v = 0; v < 4; ++v) corr[(size_t)v * nn + i] += lS * H[q][v];
@@ -1157,7 +1259,8 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
         }
         if (stats) {
             double p = pressure(gm, q);
-            if (q[0] < rmin[i] - 1e-13 * fabs(rmin[i]) || q[0] > rmax[i] + 1e-13 * fabs(rmax[i])) stats[ST_VRHO] += 1;
+            const double *lo_ = comb ? rmin2 : rmin, *hi_ = comb ? rmax2 : rmax;
+            if (q[0] < lo_[i] - 1e-13 * fabs(lo_[i]) || q[0] > hi_[i] + 1e-13 * fabs(hi_[i])) stats[ST_VRHO] += 1;
             if (p < pmin[i] - 1e-13 * fabs(pmin[i])) stats[ST_VP] += 1;
             if (!(q[0] > 0.0) || !(p > 0.0)) stats[ST_NONPOS] += 1;
             if (q[0] < stats[ST_MINRHO]) stats[ST_MINRHO] = q[0];
@@ -1166,6 +1269,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     }
     free(mbad); free(gh); free(sf); free(rdg); free(rfv); free(ds); free(ufv); free(rmin); free(rmax); free(pmin);
     free(A); free(Rp); free(Rm); free(tolr); free(exempt); free(ell); free(lmin); free(uvol); free(acc); free(corr);
+    free(rmin2); free(rmax2); free(aind); free(Rp2); free(Rm2);
     return 0;
 }
 
