@@ -91,7 +91,12 @@ typedef struct {
  *             limiter solves, blending, stage update and all sums in FP64.
  *  limiting   0: none (high-order DG); 1: positivity limiting
  *             (Eq. Bounds_Positivity); 2: local limiting -- bar-state density
- *             bounds (Eq. Bounds_Barstates, density part) plus positivity.
+ *             bounds (Eq. Bounds_Barstates, density part) plus positivity;
+ *             3: combined -- per interface and per mortar the factor
+ *             (1 - a) l_positivity + a l_local with a the element's shock
+ *             indicator (Hennemann et al.'s modal energy indicator of the
+ *             pressure; for a mortar the largest of its three elements),
+ *             Sec. 3.5 Eq. combination_posLim_local.
  *  bounds     0: bar-state bounds (the only kind built).
  *  dt_rule    0: IDP restriction (Eq. timestep_restriction); 1: low-order
  *             CFL estimate (Eq. CFLcondition_lowordermethod).

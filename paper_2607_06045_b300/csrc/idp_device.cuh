@@ -55,6 +55,12 @@ struct Ops {
     int slot_n[3 * NPMAX];
     int slot_p[3 * NPMAX][2 * NPMAX];
     LogTab lg;                       // table of the FP64 logarithm
+    // inverse of V_ik = sqrt((2k+1)/2) P_k(xi_i): nodal values to coefficients
+    // of the orthonormal Legendre basis (shock indicator, combined limiting)
+    double Vinv[NPMAX][NPMAX];
+    // shock indicator: threshold T = 0.5 10^(-1.8 (N+1)^(1/4)), sharpness
+    // s = ln((1 - 1e-4) / 1e-4)
+    double ind_T, ind_s;
 };
 
 // Per simulation: boundary data (ghost states as conserved variables).

@@ -24,7 +24,7 @@ struct StageArgs {
     double *out;          // step mode: u^(s+1); rhs mode: right-hand side
     int mode;             // 0: rhs, 1: step
     int comb;             // step mode: 0 out = ut, 1 out = 3/4 un + 1/4 ut, 2 out = un/3 + 2/3 ut
-    int limiting;         // 0 none, 1 positivity, 2 local
+    int limiting;         // 0 none, 1 positivity, 2 local, 3 combined (Sec. 3.5)
     int collect;          // statistics on/off
     double dt;            // rhs mode
     const unsigned long long *dtmin;  // step mode: per-sim min of m / sum 2d (ordered bits)
@@ -37,6 +37,7 @@ struct StageArgs {
     const Ops *ops;
     unsigned *status;
     StatsAcc *stats;
+    double *aind;         // combined limiting: per element shock indicator (written)
 };
 
 __device__ __forceinline__ double stage_dt(const StageArgs &A, int sim) {
@@ -66,13 +67,13 @@ struct ElemSm {
             double dtm[NN], ufv[4][NN], rmin[NN], rmax[NN];
             double tol[F32 ? 1 : NN];    // FP64 path: kTol |rho_FV|
             // pressure solve at u_FV in the form scaled by rho_FV: gm = (gamma-1) rho_FV,
-            // pm = p_min rho_FV = beta (gamma-1)(rho E - |m|^2/2), c0 = g(0); the
-            // FP32 form keeps pm only and forms gm and c0 where the FP64 solve runs
+            // pm = p_min rho_FV = beta (gamma-1)(rho E - |m|^2/2), c0 = g(0); pm is
+            // kept, gm and c0 are formed again where the FP64 solve runs
             double pms[NN];
-            double gms[F32 ? 1 : NN], c0[F32 ? 1 : NN];
             float ufvf[4][NN];       // FP32 copies for the certified admissibility check
             float dtmf[NN], gmsf[NN], pmsf[NN], c0f[NN];
             float tqf[NN];           // FP32 form: exemption threshold kTol |rho_FV| m / dt
+            FT ie[NP][3];            // combined limiting: modal energies e0, e1, e2 by column l
         };
     };
     union {
@@ -84,6 +85,7 @@ struct ElemSm {
             FT f2d[4][NP];           // 2 d_ij across the face (time-step check)
             double ibar[NIF];        // bar-state density across interior subcell interfaces
             FT i2d[NIF];
+            FT indT[NN];             // combined limiting: V^{-1} P (first half of the modal transform)
         };
         struct {                 // P2b - P5
             double Ad[NIF][4];       // antidiffusive flux A = Fdg - Ffv in FP64
@@ -99,6 +101,7 @@ struct ElemSm {
         };
         struct {                 // P3 - P5
             double Rp[NN], Rm[NN], ell[NIF];
+            double Rm2[NN];          // combined limiting: R- of the positivity bounds
         };
     };
     union {
@@ -109,6 +112,7 @@ struct ElemSm {
     // half and quarter edge lengths (and FP32 copies), (dx dy / 4) / dt
     double iA4, A4, dt, dt4A, hx, hy, qx, qy;
     float hxf, hyf, qxf, qyf, idtmf;
+    double aind;             // combined limiting: shock indicator of the element
 };
 
 template <int NP>
@@ -213,6 +217,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
     // reference tables: w, 1/w, Sbar, w_i w_j, 1/(w_i w_j) and FP32 copies
     __shared__ double s_w[NP], s_S[NP][NP], s_ww[NN], s_iww[NN];
     __shared__ float s_wf[NP], s_Sf[NP][NP], s_wwf[NN];
+    __shared__ FT s_Vinv[NP][NP];   // combined limiting: nodal values -> Legendre coefficients
 
     const int tid = threadIdx.x;
     if (tid < NP) { s_w[tid] = A.ops->w[tid]; s_wf[tid] = d2f(A.ops->w[tid]); }
@@ -223,7 +228,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
         s_ww[tid] = A.ops->w[i] * A.ops->w[j];
         s_iww[tid] = A.ops->iw[i] * A.ops->iw[j];
         s_wwf[tid] = d2f(s_ww[tid]);
+        s_Vinv[j][i] = to_ft<FT>(A.ops->Vinv[j][i]);
     }
+    const bool combined = A.limiting == 3;
     const Gas &G = A.gas;
     const double gm1 = G.gm1;
     FT ginv1;
@@ -403,6 +410,19 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * i2l;
             }
         }
+        if (combined) {
+            // shock indicator (R20), first half: T[k][j] = sum_i Vinv[k][i] p(x_i, y_j)
+            for (int k = tid; k < EPB * NP; k += NT) {
+                const int le = k / NP, kk = k - le * NP;
+                if (e0 + le >= mesh.K) continue;
+                SM &S = sm[le];
+                for (int j = 0; j < NP; ++j) {
+                    FT acc = FT(0);
+                    for (int i = 0; i < NP; ++i) acc += s_Vinv[kk][i] * S.pr[3][j * NP + i];
+                    S.indT[kk * NP + j] = acc;
+                }
+            }
+        }
         __syncthreads();
 
         // ---------------- P2: high-order subcell fluxes; low-order update ----
@@ -424,6 +444,23 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             if constexpr (F32) wh = s_wf[r] * (d == 0 ? S.hyf : S.hxf);
             else wh = s_w[r] * (d == 0 ? S.hy : S.hx);
             for (int v = 0; v < 4; ++v) S.Fdg[id][v] = wh * acc[v];
+        }
+        if (combined) {
+            // second half: m[k][l] = sum_j T[k][j] Vinv[l][j]; energies of the
+            // modes with max(k, l) = N (e1), = N - 1 (e2) and below (e0)
+            for (int k = tid; k < EPB * NP; k += NT) {
+                const int le = k / NP, l = k - le * NP;
+                if (e0 + le >= mesh.K) continue;
+                SM &S = sm[le];
+                FT en[3] = {FT(0), FT(0), FT(0)};
+                for (int kk = 0; kk < NP; ++kk) {
+                    FT m = FT(0);
+                    for (int j = 0; j < NP; ++j) m += S.indT[kk * NP + j] * s_Vinv[l][j];
+                    const int top = kk > l ? kk : l;
+                    en[top == N ? 1 : (top == N - 1 ? 2 : 0)] += m * m;
+                }
+                for (int q = 0; q < 3; ++q) S.ie[l][q] = en[q];
+            }
         }
         if (!dgmode) {
             for (int k = tid; k < EPB * NN; k += NT) {
@@ -484,7 +521,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 // bounds (R6): every interval contains rho_FV
                 const long long kq = okey(q[0]);
                 long long kmn, kmx;
-                if (A.limiting == 2) {
+                if (A.limiting >= 2) {   // local (and the local half of combined)
                     long long kb = okey(A.beta * q[0]);
                     kmn = kb > klo ? kb : klo;
                     kmx = khi;
@@ -503,7 +540,6 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double gms = gm1 * q[0], pms = A.beta * rp;
                 double c0 = gms * X - pms * q[0];
                 S.pms[n] = pms;
-                if constexpr (!F32) { S.gms[n] = gms; S.c0[n] = c0; }
                 S.dtmf[n] = d2f(dtm); S.gmsf[n] = d2f(gms); S.pmsf[n] = d2f(pms); S.c0f[n] = d2f(c0);
                 if constexpr (F32) {
                     S.tqf[n] = 1e-14f * fabsf(S.ufvf[0][n]) * (S.idtmf * s_wwf[n]);
@@ -562,6 +598,28 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             }
             __syncthreads();
             continue;
+        }
+
+        if (combined) {
+            // indicator alpha = 1 / (1 + exp(-(s/T)(E - T))), E the larger
+            // energy fraction of the two highest mode shells, snapped to 0 or
+            // 1 within 1e-3
+            for (int le = tid; le < EPB; le += NT) {
+                if (e0 + le >= mesh.K) continue;
+                SM &S = sm[le];
+                FT e0s = FT(0), e1s = FT(0), e2s = FT(0);
+                for (int l = 0; l < NP; ++l) { e0s += S.ie[l][0]; e1s += S.ie[l][1]; e2s += S.ie[l][2]; }
+                double E = 0.0;
+                const double t0 = (double)e0s + (double)e1s + (double)e2s, t1 = (double)e0s + (double)e2s;
+                if (t0 > 0.0) E = (double)e1s / t0;
+                if (t1 > 0.0 && (double)e2s / t1 > E) E = (double)e2s / t1;
+                const double T = A.ops->ind_T, sh = A.ops->ind_s;
+                double a = 1.0 / (1.0 + exp(-sh / T * (E - T)));
+                if (a < 1e-3) a = 0.0;
+                if (a > 1.0 - 1e-3) a = 1.0;
+                S.aind = a;
+                A.aind[e0 + le] = a;
+            }
         }
 
         // ---------------- P2b: antidiffusive fluxes A = Fdg - Ffv ------------
@@ -639,6 +697,17 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             }
             S.Rp[n] = Rp;
             S.Rm[n] = Rm;
+            if (combined) {
+                // positivity bounds [beta rho_FV, infinity): R+ = 1
+                const double rmin2 = dmin(A.beta * rfv, rfv), qm2 = rmin2 - rfv;
+                double Rm2 = 1.0;
+                if (nn_lt(qm2, pmm)) {
+                    if (!dneg(qm2)) Rm2 = 0.0;
+                    else if constexpr (F32) Rm2 = f2d(d2f(qm2) / d2f(pmm) * (1.0f - 0x1p-21f));
+                    else Rm2 = qm2 / pmm;
+                }
+                S.Rm2[n] = Rm2;
+            }
         }
         __syncthreads();
 
@@ -650,33 +719,40 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             SM &S = sm[le];
             int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
             double Ar = S.Ad[id][0];
-            double lr = S.ex[id] ? 1.0
-                                 : dneg(Ar) ? nn_min(S.Rp[nl], S.Rm[nr]) : nn_min(S.Rm[nl], S.Rp[nr]);
-            double th = lr;
-            // left end point: Gamma-scaled increment -4 dt/m A; right: +4 dt/m A
-            for (int side = 0; side < 2 && __double_as_longlong(th) > 0; ++side) {
-                int nd = side == 0 ? nl : nr;
-                float sgf = side == 0 ? -4.0f : 4.0f;
-                float u0f[4], af[4];
-                float sdf = sgf * S.dtmf[nd];
-                for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.Af[id][v]; }
-                // a certified FP32 yes implies c0 > 0 and rho_FV > 0
-                if (admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], d2f(th)))
-                    continue;   // the whole interval [0, th] is admissible
-                double u0[4], av[4];
-                double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
-                for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.Ad[id][v]; }
-                double gmsn, c0n;
-                if constexpr (F32) {
-                    gmsn = gm1 * u0[0];
+            // largest factor <= lr keeping both end points admissible for the
+            // Gamma-scaled increment (left -4 dt/m A, right +4 dt/m A), each
+            // end point searched below the previous one's result
+            auto pressure_factor = [&](double lr) {
+                double th = lr;
+                for (int side = 0; side < 2 && __double_as_longlong(th) > 0; ++side) {
+                    int nd = side == 0 ? nl : nr;
+                    float sgf = side == 0 ? -4.0f : 4.0f;
+                    float u0f[4], af[4];
+                    float sdf = sgf * S.dtmf[nd];
+                    for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.Af[id][v]; }
+                    // a certified FP32 yes implies c0 > 0 and rho_FV > 0
+                    if (admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], d2f(th)))
+                        continue;   // the whole interval [0, th] is admissible
+                    double u0[4], av[4];
+                    double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
+                    for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.Ad[id][v]; }
+                    const double gmsn = gm1 * u0[0];
                     const double X = u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2]);
-                    c0n = gmsn * X - S.pms[nd] * u0[0];
-                } else {
-                    gmsn = S.gms[nd]; c0n = S.c0[nd];
+                    const double c0n = gmsn * X - S.pms[nd] * u0[0];
+                    th = theta_max(gm1, u0, av, gmsn, S.pms[nd], c0n, th);
                 }
-                th = theta_max(gm1, u0, av, gmsn, S.pms[nd], c0n, th);
+                return th;
+            };
+            const double lr = S.ex[id] ? 1.0
+                                       : dneg(Ar) ? nn_min(S.Rp[nl], S.Rm[nr]) : nn_min(S.Rm[nl], S.Rp[nr]);
+            double th = pressure_factor(lr);
+            if (combined) {
+                // Eq. combination_posLim_local: l = (1 - a) l_positivity + a l_local
+                const double lr2 = S.ex[id] ? 1.0 : dneg(Ar) ? S.Rm2[nr] : S.Rm2[nl];
+                const double th2 = pressure_factor(lr2);
+                th = (1.0 - S.aind) * th2 + S.aind * th;
             }
-            S.ell[id] = th;   // min over both end points (each searched below the previous)
+            S.ell[id] = th;
         }
         __syncthreads();
 
@@ -761,7 +837,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     const bool act = nn_lt(lmin, 1.0);
                     if (act) { st_am += d2f(S.A4) * s_wwf[n] * (1.0f - d2f(lmin)); st_act++; }
                     if (nmort == 0) {
-                        const double rmn = S.rmin[n], rmx = S.rmax[n];
+                        const double rmn = combined ? dmin(A.beta * S.ufv[0][n], S.ufv[0][n]) : S.rmin[n];
+                        const double rmx = combined ? INFINITY : S.rmax[n];
                         if (dlt(uvol[0], rmn - kViolTol * fabs(rmn)) || dlt(rmx + kViolTol * fabs(rmx), uvol[0]))
                             st_vr++;
                         st_rmin = dmin(st_rmin, uvol[0]);

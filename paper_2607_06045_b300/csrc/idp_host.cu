@@ -166,6 +166,20 @@ void build_ops(int N, int proj, Ops &o) {
                 double lo = std::max(bl[k], lo0), hi = std::min(bl[k + 1], hi0);
                 o.wt[k][e * np + l] = (hi - lo > 1e-12) ? hi - lo : 0.0;
             }
+    {
+        std::vector<double> V(np * np);
+        for (int i = 0; i < np; ++i)
+            for (int k = 0; k < np; ++k) {
+                double pk, pkm1;
+                legendre_pair(k, x[i], pk, pkm1);
+                V[i * np + k] = std::sqrt((2.0 * k + 1.0) / 2.0) * pk;
+            }
+        invert(np, V.data());
+        for (int k = 0; k < np; ++k)
+            for (int i = 0; i < np; ++i) o.Vinv[k][i] = V[k * np + i];
+    }
+    o.ind_T = 0.5 * std::pow(10.0, -1.8 * std::pow(N + 1.0, 0.25));
+    o.ind_s = std::log((1.0 - 1e-4) / 1e-4);
     o.npair = 0;
     for (int k = 0; k < np; ++k)
         for (int r = 0; r < 2 * np; ++r)
@@ -438,6 +452,7 @@ struct idp_ctx {
     const double *graph_u = nullptr;
     long long n_stages = 0;
     double total_area = 0.0;   // sum of element areas (all simulations)
+    double *d_aind = nullptr;  // per element: shock indicator of the stage (combined limiting)
     double total_mortar_len = 0.0;   // sum of the large faces' lengths over the mortars
     // optional timing: 1 step spans around the graph launches; 2 steps
     // launched without the graph, with element-pass events
@@ -477,6 +492,7 @@ StageArgs base_args(idp_ctx *c) {
     A.ops = c->d_ops;
     A.status = c->d_status;
     A.stats = c->d_stats;
+    A.aind = c->d_aind;
     return A;
 }
 
@@ -658,7 +674,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     idp_options o;
     idp_options_default(&o);
     if (opts) o = *opts;
-    if (o.precision < 0 || o.precision > 1 || o.limiting < 0 || o.limiting > 2 || o.dt_rule < 0 || o.dt_rule > 1 ||
+    if (o.precision < 0 || o.precision > 1 || o.limiting < 0 || o.limiting > 3 || o.dt_rule < 0 || o.dt_rule > 1 ||
         !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0) || o.mortar_projection < 0 || o.mortar_projection > 1)
         return IDP_E_ARG;
     if (o.bounds != 0) return IDP_E_UNSUPPORTED;
@@ -783,6 +799,8 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(cudaMemset(c->d_status, 0, sizeof(unsigned)));
     if (ok) chk(cudaMalloc(&c->d_stats, sizeof(StatsAcc)));
     if (ok) chk(cudaMalloc(&c->d_part, sizeof(double) * 4 * (size_t)c->K));
+    if (ok) chk(cudaMalloc(&c->d_aind, sizeof(double) * (size_t)c->K));
+    if (ok) chk(cudaMemset(c->d_aind, 0, sizeof(double) * (size_t)c->K));
     if (ok) chk(cudaMalloc(&c->d_intout, sizeof(double) * 4 * n_sims));
     if (ok) chk(upload(&c->d_off, c->sim_off));
     if (ok) chk(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -1086,7 +1104,7 @@ void idp_dgsem_destroy(idp_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    void *ptrs[] = {c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+    void *ptrs[] = {c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
                     c->d_msmall, c->d_mnslot, c->d_siminfo, c->d_slot_block, c->d_buf1, c->d_buf2, c->d_hostbuf,
                     c->d_dtmin, c->d_tsim, c->d_dtlast, c->d_status, c->d_stats, c->d_part, c->d_intout, c->d_off};
     for (void *p : ptrs)

@@ -218,10 +218,11 @@ __global__ void __launch_bounds__(128)
 k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
     using ML = MortarLimitLaunch<NP>;
     constexpr int Q = ML::Q, MPB = ML::mpb;
-    __shared__ unsigned long long s_min[MPB];
+    __shared__ unsigned long long s_min[MPB], s_min2[MPB];
     const int lm = threadIdx.x / Q, q = threadIdx.x - lm * Q;
     const int m = blockIdx.x * MPB + lm;
-    if (threadIdx.x < MPB) s_min[threadIdx.x] = dbits(1.0);
+    const bool combined = A.limiting == 3;
+    if (threadIdx.x < MPB) { s_min[threadIdx.x] = dbits(1.0); s_min2[threadIdx.x] = dbits(1.0); }
     __syncthreads();
     if (lm < MPB && m < mesh.M && sl.bad[m] == 0) {
         const int L = mesh.m_large[m];
@@ -242,6 +243,15 @@ k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
         const double pm = pmin - kTol * fabs(pmin);
         const double th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
         atomicMin(&s_min[lm], dbits(dpos(th) ? th : 0.0));
+        if (combined) {
+            // the positivity bounds only: rho >= beta rho_FV, p >= p_min
+            const double rfv = sl.rfv[s], rmin2 = dmin(A.beta * rfv, rfv);
+            double lr2 = 1.0;
+            if (dneg(av[0])) { double t = (rmin2 - tl - u0[0]) * fast_rcp(av[0]); if (dlt(t, lr2)) lr2 = t; }
+            if (!dpos(lr2)) lr2 = 0.0;
+            const double th2 = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr2);
+            atomicMin(&s_min2[lm], dbits(dpos(th2) ? th2 : 0.0));
+        }
     }
     __syncthreads();
     if (threadIdx.x < 32) {
@@ -251,7 +261,14 @@ k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
             const int mm = blockIdx.x * MPB + j;
             if (mm >= mesh.M) continue;
             const bool bad = sl.bad[mm] != 0;
-            const double lS = bad ? 0.0 : __longlong_as_double((long long)s_min[j]);
+            double lS = bad ? 0.0 : __longlong_as_double((long long)s_min[j]);
+            if (combined && !bad) {
+                // Eq. combination_posLim_local with the largest indicator of
+                // the mortar's three elements
+                const int2 sm2 = mesh.m_small[mm];
+                const double am = fmax(A.aind[mesh.m_large[mm]], fmax(A.aind[sm2.x], A.aind[sm2.y]));
+                lS = (1.0 - am) * __longlong_as_double((long long)s_min2[j]) + am * lS;
+            }
             sl.ell[mm] = lS;
             if (A.collect) {
                 const int info = mesh.m_info[mm], dir = info & 1;
@@ -316,7 +333,8 @@ __global__ void __launch_bounds__(64) k_mortar_apply(MeshDev mesh, SlotsDev sl, 
             // rho p = (gamma-1)(rho E - |m|^2/2) against p_min rho, without division
             const double rp = A.gas.gm1 * (ut[0] * ut[3] - 0.5 * (ut[1] * ut[1] + ut[2] * ut[2]));
             const double pmin = sl.pmin[s0] * fast_rcp(sl.rfv[s0]);
-            const double rmin = sl.rmin[s0], rmax = sl.rmax[s0];
+            const double rmin = A.limiting == 3 ? dmin(A.beta * sl.rfv[s0], sl.rfv[s0]) : sl.rmin[s0];
+            const double rmax = A.limiting == 3 ? INFINITY : sl.rmax[s0];
             if (dlt(ut[0], rmin - kViolTol * fabs(rmin)) || dlt(rmax + kViolTol * fabs(rmax), ut[0])) vr++;
             if (dlt(rp, (pmin - kViolTol * fabs(pmin)) * ut[0])) vp++;
             if (!dpos(ut[0]) || !dpos(rp)) np_++;

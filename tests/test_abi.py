@@ -83,7 +83,7 @@ def test_rejects_bad_arguments():
     m = W.uniform_mesh(2, 2)
     assert _create(m, N=0) == idp.IDP_E_ARG
     assert _create(m, N=8) == idp.IDP_E_ARG
-    assert _create(m, limiting=3) == idp.IDP_E_ARG
+    assert _create(m, limiting=4) == idp.IDP_E_ARG
     assert _create(m, beta=1.5) == idp.IDP_E_ARG
     assert _create(m, cfl=0.0) == idp.IDP_E_ARG
     assert _create(m, elems_per_block=3) == idp.IDP_E_ARG

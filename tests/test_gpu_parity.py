@@ -280,3 +280,54 @@ def test_single_element_periodic():
     sc = np.abs(u_o).reshape(4, -1).max(axis=1)
     assert (np.abs(ud.cpu().numpy() - u_o).reshape(4, -1).max(axis=1) / sc).max() <= 1e-10
     ctx.close()
+
+
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_combined_limiting_rhs(N):
+    """Combined positivity/local limiting (Sec. 3.5): the limited right-hand
+    side on the cfg1 data, whose jump makes the shock indicator vary."""
+    m = W.cfg1_mesh()
+    check_rhs(m, N, W.cfg1_state(m, N), 3)
+
+
+def test_combined_limiting_dmr_full_size():
+    m = W.cfg2_mesh()
+    check_rhs(m, 3, W.cfg2_state(m, 3), 3)
+
+
+def test_combined_limiting_steps():
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    o = oracle.Oracle(m, 3)
+    u_o, t_o, _, st_o = o.step(u, 100, cfl=0.5, limiting=3)
+    ctx = idp.Context(m, 3, limiting=3, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    ctx.idp_dgsem_step(ud, 100, t)
+    sc = np.abs(u_o).reshape(4, -1).max(axis=1)
+    assert (np.abs(ud.cpu().numpy() - u_o).reshape(4, -1).max(axis=1) / sc).max() <= 1e-10
+    rc, st = ctx.idp_dgsem_limiter_stats()
+    assert st["n_nonpositive"] == 0 and st["n_viol_density"] == 0 and st["n_viol_pressure"] == 0
+    ctx.close()
+    # FP32 form of the same run
+    c32 = idp.Context(m, 3, limiting=3, cfl=0.5, precision=1)
+    ud = dev(u)
+    t = np.zeros(1)
+    c32.idp_dgsem_step(ud, 20, t)
+    u20, _, _, _ = o.step(u, 20, cfl=0.5, limiting=3)
+    mm = o.masses()
+    l1 = (mm * np.abs(ud.cpu().numpy()[0] - u20[0])).sum() / (mm * np.abs(u20[0])).sum()
+    assert l1 <= 1e-5, l1
+    c32.close()
+
+
+def test_combined_limiting_reduces_to_positivity_on_smooth_data():
+    m = W.density_wave_mesh(2)
+    u = W.density_wave_state(m, 3)
+    dt = 0.5 * oracle.Oracle(m, 3).dt(u, cfl=1.0)
+    outs = []
+    for lim in (1, 3):
+        ctx = idp.Context(m, 3, limiting=lim)
+        outs.append(gpu_rhs(ctx, u, 0.0, dt))
+        ctx.close()
+    assert np.array_equal(outs[0], outs[1])
