@@ -24,7 +24,7 @@ _LIB = os.path.join(_HERE, "liboracle.so")
 _lib = None
 
 ST_NAMES = ["alpha_vol_m", "mass", "n_vol_active", "alpha_mort_len", "len", "n_mort_active",
-            "viol_rho", "viol_p", "nonpositive", "dt_exceed", "min_rho", "min_p"]
+            "viol_rho", "viol_p", "nonpositive", "dt_exceed", "min_rho", "min_p", "viol_eta"]
 
 
 def build(force: bool = False) -> str:
@@ -65,9 +65,15 @@ def lib():
         L.orc_graph_size.restype = C.c_int
         L.orc_graph_size.argtypes = [C.c_void_p]
         L.orc_graph.argtypes = [C.c_void_p, ip, ip, dp, dp]
-        L.orc_stage.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, dp, dp, dp]
-        L.orc_rhs.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, dp, dp]
-        L.orc_step.argtypes = [C.c_void_p, dp, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_double, dp, dp]
+        L.orc_stage.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
+                                dp, dp, dp]
+        L.orc_rhs.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, dp, dp]
+        L.orc_step.argtypes = [C.c_void_p, dp, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
+                               C.c_int, dp, dp]
+        L.orc_theta_entropy.restype = C.c_double
+        L.orc_theta_entropy.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double]
+        L.orc_entropy_eta.restype = C.c_double
+        L.orc_entropy_eta.argtypes = [C.c_double, dp]
         L.orc_dt.restype = C.c_double
         L.orc_dt.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int]
         L.orc_integrals.argtypes = [C.c_void_p, dp, dp]
@@ -135,6 +141,19 @@ def theta(u0, a, pmin, hi, gamma=1.4):
     u0 = np.ascontiguousarray(u0, dtype=np.float64)
     a = np.ascontiguousarray(a, dtype=np.float64)
     return lib().orc_theta(gamma, _d(u0), _d(a), float(pmin), float(hi))
+
+
+def theta_entropy(u0, a, K, hi, gamma=1.4):
+    """Largest factor in [0, hi] keeping eta(u0 + theta a) >= K (R21)."""
+    u0 = np.ascontiguousarray(u0, dtype=np.float64)
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return lib().orc_theta_entropy(gamma, _d(u0), _d(a), float(K), float(hi))
+
+
+def entropy_eta(u, gamma=1.4):
+    """Modified specific entropy p rho^-gamma / (gamma - 1) of one state."""
+    u = np.ascontiguousarray(u, dtype=np.float64)
+    return lib().orc_entropy_eta(gamma, _d(u))
 
 
 
@@ -220,24 +239,26 @@ class Oracle:
         lib().orc_masses(self._h, _d(m))
         return m
 
-    def rhs(self, u, t=0.0, dt=0.0, limiting=2, beta=0.1, stats=None):
-        """Limited residual per unit mass; dt = 0 gives the unlimited DG RHS."""
+    def rhs(self, u, t=0.0, dt=0.0, limiting=2, beta=0.1, stats=None, bounds=0, entropy=0):
+        """Limited residual per unit mass; dt = 0 gives the unlimited DG RHS.
+        bounds: 0 bar states, 1 low-order solution; entropy: 1 adds the
+        entropy bound to local limiting."""
         u = self._u(u)
         out = np.zeros_like(u)
         st = np.zeros(16) if stats is None else stats
         if stats is None:
             lib().orc_stats_init(_d(st))
-        lib().orc_rhs(self._h, _d(u), t, dt, limiting, beta, _d(out), _d(st))
+        lib().orc_rhs(self._h, _d(u), t, dt, limiting, beta, bounds, entropy, _d(out), _d(st))
         return out
 
-    def stage(self, u, t, dt, limiting=2, beta=0.1, stats=None):
+    def stage(self, u, t, dt, limiting=2, beta=0.1, stats=None, bounds=0, entropy=0):
         """(mass-weighted limited residual, limited stage state)."""
         u = self._u(u)
         res, ut = np.zeros_like(u), np.zeros_like(u)
         st = np.zeros(16) if stats is None else stats
         if stats is None:
             lib().orc_stats_init(_d(st))
-        lib().orc_stage(self._h, _d(u), t, dt, limiting, beta, _d(res), _d(ut), _d(st))
+        lib().orc_stage(self._h, _d(u), t, dt, limiting, beta, bounds, entropy, _d(res), _d(ut), _d(st))
         return res, ut
 
     def dg_residual(self, u, t=0.0, form="evolution"):
@@ -259,15 +280,16 @@ class Oracle:
     def dt(self, u, t=0.0, cfl=0.5, rule=0):
         return lib().orc_dt(self._h, _d(self._u(u)), t, cfl, rule)
 
-    def step(self, u, nsteps, t=0.0, cfl=0.5, dt_rule=0, limiting=2, beta=0.1):
+    def step(self, u, nsteps, t=0.0, cfl=0.5, dt_rule=0, limiting=2, beta=0.1, bounds=0, entropy=0):
         """Returns (u_new, t_new, dt_history, stats dict)."""
         u = self._u(u).copy()
         tt = np.array([t])
         dts = np.zeros(max(nsteps, 1))
         st = np.zeros(16)
         lib().orc_stats_init(_d(st))
-        lib().orc_step(self._h, _d(u), nsteps, _d(tt), cfl, dt_rule, limiting, beta, _d(dts), _d(st))
-        return u, float(tt[0]), dts[:nsteps], dict(zip(ST_NAMES, st[:12].tolist()))
+        lib().orc_step(self._h, _d(u), nsteps, _d(tt), cfl, dt_rule, limiting, beta, bounds, entropy, _d(dts),
+                       _d(st))
+        return u, float(tt[0]), dts[:nsteps], dict(zip(ST_NAMES, st[:13].tolist()))
 
     def integrals(self, u):
         out = np.zeros(4)
@@ -276,4 +298,4 @@ class Oracle:
 
 
 def stats_dict(st):
-    return dict(zip(ST_NAMES, np.asarray(st)[:12].tolist()))
+    return dict(zip(ST_NAMES, np.asarray(st)[:13].tolist()))

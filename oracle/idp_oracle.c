@@ -43,6 +43,13 @@
  *   R16 a mortar whose interpolated large-side states are not admissible
  *      uses its low-order flux (alpha_S = 1), as the paper reports for
  *      interpolation near vacuum (Sec. 3.2).
+ *   R20 the combined limiting's indicator (Hennemann et al.'s modal energy
+ *      indicator of the pressure);
+ *   R21 entropy bound (Eq. Bounds_Barstates, right part): the largest
+ *      factor keeping eta >= eta_min (1 - 1e-12) for the Gamma-scaled
+ *      update, found by bisection, aimed 1e-12 relative inside, verified;
+ *   R22 low-order-solution bounds (Eq. Bounds_LowOrder): the node and its
+ *      graph neighbours' low-order states; ghost states are not neighbours.
  * Every bound interval is widened to contain the low-order value, which in
  * exact arithmetic it already does (Eq. convex_combination).
  */
@@ -940,6 +947,51 @@ double orc_theta(double gm, const double *u0, const double *a, double pmin, doub
     return 0.0;
 }
 
+/* modified specific entropy of Eq. Bounds_Barstates: eta = p rho^-gamma / (gamma - 1) */
+static double entropy_eta(double g, const double *u) {
+    return pressure(g, u) * pow(u[0], -g) / (g - 1.0);
+}
+
+/* relative relaxation of the entropy bound inside the limiter (R21) and the
+   tolerance of the entropy violation count */
+#define ETA_RELAX 1e-12
+#define ETA_VIOL 1e-11
+
+/* eta(v) >= K written without the power of a reciprocal: the internal energy
+   rho e = E - |m|^2 / (2 rho) against K rho^gamma (rho > 0). */
+static int entropy_ok(double g, const double *v, double K) {
+    if (!(v[0] > 0.0)) return 0;
+    double re = v[3] - 0.5 * (v[1] * v[1] + v[2] * v[2]) / v[0];
+    return re - K * pow(v[0], g) >= 0.0;
+}
+
+/* R21: largest theta in [0, hi] with eta(u0 + theta a) >= K. The set
+   {rho > 0, eta >= K} is convex, so the feasible thetas are an interval
+   [0, theta*]; theta* by bisection to adjacent doubles, then aimed a relative
+   1e-12 inside, verified, halved at most four times. */
+double orc_theta_entropy(double g, const double *u0, const double *a, double K, double hi) {
+    if (!(hi > 0.0) || !entropy_ok(g, u0, K)) return 0.0;
+    double v[4];
+    for (int k = 0; k < 4; ++k) v[k] = u0[k] + hi * a[k];
+    if (entropy_ok(g, v, K)) return hi;
+    double lo = 0.0, up = hi;
+    for (int it = 0; it < 4000; ++it) {
+        double mid = 0.5 * (lo + up);
+        if (!(mid > lo && mid < up)) break;
+        for (int k = 0; k < 4; ++k) v[k] = u0[k] + mid * a[k];
+        if (entropy_ok(g, v, K)) lo = mid; else up = mid;
+    }
+    double th = lo * (1.0 - 1e-12);
+    for (int it = 0; it < 4 && th > 0.0; ++it) {
+        for (int k = 0; k < 4; ++k) v[k] = u0[k] + th * a[k];
+        if (entropy_ok(g, v, K)) return th;
+        th *= 0.5;
+    }
+    return 0.0;
+}
+
+double orc_entropy_eta(double g, const double *u) { return entropy_eta(g, u); }
+
 /* optional per-mortar factor output (l_S) for inspection by the tests */
 static double *g_mortar_ell = NULL;
 void orc_set_mortar_ell_out(double *p) { g_mortar_ell = p; }
@@ -949,7 +1001,8 @@ static double *g_node_dbg = NULL;     /* [nn][8]: rho_FV, rmin, rmax, pmin, rho_
 void orc_set_node_dbg_out(double *p) { g_node_dbg = p; }
 
 /* statistics slots */
-enum { ST_AVOL_M = 0, ST_M, ST_NVOL, ST_AMORT_L, ST_L, ST_NMORT, ST_VRHO, ST_VP, ST_NONPOS, ST_DTX, ST_MINRHO, ST_MINP };
+enum { ST_AVOL_M = 0, ST_M, ST_NVOL, ST_AMORT_L, ST_L, ST_NMORT, ST_VRHO, ST_VP, ST_NONPOS, ST_DTX, ST_MINRHO, ST_MINP,
+       ST_VETA };
 
 /* One limited forward-Euler stage: on return res holds the mass-weighted
    limited residual m_i du_i/dt and, if utilde != NULL, utilde the limited
@@ -959,9 +1012,13 @@ enum { ST_AVOL_M = 0, ST_M, ST_NVOL, ST_AMORT_L, ST_L, ST_NMORT, ST_VRHO, ST_VP,
    3 combined: per interface and per mortar the factor
    l = (1 - a) l_positivity + a l_local with a the shock indicator of the
    element (of the mortar: the largest of its three elements), Sec. 3.5
-   Eq. combination_posLim_local. */
+   Eq. combination_posLim_local.
+   bounds (local limiting): 0 bar states (Eq. Bounds_Barstates), 1 the
+   low-order solution of the node and its neighbours (Eq. Bounds_LowOrder).
+   entropy (local limiting): 1 adds the lower bound on eta of the chosen kind
+   of bounds (R21). */
 int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int limiting,
-              double beta, double *res_out, double *utilde, double *stats) {
+              double beta, int bounds, int entropy, double *res_out, double *utilde, double *stats) {
     int np = c->np, nn = c->nn, K = c->K, N = c->N;
     double gm = c->gamma;
     double *gh = make_ghosts(c, u, time);
@@ -999,24 +1056,51 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
             for (int n = 0; n < np * np; ++n) { get_u(c, u, e * np * np + n, q); pe[n] = pressure(gm, q); }
             aind[e] = orc_indicator(N, c->xi, pe);
         }
+    /* entropy lower bound per node (R21), relaxed: K = eta_min (1 - ETA_RELAX) */
+    const int ent = entropy && limiting >= 2;
+    double *emin = malloc(sizeof(double) * nn);
     for (int i = 0; i < nn; ++i) {
         double ui[4], uj[4], q[4];
         get_u(c, u, i, ui);
         for (int v = 0; v < 4; ++v) q[v] = ufv[(size_t)v * nn + i];
-        double lo = ui[0], hi = ui[0];
-        for (int k = c->nb_off[i]; k < c->nb_off[i + 1]; ++k) {
-            const orc_nb *b = &c->nb[k];
-            node_or_ghost(c, u, gh, b->j, uj);
-            double nrm = sqrt(b->cx * b->cx + b->cy * b->cy);
-            double d = nrm * lambda_max(gm, ui, uj, b->cx / nrm, b->cy / nrm);
-            double fi[4], fj[4], fiy[4], fjy[4];
-            flux_n(gm, ui, 1.0, 0.0, fi); flux_n(gm, ui, 0.0, 1.0, fiy);
-            flux_n(gm, uj, 1.0, 0.0, fj); flux_n(gm, uj, 0.0, 1.0, fjy);
-            double cdf = b->cx * (fj[0] - fi[0]) + b->cy * (fjy[0] - fiy[0]);
-            double rb = 0.5 * (ui[0] + uj[0]) - cdf / (2.0 * d);
-            if (rb < lo) lo = rb;
-            if (rb > hi) hi = rb;
+        double lo, hi, elo;
+        if (bounds == 0) {
+            /* bar states ubar_(i,j) = (u_i + u_j)/2 - c_ij . (f_j - f_i) / (2 d_ij);
+               the node itself is one of them (R6) */
+            lo = ui[0]; hi = ui[0];
+            elo = entropy_eta(gm, ui);
+            for (int k = c->nb_off[i]; k < c->nb_off[i + 1]; ++k) {
+                const orc_nb *b = &c->nb[k];
+                node_or_ghost(c, u, gh, b->j, uj);
+                double nrm = sqrt(b->cx * b->cx + b->cy * b->cy);
+                double d = nrm * lambda_max(gm, ui, uj, b->cx / nrm, b->cy / nrm);
+                double fi[4], fj[4], fiy[4], fjy[4], ub[4];
+                flux_n(gm, ui, 1.0, 0.0, fi); flux_n(gm, ui, 0.0, 1.0, fiy);
+                flux_n(gm, uj, 1.0, 0.0, fj); flux_n(gm, uj, 0.0, 1.0, fjy);
+                for (int v = 0; v < 4; ++v) {
+                    double cdf = b->cx * (fj[v] - fi[v]) + b->cy * (fjy[v] - fiy[v]);
+                    ub[v] = 0.5 * (ui[v] + uj[v]) - cdf / (2.0 * d);
+                }
+                if (ub[0] < lo) lo = ub[0];
+                if (ub[0] > hi) hi = ub[0];
+                if (ent) { double eb = entropy_eta(gm, ub); if (eb < elo) elo = eb; }
+            }
+            if (ent) { double ef = entropy_eta(gm, q); if (ef < elo) elo = ef; }
+        } else {
+            /* low-order solution of the node and its neighbours (no ghosts) */
+            lo = q[0]; hi = q[0];
+            elo = ent ? entropy_eta(gm, q) : 0.0;
+            for (int k = c->nb_off[i]; k < c->nb_off[i + 1]; ++k) {
+                int j = c->nb[k].j;
+                if (j < 0) continue;
+                double qj[4];
+                for (int v = 0; v < 4; ++v) qj[v] = ufv[(size_t)v * nn + j];
+                if (qj[0] < lo) lo = qj[0];
+                if (qj[0] > hi) hi = qj[0];
+                if (ent) { double ej = entropy_eta(gm, qj); if (ej < elo) elo = ej; }
+            }
         }
+        emin[i] = elo * (1.0 - ETA_RELAX);
         if (limiting >= 2) {
             rmin[i] = lo > beta * q[0] ? lo : beta * q[0];
             rmax[i] = hi;
@@ -1122,8 +1206,10 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
                     double ml = mass(c, gl), mr = mass(c, gr);
                     for (int v = 0; v < 4; ++v) { u0[v] = ufv[(size_t)v * nn + gl]; av[v] = -Gam * dt / ml * A[4 * id + v]; }
                     th_l = orc_theta(gm, u0, av, pmin[gl], lr);
+                    if (ent) th_l = orc_theta_entropy(gm, u0, av, emin[gl], th_l);
                     for (int v = 0; v < 4; ++v) { u0[v] = ufv[(size_t)v * nn + gr]; av[v] = Gam * dt / mr * A[4 * id + v]; }
                     th_r = orc_theta(gm, u0, av, pmin[gr], lr);
+                    if (ent) th_r = orc_theta_entropy(gm, u0, av, emin[gr], th_r);
                     double l = th_l < th_r ? th_l : th_r;
                     if (comb) {
                         /* positivity-only factor of the same interface, blended */
@@ -1222,6 +1308,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
             else if (av[0] < 0.0) { double t = (rmin[i] - tolr[i] - u0[0]) / av[0]; if (t < lr) lr = t; }
             if (lr < 0.0) lr = 0.0;
             double th = orc_theta(gm, u0, av, pmin[i] - TOL * fabs(pmin[i]), lr);
+            if (ent) th = orc_theta_entropy(gm, u0, av, emin[i], th);
             if (th < lS) lS = th;
             if (comb) {
                 double lr2 = 1.0;
@@ -1262,6 +1349,8 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
             const double *lo_ = comb ? rmin2 : rmin, *hi_ = comb ? rmax2 : rmax;
             if (q[0] < lo_[i] - 1e-13 * fabs(lo_[i]) || q[0] > hi_[i] + 1e-13 * fabs(hi_[i])) stats[ST_VRHO] += 1;
             if (p < pmin[i] - 1e-13 * fabs(pmin[i])) stats[ST_VP] += 1;
+            if (ent && !comb && q[0] > 0.0 && entropy_eta(gm, q) < emin[i] / (1.0 - ETA_RELAX) * (1.0 - ETA_VIOL))
+                stats[ST_VETA] += 1;
             if (!(q[0] > 0.0) || !(p > 0.0)) stats[ST_NONPOS] += 1;
             if (q[0] < stats[ST_MINRHO]) stats[ST_MINRHO] = q[0];
             if (p < stats[ST_MINP]) stats[ST_MINP] = p;
@@ -1269,7 +1358,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     }
     free(mbad); free(gh); free(sf); free(rdg); free(rfv); free(ds); free(ufv); free(rmin); free(rmax); free(pmin);
     free(A); free(Rp); free(Rm); free(tolr); free(exempt); free(ell); free(lmin); free(uvol); free(acc); free(corr);
-    free(rmin2); free(rmax2); free(aind); free(Rp2); free(Rm2);
+    free(rmin2); free(rmax2); free(aind); free(Rp2); free(Rm2); free(emin);
     return 0;
 }
 
@@ -1280,8 +1369,8 @@ void orc_stats_init(double *stats) {
 
 /* residual per unit mass: rhs = res / m */
 int orc_rhs(const orc_ctx *c, const double *u, double time, double dt, int limiting, double beta,
-            double *rhs, double *stats) {
-    int rc = orc_stage(c, u, time, dt, limiting, beta, rhs, NULL, stats);
+            int bounds, int entropy, double *rhs, double *stats) {
+    int rc = orc_stage(c, u, time, dt, limiting, beta, bounds, entropy, rhs, NULL, stats);
     for (int i = 0; i < c->nn; ++i) {
         double m = mass(c, i);
         for (int v = 0; v < 4; ++v) rhs[(size_t)v * c->nn + i] /= m;
@@ -1292,18 +1381,18 @@ int orc_rhs(const orc_ctx *c, const double *u, double time, double dt, int limit
 /* SSP-RK3 (Shu-Osher) steps with dt recomputed from u^n every step (R10).
    dt_hist receives each step's dt. */
 int orc_step(const orc_ctx *c, double *u, int nsteps, double *time, double cfl, int dt_rule,
-             int limiting, double beta, double *dt_hist, double *stats) {
+             int limiting, double beta, int bounds, int entropy, double *dt_hist, double *stats) {
     size_t n = 4 * (size_t)c->nn;
     double *u1 = malloc(sizeof(double) * n), *u2 = malloc(sizeof(double) * n), *ut = malloc(sizeof(double) * n);
     double *res = malloc(sizeof(double) * n);
     for (int s = 0; s < nsteps; ++s) {
         double dt = orc_dt(c, u, *time, cfl, dt_rule);
         if (dt_hist) dt_hist[s] = dt;
-        orc_stage(c, u, *time, dt, limiting, beta, res, ut, stats);
+        orc_stage(c, u, *time, dt, limiting, beta, bounds, entropy, res, ut, stats);
         for (size_t k = 0; k < n; ++k) u1[k] = ut[k];
-        orc_stage(c, u1, *time + dt, dt, limiting, beta, res, ut, stats);
+        orc_stage(c, u1, *time + dt, dt, limiting, beta, bounds, entropy, res, ut, stats);
         for (size_t k = 0; k < n; ++k) u2[k] = 0.75 * u[k] + 0.25 * ut[k];
-        orc_stage(c, u2, *time + 0.5 * dt, dt, limiting, beta, res, ut, stats);
+        orc_stage(c, u2, *time + 0.5 * dt, dt, limiting, beta, bounds, entropy, res, ut, stats);
         for (size_t k = 0; k < n; ++k) u[k] = u[k] / 3.0 + 2.0 / 3.0 * ut[k];
         *time += dt;
     }
