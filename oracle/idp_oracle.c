@@ -47,7 +47,8 @@
  *      indicator of the pressure);
  *   R21 entropy bound (Eq. Bounds_Barstates, right part): the largest
  *      factor keeping eta >= eta_min (1 - 1e-12) for the Gamma-scaled
- *      update, found by bisection, aimed 1e-12 relative inside, verified;
+ *      update with a margin of 1e-14 of the terms of the entropy function
+ *      above rounding, found by bisection, verified;
  *   R22 low-order-solution bounds (Eq. Bounds_LowOrder): the node and its
  *      graph neighbours' low-order states; ghost states are not neighbours.
  * Every bound interval is widened to contain the low-order value, which in
@@ -957,34 +958,39 @@ static double entropy_eta(double g, const double *u) {
 #define ETA_RELAX 1e-12
 #define ETA_VIOL 1e-11
 
-/* eta(v) >= K written without the power of a reciprocal: the internal energy
-   rho e = E - |m|^2 / (2 rho) against K rho^gamma (rho > 0). */
-static int entropy_ok(double g, const double *v, double K) {
-    if (!(v[0] > 0.0)) return 0;
-    double re = v[3] - 0.5 * (v[1] * v[1] + v[2] * v[2]) / v[0];
-    return re - K * pow(v[0], g) >= 0.0;
+/* Psi(v) = rho e(v) - K rho(v)^gamma with rho e = E - |m|^2 / (2 rho): for
+   rho > 0, Psi >= 0 exactly when eta(v) >= K. -inf where rho <= 0. */
+static double entropy_psi(double g, const double *v, double K) {
+    if (!(v[0] > 0.0)) return -INFINITY;
+    return v[3] - 0.5 * (v[1] * v[1] + v[2] * v[2]) / v[0] - K * pow(v[0], g);
 }
 
-/* R21: largest theta in [0, hi] with eta(u0 + theta a) >= K. The set
-   {rho > 0, eta >= K} is convex, so the feasible thetas are an interval
-   [0, theta*]; theta* by bisection to adjacent doubles, then aimed a relative
-   1e-12 inside, verified, halved at most four times. */
+/* R21: the entropy factor. The target is Psi >= delta with
+   delta = 1e-14 (|E_0| + K rho_0^gamma), a margin above the rounding of Psi
+   (a few units in the last place of its terms), so that the decision and the
+   root do not depend on that rounding; the set {Psi >= delta} is convex (Psi
+   is concave), so the admissible thetas are an interval [0, theta*]. hi is
+   returned when it meets the target; otherwise theta* by bisection to
+   adjacent doubles, verified against Psi >= 0 and halved at most four times
+   (a safeguard). */
 double orc_theta_entropy(double g, const double *u0, const double *a, double K, double hi) {
-    if (!(hi > 0.0) || !entropy_ok(g, u0, K)) return 0.0;
+    if (!(hi > 0.0) || !(u0[0] > 0.0)) return 0.0;
+    const double delta = 1e-14 * (fabs(u0[3]) + K * pow(u0[0], g));
     double v[4];
     for (int k = 0; k < 4; ++k) v[k] = u0[k] + hi * a[k];
-    if (entropy_ok(g, v, K)) return hi;
+    if (entropy_psi(g, v, K) >= delta) return hi;
+    if (!(entropy_psi(g, u0, K) >= delta)) return 0.0;
     double lo = 0.0, up = hi;
     for (int it = 0; it < 4000; ++it) {
         double mid = 0.5 * (lo + up);
         if (!(mid > lo && mid < up)) break;
         for (int k = 0; k < 4; ++k) v[k] = u0[k] + mid * a[k];
-        if (entropy_ok(g, v, K)) lo = mid; else up = mid;
+        if (entropy_psi(g, v, K) >= delta) lo = mid; else up = mid;
     }
-    double th = lo * (1.0 - 1e-12);
+    double th = lo;
     for (int it = 0; it < 4 && th > 0.0; ++it) {
         for (int k = 0; k < 4; ++k) v[k] = u0[k] + th * a[k];
-        if (entropy_ok(g, v, K)) return th;
+        if (entropy_psi(g, v, K) >= 0.0) return th;
         th *= 0.5;
     }
     return 0.0;
