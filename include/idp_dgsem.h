@@ -97,7 +97,12 @@ typedef struct {
  *             indicator (Hennemann et al.'s modal energy indicator of the
  *             pressure; for a mortar the largest of its three elements),
  *             Sec. 3.5 Eq. combination_posLim_local.
- *  bounds     0: bar-state bounds (the only kind built).
+ *  bounds     kind of the local bounds (limiting 2 and the local half of 3):
+ *             0: bar states of the node and its graph neighbours
+ *             (Eq. Bounds_Barstates); 1: the low-order solution of the node
+ *             and its neighbours (Eq. Bounds_LowOrder; ghost states are not
+ *             neighbours). Kind 1 adds a low-order pre-pass over the elements
+ *             and a per-mortar gather to every limited stage.
  *  dt_rule    0: IDP restriction (Eq. timestep_restriction); 1: low-order
  *             CFL estimate (Eq. CFLcondition_lowordermethod).
  *  beta       positivity factor of Eq. Bounds_Positivity (paper: 0.1).
@@ -109,7 +114,11 @@ typedef struct {
  *  grid_mode  element-pass grid: 0 chosen by the autotuner (or one block per
  *             element batch when elems_per_block is set), 1 one block per
  *             element batch, 2 persistent (a grid of resident blocks that
- *             loops over the batches). */
+ *             loops over the batches).
+ *  entropy_bound  1: local limiting also keeps the modified specific entropy
+ *             eta = p rho^-gamma / (gamma - 1) at or above the minimum of eta
+ *             over the bounds' states (right parts of Eqs. Bounds_Barstates
+ *             and Bounds_LowOrder), relaxed by 1e-12 relative; 0: off. */
 typedef struct {
     int32_t precision;
     int32_t limiting;
@@ -121,6 +130,7 @@ typedef struct {
     int32_t elems_per_block;
     int32_t collect_stats;
     int32_t grid_mode;
+    int32_t entropy_bound;
 } idp_options;
 
 /* Limiter statistics accumulated over the stages since the previous call of
@@ -138,6 +148,7 @@ typedef struct {
     int64_t n_nonpositive;      /* node-stages with rho <= 0 or p <= 0 */
     int64_t n_dt_exceed;        /* node-stages with dt sum_j 2 d_ij / m_i > 1 */
     double min_rho, min_p;      /* over limited stage states */
+    int64_t n_viol_entropy;     /* node-stages with eta below its bound beyond 1e-11 relative */
 } idp_limiter_stats;
 
 typedef struct idp_ctx idp_ctx;
@@ -216,7 +227,9 @@ enum {
     IDP_K_MORTAR_LIMIT = 4, /* one limiting factor per mortar */
     IDP_K_MORTAR_APPLY = 5, /* limited mortar corrections, stage at mortar nodes */
     IDP_K_TIME_ADVANCE = 6, /* per-simulation time */
-    IDP_NKERNELS = 7
+    IDP_K_ELEMENT_LO = 7,   /* low-order pre-pass of the element pass (bounds 1) */
+    IDP_K_MORTAR_LOB = 8,   /* low-order bounds across mortars (bounds 1) */
+    IDP_NKERNELS = 9
 };
 
 /* Measurement support (the paper has no counterpart). mode 1: each step's

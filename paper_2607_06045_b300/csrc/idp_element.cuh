@@ -38,6 +38,11 @@ struct StageArgs {
     unsigned *status;
     StatsAcc *stats;
     double *aind;         // combined limiting: per element shock indicator (written)
+    // local-limiting variants (extended element kernel only)
+    int entropy;          // 1: entropy bound (R21)
+    int lob;              // 1: low-order-solution bounds (Eq. Bounds_LowOrder)
+    int pass;             // 1: low-order pre-pass (writes lofv and stops after the low-order update)
+    double *lofv;         // [2][K (N+1)^2]: rho_FV and s(u_FV) of every node (pre-pass output)
 };
 
 __device__ __forceinline__ double stage_dt(const StageArgs &A, int sim) {
@@ -53,10 +58,12 @@ __device__ __forceinline__ double stage_time(const StageArgs &A, int sim, double
 // antidiffusive fluxes, the P1-P2b subcell fluxes with the P3-P5 factors, and
 // the state (read for the last time by its own node in P2) with that node's
 // low-order residual.
-template <int NP, typename FT>
+template <int NP, typename FT, bool EXT = false>
 struct ElemSm {
     static constexpr int NN = NP * NP, N = NP - 1, NPAIR = NP * (NP - 1) / 2, NIF = 2 * NP * (NP - 1);
     static constexpr bool F32 = sizeof(FT) == 4;
+    // extended kernel (entropy bound, low-order bounds): sizes of its arrays
+    static constexpr int XN = EXT ? NN : 1, XI = EXT ? NIF : 1, XF = EXT ? 4 : 1;
     union {
         struct {                 // P0 - P1
             FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
@@ -74,6 +81,7 @@ struct ElemSm {
             float dtmf[NN], gmsf[NN], pmsf[NN], c0f[NN];
             float tqf[NN];           // FP32 form: exemption threshold kTol |rho_FV| m / dt
             FT ie[NP][3];            // combined limiting: modal energies e0, e1, e2 by column l
+            double lnK[XN];          // entropy bound: ln K per node
         };
     };
     union {
@@ -86,6 +94,10 @@ struct ElemSm {
             double ibar[NIF];        // bar-state density across interior subcell interfaces
             FT i2d[NIF];
             FT indT[NN];             // combined limiting: V^{-1} P (first half of the modal transform)
+            // entropy bound: s = ln p - gamma ln rho of the node, of the bar
+            // states at interior interfaces and across faces (or, with
+            // low-order bounds, of the neighbour's u_FV across faces)
+            double sn[XN], ibs[XI], fbs[XF][NP];
         };
         struct {                 // P2b - P5
             double Ad[NIF][4];       // antidiffusive flux A = Fdg - Ffv in FP64
@@ -130,8 +142,8 @@ struct PairTab {
     }
 };
 
-template <int NP, typename FT>
-__device__ __forceinline__ Prim<FT> load_prim(const ElemSm<NP, FT> &S, int n) {
+template <int NP, typename FT, bool EXT>
+__device__ __forceinline__ Prim<FT> load_prim(const ElemSm<NP, FT, EXT> &S, int n) {
     Prim<FT> q;
     q.rho = S.pr[0][n]; q.v1 = S.pr[1][n]; q.v2 = S.pr[2][n]; q.p = S.pr[3][n]; q.c = S.pr[4][n];
     q.E = S.pr[5][n]; q.lr = S.pr[6][n]; q.lb = S.pr[7][n]; q.beta = S.pr[8][n];
@@ -157,8 +169,9 @@ __device__ __forceinline__ int slot_of(int ft, int m, int t) {
 // the minimum pressure (a diagnostic, FP32) as a ratio compared without
 // division.
 __device__ __forceinline__ void block_stats(const StageArgs &A, float am, unsigned nact, unsigned nvr, unsigned nvp,
-                                            unsigned nnp, double rmin_, float pn, float pd) {
+                                            unsigned nnp, double rmin_, float pn, float pd, unsigned nve = 0u) {
     const unsigned FULL = 0xffffffffu;
+    nve = __reduce_add_sync(FULL, nve);
     nact = __reduce_add_sync(FULL, nact);
     nvr = __reduce_add_sync(FULL, nvr);
     nvp = __reduce_add_sync(FULL, nvp);
@@ -184,6 +197,7 @@ __device__ __forceinline__ void block_stats(const StageArgs &A, float am, unsign
         if (nvr) atomicAdd(&A.stats->n_vrho, (unsigned long long)nvr);
         if (nvp) atomicAdd(&A.stats->n_vp, (unsigned long long)nvp);
         if (nnp) atomicAdd(&A.stats->n_nonpos, (unsigned long long)nnp);
+        if (nve) atomicAdd(&A.stats->n_veta, (unsigned long long)nve);
         if (rk > 0ull && rk < 0x7FF0000000000000ull) atomicMin(&A.stats->min_rho_bits, rk);
         if (anyp && pd > 0.0f) {
             const double pmin_ = f2d(pn / pd);
@@ -203,12 +217,15 @@ struct ElemLaunch {
     static constexpr int min_blocks_f64 = 512 / threads > 0 ? 512 / threads : 1;
 };
 
-template <int NP, typename FT, int EPB>
+// EXT: the extended kernel of the local-limiting variants (entropy bound,
+// low-order-solution bounds with their pre-pass); the default kernel has
+// neither, so its shared memory and registers do not pay for them.
+template <int NP, typename FT, int EPB, bool EXT>
 __global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads,
                                   sizeof(FT) == 4 ? ElemLaunch<NP, EPB>::min_blocks_f32
                                                   : ElemLaunch<NP, EPB>::min_blocks_f64)
 k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
-    using SM = ElemSm<NP, FT>;
+    using SM = ElemSm<NP, FT, EXT>;
     constexpr int NN = NP * NP, N = NP - 1, NPAIR = SM::NPAIR, NIF = SM::NIF;
     constexpr int NT = ElemLaunch<NP, EPB>::threads;
     constexpr bool F32 = sizeof(FT) == 4;
@@ -239,6 +256,12 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
     const size_t KN = (size_t)mesh.K * NN;
     const bool limited = A.limiting > 0;
     const bool dgmode = (A.mode == 0 && A.dt == 0.0) || !limited;
+    // extended kernel: entropy bound (local half), low-order bounds and the
+    // low-order pre-pass that feeds them
+    const bool ent = EXT && A.entropy && A.limiting >= 2;
+    const bool lob = EXT && A.lob && A.limiting >= 2;
+    const bool pre = EXT && A.pass == 1;
+    const size_t KNL = EXT ? KN : 0;
 
     for (int e0 = blockIdx.x * EPB; e0 < mesh.K; e0 += gridDim.x * EPB) {
         // ---------------- P0: states, primitives, outside traces -------------
@@ -308,14 +331,14 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
         __syncthreads();
 
         // ---------------- P1: pair fluxes, face fluxes, interior FV ----------
-        for (int k = tid; k < EPB * 2 * NP * NPAIR; k += NT) {
+        for (int k = tid; k < (pre ? 0 : EPB * 2 * NP * NPAIR); k += NT) {
             int le = k / (2 * NP * NPAIR), rem = k - le * (2 * NP * NPAIR);
             int d = rem / (NP * NPAIR), r = (rem / NPAIR) % NP, pi = rem % NPAIR;
             if (e0 + le >= mesh.K) continue;
             SM &S = sm[le];
             int a, b;
             PairTab<NP>::ab(pi, a, b);
-            Prim<FT> pa = load_prim<NP, FT>(S, nodeid<NP>(d, r, a)), pb = load_prim<NP, FT>(S, nodeid<NP>(d, r, b));
+            Prim<FT> pa = load_prim<NP, FT, EXT>(S, nodeid<NP>(d, r, a)), pb = load_prim<NP, FT, EXT>(S, nodeid<NP>(d, r, b));
             FT f[4];
             ranocha<FT>(pa, pb, d, ginv1, f);
             for (int v = 0; v < 4; ++v) S.pair[d][r][pi][v] = f[v];
@@ -337,19 +360,29 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 const double sgn = (s & 1) ? -1.0 : 1.0;
                 for (int v = 0; v < 4; ++v) S.face[s][t][v] = sgn * src[(size_t)v * sl.S + q];
                 if (!dgmode) {
-                    S.fbar[s][t] = sl.rbmin[q];
-                    S.fbar2[s][t] = sl.rbmax[q];
+                    if (lob && !pre) {
+                        S.fbar[s][t] = sl.lbmin[q];
+                        S.fbar2[s][t] = sl.lbmax[q];
+                        if (ent) S.fbs[s][t] = sl.lsmin[q];
+                    } else {
+                        S.fbar[s][t] = sl.rbmin[q];
+                        S.fbar2[s][t] = sl.rbmax[q];
+                        if (ent && !pre) S.fbs[s][t] = sl.sbmin[q];
+                    }
                     S.f2d[s][t] = to_ft<FT>(sl.dsum[q]);
                 }
                 continue;
             }
             int d = s >> 1, n = face_node<NP>(s, t);
             const double *out = S.outs[s][t];
-            Prim<FT> pi = load_prim<NP, FT>(S, n);
+            Prim<FT> pi = load_prim<NP, FT, EXT>(S, n);
             FT f[4], lam;
             double i2l;
             // left/bottom state first, so that both elements of a face form
             // the same bits
+            // entropy of the face bar state (bar-state bounds, entropy bound)
+            const bool fent = ent && !lob && !pre;
+            double fs = 0.0;
             if constexpr (F32) {
                 float m1f, m2f;
                 Prim<float> po = make_prim_f32(G, out[0], out[1], out[2], out[3], false, m1f, m2f);
@@ -360,7 +393,14 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 float whf = s_wf[t] * (d == 0 ? S.hyf : S.hxf);
                 for (int v = 0; v < 4; ++v) S.face[s][t][v] = f2d(whf * f[v]);
                 S.f2d[s][t] = whf * lam;
-                i2l = f2d(0.5f / lam);
+                const float i2lf = 0.5f / lam;
+                i2l = f2d(i2lf);
+                if (EXT && fent) {
+                    float fi[4], fo[4];
+                    phys_flux<float>(ui[1], ui[2], ui[3], pi.p, d == 0 ? pi.v1 : pi.v2, d, fi);
+                    phys_flux<float>(uo[1], uo[2], uo[3], po.p, d == 0 ? po.v1 : po.v2, d, fo);
+                    fs = bar_entropy<float>(G, ui, fi, uo, fo, (s == 1 || s == 3) ? i2lf : -i2lf);
+                }
             } else {
                 Prim<FT> po = make_prim<FT>(G, out[0], out[1], out[2], out[3], false);
                 double ui[4] = {S.u[0][n], S.u[1][n], S.u[2][n], S.u[3][n]};
@@ -370,11 +410,35 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 for (int v = 0; v < 4; ++v) S.face[s][t][v] = wh * f[v];
                 S.f2d[s][t] = wh * lam;
                 i2l = 0.5 * fast_rcp(lam);
+                if (EXT && fent) {
+                    double fi[4], fo[4];
+                    phys_flux<double>(ui[1], ui[2], ui[3], pi.p, d == 0 ? pi.v1 : pi.v2, d, fi);
+                    phys_flux<double>(out[1], out[2], out[3], po.p, d == 0 ? po.v1 : po.v2, d, fo);
+                    fs = bar_entropy<double>(G, ui, fi, out, fo, (s == 1 || s == 3) ? i2l : -i2l);
+                }
             }
             double sg = (s == 1 || s == 3) ? 1.0 : -1.0;
             double fb = 0.5 * (S.u[0][n] + out[0]) - sg * (out[1 + d] - S.u[1 + d][n]) * i2l;
-            S.fbar[s][t] = fb;
-            S.fbar2[s][t] = fb;
+            if (EXT && lob && !pre) {
+                // low-order bounds: the neighbour's u_FV across a conforming
+                // face; a ghost state is not a neighbour
+                if (ft == FT_CONF) {
+                    const int4 nb4 = mesh.fnbr[e];
+                    const int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
+                    const size_t go = (size_t)nb * NN + face_node<NP>(s ^ 1, t);
+                    S.fbar[s][t] = A.lofv[go];
+                    S.fbar2[s][t] = A.lofv[go];
+                    if (ent) S.fbs[s][t] = A.lofv[KNL + go];
+                } else {
+                    S.fbar[s][t] = INFINITY;
+                    S.fbar2[s][t] = -INFINITY;
+                    if (ent) S.fbs[s][t] = INFINITY;
+                }
+            } else {
+                S.fbar[s][t] = fb;
+                S.fbar2[s][t] = fb;
+                if (EXT && fent) S.fbs[s][t] = fs;
+            }
         }
         if (!dgmode) {
             for (int k = tid; k < EPB * NIF; k += NT) {
@@ -383,7 +447,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 int d = id / (NP * N), r = (id / N) % NP, a = id % N;
                 SM &S = sm[le];
                 int na = nodeid<NP>(d, r, a), nb = nodeid<NP>(d, r, a + 1);
-                Prim<FT> pa = load_prim<NP, FT>(S, na), pb = load_prim<NP, FT>(S, nb);
+                Prim<FT> pa = load_prim<NP, FT, EXT>(S, na), pb = load_prim<NP, FT, EXT>(S, nb);
                 FT vna = d == 0 ? pa.v1 : pa.v2, vnb = d == 0 ? pb.v1 : pb.v2;
                 FT la = fabs(vna) + pa.c, lb = fabs(vnb) + pb.c;
                 FT lam = la > lb ? la : lb;
@@ -405,12 +469,29 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 }
                 S.i2d[id] = FT(2) * cc * lam;
                 double i2l;
-                if constexpr (F32) i2l = f2d(0.5f / lam);
-                else i2l = 0.5 * fast_rcp(lam);
+                FT i2lt;
+                if constexpr (F32) { i2lt = 0.5f / lam; i2l = f2d(i2lt); }
+                else { i2l = 0.5 * fast_rcp(lam); i2lt = i2l; }
                 S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * i2l;
+                if (EXT && ent && !lob && !pre) S.ibs[id] = bar_entropy<FT>(G, ua, fa, ub, fb, i2lt);
+            }
+            if (EXT && ent && !lob && !pre) {
+                // s of the node itself, one of its bar states (R6)
+                for (int k = tid; k < EPB * NN; k += NT) {
+                    const int le = k / NN, n = k - le * NN;
+                    if (e0 + le >= mesh.K) continue;
+                    SM &S = sm[le];
+                    if constexpr (F32) {
+                        const float r = S.pr[0][n], p = S.pr[3][n];
+                        S.sn[n] = (r > 0.0f && p > 0.0f) ? (double)(logf(p) - G.gf * logf(r)) : -INFINITY;
+                    } else {
+                        // ln p = ln rho - ln beta
+                        S.sn[n] = (1.0 - G.g) * S.pr[6][n] - S.pr[7][n];
+                    }
+                }
             }
         }
-        if (combined) {
+        if (combined && !pre) {
             // shock indicator (R20), first half: T[k][j] = sum_i Vinv[k][i] p(x_i, y_j)
             for (int k = tid; k < EPB * NP; k += NT) {
                 const int le = k / NP, kk = k - le * NP;
@@ -426,7 +507,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
         __syncthreads();
 
         // ---------------- P2: high-order subcell fluxes; low-order update ----
-        for (int k = tid; k < EPB * NIF; k += NT) {
+        for (int k = tid; k < (pre ? 0 : EPB * NIF); k += NT) {
             int le = k / NIF, id = k - le * NIF, e = e0 + le;
             if (e >= mesh.K) continue;
             int d = id / (NP * N), r = (id / N) % NP, a = id % N;
@@ -445,7 +526,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             else wh = s_w[r] * (d == 0 ? S.hy : S.hx);
             for (int v = 0; v < 4; ++v) S.Fdg[id][v] = wh * acc[v];
         }
-        if (combined) {
+        if (combined && !pre) {
             // second half: m[k][l] = sum_j T[k][j] Vinv[l][j]; energies of the
             // modes with max(k, l) = N (e1), = N - 1 (e2) and below (e0)
             for (int k = tid; k < EPB * NP; k += NT) {
@@ -470,7 +551,12 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 int i = n % NP, j = n / NP;
                 double dtm = S.dt4A * s_iww[n];
                 double L[4] = {0, 0, 0, 0};
-                long long klo = okey(S.u[0][n]), khi = klo;
+                // bar-state bounds start from the node itself (R6); the
+                // low-order bounds add the node's u_FV below
+                long long klo = lob ? okey(INFINITY) : okey(S.u[0][n]);
+                long long khi = lob ? okey(-INFINITY) : klo;
+                double smin = 0.0;
+                if (EXT && ent) smin = lob ? INFINITY : S.sn[n];
                 FT ds = FT(0);
                 // x direction: left then right; y: bottom then top. Interior
                 // subcell interfaces and element faces (conforming, boundary or
@@ -495,8 +581,18 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                             const double *src = interior ? S.Fv[id] : S.face[s][row];
                             for (int v = 0; v < 4; ++v) fl[v] = src[v];
                         }
-                        const double blo = interior ? S.ibar[id] : S.fbar[s][row];
-                        const double bhi = interior ? S.ibar[id] : S.fbar2[s][row];
+                        double blo = interior ? S.ibar[id] : S.fbar[s][row];
+                        double bhi = interior ? S.ibar[id] : S.fbar2[s][row];
+                        if (EXT && (lob || ent) && !pre) {
+                            // neighbour node inside the element
+                            const int nbn = d == 0 ? (side == 0 ? n - 1 : n + 1) : (side == 0 ? n - NP : n + NP);
+                            const size_t gn = (size_t)e * NN + (interior ? nbn : n);
+                            if (lob && interior) { blo = A.lofv[gn]; bhi = blo; }
+                            if (ent) {
+                                const double sv = interior ? (lob ? A.lofv[KNL + gn] : S.ibs[id]) : S.fbs[s][row];
+                                smin = dmin(smin, sv);
+                            }
+                        }
                         const FT dsv = interior ? S.i2d[id] : S.f2d[s][row];
                         for (int v = 0; v < 4; ++v) {
                             if (d == 0 && side == 0) L[v] = fl[v];
@@ -513,6 +609,13 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double q[4];
                 S.dtm[n] = dtm;
                 for (int v = 0; v < 4; ++v) q[v] = S.u[v][n] + dtm * L[v];
+                if (EXT && pre) {
+                    // low-order pre-pass: rho_FV and s(u_FV) of every node
+                    const size_t gi = (size_t)e * NN + n;
+                    A.lofv[gi] = q[0];
+                    if (A.entropy) A.lofv[KNL + gi] = entropy_s(G, q[0], q[1], q[2], q[3]);
+                    continue;
+                }
                 for (int v = 0; v < 4; ++v) {
                     S.lfv[v][n] = L[v];   // shares storage with u[v][n], read above
                     S.ufv[v][n] = q[v];
@@ -533,6 +636,10 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 kmx = kq > kmx ? kq : kmx;
                 S.rmin[n] = okey_value(kmn);
                 S.rmax[n] = okey_value(kmx);
+                if (EXT && ent) {
+                    // entropy bound (R21): widened to contain u_FV, relaxed
+                    S.lnK[n] = dmin(smin, entropy_s(G, q[0], q[1], q[2], q[3])) + G.eoff;
+                }
                 // rho p = (gamma-1) X, X = rho E - |m|^2/2; the scaled pressure
                 // solve: gm = (gamma-1) rho, pm = beta rho p, c0 = gm X - pm rho
                 double X = q[0] * q[3] - 0.5 * (q[1] * q[1] + q[2] * q[2]);
@@ -551,6 +658,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             }
         }
         __syncthreads();
+        if (EXT && pre) continue;   // the pre-pass ends with u_FV
 
         if (dgmode) {
             // ------------- unlimited high-order residual (Eq. evolutionformula)
@@ -722,7 +830,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             // largest factor <= lr keeping both end points admissible for the
             // Gamma-scaled increment (left -4 dt/m A, right +4 dt/m A), each
             // end point searched below the previous one's result
-            auto pressure_factor = [&](double lr) {
+            // (with_ent: then also the entropy bound, R21)
+            auto pressure_factor = [&](double lr, bool with_ent) {
                 double th = lr;
                 for (int side = 0; side < 2 && __double_as_longlong(th) > 0; ++side) {
                     int nd = side == 0 ? nl : nr;
@@ -731,25 +840,28 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     float sdf = sgf * S.dtmf[nd];
                     for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.Af[id][v]; }
                     // a certified FP32 yes implies c0 > 0 and rho_FV > 0
-                    if (admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], d2f(th)))
-                        continue;   // the whole interval [0, th] is admissible
+                    const bool cert = admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], d2f(th));
+                    if (cert && !(EXT && with_ent)) continue;   // the whole interval [0, th] is admissible
                     double u0[4], av[4];
                     double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
                     for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.Ad[id][v]; }
-                    const double gmsn = gm1 * u0[0];
-                    const double X = u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2]);
-                    const double c0n = gmsn * X - S.pms[nd] * u0[0];
-                    th = theta_max(gm1, u0, av, gmsn, S.pms[nd], c0n, th);
+                    if (!cert) {
+                        const double gmsn = gm1 * u0[0];
+                        const double X = u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2]);
+                        const double c0n = gmsn * X - S.pms[nd] * u0[0];
+                        th = theta_max(gm1, u0, av, gmsn, S.pms[nd], c0n, th);
+                    }
+                    if (EXT && with_ent) th = theta_entropy(G, u0, av, S.lnK[nd], th);
                 }
                 return th;
             };
             const double lr = S.ex[id] ? 1.0
                                        : dneg(Ar) ? nn_min(S.Rp[nl], S.Rm[nr]) : nn_min(S.Rm[nl], S.Rp[nr]);
-            double th = pressure_factor(lr);
+            double th = pressure_factor(lr, ent);
             if (combined) {
                 // Eq. combination_posLim_local: l = (1 - a) l_positivity + a l_local
                 const double lr2 = S.ex[id] ? 1.0 : dneg(Ar) ? S.Rm2[nr] : S.Rm2[nl];
-                const double th2 = pressure_factor(lr2);
+                const double th2 = pressure_factor(lr2, false);
                 th = (1.0 - S.aind) * th2 + S.aind * th;
             }
             S.ell[id] = th;
@@ -760,7 +872,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
         {
             float st_am = 0.0f, st_pn = 0.0f, st_pd = 0.0f;
             double st_rmin = INFINITY;
-            unsigned st_act = 0, st_vr = 0, st_vp = 0, st_np = 0;
+            unsigned st_act = 0, st_vr = 0, st_vp = 0, st_np = 0, st_ve = 0;
             for (int k = tid; k < EPB * NN; k += NT) {
                 int le = k / NN, n = k - le * NN, e = e0 + le;
                 if (e >= mesh.K) continue;
@@ -817,6 +929,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         }
                         sl.rmin[q] = S.rmin[n]; sl.rmax[q] = S.rmax[n];
                         sl.pmin[q] = S.pms[n]; sl.rfv[q] = S.ufv[0][n];
+                        if (EXT && ent) sl.lnK[q] = S.lnK[n];
                         sl.tol[q] = tol_n; sl.mass[q] = mi; sl.nmort[q] = (float)nmort;
                     }
                 }
@@ -862,11 +975,15 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         }
                         // minimum p over limited nodes (FP32 statistic)
                         if (act && pmin_n > 0.0f && !(st_pd > 0.0f && st_pn <= pmin_n)) { st_pn = pmin_n; st_pd = 1.0f; }
+                        // entropy bound (R21): eta < eta_min (1 - kEtaViol)
+                        if (EXT && ent && !combined &&
+                            dlt(entropy_s(G, uvol[0], uvol[1], uvol[2], uvol[3]), S.lnK[n] + G.eviol))
+                            st_ve++;
                     }
                 }
             }
-            if (A.collect) block_stats(A, st_am, st_act, st_vr, st_vp, st_np, st_rmin, st_pn, st_pd);
-            if ((st_vr | st_vp | st_np) != 0u) atomicOr(A.status, ST_VIOLATION);
+            if (A.collect) block_stats(A, st_am, st_act, st_vr, st_vp, st_np, st_rmin, st_pn, st_pd, st_ve);
+            if ((st_vr | st_vp | st_np | st_ve) != 0u) atomicOr(A.status, ST_VIOLATION);
         }
         __syncthreads();
     }

@@ -454,6 +454,11 @@ struct idp_ctx {
     double total_area = 0.0;   // sum of element areas (all simulations)
     double *d_aind = nullptr;  // per element: shock indicator of the stage (combined limiting)
     double total_mortar_len = 0.0;   // sum of the large faces' lengths over the mortars
+    // local-limiting variants: extended element kernel, low-order bounds
+    int ext = 0;               // entropy bound or low-order bounds in use
+    int lob = 0;               // low-order bounds (pre-pass + mortar gather each stage)
+    int ent_bar = 0;           // entropy bound with bar-state bounds (mortar bar-state entropies)
+    double *d_lofv = nullptr;  // [2][K (N+1)^2] pre-pass output
     // optional timing: 1 step spans around the graph launches; 2 steps
     // launched without the graph, with element-pass events
     int prof = 0;
@@ -493,6 +498,10 @@ StageArgs base_args(idp_ctx *c) {
     A.status = c->d_status;
     A.stats = c->d_stats;
     A.aind = c->d_aind;
+    A.entropy = c->opt.entropy_bound;
+    A.lob = c->lob;
+    A.pass = 0;
+    A.lofv = c->d_lofv;
     return A;
 }
 
@@ -527,13 +536,28 @@ void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mo
     const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
     if (c->M > 0 && need_mortar_flux) {
         int k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
-        c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, A.u, A.gas, c->d_ops);
+        c->L.mortar_flux(c->opt.precision, c->ent_bar, gm, st, c->mesh, c->slots, A.u, A.gas, c->d_ops);
         kt_end(c, st, k);
     }
-    int k = kt_begin(c, st, IDP_K_ELEMENT);
-    c->L.element(c->opt.precision, c->epb, element_grid(c, c->epb, c->persistent, c->bps), st, c->mesh, c->slots, A);
-    kt_end(c, st, k);
     bool dgmode = (A.mode == 0 && A.dt == 0.0) || A.limiting == 0;
+    const int grid = element_grid(c, c->epb, c->persistent, c->bps);
+    if (c->lob && !dgmode) {
+        // low-order bounds (Eq. Bounds_LowOrder): u_FV of every node first,
+        // then the ranges across the mortars
+        StageArgs P = A;
+        P.pass = 1;
+        int k = kt_begin(c, st, IDP_K_ELEMENT_LO);
+        c->L.element(c->opt.precision, c->ext, c->epb, grid, st, c->mesh, c->slots, P);
+        kt_end(c, st, k);
+        if (c->M > 0) {
+            k = kt_begin(c, st, IDP_K_MORTAR_LOB);
+            c->L.mortar_lob(st, c->mesh, c->slots, c->d_ops, c->d_lofv, c->opt.entropy_bound, c->num_sms);
+            kt_end(c, st, k);
+        }
+    }
+    int k = kt_begin(c, st, IDP_K_ELEMENT);
+    c->L.element(c->opt.precision, c->ext, c->epb, grid, st, c->mesh, c->slots, A);
+    kt_end(c, st, k);
     if (c->M > 0 && !dgmode) {
         k = kt_begin(c, st, IDP_K_MORTAR_LIMIT);
         c->L.mortar_limit(gm, st, c->mesh, c->slots, A);
@@ -552,7 +576,8 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) 
     if (c->M > 0 && mortar_flux && c->opt.dt_rule == 0) {
         const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
         k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
-        c->L.mortar_flux(c->opt.precision, gm, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->d_ops);
+        c->L.mortar_flux(c->opt.precision, c->ent_bar, gm, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg),
+                         c->d_ops);
         kt_end(c, st, k);
     }
     int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
@@ -592,11 +617,11 @@ idp_status autotune(idp_ctx *c, const double *u, cudaStream_t st, double dt) {
     if (c->tuned) return IDP_OK;
     long long bucket = 0;
     for (long long k = c->K; k > 1; k >>= 1) ++bucket;
-    long long key = ((long long)c->NP << 48) | ((long long)c->opt.precision << 40) |
+    long long key = ((long long)c->NP << 48) | ((long long)c->opt.precision << 40) | ((long long)c->ext << 39) |
                     ((long long)c->opt.grid_mode << 36) | ((long long)c->num_sms << 16) | bucket;
     if (c->opt.elems_per_block > 0) {
         int bps = 1;
-        if (c->L.element_prepare(c->opt.precision, c->opt.elems_per_block, &bps) != cudaSuccess || bps < 1)
+        if (c->L.element_prepare(c->opt.precision, c->ext, c->opt.elems_per_block, &bps) != cudaSuccess || bps < 1)
             return IDP_E_ARG;
         c->epb = c->opt.elems_per_block; c->bps = bps; c->persistent = c->opt.grid_mode == 2 ? 1 : 0;
         c->tuned = true;
@@ -607,7 +632,7 @@ idp_status autotune(idp_ctx *c, const double *u, cudaStream_t st, double dt) {
         auto it = g_tune_cache.find(key);
         if (it != g_tune_cache.end()) {
             int bps = 1;
-            if (c->L.element_prepare(c->opt.precision, it->second.first, &bps) == cudaSuccess) {
+            if (c->L.element_prepare(c->opt.precision, c->ext, it->second.first, &bps) == cudaSuccess) {
                 c->epb = it->second.first; c->persistent = it->second.second; c->bps = bps; c->tuned = true;
                 return IDP_OK;
             }
@@ -622,15 +647,15 @@ idp_status autotune(idp_ctx *c, const double *u, cudaStream_t st, double dt) {
     int best_epb = 0, best_pers = 0, best_bps = 1;
     for (int ci = 0; ci < kNumEpb; ++ci) {
         int epb = kEpbChoices[ci], bps = 0;
-        if (c->L.element_prepare(c->opt.precision, epb, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
+        if (c->L.element_prepare(c->opt.precision, c->ext, epb, &bps) != cudaSuccess || bps < 1) { cudaGetLastError(); continue; }
         if ((long long)epb > 4 * c->K && epb > 1) continue;
         for (int pers = 0; pers < 2; ++pers) {
             if ((c->opt.grid_mode == 1 && pers == 1) || (c->opt.grid_mode == 2 && pers == 0)) continue;
             int grid = element_grid(c, epb, pers, bps);
-            c->L.element(c->opt.precision, epb, grid, st, c->mesh, c->slots, A);   // warm-up
+            c->L.element(c->opt.precision, c->ext, epb, grid, st, c->mesh, c->slots, A);   // warm-up
             if (cudaGetLastError() != cudaSuccess) continue;                       // not launchable
             cudaEventRecord(e0, st);
-            for (int r = 0; r < 3; ++r) c->L.element(c->opt.precision, epb, grid, st, c->mesh, c->slots, A);
+            for (int r = 0; r < 3; ++r) c->L.element(c->opt.precision, c->ext, epb, grid, st, c->mesh, c->slots, A);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) { cudaEventDestroy(e0); cudaEventDestroy(e1); return IDP_E_CUDA; }
             float ms = 0.f;
@@ -677,7 +702,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (o.precision < 0 || o.precision > 1 || o.limiting < 0 || o.limiting > 3 || o.dt_rule < 0 || o.dt_rule > 1 ||
         !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0) || o.mortar_projection < 0 || o.mortar_projection > 1)
         return IDP_E_ARG;
-    if (o.bounds != 0) return IDP_E_UNSUPPORTED;
+    if (o.bounds < 0 || o.bounds > 1 || o.entropy_bound < 0 || o.entropy_bound > 1) return IDP_E_ARG;
     if (o.elems_per_block != 0 && o.elems_per_block != 1 && o.elems_per_block != 2 && o.elems_per_block != 4 &&
         o.elems_per_block != 8 && o.elems_per_block != 16)
         return IDP_E_ARG;
@@ -692,6 +717,10 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     idp_ctx *c = new (std::nothrow) idp_ctx();
     if (!c) return IDP_E_ARG;
     c->N = N; c->NP = N + 1; c->n_sims = n_sims; c->gamma = gamma; c->opt = o;
+    // the variants act only in local limiting (and its half of the combined mode)
+    c->lob = o.limiting >= 2 && o.bounds == 1;
+    c->ext = o.limiting >= 2 && (o.bounds == 1 || o.entropy_bound == 1);
+    c->ent_bar = o.limiting >= 2 && o.entropy_bound == 1 && o.bounds == 0;
     c->K = (long long)H.geom.size(); c->M = (long long)H.m_large.size();
     c->sim_off = H.sim_off;
     for (const Geo &g : H.geom) c->total_area += g.z * g.w;
@@ -762,8 +791,8 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(upload(&c->d_mnslot, mn_slot));
     // slots: one block of device memory
     const size_t S = (size_t)c->M * Q, MM = (size_t)std::max<long long>(c->M, 1), SS = std::max<size_t>(S, 1);
-    size_t bytes = sizeof(double) * (SS * (4 + 4 + 3 + 4 + 4 + 6)) + sizeof(float) * SS + sizeof(int32_t) * MM +
-                   sizeof(double) * MM + 17 * 256;   // 16 sub-arrays, each padded to 256 B
+    size_t bytes = sizeof(double) * (SS * (4 + 4 + 3 + 4 + 4 + 6 + 5)) + sizeof(float) * SS + sizeof(int32_t) * MM +
+                   sizeof(double) * MM + 22 * 256;   // 21 sub-arrays, each padded to 256 B
     if (ok) chk(cudaMalloc(&c->d_slot_block, bytes));
     if (ok) chk(cudaMemset(c->d_slot_block, 0, bytes));
     if (ok) {
@@ -787,6 +816,11 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
         sl.nmort = (float *)take(sizeof(float) * SS);
         sl.bad = (int32_t *)take(sizeof(int32_t) * MM);
         sl.ell = (double *)take(sizeof(double) * MM);
+        sl.lnK = (double *)take(sizeof(double) * SS);
+        sl.sbmin = (double *)take(sizeof(double) * SS);
+        sl.lbmin = (double *)take(sizeof(double) * SS);
+        sl.lbmax = (double *)take(sizeof(double) * SS);
+        sl.lsmin = (double *)take(sizeof(double) * SS);
         if ((size_t)(p - (char *)c->d_slot_block) > bytes) { ok = false; note(cudaErrorMemoryAllocation, "slot layout"); }
     }
     const size_t kn = KN(c);
@@ -801,6 +835,8 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(cudaMalloc(&c->d_part, sizeof(double) * 4 * (size_t)c->K));
     if (ok) chk(cudaMalloc(&c->d_aind, sizeof(double) * (size_t)c->K));
     if (ok) chk(cudaMemset(c->d_aind, 0, sizeof(double) * (size_t)c->K));
+    if (ok && c->lob) chk(cudaMalloc(&c->d_lofv, sizeof(double) * 2 * kn));
+    if (ok && c->lob) chk(cudaMemset(c->d_lofv, 0, sizeof(double) * 2 * kn));
     if (ok) chk(cudaMalloc(&c->d_intout, sizeof(double) * 4 * n_sims));
     if (ok) chk(upload(&c->d_off, c->sim_off));
     if (ok) chk(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
@@ -1048,6 +1084,7 @@ idp_status idp_dgsem_limiter_stats(idp_ctx *c, idp_limiter_stats *out, void *str
     out->n_viol_pressure = (int64_t)a.n_vp;
     out->n_nonpositive = (int64_t)a.n_nonpos;
     out->n_dt_exceed = (int64_t)a.n_dtx;
+    out->n_viol_entropy = (int64_t)a.n_veta;
     std::memcpy(&out->min_rho, &a.min_rho_bits, sizeof(double));
     std::memcpy(&out->min_p, &a.min_p_bits, sizeof(double));
     c->n_stages = 0;
@@ -1104,7 +1141,7 @@ void idp_dgsem_destroy(idp_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    void *ptrs[] = {c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+    void *ptrs[] = {c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
                     c->d_msmall, c->d_mnslot, c->d_siminfo, c->d_slot_block, c->d_buf1, c->d_buf2, c->d_hostbuf,
                     c->d_dtmin, c->d_tsim, c->d_dtlast, c->d_status, c->d_stats, c->d_part, c->d_intout, c->d_off};
     for (void *p : ptrs)

@@ -12,14 +12,17 @@ constexpr int kNumEpb = 5;
 
 struct Launchers {
     int np;
-    // element pass: fp32 selects the FP32 form; epb = elements per block
-    size_t (*element_smem)(int fp32, int epb);
+    // element pass: fp32 selects the FP32 form, ext the extended kernel of
+    // the local-limiting variants; epb = elements per block
+    size_t (*element_smem)(int fp32, int ext, int epb);
     int (*element_threads)(int epb);
-    cudaError_t (*element_prepare)(int fp32, int epb, int *blocks_per_sm);
-    void (*element)(int fp32, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
+    cudaError_t (*element_prepare)(int fp32, int ext, int epb, int *blocks_per_sm);
+    void (*element)(int fp32, int ext, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
                     const StageArgs &a);
-    void (*mortar_flux)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
-                        const Gas &gas, const Ops *ops);
+    void (*mortar_flux)(int fp32, int ent, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
+                        const double *u, const Gas &gas, const Ops *ops);
+    void (*mortar_lob)(cudaStream_t st, const MeshDev &m, const SlotsDev &s, const Ops *ops, const double *lofv,
+                       int ent, int num_sms);
     void (*mortar_limit)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
     void (*mortar_apply)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
     void (*dt)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,

@@ -37,9 +37,11 @@ __device__ __forceinline__ Prim<FT> mortar_prim(const Gas &g, const double *q) {
 // fluxes, and one nonzero local weight each for the sparse low-order flux:
 // every pair term is formed once and summed into both of its slots in a
 // fixed order.
+// ent: also the minimum over each slot's bar states of s = ln p - gamma ln rho
+// (entropy bound of local limiting with bar-state bounds).
 template <int NP, typename FT>
 __global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
-k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, const Ops *ops) {
+k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, const Ops *ops, int ent) {
     constexpr int NN = NP * NP, Q = 3 * NP, NI = 2 * NP, MP = 3 * NP, W = MORTARS_PER_BLOCK;
     __shared__ double s_u[W][Q][4];      // traces: large side, then the two small faces
     __shared__ FT s_uf[W][Q][4];         // the same in the flux type
@@ -49,6 +51,7 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
     __shared__ double s_term[W][MP][4];  // sparse low-order pair terms
     __shared__ double s_rb[W][MP];       // their bar-state densities
     __shared__ FT s_d2[W][MP];           // and 2 d
+    __shared__ double s_sb[W][MP];       // and their s (entropy bound)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m = blockIdx.x * W + warp;
     if (m >= mesh.M) return;   // uniform per warp
@@ -119,6 +122,10 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
             else s_term[warp][lane][v] = term;
         }
         s_rb[warp][lane] = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) * i2l;
+        if (ent) {
+            if constexpr (F32) s_sb[warp][lane] = bar_entropy<float>(g, af, fa, bf, fb, low ? i2l_f : -i2l_f);
+            else s_sb[warp][lane] = bar_entropy<double>(g, a, fa, b, fb, low ? i2l : -i2l);
+        }
         FT wtf;
         if constexpr (F32) wtf = d2f(wt);
         else wtf = wt;
@@ -188,6 +195,7 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
     if (lane < Q) {
         long long klo = okey(INFINITY), khi = okey(-INFINITY);
         FT ds = FT(0);
+        double smin = INFINITY;
         const int np_q = ops->slot_n[lane];
         for (int t = 0; t < np_q; ++t) {
             const int p = ops->slot_p[lane][t];
@@ -195,8 +203,10 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
             klo = kb < klo ? kb : klo;
             khi = kb > khi ? kb : khi;
             ds += s_d2[warp][p];
+            if (ent) smin = dmin(smin, s_sb[warp][p]);
         }
         const int si = m * Q + lane;
+        if (ent) sl.sbmin[si] = smin;
         sl.rbmin[si] = okey_value(klo);
         sl.rbmax[si] = okey_value(khi);
         if constexpr (F32) sl.dsum[si] = f2d(ds);
@@ -241,7 +251,9 @@ k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
         if (!dpos(lr)) lr = 0.0;
         const double pmin = sl.pmin[s] * fast_rcp(sl.rfv[s]);
         const double pm = pmin - kTol * fabs(pmin);
-        const double th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
+        double th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
+        // entropy bound of local limiting (R21)
+        if (A.entropy && A.limiting >= 2) th = theta_entropy(A.gas, u0, av, sl.lnK[s], th);
         atomicMin(&s_min[lm], dbits(dpos(th) ? th : 0.0));
         if (combined) {
             // the positivity bounds only: rho >= beta rho_FV, p >= p_min
@@ -299,7 +311,8 @@ __global__ void __launch_bounds__(64) k_mortar_apply(MeshDev mesh, SlotsDev sl, 
     const size_t KN = (size_t)mesh.K * NN;
     double st_rmin = INFINITY;
     float st_pmin = 0.0f, st_one = 0.0f;   // minimum p (FP32 statistic) as the ratio st_pmin / st_one
-    unsigned vr = 0, vp = 0, np_ = 0;
+    unsigned vr = 0, vp = 0, np_ = 0, ve = 0;
+    const bool ent = A.entropy && A.limiting == 2;   // entropy bound checked (local limiting)
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mesh.n_mnodes; k += gridDim.x * blockDim.x) {
         const int gnode = mesh.mn_node[k];
         const int2 ss = mesh.mn_slot[k];
@@ -338,13 +351,54 @@ __global__ void __launch_bounds__(64) k_mortar_apply(MeshDev mesh, SlotsDev sl, 
             if (dlt(ut[0], rmin - kViolTol * fabs(rmin)) || dlt(rmax + kViolTol * fabs(rmax), ut[0])) vr++;
             if (dlt(rp, (pmin - kViolTol * fabs(pmin)) * ut[0])) vp++;
             if (!dpos(ut[0]) || !dpos(rp)) np_++;
+            if (ent && dlt(entropy_s(A.gas, ut[0], ut[1], ut[2], ut[3]), sl.lnK[s0] + A.gas.eviol)) ve++;
             st_rmin = dmin(st_rmin, ut[0]);
             const float pf = dpos(ut[0]) ? d2f(rp) / d2f(ut[0]) : 0.0f;
             if (pf > 0.0f && (st_one == 0.0f || pf < st_pmin)) { st_pmin = pf; st_one = 1.0f; }
         }
     }
-    if (A.collect) block_stats(A, 0.0f, 0u, vr, vp, np_, st_rmin, st_pmin, st_one);
-    if ((vr | vp | np_) != 0u) atomicOr(A.status, ST_VIOLATION);
+    if (A.collect) block_stats(A, 0.0f, 0u, vr, vp, np_, st_rmin, st_pmin, st_one, ve);
+    if ((vr | vp | np_ | ve) != 0u) atomicOr(A.status, ST_VIOLATION);
+}
+
+// Low-order-solution bounds across mortars (Eq. Bounds_LowOrder): per slot,
+// the range of rho_FV and the minimum of s(u_FV) over the nodes on the other
+// side of the mortar that share a nonzero local weight with it. One thread
+// per slot; lofv is the element pre-pass output [2][K (N+1)^2].
+template <int NP>
+__global__ void __launch_bounds__(128) k_mortar_lob(MeshDev mesh, SlotsDev sl, const Ops *ops,
+                                                    const double *__restrict__ lofv, int ent) {
+    constexpr int NN = NP * NP, Q = 3 * NP;
+    const size_t KN = (size_t)mesh.K * NN;
+    for (int si = blockIdx.x * blockDim.x + threadIdx.x; si < sl.S; si += gridDim.x * blockDim.x) {
+        const int m = si / Q, q = si - m * Q;
+        const int info = mesh.m_info[m], dir = info & 1, low = (info >> 1) & 1;
+        const int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
+        const int L = mesh.m_large[m];
+        const int2 sm2 = mesh.m_small[m];
+        long long klo = okey(INFINITY), khi = okey(-INFINITY);
+        double smin = INFINITY;
+        const int np_q = ops->slot_n[q];
+        for (int t = 0; t < np_q; ++t) {
+            const int p = ops->slot_p[q][t];
+            // the pair's node on the other side: a small-face node for a
+            // large slot, the large node for a small slot
+            size_t g;
+            if (q < NP) {
+                const int r = ops->pr[p];
+                g = (size_t)(r < NP ? sm2.x : sm2.y) * NN + face_node<NP>(sS, r % NP);
+            } else {
+                g = (size_t)L * NN + face_node<NP>(sL, ops->pk[p]);
+            }
+            const long long kb = okey(lofv[g]);
+            klo = kb < klo ? kb : klo;
+            khi = kb > khi ? kb : khi;
+            if (ent) smin = dmin(smin, lofv[KN + g]);
+        }
+        sl.lbmin[si] = okey_value(klo);
+        sl.lbmax[si] = okey_value(khi);
+        if (ent) sl.lsmin[si] = smin;
+    }
 }
 
 // Time step: per node m_i / sum_j 2 d_ij (rule 0) or min over directions of

@@ -1,6 +1,8 @@
 // k_inst.cu -- instantiates the kernels of one polynomial degree (IDP_NP =
 // N + 1, set on the compiler command line) and exposes them as a launcher
 // table.
+#include <algorithm>
+
 #include "idp_launch.cuh"
 
 #ifndef IDP_NP
@@ -15,24 +17,26 @@ namespace {
 
 constexpr int NP = IDP_NP;
 
-template <typename FT, int EPB>
+template <typename FT, int EPB, bool EXT>
 void el_launch(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
-    size_t smem = sizeof(ElemSm<NP, FT>) * EPB;
-    k_element<NP, FT, EPB><<<grid, ElemLaunch<NP, EPB>::threads, smem, st>>>(m, s, a);
+    size_t smem = sizeof(ElemSm<NP, FT, EXT>) * EPB;
+    k_element<NP, FT, EPB, EXT><<<grid, ElemLaunch<NP, EPB>::threads, smem, st>>>(m, s, a);
 }
 
-template <typename FT, int EPB>
+template <typename FT, int EPB, bool EXT>
 cudaError_t el_prepare(int *bps) {
-    size_t smem = sizeof(ElemSm<NP, FT>) * EPB;
-    cudaError_t e = cudaFuncSetAttribute(k_element<NP, FT, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    size_t smem = sizeof(ElemSm<NP, FT, EXT>) * EPB;
+    cudaError_t e = cudaFuncSetAttribute(k_element<NP, FT, EPB, EXT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_element<NP, FT, EPB>,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, k_element<NP, FT, EPB, EXT>,
                                                          ElemLaunch<NP, EPB>::threads, smem);
 }
 
-size_t element_smem(int fp32, int epb) {
-    return (fp32 ? sizeof(ElemSm<NP, float>) : sizeof(ElemSm<NP, double>)) * (size_t)epb;
+size_t element_smem(int fp32, int ext, int epb) {
+    size_t per = ext ? (fp32 ? sizeof(ElemSm<NP, float, true>) : sizeof(ElemSm<NP, double, true>))
+                     : (fp32 ? sizeof(ElemSm<NP, float>) : sizeof(ElemSm<NP, double>));
+    return per * (size_t)epb;
 }
 
 int element_threads(int epb) {
@@ -45,28 +49,42 @@ int element_threads(int epb) {
     }
 }
 
-#define IDP_EPB_SWITCH(FN, ...)                                                               \
-    switch (epb) {                                                                            \
-    case 1: return fp32 ? FN<float, 1>(__VA_ARGS__) : FN<double, 1>(__VA_ARGS__);             \
-    case 2: return fp32 ? FN<float, 2>(__VA_ARGS__) : FN<double, 2>(__VA_ARGS__);             \
-    case 4: return fp32 ? FN<float, 4>(__VA_ARGS__) : FN<double, 4>(__VA_ARGS__);             \
-    case 8: return fp32 ? FN<float, 8>(__VA_ARGS__) : FN<double, 8>(__VA_ARGS__);             \
-    default: return fp32 ? FN<float, 16>(__VA_ARGS__) : FN<double, 16>(__VA_ARGS__);          \
+// dispatch on (precision, extended kernel, elements per block)
+#define IDP_EPB_CASE(FN, E, ...)                                                               \
+    case E:                                                                                    \
+        if (ext) return fp32 ? FN<float, E, true>(__VA_ARGS__) : FN<double, E, true>(__VA_ARGS__); \
+        return fp32 ? FN<float, E, false>(__VA_ARGS__) : FN<double, E, false>(__VA_ARGS__);
+#define IDP_EPB_SWITCH(FN, ...)               \
+    switch (epb) {                            \
+    IDP_EPB_CASE(FN, 1, __VA_ARGS__)          \
+    IDP_EPB_CASE(FN, 2, __VA_ARGS__)          \
+    IDP_EPB_CASE(FN, 4, __VA_ARGS__)          \
+    IDP_EPB_CASE(FN, 8, __VA_ARGS__)          \
+    default:                                  \
+        if (ext) return fp32 ? FN<float, 16, true>(__VA_ARGS__) : FN<double, 16, true>(__VA_ARGS__); \
+        return fp32 ? FN<float, 16, false>(__VA_ARGS__) : FN<double, 16, false>(__VA_ARGS__); \
     }
 
-cudaError_t element_prepare(int fp32, int epb, int *bps) {
+cudaError_t element_prepare(int fp32, int ext, int epb, int *bps) {
     if (ElemLaunch<NP, 16>::threads > 1024 && epb == 16) return cudaErrorInvalidConfiguration;
     IDP_EPB_SWITCH(el_prepare, bps)
 }
 
-void element(int fp32, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
+void element(int fp32, int ext, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
+             const StageArgs &a) {
     IDP_EPB_SWITCH(el_launch, grid, st, m, s, a)
 }
 
-void mortar_flux(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
+void mortar_flux(int fp32, int ent, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
                  const Gas &gas, const Ops *ops) {
-    if (fp32) k_mortar_flux<NP, float><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gas, ops);
-    else k_mortar_flux<NP, double><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gas, ops);
+    if (fp32) k_mortar_flux<NP, float><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gas, ops, ent);
+    else k_mortar_flux<NP, double><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gas, ops, ent);
+}
+
+void mortar_lob(cudaStream_t st, const MeshDev &m, const SlotsDev &s, const Ops *ops, const double *lofv, int ent,
+                int num_sms) {
+    const int blocks = std::max(1, std::min((s.S + 127) / 128, num_sms * 16));
+    k_mortar_lob<NP><<<blocks, 128, 0, st>>>(m, s, ops, lofv, ent);
 }
 
 void mortar_limit(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
@@ -106,6 +124,7 @@ Launchers IDP_CAT(launchers_np, IDP_NP)() {
     L.element_prepare = element_prepare;
     L.element = element;
     L.mortar_flux = mortar_flux;
+    L.mortar_lob = mortar_lob;
     L.mortar_limit = mortar_limit;
     L.mortar_apply = mortar_apply;
     L.dt = dt;

@@ -32,7 +32,8 @@ class MeshDesc(C.Structure):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("limiting", C.c_int32), ("bounds", C.c_int32), ("dt_rule", C.c_int32),
                 ("beta", C.c_double), ("cfl", C.c_double), ("mortar_projection", C.c_int32),
-                ("elems_per_block", C.c_int32), ("collect_stats", C.c_int32), ("grid_mode", C.c_int32)]
+                ("elems_per_block", C.c_int32), ("collect_stats", C.c_int32), ("grid_mode", C.c_int32),
+                ("entropy_bound", C.c_int32)]
 
 
 class LimiterStats(C.Structure):
@@ -40,7 +41,7 @@ class LimiterStats(C.Structure):
                 ("n_stages", C.c_int64), ("n_volume_active", C.c_int64), ("n_mortar_active", C.c_int64),
                 ("n_mortar_fallback", C.c_int64), ("n_viol_density", C.c_int64), ("n_viol_pressure", C.c_int64),
                 ("n_nonpositive", C.c_int64), ("n_dt_exceed", C.c_int64),
-                ("min_rho", C.c_double), ("min_p", C.c_double)]
+                ("min_rho", C.c_double), ("min_p", C.c_double), ("n_viol_entropy", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -126,7 +127,8 @@ def idp_eval_math(fn, x, y, stream=None):
 
 
 # kernel kinds of one step, in the order of the IDP_K_* constants
-KERNELS = ["dt_init", "mortar_flux", "dt", "element", "mortar_limit", "mortar_apply", "time_advance"]
+KERNELS = ["dt_init", "mortar_flux", "dt", "element", "mortar_limit", "mortar_apply", "time_advance",
+           "element_lo", "mortar_lob"]
 
 NOALLOC_MAX_ELEMS = 1 << 19
 
@@ -297,9 +299,11 @@ class Context:
         """Kernels one SSP-RK3 step launches (mirrors the step sequence)."""
         M = self.M > 0
         lim = self.opts.limiting > 0
+        # low-order bounds: a pre-pass over the elements and a mortar gather
+        lob = (1 + (1 if M else 0)) if (self.opts.limiting >= 2 and self.opts.bounds == 1) else 0
         n = 1 + (1 if (M and self.opts.dt_rule == 0) else 0) + 1          # dt init, mortar flux, dt
-        n += (1 if (M and self.opts.dt_rule != 0) else 0) + 1 + (2 if (M and lim) else 0)   # stage 1
-        n += 2 * ((1 if M else 0) + 1 + (2 if (M and lim) else 0))          # stages 2, 3
+        n += (1 if (M and self.opts.dt_rule != 0) else 0) + 1 + lob + (2 if (M and lim) else 0)   # stage 1
+        n += 2 * ((1 if M else 0) + 1 + lob + (2 if (M and lim) else 0))   # stages 2, 3
         return n + 1                                                        # time advance
 
     def idp_dgsem_sync(self, stream=None):

@@ -87,7 +87,9 @@ def test_rejects_bad_arguments():
     assert _create(m, beta=1.5) == idp.IDP_E_ARG
     assert _create(m, cfl=0.0) == idp.IDP_E_ARG
     assert _create(m, elems_per_block=3) == idp.IDP_E_ARG
-    assert _create(m, bounds=1) == idp.IDP_E_UNSUPPORTED
+    assert _create(m, bounds=2) == idp.IDP_E_ARG
+    assert _create(m, bounds=-1) == idp.IDP_E_ARG
+    assert _create(m, entropy_bound=2) == idp.IDP_E_ARG
     mb = W.uniform_mesh(2, 2, bc=(W.BC_PERIODIC, W.BC_WALL, W.BC_PERIODIC, W.BC_PERIODIC))
     assert _create(mb) == idp.IDP_E_ARG
     assert _create(m, grid_mode=3) == idp.IDP_E_ARG

@@ -1,0 +1,182 @@
+"""GPU parity of the local-limiting variants against the oracle (Sec. 2.3):
+the entropy bound (Eq. Bounds_Barstates, right part; reading R21) and the
+low-order-solution bounds (Eq. Bounds_LowOrder; reading R22), alone, together
+and inside the combined limiting (Sec. 3.5), through the C ABI.
+
+Tolerances: 1e-12 per right-hand side relative to the residual scale (as in
+test_gpu_parity) and FP32-form density L1 <= 1e-5 for every variant. After
+100 steps 1e-10 for the low-order bounds alone; with the entropy bound 1e-8:
+its factor is the root of a transcendental equation that the two sides find
+by different iterations (bisection, Newton) with different logarithm and
+exponential routines, so the factors agree to the root's conditioning (the
+rounding of Psi over its slope) rather than to the rounding order, and the
+limiter's thresholds amplify such differences over many stages (measured on
+cfg1: 3e-13 after one step, 3e-10 to 8e-10 after 100).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from conftest import rel_err, rhs_scale
+from paper_2607_06045_b300 import build, idp
+from paper_2607_06045_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [(0, 1), (1, 0), (1, 1)]   # (bounds, entropy_bound)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    yield
+
+
+def dev(u):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(u)).cuda()
+
+
+def gpu_rhs(ctx, u, t, dt):
+    import torch
+    ud = dev(u)
+    out = torch.empty_like(ud)
+    ctx.idp_dgsem_rhs(ud, t, dt, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def check_rhs(mesh, N, u, limiting, bounds, entropy, t=0.0, cfl=0.5, tol=1e-12, **kw):
+    o = oracle.Oracle(mesh, N)
+    ctx = idp.Context(mesh, N, limiting=limiting, bounds=bounds, entropy_bound=entropy, **kw)
+    dt_idp = o.dt(u, t, cfl=1.0)
+    scale = rhs_scale(u, dt_idp)
+    dt = cfl * dt_idp
+    r_o = o.rhs(u, t=t, dt=dt, limiting=limiting, bounds=bounds, entropy=entropy)
+    r_g = gpu_rhs(ctx, u, t, dt)
+    e = rel_err(r_g, r_o, scale)
+    ctx.close()
+    assert e <= tol, e
+    return r_o
+
+
+@pytest.mark.parametrize("N", [1, 3, 5])
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_variant_rhs(N, variant):
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, N)
+    r = check_rhs(m, N, u, 2, *variant)
+    # the variant changes the result (it is not silently off)
+    o = oracle.Oracle(m, N)
+    dt = 0.5 * o.dt(u, cfl=1.0)
+    if N > 1:
+        assert not np.array_equal(r, o.rhs(u, dt=dt, limiting=2))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_variant_rough_state_refined(variant):
+    m = W.box_refined_mesh(5, 4, (0.0, 0.0, 1.25, 1.0), (0.3, 0.3, 0.8, 0.7))
+    u = W.random_state(m, 3, seed=21, rho_range=(0.2, 3.0), p_range=(0.2, 3.0), vmax=1.0)
+    check_rhs(m, 3, u, 2, *variant)
+
+
+@pytest.mark.parametrize("bc", [W.BC_WALL, W.BC_DIRICHLET, W.BC_OUTFLOW])
+def test_variant_boundaries(bc):
+    m = W.box_refined_mesh(5, 3, (0.0, 0.0, 2.0, 1.0), (0.5, 0.3, 1.5, 0.7), bc=(bc,) * 4)
+    m.bc_prim = np.array([[1.2, 0.3, -0.1, 1.1], [0.9, 0.1, 0.2, 0.8], [1.0, -0.2, 0.3, 1.0], [1.1, 0.0, 0.0, 0.9]])
+    u = W.random_state(m, 3, seed=30 + bc)
+    for v in VARIANTS:
+        check_rhs(m, 3, u, 2, *v)
+
+
+def test_variants_in_combined_limiting():
+    m = W.cfg1_mesh()
+    for N in (1, 3):
+        u = W.cfg1_state(m, N)
+        for v in VARIANTS:
+            check_rhs(m, N, u, 3, *v)
+
+
+def test_variant_dmr_full_size():
+    m = W.cfg2_mesh()
+    u = W.cfg2_state(m, 3)
+    check_rhs(m, 3, u, 2, 1, 1)
+    check_rhs(m, 3, u, 2, 0, 1)
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_variant_100_steps(variant):
+    b, e = variant
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    o = oracle.Oracle(m, 3)
+    u_o, t_o, _, st_o = o.step(u, 100, cfl=0.5, limiting=2, bounds=b, entropy=e)
+    assert st_o["viol_eta"] == 0 and st_o["viol_rho"] == 0
+    ctx = idp.Context(m, 3, limiting=2, bounds=b, entropy_bound=e, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    ctx.idp_dgsem_step(ud, 100, t)
+    sc = np.abs(u_o).reshape(4, -1).max(axis=1)
+    err = (np.abs(ud.cpu().numpy() - u_o).reshape(4, -1).max(axis=1) / sc).max()
+    assert err <= (1e-8 if e else 1e-10), err
+    assert abs(t[0] - t_o) <= (1e-10 if e else 1e-12) * t_o
+    rc, st = ctx.idp_dgsem_limiter_stats()
+    assert rc == idp.IDP_OK
+    assert st["n_nonpositive"] == 0 and st["n_viol_density"] == 0 and st["n_viol_pressure"] == 0
+    assert st["n_viol_entropy"] == 0
+    ctx.close()
+    # FP32 form of the same run
+    c32 = idp.Context(m, 3, limiting=2, bounds=b, entropy_bound=e, cfl=0.5, precision=1)
+    ud = dev(u)
+    t = np.zeros(1)
+    c32.idp_dgsem_step(ud, 20, t)
+    u20, _, _, _ = o.step(u, 20, cfl=0.5, limiting=2, bounds=b, entropy=e)
+    mm = o.masses()
+    l1 = (mm * np.abs(ud.cpu().numpy()[0] - u20[0])).sum() / (mm * np.abs(u20[0])).sum()
+    assert l1 <= 1e-5, l1
+    rc, st = c32.idp_dgsem_limiter_stats()
+    assert st["n_nonpositive"] == 0 and st["n_viol_density"] == 0 and st["n_viol_entropy"] == 0
+    c32.close()
+
+
+def test_variant_batched_matches_individual():
+    ms = [W.cfg1_mesh(), W.box_refined_mesh(6, 4, (0.0, 0.0, 1.5, 1.0), (0.2, 0.2, 0.9, 0.6)),
+          W.uniform_mesh(5, 5, bc=(W.BC_OUTFLOW,) * 4)]
+    us = [W.cfg1_state(ms[0], 3), W.smooth_random_state(ms[1], 3, seed=3), W.random_state(ms[2], 3, seed=4)]
+    ctx = idp.Context(ms, 3, cfl=0.5, limiting=2, bounds=1, entropy_bound=1)
+    ud = dev(W.concat_states(us))
+    t = np.zeros(3)
+    ctx.idp_dgsem_step(ud, 5, t)
+    u_g = ud.cpu().numpy()
+    off = ctx.sim_offsets
+    for s in range(3):
+        u_o, t_o, _, _ = oracle.Oracle(ms[s], 3).step(us[s], 5, cfl=0.5, limiting=2, bounds=1, entropy=1)
+        part = u_g[:, off[s]:off[s + 1]]
+        scale = np.abs(u_o).reshape(4, -1).max(axis=1)
+        assert (np.abs(part - u_o).reshape(4, -1).max(axis=1) / scale).max() <= 1e-9, s
+    ctx.close()
+
+
+def test_variant_launch_counts():
+    """The step launches the kernels launches_per_step counts: the pre-pass
+    and the mortar gather appear once per stage with low-order bounds."""
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    for b, e in [(0, 0)] + VARIANTS:
+        ctx = idp.Context(m, 3, limiting=2, bounds=b, entropy_bound=e, cfl=0.5)
+        ud = dev(u)
+        t = np.zeros(1)
+        ctx.idp_dgsem_step(ud, 1, t)   # the first call also tunes the element pass
+        ctx.idp_dgsem_profile(2)
+        ctx.idp_dgsem_profile_kernels(reset=True)
+        ctx.idp_dgsem_step(ud, 2, t)
+        k = ctx.idp_dgsem_profile_kernels(reset=True)
+        total = sum(n for _, n in k.values())
+        assert total == 2 * ctx.launches_per_step(), (b, e, k)
+        assert k["element_lo"][1] == (6 if b == 1 else 0)
+        assert k["mortar_lob"][1] == (6 if b == 1 else 0)
+        ctx.idp_dgsem_profile(0)
+        ctx.close()
