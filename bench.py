@@ -277,6 +277,37 @@ def run_ours(args):
             e2e_t = max_over_ranks(time.perf_counter() - t0)
             results["e2e"] = e2e_t
         del u_dev
+    # limiter variants (FP64 path, same workload): combined positivity/local
+    # limiting (Sec. 3.5), the entropy bound and the low-order-solution
+    # bounds of local limiting (Sec. 2.3, Eqs. Bounds_Barstates,
+    # Bounds_LowOrder), and the low-order CFL estimate against the IDP step
+    variants = {}
+    vsteps = max(3, args.steps // 4)
+    for name, kw in (("combined", dict(limiting=3)), ("entropy_bound", dict(limiting=2, entropy_bound=1)),
+                     ("low_order_bounds", dict(limiting=2, bounds=1)),
+                     ("low_order_bounds_entropy", dict(limiting=2, bounds=1, entropy_bound=1))):
+        vctx = idp.Context(meshes[0], 3, precision=0, cfl=0.5, **kw)
+        u_dev = torch.from_numpy(u0).cuda()
+        barrier_sync()
+        vt, _, _, vk = time_steps(vctx, u_dev, vsteps, args.warmup, flush, stream, barrier_sync)
+        vt = max_over_ranks(vt)
+        _, vst = vctx.idp_dgsem_limiter_stats()
+        variants[name] = dict(value=aggregate_rate(nodes * 3 * vsteps, world, vt), unit=UNIT,
+                              ms_per_step=vt / vsteps * 1e3, steps=vsteps, options=kw,
+                              gpu_launches=int(vctx.launches_per_step() * vsteps),
+                              kernels={k: {"ms_per_launch": ms / n, "launches_per_step": n / vsteps}
+                                       for k, (ms, n) in vk.items() if n},
+                              stats={k: vst[k] for k in ("alpha_volume_mean", "alpha_mortar_mean", "n_viol_density",
+                                                         "n_viol_pressure", "n_viol_entropy", "n_nonpositive")})
+        vctx.close()
+        del u_dev
+    dts = []
+    for rule in (0, 1):
+        dctx = idp.Context(meshes[0], 3, cfl=1.0, dt_rule=rule)
+        dts.append(float(dctx.idp_dgsem_dt(torch.from_numpy(u0).cuda())[0]))
+        dctx.close()
+    variants["dt_rules"] = {"idp": dts[0], "low_order_cfl": dts[1], "ratio": dts[1] / dts[0],
+                            "note": "cfl = 1 on the initial state; steps to a fixed time scale with 1 / dt"}
     # batched workload, FP32 form
     bm, ub = build_workload("batched")
     bnodes = ub.shape[1] * ub.shape[2] * ub.shape[3]
@@ -369,6 +400,7 @@ def run_ours(args):
                                                            "n_viol_pressure", "n_nonpositive")}},
         },
         "probe": {"fp64_tflops": fp64_probe, "fp32_tflops": fp32_probe},
+        "variants": dict(variants, ms_per_step_local=r64["time"] / args.steps * 1e3),
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_full()

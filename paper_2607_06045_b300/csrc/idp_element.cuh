@@ -63,7 +63,8 @@ struct ElemSm {
     static constexpr int NN = NP * NP, N = NP - 1, NPAIR = NP * (NP - 1) / 2, NIF = 2 * NP * (NP - 1);
     static constexpr bool F32 = sizeof(FT) == 4;
     // extended kernel (entropy bound, low-order bounds): sizes of its arrays
-    static constexpr int XN = EXT ? NN : 1, XI = EXT ? NIF : 1, XF = EXT ? 4 : 1;
+    // (one element in the default kernel, which does not use them)
+    static constexpr int XN = EXT ? NN : 1, XS = EXT ? NN + NIF + 4 * NP : 1;
     union {
         struct {                 // P0 - P1
             FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
@@ -94,10 +95,10 @@ struct ElemSm {
             double ibar[NIF];        // bar-state density across interior subcell interfaces
             FT i2d[NIF];
             FT indT[NN];             // combined limiting: V^{-1} P (first half of the modal transform)
-            // entropy bound: s = ln p - gamma ln rho of the node, of the bar
-            // states at interior interfaces and across faces (or, with
-            // low-order bounds, of the neighbour's u_FV across faces)
-            double sn[XN], ibs[XI], fbs[XF][NP];
+            // entropy bound: s = ln p - gamma ln rho of the node [NN], of the
+            // bar states at interior interfaces [NIF] and across faces [4][NP]
+            // (or, with low-order bounds, of the neighbour's u_FV across faces)
+            double xs[XS];
         };
         struct {                 // P2b - P5
             double Ad[NIF][4];       // antidiffusive flux A = Fdg - Ffv in FP64
@@ -363,11 +364,11 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if (lob && !pre) {
                         S.fbar[s][t] = sl.lbmin[q];
                         S.fbar2[s][t] = sl.lbmax[q];
-                        if (ent) S.fbs[s][t] = sl.lsmin[q];
+                        if (ent) S.xs[NN + NIF + s * NP + t] = sl.lsmin[q];
                     } else {
                         S.fbar[s][t] = sl.rbmin[q];
                         S.fbar2[s][t] = sl.rbmax[q];
-                        if (ent && !pre) S.fbs[s][t] = sl.sbmin[q];
+                        if (ent && !pre) S.xs[NN + NIF + s * NP + t] = sl.sbmin[q];
                     }
                     S.f2d[s][t] = to_ft<FT>(sl.dsum[q]);
                 }
@@ -428,16 +429,16 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     const size_t go = (size_t)nb * NN + face_node<NP>(s ^ 1, t);
                     S.fbar[s][t] = A.lofv[go];
                     S.fbar2[s][t] = A.lofv[go];
-                    if (ent) S.fbs[s][t] = A.lofv[KNL + go];
+                    if (ent) S.xs[NN + NIF + s * NP + t] = A.lofv[KNL + go];
                 } else {
                     S.fbar[s][t] = INFINITY;
                     S.fbar2[s][t] = -INFINITY;
-                    if (ent) S.fbs[s][t] = INFINITY;
+                    if (ent) S.xs[NN + NIF + s * NP + t] = INFINITY;
                 }
             } else {
                 S.fbar[s][t] = fb;
                 S.fbar2[s][t] = fb;
-                if (EXT && fent) S.fbs[s][t] = fs;
+                if (EXT && fent) S.xs[NN + NIF + s * NP + t] = fs;
             }
         }
         if (!dgmode) {
@@ -473,7 +474,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 if constexpr (F32) { i2lt = 0.5f / lam; i2l = f2d(i2lt); }
                 else { i2l = 0.5 * fast_rcp(lam); i2lt = i2l; }
                 S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * i2l;
-                if (EXT && ent && !lob && !pre) S.ibs[id] = bar_entropy<FT>(G, ua, fa, ub, fb, i2lt);
+                if (EXT && ent && !lob && !pre) S.xs[NN + id] = bar_entropy<FT>(G, ua, fa, ub, fb, i2lt);
             }
             if (EXT && ent && !lob && !pre) {
                 // s of the node itself, one of its bar states (R6)
@@ -483,10 +484,10 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     SM &S = sm[le];
                     if constexpr (F32) {
                         const float r = S.pr[0][n], p = S.pr[3][n];
-                        S.sn[n] = (r > 0.0f && p > 0.0f) ? (double)(logf(p) - G.gf * logf(r)) : -INFINITY;
+                        S.xs[n] = (r > 0.0f && p > 0.0f) ? (double)(logf(p) - G.gf * logf(r)) : -INFINITY;
                     } else {
                         // ln p = ln rho - ln beta
-                        S.sn[n] = (1.0 - G.g) * S.pr[6][n] - S.pr[7][n];
+                        S.xs[n] = (1.0 - G.g) * S.pr[6][n] - S.pr[7][n];
                     }
                 }
             }
@@ -556,7 +557,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 long long klo = lob ? okey(INFINITY) : okey(S.u[0][n]);
                 long long khi = lob ? okey(-INFINITY) : klo;
                 double smin = 0.0;
-                if (EXT && ent) smin = lob ? INFINITY : S.sn[n];
+                if (EXT && ent) smin = lob ? INFINITY : S.xs[n];
                 FT ds = FT(0);
                 // x direction: left then right; y: bottom then top. Interior
                 // subcell interfaces and element faces (conforming, boundary or
@@ -589,7 +590,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                             const size_t gn = (size_t)e * NN + (interior ? nbn : n);
                             if (lob && interior) { blo = A.lofv[gn]; bhi = blo; }
                             if (ent) {
-                                const double sv = interior ? (lob ? A.lofv[KNL + gn] : S.ibs[id]) : S.fbs[s][row];
+                                const double sv = interior ? (lob ? A.lofv[KNL + gn] : S.xs[NN + id]) : S.xs[NN + NIF + s * NP + row];
                                 smin = dmin(smin, sv);
                             }
                         }

@@ -16,6 +16,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--N", type=int, default=3)
     ap.add_argument("--epb", type=int, default=0, help="elements per block (0: autotune)")
+    ap.add_argument("--limiting", type=int, default=2)
+    ap.add_argument("--bounds", type=int, default=0, help="0 bar states, 1 low-order solution")
+    ap.add_argument("--entropy", type=int, default=0, help="1: entropy bound")
     a = ap.parse_args(argv)
     import torch
     from paper_2607_06045_b300 import build, idp
@@ -31,7 +34,8 @@ def main(argv=None):
         meshes = W.cfg4_meshes(256, seed=0)
         rng = np.random.default_rng(1)
         u = W.concat_states([W.cfg4_state(m, a.N, rng) for m in meshes])
-    ctx = idp.Context(meshes, a.N, precision=a.precision, limiting=2, cfl=0.5, elems_per_block=a.epb)
+    ctx = idp.Context(meshes, a.N, precision=a.precision, limiting=a.limiting, bounds=a.bounds,
+                      entropy_bound=a.entropy, cfl=0.5, elems_per_block=a.epb)
     ud = torch.from_numpy(u).cuda()
     t = np.zeros(ctx.n_sims)
     stream = torch.cuda.Stream()
