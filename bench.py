@@ -145,6 +145,9 @@ def build_workload(name):
         ms = W.cfg4_meshes(256, seed=0)
         rng = np.random.default_rng(1)
         return ms, W.concat_states([W.cfg4_state(m, 3, rng) for m in ms])
+    if name == "vacuum":
+        m, c = W.cfg5_mesh()
+        return [m], W.cfg5_state(m, 5, c)
     raise ValueError(name)
 
 
@@ -202,6 +205,27 @@ def kernel_rooflines(work, kern, steps, step_time, peak_tflops, hbm_gbs):
     return out, {"roofline_ms": roof_step * 1e3, "measured_ms": step_time * 1e3, "frac": roof_step / step_time}
 
 
+def vacuum_entry(vac, vnodes, world, roofline, w, peak, hbm, unit):
+    """JSON entry of the near-vacuum blast (FP32 form, N = 5): rate, element-pass
+    roofline against the FP64 peak, per-kernel rooflines, invariants."""
+    steps = vac["steps"]
+    f = roofline.element_flops(5, 1, *w)
+    el = vac["el_ms"] * 1e-3 / max(vac["el_n"], 1)
+    ach = f * vnodes / el * 1e-12
+    kr, st = kernel_rooflines(roofline.kernel_work(5, 1, vac["K"], vac["M"], 18 * vac["M"], *w), vac["kern"], steps,
+                              vac["time"] / steps, peak, hbm)
+    return {"value": aggregate_rate(vnodes * 3 * steps, world, vac["time"]), "unit": unit,
+            "workload": "near-vacuum blast: 512x512 base + 2 levels within r < 0.1, N=5, rho 1e-6 / p 1e-9 "
+                        "background, disc rho 1 / p 1e3, outflow, FP32 form",
+            "elements": int(vac["K"]), "dofs": int(vnodes), "steps": steps,
+            "ms_per_step": vac["time"] / steps * 1e3, "ms_per_step_median": vac["median_ms"],
+            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "frac": ach / peak, "unit": "TFLOP/s",
+                         "launch_ms": el * 1e3, "flops_per_node_stage": f},
+            "kernels": kr, "step_roofline": st, "gpu_launches": int(vac["launches"]),
+            "stats": {k: vac["stats"][k] for k in ("alpha_volume_mean", "alpha_mortar_mean", "n_viol_density",
+                                                    "n_viol_pressure", "n_nonpositive")}}
+
+
 def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn):
     """Per-step CUDA-event timing on the launching stream, L2 flushed between
     steps. Pass 1 (the headline): CUDA-graph steps bracketed by events. Pass 2:
@@ -211,21 +235,32 @@ def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn):
     t = np.zeros(ctx.n_sims)
     for _ in range(warmup):
         ctx.idp_dgsem_step(u_dev, 1, t, stream=stream.cuda_stream)
-    out = []
+    out, per_step = [], []
     for mode in (1, 2):
         ctx.idp_dgsem_profile(mode)
         ctx.idp_dgsem_profile_read(reset=True)
         sync_fn()
+        acc = [0.0, 0.0, 0.0, 0]
         for _ in range(steps):
             with torch.cuda.stream(stream):
                 flush.zero_()          # L2 flush, outside the timed span
             ctx.idp_dgsem_step(u_dev, 1, t, stream=stream.cuda_stream)
+            if mode == 1:
+                # each step's own event span (the step synchronises in profiling modes)
+                _, _, ms, n = ctx.idp_dgsem_profile_read(reset=True)
+                per_step.append(ms)
+                acc[2] += ms
+                acc[3] += n
         sync_fn()
         kern = ctx.idp_dgsem_profile_kernels(reset=False)
-        out.append(ctx.idp_dgsem_profile_read(reset=True) + ((kern,) if mode == 2 else ()))
+        if mode == 1:
+            out.append(tuple(acc))
+        else:
+            out.append(ctx.idp_dgsem_profile_read(reset=True) + (kern,))
     ctx.idp_dgsem_profile(0)
     (_, _, step_ms, nst), (el_ms, el_n, _, _, kern) = out
     assert nst == steps
+    time_steps.median_ms = float(np.median(per_step))
     return step_ms * 1e-3, el_ms, el_n, kern
 
 
@@ -262,7 +297,8 @@ def run_ours(args):
         tot = max_over_ranks(tot)
         rc, st = ctx.idp_dgsem_limiter_stats()
         results[prec] = dict(time=tot, el_ms=el_ms, el_n=el_n, stats=st, ctx=ctx, kern=kern,
-                             launches=ctx.launches_per_step() * args.steps, u_end=u_dev.cpu().numpy())
+                             launches=ctx.launches_per_step() * args.steps, u_end=u_dev.cpu().numpy(),
+                             median_ms=time_steps.median_ms)
         if prec == 0:
             results["clocks"] = ck
             # end to end through the host-buffer entry point (pinned host state)
@@ -308,6 +344,21 @@ def run_ours(args):
         dctx.close()
     variants["dt_rules"] = {"idp": dts[0], "low_order_cfl": dts[1], "ratio": dts[1] / dts[0],
                             "note": "cfl = 1 on the initial state; steps to a fixed time scale with 1 / dt"}
+    # near-vacuum blast (512 x 512 base + 2 levels, N = 5), FP32 form
+    vm, vu = build_workload("vacuum")
+    vnodes = vu.shape[1] * vu.shape[2] * vu.shape[3]
+    vctx = idp.Context(vm[0], 5, precision=1, limiting=2, cfl=0.5)
+    vud = torch.from_numpy(vu).cuda()
+    del vu
+    vsteps_v = max(3, args.steps // 10)
+    barrier_sync()
+    vtot, vel_ms, vel_n, vkern = time_steps(vctx, vud, vsteps_v, args.warmup, flush, stream, barrier_sync)
+    vtot = max_over_ranks(vtot)
+    _, vst5 = vctx.idp_dgsem_limiter_stats()
+    vac = dict(time=vtot, el_ms=vel_ms, el_n=vel_n, kern=vkern, stats=vst5, K=vctx.K, M=vctx.M,
+               launches=vctx.launches_per_step() * vsteps_v, steps=vsteps_v, median_ms=time_steps.median_ms)
+    vctx.close()
+    del vud
     # batched workload, FP32 form
     bm, ub = build_workload("batched")
     bnodes = ub.shape[1] * ub.shape[2] * ub.shape[3]
@@ -354,6 +405,7 @@ def run_ours(args):
         "steps": args.steps,
         "warmup": args.warmup,
         "ms_per_step": r64["time"] / args.steps * 1e3,
+        "ms_per_step_median": r64["median_ms"],
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -390,6 +442,7 @@ def run_ours(args):
                           "l1_vs_fp64": dict(l1, steps=args.warmup + 2 * args.steps),
                           "stats": {k: r32["stats"][k] for k in ("alpha_volume_mean", "n_viol_density",
                                                                  "n_viol_pressure", "n_nonpositive")}},
+            "near_vacuum_fp32": vacuum_entry(vac, vnodes, world, roofline, w, peak, hbm, UNIT),
             "batched_fp32": {"value": bval, "unit": UNIT,
                              "workload": "256 simulations, 8..128 base, 0-2 levels on seeded patches, N=3, "
                                          "four-quadrant Riemann data, FP32 form",
@@ -421,7 +474,16 @@ def cpu_baseline_full():
     o.step(u, nsteps, cfl=0.5, limiting=2)
     dt = time.perf_counter() - t0
     nodes = u.shape[1] * u.shape[2] * u.shape[3]
-    return {"value": nodes * 3 * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+    cpu = "unknown"
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.startswith("model name"):
+                cpu = ln.split(":", 1)[1].strip()
+                break
+    except OSError:
+        pass
+    return {"value": nodes * 3 * nsteps / dt, "unit": UNIT, "cores": 1, "kind": "oracle", "cpu": cpu,
+            "host_threads": os.cpu_count(),
             "sample": f"{nsteps} SSP-RK3 steps of the full DMR workload ({nodes} DOFs), single-threaded C, {dt:.1f} s"}
 
 
