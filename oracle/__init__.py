@@ -70,6 +70,8 @@ def lib():
         L.orc_rhs.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, dp, dp]
         L.orc_step.argtypes = [C.c_void_p, dp, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
                                C.c_int, dp, dp]
+        L.orc_set_volume_flux.argtypes = [C.c_void_p, C.c_int]
+        L.orc_chandrashekar.argtypes = [C.c_double, dp, dp, C.c_int, dp]
         L.orc_theta_entropy.restype = C.c_double
         L.orc_theta_entropy.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double]
         L.orc_entropy_eta.restype = C.c_double
@@ -129,6 +131,14 @@ def ranocha(uL, uR, d: int, gamma=1.4):
     return f
 
 
+def chandrashekar(uL, uR, d: int, gamma=1.4):
+    uL = np.ascontiguousarray(uL, dtype=np.float64)
+    uR = np.ascontiguousarray(uR, dtype=np.float64)
+    f = np.zeros(4)
+    lib().orc_chandrashekar(gamma, _d(uL), _d(uR), d, _d(f))
+    return f
+
+
 def llf(uL, uR, n, gamma=1.4):
     uL = np.ascontiguousarray(uL, dtype=np.float64)
     uR = np.ascontiguousarray(uR, dtype=np.float64)
@@ -180,7 +190,7 @@ class Oracle:
     proj selects the L2 mortar projection (R5): 1 (default) the exact L2
     projection, 0 the LGL-weighted adjoint of interpolation."""
 
-    def __init__(self, mesh, N: int, gamma: float = 1.4, proj: int = 1):
+    def __init__(self, mesh, N: int, gamma: float = 1.4, proj: int = 1, volume_flux: int = 0):
         self.N, self.np, self.gamma = N, N + 1, gamma
         self.K = mesh.n_elems
         self._keep = [np.ascontiguousarray(mesh.level, dtype=np.int8),
@@ -198,6 +208,8 @@ class Oracle:
                                    _d(bcp), _d(post), _d(pre), C.byref(err))
         if not self._h:
             raise ValueError(f"oracle mesh rejected (code {err.value})")
+        # volume flux: 0 Ranocha (R1), 1 Chandrashekar (R23)
+        lib().orc_set_volume_flux(self._h, int(volume_flux))
 
     def __del__(self):
         if getattr(self, "_h", None):

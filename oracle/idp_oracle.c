@@ -50,7 +50,10 @@
  *      update with a margin of 1e-14 of the terms of the entropy function
  *      above rounding, found by bisection, verified;
  *   R22 low-order-solution bounds (Eq. Bounds_LowOrder): the node and its
- *      graph neighbours' low-order states; ghost states are not neighbours.
+ *      graph neighbours' low-order states; ghost states are not neighbours;
+ *   R23 Chandrashekar's volume flux (the paper's astrophysical jet);
+ *   R24 the jet's boundary: inflow band |y| <= 0.05 on the -x side, the
+ *      ambient state elsewhere on the x sides.
  * Every bound interval is widened to contain the low-order value, which in
  * exact arithmetic it already does (Eq. convex_combination).
  */
@@ -68,7 +71,7 @@
 /* ------------------------------------------------------------------------ */
 
 enum { F_CONF = 0, F_BND = 1, F_MORT_LARGE = 2, F_MORT_SMALL = 3 };
-enum { BC_PERIODIC = 0, BC_WALL = 1, BC_DIRICHLET = 2, BC_OUTFLOW = 3, BC_DMR = 4 };
+enum { BC_PERIODIC = 0, BC_WALL = 1, BC_DIRICHLET = 2, BC_OUTFLOW = 3, BC_DMR = 4, BC_JET = 5 };
 
 typedef struct {
     int j;          /* neighbour global node index, or -1-g for ghost g */
@@ -106,6 +109,7 @@ typedef struct {
     int *g_elem, *g_side, *g_t;  /* ghost owner element, side, face index */
     int *ghost_of;                /* [K][4][np] ghost index or -1 */
     int *mcount;  /* number of mortars incident on node */
+    int vflux;    /* volume flux: 0 Ranocha (R1), 1 Chandrashekar (R23) */
 } orc_ctx;
 
 /* ------------------------------------------------------------------------ */
@@ -336,6 +340,35 @@ void orc_ranocha(double g, const double *uL, const double *uR, int d, double *f)
     f[2] = fr * v2a + (d == 1 ? pa : 0.0);
     f[3] = fr * (0.5 * (v1L * v1R + v2L * v2R) + inv_beta / (g - 1.0)) + 0.5 * (pL * vnR + pR * vnL);
 }
+
+/* R23: Chandrashekar's EC/KEP two-point flux along the unit axis d, in his
+   notation beta = rho / (2 p): f_rho = {rho}_ln {v_n}, f_m = f_rho {v}
+   + p_hat n with p_hat = {rho} / (2 {beta}), f_E = f_rho (1 / (2 (gamma-1)
+   {beta}_ln) - {|v|^2} / 2) + f_m . {v} (Sec. 3: the paper's astrophysical
+   jet uses it for the volume fluxes). */
+void orc_chandrashekar(double g, const double *uL, const double *uR, int d, double *f) {
+    double rL = uL[0], rR = uR[0];
+    double v1L = uL[1] / rL, v2L = uL[2] / rL, v1R = uR[1] / rR, v2R = uR[2] / rR;
+    double pL = pressure(g, uL), pR = pressure(g, uR);
+    double bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
+    double rho_ln = orc_logmean(rL, rR), beta_ln = orc_logmean(bL, bR);
+    double p_hat = 0.5 * (rL + rR) / (2.0 * 0.5 * (bL + bR));
+    double v1a = 0.5 * (v1L + v1R), v2a = 0.5 * (v2L + v2R);
+    double vna = d == 0 ? v1a : v2a;
+    double v2avg = 0.5 * ((v1L * v1L + v2L * v2L) + (v1R * v1R + v2R * v2R));
+    double fr = rho_ln * vna;
+    f[0] = fr;
+    f[1] = fr * v1a + (d == 0 ? p_hat : 0.0);
+    f[2] = fr * v2a + (d == 1 ? p_hat : 0.0);
+    f[3] = fr * (1.0 / (2.0 * (g - 1.0) * beta_ln) - 0.5 * v2avg) + f[1] * v1a + f[2] * v2a;
+}
+
+static void volume_flux(const orc_ctx *c, const double *uL, const double *uR, int d, double *f) {
+    if (c->vflux == 1) orc_chandrashekar(c->gamma, uL, uR, d, f);
+    else orc_ranocha(c->gamma, uL, uR, d, f);
+}
+
+void orc_set_volume_flux(orc_ctx *c, int k) { c->vflux = k; }
 
 /* ------------------------------------------------------------------------ */
 /* mesh connectivity (naive: sorted leaf keys and binary search)            */
@@ -578,6 +611,14 @@ static void ghost_state(const orc_ctx *c, const double *u, int e, int s, int t, 
     double nx, ny; side_normal(s, &nx, &ny);
     int kind = c->bc[s];
     double x = c->xc[e] + 0.5 * c->dx[e] * c->xi[i];
+    double y = c->yc[e] + 0.5 * c->dy[e] * c->xi[j];
+    if (kind == BC_JET) {
+        /* R24: the jet inflow band |y| <= 0.05 of the -x side, the ambient
+           state elsewhere on the x sides, outflow on the y sides */
+        if (s == 0) kind = (fabs(y) <= 0.05) ? BC_DIRICHLET + 100 : BC_DIRICHLET + 200;
+        else if (s == 1) kind = BC_DIRICHLET + 200;
+        else kind = BC_OUTFLOW;
+    }
     if (kind == BC_DMR) {
         if (s == 0) kind = BC_DIRICHLET + 100;        /* post-shock inflow */
         else if (s == 1) kind = BC_OUTFLOW;
@@ -761,10 +802,10 @@ static void dg_residual(const orc_ctx *c, const double *u, const double *sf, dou
                 get_u(c, u, gidx(c, e, i, j), ui);
                 for (int k = 0; k < np; ++k) {
                     get_u(c, u, gidx(c, e, k, j), uk);
-                    orc_ranocha(g, ui, uk, 0, f);
+                    volume_flux(c, ui, uk, 0, f);
                     for (int v = 0; v < 4; ++v) F1[v] -= c->S[i][k] * (c->dy[e] / 2.0) * f[v];
                     get_u(c, u, gidx(c, e, i, k), uk);
-                    orc_ranocha(g, ui, uk, 1, f);
+                    volume_flux(c, ui, uk, 1, f);
                     for (int v = 0; v < 4; ++v) F2[v] -= c->S[j][k] * (c->dx[e] / 2.0) * f[v];
                 }
                 for (int v = 0; v < 4; ++v) {
@@ -789,7 +830,7 @@ static void dg_subcell_flux(const orc_ctx *c, const double *u, int e, int d, int
         for (int k = 0; k < np; ++k) {
             get_u(c, u, d == 0 ? gidx(c, e, l, r) : gidx(c, e, r, l), ul);
             get_u(c, u, d == 0 ? gidx(c, e, k, r) : gidx(c, e, r, k), uk);
-            orc_ranocha(c->gamma, ul, uk, d, f);
+            volume_flux(c, ul, uk, d, f);
             for (int v = 0; v < 4; ++v) fh[v] += c->S[l][k] * half * f[v];
         }
 }

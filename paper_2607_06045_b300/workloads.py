@@ -24,7 +24,7 @@ from typing import Callable, List, Optional, Sequence
 import numpy as np
 
 # Boundary kinds, numbered as in the C header (idp_bc).
-BC_PERIODIC, BC_WALL, BC_DIRICHLET, BC_OUTFLOW, BC_DMR = 0, 1, 2, 3, 4
+BC_PERIODIC, BC_WALL, BC_DIRICHLET, BC_OUTFLOW, BC_DMR, BC_JET = 0, 1, 2, 3, 4, 5
 
 
 @dataclasses.dataclass
@@ -375,6 +375,45 @@ def cfg5_state(mesh: Mesh, N: int, centre, gamma=1.4):
     p = np.where(disc, 1e3, 1e-9)
     z = np.zeros_like(X)
     return conserved(rho, z, z, p, gamma)
+
+
+# --- high-Mach jet (gamma = 5/3) ---------------------------------------------
+
+JET_IN = np.array([5.0, 800.0, 0.0, 0.4127])      # inflow band (rho, v1, v2, p)
+JET_AMBIENT = np.array([0.5, 0.0, 0.0, 0.4127])   # gas at rest
+JET_GAMMA = 5.0 / 3.0
+
+
+def jet_mesh(n0=64, levels=3, half_width=0.1):
+    """Astrophysical-jet geometry of Sec. 3 on a static mesh: [-0.5, 0.5]^2,
+    n0 x n0 base grid, `levels` extra levels for leaves within |y| < half_width,
+    balanced 2:1; jet boundary on the x sides (inflow band |y| <= 0.05 on -x,
+    ambient state elsewhere), periodic in y."""
+    box = (-0.5, -0.5, 0.5, 0.5)
+    lmap = np.zeros((n0 << levels, n0 << levels), dtype=np.int16)
+    for _ in range(levels):
+        def band(cx, cy, hx, hy):
+            return np.abs(cy) < half_width
+        lmap = refine_where(lmap, levels, n0, n0, box, band, levels)
+        lmap = balance_2to1(lmap, levels, (False, True))
+    m = mesh_from_map(lmap, levels, n0, n0, box, bc=(BC_JET, BC_JET, BC_PERIODIC, BC_PERIODIC))
+    m.dmr_post = JET_IN.copy()
+    m.dmr_pre = JET_AMBIENT.copy()
+    return m
+
+
+def jet_state(mesh: Mesh, N: int, gamma=JET_GAMMA, seed=None):
+    """The ambient gas at rest; with a seed, a small seeded perturbation of the
+    density (1%) so that the volume fluxes do not vanish before the jet enters."""
+    X, Y = node_coords(mesh, N)
+    rho = np.full_like(X, JET_AMBIENT[0])
+    if seed is not None:
+        rng = np.random.default_rng(seed)
+        k = rng.integers(1, 4, 2)
+        ph = rng.uniform(0, 2 * math.pi, 2)
+        rho = rho * (1.0 + 0.01 * np.sin(2 * math.pi * k[0] * X + ph[0]) * np.sin(2 * math.pi * k[1] * Y + ph[1]))
+    z = np.zeros_like(X)
+    return conserved(rho, z, z, np.full_like(X, JET_AMBIENT[3]), gamma)
 
 
 # --- smooth test problems ----------------------------------------------------
