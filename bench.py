@@ -337,6 +337,31 @@ def run_ours(args):
                                                          "n_viol_pressure", "n_viol_entropy", "n_nonpositive")})
         vctx.close()
         del u_dev
+    # high-Mach jet (gamma = 5/3, Mach ~2000 inflow), Chandrashekar's volume
+    # flux with combined limiting as in the paper's astrophysical jet, on a
+    # static 53,632-element mesh, both precisions
+    from paper_2607_06045_b300 import workloads as W
+    jm = W.jet_mesh()
+    ju = W.jet_state(jm, 3, W.JET_GAMMA)
+    jnodes = ju.shape[1] * ju.shape[2] * ju.shape[3]
+    for prec in (0, 1):
+        jctx = idp.Context(jm, 3, gamma=W.JET_GAMMA, precision=prec, limiting=3, volume_flux=1, cfl=0.5)
+        jud = torch.from_numpy(ju).cuda()
+        barrier_sync()
+        jt, _, _, jk = time_steps(jctx, jud, vsteps, args.warmup, flush, stream, barrier_sync)
+        jt = max_over_ranks(jt)
+        _, jst = jctx.idp_dgsem_limiter_stats()
+        variants[f"jet_chandrashekar_{'fp32' if prec else 'fp64'}"] = dict(
+            value=aggregate_rate(jnodes * 3 * vsteps, world, jt), unit=UNIT, ms_per_step=jt / vsteps * 1e3,
+            steps=vsteps, elements=int(jctx.K), dofs=int(jnodes),
+            workload="jet: [-0.5,0.5]^2, 64x64 base + 3 levels in |y| < 0.1, N=3, gamma 5/3, rho 5 / v1 800 "
+                     "inflow band, combined limiting, Chandrashekar volume flux",
+            gpu_launches=int(jctx.launches_per_step() * vsteps),
+            kernels={k: {"ms_per_launch": ms / n, "launches_per_step": n / vsteps} for k, (ms, n) in jk.items() if n},
+            stats={k: jst[k] for k in ("alpha_volume_mean", "alpha_mortar_mean", "n_viol_density",
+                                       "n_viol_pressure", "n_nonpositive")})
+        jctx.close()
+        del jud
     dts = []
     for rule in (0, 1):
         dctx = idp.Context(meshes[0], 3, cfl=1.0, dt_rule=rule)

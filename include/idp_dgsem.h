@@ -59,13 +59,18 @@ typedef enum {
  *  DMR       double Mach reflection: side -x post-shock Dirichlet, +x
  *            outflow, -y post-shock Dirichlet for x < 1/6 and wall
  *            otherwise, +y post-shock for x < 1/6 + (y1 + 20 t)/sqrt(3) and
- *            pre-shock otherwise (states dmr_post and dmr_pre). */
+ *            pre-shock otherwise (states dmr_post and dmr_pre);
+ *  JET       high-Mach jet (Sec. 3, astrophysical jet): on side -x the
+ *            inflow state dmr_post for |y| <= 0.05 and the ambient state
+ *            dmr_pre elsewhere, on side +x the ambient state dmr_pre (both
+ *            Dirichlet), outflow on the y sides. */
 typedef enum {
     IDP_BC_PERIODIC = 0,
     IDP_BC_WALL = 1,
     IDP_BC_DIRICHLET = 2,
     IDP_BC_OUTFLOW = 3,
-    IDP_BC_DMR = 4
+    IDP_BC_DMR = 4,
+    IDP_BC_JET = 5
 } idp_bc;
 
 /* A quadtree mesh: an nx0 x ny0 level-0 grid over [x0,x1] x [y0,y1]; leaf e
@@ -118,7 +123,10 @@ typedef struct {
  *  entropy_bound  1: local limiting also keeps the modified specific entropy
  *             eta = p rho^-gamma / (gamma - 1) at or above the minimum of eta
  *             over the bounds' states (right parts of Eqs. Bounds_Barstates
- *             and Bounds_LowOrder), relaxed by 1e-12 relative; 0: off. */
+ *             and Bounds_LowOrder), relaxed by 1e-12 relative; 0: off.
+ *  volume_flux  two-point volume flux of the split form: 0 Ranocha's
+ *             entropy-conserving, kinetic-energy-preserving flux (Sec. 3);
+ *             1 Chandrashekar's (the paper's astrophysical jet). */
 typedef struct {
     int32_t precision;
     int32_t limiting;
@@ -131,6 +139,7 @@ typedef struct {
     int32_t collect_stats;
     int32_t grid_mode;
     int32_t entropy_bound;
+    int32_t volume_flux;
 } idp_options;
 
 /* Limiter statistics accumulated over the stages since the previous call of

@@ -24,7 +24,7 @@ constexpr double kEtaViol = 1e-11;   // entropy bound: tolerance of the violatio
 // Face kinds of an element side (-x, +x, -y, +y).
 enum : int { FT_CONF = 0, FT_BND = 1, FT_MLARGE = 2, FT_MSLO = 3, FT_MSHI = 4 };
 // Boundary kinds (idp_bc)
-enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_DIRICHLET = 2, BC_OUTFLOW = 3, BC_DMR = 4 };
+enum : int { BC_PERIODIC = 0, BC_WALL = 1, BC_DIRICHLET = 2, BC_OUTFLOW = 3, BC_DMR = 4, BC_JET = 5 };
 // status bits
 enum : unsigned { ST_BAD_INPUT = 1u, ST_VIOLATION = 2u, ST_NONFINITE = 4u };
 
@@ -193,6 +193,26 @@ __device__ __forceinline__ void log_means(const Prim<FT> &a, const Prim<FT> &b, 
     } else {
         ibeta = lb * ixb;
     }
+}
+
+// Chandrashekar's entropy-conserving, kinetic-energy-preserving two-point
+// flux along axis d (reading R23; the paper's astrophysical jet), with
+// beta = rho / p: f_rho = {rho}_ln {v_n}, f_m = f_rho {v} + ({rho}/{beta}) n,
+// f_E = f_rho (1 / ((gamma-1) {beta}_ln) - {|v|^2} / 2) + f_m . {v}.
+template <typename FT>
+__device__ __forceinline__ void chandrashekar(const Prim<FT> &a, const Prim<FT> &b, int d, FT ginv1, FT f[4]) {
+    FT rho_ln, ibeta;
+    log_means<FT>(a, b, rho_ln, ibeta);
+    FT v1m = FT(0.5) * (a.v1 + b.v1), v2m = FT(0.5) * (a.v2 + b.v2);
+    FT fr = rho_ln * (d == 0 ? v1m : v2m);
+    FT ph;
+    if constexpr (sizeof(FT) == 8) ph = (a.rho + b.rho) * fast_rcp(a.beta + b.beta);
+    else ph = (a.rho + b.rho) / (a.beta + b.beta);
+    FT v2a = FT(0.5) * ((a.v1 * a.v1 + a.v2 * a.v2) + (b.v1 * b.v1 + b.v2 * b.v2));
+    f[0] = fr;
+    f[1] = fr * v1m + (d == 0 ? ph : FT(0));
+    f[2] = fr * v2m + (d == 1 ? ph : FT(0));
+    f[3] = fr * (ibeta * ginv1 - FT(0.5) * v2a) + f[1] * v1m + f[2] * v2m;
 }
 
 // Ranocha's entropy-conserving, kinetic-energy-preserving two-point flux
@@ -481,13 +501,18 @@ __device__ __forceinline__ double theta_entropy(const Gas &G, const double u0[4]
     return 0.0;
 }
 
-// Ghost state across boundary side s (reading R4). in: interior conserved
-// state at the face node, x: its x coordinate, t: time.
-__device__ __forceinline__ void ghost_state(const SimInfo &si, int s, const double in[4], double x, double t,
-                                            double gst[4]) {
+// Ghost state across boundary side s (readings R4, R24). in: interior
+// conserved state at the face node, (x, y): its coordinates, t: time.
+__device__ __forceinline__ void ghost_state(const SimInfo &si, int s, const double in[4], double x, double y,
+                                            double t, double gst[4]) {
     int kind = si.bc[s];
     const double *dir = nullptr;
-    if (kind == BC_DMR) {
+    if (kind == BC_JET) {
+        // inflow band |y| <= 0.05 on -x, ambient state elsewhere on the x sides
+        if (s == 0) dir = fabs(y) <= 0.05 ? si.dmr_post : si.dmr_pre;
+        else if (s == 1) dir = si.dmr_pre;
+        kind = dir ? BC_DIRICHLET : BC_OUTFLOW;
+    } else if (kind == BC_DMR) {
         if (s == 0) dir = si.dmr_post;
         else if (s == 1) kind = BC_OUTFLOW;
         else if (s == 2) { if (x < 1.0 / 6.0) dir = si.dmr_post; else kind = BC_WALL; }

@@ -43,6 +43,7 @@ struct StageArgs {
     int lob;              // 1: low-order-solution bounds (Eq. Bounds_LowOrder)
     int pass;             // 1: low-order pre-pass (writes lofv and stops after the low-order update)
     double *lofv;         // [2][K (N+1)^2]: rho_FV and s(u_FV) of every node (pre-pass output)
+    int vflux;            // volume flux: 0 Ranocha, 1 Chandrashekar (extended kernel)
 };
 
 __device__ __forceinline__ double stage_dt(const StageArgs &A, int sim) {
@@ -324,8 +325,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 double dtt = stage_dt(A, sim);
                 double tt = stage_time(A, sim, dtt);
                 double xn = geo.x + 0.5 * geo.z * (1.0 + A.ops->xi[ii]);
+                double yn = geo.y + 0.5 * geo.w * (1.0 + A.ops->xi[face_node<NP>(s, t) / NP]);
                 double gst[4];
-                ghost_state(mesh.siminfo[sim], s, in, xn, tt, gst);
+                ghost_state(mesh.siminfo[sim], s, in, xn, yn, tt, gst);
                 for (int v = 0; v < 4; ++v) S.outs[s][t][v] = gst[v];
             }
         }
@@ -341,7 +343,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             PairTab<NP>::ab(pi, a, b);
             Prim<FT> pa = load_prim<NP, FT, EXT>(S, nodeid<NP>(d, r, a)), pb = load_prim<NP, FT, EXT>(S, nodeid<NP>(d, r, b));
             FT f[4];
-            ranocha<FT>(pa, pb, d, ginv1, f);
+            if (EXT && A.vflux == 1) chandrashekar<FT>(pa, pb, d, ginv1, f);
+            else ranocha<FT>(pa, pb, d, ginv1, f);
             for (int v = 0; v < 4; ++v) S.pair[d][r][pi][v] = f[v];
         }
         for (int k = tid; k < EPB * 4 * NP; k += NT) {

@@ -260,7 +260,7 @@ idp_status build_mesh(const idp_mesh_desc &d, double gamma, int simid, HostMesh 
     if (d.nx0 < 1 || d.ny0 < 1 || d.n_leaves < 1 || !d.level || !d.ix || !d.iy) return IDP_E_ARG;
     if (!(d.x1 > d.x0) || !(d.y1 > d.y0)) return IDP_E_ARG;
     for (int s = 0; s < 4; ++s)
-        if (d.bc[s] < IDP_BC_PERIODIC || d.bc[s] > IDP_BC_DMR) return IDP_E_ARG;
+        if (d.bc[s] < IDP_BC_PERIODIC || d.bc[s] > IDP_BC_JET) return IDP_E_ARG;
     if ((d.bc[0] == IDP_BC_PERIODIC) != (d.bc[1] == IDP_BC_PERIODIC)) return IDP_E_ARG;
     if ((d.bc[2] == IDP_BC_PERIODIC) != (d.bc[3] == IDP_BC_PERIODIC)) return IDP_E_ARG;
     const int K = d.n_leaves, base = (int)H.geom.size(), mbase = (int)H.m_large.size();
@@ -502,6 +502,7 @@ StageArgs base_args(idp_ctx *c) {
     A.lob = c->lob;
     A.pass = 0;
     A.lofv = c->d_lofv;
+    A.vflux = c->opt.volume_flux;
     return A;
 }
 
@@ -702,7 +703,9 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (o.precision < 0 || o.precision > 1 || o.limiting < 0 || o.limiting > 3 || o.dt_rule < 0 || o.dt_rule > 1 ||
         !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0) || o.mortar_projection < 0 || o.mortar_projection > 1)
         return IDP_E_ARG;
-    if (o.bounds < 0 || o.bounds > 1 || o.entropy_bound < 0 || o.entropy_bound > 1) return IDP_E_ARG;
+    if (o.bounds < 0 || o.bounds > 1 || o.entropy_bound < 0 || o.entropy_bound > 1 || o.volume_flux < 0 ||
+        o.volume_flux > 1)
+        return IDP_E_ARG;
     if (o.elems_per_block != 0 && o.elems_per_block != 1 && o.elems_per_block != 2 && o.elems_per_block != 4 &&
         o.elems_per_block != 8 && o.elems_per_block != 16)
         return IDP_E_ARG;
@@ -719,7 +722,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     c->N = N; c->NP = N + 1; c->n_sims = n_sims; c->gamma = gamma; c->opt = o;
     // the variants act only in local limiting (and its half of the combined mode)
     c->lob = o.limiting >= 2 && o.bounds == 1;
-    c->ext = o.limiting >= 2 && (o.bounds == 1 || o.entropy_bound == 1);
+    c->ext = (o.limiting >= 2 && (o.bounds == 1 || o.entropy_bound == 1)) || o.volume_flux == 1;
     c->ent_bar = o.limiting >= 2 && o.entropy_bound == 1 && o.bounds == 0;
     c->K = (long long)H.geom.size(); c->M = (long long)H.m_large.size();
     c->sim_off = H.sim_off;

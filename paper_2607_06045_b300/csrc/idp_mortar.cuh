@@ -455,7 +455,8 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
                         size_t gi = (size_t)e * NN + n;
                         double ui[4] = {u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi]};
                         double xn = geo.x + 0.5 * geo.z * (1.0 + ops->xi[i]);
-                        ghost_state(mesh.siminfo[sim], s, ui, xn, t_sim[sim], uo);
+                        double yn = geo.y + 0.5 * geo.w * (1.0 + ops->xi[n / NP]);
+                        ghost_state(mesh.siminfo[sim], s, ui, xn, yn, t_sim[sim], uo);
                     }
                     Prim<FT> po = mortar_prim<NP, FT>(g, uo);
                     s_o[le][s][t] = fabs((s >> 1) == 0 ? po.v1 : po.v2) + po.c;
