@@ -46,7 +46,7 @@ def lib():
         L.orc_create.restype = C.c_void_p
         L.orc_create.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                  C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int8), ip, ip, ip,
-                                 dp, dp, dp, C.POINTER(C.c_int)]
+                                 dp, dp, dp, C.c_int, C.POINTER(C.c_int)]
         L.orc_destroy.argtypes = [C.c_void_p]
         L.orc_lgl.argtypes = [C.c_int, dp, dp]
         L.orc_operators.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, dp]
@@ -71,6 +71,7 @@ def lib():
         L.orc_step.argtypes = [C.c_void_p, dp, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
                                C.c_int, dp, dp]
         L.orc_set_volume_flux.argtypes = [C.c_void_p, C.c_int]
+        L.orc_mortar_weights.argtypes = [C.c_void_p, dp]
         L.orc_chandrashekar.argtypes = [C.c_double, dp, dp, C.c_int, dp]
         L.orc_theta_entropy.restype = C.c_double
         L.orc_theta_entropy.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double]
@@ -188,9 +189,12 @@ class Oracle:
     """Oracle context for one mesh, degree N and gamma.
 
     proj selects the L2 mortar projection (R5): 1 (default) the exact L2
-    projection, 0 the LGL-weighted adjoint of interpolation."""
+    projection, 0 the LGL-weighted adjoint of interpolation. volume_flux: 0
+    Ranocha (R1), 1 Chandrashekar (R23). mortar_low: 0 the sparse local
+    weights (Eq. local_weights), 1 the all-to-all weights (Eq. nonlocal_weight,
+    R25) in the low-order mortar flux."""
 
-    def __init__(self, mesh, N: int, gamma: float = 1.4, proj: int = 1, volume_flux: int = 0):
+    def __init__(self, mesh, N: int, gamma: float = 1.4, proj: int = 1, volume_flux: int = 0, mortar_low: int = 0):
         self.N, self.np, self.gamma = N, N + 1, gamma
         self.K = mesh.n_elems
         self._keep = [np.ascontiguousarray(mesh.level, dtype=np.int8),
@@ -205,7 +209,7 @@ class Oracle:
         x0, y0, x1, y1 = mesh.box
         self._h = lib().orc_create(N, gamma, proj, mesh.nx0, mesh.ny0, x0, y0, x1, y1, self.K,
                                    lev.ctypes.data_as(C.POINTER(C.c_int8)), _i(ix), _i(iy), _i(bc),
-                                   _d(bcp), _d(post), _d(pre), C.byref(err))
+                                   _d(bcp), _d(post), _d(pre), int(mortar_low), C.byref(err))
         if not self._h:
             raise ValueError(f"oracle mesh rejected (code {err.value})")
         # volume flux: 0 Ranocha (R1), 1 Chandrashekar (R23)
@@ -229,6 +233,12 @@ class Oracle:
         out = np.zeros((self.n_mortars, 5), dtype=np.int32)
         if self.n_mortars:
             lib().orc_mortars(self._h, _i(out))
+        return out
+
+    def mortar_weights(self):
+        """Weights of the low-order mortar flux [np][2 np] (reference units)."""
+        out = np.zeros((self.np, 2 * self.np))
+        lib().orc_mortar_weights(self._h, _d(out))
         return out
 
     def faces(self):

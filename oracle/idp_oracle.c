@@ -53,7 +53,8 @@
  *      graph neighbours' low-order states; ghost states are not neighbours;
  *   R23 Chandrashekar's volume flux (the paper's astrophysical jet);
  *   R24 the jet's boundary: inflow band |y| <= 0.05 on the -x side, the
- *      ambient state elsewhere on the x sides.
+ *      ambient state elsewhere on the x sides;
+ *   R25 all-to-all mortar weights by the LGL quadrature of the small face.
  * Every bound interval is widened to contain the low-order value, which in
  * exact arithmetic it already does (Eq. convex_combination).
  */
@@ -84,6 +85,7 @@ typedef struct {
     double xi[NPMAX], w[NPMAX];
     double D[NPMAX][NPMAX], S[NPMAX][NPMAX];
     double wt[NPMAX][2 * NPMAX];   /* local weights, reference units */
+    double mw[NPMAX][2 * NPMAX];   /* weights of the low-order mortar flux: wt, or all-to-all (R25) */
     double Iint[2 * NPMAX][NPMAX]; /* interpolation large -> small nodes */
     double P[NPMAX][2 * NPMAX];    /* projection small -> large */
 
@@ -370,6 +372,12 @@ static void volume_flux(const orc_ctx *c, const double *uL, const double *uR, in
 
 void orc_set_volume_flux(orc_ctx *c, int k) { c->vflux = k; }
 
+/* the weights of the low-order mortar flux, [np][2 np], reference units */
+void orc_mortar_weights(const orc_ctx *c, double *out) {
+    for (int a = 0; a < c->np; ++a)
+        for (int b = 0; b < 2 * c->np; ++b) out[a * 2 * c->np + b] = c->mw[a][b];
+}
+
 /* ------------------------------------------------------------------------ */
 /* mesh connectivity (naive: sorted leaf keys and binary search)            */
 /* ------------------------------------------------------------------------ */
@@ -420,7 +428,7 @@ static void push_nb(orc_nb **buf, int *n, int *cap, int j, double cx, double cy)
 orc_ctx *orc_create(int N, double gamma, int proj, int nx0, int ny0, double x0, double y0,
                     double x1, double y1, int K, const int8_t *level, const int32_t *ix,
                     const int32_t *iy, const int32_t *bc, const double *bc_prim,
-                    const double *dmr_post, const double *dmr_pre, int *err) {
+                    const double *dmr_post, const double *dmr_pre, int a2a, int *err) {
     *err = 0;
     if (N < 1 || N + 1 > NPMAX || K < 1) { *err = 1; return NULL; }
     orc_ctx *c = calloc(1, sizeof(orc_ctx));
@@ -435,6 +443,19 @@ orc_ctx *orc_create(int N, double gamma, int proj, int nx0, int ny0, double x0, 
         for (int a = 0; a < np; ++a) for (int b = 0; b < np; ++b) { c->D[a][b] = D[a * np + b]; c->S[a][b] = S[a * np + b]; }
         for (int a = 0; a < np; ++a) for (int b = 0; b < 2 * np; ++b) { c->wt[a][b] = wt[a * 2 * np + b]; c->P[a][b] = P[a * 2 * np + b]; }
         for (int a = 0; a < 2 * np; ++a) for (int b = 0; b < np; ++b) c->Iint[a][b] = I[a * np + b];
+        /* low-order mortar weights: the sparse local weights of Eq. local_weights,
+           or the all-to-all weights of Eq. nonlocal_weight, omega_(i,j) =
+           int_{S,N} phi_i^- phi_j^+ ds by the LGL quadrature of the small face S
+           (R25): w_j |S|/2 phi_i(x_j), i.e. w_l / 2 * I[p np + l][k] in units of the
+           large face's half length */
+        for (int a = 0; a < np; ++a)
+            for (int b = 0; b < 2 * np; ++b) {
+                double x = 0.5 * w[b % np] * I[b * np + a];
+                /* rounding-level values where a small-face node meets a large
+                   node are zero (as R14 for the local weights) */
+                if (fabs(x) < 1e-13) x = 0.0;
+                c->mw[a][b] = a2a ? x : c->wt[a][b];
+            }
     }
     c->nx0 = nx0; c->ny0 = ny0; c->x0 = x0; c->y0 = y0; c->x1 = x1; c->y1 = y1;
     for (int s = 0; s < 4; ++s) { c->bc[s] = bc[s]; for (int v = 0; v < 4; ++v) c->bc_prim[s][v] = bc_prim[4 * s + v]; }
@@ -552,8 +573,8 @@ orc_ctx *orc_create(int N, double gamma, int proj, int nx0, int ny0, double x0, 
                         for (int p = 0; p < 2; ++p) {
                             int es = c->mort[5 * m + 3 + p];
                             for (int l = 0; l < np; ++l) {
-                                double wt = c->wt[t][p * np + l];
-                                if (wt <= 0.0) continue;
+                                double wt = c->mw[t][p * np + l];
+                                if (wt == 0.0) continue;
                                 int si, sj; face_node(np, s_small, l, &si, &sj);
                                 double cc = wt * halfL / 2.0;
                                 push_nb(&buf, &cnt, &cap, gidx(c, es, si, sj), cc * nx, cc * ny);
@@ -563,8 +584,8 @@ orc_ctx *orc_create(int N, double gamma, int proj, int nx0, int ny0, double x0, 
                         int p = c->fpos[4 * e + s];
                         int s_large = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2);
                         for (int k = 0; k < np; ++k) {
-                            double wt = c->wt[k][p * np + t];
-                            if (wt <= 0.0) continue;
+                            double wt = c->mw[k][p * np + t];
+                            if (wt == 0.0) continue;
                             int li, lj; face_node(np, s_large, k, &li, &lj);
                             double cc = wt * halfL / 2.0;
                             push_nb(&buf, &cnt, &cap, gidx(c, large, li, lj), cc * nx, cc * ny);
@@ -682,15 +703,18 @@ static void mortar_low(const orc_ctx *c, const double *u, int m, double Flo[][4]
     for (int k = 0; k < np; ++k)
         for (int p = 0; p < 2; ++p)
             for (int l = 0; l < np; ++l) {
-                double wt = c->wt[k][p * np + l] * halfL;
-                if (wt <= 0.0) continue;
+                double wt = c->mw[k][p * np + l] * halfL;
+                if (wt == 0.0) continue;
                 double ui[4], uj[4], fi[4], fj[4];
                 get_u(c, u, gnode[k], ui); get_u(c, u, gnode[np + p * np + l], uj);
                 flux_n(gm, ui, nxL, nyL, fi); flux_n(gm, uj, nxL, nyL, fj);
                 double lam = lambda_max(gm, ui, uj, nxL, nyL);
+                /* c_ij = omega n / 2 and d_ij = |c_ij| lambda (the all-to-all
+                   weights can be negative) */
+                double aw = fabs(wt);
                 for (int v = 0; v < 4; ++v) {
-                    Flo[k][v] += 0.5 * wt * ((fi[v] + fj[v]) - lam * (uj[v] - ui[v]));
-                    Flo[np + p * np + l][v] += 0.5 * wt * (-(fi[v] + fj[v]) - lam * (ui[v] - uj[v]));
+                    Flo[k][v] += 0.5 * (wt * (fi[v] + fj[v]) - aw * lam * (uj[v] - ui[v]));
+                    Flo[np + p * np + l][v] += 0.5 * (-wt * (fi[v] + fj[v]) - aw * lam * (ui[v] - uj[v]));
                 }
             }
 }
