@@ -126,7 +126,11 @@ typedef struct {
  *             and Bounds_LowOrder), relaxed by 1e-12 relative; 0: off.
  *  volume_flux  two-point volume flux of the split form: 0 Ranocha's
  *             entropy-conserving, kinetic-energy-preserving flux (Sec. 3);
- *             1 Chandrashekar's (the paper's astrophysical jet). */
+ *             1 Chandrashekar's (the paper's astrophysical jet).
+ *  mortar_low weights of the low-order mortar flux: 0 the sparse local
+ *             weights (Eq. local_weights, App. A); 1 the all-to-all weights
+ *             (Eq. nonlocal_weight, by the small face's LGL quadrature), the
+ *             diffusive baseline the paper starts from. */
 typedef struct {
     int32_t precision;
     int32_t limiting;
@@ -140,6 +144,7 @@ typedef struct {
     int32_t grid_mode;
     int32_t entropy_bound;
     int32_t volume_flux;
+    int32_t mortar_low;
 } idp_options;
 
 /* Limiter statistics accumulated over the stages since the previous call of

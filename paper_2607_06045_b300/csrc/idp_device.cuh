@@ -46,14 +46,16 @@ struct Ops {
     double w[NPMAX];                 // LGL weights
     double iw[NPMAX];                // 1 / w
     double S[NPMAX][NPMAX];          // Sbar = 2 Qbar - Bbar
-    double wt[NPMAX][2 * NPMAX];     // local mortar weights (reference units)
+    double wt[NPMAX][2 * NPMAX];     // low-order mortar weights (reference units): local or all-to-all
     double I[2 * NPMAX][NPMAX];      // interpolation large -> small-face nodes
     double P[NPMAX][2 * NPMAX];      // projection small-face fluxes -> large
-    // nonzero local weights as a pair list (large node k, small-face node r),
-    // k-major with r ascending, and per mortar slot (large nodes first, then
-    // the small-face nodes) the pairs that touch it, in the same order
+    // nonzero low-order mortar weights as a pair list (large node k,
+    // small-face node r), k-major with r ascending, and per mortar slot (large
+    // nodes first, then the small-face nodes) the pairs that touch it, in the
+    // same order (at most 3 N + 2 pairs for the sparse local weights, all
+    // 2 (N+1)^2 for the all-to-all weights)
     int npair;
-    int pk[3 * NPMAX], pr[3 * NPMAX];
+    int pk[2 * NPMAX * NPMAX], pr[2 * NPMAX * NPMAX];
     int slot_n[3 * NPMAX];
     int slot_p[3 * NPMAX][2 * NPMAX];
     LogTab lg;                       // table of the FP64 logarithm

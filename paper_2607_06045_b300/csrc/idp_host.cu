@@ -127,7 +127,7 @@ void host_log_table_impl(LogTab &T) {
     T.ln2_lo = (double)(ln2 - (long double)h);
 }
 
-void build_ops(int N, int proj, Ops &o) {
+void build_ops(int N, int proj, int a2a, Ops &o) {
     std::memset(&o, 0, sizeof(o));
     host_log_table_impl(o.lg);
     const int np = N + 1;
@@ -180,15 +180,6 @@ void build_ops(int N, int proj, Ops &o) {
     }
     o.ind_T = 0.5 * std::pow(10.0, -1.8 * std::pow(N + 1.0, 0.25));
     o.ind_s = std::log((1.0 - 1e-4) / 1e-4);
-    o.npair = 0;
-    for (int k = 0; k < np; ++k)
-        for (int r = 0; r < 2 * np; ++r)
-            if (o.wt[k][r] > 0.0) {
-                const int p = o.npair++;
-                o.pk[p] = k; o.pr[p] = r;
-                o.slot_p[k][o.slot_n[k]++] = p;
-                o.slot_p[np + r][o.slot_n[np + r]++] = p;
-            }
     // interpolation to the small-face nodes s = (x_l -/+ 1) / 2
     for (int e = 0; e < 2; ++e)
         for (int l = 0; l < np; ++l) {
@@ -196,6 +187,26 @@ void build_ops(int N, int proj, Ops &o) {
             bary_basis(np, x, lam, 0.5 * (x[l] + (e == 0 ? -1.0 : 1.0)), phi);
             for (int k = 0; k < np; ++k) o.I[e * np + l][k] = phi[k];
         }
+    if (a2a) {
+        // all-to-all weights (Eq. nonlocal_weight) by the small face's LGL
+        // quadrature: w_l / 2 * phi_k(x_(e,l)) in units of the large face's
+        // half length; rounding-level values where nodes meet are zero
+        for (int k = 0; k < np; ++k)
+            for (int r = 0; r < 2 * np; ++r) {
+                const double v = 0.5 * w[r % np] * o.I[r][k];
+                o.wt[k][r] = std::fabs(v) < 1e-13 ? 0.0 : v;
+            }
+    }
+    // nonzero weights as pairs (the all-to-all weights can be negative)
+    o.npair = 0;
+    for (int k = 0; k < np; ++k)
+        for (int r = 0; r < 2 * np; ++r)
+            if (o.wt[k][r] != 0.0) {
+                const int p = o.npair++;
+                o.pk[p] = k; o.pr[p] = r;
+                o.slot_p[k][o.slot_n[k]++] = p;
+                o.slot_p[np + r][o.slot_n[np + r]++] = p;
+            }
     if (proj == 0) {
         for (int k = 0; k < np; ++k)
             for (int c = 0; c < 2 * np; ++c) o.P[k][c] = 0.5 * w[c % np] * o.I[c][k] / w[k];
@@ -537,7 +548,7 @@ void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mo
     const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
     if (c->M > 0 && need_mortar_flux) {
         int k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
-        c->L.mortar_flux(c->opt.precision, c->ent_bar, gm, st, c->mesh, c->slots, A.u, A.gas, c->d_ops);
+        c->L.mortar_flux(c->opt.precision, c->ent_bar, c->opt.mortar_low, gm, st, c->mesh, c->slots, A.u, A.gas, c->d_ops);
         kt_end(c, st, k);
     }
     bool dgmode = (A.mode == 0 && A.dt == 0.0) || A.limiting == 0;
@@ -577,7 +588,7 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) 
     if (c->M > 0 && mortar_flux && c->opt.dt_rule == 0) {
         const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
         k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
-        c->L.mortar_flux(c->opt.precision, c->ent_bar, gm, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg),
+        c->L.mortar_flux(c->opt.precision, c->ent_bar, c->opt.mortar_low, gm, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg),
                          c->d_ops);
         kt_end(c, st, k);
     }
@@ -704,7 +715,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
         !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0) || o.mortar_projection < 0 || o.mortar_projection > 1)
         return IDP_E_ARG;
     if (o.bounds < 0 || o.bounds > 1 || o.entropy_bound < 0 || o.entropy_bound > 1 || o.volume_flux < 0 ||
-        o.volume_flux > 1)
+        o.volume_flux > 1 || o.mortar_low < 0 || o.mortar_low > 1)
         return IDP_E_ARG;
     if (o.elems_per_block != 0 && o.elems_per_block != 1 && o.elems_per_block != 2 && o.elems_per_block != 4 &&
         o.elems_per_block != 8 && o.elems_per_block != 16)
@@ -737,7 +748,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
     if (ce != cudaSuccess) { note(ce, "device query"); delete c; return IDP_E_CUDA; }
     Ops ops;
-    build_ops(N, o.mortar_projection, ops);
+    build_ops(N, o.mortar_projection, o.mortar_low, ops);
     // unique mortar nodes, slots ordered by mortar id
     const int NP = c->NP, NN = NP * NP, Q = 3 * NP;
     std::vector<std::pair<long long, int>> ns;

@@ -39,10 +39,11 @@ __device__ __forceinline__ Prim<FT> mortar_prim(const Gas &g, const double *q) {
 // fixed order.
 // ent: also the minimum over each slot's bar states of s = ln p - gamma ln rho
 // (entropy bound of local limiting with bar-state bounds).
-template <int NP, typename FT>
+// A2A: all-to-all weights (every large node with every small-face node).
+template <int NP, typename FT, bool A2A>
 __global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
 k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, const Ops *ops, int ent) {
-    constexpr int NN = NP * NP, Q = 3 * NP, NI = 2 * NP, MP = 3 * NP, W = MORTARS_PER_BLOCK;
+    constexpr int NN = NP * NP, Q = 3 * NP, NI = 2 * NP, MP = A2A ? 2 * NP * NP : 3 * NP, W = MORTARS_PER_BLOCK;
     __shared__ double s_u[W][Q][4];      // traces: large side, then the two small faces
     __shared__ FT s_uf[W][Q][4];         // the same in the flux type
     __shared__ FT s_pr[W][Q][3];         // normal velocity, p, c
@@ -100,8 +101,8 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
     // sparse low-order pair terms (Eq. interfaceflux_local) with their bar
     // states and 2 d; term enters the large slot with -, the small with +
     const int npair = ops->npair;
-    if (lane < npair) {
-        const int k = ops->pk[lane], r = ops->pr[lane];
+    for (int pp = lane; pp < npair; pp += 32) {
+        const int k = ops->pk[pp], r = ops->pr[pp];
         const double wt = ops->wt[k][r] * halfL;
         const double *a = s_u[warp][k], *b = s_u[warp][NP + r];
         const FT *af = s_uf[warp][k], *bf = s_uf[warp][NP + r];
@@ -116,20 +117,26 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
         double i2l;
         if constexpr (F32) { hw = d2f(0.5 * wt); i2l_f = 0.5f / lam; i2l = f2d(i2l_f); }
         else { hw = 0.5 * wt; i2l = 0.5 * fast_rcp(lam); }
+        // the all-to-all weights can be negative: c_ij = omega n / 2 and
+        // d_ij = |c_ij| lambda, so the bar state looks along sign(omega) n
+        const double sgw = (A2A && wt < 0.0) ? -sg : sg;
         for (int v = 0; v < 4; ++v) {
-            FT term = hw * ((sgf * fa[v] + sgf * fb[v]) - lam * (bf[v] - af[v]));
-            if constexpr (F32) s_term[warp][lane][v] = f2d(term);
-            else s_term[warp][lane][v] = term;
+            FT term;
+            if constexpr (A2A) term = hw * (sgf * fa[v] + sgf * fb[v]) - fabs(hw) * lam * (bf[v] - af[v]);
+            else term = hw * ((sgf * fa[v] + sgf * fb[v]) - lam * (bf[v] - af[v]));
+            if constexpr (F32) s_term[warp][pp][v] = f2d(term);
+            else s_term[warp][pp][v] = term;
         }
-        s_rb[warp][lane] = 0.5 * (a[0] + b[0]) - sg * (b[1 + dir] - a[1 + dir]) * i2l;
+        s_rb[warp][pp] = 0.5 * (a[0] + b[0]) - sgw * (b[1 + dir] - a[1 + dir]) * i2l;
         if (ent) {
-            if constexpr (F32) s_sb[warp][lane] = bar_entropy<float>(g, af, fa, bf, fb, low ? i2l_f : -i2l_f);
-            else s_sb[warp][lane] = bar_entropy<double>(g, a, fa, b, fb, low ? i2l : -i2l);
+            const bool pos = sgw > 0.0;
+            if constexpr (F32) s_sb[warp][pp] = bar_entropy<float>(g, af, fa, bf, fb, pos ? i2l_f : -i2l_f);
+            else s_sb[warp][pp] = bar_entropy<double>(g, a, fa, b, fb, pos ? i2l : -i2l);
         }
         FT wtf;
-        if constexpr (F32) wtf = d2f(wt);
-        else wtf = wt;
-        s_d2[warp][lane] = wtf * lam;
+        if constexpr (F32) wtf = d2f(fabs(wt));
+        else wtf = fabs(wt);
+        s_d2[warp][pp] = wtf * lam;
     }
     __syncwarp();
     // admissibility of the interpolated states; LLF on the small faces

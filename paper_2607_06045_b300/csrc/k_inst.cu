@@ -75,10 +75,16 @@ void element(int fp32, int ext, int epb, int grid, cudaStream_t st, const MeshDe
     IDP_EPB_SWITCH(el_launch, grid, st, m, s, a)
 }
 
-void mortar_flux(int fp32, int ent, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
-                 const Gas &gas, const Ops *ops) {
-    if (fp32) k_mortar_flux<NP, float><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gas, ops, ent);
-    else k_mortar_flux<NP, double><<<grid, 32 * MORTARS_PER_BLOCK, 0, st>>>(m, s, u, gas, ops, ent);
+void mortar_flux(int fp32, int ent, int a2a, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
+                 const double *u, const Gas &gas, const Ops *ops) {
+    constexpr int T = 32 * MORTARS_PER_BLOCK;
+    if (a2a) {
+        if (fp32) k_mortar_flux<NP, float, true><<<grid, T, 0, st>>>(m, s, u, gas, ops, ent);
+        else k_mortar_flux<NP, double, true><<<grid, T, 0, st>>>(m, s, u, gas, ops, ent);
+    } else {
+        if (fp32) k_mortar_flux<NP, float, false><<<grid, T, 0, st>>>(m, s, u, gas, ops, ent);
+        else k_mortar_flux<NP, double, false><<<grid, T, 0, st>>>(m, s, u, gas, ops, ent);
+    }
 }
 
 void mortar_lob(cudaStream_t st, const MeshDev &m, const SlotsDev &s, const Ops *ops, const double *lofv, int ent,

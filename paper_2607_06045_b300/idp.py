@@ -33,7 +33,7 @@ class Options(C.Structure):
     _fields_ = [("precision", C.c_int32), ("limiting", C.c_int32), ("bounds", C.c_int32), ("dt_rule", C.c_int32),
                 ("beta", C.c_double), ("cfl", C.c_double), ("mortar_projection", C.c_int32),
                 ("elems_per_block", C.c_int32), ("collect_stats", C.c_int32), ("grid_mode", C.c_int32),
-                ("entropy_bound", C.c_int32), ("volume_flux", C.c_int32)]
+                ("entropy_bound", C.c_int32), ("volume_flux", C.c_int32), ("mortar_low", C.c_int32)]
 
 
 class LimiterStats(C.Structure):

@@ -91,6 +91,7 @@ def test_rejects_bad_arguments():
     assert _create(m, bounds=-1) == idp.IDP_E_ARG
     assert _create(m, entropy_bound=2) == idp.IDP_E_ARG
     assert _create(m, volume_flux=2) == idp.IDP_E_ARG
+    assert _create(m, mortar_low=2) == idp.IDP_E_ARG
     mj = W.uniform_mesh(2, 2, bc=(6, 6, W.BC_PERIODIC, W.BC_PERIODIC))
     assert _create(mj) == idp.IDP_E_ARG
     mb = W.uniform_mesh(2, 2, bc=(W.BC_PERIODIC, W.BC_WALL, W.BC_PERIODIC, W.BC_PERIODIC))
