@@ -321,7 +321,8 @@ def run_ours(args):
     vsteps = max(3, args.steps // 4)
     for name, kw in (("combined", dict(limiting=3)), ("entropy_bound", dict(limiting=2, entropy_bound=1)),
                      ("low_order_bounds", dict(limiting=2, bounds=1)),
-                     ("low_order_bounds_entropy", dict(limiting=2, bounds=1, entropy_bound=1))):
+                     ("low_order_bounds_entropy", dict(limiting=2, bounds=1, entropy_bound=1)),
+                     ("all_to_all_mortar", dict(limiting=2, mortar_low=1))):
         vctx = idp.Context(meshes[0], 3, precision=0, cfl=0.5, **kw)
         u_dev = torch.from_numpy(u0).cuda()
         barrier_sync()
