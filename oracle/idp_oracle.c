@@ -54,7 +54,11 @@
  *   R23 Chandrashekar's volume flux (the paper's astrophysical jet);
  *   R24 the jet's boundary: inflow band |y| <= 0.05 on the -x side, the
  *      ambient state elsewhere on the x sides;
- *   R25 all-to-all mortar weights by the LGL quadrature of the small face.
+ *   R25 all-to-all mortar weights by the LGL quadrature of the small face;
+ *   R26 AMR transfer: interpolation (refinement), exact L2 projection
+ *      (coarsening), Zhang-Shu scaling toward the parent's mean with one
+ *      factor per family;
+ *   R27 Loehner-type second-difference indicator.
  * Every bound interval is widened to contain the low-order value, which in
  * exact arithmetic it already does (Eq. convex_combination).
  */
@@ -1545,4 +1549,123 @@ void orc_mortar_sparse(int N, double g, const double *uL, const double *us, doub
                 Flo[4 * (np + q) + v] += 0.5 * ww * (-(fi[v] + fj[v]) - lam * (uL[4 * k + v] - us[4 * q + v]));
             }
         }
+}
+
+/* ------------------------------------------------------------------------ */
+/* adaptive mesh refinement: indicators, solution transfer (Sec. 2.4,       */
+/* Sec. 3); the adaptation plan itself is in oracle/amr.py                  */
+/* ------------------------------------------------------------------------ */
+
+/* R27: Loehner-type second-difference indicator of nodal values v[j][i] of
+   one element: the largest, over every row and column and every three
+   consecutive nodes (a, b, c), of
+   |a - 2b + c| / (|c - b| + |b - a| + f (|a| + 2|b| + |c|)), f the noise
+   filter (0 if the denominator is 0). */
+double orc_lohner(int N, double f, const double *v) {
+    int np = N + 1;
+    double best = 0.0;
+    if (np < 3) return 0.0;
+    for (int d = 0; d < 2; ++d)
+        for (int r = 0; r < np; ++r)
+            for (int k = 1; k < np - 1; ++k) {
+                double a, b, c;
+                if (d == 0) { a = v[r * np + k - 1]; b = v[r * np + k]; c = v[r * np + k + 1]; }
+                else { a = v[(k - 1) * np + r]; b = v[k * np + r]; c = v[(k + 1) * np + r]; }
+                double num = fabs(a - 2.0 * b + c);
+                double den = fabs(c - b) + fabs(b - a) + f * (fabs(a) + 2.0 * fabs(b) + fabs(c));
+                double q = den > 0.0 ? num / den : 0.0;
+                if (q > best) best = q;
+            }
+    return best;
+}
+
+/* R26: refinement by interpolation. parent[4][np][np] (variable, j, i) ->
+   children[4 children][4][np][np], child c = cx + 2 cy covering
+   [cx - 1, cx] x [cy - 1, cy] of the parent's reference square halves:
+   u_c(x_i, y_j) = sum_kl phi_k(s_i) phi_l(t_j) u_p(x_k, y_l). */
+void orc_refine(int N, const double *parent, double *children) {
+    int np = N + 1, nn = np * np;
+    double xi[NPMAX], w[NPMAX], D[NPMAX * NPMAX], S[NPMAX * NPMAX], wt[NPMAX * 2 * NPMAX], I[2 * NPMAX * NPMAX],
+        P[NPMAX * 2 * NPMAX];
+    orc_operators(N, 1, xi, w, D, S, wt, I, P);
+    for (int c = 0; c < 4; ++c) {
+        int cx = c & 1, cy = c >> 1;
+        for (int v = 0; v < 4; ++v)
+            for (int j = 0; j < np; ++j)
+                for (int i = 0; i < np; ++i) {
+                    double acc = 0.0;
+                    for (int l = 0; l < np; ++l)
+                        for (int k = 0; k < np; ++k)
+                            acc += I[(cx * np + i) * np + k] * I[(cy * np + j) * np + l] * parent[(v * np + l) * np + k];
+                    children[((c * 4 + v) * np + j) * np + i] = acc;
+                }
+    }
+    (void)nn;
+}
+
+/* R26: coarsening by the exact L2 projection of the four children onto the
+   parent's polynomials (tensor product of the 1D projections of R5). */
+void orc_coarsen(int N, const double *children, double *parent) {
+    int np = N + 1;
+    double xi[NPMAX], w[NPMAX], D[NPMAX * NPMAX], S[NPMAX * NPMAX], wt[NPMAX * 2 * NPMAX], I[2 * NPMAX * NPMAX],
+        P[NPMAX * 2 * NPMAX];
+    orc_operators(N, 1, xi, w, D, S, wt, I, P);
+    for (int v = 0; v < 4; ++v)
+        for (int l = 0; l < np; ++l)
+            for (int k = 0; k < np; ++k) {
+                double acc = 0.0;
+                for (int c = 0; c < 4; ++c) {
+                    int cx = c & 1, cy = c >> 1;
+                    for (int j = 0; j < np; ++j)
+                        for (int i = 0; i < np; ++i)
+                            acc += P[k * 2 * np + cx * np + i] * P[l * 2 * np + cy * np + j] *
+                                   children[((c * 4 + v) * np + j) * np + i];
+                }
+                parent[(v * np + l) * np + k] = acc;
+            }
+}
+
+/* R26: Zhang-Shu scaling of n_el elements' nodal states e[n_el][4][np][np]
+   toward the reference state ref[4] (the mean of the parent before
+   refinement, or of the coarsened parent): if some node has rho < eps or
+   p < eps, theta_rho = min over such nodes of (rho_ref - eps) / (rho_ref -
+   rho_i) scales every node, then theta_p, the smallest over the scaled
+   nodes of the largest theta in [0, 1] with p(ref + theta (u_i - ref)) >=
+   eps (the quadratic of R8 with pmin = eps). One common factor per call
+   keeps the sum of the elements' masses. Returns the product of the two
+   factors (1 when nothing was scaled). A reference state that is itself
+   not admissible is left alone (returns -1). */
+double orc_zhang_shu(int N, double g, int n_el, double *e, const double *ref, double eps) {
+    int np = N + 1, nn = np * np;
+    double pref = (g - 1.0) * (ref[3] - 0.5 * (ref[1] * ref[1] + ref[2] * ref[2]) / ref[0]);
+    if (!(ref[0] > eps) || !(pref > eps)) return -1.0;
+    double th1 = 1.0;
+    for (int q = 0; q < n_el; ++q)
+        for (int n = 0; n < nn; ++n) {
+            double r = e[(size_t)(q * 4 + 0) * nn + n];
+            if (r < eps) { double t = (ref[0] - eps) / (ref[0] - r); if (t < th1) th1 = t; }
+        }
+    if (th1 < 1.0)
+        for (int q = 0; q < n_el; ++q)
+            for (int v = 0; v < 4; ++v)
+                for (int n = 0; n < nn; ++n) {
+                    double *x = &e[(size_t)(q * 4 + v) * nn + n];
+                    *x = ref[v] + th1 * (*x - ref[v]);
+                }
+    double th2 = 1.0;
+    for (int q = 0; q < n_el; ++q)
+        for (int n = 0; n < nn; ++n) {
+            double a[4], u0[4];
+            for (int v = 0; v < 4; ++v) { u0[v] = ref[v]; a[v] = e[(size_t)(q * 4 + v) * nn + n] - ref[v]; }
+            double t = orc_theta(g, u0, a, eps, 1.0);
+            if (t < th2) th2 = t;
+        }
+    if (th2 < 1.0)
+        for (int q = 0; q < n_el; ++q)
+            for (int v = 0; v < 4; ++v)
+                for (int n = 0; n < nn; ++n) {
+                    double *x = &e[(size_t)(q * 4 + v) * nn + n];
+                    *x = ref[v] + th2 * (*x - ref[v]);
+                }
+    return th1 * th2;
 }

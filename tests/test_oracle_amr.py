@@ -1,0 +1,225 @@
+"""Pins of the oracle's adaptive-mesh-refinement step (Sec. 2.4; readings
+R26-R28):
+
+- the Loehner-type indicator's closed forms (0 on linear and constant data,
+  2 / (2 + 2 f) on a single spike);
+- refinement reproduces every polynomial of degree <= N at the children's
+  nodes (evaluated here with numpy), coarsening after refinement is the
+  identity, and coarsening is the L2 projection: the residual is orthogonal
+  to every parent basis function under a fine Gauss quadrature formed here;
+- the Zhang-Shu scaling leaves admissible data alone, makes the rest
+  admissible with the largest common factor, and keeps the family's mass;
+- the plan on hand-made cases (refinement, coarsening of complete families
+  only, balance propagation across a face and across a periodic boundary)
+  and a balanced result on a random indicator;
+- the transfer conserves mass and momentum on the whole mesh.
+"""
+import numpy as np
+import pytest
+from numpy.polynomial import legendre as Lg
+
+import oracle
+from oracle import amr
+from paper_2607_06045_b300 import workloads as W
+
+G = 1.4
+
+
+def lagrange_matrix(xs, x):
+    """[len(x)][len(xs)] Lagrange basis of nodes xs at points x."""
+    out = np.ones((len(x), len(xs)))
+    for k in range(len(xs)):
+        for m in range(len(xs)):
+            if m != k:
+                out[:, k] *= (x - xs[m]) / (xs[k] - xs[m])
+    return out
+
+
+def test_lohner_closed_forms():
+    L = amr._setup()
+    N = 3
+    X, Y = np.meshgrid(np.linspace(-1, 1, 4), np.linspace(-1, 1, 4))
+    # values linear in the node index along every line, and constant values
+    for v in (2.0 + 3.0 * X - Y, np.full((4, 4), 5.0)):
+        assert L.orc_lohner(N, 0.2, oracle._d(np.ascontiguousarray(v))) <= 1e-15
+    v = np.zeros((4, 4))
+    v[1, 1] = 1.0
+    f = 0.2
+    assert abs(L.orc_lohner(N, f, oracle._d(v)) - 2.0 / (2.0 + 2.0 * f)) < 1e-15
+
+
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_refine_reproduces_polynomials_and_coarsen_inverts(N):
+    L = amr._setup()
+    xi, w = oracle.lgl(N)
+    rng = np.random.default_rng(N)
+    np_ = N + 1
+    c = rng.normal(size=(4, np_, np_))   # coefficients of x^a y^b, a, b <= N
+
+    def poly(v, x, y):
+        return sum(c[v, b, a] * x ** a * y ** b for a in range(np_) for b in range(np_))
+    X, Y = np.meshgrid(xi, xi)            # [j][i]
+    parent = np.ascontiguousarray(np.stack([poly(v, X, Y) for v in range(4)]))
+    ch = np.zeros((4, 4, np_, np_))
+    L.orc_refine(N, oracle._d(parent), oracle._d(ch))
+    for cc in range(4):
+        cx, cy = cc & 1, cc >> 1
+        Xs, Ys = (X + (2 * cx - 1)) / 2.0, (Y + (2 * cy - 1)) / 2.0
+        for v in range(4):
+            np.testing.assert_allclose(ch[cc, v], poly(v, Xs, Ys), rtol=1e-11, atol=1e-11)
+    back = np.zeros((4, np_, np_))
+    L.orc_coarsen(N, oracle._d(ch), oracle._d(back))
+    np.testing.assert_allclose(back, parent, rtol=1e-12, atol=1e-12)
+
+
+@pytest.mark.parametrize("N", [2, 4])
+def test_coarsen_is_the_l2_projection(N):
+    L = amr._setup()
+    xi, w = oracle.lgl(N)
+    np_ = N + 1
+    rng = np.random.default_rng(7)
+    ch = np.ascontiguousarray(rng.normal(size=(4, 4, np_, np_)))
+    par = np.zeros((4, np_, np_))
+    L.orc_coarsen(N, oracle._d(ch), oracle._d(par))
+    # fine Gauss quadrature on each child, mapped into the parent square
+    g, gw = Lg.leggauss(2 * N + 4)
+    for v in range(4):
+        res = np.zeros((np_, np_))
+        for cc in range(4):
+            cx, cy = cc & 1, cc >> 1
+            xs, ys = (g + (2 * cx - 1)) / 2.0, (g + (2 * cy - 1)) / 2.0
+            Pc = lagrange_matrix(xi, g)                 # child basis at child-local points
+            Px, Py = lagrange_matrix(xi, xs), lagrange_matrix(xi, ys)   # parent basis
+            uc = Pc @ ch[cc, v].T @ Pc.T                # u_c at (x_g, y_h): [g][h]
+            up = Px @ par[v].T @ Py.T
+            diff = (uc - up) * np.outer(gw, gw) / 4.0
+            res += Px.T @ diff @ Py                     # [k][l] against phi_k(x) phi_l(y)
+        assert np.abs(res).max() < 1e-12
+
+
+def test_zhang_shu():
+    L = amr._setup()
+    N = 3
+    np_ = N + 1
+    rng = np.random.default_rng(11)
+    eps = 1e-10
+    ref = np.array([1.0, 0.2, -0.1, 2.5])
+    e = np.ascontiguousarray(np.broadcast_to(ref[None, :, None, None], (4, 4, np_, np_)).copy()
+                             + 0.05 * rng.normal(size=(4, 4, np_, np_)))
+    e0 = e.copy()
+    assert L.orc_zhang_shu(N, G, 4, oracle._d(e), oracle._d(ref), eps) == 1.0
+    assert np.array_equal(e, e0)
+    # negative density and pressure at a few nodes
+    e[1, 0, 2, 1] = -0.3
+    e[2, 3, 0, 0] = 0.01
+    e0 = e.copy()
+    th = L.orc_zhang_shu(N, G, 4, oracle._d(e), oracle._d(ref), eps)
+    assert 0.0 < th < 1.0
+    rho = e[:, 0]
+    p = (G - 1) * (e[:, 3] - 0.5 * (e[:, 1] ** 2 + e[:, 2] ** 2) / e[:, 0])
+    assert rho.min() >= eps * (1 - 1e-12) and p.min() >= eps * (1 - 1e-12)
+    # the result is ref + th (e0 - ref): the family's mean moves toward ref only
+    np.testing.assert_allclose(e, ref[None, :, None, None] + th * (e0 - ref[None, :, None, None]), atol=1e-13)
+    # the factor is maximal: a slightly larger one leaves a node below eps
+    t2 = th * (1 + 1e-6)
+    e2 = ref[None, :, None, None] + t2 * (e0 - ref[None, :, None, None])
+    p2 = (G - 1) * (e2[:, 3] - 0.5 * (e2[:, 1] ** 2 + e2[:, 2] ** 2) / e2[:, 0])
+    assert e2[:, 0].min() < eps or p2.min() < eps
+
+
+def _p(**kw):
+    return amr.Params(**kw)
+
+
+def test_plan_refine_and_coarsen():
+    m = W.uniform_mesh(4, 4, level=1)          # 8 x 8 leaves at level 1
+    K = m.n_elems
+    ind = np.full(K, 0.2)
+    e_ref = 9
+    ind[e_ref] = 0.9                            # refine
+    # a complete family marked for coarsening: the children of the level-0 cell (3, 3)
+    fam = [k for k in range(K) if m.ix[k] >> 1 == 3 and m.iy[k] >> 1 == 3]
+    ind[fam] = 0.0
+    # an incomplete one: three of the four children of (0, 3)
+    fam2 = [k for k in range(K) if m.ix[k] >> 1 == 0 and m.iy[k] >> 1 == 3][:3]
+    ind[fam2] = 0.0
+    l, x, y, kind, src = amr.plan(m, ind, _p(refine_threshold=0.5, coarsen_threshold=0.1, min_level=0,
+                                               max_level=2))
+    assert (kind == 1).sum() == 4 and (kind == 2).sum() == 1
+    assert len(kind) == K + 3 - 3
+    ch = np.where(kind == 1)[0]
+    assert (src[ch, 0] == e_ref).all() and list(src[ch, 1]) == [0, 1, 2, 3]
+    assert list(l[ch]) == [2] * 4
+    pa = np.where(kind == 2)[0][0]
+    assert l[pa] == 0 and (x[pa], y[pa]) == (3, 3) and sorted(src[pa]) == sorted(fam)
+    mesh2 = W.Mesh(nx0=4, ny0=4, box=m.box, level=l, ix=x, iy=y, bc=m.bc)
+    assert W.check_balanced(mesh2)
+    oracle.Oracle(mesh2, 2)   # a valid quadtree
+
+
+@pytest.mark.parametrize("periodic", [False, True])
+def test_plan_balance_propagates(periodic):
+    bc = (W.BC_PERIODIC,) * 4 if periodic else (W.BC_OUTFLOW,) * 4
+    m = W.box_refined_mesh(4, 4, (0.0, 0.0, 1.0, 1.0), (0.0, 0.0, 0.25, 1.0), bc=bc)   # x < 0.25 at level 1
+    K = m.n_elems
+    ind = np.zeros(K) + 0.2
+    # refine the level-1 leaves at the left edge: their level-1 neighbours to
+    # the right stay (difference 1); nothing at level 0 touches them
+    left = [k for k in range(K) if m.level[k] == 1 and m.ix[k] == 0]
+    ind[left] = 0.9
+    l, x, y, kind, src = amr.plan(m, ind, _p(refine_threshold=0.5, coarsen_threshold=0.1, max_level=3))
+    mesh2 = W.Mesh(nx0=4, ny0=4, box=m.box, level=l, ix=x, iy=y, bc=m.bc)
+    assert W.check_balanced(mesh2)
+    # periodic: the level-0 leaves at the right edge touch level-2 leaves
+    # across the boundary and must be refined; otherwise they stay
+    right = [k for k in range(K) if m.level[k] == 0 and m.ix[k] == 3]
+    refined = set(src[kind == 1, 0].tolist())
+    assert set(right) <= refined if periodic else not (set(right) & refined)
+
+
+def test_plan_random_is_balanced_and_transfer_conserves():
+    m = W.cfg1_mesh()
+    N = 3
+    u = W.cfg1_state(m, N)
+    rng = np.random.default_rng(5)
+    # one random value per level-0 cell, so that whole families can coarsen
+    cell = rng.uniform(0, 1, (m.nx0, m.ny0))
+    ind = np.array([cell[x >> l, y >> l] for l, x, y in zip(m.level.tolist(), m.ix.tolist(), m.iy.tolist())])
+    pl = amr.plan(m, ind, _p(refine_threshold=0.8, coarsen_threshold=0.5, min_level=0, max_level=2))
+    l, x, y, kind, src = pl
+    assert (kind == 1).any() and (kind == 2).any()
+    mesh2 = W.Mesh(nx0=m.nx0, ny0=m.ny0, box=m.box, level=l, ix=x, iy=y, bc=m.bc)
+    assert W.check_balanced(mesh2)
+    un, scaled = amr.transfer(u, N, pl, G)
+    o1, o2 = oracle.Oracle(m, N), oracle.Oracle(mesh2, N)
+    I1, I2 = o1.integrals(u), o2.integrals(un)
+    assert np.abs(I1 - I2).max() <= 1e-13 * np.abs(I1).max()
+    # the projection of the disc's pressure jump undershoots to p < 0 in two
+    # coarsened parents, which the Zhang-Shu scaling repairs
+    assert scaled == 2
+    pn = (G - 1) * (un[3] - 0.5 * (un[1] ** 2 + un[2] ** 2) / un[0])
+    assert un[0].min() > 0 and pn.min() >= 1e-10 * (1 - 1e-12)
+
+
+def test_transfer_near_vacuum_is_fixed():
+    m = W.uniform_mesh(4, 4, level=1, bc=(W.BC_OUTFLOW,) * 4)
+    N = 4
+    # a steep near-vacuum profile whose interpolation undershoots
+    X, Y = W.node_coords(m, N)
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    rho = np.where(r < 0.2, 1.0, 1e-9)
+    p = np.where(r < 0.2, 1.0, 1e-9)
+    u = W.conserved(rho, 0.0 * X, 0.0 * X, p, G)
+    ind = np.ones(m.n_elems)
+    pl = amr.plan(m, ind, _p(refine_threshold=0.5, max_level=2))
+    un, scaled = amr.transfer(u, N, pl, G, eps=1e-10)
+    assert scaled > 0
+    l, x, y, kind, src = pl
+    mesh2 = W.Mesh(nx0=4, ny0=4, box=m.box, level=l, ix=x, iy=y, bc=m.bc)
+    assert un[0].min() >= 1e-10 * (1 - 1e-12)
+    # the pressure near 1e-10 is a small difference of the energies: compare
+    # within the rounding of that difference
+    pn = (G - 1) * (un[3] - 0.5 * (un[1] ** 2 + un[2] ** 2) / un[0])
+    assert pn.min() >= 1e-10 * (1 - 1e-4)
+    I1, I2 = oracle.Oracle(m, N).integrals(u), oracle.Oracle(mesh2, N).integrals(un)
+    assert abs(I1[0] - I2[0]) <= 1e-13 * I1[0] and abs(I1[3] - I2[3]) <= 1e-13 * I1[3]
