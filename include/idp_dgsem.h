@@ -302,6 +302,79 @@ idp_status idp_integrals_noalloc(const double *u, const double *elem_area, int64
                                  const int64_t *sim_elem_offsets, int32_t n_sims, double *out,
                                  void *stream);
 
+/* ---- adaptive mesh refinement (Sec. 2.4 and the adaptive runs of Sec. 3) --
+ * One adaptation step is: element indicators on the device
+ * (idp_dgsem_amr_indicator), the new leaf set on the host (idp_amr_plan),
+ * the solution transfer on the device (idp_amr_transfer), then a context for
+ * the new mesh (idp_dgsem_create). */
+
+/* Indicator kinds and the variable they look at. */
+enum { IDP_AMR_HENNEMANN = 0, IDP_AMR_LOHNER = 1, IDP_AMR_MAX = 2 };
+enum { IDP_AMR_DENSITY = 0, IDP_AMR_PRESSURE = 1 };
+
+/* indicator         IDP_AMR_HENNEMANN: Hennemann et al.'s modal energy
+ *                   indicator in [0, 1] (as for the combined limiting);
+ *                   IDP_AMR_LOHNER: the largest second-difference ratio
+ *                   |a - 2b + c| / (|c - b| + |b - a| + f (|a| + 2|b| + |c|))
+ *                   over consecutive nodes (a, b, c) of every row and column
+ *                   (a Loehner-type estimator, f = lohner_filter);
+ *                   IDP_AMR_MAX: the larger of the two.
+ * variable          IDP_AMR_DENSITY or IDP_AMR_PRESSURE.
+ * refine_threshold  a leaf whose indicator exceeds it is refined one level
+ *                   (up to max_level);
+ * coarsen_threshold four sibling leaves whose indicators are all below it are
+ *                   coarsened one level (down to min_level);
+ * zs_threshold      the transfer's positivity threshold for density and
+ *                   pressure (Zhang-Shu scaling; the paper uses 1e-10). */
+typedef struct {
+    int32_t indicator;
+    int32_t variable;
+    double refine_threshold;
+    double coarsen_threshold;
+    int32_t min_level, max_level;
+    double lohner_filter;
+    double zs_threshold;
+} idp_amr_params;
+
+/* Fills p with the defaults: Hennemann on density, refine above 0.5, coarsen
+ * below 0.05, levels 0..3, filter 0.2, threshold 1e-10. */
+idp_status idp_amr_params_default(idp_amr_params *p);
+
+/* ind[e] = the indicator of element e of u (device arrays: u in the layout
+ * above, ind of n_elems doubles). Asynchronous on `stream`. IDP_E_ARG for
+ * null pointers or parameters out of range. */
+idp_status idp_dgsem_amr_indicator(idp_ctx *ctx, const double *u, const idp_amr_params *p, double *ind,
+                                   void *stream);
+
+/* The adapted leaf set of one mesh (host function, no GPU): from the mesh
+ * and its elements' indicators (host array, mesh order) one level of
+ * refinement or coarsening per leaf; coarsening needs all four siblings to
+ * be leaves marked for it; then 2:1 face balance, refinement winning (a
+ * coarser face neighbour two levels apart gives up its coarsening or is
+ * refined). New leaves follow the old order: a refined leaf becomes its four
+ * children c = cx + 2 cy in place, a coarsened family its parent at its
+ * first member's place. Outputs (caller-owned host arrays of `capacity`
+ * entries; 4 * n_leaves always suffices): n_new, level/ix/iy of the new
+ * leaves, kind (0 copy, 1 child, 2 coarsened parent) and src[4] per new
+ * leaf (copy: the old leaf; child: the old parent and the child position;
+ * parent: the four old children in child order; unused entries -1).
+ * IDP_E_ARG for bad arguments or a capacity too small, IDP_E_MESH for an
+ * invalid or unbalanced input mesh. */
+idp_status idp_amr_plan(const idp_mesh_desc *mesh, const double *ind, const idp_amr_params *p, int32_t capacity,
+                        int32_t *n_new, int8_t *level, int32_t *ix, int32_t *iy, int32_t *kind, int32_t *src);
+
+/* The solution on the adapted mesh (device): u_new (n_new elements) from
+ * u_old (n_old elements) of degree N by the plan's kind/src (HOST arrays,
+ * copied): copies, children by interpolation of the parent, parents by the
+ * exact L2 projection of the four children; then every refined family is
+ * scaled toward its parent's mean and every coarsened parent toward its own
+ * mean, with one factor per family, until density and pressure reach
+ * zs_threshold (Zhang-Shu). *n_scaled (host, may be NULL) receives the
+ * number of scaled families. Synchronises `stream`. */
+idp_status idp_amr_transfer(int32_t N, double gamma, const double *u_old, int64_t n_old, double *u_new, int64_t n_new,
+                            const int32_t *kind, const int32_t *src, double zs_threshold, int64_t *n_scaled,
+                            void *stream);
+
 /* Synchronise the stream and report any device-flagged condition. */
 idp_status idp_dgsem_sync(idp_ctx *ctx, void *stream);
 

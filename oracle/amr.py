@@ -145,7 +145,8 @@ def plan(mesh, ind, params: Params):
                     if lev[f] + mark[f] - fe >= 2:
                         if mark[e] == -1:
                             for m in family(e):
-                                mark[m] = 0
+                                if m >= 0:
+                                    mark[m] = 0
                         else:
                             mark[e] = 1
                         fe = lev[e] + mark[e]
@@ -202,7 +203,7 @@ def transfer(u, N, pl, gamma=1.4, eps=1e-10):
             fam = np.ascontiguousarray(ch)
             ref = np.ascontiguousarray(element_mean(parent))
             th = L.orc_zhang_shu(N, gamma, 4, _d(fam), _d(ref), eps)
-            scaled += th < 1.0
+            scaled += 0.0 <= th < 1.0
             for c in range(4):
                 un[:, e + c] = fam[c]
             e += 4
@@ -213,7 +214,7 @@ def transfer(u, N, pl, gamma=1.4, eps=1e-10):
             ref = np.ascontiguousarray(element_mean(par))
             par = np.ascontiguousarray(par)
             th = L.orc_zhang_shu(N, gamma, 1, _d(par), _d(ref), eps)
-            scaled += th < 1.0
+            scaled += 0.0 <= th < 1.0
             un[:, e] = par
             e += 1
     return un, scaled

@@ -1151,6 +1151,216 @@ idp_status idp_dgsem_sync(idp_ctx *c, void *stream) {
     return read_status(c);
 }
 
+// ---- adaptive mesh refinement -------------------------------------------
+
+idp_status idp_amr_params_default(idp_amr_params *p) {
+    if (!p) return IDP_E_ARG;
+    std::memset(p, 0, sizeof(*p));
+    p->indicator = IDP_AMR_HENNEMANN;
+    p->variable = IDP_AMR_DENSITY;
+    p->refine_threshold = 0.5;
+    p->coarsen_threshold = 0.05;
+    p->min_level = 0;
+    p->max_level = 3;
+    p->lohner_filter = 0.2;
+    p->zs_threshold = 1e-10;
+    return IDP_OK;
+}
+
+static bool amr_params_ok(const idp_amr_params *p) {
+    return p && p->indicator >= IDP_AMR_HENNEMANN && p->indicator <= IDP_AMR_MAX && p->variable >= 0 &&
+           p->variable <= 1 && p->min_level >= 0 && p->max_level >= p->min_level && p->max_level <= 24 &&
+           p->lohner_filter >= 0.0 && p->zs_threshold >= 0.0;
+}
+
+idp_status idp_dgsem_amr_indicator(idp_ctx *c, const double *u, const idp_amr_params *p, double *ind, void *stream) {
+    if (!c || !u || !ind || !amr_params_ok(p)) return IDP_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    c->L.amr_indicator(st, u, (int)c->K, c->d_ops, c->gamma - 1.0, p->indicator, p->variable, p->lohner_filter, ind,
+                       c->num_sms);
+    return check_cuda(cudaGetLastError());
+}
+
+// The adaptation plan (host): marks, complete families for coarsening, 2:1
+// face balance with refinement winning, new leaves in the old order.
+idp_status idp_amr_plan(const idp_mesh_desc *mesh, const double *ind, const idp_amr_params *p, int32_t capacity,
+                        int32_t *n_new, int8_t *level, int32_t *ix, int32_t *iy, int32_t *kind, int32_t *src) {
+    if (!mesh || !ind || !amr_params_ok(p) || !n_new || !level || !ix || !iy || !kind || !src || capacity < 0)
+        return IDP_E_ARG;
+    {   // the input must be a valid balanced quadtree
+        HostMesh H;
+        idp_status r = build_mesh(*mesh, 1.4, 0, H);
+        if (r != IDP_OK) return r;
+    }
+    const idp_mesh_desc &d = *mesh;
+    const int K = d.n_leaves;
+    std::unordered_map<uint64_t, int> key;
+    key.reserve((size_t)K * 2);
+    for (int e = 0; e < K; ++e) key.emplace(leaf_key(d.level[e], d.ix[e], d.iy[e]), e);
+    auto find = [&](int l, int64_t x, int64_t y) {
+        if (l < 0) return -1;
+        auto it = key.find(leaf_key(l, x, y));
+        return it == key.end() ? -1 : it->second;
+    };
+    std::vector<int> mark(K, 0);
+    for (int e = 0; e < K; ++e) {
+        if (ind[e] > p->refine_threshold && d.level[e] < p->max_level) mark[e] = 1;
+        else if (ind[e] < p->coarsen_threshold && d.level[e] > p->min_level) mark[e] = -1;
+    }
+    auto family = [&](int e, int f[4]) {
+        const int l = d.level[e];
+        const int64_t px = d.ix[e] >> 1, py = d.iy[e] >> 1;
+        for (int c = 0; c < 4; ++c) f[c] = find(l, 2 * px + (c & 1), 2 * py + (c >> 1));
+    };
+    for (int e = 0; e < K; ++e) {
+        if (mark[e] != -1) continue;
+        int f[4];
+        family(e, f);
+        bool ok = true;
+        for (int c = 0; c < 4; ++c) ok = ok && f[c] >= 0 && mark[f[c]] == -1;
+        if (!ok)
+            for (int c = 0; c < 4; ++c)
+                if (f[c] >= 0 && mark[f[c]] == -1) mark[f[c]] = 0;
+    }
+    const bool perx = d.bc[0] == IDP_BC_PERIODIC, pery = d.bc[2] == IDP_BC_PERIODIC;
+    auto neighbours = [&](int e, int s, int out[2]) {
+        const int l = d.level[e];
+        const int64_t nx = (int64_t)d.nx0 << l, ny = (int64_t)d.ny0 << l;
+        int64_t qx = d.ix[e] + (s == 0 ? -1 : (s == 1 ? 1 : 0));
+        int64_t qy = d.iy[e] + (s == 2 ? -1 : (s == 3 ? 1 : 0));
+        if (qx < 0 || qx >= nx) { if (!perx) return 0; qx = (qx + nx) % nx; }
+        if (qy < 0 || qy >= ny) { if (!pery) return 0; qy = (qy + ny) % ny; }
+        int f = find(l, qx, qy);
+        if (f >= 0) { out[0] = f; return 1; }
+        f = find(l - 1, qx >> 1, qy >> 1);
+        if (l > 0 && f >= 0) { out[0] = f; return 1; }
+        if (s < 2) {
+            const int cx = s == 0 ? 1 : 0;
+            out[0] = find(l + 1, 2 * qx + cx, 2 * qy);
+            out[1] = find(l + 1, 2 * qx + cx, 2 * qy + 1);
+        } else {
+            const int cy = s == 2 ? 1 : 0;
+            out[0] = find(l + 1, 2 * qx, 2 * qy + cy);
+            out[1] = find(l + 1, 2 * qx + 1, 2 * qy + cy);
+        }
+        return 2;
+    };
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (int e = 0; e < K; ++e) {
+            int fe = d.level[e] + mark[e];
+            for (int s = 0; s < 4; ++s) {
+                int nb[2];
+                const int cnt = neighbours(e, s, nb);
+                for (int t = 0; t < cnt; ++t) {
+                    const int f = nb[t];
+                    if (f < 0) return IDP_E_MESH;
+                    if (d.level[f] + mark[f] - fe >= 2) {
+                        if (mark[e] == -1) {
+                            int fam[4];
+                            family(e, fam);
+                            for (int c = 0; c < 4; ++c)
+                                if (fam[c] >= 0) mark[fam[c]] = 0;
+                        } else {
+                            mark[e] = 1;
+                        }
+                        fe = d.level[e] + mark[e];
+                        changed = true;
+                    }
+                }
+            }
+        }
+    }
+    int n = 0;
+    auto emit = [&](int l, int64_t x, int64_t y, int k, int s0, int s1, int s2, int s3) {
+        if (n < capacity) {
+            level[n] = (int8_t)l; ix[n] = (int32_t)x; iy[n] = (int32_t)y; kind[n] = k;
+            src[4 * n] = s0; src[4 * n + 1] = s1; src[4 * n + 2] = s2; src[4 * n + 3] = s3;
+        }
+        ++n;
+    };
+    for (int e = 0; e < K; ++e) {
+        const int l = d.level[e];
+        const int64_t x = d.ix[e], y = d.iy[e];
+        if (mark[e] == 1) {
+            for (int c = 0; c < 4; ++c) emit(l + 1, 2 * x + (c & 1), 2 * y + (c >> 1), 1, e, c, -1, -1);
+        } else if (mark[e] == -1) {
+            int f[4];
+            family(e, f);
+            if (std::min(std::min(f[0], f[1]), std::min(f[2], f[3])) == e) emit(l - 1, x >> 1, y >> 1, 2, f[0], f[1], f[2], f[3]);
+        } else {
+            emit(l, x, y, 0, e, -1, -1, -1);
+        }
+    }
+    *n_new = n;
+    return n <= capacity ? IDP_OK : IDP_E_ARG;
+}
+
+idp_status idp_amr_transfer(int32_t N, double gamma, const double *u_old, int64_t n_old, double *u_new, int64_t n_new,
+                            const int32_t *kind, const int32_t *src, double zs_threshold, int64_t *n_scaled,
+                            void *stream) {
+    if (N < 1 || N > NPMAX - 1 || !(gamma > 1.0) || !u_old || !u_new || n_old < 1 || n_new < 1 || !kind || !src ||
+        !(zs_threshold >= 0.0) || n_old > INT32_MAX || n_new > INT32_MAX)
+        return IDP_E_ARG;
+    // families for the Zhang-Shu scaling, and an argument check of the plan
+    std::vector<int4> fam;
+    for (int64_t e = 0; e < n_new;) {
+        const int k = kind[e];
+        const int32_t *s = src + 4 * e;
+        if (k == 0) {
+            if (s[0] < 0 || s[0] >= n_old) return IDP_E_ARG;
+            ++e;
+        } else if (k == 1) {
+            if (e + 4 > n_new) return IDP_E_ARG;
+            for (int c = 0; c < 4; ++c)
+                if (kind[e + c] != 1 || src[4 * (e + c)] != s[0] || src[4 * (e + c) + 1] != c || s[0] < 0 || s[0] >= n_old)
+                    return IDP_E_ARG;
+            fam.push_back(make_int4((int)e, 4, 0, s[0]));
+            e += 4;
+        } else if (k == 2) {
+            for (int c = 0; c < 4; ++c)
+                if (s[c] < 0 || s[c] >= n_old) return IDP_E_ARG;
+            fam.push_back(make_int4((int)e, 1, 1, (int)e));
+            ++e;
+        } else {
+            return IDP_E_ARG;
+        }
+    }
+    int dev = 0, sms = 1;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return IDP_E_CUDA;
+    Ops ops;
+    build_ops(N, 1, 0, ops);
+    Launchers L = get_launchers(N + 1);
+    cudaStream_t st = (cudaStream_t)stream;
+    Ops *d_ops = nullptr;
+    int *d_kind = nullptr;
+    int4 *d_src = nullptr, *d_fam = nullptr;
+    unsigned long long *d_cnt = nullptr;
+    idp_status rc = IDP_OK;
+    std::vector<int4> src4((size_t)n_new);
+    for (int64_t e = 0; e < n_new; ++e) src4[e] = make_int4(src[4 * e], src[4 * e + 1], src[4 * e + 2], src[4 * e + 3]);
+    auto ok = [&](cudaError_t e, const char *w) { if (e != cudaSuccess && rc == IDP_OK) { note(e, w); rc = IDP_E_CUDA; } return rc == IDP_OK; };
+    if (ok(cudaMalloc(&d_ops, sizeof(Ops)), "amr alloc") && ok(cudaMalloc(&d_kind, sizeof(int) * n_new), "amr alloc") &&
+        ok(cudaMalloc(&d_src, sizeof(int4) * n_new), "amr alloc") &&
+        ok(cudaMalloc(&d_fam, sizeof(int4) * std::max<size_t>(fam.size(), 1)), "amr alloc") &&
+        ok(cudaMalloc(&d_cnt, sizeof(unsigned long long)), "amr alloc") &&
+        ok(cudaMemcpyAsync(d_ops, &ops, sizeof(Ops), cudaMemcpyHostToDevice, st), "amr copy") &&
+        ok(cudaMemcpyAsync(d_kind, kind, sizeof(int) * n_new, cudaMemcpyHostToDevice, st), "amr copy") &&
+        ok(cudaMemcpyAsync(d_src, src4.data(), sizeof(int4) * n_new, cudaMemcpyHostToDevice, st), "amr copy") &&
+        (fam.empty() || ok(cudaMemcpyAsync(d_fam, fam.data(), sizeof(int4) * fam.size(), cudaMemcpyHostToDevice, st), "amr copy")) &&
+        ok(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st), "amr copy")) {
+        L.amr_transfer(st, u_old, (int)n_old, u_new, (int)n_new, d_kind, d_src, d_ops, sms);
+        L.amr_zs(st, u_new, (int)n_new, u_old, (int)n_old, d_fam, (int)fam.size(), d_ops, gamma - 1.0, zs_threshold, d_cnt);
+        unsigned long long cnt = 0;
+        if (ok(cudaGetLastError(), "amr launch") && ok(cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st), "amr copy") &&
+            ok(cudaStreamSynchronize(st), "amr sync") && n_scaled)
+            *n_scaled = (int64_t)cnt;
+    }
+    cudaFree(d_ops); cudaFree(d_kind); cudaFree(d_src); cudaFree(d_fam); cudaFree(d_cnt);
+    return rc;
+}
+
 void idp_dgsem_destroy(idp_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);

@@ -3,6 +3,7 @@
 // host selects the table for its N at create time.
 #pragma once
 
+#include "idp_amr.cuh"
 #include "idp_mortar.cuh"
 
 namespace idp {
@@ -29,6 +30,13 @@ struct Launchers {
                const Gas &gas, int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin,
                unsigned *status);
     void (*integrals)(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part);
+    // adaptive mesh refinement (idp_amr.cuh)
+    void (*amr_indicator)(cudaStream_t st, const double *u, int K, const Ops *ops, double gm1, int kind, int var,
+                          double filt, double *ind, int num_sms);
+    void (*amr_transfer)(cudaStream_t st, const double *uo, int Ko, double *un, int Kn, const int *kind,
+                         const int4 *src, const Ops *ops, int num_sms);
+    void (*amr_zs)(cudaStream_t st, double *un, int Kn, const double *uo, int Ko, const int4 *fam, int nfam,
+                   const Ops *ops, double gm1, double eps, unsigned long long *nscaled);
 };
 
 Launchers launchers_np2();

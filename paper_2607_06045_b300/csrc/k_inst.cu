@@ -120,6 +120,25 @@ void integrals(int grid, cudaStream_t st, const MeshDev &m, const double *u, con
     k_elem_integrals<NP><<<grid, 256, 0, st>>>(m, u, ops, part);
 }
 
+void amr_indicator(cudaStream_t st, const double *u, int K, const Ops *ops, double gm1, int kind, int var, double filt,
+                   double *ind, int num_sms) {
+    const int blocks = std::max(1, std::min((K + 127) / 128, num_sms * 8));
+    k_amr_indicator<NP><<<blocks, 128, 0, st>>>(u, K, ops, gm1, kind, var, filt, ind);
+}
+
+void amr_transfer(cudaStream_t st, const double *uo, int Ko, double *un, int Kn, const int *kind, const int4 *src,
+                  const Ops *ops, int num_sms) {
+    const long long nodes = (long long)Kn * NP * NP;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((nodes + 255) / 256, (long long)num_sms * 16));
+    k_amr_transfer<NP><<<blocks, 256, 0, st>>>(uo, Ko, un, Kn, kind, src, ops);
+}
+
+void amr_zs(cudaStream_t st, double *un, int Kn, const double *uo, int Ko, const int4 *fam, int nfam, const Ops *ops,
+            double gm1, double eps, unsigned long long *nscaled) {
+    if (nfam <= 0) return;
+    k_amr_zs<NP><<<(nfam + 3) / 4, 128, 0, st>>>(un, Kn, uo, Ko, fam, nfam, ops, gm1, eps, nscaled);
+}
+
 }  // namespace
 
 Launchers IDP_CAT(launchers_np, IDP_NP)() {
@@ -135,6 +154,9 @@ Launchers IDP_CAT(launchers_np, IDP_NP)() {
     L.mortar_apply = mortar_apply;
     L.dt = dt;
     L.integrals = integrals;
+    L.amr_indicator = amr_indicator;
+    L.amr_transfer = amr_transfer;
+    L.amr_zs = amr_zs;
     return L;
 }
 

@@ -36,6 +36,12 @@ class Options(C.Structure):
                 ("entropy_bound", C.c_int32), ("volume_flux", C.c_int32), ("mortar_low", C.c_int32)]
 
 
+class AmrParams(C.Structure):
+    _fields_ = [("indicator", C.c_int32), ("variable", C.c_int32), ("refine_threshold", C.c_double),
+                ("coarsen_threshold", C.c_double), ("min_level", C.c_int32), ("max_level", C.c_int32),
+                ("lohner_filter", C.c_double), ("zs_threshold", C.c_double)]
+
+
 class LimiterStats(C.Structure):
     _fields_ = [("alpha_volume_mean", C.c_double), ("alpha_mortar_mean", C.c_double),
                 ("n_stages", C.c_int64), ("n_volume_active", C.c_int64), ("n_mortar_active", C.c_int64),
@@ -54,7 +60,8 @@ EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", 
            "idp_dgsem_limiter_stats", "idp_dgsem_sync", "idp_dgsem_destroy", "idp_status_str",
            "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_dgsem_profile_kernels",
            "idp_probe_pipes", "idp_eval_math",
-           "idp_integrals_noalloc"]
+           "idp_integrals_noalloc", "idp_amr_params_default", "idp_dgsem_amr_indicator", "idp_amr_plan",
+           "idp_amr_transfer"]
 
 
 def lib():
@@ -89,6 +96,12 @@ def lib():
         L.idp_probe_pipes.argtypes = [dp, vp]
         L.idp_eval_math.argtypes = [C.c_int32, vp, vp, C.c_int64, vp]
         L.idp_integrals_noalloc.argtypes = [vp, vp, C.c_int64, C.c_int32, vp, C.c_int32, vp, vp]
+        ip, i8p = C.POINTER(C.c_int32), C.POINTER(C.c_int8)
+        L.idp_amr_params_default.argtypes = [C.POINTER(AmrParams)]
+        L.idp_dgsem_amr_indicator.argtypes = [vp, vp, C.POINTER(AmrParams), vp, vp]
+        L.idp_amr_plan.argtypes = [C.POINTER(MeshDesc), dp, C.POINTER(AmrParams), C.c_int32, ip, i8p, ip, ip, ip, ip]
+        L.idp_amr_transfer.argtypes = [C.c_int32, C.c_double, vp, C.c_int64, vp, C.c_int64, ip, ip, C.c_double,
+                                       C.POINTER(C.c_int64), vp]
         L.idp_dgsem_destroy.restype = None
         for f in EXPORTS:
             if f not in ("idp_dgsem_destroy", "idp_status_str", "idp_last_cuda_error"):
@@ -197,6 +210,7 @@ class Context:
         self.N, self.np, self.gamma, self.opts = N, N + 1, gamma, opts
         single = not isinstance(meshes, (list, tuple))
         ml = [meshes] if single else list(meshes)
+        self.meshes = ml
         descs, self._keep = [], []
         for m in ml:
             d, keep = mesh_desc(m)
@@ -308,3 +322,71 @@ class Context:
 
     def idp_dgsem_sync(self, stream=None):
         return lib().idp_dgsem_sync(self._h, _stream(stream))
+
+    # ---- adaptive mesh refinement -------------------------------------------
+
+    def idp_dgsem_amr_indicator(self, u, params=None, stream=None):
+        """Per-element AMR indicator of the device state u (a device tensor of K doubles)."""
+        import torch
+        p = params if params is not None else amr_params()
+        ind = torch.empty(self.K, dtype=torch.float64, device=u.device)
+        _check(lib().idp_dgsem_amr_indicator(self._h, _ptr(u), C.byref(p), _ptr(ind), _stream(stream)),
+               "idp_dgsem_amr_indicator")
+        return ind
+
+    def adapt(self, u, params=None, stream=None):
+        """One AMR step of a single-mesh context: indicator (device), plan (host),
+        transfer (device) and a context for the adapted mesh with the same
+        options. Returns (context, state, (kind, src), scaled families)."""
+        import dataclasses
+        import torch
+        if self.n_sims != 1:
+            raise ValueError("adapt works on single-mesh contexts")
+        p = params if params is not None else amr_params()
+        ind = self.idp_dgsem_amr_indicator(u, p, stream)
+        torch.cuda.synchronize()
+        lev, ix, iy, kind, src = idp_amr_plan(self.meshes[0], ind.cpu().numpy(), p)
+        mesh2 = dataclasses.replace(self.meshes[0], level=lev, ix=ix, iy=iy)
+        un, scaled = idp_amr_transfer(self.N, self.gamma, u, kind, src, p.zs_threshold, stream)
+        return Context(mesh2, self.N, self.gamma, opts=self.opts), un, (kind, src), scaled
+
+
+def amr_params(**kw) -> AmrParams:
+    p = AmrParams()
+    lib().idp_amr_params_default(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def idp_amr_plan(mesh, ind, params=None):
+    """(level, ix, iy, kind, src) of the adapted mesh (host arrays)."""
+    p = params if params is not None else amr_params()
+    d, keep = mesh_desc(mesh)
+    ind = np.ascontiguousarray(ind, dtype=np.float64)
+    cap = 4 * mesh.n_elems
+    lev = np.zeros(cap, np.int8)
+    ix, iy, kind = np.zeros(cap, np.int32), np.zeros(cap, np.int32), np.zeros(cap, np.int32)
+    src = np.zeros((cap, 4), np.int32)
+    n = C.c_int32()
+    ip = C.POINTER(C.c_int32)
+    _check(lib().idp_amr_plan(C.byref(d), ind.ctypes.data_as(C.POINTER(C.c_double)), C.byref(p), cap, C.byref(n),
+                              lev.ctypes.data_as(C.POINTER(C.c_int8)), ix.ctypes.data_as(ip), iy.ctypes.data_as(ip),
+                              kind.ctypes.data_as(ip), src.ctypes.data_as(ip)), "idp_amr_plan")
+    k = n.value
+    return lev[:k].copy(), ix[:k].copy(), iy[:k].copy(), kind[:k].copy(), src[:k].copy()
+
+
+def idp_amr_transfer(N, gamma, u_old, kind, src, zs_threshold=1e-10, stream=None):
+    """(state on the adapted mesh as a new device tensor, scaled families)."""
+    import torch
+    kind = np.ascontiguousarray(kind, dtype=np.int32)
+    src = np.ascontiguousarray(src, dtype=np.int32)
+    n_new = kind.shape[0]
+    un = torch.empty((4, n_new, N + 1, N + 1), dtype=torch.float64, device=u_old.device)
+    sc = C.c_int64()
+    ip = C.POINTER(C.c_int32)
+    _check(lib().idp_amr_transfer(int(N), float(gamma), _ptr(u_old), int(u_old.shape[1]), _ptr(un), n_new,
+                                  kind.ctypes.data_as(ip), src.ctypes.data_as(ip), float(zs_threshold), C.byref(sc),
+                                  _stream(stream)), "idp_amr_transfer")
+    return un, sc.value

@@ -1,0 +1,120 @@
+"""GPU parity of the AMR step (Sec. 2.4) against the oracle through the C
+ABI: element indicators (modal energy, Loehner-type, both; density and
+pressure), the solution transfer with the Zhang-Shu fix on the same plan,
+and an adapt-and-step loop that keeps conservation and the invariants.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import amr
+from paper_2607_06045_b300 import build, idp
+from paper_2607_06045_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    yield
+
+
+def dev(u):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(u)).cuda()
+
+
+@pytest.mark.parametrize("N", [1, 3, 5])
+def test_indicators(N):
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, N)
+    ctx = idp.Context(m, N)
+    ud = dev(u)
+    for kind in (amr.IND_HENNEMANN, amr.IND_LOHNER, amr.IND_MAX):
+        for var in (amr.VAR_DENSITY, amr.VAR_PRESSURE):
+            g = ctx.idp_dgsem_amr_indicator(ud, idp.amr_params(indicator=kind, variable=var)).cpu().numpy()
+            o = amr.indicators(u, N, amr.Params(indicator=kind, variable=var))
+            assert np.abs(g - o).max() <= 1e-12, (kind, var)
+            if N > 1:
+                assert o.max() > 0.1   # the disc's jump is detected
+    ctx.close()
+
+
+def _family_random(mesh, seed):
+    rng = np.random.default_rng(seed)
+    cell = rng.uniform(0, 1, (mesh.nx0, mesh.ny0))
+    return np.array([cell[x >> l, y >> l] for l, x, y in zip(mesh.level.tolist(), mesh.ix.tolist(), mesh.iy.tolist())])
+
+
+@pytest.mark.parametrize("N", [2, 3, 5])
+def test_transfer(N):
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, N)
+    pl = idp.idp_amr_plan(m, _family_random(m, 5), idp.amr_params(refine_threshold=0.8, coarsen_threshold=0.5,
+                                                                      max_level=2))
+    kind, src = pl[3], pl[4]
+    un, sc = idp.idp_amr_transfer(N, 1.4, dev(u), kind, src, 1e-10)
+    uo, sco = amr.transfer(u, N, pl, 1.4, 1e-10)
+    scale = np.abs(uo).reshape(4, -1).max(axis=1)
+    err = (np.abs(un.cpu().numpy() - uo).reshape(4, -1).max(axis=1) / scale).max()
+    assert err <= 1e-13, err
+    assert sc == sco
+
+
+def test_transfer_near_vacuum():
+    m = W.uniform_mesh(4, 4, level=1, bc=(W.BC_OUTFLOW,) * 4)
+    N = 4
+    X, Y = W.node_coords(m, N)
+    r = np.sqrt((X - 0.5) ** 2 + (Y - 0.5) ** 2)
+    rho = np.where(r < 0.2, 1.0, 1e-9)
+    p = np.where(r < 0.2, 1.0, 1e-9)
+    u = W.conserved(rho, 0.0 * X, 0.0 * X, p, 1.4)
+    pl = idp.idp_amr_plan(m, np.ones(m.n_elems), idp.amr_params(max_level=2))
+    un, sc = idp.idp_amr_transfer(N, 1.4, dev(u), pl[3], pl[4], 1e-10)
+    uo, sco = amr.transfer(u, N, pl, 1.4, 1e-10)
+    assert sc == sco and sc > 0
+    g = un.cpu().numpy()
+    # the fluid is at rest: compare momentum on the density-energy scale. Where
+    # rho and E undershoot alike, the pressure factor is a near-double root of
+    # R8's quadratic, fixed only to about the square root of the rounding
+    # (1e-8), so the scaled families agree to 1e-7
+    sc_v = np.abs(uo).reshape(4, -1).max(axis=1)
+    sc_v[1:3] = sc_v[3]
+    assert (np.abs(g - uo).reshape(4, -1).max(axis=1) / sc_v).max() <= 1e-7
+    assert g[0].min() >= 1e-10 * (1 - 1e-12)
+
+
+def test_adapt_and_step_loop():
+    """Five cycles of (adapt, 5 limited steps) on the periodic cfg1 data:
+    mass, momentum and energy are conserved through the transfers and the
+    steps, no invariant is violated, and the mesh follows the disc."""
+    import torch
+    m = W.cfg1_mesh()
+    N = 3
+    u = W.cfg1_state(m, N)
+    ctx = idp.Context(m, N, limiting=2, cfl=0.5)
+    ud = dev(u)
+    I0 = ctx.idp_dgsem_integrals(ud)[0]
+    p = idp.amr_params(indicator=amr.IND_MAX, refine_threshold=0.2, coarsen_threshold=0.02, min_level=0,
+                       max_level=2)
+    t = np.zeros(1)
+    sizes = []
+    for _ in range(5):
+        ctx2, ud2, (kind, src), sc = ctx.adapt(ud, p)
+        ctx.close()
+        ctx, ud = ctx2, ud2
+        sizes.append(ctx.K)
+        ctx.idp_dgsem_step(ud, 5, t)
+        rc, st = ctx.idp_dgsem_limiter_stats()
+        assert rc == idp.IDP_OK
+        assert st["n_nonpositive"] == 0 and st["n_viol_density"] == 0 and st["n_viol_pressure"] == 0
+    I1 = ctx.idp_dgsem_integrals(ud)[0]
+    scale = np.abs(I0).max()
+    assert np.abs(I1 - I0).max() <= 1e-12 * scale
+    assert max(sizes) > m.n_elems or min(sizes) < m.n_elems
+    torch.cuda.synchronize()
+    ctx.close()
