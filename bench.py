@@ -69,6 +69,23 @@ def dist_helpers(dist, device, sync=None):
     return barrier_sync, max_over_ranks
 
 
+def shard_sims(n_sims, rank, world):
+    """Simulations of the batched workload that rank `rank` of `world` runs:
+    every world-th one, so that the ranks' loads stay alike (weak in ranks,
+    the batch of independent simulations split with no communication)."""
+    return list(range(rank, n_sims, world))
+
+
+def sum_over_ranks(dist, device, x):
+    """Sum of a number over the ranks (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def aggregate_rate(units_per_rank, world, max_time):
     """Whole-job throughput: units all ranks processed over the slowest rank's time."""
     return world * units_per_rank / max_time
@@ -136,7 +153,7 @@ class Clocks:
         return out
 
 
-def build_workload(name):
+def build_workload(name, subset=None):
     from paper_2607_06045_b300 import workloads as W
     if name == "dmr":
         m = W.cfg2_mesh()
@@ -144,7 +161,9 @@ def build_workload(name):
     if name == "batched":
         ms = W.cfg4_meshes(256, seed=0)
         rng = np.random.default_rng(1)
-        return ms, W.concat_states([W.cfg4_state(m, 3, rng) for m in ms])
+        us = [W.cfg4_state(m, 3, rng) for m in ms]
+        keep = range(len(ms)) if subset is None else subset
+        return [ms[i] for i in keep], W.concat_states([us[i] for i in keep])
     if name == "vacuum":
         m, c = W.cfg5_mesh()
         return [m], W.cfg5_state(m, 5, c)
@@ -432,8 +451,10 @@ def run_ours(args):
     vctx.close()
     del vud
     # batched workload, FP32 form
-    bm, ub = build_workload("batched")
+    # the batch's independent simulations are split across the ranks
+    bm, ub = build_workload("batched", shard_sims(256, rank, world) if world > 1 else None)
     bnodes = ub.shape[1] * ub.shape[2] * ub.shape[3]
+    bnodes_all = sum_over_ranks(dist, "cuda", bnodes)
     bctx = idp.Context(bm, 3, precision=1, limiting=2, cfl=0.5)
     ubd = torch.from_numpy(ub).cuda()
     del ub
@@ -458,7 +479,7 @@ def run_ours(args):
     f32 = roofline.element_flops(3, 1, *w)
     el32 = r32["el_ms"] * 1e-3 / max(r32["el_n"], 1)
     ach32 = f32 * nodes / el32 * 1e-12
-    bval = aggregate_rate(bnodes * 3 * bsteps, world, btot)
+    bval = bnodes_all * 3 * bsteps / btot   # the whole batch over the slowest rank
     hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
     K, M = r64["ctx"].K, r64["ctx"].M
@@ -518,7 +539,8 @@ def run_ours(args):
             "batched_fp32": {"value": bval, "unit": UNIT,
                              "workload": "256 simulations, 8..128 base, 0-2 levels on seeded patches, N=3, "
                                          "four-quadrant Riemann data, FP32 form",
-                             "elements": int(bctx.K), "dofs": int(bnodes), "steps": bsteps,
+                             "elements_rank0": int(bctx.K), "dofs": int(bnodes_all), "steps": bsteps,
+                             "scaling": "strong: the 256 simulations split across the ranks, no communication",
                              "speedup_vs_fp64": bval / value,
                              "gpu_launches": int(bctx.launches_per_step() * bsteps),
                              "stats": {k: bst[k] for k in ("alpha_volume_mean", "n_viol_density",

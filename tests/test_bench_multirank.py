@@ -47,6 +47,30 @@ def test_max_over_ranks_and_aggregate_gloo():
         assert v == pytest.approx(world * 962224 * 3 * 10 / 0.8)
 
 
+def _shard_worker(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mine = bench.shard_sims(256, rank, world)
+    out[rank] = (mine, bench.sum_over_ranks(dist, "cpu", len(mine) * 10))
+    dist.destroy_process_group()
+
+
+def test_batched_shards_gloo():
+    """The batched workload's simulations split across two ranks: disjoint,
+    complete, balanced, and the node totals sum over the ranks."""
+    world, port = 2, _free_port()
+    with mp.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_shard_worker, args=(world, port, out), nprocs=world, join=True)
+        res = dict(out)
+    a, b = res[0][0], res[1][0]
+    assert not set(a) & set(b) and sorted(a + b) == list(range(256)) and len(a) == len(b) == 128
+    assert res[0][1] == res[1][1] == 2560
+    assert bench.shard_sims(256, 0, 1) == list(range(256))
+
+
 def test_single_process_helpers():
     barrier_sync, max_over_ranks = bench.dist_helpers(None, "cpu")
     barrier_sync()
