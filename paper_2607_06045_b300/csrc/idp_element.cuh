@@ -15,6 +15,7 @@
 #pragma once
 
 #include "idp_device.cuh"
+#include "idp_variants.cuh"
 
 namespace idp {
 
