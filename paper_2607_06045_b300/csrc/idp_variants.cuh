@@ -89,7 +89,11 @@ __device__ __forceinline__ double theta_entropy(const Gas &G, const double u0[4]
                                                 double hi) {
     if (!dpos(hi) || !dnormpos(u0[0])) return 0.0;
     double v[4], dp;
-    const double delta = 1e-14 * (fabs(u0[3]) + exp(lnK + G.g * fast_log(u0[0], G.lg)));
+    // the margin is a scale, not a decision: K rho_0^gamma in FP32 (FP64 only
+    // outside the FP32 range)
+    float kr0 = expf(d2f(lnK) + G.gf * logf(d2f(u0[0])));
+    const double krd = (kr0 < 3e38f) ? f2d(kr0) : exp(lnK + G.g * fast_log(u0[0], G.lg));
+    const double delta = 1e-14 * (fabs(u0[3]) + krd);
     for (int k = 0; k < 4; ++k) v[k] = u0[k] + hi * a[k];
     if (dnormpos(v[0]) && !dlt(entropy_psi(G, v, a, lnK, dp), delta)) return hi;
     if (dlt(entropy_psi(G, u0, a, lnK, dp), delta)) return 0.0;
