@@ -80,3 +80,25 @@ def test_plan_argument_errors():
                 iy=np.array([0] + [b for a in range(4) for b in range(4)], np.int32), bc=(W.BC_OUTFLOW,) * 4)
     with pytest.raises(Exception):
         idp.idp_amr_plan(mu, np.zeros(mu.n_elems))
+
+
+def test_transfer_argument_errors_without_gpu():
+    """idp_amr_transfer checks the plan before it touches the GPU."""
+    import ctypes as C
+    L = idp.lib()
+    ip = C.POINTER(C.c_int32)
+    dummy = C.c_void_p(16)   # never dereferenced: every case below fails its checks first
+
+    def call(kind, src, n_old=4, N=3, gamma=1.4, eps=1e-10):
+        kind = np.ascontiguousarray(kind, np.int32)
+        src = np.ascontiguousarray(src, np.int32).reshape(-1, 4)
+        return L.idp_amr_transfer(N, gamma, dummy, n_old, dummy, len(kind), kind.ctypes.data_as(ip),
+                                  src.ctypes.data_as(ip), eps, None, None)
+    assert call([0], [[7, -1, -1, -1]]) == idp.IDP_E_ARG                   # source out of range
+    assert call([1, 1, 1], [[0, 0, -1, -1], [0, 1, -1, -1], [0, 2, -1, -1]]) == idp.IDP_E_ARG   # short family
+    assert call([1, 1, 1, 1], [[0, 0, -1, -1], [0, 1, -1, -1], [0, 3, -1, -1], [0, 2, -1, -1]]) == idp.IDP_E_ARG
+    assert call([2], [[0, 1, 2, 9]]) == idp.IDP_E_ARG                      # coarsened child out of range
+    assert call([3], [[0, -1, -1, -1]]) == idp.IDP_E_ARG                   # unknown kind
+    assert call([0], [[0, -1, -1, -1]], N=8) == idp.IDP_E_ARG              # degree beyond the library's
+    assert call([0], [[0, -1, -1, -1]], gamma=1.0) == idp.IDP_E_ARG
+    assert call([0], [[0, -1, -1, -1]], eps=-1.0) == idp.IDP_E_ARG
