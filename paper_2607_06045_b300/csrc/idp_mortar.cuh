@@ -1,11 +1,11 @@
 // idp_mortar.cuh -- face-list kernels at nonconforming interfaces and the
 // per-step reductions of the IDP LGL-DGSEM (arXiv 2607.06045).
 //
-//  k_mortar_flux   per mortar (one warp): high-order L2 mortar flux (Sec. 2.3,
+//  k_mortar_flux   per block of mortars: high-order L2 mortar flux (Sec. 2.3,
 //                  interpolate, LLF on the two small faces, project back) and
 //                  the sparse low-order IDP mortar flux (Eq. interfaceflux_local)
 //                  with its bar states and graph-viscosity sums.
-//  k_mortar_limit  per mortar (one warp): one factor l_S per mortar after the
+//  k_mortar_limit  one thread per mortar slot: one factor l_S per mortar after the
 //                  volume correction, each node's correction budget scaled by
 //                  its number of mortars n_i (Sec. 2.3, mortar limiting).
 //  k_mortar_apply  per mortar node: apply the limited corrections in mortar
@@ -18,7 +18,7 @@
 
 namespace idp {
 
-constexpr int MORTARS_PER_BLOCK = 4;   // one warp per mortar
+constexpr int MORTARS_PER_BLOCK = 4;   // mortars of one block (32 threads each)
 
 // FT: flux arithmetic type (FP32 in the FP32 form). Interpolation, the
 // admissibility test, bar states and all sums are FP64.
@@ -32,11 +32,12 @@ __device__ __forceinline__ Prim<FT> mortar_prim(const Gas &g, const double *q) {
     }
 }
 
-// One warp per mortar. Lanes take (node, variable) items for the
+// MORTARS_PER_BLOCK mortars per block. Every phase is one loop of the whole
+// block over the items of all its mortars -- (node, variable) items for the
 // interpolation and the projection, one small-face node each for the LLF
-// fluxes, and one nonzero local weight each for the sparse low-order flux:
-// every pair term is formed once and summed into both of its slots in a
-// fixed order.
+// fluxes, one nonzero weight each for the low-order pair terms -- so the
+// phases with few items per mortar still fill whole warps. Every pair term is
+// formed once and summed into both of its slots in a fixed order.
 // ent: also the minimum over each slot's bar states of s = ln p - gamma ln rho
 // (entropy bound of local limiting with bar-state bounds).
 // A2A: all-to-all weights (every large node with every small-face node).
@@ -44,6 +45,7 @@ template <int NP, typename FT, bool A2A>
 __global__ void __launch_bounds__(32 * MORTARS_PER_BLOCK)
 k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, const Ops *ops, int ent) {
     constexpr int NN = NP * NP, Q = 3 * NP, NI = 2 * NP, MP = A2A ? 2 * NP * NP : 3 * NP, W = MORTARS_PER_BLOCK;
+    constexpr int NT = 32 * W;
     __shared__ double s_u[W][Q][4];      // traces: large side, then the two small faces
     __shared__ FT s_uf[W][Q][4];         // the same in the flux type
     __shared__ FT s_pr[W][Q][3];         // normal velocity, p, c
@@ -53,60 +55,73 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
     __shared__ double s_rb[W][MP];       // their bar-state densities
     __shared__ FT s_d2[W][MP];           // and 2 d
     __shared__ double s_sb[W][MP];       // and their s (entropy bound)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m = blockIdx.x * W + warp;
-    if (m >= mesh.M) return;   // uniform per warp
+    __shared__ int s_info[W], s_L[W], s_bad[W];
+    __shared__ int2 s_sm[W];
+    __shared__ double s_halfL[W];
+    const int tid = threadIdx.x;
+    const int m0 = blockIdx.x * W;
+    const int nm = min(W, mesh.M - m0);   // mortars of this block
+    if (nm <= 0) return;                  // uniform per block
     const size_t KN = (size_t)mesh.K * NN;
-    const int info = mesh.m_info[m], dir = info & 1, low = (info >> 1) & 1;
-    const int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
-    const int L = mesh.m_large[m];
-    const int2 sm2 = mesh.m_small[m];
-    const Geo geoL = mesh.geom[L];
-    const double halfL = dir == 0 ? 0.5 * geoL.w : 0.5 * geoL.z, halfS = 0.5 * halfL;
-    const double sg = low ? 1.0 : -1.0;   // large side's outward normal along +dir
     const Gas &g = gas;
     constexpr bool F32 = sizeof(FT) == 4;
+    if (tid < nm) {
+        const int m = m0 + tid, info = mesh.m_info[m], L = mesh.m_large[m];
+        const Geo geoL = mesh.geom[L];
+        s_info[tid] = info;
+        s_L[tid] = L;
+        s_sm[tid] = mesh.m_small[m];
+        s_halfL[tid] = (info & 1) == 0 ? 0.5 * geoL.w : 0.5 * geoL.z;
+        s_bad[tid] = 0;
+    }
+    __syncthreads();
     // traces and their primitives
-    if (lane < Q) {
+    for (int it = tid; it < nm * Q; it += NT) {
+        const int mi = it / Q, q = it - mi * Q;
+        const int info = s_info[mi], dir = info & 1, low = (info >> 1) & 1;
+        const int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
         int gnode;
-        if (lane < NP) gnode = L * NN + face_node<NP>(sL, lane);
+        if (q < NP) gnode = s_L[mi] * NN + face_node<NP>(sL, q);
         else {
-            int p = (lane - NP) / NP, l = (lane - NP) % NP;
-            gnode = (p == 0 ? sm2.x : sm2.y) * NN + face_node<NP>(sS, l);
+            int p = (q - NP) / NP, l = (q - NP) % NP;
+            gnode = (p == 0 ? s_sm[mi].x : s_sm[mi].y) * NN + face_node<NP>(sS, l);
         }
-        double q[4];
-        for (int v = 0; v < 4; ++v) { q[v] = u[v * KN + gnode]; s_u[warp][lane][v] = q[v]; }
+        double qv[4];
+        for (int v = 0; v < 4; ++v) { qv[v] = u[v * KN + gnode]; s_u[mi][q][v] = qv[v]; }
         Prim<FT> pr;
         if constexpr (F32) {
             float m1f, m2f;
-            pr = make_prim_f32(g, q[0], q[1], q[2], q[3], false, m1f, m2f);
-            s_uf[warp][lane][0] = pr.rho; s_uf[warp][lane][1] = m1f; s_uf[warp][lane][2] = m2f;
-            s_uf[warp][lane][3] = pr.E;
+            pr = make_prim_f32(g, qv[0], qv[1], qv[2], qv[3], false, m1f, m2f);
+            s_uf[mi][q][0] = pr.rho; s_uf[mi][q][1] = m1f; s_uf[mi][q][2] = m2f;
+            s_uf[mi][q][3] = pr.E;
         } else {
-            pr = make_prim<FT>(g, q[0], q[1], q[2], q[3], false);
-            for (int v = 0; v < 4; ++v) s_uf[warp][lane][v] = q[v];
+            pr = make_prim<FT>(g, qv[0], qv[1], qv[2], qv[3], false);
+            for (int v = 0; v < 4; ++v) s_uf[mi][q][v] = qv[v];
         }
-        s_pr[warp][lane][0] = dir == 0 ? pr.v1 : pr.v2;
-        s_pr[warp][lane][1] = pr.p;
-        s_pr[warp][lane][2] = pr.c;
+        s_pr[mi][q][0] = dir == 0 ? pr.v1 : pr.v2;
+        s_pr[mi][q][1] = pr.p;
+        s_pr[mi][q][2] = pr.c;
     }
-    __syncwarp();
+    __syncthreads();
     // interpolation of the large trace to the small-face nodes (FP64)
-    for (int it = lane; it < NI * 4; it += 32) {
-        const int r = it >> 2, v = it & 3;
+    for (int it = tid; it < nm * NI * 4; it += NT) {
+        const int mi = it / (NI * 4), rem = it - mi * (NI * 4), r = rem >> 2, v = rem & 3;
         double acc = 0.0;
-        for (int k = 0; k < NP; ++k) acc += ops->I[r][k] * s_u[warp][k][v];
-        s_ui[warp][r][v] = acc;
+        for (int k = 0; k < NP; ++k) acc += ops->I[r][k] * s_u[mi][k][v];
+        s_ui[mi][r][v] = acc;
     }
-    // sparse low-order pair terms (Eq. interfaceflux_local) with their bar
-    // states and 2 d; term enters the large slot with -, the small with +
+    // low-order pair terms (Eq. interfaceflux_local) with their bar states
+    // and 2 d; term enters the large slot with -, the small with +
     const int npair = ops->npair;
-    for (int pp = lane; pp < npair; pp += 32) {
+    for (int it = tid; it < nm * npair; it += NT) {
+        const int mi = it / npair, pp = it - mi * npair;
+        const int info = s_info[mi], dir = info & 1, low = (info >> 1) & 1;
+        const double sg = low ? 1.0 : -1.0;   // large side's outward normal along +dir
         const int k = ops->pk[pp], r = ops->pr[pp];
-        const double wt = ops->wt[k][r] * halfL;
-        const double *a = s_u[warp][k], *b = s_u[warp][NP + r];
-        const FT *af = s_uf[warp][k], *bf = s_uf[warp][NP + r];
-        const FT *pa = s_pr[warp][k], *pb = s_pr[warp][NP + r];
+        const double wt = ops->wt[k][r] * s_halfL[mi];
+        const double *a = s_u[mi][k], *b = s_u[mi][NP + r];
+        const FT *af = s_uf[mi][k], *bf = s_uf[mi][NP + r];
+        const FT *pa = s_pr[mi][k], *pb = s_pr[mi][NP + r];
         FT la = fabs(pa[0]) + pa[2], lb = fabs(pb[0]) + pb[2];
         FT lam = la > lb ? la : lb;
         FT fa[4], fb[4];
@@ -124,71 +139,75 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
             FT term;
             if constexpr (A2A) term = hw * (sgf * fa[v] + sgf * fb[v]) - fabs(hw) * lam * (bf[v] - af[v]);
             else term = hw * ((sgf * fa[v] + sgf * fb[v]) - lam * (bf[v] - af[v]));
-            if constexpr (F32) s_term[warp][pp][v] = f2d(term);
-            else s_term[warp][pp][v] = term;
+            if constexpr (F32) s_term[mi][pp][v] = f2d(term);
+            else s_term[mi][pp][v] = term;
         }
-        s_rb[warp][pp] = 0.5 * (a[0] + b[0]) - sgw * (b[1 + dir] - a[1 + dir]) * i2l;
+        s_rb[mi][pp] = 0.5 * (a[0] + b[0]) - sgw * (b[1 + dir] - a[1 + dir]) * i2l;
         if (ent) {
             const bool pos = sgw > 0.0;
-            if constexpr (F32) s_sb[warp][pp] = bar_entropy<float>(g, af, fa, bf, fb, pos ? i2l_f : -i2l_f);
-            else s_sb[warp][pp] = bar_entropy<double>(g, a, fa, b, fb, pos ? i2l : -i2l);
+            if constexpr (F32) s_sb[mi][pp] = bar_entropy<float>(g, af, fa, bf, fb, pos ? i2l_f : -i2l_f);
+            else s_sb[mi][pp] = bar_entropy<double>(g, a, fa, b, fb, pos ? i2l : -i2l);
         }
         FT wtf;
         if constexpr (F32) wtf = d2f(fabs(wt));
         else wtf = fabs(wt);
-        s_d2[warp][pp] = wtf * lam;
+        s_d2[mi][pp] = wtf * lam;
     }
-    __syncwarp();
+    __syncthreads();
     // admissibility of the interpolated states; LLF on the small faces
-    // (left/bottom state first)
-    bool badl = false;
-    Prim<FT> pint;
-    if (lane < NI) {
-        const double *acc = s_ui[warp][lane];
+    // (left/bottom state first); a mortar with an inadmissible interpolated
+    // state keeps its low-order flux (its LLF values are not used)
+    for (int it = tid; it < nm * NI; it += NT) {
+        const int mi = it / NI, r = it - mi * NI;
+        const int info = s_info[mi], dir = info & 1, low = (info >> 1) & 1;
+        const double *acc = s_ui[mi][r];
         // rho > 0 and rho p > 0, without a division
-        badl = !dpos(acc[0]) || !dpos(acc[0] * acc[3] - 0.5 * (acc[1] * acc[1] + acc[2] * acc[2]));
-        if (!badl) pint = mortar_prim<NP, FT>(g, acc);
-    }
-    const bool bad = __any_sync(0xffffffffu, badl);
-    if (!bad && lane < NI) {
+        if (!dpos(acc[0]) || !dpos(acc[0] * acc[3] - 0.5 * (acc[1] * acc[1] + acc[2] * acc[2]))) {
+            atomicOr(&s_bad[mi], 1);
+            continue;
+        }
+        const Prim<FT> pint = mortar_prim<NP, FT>(g, acc);
         FT f[4];
         Prim<FT> ps;
-        ps.v1 = dir == 0 ? s_pr[warp][NP + lane][0] : FT(0);
-        ps.v2 = dir == 1 ? s_pr[warp][NP + lane][0] : FT(0);
-        ps.p = s_pr[warp][NP + lane][1];
-        ps.c = s_pr[warp][NP + lane][2];
-        const FT *us = s_uf[warp][NP + lane];
+        ps.v1 = dir == 0 ? s_pr[mi][NP + r][0] : FT(0);
+        ps.v2 = dir == 1 ? s_pr[mi][NP + r][0] : FT(0);
+        ps.p = s_pr[mi][NP + r][1];
+        ps.c = s_pr[mi][NP + r][2];
+        const FT *us = s_uf[mi][NP + r];
         FT ui[4];
-        for (int v = 0; v < 4; ++v) ui[v] = to_ft<FT>(s_ui[warp][lane][v]);
+        for (int v = 0; v < 4; ++v) ui[v] = to_ft<FT>(s_ui[mi][r][v]);
         if (low) llf_prim<FT, FT>(ui, pint, us, ps, dir, f);
         else llf_prim<FT, FT>(us, ps, ui, pint, dir, f);
-        for (int v = 0; v < 4; ++v) s_f[warp][lane][v] = f[v];
+        for (int v = 0; v < 4; ++v) s_f[mi][r][v] = f[v];
     }
-    __syncwarp();
+    __syncthreads();
     // per (slot, variable): high-order contribution (projection summed in
     // FP64, so conservation across the mortar holds to FP64 rounding whatever
-    // the flux type) and the sparse low-order sum
-    for (int it = lane; it < Q * 4; it += 32) {
-        const int q = it >> 2, v = it & 3;
+    // the flux type) and the low-order sum
+    for (int it = tid; it < nm * Q * 4; it += NT) {
+        const int mi = it / (Q * 4), rem = it - mi * (Q * 4), q = rem >> 2, v = rem & 3;
+        const int m = m0 + mi;
+        const double sg = ((s_info[mi] >> 1) & 1) ? 1.0 : -1.0;
+        const double halfL = s_halfL[mi], halfS = 0.5 * halfL;
         double chi = 0.0, clo = 0.0;
         const int np_q = ops->slot_n[q];
-        for (int t = 0; t < np_q; ++t) clo += s_term[warp][ops->slot_p[q][t]][v];
+        for (int t = 0; t < np_q; ++t) clo += s_term[mi][ops->slot_p[q][t]][v];
         if (q < NP) clo = -clo;
-        if (!bad) {
+        if (!s_bad[mi]) {
             if (q < NP) {
                 double acc = 0.0;
                 for (int r = 0; r < NI; ++r) {
                     double fr;
-                    if constexpr (F32) fr = f2d(s_f[warp][r][v]);
-                    else fr = s_f[warp][r][v];
+                    if constexpr (F32) fr = f2d(s_f[mi][r][v]);
+                    else fr = s_f[mi][r][v];
                     acc += ops->P[q][r] * fr;
                 }
                 chi = -sg * ops->w[q] * (halfL * acc);
             } else {
                 const int l = (q - NP) % NP;
                 double fr;
-                if constexpr (F32) fr = f2d(s_f[warp][q - NP][v]);
-                else fr = s_f[warp][q - NP][v];
+                if constexpr (F32) fr = f2d(s_f[mi][q - NP][v]);
+                else fr = s_f[mi][q - NP][v];
                 chi = sg * ops->w[l] * (halfS * fr);
             }
         } else {
@@ -199,27 +218,28 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
         sl.clo[si] = clo;
     }
     // per slot: bar-state range and 2 d sum over its pairs
-    if (lane < Q) {
+    for (int it = tid; it < nm * Q; it += NT) {
+        const int mi = it / Q, q = it - mi * Q;
         long long klo = okey(INFINITY), khi = okey(-INFINITY);
         FT ds = FT(0);
         double smin = INFINITY;
-        const int np_q = ops->slot_n[lane];
+        const int np_q = ops->slot_n[q];
         for (int t = 0; t < np_q; ++t) {
-            const int p = ops->slot_p[lane][t];
-            const long long kb = okey(s_rb[warp][p]);
+            const int p = ops->slot_p[q][t];
+            const long long kb = okey(s_rb[mi][p]);
             klo = kb < klo ? kb : klo;
             khi = kb > khi ? kb : khi;
-            ds += s_d2[warp][p];
-            if (ent) smin = dmin(smin, s_sb[warp][p]);
+            ds += s_d2[mi][p];
+            if (ent) smin = dmin(smin, s_sb[mi][p]);
         }
-        const int si = m * Q + lane;
+        const int si = (m0 + mi) * Q + q;
         if (ent) sl.sbmin[si] = smin;
         sl.rbmin[si] = okey_value(klo);
         sl.rbmax[si] = okey_value(khi);
         if constexpr (F32) sl.dsum[si] = f2d(ds);
         else sl.dsum[si] = ds;
     }
-    if (lane == 0) sl.bad[m] = bad ? 1 : 0;
+    if (tid < nm) sl.bad[m0 + tid] = s_bad[tid] ? 1 : 0;
 }
 
 // Mortar limiting: one thread per mortar slot, 128 / (3 (N+1)) mortars per
