@@ -169,7 +169,19 @@ __device__ __forceinline__ void log_means(const Prim<FT> &a, const Prim<FT> &b, 
     const FT thr = dbl ? FT(1e-4) : FT(1e-2);
     FT dr = a.rho - b.rho, sr = a.rho + b.rho;
     FT db = a.beta - b.beta, sb = a.beta + b.beta;
-    bool nr = dr * dr < thr * (sr * sr), nb = db * db < thr * (sb * sb);
+    bool nr, nb;
+    if constexpr (dbl) {
+        // the test only picks between two forms that agree to rounding near
+        // the threshold, so FP32 (converted on the integer pipe) suffices and
+        // spares four FP64 operations per mean; <= keeps equal states that
+        // flush to zero in FP32 on the series
+        const float drf = d2f(dr), srf = d2f(sr), dbf = d2f(db), sbf = d2f(sb);
+        nr = drf * drf <= 1e-4f * (srf * srf);
+        nb = dbf * dbf <= 1e-4f * (sbf * sbf);
+    } else {
+        nr = dr * dr < thr * (sr * sr);
+        nb = db * db < thr * (sb * sb);
+    }
     FT lr, lb;
     if (dbl) { lr = a.lr - b.lr; lb = a.lb - b.lb; }
     else {
