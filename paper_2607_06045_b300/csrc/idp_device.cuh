@@ -151,6 +151,11 @@ __device__ __forceinline__ double pressure_d(double gm1, double r, double m1, do
     return gm1 * (E - 0.5 * (m1 * m1 + m2 * m2) / r);
 }
 
+// max of two non-negative wave speeds: doubles by their bits (integer pipe),
+// floats directly
+__device__ __forceinline__ double speed_max(double a, double b) { return nn_lt(a, b) ? b : a; }
+__device__ __forceinline__ float speed_max(float a, float b) { return a > b ? a : b; }
+
 // Node primitives in the flux type.
 template <typename FT> struct Prim {
     FT rho, v1, v2, p, c, E, lr, lb, beta;
@@ -314,7 +319,7 @@ __device__ __forceinline__ FT llf_prim(const ST uL[4], const Prim<FT> &a, const 
                                        FT f[4]) {
     FT vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
     FT la = fabs(vna) + a.c, lb = fabs(vnb) + b.c;
-    FT lam = la > lb ? la : lb;
+    FT lam = speed_max(la, lb);
     FT fa[4], fb[4], ul[4], ur[4];
     for (int v = 0; v < 4; ++v) { ul[v] = to_ft<FT>(uL[v]); ur[v] = to_ft<FT>(uR[v]); }
     phys_flux<FT>(ul[1], ul[2], ul[3], a.p, vna, d, fa);

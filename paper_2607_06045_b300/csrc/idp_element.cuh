@@ -93,9 +93,9 @@ struct ElemSm {
             double face[4][NP][4];   // (w_t |face|/2) * numerical flux along +x/+y
             double fbar[4][NP];      // bar-state density across the face (mortar sides: the minimum)
             double fbar2[4][NP];     // mortar sides: the maximum (conforming: = fbar)
-            FT f2d[4][NP];           // 2 d_ij across the face (time-step check)
+            float f2d[4][NP];        // 2 d_ij across the face (time-step statistic, FP32)
             double ibar[NIF];        // bar-state density across interior subcell interfaces
-            FT i2d[NIF];
+            float i2d[NIF];
             FT indT[NN];             // combined limiting: V^{-1} P (first half of the modal transform)
             // entropy bound: s = ln p - gamma ln rho of the node [NN], of the
             // bar states at interior interfaces [NIF] and across faces [4][NP]
@@ -299,8 +299,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 S.dt = dt;
                 S.dt4A = dt * gc.iA4;
                 S.hx = gc.hx; S.hy = gc.hy; S.qx = gc.qx; S.qy = gc.qy;
+                S.hxf = gc.hxf; S.hyf = gc.hyf; S.qxf = gc.qxf; S.qyf = gc.qyf;
                 if constexpr (F32) {
-                    S.hxf = gc.hxf; S.hyf = gc.hyf; S.qxf = gc.qxf; S.qyf = gc.qyf;
                     const float dtf = d2f(dt);
                     S.idtmf = dtf > 0.0f ? gc.A4f / dtf : 0.0f;
                 }
@@ -374,7 +374,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                         S.fbar2[s][t] = sl.rbmax[q];
                         if (ent && !pre) S.xs[NN + NIF + s * NP + t] = sl.sbmin[q];
                     }
-                    S.f2d[s][t] = to_ft<FT>(sl.dsum[q]);
+                    S.f2d[s][t] = d2f(sl.dsum[q]);
                 }
                 continue;
             }
@@ -413,7 +413,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                                          : llf_prim<FT, double>(ui, pi, out, po, d, f);
                 double wh = s_w[t] * (d == 0 ? S.hy : S.hx);
                 for (int v = 0; v < 4; ++v) S.face[s][t][v] = wh * f[v];
-                S.f2d[s][t] = wh * lam;
+                S.f2d[s][t] = s_wf[t] * (d == 0 ? S.hyf : S.hxf) * d2f(lam);
                 i2l = 0.5 * fast_rcp(lam);
                 if (EXT && fent) {
                     double fi[4], fo[4];
@@ -455,7 +455,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 Prim<FT> pa = load_prim<NP, FT, EXT>(S, na), pb = load_prim<NP, FT, EXT>(S, nb);
                 FT vna = d == 0 ? pa.v1 : pa.v2, vnb = d == 0 ? pb.v1 : pb.v2;
                 FT la = fabs(vna) + pa.c, lb = fabs(vnb) + pb.c;
-                FT lam = la > lb ? la : lb;
+                FT lam = speed_max(la, lb);
                 FT ua[4], ub[4];
                 for (int v = 0; v < 4; ++v) {
                     if constexpr (F32) { ua[v] = S.uf[v][na]; ub[v] = S.uf[v][nb]; }
@@ -472,7 +472,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if constexpr (F32) S.Ffv[id][v] = fv;
                     else S.Fv[id][v] = fv;
                 }
-                S.i2d[id] = FT(2) * cc * lam;
+                if constexpr (F32) S.i2d[id] = FT(2) * cc * lam;
+                else S.i2d[id] = 2.0f * (s_wf[r] * (d == 0 ? S.qyf : S.qxf)) * d2f(lam);
                 double i2l;
                 FT i2lt;
                 if constexpr (F32) { i2lt = 0.5f / lam; i2l = f2d(i2lt); }
@@ -562,7 +563,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 long long khi = lob ? okey(-INFINITY) : klo;
                 double smin = 0.0;
                 if (EXT && ent) smin = lob ? INFINITY : S.xs[n];
-                FT ds = FT(0);
+                float ds = 0.0f;   // sum_j 2 d_ij for the time-step statistic (FP32)
                 // x direction: left then right; y: bottom then top. Interior
                 // subcell interfaces and element faces (conforming, boundary or
                 // mortar) are read through one path so that the warp does not
@@ -598,7 +599,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                                 smin = dmin(smin, sv);
                             }
                         }
-                        const FT dsv = interior ? S.i2d[id] : S.f2d[s][row];
+                        const float dsv = interior ? S.i2d[id] : S.f2d[s][row];
                         for (int v = 0; v < 4; ++v) {
                             if (d == 0 && side == 0) L[v] = fl[v];
                             else if (side == 0) L[v] += fl[v];
@@ -658,7 +659,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     if (A.collect && S.dtmf[n] * ds > 1.0f) atomicAdd(&A.stats->n_dtx, 1ull);
                 } else {
                     if constexpr (!F32) S.tol[n] = kTol * fabs(q[0]);
-                    if (A.collect && nn_lt(1.0, dtm * ds)) atomicAdd(&A.stats->n_dtx, 1ull);
+                    if (A.collect && S.dtmf[n] * ds > 1.0f) atomicAdd(&A.stats->n_dtx, 1ull);
                 }
             }
         }

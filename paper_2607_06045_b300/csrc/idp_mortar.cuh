@@ -123,7 +123,7 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
         const FT *af = s_uf[mi][k], *bf = s_uf[mi][NP + r];
         const FT *pa = s_pr[mi][k], *pb = s_pr[mi][NP + r];
         FT la = fabs(pa[0]) + pa[2], lb = fabs(pb[0]) + pb[2];
-        FT lam = la > lb ? la : lb;
+        FT lam = speed_max(la, lb);
         FT fa[4], fb[4];
         phys_flux<FT>(af[1], af[2], af[3], pa[1], pa[0], dir, fa);
         phys_flux<FT>(bf[1], bf[2], bf[3], pb[1], pb[0], dir, fb);
