@@ -161,6 +161,18 @@ template <typename FT> struct Prim {
     FT rho, v1, v2, p, c, E, lr, lb, beta;
 };
 
+// a where c holds, else b, field by field: per-lane selects on the integer
+// pipe, so that lanes which need a two-point flux with their operands in
+// either order share one inlined copy of it
+template <typename FT>
+__device__ __forceinline__ Prim<FT> pick_prim(bool c, const Prim<FT> &a, const Prim<FT> &b) {
+    Prim<FT> r;
+    r.rho = c ? a.rho : b.rho; r.v1 = c ? a.v1 : b.v1; r.v2 = c ? a.v2 : b.v2;
+    r.p = c ? a.p : b.p; r.c = c ? a.c : b.c; r.E = c ? a.E : b.E;
+    r.lr = c ? a.lr : b.lr; r.lb = c ? a.lb : b.lb; r.beta = c ? a.beta : b.beta;
+    return r;
+}
+
 // Logarithmic means of Ranocha's flux with one division per pair: the
 // density mean {rho}_ln and the inverse mean 1/{rho/p}_ln. For each mean the
 // far branch is (a-b)/(ln a - ln b) from per-node logarithms (FP64) or

@@ -384,7 +384,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             FT f[4], lam;
             double i2l;
             // left/bottom state first, so that both elements of a face form
-            // the same bits
+            // the same bits (FP64: operands selected per lane, so that the
+            // four sides of a warp share one flux evaluation)
+            const bool olft = s == 0 || s == 2;
             // entropy of the face bar state (bar-state bounds, entropy bound)
             const bool fent = ent && !lob && !pre;
             double fs = 0.0;
@@ -393,8 +395,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 Prim<float> po = make_prim_f32(G, out[0], out[1], out[2], out[3], false, m1f, m2f);
                 float ui[4] = {S.uf[0][n], S.uf[1][n], S.uf[2][n], S.uf[3][n]};
                 float uo[4] = {po.rho, m1f, m2f, po.E};
-                lam = (s == 0 || s == 2) ? llf_prim<float, float>(uo, po, ui, pi, d, f)
-                                         : llf_prim<float, float>(ui, pi, uo, po, d, f);
+                // (FP32 form: the FP32 flux is cheaper than the selects)
+                lam = olft ? llf_prim<float, float>(uo, po, ui, pi, d, f) : llf_prim<float, float>(ui, pi, uo, po, d, f);
                 float whf = s_wf[t] * (d == 0 ? S.hyf : S.hxf);
                 for (int v = 0; v < 4; ++v) S.face[s][t][v] = f2d(whf * f[v]);
                 S.f2d[s][t] = whf * lam;
@@ -409,8 +411,13 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             } else {
                 Prim<FT> po = make_prim<FT>(G, out[0], out[1], out[2], out[3], false);
                 double ui[4] = {S.u[0][n], S.u[1][n], S.u[2][n], S.u[3][n]};
-                lam = (s == 0 || s == 2) ? llf_prim<FT, double>(out, po, ui, pi, d, f)
-                                         : llf_prim<FT, double>(ui, pi, out, po, d, f);
+                double uL[4], uR[4];
+                for (int v = 0; v < 4; ++v) {
+                    const double o = out[v];
+                    uL[v] = olft ? o : ui[v];
+                    uR[v] = olft ? ui[v] : o;
+                }
+                lam = llf_prim<FT, double>(uL, pick_prim(olft, po, pi), uR, pick_prim(olft, pi, po), d, f);
                 double wh = s_w[t] * (d == 0 ? S.hy : S.hx);
                 for (int v = 0; v < 4; ++v) S.face[s][t][v] = wh * f[v];
                 S.f2d[s][t] = s_wf[t] * (d == 0 ? S.hyf : S.hxf) * d2f(lam);
