@@ -317,7 +317,9 @@ def run_ours(args):
         rc, st = ctx.idp_dgsem_limiter_stats()
         results[prec] = dict(time=tot, el_ms=el_ms, el_n=el_n, stats=st, ctx=ctx, kern=kern,
                              launches=ctx.launches_per_step() * args.steps, u_end=u_dev.cpu().numpy(),
-                             median_ms=time_steps.median_ms)
+                             median_ms=time_steps.median_ms,
+                             launch=dict(zip(("elems_per_block", "persistent", "grid"),
+                                             ctx.idp_dgsem_launch_config())))
         if prec == 0:
             results["clocks"] = ck
             # end to end through the host-buffer entry point (pinned host state)
@@ -505,7 +507,7 @@ def run_ours(args):
         "dtype": "f64",
         "data": "synthetic",
         "config": dict(DMR_CONFIG, precision="fp64", l2="flushed between steps (256 MiB write)",
-                       parallelism=f"replicas x{world}"),
+                       parallelism=f"replicas x{world}", element_launch=r64["launch"]),
         "roofline": {"bound": "alu", "kernel": "k_element (element pass, FP64 path)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"derived: {SMS} SMs x {DFMA_PER_CLK_SM} FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz",
@@ -526,6 +528,7 @@ def run_ours(args):
             "fp32_form": {"value": aggregate_rate(nodes * 3 * args.steps, world, r32["time"]), "unit": UNIT,
                           "ms_per_step": r32["time"] / args.steps * 1e3,
                           "speedup_vs_fp64": r64["time"] / r32["time"],
+                          "element_launch": r32["launch"],
                           "roofline": {"bound": "alu", "achieved": ach32, "peak": peak, "frac": ach32 / peak,
                                        "unit": "TFLOP/s", "launch_ms": el32 * 1e3,
                                        "flops_per_node_stage": f32},

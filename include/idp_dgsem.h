@@ -194,6 +194,14 @@ idp_status idp_dgsem_create_batch(const idp_mesh_desc *meshes, int32_t n_sims, i
 idp_status idp_dgsem_layout(const idp_ctx *ctx, int64_t *n_elems, int64_t *n_mortars,
                             int32_t *n_sims, int64_t *sim_elem_offsets);
 
+/* Element-pass launch configuration in use: elements per thread block, 1 if
+ * the grid is persistent (resident blocks looping over element batches) else
+ * 0, and the grid size. Before the first rhs/dt/step call of an autotuned
+ * context (elems_per_block = 0) all three are 0. Any pointer may be NULL.
+ * Host only; no device work. */
+idp_status idp_dgsem_launch_config(const idp_ctx *ctx, int32_t *elems_per_block, int32_t *persistent,
+                                   int32_t *grid);
+
 /* Right-hand side at time t (Eq. evolutionformula with the limited fluxes of
  * Sec. 2.3). dt == 0: the unlimited high-order DG right-hand side du/dt.
  * dt > 0: the limited forward-Euler increment (u_lim - u)/dt of one

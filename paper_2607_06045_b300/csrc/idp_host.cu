@@ -938,6 +938,16 @@ idp_status idp_dgsem_layout(const idp_ctx *c, int64_t *n_elems, int64_t *n_morta
     return IDP_OK;
 }
 
+idp_status idp_dgsem_launch_config(const idp_ctx *c, int32_t *elems_per_block, int32_t *persistent,
+                                   int32_t *grid) {
+    if (!c) return IDP_E_ARG;
+    const bool t = c->tuned;
+    if (elems_per_block) *elems_per_block = t ? c->epb : 0;
+    if (persistent) *persistent = t ? c->persistent : 0;
+    if (grid) *grid = t ? element_grid(c, c->epb, c->persistent, c->bps) : 0;
+    return IDP_OK;
+}
+
 idp_status idp_dgsem_rhs(idp_ctx *c, const double *u, double t, double dt, double *rhs, void *stream) {
     if (!c || !u || !rhs || u == rhs || !(dt >= 0.0) || !std::isfinite(dt)) return IDP_E_ARG;
     cudaStream_t st = (cudaStream_t)stream;

@@ -168,7 +168,7 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
         }
         const Prim<FT> pint = mortar_prim<NP, FT>(g, acc);
         FT f[4];
-        Prim<FT> ps;
+        Prim<FT> ps{};
         ps.v1 = dir == 0 ? s_pr[mi][NP + r][0] : FT(0);
         ps.v2 = dir == 1 ? s_pr[mi][NP + r][0] : FT(0);
         ps.p = s_pr[mi][NP + r][1];
@@ -176,8 +176,20 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
         const FT *us = s_uf[mi][NP + r];
         FT ui[4];
         for (int v = 0; v < 4; ++v) ui[v] = to_ft<FT>(s_ui[mi][r][v]);
-        if (low) llf_prim<FT, FT>(ui, pint, us, ps, dir, f);
-        else llf_prim<FT, FT>(us, ps, ui, pint, dir, f);
+        if constexpr (F32) {
+            if (low) llf_prim<FT, FT>(ui, pint, us, ps, dir, f);
+            else llf_prim<FT, FT>(us, ps, ui, pint, dir, f);
+        } else {
+            // operands selected per lane: the warp's mortars of either
+            // orientation share one flux evaluation
+            FT uL[4], uR[4];
+            for (int v = 0; v < 4; ++v) {
+                const FT o = us[v];
+                uL[v] = low ? ui[v] : o;
+                uR[v] = low ? o : ui[v];
+            }
+            llf_prim<FT, FT>(uL, pick_prim(low != 0, pint, ps), uR, pick_prim(low != 0, ps, pint), dir, f);
+        }
         for (int v = 0; v < 4; ++v) s_f[mi][r][v] = f[v];
     }
     __syncthreads();
@@ -526,7 +538,7 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
                         const int on = d == 0 ? n + (side == 0 ? -1 : 1) : n + (side == 0 ? -NP : NP);
                         const FT lo = interior ? s_l[le][d][interior ? on : n] : s_o[le][s][row];
                         const bool mort = !interior && ft != FT_CONF && ft != FT_BND;
-                        ds += mort ? lo : cc2 * (li > lo ? li : lo);
+                        ds += mort ? lo : cc2 * speed_max(li, lo);   // FP64: on the integer pipe
                     }
                 }
                 if constexpr (F32) val = f2d(gc.A4f * d2f(s_w[i] * s_w[j]) / ds * (1.0f - 4e-6f));

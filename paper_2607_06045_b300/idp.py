@@ -56,6 +56,7 @@ class LimiterStats(C.Structure):
 _lib = None
 
 EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", "idp_dgsem_layout",
+           "idp_dgsem_launch_config",
            "idp_dgsem_rhs", "idp_dgsem_dt", "idp_dgsem_step", "idp_dgsem_step_host", "idp_dgsem_integrals",
            "idp_dgsem_limiter_stats", "idp_dgsem_sync", "idp_dgsem_destroy", "idp_status_str",
            "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_dgsem_profile_kernels",
@@ -82,6 +83,8 @@ def lib():
                                              C.POINTER(Options), C.POINTER(vp)]
         L.idp_dgsem_layout.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32),
                                        C.POINTER(C.c_int64)]
+        L.idp_dgsem_launch_config.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32),
+                                              C.POINTER(C.c_int32)]
         L.idp_dgsem_rhs.argtypes = [vp, vp, C.c_double, C.c_double, vp, vp]
         L.idp_dgsem_dt.argtypes = [vp, vp, dp, dp, vp]
         L.idp_dgsem_step.argtypes = [vp, vp, C.c_int32, dp, dp, vp]
@@ -319,6 +322,13 @@ class Context:
         n += (1 if (M and self.opts.dt_rule != 0) else 0) + 1 + lob + (2 if (M and lim) else 0)   # stage 1
         n += 2 * ((1 if M else 0) + 1 + lob + (2 if (M and lim) else 0))   # stages 2, 3
         return n + 1                                                        # time advance
+
+    def idp_dgsem_launch_config(self):
+        """(elements per block, persistent grid 0/1, grid size) of the element pass; zeros before tuning."""
+        e, p, g = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().idp_dgsem_launch_config(self._h, C.byref(e), C.byref(p), C.byref(g)),
+               "idp_dgsem_launch_config")
+        return e.value, p.value, g.value
 
     def idp_dgsem_sync(self, stream=None):
         return lib().idp_dgsem_sync(self._h, _stream(stream))
