@@ -538,7 +538,7 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
                         const int on = d == 0 ? n + (side == 0 ? -1 : 1) : n + (side == 0 ? -NP : NP);
                         const FT lo = interior ? s_l[le][d][interior ? on : n] : s_o[le][s][row];
                         const bool mort = !interior && ft != FT_CONF && ft != FT_BND;
-                        ds += mort ? lo : cc2 * speed_max(li, lo);   // FP64: on the integer pipe
+                        ds += mort ? lo : cc2 * (li > lo ? li : lo);
                     }
                 }
                 if constexpr (F32) val = f2d(gc.A4f * d2f(s_w[i] * s_w[j]) / ds * (1.0f - 4e-6f));
