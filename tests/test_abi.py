@@ -33,6 +33,11 @@ def test_exports_every_declared_symbol():
     assert set(names) == set(idp.EXPORTS)
 
 
+def test_launch_config_rejects_null_context():
+    L = idp.lib()
+    assert L.idp_dgsem_launch_config(None, None, None, None) == 1   # IDP_E_ARG
+
+
 def test_status_strings_and_defaults():
     L = idp.lib()
     for code in range(9):

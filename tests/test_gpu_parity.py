@@ -259,11 +259,40 @@ def test_ragged_tails_every_launch_shape():
             for gm in (1, 2):
                 ctx = idp.Context(m, 3, precision=prec, elems_per_block=epb, grid_mode=gm)
                 outs.append(gpu_rhs(ctx, u, 0.0, dt))
+                e, p, g = ctx.idp_dgsem_launch_config()
+                nb = -(-m.n_elems // epb)
+                assert (e, p) == (epb, 1 if gm == 2 else 0)
+                assert g == nb if gm == 1 else 1 <= g <= nb
                 ctx.close()
         for r in outs[1:]:
             assert np.array_equal(r, outs[0])
         if prec == 0:
             assert rel_err(outs[0], r_o, scale) <= 1e-12
+
+
+def test_autotuned_step_launch_config():
+    """An autotuned context reports no launch before its first call and one
+    of the candidates after it; its steps equal, bit for bit, those of a
+    context with another fixed launch."""
+    import torch
+    m = W.cfg1_mesh()
+    u = W.cfg1_state(m, 3)
+    ctx = idp.Context(m, 3, limiting=2, cfl=0.5)
+    assert ctx.idp_dgsem_launch_config() == (0, 0, 0)
+    ua, ta = dev(u), np.zeros(1)
+    ctx.idp_dgsem_step(ua, 3, ta)
+    e, p, g = ctx.idp_dgsem_launch_config()
+    assert e in (1, 2, 4, 8, 16) and p in (0, 1) and g >= 1
+    other = 16 if e != 16 else 8
+    fixed = idp.Context(m, 3, limiting=2, cfl=0.5, elems_per_block=other, grid_mode=1)
+    ub, tb = dev(u), np.zeros(1)
+    fixed.idp_dgsem_step(ub, 3, tb)
+    torch.cuda.synchronize()
+    assert fixed.idp_dgsem_launch_config() == (other, 0, -(-m.n_elems // other))
+    assert ta[0] == tb[0]
+    assert np.array_equal(ua.cpu().numpy(), ub.cpu().numpy())
+    ctx.close()
+    fixed.close()
 
 
 def test_single_element_periodic():
