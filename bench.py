@@ -163,17 +163,17 @@ class Clocks:
 def build_workload(name, subset=None):
     from paper_2607_06045_b300 import workloads as W
     if name == "dmr":
-        m = W.cfg2_mesh()
-        return [m], W.cfg2_state(m, 3)
+        m = W.dmr_mesh()
+        return [m], W.dmr_state(m, 3)
     if name == "batched":
-        ms = W.cfg4_meshes(256, seed=0)
+        ms = W.batch_meshes(256, seed=0)
         rng = np.random.default_rng(1)
-        us = [W.cfg4_state(m, 3, rng) for m in ms]
+        us = [W.riemann4_state(m, 3, rng) for m in ms]
         keep = range(len(ms)) if subset is None else subset
         return [ms[i] for i in keep], W.concat_states([us[i] for i in keep])
     if name == "vacuum":
-        m, c = W.cfg5_mesh()
-        return [m], W.cfg5_state(m, 5, c)
+        m, c = W.blast_mesh()
+        return [m], W.blast_state(m, 5, c)
     raise ValueError(name)
 
 
@@ -570,8 +570,8 @@ def cpu_baseline_full():
     the full DMR workload."""
     import oracle
     from paper_2607_06045_b300 import workloads as W
-    m = W.cfg2_mesh()
-    u = W.cfg2_state(m, 3)
+    m = W.dmr_mesh()
+    u = W.dmr_state(m, 3)
     o = oracle.Oracle(m, 3)
     t0 = time.perf_counter()
     nsteps = 2
@@ -597,8 +597,8 @@ def run_reference(args):
         return
     import oracle
     from paper_2607_06045_b300 import workloads as W
-    m = W.cfg2_sample_mesh()
-    u = W.cfg2_state(m, 3)
+    m = W.dmr_sample_mesh()
+    u = W.dmr_state(m, 3)
     o = oracle.Oracle(m, 3)
     nodes = u.shape[1] * u.shape[2] * u.shape[3]
     t = 0.0

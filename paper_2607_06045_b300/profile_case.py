@@ -11,7 +11,7 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="dmr", choices=["dmr", "cfg1", "cfg5", "batched"])
+    ap.add_argument("--workload", default="dmr", choices=["dmr", "square", "blast", "batched"])
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--N", type=int, default=3)
@@ -25,15 +25,15 @@ def main(argv=None):
     from paper_2607_06045_b300 import workloads as W
     build.build()
     if a.workload == "dmr":
-        meshes = W.cfg2_mesh(); u = W.cfg2_state(meshes, a.N)
-    elif a.workload == "cfg1":
-        meshes = W.cfg1_mesh(); u = W.cfg1_state(meshes, a.N)
-    elif a.workload == "cfg5":
-        meshes, c = W.cfg5_mesh(); u = W.cfg5_state(meshes, a.N, c)
+        meshes = W.dmr_mesh(); u = W.dmr_state(meshes, a.N)
+    elif a.workload == "square":
+        meshes = W.square_mesh(); u = W.disc_wave_state(meshes, a.N)
+    elif a.workload == "blast":
+        meshes, c = W.blast_mesh(); u = W.blast_state(meshes, a.N, c)
     else:
-        meshes = W.cfg4_meshes(256, seed=0)
+        meshes = W.batch_meshes(256, seed=0)
         rng = np.random.default_rng(1)
-        u = W.concat_states([W.cfg4_state(m, a.N, rng) for m in meshes])
+        u = W.concat_states([W.riemann4_state(m, a.N, rng) for m in meshes])
     ctx = idp.Context(meshes, a.N, precision=a.precision, limiting=a.limiting, bounds=a.bounds,
                       entropy_bound=a.entropy, cfl=0.5, elems_per_block=a.epb)
     ud = torch.from_numpy(u).cuda()

@@ -222,13 +222,13 @@ def box_refined_mesh(nx0, ny0, box, rbox, base_level=0, bc=(BC_PERIODIC,) * 4):
     return mesh_from_map(lmap, L, nx0, ny0, box, bc=bc)
 
 
-def cfg1_mesh():
+def square_mesh():
     """Periodic unit square, 16 x 16 base grid, the central 4 x 4 block refined
     once: 304 elements and 16 hanging faces."""
     return box_refined_mesh(16, 16, (0.0, 0.0, 1.0, 1.0), (0.375, 0.375, 0.625, 0.625))
 
 
-def cfg1_state(mesh: Mesh, N: int, gamma=1.4):
+def disc_wave_state(mesh: Mesh, N: int, gamma=1.4):
     """Smooth density 1 + 0.5 sin(2 pi x) sin(2 pi y) with a disc r < 0.15 about
     the domain centre at rho = 2, p = 5 (p = 1 elsewhere); u = v = 0.1."""
     X, Y = node_coords(mesh, N)
@@ -244,7 +244,7 @@ DMR_POST = np.array([8.0, 8.25 * math.cos(math.pi / 6), -8.25 * math.sin(math.pi
 DMR_PRE = np.array([1.4, 0.0, 0.0, 1.0])
 
 
-def cfg2_mesh(seed=0, target=(54000, 66000), max_extra=3, nx0=256, ny0=64):
+def dmr_mesh(seed=0, target=(54000, 66000), max_extra=3, nx0=256, ny0=64):
     """[0,4] x [0,1], 256 x 64 base grid, up to three extra levels where a
     density-jump indicator fires across the 60 degree Mach-10 shock, balanced
     2:1; the indicator threshold is bisected until K lies in ``target``.
@@ -294,13 +294,13 @@ def cfg2_mesh(seed=0, target=(54000, 66000), max_extra=3, nx0=256, ny0=64):
     return m
 
 
-def cfg2_sample_mesh(seed=0):
+def dmr_sample_mesh(seed=0):
     """A 1/16-size instance of the same DMR workload (64 x 16 base grid, the
     same three-level shock refinement, K in [3400, 4100]) for CPU timing."""
-    return cfg2_mesh(seed=seed, target=(3400, 4100), nx0=64, ny0=16)
+    return dmr_mesh(seed=seed, target=(3400, 4100), nx0=64, ny0=16)
 
 
-def cfg2_state(mesh: Mesh, N: int, gamma=1.4):
+def dmr_state(mesh: Mesh, N: int, gamma=1.4):
     """Post-shock state left of x = 1/6 + y / sqrt(3), quiescent gas right of it."""
     X, Y = node_coords(mesh, N)
     left = X < 1.0 / 6.0 + Y / math.sqrt(3.0)
@@ -308,7 +308,7 @@ def cfg2_state(mesh: Mesh, N: int, gamma=1.4):
     return conserved(pr[0], pr[1], pr[2], pr[3], gamma)
 
 
-def cfg4_meshes(n_sims=256, seed=0):
+def batch_meshes(n_sims=256, seed=0):
     """Batched workload: base side s = round(8 * 16**U) per simulation, then 0-2
     refinement levels on 1-4 random rectangular patches, balanced 2:1; outflow
     boundaries on the unit square."""
@@ -338,7 +338,7 @@ def cfg4_meshes(n_sims=256, seed=0):
     return meshes
 
 
-def cfg4_state(mesh: Mesh, N: int, rng: np.random.Generator, gamma=1.4):
+def riemann4_state(mesh: Mesh, N: int, rng: np.random.Generator, gamma=1.4):
     """Seeded four-quadrant Riemann problem split at (0.5, 0.5): rho, p
     log-uniform in [0.1, 10], u, v uniform in [-1, 1] per quadrant."""
     X, Y = node_coords(mesh, N)
@@ -350,7 +350,7 @@ def cfg4_state(mesh: Mesh, N: int, rng: np.random.Generator, gamma=1.4):
     return conserved(rho_q[q], u_q[q], v_q[q], p_q[q], gamma)
 
 
-def cfg5_mesh(seed=0, n0=512):
+def blast_mesh(seed=0, n0=512):
     """Near-vacuum blast: n0 x n0 base grid on the unit square, two extra levels
     for leaves within r < 0.1 of a seeded centre in [0.3, 0.7]^2, balanced 2:1,
     outflow boundaries. Returns (mesh, centre)."""
@@ -367,7 +367,7 @@ def cfg5_mesh(seed=0, n0=512):
     return mesh_from_map(lmap, L, n0, n0, box, bc=(BC_OUTFLOW,) * 4), c
 
 
-def cfg5_state(mesh: Mesh, N: int, centre, gamma=1.4):
+def blast_state(mesh: Mesh, N: int, centre, gamma=1.4):
     """Background rho = 1e-6, p = 1e-9; disc r < 0.05 with rho = 1, p = 1e3."""
     X, Y = node_coords(mesh, N)
     disc = (X - centre[0]) ** 2 + (Y - centre[1]) ** 2 < 0.05 ** 2

@@ -121,4 +121,4 @@ def test_valid_mesh_without_gpu_is_a_cuda_error():
     import torch
     if torch.cuda.is_available():
         pytest.skip("GPU present")
-    assert _create(W.cfg1_mesh()) == idp.IDP_E_CUDA
+    assert _create(W.square_mesh()) == idp.IDP_E_CUDA

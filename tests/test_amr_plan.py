@@ -30,7 +30,7 @@ def _family_random(mesh, seed):
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
 def test_plan_matches_oracle_random(seed):
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     ind = _family_random(m, seed)
     pl = _both(m, ind, refine_threshold=0.7, coarsen_threshold=0.4, min_level=0, max_level=3)
     assert (pl[3] == 1).any()
@@ -50,8 +50,8 @@ def test_plan_matches_oracle_balance(periodic):
 
 
 def test_plan_matches_oracle_dmr_indicators():
-    m = W.cfg2_mesh()
-    u = W.cfg2_state(m, 3)
+    m = W.dmr_mesh()
+    u = W.dmr_state(m, 3)
     ind = amr.indicators(u, 3, amr.Params(indicator=amr.IND_MAX))
     pl = _both(m, ind, indicator=amr.IND_MAX, refine_threshold=0.3, coarsen_threshold=0.01, min_level=0,
                max_level=4)

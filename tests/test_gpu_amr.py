@@ -30,8 +30,8 @@ def dev(u):
 
 @pytest.mark.parametrize("N", [1, 3, 5])
 def test_indicators(N):
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, N)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, N)
     ctx = idp.Context(m, N)
     ud = dev(u)
     for kind in (amr.IND_HENNEMANN, amr.IND_LOHNER, amr.IND_MAX):
@@ -52,8 +52,8 @@ def _family_random(mesh, seed):
 
 @pytest.mark.parametrize("N", [2, 3, 5])
 def test_transfer(N):
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, N)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, N)
     pl = idp.idp_amr_plan(m, _family_random(m, 5), idp.amr_params(refine_threshold=0.8, coarsen_threshold=0.5,
                                                                       max_level=2))
     kind, src = pl[3], pl[4]
@@ -89,13 +89,13 @@ def test_transfer_near_vacuum():
 
 
 def test_adapt_and_step_loop():
-    """Five cycles of (adapt, 5 limited steps) on the periodic cfg1 data:
+    """Five cycles of (adapt, 5 limited steps) on the periodic refined-square data:
     mass, momentum and energy are conserved through the transfers and the
     steps, no invariant is violated, and the mesh follows the disc."""
     import torch
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     N = 3
-    u = W.cfg1_state(m, N)
+    u = W.disc_wave_state(m, N)
     ctx = idp.Context(m, N, limiting=2, cfl=0.5)
     ud = dev(u)
     I0 = ctx.idp_dgsem_integrals(ud)[0]

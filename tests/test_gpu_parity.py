@@ -60,9 +60,9 @@ def check_rhs(mesh, N, u, limiting, t=0.0, cfl=0.5, gamma=1.4, tol=1e-12, precis
 
 
 @pytest.mark.parametrize("limiting", [1, 2])
-def test_cfg1_rhs(limiting):
-    m = W.cfg1_mesh()
-    check_rhs(m, 3, W.cfg1_state(m, 3), limiting)
+def test_square_rhs(limiting):
+    m = W.square_mesh()
+    check_rhs(m, 3, W.disc_wave_state(m, 3), limiting)
 
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5, 6, 7])
@@ -90,14 +90,14 @@ def test_dmr_boundaries():
     m = W.box_refined_mesh(16, 4, (0.0, 0.0, 4.0, 1.0), (0.0, 0.0, 1.0, 0.5), bc=(W.BC_DMR,) * 4)
     m.dmr_post = W.DMR_POST.copy()
     m.dmr_pre = W.DMR_PRE.copy()
-    u = W.cfg2_state(m, 3)
+    u = W.dmr_state(m, 3)
     for t in (0.0, 0.05):
         check_rhs(m, 3, u, 2, t=t)
 
 
 def test_dt_parity():
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     o = oracle.Oracle(m, 3)
     for rule in (0, 1):
         ctx = idp.Context(m, 3, dt_rule=rule, cfl=0.7)
@@ -107,9 +107,9 @@ def test_dt_parity():
 
 
 @pytest.mark.parametrize("limiting", [1, 2])
-def test_cfg1_100_steps(limiting):
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+def test_square_100_steps(limiting):
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     o = oracle.Oracle(m, 3)
     u_o, t_o, dts, st = o.step(u, 100, cfl=0.5, limiting=limiting)
     ctx = idp.Context(m, 3, limiting=limiting, cfl=0.5)
@@ -130,8 +130,8 @@ def test_cfg1_100_steps(limiting):
 
 def test_epb_invariance():
     import torch
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     dt = oracle.Oracle(m, 3).dt(u, cfl=0.5)
     outs = []
     for epb in (1, 2, 4, 8, 16):
@@ -143,9 +143,9 @@ def test_epb_invariance():
 
 
 def test_batched_matches_individual():
-    ms = [W.cfg1_mesh(), W.box_refined_mesh(6, 4, (0.0, 0.0, 1.5, 1.0), (0.2, 0.2, 0.9, 0.6)),
+    ms = [W.square_mesh(), W.box_refined_mesh(6, 4, (0.0, 0.0, 1.5, 1.0), (0.2, 0.2, 0.9, 0.6)),
           W.uniform_mesh(5, 5, bc=(W.BC_OUTFLOW,) * 4)]
-    us = [W.cfg1_state(ms[0], 3), W.smooth_random_state(ms[1], 3, seed=3), W.random_state(ms[2], 3, seed=4)]
+    us = [W.disc_wave_state(ms[0], 3), W.smooth_random_state(ms[1], 3, seed=3), W.random_state(ms[2], 3, seed=4)]
     ctx = idp.Context(ms, 3, cfl=0.5)
     ub = W.concat_states(us)
     ud = dev(ub)
@@ -166,14 +166,14 @@ def test_batched_matches_individual():
 
 def test_conservation_and_free_stream():
     import torch
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     sh = (m.n_elems, 4, 4)
     uf = W.conserved(1.3 * np.ones(sh), 0.4 * np.ones(sh), -0.7 * np.ones(sh), 2.0 * np.ones(sh), 1.4)
     ctx = idp.Context(m, 3)
     r = gpu_rhs(ctx, uf, 0.0, 0.0)
     mm = oracle.Oracle(m, 3).masses()
     assert np.abs(r).max() < 1e-12 * 3.0 / mm.min()
-    u = W.cfg1_state(m, 3)
+    u = W.disc_wave_state(m, 3)
     ud = dev(u)
     I0 = ctx.idp_dgsem_integrals(ud)[0]
     t = np.zeros(1)
@@ -185,8 +185,8 @@ def test_conservation_and_free_stream():
 
 
 def test_invalid_state_reported():
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     u[0, 5, 1, 1] = -1.0
     ctx = idp.Context(m, 3)
     ud = dev(u)
@@ -198,8 +198,8 @@ def test_invalid_state_reported():
 
 def test_step_host_equals_device():
     import torch
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     ctx = idp.Context(m, 3)
     ud = dev(u)
     t1 = np.zeros(1)
@@ -212,20 +212,20 @@ def test_step_host_equals_device():
     ctx.close()
 
 
-def test_cfg2_full_size_rhs():
+def test_dmr_full_size_rhs():
     """Full-size DMR workload (about 60k elements) in the benchmark's launch
     configuration: the limited right-hand side on every node."""
-    m = W.cfg2_mesh()
-    u = W.cfg2_state(m, 3)
+    m = W.dmr_mesh()
+    u = W.dmr_state(m, 3)
     check_rhs(m, 3, u, 2)
 
 
-def test_fp32_form_error_cfg3():
+def test_fp32_form_error_high_degree():
     """FP32 form (flux arithmetic in FP32, limiter and sums in FP64) against the
     FP64 oracle: density L1 error and zero positivity violations."""
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     for N in (4, 7):
-        u = W.cfg1_state(m, N)
+        u = W.disc_wave_state(m, N)
         o = oracle.Oracle(m, N)
         nst = 20
         u_o, t_o, _, _ = o.step(u, nst, cfl=0.5)
@@ -275,8 +275,8 @@ def test_autotuned_step_launch_config():
     of the candidates after it; its steps equal, bit for bit, those of a
     context with another fixed launch."""
     import torch
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     ctx = idp.Context(m, 3, limiting=2, cfl=0.5)
     assert ctx.idp_dgsem_launch_config() == (0, 0, 0)
     ua, ta = dev(u), np.zeros(1)
@@ -314,19 +314,19 @@ def test_single_element_periodic():
 @pytest.mark.parametrize("N", [1, 3, 5])
 def test_combined_limiting_rhs(N):
     """Combined positivity/local limiting (Sec. 3.5): the limited right-hand
-    side on the cfg1 data, whose jump makes the shock indicator vary."""
-    m = W.cfg1_mesh()
-    check_rhs(m, N, W.cfg1_state(m, N), 3)
+    side on the refined-square data, whose jump makes the shock indicator vary."""
+    m = W.square_mesh()
+    check_rhs(m, N, W.disc_wave_state(m, N), 3)
 
 
 def test_combined_limiting_dmr_full_size():
-    m = W.cfg2_mesh()
-    check_rhs(m, 3, W.cfg2_state(m, 3), 3)
+    m = W.dmr_mesh()
+    check_rhs(m, 3, W.dmr_state(m, 3), 3)
 
 
 def test_combined_limiting_steps():
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     o = oracle.Oracle(m, 3)
     u_o, t_o, _, st_o = o.step(u, 100, cfl=0.5, limiting=3)
     ctx = idp.Context(m, 3, limiting=3, cfl=0.5)

@@ -12,7 +12,7 @@ by different iterations (bisection, Newton) with different logarithm and
 exponential routines, so the factors agree to the root's conditioning (the
 rounding of Psi over its slope) rather than to the rounding order, and the
 limiter's thresholds amplify such differences over many stages (measured on
-cfg1: 3e-13 after one step, 3e-10 to 8e-10 after 100).
+the refined square: 3e-13 after one step, 3e-10 to 8e-10 after 100).
 """
 import numpy as np
 import pytest
@@ -68,8 +68,8 @@ def check_rhs(mesh, N, u, limiting, bounds, entropy, t=0.0, cfl=0.5, tol=None, *
 @pytest.mark.parametrize("N", [1, 3, 5])
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_variant_rhs(N, variant):
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, N)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, N)
     r = check_rhs(m, N, u, 2, *variant)
     # the variant changes the result (it is not silently off)
     o = oracle.Oracle(m, N)
@@ -95,16 +95,16 @@ def test_variant_boundaries(bc):
 
 
 def test_variants_in_combined_limiting():
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     for N in (1, 3):
-        u = W.cfg1_state(m, N)
+        u = W.disc_wave_state(m, N)
         for v in VARIANTS:
             check_rhs(m, N, u, 3, *v)
 
 
 def test_variant_dmr_full_size():
-    m = W.cfg2_mesh()
-    u = W.cfg2_state(m, 3)
+    m = W.dmr_mesh()
+    u = W.dmr_state(m, 3)
     check_rhs(m, 3, u, 2, 1, 1)
     check_rhs(m, 3, u, 2, 0, 1)
 
@@ -112,8 +112,8 @@ def test_variant_dmr_full_size():
 @pytest.mark.parametrize("variant", VARIANTS)
 def test_variant_100_steps(variant):
     b, e = variant
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     o = oracle.Oracle(m, 3)
     u_o, t_o, _, st_o = o.step(u, 100, cfl=0.5, limiting=2, bounds=b, entropy=e)
     assert st_o["viol_eta"] == 0 and st_o["viol_rho"] == 0
@@ -145,9 +145,9 @@ def test_variant_100_steps(variant):
 
 
 def test_variant_batched_matches_individual():
-    ms = [W.cfg1_mesh(), W.box_refined_mesh(6, 4, (0.0, 0.0, 1.5, 1.0), (0.2, 0.2, 0.9, 0.6)),
+    ms = [W.square_mesh(), W.box_refined_mesh(6, 4, (0.0, 0.0, 1.5, 1.0), (0.2, 0.2, 0.9, 0.6)),
           W.uniform_mesh(5, 5, bc=(W.BC_OUTFLOW,) * 4)]
-    us = [W.cfg1_state(ms[0], 3), W.smooth_random_state(ms[1], 3, seed=3), W.random_state(ms[2], 3, seed=4)]
+    us = [W.disc_wave_state(ms[0], 3), W.smooth_random_state(ms[1], 3, seed=3), W.random_state(ms[2], 3, seed=4)]
     ctx = idp.Context(ms, 3, cfl=0.5, limiting=2, bounds=1, entropy_bound=1)
     ud = dev(W.concat_states(us))
     t = np.zeros(3)
@@ -165,8 +165,8 @@ def test_variant_batched_matches_individual():
 def test_variant_launch_counts():
     """The step launches the kernels launches_per_step counts: the pre-pass
     and the mortar gather appear once per stage with low-order bounds."""
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     for b, e in [(0, 0)] + VARIANTS:
         ctx = idp.Context(m, 3, limiting=2, bounds=b, entropy_bound=e, cfl=0.5)
         ud = dev(u)
@@ -189,9 +189,9 @@ def test_variant_launch_counts():
 @pytest.mark.parametrize("N", [1, 3, 5])
 def test_chandrashekar_rhs(N):
     """Chandrashekar's flux (R23): unlimited, locally limited and combined
-    right-hand sides on the cfg1 data."""
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, N)
+    right-hand sides on the refined-square data."""
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, N)
     o = oracle.Oracle(m, N, volume_flux=1)
     dt_idp = o.dt(u, cfl=1.0)
     scale = rhs_scale(u, dt_idp)
@@ -279,8 +279,8 @@ def test_jet_full_size_fp32_invariants():
 
 @pytest.mark.parametrize("N", [1, 2, 3, 5])
 def test_all_to_all_mortar_rhs(N):
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, N)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, N)
     o = oracle.Oracle(m, N, mortar_low=1)
     dt_idp = o.dt(u, cfl=1.0)
     scale = rhs_scale(u, dt_idp)
@@ -302,8 +302,8 @@ def test_all_to_all_mortar_rhs(N):
 
 
 def test_all_to_all_mortar_steps():
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     o = oracle.Oracle(m, 3, mortar_low=1)
     u_o, t_o, _, _ = o.step(u, 100, cfl=0.5, limiting=2)
     ctx = idp.Context(m, 3, limiting=2, mortar_low=1, cfl=0.5)

@@ -42,9 +42,9 @@ def invariants_clean(ctx):
 
 
 def test_vacuum_reduced_parity():
-    m, c = W.cfg5_mesh(n0=16)
+    m, c = W.blast_mesh(n0=16)
     N = 5
-    u = W.cfg5_state(m, N, c)
+    u = W.blast_state(m, N, c)
     o = oracle.Oracle(m, N)
     # limited right-hand side
     dt_idp = o.dt(u, 0.0, cfl=1.0)
@@ -84,9 +84,9 @@ def test_vacuum_reduced_parity():
 
 
 def test_vacuum_full_size_fp32_200_steps():
-    m, c = W.cfg5_mesh()
+    m, c = W.blast_mesh()
     N = 5
-    u = W.cfg5_state(m, N, c)
+    u = W.blast_state(m, N, c)
     ctx = idp.Context(m, N, precision=1, limiting=2)
     ud = dev(u)
     I0 = ctx.idp_dgsem_integrals(ud)[0]
@@ -107,8 +107,8 @@ def test_vacuum_full_size_fp32_200_steps():
 
 
 def test_dmr_500_steps_fp64():
-    m = W.cfg2_mesh()
-    u = W.cfg2_state(m, 3)
+    m = W.dmr_mesh()
+    u = W.dmr_state(m, 3)
     ctx = idp.Context(m, 3, limiting=2, cfl=0.5)
     ud = dev(u)
     t = np.zeros(1)
@@ -122,9 +122,9 @@ def test_dmr_500_steps_fp64():
 
 
 def test_batched_full_size_sampled():
-    ms = W.cfg4_meshes(256, seed=0)
+    ms = W.batch_meshes(256, seed=0)
     rng = np.random.default_rng(1)
-    us = [W.cfg4_state(mm, 3, rng) for mm in ms]
+    us = [W.riemann4_state(mm, 3, rng) for mm in ms]
     ub = W.concat_states(us)
     smallest = np.argsort([mm.n_elems for mm in ms])[:3].tolist()
     nst = 2

@@ -29,7 +29,7 @@ def lagrange(xs, i, x):
 
 @pytest.mark.parametrize("N", [1, 2, 3, 4, 5])
 def test_weights_closed_form_and_sums(N):
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     o = oracle.Oracle(m, N, mortar_low=1)
     wa = o.mortar_weights()
     xi, w = oracle.lgl(N)
@@ -53,7 +53,7 @@ def test_weights_closed_form_and_sums(N):
 
 
 def test_graph_identities_and_conservation():
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     o = oracle.Oracle(m, 3, mortar_low=1)
     off, j, cx, cy = o.graph()
     sx, sy = np.add.reduceat(cx, off[:-1]), np.add.reduceat(cy, off[:-1])
@@ -67,7 +67,7 @@ def test_graph_identities_and_conservation():
         assert abs(c[0] + d[0]) < 1e-18 and abs(c[1] + d[1]) < 1e-18
     # more graph edges than the sparse weights
     assert len(j) > len(oracle.Oracle(m, 3).graph()[1])
-    u = W.cfg1_state(m, 3)
+    u = W.disc_wave_state(m, 3)
     mm = o.masses()
     dt = o.dt(u, cfl=0.5)
     for lim in (0, 2):
@@ -77,7 +77,7 @@ def test_graph_identities_and_conservation():
 
 
 def test_free_stream_and_convexity():
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     o = oracle.Oracle(m, 3, mortar_low=1)
     sh = (m.n_elems, 4, 4)
     uf = W.conserved(1.3 * np.ones(sh), 0.4 * np.ones(sh), -0.7 * np.ones(sh), 2.0 * np.ones(sh), G)

@@ -178,9 +178,9 @@ def test_plan_balance_propagates(periodic):
 
 
 def test_plan_random_is_balanced_and_transfer_conserves():
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     N = 3
-    u = W.cfg1_state(m, N)
+    u = W.disc_wave_state(m, N)
     rng = np.random.default_rng(5)
     # one random value per level-0 cell, so that whole families can coarsen
     cell = rng.uniform(0, 1, (m.nx0, m.ny0))

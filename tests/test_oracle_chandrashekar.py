@@ -93,7 +93,7 @@ def test_kinetic_energy_preserving_form():
 
 
 def test_scheme_forms_and_free_stream():
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     o = oracle.Oracle(m, 3, volume_flux=1)
     u = W.smooth_random_state(m, 3, seed=4)
     r1, r2 = o.dg_residual(u), o.dg_residual(u, form="fd")

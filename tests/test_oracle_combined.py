@@ -60,16 +60,16 @@ def test_combined_reduces_to_positivity_on_smooth_data():
 
 
 def test_combined_reduces_to_local_at_degree_one():
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 1)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 1)
     o = oracle.Oracle(m, 1)
     dt = 0.5 * o.dt(u, cfl=1.0)
     assert np.array_equal(o.rhs(u, dt=dt, limiting=3), o.rhs(u, dt=dt, limiting=2))
 
 
 def test_combined_positivity_and_conservation():
-    m = W.cfg1_mesh()
-    u = W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    u = W.disc_wave_state(m, 3)
     o = oracle.Oracle(m, 3)
     # the blend is active: neither of the two pure schemes
     dt = 0.5 * o.dt(u, cfl=1.0)

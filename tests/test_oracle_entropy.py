@@ -114,8 +114,8 @@ def _bar_state_eta_min(o, u):
 
 @pytest.fixture(scope="module")
 def disc():
-    m = W.cfg1_mesh()
-    return m, oracle.Oracle(m, 3), W.cfg1_state(m, 3)
+    m = W.square_mesh()
+    return m, oracle.Oracle(m, 3), W.disc_wave_state(m, 3)
 
 
 def _stage(o, u, dt, **kw):

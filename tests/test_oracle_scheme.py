@@ -29,9 +29,9 @@ G = 1.4
 
 
 @pytest.fixture(scope="module")
-def cfg1():
-    m = W.cfg1_mesh()
-    return m, oracle.Oracle(m, 3), W.cfg1_state(m, 3)
+def square():
+    m = W.square_mesh()
+    return m, oracle.Oracle(m, 3), W.disc_wave_state(m, 3)
 
 
 def euler_flux(u, n):
@@ -41,8 +41,8 @@ def euler_flux(u, n):
     return np.array([rho * vn, m1 * vn + p * n[0], m2 * vn + p * n[1], (E + p) * vn])
 
 
-def test_evolution_equals_flux_differencing(cfg1):
-    m, o, u = cfg1
+def test_evolution_equals_flux_differencing(square):
+    m, o, u = square
     r1 = o.dg_residual(u)
     r2 = o.dg_residual(u, form="fd")
     assert np.abs(r1 - r2).max() <= 1e-13 * np.abs(r1).max()
@@ -51,8 +51,8 @@ def test_evolution_equals_flux_differencing(cfg1):
     assert np.abs(r1 - r2).max() <= 1e-13 * np.abs(r1).max()
 
 
-def test_free_stream_nonconforming(cfg1):
-    m, o, _ = cfg1
+def test_free_stream_nonconforming(square):
+    m, o, _ = square
     sh = (m.n_elems, 4, 4)
     u = W.conserved(1.3 * np.ones(sh), 0.4 * np.ones(sh), -0.7 * np.ones(sh), 2.0 * np.ones(sh), G)
     mm = o.masses()
@@ -84,8 +84,8 @@ def test_dirichlet_free_stream():
 
 
 @pytest.mark.parametrize("limiting", [0, 1, 2])
-def test_conservation_of_residual(cfg1, limiting):
-    m, o, u = cfg1
+def test_conservation_of_residual(square, limiting):
+    m, o, u = square
     mm = o.masses()
     dt = o.dt(u, cfl=0.5)
     r = o.rhs(u, dt=dt if limiting else 0.0, limiting=limiting)
@@ -95,8 +95,8 @@ def test_conservation_of_residual(cfg1, limiting):
         assert abs(tot) <= 1e-13 * scale, (v, tot, scale)
 
 
-def test_conservation_100_steps(cfg1):
-    m, o, u = cfg1
+def test_conservation_100_steps(square):
+    m, o, u = square
     I0 = o.integrals(u)
     un, t, dts, st = o.step(u, 100, cfl=0.5, limiting=2)
     I1 = o.integrals(un)
@@ -109,8 +109,8 @@ def test_conservation_100_steps(cfg1):
     assert np.all(dts > 0)
 
 
-def test_metric_identities(cfg1):
-    m, o, _ = cfg1
+def test_metric_identities(square):
+    m, o, _ = square
     off, j, cx, cy = o.graph()
     nn = len(off) - 1
     sx = np.add.reduceat(cx, off[:-1])
@@ -150,15 +150,15 @@ def bar_state_residual(o, u, mesh):
     return res.reshape(u.shape)
 
 
-def test_bar_state_form(cfg1):
-    m, o, u = cfg1
+def test_bar_state_form(square):
+    m, o, u = square
     r_cd, _ = o.fv_residual(u)
     r_bar = bar_state_residual(o, u, m)
     assert np.abs(r_cd - r_bar).max() <= 1e-12 * np.abs(r_cd).max()
 
 
 def test_low_order_step_is_convex():
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     o = oracle.Oracle(m, 3)
     u = W.random_state(m, 3, seed=3, rho_range=(0.01, 10.0), p_range=(0.01, 10.0), vmax=3.0)
     dt = o.dt(u, cfl=1.0)
@@ -186,8 +186,8 @@ def test_smooth_data_no_limiting():
     assert np.abs(o.rhs(u, dt=dt, limiting=0) - r_dg).max() == 0.0
 
 
-def test_local_bounds_after_stage(cfg1):
-    m, o, u = cfg1
+def test_local_bounds_after_stage(square):
+    m, o, u = square
     dt = o.dt(u, cfl=0.5)
     st = np.zeros(16); oracle.lib().orc_stats_init(oracle._d(st))
     _, ut = o.stage(u, 0.0, dt, limiting=2, stats=st)
@@ -212,7 +212,7 @@ def _mirror_maps(mesh, np_):
 
 
 def test_mirror_and_transpose_symmetry():
-    m = W.cfg1_mesh()
+    m = W.square_mesh()
     o = oracle.Oracle(m, 3)
     X, Y = W.node_coords(m, 3)
     # symmetric under x -> 1 - x and under x <-> y

@@ -30,7 +30,7 @@ def test_noalloc_integrals_match_context_integrals():
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
     build.build()
-    cases = [([W.cfg1_mesh(), W.box_refined_mesh(6, 4, (0.0, 0.0, 1.5, 1.0), (0.2, 0.2, 0.9, 0.6))], 4),
+    cases = [([W.square_mesh(), W.box_refined_mesh(6, 4, (0.0, 0.0, 1.5, 1.0), (0.2, 0.2, 0.9, 0.6))], 4),
              ([W.uniform_mesh(5, 3, (0.0, 0.0, 2.0, 1.0), bc=(W.BC_OUTFLOW,) * 4)], 3)]
     for call, (meshes, N) in enumerate(cases):
         us = [W.random_state(m, N, seed=call * 10 + k) for k, m in enumerate(meshes)]
