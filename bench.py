@@ -515,7 +515,7 @@ def run_ours(args):
         "data": "synthetic",
         "config": dict(DMR_CONFIG, precision="fp64", l2="flushed between steps (256 MiB write)",
                        parallelism=f"replicas x{world}", element_launch=r64["launch"]),
-        "roofline": {"bound": "alu", "kernel": "k_element (element pass, FP64 path)",
+        "roofline": {"bound": "alu", "kernel": "k_face + k_element (element pass, FP64 path)",
                      "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                      "peak_source": f"derived: {SMS} SMs x {DFMA_PER_CLK_SM} FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz",
                      "peak_probe": fp64_probe,

@@ -251,7 +251,8 @@ enum {
     IDP_K_TIME_ADVANCE = 6, /* per-simulation time */
     IDP_K_ELEMENT_LO = 7,   /* low-order pre-pass of the element pass (bounds 1) */
     IDP_K_MORTAR_LOB = 8,   /* low-order bounds across mortars (bounds 1) */
-    IDP_NKERNELS = 9
+    IDP_K_FACE = 9,         /* conforming-face fluxes of the FP64 element pass (part of it) */
+    IDP_NKERNELS = 10
 };
 
 /* Measurement support (the paper has no counterpart). mode 1: each step's
@@ -260,7 +261,9 @@ enum {
  * and around every kernel launch; mode 0: off. In modes 1 and 2
  * idp_dgsem_step synchronises after every step to accumulate the durations.
  * idp_dgsem_profile_read returns the accumulated element-pass milliseconds
- * and launches, and step milliseconds and steps (any pointer may be NULL;
+ * (mode 2: the element kernel plus, in the FP64 path, the conforming-face
+ * kernel that feeds it) and element-kernel launches, and step milliseconds
+ * and steps (any pointer may be NULL;
  * reset != 0 clears them). idp_dgsem_profile_kernels writes, for each kernel
  * kind k < IDP_NKERNELS, the accumulated milliseconds ms[k] and launches
  * launches[k] of mode 2 (caller arrays of IDP_NKERNELS entries, either may be

@@ -45,6 +45,9 @@ struct StageArgs {
     int pass;             // 1: low-order pre-pass (writes lofv and stops after the low-order update)
     double *lofv;         // [2][K (N+1)^2]: rho_FV and s(u_FV) of every node (pre-pass output)
     int vflux;            // volume flux: 0 Ranocha, 1 Chandrashekar (extended kernel)
+    // FP64 path (default kernel): conforming-face data of this stage's state
+    // from k_face, layout as k_face writes it
+    const double *fbuf;
 };
 
 __device__ __forceinline__ double stage_dt(const StageArgs &A, int sim) {
@@ -52,6 +55,45 @@ __device__ __forceinline__ double stage_dt(const StageArgs &A, int sim) {
 }
 __device__ __forceinline__ double stage_time(const StageArgs &A, int sim, double dt) {
     return A.mode == 0 ? A.t : A.t_sim[sim] + A.tstage * dt;
+}
+
+// Conforming faces of the FP64 element pass, each formed once: for the +x
+// and +y side of every element whose neighbour there is conforming, at each
+// face node t, the LLF flux along +x/+y scaled by w_t |face|/2 (left/bottom
+// state first), the bar-state density across the face and the FP32 term
+// 2 d of the time-step statistic. The element pass of both elements reads
+// them instead of forming the flux itself; the operations are those it
+// would apply. Entry (2 e + d)(N+1) + t of F = 2 K (N+1): flux [4][F]
+// doubles, bar state [F] doubles, then [F] floats.
+template <int NP>
+__global__ void __launch_bounds__(256) k_face(MeshDev mesh, const double *__restrict__ u, Gas G,
+                                              const Ops *__restrict__ ops, double *__restrict__ fb) {
+    const size_t KN = (size_t)mesh.K * NP * NP;
+    const long long F = 2ll * mesh.K * NP;
+    float *fl = reinterpret_cast<float *>(fb + 5 * F);
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < F;
+         k += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(k % NP), d = (int)((k / NP) & 1), e = (int)(k / (2 * NP));
+        const uchar4 ftv = mesh.ftype[e];
+        if ((d == 0 ? ftv.y : ftv.w) != FT_CONF) continue;
+        const int4 nb4 = mesh.fnbr[e];
+        const int nb = d == 0 ? nb4.y : nb4.w, s = 2 * d + 1;
+        const size_t gl = (size_t)e * NP * NP + face_node<NP>(s, t);
+        const size_t gr = (size_t)nb * NP * NP + face_node<NP>(s ^ 1, t);
+        double uL[4], uR[4];
+        for (int v = 0; v < 4; ++v) { uL[v] = u[v * KN + gl]; uR[v] = u[v * KN + gr]; }
+        const Prim<double> pL = make_prim<double>(G, uL[0], uL[1], uL[2], uL[3], false);
+        const Prim<double> pR = make_prim<double>(G, uR[0], uR[1], uR[2], uR[3], false);
+        double f[4];
+        const double lam = llf_prim<double, double>(uL, pL, uR, pR, d, f);
+        const GeoC gc = mesh.geoc[e];
+        const double wh = ops->w[t] * (d == 0 ? gc.hy : gc.hx);
+        for (int v = 0; v < 4; ++v) fb[v * F + k] = wh * f[v];
+        const double i2l = 0.5 * fast_rcp(lam);
+        const double mL = d == 0 ? uL[1] : uL[2], mR = d == 0 ? uR[1] : uR[2];
+        fb[4 * F + k] = 0.5 * (uL[0] + uR[0]) - (mR - mL) * i2l;
+        fl[k] = d2f(ops->w[t]) * (d == 0 ? gc.hyf : gc.hxf) * d2f(lam);
+    }
 }
 
 // Shared memory of one element. Arrays whose lifetimes (in phases P0..P5 of
@@ -232,6 +274,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
     constexpr int NN = NP * NP, N = NP - 1, NPAIR = SM::NPAIR, NIF = SM::NIF;
     constexpr int NT = ElemLaunch<NP, EPB>::threads;
     constexpr bool F32 = sizeof(FT) == 4;
+    // FP64 default kernel: conforming faces come from k_face
+    constexpr bool FACEBUF = !F32 && !EXT;
     extern __shared__ __align__(16) unsigned char smraw[];
     SM *sm = reinterpret_cast<SM *>(smraw);
     // reference tables: w, 1/w, Sbar, w_i w_j, 1/(w_i w_j) and FP32 copies
@@ -313,10 +357,12 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
             SM &S = sm[le];
             if (ft == FT_CONF) {
-                int4 nb4 = mesh.fnbr[e];
-                int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
-                size_t gi = (size_t)nb * NN + face_node<NP>(s ^ 1, t);
-                for (int v = 0; v < 4; ++v) S.outs[s][t][v] = A.u[v * KN + gi];
+                if constexpr (!FACEBUF) {
+                    int4 nb4 = mesh.fnbr[e];
+                    int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
+                    size_t gi = (size_t)nb * NN + face_node<NP>(s ^ 1, t);
+                    for (int v = 0; v < 4; ++v) S.outs[s][t][v] = A.u[v * KN + gi];
+                }
             } else if (ft == FT_BND) {
                 size_t gi = (size_t)e * NN + face_node<NP>(s, t);
                 double in[4] = {A.u[gi], A.u[KN + gi], A.u[2 * KN + gi], A.u[3 * KN + gi]};
@@ -377,6 +423,20 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     S.f2d[s][t] = d2f(sl.dsum[q]);
                 }
                 continue;
+            }
+            if constexpr (FACEBUF) {
+                if (ft == FT_CONF) {
+                    // the face's entry belongs to the element on its left/bottom
+                    int owner = e;
+                    if (!(s & 1)) { const int4 nb4 = mesh.fnbr[e]; owner = s == 0 ? nb4.x : nb4.z; }
+                    const long long F = 2ll * mesh.K * NP, q = (2ll * owner + (s >> 1)) * NP + t;
+                    for (int v = 0; v < 4; ++v) S.face[s][t][v] = A.fbuf[v * F + q];
+                    const double fbv = A.fbuf[4 * F + q];
+                    S.fbar[s][t] = fbv;
+                    S.fbar2[s][t] = fbv;
+                    S.f2d[s][t] = reinterpret_cast<const float *>(A.fbuf + 5 * F)[q];
+                    continue;
+                }
             }
             int d = s >> 1, n = face_node<NP>(s, t);
             const double *out = S.outs[s][t];

@@ -470,6 +470,8 @@ struct idp_ctx {
     int lob = 0;               // low-order bounds (pre-pass + mortar gather each stage)
     int ent_bar = 0;           // entropy bound with bar-state bounds (mortar bar-state entropies)
     double *d_lofv = nullptr;  // [2][K (N+1)^2] pre-pass output
+    int facebuf = 0;           // FP64 default kernel: conforming faces from k_face
+    double *d_fbuf = nullptr;  // k_face output: [5][2 K (N+1)] doubles + [2 K (N+1)] floats
     // optional timing: 1 step spans around the graph launches; 2 steps
     // launched without the graph, with element-pass events
     int prof = 0;
@@ -513,6 +515,7 @@ StageArgs base_args(idp_ctx *c) {
     A.lob = c->lob;
     A.pass = 0;
     A.lofv = c->d_lofv;
+    A.fbuf = c->d_fbuf;
     A.vflux = c->opt.volume_flux;
     return A;
 }
@@ -567,7 +570,13 @@ void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mo
             kt_end(c, st, k);
         }
     }
-    int k = kt_begin(c, st, IDP_K_ELEMENT);
+    int k;
+    if (c->facebuf) {
+        k = kt_begin(c, st, IDP_K_FACE);
+        c->L.face(st, c->mesh, A.u, A.gas, c->d_ops, c->d_fbuf, c->num_sms);
+        kt_end(c, st, k);
+    }
+    k = kt_begin(c, st, IDP_K_ELEMENT);
     c->L.element(c->opt.precision, c->ext, c->epb, grid, st, c->mesh, c->slots, A);
     kt_end(c, st, k);
     if (c->M > 0 && !dgmode) {
@@ -657,6 +666,7 @@ idp_status autotune(idp_ctx *c, const double *u, cudaStream_t st, double dt, int
     StageArgs A = base_args(c);
     A.mode = 0; A.u = u; A.out = c->d_buf1; A.dt = dt; A.t = 0.0; A.collect = 0;
     if (step_mode) { A.mode = 1; A.un = u; A.comb = 2; A.tstage = 0.5; }
+    if (c->facebuf) c->L.face(st, c->mesh, u, A.gas, c->d_ops, c->d_fbuf, c->num_sms);   // faces of u, once
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -760,6 +770,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     c->lob = o.limiting >= 2 && o.bounds == 1;
     c->ext = (o.limiting >= 2 && (o.bounds == 1 || o.entropy_bound == 1)) || o.volume_flux == 1;
     c->ent_bar = o.limiting >= 2 && o.entropy_bound == 1 && o.bounds == 0;
+    c->facebuf = o.precision == 0 && !c->ext;
     c->K = (long long)H.geom.size(); c->M = (long long)H.m_large.size();
     c->sim_off = H.sim_off;
     for (const Geo &g : H.geom) c->total_area += g.z * g.w;
@@ -874,6 +885,10 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(cudaMalloc(&c->d_part, sizeof(double) * 4 * (size_t)c->K));
     if (ok) chk(cudaMalloc(&c->d_aind, sizeof(double) * (size_t)c->K));
     if (ok) chk(cudaMemset(c->d_aind, 0, sizeof(double) * (size_t)c->K));
+    if (ok && c->facebuf) {
+        const size_t F = (size_t)2 * c->K * c->NP;
+        chk(cudaMalloc(&c->d_fbuf, sizeof(double) * 5 * F + sizeof(float) * F));
+    }
     if (ok && c->lob) chk(cudaMalloc(&c->d_lofv, sizeof(double) * 2 * kn));
     if (ok && c->lob) chk(cudaMemset(c->d_lofv, 0, sizeof(double) * 2 * kn));
     if (ok) chk(cudaMalloc(&c->d_intout, sizeof(double) * 4 * n_sims));
@@ -1158,7 +1173,7 @@ idp_status idp_dgsem_profile(idp_ctx *c, int32_t mode) {
 idp_status idp_dgsem_profile_read(idp_ctx *c, double *element_ms, int64_t *element_launches, double *step_ms,
                                   int64_t *steps, int32_t reset) {
     if (!c) return IDP_E_ARG;
-    if (element_ms) *element_ms = c->kms[IDP_K_ELEMENT];
+    if (element_ms) *element_ms = c->kms[IDP_K_ELEMENT] + c->kms[IDP_K_FACE];
     if (element_launches) *element_launches = c->kcnt[IDP_K_ELEMENT];
     if (step_ms) *step_ms = c->prof_step_ms;
     if (steps) *steps = c->prof_steps;
@@ -1400,7 +1415,7 @@ void idp_dgsem_destroy(idp_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    void *ptrs[] = {c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+    void *ptrs[] = {c->d_fbuf, c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
                     c->d_msmall, c->d_mnslot, c->d_siminfo, c->d_slot_block, c->d_buf1, c->d_buf2, c->d_hostbuf,
                     c->d_dtmin, c->d_tsim, c->d_dtlast, c->d_status, c->d_stats, c->d_part, c->d_intout, c->d_off};
     for (void *p : ptrs)

@@ -20,6 +20,9 @@ struct Launchers {
     cudaError_t (*element_prepare)(int fp32, int ext, int epb, int *blocks_per_sm);
     void (*element)(int fp32, int ext, int epb, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
                     const StageArgs &a);
+    // conforming-face fluxes of the FP64 element pass (k_face)
+    void (*face)(cudaStream_t st, const MeshDev &m, const double *u, const Gas &gas, const Ops *ops, double *fbuf,
+                 int num_sms);
     void (*mortar_flux)(int fp32, int ent, int a2a, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
                         const double *u, const Gas &gas, const Ops *ops);
     void (*mortar_lob)(cudaStream_t st, const MeshDev &m, const SlotsDev &s, const Ops *ops, const double *lofv,

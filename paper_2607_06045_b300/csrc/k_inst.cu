@@ -75,6 +75,13 @@ void element(int fp32, int ext, int epb, int grid, cudaStream_t st, const MeshDe
     IDP_EPB_SWITCH(el_launch, grid, st, m, s, a)
 }
 
+void face(cudaStream_t st, const MeshDev &m, const double *u, const Gas &gas, const Ops *ops, double *fbuf,
+          int num_sms) {
+    const long long F = 2ll * m.K * NP;
+    const int blocks = (int)std::max<long long>(1, std::min<long long>((F + 255) / 256, (long long)num_sms * 16));
+    k_face<NP><<<blocks, 256, 0, st>>>(m, u, gas, ops, fbuf);
+}
+
 void mortar_flux(int fp32, int ent, int a2a, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s,
                  const double *u, const Gas &gas, const Ops *ops) {
     constexpr int T = 32 * MORTARS_PER_BLOCK;
@@ -148,6 +155,7 @@ Launchers IDP_CAT(launchers_np, IDP_NP)() {
     L.element_threads = element_threads;
     L.element_prepare = element_prepare;
     L.element = element;
+    L.face = face;
     L.mortar_flux = mortar_flux;
     L.mortar_lob = mortar_lob;
     L.mortar_limit = mortar_limit;

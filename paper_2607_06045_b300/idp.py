@@ -144,7 +144,7 @@ def idp_eval_math(fn, x, y, stream=None):
 
 # kernel kinds of one step, in the order of the IDP_K_* constants
 KERNELS = ["dt_init", "mortar_flux", "dt", "element", "mortar_limit", "mortar_apply", "time_advance",
-           "element_lo", "mortar_lob"]
+           "element_lo", "mortar_lob", "face"]
 
 NOALLOC_MAX_ELEMS = 1 << 19
 
@@ -318,9 +318,13 @@ class Context:
         lim = self.opts.limiting > 0
         # low-order bounds: a pre-pass over the elements and a mortar gather
         lob = (1 + (1 if M else 0)) if (self.opts.limiting >= 2 and self.opts.bounds == 1) else 0
+        # FP64 path, default kernel: the conforming-face kernel before each element pass
+        o = self.opts
+        ext = (o.limiting >= 2 and (o.bounds == 1 or o.entropy_bound == 1)) or o.volume_flux == 1
+        el = 2 if (o.precision == 0 and not ext) else 1
         n = 1 + (1 if (M and self.opts.dt_rule == 0) else 0) + 1          # dt init, mortar flux, dt
-        n += (1 if (M and self.opts.dt_rule != 0) else 0) + 1 + lob + (2 if (M and lim) else 0)   # stage 1
-        n += 2 * ((1 if M else 0) + 1 + lob + (2 if (M and lim) else 0))   # stages 2, 3
+        n += (1 if (M and self.opts.dt_rule != 0) else 0) + el + lob + (2 if (M and lim) else 0)   # stage 1
+        n += 2 * ((1 if M else 0) + el + lob + (2 if (M and lim) else 0))   # stages 2, 3
         return n + 1                                                        # time advance
 
     def idp_dgsem_launch_config(self):

@@ -140,13 +140,27 @@ def mortar_apply_ops_per_node(precision: int = 0) -> Ops:
 
 
 def kernel_work(N: int, precision: int, K: int, M: int, n_mnodes: int, w_div: float, w_sqrt: float,
-                w_log: float) -> dict:
-    """Per launch: (FP64 DFMA-equivalent flops, HBM bytes) of each kernel."""
+                w_log: float, face_kernel=None) -> dict:
+    """Per launch: (FP64 DFMA-equivalent flops, HBM bytes) of each kernel.
+    With the conforming-face kernel (the FP64 path's default element kernel)
+    the face fluxes (row a4) are its work and the rest the element kernel's;
+    its bytes are the two face-node states it reads and the 44 bytes per face
+    node it writes."""
     nodes = K * (N + 1) ** 2
     Q = 3 * (N + 1)
     w = (w_div, w_sqrt, w_log)
+    if face_kernel is None:
+        face_kernel = precision == 0
+    rows = element_ops_per_node(N, precision)
+    el_flops = element_flops(N, precision, *w) * nodes
+    face = {}
+    if face_kernel:
+        fa = 2.0 * rows["a4_face_flux"].dfma_eq(*w) * nodes
+        face = {"face": (fa, (64.0 + 44.0) * 2.0 / (N + 1) * nodes)}
+        el_flops -= fa
     return {
-        "element": (element_flops(N, precision, *w) * nodes, BYTES_PER_NODE_STAGE * nodes),
+        **face,
+        "element": (el_flops, BYTES_PER_NODE_STAGE * nodes),
         "dt": (2.0 * dt_ops_per_node(N, precision).dfma_eq(*w) * nodes, 32.0 * nodes),
         "mortar_flux": (2.0 * mortar_flux_ops_per_mortar(N, precision).dfma_eq(*w) * M, (96.0 + 264.0) * (N + 1) * M),
         "mortar_limit": (2.0 * mortar_limit_ops_per_slot(precision).dfma_eq(*w) * Q * M, 112.0 * Q * M),
