@@ -61,16 +61,18 @@ __device__ __forceinline__ double stage_time(const StageArgs &A, int sim, double
 // and +y side of every element whose neighbour there is conforming, at each
 // face node t, the LLF flux along +x/+y scaled by w_t |face|/2 (left/bottom
 // state first), the bar-state density across the face and the FP32 term
-// 2 d of the time-step statistic. The element pass of both elements reads
-// them instead of forming the flux itself; the operations are those it
-// would apply. Entry (2 e + d)(N+1) + t of F = 2 K (N+1): flux [4][F]
-// doubles, bar state [F] doubles, then [F] floats.
+// 2 d of the time-step statistic; and the face's wave speed lambda, which
+// the time-step kernel reads when the faces are formed on u^n before it.
+// The element pass of both elements reads them instead of forming the flux
+// itself; the operations are those it would apply. Entry (2 e + d)(N+1) + t
+// of F = 2 K (N+1): flux [4][F], bar state [F], lambda [F] doubles, then
+// [F] floats.
 template <int NP>
 __global__ void __launch_bounds__(256) k_face(MeshDev mesh, const double *__restrict__ u, Gas G,
                                               const Ops *__restrict__ ops, double *__restrict__ fb) {
     const size_t KN = (size_t)mesh.K * NP * NP;
     const long long F = 2ll * mesh.K * NP;
-    float *fl = reinterpret_cast<float *>(fb + 5 * F);
+    float *fl = reinterpret_cast<float *>(fb + 6 * F);
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < F;
          k += (long long)gridDim.x * blockDim.x) {
         const int t = (int)(k % NP), d = (int)((k / NP) & 1), e = (int)(k / (2 * NP));
@@ -92,6 +94,7 @@ __global__ void __launch_bounds__(256) k_face(MeshDev mesh, const double *__rest
         const double i2l = 0.5 * fast_rcp(lam);
         const double mL = d == 0 ? uL[1] : uL[2], mR = d == 0 ? uR[1] : uR[2];
         fb[4 * F + k] = 0.5 * (uL[0] + uR[0]) - (mR - mL) * i2l;
+        fb[5 * F + k] = lam;
         fl[k] = d2f(ops->w[t]) * (d == 0 ? gc.hyf : gc.hxf) * d2f(lam);
     }
 }
@@ -434,7 +437,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     const double fbv = A.fbuf[4 * F + q];
                     S.fbar[s][t] = fbv;
                     S.fbar2[s][t] = fbv;
-                    S.f2d[s][t] = reinterpret_cast<const float *>(A.fbuf + 5 * F)[q];
+                    S.f2d[s][t] = reinterpret_cast<const float *>(A.fbuf + 6 * F)[q];
                     continue;
                 }
             }

@@ -471,7 +471,7 @@ struct idp_ctx {
     int ent_bar = 0;           // entropy bound with bar-state bounds (mortar bar-state entropies)
     double *d_lofv = nullptr;  // [2][K (N+1)^2] pre-pass output
     int facebuf = 0;           // FP64 default kernel: conforming faces from k_face
-    double *d_fbuf = nullptr;  // k_face output: [5][2 K (N+1)] doubles + [2 K (N+1)] floats
+    double *d_fbuf = nullptr;  // k_face output: [6][2 K (N+1)] doubles + [2 K (N+1)] floats
     // optional timing: 1 step spans around the graph launches; 2 steps
     // launched without the graph, with element-pass events
     int prof = 0;
@@ -547,7 +547,7 @@ cudaError_t kt_collect(idp_ctx *c) {
 
 // one stage: mortar fluxes (unless already current), element pass, mortar
 // limiting
-void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux) {
+void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux, bool need_face) {
     const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
     if (c->M > 0 && need_mortar_flux) {
         int k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
@@ -571,7 +571,7 @@ void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mo
         }
     }
     int k;
-    if (c->facebuf) {
+    if (c->facebuf && need_face) {
         k = kt_begin(c, st, IDP_K_FACE);
         c->L.face(st, c->mesh, A.u, A.gas, c->d_ops, c->d_fbuf, c->num_sms);
         kt_end(c, st, k);
@@ -601,10 +601,18 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) 
                          c->d_ops);
         kt_end(c, st, k);
     }
+    // FP64 path: the conforming faces of u^n first; the time step reads their
+    // wave speeds and stage 1 of a step their fluxes
+    const bool faces = c->facebuf && c->opt.dt_rule == 0;
+    if (faces) {
+        k = kt_begin(c, st, IDP_K_FACE);
+        c->L.face(st, c->mesh, u, make_gas(c->gamma, &c->d_ops->lg), c->d_ops, c->d_fbuf, c->num_sms);
+        kt_end(c, st, k);
+    }
     int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
     k = kt_begin(c, st, IDP_K_DT);
     c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
-            c->d_status);
+            c->d_status, faces ? c->d_fbuf : nullptr);
     kt_end(c, st, k);
 }
 
@@ -616,13 +624,13 @@ void enqueue_step(idp_ctx *c, cudaStream_t st, double *u) {
     A.un = u;
     // stage 1: u1 = ut(u)
     A.u = u; A.out = c->d_buf1; A.comb = 0; A.tstage = 0.0;
-    enqueue_stage(c, st, A, c->opt.dt_rule != 0);
+    enqueue_stage(c, st, A, c->opt.dt_rule != 0, c->opt.dt_rule != 0);   // mortars and faces of u^n are current
     // stage 2: u2 = 3/4 u + 1/4 ut(u1)
     A.u = c->d_buf1; A.out = c->d_buf2; A.comb = 1; A.tstage = 1.0;
-    enqueue_stage(c, st, A, true);
+    enqueue_stage(c, st, A, true, true);
     // stage 3: u3 = u/3 + 2/3 ut(u2), in place
     A.u = c->d_buf2; A.out = u; A.comb = 2; A.tstage = 0.5;
-    enqueue_stage(c, st, A, true);
+    enqueue_stage(c, st, A, true, true);
     const int k = kt_begin(c, st, IDP_K_TIME_ADVANCE);
     k_time_advance<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_tsim, c->d_dtmin, c->opt.cfl, c->d_dtlast,
                                                            c->n_sims);
@@ -887,7 +895,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(cudaMemset(c->d_aind, 0, sizeof(double) * (size_t)c->K));
     if (ok && c->facebuf) {
         const size_t F = (size_t)2 * c->K * c->NP;
-        chk(cudaMalloc(&c->d_fbuf, sizeof(double) * 5 * F + sizeof(float) * F));
+        chk(cudaMalloc(&c->d_fbuf, sizeof(double) * 6 * F + sizeof(float) * F));
     }
     if (ok && c->lob) chk(cudaMalloc(&c->d_lofv, sizeof(double) * 2 * kn));
     if (ok && c->lob) chk(cudaMemset(c->d_lofv, 0, sizeof(double) * 2 * kn));
@@ -995,7 +1003,7 @@ idp_status idp_dgsem_rhs(idp_ctx *c, const double *u, double t, double dt, doubl
     if (r != IDP_OK) return r;
     StageArgs A = base_args(c);
     A.mode = 0; A.u = u; A.out = rhs; A.dt = dt; A.t = t;
-    enqueue_stage(c, st, A, true);
+    enqueue_stage(c, st, A, true, true);
     if (dt > 0.0 && c->opt.limiting > 0) c->n_stages += 1;
     return check_cuda(cudaGetLastError());
 }

@@ -31,7 +31,7 @@ struct Launchers {
     void (*mortar_apply)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
     void (*dt)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
                const Gas &gas, int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin,
-               unsigned *status);
+               unsigned *status, const double *fbuf);
     void (*integrals)(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part);
     // adaptive mesh refinement (idp_amr.cuh)
     void (*amr_indicator)(cudaStream_t st, const double *u, int K, const Ops *ops, double gm1, int kind, int var,

@@ -452,7 +452,7 @@ __global__ void __launch_bounds__(128) k_mortar_lob(MeshDev mesh, SlotsDev sl, c
 template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads)
 k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule, const Ops *ops,
-     const double *t_sim, unsigned long long *dtmin, unsigned *status) {
+     const double *t_sim, unsigned long long *dtmin, unsigned *status, const double *__restrict__ fbuf) {
     constexpr int NN = NP * NP, N = NP - 1, NT = ElemLaunch<NP, EPB>::threads;
     constexpr bool F32 = sizeof(FT) == 4;
     __shared__ FT s_l[EPB][2][NN];       // |v_x| + c, |v_y| + c per node
@@ -483,7 +483,14 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
                 const int4 nb4 = mesh.fnbr[e];
                 const int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
                 const int nb = s == 0 ? nb4.x : (s == 1 ? nb4.y : (s == 2 ? nb4.z : nb4.w));
-                if (ft == FT_CONF || ft == FT_BND) {
+                if (ft == FT_CONF && fbuf != nullptr) {
+                    // FP64 path: the face's lambda = max of both wave speeds
+                    // from k_face on the same state (the entry of the element
+                    // on the face's left/bottom); max(own, lambda) = lambda
+                    const int owner = (s & 1) ? e : nb;
+                    const long long F = 2ll * mesh.K * NP, q = (2ll * owner + (s >> 1)) * NP + t;
+                    s_o[le][s][t] = to_ft<FT>(fbuf[5 * F + q]);
+                } else if (ft == FT_CONF || ft == FT_BND) {
                     double uo[4];
                     if (ft == FT_CONF) {
                         size_t ko = (size_t)nb * NN + face_node<NP>(s ^ 1, t);

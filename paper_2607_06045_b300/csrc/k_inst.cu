@@ -111,15 +111,16 @@ void mortar_apply(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s
 }
 
 void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, const Gas &gamma,
-        int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status) {
+        int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status,
+        const double *fbuf) {
     constexpr int EPB = NP * NP >= 64 ? 2 : (NP * NP >= 25 ? 4 : 8);
     int blocks = (m.K + EPB - 1) / EPB;
     if (fp32)
         k_dt<NP, EPB, float><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
-                                                                             dtmin, status);
+                                                                             dtmin, status, nullptr);
     else
         k_dt<NP, EPB, double><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
-                                                                              dtmin, status);
+                                                                              dtmin, status, fbuf);
     (void)grid;
 }
 

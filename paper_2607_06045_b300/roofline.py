@@ -101,13 +101,14 @@ def _prim(precision: int) -> Ops:
     return Ops(inst=7, div=1, sqrt=1) if precision == 0 else Ops()
 
 
-def dt_ops_per_node(N: int, precision: int = 0) -> Ops:
+def dt_ops_per_node(N: int, precision: int = 0, face: bool = False) -> Ops:
     """k_dt: own wave speeds, the outside wave speed of each face node (one
     per node on average at one face node per element side and node row), the
-    2d sum and m / sum."""
+    2d sum and m / sum. With face = True (the FP64 path's face kernel runs on
+    u^n first) the face's wave speed is read, not formed."""
     NP = N + 1
     facen = 4.0 * NP / (NP * NP)
-    o = _prim(precision) + facen * _prim(precision)
+    o = _prim(precision) + (0.0 if face else facen) * _prim(precision)
     if precision == 0:
         o = o + Ops(inst=8 + 2, div=1)
     return o
@@ -144,8 +145,8 @@ def kernel_work(N: int, precision: int, K: int, M: int, n_mnodes: int, w_div: fl
     """Per launch: (FP64 DFMA-equivalent flops, HBM bytes) of each kernel.
     With the conforming-face kernel (the FP64 path's default element kernel)
     the face fluxes (row a4) are its work and the rest the element kernel's;
-    its bytes are the two face-node states it reads and the 44 bytes per face
-    node it writes."""
+    its bytes are the two face-node states it reads and the 52 bytes per face
+    node it writes; the time-step kernel then reads the faces' wave speeds."""
     nodes = K * (N + 1) ** 2
     Q = 3 * (N + 1)
     w = (w_div, w_sqrt, w_log)
@@ -156,12 +157,13 @@ def kernel_work(N: int, precision: int, K: int, M: int, n_mnodes: int, w_div: fl
     face = {}
     if face_kernel:
         fa = 2.0 * rows["a4_face_flux"].dfma_eq(*w) * nodes
-        face = {"face": (fa, (64.0 + 44.0) * 2.0 / (N + 1) * nodes)}
+        face = {"face": (fa, (64.0 + 52.0) * 2.0 / (N + 1) * nodes)}
         el_flops -= fa
     return {
         **face,
         "element": (el_flops, BYTES_PER_NODE_STAGE * nodes),
-        "dt": (2.0 * dt_ops_per_node(N, precision).dfma_eq(*w) * nodes, 32.0 * nodes),
+        "dt": (2.0 * dt_ops_per_node(N, precision, face_kernel).dfma_eq(*w) * nodes,
+               (32.0 + (8.0 * 4.0 / (N + 1) if face_kernel else 0.0)) * nodes),
         "mortar_flux": (2.0 * mortar_flux_ops_per_mortar(N, precision).dfma_eq(*w) * M, (96.0 + 264.0) * (N + 1) * M),
         "mortar_limit": (2.0 * mortar_limit_ops_per_slot(precision).dfma_eq(*w) * Q * M, 112.0 * Q * M),
         "mortar_apply": (2.0 * mortar_apply_ops_per_node(precision).dfma_eq(*w) * n_mnodes, 136.0 * n_mnodes),
