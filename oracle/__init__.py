@@ -37,60 +37,100 @@ def build(force: bool = False) -> str:
 
 
 def lib():
+    """The loaded oracle library (built on first use)."""
     global _lib
     if _lib is None:
-        build()
-        L = C.CDLL(_LIB)
-        dp = C.POINTER(C.c_double)
-        ip = C.POINTER(C.c_int32)
-        L.orc_create.restype = C.c_void_p
-        L.orc_create.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
-                                 C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int8), ip, ip, ip,
-                                 dp, dp, dp, C.c_int, C.POINTER(C.c_int)]
-        L.orc_destroy.argtypes = [C.c_void_p]
-        L.orc_lgl.argtypes = [C.c_int, dp, dp]
-        L.orc_operators.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, dp]
-        L.orc_logmean.restype = C.c_double
-        L.orc_logmean.argtypes = [C.c_double, C.c_double]
-        L.orc_ranocha.argtypes = [C.c_double, dp, dp, C.c_int, dp]
-        L.orc_llf.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double, dp]
-        L.orc_theta.restype = C.c_double
-        L.orc_theta.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double]
-        L.orc_indicator.restype = C.c_double
-        L.orc_indicator.argtypes = [C.c_int, dp, dp]
-        L.orc_n_mortars.restype = C.c_int
-        L.orc_n_mortars.argtypes = [C.c_void_p]
-        L.orc_mortars.argtypes = [C.c_void_p, ip]
-        L.orc_faces.argtypes = [C.c_void_p, ip, ip]
-        L.orc_graph_size.restype = C.c_int
-        L.orc_graph_size.argtypes = [C.c_void_p]
-        L.orc_graph.argtypes = [C.c_void_p, ip, ip, dp, dp]
-        L.orc_stage.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
-                                dp, dp, dp]
-        L.orc_rhs.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, dp, dp]
-        L.orc_step.argtypes = [C.c_void_p, dp, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
-                               C.c_int, dp, dp]
-        L.orc_set_volume_flux.argtypes = [C.c_void_p, C.c_int]
-        L.orc_mortar_weights.argtypes = [C.c_void_p, dp]
-        L.orc_chandrashekar.argtypes = [C.c_double, dp, dp, C.c_int, dp]
-        L.orc_theta_entropy.restype = C.c_double
-        L.orc_theta_entropy.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double]
-        L.orc_entropy_eta.restype = C.c_double
-        L.orc_entropy_eta.argtypes = [C.c_double, dp]
-        L.orc_dt.restype = C.c_double
-        L.orc_dt.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int]
-        L.orc_integrals.argtypes = [C.c_void_p, dp, dp]
-        L.orc_dg_residual.argtypes = [C.c_void_p, dp, C.c_double, dp]
-        L.orc_dg_residual_fd.argtypes = [C.c_void_p, dp, C.c_double, dp]
-        L.orc_fv_residual.argtypes = [C.c_void_p, dp, C.c_double, dp, dp]
-        L.orc_masses.argtypes = [C.c_void_p, dp]
-        L.orc_stats_init.argtypes = [dp]
-        L.orc_mortar_sparse.argtypes = [C.c_int, C.c_double, dp, dp, dp]
-        L.orc_set_mortar_ell_out.argtypes = [dp]
-        L.orc_set_mortar_dbg_out.argtypes = [dp]
-        L.orc_set_node_dbg_out.argtypes = [dp]
-        _lib = L
+        _lib = load(build())
     return _lib
+
+
+def compile_source(src: str, out: str) -> str:
+    """Compile oracle C source text to the shared library ``out`` with the
+    oracle's own flags (used by the tests that plant a mistake in a copy of
+    the oracle to check that a pin catches it)."""
+    c_path = out[:-3] + ".c" if out.endswith(".so") else out + ".c"
+    with open(c_path, "w") as f:
+        f.write(src)
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC",
+                           "-shared", "-o", out, c_path, "-lm"])
+    return out
+
+
+class using:
+    """Context manager: route every call of this module through the oracle
+    library at ``path`` (another build of the oracle source), restoring the
+    default library on exit. Oracle objects must be created inside it."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self._saved = _lib
+        _lib = load(self.path)
+        return _lib
+
+    def __exit__(self, *exc):
+        global _lib
+        _lib = self._saved
+        return False
+
+
+def load(path: str):
+    """Load an oracle library and declare its entry points."""
+    L = C.CDLL(path)
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int32)
+    L.orc_create.restype = C.c_void_p
+    L.orc_create.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                             C.c_double, C.c_double, C.c_int, C.POINTER(C.c_int8), ip, ip, ip,
+                             dp, dp, dp, C.c_int, C.POINTER(C.c_int)]
+    L.orc_destroy.argtypes = [C.c_void_p]
+    L.orc_lgl.argtypes = [C.c_int, dp, dp]
+    L.orc_operators.argtypes = [C.c_int, C.c_int, dp, dp, dp, dp, dp, dp, dp]
+    L.orc_logmean.restype = C.c_double
+    L.orc_logmean.argtypes = [C.c_double, C.c_double]
+    L.orc_ranocha.argtypes = [C.c_double, dp, dp, C.c_int, dp]
+    L.orc_llf.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double, dp]
+    L.orc_theta.restype = C.c_double
+    L.orc_theta.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double]
+    L.orc_indicator.restype = C.c_double
+    L.orc_indicator.argtypes = [C.c_int, dp, dp]
+    L.orc_n_mortars.restype = C.c_int
+    L.orc_n_mortars.argtypes = [C.c_void_p]
+    L.orc_mortars.argtypes = [C.c_void_p, ip]
+    L.orc_faces.argtypes = [C.c_void_p, ip, ip]
+    L.orc_graph_size.restype = C.c_int
+    L.orc_graph_size.argtypes = [C.c_void_p]
+    L.orc_graph.argtypes = [C.c_void_p, ip, ip, dp, dp]
+    L.orc_stage.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int,
+                            dp, dp, dp]
+    L.orc_rhs.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int, C.c_int, dp, dp]
+    L.orc_step.argtypes = [C.c_void_p, dp, C.c_int, dp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_int,
+                           C.c_int, dp, dp]
+    L.orc_set_volume_flux.argtypes = [C.c_void_p, C.c_int]
+    L.orc_mortar_weights.argtypes = [C.c_void_p, dp]
+    L.orc_chandrashekar.argtypes = [C.c_double, dp, dp, C.c_int, dp]
+    L.orc_theta_entropy.restype = C.c_double
+    L.orc_theta_entropy.argtypes = [C.c_double, dp, dp, C.c_double, C.c_double]
+    L.orc_entropy_eta.restype = C.c_double
+    L.orc_entropy_eta.argtypes = [C.c_double, dp]
+    L.orc_dt.restype = C.c_double
+    L.orc_dt.argtypes = [C.c_void_p, dp, C.c_double, C.c_double, C.c_int]
+    L.orc_integrals.argtypes = [C.c_void_p, dp, dp]
+    L.orc_dg_residual.argtypes = [C.c_void_p, dp, C.c_double, dp]
+    L.orc_dg_residual_fd.argtypes = [C.c_void_p, dp, C.c_double, dp]
+    L.orc_fv_residual.argtypes = [C.c_void_p, dp, C.c_double, dp, dp]
+    L.orc_masses.argtypes = [C.c_void_p, dp]
+    L.orc_stats_init.argtypes = [dp]
+    L.orc_mortar_sparse.argtypes = [C.c_int, C.c_double, dp, dp, dp]
+    L.orc_set_mortar_ell_out.argtypes = [dp]
+    L.orc_set_mortar_dbg_out.argtypes = [dp]
+    L.orc_set_node_dbg_out.argtypes = [dp]
+    L.orc_set_iface_dbg_out.argtypes = [dp]
+    L.orc_set_force_ell.argtypes = [C.c_double]
+    L.orc_face_sparse.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp, dp, dp]
+    return L
 
 
 def _d(a: np.ndarray):
@@ -177,6 +217,20 @@ def indicator(N, p):
     pp = np.ascontiguousarray(p, dtype=np.float64).reshape(-1)
     return float(lib().orc_indicator(N, xi.ctypes.data_as(C.POINTER(C.c_double)), pp.ctypes.data_as(C.POINTER(C.c_double))))
 
+def face_sparse(N, ratio, uA, us, gamma=1.4):
+    """Low-order fluxes of one interface through the stage's weights and pair
+    terms: single face uA[np][4] against ratio faces us[ratio np][4] (ratio 1
+    conforming, 2 a 2:1 mortar). Returns (outward fluxes [(1 + ratio) np][4],
+    weights [np][ratio np] in reference units)."""
+    uA = np.ascontiguousarray(uA, dtype=np.float64)
+    us = np.ascontiguousarray(us, dtype=np.float64)
+    np_ = N + 1
+    F = np.zeros(4 * (1 + ratio) * np_)
+    wt = np.zeros(np_ * ratio * np_)
+    lib().orc_face_sparse(N, ratio, gamma, _d(uA), _d(us), _d(F), _d(wt))
+    return F.reshape((1 + ratio) * np_, 4), wt.reshape(np_, ratio * np_)
+
+
 def mortar_sparse(N, uL, us, gamma=1.4):
     uL = np.ascontiguousarray(uL, dtype=np.float64)
     us = np.ascontiguousarray(us, dtype=np.float64)
@@ -205,19 +259,20 @@ class Oracle:
                       np.ascontiguousarray(mesh.dmr_post, dtype=np.float64),
                       np.ascontiguousarray(mesh.dmr_pre, dtype=np.float64)]
         lev, ix, iy, bc, bcp, post, pre = self._keep
+        self._L = lib()
         err = C.c_int(0)
         x0, y0, x1, y1 = mesh.box
-        self._h = lib().orc_create(N, gamma, proj, mesh.nx0, mesh.ny0, x0, y0, x1, y1, self.K,
+        self._h = self._L.orc_create(N, gamma, proj, mesh.nx0, mesh.ny0, x0, y0, x1, y1, self.K,
                                    lev.ctypes.data_as(C.POINTER(C.c_int8)), _i(ix), _i(iy), _i(bc),
                                    _d(bcp), _d(post), _d(pre), int(mortar_low), C.byref(err))
         if not self._h:
             raise ValueError(f"oracle mesh rejected (code {err.value})")
         # volume flux: 0 Ranocha (R1), 1 Chandrashekar (R23)
-        lib().orc_set_volume_flux(self._h, int(volume_flux))
+        self._L.orc_set_volume_flux(self._h, int(volume_flux))
 
     def __del__(self):
         if getattr(self, "_h", None):
-            lib().orc_destroy(self._h)
+            self._L.orc_destroy(self._h)
             self._h = None
 
     def _u(self, u):
@@ -227,38 +282,38 @@ class Oracle:
 
     @property
     def n_mortars(self) -> int:
-        return lib().orc_n_mortars(self._h)
+        return self._L.orc_n_mortars(self._h)
 
     def mortars(self):
         out = np.zeros((self.n_mortars, 5), dtype=np.int32)
         if self.n_mortars:
-            lib().orc_mortars(self._h, _i(out))
+            self._L.orc_mortars(self._h, _i(out))
         return out
 
     def mortar_weights(self):
         """Weights of the low-order mortar flux [np][2 np] (reference units)."""
         out = np.zeros((self.np, 2 * self.np))
-        lib().orc_mortar_weights(self._h, _d(out))
+        self._L.orc_mortar_weights(self._h, _d(out))
         return out
 
     def faces(self):
         ft = np.zeros((self.K, 4), dtype=np.int32)
         fn = np.zeros((self.K, 4), dtype=np.int32)
-        lib().orc_faces(self._h, _i(ft), _i(fn))
+        self._L.orc_faces(self._h, _i(ft), _i(fn))
         return ft, fn
 
     def graph(self):
-        n = lib().orc_graph_size(self._h)
+        n = self._L.orc_graph_size(self._h)
         nn = self.K * self.np * self.np
         off = np.zeros(nn + 1, dtype=np.int32)
         j = np.zeros(n, dtype=np.int32)
         cx, cy = np.zeros(n), np.zeros(n)
-        lib().orc_graph(self._h, _i(off), _i(j), _d(cx), _d(cy))
+        self._L.orc_graph(self._h, _i(off), _i(j), _d(cx), _d(cy))
         return off, j, cx, cy
 
     def masses(self):
         m = np.zeros((self.K, self.np, self.np))
-        lib().orc_masses(self._h, _d(m))
+        self._L.orc_masses(self._h, _d(m))
         return m
 
     def rhs(self, u, t=0.0, dt=0.0, limiting=2, beta=0.1, stats=None, bounds=0, entropy=0):
@@ -269,8 +324,8 @@ class Oracle:
         out = np.zeros_like(u)
         st = np.zeros(16) if stats is None else stats
         if stats is None:
-            lib().orc_stats_init(_d(st))
-        lib().orc_rhs(self._h, _d(u), t, dt, limiting, beta, bounds, entropy, _d(out), _d(st))
+            self._L.orc_stats_init(_d(st))
+        self._L.orc_rhs(self._h, _d(u), t, dt, limiting, beta, bounds, entropy, _d(out), _d(st))
         return out
 
     def stage(self, u, t, dt, limiting=2, beta=0.1, stats=None, bounds=0, entropy=0):
@@ -279,28 +334,66 @@ class Oracle:
         res, ut = np.zeros_like(u), np.zeros_like(u)
         st = np.zeros(16) if stats is None else stats
         if stats is None:
-            lib().orc_stats_init(_d(st))
-        lib().orc_stage(self._h, _d(u), t, dt, limiting, beta, bounds, entropy, _d(res), _d(ut), _d(st))
+            self._L.orc_stats_init(_d(st))
+        self._L.orc_stage(self._h, _d(u), t, dt, limiting, beta, bounds, entropy, _d(res), _d(ut), _d(st))
         return res, ut
+
+    def stage_debug(self, u, t, dt, limiting=2, beta=0.1, bounds=0, entropy=0, force_ell=None):
+        """One limited stage with the limiter's intermediate values recorded
+        (test use). force_ell in [0, 1] replaces every volume and mortar
+        factor. Returns a dict: res (mass-weighted residual), ut (stage
+        state), stats, node [nn][8] (rho_FV, rho_min, rho_max, p_min, rho_vol,
+        min factor, R+, R-), iface [nif][8] (left node, right node, A_rho,
+        exempt, Zalesak factor, theta_left, theta_right, factor; node left
+        receives -A, node right +A), mortar [M][3np][16] (node, density cap,
+        factor, u_vol[4], scaled correction a[4], rho_min, rho_max, p_min,
+        n_i, H_rho) and mortar_ell [M]."""
+        u = self._u(u)
+        K, np_, N = self.K, self.np, self.N
+        nn = K * np_ * np_
+        M = self.n_mortars
+        node = np.zeros((nn, 8))
+        iface = np.zeros((K * 2 * np_ * N, 8))
+        mort = np.zeros((max(M, 1), 3 * np_, 16))
+        mell = np.zeros(max(M, 1))
+        res, ut = np.zeros_like(u), np.zeros_like(u)
+        st = np.zeros(16)
+        L = self._L
+        L.orc_stats_init(_d(st))
+        L.orc_set_node_dbg_out(_d(node))
+        L.orc_set_iface_dbg_out(_d(iface))
+        L.orc_set_mortar_dbg_out(_d(mort))
+        L.orc_set_mortar_ell_out(_d(mell))
+        L.orc_set_force_ell(-1.0 if force_ell is None else float(force_ell))
+        try:
+            L.orc_stage(self._h, _d(u), t, dt, limiting, beta, bounds, entropy, _d(res), _d(ut), _d(st))
+        finally:
+            null = C.POINTER(C.c_double)()
+            L.orc_set_node_dbg_out(null)
+            L.orc_set_iface_dbg_out(null)
+            L.orc_set_mortar_dbg_out(null)
+            L.orc_set_mortar_ell_out(null)
+            L.orc_set_force_ell(-1.0)
+        return dict(res=res, ut=ut, stats=stats_dict(st), node=node, iface=iface, mortar=mort[:M], mortar_ell=mell[:M])
 
     def dg_residual(self, u, t=0.0, form="evolution"):
         u = self._u(u)
         out = np.zeros_like(u)
         if form == "evolution":
-            lib().orc_dg_residual(self._h, _d(u), t, _d(out))
+            self._L.orc_dg_residual(self._h, _d(u), t, _d(out))
         else:
-            lib().orc_dg_residual_fd(self._h, _d(u), t, _d(out))
+            self._L.orc_dg_residual_fd(self._h, _d(u), t, _d(out))
         return out
 
     def fv_residual(self, u, t=0.0):
         u = self._u(u)
         out = np.zeros_like(u)
         ds = np.zeros((self.K, self.np, self.np))
-        lib().orc_fv_residual(self._h, _d(u), t, _d(out), _d(ds))
+        self._L.orc_fv_residual(self._h, _d(u), t, _d(out), _d(ds))
         return out, ds
 
     def dt(self, u, t=0.0, cfl=0.5, rule=0):
-        return lib().orc_dt(self._h, _d(self._u(u)), t, cfl, rule)
+        return self._L.orc_dt(self._h, _d(self._u(u)), t, cfl, rule)
 
     def step(self, u, nsteps, t=0.0, cfl=0.5, dt_rule=0, limiting=2, beta=0.1, bounds=0, entropy=0):
         """Returns (u_new, t_new, dt_history, stats dict)."""
@@ -308,14 +401,14 @@ class Oracle:
         tt = np.array([t])
         dts = np.zeros(max(nsteps, 1))
         st = np.zeros(16)
-        lib().orc_stats_init(_d(st))
-        lib().orc_step(self._h, _d(u), nsteps, _d(tt), cfl, dt_rule, limiting, beta, bounds, entropy, _d(dts),
+        self._L.orc_stats_init(_d(st))
+        self._L.orc_step(self._h, _d(u), nsteps, _d(tt), cfl, dt_rule, limiting, beta, bounds, entropy, _d(dts),
                        _d(st))
         return u, float(tt[0]), dts[:nsteps], dict(zip(ST_NAMES, st[:13].tolist()))
 
     def integrals(self, u):
         out = np.zeros(4)
-        lib().orc_integrals(self._h, _d(self._u(u)), _d(out))
+        self._L.orc_integrals(self._h, _d(self._u(u)), _d(out))
         return out
 
 

@@ -220,6 +220,32 @@ static void solve(int n, int m, double *A, double *B) {
 
 /* Operators for degree N: Sbar, local weights, mortar interpolation and
    projection (proj 0: LGL-weighted adjoint of interpolation; 1: exact L2). */
+/* Local weights of Eq. local_weights (App. A) on one interface between a
+   side with one face and a side with `ratio` faces (1: a conforming face,
+   2: a 2:1 mortar) on the reference interval [-1, 1]: the length of the
+   overlap of the LGL subcell [a_L, a_U] of node k of the single face with the
+   subcell [b_L, b_U] of node l of face e of the other side, whose subcells are
+   1/ratio as wide. wt[k][e np + l], np x ratio np. */
+static void face_overlap_weights(int np, const double *w, int ratio, double *wt) {
+    for (int k = 0; k < np; ++k) {
+        double aL = -1.0, aU;
+        for (int m = 0; m < k; ++m) aL += w[m];
+        aU = aL + w[k];
+        for (int e = 0; e < ratio; ++e) {
+            for (int l = 0; l < np; ++l) {
+                double bL = ratio == 1 ? -1.0 : (e == 0 ? -1.0 : 0.0), bU;
+                double sc = ratio == 1 ? 1.0 : 0.5;
+                for (int m = 0; m < l; ++m) bL += sc * w[m];
+                bU = bL + sc * w[l];
+                double lo = aL > bL ? aL : bL, hi = aU < bU ? aU : bU;
+                /* subcells that only touch at a point (b_U = b_L in exact
+                   arithmetic) do not overlap: rounding-level overlaps are 0 */
+                wt[k * ratio * np + e * np + l] = hi - lo > 1e-13 ? hi - lo : 0.0;
+            }
+        }
+    }
+}
+
 void orc_operators(int N, int proj, double *xi, double *w, double *D, double *S,
                    double *wt, double *Iint, double *P) {
     int np = N + 1;
@@ -234,22 +260,7 @@ void orc_operators(int N, int proj, double *xi, double *w, double *D, double *S,
         }
     /* local weights (App. A): overlap length of the LGL subcell of large node
        k and of small node (e, l), the small subcells being half as wide */
-    for (int k = 0; k < np; ++k) {
-        double aL = -1.0, aU;
-        for (int m = 0; m < k; ++m) aL += w[m];
-        aU = aL + w[k];
-        for (int e = 0; e < 2; ++e) {
-            for (int l = 0; l < np; ++l) {
-                double bL = (e == 0 ? -1.0 : 0.0), bU;
-                for (int m = 0; m < l; ++m) bL += 0.5 * w[m];
-                bU = bL + 0.5 * w[l];
-                double lo = aL > bL ? aL : bL, hi = aU < bU ? aU : bU;
-                /* subcells that only touch at a point (b_U = b_L in exact
-                   arithmetic) do not overlap: rounding-level overlaps are 0 */
-                wt[k * 2 * np + e * np + l] = hi - lo > 1e-13 ? hi - lo : 0.0;
-            }
-        }
-    }
+    face_overlap_weights(np, w, 2, wt);
     /* interpolation to the small-face nodes s = (xi_l -/+ 1)/2 */
     for (int e = 0; e < 2; ++e)
         for (int l = 0; l < np; ++l) {
@@ -314,6 +325,23 @@ static double lambda_max(double g, const double *a, const double *b, double nx, 
 }
 
 /* local Lax-Friedrichs (Rusanov) flux along a unit normal */
+/* One nonzero weight of the low-order interface flux (Eq. interfaceflux_local,
+   Sec. 2.2): node i on the side the unit normal (nx, ny) points away from and
+   node j across the interface, coupled by the weight wt (physical length;
+   c_ij = wt n / 2, d_ij = aw lambda_ij / 2 with aw = |wt|, R25). Adds the
+   pair's outward contributions to Fi (node i) and Fj (node j); they sum to
+   zero (Eq. conservationProperty). */
+static void sparse_pair_flux(double g, double wt, double aw, const double *ui, const double *uj,
+                             double nx, double ny, double *Fi, double *Fj) {
+    double fi[4], fj[4];
+    flux_n(g, ui, nx, ny, fi); flux_n(g, uj, nx, ny, fj);
+    double lam = lambda_max(g, ui, uj, nx, ny);
+    for (int v = 0; v < 4; ++v) {
+        Fi[v] += 0.5 * (wt * (fi[v] + fj[v]) - aw * lam * (uj[v] - ui[v]));
+        Fj[v] += 0.5 * (-wt * (fi[v] + fj[v]) - aw * lam * (ui[v] - uj[v]));
+    }
+}
+
 void orc_llf(double g, const double *uL, const double *uR, double nx, double ny, double *f) {
     double fL[4], fR[4];
     flux_n(g, uL, nx, ny, fL);
@@ -709,17 +737,11 @@ static void mortar_low(const orc_ctx *c, const double *u, int m, double Flo[][4]
             for (int l = 0; l < np; ++l) {
                 double wt = c->mw[k][p * np + l] * halfL;
                 if (wt == 0.0) continue;
-                double ui[4], uj[4], fi[4], fj[4];
+                double ui[4], uj[4];
                 get_u(c, u, gnode[k], ui); get_u(c, u, gnode[np + p * np + l], uj);
-                flux_n(gm, ui, nxL, nyL, fi); flux_n(gm, uj, nxL, nyL, fj);
-                double lam = lambda_max(gm, ui, uj, nxL, nyL);
                 /* c_ij = omega n / 2 and d_ij = |c_ij| lambda (the all-to-all
                    weights can be negative) */
-                double aw = fabs(wt);
-                for (int v = 0; v < 4; ++v) {
-                    Flo[k][v] += 0.5 * (wt * (fi[v] + fj[v]) - aw * lam * (uj[v] - ui[v]));
-                    Flo[np + p * np + l][v] += 0.5 * (-wt * (fi[v] + fj[v]) - aw * lam * (ui[v] - uj[v]));
-                }
+                sparse_pair_flux(gm, wt, fabs(wt), ui, uj, nxL, nyL, Flo[k], Flo[np + p * np + l]);
             }
 }
 
@@ -1070,10 +1092,18 @@ double orc_entropy_eta(double g, const double *u) { return entropy_eta(g, u); }
 /* optional per-mortar factor output (l_S) for inspection by the tests */
 static double *g_mortar_ell = NULL;
 void orc_set_mortar_ell_out(double *p) { g_mortar_ell = p; }
-static double *g_mortar_dbg = NULL;   /* [M][3np][16]: node, lr, th, u0[4], av[4], rmin, rmax, pmin, n */
+static double *g_mortar_dbg = NULL;   /* [M][3np][16]: node, lr, th, u0[4], av[4], rmin, rmax, pmin, n, H_rho */
 void orc_set_mortar_dbg_out(double *p) { g_mortar_dbg = p; }
 static double *g_node_dbg = NULL;     /* [nn][8]: rho_FV, rmin, rmax, pmin, rho_vol, lmin, R+, R- */
 void orc_set_node_dbg_out(double *p) { g_node_dbg = p; }
+static double *g_iface_dbg = NULL;    /* [nif][8]: gl, gr, A_rho, exempt, l_rho, theta_l, theta_r, l */
+void orc_set_iface_dbg_out(double *p) { g_iface_dbg = p; }
+/* Test hook: a value in [0, 1] replaces every volume interface factor and
+   every mortar factor of the following stages (negative: off), so that the
+   pins can compare the FCT assembly with the pure low-order (0) and the
+   unlimited high-order (1) residuals. */
+static double g_force_ell = -1.0;
+void orc_set_force_ell(double v) { g_force_ell = v; }
 
 /* statistics slots */
 enum { ST_AVOL_M = 0, ST_M, ST_NVOL, ST_AMORT_L, ST_L, ST_NMORT, ST_VRHO, ST_VP, ST_NONPOS, ST_DTX, ST_MINRHO, ST_MINP,
@@ -1298,6 +1328,11 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
                         double l2 = t2l < t2r ? t2l : t2r;
                         l = (1.0 - aind[e]) * l2 + aind[e] * l;
                     }
+                    if (g_iface_dbg) {
+                        double *o = g_iface_dbg + (size_t)id * 8;
+                        o[0] = gl; o[1] = gr; o[2] = Ar; o[3] = exempt[id]; o[4] = lr; o[5] = th_l; o[6] = th_r; o[7] = l;
+                    }
+                    if (g_force_ell >= 0.0) l = g_force_ell;
                     ell[id] = l;
                     if (l < lmin[gl]) lmin[gl] = l;
                     if (l < lmin[gr]) lmin[gr] = l;
@@ -1396,10 +1431,11 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
                 double *o = g_mortar_dbg + ((size_t)m * 3 * np + q) * 16;
                 o[0] = i; o[1] = lr; o[2] = th;
                 for (int v = 0; v < 4; ++v) { o[3 + v] = u0[v]; o[7 + v] = av[v]; }
-                o[11] = rmin[i]; o[12] = rmax[i]; o[13] = pmin[i]; o[14] = ni;
+                o[11] = rmin[i]; o[12] = rmax[i]; o[13] = pmin[i]; o[14] = ni; o[15] = H[q][0];
             }
         }
         if (comb && !mbad[m]) lS = (1.0 - am) * lS2 + am * lS;
+        if (g_force_ell >= 0.0) lS = g_force_ell;
         for (int q = 0; q < 3 * np; ++q) {
             int i = gnode[q];
             for (int v = 0; v < 4; ++v) corr[(size_t)v * nn + i] += lS * H[q][v];
@@ -1529,26 +1565,31 @@ void orc_dg_residual(const orc_ctx *c, const double *u, double time, double *res
 /* node masses */
 void orc_masses(const orc_ctx *c, double *m) { for (int i = 0; i < c->nn; ++i) m[i] = mass(c, i); }
 
-/* single-mortar low-order fluxes for a pin: large-side states uL[np][4],
-   small states us[2np][4]; outputs outward mass-weighted fluxes Flo[3np][4]
-   (large first) with unit face half-length, normal +x, large on the left. */
-void orc_mortar_sparse(int N, double g, const double *uL, const double *us, double *Flo) {
-    double xi[NPMAX], w[NPMAX], D[NPMAX * NPMAX], S[NPMAX * NPMAX], wt[NPMAX * 2 * NPMAX], I[2 * NPMAX * NPMAX], P[NPMAX * 2 * NPMAX];
+/* Low-order interface fluxes of one interface for the pins, through the same
+   weights and pair terms as the stage: the single face carries uA[np][4], the
+   other side its `ratio` faces us[ratio np][4] (ratio 1: a conforming face,
+   ratio 2: a mortar with the lower small face first); unit face half-length,
+   normal +x, the single face on the left. Writes the outward mass-weighted
+   fluxes F[(1 + ratio) np][4] (single face first) and the weights
+   wt[np][ratio np] in reference units. */
+void orc_face_sparse(int N, int ratio, double g, const double *uA, const double *us, double *F, double *wt) {
+    double xi[NPMAX], w[NPMAX];
     int np = N + 1;
-    orc_operators(N, 0, xi, w, D, S, wt, I, P);
-    for (int k = 0; k < 12 * NPMAX; ++k) Flo[k] = 0.0;
+    orc_lgl(N, xi, w);
+    face_overlap_weights(np, w, ratio, wt);
+    for (int k = 0; k < 4 * (1 + ratio) * np; ++k) F[k] = 0.0;
     for (int k = 0; k < np; ++k)
-        for (int q = 0; q < 2 * np; ++q) {
-            double ww = wt[k * 2 * np + q];
-            if (ww <= 0.0) continue;
-            double fi[4], fj[4];
-            flux_n(g, uL + 4 * k, 1.0, 0.0, fi); flux_n(g, us + 4 * q, 1.0, 0.0, fj);
-            double lam = lambda_max(g, uL + 4 * k, us + 4 * q, 1.0, 0.0);
-            for (int v = 0; v < 4; ++v) {
-                Flo[4 * k + v] += 0.5 * ww * ((fi[v] + fj[v]) - lam * (us[4 * q + v] - uL[4 * k + v]));
-                Flo[4 * (np + q) + v] += 0.5 * ww * (-(fi[v] + fj[v]) - lam * (uL[4 * k + v] - us[4 * q + v]));
-            }
+        for (int q = 0; q < ratio * np; ++q) {
+            double ww = wt[k * ratio * np + q];
+            if (ww == 0.0) continue;
+            sparse_pair_flux(g, ww, fabs(ww), uA + 4 * k, us + 4 * q, 1.0, 0.0, F + 4 * k, F + 4 * (np + q));
         }
+}
+
+/* the 2:1 mortar case of orc_face_sparse (Flo[3np][4]) */
+void orc_mortar_sparse(int N, double g, const double *uL, const double *us, double *Flo) {
+    double wt[NPMAX * 2 * NPMAX];
+    orc_face_sparse(N, 2, g, uL, us, Flo, wt);
 }
 
 /* ------------------------------------------------------------------------ */
