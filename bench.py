@@ -45,6 +45,8 @@ DMR_ELEMS_PER_BLOCK = 8
 # B300: 148 SMs, each retiring 2 FP64 fused multiply-adds per clock (the
 # nominal 1.25 TFLOP/s FP64 rate at the maximum SM clock).
 SMS, DFMA_PER_CLK_SM = 148, 2
+# and 128 FP32 fused multiply-adds per clock
+FFMA_PER_CLK_SM = 128
 DMR_CONFIG = {"workload": "double Mach reflection, [0,4]x[0,1], 256x64 base + 3 levels along the shock",
               "elements": 60139, "N": 3, "dofs": 962224, "limiting": "local + positivity", "cfl": 0.5,
               "step": "one SSP-RK3 step (3 stages + dt)"}
@@ -210,11 +212,22 @@ def l1_per_field(u, ref, m):
             for v, f in enumerate(("rho", "rho_v1", "rho_v2", "E"))}
 
 
-def kernel_rooflines(work, kern, steps, step_time, peak_tflops, hbm_gbs):
+def method_work(roofline, N, precision, K, M, n_mnodes, w):
+    """Per kernel and launch: (FP64 flops, FP32 flops, HBM bytes), the flops
+    from the method's work table (the oracle's counting build), the bytes
+    from the kernels' algorithmic traffic; the mortar application kernel's
+    roofline is its traffic."""
+    fl = roofline.method_kernel_work(N, precision, K)
+    by = roofline.kernel_work(N, precision, K, M, n_mnodes, *w)
+    out = {name: fl.get(name, (0.0, 0.0)) + (b,) for name, (_, b) in by.items()}
+    return out
+
+
+def kernel_rooflines(work, kern, steps, step_time, peak_tflops, hbm_gbs, peak32_tflops=None):
     """Per kernel: measured ms per launch, share of the kernel time, roofline
-    time max(flops / FP64 peak, bytes / HBM) and its fraction of the measured
-    time; and the step's roofline fraction (sum of the kernels' roofline times
-    over the measured step time)."""
+    time max(FP64 flops / FP64 peak + FP32 flops / FP32 peak, bytes / HBM) and
+    its fraction of the measured time; and the step's roofline fraction (sum
+    of the kernels' roofline times over the measured step time)."""
     out, tot, roof_step = {}, sum(ms for ms, n in kern.values()), 0.0
     for name, (ms, n) in kern.items():
         if n == 0:
@@ -222,8 +235,12 @@ def kernel_rooflines(work, kern, steps, step_time, peak_tflops, hbm_gbs):
         t = ms * 1e-3 / n
         d = {"ms_per_launch": t * 1e3, "launches_per_step": n / steps, "share": ms / tot}
         if name in work:
-            fl, by = work[name]
-            ta, tb = fl / (peak_tflops * 1e12), by / (hbm_gbs * 1e9)
+            if len(work[name]) == 3:
+                f64, f32, by = work[name]
+            else:
+                (f64, by), f32 = work[name], 0.0
+            ta = f64 / (peak_tflops * 1e12) + (f32 / (peak32_tflops * 1e12) if f32 else 0.0)
+            tb = by / (hbm_gbs * 1e9)
             d.update({"bound": "alu" if ta >= tb else "hbm", "roofline_ms": max(ta, tb) * 1e3,
                       "frac": max(ta, tb) / t})
             roof_step += max(ta, tb) * n / steps
@@ -231,22 +248,38 @@ def kernel_rooflines(work, kern, steps, step_time, peak_tflops, hbm_gbs):
     return out, {"roofline_ms": roof_step * 1e3, "measured_ms": step_time * 1e3, "frac": roof_step / step_time}
 
 
-def vacuum_entry(vac, vnodes, world, roofline, w, peak, hbm, unit):
+def form_roofline(roofline, N, precision, nodes, el_s, peak, peak32, w):
+    """Element-pass roofline of one form: the method's flops per node and
+    stage (the oracle's counting build), FP64 rows over the FP64 peak and, in
+    the FP32 form, the flux rows over the FP32 peak; beside it the issued
+    FP64 efficiency of the kernels' own FP64 instruction count."""
+    f64, f32 = roofline.method_flops(N, roofline.ELEMENT_ROWS, precision)
+    t_roof = nodes * (f64 / (peak * 1e12) + f32 / (peak32 * 1e12))
+    ach = (f64 + f32) * nodes / el_s * 1e-12
+    issued = roofline.element_flops(N, precision, *w)
+    ach_i = issued * nodes / el_s * 1e-12
+    return {"bound": "alu", "achieved": ach, "peak": (f64 + f32) * nodes / t_roof * 1e-12, "unit": "TFLOP/s",
+            "frac": t_roof / el_s, "flops_per_node_stage": f64 + f32, "fp64_flops_per_node_stage": f64,
+            "fp32_flops_per_node_stage": f32, "flops_source": "oracle op-counting build (method_work.json), "
+                                                             "one flop per operation",
+            "peak_fp64": peak, "peak_fp32": peak32, "launch_ms": el_s * 1e3,
+            "issued_fp64": {"flops_per_node_stage": issued, "achieved": ach_i, "peak": peak, "frac": ach_i / peak,
+                            "weights_dfma_eq": {"div": w[0], "sqrt": w[1], "log": w[2]}}}
+
+
+def vacuum_entry(vac, vnodes, world, roofline, w, peak, hbm, unit, peak32):
     """JSON entry of the near-vacuum blast (FP32 form, N = 5): rate, element-pass
-    roofline against the FP64 peak, per-kernel rooflines, invariants."""
+    roofline, per-kernel rooflines, invariants."""
     steps = vac["steps"]
-    f = roofline.element_flops(5, 1, *w)
     el = vac["el_ms"] * 1e-3 / max(vac["el_n"], 1)
-    ach = f * vnodes / el * 1e-12
-    kr, st = kernel_rooflines(roofline.kernel_work(5, 1, vac["K"], vac["M"], 18 * vac["M"], *w), vac["kern"], steps,
-                              vac["time"] / steps, peak, hbm)
+    kr, st = kernel_rooflines(method_work(roofline, 5, 1, vac["K"], vac["M"], 18 * vac["M"], w), vac["kern"],
+                              steps, vac["time"] / steps, peak, hbm, peak32)
     return {"value": aggregate_rate(vnodes * 3 * steps, world, vac["time"]), "unit": unit,
             "workload": "near-vacuum blast: 512x512 base + 2 levels within r < 0.1, N=5, rho 1e-6 / p 1e-9 "
                         "background, disc rho 1 / p 1e3, outflow, FP32 form",
             "elements": int(vac["K"]), "dofs": int(vnodes), "steps": steps,
             "ms_per_step": vac["time"] / steps * 1e3, "ms_per_step_median": vac["median_ms"],
-            "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "frac": ach / peak, "unit": "TFLOP/s",
-                         "launch_ms": el * 1e3, "flops_per_node_stage": f},
+            "roofline": form_roofline(roofline, 5, 1, vnodes, el, peak, peak32, w),
             "kernels": kr, "step_roofline": st, "gpu_launches": int(vac["launches"]),
             "stats": {k: vac["stats"][k] for k in ("alpha_volume_mean", "alpha_mortar_mean", "n_viol_density",
                                                     "n_viol_pressure", "n_nonpositive")}}
@@ -481,21 +514,20 @@ def run_ours(args):
     value = aggregate_rate(nodes * 3 * args.steps, world, r64["time"])
     sm_mhz = ck["sm_max_mhz"] or 2032.0
     peak = SMS * DFMA_PER_CLK_SM * 2 * sm_mhz * 1e6 * 1e-12
+    peak32 = SMS * FFMA_PER_CLK_SM * 2 * sm_mhz * 1e6 * 1e-12
     w = (w_div, w_sqrt, w_log)
-    f64 = roofline.element_flops(3, 0, *w)
     el_avg = r64["el_ms"] * 1e-3 / max(r64["el_n"], 1)
-    achieved = f64 * nodes / el_avg * 1e-12
-    f32 = roofline.element_flops(3, 1, *w)
     el32 = r32["el_ms"] * 1e-3 / max(r32["el_n"], 1)
-    ach32 = f32 * nodes / el32 * 1e-12
+    roof64 = form_roofline(roofline, 3, 0, nodes, el_avg, peak, peak32, w)
+    roof32 = form_roofline(roofline, 3, 1, nodes, el32, peak, peak32, w)
     bval = bnodes_all * 3 * bsteps / btot   # the whole batch over the slowest rank
     hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
     K, M = r64["ctx"].K, r64["ctx"].M
-    kr64, st64 = kernel_rooflines(roofline.kernel_work(3, 0, K, M, 12 * M, *w), r64["kern"], args.steps,
-                                  r64["time"] / args.steps, peak, hbm)
-    kr32, st32 = kernel_rooflines(roofline.kernel_work(3, 1, K, M, 12 * M, *w), r32["kern"], args.steps,
-                                  r32["time"] / args.steps, peak, hbm)
+    kr64, st64 = kernel_rooflines(method_work(roofline, 3, 0, K, M, 12 * M, w), r64["kern"], args.steps,
+                                  r64["time"] / args.steps, peak, hbm, peak32)
+    kr32, st32 = kernel_rooflines(method_work(roofline, 3, 1, K, M, 12 * M, w), r32["kern"], args.steps,
+                                  r32["time"] / args.steps, peak, hbm, peak32)
     # FP32 form against the FP64 path after the same number of steps from the
     # same state (the FP64 path matches the FP64 oracle to 1e-10 over 100 steps)
     l1 = l1_per_field(r32["u_end"], r64["u_end"], node_masses(meshes[0], 3))
@@ -515,14 +547,9 @@ def run_ours(args):
         "data": "synthetic",
         "config": dict(DMR_CONFIG, precision="fp64", l2="flushed between steps (256 MiB write)",
                        parallelism=f"replicas x{world}", element_launch=r64["launch"]),
-        "roofline": {"bound": "alu", "kernel": "k_face + k_element (element pass, FP64 path)",
-                     "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                     "peak_source": f"derived: {SMS} SMs x {DFMA_PER_CLK_SM} FP64 FMA/clk x 2 flop x {sm_mhz:.0f} MHz",
-                     "peak_probe": fp64_probe,
-                     "flops_per_node_stage": f64,
-                     "weights_dfma_eq": {"div": w_div, "sqrt": w_sqrt, "log": w_log},
-                     "launch_ms": el_avg * 1e3,
-                     "traffic": recorded_traffic()},
+        "roofline": dict(roof64, kernel="k_face + k_element (element pass, FP64 path)",
+                         peak_source=f"derived: {SMS} SMs x {DFMA_PER_CLK_SM} FP64 FMA/clk x 2 flop x "
+                                     f"{sm_mhz:.0f} MHz", peak_probe=fp64_probe, traffic=recorded_traffic()),
         "e2e": {"value": aggregate_rate(nodes * 3 * args.steps, world, results["e2e"]), "unit": UNIT,
                 "h2d_bytes_per_step": int(u0.nbytes), "d2h_bytes_per_step": int(u0.nbytes)},
         "gpu_launches": int(r64["launches"]),
@@ -536,16 +563,14 @@ def run_ours(args):
                           "ms_per_step": r32["time"] / args.steps * 1e3,
                           "speedup_vs_fp64": r64["time"] / r32["time"],
                           "element_launch": r32["launch"],
-                          "roofline": {"bound": "alu", "achieved": ach32, "peak": peak, "frac": ach32 / peak,
-                                       "unit": "TFLOP/s", "launch_ms": el32 * 1e3,
-                                       "flops_per_node_stage": f32},
+                          "roofline": roof32,
                           "gpu_launches": int(r32["launches"]),
                           "kernels": kr32,
                           "step_roofline": st32,
                           "l1_vs_fp64": dict(l1, steps=args.warmup + 2 * args.steps),
                           "stats": {k: r32["stats"][k] for k in ("alpha_volume_mean", "n_viol_density",
                                                                  "n_viol_pressure", "n_nonpositive")}},
-            "near_vacuum_fp32": vacuum_entry(vac, vnodes, world, roofline, w, peak, hbm, UNIT),
+            "near_vacuum_fp32": vacuum_entry(vac, vnodes, world, roofline, w, peak, hbm, UNIT, peak32),
             "batched_fp32": {"value": bval, "unit": UNIT,
                              "workload": "256 simulations, 8..128 base, 0-2 levels on seeded patches, N=3, "
                                          "four-quadrant Riemann data, FP32 form",

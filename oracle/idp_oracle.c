@@ -69,6 +69,36 @@
 
 #define NPMAX 9
 #define NSTAT 16
+
+/* Work accounting. The op-counting build (opcount.cpp) compiles this file
+   with a counted scalar type in place of double and defines these hooks:
+   ORC_ROW(r) attributes the following arithmetic to a step of the hot path;
+   ORC_PURE(id, ...) at the top of a pure function counts its arithmetic only
+   the first time the function sees the same arguments within a stage
+   (ORC_PURE_PAIR: the same unordered pair of states, ORC_PURE2: the same
+   ordered pair), so that each distinct
+   evaluation of a primitive is counted once. A state identifies as node g
+   when it was fetched from the solution (ORC_TAG); evaluations on other
+   states (low-order, bar, interpolated states) are all counted. ORC_SCOPE
+   opens the accounting of one state at one time (a time step and its first
+   stage share one). ORC_CONST(x) marks a value formed once per step (the
+   time step) as a constant of the stages that use it. In this build they do
+   nothing. */
+enum { ROW_OTHER = 0, ROW_NODE_PREP, ROW_VOLUME_FLUX, ROW_SUBCELL_FV, ROW_FACE_FLUX, ROW_MORTAR_FLUX,
+       ROW_LOW_UPDATE, ROW_BOUNDS, ROW_VOLUME_LIMIT, ROW_MORTAR_LIMIT, ROW_STAGE, ROW_DT,
+       ROW_REFORM /* a quantity formed again that an earlier step already holds */,
+       ROW_STATS /* statistics and violation counts, not part of the method */, ROW_COUNT };
+enum { PF_PRESSURE = 1, PF_VELOCITY, PF_BETA, PF_SOUND, PF_WAVE, PF_FLUX, PF_LOGMEAN, PF_RANOCHA,
+       PF_CHANDRASHEKAR, PF_LLF, PF_ETA, PF_BAR };
+#ifndef ORC_ROW
+#define ORC_ROW(r) ((void)0)
+#define ORC_PURE(...) ((void)0)
+#define ORC_PURE_PAIR(...) ((void)0)
+#define ORC_PURE2(...) ((void)0)
+#define ORC_TAG(q, g) ((void)0)
+#define ORC_SCOPE(u, t) ((void)0)
+#define ORC_CONST(x) ((void)0)
+#endif
 #define TOL 1e-14   /* R15: relative bound relaxation inside the limiter */
 
 /* ------------------------------------------------------------------------ */
@@ -117,6 +147,10 @@ typedef struct {
     int *mcount;  /* number of mortars incident on node */
     int vflux;    /* volume flux: 0 Ranocha (R1), 1 Chandrashekar (R23) */
 } orc_ctx;
+
+#ifdef ORC_COUNTING
+static void orc_count_node_prep(const orc_ctx *c, const double *u);
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* reference operators (Sec. 2.1)                                           */
@@ -258,6 +292,9 @@ void orc_operators(int N, int proj, double *xi, double *w, double *D, double *S,
             double B = (i == j) ? (i == 0 ? -1.0 : (i == N ? 1.0 : 0.0)) : 0.0;
             S[i * np + j] = 2.0 * Q - B;
         }
+    /* the SBP property Qbar + Qbar^T = Bbar makes Sbar = 2 Qbar - Bbar
+       skew-symmetric: its diagonal is zero exactly (rounding leaves ~1e-16) */
+    for (int i = 0; i < np; ++i) S[i * np + i] = 0.0;
     /* local weights (App. A): overlap length of the LGL subcell of large node
        k and of small node (e, l), the small subcells being half as wide */
     face_overlap_weights(np, w, 2, wt);
@@ -303,12 +340,34 @@ void orc_operators(int N, int proj, double *xi, double *w, double *D, double *S,
 /* ------------------------------------------------------------------------ */
 
 static double pressure(double g, const double *u) {
+    ORC_PURE(PF_PRESSURE, u);
     return (g - 1.0) * (u[3] - 0.5 * (u[1] * u[1] + u[2] * u[2]) / u[0]);
+}
+
+/* velocity v = m / rho of a state */
+static void velocity(const double *u, double *v1, double *v2) {
+    ORC_PURE(PF_VELOCITY, u);
+    *v1 = u[1] / u[0];
+    *v2 = u[2] / u[0];
+}
+
+/* rho / p of a state */
+static double rho_over_p(double g, const double *u) {
+    ORC_PURE(PF_BETA, u);
+    return u[0] / pressure(g, u);
+}
+
+/* speed of sound sqrt(gamma p / rho) */
+static double sound_speed(double g, const double *u) {
+    ORC_PURE(PF_SOUND, u);
+    return sqrt(g * pressure(g, u) / u[0]);
 }
 
 /* physical flux f(u) . n for a unit normal n = (nx, ny) */
 static void flux_n(double g, const double *u, double nx, double ny, double *f) {
-    double v1 = u[1] / u[0], v2 = u[2] / u[0], p = pressure(g, u);
+    ORC_PURE(PF_FLUX, u, nx, ny);
+    double v1, v2, p = pressure(g, u);
+    velocity(u, &v1, &v2);
     double vn = v1 * nx + v2 * ny;
     f[0] = u[0] * vn;
     f[1] = u[1] * vn + p * nx;
@@ -316,15 +375,21 @@ static void flux_n(double g, const double *u, double nx, double ny, double *f) {
     f[3] = (u[3] + p) * vn;
 }
 
+/* |v . n| + c of one state along the unit normal n */
+static double wave_speed(double g, const double *a, double nx, double ny) {
+    /* (|v . n| does not depend on the sign of n, and the negation is exact:
+       the accounting treats n and -n as the same evaluation) */
+    ORC_PURE(PF_WAVE, a, nx, ny);
+    double va = (a[1] * nx + a[2] * ny) / a[0];
+    return fabs(va) + sound_speed(g, a);
+}
+
 /* R3: Davis estimate of the maximum wave speed along n */
 static double lambda_max(double g, const double *a, const double *b, double nx, double ny) {
-    double va = (a[1] * nx + a[2] * ny) / a[0], vb = (b[1] * nx + b[2] * ny) / b[0];
-    double ca = sqrt(g * pressure(g, a) / a[0]), cb = sqrt(g * pressure(g, b) / b[0]);
-    double la = fabs(va) + ca, lb = fabs(vb) + cb;
+    double la = wave_speed(g, a, nx, ny), lb = wave_speed(g, b, nx, ny);
     return la > lb ? la : lb;
 }
 
-/* local Lax-Friedrichs (Rusanov) flux along a unit normal */
 /* One nonzero weight of the low-order interface flux (Eq. interfaceflux_local,
    Sec. 2.2): node i on the side the unit normal (nx, ny) points away from and
    node j across the interface, coupled by the weight wt (physical length;
@@ -342,7 +407,27 @@ static void sparse_pair_flux(double g, double wt, double aw, const double *ui, c
     }
 }
 
+/* Bar state of the graph pair (i, j) with coefficient c_ij = (cx, cy)
+   (Eq. barstateform): ubar = (u_i + u_j)/2 - c_ij . (f(u_j) - f(u_i)) / (2 d_ij),
+   d_ij = |c_ij| lambda_ij. It is the same state for (j, i), c_ji = -c_ij.
+   nvar: how many variables to form (1: the density alone). */
+static void bar_state(double gm, const double *ui, const double *uj, double cx, double cy, int nvar,
+                      double *ub) {
+    ORC_PURE_PAIR(PF_BAR, ui, uj, cx, cy, nvar);
+    double nrm = sqrt(cx * cx + cy * cy);
+    double d = nrm * lambda_max(gm, ui, uj, cx / nrm, cy / nrm);
+    double fi[4], fj[4], fiy[4], fjy[4];
+    flux_n(gm, ui, 1.0, 0.0, fi); flux_n(gm, ui, 0.0, 1.0, fiy);
+    flux_n(gm, uj, 1.0, 0.0, fj); flux_n(gm, uj, 0.0, 1.0, fjy);
+    for (int v = 0; v < nvar; ++v) {
+        double cdf = cx * (fj[v] - fi[v]) + cy * (fjy[v] - fiy[v]);
+        ub[v] = 0.5 * (ui[v] + uj[v]) - cdf / (2.0 * d);
+    }
+}
+
+/* local Lax-Friedrichs (Rusanov) flux along a unit normal */
 void orc_llf(double g, const double *uL, const double *uR, double nx, double ny, double *f) {
+    ORC_PURE2(PF_LLF, uL, uR, nx, ny);
     double fL[4], fR[4];
     flux_n(g, uL, nx, ny, fL);
     flux_n(g, uR, nx, ny, fR);
@@ -361,11 +446,14 @@ double orc_logmean(double a, double b) {
 
 /* R1: Ranocha's EC/KEP two-point flux along the unit axis d (0 x, 1 y) */
 void orc_ranocha(double g, const double *uL, const double *uR, int d, double *f) {
+    ORC_PURE_PAIR(PF_RANOCHA, uL, uR, d);
     double rL = uL[0], rR = uR[0];
-    double v1L = uL[1] / rL, v2L = uL[2] / rL, v1R = uR[1] / rR, v2R = uR[2] / rR;
+    double v1L, v2L, v1R, v2R;
+    velocity(uL, &v1L, &v2L);
+    velocity(uR, &v1R, &v2R);
     double pL = pressure(g, uL), pR = pressure(g, uR);
     double rho_ln = orc_logmean(rL, rR);
-    double inv_beta = 1.0 / orc_logmean(rL / pL, rR / pR);   /* 1/{rho/p}_ln */
+    double inv_beta = 1.0 / orc_logmean(rho_over_p(g, uL), rho_over_p(g, uR));   /* 1/{rho/p}_ln */
     double v1a = 0.5 * (v1L + v1R), v2a = 0.5 * (v2L + v2R), pa = 0.5 * (pL + pR);
     double vnL = d == 0 ? v1L : v2L, vnR = d == 0 ? v1R : v2R, vna = 0.5 * (vnL + vnR);
     double fr = rho_ln * vna;
@@ -381,8 +469,11 @@ void orc_ranocha(double g, const double *uL, const double *uR, int d, double *f)
    {beta}_ln) - {|v|^2} / 2) + f_m . {v} (Sec. 3: the paper's astrophysical
    jet uses it for the volume fluxes). */
 void orc_chandrashekar(double g, const double *uL, const double *uR, int d, double *f) {
+    ORC_PURE_PAIR(PF_CHANDRASHEKAR, uL, uR, d);
     double rL = uL[0], rR = uR[0];
-    double v1L = uL[1] / rL, v2L = uL[2] / rL, v1R = uR[1] / rR, v2R = uR[2] / rR;
+    double v1L, v2L, v1R, v2R;
+    velocity(uL, &v1L, &v2L);
+    velocity(uR, &v1R, &v2R);
     double pL = pressure(g, uL), pR = pressure(g, uR);
     double bL = rL / (2.0 * pL), bR = rR / (2.0 * pR);
     double rho_ln = orc_logmean(rL, rR), beta_ln = orc_logmean(bL, bR);
@@ -650,6 +741,7 @@ void orc_graph(const orc_ctx *c, int32_t *off, int32_t *nbj, double *cx, double 
 
 static void get_u(const orc_ctx *c, const double *u, int g, double *q) {
     for (int v = 0; v < 4; ++v) q[v] = u[(size_t)v * c->nn + g];
+    ORC_TAG(q, g);
 }
 
 static void prim_to_cons(double gm, const double *w, double *q) {
@@ -700,7 +792,10 @@ static double *make_ghosts(const orc_ctx *c, const double *u, double time) {
 
 static void node_or_ghost(const orc_ctx *c, const double *u, const double *gh, int j, double *q) {
     if (j >= 0) get_u(c, u, j, q);
-    else for (int v = 0; v < 4; ++v) q[v] = gh[4 * (-1 - j) + v];
+    else {
+        for (int v = 0; v < 4; ++v) q[v] = gh[4 * (-1 - j) + v];
+        ORC_TAG(q, j);
+    }
 }
 
 static double mass(const orc_ctx *c, int g) {
@@ -785,6 +880,7 @@ static double *surface_fluxes_b(const orc_ctx *c, const double *u, const double 
             }
         }
     for (int m = 0; m < c->M; ++m) {
+        ORC_ROW(ROW_MORTAR_FLUX);
         int dir = c->mort[5 * m], L = c->mort[5 * m + 1], low = c->mort[5 * m + 2];
         int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
         double ax = dir == 0 ? 1.0 : 0.0, ay = 1.0 - ax;
@@ -838,6 +934,7 @@ static double *surface_fluxes_b(const orc_ctx *c, const double *u, const double 
                 sf[((size_t)(4 * L + sL) * np + k) * 4 + v] = halfL * acc;
             }
     }
+    ORC_ROW(ROW_FACE_FLUX);
     return sf;
 }
 
@@ -851,12 +948,19 @@ static void dg_residual(const orc_ctx *c, const double *u, const double *sf, dou
                 double ui[4], uk[4], f[4], F1[4] = {0, 0, 0, 0}, F2[4] = {0, 0, 0, 0};
                 get_u(c, u, gidx(c, e, i, j), ui);
                 for (int k = 0; k < np; ++k) {
-                    get_u(c, u, gidx(c, e, k, j), uk);
-                    volume_flux(c, ui, uk, 0, f);
-                    for (int v = 0; v < 4; ++v) F1[v] -= c->S[i][k] * (c->dy[e] / 2.0) * f[v];
-                    get_u(c, u, gidx(c, e, i, k), uk);
-                    volume_flux(c, ui, uk, 1, f);
-                    for (int v = 0; v < 4; ++v) F2[v] -= c->S[j][k] * (c->dx[e] / 2.0) * f[v];
+                    /* Sbar_ii = 0: the node's own pair adds nothing */
+                    if (k != i) {
+                        get_u(c, u, gidx(c, e, k, j), uk);
+                        volume_flux(c, ui, uk, 0, f);
+                        double sh = c->S[i][k] * (c->dy[e] / 2.0);
+                        for (int v = 0; v < 4; ++v) F1[v] -= sh * f[v];
+                    }
+                    if (k != j) {
+                        get_u(c, u, gidx(c, e, i, k), uk);
+                        volume_flux(c, ui, uk, 1, f);
+                        double sh = c->S[j][k] * (c->dx[e] / 2.0);
+                        for (int v = 0; v < 4; ++v) F2[v] -= sh * f[v];
+                    }
                 }
                 for (int v = 0; v < 4; ++v) {
                     double a = F1[v], b = F2[v];
@@ -871,6 +975,28 @@ static void dg_residual(const orc_ctx *c, const double *u, const double *sf, dou
 
 /* high-order subcell flux between nodes (l=a) and a+1 of a row/column
    (Eq. fluxdifferencingform), d = 0 for x rows (row index r = j), 1 for y */
+/* all N high-order subcell fluxes of one row (d = 0) or column (d = 1) r of
+   element e, fh[a] between nodes a and a+1: the same sums as
+   dg_subcell_flux, in the same order, each extending the previous one
+   (Eq. fluxdifferencingform). Sbar has a zero diagonal, so a node's own pair
+   adds nothing and is skipped. */
+static void dg_subcell_fluxes_row(const orc_ctx *c, const double *u, int e, int d, int r, double fh[][4]) {
+    int np = c->np, N = c->N;
+    double f[4], ul[4], uk[4], acc[4] = {0, 0, 0, 0};
+    double half = (d == 0 ? c->dy[e] : c->dx[e]) / 2.0;
+    for (int l = 0; l < N; ++l) {
+        for (int k = 0; k < np; ++k) {
+            if (k == l) continue;
+            get_u(c, u, d == 0 ? gidx(c, e, l, r) : gidx(c, e, r, l), ul);
+            get_u(c, u, d == 0 ? gidx(c, e, k, r) : gidx(c, e, r, k), uk);
+            volume_flux(c, ul, uk, d, f);
+            double sh = c->S[l][k] * half;
+            for (int v = 0; v < 4; ++v) acc[v] += sh * f[v];
+        }
+        for (int v = 0; v < 4; ++v) fh[l][v] = acc[v];
+    }
+}
+
 static void dg_subcell_flux(const orc_ctx *c, const double *u, int e, int d, int r, int a, double *fh) {
     int np = c->np;
     double f[4], ul[4], uk[4];
@@ -896,6 +1022,9 @@ static void fv_residual(const orc_ctx *c, const double *u, const double *gh, dou
         get_u(c, u, i, ui);
         for (int k = c->nb_off[i]; k < c->nb_off[i + 1]; ++k) {
             const orc_nb *b = &c->nb[k];
+            ORC_ROW(b->j >= 0 && b->j / (c->np * c->np) == i / (c->np * c->np) ? ROW_SUBCELL_FV
+                    : b->j >= 0 && c->lev[b->j / (c->np * c->np)] != c->lev[i / (c->np * c->np)] ? ROW_MORTAR_FLUX
+                    : ROW_FACE_FLUX);
             node_or_ghost(c, u, gh, b->j, uj);
             double nrm = sqrt(b->cx * b->cx + b->cy * b->cy);
             double fx[4], fy[4];
@@ -906,6 +1035,7 @@ static void fv_residual(const orc_ctx *c, const double *u, const double *gh, dou
             for (int v = 0; v < 4; ++v) acc[v] += -(b->cx * fx[v] + b->cy * fy[v]) + d * (uj[v] - ui[v]);
             s2d += 2.0 * d;
         }
+        ORC_ROW(ROW_SUBCELL_FV);
         for (int v = 0; v < 4; ++v) res[(size_t)v * c->nn + i] = acc[v];
         if (dsum) dsum[i] = s2d;
     }
@@ -915,12 +1045,26 @@ static void fv_residual(const orc_ctx *c, const double *u, const double *gh, dou
    estimate (R11): min over nodes and directions of (w_i dx/2) / (|v| + c). */
 double orc_dt(const orc_ctx *c, const double *u, double time, double cfl, int rule) {
     double best = INFINITY;
+    ORC_SCOPE(u, time);
+    ORC_ROW(ROW_DT);
     if (rule == 0) {
         double *gh = make_ghosts(c, u, time);
-        double *res = malloc(sizeof(double) * 4 * c->nn), *ds = malloc(sizeof(double) * c->nn);
-        fv_residual(c, u, gh, res, ds);
-        for (int i = 0; i < c->nn; ++i) { double t = mass(c, i) / ds[i]; if (t < best) best = t; }
-        free(gh); free(res); free(ds);
+        for (int i = 0; i < c->nn; ++i) {
+            /* sum_j 2 d_ij over the node's graph neighbours, as in the
+               low-order residual */
+            double ui[4], uj[4], s2d = 0.0;
+            get_u(c, u, i, ui);
+            for (int k = c->nb_off[i]; k < c->nb_off[i + 1]; ++k) {
+                const orc_nb *b = &c->nb[k];
+                node_or_ghost(c, u, gh, b->j, uj);
+                double nrm = sqrt(b->cx * b->cx + b->cy * b->cy);
+                double d = nrm * lambda_max(c->gamma, ui, uj, b->cx / nrm, b->cy / nrm);
+                s2d += 2.0 * d;
+            }
+            double t = mass(c, i) / s2d;
+            if (t < best) best = t;
+        }
+        free(gh);
     } else {
         int np = c->np;
         for (int i = 0; i < c->nn; ++i) {
@@ -1041,6 +1185,7 @@ double orc_theta(double gm, const double *u0, const double *a, double pmin, doub
 
 /* modified specific entropy of Eq. Bounds_Barstates: eta = p rho^-gamma / (gamma - 1) */
 static double entropy_eta(double g, const double *u) {
+    ORC_PURE(PF_ETA, u);
     return pressure(g, u) * pow(u[0], -g) / (g - 1.0);
 }
 
@@ -1126,12 +1271,19 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
               double beta, int bounds, int entropy, double *res_out, double *utilde, double *stats) {
     int np = c->np, nn = c->nn, K = c->K, N = c->N;
     double gm = c->gamma;
+    ORC_SCOPE(u, time);
+#ifdef ORC_COUNTING
+    orc_count_node_prep(c, u);
+#endif
+    ORC_ROW(ROW_FACE_FLUX);
     double *gh = make_ghosts(c, u, time);
     char *mbad = calloc(c->M + 1, 1);
     double *sf = surface_fluxes_b(c, u, gh, mbad);
     double *rdg = malloc(sizeof(double) * 4 * nn);
-    dg_residual(c, u, sf, rdg);
     if (dt == 0.0 || limiting == 0) {
+        ORC_ROW(ROW_VOLUME_FLUX);
+        dg_residual(c, u, sf, rdg);
+        ORC_ROW(ROW_STAGE);
         free(mbad);
         for (int k = 0; k < 4 * nn; ++k) res_out[k] = rdg[k];
         if (utilde) for (int i = 0; i < nn; ++i) for (int v = 0; v < 4; ++v)
@@ -1142,6 +1294,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     double *rfv = malloc(sizeof(double) * 4 * nn), *ds = malloc(sizeof(double) * nn);
     fv_residual(c, u, gh, rfv, ds);
     /* low-order update */
+    ORC_ROW(ROW_LOW_UPDATE);
     double *ufv = malloc(sizeof(double) * 4 * nn);
     for (int i = 0; i < nn; ++i) {
         double m = mass(c, i);
@@ -1149,6 +1302,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
         if (dt * ds[i] / m > 1.0 && stats) stats[ST_DTX] += 1;
     }
     /* bounds (R6 and Eqs. Bounds_Positivity, Bounds_Barstates) */
+    ORC_ROW(ROW_BOUNDS);
     double *rmin = malloc(sizeof(double) * nn), *rmax = malloc(sizeof(double) * nn), *pmin = malloc(sizeof(double) * nn);
     /* combined limiting: the positivity bounds beside the local ones, and
        the indicator per element */
@@ -1173,19 +1327,14 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
             /* bar states ubar_(i,j) = (u_i + u_j)/2 - c_ij . (f_j - f_i) / (2 d_ij);
                the node itself is one of them (R6) */
             lo = ui[0]; hi = ui[0];
-            elo = entropy_eta(gm, ui);
+            elo = ent ? entropy_eta(gm, ui) : 0.0;
             for (int k = c->nb_off[i]; k < c->nb_off[i + 1]; ++k) {
                 const orc_nb *b = &c->nb[k];
                 node_or_ghost(c, u, gh, b->j, uj);
-                double nrm = sqrt(b->cx * b->cx + b->cy * b->cy);
-                double d = nrm * lambda_max(gm, ui, uj, b->cx / nrm, b->cy / nrm);
-                double fi[4], fj[4], fiy[4], fjy[4], ub[4];
-                flux_n(gm, ui, 1.0, 0.0, fi); flux_n(gm, ui, 0.0, 1.0, fiy);
-                flux_n(gm, uj, 1.0, 0.0, fj); flux_n(gm, uj, 0.0, 1.0, fjy);
-                for (int v = 0; v < 4; ++v) {
-                    double cdf = b->cx * (fj[v] - fi[v]) + b->cy * (fjy[v] - fiy[v]);
-                    ub[v] = 0.5 * (ui[v] + uj[v]) - cdf / (2.0 * d);
-                }
+                double ub[4];
+                /* the density bounds need the density alone, the entropy
+                   bound the whole state */
+                bar_state(gm, ui, uj, b->cx, b->cy, ent ? 4 : 1, ub);
                 if (ub[0] < lo) lo = ub[0];
                 if (ub[0] > hi) hi = ub[0];
                 if (ent) { double eb = entropy_eta(gm, ub); if (eb < elo) elo = eb; }
@@ -1227,12 +1376,18 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     for (int e = 0; e < K; ++e)
         for (int d = 0; d < 2; ++d)
             for (int r = 0; r < np; ++r)
+            {
+                double fhr[NPMAX][4];
+                ORC_ROW(ROW_VOLUME_FLUX);
+                dg_subcell_fluxes_row(c, u, e, d, r, fhr);
                 for (int a = 0; a < N; ++a) {
                     int id = ((e * 2 + d) * np + r) * N + a;
                     int gl = d == 0 ? gidx(c, e, a, r) : gidx(c, e, r, a);
                     int gr = d == 0 ? gidx(c, e, a + 1, r) : gidx(c, e, r, a + 1);
-                    double fh[4], ul[4], ur[4], fl[4], fr[4];
-                    dg_subcell_flux(c, u, e, d, r, a, fh);
+                    double *fh = fhr[a], ul[4], ur[4], fl[4], fr[4];
+                    /* the low-order subcell flux again (the graph form above
+                       carries the same terms: not counted twice) */
+                    ORC_ROW(ROW_REFORM);
                     get_u(c, u, gl, ul); get_u(c, u, gr, ur);
                     double cc = c->w[r] * (d == 0 ? c->dy[e] : c->dx[e]) / 4.0;
                     flux_n(gm, ul, d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0, fl);
@@ -1240,12 +1395,16 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
                     double lam = lambda_max(gm, ul, ur, d == 0 ? 1.0 : 0.0, d == 1 ? 1.0 : 0.0);
                     for (int v = 0; v < 4; ++v) {
                         double ffv = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
+                        ORC_ROW(ROW_VOLUME_LIMIT);
                         A[4 * id + v] = c->w[r] * fh[v] - ffv;
+                        ORC_ROW(ROW_REFORM);
                     }
                 }
+            }
     /* R15: an interface whose density antidiffusion changes neither end
        node's density by more than TOL relative is exempt from the density
        limiter (the mortar step below works on bounds relaxed by TOL) */
+    ORC_ROW(ROW_VOLUME_LIMIT);
     double *tolr = malloc(sizeof(double) * nn);
     for (int i = 0; i < nn; ++i) tolr[i] = TOL * fabs(ufv[i]);
     char *exempt = malloc(nif);
@@ -1353,11 +1512,13 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
             acc[(size_t)v * nn + i] = s[v];
             uvol[(size_t)v * nn + i] = ufv[(size_t)v * nn + i] + dt / m * s[v];
         }
+        ORC_ROW(ROW_STATS);
         if (stats) {
             stats[ST_AVOL_M] += m * (1.0 - lmin[i]);
             stats[ST_M] += m;
             if (lmin[i] < 1.0) stats[ST_NVOL] += 1;
         }
+        ORC_ROW(ROW_VOLUME_LIMIT);
     }
     if (g_node_dbg)
         for (int i = 0; i < nn; ++i) {
@@ -1376,9 +1537,12 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
         int gnode[3 * NPMAX];
         double H[3 * NPMAX][4];
         mortar_nodes(c, m, gnode);
-        /* low-order sparse fluxes, outward for each side */
+        /* low-order sparse fluxes, outward for each side (the graph form
+           above carries the same terms) */
         double Flo[3 * NPMAX][4];
+        ORC_ROW(ROW_REFORM);
         mortar_low(c, u, m, Flo);
+        ORC_ROW(ROW_MORTAR_LIMIT);
         /* high-order outward fluxes from the surface fluxes (signs: +x-direction
            J-weighted fluxes sf; the element on the low side loses it) */
         for (int k = 0; k < np; ++k) {
@@ -1441,20 +1605,24 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
             for (int v = 0; v < 4; ++v) corr[(size_t)v * nn + i] += lS * H[q][v];
         }
         if (g_mortar_ell) g_mortar_ell[m] = lS;
+        ORC_ROW(ROW_STATS);
         if (stats) {
             stats[ST_AMORT_L] += 2.0 * halfL * (1.0 - lS);
             stats[ST_L] += 2.0 * halfL;
             if (lS < 1.0) stats[ST_NMORT] += 1;
         }
+        ORC_ROW(ROW_MORTAR_LIMIT);
     }
     /* limited residual and stage state; violations (R13) */
     for (int i = 0; i < nn; ++i) {
+        ORC_ROW(ROW_STAGE);
         double m = mass(c, i), q[4];
         for (int v = 0; v < 4; ++v) {
             res_out[(size_t)v * nn + i] = rfv[(size_t)v * nn + i] + acc[(size_t)v * nn + i] + corr[(size_t)v * nn + i];
             q[v] = uvol[(size_t)v * nn + i] + dt / m * corr[(size_t)v * nn + i];
             if (utilde) utilde[(size_t)v * nn + i] = q[v];
         }
+        ORC_ROW(ROW_STATS);
         if (stats) {
             double p = pressure(gm, q);
             const double *lo_ = comb ? rmin2 : rmin, *hi_ = comb ? rmax2 : rmax;
@@ -1498,12 +1666,15 @@ int orc_step(const orc_ctx *c, double *u, int nsteps, double *time, double cfl, 
     double *res = malloc(sizeof(double) * n);
     for (int s = 0; s < nsteps; ++s) {
         double dt = orc_dt(c, u, *time, cfl, dt_rule);
+        ORC_CONST(dt);
         if (dt_hist) dt_hist[s] = dt;
         orc_stage(c, u, *time, dt, limiting, beta, bounds, entropy, res, ut, stats);
         for (size_t k = 0; k < n; ++k) u1[k] = ut[k];
         orc_stage(c, u1, *time + dt, dt, limiting, beta, bounds, entropy, res, ut, stats);
+        ORC_ROW(ROW_STAGE);
         for (size_t k = 0; k < n; ++k) u2[k] = 0.75 * u[k] + 0.25 * ut[k];
         orc_stage(c, u2, *time + 0.5 * dt, dt, limiting, beta, bounds, entropy, res, ut, stats);
+        ORC_ROW(ROW_STAGE);
         for (size_t k = 0; k < n; ++k) u[k] = u[k] / 3.0 + 2.0 / 3.0 * ut[k];
         *time += dt;
     }

@@ -1,0 +1,232 @@
+/*
+ * opcount.cpp -- op-counting build of the oracle (test and measurement
+ * infrastructure; only the tests and the benchmark's work model read its
+ * output, through oracle/opcount.py).
+ *
+ * idp_oracle.c is compiled here with `double` replaced by a counted scalar,
+ * so every floating-point operation of one SSP-RK3 step of the oracle is
+ * tallied by class (add, mul, div, sqrt, log, exp, pow, compare, abs) and by
+ * the step of the hot path it belongs to (the oracle's ORC_ROW markers). The
+ * count is the method's arithmetic as the oracle writes it, with three rules
+ * that keep it to the work one evaluation of the method needs:
+ *   - an operation counts only when an operand depends on the solution:
+ *     mesh geometry, node masses, graph coefficients, the operators and the
+ *     time step once formed are the constants a stage works with, and a
+ *     division by a constant counts as a multiply by its reciprocal;
+ *   - a pure primitive (ORC_PURE, ORC_PURE_PAIR, ORC_PURE2) evaluated again on
+ *     the same solution nodes within a stage counts once (the oracle re-forms
+ *     node fluxes, wave speeds and pair fluxes wherever it needs them);
+ *   - quantities the oracle forms a second time (ROW_REFORM) and the
+ *     statistics (ROW_STATS) are tallied apart.
+ * The arithmetic itself is the oracle's: the counted step returns the same
+ * bits as the plain oracle (checked by the tests).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <initializer_list>
+#include <string>
+#include <unordered_map>
+#include <unordered_set>
+#include <vector>
+
+struct cdbl;
+namespace opc {
+enum { C_ADD, C_MUL, C_DIV, C_SQRT, C_LOG, C_EXP, C_POW, C_CMP, C_ABS, N_CLS };
+static const int NROWS = 32;
+static long long cnt[NROWS][N_CLS];
+static int row = 0;
+static int off = 0;
+static inline void add(int cls, bool dep) {
+    if (dep && off == 0) cnt[row][cls] += 1;
+}
+}  // namespace opc
+
+struct cdbl {
+    double v;
+    bool d;  // depends on the solution
+    cdbl() = default;
+    cdbl(double x) : v(x), d(false) {}
+    cdbl(float x) : v(x), d(false) {}
+    cdbl(int x) : v(x), d(false) {}
+    cdbl(long x) : v((double)x), d(false) {}
+    cdbl(long long x) : v((double)x), d(false) {}
+    cdbl(unsigned x) : v(x), d(false) {}
+    cdbl(unsigned long x) : v((double)x), d(false) {}
+    cdbl(char x) : v(x), d(false) {}
+    cdbl(signed char x) : v(x), d(false) {}
+    cdbl(bool x) : v(x), d(false) {}
+    static cdbl mk(double x, bool dep) { cdbl r(x); r.d = dep; return r; }
+    explicit operator int() const { return (int)v; }
+    explicit operator long() const { return (long)v; }
+    explicit operator long long() const { return (long long)v; }
+    explicit operator unsigned long() const { return (unsigned long)v; }
+    explicit operator char() const { return (char)v; }
+    explicit operator bool() const { return v != 0.0; }
+    cdbl operator-() const { return mk(-v, d); }
+    cdbl operator+() const { return *this; }
+    cdbl &operator+=(const cdbl &o) { opc::add(opc::C_ADD, d || o.d); v += o.v; d = d || o.d; return *this; }
+    cdbl &operator-=(const cdbl &o) { opc::add(opc::C_ADD, d || o.d); v -= o.v; d = d || o.d; return *this; }
+    cdbl &operator*=(const cdbl &o) { opc::add(opc::C_MUL, d || o.d); v *= o.v; d = d || o.d; return *this; }
+    cdbl &operator/=(const cdbl &o) { opc::add(o.d ? opc::C_DIV : opc::C_MUL, d || o.d); v /= o.v; d = d || o.d; return *this; }
+};
+
+static inline cdbl operator+(const cdbl &a, const cdbl &b) { opc::add(opc::C_ADD, a.d || b.d); return cdbl::mk(a.v + b.v, a.d || b.d); }
+static inline cdbl operator-(const cdbl &a, const cdbl &b) { opc::add(opc::C_ADD, a.d || b.d); return cdbl::mk(a.v - b.v, a.d || b.d); }
+static inline cdbl operator*(const cdbl &a, const cdbl &b) { opc::add(opc::C_MUL, a.d || b.d); return cdbl::mk(a.v * b.v, a.d || b.d); }
+/* a division by a constant is a multiply by its reciprocal */
+static inline cdbl operator/(const cdbl &a, const cdbl &b) {
+    opc::add(b.d ? opc::C_DIV : opc::C_MUL, a.d || b.d);
+    return cdbl::mk(a.v / b.v, a.d || b.d);
+}
+#define OPC_CMP(op) \
+    static inline bool operator op(const cdbl &a, const cdbl &b) { opc::add(opc::C_CMP, a.d || b.d); return a.v op b.v; }
+OPC_CMP(<)
+OPC_CMP(>)
+OPC_CMP(<=)
+OPC_CMP(>=)
+OPC_CMP(==)
+OPC_CMP(!=)
+#undef OPC_CMP
+static inline bool operator!(const cdbl &a) { return !(a.v != 0.0); }
+static inline cdbl fabs(const cdbl &a) { opc::add(opc::C_ABS, a.d); return cdbl::mk(::fabs(a.v), a.d); }
+static inline cdbl sqrt(const cdbl &a) { opc::add(opc::C_SQRT, a.d); return cdbl::mk(::sqrt(a.v), a.d); }
+static inline cdbl log(const cdbl &a) { opc::add(opc::C_LOG, a.d); return cdbl::mk(::log(a.v), a.d); }
+static inline cdbl exp(const cdbl &a) { opc::add(opc::C_EXP, a.d); return cdbl::mk(::exp(a.v), a.d); }
+static inline cdbl pow(const cdbl &a, const cdbl &b) { opc::add(opc::C_POW, a.d || b.d); return cdbl::mk(::pow(a.v, b.v), a.d || b.d); }
+static inline cdbl fmin(const cdbl &a, const cdbl &b) { opc::add(opc::C_CMP, a.d || b.d); return cdbl::mk(::fmin(a.v, b.v), a.d || b.d); }
+static inline cdbl fmax(const cdbl &a, const cdbl &b) { opc::add(opc::C_CMP, a.d || b.d); return cdbl::mk(::fmax(a.v, b.v), a.d || b.d); }
+
+namespace opc {
+/* states identified as solution nodes: address -> (node, values at tag time) */
+struct Tag { long id; double q[4]; };
+static std::unordered_map<const void *, Tag> tags;
+static std::unordered_set<std::string> seen;
+static const void *scope_u = nullptr;
+static double scope_t = -1e300;
+static const int node_level[] = {1, 2, 3, 4, 5, 6, 11};   // PF_ ids counted as node preparation
+
+static void tag(const cdbl *q, long id) {
+    Tag t;
+    t.id = id;
+    for (int v = 0; v < 4; ++v) t.q[v] = q[v].v;
+    tags[(const void *)q] = t;
+}
+static bool ident(const cdbl *q, long *id) {
+    auto it = tags.find((const void *)q);
+    if (it == tags.end()) return false;
+    for (int v = 0; v < 4; ++v)
+        if (memcmp(&it->second.q[v], &q[v].v, sizeof(double)) != 0) return false;
+    *id = it->second.id;
+    return true;
+}
+static void scope(const cdbl *u, const cdbl &t) {
+    if ((const void *)u == scope_u && t.v == scope_t) return;
+    scope_u = (const void *)u;
+    scope_t = t.v;
+    seen.clear();
+    tags.clear();
+}
+static void put(std::string &k, double x) { k.append((const char *)&x, sizeof x); }
+
+/* Guard of a pure function: counting is suspended for the call when the same
+   evaluation was counted before; node-level primitives count as node
+   preparation. */
+struct Guard {
+    bool suspended = false, moved = false;
+    int saved_row = 0;
+    Guard(int fid, int kind, const cdbl *a, const cdbl *b, std::initializer_list<cdbl> xs) {
+        long ia = 0, ib = 0;
+        if (!ident(a, &ia)) return;
+        if (b && !ident(b, &ib)) return;
+        if (kind == 1 && ib < ia) { long t = ia; ia = ib; ib = t; }
+        std::string k;
+        k.append((const char *)&fid, sizeof fid);
+        k.append((const char *)&ia, sizeof ia);
+        k.append((const char *)&ib, sizeof ib);
+        for (const cdbl &x : xs) put(k, (fid == 5 || fid == 12) ? ::fabs(x.v) : x.v);
+        if (seen.count(k)) {
+            suspended = true;
+            ++off;
+        } else {
+            seen.insert(k);
+        }
+        if (!b)
+            for (int n : node_level)
+                if (n == fid) { moved = true; saved_row = row; row = 1; }
+    }
+    ~Guard() {
+        if (suspended) --off;
+        if (moved) row = saved_row;
+    }
+};
+}  // namespace opc
+
+#define ORC_COUNTING 1
+#define ORC_ROW(r) (opc::row = (r))
+#define ORC_PURE(fid, st, ...) opc::Guard orc_guard_(fid, 0, st, nullptr, {__VA_ARGS__})
+#define ORC_PURE_PAIR(fid, a, b, ...) opc::Guard orc_guard_(fid, 1, a, b, {__VA_ARGS__})
+#define ORC_PURE2(fid, a, b, ...) opc::Guard orc_guard_(fid, 2, a, b, {__VA_ARGS__})
+#define ORC_TAG(q, g) opc::tag(q, g)
+#define ORC_SCOPE(u, t) opc::scope(u, t)
+#define ORC_CONST(x) ((x).d = false)
+
+#define double cdbl
+#include "idp_oracle.c"
+#undef double
+
+/* node preparation, counted once per node and stage: the primitives that the
+   later steps take from each node (velocity, pressure, sound speed, rho/p,
+   the physical fluxes along x and y, the wave speeds along x and y) */
+static void orc_count_node_prep(const orc_ctx *c, const cdbl *u) {
+    int saved = opc::row;
+    opc::row = ROW_NODE_PREP;
+    for (int i = 0; i < c->nn; ++i) {
+        cdbl q[4], v1, v2, f[4];
+        get_u(c, u, i, q);
+        velocity(q, &v1, &v2);
+        (void)pressure(c->gamma, q);
+        (void)sound_speed(c->gamma, q);
+        (void)rho_over_p(c->gamma, q);
+        flux_n(c->gamma, q, 1.0, 0.0, f);
+        flux_n(c->gamma, q, 0.0, 1.0, f);
+        (void)wave_speed(c->gamma, q, 1.0, 0.0);
+        (void)wave_speed(c->gamma, q, 0.0, 1.0);
+    }
+    opc::row = saved;
+}
+
+/* One SSP-RK3 step of the oracle on the given mesh and state (plain double
+   arrays, as orc_create and orc_step take them). counts[row][class] receive
+   the tallies (ROW_COUNT x 9); u is advanced in place. Returns 0 on success. */
+extern "C" int opc_count_step(int N, double gamma, int nx0, int ny0, double x0, double y0, double x1,
+                              double y1, int K, const int8_t *level, const int32_t *ix, const int32_t *iy,
+                              const int32_t *bc, const double *bc_prim, const double *dmr_post,
+                              const double *dmr_pre, double *u_io, double t0, double cfl, int limiting,
+                              int vflux, long long *counts) {
+    std::vector<cdbl> bcp(16), post(4), pre(4);
+    for (int k = 0; k < 16; ++k) bcp[k] = bc_prim[k];
+    for (int k = 0; k < 4; ++k) { post[k] = dmr_post[k]; pre[k] = dmr_pre[k]; }
+    int err = 0;
+    orc_ctx *c = orc_create(N, gamma, 1, nx0, ny0, x0, y0, x1, y1, K, level, ix, iy, bc, bcp.data(),
+                            post.data(), pre.data(), 0, &err);
+    if (!c) return 1;
+    orc_set_volume_flux(c, vflux);
+    size_t n = 4 * (size_t)c->nn;
+    std::vector<cdbl> u(n);
+    for (size_t k = 0; k < n; ++k) u[k] = cdbl::mk(u_io[k], true);
+    memset(opc::cnt, 0, sizeof opc::cnt);
+    opc::row = ROW_OTHER;
+    cdbl t = t0, st[NSTAT], dth[1];
+    orc_stats_init(st);
+    orc_step(c, u.data(), 1, &t, cfl, 0, limiting, 0.1, 0, 0, dth, st);
+    for (size_t k = 0; k < n; ++k) u_io[k] = u[k].v;
+    for (int r = 0; r < ROW_COUNT; ++r)
+        for (int k = 0; k < opc::N_CLS; ++k) counts[r * opc::N_CLS + k] = opc::cnt[r][k];
+    orc_destroy(c);
+    return 0;
+}
+
+extern "C" int opc_n_rows(void) { return ROW_COUNT; }

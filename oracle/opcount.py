@@ -1,0 +1,130 @@
+"""Op counts of the method from the oracle's counting build (opcount.cpp).
+
+TEST AND MEASUREMENT INFRASTRUCTURE: the tests call it, and running it as a
+script writes the work table that the benchmark's roofline reads
+(``paper_2607_06045_b300/method_work.json``). The numbers are the oracle's
+own arithmetic for one SSP-RK3 step, tallied per step of the hot path and
+per operation class, normalised per node and stage.
+
+  python -m oracle.opcount            # rewrite the work table
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "opcount.cpp")
+_LIB = os.path.join(_HERE, "libopcount.so")
+_lib = None
+
+ROWS = ["other", "node_prep", "volume_flux", "subcell_fv", "face_flux", "mortar_flux", "low_update", "bounds",
+        "volume_limit", "mortar_limit", "stage", "dt", "reform", "stats"]
+CLASSES = ["add", "mul", "div", "sqrt", "log", "exp", "pow", "cmp", "abs"]
+# rows that are the method's work (the re-formed quantities and the
+# statistics are tallied apart)
+METHOD_ROWS = ["node_prep", "volume_flux", "subcell_fv", "face_flux", "mortar_flux", "low_update", "bounds",
+               "volume_limit", "mortar_limit", "stage", "dt"]
+# flops per operation: every floating-point operation the oracle performs
+# counts as one flop (add, multiply, divide, square root, logarithm,
+# exponential, power, compare, absolute value), a fixed convention that no
+# kernel's own routines enter; the per-class counts stay in the table
+WEIGHTS = {k: 1 for k in CLASSES}
+
+
+def build(force: bool = False) -> str:
+    srcs = [_SRC, os.path.join(_HERE, "idp_oracle.c")]
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(p) for p in srcs):
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fpermissive", "-w", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", _LIB, _SRC], cwd=_HERE)
+    return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = C.CDLL(build())
+        dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
+        L.opc_count_step.restype = C.c_int
+        L.opc_count_step.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double,
+                                     C.c_double, C.c_int, C.POINTER(C.c_int8), ip, ip, ip, dp, dp, dp, dp,
+                                     C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
+        L.opc_n_rows.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def count_step(mesh, N, u, cfl=0.5, limiting=2, gamma=1.4, vflux=0, t0=0.0):
+    """One counted SSP-RK3 step. Returns (counts[row][class] as a dict of
+    dicts of ints, u after the step)."""
+    L = lib()
+    nrow = L.opc_n_rows()
+    assert nrow == len(ROWS), (nrow, len(ROWS))
+    lev = np.ascontiguousarray(mesh.level, dtype=np.int8)
+    ix = np.ascontiguousarray(mesh.ix, dtype=np.int32)
+    iy = np.ascontiguousarray(mesh.iy, dtype=np.int32)
+    bc = np.ascontiguousarray(mesh.bc, dtype=np.int32)
+    bcp = np.ascontiguousarray(mesh.bc_prim, dtype=np.float64).reshape(16)
+    post = np.ascontiguousarray(mesh.dmr_post, dtype=np.float64)
+    pre = np.ascontiguousarray(mesh.dmr_pre, dtype=np.float64)
+    uu = np.ascontiguousarray(u, dtype=np.float64).copy()
+    out = np.zeros(nrow * len(CLASSES), dtype=np.int64)
+    dp = C.POINTER(C.c_double)
+    ip = C.POINTER(C.c_int32)
+    x0, y0, x1, y1 = mesh.box
+    rc = L.opc_count_step(N, gamma, mesh.nx0, mesh.ny0, x0, y0, x1, y1, mesh.n_elems,
+                          lev.ctypes.data_as(C.POINTER(C.c_int8)), ix.ctypes.data_as(ip), iy.ctypes.data_as(ip),
+                          bc.ctypes.data_as(ip), bcp.ctypes.data_as(dp), post.ctypes.data_as(dp),
+                          pre.ctypes.data_as(dp), uu.ctypes.data_as(dp), t0, cfl, limiting, vflux,
+                          out.ctypes.data_as(C.POINTER(C.c_longlong)))
+    if rc != 0:
+        raise ValueError("counting build rejected the mesh")
+    cnt = out.reshape(nrow, len(CLASSES))
+    return {r: {k: int(cnt[i, j]) for j, k in enumerate(CLASSES)} for i, r in enumerate(ROWS)}, uu
+
+
+def per_node_stage(counts, n_nodes):
+    """Counts per node and stage (a step has three stages)."""
+    return {r: {k: v / (3.0 * n_nodes) for k, v in cl.items()} for r, cl in counts.items()}
+
+
+def flops(classes: dict) -> float:
+    return float(sum(WEIGHTS[k] * v for k, v in classes.items()))
+
+
+def work_table(degrees=(1, 2, 3, 4, 5, 6, 7)):
+    """Per-node-and-stage op counts by row and class, and the method's flops,
+    on the 1/16-size double-Mach-reflection instance (its local limiting,
+    shock and quiescent regions in the proportions of the full mesh)."""
+    sys.path.insert(0, os.path.dirname(_HERE))
+    from paper_2607_06045_b300 import workloads as W
+    m = W.dmr_sample_mesh()
+    table = {"workload": "double Mach reflection, 64x16 base + 3 levels (dmr_sample_mesh), one SSP-RK3 step "
+                         "from the initial state, local + positivity limiting, CFL 0.5",
+             "elements": int(m.n_elems), "weights": WEIGHTS, "method_rows": METHOD_ROWS, "degrees": {}}
+    for N in degrees:
+        u = W.dmr_state(m, N)
+        c, _ = count_step(m, N, u)
+        nodes = m.n_elems * (N + 1) ** 2
+        pn = per_node_stage(c, nodes)
+        rows = {r: {"ops": {k: round(v, 4) for k, v in pn[r].items() if v}, "flops": round(flops(pn[r]), 3)}
+                for r in ROWS}
+        total = sum(rows[r]["flops"] for r in METHOD_ROWS)
+        table["degrees"][str(N)] = {"nodes": nodes, "rows": rows, "method_flops_per_node_stage": round(total, 3)}
+    return table
+
+
+TABLE = os.path.join(os.path.dirname(_HERE), "paper_2607_06045_b300", "method_work.json")
+
+if __name__ == "__main__":
+    t = work_table()
+    with open(TABLE, "w") as f:
+        json.dump(t, f, indent=1, sort_keys=True)
+        f.write("\n")
+    for N, d in t["degrees"].items():
+        print(N, d["method_flops_per_node_stage"], {r: d["rows"][r]["flops"] for r in ROWS})

@@ -1,5 +1,20 @@
-"""Algorithmic FP64 work per node and stage of the element pass (the roofline
-numerator).
+"""Work per node and stage of the hot path's kernels: the roofline numerators.
+
+Two views are kept.
+
+The method's work (``method_*``): the floating-point operations of the
+method, counted on the oracle's own arithmetic by its op-counting build for
+one SSP-RK3 step of the double-Mach-reflection instance, per step of the hot
+path and normalised per node and stage (``method_work.json``, written by
+``python -m oracle.opcount`` and checked by the tests). Every operation counts
+as one flop. In the FP32 form the flux rows (node preparation, volume,
+subcell, face and mortar fluxes) are FP32 work and the rest FP64, as the form
+defines them; its roofline time is the FP64 work over the FP64 peak plus the
+FP32 work over the FP32 peak.
+
+The issued FP64 view (``element_ops_per_node`` and below) follows the
+kernels' own FP64 instruction economy and is kept as the FP64-issue
+efficiency beside the method's roofline:
 
 B300 runs FP64 at 1/64 of the FP32 rate (measured 1.20 TFLOP/s with DFMA),
 so the element pass is bound by the FP64 pipe; HBM traffic (about 100 bytes
@@ -17,7 +32,65 @@ counted. Conforming face fluxes are counted once per face.
 """
 from __future__ import annotations
 
+import json
+import os
 from dataclasses import dataclass
+
+_TABLE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "method_work.json")
+_work = None
+
+# rows of the hot path computed in FP32 by the FP32 form
+FP32_FORM_FP32_ROWS = ("node_prep", "volume_flux", "subcell_fv", "face_flux", "mortar_flux")
+# the kernels that carry each row: the element pass (its face kernel takes
+# the face row where it runs), the mortar flux kernel, the mortar limiting
+# kernels (the factors and their application share the row) and the time step
+ELEMENT_ROWS = ("node_prep", "volume_flux", "subcell_fv", "face_flux", "low_update", "bounds", "volume_limit",
+                "stage")
+KERNEL_ROWS = {"element": ELEMENT_ROWS, "face": ("face_flux",), "mortar_flux": ("mortar_flux",),
+               "mortar_limit": ("mortar_limit",), "dt": ("dt",)}
+
+
+def method_table() -> dict:
+    """The work table of the oracle's counting build."""
+    global _work
+    if _work is None:
+        with open(_TABLE) as f:
+            _work = json.load(f)
+    return _work
+
+
+def method_rows(N: int) -> dict:
+    """Flops per node and stage of each row of the hot path at degree N."""
+    d = method_table()["degrees"][str(N)]
+    return {r: v["flops"] for r, v in d["rows"].items()}
+
+
+def method_flops(N: int, rows, precision: int = 0):
+    """(FP64 flops, FP32 flops) per node and stage of the given rows: all FP64
+    in the FP64 path; the flux rows in FP32 in the FP32 form."""
+    r = method_rows(N)
+    f64 = sum(r[k] for k in rows if precision == 0 or k not in FP32_FORM_FP32_ROWS)
+    f32 = sum(r[k] for k in rows if precision == 1 and k in FP32_FORM_FP32_ROWS)
+    return f64, f32
+
+
+def method_kernel_work(N: int, precision: int, K: int, face_kernel=None) -> dict:
+    """Per launch: (FP64 flops, FP32 flops) of each kernel's rows over the K
+    elements of one launch (the mortar rows are per node of the whole mesh,
+    as the table normalises them). With the face kernel the face row is its
+    work and the rest the element kernel's."""
+    nodes = K * (N + 1) ** 2
+    if face_kernel is None:
+        face_kernel = precision == 0
+    out = {}
+    for name, rows in KERNEL_ROWS.items():
+        if name == "face" and not face_kernel:
+            continue
+        if name == "element" and face_kernel:
+            rows = tuple(r for r in rows if r != "face_flux")
+        a, b = method_flops(N, rows, precision)
+        out[name] = (a * nodes, b * nodes)
+    return out
 
 
 @dataclass
