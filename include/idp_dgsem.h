@@ -300,7 +300,9 @@ idp_status idp_eval_math(int32_t fn, const double *x, double *y, int64_t n, void
  * w_i w_j u[v][e][j][i], the same totals as idp_dgsem_integrals, with no
  * context. All pointers are caller-owned DEVICE memory: u (layout as above,
  * n_elems elements, degree N), elem_area (n_elems values dx * dy),
- * sim_elem_offsets (n_sims + 1 values) and out (4 * n_sims values). The
+ * sim_elem_offsets (n_sims + 1 values; each is clamped to [0, n_elems], so
+ * an offset out of range sums fewer elements, never memory beyond this
+ * call's partials) and out (4 * n_sims values). The
  * per-element partial sums go to a fixed array of 4 * IDP_NOALLOC_MAX_ELEMS
  * doubles (16 MiB) that the library keeps on every device it is used on
  * until the process exits; n_elems above IDP_NOALLOC_MAX_ELEMS returns

@@ -36,6 +36,20 @@ def build(force: bool = False) -> str:
     return _LIB
 
 
+_LIB_OMP = os.path.join(_HERE, "liboracle_omp.so")
+
+
+def build_omp(force: bool = False) -> str:
+    """The same source with OpenMP over the loops whose iterations write
+    disjoint outputs (the all-cores CPU baseline; same bits as the serial
+    build)."""
+    if force or not os.path.exists(_LIB_OMP) or os.path.getmtime(_LIB_OMP) < os.path.getmtime(_SRC):
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fopenmp", "-fPIC",
+               "-shared", "-o", _LIB_OMP, _SRC, "-lm"]
+        subprocess.check_call(cmd)
+    return _LIB_OMP
+
+
 def lib():
     """The loaded oracle library (built on first use)."""
     global _lib
@@ -130,6 +144,8 @@ def load(path: str):
     L.orc_set_iface_dbg_out.argtypes = [dp]
     L.orc_set_force_ell.argtypes = [C.c_double]
     L.orc_face_sparse.argtypes = [C.c_int, C.c_int, C.c_double, dp, dp, dp, dp]
+    L.orc_set_threads.restype = C.c_int
+    L.orc_set_threads.argtypes = [C.c_int]
     return L
 
 

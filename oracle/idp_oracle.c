@@ -66,6 +66,21 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* Built with -fopenmp (the all-cores CPU baseline), the loops marked
+   ORC_PARALLEL run their iterations on all threads: each iteration writes
+   only its own node's, interface's or element's outputs, so the results are
+   the same bits as the serial build's. Every sum across iterations stays
+   serial. */
+#define ORC_PRAGMA(x) _Pragma(#x)
+#ifdef _OPENMP
+#define ORC_PARALLEL ORC_PRAGMA(omp parallel for schedule(static))
+#else
+#define ORC_PARALLEL
+#endif
 
 #define NPMAX 9
 #define NSTAT 16
@@ -786,6 +801,7 @@ static void ghost_state(const orc_ctx *c, const double *u, int e, int s, int t, 
 
 static double *make_ghosts(const orc_ctx *c, const double *u, double time) {
     double *gh = malloc(sizeof(double) * 4 * (c->ng + 1));
+    ORC_PARALLEL
     for (int k = 0; k < c->ng; ++k) ghost_state(c, u, c->g_elem[k], c->g_side[k], c->g_t[k], time, gh + 4 * k);
     return gh;
 }
@@ -858,6 +874,7 @@ static double *surface_fluxes_b(const orc_ctx *c, const double *u, const double 
     int np = c->np, K = c->K;
     double *sf = calloc((size_t)K * 4 * np * 4, sizeof(double));
     double g = c->gamma;
+    ORC_PARALLEL
     for (int e = 0; e < K; ++e)
         for (int s = 0; s < 4; ++s) {
             int ft = c->ftype[4 * e + s];
@@ -941,7 +958,7 @@ static double *surface_fluxes_b(const orc_ctx *c, const double *u, const double 
 /* mass-weighted high-order residual J w_i w_j du/dt (Eq. evolutionformula) */
 static void dg_residual(const orc_ctx *c, const double *u, const double *sf, double *res) {
     int np = c->np, N = c->N;
-    double g = c->gamma;
+    ORC_PARALLEL
     for (int e = 0; e < c->K; ++e)
         for (int j = 0; j < np; ++j)
             for (int i = 0; i < np; ++i) {
@@ -1017,6 +1034,7 @@ static void dg_subcell_flux(const orc_ctx *c, const double *u, int e, int d, int
 
 static void fv_residual(const orc_ctx *c, const double *u, const double *gh, double *res, double *dsum) {
     double g = c->gamma;
+    ORC_PARALLEL
     for (int i = 0; i < c->nn; ++i) {
         double ui[4], uj[4], acc[4] = {0, 0, 0, 0}, s2d = 0.0;
         get_u(c, u, i, ui);
@@ -1049,6 +1067,8 @@ double orc_dt(const orc_ctx *c, const double *u, double time, double cfl, int ru
     ORC_ROW(ROW_DT);
     if (rule == 0) {
         double *gh = make_ghosts(c, u, time);
+        double *tq = malloc(sizeof(double) * c->nn);
+        ORC_PARALLEL
         for (int i = 0; i < c->nn; ++i) {
             /* sum_j 2 d_ij over the node's graph neighbours, as in the
                low-order residual */
@@ -1061,10 +1081,10 @@ double orc_dt(const orc_ctx *c, const double *u, double time, double cfl, int ru
                 double d = nrm * lambda_max(c->gamma, ui, uj, b->cx / nrm, b->cy / nrm);
                 s2d += 2.0 * d;
             }
-            double t = mass(c, i) / s2d;
-            if (t < best) best = t;
+            tq[i] = mass(c, i) / s2d;
         }
-        free(gh);
+        for (int i = 0; i < c->nn; ++i) if (tq[i] < best) best = tq[i];
+        free(gh); free(tq);
     } else {
         int np = c->np;
         for (int i = 0; i < c->nn; ++i) {
@@ -1296,11 +1316,13 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     /* low-order update */
     ORC_ROW(ROW_LOW_UPDATE);
     double *ufv = malloc(sizeof(double) * 4 * nn);
+    ORC_PARALLEL
     for (int i = 0; i < nn; ++i) {
         double m = mass(c, i);
         for (int v = 0; v < 4; ++v) ufv[(size_t)v * nn + i] = u[(size_t)v * nn + i] + dt / m * rfv[(size_t)v * nn + i];
-        if (dt * ds[i] / m > 1.0 && stats) stats[ST_DTX] += 1;
     }
+    for (int i = 0; i < nn; ++i)
+        if (dt * ds[i] / mass(c, i) > 1.0 && stats) stats[ST_DTX] += 1;
     /* bounds (R6 and Eqs. Bounds_Positivity, Bounds_Barstates) */
     ORC_ROW(ROW_BOUNDS);
     double *rmin = malloc(sizeof(double) * nn), *rmax = malloc(sizeof(double) * nn), *pmin = malloc(sizeof(double) * nn);
@@ -1318,6 +1340,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     /* entropy lower bound per node (R21), relaxed: K = eta_min (1 - ETA_RELAX) */
     const int ent = entropy && limiting >= 2;
     double *emin = malloc(sizeof(double) * nn);
+    ORC_PARALLEL
     for (int i = 0; i < nn; ++i) {
         double ui[4], uj[4], q[4];
         get_u(c, u, i, ui);
@@ -1373,6 +1396,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
        the +x (+y) direction, mass-weighted; node a gets -l A, node a+1 +l A */
     int nif = K * 2 * np * N;
     double *A = malloc(sizeof(double) * 4 * nif);
+    ORC_PARALLEL
     for (int e = 0; e < K; ++e)
         for (int d = 0; d < 2; ++d)
             for (int r = 0; r < np; ++r)
@@ -1408,6 +1432,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     double *tolr = malloc(sizeof(double) * nn);
     for (int i = 0; i < nn; ++i) tolr[i] = TOL * fabs(ufv[i]);
     char *exempt = malloc(nif);
+    ORC_PARALLEL
     for (int e = 0; e < K; ++e)
         for (int d = 0; d < 2; ++d)
             for (int r = 0; r < np; ++r)
@@ -1421,6 +1446,7 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     /* R7: Zalesak factors for density */
     double *Rp = malloc(sizeof(double) * nn), *Rm = malloc(sizeof(double) * nn);
     double *Rp2 = malloc(sizeof(double) * nn), *Rm2 = malloc(sizeof(double) * nn);
+    ORC_PARALLEL
     for (int i = 0; i < nn; ++i) {
         int e = i / (np * np), rr = i % (np * np), a = rr % np, b = rr / np;
         double Pp = 0.0, Pm = 0.0;
@@ -1455,6 +1481,8 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     double *ell = malloc(sizeof(double) * nif);
     double *lmin = malloc(sizeof(double) * nn);
     for (int i = 0; i < nn; ++i) lmin[i] = 1.0;
+    /* (an element's interfaces touch only its own nodes' lmin) */
+    ORC_PARALLEL
     for (int e = 0; e < K; ++e)
         for (int d = 0; d < 2; ++d)
             for (int r = 0; r < np; ++r)
@@ -1641,6 +1669,18 @@ int orc_stage(const orc_ctx *c, const double *u, double time, double dt, int lim
     return 0;
 }
 
+/* threads of the OpenMP build (no effect in the serial build); returns the
+   count in use */
+int orc_set_threads(int n) {
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 void orc_stats_init(double *stats) {
     for (int k = 0; k < NSTAT; ++k) stats[k] = 0.0;
     stats[ST_MINRHO] = INFINITY; stats[ST_MINP] = INFINITY;
@@ -1669,12 +1709,15 @@ int orc_step(const orc_ctx *c, double *u, int nsteps, double *time, double cfl, 
         ORC_CONST(dt);
         if (dt_hist) dt_hist[s] = dt;
         orc_stage(c, u, *time, dt, limiting, beta, bounds, entropy, res, ut, stats);
+        ORC_PARALLEL
         for (size_t k = 0; k < n; ++k) u1[k] = ut[k];
         orc_stage(c, u1, *time + dt, dt, limiting, beta, bounds, entropy, res, ut, stats);
         ORC_ROW(ROW_STAGE);
+        ORC_PARALLEL
         for (size_t k = 0; k < n; ++k) u2[k] = 0.75 * u[k] + 0.25 * ut[k];
         orc_stage(c, u2, *time + 0.5 * dt, dt, limiting, beta, bounds, entropy, res, ut, stats);
         ORC_ROW(ROW_STAGE);
+        ORC_PARALLEL
         for (size_t k = 0; k < n; ++k) u[k] = u[k] / 3.0 + 2.0 / 3.0 * ut[k];
         *time += dt;
     }

@@ -50,11 +50,15 @@ __global__ void k_partials_noalloc(const double *__restrict__ u, const double *_
     }
 }
 
-// per simulation: fixed-order tree sum of the partials in [off[s], off[s+1])
-__global__ void k_segments_noalloc(const double *part, const int64_t *off, double *out) {
+// per simulation: fixed-order tree sum of the partials in [off[s], off[s+1]),
+// the offsets clamped to [0, K] (the partials of this call), so that a bad
+// offset sums fewer partials instead of stale ones or memory past the array
+__global__ void k_segments_noalloc(const double *part, const int64_t *off, long long K, double *out) {
     __shared__ double red[4][256];
     const int s = blockIdx.x;
-    const long long b = off[s], e = off[s + 1];
+    long long b = off[s], e = off[s + 1];
+    b = b < 0 ? 0 : (b > K ? K : b);
+    e = e < b ? b : (e > K ? K : e);
     double acc[4] = {0, 0, 0, 0};
     for (long long k = b + threadIdx.x; k < e; k += blockDim.x)
         for (int v = 0; v < 4; ++v) acc[v] += part[(size_t)v * IDP_NOALLOC_MAX_ELEMS + k];
@@ -106,6 +110,6 @@ extern "C" idp_status idp_integrals_noalloc(const double *u, const double *elem_
     int blocks = (int)((n_elems + 255) / 256);
     if (blocks > 4096) blocks = 4096;
     k_partials_noalloc<<<blocks, 256, 0, s>>>(u, elem_area, (int)n_elems, N + 1, W, part);
-    k_segments_noalloc<<<n_sims, 256, 0, s>>>(part, sim_elem_offsets, out);
+    k_segments_noalloc<<<n_sims, 256, 0, s>>>(part, sim_elem_offsets, (long long)n_elems, out);
     return cudaGetLastError() == cudaSuccess ? IDP_OK : IDP_E_CUDA;
 }

@@ -155,7 +155,12 @@ def idp_integrals_noalloc(u, elem_area, N, sim_offsets, out, stream=None):
     int64 [n_sims+1], out FP64 [n_sims][4]). Returns the status code."""
     import torch
     assert elem_area.is_cuda and elem_area.dtype == torch.float64 and sim_offsets.dtype == torch.int64
-    assert out.is_cuda and out.dtype == torch.float64
+    assert out.is_cuda and out.dtype == torch.float64 and out.is_contiguous()
+    assert elem_area.is_contiguous() and sim_offsets.is_cuda and sim_offsets.is_contiguous()
+    # u must hold the elements the areas describe, at degree N
+    assert u.is_cuda and u.dtype == torch.float64 and u.is_contiguous()
+    assert tuple(u.shape) == (4, elem_area.shape[0], N + 1, N + 1), (tuple(u.shape), elem_area.shape[0], N)
+    assert out.numel() >= 4 * (sim_offsets.shape[0] - 1)
     return lib().idp_integrals_noalloc(_ptr(u), C.c_void_p(elem_area.data_ptr()), int(elem_area.shape[0]), int(N),
                                        C.c_void_p(sim_offsets.data_ptr()), int(sim_offsets.shape[0] - 1),
                                        C.c_void_p(out.data_ptr()), _stream(stream))

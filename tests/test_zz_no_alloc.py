@@ -5,10 +5,13 @@ Callers that may not allocate device memory -- code recording a CUDA graph, a
 framework with a fixed memory budget, a host callback -- use that entry
 point; its scratch is a fixed array inside the library, shared by all calls.
 The second call uses a smaller mesh than the first, so a stale partial left
-in the shared scratch would show up in its totals."""
+in the shared scratch would show up in its totals. Both calls are also
+compared with the oracle's totals, and an offset beyond the mesh is clamped
+to the call's own elements."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2607_06045_b300 import build, idp
 from paper_2607_06045_b300 import workloads as W
 
@@ -46,7 +49,32 @@ def test_noalloc_integrals_match_context_integrals():
         torch.cuda.synchronize()
         got = out.cpu().numpy()
         np.testing.assert_allclose(got, ref, rtol=1e-13, atol=0.0)
+        # and against the oracle's totals of each simulation
+        for k, (m, uk) in enumerate(zip(meshes, us)):
+            tot = oracle.Oracle(m, N).integrals(uk)
+            scale = np.abs(uk).reshape(4, -1).max(axis=1) * areas([m]).sum()
+            assert np.all(np.abs(got[k] - tot) <= 1e-13 * scale), (got[k], tot)
         ctx.close()
+
+
+def test_noalloc_offsets_are_clamped():
+    # an offset beyond the mesh sums only this call's partials: the totals
+    # equal those of the elements that exist
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    m, N = W.square_mesh(), 3
+    u = W.random_state(m, N, seed=5)
+    ud = torch.from_numpy(u).cuda()
+    area = torch.from_numpy(areas([m])).cuda()
+    K = m.n_elems
+    off = torch.tensor([0, K + 1000], dtype=torch.int64, device="cuda")
+    out = torch.zeros((1, 4), dtype=torch.float64, device="cuda")
+    assert idp.idp_integrals_noalloc(ud, area, N, off, out) == idp.IDP_OK
+    torch.cuda.synchronize()
+    tot = oracle.Oracle(m, N).integrals(u)
+    scale = np.abs(u).reshape(4, -1).max(axis=1) * areas([m]).sum()
+    assert np.all(np.abs(out.cpu().numpy()[0] - tot) <= 1e-13 * scale)
 
 
 def test_noalloc_rejects_oversized_meshes():
