@@ -207,20 +207,93 @@ def node_masses(mesh, N):
 
 
 def l1_per_field(u, ref, m):
-    """sum m |u - ref| / sum m |ref| per conserved field (rho, rho v1, rho v2, E)."""
-    return {f: float((m * np.abs(u[v] - ref[v])).sum() / max((m * np.abs(ref[v])).sum(), 1e-300))
-            for v, f in enumerate(("rho", "rho_v1", "rho_v2", "E"))}
+    """Mass-weighted L1 difference per conserved field: sum m |u - ref| over
+    sum m |ref| for rho and E, over sum m (|ref| + sqrt(rho E)) for the
+    momenta (the state's momentum scale; a fluid at rest has none of its
+    own)."""
+    ps = np.sqrt(np.abs(ref[0] * ref[3]))
+    out = {}
+    for v, f in enumerate(("rho", "rho_v1", "rho_v2", "E")):
+        den = (m * np.abs(ref[v])).sum() + ((m * ps).sum() if v in (1, 2) else 0.0)
+        out[f] = float((m * np.abs(u[v] - ref[v])).sum() / max(den, 1e-300))
+    return out
+
+
+def parity_samples():
+    """The parity-sized samples on which each FP32-form result states its L1
+    error against the FP64 oracle: the 1/16 DMR instance (N = 3), the three
+    smallest simulations of the batch (N = 3, as one batched context) and the
+    near-vacuum blast on a 16 x 16 base (N = 5); five SSP-RK3 steps each."""
+    from paper_2607_06045_b300 import workloads as W
+    out = {}
+    m = W.dmr_sample_mesh()
+    out["fp32_form"] = dict(meshes=[m], N=3, u=[W.dmr_state(m, 3)], gamma=1.4,
+                            sample="1/16 DMR instance (64x16 base + 3 levels), N=3, 5 steps")
+    ms = W.batch_meshes(256, seed=0)
+    rng = np.random.default_rng(1)
+    us = [W.riemann4_state(mm, 3, rng) for mm in ms]
+    small = np.argsort([mm.n_elems for mm in ms])[:3].tolist()
+    out["batched_fp32"] = dict(meshes=[ms[k] for k in small], N=3, u=[us[k] for k in small], gamma=1.4,
+                               sample=f"simulations {small} of the 256 (the three smallest), one batched context, "
+                                      f"N=3, 5 steps")
+    mv, cv = W.blast_mesh(n0=16)
+    out["near_vacuum_fp32"] = dict(meshes=[mv], N=5, u=[W.blast_state(mv, 5, cv)], gamma=1.4,
+                                   sample="near-vacuum blast on a 16x16 base + 2 levels, N=5, 5 steps")
+    return out
+
+
+PARITY_STEPS = 5
+
+
+def cpu_baseline_parity_refs(samples):
+    """CPU-baseline leg: the oracle (all host threads) on each parity sample."""
+    import oracle
+    refs = {}
+    with oracle.using(oracle.build_omp()) as L:
+        L.orc_set_threads(os.cpu_count() or 1)
+        for name, smp in samples.items():
+            refs[name] = []
+            for m, u in zip(smp["meshes"], smp["u"]):
+                o = oracle.Oracle(m, smp["N"], gamma=smp["gamma"])
+                uo, _, _, _ = o.step(u, PARITY_STEPS, cfl=0.5, limiting=2)
+                refs[name].append(uo)
+    return refs
+
+
+def l1_vs_oracle(samples, refs):
+    """The FP32 form on each parity sample on the GPU against the oracle's
+    states: per-field L1 (l1_per_field), the worst over a sample's
+    simulations."""
+    import torch
+    from paper_2607_06045_b300 import idp
+    from paper_2607_06045_b300 import workloads as W
+    out = {}
+    for name, smp in samples.items():
+        ms, N = smp["meshes"], smp["N"]
+        ctx = idp.Context(ms if len(ms) > 1 else ms[0], N, precision=1, limiting=2, cfl=0.5)
+        ud = torch.from_numpy(W.concat_states(smp["u"])).cuda()
+        t = np.zeros(len(ms))
+        ctx.idp_dgsem_step(ud, PARITY_STEPS, t)
+        ug = ud.cpu().numpy()
+        off = ctx.sim_offsets
+        worst = {}
+        for k, (m, uo) in enumerate(zip(ms, refs[name])):
+            e = l1_per_field(ug[:, off[k]:off[k + 1]], uo, node_masses(m, N))
+            worst = {f: max(worst.get(f, 0.0), v) for f, v in e.items()}
+        ctx.close()
+        out[name] = dict(worst, steps=PARITY_STEPS, sample=smp["sample"], reference="FP64 oracle")
+    return out
 
 
 def method_work(roofline, N, precision, K, M, n_mnodes, w):
     """Per kernel and launch: (FP64 flops, FP32 flops, HBM bytes), the flops
     from the method's work table (the oracle's counting build), the bytes
-    from the kernels' algorithmic traffic; the mortar application kernel's
-    roofline is its traffic."""
+    from the kernels' algorithmic traffic."""
     fl = roofline.method_kernel_work(N, precision, K)
-    by = roofline.kernel_work(N, precision, K, M, n_mnodes, *w)
-    out = {name: fl.get(name, (0.0, 0.0)) + (b,) for name, (_, b) in by.items()}
-    return out
+    by = {name: b for name, (_, b) in roofline.kernel_work(N, precision, K, M, n_mnodes, *w).items()}
+    # one kernel limits the mortars and applies their corrections
+    by["mortar_limit"] += by.pop("mortar_apply")
+    return {name: fl.get(name, (0.0, 0.0)) + (b,) for name, b in by.items()}
 
 
 def kernel_rooflines(work, kern, steps, step_time, peak_tflops, hbm_gbs, peak32_tflops=None):
@@ -399,10 +472,49 @@ def run_ours(args):
                                                          "n_viol_pressure", "n_viol_entropy", "n_nonpositive")})
         vctx.close()
         del u_dev
+    from paper_2607_06045_b300 import workloads as W
+    # the refined periodic square (16 x 16 base, central 4 x 4 refined, N = 3,
+    # FP64): too small to fill the GPU, timed for its latency per step
+    sq = W.square_mesh()
+    usq = W.disc_wave_state(sq, 3)
+    lctx = idp.Context(sq, 3, limiting=2, cfl=0.5)
+    lud = torch.from_numpy(usq).cuda()
+    barrier_sync()
+    lt, _, _, _ = time_steps(lctx, lud, args.steps, args.warmup, flush, stream, barrier_sync)
+    variants["square_latency"] = dict(
+        ms_per_step=lt / args.steps * 1e3, ms_per_step_median=time_steps.median_ms, steps=args.steps,
+        elements=int(lctx.K), dofs=int(usq[0].size), value=usq[0].size * 3 * args.steps / lt, unit=UNIT,
+        workload="periodic unit square, 16x16 base with the central 4x4 refined once, N=3, disc on a smooth "
+                 "wave, local + positivity limiting, FP64",
+        gpu_launches=int(lctx.launches_per_step() * args.steps))
+    lctx.close()
+    del lud
+    # the DMR mesh at N = 4 and N = 7, the FP64 path and the FP32 form
+    for NN_ in (4, 7):
+        uN = W.dmr_state(meshes[0], NN_)
+        nN = uN[0].size
+        ent = {}
+        for prec in (0, 1):
+            nctx = idp.Context(meshes[0], NN_, precision=prec, limiting=2, cfl=0.5)
+            nud = torch.from_numpy(uN).cuda()
+            barrier_sync()
+            nt, nel_ms, nel_n, nk = time_steps(nctx, nud, vsteps, args.warmup, flush, stream, barrier_sync)
+            nt = max_over_ranks(nt)
+            _, nst_ = nctx.idp_dgsem_limiter_stats()
+            ent["fp32" if prec else "fp64"] = dict(
+                value=aggregate_rate(nN * 3 * vsteps, world, nt), unit=UNIT, ms_per_step=nt / vsteps * 1e3,
+                steps=vsteps, _el_s=nel_ms * 1e-3 / max(nel_n, 1), gpu_launches=int(nctx.launches_per_step() * vsteps),
+                launch=dict(zip(("elems_per_block", "persistent", "grid"), nctx.idp_dgsem_launch_config())),
+                stats={k: nst_[k] for k in ("alpha_volume_mean", "alpha_mortar_mean", "n_viol_density",
+                                            "n_viol_pressure", "n_nonpositive")})
+            nctx.close()
+            del nud
+        ent["speedup_fp32_vs_fp64"] = ent["fp64"]["ms_per_step"] / ent["fp32"]["ms_per_step"]
+        variants[f"dmr_N{NN_}"] = dict(ent, elements=int(meshes[0].n_elems), dofs=int(nN), N=NN_,
+                                       workload=f"the DMR mesh and initial data at N={NN_}")
     # high-Mach jet (gamma = 5/3, Mach ~2000 inflow), Chandrashekar's volume
     # flux with combined limiting as in the paper's astrophysical jet, on a
     # static 53,632-element mesh, both precisions
-    from paper_2607_06045_b300 import workloads as W
     jm = W.jet_mesh()
     ju = W.jet_state(jm, 3, W.JET_GAMMA)
     jnodes = ju.shape[1] * ju.shape[2] * ju.shape[3]
@@ -520,6 +632,11 @@ def run_ours(args):
     el32 = r32["el_ms"] * 1e-3 / max(r32["el_n"], 1)
     roof64 = form_roofline(roofline, 3, 0, nodes, el_avg, peak, peak32, w)
     roof32 = form_roofline(roofline, 3, 1, nodes, el32, peak, peak32, w)
+    for NN_ in (4, 7):
+        ent = variants[f"dmr_N{NN_}"]
+        for key, prec in (("fp64", 0), ("fp32", 1)):
+            e = ent[key]
+            e["roofline"] = form_roofline(roofline, NN_, prec, ent["dofs"], e.pop("_el_s"), peak, peak32, w)
     bval = bnodes_all * 3 * bsteps / btot   # the whole batch over the slowest rank
     hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0
@@ -586,6 +703,10 @@ def run_ours(args):
     }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_full()
+        samples = parity_samples()
+        l1o = l1_vs_oracle(samples, cpu_baseline_parity_refs(samples))
+        for name, e in l1o.items():
+            line["forms"][name]["l1_vs_oracle"] = e
     print(json.dumps(line), flush=True)
     barrier_sync()
 

@@ -246,8 +246,11 @@ enum {
     IDP_K_MORTAR_FLUX = 1,  /* mortar fluxes (L2 and sparse IDP), bar states */
     IDP_K_DT = 2,           /* IDP time step */
     IDP_K_ELEMENT = 3,      /* element pass: volume, faces, low order, limiting, stage */
-    IDP_K_MORTAR_LIMIT = 4, /* one limiting factor per mortar */
-    IDP_K_MORTAR_APPLY = 5, /* limited mortar corrections, stage at mortar nodes */
+    IDP_K_MORTAR_LIMIT = 4, /* one limiting factor per mortar, then the limited
+                               mortar corrections and the stage at mortar nodes */
+    IDP_K_MORTAR_APPLY = 5, /* (kept for the numbering: no kernel of this kind
+                               is launched, the mortar corrections are part of
+                               IDP_K_MORTAR_LIMIT) */
     IDP_K_TIME_ADVANCE = 6, /* per-simulation time */
     IDP_K_ELEMENT_LO = 7,   /* low-order pre-pass of the element pass (bounds 1) */
     IDP_K_MORTAR_LOB = 8,   /* low-order bounds across mortars (bounds 1) */

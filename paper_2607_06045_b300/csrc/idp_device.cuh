@@ -99,6 +99,11 @@ struct MeshDev {
     const SimInfo *siminfo;
     const int32_t *mn_node;   // unique mortar nodes: global node index
     const int2 *mn_slot;      // their (first, second or -1) slot
+    // mortar limiting blocks (k_mortar_limit_apply): per block its owned
+    // nodes mn[mb_node_off[b] .. mb_node_off[b+1]) and its foreign mortars
+    // mb_foreign[mb_for_off[b] .. mb_for_off[b+1]); mb_fmax their largest count
+    const int32_t *mb_node_off, *mb_for_off, *mb_foreign;
+    int mb_fmax, mb_blocks;
 };
 
 // Per-mortar-node scratch ("slots", index m * 3NP + q, large nodes first,

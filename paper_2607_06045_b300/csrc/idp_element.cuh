@@ -112,6 +112,7 @@ struct ElemSm {
     // extended kernel (entropy bound, low-order bounds): sizes of its arrays
     // (one element in the default kernel, which does not use them)
     static constexpr int XN = EXT ? NN : 1, XS = EXT ? NN + NIF + 4 * NP : 1;
+    static_assert(NIF < 256, "P4's pending list stores an interface id in 8 bits");
     union {
         struct {                 // P0 - P1
             FT pr[9][NN];            // rho, v1, v2, p, c, E, ln rho, ln beta, beta
@@ -162,6 +163,10 @@ struct ElemSm {
         struct {                 // P3 - P5
             double Rp[NN], Rm[NN], ell[NIF];
             double Rm2[NN];          // combined limiting: R- of the positivity bounds
+            // P4: interface ends whose FP32 certificate did not decide, for
+            // the FP64 solve by whole warps (interface id | end << 8)
+            unsigned short pend[NIF];
+            int npend;
         };
     };
     union {
@@ -898,6 +903,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             }
             S.Rp[n] = Rp;
             S.Rm[n] = Rm;
+            if (n == 0) S.npend = 0;
             if (combined) {
                 // positivity bounds [beta rho_FV, infinity): R+ = 1
                 const double rmin2 = dmin(A.beta * rfv, rfv), qm2 = rmin2 - rfv;
@@ -913,51 +919,103 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
         __syncthreads();
 
         // ---------------- P4: per interface factor (R7, R8; Gamma = 4) -----
-        for (int k = tid; k < EPB * NIF; k += NT) {
-            int le = k / NIF, id = k - le * NIF, e = e0 + le;
-            if (e >= mesh.K) continue;
-            int d = id / (NP * N), r = (id / N) % NP, a = id % N;
-            SM &S = sm[le];
-            int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
-            double Ar = S.Ad[id][0];
-            // largest factor <= lr keeping both end points admissible for the
-            // Gamma-scaled increment (left -4 dt/m A, right +4 dt/m A), each
-            // end point searched below the previous one's result
-            // (with_ent: then also the entropy bound, R21)
-            auto pressure_factor = [&](double lr, bool with_ent) {
-                double th = lr;
-                for (int side = 0; side < 2 && __double_as_longlong(th) > 0; ++side) {
-                    int nd = side == 0 ? nl : nr;
-                    float sgf = side == 0 ? -4.0f : 4.0f;
-                    float u0f[4], af[4];
-                    float sdf = sgf * S.dtmf[nd];
-                    for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.Af[id][v]; }
-                    // a certified FP32 yes implies c0 > 0 and rho_FV > 0
-                    const bool cert = admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], d2f(th));
-                    if (cert && !(EXT && with_ent)) continue;   // the whole interval [0, th] is admissible
-                    double u0[4], av[4];
-                    double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
-                    for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.Ad[id][v]; }
-                    if (!cert) {
-                        const double gmsn = gm1 * u0[0];
-                        const double X = u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2]);
-                        const double c0n = gmsn * X - S.pms[nd] * u0[0];
-                        th = theta_max(gm1, u0, av, gmsn, S.pms[nd], c0n, th);
-                    }
-                    if (EXT && with_ent) th = theta_entropy(G, u0, av, S.lnK[nd], th);
-                }
-                return th;
-            };
-            const double lr = S.ex[id] ? 1.0
-                                       : dneg(Ar) ? nn_min(S.Rp[nl], S.Rm[nr]) : nn_min(S.Rm[nl], S.Rp[nr]);
-            double th = pressure_factor(lr, ent);
-            if (combined) {
-                // Eq. combination_posLim_local: l = (1 - a) l_positivity + a l_local
-                const double lr2 = S.ex[id] ? 1.0 : dneg(Ar) ? S.Rm2[nr] : S.Rm2[nl];
-                const double th2 = pressure_factor(lr2, false);
-                th = (1.0 - S.aind) * th2 + S.aind * th;
+        // largest factor <= lr keeping both end points admissible for the
+        // Gamma-scaled increment (left -4 dt/m A, right +4 dt/m A), each end
+        // point searched below the previous one's result. An end whose FP32
+        // certificate decides costs no FP64 work; the FP64 solve of an end
+        // that it leaves undecided runs in the second pass below.
+        // FP64 solve of end `side` of interface id below th (and, with_ent,
+        // the entropy bound, R21)
+        auto solve_end = [&](SM &S, int id, int side, double th, bool with_ent) {
+            const int d = id / (NP * N), r = (id / N) % NP, a = id % N;
+            const int nd = side == 0 ? nodeid<NP>(d, r, a) : nodeid<NP>(d, r, a + 1);
+            double u0[4], av[4];
+            const double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
+            for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.Ad[id][v]; }
+            const double gmsn = gm1 * u0[0];
+            const double X = u0[0] * u0[3] - 0.5 * (u0[1] * u0[1] + u0[2] * u0[2]);
+            const double c0n = gmsn * X - S.pms[nd] * u0[0];
+            th = theta_max(gm1, u0, av, gmsn, S.pms[nd], c0n, th);
+            if (EXT && with_ent) th = theta_entropy(G, u0, av, S.lnK[nd], th);
+            return th;
+        };
+        // the FP32 certificate of end `side` at th
+        auto cert_end = [&](SM &S, int id, int side, double th) {
+            const int d = id / (NP * N), r = (id / N) % NP, a = id % N;
+            const int nd = side == 0 ? nodeid<NP>(d, r, a) : nodeid<NP>(d, r, a + 1);
+            float u0f[4], af[4];
+            const float sdf = (side == 0 ? -4.0f : 4.0f) * S.dtmf[nd];
+            for (int v = 0; v < 4; ++v) { u0f[v] = S.ufvf[v][nd]; af[v] = sdf * S.Af[id][v]; }
+            // a certified FP32 yes implies c0 > 0 and rho_FV > 0
+            return admissible_f32(S.gmsf[nd], u0f, af, S.pmsf[nd], S.c0f[nd], d2f(th));
+        };
+        if (!EXT && !combined) {
+            // pass 1: certificates; the first undecided end of an interface
+            // goes to its element's list with the factor reached so far
+            for (int k = tid; k < EPB * NIF; k += NT) {
+                int le = k / NIF, id = k - le * NIF;
+                if (e0 + le >= mesh.K) continue;
+                SM &S = sm[le];
+                int d = id / (NP * N), r = (id / N) % NP, a = id % N;
+                int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
+                const double Ar = S.Ad[id][0];
+                double th = S.ex[id] ? 1.0 : dneg(Ar) ? nn_min(S.Rp[nl], S.Rm[nr]) : nn_min(S.Rm[nl], S.Rp[nr]);
+                int pend = -1;
+                for (int side = 0; side < 2 && __double_as_longlong(th) > 0; ++side)
+                    if (!cert_end(S, id, side, th)) { pend = side; break; }
+                S.ell[id] = th;
+                if (pend >= 0) S.pend[atomicAdd(&S.npend, 1)] = (unsigned short)(id | (pend << 8));
             }
-            S.ell[id] = th;
+            __syncthreads();
+            // pass 2: the undecided ends of all elements of the block, one
+            // lane each (whole warps instead of one lane per warp)
+            int tot = 0;
+            for (int le = 0; le < EPB; ++le) tot += (e0 + le < mesh.K) ? sm[le].npend : 0;
+            for (int k = tid; k < tot; k += NT) {
+                int le = 0, j = k;
+                while (j >= sm[le].npend) { j -= sm[le].npend; ++le; }
+                SM &S = sm[le];
+                const int item = S.pend[j], id = item & 0xff, side0 = item >> 8;
+                double th = solve_end(S, id, side0, S.ell[id], false);
+                if (side0 == 0 && __double_as_longlong(th) > 0 && !cert_end(S, id, 1, th))
+                    th = solve_end(S, id, 1, th, false);
+                S.ell[id] = th;
+            }
+        } else {
+            for (int k = tid; k < EPB * NIF; k += NT) {
+                int le = k / NIF, id = k - le * NIF, e = e0 + le;
+                if (e >= mesh.K) continue;
+                int d = id / (NP * N), r = (id / N) % NP, a = id % N;
+                SM &S = sm[le];
+                int nl = nodeid<NP>(d, r, a), nr = nodeid<NP>(d, r, a + 1);
+                double Ar = S.Ad[id][0];
+                auto pressure_factor = [&](double lr, bool with_ent) {
+                    double th = lr;
+                    for (int side = 0; side < 2 && __double_as_longlong(th) > 0; ++side) {
+                        const bool cert = cert_end(S, id, side, th);
+                        if (cert && !(EXT && with_ent)) continue;   // the whole interval [0, th] is admissible
+                        if (!cert) th = solve_end(S, id, side, th, with_ent);
+                        else if (EXT && with_ent) {
+                            const int nd = side == 0 ? nl : nr;
+                            double u0[4], av[4];
+                            const double sd = (side == 0 ? -4.0 : 4.0) * S.dtm[nd];
+                            for (int v = 0; v < 4; ++v) { u0[v] = S.ufv[v][nd]; av[v] = sd * S.Ad[id][v]; }
+                            th = theta_entropy(G, u0, av, S.lnK[nd], th);
+                        }
+                    }
+                    return th;
+                };
+                const double lr = S.ex[id] ? 1.0
+                                           : dneg(Ar) ? nn_min(S.Rp[nl], S.Rm[nr]) : nn_min(S.Rm[nl], S.Rp[nr]);
+                double th = pressure_factor(lr, ent);
+                if (combined) {
+                    // Eq. combination_posLim_local: l = (1 - a) l_positivity + a l_local
+                    const double lr2 = S.ex[id] ? 1.0 : dneg(Ar) ? S.Rm2[nr] : S.Rm2[nl];
+                    const double th2 = pressure_factor(lr2, false);
+                    th = (1.0 - S.aind) * th2 + S.aind * th;
+                }
+                S.ell[id] = th;
+            }
         }
         __syncthreads();
 

@@ -443,6 +443,8 @@ struct idp_ctx {
     Geo *d_geom = nullptr;
     GeoC *d_geoc = nullptr;
     int32_t *d_sim = nullptr, *d_mlarge = nullptr, *d_minfo = nullptr, *d_mnnode = nullptr;
+    int32_t *d_mbnode = nullptr, *d_mbfor = nullptr, *d_mbforeign = nullptr;
+    int mb_fmax = 0, mb_blocks = 0;
     int4 *d_fnbr = nullptr;
     uchar4 *d_ftype = nullptr;
     int2 *d_msmall = nullptr, *d_mnslot = nullptr;
@@ -472,6 +474,7 @@ struct idp_ctx {
     double *d_lofv = nullptr;  // [2][K (N+1)^2] pre-pass output
     int facebuf = 0;           // FP64 default kernel: conforming faces from k_face
     double *d_fbuf = nullptr;  // k_face output: [6][2 K (N+1)] doubles + [2 K (N+1)] floats
+    void *d_lam = nullptr;     // wave speeds of every node for the time step (no face buffer)
     // optional timing: 1 step spans around the graph launches; 2 steps
     // launched without the graph, with element-pass events
     int prof = 0;
@@ -583,10 +586,6 @@ void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mo
         k = kt_begin(c, st, IDP_K_MORTAR_LIMIT);
         c->L.mortar_limit(gm, st, c->mesh, c->slots, A);
         kt_end(c, st, k);
-        int ga = std::max(1, std::min((c->n_mnodes + 63) / 64, c->num_sms * 32));
-        k = kt_begin(c, st, IDP_K_MORTAR_APPLY);
-        c->L.mortar_apply(ga, st, c->mesh, c->slots, A);
-        kt_end(c, st, k);
     }
 }
 
@@ -612,7 +611,7 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) 
     int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
     k = kt_begin(c, st, IDP_K_DT);
     c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
-            c->d_status, faces ? c->d_fbuf : nullptr);
+            c->d_status, faces ? c->d_fbuf : nullptr, faces ? nullptr : c->d_lam, c->num_sms);
     kt_end(c, st, k);
 }
 
@@ -820,6 +819,40 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
         k = k2;
     }
     c->n_mnodes = (int)mn_node.size();
+    // blocks of the mortar limiting kernel: block b owns mortars [b W, b W + W)
+    // and the nodes whose first mortar is one of them (the node list reordered
+    // by owner, node order within a block); a node's second mortar in a later
+    // block is one of the block's foreign mortars, whose factor it forms too
+    std::vector<int32_t> mb_node_off(1, 0), mb_for_off(1, 0), mb_foreign;
+    {
+        const int MW = c->L.mortar_w;
+        const int nb = c->M > 0 ? (int)((c->M + MW - 1) / MW) : 0;
+        std::vector<std::vector<int>> own(nb);
+        std::vector<std::vector<int32_t>> fore(nb);
+        for (int k = 0; k < c->n_mnodes; ++k) {
+            const int m0 = mn_slot[k].x / Q, m1 = mn_slot[k].y >= 0 ? mn_slot[k].y / Q : -1;
+            const int b = m0 / MW;
+            own[b].push_back(k);
+            if (m1 >= 0 && m1 / MW != b) fore[b].push_back(m1);
+        }
+        std::vector<int32_t> node2;
+        std::vector<int2> slot2;
+        node2.reserve(mn_node.size());
+        slot2.reserve(mn_slot.size());
+        for (int b = 0; b < nb; ++b) {
+            for (int k : own[b]) { node2.push_back(mn_node[k]); slot2.push_back(mn_slot[k]); }
+            mb_node_off.push_back((int32_t)node2.size());
+            std::sort(fore[b].begin(), fore[b].end());
+            fore[b].erase(std::unique(fore[b].begin(), fore[b].end()), fore[b].end());
+            for (int32_t m : fore[b]) mb_foreign.push_back(m);
+            mb_for_off.push_back((int32_t)mb_foreign.size());
+            c->mb_fmax = std::max(c->mb_fmax, (int)fore[b].size());
+        }
+        mn_node.swap(node2);
+        mn_slot.swap(slot2);
+        c->mb_blocks = nb;
+        if (mb_foreign.empty()) mb_foreign.push_back(0);
+    }
     bool ok = true;
     int step_no = 0;
     auto chk = [&](cudaError_t e) { ++step_no; if (e != cudaSuccess) { ok = false; char w[32]; std::snprintf(w, 32, "create step %d", step_no); note(e, w); } };
@@ -847,6 +880,9 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(upload(&c->d_siminfo, H.siminfo));
     if (ok) chk(upload(&c->d_mnnode, mn_node));
     if (ok) chk(upload(&c->d_mnslot, mn_slot));
+    if (ok) chk(upload(&c->d_mbnode, mb_node_off));
+    if (ok) chk(upload(&c->d_mbfor, mb_for_off));
+    if (ok) chk(upload(&c->d_mbforeign, mb_foreign));
     // slots: one block of device memory
     const size_t S = (size_t)c->M * Q, MM = (size_t)std::max<long long>(c->M, 1), SS = std::max<size_t>(S, 1);
     size_t bytes = sizeof(double) * (SS * (4 + 4 + 3 + 4 + 4 + 6 + 5)) + sizeof(float) * SS + sizeof(int32_t) * MM +
@@ -897,6 +933,8 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
         const size_t F = (size_t)2 * c->K * c->NP;
         chk(cudaMalloc(&c->d_fbuf, sizeof(double) * 6 * F + sizeof(float) * F));
     }
+    if (ok && (!c->facebuf || o.dt_rule != 0))
+        chk(cudaMalloc(&c->d_lam, (o.precision ? sizeof(float) : sizeof(double)) * 2 * kn));
     if (ok && c->lob) chk(cudaMalloc(&c->d_lofv, sizeof(double) * 2 * kn));
     if (ok && c->lob) chk(cudaMemset(c->d_lofv, 0, sizeof(double) * 2 * kn));
     if (ok) chk(cudaMalloc(&c->d_intout, sizeof(double) * 4 * n_sims));
@@ -910,6 +948,8 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     md.geom = c->d_geom; md.geoc = c->d_geoc; md.sim = c->d_sim; md.fnbr = c->d_fnbr; md.ftype = c->d_ftype;
     md.m_large = c->d_mlarge; md.m_small = c->d_msmall; md.m_info = c->d_minfo; md.siminfo = c->d_siminfo;
     md.mn_node = c->d_mnnode; md.mn_slot = c->d_mnslot;
+    md.mb_node_off = c->d_mbnode; md.mb_for_off = c->d_mbfor; md.mb_foreign = c->d_mbforeign;
+    md.mb_fmax = c->mb_fmax; md.mb_blocks = c->mb_blocks;
     reset_stats(c, c->stream);
     std::vector<double> tz(n_sims, 0.0);
     cudaMemcpy(c->d_tsim, tz.data(), sizeof(double) * n_sims, cudaMemcpyHostToDevice);
@@ -1423,7 +1463,8 @@ void idp_dgsem_destroy(idp_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    void *ptrs[] = {c->d_fbuf, c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+    void *ptrs[] = {c->d_fbuf, c->d_lam, c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+                    c->d_mbnode, c->d_mbfor, c->d_mbforeign,
                     c->d_msmall, c->d_mnslot, c->d_siminfo, c->d_slot_block, c->d_buf1, c->d_buf2, c->d_hostbuf,
                     c->d_dtmin, c->d_tsim, c->d_dtlast, c->d_status, c->d_stats, c->d_part, c->d_intout, c->d_off};
     for (void *p : ptrs)

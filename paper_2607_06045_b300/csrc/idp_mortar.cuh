@@ -5,11 +5,11 @@
 //                  interpolate, LLF on the two small faces, project back) and
 //                  the sparse low-order IDP mortar flux (Eq. interfaceflux_local)
 //                  with its bar states and graph-viscosity sums.
-//  k_mortar_limit  one thread per mortar slot: one factor l_S per mortar after the
-//                  volume correction, each node's correction budget scaled by
-//                  its number of mortars n_i (Sec. 2.3, mortar limiting).
-//  k_mortar_apply  per mortar node: apply the limited corrections in mortar
-//                  order and finish the stage.
+//  k_mortar_limit_apply  one factor l_S per mortar after the volume
+//                  correction, each node's correction budget scaled by its
+//                  number of mortars n_i (Sec. 2.3, mortar limiting), then the
+//                  limited corrections at the mortar nodes in mortar order and
+//                  the stage there, in one launch.
 //  k_dt            IDP time step (Eq. timestep_restriction) or the low-order
 //                  CFL estimate (Eq. CFLcondition_lowordermethod), per simulation.
 #pragma once
@@ -254,29 +254,16 @@ k_mortar_flux(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, 
     if (tid < nm) sl.bad[m0 + tid] = s_bad[tid] ? 1 : 0;
 }
 
-// Mortar limiting: one thread per mortar slot, 128 / (3 (N+1)) mortars per
-// block; the factor of a mortar is the minimum over its slots (shared-memory
-// minimum on the bits of the non-negative factors).
+// Largest factor of slot s of mortar m (R9): its node stays inside the
+// density interval and above the pressure bound (and, with the entropy bound,
+// above it) for the correction scaled by n_i dt / m_i; th2 the same for the
+// positivity bounds alone (combined limiting).
 template <int NP>
-struct MortarLimitLaunch {
-    static constexpr int Q = 3 * NP, threads = 128, mpb = threads / Q;
-};
-
-template <int NP>
-__global__ void __launch_bounds__(128)
-k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
-    using ML = MortarLimitLaunch<NP>;
-    constexpr int Q = ML::Q, MPB = ML::mpb;
-    __shared__ unsigned long long s_min[MPB], s_min2[MPB];
-    const int lm = threadIdx.x / Q, q = threadIdx.x - lm * Q;
-    const int m = blockIdx.x * MPB + lm;
-    const bool combined = A.limiting == 3;
-    if (threadIdx.x < MPB) { s_min[threadIdx.x] = dbits(1.0); s_min2[threadIdx.x] = dbits(1.0); }
-    __syncthreads();
-    if (lm < MPB && m < mesh.M && sl.bad[m] == 0) {
+__device__ __forceinline__ void mortar_slot_factor(const MeshDev &mesh, const SlotsDev &sl, const StageArgs &A, int m,
+                                                   int s, double &th, double &th2) {
+    {
         const int L = mesh.m_large[m];
         const double dt = stage_dt(A, mesh.sim[L]);
-        const int s = m * Q + q;
         double u0[4], av[4];
         const double f = (double)sl.nmort[s] * dt * fast_rcp(sl.mass[s]);   // n_i dt / m_i
         for (int v = 0; v < 4; ++v) {
@@ -290,69 +277,116 @@ k_mortar_limit(MeshDev mesh, SlotsDev sl, StageArgs A) {
         if (!dpos(lr)) lr = 0.0;
         const double pmin = sl.pmin[s] * fast_rcp(sl.rfv[s]);
         const double pm = pmin - kTol * fabs(pmin);
-        double th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
+        th = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr);
         // entropy bound of local limiting (R21)
         if (A.entropy && A.limiting >= 2) th = theta_entropy(A.gas, u0, av, sl.lnK[s], th);
-        atomicMin(&s_min[lm], dbits(dpos(th) ? th : 0.0));
-        if (combined) {
+        th2 = 1.0;
+        if (A.limiting == 3) {
             // the positivity bounds only: rho >= beta rho_FV, p >= p_min
             const double rfv = sl.rfv[s], rmin2 = dmin(A.beta * rfv, rfv);
             double lr2 = 1.0;
             if (dneg(av[0])) { double t = (rmin2 - tl - u0[0]) * fast_rcp(av[0]); if (dlt(t, lr2)) lr2 = t; }
             if (!dpos(lr2)) lr2 = 0.0;
-            const double th2 = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr2);
-            atomicMin(&s_min2[lm], dbits(dpos(th2) ? th2 : 0.0));
-        }
-    }
-    __syncthreads();
-    if (threadIdx.x < 32) {
-        float am = 0.0f;
-        unsigned nm = 0, nf = 0;
-        for (int j = threadIdx.x; j < MPB; j += 32) {
-            const int mm = blockIdx.x * MPB + j;
-            if (mm >= mesh.M) continue;
-            const bool bad = sl.bad[mm] != 0;
-            double lS = bad ? 0.0 : __longlong_as_double((long long)s_min[j]);
-            if (combined && !bad) {
-                // Eq. combination_posLim_local with the largest indicator of
-                // the mortar's three elements
-                const int2 sm2 = mesh.m_small[mm];
-                const double am = fmax(A.aind[mesh.m_large[mm]], fmax(A.aind[sm2.x], A.aind[sm2.y]));
-                lS = (1.0 - am) * __longlong_as_double((long long)s_min2[j]) + am * lS;
-            }
-            sl.ell[mm] = lS;
-            if (A.collect) {
-                const int info = mesh.m_info[mm], dir = info & 1;
-                const GeoC gc = mesh.geoc[mesh.m_large[mm]];
-                am += d2f(2.0 * (dir == 0 ? gc.hy : gc.hx)) * (1.0f - d2f(lS));   // face length (1 - l_S)
-                nm += nn_lt(lS, 1.0);
-                nf += bad;
-            }
-        }
-        if (A.collect) {
-            for (int o = 16; o > 0; o >>= 1) am += __shfl_down_sync(0xffffffffu, am, o);
-            nm = __reduce_add_sync(0xffffffffu, nm);
-            nf = __reduce_add_sync(0xffffffffu, nf);
-            if (threadIdx.x == 0) {
-                if (am > 0.0f) atomicAdd(&A.stats->alpha_mort_len, (double)am);
-                if (nm) atomicAdd(&A.stats->n_mort, (unsigned long long)nm);
-                if (nf) atomicAdd(&A.stats->n_fallback, (unsigned long long)nf);
-            }
+            th2 = theta_max(A.gas.gm1, u0, av, A.gas.gm1, pm, g_zero(A.gas.gm1, u0, pm), lr2);
         }
     }
 }
 
-// Limited mortar corrections at the mortar nodes (corner nodes of two
-// mortars in mortar order) and the stage combination there.
+// Mortar limiting and the limited corrections in one launch. Block b owns
+// the mortars [b W, b W + W) and the mortar nodes whose first mortar (in
+// mortar order) is one of them; for a corner node whose second mortar lies in
+// a later block, that mortar's factor is formed here too (its "foreign"
+// mortars, listed per block by the host), so no block waits for another.
+// Phase 1: one item per slot of the own and foreign mortars, the factor of a
+// mortar the minimum over its slots (shared-memory minimum on the bits of
+// the non-negative factors). Phase 2: the owned nodes' corrections in mortar
+// order and the stage combination there.
 template <int NP>
-__global__ void __launch_bounds__(64) k_mortar_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
-    constexpr int NN = NP * NP, Q = 3 * NP;
+struct MortarLaunch {
+    static constexpr int Q = 3 * NP, threads = 128;
+    // own mortars per block: the slots of W mortars and two foreign ones fill
+    // about one pass of the block
+    static constexpr int W = (threads - 2 * Q) / Q > 0 ? (threads - 2 * Q) / Q : 1;
+};
+
+template <int NP>
+__global__ void __launch_bounds__(128) k_mortar_limit_apply(MeshDev mesh, SlotsDev sl, StageArgs A) {
+    constexpr int NN = NP * NP, Q = 3 * NP, NT = 128, W = MortarLaunch<NP>::W;
+    extern __shared__ __align__(16) unsigned char mort_smem[];
+    const int LW = W + mesh.mb_fmax;                     // local mortars: own, then foreign
+    unsigned long long *s_min = reinterpret_cast<unsigned long long *>(mort_smem);
+    unsigned long long *s_min2 = s_min + LW;
+    double *s_ell = reinterpret_cast<double *>(s_min2 + LW);
+    const int b = blockIdx.x, m0 = b * W, tid = threadIdx.x;
+    const int nown = min(W, mesh.M - m0);
+    const int f0 = mesh.mb_for_off[b], nfor = mesh.mb_for_off[b + 1] - f0;
+    const int nloc = nown + nfor;
+    const bool combined = A.limiting == 3;
+    auto mortar_of = [&](int lm) { return lm < nown ? m0 + lm : mesh.mb_foreign[f0 + lm - nown]; };
+    for (int j = tid; j < nloc; j += NT) { s_min[j] = dbits(1.0); s_min2[j] = dbits(1.0); }
+    __syncthreads();
+    for (int k = tid; k < nloc * Q; k += NT) {
+        const int lm = k / Q, q = k - lm * Q, m = mortar_of(lm);
+        if (sl.bad[m] != 0) continue;
+        double th, th2;
+        mortar_slot_factor<NP>(mesh, sl, A, m, m * Q + q, th, th2);
+        atomicMin(&s_min[lm], dbits(dpos(th) ? th : 0.0));
+        if (combined) atomicMin(&s_min2[lm], dbits(dpos(th2) ? th2 : 0.0));
+    }
+    __syncthreads();
+    for (int j = tid; j < nloc; j += NT) {
+        const int mm = mortar_of(j);
+        const bool bad = sl.bad[mm] != 0;
+        double lS = bad ? 0.0 : __longlong_as_double((long long)s_min[j]);
+        if (combined && !bad) {
+            // Eq. combination_posLim_local with the largest indicator of the
+            // mortar's three elements
+            const int2 sm2 = mesh.m_small[mm];
+            const double am = fmax(A.aind[mesh.m_large[mm]], fmax(A.aind[sm2.x], A.aind[sm2.y]));
+            lS = (1.0 - am) * __longlong_as_double((long long)s_min2[j]) + am * lS;
+        }
+        s_ell[j] = lS;
+        if (j < nown) sl.ell[mm] = lS;
+    }
+    __syncthreads();
+    if (A.collect && tid < 32) {
+        // statistics of the own mortars: face length (1 - l_S), active and
+        // low-order-only mortars
+        float am = 0.0f;
+        unsigned nm = 0, nf = 0;
+        for (int j = tid; j < nown; j += 32) {
+            const int mm = m0 + j;
+            const double lS = s_ell[j];
+            const int info = mesh.m_info[mm], dir = info & 1;
+            const GeoC gc = mesh.geoc[mesh.m_large[mm]];
+            am += d2f(2.0 * (dir == 0 ? gc.hy : gc.hx)) * (1.0f - d2f(lS));
+            nm += nn_lt(lS, 1.0);
+            nf += sl.bad[mm] != 0;
+        }
+        for (int o = 16; o > 0; o >>= 1) am += __shfl_down_sync(0xffffffffu, am, o);
+        nm = __reduce_add_sync(0xffffffffu, nm);
+        nf = __reduce_add_sync(0xffffffffu, nf);
+        if (tid == 0) {
+            if (am > 0.0f) atomicAdd(&A.stats->alpha_mort_len, (double)am);
+            if (nm) atomicAdd(&A.stats->n_mort, (unsigned long long)nm);
+            if (nf) atomicAdd(&A.stats->n_fallback, (unsigned long long)nf);
+        }
+    }
+    // the factor of the mortar of slot s (own or foreign)
+    auto ell_of = [&](int s) {
+        const int mm = s / Q;
+        if (mm >= m0 && mm < m0 + nown) return s_ell[mm - m0];
+        for (int f = 0; f < nfor; ++f)
+            if (mesh.mb_foreign[f0 + f] == mm) return s_ell[nown + f];
+        return 0.0;   // not reached: the host lists every foreign mortar
+    };
     const size_t KN = (size_t)mesh.K * NN;
     double st_rmin = INFINITY;
     float st_pmin = 0.0f, st_one = 0.0f;   // minimum p (FP32 statistic) as the ratio st_pmin / st_one
     unsigned vr = 0, vp = 0, np_ = 0, ve = 0;
     const bool ent = A.entropy && A.limiting == 2;   // entropy bound checked (local limiting)
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < mesh.n_mnodes; k += gridDim.x * blockDim.x) {
+    const int n0 = mesh.mb_node_off[b], n1 = mesh.mb_node_off[b + 1];
+    for (int k = n0 + tid; k < n1; k += NT) {
         const int gnode = mesh.mn_node[k];
         const int2 ss = mesh.mn_slot[k];
         const int s0 = ss.x;
@@ -363,7 +397,7 @@ __global__ void __launch_bounds__(64) k_mortar_apply(MeshDev mesh, SlotsDev sl, 
         for (int c = 0; c < 2; ++c) {
             int s = c == 0 ? ss.x : ss.y;
             if (s < 0) continue;
-            double l = sl.ell[s / Q];
+            double l = ell_of(s);
             for (int v = 0; v < 4; ++v) corr[v] += l * (sl.chi[(size_t)v * sl.S + s] - sl.clo[(size_t)v * sl.S + s]);
         }
         double ut[4];
@@ -398,6 +432,12 @@ __global__ void __launch_bounds__(64) k_mortar_apply(MeshDev mesh, SlotsDev sl, 
     }
     if (A.collect) block_stats(A, 0.0f, 0u, vr, vp, np_, st_rmin, st_pmin, st_one, ve);
     if ((vr | vp | np_ | ve) != 0u) atomicOr(A.status, ST_VIOLATION);
+}
+
+// shared memory of k_mortar_limit_apply for at most fmax foreign mortars per block
+template <int NP>
+constexpr size_t mortar_smem(int fmax) {
+    return (size_t)(MortarLaunch<NP>::W + fmax) * (2 * sizeof(unsigned long long) + sizeof(double));
 }
 
 // Low-order-solution bounds across mortars (Eq. Bounds_LowOrder): per slot,
@@ -449,15 +489,38 @@ __global__ void __launch_bounds__(128) k_mortar_lob(MeshDev mesh, SlotsDev sl, c
 // the wave speeds, sums and the quotient are FP32 and the result is scaled by
 // (1 - 4e-6), more than the FP32 rounding of these few operations, so the
 // step never exceeds the FP64 limit.
+// Wave speeds |v_x| + c and |v_y| + c of every node, lam[2][K (N+1)^2], for
+// k_dt: one thread per node, so that the time step reads a conforming
+// neighbour's speed (one value) instead of its state (four) and does not form
+// the neighbour's primitives again.
+template <int NP, typename FT>
+__global__ void __launch_bounds__(256) k_dt_speed(MeshDev mesh, const double *__restrict__ u, Gas gas,
+                                                  unsigned *status, FT *__restrict__ lam) {
+    const size_t KN = (size_t)mesh.K * NP * NP;
+    for (size_t gi = (size_t)blockIdx.x * blockDim.x + threadIdx.x; gi < KN; gi += (size_t)gridDim.x * blockDim.x) {
+        double qd[4] = {u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi]};
+        Prim<FT> q = mortar_prim<NP, FT>(gas, qd);
+        bool okp;
+        if constexpr (sizeof(FT) == 4) okp = q.p > 0.0f;
+        else okp = dpos(q.p);
+        if (!dpos(qd[0]) || !okp) atomicOr(status, ST_BAD_INPUT);
+        lam[gi] = fabs(q.v1) + q.c;
+        lam[KN + gi] = fabs(q.v2) + q.c;
+    }
+}
+
 template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads)
 k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule, const Ops *ops,
-     const double *t_sim, unsigned long long *dtmin, unsigned *status, const double *__restrict__ fbuf) {
+     const double *t_sim, unsigned long long *dtmin, unsigned *status, const double *__restrict__ fbuf,
+     const FT *__restrict__ lam) {
     constexpr int NN = NP * NP, N = NP - 1, NT = ElemLaunch<NP, EPB>::threads;
     constexpr bool F32 = sizeof(FT) == 4;
     __shared__ FT s_l[EPB][2][NN];       // |v_x| + c, |v_y| + c per node
     __shared__ FT s_o[EPB][4][NP];       // outside wave speed, or 2d sum of a mortar side
     __shared__ double s_w[NP];
+    __shared__ int s_wsim[NT / 32];                 // per warp: its lane 0's simulation
+    __shared__ unsigned long long s_wbest[NT / 32];  // and that simulation's minimum
     if (threadIdx.x < NP) s_w[threadIdx.x] = ops->w[threadIdx.x];
     const size_t KN = (size_t)mesh.K * NN;
     const Gas &g = gas;
@@ -466,6 +529,12 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
             int le = k / NN, n = k - le * NN, e = e0 + le;
             if (e >= mesh.K) continue;
             size_t gi = (size_t)e * NN + n;
+            if (lam) {
+                // from k_dt_speed
+                s_l[le][0][n] = lam[gi];
+                s_l[le][1][n] = lam[KN + gi];
+                continue;
+            }
             double qd[4] = {u[gi], u[KN + gi], u[2 * KN + gi], u[3 * KN + gi]};
             Prim<FT> q = mortar_prim<NP, FT>(g, qd);
             bool okp;
@@ -490,6 +559,10 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
                     const int owner = (s & 1) ? e : nb;
                     const long long F = 2ll * mesh.K * NP, q = (2ll * owner + (s >> 1)) * NP + t;
                     s_o[le][s][t] = to_ft<FT>(fbuf[5 * F + q]);
+                } else if (ft == FT_CONF && lam) {
+                    // the neighbour's wave speed along the face normal
+                    const size_t ko = (size_t)nb * NN + face_node<NP>(s ^ 1, t);
+                    s_o[le][s][t] = lam[(size_t)(s >> 1) * KN + ko];
                 } else if (ft == FT_CONF || ft == FT_BND) {
                     double uo[4];
                     if (ft == FT_CONF) {
@@ -560,8 +633,10 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
             }
             if (dpos(val) && vb < best) best = vb;
         }
-        // warp minimum among the lanes that share lane 0's simulation, then
-        // one atomic per warp (other simulations: one atomic per lane)
+        // warp minimum among the lanes that share lane 0's simulation (other
+        // simulations: one atomic per lane), then the block's warps of the
+        // same simulation merged in shared memory, one atomic per block and
+        // simulation (same-address atomics serialise in L2)
         {
             const int s0 = __shfl_sync(0xffffffffu, bsim, 0);
             const bool same = bsim == s0;
@@ -570,8 +645,19 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
                 const unsigned long long ob = __shfl_down_sync(0xffffffffu, bw, o);
                 bw = ob < bw ? ob : bw;
             }
-            if ((threadIdx.x & 31) == 0 && s0 >= 0 && bw < dbits(INFINITY)) atomicMin(&dtmin[s0], bw);
+            if ((threadIdx.x & 31) == 0) { s_wsim[threadIdx.x >> 5] = s0; s_wbest[threadIdx.x >> 5] = bw; }
             if (!same && bsim >= 0 && best < dbits(INFINITY)) atomicMin(&dtmin[bsim], best);
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                for (int w = 0; w < NT / 32; ++w) {
+                    const int sw = s_wsim[w];
+                    if (sw < 0) continue;
+                    unsigned long long bm = s_wbest[w];
+                    for (int w2 = w + 1; w2 < NT / 32; ++w2)
+                        if (s_wsim[w2] == sw) { bm = s_wbest[w2] < bm ? s_wbest[w2] : bm; s_wsim[w2] = -1; }
+                    if (bm < dbits(INFINITY)) atomicMin(&dtmin[sw], bm);
+                }
+            }
         }
         __syncthreads();
     }

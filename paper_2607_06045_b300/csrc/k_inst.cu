@@ -101,26 +101,30 @@ void mortar_lob(cudaStream_t st, const MeshDev &m, const SlotsDev &s, const Ops 
 }
 
 void mortar_limit(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
-    using ML = MortarLimitLaunch<NP>;
     (void)grid;
-    k_mortar_limit<NP><<<(m.M + ML::mpb - 1) / ML::mpb, ML::threads, 0, st>>>(m, s, a);
-}
-
-void mortar_apply(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a) {
-    k_mortar_apply<NP><<<grid, 64, 0, st>>>(m, s, a);
+    if (m.mb_blocks > 0)
+        k_mortar_limit_apply<NP><<<m.mb_blocks, MortarLaunch<NP>::threads, mortar_smem<NP>(m.mb_fmax), st>>>(m, s, a);
 }
 
 void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, const Gas &gamma,
         int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status,
-        const double *fbuf) {
+        const double *fbuf, void *lam, int num_sms) {
     constexpr int EPB = NP * NP >= 64 ? 2 : (NP * NP >= 25 ? 4 : 8);
     int blocks = (m.K + EPB - 1) / EPB;
-    if (fp32)
+    // with a wave-speed buffer (no face buffer): every node's speeds first
+    const long long KN = (long long)m.K * NP * NP;
+    const int sb = (int)std::max<long long>(1, std::min<long long>((KN + 255) / 256, (long long)num_sms * 32));
+    if (fp32) {
+        float *lf = (float *)lam;
+        if (lf) k_dt_speed<NP, float><<<sb, 256, 0, st>>>(m, u, gamma, status, lf);
         k_dt<NP, EPB, float><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
-                                                                             dtmin, status, nullptr);
-    else
+                                                                             dtmin, status, nullptr, lf);
+    } else {
+        double *ld = fbuf ? nullptr : (double *)lam;
+        if (ld) k_dt_speed<NP, double><<<sb, 256, 0, st>>>(m, u, gamma, status, ld);
         k_dt<NP, EPB, double><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
-                                                                              dtmin, status, fbuf);
+                                                                              dtmin, status, fbuf, ld);
+    }
     (void)grid;
 }
 
@@ -160,7 +164,7 @@ Launchers IDP_CAT(launchers_np, IDP_NP)() {
     L.mortar_flux = mortar_flux;
     L.mortar_lob = mortar_lob;
     L.mortar_limit = mortar_limit;
-    L.mortar_apply = mortar_apply;
+    L.mortar_w = MortarLaunch<NP>::W;
     L.dt = dt;
     L.integrals = integrals;
     L.amr_indicator = amr_indicator;

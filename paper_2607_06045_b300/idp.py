@@ -328,8 +328,9 @@ class Context:
         ext = (o.limiting >= 2 and (o.bounds == 1 or o.entropy_bound == 1)) or o.volume_flux == 1
         el = 2 if (o.precision == 0 and not ext) else 1
         n = 1 + (1 if (M and self.opts.dt_rule == 0) else 0) + 1          # dt init, mortar flux, dt
-        n += (1 if (M and self.opts.dt_rule != 0) else 0) + el + lob + (2 if (M and lim) else 0)   # stage 1
-        n += 2 * ((1 if M else 0) + el + lob + (2 if (M and lim) else 0))   # stages 2, 3
+        # per stage with mortars and limiting: one mortar limiting-and-apply launch
+        n += (1 if (M and self.opts.dt_rule != 0) else 0) + el + lob + (1 if (M and lim) else 0)   # stage 1
+        n += 2 * ((1 if M else 0) + el + lob + (1 if (M and lim) else 0))   # stages 2, 3
         return n + 1                                                        # time advance
 
     def idp_dgsem_launch_config(self):
