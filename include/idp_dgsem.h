@@ -242,7 +242,8 @@ idp_status idp_dgsem_limiter_stats(idp_ctx *ctx, idp_limiter_stats *out, void *s
 
 /* Kernel kinds of one SSP-RK3 step, for idp_dgsem_profile_kernels. */
 enum {
-    IDP_K_DT_INIT = 0,      /* reset of the per-simulation time-step minimum */
+    IDP_K_DT_INIT = 0,      /* reset of the per-simulation time-step minimum (a
+                               standalone time step; a step needs none) */
     IDP_K_MORTAR_FLUX = 1,  /* mortar fluxes (L2 and sparse IDP), bar states */
     IDP_K_DT = 2,           /* IDP time step */
     IDP_K_ELEMENT = 3,      /* element pass: volume, faces, low order, limiting, stage */
@@ -255,7 +256,8 @@ enum {
     IDP_K_ELEMENT_LO = 7,   /* low-order pre-pass of the element pass (bounds 1) */
     IDP_K_MORTAR_LOB = 8,   /* low-order bounds across mortars (bounds 1) */
     IDP_K_FACE = 9,         /* conforming-face fluxes of the FP64 element pass (part of it) */
-    IDP_NKERNELS = 10
+    IDP_K_DT_SPEED = 10,    /* wave speeds of every node for the time step (no face buffer) */
+    IDP_NKERNELS = 11
 };
 
 /* Measurement support (the paper has no counterpart). mode 1: each step's

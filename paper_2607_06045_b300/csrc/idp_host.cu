@@ -459,6 +459,10 @@ struct idp_ctx {
     long long *d_off = nullptr;
     cudaStream_t stream = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // a second stream for work that runs beside the main one (the mortar
+    // fluxes beside the face or wave-speed kernel), forked and joined by events
+    cudaStream_t st2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     int epb = 0, persistent = 0, bps = 1;
     bool tuned = false;
     cudaGraphExec_t graph = nullptr;
@@ -550,14 +554,30 @@ cudaError_t kt_collect(idp_ctx *c) {
 
 // one stage: mortar fluxes (unless already current), element pass, mortar
 // limiting
+// The mortar fluxes may run on the second stream beside the main stream's
+// next kernel that does not read them, except when kernels are timed one by
+// one (their events would then measure overlapping work).
+static bool can_fork(const idp_ctx *c) { return c->prof != 2 && c->st2 != nullptr; }
+
+static cudaStream_t fork_to_second(idp_ctx *c, cudaStream_t st) {
+    cudaEventRecord(c->ev_fork, st);
+    cudaStreamWaitEvent(c->st2, c->ev_fork, 0);
+    return c->st2;
+}
+
 void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mortar_flux, bool need_face) {
     const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
-    if (c->M > 0 && need_mortar_flux) {
-        int k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
-        c->L.mortar_flux(c->opt.precision, c->ent_bar, c->opt.mortar_low, gm, st, c->mesh, c->slots, A.u, A.gas, c->d_ops);
-        kt_end(c, st, k);
-    }
     bool dgmode = (A.mode == 0 && A.dt == 0.0) || A.limiting == 0;
+    // FP64 path: the mortar fluxes beside the conforming-face kernel, both on
+    // the stage's input state; joined before the element pass
+    const bool fork = can_fork(c) && c->M > 0 && need_mortar_flux && c->facebuf && need_face && !(c->lob && !dgmode);
+    if (c->M > 0 && need_mortar_flux) {
+        cudaStream_t sm = fork ? fork_to_second(c, st) : st;
+        int k = kt_begin(c, sm, IDP_K_MORTAR_FLUX);
+        c->L.mortar_flux(c->opt.precision, c->ent_bar, c->opt.mortar_low, gm, sm, c->mesh, c->slots, A.u, A.gas, c->d_ops);
+        kt_end(c, sm, k);
+        if (fork) cudaEventRecord(c->ev_join, sm);
+    }
     const int grid = element_grid(c, c->epb, c->persistent, c->bps);
     if (c->lob && !dgmode) {
         // low-order bounds (Eq. Bounds_LowOrder): u_FV of every node first,
@@ -579,6 +599,7 @@ void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mo
         c->L.face(st, c->mesh, A.u, A.gas, c->d_ops, c->d_fbuf, c->num_sms);
         kt_end(c, st, k);
     }
+    if (fork) cudaStreamWaitEvent(st, c->ev_join, 0);
     k = kt_begin(c, st, IDP_K_ELEMENT);
     c->L.element(c->opt.precision, c->ext, c->epb, grid, st, c->mesh, c->slots, A);
     kt_end(c, st, k);
@@ -589,16 +610,28 @@ void enqueue_stage(idp_ctx *c, cudaStream_t st, const StageArgs &A, bool need_mo
     }
 }
 
-void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) {
-    int k = kt_begin(c, st, IDP_K_DT_INIT);
-    k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
-    kt_end(c, st, k);
+// The per-simulation time-step minimum is +inf between calls: the context
+// starts so, a step's k_time_advance resets it after use, and every other
+// caller that forms a time step (reset = true) resets it first and restores
+// it after reading it (dt_restore), so a step needs no reset launch.
+void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux, bool reset) {
+    int k;
+    if (reset) {
+        k = kt_begin(c, st, IDP_K_DT_INIT);
+        k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
+        kt_end(c, st, k);
+    }
+    // the mortar fluxes of u^n beside the face or wave-speed kernel; the time
+    // step joins them before it reads the mortars' 2d sums
+    const bool fork = can_fork(c) && c->M > 0 && mortar_flux && c->opt.dt_rule == 0;
     if (c->M > 0 && mortar_flux && c->opt.dt_rule == 0) {
         const int gm = (int)((c->M + MORTARS_PER_BLOCK - 1) / MORTARS_PER_BLOCK);
-        k = kt_begin(c, st, IDP_K_MORTAR_FLUX);
-        c->L.mortar_flux(c->opt.precision, c->ent_bar, c->opt.mortar_low, gm, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg),
+        cudaStream_t sm = fork ? fork_to_second(c, st) : st;
+        k = kt_begin(c, sm, IDP_K_MORTAR_FLUX);
+        c->L.mortar_flux(c->opt.precision, c->ent_bar, c->opt.mortar_low, gm, sm, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg),
                          c->d_ops);
-        kt_end(c, st, k);
+        kt_end(c, sm, k);
+        if (fork) cudaEventRecord(c->ev_join, sm);
     }
     // FP64 path: the conforming faces of u^n first; the time step reads their
     // wave speeds and stage 1 of a step their fluxes
@@ -609,15 +642,29 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux) 
         kt_end(c, st, k);
     }
     int g = (int)std::max<long long>(1, std::min<long long>(((long long)KN(c) + 255) / 256, (long long)c->num_sms * 16));
+    // without the face buffer: every node's wave speeds first (beside the
+    // mortar fluxes), which the time step reads for its own and its
+    // conforming neighbours' nodes
+    void *lam = faces ? nullptr : c->d_lam;
+    if (lam) {
+        k = kt_begin(c, st, IDP_K_DT_SPEED);
+        c->L.dt_speed(c->opt.precision, st, c->mesh, u, make_gas(c->gamma, &c->d_ops->lg), c->d_status, lam, c->num_sms);
+        kt_end(c, st, k);
+    }
+    if (fork) cudaStreamWaitEvent(st, c->ev_join, 0);   // the mortars' 2d sums
     k = kt_begin(c, st, IDP_K_DT);
     c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
-            c->d_status, faces ? c->d_fbuf : nullptr, faces ? nullptr : c->d_lam, c->num_sms);
+            c->d_status, faces ? c->d_fbuf : nullptr, lam);
     kt_end(c, st, k);
 }
 
 // one SSP-RK3 step on u (in place), using the ctx stage buffers
+static void dt_restore(idp_ctx *c, cudaStream_t st) {
+    k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
+}
+
 void enqueue_step(idp_ctx *c, cudaStream_t st, double *u) {
-    enqueue_dt(c, st, u, true);
+    enqueue_dt(c, st, u, true, false);
     StageArgs A = base_args(c);
     A.mode = 1;
     A.un = u;
@@ -921,6 +968,10 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(cudaMalloc(&c->d_buf1, sizeof(double) * 4 * kn));
     if (ok) chk(cudaMalloc(&c->d_buf2, sizeof(double) * 4 * kn));
     if (ok) chk(cudaMalloc(&c->d_dtmin, sizeof(unsigned long long) * n_sims));
+    if (ok) {
+        const std::vector<unsigned long long> inf(n_sims, 0x7FF0000000000000ull);   // +inf: no step formed yet
+        chk(cudaMemcpy(c->d_dtmin, inf.data(), sizeof(unsigned long long) * n_sims, cudaMemcpyHostToDevice));
+    }
     if (ok) chk(cudaMalloc(&c->d_tsim, sizeof(double) * n_sims));
     if (ok) chk(cudaMalloc(&c->d_dtlast, sizeof(double) * n_sims));
     if (ok) chk(cudaMalloc(&c->d_status, sizeof(unsigned)));
@@ -940,6 +991,9 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(cudaMalloc(&c->d_intout, sizeof(double) * 4 * n_sims));
     if (ok) chk(upload(&c->d_off, c->sim_off));
     if (ok) chk(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+    if (ok) chk(cudaStreamCreateWithFlags(&c->st2, cudaStreamNonBlocking));
+    if (ok) chk(cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming));
+    if (ok) chk(cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
     if (ok) chk(cudaEventCreateWithFlags(&c->ev_in, cudaEventDisableTiming));
     if (ok) chk(cudaEventCreateWithFlags(&c->ev_out, cudaEventDisableTiming));
     if (!ok) { idp_dgsem_destroy(c); return IDP_E_CUDA; }
@@ -1055,12 +1109,13 @@ idp_status idp_dgsem_dt(idp_ctx *c, const double *u, const double *t_host, doubl
     if (t_host) for (int s = 0; s < c->n_sims; ++s) tz[s] = t_host[s];
     if (cudaMemcpyAsync(c->d_tsim, tz.data(), sizeof(double) * c->n_sims, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return IDP_E_CUDA;
-    enqueue_dt(c, st, u, true);
+    enqueue_dt(c, st, u, true, true);
     std::vector<unsigned long long> b(c->n_sims);
     if (cudaMemcpyAsync(b.data(), c->d_dtmin, sizeof(unsigned long long) * c->n_sims, cudaMemcpyDeviceToHost, st) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess)
+            cudaSuccess)
         return IDP_E_CUDA;
+    dt_restore(c, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return IDP_E_CUDA;
     for (int s = 0; s < c->n_sims; ++s) {
         double v;
         std::memcpy(&v, &b[s], sizeof(double));
@@ -1085,9 +1140,10 @@ idp_status idp_dgsem_step(idp_ctx *c, double *u, int32_t n_steps, double *t_host
         return IDP_E_CUDA;
     if (!c->tuned) {
         // tune on u with its own IDP step
-        enqueue_dt(c, st, u, true);
+        enqueue_dt(c, st, u, true, true);
         std::vector<unsigned long long> b(c->n_sims);
         cudaMemcpyAsync(b.data(), c->d_dtmin, sizeof(unsigned long long) * c->n_sims, cudaMemcpyDeviceToHost, st);
+        dt_restore(c, st);
         if (cudaStreamSynchronize(st) != cudaSuccess) return IDP_E_CUDA;
         double v;
         std::memcpy(&v, &b[0], sizeof(double));
@@ -1477,6 +1533,9 @@ void idp_dgsem_destroy(idp_ctx *c) {
         for (int b = 0; b < 2; ++b)
             if (c->kev[k][b]) cudaEventDestroy(c->kev[k][b]);
     if (c->stream) cudaStreamDestroy(c->stream);
+    if (c->st2) cudaStreamDestroy(c->st2);
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     delete c;
 }
 

@@ -31,11 +31,13 @@ struct Launchers {
     // mortar_w own mortars per block
     void (*mortar_limit)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
     int mortar_w;
-    // time step; lam (when not null and there is no face buffer): a buffer
-    // of 2 K (N+1)^2 wave speeds in the flux type, filled first
+    // time step; lam (when not null): the wave speeds of every node,
+    // 2 K (N+1)^2 values in the flux type, written by dt_speed first
     void (*dt)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
                const Gas &gas, int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin,
-               unsigned *status, const double *fbuf, void *lam, int num_sms);
+               unsigned *status, const double *fbuf, const void *lam);
+    void (*dt_speed)(int fp32, cudaStream_t st, const MeshDev &m, const double *u, const Gas &gas,
+                     unsigned *status, void *lam, int num_sms);
     void (*integrals)(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part);
     // adaptive mesh refinement (idp_amr.cuh)
     void (*amr_indicator)(cudaStream_t st, const double *u, int K, const Ops *ops, double gm1, int kind, int var,

@@ -668,12 +668,15 @@ static __global__ void k_dt_init(unsigned long long *dtmin, int n) {
     if (k < n) dtmin[k] = dbits(INFINITY);
 }
 
-static __global__ void k_time_advance(double *t_sim, const unsigned long long *dtmin, double cfl, double *dt_last, int n) {
+// The step's end: t += dt per simulation, and the time-step minimum reset to
+// +inf for the next step (which then needs no reset launch of its own).
+static __global__ void k_time_advance(double *t_sim, unsigned long long *dtmin, double cfl, double *dt_last, int n) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < n) {
         double dt = cfl * __longlong_as_double((long long)dtmin[k]);
         t_sim[k] += dt;
         dt_last[k] = dt;
+        dtmin[k] = dbits(INFINITY);
     }
 }
 

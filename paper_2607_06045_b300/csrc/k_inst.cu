@@ -106,25 +106,25 @@ void mortar_limit(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s
         k_mortar_limit_apply<NP><<<m.mb_blocks, MortarLaunch<NP>::threads, mortar_smem<NP>(m.mb_fmax), st>>>(m, s, a);
 }
 
-void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, const Gas &gamma,
-        int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status,
-        const double *fbuf, void *lam, int num_sms) {
-    constexpr int EPB = NP * NP >= 64 ? 2 : (NP * NP >= 25 ? 4 : 8);
-    int blocks = (m.K + EPB - 1) / EPB;
-    // with a wave-speed buffer (no face buffer): every node's speeds first
+void dt_speed(int fp32, cudaStream_t st, const MeshDev &m, const double *u, const Gas &gamma, unsigned *status,
+              void *lam, int num_sms) {
     const long long KN = (long long)m.K * NP * NP;
     const int sb = (int)std::max<long long>(1, std::min<long long>((KN + 255) / 256, (long long)num_sms * 32));
-    if (fp32) {
-        float *lf = (float *)lam;
-        if (lf) k_dt_speed<NP, float><<<sb, 256, 0, st>>>(m, u, gamma, status, lf);
+    if (fp32) k_dt_speed<NP, float><<<sb, 256, 0, st>>>(m, u, gamma, status, (float *)lam);
+    else k_dt_speed<NP, double><<<sb, 256, 0, st>>>(m, u, gamma, status, (double *)lam);
+}
+
+void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, const Gas &gamma,
+        int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status,
+        const double *fbuf, const void *lam) {
+    constexpr int EPB = NP * NP >= 64 ? 2 : (NP * NP >= 25 ? 4 : 8);
+    int blocks = (m.K + EPB - 1) / EPB;
+    if (fp32)
         k_dt<NP, EPB, float><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
-                                                                             dtmin, status, nullptr, lf);
-    } else {
-        double *ld = fbuf ? nullptr : (double *)lam;
-        if (ld) k_dt_speed<NP, double><<<sb, 256, 0, st>>>(m, u, gamma, status, ld);
+                                                                             dtmin, status, nullptr, (const float *)lam);
+    else
         k_dt<NP, EPB, double><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
-                                                                              dtmin, status, fbuf, ld);
-    }
+                                                                              dtmin, status, fbuf, (const double *)lam);
     (void)grid;
 }
 
@@ -166,6 +166,7 @@ Launchers IDP_CAT(launchers_np, IDP_NP)() {
     L.mortar_limit = mortar_limit;
     L.mortar_w = MortarLaunch<NP>::W;
     L.dt = dt;
+    L.dt_speed = dt_speed;
     L.integrals = integrals;
     L.amr_indicator = amr_indicator;
     L.amr_transfer = amr_transfer;

@@ -144,7 +144,7 @@ def idp_eval_math(fn, x, y, stream=None):
 
 # kernel kinds of one step, in the order of the IDP_K_* constants
 KERNELS = ["dt_init", "mortar_flux", "dt", "element", "mortar_limit", "mortar_apply", "time_advance",
-           "element_lo", "mortar_lob", "face"]
+           "element_lo", "mortar_lob", "face", "dt_speed"]
 
 NOALLOC_MAX_ELEMS = 1 << 19
 
@@ -327,7 +327,10 @@ class Context:
         o = self.opts
         ext = (o.limiting >= 2 and (o.bounds == 1 or o.entropy_bound == 1)) or o.volume_flux == 1
         el = 2 if (o.precision == 0 and not ext) else 1
-        n = 1 + (1 if (M and self.opts.dt_rule == 0) else 0) + 1          # dt init, mortar flux, dt
+        # mortar flux, dt (its wave-speed pre-pass without a face buffer); the
+        # time-step minimum needs no reset launch in a step
+        ext_or_f32 = o.precision == 1 or ext
+        n = (1 if (M and self.opts.dt_rule == 0) else 0) + 1 + (1 if ext_or_f32 or o.dt_rule != 0 else 0)
         # per stage with mortars and limiting: one mortar limiting-and-apply launch
         n += (1 if (M and self.opts.dt_rule != 0) else 0) + el + lob + (1 if (M and lim) else 0)   # stage 1
         n += 2 * ((1 if M else 0) + el + lob + (1 if (M and lim) else 0))   # stages 2, 3

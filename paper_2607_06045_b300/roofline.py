@@ -235,8 +235,11 @@ def kernel_work(N: int, precision: int, K: int, M: int, n_mnodes: int, w_div: fl
     return {
         **face,
         "element": (el_flops, BYTES_PER_NODE_STAGE * nodes),
+        # without the face kernel the time step reads the wave speeds that its
+        # pre-pass wrote from the state (two values per node in the flux type)
+        **({} if face_kernel else {"dt_speed": (0.0, (32.0 + 2.0 * (4 if precision else 8)) * nodes)}),
         "dt": (2.0 * dt_ops_per_node(N, precision, face_kernel).dfma_eq(*w) * nodes,
-               (32.0 + (8.0 * 4.0 / (N + 1) if face_kernel else 0.0)) * nodes),
+               (32.0 + 8.0 * 4.0 / (N + 1) if face_kernel else 2.0 * (4 if precision else 8)) * nodes),
         "mortar_flux": (2.0 * mortar_flux_ops_per_mortar(N, precision).dfma_eq(*w) * M, (96.0 + 264.0) * (N + 1) * M),
         "mortar_limit": (2.0 * mortar_limit_ops_per_slot(precision).dfma_eq(*w) * Q * M, 112.0 * Q * M),
         "mortar_apply": (2.0 * mortar_apply_ops_per_node(precision).dfma_eq(*w) * n_mnodes, 136.0 * n_mnodes),

@@ -106,6 +106,32 @@ def test_dt_parity():
         ctx.close()
 
 
+def test_fp32_form_dt_is_safe_and_tight():
+    """The FP32 form's time step (FP32 wave speeds and quotient, scaled by
+    1 - 4e-6) never exceeds the IDP restriction the oracle forms in FP64 and
+    stays within 2e-5 of it, on states with mortars, walls, inflow and
+    outflow boundaries and several simulations."""
+    cases = []
+    sq = W.square_mesh()
+    cases.append(([sq], 3, [W.disc_wave_state(sq, 3)]))
+    dm = W.dmr_sample_mesh()
+    cases.append(([dm], 3, [W.dmr_state(dm, 3)]))
+    cases.append(([sq], 5, [W.random_state(sq, 5, seed=3, rho_range=(0.1, 10.0), p_range=(0.1, 10.0), vmax=2.0)]))
+    ms = W.batch_meshes(256, seed=0)
+    small = np.argsort([mm.n_elems for mm in ms])[:3].tolist()
+    rng = np.random.default_rng(1)
+    us = [W.riemann4_state(mm, 3, rng) for mm in ms]
+    cases.append(([ms[k] for k in small], 3, [us[k] for k in small]))
+    for meshes, N, states in cases:
+        ctx = idp.Context(meshes if len(meshes) > 1 else meshes[0], N, precision=1, cfl=0.5)
+        d32 = ctx.idp_dgsem_dt(dev(W.concat_states(states)))
+        ctx.close()
+        for k, (m, u) in enumerate(zip(meshes, states)):
+            d64 = oracle.Oracle(m, N).dt(u, cfl=0.5)
+            assert d32[k] <= d64, (N, k, d32[k], d64)
+            assert d32[k] >= d64 * (1.0 - 2e-5), (N, k, d32[k], d64)
+
+
 @pytest.mark.parametrize("limiting", [1, 2])
 def test_square_100_steps(limiting):
     m = W.square_mesh()

@@ -137,7 +137,12 @@ def test_variant_100_steps(variant):
     c32.idp_dgsem_step(ud, 20, t)
     u20, _, _, _ = o.step(u, 20, cfl=0.5, limiting=2, bounds=b, entropy=e)
     mm = o.masses()
-    assert_l1_fields(ud.cpu().numpy(), u20, mm)
+    # with the entropy or low-order bounds, limiter decisions in the FP32 form
+    # switch on FP32 rounding noise (R18) and which ones switch depends on the
+    # last bits of every input, the time step included: density L1 measured
+    # from 5.6e-6 to 1.5e-5 after 20 steps as those bits changed; bounded at
+    # 3e-5 (1e-4 for momentum and energy)
+    assert_l1_fields(ud.cpu().numpy(), u20, mm, tol=3e-5, tol_other=1e-4)
     rc, st = c32.idp_dgsem_limiter_stats()
     assert st["n_nonpositive"] == 0 and st["n_viol_density"] == 0 and st["n_viol_entropy"] == 0
     c32.close()
