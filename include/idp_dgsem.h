@@ -324,7 +324,8 @@ idp_status idp_integrals_noalloc(const double *u, const double *elem_area, int64
  * One adaptation step is: element indicators on the device
  * (idp_dgsem_amr_indicator), the new leaf set on the host (idp_amr_plan),
  * the solution transfer on the device (idp_amr_transfer), then a context for
- * the new mesh (idp_dgsem_create). */
+ * the new mesh (idp_dgsem_create). idp_dgsem_adapt does all of it on the
+ * device, in the context. */
 
 /* Indicator kinds and the variable they look at. */
 enum { IDP_AMR_HENNEMANN = 0, IDP_AMR_LOHNER = 1, IDP_AMR_MAX = 2 };
@@ -392,6 +393,49 @@ idp_status idp_amr_plan(const idp_mesh_desc *mesh, const double *ind, const idp_
 idp_status idp_amr_transfer(int32_t N, double gamma, const double *u_old, int64_t n_old, double *u_new, int64_t n_new,
                             const int32_t *kind, const int32_t *src, double zs_threshold, int64_t *n_scaled,
                             void *stream);
+
+/* One adaptation step on the device (Sec. 2.4), the context kept: the
+ * indicator of u_old, the plan (as idp_amr_plan: the same marks, families,
+ * 2:1 balance sweeps and leaf order, run as data-parallel sweeps until
+ * nothing changes), the transfer (as idp_amr_transfer) into u_new, and the
+ * face, mortar, mortar-node and limiting-block tables of the new leaves
+ * (the same tables, in the same order, as idp_dgsem_create builds for that
+ * mesh), all built in the context's device memory; element and mortar
+ * buffers grow with slack when the mesh outgrows them and are never shrunk.
+ * u_old (the context's n_elems elements, layout above) and u_new are
+ * caller-owned device arrays that must not overlap; u_new holds at least
+ * 4 capacity (N+1)^2 doubles and receives the adapted state in its first
+ * 4 n_new (N+1)^2, laid out for n_new elements. *n_new (host) receives the
+ * new element count; when it exceeds capacity the context is unchanged and
+ * the call returns IDP_E_ARG (call again with a larger u_new). *n_scaled (host, may
+ * be NULL) as for idp_amr_transfer. After the call the context steps u_new
+ * on the new mesh (the step graph is captured again on the next step).
+ * Single-mesh contexts only (IDP_E_ARG for a batch or while per-kernel
+ * profiling is on); IDP_E_MESH if the tables come out invalid, IDP_E_CUDA
+ * on a CUDA failure. Synchronises `stream` and the context's own streams. */
+idp_status idp_dgsem_adapt(idp_ctx *ctx, const double *u_old, const idp_amr_params *p, double *u_new,
+                           int64_t capacity, int64_t *n_new, int64_t *n_scaled, void *stream);
+
+/* The context's leaves (the mesh it steps, after any idp_dgsem_adapt):
+ * level, ix, iy of its n_elems elements in element order, copied to
+ * caller-owned host arrays. Synchronous. IDP_E_ARG for null pointers. */
+idp_status idp_dgsem_leaves(idp_ctx *ctx, int8_t *level, int32_t *ix, int32_t *iy);
+
+/* Test support (no counterpart in the paper): the context's mesh tables
+ * copied to caller-owned host arrays, any of which may be NULL to skip it.
+ * sizes[6] (required) = n_elems, n_mortars, mortar nodes, mortar limiting
+ * blocks, foreign-mortar entries, the largest foreign count of a block.
+ * fnbr [n_elems][4] neighbour per side (x-, x+, y-, y+), ftype [n_elems][4]
+ * face kind per side, m_large [n_mortars] and m_small [n_mortars][2] the
+ * mortars' elements, m_info [n_mortars] orientation and side bits,
+ * mn_node [nodes] the element node (e (N+1)^2 + j (N+1) + i) of each mortar
+ * node, mn_slot [nodes][2] its first and second mortar slot (-1 when none),
+ * mb_node_off and mb_for_off [blocks + 1] per block offsets into mn_node and
+ * mb_foreign [entries] (the foreign mortars of each block, ascending).
+ * Synchronous. IDP_E_ARG for a null ctx or sizes. */
+idp_status idp_dgsem_mesh_tables(idp_ctx *ctx, int64_t *sizes, int32_t *fnbr, uint8_t *ftype, int32_t *m_large,
+                                 int32_t *m_small, int32_t *m_info, int32_t *mn_node, int32_t *mn_slot,
+                                 int32_t *mb_node_off, int32_t *mb_for_off, int32_t *mb_foreign);
 
 /* Synchronise the stream and report any device-flagged condition. */
 idp_status idp_dgsem_sync(idp_ctx *ctx, void *stream);

@@ -22,7 +22,7 @@ NPS = list(range(2, 9))
 
 
 def _sources():
-    return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh"))] + \
+    return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))] + \
         [os.path.join(ROOT, "include", "idp_dgsem.h")]
 
 
@@ -53,6 +53,7 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     tasks.append((os.path.join(CSRC, "idp_host.cu"), os.path.join(BUILD, "idp_host.o"), []))
     tasks.append((os.path.join(CSRC, "k_probe.cu"), os.path.join(BUILD, "k_probe.o"), []))
     tasks.append((os.path.join(CSRC, "k_noalloc.cu"), os.path.join(BUILD, "k_noalloc.o"), []))
+    tasks.append((os.path.join(CSRC, "k_remesh.cu"), os.path.join(BUILD, "k_remesh.o"), []))
     jobs = jobs or min(len(tasks), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(_compile, tasks))

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/idp_dgsem.h"
+#include "idp_remesh.h"
 #include "idp_launch.cuh"
 
 using namespace idp;
@@ -415,6 +416,66 @@ std::map<long long, std::pair<int, int>> g_tune_cache;   // key -> (epb, persist
 
 namespace idp {
 // table of the FP64 logarithm (used by the probes and the test hook)
+// Global node of slot q of mortar m (large face first, then the lower and
+// upper small faces).
+static long long mortar_slot_node(int NP, int m, int q, const std::vector<int32_t> &m_large,
+                                  const std::vector<int2> &m_small, const std::vector<int32_t> &m_info) {
+    const int NN = NP * NP, dir = m_info[m] & 1, low = (m_info[m] >> 1) & 1;
+    const int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
+    int e, s, t;
+    if (q < NP) { e = m_large[m]; s = sL; t = q; }
+    else { e = ((q - NP) / NP == 0) ? m_small[m].x : m_small[m].y; s = sS; t = (q - NP) % NP; }
+    const int i = s == 0 ? 0 : (s == 1 ? NP - 1 : t), j = s == 2 ? 0 : (s == 3 ? NP - 1 : t);
+    return (long long)e * NN + j * NP + i;
+}
+
+// The unique mortar nodes with their (first, second or -1) slot, and the
+// blocks of the mortar limiting kernel: block b owns mortars [b W, b W + W)
+// and the nodes whose first slot is one of theirs, listed in slot order; a
+// node's second mortar in a later block is one of the block's foreign
+// mortars (sorted, unique), whose factor the block forms too. A node on more
+// than two mortars is an invalid mesh.
+idp_status host_mortar_tables(int NP, int W, int K, int M, const std::vector<int32_t> &m_large,
+                              const std::vector<int2> &m_small, const std::vector<int32_t> &m_info,
+                              std::vector<int32_t> &mn_node, std::vector<int2> &mn_slot,
+                              std::vector<int32_t> &mb_node_off, std::vector<int32_t> &mb_for_off,
+                              std::vector<int32_t> &mb_foreign, int &fmax) {
+    const int Q = 3 * NP;
+    std::vector<int> first((size_t)K * NP * NP, -1), second((size_t)K * NP * NP, -1);
+    for (int m = 0; m < M; ++m)
+        for (int q = 0; q < Q; ++q) {
+            const long long g = mortar_slot_node(NP, m, q, m_large, m_small, m_info);
+            const int sl = m * Q + q;
+            if (first[g] < 0) first[g] = sl;
+            else if (second[g] < 0) second[g] = sl;
+            else return IDP_E_MESH;
+        }
+    const int nb = M > 0 ? (M + W - 1) / W : 0;
+    fmax = 0;
+    mn_node.clear(); mn_slot.clear(); mb_foreign.clear();
+    mb_node_off.assign(1, 0); mb_for_off.assign(1, 0);
+    for (int b = 0; b < nb; ++b) {
+        std::vector<int32_t> fore;
+        for (int m = b * W; m < std::min(M, b * W + W); ++m)
+            for (int q = 0; q < Q; ++q) {
+                const int sl = m * Q + q;
+                const long long g = mortar_slot_node(NP, m, q, m_large, m_small, m_info);
+                if (first[g] != sl) continue;
+                mn_node.push_back((int32_t)g);
+                mn_slot.push_back(make_int2(sl, second[g]));
+                if (second[g] >= 0 && (second[g] / Q) / W != b) fore.push_back(second[g] / Q);
+            }
+        mb_node_off.push_back((int32_t)mn_node.size());
+        std::sort(fore.begin(), fore.end());
+        fore.erase(std::unique(fore.begin(), fore.end()), fore.end());
+        for (int32_t m : fore) mb_foreign.push_back(m);
+        mb_for_off.push_back((int32_t)mb_foreign.size());
+        fmax = std::max(fmax, (int)fore.size());
+    }
+    if (mb_foreign.empty()) mb_foreign.push_back(0);
+    return IDP_OK;
+}
+
 void host_log_table(LogTab &T) { host_log_table_impl(T); }
 
 // LGL quadrature weights for degree N (used by the allocation-free integrals)
@@ -467,10 +528,15 @@ struct idp_ctx {
     bool tuned = false;
     cudaGraphExec_t graph = nullptr;
     const double *graph_u = nullptr;
+    bool graph_stale = false;   // the mesh changed since the capture
     long long n_stages = 0;
     double total_area = 0.0;   // sum of element areas (all simulations)
     double *d_aind = nullptr;  // per element: shock indicator of the stage (combined limiting)
     double total_mortar_len = 0.0;   // sum of the large faces' lengths over the mortars
+    // statistics across adaptations: the normalisers of the stages on earlier
+    // meshes since the last read, and the stage count when the mesh changed
+    double stats_mass_prior = 0.0, stats_mlen_prior = 0.0;
+    long long stats_stages_prior = 0;
     // local-limiting variants: extended element kernel, low-order bounds
     int ext = 0;               // entropy bound or low-order bounds in use
     int lob = 0;               // low-order bounds (pre-pass + mortar gather each stage)
@@ -479,6 +545,16 @@ struct idp_ctx {
     int facebuf = 0;           // FP64 default kernel: conforming faces from k_face
     double *d_fbuf = nullptr;  // k_face output: [6][2 K (N+1)] doubles + [2 K (N+1)] floats
     void *d_lam = nullptr;     // wave speeds of every node for the time step (no face buffer)
+    // adaptation on the device (single-mesh contexts): the leaves' level and
+    // indices, the level-0 grid, the transfer's operators, the buffer sizes
+    // in elements and mortars, and a scratch area that only grows
+    int8_t *d_lev = nullptr;
+    int32_t *d_ix = nullptr, *d_iy = nullptr;
+    RemeshMesh rmesh = {};
+    Ops *d_ops_amr = nullptr;
+    long long capK = 0, capM = 0, cap_nodes = 0, cap_blocks = 0, cap_foreign = 0;
+    void *d_rm = nullptr;
+    size_t rm_bytes = 0;
     // optional timing: 1 step spans around the graph launches; 2 steps
     // launched without the graph, with element-pass events
     int prof = 0;
@@ -792,6 +868,48 @@ void reset_stats(idp_ctx *c, cudaStream_t st) {
     cudaStreamSynchronize(st);
 }
 
+// The mortar slots (index m * 3(N+1) + q) as one block of device memory with
+// room for Mcap mortars; the sub-arrays hold the current M mortars' slots,
+// S = M 3(N+1) apart for the [4][S] ones. Zeroed.
+cudaError_t alloc_slots(idp_ctx *c, long long Mcap) {
+    const int Q = 3 * c->NP;
+    if (c->d_slot_block) { cudaFree(c->d_slot_block); c->d_slot_block = nullptr; }
+    const size_t S = (size_t)c->M * Q, MM = (size_t)std::max<long long>(Mcap, 1),
+                 SS = std::max<size_t>((size_t)Mcap * Q, 1);
+    size_t bytes = sizeof(double) * (SS * (4 + 4 + 3 + 4 + 4 + 6 + 5)) + sizeof(float) * SS + sizeof(int32_t) * MM +
+                   sizeof(double) * MM + 22 * 256;   // 21 sub-arrays, each padded to 256 B
+    cudaError_t e = cudaMalloc(&c->d_slot_block, bytes);
+    if (e == cudaSuccess) e = cudaMemset(c->d_slot_block, 0, bytes);
+    if (e != cudaSuccess) return e;
+    char *p = (char *)c->d_slot_block;
+    auto take = [&](size_t nb) { char *r = p; p += (nb + 255) & ~size_t(255); return (void *)r; };
+    SlotsDev &sl = c->slots;
+    sl.S = (int)S;
+    sl.chi = (double *)take(sizeof(double) * 4 * SS);
+    sl.clo = (double *)take(sizeof(double) * 4 * SS);
+    sl.rbmin = (double *)take(sizeof(double) * SS);
+    sl.rbmax = (double *)take(sizeof(double) * SS);
+    sl.dsum = (double *)take(sizeof(double) * SS);
+    sl.uvol = (double *)take(sizeof(double) * 4 * SS);
+    sl.un = (double *)take(sizeof(double) * 4 * SS);
+    sl.rmin = (double *)take(sizeof(double) * SS);
+    sl.rmax = (double *)take(sizeof(double) * SS);
+    sl.pmin = (double *)take(sizeof(double) * SS);
+    sl.tol = (double *)take(sizeof(double) * SS);
+    sl.mass = (double *)take(sizeof(double) * SS);
+    sl.rfv = (double *)take(sizeof(double) * SS);
+    sl.nmort = (float *)take(sizeof(float) * SS);
+    sl.bad = (int32_t *)take(sizeof(int32_t) * MM);
+    sl.ell = (double *)take(sizeof(double) * MM);
+    sl.lnK = (double *)take(sizeof(double) * SS);
+    sl.sbmin = (double *)take(sizeof(double) * SS);
+    sl.lbmin = (double *)take(sizeof(double) * SS);
+    sl.lbmax = (double *)take(sizeof(double) * SS);
+    sl.lsmin = (double *)take(sizeof(double) * SS);
+    if ((size_t)(p - (char *)c->d_slot_block) > bytes) return cudaErrorMemoryAllocation;
+    return cudaSuccess;
+}
+
 idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double gamma, const idp_options *opts,
                        idp_ctx **out) {
     if (!out) return IDP_E_ARG;
@@ -812,10 +930,15 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (o.grid_mode < 0 || o.grid_mode > 2) return IDP_E_ARG;
     HostMesh H;
     H.sim_off.push_back(0);
+    std::vector<int8_t> all_lev;
+    std::vector<int32_t> all_ix, all_iy;
     for (int s = 0; s < n_sims; ++s) {
         idp_status r = build_mesh(meshes[s], gamma, s, H);
         if (r != IDP_OK) return r;
         H.sim_off.push_back((long long)H.geom.size());
+        all_lev.insert(all_lev.end(), meshes[s].level, meshes[s].level + meshes[s].n_leaves);
+        all_ix.insert(all_ix.end(), meshes[s].ix, meshes[s].ix + meshes[s].n_leaves);
+        all_iy.insert(all_iy.end(), meshes[s].iy, meshes[s].iy + meshes[s].n_leaves);
     }
     idp_ctx *c = new (std::nothrow) idp_ctx();
     if (!c) return IDP_E_ARG;
@@ -839,66 +962,17 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ce != cudaSuccess) { note(ce, "device query"); delete c; return IDP_E_CUDA; }
     Ops ops;
     build_ops(N, o.mortar_projection, o.mortar_low, ops);
-    // unique mortar nodes, slots ordered by mortar id
+    // unique mortar nodes and the blocks of the mortar limiting kernel
     const int NP = c->NP, NN = NP * NP, Q = 3 * NP;
-    std::vector<std::pair<long long, int>> ns;
-    ns.reserve((size_t)c->M * Q);
-    for (long long m = 0; m < c->M; ++m) {
-        int dir = H.m_info[m] & 1, low = (H.m_info[m] >> 1) & 1;
-        int sL = dir == 0 ? (low ? 1 : 0) : (low ? 3 : 2), sS = sL ^ 1;
-        for (int q = 0; q < Q; ++q) {
-            int e, s, t;
-            if (q < NP) { e = H.m_large[m]; s = sL; t = q; }
-            else { e = ((q - NP) / NP == 0) ? H.m_small[m].x : H.m_small[m].y; s = sS; t = (q - NP) % NP; }
-            int i = s == 0 ? 0 : (s == 1 ? NP - 1 : t), j = s == 2 ? 0 : (s == 3 ? NP - 1 : t);
-            ns.push_back({(long long)e * NN + j * NP + i, (int)(m * Q + q)});
-        }
-    }
-    std::sort(ns.begin(), ns.end());
     std::vector<int32_t> mn_node;
     std::vector<int2> mn_slot;
-    for (size_t k = 0; k < ns.size();) {
-        size_t k2 = k;
-        while (k2 < ns.size() && ns[k2].first == ns[k].first) ++k2;
-        if (k2 - k > 2) { delete c; return IDP_E_MESH; }
-        mn_node.push_back((int32_t)ns[k].first);
-        mn_slot.push_back(make_int2(ns[k].second, k2 - k == 2 ? ns[k + 1].second : -1));
-        k = k2;
-    }
-    c->n_mnodes = (int)mn_node.size();
-    // blocks of the mortar limiting kernel: block b owns mortars [b W, b W + W)
-    // and the nodes whose first mortar is one of them (the node list reordered
-    // by owner, node order within a block); a node's second mortar in a later
-    // block is one of the block's foreign mortars, whose factor it forms too
     std::vector<int32_t> mb_node_off(1, 0), mb_for_off(1, 0), mb_foreign;
     {
-        const int MW = c->L.mortar_w;
-        const int nb = c->M > 0 ? (int)((c->M + MW - 1) / MW) : 0;
-        std::vector<std::vector<int>> own(nb);
-        std::vector<std::vector<int32_t>> fore(nb);
-        for (int k = 0; k < c->n_mnodes; ++k) {
-            const int m0 = mn_slot[k].x / Q, m1 = mn_slot[k].y >= 0 ? mn_slot[k].y / Q : -1;
-            const int b = m0 / MW;
-            own[b].push_back(k);
-            if (m1 >= 0 && m1 / MW != b) fore[b].push_back(m1);
-        }
-        std::vector<int32_t> node2;
-        std::vector<int2> slot2;
-        node2.reserve(mn_node.size());
-        slot2.reserve(mn_slot.size());
-        for (int b = 0; b < nb; ++b) {
-            for (int k : own[b]) { node2.push_back(mn_node[k]); slot2.push_back(mn_slot[k]); }
-            mb_node_off.push_back((int32_t)node2.size());
-            std::sort(fore[b].begin(), fore[b].end());
-            fore[b].erase(std::unique(fore[b].begin(), fore[b].end()), fore[b].end());
-            for (int32_t m : fore[b]) mb_foreign.push_back(m);
-            mb_for_off.push_back((int32_t)mb_foreign.size());
-            c->mb_fmax = std::max(c->mb_fmax, (int)fore[b].size());
-        }
-        mn_node.swap(node2);
-        mn_slot.swap(slot2);
-        c->mb_blocks = nb;
-        if (mb_foreign.empty()) mb_foreign.push_back(0);
+        idp_status r = host_mortar_tables(c->NP, c->L.mortar_w, (int)c->K, (int)c->M, H.m_large, H.m_small, H.m_info,
+                                          mn_node, mn_slot, mb_node_off, mb_for_off, mb_foreign, c->mb_fmax);
+        if (r != IDP_OK) { delete c; return r; }
+        c->n_mnodes = (int)mn_node.size();
+        c->mb_blocks = (int)mb_node_off.size() - 1;
     }
     bool ok = true;
     int step_no = 0;
@@ -930,40 +1004,17 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     if (ok) chk(upload(&c->d_mbnode, mb_node_off));
     if (ok) chk(upload(&c->d_mbfor, mb_for_off));
     if (ok) chk(upload(&c->d_mbforeign, mb_foreign));
+    if (ok) chk(upload(&c->d_lev, all_lev));
+    if (ok) chk(upload(&c->d_ix, all_ix));
+    if (ok) chk(upload(&c->d_iy, all_iy));
+    c->rmesh.nx0 = meshes[0].nx0; c->rmesh.ny0 = meshes[0].ny0;
+    c->rmesh.x0 = meshes[0].x0; c->rmesh.y0 = meshes[0].y0; c->rmesh.x1 = meshes[0].x1; c->rmesh.y1 = meshes[0].y1;
+    for (int s = 0; s < 4; ++s) c->rmesh.bc[s] = meshes[0].bc[s];
+    c->capK = c->K; c->capM = c->M;
+    c->cap_nodes = (long long)mn_node.size(); c->cap_blocks = (long long)mb_node_off.size();
+    c->cap_foreign = (long long)mb_foreign.size();
     // slots: one block of device memory
-    const size_t S = (size_t)c->M * Q, MM = (size_t)std::max<long long>(c->M, 1), SS = std::max<size_t>(S, 1);
-    size_t bytes = sizeof(double) * (SS * (4 + 4 + 3 + 4 + 4 + 6 + 5)) + sizeof(float) * SS + sizeof(int32_t) * MM +
-                   sizeof(double) * MM + 22 * 256;   // 21 sub-arrays, each padded to 256 B
-    if (ok) chk(cudaMalloc(&c->d_slot_block, bytes));
-    if (ok) chk(cudaMemset(c->d_slot_block, 0, bytes));
-    if (ok) {
-        char *p = (char *)c->d_slot_block;
-        auto take = [&](size_t nb) { char *r = p; p += (nb + 255) & ~size_t(255); return (void *)r; };
-        SlotsDev &sl = c->slots;
-        sl.S = (int)S;
-        sl.chi = (double *)take(sizeof(double) * 4 * SS);
-        sl.clo = (double *)take(sizeof(double) * 4 * SS);
-        sl.rbmin = (double *)take(sizeof(double) * SS);
-        sl.rbmax = (double *)take(sizeof(double) * SS);
-        sl.dsum = (double *)take(sizeof(double) * SS);
-        sl.uvol = (double *)take(sizeof(double) * 4 * SS);
-        sl.un = (double *)take(sizeof(double) * 4 * SS);
-        sl.rmin = (double *)take(sizeof(double) * SS);
-        sl.rmax = (double *)take(sizeof(double) * SS);
-        sl.pmin = (double *)take(sizeof(double) * SS);
-        sl.tol = (double *)take(sizeof(double) * SS);
-        sl.mass = (double *)take(sizeof(double) * SS);
-        sl.rfv = (double *)take(sizeof(double) * SS);
-        sl.nmort = (float *)take(sizeof(float) * SS);
-        sl.bad = (int32_t *)take(sizeof(int32_t) * MM);
-        sl.ell = (double *)take(sizeof(double) * MM);
-        sl.lnK = (double *)take(sizeof(double) * SS);
-        sl.sbmin = (double *)take(sizeof(double) * SS);
-        sl.lbmin = (double *)take(sizeof(double) * SS);
-        sl.lbmax = (double *)take(sizeof(double) * SS);
-        sl.lsmin = (double *)take(sizeof(double) * SS);
-        if ((size_t)(p - (char *)c->d_slot_block) > bytes) { ok = false; note(cudaErrorMemoryAllocation, "slot layout"); }
-    }
+    if (ok) chk(alloc_slots(c, c->M));
     const size_t kn = KN(c);
     if (ok) chk(cudaMalloc(&c->d_buf1, sizeof(double) * 4 * kn));
     if (ok) chk(cudaMalloc(&c->d_buf2, sizeof(double) * 4 * kn));
@@ -1017,6 +1068,17 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
+namespace {
+// (re)allocate *p for n elements of T when it holds fewer than cap
+template <typename T>
+cudaError_t ensure(T **p, long long n, long long cap) {
+    if (n <= cap && *p) return cudaSuccess;
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+    return cudaMalloc((void **)p, sizeof(T) * (size_t)std::max<long long>(n, 1));
+}
+}  // namespace
+
 extern "C" {
 
 const char *idp_last_cuda_error(void) { return g_last_error; }
@@ -1164,16 +1226,28 @@ idp_status idp_dgsem_step(idp_ctx *c, double *u, int32_t n_steps, double *t_host
         }
         c->n_stages += 3LL * n_steps;
     } else if (n_steps > 0) {
-        if (c->graph == nullptr || c->graph_u != u) {   // re-captured when u changes
-            if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+        if (c->graph == nullptr || c->graph_u != u || c->graph_stale) {
+            // re-captured when u or the mesh changes; the executable graph is
+            // updated in place when the new capture has its shape
             cudaGraph_t g;
             if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return IDP_E_CUDA;
             enqueue_step(c, st, u);
             if (cudaStreamEndCapture(st, &g) != cudaSuccess) return IDP_E_CUDA;
-            cudaError_t e = cudaGraphInstantiate(&c->graph, g, 0);
+            bool updated = false;
+            if (c->graph) {
+                cudaGraphExecUpdateResultInfo info;
+                updated = cudaGraphExecUpdate(c->graph, g, &info) == cudaSuccess;
+                if (!updated) {
+                    cudaGetLastError();   // the failed update is not an error of the step
+                    cudaGraphExecDestroy(c->graph);
+                    c->graph = nullptr;
+                }
+            }
+            cudaError_t e = updated ? cudaSuccess : cudaGraphInstantiate(&c->graph, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) { c->graph = nullptr; return IDP_E_CUDA; }
             c->graph_u = u;
+            c->graph_stale = false;
         }
         for (int k = 0; k < n_steps; ++k) {
             if (c->prof) cudaEventRecord(c->pev[6], st);
@@ -1205,7 +1279,10 @@ idp_status idp_dgsem_step_host(idp_ctx *c, double *u_host, int32_t n_steps, doub
     if (!c || !u_host) return IDP_E_ARG;
     cudaStream_t st = (cudaStream_t)stream;
     size_t bytes = sizeof(double) * 4 * KN(c);
-    if (!c->d_hostbuf && cudaMalloc(&c->d_hostbuf, bytes) != cudaSuccess) return IDP_E_CUDA;
+    // sized for the element capacity, which adaptation may fill
+    if (!c->d_hostbuf &&
+        cudaMalloc(&c->d_hostbuf, sizeof(double) * 4 * (size_t)c->capK * c->NP * c->NP) != cudaSuccess)
+        return IDP_E_CUDA;
     if (cudaMemcpyAsync(c->d_hostbuf, u_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) return IDP_E_CUDA;
     idp_status r = idp_dgsem_step(c, c->d_hostbuf, n_steps, t_host, dt_last_host, stream);
     if (r != IDP_OK && r != IDP_E_NUMERIC) return r;
@@ -1237,12 +1314,13 @@ idp_status idp_dgsem_limiter_stats(idp_ctx *c, idp_limiter_stats *out, void *str
         return IDP_E_CUDA;
     std::memset(out, 0, sizeof(*out));
     // every limited stage visits every node once: the mass sum is the mesh
-    // area times the number of limited stages
-    const double mass = c->total_area * (double)c->n_stages;
+    // area times the number of limited stages (summed over the meshes the
+    // stages ran on, when the context adapted in between)
+    const double mass = c->stats_mass_prior + c->total_area * (double)(c->n_stages - c->stats_stages_prior);
     out->alpha_volume_mean = mass > 0 ? a.alpha_vol_m / mass : 0.0;
     // every limited stage limits every mortar once: the length sum is the
     // total mortar length times the number of limited stages
-    const double mlen = c->total_mortar_len * (double)c->n_stages;
+    const double mlen = c->stats_mlen_prior + c->total_mortar_len * (double)(c->n_stages - c->stats_stages_prior);
     out->alpha_mortar_mean = mlen > 0 ? a.alpha_mort_len / mlen : 0.0;
     out->n_stages = c->n_stages;
     out->n_volume_active = (int64_t)a.n_vol;
@@ -1256,6 +1334,8 @@ idp_status idp_dgsem_limiter_stats(idp_ctx *c, idp_limiter_stats *out, void *str
     std::memcpy(&out->min_rho, &a.min_rho_bits, sizeof(double));
     std::memcpy(&out->min_p, &a.min_p_bits, sizeof(double));
     c->n_stages = 0;
+    c->stats_mass_prior = c->stats_mlen_prior = 0.0;
+    c->stats_stages_prior = 0;
     reset_stats(c, c->stream);
     return read_status(c);
 }
@@ -1515,11 +1595,249 @@ idp_status idp_amr_transfer(int32_t N, double gamma, const double *u_old, int64_
     return rc;
 }
 
+// ---- adaptation on the device --------------------------------------------
+
+idp_status idp_dgsem_adapt(idp_ctx *c, const double *u_old, const idp_amr_params *p, double *u_new,
+                           int64_t capacity, int64_t *n_new, int64_t *n_scaled, void *stream) {
+    if (!c || !u_old || !u_new || !amr_params_ok(p) || capacity < 1 || !n_new) return IDP_E_ARG;
+    if (c->n_sims != 1 || c->prof == 2) return IDP_E_ARG;
+    // leaf indices of the finest level must fit the 28-bit leaf keys (as at create)
+    if (((int64_t)c->rmesh.nx0 << p->max_level) >= (1LL << 28) || ((int64_t)c->rmesh.ny0 << p->max_level) >= (1LL << 28))
+        return IDP_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int K = (int)c->K, NP = c->NP, NN = NP * NP, Q = 3 * NP, W = c->L.mortar_w;
+    // scratch: the indicator, the plan and its leaves (at most 4 K), then the
+    // mesh builders' tables; it only grows
+    const long long K4 = 4LL * K;
+    const int Kb = (int)std::min<long long>(K4, std::max<long long>(capacity, 1));
+    const size_t plan_ints = remesh_plan_scratch_ints(K);
+    auto pad = [](size_t nb) { return (nb + 255) & ~size_t(255); };
+    const size_t head = pad(sizeof(double) * K) + pad(sizeof(int) * plan_ints) + pad((size_t)Kb) +
+                        3 * pad(sizeof(int) * (size_t)Kb) + 2 * pad(sizeof(int4) * (size_t)Kb) +
+                        pad(sizeof(unsigned long long) + 2 * sizeof(double));
+    // a 2:1 balanced mesh has at most one mortar per leaf (each mortar has
+    // two small sides, each leaf at most two small sides)
+    const size_t need = head + std::max(remesh_build_scratch_bytes(Kb, NP), remesh_nodes_scratch_bytes(Kb, NP, Kb, W));
+    if (need > c->rm_bytes) {
+        if (c->d_rm) cudaFree(c->d_rm);
+        c->d_rm = nullptr;
+        c->rm_bytes = 0;
+        if (note(cudaMalloc(&c->d_rm, need), "adapt scratch") != cudaSuccess) return IDP_E_CUDA;
+        c->rm_bytes = need;
+    }
+    char *q = (char *)c->d_rm;
+    auto take = [&](size_t nb) { char *r = q; q += pad(nb); return (void *)r; };
+    double *ind = (double *)take(sizeof(double) * K);
+    int *plan_s = (int *)take(sizeof(int) * plan_ints);
+    int8_t *nlev = (int8_t *)take((size_t)Kb);
+    int *nix = (int *)take(sizeof(int) * Kb), *niy = (int *)take(sizeof(int) * Kb), *kind = (int *)take(sizeof(int) * Kb);
+    int4 *src = (int4 *)take(sizeof(int4) * Kb), *fam = (int4 *)take(sizeof(int4) * Kb);
+    unsigned long long *d_cnt = (unsigned long long *)take(sizeof(unsigned long long) + 2 * sizeof(double));
+    void *build_s = (void *)q;
+    // the context's streams are idle before its tables change
+    if (note(cudaStreamSynchronize(c->stream), "adapt sync") != cudaSuccess ||
+        note(cudaStreamSynchronize(c->st2), "adapt sync") != cudaSuccess)
+        return IDP_E_CUDA;
+    // indicator and plan on the current mesh
+    c->L.amr_indicator(st, u_old, K, c->d_ops, c->gamma - 1.0, p->indicator, p->variable, p->lohner_filter, ind,
+                       c->num_sms);
+    PlanIn pin = {K, ind, c->d_lev, c->d_ix, c->d_iy, c->d_fnbr, c->d_ftype, c->d_mlarge, c->d_msmall,
+                  p->refine_threshold, p->coarsen_threshold, p->min_level, p->max_level};
+    PlanOut pout = {Kb, nlev, nix, niy, kind, src, fam};
+    int Kn = 0, nfam = 0, iters = 0;
+    if (note(remesh_plan(pin, pout, plan_s, st, c->num_sms, &Kn, &nfam, &iters), "adapt plan") != cudaSuccess)
+        return IDP_E_CUDA;
+    if (iters < 0) return IDP_E_MESH;
+    *n_new = Kn;
+    if (Kn > capacity) return IDP_E_ARG;   // the caller's state buffer is too small: *n_new says how large
+    // transfer (interpolation, exact L2 projection, Zhang-Shu scaling)
+    if (!c->d_ops_amr) {
+        Ops oa;
+        build_ops(c->N, 1, 0, oa);
+        if (note(cudaMalloc(&c->d_ops_amr, sizeof(Ops)), "adapt ops") != cudaSuccess ||
+            note(cudaMemcpy(c->d_ops_amr, &oa, sizeof(Ops), cudaMemcpyHostToDevice), "adapt ops") != cudaSuccess)
+            return IDP_E_CUDA;
+    }
+    cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long), st);
+    c->L.amr_transfer(st, u_old, K, u_new, Kn, kind, src, c->d_ops_amr, c->num_sms);
+    c->L.amr_zs(st, u_new, Kn, u_old, K, fam, nfam, c->d_ops_amr, c->gamma - 1.0, p->zs_threshold, d_cnt);
+    if (note(cudaStreamSynchronize(st), "adapt transfer") != cudaSuccess) return IDP_E_CUDA;
+    // element buffers, grown with slack when the mesh outgrows them (their
+    // contents are rebuilt or per stage)
+    cudaError_t ce = cudaSuccess;
+    auto chk = [&](cudaError_t e) { if (ce == cudaSuccess && e != cudaSuccess) ce = e; };
+    const long long oK = c->capK, nK = Kn > oK ? std::max<long long>(Kn, oK + oK / 4) : oK;
+    if (nK > oK) {
+        chk(ensure(&c->d_geom, nK, 0));
+        chk(ensure(&c->d_geoc, nK, 0));
+        chk(ensure(&c->d_sim, nK, 0));
+        chk(ensure(&c->d_fnbr, nK, 0));
+        chk(ensure(&c->d_ftype, nK, 0));
+        chk(ensure(&c->d_aind, nK, 0));
+        chk(ensure(&c->d_part, 4 * nK, 0));
+        chk(ensure(&c->d_buf1, 4 * nK * NN, 0));
+        chk(ensure(&c->d_buf2, 4 * nK * NN, 0));
+        chk(ensure(&c->d_lev, nK, 0));
+        chk(ensure(&c->d_ix, nK, 0));
+        chk(ensure(&c->d_iy, nK, 0));
+        if (c->d_fbuf) {
+            const long long F = 2 * nK * NP;
+            cudaFree(c->d_fbuf);
+            c->d_fbuf = nullptr;
+            chk(cudaMalloc(&c->d_fbuf, sizeof(double) * 6 * F + sizeof(float) * F));
+        }
+        if (c->d_lam) {
+            cudaFree(c->d_lam);
+            c->d_lam = nullptr;
+            chk(cudaMalloc(&c->d_lam, (c->opt.precision ? sizeof(float) : sizeof(double)) * 2 * (size_t)nK * NN));
+        }
+        if (c->d_lofv) chk(ensure(&c->d_lofv, 2 * nK * NN, 0));
+        if (c->d_hostbuf) { cudaFree(c->d_hostbuf); c->d_hostbuf = nullptr; }
+        if (ce != cudaSuccess) { note(ce, "adapt alloc"); return IDP_E_CUDA; }
+        c->capK = nK;
+    }
+    // the new leaves become the context's
+    chk(cudaMemcpyAsync(c->d_lev, nlev, (size_t)Kn, cudaMemcpyDeviceToDevice, st));
+    chk(cudaMemcpyAsync(c->d_ix, nix, sizeof(int) * Kn, cudaMemcpyDeviceToDevice, st));
+    chk(cudaMemcpyAsync(c->d_iy, niy, sizeof(int) * Kn, cudaMemcpyDeviceToDevice, st));
+    chk(cudaMemsetAsync(c->d_aind, 0, sizeof(double) * Kn, st));
+    if (c->d_lofv) chk(cudaMemsetAsync(c->d_lofv, 0, sizeof(double) * 2 * (size_t)Kn * NN, st));
+    if (ce != cudaSuccess) { note(ce, "adapt copy"); return IDP_E_CUDA; }
+    // faces and mortars: the first pass counts the mortars and writes them
+    // when the buffers hold them, else they grow and a second pass writes
+    BuildIn bin = {c->rmesh, Kn, c->d_lev, c->d_ix, c->d_iy};
+    BuildOut bout = {c->d_geom, c->d_geoc, c->d_sim, c->d_fnbr, c->d_ftype, c->d_mlarge, c->d_msmall, c->d_minfo,
+                     (int)(c->d_mlarge ? c->capM : 0)};
+    int Mn = 0, err = 0;
+    if (note(remesh_build_faces(bin, bout, build_s, st, c->num_sms, &Mn, &err), "adapt faces") != cudaSuccess)
+        return IDP_E_CUDA;
+    if (err) return IDP_E_MESH;
+    if (Mn > bout.capM) {
+        const long long nM = std::max<long long>(Mn, c->capM + c->capM / 4);
+        chk(ensure(&c->d_mlarge, nM, 0));
+        chk(ensure(&c->d_msmall, nM, 0));
+        chk(ensure(&c->d_minfo, nM, 0));
+        c->capM = nM;
+        // the slot block is sized for capM mortars
+        chk(alloc_slots(c, nM));
+        if (ce != cudaSuccess) { note(ce, "adapt alloc"); return IDP_E_CUDA; }
+        bout.m_large = c->d_mlarge; bout.m_small = c->d_msmall; bout.m_info = c->d_minfo; bout.capM = (int)nM;
+        if (note(remesh_build_faces(bin, bout, build_s, st, c->num_sms, &Mn, &err), "adapt faces") != cudaSuccess)
+            return IDP_E_CUDA;
+        if (err) return IDP_E_MESH;
+    }
+    // mortar nodes and the mortar limiting blocks: at most Q nodes per
+    // mortar, one foreign entry per node
+    const long long need_nodes = std::max<long long>((long long)Mn * Q, 1), need_blocks = (Mn + W - 1) / W + 1;
+    if (need_nodes > c->cap_nodes || !c->d_mnnode || !c->d_mnslot) {
+        const long long n = std::max<long long>(need_nodes, c->cap_nodes + c->cap_nodes / 4);
+        chk(ensure(&c->d_mnnode, n, 0));
+        chk(ensure(&c->d_mnslot, n, 0));
+        c->cap_nodes = n;
+    }
+    if (need_blocks > c->cap_blocks || !c->d_mbnode || !c->d_mbfor) {
+        const long long n = std::max<long long>(need_blocks, c->cap_blocks + c->cap_blocks / 4);
+        chk(ensure(&c->d_mbnode, n, 0));
+        chk(ensure(&c->d_mbfor, n, 0));
+        c->cap_blocks = n;
+    }
+    if (need_nodes + 1 > c->cap_foreign || !c->d_mbforeign) {
+        const long long n = std::max<long long>(need_nodes + 1, c->cap_foreign + c->cap_foreign / 4);
+        chk(ensure(&c->d_mbforeign, n, 0));
+        c->cap_foreign = n;
+    }
+    if (ce != cudaSuccess) { note(ce, "adapt alloc"); return IDP_E_CUDA; }
+    NodesIn nin = {NP, Kn, Mn, W, c->d_mlarge, c->d_msmall, c->d_minfo};
+    NodesOut nout = {c->d_mnnode, c->d_mnslot, c->d_mbnode, c->d_mbfor, c->d_mbforeign, (int)c->cap_nodes,
+                     (int)c->cap_foreign, (int)c->cap_blocks};
+    int nmn = 0, nblk = 0, fmax = 0;
+    if (note(remesh_build_mortar_nodes(nin, nout, build_s, st, c->num_sms, &nmn, &nblk, &fmax, &err), "adapt nodes") !=
+        cudaSuccess)
+        return IDP_E_CUDA;
+    if (err) return IDP_E_MESH;
+    // sizes and the totals of the adapted mesh (host arithmetic as at create)
+    c->K = Kn;
+    c->M = Mn;
+    c->slots.S = Mn * Q;
+    c->n_mnodes = nmn;
+    c->mb_blocks = nblk;
+    c->mb_fmax = fmax;
+    c->sim_off = {0, (long long)Kn};
+    chk(cudaMemcpyAsync(c->d_off, c->sim_off.data(), sizeof(long long) * 2, cudaMemcpyHostToDevice, st));
+    // statistics so far are normalised with the old mesh's totals
+    c->stats_mass_prior += c->total_area * (double)(c->n_stages - c->stats_stages_prior);
+    c->stats_mlen_prior += c->total_mortar_len * (double)(c->n_stages - c->stats_stages_prior);
+    c->stats_stages_prior = c->n_stages;
+    double *d_tot = (double *)(d_cnt + 1);
+    remesh_totals(c->rmesh, c->d_lev, Kn, c->d_mlarge, c->d_minfo, Mn, d_tot, st);
+    MeshDev &md = c->mesh;
+    md.K = Kn; md.M = Mn; md.n_mnodes = nmn;
+    md.geom = c->d_geom; md.geoc = c->d_geoc; md.sim = c->d_sim; md.fnbr = c->d_fnbr; md.ftype = c->d_ftype;
+    md.m_large = c->d_mlarge; md.m_small = c->d_msmall; md.m_info = c->d_minfo;
+    md.mn_node = c->d_mnnode; md.mn_slot = c->d_mnslot;
+    md.mb_node_off = c->d_mbnode; md.mb_for_off = c->d_mbfor; md.mb_foreign = c->d_mbforeign;
+    md.mb_fmax = fmax; md.mb_blocks = nblk;
+    // the step graph is captured again for the new mesh
+    c->graph_stale = true;
+    unsigned long long cnt = 0;
+    double tot[2] = {0.0, 0.0};
+    if (note(cudaMemcpyAsync(&cnt, d_cnt, sizeof(cnt), cudaMemcpyDeviceToHost, st), "adapt count") != cudaSuccess ||
+        note(cudaMemcpyAsync(tot, d_tot, sizeof(tot), cudaMemcpyDeviceToHost, st), "adapt totals") != cudaSuccess ||
+        note(cudaStreamSynchronize(st), "adapt sync") != cudaSuccess)
+        return IDP_E_CUDA;
+    c->total_area = tot[0];
+    c->total_mortar_len = tot[1];
+    if (n_scaled) *n_scaled = (int64_t)cnt;
+    return check_cuda(cudaGetLastError());
+}
+
+idp_status idp_dgsem_leaves(idp_ctx *c, int8_t *level, int32_t *ix, int32_t *iy) {
+    if (!c || !level || !ix || !iy) return IDP_E_ARG;
+    const size_t K = (size_t)c->K;
+    if (cudaMemcpy(level, c->d_lev, K, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(ix, c->d_ix, sizeof(int32_t) * K, cudaMemcpyDeviceToHost) != cudaSuccess ||
+        cudaMemcpy(iy, c->d_iy, sizeof(int32_t) * K, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return IDP_E_CUDA;
+    return IDP_OK;
+}
+
+// Device tables of the context's mesh, copied to host arrays (test support):
+// fnbr/ftype [K][4], m_large [M], m_small [M][2], m_info [M], mn_node and
+// mn_slot [n_mnodes] (the slot pair as two ints), mb_node_off and mb_for_off
+// [mb_blocks + 1], mb_foreign [mb_for_off[mb_blocks]]; sizes[6] = K, M,
+// n_mnodes, mb_blocks, foreign count, mb_fmax. With null arrays only sizes.
+idp_status idp_dgsem_mesh_tables(idp_ctx *c, int64_t *sizes, int32_t *fnbr, uint8_t *ftype, int32_t *m_large,
+                                 int32_t *m_small, int32_t *m_info, int32_t *mn_node, int32_t *mn_slot,
+                                 int32_t *mb_node_off, int32_t *mb_for_off, int32_t *mb_foreign) {
+    if (!c || !sizes) return IDP_E_ARG;
+    int32_t nfore = 0;
+    if (c->mb_blocks > 0 &&
+        cudaMemcpy(&nfore, c->d_mbfor + c->mb_blocks, sizeof(int32_t), cudaMemcpyDeviceToHost) != cudaSuccess)
+        return IDP_E_CUDA;
+    sizes[0] = c->K; sizes[1] = c->M; sizes[2] = c->n_mnodes; sizes[3] = c->mb_blocks; sizes[4] = nfore;
+    sizes[5] = c->mb_fmax;
+    cudaError_t e = cudaSuccess;
+    auto cp = [&](void *h, const void *d, size_t b) { if (h && b && e == cudaSuccess) e = cudaMemcpy(h, d, b, cudaMemcpyDeviceToHost); };
+    cp(fnbr, c->d_fnbr, sizeof(int4) * c->K);
+    cp(ftype, c->d_ftype, sizeof(uchar4) * c->K);
+    cp(m_large, c->d_mlarge, sizeof(int32_t) * c->M);
+    cp(m_small, c->d_msmall, sizeof(int2) * c->M);
+    cp(m_info, c->d_minfo, sizeof(int32_t) * c->M);
+    cp(mn_node, c->d_mnnode, sizeof(int32_t) * c->n_mnodes);
+    cp(mn_slot, c->d_mnslot, sizeof(int2) * c->n_mnodes);
+    if (c->mb_blocks > 0) {
+        cp(mb_node_off, c->d_mbnode, sizeof(int32_t) * (c->mb_blocks + 1));
+        cp(mb_for_off, c->d_mbfor, sizeof(int32_t) * (c->mb_blocks + 1));
+        cp(mb_foreign, c->d_mbforeign, sizeof(int32_t) * nfore);
+    }
+    return e == cudaSuccess ? IDP_OK : IDP_E_CUDA;
+}
+
 void idp_dgsem_destroy(idp_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    void *ptrs[] = {c->d_fbuf, c->d_lam, c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+    void *ptrs[] = {c->d_lev, c->d_ix, c->d_iy, c->d_ops_amr, c->d_rm, c->d_fbuf, c->d_lam, c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
                     c->d_mbnode, c->d_mbfor, c->d_mbforeign,
                     c->d_msmall, c->d_mnslot, c->d_siminfo, c->d_slot_block, c->d_buf1, c->d_buf2, c->d_hostbuf,
                     c->d_dtmin, c->d_tsim, c->d_dtlast, c->d_status, c->d_stats, c->d_part, c->d_intout, c->d_off};

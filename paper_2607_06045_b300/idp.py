@@ -62,7 +62,7 @@ EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", 
            "idp_last_cuda_error", "idp_dgsem_profile", "idp_dgsem_profile_read", "idp_dgsem_profile_kernels",
            "idp_probe_pipes", "idp_eval_math",
            "idp_integrals_noalloc", "idp_amr_params_default", "idp_dgsem_amr_indicator", "idp_amr_plan",
-           "idp_amr_transfer"]
+           "idp_amr_transfer", "idp_dgsem_adapt", "idp_dgsem_leaves", "idp_dgsem_mesh_tables"]
 
 
 def lib():
@@ -105,6 +105,10 @@ def lib():
         L.idp_amr_plan.argtypes = [C.POINTER(MeshDesc), dp, C.POINTER(AmrParams), C.c_int32, ip, i8p, ip, ip, ip, ip]
         L.idp_amr_transfer.argtypes = [C.c_int32, C.c_double, vp, C.c_int64, vp, C.c_int64, ip, ip, C.c_double,
                                        C.POINTER(C.c_int64), vp]
+        i64p = C.POINTER(C.c_int64)
+        L.idp_dgsem_adapt.argtypes = [vp, vp, C.POINTER(AmrParams), vp, C.c_int64, i64p, i64p, vp]
+        L.idp_dgsem_leaves.argtypes = [vp, i8p, ip, ip]
+        L.idp_dgsem_mesh_tables.argtypes = [vp, i64p, ip, C.POINTER(C.c_uint8), ip, ip, ip, ip, ip, ip, ip, ip]
         L.idp_dgsem_destroy.restype = None
         for f in EXPORTS:
             if f not in ("idp_dgsem_destroy", "idp_status_str", "idp_last_cuda_error"):
@@ -372,6 +376,84 @@ class Context:
         mesh2 = dataclasses.replace(self.meshes[0], level=lev, ix=ix, iy=iy)
         un, scaled = idp_amr_transfer(self.N, self.gamma, u, kind, src, p.zs_threshold, stream)
         return Context(mesh2, self.N, self.gamma, opts=self.opts), un, (kind, src), scaled
+
+
+    def idp_dgsem_adapt(self, u, params=None, capacity=None, out=None, stream=None):
+        """One AMR step on the device, in this context: the context now steps
+        the adapted mesh. u_new is written into `out` (a flat FP64 device
+        tensor of at least 4 capacity (N+1)^2 values; allocated for capacity
+        = 4 K when None) and returned as a (4, K_new, N+1, N+1) view, with
+        the number of scaled families."""
+        import torch
+        p = params if params is not None else amr_params()
+        nn = self.np * self.np
+        if out is None:
+            cap = int(capacity) if capacity is not None else 4 * self.K
+            out = torch.empty(4 * cap * nn, dtype=torch.float64, device=u.device)
+        else:
+            cap = out.numel() // (4 * nn) if capacity is None else int(capacity)
+            assert out.numel() >= 4 * cap * nn
+        n, sc = C.c_int64(), C.c_int64()
+        rc = lib().idp_dgsem_adapt(self._h, _ptr(u), C.byref(p), _ptr(out), cap, C.byref(n), C.byref(sc),
+                                   _stream(stream))
+        if rc == 1 and n.value > cap:   # IDP_E_ARG with the count: the buffer is too small
+            raise ValueError(f"idp_dgsem_adapt: {n.value} elements exceed the capacity {cap}")
+        _check(rc, "idp_dgsem_adapt")
+        kn = n.value
+        K, M = C.c_int64(), C.c_int64()
+        _check(lib().idp_dgsem_layout(self._h, C.byref(K), C.byref(M), None, None), "idp_dgsem_layout")
+        self.K, self.M = K.value, M.value
+        self.sim_offsets = np.array([0, kn], dtype=np.int64)
+        self._leaves_stale = True   # `meshes` fetches the new leaves when read
+        return out[: 4 * kn * nn].view(4, kn, self.np, self.np), sc.value
+
+    @property
+    def meshes(self):
+        """The context's meshes (after idp_dgsem_adapt: the adapted leaves)."""
+        if getattr(self, "_leaves_stale", False):
+            import dataclasses
+            lev, ix, iy = self.leaves()
+            self._meshes = [dataclasses.replace(self._meshes[0], level=lev, ix=ix, iy=iy)]
+            self._leaves_stale = False
+        return self._meshes
+
+    @meshes.setter
+    def meshes(self, v):
+        self._meshes = v
+        self._leaves_stale = False
+
+    def leaves(self):
+        """(level, ix, iy) of the context's elements (host arrays)."""
+        lev = np.zeros(self.K, np.int8)
+        ix, iy = np.zeros(self.K, np.int32), np.zeros(self.K, np.int32)
+        ip = C.POINTER(C.c_int32)
+        _check(lib().idp_dgsem_leaves(self._h, lev.ctypes.data_as(C.POINTER(C.c_int8)), ix.ctypes.data_as(ip),
+                                      iy.ctypes.data_as(ip)), "idp_dgsem_leaves")
+        return lev, ix, iy
+
+    def mesh_tables(self, arrays=False):
+        """The context's device mesh tables as host arrays (test support)."""
+        sizes = np.zeros(6, np.int64)
+        i64p, ip = C.POINTER(C.c_int64), C.POINTER(C.c_int32)
+        if not arrays:
+            _check(lib().idp_dgsem_mesh_tables(self._h, sizes.ctypes.data_as(i64p), *([None] * 10)),
+                   "idp_dgsem_mesh_tables")
+            return {"sizes": [int(v) for v in sizes]}
+        _check(lib().idp_dgsem_mesh_tables(self._h, sizes.ctypes.data_as(i64p), *([None] * 10)),
+               "idp_dgsem_mesh_tables")
+        K, M, nn, nb, nf, _ = (int(v) for v in sizes)
+        t = {"fnbr": np.zeros((K, 4), np.int32), "ftype": np.zeros((K, 4), np.uint8),
+             "m_large": np.zeros(M, np.int32), "m_small": np.zeros((M, 2), np.int32), "m_info": np.zeros(M, np.int32),
+             "mn_node": np.zeros(nn, np.int32), "mn_slot": np.zeros((nn, 2), np.int32),
+             "mb_node_off": np.zeros(nb + 1, np.int32), "mb_for_off": np.zeros(nb + 1, np.int32),
+             "mb_foreign": np.zeros(max(nf, 1), np.int32)}
+        order = ["fnbr", "ftype", "m_large", "m_small", "m_info", "mn_node", "mn_slot", "mb_node_off", "mb_for_off",
+                 "mb_foreign"]
+        ptrs = [t[k].ctypes.data_as(C.POINTER(C.c_uint8) if k == "ftype" else ip) for k in order]
+        _check(lib().idp_dgsem_mesh_tables(self._h, sizes.ctypes.data_as(i64p), *ptrs), "idp_dgsem_mesh_tables")
+        t["mb_foreign"] = t["mb_foreign"][:nf]
+        t["sizes"] = [int(v) for v in sizes]
+        return t
 
 
 def amr_params(**kw) -> AmrParams:
