@@ -39,6 +39,31 @@ def rhs_scale(u, dt_idp):
     return np.abs(u).reshape(4, -1).max(axis=1) / dt_idp
 
 
+def local_rhs_err(a, ref, u, mesh, N, gamma=1.4):
+    """max over elements e and variables v of max_{i in e} |a - ref| / S_ev,
+    with the element's own residual scale S_ev = max_{i in e} |ref_v| +
+    U_ev lambda_e / h_e: U_ev = max_{i in e} |u_v| (for the momenta at least
+    max sqrt(rho E), the momentum scale of a fluid at rest), lambda_e the
+    largest wave speed |v| + c at the element's nodes and h_e = w_min
+    min(dx, dy) / 2 its smallest subcell width. Stricter than rhs_scale where
+    an element's state or speeds are far below the mesh maximum."""
+    import numpy as np
+    a, ref, u = (np.asarray(x).reshape(4, mesh.n_elems, -1) for x in (a, ref, u))
+    rho, m1, m2, E = u
+    p = (gamma - 1.0) * (E - 0.5 * (m1 * m1 + m2 * m2) / rho)
+    lam = (np.sqrt(m1 * m1 + m2 * m2) / rho + np.sqrt(gamma * np.abs(p) / rho)).max(axis=1)
+    wmin = 2.0 / (N * (N + 1))   # the LGL end weight, the smallest
+    x0, y0, x1, y1 = mesh.box
+    lv = mesh.level.astype(np.float64)
+    dx = (x1 - x0) / (mesh.nx0 * 2.0 ** lv)
+    dy = (y1 - y0) / (mesh.ny0 * 2.0 ** lv)
+    h = wmin * np.minimum(dx, dy) / 2.0
+    U = np.abs(u).max(axis=2)
+    U[1:3] = np.maximum(U[1:3], np.sqrt(np.abs(rho * E)).max(axis=1))
+    S = np.abs(ref).max(axis=2) + U * (lam / h)[None, :]
+    return float((np.abs(a - ref).max(axis=2) / S).max())
+
+
 def rel_err(a, b, scale):
     """max_v max_i |a - b| / scale_v"""
     import numpy as np

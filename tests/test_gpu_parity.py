@@ -3,7 +3,9 @@ the same seeded inputs.
 
 Tolerances (FP64 path): per right-hand side 1e-12 relative to the residual
 scale max|u_v| / dt_idp (the change of u over one IDP step, see
-conftest.rhs_scale); after 100 SSP-RK3 steps 1e-10 relative to max|u_v|.
+conftest.rhs_scale) and 1e-12 element by element relative to each element's
+own residual scale (conftest.local_rhs_err); after 100 SSP-RK3 steps 1e-10
+relative to max|u_v|.
 """
 import math
 
@@ -11,7 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
-from conftest import rel_err, rhs_scale, assert_l1_fields
+from conftest import rel_err, rhs_scale, assert_l1_fields, local_rhs_err
 from paper_2607_06045_b300 import build, idp
 from paper_2607_06045_b300 import workloads as W
 
@@ -50,12 +52,17 @@ def check_rhs(mesh, N, u, limiting, t=0.0, cfl=0.5, gamma=1.4, tol=1e-12, precis
     r_g = gpu_rhs(ctx, u, t, 0.0)
     e0 = rel_err(r_g, r_o, scale)
     assert e0 <= tol, ("dg", e0)
+    # element by element against each element's own residual scale
+    l0 = local_rhs_err(r_g, r_o, u, mesh, N, gamma)
+    assert l0 <= tol, ("dg, per element", l0)
     if limiting:
         dt = cfl * dt_idp
         r_o = o.rhs(u, t=t, dt=dt, limiting=limiting)
         r_g = gpu_rhs(ctx, u, t, dt)
         e1 = rel_err(r_g, r_o, scale)
         assert e1 <= tol, ("limited", e1)
+        l1 = local_rhs_err(r_g, r_o, u, mesh, N, gamma)
+        assert l1 <= tol, ("limited, per element", l1)
     ctx.close()
 
 
