@@ -14,6 +14,11 @@
   LLF surface flux with its wave speed (R3), the L2 mortar (R5), SSP-RK3
   and the IDP time step.
 - The same pin fails on a planted mistake in the volume flux.
+- With local limiting (density and entropy bounds; Table
+  ConvergenceTestLocalLimiting) the errors lie within 25% of the printed
+  ones and the EOC within 0.2 of 1.68: a band, not the digits, since the
+  limiter details the paper defers set the amount of low-order flux (parity
+  unpinned in those digits).
 - Isentropic vortex (exact solution: the advected initial state) on a
   nonconforming periodic mesh: EOC above 2.5.
 """
@@ -30,14 +35,14 @@ G = 1.4
 SRC = os.path.join(os.path.dirname(oracle.__file__), "idp_oracle.c")
 
 
-def run_to(o, u, T, cfl, limiting):
+def run_to(o, u, T, cfl, limiting, entropy=0):
     t = 0.0
     while t < T - 1e-14:
         dt = min(o.dt(u, t, cfl=cfl), T - t)
-        _, u1 = o.stage(u, t, dt, limiting=limiting)
-        _, ut = o.stage(u1, t + dt, dt, limiting=limiting)
+        _, u1 = o.stage(u, t, dt, limiting=limiting, entropy=entropy)
+        _, ut = o.stage(u1, t + dt, dt, limiting=limiting, entropy=entropy)
         u2 = 0.75 * u + 0.25 * ut
-        _, ut = o.stage(u2, t + 0.5 * dt, dt, limiting=limiting)
+        _, ut = o.stage(u2, t + 0.5 * dt, dt, limiting=limiting, entropy=entropy)
         u = u / 3.0 + 2.0 / 3.0 * ut
         t += dt
     return u
@@ -98,15 +103,15 @@ def density_wave_errors(N, level, T=1.0):
     return _ERRS[key]
 
 
-def _density_wave_errors(N, level, T):
+def _density_wave_errors(N, level, T, limiting=1, entropy=0):
     m = W.density_wave_mesh(level)
     o = oracle.Oracle(m, N)
-    u = run_to(o, W.density_wave_state(m, N), T, 0.95, limiting=1)
+    u = run_to(o, W.density_wave_state(m, N), T, 0.95, limiting=limiting, entropy=entropy)
     return analysis_l2(m, N, u, density_wave_exact(T), 4.0)
 
 
-def printed(N, level):
-    for row in read_golden(f"density_wave_positivity_N{N}.txt"):
+def printed(N, level, table="positivity"):
+    for row in read_golden(f"density_wave_{table}_N{N}.txt"):
         if row[0] == level:
             return np.array(row[1:5])
     raise KeyError(level)
@@ -144,6 +149,44 @@ def test_density_wave_pin_catches_planted_mistake(tmp_path):
     with oracle.using(lib):
         e = density_wave_errors(3, 2)
     assert not np.all(three_digits_agree(e, printed(3, 2))), e
+
+
+def test_density_wave_local_limiting_band():
+    """Table ConvergenceTestLocalLimiting (N = 3) within a band, not to its
+    digits. Local limiting as Sec. 3 defines it: the density bounds and the
+    entropy bound from the bar states (readings R6, R21). The limiter details
+    the paper defers to a cited paper (readings R7-R9, R15, R21) set how much
+    low-order flux it admits on this smooth wave, and the oracle's errors
+    come out 16% and 11% below the printed ones at levels 2 and 3 (parity
+    unpinned in those digits; with the low-order-solution bounds instead of
+    the bar states they come out 10% above and 3% below). What the band
+    pins: local limiting is active (the errors are some 6 and 16 times the
+    positivity table's) with the paper's amount of dissipation within 25%,
+    the momentum and energy errors in the wave's ratios to the density error
+    (0.1, 0.2, 0.025), and an EOC within 0.2 of the printed 1.68."""
+    e2 = _density_wave_errors(3, 2, 1.0, limiting=2, entropy=1)
+    e3 = _density_wave_errors(3, 3, 1.0, limiting=2, entropy=1)
+    for e, lv in ((e2, 2), (e3, 3)):
+        ratio = e / printed(3, lv, "local")
+        assert np.all((ratio > 0.75) & (ratio < 1.25)), (lv, e, ratio)
+        assert np.allclose(e[1:] / e[0], [0.1, 0.2, 0.025], rtol=0.02), (lv, e)
+        assert e[0] > 5 * printed(3, lv)[0]   # far above the positivity-limited error
+    eoc = np.log2(e2[0] / e3[0])
+    assert abs(eoc - 1.68) < 0.2, eoc
+
+
+def test_local_limiting_band_catches_planted_mistake(tmp_path):
+    # the entropy factor formed at the left end of each interface only (the
+    # right end keeps its pressure factor): still admissible at one end,
+    # but not the entropy bound of Eq. Bounds_Barstates at every node
+    src = open(SRC).read()
+    old = "                    if (ent) th_r = orc_theta_entropy(gm, u0, av, emin[gr], th_r);\n"
+    assert src.count(old) == 1
+    lib = oracle.compile_source(src.replace(old, "\n"), str(tmp_path / "lib_ent.so"))
+    with oracle.using(lib):
+        e = _density_wave_errors(3, 2, 1.0, limiting=2, entropy=1)
+    ratio = e / printed(3, 2, "local")
+    assert not np.all((ratio > 0.75) & (ratio < 1.25)), (e, ratio)
 
 
 def test_vortex_order_N3():
