@@ -487,3 +487,107 @@ def smooth_random_state(mesh, N, seed=0, gamma=1.4, amp=0.2, modes=3):
 def concat_states(states: Sequence[np.ndarray]) -> np.ndarray:
     """Concatenate per-simulation states [4][K_s][..] along the element axis."""
     return np.ascontiguousarray(np.concatenate(states, axis=1))
+
+
+# ----------------------------------------------------------------------------
+# 3D: conforming Cartesian grids of hexahedra
+# ----------------------------------------------------------------------------
+
+@dataclasses.dataclass
+class Grid3:
+    """A conforming nx x ny x nz grid of hexahedra over box (x0, y0, z0, x1,
+    y1, z1), boundary kinds per side (-x, +x, -y, +y, -z, +z) and the
+    Dirichlet primitive states (rho, v1, v2, v3, p) per side. Elements are
+    ordered e = (ez ny + ey) nx + ex."""
+
+    nx: int
+    ny: int
+    nz: int
+    box: tuple = (0.0, 0.0, 0.0, 1.0, 1.0, 1.0)
+    bc: tuple = (BC_PERIODIC,) * 6
+    bc_prim: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((6, 5)))
+
+    @property
+    def n_elems(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def node_coords3(grid: Grid3, N: int):
+    """x, y, z of every node, shape [K][N+1][N+1][N+1] indexed [e][k][j][i]."""
+    x0, y0, z0, x1, y1, z1 = grid.box
+    hx, hy, hz = (x1 - x0) / grid.nx, (y1 - y0) / grid.ny, (z1 - z0) / grid.nz
+    ez, ey, ex = np.meshgrid(np.arange(grid.nz), np.arange(grid.ny), np.arange(grid.nx), indexing="ij")
+    cx = (x0 + (ex.ravel() + 0.5) * hx)[:, None, None, None]
+    cy = (y0 + (ey.ravel() + 0.5) * hy)[:, None, None, None]
+    cz = (z0 + (ez.ravel() + 0.5) * hz)[:, None, None, None]
+    s = lgl_points(N)
+    shape = (grid.n_elems, N + 1, N + 1, N + 1)
+    X = np.broadcast_to(cx + 0.5 * hx * s[None, None, None, :], shape).copy()
+    Y = np.broadcast_to(cy + 0.5 * hy * s[None, None, :, None], shape).copy()
+    Z = np.broadcast_to(cz + 0.5 * hz * s[None, :, None, None], shape).copy()
+    return X, Y, Z
+
+
+def conserved3(rho, v1, v2, v3, p, gamma):
+    """Ideal-gas conserved state (rho, rho v1, rho v2, rho v3, E) on axis 0."""
+    rho = np.asarray(rho, dtype=np.float64)
+    E = p / (gamma - 1.0) + 0.5 * rho * (v1 * v1 + v2 * v2 + v3 * v3)
+    return np.ascontiguousarray(np.stack([rho, rho * v1, rho * v2, rho * v3, E * np.ones_like(rho)], axis=0))
+
+
+def density_wave3_state(grid: Grid3, N: int, t=0.0, gamma=1.4, vel=(0.1, 0.2, -0.1)):
+    """The density wave of Sec. 3.1 (Eq. entropywave2D) with a third direction:
+    rho = 2 + 0.98 sin(2 pi (x + y + z - (v1 + v2 + v3) t) / L), constant
+    velocity and p = 20 on a periodic box of side L in each direction (the
+    exact solution is the advected initial state)."""
+    X, Y, Z = node_coords3(grid, N)
+    x0, y0, z0, x1, y1, z1 = grid.box
+    L = x1 - x0
+    ph = (X - vel[0] * t) + (Y - vel[1] * t) + (Z - vel[2] * t)
+    rho = 2.0 + 0.98 * np.sin(2 * np.pi * ph / L)
+    one = np.ones_like(X)
+    return conserved3(rho, vel[0] * one, vel[1] * one, vel[2] * one, 20.0 * one, gamma)
+
+
+def random3_state(grid: Grid3, N: int, seed=0, gamma=1.4, rho_range=(0.5, 2.0), p_range=(0.5, 2.0), vmax=0.5):
+    """Seeded nodal noise: rho and p log-uniform in their ranges, velocities
+    uniform in [-vmax, vmax]."""
+    rng = np.random.default_rng(seed)
+    shape = (grid.n_elems, N + 1, N + 1, N + 1)
+    rho = np.exp(rng.uniform(np.log(rho_range[0]), np.log(rho_range[1]), shape))
+    p = np.exp(rng.uniform(np.log(p_range[0]), np.log(p_range[1]), shape))
+    v = [rng.uniform(-vmax, vmax, shape) for _ in range(3)]
+    return conserved3(rho, v[0], v[1], v[2], p, gamma)
+
+
+def blast3_state(grid: Grid3, N: int, centre=(0.5, 0.5, 0.5), r0=0.15, gamma=1.4, rho_bg=1e-3, p_bg=1e-3,
+                 rho_in=1.0, p_in=10.0):
+    """A sphere r < r0 about centre at (rho_in, p_in) in a gas at rest at
+    (rho_bg, p_bg): a 3D blast with a near-vacuum background."""
+    X, Y, Z = node_coords3(grid, N)
+    r2 = (X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2
+    inside = r2 < r0 * r0
+    rho = np.where(inside, rho_in, rho_bg)
+    p = np.where(inside, p_in, p_bg)
+    zero = np.zeros_like(X)
+    return conserved3(rho, zero, zero, zero, p, gamma)
+
+
+def slab_from_2d(u2, mesh, N: int, nz: int):
+    """A 3D state [5][nx ny nz][N+1]^3 that repeats the 2D state [4][K][N+1]^2
+    of a uniform level-0 mesh in z (v3 = 0), on the grid Grid3(mesh.nx0,
+    mesh.ny0, nz): the reduction of the 3D scheme to the 2D one. Also returns
+    for each 3D element its 2D element."""
+    nx, ny = mesh.nx0, mesh.ny0
+    src = np.asarray(u2).reshape(4, mesh.n_elems, N + 1, N + 1)
+    e2 = np.zeros(nx * ny * nz, dtype=np.int64)
+    for e in range(mesh.n_elems):
+        for ez in range(nz):
+            e2[(ez * ny + int(mesh.iy[e])) * nx + int(mesh.ix[e])] = e
+    out = np.zeros((5, nx * ny * nz, N + 1, N + 1, N + 1))
+    for k in range(N + 1):
+        out[0, :, k] = src[0][e2]
+        out[1, :, k] = src[1][e2]
+        out[2, :, k] = src[2][e2]
+        out[4, :, k] = src[3][e2]
+    return out, e2
