@@ -1,0 +1,106 @@
+/*
+ * idp_dgsem3d.h -- C ABI of the 3D IDP-limited LGL-DGSEM (arXiv 2607.06045,
+ * Sec. 2 with d = 3) on a conforming Cartesian grid of hexahedra, in the same
+ * library as idp_dgsem.h (libidpdgsem.so, CUDA, sm_103a).
+ *
+ * The method per stage: the flux-differencing volume terms of
+ * Eq. evolutionformula along x, y and z with Ranocha's two-point flux and
+ * LLF faces; the low-order graph-viscosity scheme of
+ * Eq. LowOrderScheme_globalIndices; bar-state density bounds and positivity
+ * (Eqs. Bounds_Positivity, Bounds_Barstates); Zalesak density limiting and
+ * the pressure factor with Gamma = 2d = 6 (Sec. 2.3); the IDP time step
+ * (Eq. timestep_restriction) and SSP-RK3 (Sec. 3). FP64 throughout.
+ *
+ * State layout (caller-owned device memory): u[5][K][N+1][N+1][N+1] doubles,
+ * variables (rho, rho v1, rho v2, rho v3, rho e), then element, then node
+ * (k, j, i) with the x index i fastest; elements e = (ez ny + ey) nx + ex.
+ * Degrees N = 1..4. Errors: the idp_status codes of idp_dgsem.h.
+ */
+#ifndef IDP_DGSEM3D_H
+#define IDP_DGSEM3D_H
+
+#include <stdint.h>
+
+#include "idp_dgsem.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct idp3d_ctx idp3d_ctx;
+
+/* The grid: nx x ny x nz elements over [x0,x1] x [y0,y1] x [z0,z1]; bc per
+ * side (-x, +x, -y, +y, -z, +z) one of IDP_BC_PERIODIC, IDP_BC_WALL
+ * (mirrored normal momentum), IDP_BC_DIRICHLET (the primitive state
+ * bc_prim[s] = rho, v1, v2, v3, p) or IDP_BC_OUTFLOW (copy); opposite sides
+ * are both periodic or neither. */
+typedef struct {
+    int32_t nx, ny, nz;
+    double x0, y0, z0, x1, y1, z1;
+    int32_t bc[6];
+    double bc_prim[6][5];
+} idp3d_grid_desc;
+
+/* limiting: 0 none (the high-order scheme), 1 positivity, 2 local (density
+ * bounds from the bar states, with positivity); beta the positivity factor
+ * of Eq. Bounds_Positivity (0.1); cfl the factor on the IDP time step. */
+typedef struct {
+    int32_t limiting;
+    double beta;
+    double cfl;
+} idp3d_options;
+
+/* limiting 2, beta 0.1, cfl 0.5 */
+idp_status idp3d_options_default(idp3d_options *o);
+
+/* Context for one grid and degree N (1..4); *out receives it. IDP_E_ARG for
+ * bad arguments (N, sizes, a box of non-positive extent, inconsistent
+ * periodic sides, options out of range), IDP_E_CUDA on a CUDA failure. */
+idp_status idp3d_create(const idp3d_grid_desc *grid, int32_t N, double gamma, const idp3d_options *opts,
+                        idp3d_ctx **out);
+
+/* n_elems and nodes per element (N+1)^3; either may be NULL. */
+idp_status idp3d_layout(const idp3d_ctx *ctx, int64_t *n_elems, int32_t *nodes_per_elem);
+
+/* rhs = the limited residual per unit mass of u for a stage of length dt
+ * (dt = 0: the unlimited high-order residual), device arrays in the layout
+ * above. Asynchronous on `stream`. */
+idp_status idp3d_rhs(idp3d_ctx *ctx, const double *u, double dt, double *rhs, void *stream);
+
+/* *dt_host = cfl * min_i m_i / sum_j 2 d_ij of u (Eq. timestep_restriction).
+ * Synchronises `stream`. IDP_E_NUMERIC if u holds a non-admissible state. */
+idp_status idp3d_dt(idp3d_ctx *ctx, const double *u, double *dt_host, void *stream);
+
+/* n_steps SSP-RK3 steps of u in place (device array), each with the IDP time
+ * step of its u^n; t_host (in/out) the time, dt_last_host (may be NULL) the
+ * last step's dt. The step is one CUDA graph per state pointer, launched on
+ * `stream` (the context's own stream when NULL). Synchronises. IDP_E_NUMERIC
+ * if a stage met a non-admissible input or (with statistics on) a bound
+ * violation. */
+idp_status idp3d_step(idp3d_ctx *ctx, double *u, int32_t n_steps, double *t_host, double *dt_last_host,
+                      void *stream);
+
+/* out_host[5] = sum_i m_i u_i (conservation totals), summed in a fixed order.
+ * Synchronises `stream`. */
+idp_status idp3d_integrals(idp3d_ctx *ctx, const double *u, double *out_host, void *stream);
+
+/* Statistics of the limited stages since the last call (then reset):
+ * mass-weighted mean of 1 - (the node's smallest interface factor), nodes
+ * with a factor below one, violations of the density bounds and of the
+ * pressure bound (beyond 1e-13 relative), non-admissible results, the
+ * smallest density and pressure seen, and the stage count. */
+typedef struct {
+    double alpha_mean;
+    int64_t n_active, n_viol_density, n_viol_pressure, n_nonpositive, n_stages;
+    double min_rho, min_p;
+} idp3d_stats;
+
+idp_status idp3d_limiter_stats(idp3d_ctx *ctx, idp3d_stats *out, void *stream);
+
+void idp3d_destroy(idp3d_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IDP_DGSEM3D_H */

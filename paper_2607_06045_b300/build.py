@@ -23,7 +23,7 @@ NPS = list(range(2, 9))
 
 def _sources():
     return [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h"))] + \
-        [os.path.join(ROOT, "include", "idp_dgsem.h")]
+        [os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h")]
 
 
 def _newest_source() -> float:
@@ -54,6 +54,10 @@ def build(force: bool = False, jobs: int | None = None, verbose: bool = False) -
     tasks.append((os.path.join(CSRC, "k_probe.cu"), os.path.join(BUILD, "k_probe.o"), []))
     tasks.append((os.path.join(CSRC, "k_noalloc.cu"), os.path.join(BUILD, "k_noalloc.o"), []))
     tasks.append((os.path.join(CSRC, "k_remesh.cu"), os.path.join(BUILD, "k_remesh.o"), []))
+    # 3D (N = 1..4): one translation unit per degree, and its host runtime
+    tasks += [(os.path.join(CSRC, "k_inst3d.cu"), os.path.join(BUILD, f"k3d_np{n}.o"), [f"-DIDP3_NP={n}"])
+              for n in (2, 3, 4, 5)]
+    tasks.append((os.path.join(CSRC, "idp3d_host.cu"), os.path.join(BUILD, "idp3d_host.o"), []))
     jobs = jobs or min(len(tasks), os.cpu_count() or 4)
     with cf.ThreadPoolExecutor(jobs) as ex:
         objs = list(ex.map(_compile, tasks))

@@ -1,0 +1,27 @@
+// idp3d_launch.h -- the per-degree launcher table of the 3D kernels
+// (instantiated in k_inst3d.cu, one translation unit per N + 1).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "idp3d.cuh"
+
+namespace idp3 {
+
+struct Launchers3 {
+    int np = 0, epb = 0, threads = 0;
+    size_t smem = 0;   // dynamic shared memory of one element-kernel block
+    cudaError_t (*prepare)() = nullptr;
+    void (*element)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) = nullptr;
+    void (*dt)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
+               unsigned long long *dtmin, unsigned *status) = nullptr;
+};
+
+Launchers3 launchers3_np2();
+Launchers3 launchers3_np3();
+Launchers3 launchers3_np4();
+Launchers3 launchers3_np5();
+
+}  // namespace idp3

@@ -483,6 +483,17 @@ void host_lgl_weights(int N, double *w) {
     double x[NPMAX];
     lgl_nodes(N, x, w);
 }
+
+// LGL nodes and weights and Sbar (row-major, (N+1)^2) for degree N (the 3D
+// contexts), the operators the 2D contexts use
+void host_lgl_sbar(int N, double *x, double *w, double *S) {
+    Ops o;
+    build_ops(N, 1, 0, o);
+    const int np = N + 1;
+    for (int i = 0; i < np; ++i) { x[i] = o.xi[i]; w[i] = o.w[i]; }
+    for (int i = 0; i < np; ++i)
+        for (int j = 0; j < np; ++j) S[i * np + j] = o.S[i][j];
+}
 }  // namespace idp
 
 // ---------------------------------------------------------------------------

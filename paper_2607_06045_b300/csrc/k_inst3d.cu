@@ -1,0 +1,48 @@
+// k_inst3d.cu -- the 3D kernels of one polynomial degree (IDP3_NP = N + 1 on
+// the compiler command line) behind a launcher table.
+#include "idp3d_launch.h"
+
+#ifndef IDP3_NP
+#error "IDP3_NP must be defined"
+#endif
+
+#define IDP3_CAT2(a, b) a##b
+#define IDP3_CAT(a, b) IDP3_CAT2(a, b)
+
+namespace idp3 {
+namespace {
+
+constexpr int NP = IDP3_NP;
+// elements per block: about 128 threads, one per node
+constexpr int EPB = NP == 2 ? 16 : (NP == 3 ? 4 : (NP == 4 ? 2 : 1));
+using L3 = Launch3<NP, EPB>;
+
+cudaError_t prepare() {
+    return cudaFuncSetAttribute(k_element3d<NP, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(Sm3<NP>) * EPB));
+}
+
+void element(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) {
+    k_element3d<NP, EPB><<<grid, L3::threads, sizeof(Sm3<NP>) * EPB, st>>>(G, ops, A);
+}
+
+void dt(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
+        unsigned long long *dtmin, unsigned *status) {
+    k_dt3d<NP, EPB><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status);
+}
+
+}  // namespace
+
+Launchers3 IDP3_CAT(launchers3_np, IDP3_NP)() {
+    Launchers3 L;
+    L.np = NP;
+    L.epb = EPB;
+    L.threads = L3::threads;
+    L.smem = sizeof(Sm3<NP>) * EPB;
+    L.prepare = prepare;
+    L.element = element;
+    L.dt = dt;
+    return L;
+}
+
+}  // namespace idp3

@@ -65,6 +65,30 @@ EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", 
            "idp_amr_transfer", "idp_dgsem_adapt", "idp_dgsem_leaves", "idp_dgsem_mesh_tables"]
 
 
+EXPORTS3 = ["idp3d_options_default", "idp3d_create", "idp3d_layout", "idp3d_rhs", "idp3d_dt", "idp3d_step",
+            "idp3d_integrals", "idp3d_limiter_stats", "idp3d_destroy"]
+
+
+class GridDesc3(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32),
+                ("x0", C.c_double), ("y0", C.c_double), ("z0", C.c_double),
+                ("x1", C.c_double), ("y1", C.c_double), ("z1", C.c_double),
+                ("bc", C.c_int32 * 6), ("bc_prim", (C.c_double * 5) * 6)]
+
+
+class Options3(C.Structure):
+    _fields_ = [("limiting", C.c_int32), ("beta", C.c_double), ("cfl", C.c_double)]
+
+
+class LimiterStats3(C.Structure):
+    _fields_ = [("alpha_mean", C.c_double), ("n_active", C.c_int64), ("n_viol_density", C.c_int64),
+                ("n_viol_pressure", C.c_int64), ("n_nonpositive", C.c_int64), ("n_stages", C.c_int64),
+                ("min_rho", C.c_double), ("min_p", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 def lib():
     """Load the CUDA library (raises if it has not been built)."""
     global _lib
@@ -109,6 +133,19 @@ def lib():
         L.idp_dgsem_adapt.argtypes = [vp, vp, C.POINTER(AmrParams), vp, C.c_int64, i64p, i64p, vp]
         L.idp_dgsem_leaves.argtypes = [vp, i8p, ip, ip]
         L.idp_dgsem_mesh_tables.argtypes = [vp, i64p, ip, C.POINTER(C.c_uint8), ip, ip, ip, ip, ip, ip, ip, ip]
+        L.idp3d_options_default.argtypes = [C.POINTER(Options3)]
+        L.idp3d_create.argtypes = [C.POINTER(GridDesc3), C.c_int32, C.c_double, C.POINTER(Options3), C.POINTER(vp)]
+        L.idp3d_layout.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        L.idp3d_rhs.argtypes = [vp, vp, C.c_double, vp, vp]
+        L.idp3d_dt.argtypes = [vp, vp, dp, vp]
+        L.idp3d_step.argtypes = [vp, vp, C.c_int32, dp, dp, vp]
+        L.idp3d_integrals.argtypes = [vp, vp, dp, vp]
+        L.idp3d_limiter_stats.argtypes = [vp, C.POINTER(LimiterStats3), vp]
+        L.idp3d_destroy.argtypes = [vp]
+        L.idp3d_destroy.restype = None
+        for f in EXPORTS3:
+            if f != "idp3d_destroy":
+                getattr(L, f).restype = C.c_int
         L.idp_dgsem_destroy.restype = None
         for f in EXPORTS:
             if f not in ("idp_dgsem_destroy", "idp_status_str", "idp_last_cuda_error"):
@@ -495,3 +532,81 @@ def idp_amr_transfer(N, gamma, u_old, kind, src, zs_threshold=1e-10, stream=None
                                   kind.ctypes.data_as(ip), src.ctypes.data_as(ip), float(zs_threshold), C.byref(sc),
                                   _stream(stream)), "idp_amr_transfer")
     return un, sc.value
+
+
+# ---- 3D (include/idp_dgsem3d.h) ----------------------------------------------
+
+def options3(**kw) -> Options3:
+    o = Options3()
+    lib().idp3d_options_default(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+class Context3D:
+    """idp3d context for a conforming grid of hexahedra (a workloads.Grid3-like
+    object: nx, ny, nz, box, bc, bc_prim) and degree N (1..4)."""
+
+    def __init__(self, grid, N: int, gamma: float = 1.4, opts: Optional[Options3] = None, **kw):
+        if opts is None:
+            opts = options3(**kw)
+        self.grid, self.N, self.np, self.gamma, self.opts = grid, N, N + 1, gamma, opts
+        d = GridDesc3()
+        d.nx, d.ny, d.nz = grid.nx, grid.ny, grid.nz
+        d.x0, d.y0, d.z0, d.x1, d.y1, d.z1 = (float(v) for v in grid.box)
+        for s in range(6):
+            d.bc[s] = int(grid.bc[s])
+            for v in range(5):
+                d.bc_prim[s][v] = float(np.asarray(grid.bc_prim)[s, v])
+        h = C.c_void_p()
+        _check(lib().idp3d_create(C.byref(d), N, gamma, C.byref(opts), C.byref(h)), "idp3d_create")
+        self._h = h
+        K, npe = C.c_int64(), C.c_int32()
+        lib().idp3d_layout(h, C.byref(K), C.byref(npe))
+        self.K, self.nodes_per_elem = K.value, npe.value
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().idp3d_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self):
+        return (5, self.K, self.np, self.np, self.np)
+
+    def idp3d_rhs(self, u, dt, out, stream=None):
+        _check(lib().idp3d_rhs(self._h, _ptr(u), float(dt), _ptr(out), _stream(stream)), "idp3d_rhs")
+
+    def idp3d_dt(self, u, stream=None):
+        dt = C.c_double()
+        _check(lib().idp3d_dt(self._h, _ptr(u), C.byref(dt), _stream(stream)), "idp3d_dt")
+        return dt.value
+
+    def idp3d_step(self, u, n_steps, t, stream=None, check=True):
+        """n_steps steps in place; t is a length-1 numpy array (updated)."""
+        tt = np.ascontiguousarray(t, dtype=np.float64)
+        dl = C.c_double()
+        rc = lib().idp3d_step(self._h, _ptr(u), int(n_steps), tt.ctypes.data_as(C.POINTER(C.c_double)),
+                              C.byref(dl), C.c_void_p(stream) if stream is not None else None)
+        t[...] = tt
+        if check:
+            _check(rc, "idp3d_step")
+        return rc, dl.value
+
+    def idp3d_integrals(self, u, stream=None):
+        out = np.zeros(5)
+        _check(lib().idp3d_integrals(self._h, _ptr(u), out.ctypes.data_as(C.POINTER(C.c_double)),
+                                     _stream(stream)), "idp3d_integrals")
+        return out
+
+    def idp3d_limiter_stats(self, stream=None):
+        st = LimiterStats3()
+        rc = lib().idp3d_limiter_stats(self._h, C.byref(st), _stream(stream))
+        return rc, st.as_dict()

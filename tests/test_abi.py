@@ -18,10 +18,10 @@ def built():
     build.build()
 
 
-def header_functions():
-    src = open(os.path.join(ROOT, "include", "idp_dgsem.h")).read()
+def header_functions(name="idp_dgsem.h"):
+    src = open(os.path.join(ROOT, "include", name)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(idp_\w+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(idp\w*_\w+)\s*\(", src)))
 
 
 def test_exports_every_declared_symbol():
@@ -31,6 +31,12 @@ def test_exports_every_declared_symbol():
     for n in names:
         assert hasattr(L, n), n
     assert set(names) == set(idp.EXPORTS)
+    names3 = header_functions("idp_dgsem3d.h")
+    for n in names3:
+        assert hasattr(L, n), n
+    assert set(names3) == set(idp.EXPORTS3)
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert headers == ["idp_dgsem.h", "idp_dgsem3d.h"]
 
 
 def test_launch_config_rejects_null_context():

@@ -1,0 +1,165 @@
+"""GPU parity of the 3D path (include/idp_dgsem3d.h) against the 3D oracle
+(oracle/o3d.py) on the same seeded inputs, through the C ABI.
+
+Tolerances: right-hand sides (unlimited and limited) 1e-12 relative to the
+residual scale max|u_v| / dt_idp, as in 2D; the time step 1e-13; SSP-RK3
+steps 1e-10 relative to max|u_v| after 20 steps.
+"""
+import numpy as np
+import pytest
+
+from oracle import o3d
+from paper_2607_06045_b300 import build, idp
+from paper_2607_06045_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+G = 1.4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    build.build()
+    yield
+
+
+def dev(u):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(u)).cuda()
+
+
+def grid(kind, n=(3, 2, 4)):
+    if kind == "periodic":
+        return W.Grid3(*n, box=(0.0, 0.0, 0.0, 0.9, 0.6, 1.2))
+    if kind == "walls":
+        return W.Grid3(*n, box=(0.0, 0.0, 0.0, 0.9, 0.6, 1.2),
+                       bc=(o3d.BC_WALL, o3d.BC_WALL, o3d.BC_OUTFLOW, o3d.BC_OUTFLOW, o3d.BC_PERIODIC, o3d.BC_PERIODIC))
+    bcp = np.zeros((6, 5))
+    bcp[:] = [1.2, 0.3, -0.2, 0.1, 1.5]
+    return W.Grid3(*n, box=(0.0, 0.0, 0.0, 0.9, 0.6, 1.2),
+                   bc=(o3d.BC_DIRICHLET, o3d.BC_OUTFLOW, o3d.BC_WALL, o3d.BC_DIRICHLET, o3d.BC_OUTFLOW, o3d.BC_WALL),
+                   bc_prim=bcp)
+
+
+def gpu_rhs(ctx, u, dt):
+    import torch
+    ud = dev(u)
+    out = torch.empty_like(ud)
+    ctx.idp3d_rhs(ud, dt, out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def scale(u, dt_idp):
+    return np.abs(u).reshape(5, -1).max(axis=1) / dt_idp
+
+
+def rel(a, b, sc):
+    return float((np.abs(np.asarray(a) - np.asarray(b)).reshape(5, -1).max(axis=1) / sc).max())
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind", ["periodic", "walls", "dirichlet"])
+def test_rhs(N, kind):
+    g = grid(kind)
+    u = W.random3_state(g, N, seed=10 * N + len(kind), rho_range=(0.3, 3.0), p_range=(0.3, 3.0), vmax=1.0)
+    o = o3d.Oracle3D(g, N)
+    dt_idp = o.dt(u, cfl=1.0)
+    sc = scale(u, dt_idp)
+    for lim in (0, 1, 2):
+        ctx = idp.Context3D(g, N, limiting=lim)
+        dt = 0.0 if lim == 0 else 0.5 * dt_idp
+        r_o = o.rhs(u, dt=dt, limiting=lim)
+        r_g = gpu_rhs(ctx, u, dt)
+        e = rel(r_g, r_o, sc)
+        assert e <= 1e-12, (lim, e)
+        ctx.close()
+
+
+@pytest.mark.parametrize("N", [1, 3])
+def test_dt(N):
+    g = grid("dirichlet")
+    u = W.random3_state(g, N, seed=3)
+    o = o3d.Oracle3D(g, N)
+    ctx = idp.Context3D(g, N, cfl=0.7)
+    d_g = ctx.idp3d_dt(dev(u))
+    d_o = o.dt(u, cfl=0.7)
+    assert abs(d_g - d_o) <= 1e-13 * d_o
+    ctx.close()
+
+
+@pytest.mark.parametrize("N,lim", [(2, 2), (3, 1), (3, 2), (4, 2)])
+def test_steps(N, lim):
+    import torch
+    g = grid("walls", n=(3, 3, 2))
+    u = W.random3_state(g, N, seed=N, rho_range=(0.5, 2.0), p_range=(0.5, 2.0), vmax=0.5)
+    o = o3d.Oracle3D(g, N)
+    u_o, t_o, _, st_o = o.step(u, 20, cfl=0.5, limiting=lim)
+    ctx = idp.Context3D(g, N, limiting=lim, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    rc, _ = ctx.idp3d_step(ud, 20, t)
+    assert rc == idp.IDP_OK
+    torch.cuda.synchronize()
+    sc = np.abs(u_o).reshape(5, -1).max(axis=1)
+    err = (np.abs(ud.cpu().numpy() - u_o).reshape(5, -1).max(axis=1) / sc).max()
+    assert err <= 1e-10, err
+    assert abs(t[0] - t_o) <= 1e-12 * t_o
+    rc, st = ctx.idp3d_limiter_stats()
+    assert rc == idp.IDP_OK
+    assert st["n_viol_density"] == 0 and st["n_viol_pressure"] == 0 and st["n_nonpositive"] == 0
+    assert st["n_stages"] == 60
+    ctx.close()
+
+
+def test_conservation_and_blast_positivity():
+    import torch
+    N = 3
+    g = W.Grid3(6, 6, 6)
+    u = W.blast3_state(g, N, rho_bg=1e-5, p_bg=1e-6, rho_in=1.0, p_in=1e2)
+    ctx = idp.Context3D(g, N, limiting=1, cfl=0.9)
+    ud = dev(u)
+    I0 = ctx.idp3d_integrals(ud)
+    t = np.zeros(1)
+    rc, _ = ctx.idp3d_step(ud, 40, t)
+    assert rc == idp.IDP_OK
+    I1 = ctx.idp3d_integrals(ud)
+    assert np.abs(I1 - I0).max() <= 1e-12 * np.abs(I0).max()
+    q = ud.cpu().numpy().reshape(5, -1)
+    p = (G - 1.0) * (q[4] - 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / q[0])
+    assert q[0].min() > 0.0 and p.min() > 0.0
+    rc, st = ctx.idp3d_limiter_stats()
+    assert st["n_nonpositive"] == 0 and st["n_viol_pressure"] == 0 and st["n_active"] > 0
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+def test_larger_grid_one_step():
+    """16 x 16 x 8 elements at N = 3 (131k nodes, several element blocks per
+    SM): one SSP-RK3 step against the oracle."""
+    import torch
+    N = 3
+    g = W.Grid3(16, 16, 8, box=(0.0, 0.0, 0.0, 2.0, 2.0, 1.0))
+    u = W.random3_state(g, N, seed=21, rho_range=(0.5, 2.0), p_range=(0.5, 2.0), vmax=0.5)
+    o = o3d.Oracle3D(g, N)
+    u_o, t_o, _, _ = o.step(u, 1, cfl=0.5, limiting=2)
+    ctx = idp.Context3D(g, N, limiting=2, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    ctx.idp3d_step(ud, 1, t)
+    torch.cuda.synchronize()
+    sc = np.abs(u_o).reshape(5, -1).max(axis=1)
+    err = (np.abs(ud.cpu().numpy() - u_o).reshape(5, -1).max(axis=1) / sc).max()
+    assert err <= 1e-12, err
+    ctx.close()
+
+
+def test_bad_arguments():
+    g = W.Grid3(2, 2, 2)
+    with pytest.raises(idp.IdpError):
+        idp.Context3D(g, 5)
+    bad = W.Grid3(2, 2, 2, bc=(o3d.BC_PERIODIC, o3d.BC_WALL) + (o3d.BC_PERIODIC,) * 4)
+    with pytest.raises(idp.IdpError):
+        idp.Context3D(bad, 2)
