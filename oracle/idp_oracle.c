@@ -105,12 +105,14 @@ enum { ROW_OTHER = 0, ROW_NODE_PREP, ROW_VOLUME_FLUX, ROW_SUBCELL_FV, ROW_FACE_F
        ROW_STATS /* statistics and violation counts, not part of the method */, ROW_COUNT };
 enum { PF_PRESSURE = 1, PF_VELOCITY, PF_BETA, PF_SOUND, PF_WAVE, PF_FLUX, PF_LOGMEAN, PF_RANOCHA,
        PF_CHANDRASHEKAR, PF_LLF, PF_ETA, PF_BAR };
+#define ORC_ROWS_DEFINED 1
 #ifndef ORC_ROW
 #define ORC_ROW(r) ((void)0)
 #define ORC_PURE(...) ((void)0)
 #define ORC_PURE_PAIR(...) ((void)0)
 #define ORC_PURE2(...) ((void)0)
 #define ORC_TAG(q, g) ((void)0)
+#define ORC_TAG_N(q, g, n) ((void)0)
 #define ORC_SCOPE(u, t) ((void)0)
 #define ORC_CONST(x) ((void)0)
 #endif

@@ -44,11 +44,35 @@ void orc_operators(int N, int proj, double *xi, double *w, double *D, double *S,
                    double *wt, double *Iint, double *P);
 double orc_logmean(double a, double b);
 
+/* Work accounting hooks, as in idp_oracle.c (the op-counting build defines
+   them; here they do nothing): ORC_ROW(r) attributes the following
+   arithmetic to a step of the hot path, ORC_PURE* make a pure function count
+   once per distinct evaluation on solution nodes (ORC_TAG_N identifies a
+   state as node g), ORC_SCOPE opens one stage's accounting and ORC_CONST
+   marks the time step as a constant of the stages. */
+#ifndef ORC_ROWS_DEFINED
+enum { ROW_OTHER = 0, ROW_NODE_PREP, ROW_VOLUME_FLUX, ROW_SUBCELL_FV, ROW_FACE_FLUX, ROW_MORTAR_FLUX,
+       ROW_LOW_UPDATE, ROW_BOUNDS, ROW_VOLUME_LIMIT, ROW_MORTAR_LIMIT, ROW_STAGE, ROW_DT,
+       ROW_REFORM, ROW_STATS, ROW_COUNT };
+enum { PF_PRESSURE = 1, PF_VELOCITY, PF_BETA, PF_SOUND, PF_WAVE, PF_FLUX, PF_LOGMEAN, PF_RANOCHA,
+       PF_CHANDRASHEKAR, PF_LLF, PF_ETA, PF_BAR };
+#endif
+#ifndef ORC_ROW
+#define ORC_ROW(r) ((void)0)
+#define ORC_PURE(...) ((void)0)
+#define ORC_PURE_PAIR(...) ((void)0)
+#define ORC_PURE2(...) ((void)0)
+#define ORC_TAG_N(q, g, n) ((void)0)
+#define ORC_SCOPE(u, t) ((void)0)
+#define ORC_CONST(x) ((void)0)
+#endif
+
 enum { B3_PERIODIC = 0, B3_WALL = 1, B3_DIRICHLET = 2, B3_OUTFLOW = 3 };
 enum { S3_AVOL_M = 0, S3_M, S3_NVOL, S3_VRHO, S3_VP, S3_NONPOS, S3_DTX, S3_MINRHO, S3_MINP, S3_N };
 
 typedef struct {
     int j;            /* neighbour node, or -1-q for ghost q */
+    int face;         /* 1: across an element face, 0: a subcell neighbour */
     double c[3];      /* c_(i,j) */
 } o3_nb;
 
@@ -65,17 +89,43 @@ typedef struct {
     int *g_side;      /* and the side */
 } o3_ctx;
 
+#ifdef ORC_COUNTING
+static void o3_count_node_prep(const o3_ctx *c, const double *u);
+#endif
+
 /* ------------------------------------------------------------------------ */
 /* Euler physics in 3D                                                       */
 /* ------------------------------------------------------------------------ */
 
 static double pressure3(double g, const double *u) {
+    ORC_PURE(PF_PRESSURE, u);
     return (g - 1.0) * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
+}
+
+/* velocity v = m / rho */
+static void velocity3(const double *u, double *v) {
+    ORC_PURE(PF_VELOCITY, u);
+    for (int a = 0; a < 3; ++a) v[a] = u[1 + a] / u[0];
+}
+
+/* rho / p */
+static double beta3(double g, const double *u) {
+    ORC_PURE(PF_BETA, u);
+    return u[0] / pressure3(g, u);
+}
+
+/* speed of sound sqrt(gamma p / rho) */
+static double sound3(double g, const double *u) {
+    ORC_PURE(PF_SOUND, u);
+    return sqrt(g * pressure3(g, u) / u[0]);
 }
 
 /* physical flux along axis d (0 x, 1 y, 2 z) */
 static void flux3(double g, const double *u, int d, double *f) {
-    double p = pressure3(g, u), vn = u[1 + d] / u[0];
+    ORC_PURE(PF_FLUX, u, d);
+    double v[3], p = pressure3(g, u);
+    velocity3(u, v);
+    double vn = v[d];
     f[0] = u[0] * vn;
     for (int a = 0; a < 3; ++a) f[1 + a] = u[1 + a] * vn + (a == d ? p : 0.0);
     f[4] = (u[4] + p) * vn;
@@ -83,7 +133,10 @@ static void flux3(double g, const double *u, int d, double *f) {
 
 /* |v_d| + c */
 static double wave3(double g, const double *u, int d) {
-    return fabs(u[1 + d] / u[0]) + sqrt(g * pressure3(g, u) / u[0]);
+    ORC_PURE(PF_WAVE, u, d);
+    double v[3];
+    velocity3(u, v);
+    return fabs(v[d]) + sound3(g, u);
 }
 
 /* R3: Davis estimate along axis d */
@@ -94,6 +147,7 @@ static double lambda3(double g, const double *a, const double *b, int d) {
 
 /* LLF flux along axis d, left state first */
 void o3_llf(double g, const double *uL, const double *uR, int d, double *f) {
+    ORC_PURE2(PF_LLF, uL, uR, d);
     double fL[NV], fR[NV];
     flux3(g, uL, d, fL);
     flux3(g, uR, d, fR);
@@ -105,11 +159,13 @@ void o3_llf(double g, const double *uL, const double *uR, int d, double *f) {
    f_rho = {rho}_ln {v_d}, f_m = f_rho {v} + {p} e_d,
    f_E = f_rho (v_L . v_R / 2 + 1 / ((gamma - 1) {rho/p}_ln)) + (p_L v_d,R + p_R v_d,L) / 2 */
 void o3_ranocha(double g, const double *uL, const double *uR, int d, double *f) {
+    ORC_PURE_PAIR(PF_RANOCHA, uL, uR, d);
     double vL[3], vR[3];
-    for (int a = 0; a < 3; ++a) { vL[a] = uL[1 + a] / uL[0]; vR[a] = uR[1 + a] / uR[0]; }
+    velocity3(uL, vL);
+    velocity3(uR, vR);
     double pL = pressure3(g, uL), pR = pressure3(g, uR);
     double rho_ln = orc_logmean(uL[0], uR[0]);
-    double bet_ln = orc_logmean(uL[0] / pL, uR[0] / pR);
+    double bet_ln = orc_logmean(beta3(g, uL), beta3(g, uR));
     double vdot = vL[0] * vR[0] + vL[1] * vR[1] + vL[2] * vR[2];
     double fr = rho_ln * 0.5 * (vL[d] + vR[d]);
     f[0] = fr;
@@ -117,16 +173,19 @@ void o3_ranocha(double g, const double *uL, const double *uR, int d, double *f) 
     f[4] = fr * (0.5 * vdot + 1.0 / ((g - 1.0) * bet_ln)) + 0.5 * (pL * vR[d] + pR * vL[d]);
 }
 
-/* Bar state of the pair (i, j) with c_ij along an axis (Eq. barstateform):
-   ubar = (u_i + u_j)/2 - c_ij . (f(u_j) - f(u_i)) / (2 d_ij), d_ij = |c_ij| lambda_ij */
-static void bar_state3(double g, const double *ui, const double *uj, const double *cij, double *ub) {
+/* Density of the bar state of the pair (i, j) with c_ij along an axis
+   (Eq. barstateform): rhobar = (rho_i + rho_j)/2 - c_ij . (f_rho(u_j) -
+   f_rho(u_i)) / (2 d_ij), d_ij = |c_ij| lambda_ij (the density bounds need
+   the density alone) */
+static double bar_rho3(double g, const double *ui, const double *uj, const double *cij) {
+    ORC_PURE_PAIR(PF_BAR, ui, uj, cij[0], cij[1], cij[2]);
     int d = cij[0] != 0.0 ? 0 : (cij[1] != 0.0 ? 1 : 2);
     double cn = cij[d], nrm = fabs(cn);
     double dd = nrm * lambda3(g, ui, uj, d);
     double fi[NV], fj[NV];
     flux3(g, ui, d, fi);
     flux3(g, uj, d, fj);
-    for (int v = 0; v < NV; ++v) ub[v] = 0.5 * (ui[v] + uj[v]) - cn * (fj[v] - fi[v]) / (2.0 * dd);
+    return 0.5 * (ui[0] + uj[0]) - cn * (fj[0] - fi[0]) / (2.0 * dd);
 }
 
 /* R8 with 5 variables: the largest theta <= hi with rho(u0 + theta a) > 0
@@ -179,10 +238,10 @@ double o3_theta(double g, const double *u0, const double *a, double pmin, double
 
 static int g3(const o3_ctx *c, int e, int i, int j, int k) { return ((e * c->np + k) * c->np + j) * c->np + i; }
 
-static void push3(o3_nb **buf, int *n, int *cap, int j, int d, double cd) {
+static void push3(o3_nb **buf, int *n, int *cap, int j, int d, double cd, int face) {
     if (*n == *cap) { *cap = *cap ? 2 * *cap : 4096; *buf = realloc(*buf, sizeof(o3_nb) * (*cap)); }
     o3_nb *b = &(*buf)[*n];
-    b->j = j; b->c[0] = b->c[1] = b->c[2] = 0.0; b->c[d] = cd;
+    b->j = j; b->face = face; b->c[0] = b->c[1] = b->c[2] = 0.0; b->c[d] = cd;
     ++*n;
 }
 
@@ -236,11 +295,11 @@ o3_ctx *o3_create(int N, double gamma, int nx, int ny, int nz, const double *box
                 /* subcell neighbours (Sec. 2.1) */
                 if (pos > 0) {
                     int q[3] = {i, j, k}; q[d] -= 1;
-                    push3(&buf, &cnt, &cap, g3(c, e, q[0], q[1], q[2]), d, -cd);
+                    push3(&buf, &cnt, &cap, g3(c, e, q[0], q[1], q[2]), d, -cd, 0);
                 }
                 if (pos < N) {
                     int q[3] = {i, j, k}; q[d] += 1;
-                    push3(&buf, &cnt, &cap, g3(c, e, q[0], q[1], q[2]), d, cd);
+                    push3(&buf, &cnt, &cap, g3(c, e, q[0], q[1], q[2]), d, cd, 0);
                 }
                 /* face neighbours: the matching node of the element across */
                 for (int side = 0; side < 2; ++side) {
@@ -252,14 +311,14 @@ o3_ctx *o3_create(int N, double gamma, int nx, int ny, int nz, const double *box
                     double cs = side == 0 ? -cd : cd;
                     if (out && bc[s] != B3_PERIODIC) {
                         c->g_node[c->ng] = g; c->g_side[c->ng] = s;
-                        push3(&buf, &cnt, &cap, -1 - c->ng, d, cs);
+                        push3(&buf, &cnt, &cap, -1 - c->ng, d, cs, 1);
                         c->ng++;
                         continue;
                     }
                     nc[d] = (nc[d] + en[d]) % en[d];
                     int f = (nc[2] * ny + nc[1]) * nx + nc[0];
                     int q[3] = {i, j, k}; q[d] = side == 0 ? N : 0;
-                    push3(&buf, &cnt, &cap, g3(c, f, q[0], q[1], q[2]), d, cs);
+                    push3(&buf, &cnt, &cap, g3(c, f, q[0], q[1], q[2]), d, cs, 1);
                 }
             }
         }
@@ -278,6 +337,7 @@ static double mass3(const o3_ctx *c, int g) {
 
 static void get3(const o3_ctx *c, const double *u, int g, double *q) {
     for (int v = 0; v < NV; ++v) q[v] = u[(size_t)v * c->nn + g];
+    ORC_TAG_N(q, g, NV);
 }
 
 static void prim_cons3(double g, const double *w, double *q) {
@@ -384,6 +444,7 @@ static void fv_residual3(const o3_ctx *c, const double *u, double *res, double *
         for (int b = c->nb_off[i]; b < c->nb_off[i + 1]; ++b) {
             const o3_nb *nb = &c->nb[b];
             int d = nb->c[0] != 0.0 ? 0 : (nb->c[1] != 0.0 ? 1 : 2);
+            ORC_ROW(nb->face ? ROW_FACE_FLUX : ROW_SUBCELL_FV);
             double uj[NV], f[NV];
             node_or_ghost3(c, u, nb->j, uj);
             flux3(g, uj, d, f);
@@ -398,11 +459,21 @@ static void fv_residual3(const o3_ctx *c, const double *u, double *res, double *
 
 /* IDP time step (Eq. timestep_restriction): cfl * min_i m_i / sum_j 2 d_ij */
 double o3_dt(const o3_ctx *c, const double *u, double cfl) {
+    ORC_SCOPE(u, 0.0);
+    ORC_ROW(ROW_DT);
     double best = INFINITY;
-    double *res = malloc(sizeof(double) * NV * (size_t)c->nn), *ds = malloc(sizeof(double) * c->nn);
-    fv_residual3(c, u, res, ds);
-    for (int i = 0; i < c->nn; ++i) { double t = mass3(c, i) / ds[i]; if (t < best) best = t; }
-    free(res); free(ds);
+    for (int i = 0; i < c->nn; ++i) {
+        double ui[NV], uj[NV], s2d = 0.0;
+        get3(c, u, i, ui);
+        for (int b = c->nb_off[i]; b < c->nb_off[i + 1]; ++b) {
+            const o3_nb *nb = &c->nb[b];
+            int d = nb->c[0] != 0.0 ? 0 : (nb->c[1] != 0.0 ? 1 : 2);
+            node_or_ghost3(c, u, nb->j, uj);
+            s2d += 2.0 * (fabs(nb->c[d]) * lambda3(c->gamma, ui, uj, d));
+        }
+        double t = mass3(c, i) / s2d;
+        if (t < best) best = t;
+    }
     return cfl * best;
 }
 
@@ -431,6 +502,10 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
              double *utilde, double *stats) {
     int np = c->np, nn = c->nn, K = c->K, N = c->N;
     double gm = c->gamma;
+    ORC_SCOPE(u, 0.0);
+#ifdef ORC_COUNTING
+    o3_count_node_prep(c, u);
+#endif
     double *rdg = malloc(sizeof(double) * NV * (size_t)nn);
     if (dt == 0.0 || limiting == 0) {
         dg_residual3(c, u, rdg);
@@ -444,6 +519,7 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
     double *rfv = malloc(sizeof(double) * NV * (size_t)nn), *ds = malloc(sizeof(double) * nn);
     fv_residual3(c, u, rfv, ds);
     double *ufv = malloc(sizeof(double) * NV * (size_t)nn);
+    ORC_ROW(ROW_LOW_UPDATE);
     for (int i = 0; i < nn; ++i) {
         double m = mass3(c, i);
         for (int v = 0; v < NV; ++v) ufv[(size_t)v * nn + i] = u[(size_t)v * nn + i] + dt / m * rfv[(size_t)v * nn + i];
@@ -452,17 +528,18 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
     /* bounds (R6): bar states of every graph neighbour, the node itself
        included; positivity bounds beta rho_FV, beta p_FV */
     double *rmin = malloc(sizeof(double) * nn), *rmax = malloc(sizeof(double) * nn), *pmin = malloc(sizeof(double) * nn);
+    ORC_ROW(ROW_BOUNDS);
     for (int i = 0; i < nn; ++i) {
         double ui[NV], q[NV];
         get3(c, u, i, ui);
         for (int v = 0; v < NV; ++v) q[v] = ufv[(size_t)v * nn + i];
         double lo = ui[0], hi = ui[0];
         for (int b = c->nb_off[i]; b < c->nb_off[i + 1]; ++b) {
-            double uj[NV], ub[NV];
+            double uj[NV];
             node_or_ghost3(c, u, c->nb[b].j, uj);
-            bar_state3(gm, ui, uj, c->nb[b].c, ub);
-            if (ub[0] < lo) lo = ub[0];
-            if (ub[0] > hi) hi = ub[0];
+            double rb = bar_rho3(gm, ui, uj, c->nb[b].c);
+            if (rb < lo) lo = rb;
+            if (rb > hi) hi = rb;
         }
         if (limiting >= 2) { rmin[i] = lo > beta * q[0] ? lo : beta * q[0]; rmax[i] = hi; }
         else { rmin[i] = beta * q[0]; rmax[i] = INFINITY; }
@@ -481,12 +558,16 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
                 int idx[3];
                 idx[d] = 0; idx[(d + 1) % 3] = t1; idx[(d + 2) % 3] = t2;
                 double fh[NP3][NV];
+                ORC_ROW(ROW_VOLUME_FLUX);
                 dg_subcell_row3(c, u, e, d, idx, fh);
                 double wt = c->w[t1] * c->w[t2], cc = wt * area[d] / 2.0;
                 for (int a = 0; a < N; ++a) {
                     int ql[3] = {idx[0], idx[1], idx[2]}, qr[3] = {idx[0], idx[1], idx[2]};
                     ql[d] = a; qr[d] = a + 1;
                     double ul[NV], ur[NV], fl[NV], fr[NV];
+                    /* the low-order subcell flux again (the graph form above
+                       carries the same terms: not counted twice) */
+                    ORC_ROW(ROW_REFORM);
                     get3(c, u, g3(c, e, ql[0], ql[1], ql[2]), ul);
                     get3(c, u, g3(c, e, qr[0], qr[1], qr[2]), ur);
                     flux3(gm, ul, d, fl);
@@ -495,11 +576,14 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
                     int id = iface3(c, e, d, idx, a);
                     for (int v = 0; v < NV; ++v) {
                         double ffv = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
+                        ORC_ROW(ROW_VOLUME_LIMIT);
                         A[(size_t)NV * id + v] = wt * fh[a][v] - ffv;
+                        ORC_ROW(ROW_REFORM);
                     }
                 }
             }
     /* R15 exemption, then Zalesak (R7) */
+    ORC_ROW(ROW_VOLUME_LIMIT);
     char *exempt = malloc(nif);
     for (int e = 0; e < K; ++e)
         for (int d = 0; d < 3; ++d)
@@ -582,6 +666,7 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
         int e = i / (np * np * np), rr = i % (np * np * np);
         int idx[3] = {rr % np, (rr / np) % np, rr / (np * np)};
         double s[NV] = {0, 0, 0, 0, 0};
+        ORC_ROW(ROW_VOLUME_LIMIT);
         /* the node's interfaces in a fixed order: x low, x high, y low, y high, z low, z high */
         for (int d = 0; d < 3; ++d) {
             int pos = idx[d];
@@ -589,11 +674,13 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
             if (pos < N) { int id = iface3(c, e, d, idx, pos); for (int v = 0; v < NV; ++v) s[v] -= ell[id] * A[(size_t)NV * id + v]; }
         }
         double m = mass3(c, i), q[NV];
+        ORC_ROW(ROW_STAGE);
         for (int v = 0; v < NV; ++v) {
             res_out[(size_t)v * nn + i] = rfv[(size_t)v * nn + i] + s[v];
             q[v] = ufv[(size_t)v * nn + i] + dt / m * s[v];
             if (utilde) utilde[(size_t)v * nn + i] = q[v];
         }
+        ORC_ROW(ROW_STATS);
         if (stats) {
             double p = pressure3(gm, q);
             stats[S3_AVOL_M] += m * (1.0 - lmin[i]);
@@ -634,12 +721,15 @@ int o3_step(const o3_ctx *c, double *u, int nsteps, double *time, double cfl, in
     double *res = malloc(sizeof(double) * n);
     for (int s = 0; s < nsteps; ++s) {
         double dt = o3_dt(c, u, cfl);
+        ORC_CONST(dt);
         if (dt_hist) dt_hist[s] = dt;
         o3_stage(c, u, dt, limiting, beta, res, ut, stats);
         for (size_t k = 0; k < n; ++k) u1[k] = ut[k];
         o3_stage(c, u1, dt, limiting, beta, res, ut, stats);
+        ORC_ROW(ROW_STAGE);
         for (size_t k = 0; k < n; ++k) u2[k] = 0.75 * u[k] + 0.25 * ut[k];
         o3_stage(c, u2, dt, limiting, beta, res, ut, stats);
+        ORC_ROW(ROW_STAGE);
         for (size_t k = 0; k < n; ++k) u[k] = u[k] / 3.0 + 2.0 / 3.0 * ut[k];
         *time += dt;
     }

@@ -101,23 +101,24 @@ static inline cdbl fmax(const cdbl &a, const cdbl &b) { opc::add(opc::C_CMP, a.d
 
 namespace opc {
 /* states identified as solution nodes: address -> (node, values at tag time) */
-struct Tag { long id; double q[4]; };
+struct Tag { long id; int n; double q[5]; };
 static std::unordered_map<const void *, Tag> tags;
 static std::unordered_set<std::string> seen;
 static const void *scope_u = nullptr;
 static double scope_t = -1e300;
 static const int node_level[] = {1, 2, 3, 4, 5, 6, 11};   // PF_ ids counted as node preparation
 
-static void tag(const cdbl *q, long id) {
+static void tag(const cdbl *q, long id, int n = 4) {
     Tag t;
     t.id = id;
-    for (int v = 0; v < 4; ++v) t.q[v] = q[v].v;
+    t.n = n;
+    for (int v = 0; v < n; ++v) t.q[v] = q[v].v;
     tags[(const void *)q] = t;
 }
 static bool ident(const cdbl *q, long *id) {
     auto it = tags.find((const void *)q);
     if (it == tags.end()) return false;
-    for (int v = 0; v < 4; ++v)
+    for (int v = 0; v < it->second.n; ++v)
         if (memcmp(&it->second.q[v], &q[v].v, sizeof(double)) != 0) return false;
     *id = it->second.id;
     return true;
@@ -170,11 +171,13 @@ struct Guard {
 #define ORC_PURE_PAIR(fid, a, b, ...) opc::Guard orc_guard_(fid, 1, a, b, {__VA_ARGS__})
 #define ORC_PURE2(fid, a, b, ...) opc::Guard orc_guard_(fid, 2, a, b, {__VA_ARGS__})
 #define ORC_TAG(q, g) opc::tag(q, g)
+#define ORC_TAG_N(q, g, n) opc::tag(q, g, n)
 #define ORC_SCOPE(u, t) opc::scope(u, t)
 #define ORC_CONST(x) ((x).d = false)
 
 #define double cdbl
 #include "idp_oracle.c"
+#include "idp_oracle3d.c"
 #undef double
 
 /* node preparation, counted once per node and stage: the primitives that the
@@ -230,3 +233,48 @@ extern "C" int opc_count_step(int N, double gamma, int nx0, int ny0, double x0, 
 }
 
 extern "C" int opc_n_rows(void) { return ROW_COUNT; }
+
+/* node preparation of the 3D stage, once per node: velocity, pressure,
+   sound speed, rho/p, the physical fluxes and wave speeds along x, y, z */
+static void o3_count_node_prep(const o3_ctx *c, const cdbl *u) {
+    int saved = opc::row;
+    opc::row = ROW_NODE_PREP;
+    for (int i = 0; i < c->nn; ++i) {
+        cdbl q[5], v[3], f[5];
+        get3(c, u, i, q);
+        velocity3(q, v);
+        (void)pressure3(c->gamma, q);
+        (void)sound3(c->gamma, q);
+        (void)beta3(c->gamma, q);
+        for (int d = 0; d < 3; ++d) {
+            flux3(c->gamma, q, d, f);
+            (void)wave3(c->gamma, q, d);
+        }
+    }
+    opc::row = saved;
+}
+
+/* One counted SSP-RK3 step of the 3D oracle (conforming grid, as o3_create
+   takes it); counts[row][class] as for opc_count_step; u advanced in place. */
+extern "C" int opc_count_step3(int N, double gamma, int nx, int ny, int nz, const double *box, const int32_t *bc,
+                               const double *bc_prim, double *u_io, double cfl, int limiting, long long *counts) {
+    std::vector<cdbl> bx(6), bcp(30);
+    for (int k = 0; k < 6; ++k) bx[k] = box[k];
+    for (int k = 0; k < 30; ++k) bcp[k] = bc_prim[k];
+    int err = 0;
+    o3_ctx *c = o3_create(N, gamma, nx, ny, nz, bx.data(), bc, bcp.data(), &err);
+    if (!c) return 1;
+    size_t n = 5 * (size_t)c->nn;
+    std::vector<cdbl> u(n);
+    for (size_t k = 0; k < n; ++k) u[k] = cdbl::mk(u_io[k], true);
+    memset(opc::cnt, 0, sizeof opc::cnt);
+    opc::row = ROW_OTHER;
+    cdbl t = 0.0, st[16], dth[1];
+    o3_stats_init(st);
+    o3_step(c, u.data(), 1, &t, cfl, limiting, 0.1, dth, st);
+    for (size_t k = 0; k < n; ++k) u_io[k] = u[k].v;
+    for (int r = 0; r < ROW_COUNT; ++r)
+        for (int k = 0; k < opc::N_CLS; ++k) counts[r * opc::N_CLS + k] = opc::cnt[r][k];
+    o3_destroy(c);
+    return 0;
+}

@@ -38,7 +38,7 @@ WEIGHTS = {k: 1 for k in CLASSES}
 
 
 def build(force: bool = False) -> str:
-    srcs = [_SRC, os.path.join(_HERE, "idp_oracle.c")]
+    srcs = [_SRC, os.path.join(_HERE, "idp_oracle.c"), os.path.join(_HERE, "idp_oracle3d.c")]
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < max(os.path.getmtime(p) for p in srcs):
         subprocess.check_call(["g++", "-O2", "-std=c++17", "-fpermissive", "-w", "-ffp-contract=off", "-fPIC",
                                "-shared", "-o", _LIB, _SRC], cwd=_HERE)
@@ -55,6 +55,9 @@ def lib():
                                      C.c_double, C.c_int, C.POINTER(C.c_int8), ip, ip, ip, dp, dp, dp, dp,
                                      C.c_double, C.c_double, C.c_int, C.c_int, C.POINTER(C.c_longlong)]
         L.opc_n_rows.restype = C.c_int
+        L.opc_count_step3.restype = C.c_int
+        L.opc_count_step3.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, ip, dp, dp, C.c_double,
+                                      C.c_int, C.POINTER(C.c_longlong)]
         _lib = L
     return _lib
 
@@ -84,6 +87,26 @@ def count_step(mesh, N, u, cfl=0.5, limiting=2, gamma=1.4, vflux=0, t0=0.0):
                           out.ctypes.data_as(C.POINTER(C.c_longlong)))
     if rc != 0:
         raise ValueError("counting build rejected the mesh")
+    cnt = out.reshape(nrow, len(CLASSES))
+    return {r: {k: int(cnt[i, j]) for j, k in enumerate(CLASSES)} for i, r in enumerate(ROWS)}, uu
+
+
+def count_step3(grid, N, u, cfl=0.5, limiting=2, gamma=1.4):
+    """One counted SSP-RK3 step of the 3D oracle on a conforming grid.
+    Returns (counts[row][class], u after the step)."""
+    L = lib()
+    nrow = L.opc_n_rows()
+    box = np.ascontiguousarray(grid.box, dtype=np.float64)
+    bc = np.ascontiguousarray(grid.bc, dtype=np.int32)
+    bcp = np.ascontiguousarray(grid.bc_prim, dtype=np.float64).reshape(30)
+    uu = np.ascontiguousarray(u, dtype=np.float64).copy()
+    out = np.zeros(nrow * len(CLASSES), dtype=np.int64)
+    dp = C.POINTER(C.c_double)
+    rc = L.opc_count_step3(N, gamma, grid.nx, grid.ny, grid.nz, box.ctypes.data_as(dp),
+                           bc.ctypes.data_as(C.POINTER(C.c_int32)), bcp.ctypes.data_as(dp), uu.ctypes.data_as(dp),
+                           cfl, limiting, out.ctypes.data_as(C.POINTER(C.c_longlong)))
+    if rc != 0:
+        raise ValueError("counting build rejected the grid")
     cnt = out.reshape(nrow, len(CLASSES))
     return {r: {k: int(cnt[i, j]) for j, k in enumerate(CLASSES)} for i, r in enumerate(ROWS)}, uu
 
@@ -119,10 +142,33 @@ def work_table(degrees=(1, 2, 3, 4, 5, 6, 7)):
     return table
 
 
+def work_table3(degrees=(1, 2, 3, 4), n=10):
+    """The same per-node-and-stage counts for the 3D scheme on the 3D blast
+    workload at 1/64 of the benchmark's size (n^3 hexahedra, n = 10 against
+    40; the same sphere and states)."""
+    sys.path.insert(0, os.path.dirname(_HERE))
+    from paper_2607_06045_b300 import workloads as W
+    g = W.Grid3(n, n, n, bc=(3,) * 6)
+    out = {"workload": f"3D blast, {n}^3 hexahedra over [0,1]^3 (sphere r < 0.15 at p = 10 in rho = 1, "
+                       "p = 0.1, outflow), one SSP-RK3 step, local limiting, CFL 0.5",
+           "elements": int(g.n_elems), "degrees": {}}
+    for N in degrees:
+        u = W.blast3_state(g, N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0)
+        c, _ = count_step3(g, N, u)
+        nodes = g.n_elems * (N + 1) ** 3
+        pn = per_node_stage(c, nodes)
+        rows = {r: {"ops": {k: round(v, 4) for k, v in pn[r].items() if v}, "flops": round(flops(pn[r]), 3)}
+                for r in ROWS}
+        total = sum(rows[r]["flops"] for r in METHOD_ROWS)
+        out["degrees"][str(N)] = {"nodes": nodes, "rows": rows, "method_flops_per_node_stage": round(total, 3)}
+    return out
+
+
 TABLE = os.path.join(os.path.dirname(_HERE), "paper_2607_06045_b300", "method_work.json")
 
 if __name__ == "__main__":
     t = work_table()
+    t["3d"] = work_table3()
     with open(TABLE, "w") as f:
         json.dump(t, f, indent=1, sort_keys=True)
         f.write("\n")

@@ -75,3 +75,26 @@ def test_kernel_split_keeps_every_row_once(precision):
         assert f32 == 0
     else:
         assert f32 == pytest.approx(sum(rows[r] for r in R.FP32_FORM_FP32_ROWS), rel=1e-12)
+
+
+def test_counted_3d_step_is_the_oracle():
+    from oracle import o3d
+    g = W.Grid3(3, 3, 2, bc=(3,) * 6)
+    N = 3
+    u = W.blast3_state(g, N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0, centre=(0.4, 0.5, 0.5), r0=0.3)
+    _, u1 = OC.count_step3(g, N, u)
+    u2, *_ = o3d.Oracle3D(g, N).step(u, 1, cfl=0.5, limiting=2)
+    assert np.array_equal(u1.reshape(u2.shape), u2)
+
+
+def test_stored_3d_table_matches_the_counting_build():
+    t3 = R.method_table()["3d"]
+    n = round(t3["elements"] ** (1.0 / 3.0))
+    assert n ** 3 == t3["elements"]
+    g = W.Grid3(n, n, n, bc=(3,) * 6)
+    N = 2
+    c, _ = OC.count_step3(g, N, W.blast3_state(g, N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0))
+    pn = OC.per_node_stage(c, g.n_elems * (N + 1) ** 3)
+    stored = t3["degrees"][str(N)]["rows"]
+    for r in OC.ROWS:
+        assert stored[r]["flops"] == pytest.approx(round(OC.flops(pn[r]), 3), abs=1e-3), r
