@@ -18,6 +18,7 @@
 #include <stdint.h>
 
 #include "idp_bits.cuh"
+#include "idp_fastmath.cuh"
 
 namespace idp3 {
 
@@ -40,7 +41,7 @@ struct Grid3 {
 
 // LGL nodes and weights, Sbar (Sec. 2.1), 1 / w
 struct Ops3 {
-    double xi[NPMAX3], w[NPMAX3], S[NPMAX3][NPMAX3];
+    double xi[NPMAX3], w[NPMAX3], iw[NPMAX3], S[NPMAX3][NPMAX3];
 };
 
 // statistics of the limited stages (atomics)
@@ -72,7 +73,7 @@ __device__ __forceinline__ double stage_dt3(const Stage3 &A) {
 }
 
 __device__ __forceinline__ double pres3(double g, const double *u) {
-    return (g - 1.0) * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) / u[0]);
+    return (g - 1.0) * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * idp::fast_rcp(u[0]));
 }
 
 __device__ __forceinline__ void flux3(double g, const double *u, int d, double *f) {
@@ -150,6 +151,42 @@ __device__ __forceinline__ double theta3(double g, const double *u0, const doubl
     return 0.0;
 }
 
+// Certifies in FP32 that theta = h is admissible for u0 + theta a (rho > 0 and
+// g(h) = (gamma-1)(rho E - |m|^2/2) - pmin rho >= 0 in exact arithmetic),
+// given c0 = g(0) formed in FP64: every FP32 product and sum below stays
+// within 20 unit roundings (2^-24) of the sum S of the absolute terms, so
+// g_f32 > 4e-6 S (67 unit roundings) implies g(h) > 0 with a threefold
+// margin, and the same holds for the density. h rounded to FP32 moves g by
+// less than 2 unit roundings of S. Returns false when it cannot decide (near
+// the bound, or magnitudes outside the FP32 range); the FP64 solve then runs.
+__device__ __forceinline__ bool admissible3_f32(double gm1, const double *u0, const double *a, double pmin, double c0,
+                                                double h) {
+    if (!(c0 > 0.0) || !(u0[0] > 0.0) || !(h > 0.0)) return false;
+    float r0 = idp::d2f(u0[0]), E0 = idp::d2f(u0[4]), ar = idp::d2f(a[0]), aE = idp::d2f(a[4]);
+    float gm = idp::d2f(gm1), pm = idp::d2f(pmin), hf = idp::d2f(h);
+    float t1 = r0 * aE, t2 = ar * E0, t5 = pm * ar;
+    float tm = 0.0f, sm = 0.0f, q2 = 0.0f;
+    for (int c = 1; c <= 3; ++c) {
+        const float mc = idp::d2f(u0[c]), ac = idp::d2f(a[c]);
+        const float t = mc * ac;
+        tm += t;
+        sm += fabsf(t);
+        q2 += ac * ac;
+    }
+    float c1 = gm * (t1 + t2 - tm) - t5;
+    float s1 = gm * (fabsf(t1) + fabsf(t2) + sm) + fabsf(t5);
+    float q1 = ar * aE;
+    float c2 = gm * (q1 - 0.5f * q2);
+    float s2 = gm * (fabsf(q1) + 0.5f * q2);
+    float c0f = idp::d2f(c0);
+    float S = fabsf(c0f) + hf * (s1 + hf * s2);
+    if (!(S > 1e-30f) || !(S < 1e30f)) return false;
+    float gh = c0f + hf * (c1 + hf * c2);
+    if (!(gh > 4e-6f * S)) return false;
+    float rh = r0 + hf * ar;
+    return rh > 4e-6f * (r0 + hf * fabsf(ar));
+}
+
 // the ghost state across boundary side s (R4: wall, Dirichlet, outflow)
 __device__ __forceinline__ void ghost3(const Grid3 &G, int s, const double *in, double *q) {
     const int kind = G.bc[s];
@@ -201,7 +238,9 @@ struct Sm3 {
         double u[NV][NN];      // P0 - P2: the stage input
         double rfv[NV][NN];    // P2 - P5: low-order residual (each node overwrites only its own u)
     };
-    double pr[4][NN];          // P0 - P1: v1, v2, v3, p
+    double pr[7][NN];          // P0 - P1: v1, v2, v3, p, ln rho, ln (rho / p), rho / p
+    double lam[3][NN];         // P0 - P1: |v_d| + c
+    double outp[6][NR][3];     // P0 - P1: outside states' normal velocity, pressure, wave speed
     union {
         double outs[6][NR][NV];   // P0 - P1: outside states of the six faces
         struct {                  // P2b - P5
@@ -222,6 +261,8 @@ struct Sm3 {
     double fvf[NIF][NV];       // P1 - P2b: low-order subcell fluxes, mass-weighted, along +d
     double ufv[NV][NN];        // P2 - P5
     double rmin[NN], rmax[NN], pmin[NN];
+    double c0[NN];             // P2 - P4: g(0) = (gamma-1)(rho E - |m|^2/2) - p_min rho at u_FV
+    double im[NN];             // P2 - P5: 1 / m
 };
 
 // threads of a block of EPB elements: one per node, rounded up to whole warps
@@ -230,8 +271,45 @@ struct Launch3 {
     static constexpr int items = EPB * NP * NP * NP, threads = (items + 31) / 32 * 32;
 };
 
+// logarithmic mean of a and b from their logarithms (R2): (a - b) / (la - lb),
+// and the Ismail-Roe series where ((a - b)/(a + b))^2 < 1e-4 (the branch
+// test taken in FP32: the two forms agree to rounding near the threshold)
+__device__ __forceinline__ double logmean_l(double a, double b, double la, double lb) {
+    const double x = a + b, y = a - b;
+    const float yf = (float)y, xf = (float)x;
+    if (yf * yf < 1e-4f * xf * xf) {
+        const double ix = idp::fast_rcp(x), uu = (y * ix) * (y * ix);
+        // x / (2 F(u)) with 1/F = 1 - u/3 - 4u^2/45 - 44u^3/945
+        return 0.5 * x * (1.0 - uu * (1.0 / 3.0 + uu * (4.0 / 45.0 + uu * (44.0 / 945.0))));
+    }
+    return y * idp::fast_rcp(la - lb);
+}
+
+// 1 / (logarithmic mean) of a and b from their logarithms
+__device__ __forceinline__ double inv_logmean_l(double a, double b, double la, double lb) {
+    const double x = a + b, y = a - b;
+    const float yf = (float)y, xf = (float)x;
+    if (yf * yf < 1e-4f * xf * xf) {
+        const double ix = idp::fast_rcp(x), uu = (y * ix) * (y * ix);
+        // 2 F(u) / x with F = 1 + u/3 + u^2/5 + u^3/7
+        return 2.0 * ix * (1.0 + uu * (1.0 / 3.0 + uu * (1.0 / 5.0 + uu * (1.0 / 7.0))));
+    }
+    return (la - lb) * idp::fast_rcp(y);
+}
+
+// physical flux along d from the state and its velocity along d and pressure
+__device__ __forceinline__ void flux_p(const double *u, double vd, double p, int d, double *f) {
+    f[0] = u[1 + d];
+    f[1] = u[1] * vd + (d == 0 ? p : 0.0);
+    f[2] = u[2] * vd + (d == 1 ? p : 0.0);
+    f[3] = u[3] * vd + (d == 2 ? p : 0.0);
+    f[4] = (u[4] + p) * vd;
+}
+
 // One block of EPB elements, one thread per node; items of each phase are
-// spread over the block.
+// spread over the block. Per node, its primitives, logarithms and wave
+// speeds are formed once (P0); the pair, face and subcell fluxes take them
+// from shared memory.
 template <int NP, int EPB>
 __global__ void __launch_bounds__(Launch3<NP, EPB>::threads)
 k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
@@ -245,21 +323,33 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     for (int k = tid; k < (int)(sizeof(Ops3) / sizeof(double)); k += NT)
         reinterpret_cast<double *>(&ops)[k] = reinterpret_cast<const double *>(ops_g)[k];
     const size_t KN = (size_t)G.K * NN;
-    const double g = A.gamma;
+    const double g = A.gamma, gm1 = g - 1.0;
     const double dt = stage_dt3(A);
     const double q[3] = {G.dy * G.dz / 4.0, G.dx * G.dz / 4.0, G.dx * G.dy / 4.0};   // quarter face areas
-    const double J = G.dx * G.dy * G.dz / 8.0;
+    const double iJ = 8.0 / (G.dx * G.dy * G.dz);
     const int e0 = blockIdx.x * EPB;
-    // ---- P0: state, primitives, outside states
+    // ---- P0: state, primitives, logarithms, wave speeds; outside states
     for (int k = tid; k < EPB * NN; k += NT) {
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
         double uv[NV];
         for (int v = 0; v < NV; ++v) { uv[v] = A.u[v * KN + (size_t)e * NN + n]; S[le].u[v][n] = uv[v]; }
-        const double p = pres3(g, uv);
-        for (int a = 0; a < 3; ++a) S[le].pr[a][n] = uv[1 + a] / uv[0];
-        S[le].pr[3][n] = p;
-        if (!(uv[0] > 0.0) || !(p > 0.0)) atomicOr(A.status, S_BAD_INPUT);
+        const double ir = idp::fast_rcp(uv[0]);
+        const double v1 = uv[1] * ir, v2 = uv[2] * ir, v3 = uv[3] * ir;
+        const double p = gm1 * (uv[4] - 0.5 * (uv[1] * v1 + uv[2] * v2 + uv[3] * v3));
+        S[le].pr[0][n] = v1; S[le].pr[1][n] = v2; S[le].pr[2][n] = v3; S[le].pr[3][n] = p;
+        if (!(uv[0] > 0.0) || !(p > 0.0)) {
+            atomicOr(A.status, S_BAD_INPUT);
+            S[le].pr[4][n] = 0.0; S[le].pr[5][n] = 0.0; S[le].pr[6][n] = 1.0;
+            for (int d = 0; d < 3; ++d) S[le].lam[d][n] = 0.0;
+            continue;
+        }
+        const double c = idp::fast_sqrt(g * p * ir);
+        const double bet = uv[0] * idp::fast_rcp(p);
+        S[le].pr[4][n] = log(uv[0]);
+        S[le].pr[5][n] = log(bet);
+        S[le].pr[6][n] = bet;
+        S[le].lam[0][n] = fabs(v1) + c; S[le].lam[1][n] = fabs(v2) + c; S[le].lam[2][n] = fabs(v3) + c;
     }
     for (int k = tid; k < EPB * 6 * NR; k += NT) {
         const int le = k / (6 * NR), r0 = k - le * 6 * NR, s = r0 / NR, t = r0 - s * NR, e = e0 + le;
@@ -277,6 +367,13 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             ghost3(G, s, in, o);
         }
         for (int v = 0; v < NV; ++v) S[le].outs[s][t][v] = o[v];
+        // the outside state's normal velocity, pressure and wave speed
+        const double ir = idp::fast_rcp(o[0]);
+        const double vd = o[1 + d] * ir;
+        const double po = gm1 * (o[4] - 0.5 * (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) * ir);
+        S[le].outp[s][t][0] = vd;
+        S[le].outp[s][t][1] = po;
+        S[le].outp[s][t][2] = (o[0] > 0.0 && po > 0.0) ? fabs(vd) + idp::fast_sqrt(g * po * ir) : 0.0;
     }
     __syncthreads();
     // ---- P1a: two-point fluxes of every row, each unordered pair once
@@ -289,10 +386,19 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         while (rem >= N - a) { rem -= N - a; ++a; }
         const int b = a + 1 + rem;
         const int na = node_of<NP>(d, r, a), nb = node_of<NP>(d, r, b);
-        double ua[NV], ub[NV], va[3], vb[3], f[NV];
-        for (int v = 0; v < NV; ++v) { ua[v] = S[le].u[v][na]; ub[v] = S[le].u[v][nb]; }
-        for (int c = 0; c < 3; ++c) { va[c] = S[le].pr[c][na]; vb[c] = S[le].pr[c][nb]; }
-        ranocha3(g, ua, va, S[le].pr[3][na], ub, vb, S[le].pr[3][nb], d, f);
+        const SM &X = S[le];
+        const double rho_ln = logmean_l(X.u[0][na], X.u[0][nb], X.pr[4][na], X.pr[4][nb]);
+        const double pa = X.pr[3][na], pb = X.pr[3][nb];
+        const double iba = inv_logmean_l(X.pr[6][na], X.pr[6][nb], X.pr[5][na], X.pr[5][nb]);
+        double va[3], vb[3];
+        for (int cc = 0; cc < 3; ++cc) { va[cc] = X.pr[cc][na]; vb[cc] = X.pr[cc][nb]; }
+        // R1 (Ranocha) along d
+        const double vdot = va[0] * vb[0] + va[1] * vb[1] + va[2] * vb[2];
+        const double fr = rho_ln * 0.5 * (va[d] + vb[d]);
+        double f[NV];
+        f[0] = fr;
+        for (int cc = 0; cc < 3; ++cc) f[1 + cc] = fr * 0.5 * (va[cc] + vb[cc]) + (cc == d ? 0.5 * (pa + pb) : 0.0);
+        f[4] = fr * (0.5 * vdot + iba * (1.0 / gm1)) + 0.5 * (pa * vb[d] + pb * va[d]);
         for (int v = 0; v < NV; ++v) S[le].pair[d][r][pp][v] = f[v];
     }
     // ---- P1b: LLF faces (mass-weighted, along +d) and their bar-state densities
@@ -301,18 +407,19 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         if (e0 + le >= G.K) continue;
         const int d = s / 2, side = s & 1;
         const int nin = node_of<NP>(d, t, side ? N : 0);
+        const SM &X = S[le];
         double ui[NV], uo[NV], fi[NV], fo[NV];
-        for (int v = 0; v < NV; ++v) { ui[v] = S[le].u[v][nin]; uo[v] = S[le].outs[s][t][v]; }
-        flux3(g, ui, d, fi);
-        flux3(g, uo, d, fo);
-        const double lam = fmax(wave3(g, ui, d), wave3(g, uo, d));
+        for (int v = 0; v < NV; ++v) { ui[v] = X.u[v][nin]; uo[v] = X.outs[s][t][v]; }
+        flux_p(ui, X.pr[d][nin], X.pr[3][nin], d, fi);
+        flux_p(uo, X.outp[s][t][0], X.outp[s][t][1], d, fo);
+        const double lam = fmax(X.lam[d][nin], X.outp[s][t][2]);
         const double wt = ops.w[t % NP] * ops.w[t / NP], cw = wt * q[d];
         // left state first: the outside is on the left of a low face
         const double *uL = side ? ui : uo, *uR = side ? uo : ui, *fL = side ? fi : fo, *fR = side ? fo : fi;
         for (int v = 0; v < NV; ++v) S[le].ff[s][t][v] = cw * (0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]));
         // ubar = (u_i + u_o)/2 - c.(f_o - f_i)/(2 |c| lambda), c along the outward normal
-        const double sg = side ? 1.0 : -1.0;
-        S[le].fbar[s][t] = 0.5 * (ui[0] + uo[0]) - sg * (fo[0] - fi[0]) / (2.0 * lam);
+        const double sg = side ? 0.5 : -0.5;
+        S[le].fbar[s][t] = 0.5 * (ui[0] + uo[0]) - sg * (fo[0] - fi[0]) * idp::fast_rcp(lam);
     }
     // ---- P1c: low-order subcell fluxes at the interior interfaces
     for (int k = tid; k < EPB * NIF; k += NT) {
@@ -320,14 +427,15 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         if (e0 + le >= G.K) continue;
         const int d = id / (NR * N), r1 = id - d * NR * N, r = r1 / N, a = r1 - r * N;
         const int nl = node_of<NP>(d, r, a), nr = node_of<NP>(d, r, a + 1);
+        const SM &X = S[le];
         double ul[NV], ur[NV], fl[NV], fr[NV];
-        for (int v = 0; v < NV; ++v) { ul[v] = S[le].u[v][nl]; ur[v] = S[le].u[v][nr]; }
-        flux3(g, ul, d, fl);
-        flux3(g, ur, d, fr);
-        const double lam = fmax(wave3(g, ul, d), wave3(g, ur, d));
+        for (int v = 0; v < NV; ++v) { ul[v] = X.u[v][nl]; ur[v] = X.u[v][nr]; }
+        flux_p(ul, X.pr[d][nl], X.pr[3][nl], d, fl);
+        flux_p(ur, X.pr[d][nr], X.pr[3][nr], d, fr);
+        const double lam = fmax(X.lam[d][nl], X.lam[d][nr]);
         const double cc = ops.w[r % NP] * ops.w[r / NP] * q[d] / 2.0;
         for (int v = 0; v < NV; ++v) S[le].fvf[id][v] = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
-        S[le].ibar[id] = 0.5 * (ul[0] + ur[0]) - (fr[0] - fl[0]) / (2.0 * lam);
+        S[le].ibar[id] = 0.5 * (ul[0] + ur[0]) - 0.5 * (fr[0] - fl[0]) * idp::fast_rcp(lam);
     }
     __syncthreads();
     // ---- P2: low-order residual, low-order update and bounds per node
@@ -335,42 +443,49 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / NN, n = k - le * NN;
         if (e0 + le >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
-        const double m = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * J;
+        const double im = ops.iw[idx[0]] * ops.iw[idx[1]] * ops.iw[idx[2]] * iJ;
         double r[NV] = {0, 0, 0, 0, 0}, uv[NV];
         for (int v = 0; v < NV; ++v) uv[v] = S[le].u[v][n];
         double lo = uv[0], hi = uv[0];
         for (int d = 0; d < 3; ++d) {
             const int pos = idx[d], row = idx[(d + 1) % 3] + NP * idx[(d + 2) % 3];
             // low side: the interface (pos-1, pos) or the low face
+            double b0, b1;
             if (pos > 0) {
                 const int id = (d * NR + row) * N + pos - 1;
                 for (int v = 0; v < NV; ++v) r[v] += S[le].fvf[id][v];
-                lo = fmin(lo, S[le].ibar[id]); hi = fmax(hi, S[le].ibar[id]);
+                b0 = S[le].ibar[id];
             } else {
                 for (int v = 0; v < NV; ++v) r[v] += S[le].ff[2 * d][row][v];
-                lo = fmin(lo, S[le].fbar[2 * d][row]); hi = fmax(hi, S[le].fbar[2 * d][row]);
+                b0 = S[le].fbar[2 * d][row];
             }
             if (pos < N) {
                 const int id = (d * NR + row) * N + pos;
                 for (int v = 0; v < NV; ++v) r[v] -= S[le].fvf[id][v];
-                lo = fmin(lo, S[le].ibar[id]); hi = fmax(hi, S[le].ibar[id]);
+                b1 = S[le].ibar[id];
             } else {
                 for (int v = 0; v < NV; ++v) r[v] -= S[le].ff[2 * d + 1][row][v];
-                lo = fmin(lo, S[le].fbar[2 * d + 1][row]); hi = fmax(hi, S[le].fbar[2 * d + 1][row]);
+                b1 = S[le].fbar[2 * d + 1][row];
             }
+            lo = idp::dmin(lo, idp::dmin(b0, b1));
+            hi = idp::dmax(hi, idp::dmax(b0, b1));
         }
         double uf[NV];
         for (int v = 0; v < NV; ++v) {
-            uf[v] = uv[v] + dt / m * r[v];
+            uf[v] = uv[v] + dt * im * r[v];
             S[le].ufv[v][n] = uf[v];
             S[le].rfv[v][n] = r[v];   // overwrites this node's own u only
         }
         double rmn, rmx;
-        if (A.limiting >= 2) { rmn = fmax(lo, A.beta * uf[0]); rmx = hi; }
+        if (A.limiting >= 2) { rmn = idp::dmax(lo, A.beta * uf[0]); rmx = hi; }
         else { rmn = A.beta * uf[0]; rmx = INFINITY; }
-        S[le].rmin[n] = fmin(rmn, uf[0]);
-        S[le].rmax[n] = fmax(rmx, uf[0]);
-        S[le].pmin[n] = A.beta * pres3(g, uf);
+        S[le].rmin[n] = idp::dmin(rmn, uf[0]);
+        S[le].rmax[n] = idp::dmax(rmx, uf[0]);
+        const double rhoe = uf[0] * uf[4] - 0.5 * (uf[1] * uf[1] + uf[2] * uf[2] + uf[3] * uf[3]);
+        const double pm = A.beta * gm1 * rhoe * idp::fast_rcp(uf[0]);
+        S[le].pmin[n] = pm;
+        S[le].c0[n] = gm1 * rhoe - pm * uf[0];
+        S[le].im[n] = im;
     }
     __syncthreads();
     // ---- P2b: telescoped high-order subcell fluxes per row, then A = F_DG - F_FV
@@ -391,12 +506,10 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             }
             const int id = (d * NR + r) * N + l;
             const int nl = node_of<NP>(d, r, l), nr = node_of<NP>(d, r, l + 1);
-            const int il[3] = {nl % NP, (nl / NP) % NP, nl / (NP * NP)}, ir[3] = {nr % NP, (nr / NP) % NP, nr / (NP * NP)};
-            const double ml = ops.w[il[0]] * ops.w[il[1]] * ops.w[il[2]] * J;
-            const double mr = ops.w[ir[0]] * ops.w[ir[1]] * ops.w[ir[2]] * J;
+            const double iml = S[le].im[nl], imr = S[le].im[nr];
             for (int v = 0; v < NV; ++v) S[le].A[id][v] = wt * acc[v] - S[le].fvf[id][v];
             const double Ar = fabs(S[le].A[id][0]);
-            S[le].ex[id] = (dt / ml * Ar <= kTol3 * fabs(S[le].ufv[0][nl])) && (dt / mr * Ar <= kTol3 * fabs(S[le].ufv[0][nr]));
+            S[le].ex[id] = (dt * iml * Ar <= kTol3 * fabs(S[le].ufv[0][nl])) && (dt * imr * Ar <= kTol3 * fabs(S[le].ufv[0][nr]));
         }
     }
     __syncthreads();
@@ -405,7 +518,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / NN, n = k - le * NN;
         if (e0 + le >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
-        const double m = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * J;
+        const double m = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * (G.dx * G.dy * G.dz / 8.0);
         double Pp = 0.0, Pm = 0.0;
         for (int d = 0; d < 3; ++d) {
             const int pos = idx[d], row = idx[(d + 1) % 3] + NP * idx[(d + 2) % 3];
@@ -439,14 +552,15 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             const double *Ai = S[le].A[id];
             const double lr = S[le].ex[id] ? 1.0
                             : (-Ai[0] > 0.0) ? fmin(S[le].Rp[nl], S[le].Rm[nr]) : fmin(S[le].Rm[nl], S[le].Rp[nr]);
-            const int il[3] = {nl % NP, (nl / NP) % NP, nl / (NP * NP)}, ir[3] = {nr % NP, (nr / NP) % NP, nr / (NP * NP)};
-            const double ml = ops.w[il[0]] * ops.w[il[1]] * ops.w[il[2]] * J;
-            const double mr = ops.w[ir[0]] * ops.w[ir[1]] * ops.w[ir[2]] * J;
+            const double gl = -kGamma3 * dt * S[le].im[nl], gr = kGamma3 * dt * S[le].im[nr];
             double u0[NV], av[NV];
-            for (int v = 0; v < NV; ++v) { u0[v] = S[le].ufv[v][nl]; av[v] = -kGamma3 * dt / ml * Ai[v]; }
-            const double thl = theta3(g, u0, av, S[le].pmin[nl], lr);
-            for (int v = 0; v < NV; ++v) { u0[v] = S[le].ufv[v][nr]; av[v] = kGamma3 * dt / mr * Ai[v]; }
-            const double thr = theta3(g, u0, av, S[le].pmin[nr], lr);
+            // each end: certified in FP32 at lr, else the FP64 solve (R8)
+            for (int v = 0; v < NV; ++v) { u0[v] = S[le].ufv[v][nl]; av[v] = gl * Ai[v]; }
+            const double thl = admissible3_f32(gm1, u0, av, S[le].pmin[nl], S[le].c0[nl], lr)
+                             ? lr : theta3(g, u0, av, S[le].pmin[nl], lr);
+            for (int v = 0; v < NV; ++v) { u0[v] = S[le].ufv[v][nr]; av[v] = gr * Ai[v]; }
+            const double thr = admissible3_f32(gm1, u0, av, S[le].pmin[nr], S[le].c0[nr], lr)
+                             ? lr : theta3(g, u0, av, S[le].pmin[nr], lr);
             l = fmin(thl, thr);
         }
         S[le].ell[id] = l;
@@ -459,7 +573,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
-        const double m = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * J;
+        const double im = S[le].im[n];
         double s[NV] = {0, 0, 0, 0, 0}, lm = 1.0;
         // the node's interfaces in a fixed order: x low, x high, y low, y high, z low, z high
         for (int d = 0; d < 3; ++d) {
@@ -467,13 +581,13 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             if (pos > 0) {
                 const int id = (d * NR + row) * N + pos - 1;
                 const double l = S[le].ell[id];
-                lm = fmin(lm, l);
+                lm = idp::dmin(lm, l);
                 for (int v = 0; v < NV; ++v) s[v] += l * S[le].A[id][v];
             }
             if (pos < N) {
                 const int id = (d * NR + row) * N + pos;
                 const double l = S[le].ell[id];
-                lm = fmin(lm, l);
+                lm = idp::dmin(lm, l);
                 for (int v = 0; v < NV; ++v) s[v] -= l * S[le].A[id][v];
             }
         }
@@ -481,9 +595,9 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         double ut[NV];
         for (int v = 0; v < NV; ++v) {
             const double res = S[le].rfv[v][n] + s[v];
-            ut[v] = S[le].ufv[v][n] + dt / m * s[v];
+            ut[v] = S[le].ufv[v][n] + dt * im * s[v];
             double o;
-            if (A.mode == 0) o = res / m;
+            if (A.mode == 0) o = res * im;
             else if (A.comb == 1) o = 0.75 * A.un[v * KN + gi] + 0.25 * ut[v];
             else if (A.comb == 2) o = A.un[v * KN + gi] * (1.0 / 3.0) + 2.0 / 3.0 * ut[v];
             else o = ut[v];
@@ -495,10 +609,11 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             if (ut[0] < rl - kViol3 * fabs(rl) || ut[0] > rh + kViol3 * fabs(rh)) vr++;
             if (p < pl - kViol3 * fabs(pl)) vp++;
             if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
-            am += m * (1.0 - lm);
+            const double mm_ = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * (G.dx * G.dy * G.dz / 8.0);
+            am += mm_ * (1.0 - lm);
             if (lm < 1.0) nact++;
-            rmin_st = fmin(rmin_st, ut[0]);
-            pmin_st = fmin(pmin_st, p);
+            rmin_st = idp::dmin(rmin_st, ut[0]);
+            pmin_st = idp::dmin(pmin_st, p);
         }
     }
     if (A.collect && A.limiting > 0) {
@@ -509,8 +624,8 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         nact = __reduce_add_sync(FULL, nact);
         for (int o = 16; o > 0; o >>= 1) {
             am += __shfl_down_sync(FULL, am, o);
-            rmin_st = fmin(rmin_st, __shfl_down_sync(FULL, rmin_st, o));
-            pmin_st = fmin(pmin_st, __shfl_down_sync(FULL, pmin_st, o));
+            rmin_st = idp::dmin(rmin_st, __shfl_down_sync(FULL, rmin_st, o));
+            pmin_st = idp::dmin(pmin_st, __shfl_down_sync(FULL, pmin_st, o));
         }
         if ((tid & 31) == 0) {
             if (am > 0.0) atomicAdd(&A.stats->alpha_m, am);

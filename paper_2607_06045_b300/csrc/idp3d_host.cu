@@ -188,7 +188,7 @@ idp_status idp3d_create(const idp3d_grid_desc *gd, int32_t N, double gamma, cons
     {
         double x[NPMAX3], w[NPMAX3], S[NPMAX3 * NPMAX3];
         idp::host_lgl_sbar(N, x, w, S);
-        for (int i = 0; i <= N; ++i) { ops.xi[i] = x[i]; ops.w[i] = w[i]; }
+        for (int i = 0; i <= N; ++i) { ops.xi[i] = x[i]; ops.w[i] = w[i]; ops.iw[i] = 1.0 / w[i]; }
         for (int i = 0; i <= N; ++i) for (int j = 0; j <= N; ++j) ops.S[i][j] = S[i * (N + 1) + j];
     }
     bool ok = true;

@@ -11,7 +11,8 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="dmr", choices=["dmr", "square", "blast", "batched"])
+    ap.add_argument("--workload", default="dmr", choices=["dmr", "square", "blast", "batched", "blast3d"])
+    ap.add_argument("--n3", type=int, default=40, help="3D: elements per direction")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--N", type=int, default=3)
@@ -24,6 +25,16 @@ def main(argv=None):
     from paper_2607_06045_b300 import build, idp
     from paper_2607_06045_b300 import workloads as W
     build.build()
+    if a.workload == "blast3d":
+        g = W.Grid3(a.n3, a.n3, a.n3, bc=(3,) * 6)
+        u = W.blast3_state(g, a.N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0)
+        ctx = idp.Context3D(g, a.N, limiting=a.limiting, cfl=0.5)
+        ud = torch.from_numpy(u).cuda()
+        t = np.zeros(1)
+        ctx.idp3d_step(ud, a.steps, t)
+        torch.cuda.synchronize()
+        print(f"ok: blast3d K={ctx.K} steps={a.steps} t={t[0]}")
+        return
     if a.workload == "dmr":
         meshes = W.dmr_mesh(); u = W.dmr_state(meshes, a.N)
     elif a.workload == "square":
