@@ -1,7 +1,7 @@
 /*
  * idp_oracle3d.c -- plain, slow FP64 CPU oracle of the IDP-limited LGL-DGSEM
- * for the 3D Euler equations (d = 3 of Sec. 2, Eq. conservationlaw) on a
- * conforming Cartesian grid of hexahedra (Bolm, Rueda-Ramirez, Kuzmin,
+ * for the 3D Euler equations (d = 3 of Sec. 2, Eq. conservationlaw) on
+ * 2:1-balanced Cartesian octrees of hexahedra (Bolm, Rueda-Ramirez, Kuzmin,
  * Gassner, arXiv 2607.06045).
  *
  * TEST INFRASTRUCTURE ONLY. Only the tests, the smoke check and the CPU
@@ -10,25 +10,36 @@
  * (orc_operators: nodes, weights, Sbar) and logarithmic mean (orc_logmean,
  * R2) it uses; everything three-dimensional is here.
  *
- * The method is the 2D one of the paper with the third direction added, as
+ * The mesh is a 2:1-balanced octree of hexahedra (a leaf at level l is one
+ * cell of the (nx0 2^l) x (ny0 2^l) x (nz0 2^l) grid over the box); a face
+ * between a leaf and four finer ones is a mortar with 2 x 2 small faces. The
+ * method is the 2D one of the paper with the third direction added, as
  * Sec. 2 states it for d in {1, 2, 3}:
  *   - the high-order residual of Eq. evolutionformula, a sum over the three
  *     directions of the flux-differencing volume terms with Sbar and the LLF
  *     surface terms, and its subcell fluxes (Eq. fluxdifferencingform);
  *   - the low-order residual in the global graph form of
  *     Eq. LowOrderScheme_globalIndices with the c/d coefficients of Sec. 2.1,
- *     the three directions' subcell neighbours and the face neighbours;
+ *     the three directions' subcell neighbours, the face neighbours and, at
+ *     mortars, Eq. c_nonconforming with the local weights of App. A taken
+ *     as products of the 1D overlap weights along the face's two tangential
+ *     directions (reading R32: the overlap of tensor-product subcells);
+ *   - the L2 mortar (R5) as the tensor product of the 1D interpolation and
+ *     exact L2 projection, and the sparse IDP mortar flux of
+ *     Eq. interfaceflux_local with those weights;
  *   - bar states, density bounds (Eqs. Bounds_Positivity, Bounds_Barstates),
  *     Zalesak density limiting and the pressure factor with Gamma = 2d = 6
- *     (Sec. 2.3);
+ *     (Sec. 2.3), and one factor per mortar after the volume correction with
+ *     the n_i budget (R9);
  *   - the IDP time step (Eq. timestep_restriction) and SSP-RK3.
- * Readings as in idp_oracle.c (R1-R3, R6-R8, R10, R13, R15, R17), with the
+ * Readings as in idp_oracle.c (R1-R3, R5-R10, R13, R15-R17), with the
  * states u = (rho, rho v1, rho v2, rho v3, rho e) and
  * p = (gamma - 1)(rho e - |m|^2 / (2 rho)); the boundary kinds of R4 without
  * the 2D problem-specific ones (periodic, wall, Dirichlet, outflow).
  *
- * Layout: element e = (ez ny + ey) nx + ex, node g = ((e np + k) np + j) np + i
- * (x index i fastest), state u[5][K np^3].
+ * Layout: node g = ((e np + k) np + j) np + i (x index i fastest) of leaf e
+ * in the caller's order, state u[5][K np^3]; a uniform grid (o3_create)
+ * orders its elements e = (ez ny + ey) nx + ex.
  */
 #include <math.h>
 #include <stdint.h>
@@ -68,25 +79,35 @@ enum { PF_PRESSURE = 1, PF_VELOCITY, PF_BETA, PF_SOUND, PF_WAVE, PF_FLUX, PF_LOG
 #endif
 
 enum { B3_PERIODIC = 0, B3_WALL = 1, B3_DIRICHLET = 2, B3_OUTFLOW = 3 };
-enum { S3_AVOL_M = 0, S3_M, S3_NVOL, S3_VRHO, S3_VP, S3_NONPOS, S3_DTX, S3_MINRHO, S3_MINP, S3_N };
+enum { F3_CONF = 0, F3_BND = 1, F3_ML = 2, F3_MS = 3 };
+enum { S3_AVOL_M = 0, S3_M, S3_NVOL, S3_VRHO, S3_VP, S3_NONPOS, S3_DTX, S3_MINRHO, S3_MINP, S3_AMORT_A, S3_A,
+       S3_NMORT, S3_N };
 
 typedef struct {
     int j;            /* neighbour node, or -1-q for ghost q */
-    int face;         /* 1: across an element face, 0: a subcell neighbour */
+    int face;         /* 0 subcell neighbour, 1 across a conforming or boundary face, 2 across a mortar */
     double c[3];      /* c_(i,j) */
 } o3_nb;
 
 typedef struct {
-    int N, np, nx, ny, nz, K, nn, ng;
+    int N, np, K, nn, ng, M;
     double gamma;
     double xi[NP3], w[NP3], S[NP3][NP3];
-    double x0, y0, z0, dx, dy, dz;
+    double wt[NP3][2 * NP3];    /* 1D local weights (App. A), reference units of the large face */
+    double Ii[2 * NP3][NP3];    /* 1D interpolation large -> small-face nodes */
+    double P[NP3][2 * NP3];     /* 1D exact L2 projection small -> large */
+    int n0[3];
+    double box[6];
     int bc[6];
     double bc_prim[6][NV];
+    int *lev, *ic;              /* [K], [K][3] */
+    double *h;                  /* [K][3] element sides */
+    int *ftype, *fnbr, *fpos;   /* [K][6] */
+    int *mort;                  /* [M][7]: d, large, large on the low side, small[4] (p = p1 + 2 p2) */
     int *nb_off;
     o3_nb *nb;
-    int *g_node;      /* ghost q: the boundary node it mirrors */
-    int *g_side;      /* and the side */
+    int *g_node, *g_side;       /* ghost q: the boundary node it mirrors, and the side */
+    int *mcount;                /* [nn] mortars incident on the node */
 } o3_ctx;
 
 #ifdef ORC_COUNTING
@@ -237,6 +258,10 @@ double o3_theta(double g, const double *u0, const double *a, double pmin, double
 /* ------------------------------------------------------------------------ */
 
 static int g3(const o3_ctx *c, int e, int i, int j, int k) { return ((e * c->np + k) * c->np + j) * c->np + i; }
+static int g3v(const o3_ctx *c, int e, const int *idx) { return g3(c, e, idx[0], idx[1], idx[2]); }
+
+/* quarter area of the faces of element e normal to d */
+static double qarea(const o3_ctx *c, int e, int d) { return c->h[3 * e + (d + 1) % 3] * c->h[3 * e + (d + 2) % 3] / 4.0; }
 
 static void push3(o3_nb **buf, int *n, int *cap, int j, int d, double cd, int face) {
     if (*n == *cap) { *cap = *cap ? 2 * *cap : 4096; *buf = realloc(*buf, sizeof(o3_nb) * (*cap)); }
@@ -247,92 +272,204 @@ static void push3(o3_nb **buf, int *n, int *cap, int j, int d, double cd, int fa
 
 void o3_destroy(o3_ctx *c) {
     if (!c) return;
-    free(c->nb_off); free(c->nb); free(c->g_node); free(c->g_side);
+    free(c->lev); free(c->ic); free(c->h); free(c->ftype); free(c->fnbr); free(c->fpos); free(c->mort);
+    free(c->nb_off); free(c->nb); free(c->g_node); free(c->g_side); free(c->mcount);
     free(c);
 }
 
-/* box = {x0, y0, z0, x1, y1, z1}; bc[6] per side; bc_prim[6][5] primitive
-   Dirichlet states (rho, v1, v2, v3, p). Opposite sides are both periodic or
-   neither. */
-o3_ctx *o3_create(int N, double gamma, int nx, int ny, int nz, const double *box, const int32_t *bc,
-                  const double *bc_prim, int *err) {
+typedef struct { int64_t key; int e; } lk3;
+static int cmp_lk3(const void *a, const void *b) {
+    int64_t x = ((const lk3 *)a)->key, y = ((const lk3 *)b)->key;
+    return x < y ? -1 : (x > y ? 1 : 0);
+}
+static int64_t key3(int l, int64_t x, int64_t y, int64_t z) { return ((int64_t)l << 57) | (x << 38) | (y << 19) | z; }
+static int find3(const lk3 *t, int K, int l, int64_t x, int64_t y, int64_t z) {
+    if (l < 0) return -1;
+    lk3 q; q.key = key3(l, x, y, z); q.e = -1;
+    const lk3 *r = bsearch(&q, t, K, sizeof(lk3), cmp_lk3);
+    return r ? r->e : -1;
+}
+
+/* element node of face node (a, b) on side s: idx[d] at the side, idx[d+1] = a,
+   idx[d+2] = b (tangential axes in cyclic order) */
+static void face_idx3(int np, int s, int a, int b, int *idx) {
+    int d = s / 2;
+    idx[d] = (s & 1) ? np - 1 : 0;
+    idx[(d + 1) % 3] = a;
+    idx[(d + 2) % 3] = b;
+}
+
+/* An octree: nx0 x ny0 x nz0 level-0 cells over box = {x0, y0, z0, x1, y1,
+   z1}; leaf e at level level[e] and position (ix, iy, iz)[e] on its level's
+   grid. bc[6] per side, bc_prim[6][5] primitive Dirichlet states. err: 1 bad
+   arguments, 2 not 2:1 balanced (or a gap). */
+o3_ctx *o3_create_leaves(int N, double gamma, int nx0, int ny0, int nz0, const double *box, int K,
+                         const int8_t *level, const int32_t *ix, const int32_t *iy, const int32_t *iz,
+                         const int32_t *bc, const double *bc_prim, int *err) {
     *err = 0;
-    if (N < 1 || N + 1 > NP3 || nx < 1 || ny < 1 || nz < 1) { *err = 1; return NULL; }
+    if (N < 1 || N + 1 > NP3 || nx0 < 1 || ny0 < 1 || nz0 < 1 || K < 1) { *err = 1; return NULL; }
     for (int d = 0; d < 3; ++d)
         if ((bc[2 * d] == B3_PERIODIC) != (bc[2 * d + 1] == B3_PERIODIC)) { *err = 1; return NULL; }
     o3_ctx *c = calloc(1, sizeof(o3_ctx));
-    c->N = N; c->np = N + 1; c->gamma = gamma; c->nx = nx; c->ny = ny; c->nz = nz;
-    int np = N + 1;
+    c->N = N; c->np = N + 1; c->gamma = gamma; c->K = K;
+    int np = N + 1, NR = np * np;
     {
         double xi[NP3], w[NP3], D[NP3 * NP3], S[NP3 * NP3], wt[NP3 * 2 * NP3], I[2 * NP3 * NP3], P[NP3 * 2 * NP3];
         orc_operators(N, 1, xi, w, D, S, wt, I, P);
         for (int a = 0; a < np; ++a) { c->xi[a] = xi[a]; c->w[a] = w[a]; }
         for (int a = 0; a < np; ++a) for (int b = 0; b < np; ++b) c->S[a][b] = S[a * np + b];
+        for (int a = 0; a < np; ++a)
+            for (int b = 0; b < 2 * np; ++b) { c->wt[a][b] = wt[a * 2 * np + b]; c->P[a][b] = P[a * 2 * np + b]; }
+        for (int a = 0; a < 2 * np; ++a) for (int b = 0; b < np; ++b) c->Ii[a][b] = I[a * np + b];
     }
-    c->x0 = box[0]; c->y0 = box[1]; c->z0 = box[2];
-    c->dx = (box[3] - box[0]) / nx; c->dy = (box[4] - box[1]) / ny; c->dz = (box[5] - box[2]) / nz;
+    c->n0[0] = nx0; c->n0[1] = ny0; c->n0[2] = nz0;
+    for (int k = 0; k < 6; ++k) c->box[k] = box[k];
     for (int s = 0; s < 6; ++s) { c->bc[s] = bc[s]; for (int v = 0; v < NV; ++v) c->bc_prim[s][v] = bc_prim[NV * s + v]; }
-    c->K = nx * ny * nz;
-    c->nn = c->K * np * np * np;
-    /* ghosts: one per boundary face node */
-    c->g_node = malloc(sizeof(int) * 6 * np * np * (size_t)(nx * ny + ny * nz + nx * nz) + sizeof(int));
-    c->g_side = malloc(sizeof(int) * 6 * np * np * (size_t)(nx * ny + ny * nz + nx * nz) + sizeof(int));
+    c->lev = malloc(sizeof(int) * K); c->ic = malloc(sizeof(int) * 3 * K); c->h = malloc(sizeof(double) * 3 * K);
+    lk3 *tab = malloc(sizeof(lk3) * K);
+    for (int e = 0; e < K; ++e) {
+        int l = level[e];
+        c->lev[e] = l; c->ic[3 * e] = ix[e]; c->ic[3 * e + 1] = iy[e]; c->ic[3 * e + 2] = iz[e];
+        for (int d = 0; d < 3; ++d) c->h[3 * e + d] = (box[3 + d] - box[d]) / ((double)c->n0[d] * (double)(1 << l));
+        tab[e].key = key3(l, ix[e], iy[e], iz[e]); tab[e].e = e;
+    }
+    qsort(tab, K, sizeof(lk3), cmp_lk3);
+    c->ftype = malloc(sizeof(int) * 6 * K); c->fnbr = malloc(sizeof(int) * 6 * K); c->fpos = malloc(sizeof(int) * 6 * K);
+    c->mort = malloc(sizeof(int) * 7 * 6 * K);
+    c->M = 0;
+    /* pass 1: conforming, boundary and large-side mortar faces */
+    for (int e = 0; e < K && !*err; ++e) {
+        int l = c->lev[e];
+        for (int s = 0; s < 6; ++s) {
+            int d = s / 2, side = s & 1, a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+            int64_t nl[3], q[3];
+            for (int a = 0; a < 3; ++a) { nl[a] = (int64_t)c->n0[a] << l; q[a] = c->ic[3 * e + a]; }
+            q[d] += side ? 1 : -1;
+            c->fpos[6 * e + s] = -1;
+            if (q[d] < 0 || q[d] >= nl[d]) {
+                if (bc[s] != B3_PERIODIC) { c->ftype[6 * e + s] = F3_BND; c->fnbr[6 * e + s] = -1; continue; }
+                q[d] = (q[d] + nl[d]) % nl[d];
+            }
+            int f = find3(tab, K, l, q[0], q[1], q[2]);
+            if (f >= 0) { c->ftype[6 * e + s] = F3_CONF; c->fnbr[6 * e + s] = f; continue; }
+            if (l > 0 && find3(tab, K, l - 1, q[0] >> 1, q[1] >> 1, q[2] >> 1) >= 0) {
+                c->ftype[6 * e + s] = F3_MS; c->fnbr[6 * e + s] = -1; continue;   /* filled in pass 2 */
+            }
+            /* four finer neighbours across the face */
+            int m = c->M, ok = 1;
+            int *mr = c->mort + 7 * m;
+            mr[0] = d; mr[1] = e; mr[2] = side;   /* large on the low side when its +d side is the face */
+            for (int p2 = 0; p2 < 2; ++p2)
+                for (int p1 = 0; p1 < 2; ++p1) {
+                    int64_t r[3];
+                    r[d] = 2 * q[d] + (side ? 0 : 1);
+                    r[a1] = 2 * q[a1] + p1;
+                    r[a2] = 2 * q[a2] + p2;
+                    int sm = find3(tab, K, l + 1, r[0], r[1], r[2]);
+                    if (sm < 0) ok = 0;
+                    mr[3 + p1 + 2 * p2] = sm;
+                }
+            if (!ok) { *err = 2; break; }
+            c->M++;
+            c->ftype[6 * e + s] = F3_ML; c->fnbr[6 * e + s] = m;
+        }
+    }
+    free(tab);
+    if (*err) { o3_destroy(c); return NULL; }
+    /* pass 2: small-side mortar faces */
+    for (int m = 0; m < c->M; ++m) {
+        int *mr = c->mort + 7 * m;
+        int s_small = 2 * mr[0] + (mr[2] ? 0 : 1);
+        for (int p = 0; p < 4; ++p) {
+            int e = mr[3 + p];
+            c->ftype[6 * e + s_small] = F3_MS; c->fnbr[6 * e + s_small] = m; c->fpos[6 * e + s_small] = p;
+        }
+    }
+    for (int e = 0; e < K; ++e) for (int s = 0; s < 6; ++s)
+        if (c->ftype[6 * e + s] == F3_MS && c->fnbr[6 * e + s] < 0) { *err = 2; o3_destroy(c); return NULL; }
+    /* global node graph with c_(i,j) (Sec. 2.1, Eq. c_nonconforming) */
+    c->nn = K * np * np * np;
     c->nb_off = malloc(sizeof(int) * (c->nn + 1));
+    c->mcount = calloc(c->nn, sizeof(int));
+    c->g_node = malloc(sizeof(int) * 6 * (size_t)NR * K);
+    c->g_side = malloc(sizeof(int) * 6 * (size_t)NR * K);
     o3_nb *buf = NULL;
     int cnt = 0, cap = 0;
-    double area[3] = {c->dy * c->dz / 4.0, c->dx * c->dz / 4.0, c->dx * c->dy / 4.0};   /* quarter face areas */
-    for (int ez = 0; ez < nz; ++ez) for (int ey = 0; ey < ny; ++ey) for (int ex = 0; ex < nx; ++ex) {
-        int e = (ez * ny + ey) * nx + ex;
-        int ec[3] = {ex, ey, ez}, en[3] = {nx, ny, nz};
+    for (int e = 0; e < K; ++e)
         for (int k = 0; k < np; ++k) for (int j = 0; j < np; ++j) for (int i = 0; i < np; ++i) {
             int g = g3(c, e, i, j, k), idx[3] = {i, j, k};
             c->nb_off[g] = cnt;
             for (int d = 0; d < 3; ++d) {
-                /* transverse weights of the node along direction d */
-                double wt = c->w[idx[(d + 1) % 3]] * c->w[idx[(d + 2) % 3]];
-                double cd = wt * area[d] / 2.0;   /* |c_ij| of the subcell and face pairs */
-                int pos = idx[d];
+                int a1 = (d + 1) % 3, a2 = (d + 2) % 3, t1 = idx[a1], t2 = idx[a2], pos = idx[d];
+                double cd = c->w[t1] * c->w[t2] * qarea(c, e, d) / 2.0;   /* |c_ij| of subcell and conforming pairs */
                 /* subcell neighbours (Sec. 2.1) */
-                if (pos > 0) {
-                    int q[3] = {i, j, k}; q[d] -= 1;
-                    push3(&buf, &cnt, &cap, g3(c, e, q[0], q[1], q[2]), d, -cd, 0);
-                }
-                if (pos < N) {
-                    int q[3] = {i, j, k}; q[d] += 1;
-                    push3(&buf, &cnt, &cap, g3(c, e, q[0], q[1], q[2]), d, cd, 0);
-                }
-                /* face neighbours: the matching node of the element across */
+                if (pos > 0) { int qq[3] = {i, j, k}; qq[d] -= 1; push3(&buf, &cnt, &cap, g3v(c, e, qq), d, -cd, 0); }
+                if (pos < N) { int qq[3] = {i, j, k}; qq[d] += 1; push3(&buf, &cnt, &cap, g3v(c, e, qq), d, cd, 0); }
                 for (int side = 0; side < 2; ++side) {
                     if ((side == 0 && pos != 0) || (side == 1 && pos != N)) continue;
-                    int s = 2 * d + side;
-                    int nc[3] = {ec[0], ec[1], ec[2]};
-                    nc[d] += side == 0 ? -1 : 1;
-                    int out = nc[d] < 0 || nc[d] >= en[d];
-                    double cs = side == 0 ? -cd : cd;
-                    if (out && bc[s] != B3_PERIODIC) {
+                    int s = 2 * d + side, ft = c->ftype[6 * e + s];
+                    double sg = side ? 1.0 : -1.0;   /* outward normal along d */
+                    if (ft == F3_CONF) {
+                        int qq[3] = {i, j, k}; qq[d] = side ? 0 : N;
+                        push3(&buf, &cnt, &cap, g3v(c, c->fnbr[6 * e + s], qq), d, sg * cd, 1);
+                    } else if (ft == F3_BND) {
                         c->g_node[c->ng] = g; c->g_side[c->ng] = s;
-                        push3(&buf, &cnt, &cap, -1 - c->ng, d, cs, 1);
+                        push3(&buf, &cnt, &cap, -1 - c->ng, d, sg * cd, 1);
                         c->ng++;
-                        continue;
+                    } else if (ft == F3_ML) {
+                        int m = c->fnbr[6 * e + s];
+                        const int *mr = c->mort + 7 * m;
+                        double qa = qarea(c, e, d);
+                        c->mcount[g]++;
+                        for (int p2 = 0; p2 < 2; ++p2) for (int p1 = 0; p1 < 2; ++p1)
+                            for (int l2 = 0; l2 < np; ++l2) for (int l1 = 0; l1 < np; ++l1) {
+                                double wgt = c->wt[t1][p1 * np + l1] * c->wt[t2][p2 * np + l2];
+                                if (wgt == 0.0) continue;
+                                int qq[3];
+                                face_idx3(np, s ^ 1, l1, l2, qq);
+                                push3(&buf, &cnt, &cap, g3v(c, mr[3 + p1 + 2 * p2], qq), d, sg * wgt * qa / 2.0, 2);
+                            }
+                    } else {
+                        int m = c->fnbr[6 * e + s], p = c->fpos[6 * e + s], p1 = p & 1, p2 = p >> 1;
+                        const int *mr = c->mort + 7 * m;
+                        int L = mr[1];
+                        double qa = qarea(c, L, d);
+                        c->mcount[g]++;
+                        for (int k2 = 0; k2 < np; ++k2) for (int k1 = 0; k1 < np; ++k1) {
+                            double wgt = c->wt[k1][p1 * np + t1] * c->wt[k2][p2 * np + t2];
+                            if (wgt == 0.0) continue;
+                            int qq[3];
+                            face_idx3(np, s ^ 1, k1, k2, qq);
+                            push3(&buf, &cnt, &cap, g3v(c, L, qq), d, sg * wgt * qa / 2.0, 2);
+                        }
                     }
-                    nc[d] = (nc[d] + en[d]) % en[d];
-                    int f = (nc[2] * ny + nc[1]) * nx + nc[0];
-                    int q[3] = {i, j, k}; q[d] = side == 0 ? N : 0;
-                    push3(&buf, &cnt, &cap, g3(c, f, q[0], q[1], q[2]), d, cs, 1);
                 }
             }
         }
-    }
     c->nb_off[c->nn] = cnt;
     c->nb = buf;
     return c;
 }
 
+/* a uniform grid: all leaves at level 0, e = (ez ny + ey) nx + ex */
+o3_ctx *o3_create(int N, double gamma, int nx, int ny, int nz, const double *box, const int32_t *bc,
+                  const double *bc_prim, int *err) {
+    if (nx < 1 || ny < 1 || nz < 1) { *err = 1; return NULL; }
+    int K = nx * ny * nz;
+    int8_t *lev = calloc(K, 1);
+    int32_t *ix = malloc(sizeof(int32_t) * K), *iy = malloc(sizeof(int32_t) * K), *iz = malloc(sizeof(int32_t) * K);
+    for (int e = 0; e < K; ++e) { ix[e] = e % nx; iy[e] = (e / nx) % ny; iz[e] = e / (nx * ny); }
+    o3_ctx *c = o3_create_leaves(N, gamma, nx, ny, nz, box, K, lev, ix, iy, iz, bc, bc_prim, err);
+    free(lev); free(ix); free(iy); free(iz);
+    return c;
+}
+
 int o3_n_nodes(const o3_ctx *c) { return c->nn; }
+int o3_n_mortars(const o3_ctx *c) { return c->M; }
 
 static double mass3(const o3_ctx *c, int g) {
-    int np = c->np, i = g % np, j = (g / np) % np, k = (g / (np * np)) % np;
-    return c->w[i] * c->w[j] * c->w[k] * c->dx * c->dy * c->dz / 8.0;
+    int np = c->np, e = g / (np * np * np), i = g % np, j = (g / np) % np, k = (g / (np * np)) % np;
+    return c->w[i] * c->w[j] * c->w[k] * c->h[3 * e] * c->h[3 * e + 1] * c->h[3 * e + 2] / 8.0;
 }
 
 static void get3(const o3_ctx *c, const double *u, int g, double *q) {
@@ -368,43 +505,180 @@ static void node_or_ghost3(const o3_ctx *c, const double *u, int j, double *q) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* mortars                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* mortar m: the nodes of its large face (k1 + np k2) and of its small faces
+   p (np^2 + p np^2 + l1 + np l2) */
+static void mortar_nodes3(const o3_ctx *c, int m, int *gnode) {
+    int np = c->np, NR = np * np;
+    const int *mr = c->mort + 7 * m;
+    int sL = 2 * mr[0] + mr[2], sS = sL ^ 1;
+    for (int b = 0; b < np; ++b) for (int a = 0; a < np; ++a) {
+        int qq[3];
+        face_idx3(np, sL, a, b, qq);
+        gnode[a + np * b] = g3v(c, mr[1], qq);
+        face_idx3(np, sS, a, b, qq);
+        for (int p = 0; p < 4; ++p) gnode[NR + p * NR + a + np * b] = g3v(c, mr[3 + p], qq);
+    }
+}
+
+/* outward low-order sparse fluxes of Eq. interfaceflux_local at the mortar's
+   nodes (mass-weighted), with the weights of reading R32 */
+static void mortar_low3(const o3_ctx *c, const double *u, int m, double Flo[][NV]) {
+    int np = c->np, NR = np * np;
+    double gm = c->gamma;
+    const int *mr = c->mort + 7 * m;
+    int d = mr[0], low = mr[2];
+    double nL = low ? 1.0 : -1.0, qa = qarea(c, mr[1], d);
+    int gnode[5 * NP3 * NP3];
+    mortar_nodes3(c, m, gnode);
+    for (int q = 0; q < 5 * NR; ++q) for (int v = 0; v < NV; ++v) Flo[q][v] = 0.0;
+    for (int k2 = 0; k2 < np; ++k2) for (int k1 = 0; k1 < np; ++k1)
+        for (int p2 = 0; p2 < 2; ++p2) for (int p1 = 0; p1 < 2; ++p1)
+            for (int l2 = 0; l2 < np; ++l2) for (int l1 = 0; l1 < np; ++l1) {
+                double wgt = c->wt[k1][p1 * np + l1] * c->wt[k2][p2 * np + l2] * qa;
+                if (wgt == 0.0) continue;
+                int qi = k1 + np * k2, qj = NR + (p1 + 2 * p2) * NR + l1 + np * l2;
+                double ui[NV], uj[NV], fi[NV], fj[NV];
+                get3(c, u, gnode[qi], ui); get3(c, u, gnode[qj], uj);
+                flux3(gm, ui, d, fi); flux3(gm, uj, d, fj);
+                double lam = lambda3(gm, ui, uj, d);
+                for (int v = 0; v < NV; ++v) {
+                    Flo[qi][v] += 0.5 * (wgt * nL * (fi[v] + fj[v]) - wgt * lam * (uj[v] - ui[v]));
+                    Flo[qj][v] += 0.5 * (-wgt * nL * (fi[v] + fj[v]) - wgt * lam * (ui[v] - uj[v]));
+                }
+            }
+}
+
+/* Surface fluxes of every element side, the +d numerical flux times the
+   side's quarter area per face node: sf[e][s][a + np b][v]. Mortars: R5 as
+   tensor products (interpolate to the small-face nodes, LLF there, exact L2
+   projection back); R16: a mortar whose interpolated states are not
+   admissible uses its low-order sparse flux and is flagged in mbad. With
+   conforming = 0 only the mortar sides are formed (the limited stage takes
+   its conforming and boundary faces from the graph, where the LLF flux is
+   the low-order face term itself). */
+static double *surface_fluxes3(const o3_ctx *c, const double *u, char *mbad, int conforming) {
+    int np = c->np, NR = np * np, K = c->K;
+    double g = c->gamma;
+    double *sf = calloc((size_t)K * 6 * NR * NV, sizeof(double));
+    ORC_ROW(ROW_FACE_FLUX);
+    for (int e = 0; e < K && conforming; ++e)
+        for (int s = 0; s < 6; ++s) {
+            int ft = c->ftype[6 * e + s], d = s / 2, side = s & 1;
+            if (ft == F3_ML || ft == F3_MS) continue;
+            double qa = qarea(c, e, d);
+            for (int b = 0; b < np; ++b) for (int a = 0; a < np; ++a) {
+                int qq[3];
+                face_idx3(np, s, a, b, qq);
+                double in[NV], out[NV], f[NV];
+                get3(c, u, g3v(c, e, qq), in);
+                if (ft == F3_CONF) {
+                    int qo[3];
+                    face_idx3(np, s ^ 1, a, b, qo);
+                    get3(c, u, g3v(c, c->fnbr[6 * e + s], qo), out);
+                } else {
+                    ghost3(c, in, s, out);
+                }
+                if (side) o3_llf(g, in, out, d, f); else o3_llf(g, out, in, d, f);
+                for (int v = 0; v < NV; ++v) sf[((size_t)(6 * e + s) * NR + a + np * b) * NV + v] = qa * f[v];
+            }
+        }
+    for (int m = 0; m < c->M; ++m) {
+        ORC_ROW(ROW_MORTAR_FLUX);
+        const int *mr = c->mort + 7 * m;
+        int d = mr[0], L = mr[1], low = mr[2], sL = 2 * d + low, sS = sL ^ 1;
+        double qaL = qarea(c, L, d), qaS = qaL / 4.0;
+        double uL[NP3 * NP3][NV];
+        for (int b = 0; b < np; ++b) for (int a = 0; a < np; ++a) {
+            int qq[3];
+            face_idx3(np, sL, a, b, qq);
+            get3(c, u, g3v(c, L, qq), uL[a + np * b]);
+        }
+        /* interpolated large-side states on each small face */
+        double ui[4][NP3 * NP3][NV];
+        int bad = 0;
+        for (int p = 0; p < 4; ++p)
+            for (int l2 = 0; l2 < np; ++l2) for (int l1 = 0; l1 < np; ++l1) {
+                double *x = ui[p][l1 + np * l2];
+                for (int v = 0; v < NV; ++v) x[v] = 0.0;
+                for (int k2 = 0; k2 < np; ++k2) for (int k1 = 0; k1 < np; ++k1) {
+                    double wgt = c->Ii[(p & 1) * np + l1][k1] * c->Ii[(p >> 1) * np + l2][k2];
+                    for (int v = 0; v < NV; ++v) x[v] += wgt * uL[k1 + np * k2][v];
+                }
+                if (!(x[0] > 0.0) || !(pressure3(g, x) > 0.0)) bad = 1;
+            }
+        if (mbad) mbad[m] = (char)bad;
+        if (bad) {
+            double Flo[5 * NP3 * NP3][NV];
+            mortar_low3(c, u, m, Flo);
+            for (int b = 0; b < np; ++b) for (int a = 0; a < np; ++a) {
+                double wk = c->w[a] * c->w[b];
+                for (int v = 0; v < NV; ++v)
+                    sf[((size_t)(6 * L + sL) * NR + a + np * b) * NV + v] = (low ? 1.0 : -1.0) * Flo[a + np * b][v] / wk;
+                for (int p = 0; p < 4; ++p)
+                    for (int v = 0; v < NV; ++v)
+                        sf[((size_t)(6 * mr[3 + p] + sS) * NR + a + np * b) * NV + v] =
+                            (low ? -1.0 : 1.0) * Flo[NR + p * NR + a + np * b][v] / wk;
+            }
+            continue;
+        }
+        double fs[4][NP3 * NP3][NV];
+        for (int p = 0; p < 4; ++p)
+            for (int b = 0; b < np; ++b) for (int a = 0; a < np; ++a) {
+                int qq[3];
+                face_idx3(np, sS, a, b, qq);
+                double us[NV], f[NV];
+                get3(c, u, g3v(c, mr[3 + p], qq), us);
+                if (low) o3_llf(g, ui[p][a + np * b], us, d, f); else o3_llf(g, us, ui[p][a + np * b], d, f);
+                for (int v = 0; v < NV; ++v) {
+                    fs[p][a + np * b][v] = f[v];
+                    sf[((size_t)(6 * mr[3 + p] + sS) * NR + a + np * b) * NV + v] = qaS * f[v];
+                }
+            }
+        for (int k2 = 0; k2 < np; ++k2) for (int k1 = 0; k1 < np; ++k1)
+            for (int v = 0; v < NV; ++v) {
+                double acc = 0.0;
+                for (int p = 0; p < 4; ++p)
+                    for (int l2 = 0; l2 < np; ++l2) for (int l1 = 0; l1 < np; ++l1)
+                        acc += c->P[k1][(p & 1) * np + l1] * c->P[k2][(p >> 1) * np + l2] * fs[p][l1 + np * l2][v];
+                sf[((size_t)(6 * L + sL) * NR + k1 + np * k2) * NV + v] = qaL * acc;
+            }
+    }
+    return sf;
+}
+
+/* ------------------------------------------------------------------------ */
 /* residuals                                                                 */
 /* ------------------------------------------------------------------------ */
 
 /* mass-weighted high-order residual (Eq. evolutionformula in 3D): per node
-   sum over d of (transverse weights) ( -sum_l Sbar_(pos,l) (A_d/4) f*_d(u, u_l)
-   + surface LLF terms at the element's faces ) */
-static void dg_residual3(const o3_ctx *c, const double *u, double *res) {
-    int np = c->np, N = c->N;
+   the sum over d of the transverse weights times ( -sum_l Sbar_(pos,l) (A_d/4)
+   f*_d(u, u_l) + the surface terms of the element's faces ) */
+static void dg_residual3(const o3_ctx *c, const double *u, const double *sf, double *res) {
+    int np = c->np, N = c->N, NR = np * np;
     double g = c->gamma;
-    double area[3] = {c->dy * c->dz / 4.0, c->dx * c->dz / 4.0, c->dx * c->dy / 4.0};
     for (int e = 0; e < c->K; ++e)
         for (int k = 0; k < np; ++k) for (int j = 0; j < np; ++j) for (int i = 0; i < np; ++i) {
             int gi = g3(c, e, i, j, k), idx[3] = {i, j, k};
             double ui[NV], tot[NV] = {0, 0, 0, 0, 0};
             get3(c, u, gi, ui);
             for (int d = 0; d < 3; ++d) {
-                double F[NV] = {0, 0, 0, 0, 0};
-                int pos = idx[d];
+                double F[NV] = {0, 0, 0, 0, 0}, qa = qarea(c, e, d);
+                int pos = idx[d], t1 = idx[(d + 1) % 3], t2 = idx[(d + 2) % 3];
                 for (int l = 0; l < np; ++l) {
                     if (l == pos) continue;   /* Sbar has a zero diagonal */
                     int q[3] = {i, j, k}; q[d] = l;
                     double ul[NV], f[NV];
-                    get3(c, u, g3(c, e, q[0], q[1], q[2]), ul);
+                    get3(c, u, g3v(c, e, q), ul);
                     o3_ranocha(g, ui, ul, d, f);
-                    for (int v = 0; v < NV; ++v) F[v] -= c->S[pos][l] * area[d] * f[v];
+                    for (int v = 0; v < NV; ++v) F[v] -= c->S[pos][l] * qa * f[v];
                 }
-                /* surface terms: the graph holds two entries per direction
-                   (pushed low, high, then the face), so at pos 0 or N the
-                   face neighbour is the direction's second entry */
-                for (int side = 0; side < 2; ++side) {
-                    if ((side == 0 && pos != 0) || (side == 1 && pos != N)) continue;
-                    double out[NV], f[NV];
-                    node_or_ghost3(c, u, c->nb[c->nb_off[gi] + 2 * d + 1].j, out);
-                    if (side == 0) { o3_llf(g, out, ui, d, f); for (int v = 0; v < NV; ++v) F[v] += area[d] * f[v]; }
-                    else { o3_llf(g, ui, out, d, f); for (int v = 0; v < NV; ++v) F[v] -= area[d] * f[v]; }
-                }
-                double wt = c->w[idx[(d + 1) % 3]] * c->w[idx[(d + 2) % 3]];
+                int t = t1 + np * t2;
+                if (pos == 0) for (int v = 0; v < NV; ++v) F[v] += sf[((size_t)(6 * e + 2 * d) * NR + t) * NV + v];
+                if (pos == N) for (int v = 0; v < NV; ++v) F[v] -= sf[((size_t)(6 * e + 2 * d + 1) * NR + t) * NV + v];
+                double wt = c->w[t1] * c->w[t2];
                 for (int v = 0; v < NV; ++v) tot[v] += wt * F[v];
             }
             for (int v = 0; v < NV; ++v) res[(size_t)v * c->nn + gi] = tot[v];
@@ -416,19 +690,19 @@ static void dg_residual3(const o3_ctx *c, const double *u, double *res) {
    the row is fixed by the node (i, j, k) with its d index ignored */
 static void dg_subcell_row3(const o3_ctx *c, const double *u, int e, int d, const int *idx, double fh[][NV]) {
     int np = c->np, N = c->N;
-    double area[3] = {c->dy * c->dz / 4.0, c->dx * c->dz / 4.0, c->dx * c->dy / 4.0};
+    double qa = qarea(c, e, d);
     double acc[NV] = {0, 0, 0, 0, 0};
     for (int l = 0; l < N; ++l) {
-        int qa[3] = {idx[0], idx[1], idx[2]}; qa[d] = l;
+        int qa_[3] = {idx[0], idx[1], idx[2]}; qa_[d] = l;
         double ua[NV];
-        get3(c, u, g3(c, e, qa[0], qa[1], qa[2]), ua);
+        get3(c, u, g3v(c, e, qa_), ua);
         for (int m = 0; m < np; ++m) {
             if (m == l) continue;
             int qm[3] = {idx[0], idx[1], idx[2]}; qm[d] = m;
             double um[NV], f[NV];
-            get3(c, u, g3(c, e, qm[0], qm[1], qm[2]), um);
+            get3(c, u, g3v(c, e, qm), um);
             o3_ranocha(c->gamma, ua, um, d, f);
-            for (int v = 0; v < NV; ++v) acc[v] += c->S[l][m] * area[d] * f[v];
+            for (int v = 0; v < NV; ++v) acc[v] += c->S[l][m] * qa * f[v];
         }
         for (int v = 0; v < NV; ++v) fh[l][v] = acc[v];
     }
@@ -444,7 +718,7 @@ static void fv_residual3(const o3_ctx *c, const double *u, double *res, double *
         for (int b = c->nb_off[i]; b < c->nb_off[i + 1]; ++b) {
             const o3_nb *nb = &c->nb[b];
             int d = nb->c[0] != 0.0 ? 0 : (nb->c[1] != 0.0 ? 1 : 2);
-            ORC_ROW(nb->face ? ROW_FACE_FLUX : ROW_SUBCELL_FV);
+            ORC_ROW(nb->face == 2 ? ROW_MORTAR_FLUX : nb->face ? ROW_FACE_FLUX : ROW_SUBCELL_FV);
             double uj[NV], f[NV];
             node_or_ghost3(c, u, nb->j, uj);
             flux3(g, uj, d, f);
@@ -452,6 +726,7 @@ static void fv_residual3(const o3_ctx *c, const double *u, double *res, double *
             for (int v = 0; v < NV; ++v) acc[v] += -nb->c[d] * f[v] + dd * (uj[v] - ui[v]);
             s2d += 2.0 * dd;
         }
+        ORC_ROW(ROW_SUBCELL_FV);
         for (int v = 0; v < NV; ++v) res[(size_t)v * c->nn + i] = acc[v];
         if (dsum) dsum[i] = s2d;
     }
@@ -487,8 +762,17 @@ void o3_set_force_ell(double v) { g_force3 = v; }
 /* test hooks: per node [u_FV (5), rho_min, rho_max, p_min, R+, R-] and per
    interface [left node, right node, exempt, Zalesak factor, theta_left,
    theta_right, factor, A (5)] of the next limited stage */
-static double *g_node3 = NULL, *g_iface3 = NULL;
+static double *g_node3 = NULL, *g_iface3 = NULL, *g_mortar3 = NULL, *g_mrec3 = NULL;
 void o3_set_dbg_out(double *node, double *iface) { g_node3 = node; g_iface3 = iface; }
+/* test hooks: each mortar's factor l_S of the next limited stage and, per
+   mortar node (large face, then the small faces p = p1 + 2 p2, each face's
+   nodes a + (N+1) b), [node, u_vol (5), n_i dt/m_i H (5), rho_min, rho_max,
+   p_min, n_i, H (5)] */
+void o3_set_mortar_out(double *ell, double *rec) { g_mortar3 = ell; g_mrec3 = rec; }
+
+/* the mortar table: per mortar [d, large element, large on the low side,
+   small elements p = 0..3] */
+void o3_mortar_table(const o3_ctx *c, int *out) { for (int k = 0; k < 7 * c->M; ++k) out[k] = c->mort[k]; }
 
 /* interface id of the subcell interface between positions a and a+1 along d
    in the row of node idx of element e */
@@ -506,14 +790,19 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
 #ifdef ORC_COUNTING
     o3_count_node_prep(c, u);
 #endif
-    double *rdg = malloc(sizeof(double) * NV * (size_t)nn);
-    if (dt == 0.0 || limiting == 0) {
-        dg_residual3(c, u, rdg);
+    char *mbad = calloc(c->M + 1, 1);
+    int high = dt == 0.0 || limiting == 0;
+    double *sf = surface_fluxes3(c, u, mbad, high);
+    if (high) {
+        double *rdg = malloc(sizeof(double) * NV * (size_t)nn);
+        ORC_ROW(ROW_VOLUME_FLUX);
+        dg_residual3(c, u, sf, rdg);
+        ORC_ROW(ROW_STAGE);
         for (size_t k = 0; k < (size_t)NV * nn; ++k) res_out[k] = rdg[k];
         if (utilde)
             for (int i = 0; i < nn; ++i) for (int v = 0; v < NV; ++v)
                 utilde[(size_t)v * nn + i] = u[(size_t)v * nn + i] + dt / mass3(c, i) * rdg[(size_t)v * nn + i];
-        free(rdg);
+        free(rdg); free(sf); free(mbad);
         return 0;
     }
     double *rfv = malloc(sizeof(double) * NV * (size_t)nn), *ds = malloc(sizeof(double) * nn);
@@ -551,7 +840,6 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
        interfaces, mass-weighted; node a gets -l A, node a+1 +l A */
     int nif = K * 3 * np * np * N;
     double *A = malloc(sizeof(double) * NV * (size_t)nif);
-    double area[3] = {c->dy * c->dz / 4.0, c->dx * c->dz / 4.0, c->dx * c->dy / 4.0};
     for (int e = 0; e < K; ++e)
         for (int d = 0; d < 3; ++d)
             for (int t2 = 0; t2 < np; ++t2) for (int t1 = 0; t1 < np; ++t1) {
@@ -560,7 +848,7 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
                 double fh[NP3][NV];
                 ORC_ROW(ROW_VOLUME_FLUX);
                 dg_subcell_row3(c, u, e, d, idx, fh);
-                double wt = c->w[t1] * c->w[t2], cc = wt * area[d] / 2.0;
+                double wt = c->w[t1] * c->w[t2], cc = wt * qarea(c, e, d) / 2.0;
                 for (int a = 0; a < N; ++a) {
                     int ql[3] = {idx[0], idx[1], idx[2]}, qr[3] = {idx[0], idx[1], idx[2]};
                     ql[d] = a; qr[d] = a + 1;
@@ -661,31 +949,114 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
             for (int v = 0; v < NV; ++v) o[v] = ufv[(size_t)v * nn + i];
             o[5] = rmin[i]; o[6] = rmax[i]; o[7] = pmin[i]; o[8] = Rp[i]; o[9] = Rm[i];
         }
-    /* limited residual and stage state; violations (R13) */
+    /* volume-corrected state u_vol = u_FV + dt/m sum l A */
+    double *uvol = malloc(sizeof(double) * NV * (size_t)nn), *acc = calloc(NV * (size_t)nn, sizeof(double));
     for (int i = 0; i < nn; ++i) {
         int e = i / (np * np * np), rr = i % (np * np * np);
         int idx[3] = {rr % np, (rr / np) % np, rr / (np * np)};
-        double s[NV] = {0, 0, 0, 0, 0};
+        double sv[NV] = {0, 0, 0, 0, 0};
         ORC_ROW(ROW_VOLUME_LIMIT);
         /* the node's interfaces in a fixed order: x low, x high, y low, y high, z low, z high */
         for (int d = 0; d < 3; ++d) {
             int pos = idx[d];
-            if (pos > 0) { int id = iface3(c, e, d, idx, pos - 1); for (int v = 0; v < NV; ++v) s[v] += ell[id] * A[(size_t)NV * id + v]; }
-            if (pos < N) { int id = iface3(c, e, d, idx, pos); for (int v = 0; v < NV; ++v) s[v] -= ell[id] * A[(size_t)NV * id + v]; }
+            if (pos > 0) { int id = iface3(c, e, d, idx, pos - 1); for (int v = 0; v < NV; ++v) sv[v] += ell[id] * A[(size_t)NV * id + v]; }
+            if (pos < N) { int id = iface3(c, e, d, idx, pos); for (int v = 0; v < NV; ++v) sv[v] -= ell[id] * A[(size_t)NV * id + v]; }
         }
+        double m = mass3(c, i);
+        for (int v = 0; v < NV; ++v) {
+            acc[(size_t)v * nn + i] = sv[v];
+            uvol[(size_t)v * nn + i] = ufv[(size_t)v * nn + i] + dt / m * sv[v];
+        }
+        ORC_ROW(ROW_STATS);
+        if (stats) {
+            stats[S3_AVOL_M] += m * (1.0 - lmin[i]);
+            stats[S3_M] += m;
+            if (lmin[i] < 1.0) stats[S3_NVOL] += 1;
+        }
+    }
+    /* R9: mortar limiting after the volume correction. Per mortar node the
+       high-order (R5) and low-order outward fluxes; H = -(F_L2 - F_lo) is the
+       antidiffusive contribution; one factor per mortar with the n_i budget */
+    double *corr = calloc(NV * (size_t)nn, sizeof(double));
+    int NR = np * np;
+    for (int m = 0; m < c->M; ++m) {
+        ORC_ROW(ROW_MORTAR_LIMIT);
+        const int *mr = c->mort + 7 * m;
+        int d = mr[0], L = mr[1], low = mr[2], sL = 2 * d + low, sS = sL ^ 1;
+        int gnode[5 * NP3 * NP3];
+        double H[5 * NP3 * NP3][NV], Flo[5 * NP3 * NP3][NV];
+        mortar_nodes3(c, m, gnode);
+        ORC_ROW(ROW_REFORM);
+        mortar_low3(c, u, m, Flo);
+        ORC_ROW(ROW_MORTAR_LIMIT);
+        for (int b = 0; b < np; ++b) for (int a = 0; a < np; ++a) {
+            double wk = c->w[a] * c->w[b];
+            int t = a + np * b;
+            for (int v = 0; v < NV; ++v) {
+                double FL2 = (low ? 1.0 : -1.0) * wk * sf[((size_t)(6 * L + sL) * NR + t) * NV + v];
+                H[t][v] = -(FL2 - Flo[t][v]);
+            }
+            for (int p = 0; p < 4; ++p)
+                for (int v = 0; v < NV; ++v) {
+                    double FL2 = (low ? -1.0 : 1.0) * wk * sf[((size_t)(6 * mr[3 + p] + sS) * NR + t) * NV + v];
+                    H[NR + p * NR + t][v] = -(FL2 - Flo[NR + p * NR + t][v]);
+                }
+        }
+        double lS = 1.0;
+        if (mbad[m]) {
+            /* R16: no admissible high-order flux, pure low order */
+            for (int q = 0; q < 5 * NR; ++q) for (int v = 0; v < NV; ++v) H[q][v] = 0.0;
+            lS = 0.0;
+        }
+        for (int q = 0; q < 5 * NR && !mbad[m]; ++q) {
+            int i = gnode[q];
+            double mi = mass3(c, i), ni = (double)c->mcount[i], tolr = TOL3 * fabs(ufv[i]);
+            double u0[NV], av[NV];
+            for (int v = 0; v < NV; ++v) { u0[v] = uvol[(size_t)v * nn + i]; av[v] = ni * dt / mi * H[q][v]; }
+            double lr = 1.0;
+            if (av[0] > 0.0) { double t = (rmax[i] + tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
+            else if (av[0] < 0.0) { double t = (rmin[i] - tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
+            if (lr < 0.0) lr = 0.0;
+            double th = o3_theta(gm, u0, av, pmin[i] - TOL3 * fabs(pmin[i]), lr);
+            if (th < lS) lS = th;
+        }
+        for (int q = 0; q < 5 * NR && g_mrec3; ++q) {
+            int i = gnode[q];
+            double ni = (double)c->mcount[i], *o = g_mrec3 + ((size_t)m * 5 * NR + q) * 20;
+            o[0] = i;
+            for (int v = 0; v < NV; ++v) {
+                o[1 + v] = uvol[(size_t)v * nn + i];
+                o[6 + v] = ni * dt / mass3(c, i) * H[q][v];
+                o[15 + v] = H[q][v];
+            }
+            o[11] = rmin[i]; o[12] = rmax[i]; o[13] = pmin[i]; o[14] = ni;
+        }
+        if (g_force3 >= 0.0) lS = g_force3;
+        if (g_mortar3) g_mortar3[m] = lS;
+        for (int q = 0; q < 5 * NR; ++q) {
+            int i = gnode[q];
+            for (int v = 0; v < NV; ++v) corr[(size_t)v * nn + i] += lS * H[q][v];
+        }
+        ORC_ROW(ROW_STATS);
+        if (stats) {
+            double area = 4.0 * qarea(c, L, d);
+            stats[S3_AMORT_A] += area * (1.0 - lS);
+            stats[S3_A] += area;
+            if (lS < 1.0) stats[S3_NMORT] += 1;
+        }
+    }
+    /* limited residual and stage state; violations (R13) */
+    for (int i = 0; i < nn; ++i) {
         double m = mass3(c, i), q[NV];
         ORC_ROW(ROW_STAGE);
         for (int v = 0; v < NV; ++v) {
-            res_out[(size_t)v * nn + i] = rfv[(size_t)v * nn + i] + s[v];
-            q[v] = ufv[(size_t)v * nn + i] + dt / m * s[v];
+            res_out[(size_t)v * nn + i] = rfv[(size_t)v * nn + i] + acc[(size_t)v * nn + i] + corr[(size_t)v * nn + i];
+            q[v] = uvol[(size_t)v * nn + i] + dt / m * corr[(size_t)v * nn + i];
             if (utilde) utilde[(size_t)v * nn + i] = q[v];
         }
         ORC_ROW(ROW_STATS);
         if (stats) {
             double p = pressure3(gm, q);
-            stats[S3_AVOL_M] += m * (1.0 - lmin[i]);
-            stats[S3_M] += m;
-            if (lmin[i] < 1.0) stats[S3_NVOL] += 1;
             if (q[0] < rmin[i] - 1e-13 * fabs(rmin[i]) || q[0] > rmax[i] + 1e-13 * fabs(rmax[i])) stats[S3_VRHO] += 1;
             if (p < pmin[i] - 1e-13 * fabs(pmin[i])) stats[S3_VP] += 1;
             if (!(q[0] > 0.0) || !(p > 0.0)) stats[S3_NONPOS] += 1;
@@ -693,7 +1064,8 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
             if (p < stats[S3_MINP]) stats[S3_MINP] = p;
         }
     }
-    free(rdg); free(rfv); free(ds); free(ufv); free(rmin); free(rmax); free(pmin); free(A); free(exempt);
+    free(uvol); free(acc); free(corr); free(sf); free(mbad);
+    free(rfv); free(ds); free(ufv); free(rmin); free(rmax); free(pmin); free(A); free(exempt);
     free(Rp); free(Rm); free(ell); free(lmin);
     return 0;
 }
@@ -748,5 +1120,9 @@ void o3_integrals(const o3_ctx *c, const double *u, double *out) {
 void o3_masses(const o3_ctx *c, double *m) { for (int i = 0; i < c->nn; ++i) m[i] = mass3(c, i); }
 
 /* the two residuals alone (pins) */
-void o3_dg_residual(const o3_ctx *c, const double *u, double *res) { dg_residual3(c, u, res); }
+void o3_dg_residual(const o3_ctx *c, const double *u, double *res) {
+    double *sf = surface_fluxes3(c, u, NULL, 1);
+    dg_residual3(c, u, sf, res);
+    free(sf);
+}
 void o3_fv_residual(const o3_ctx *c, const double *u, double *res, double *dsum) { fv_residual3(c, u, res, dsum); }

@@ -25,7 +25,7 @@ _lib = None
 
 BC_PERIODIC, BC_WALL, BC_DIRICHLET, BC_OUTFLOW = 0, 1, 2, 3
 ST_NAMES = ["alpha_vol_m", "mass", "n_vol_active", "viol_rho", "viol_p", "nonpositive", "dt_exceed",
-            "min_rho", "min_p"]
+            "min_rho", "min_p", "alpha_mort_a", "mort_area", "n_mort_active"]
 _FLAGS = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC", "-shared"]
 
 
@@ -51,6 +51,13 @@ def load(path: str):
     dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
     L.o3_create.restype = C.c_void_p
     L.o3_create.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, ip, dp, C.POINTER(C.c_int)]
+    L.o3_create_leaves.restype = C.c_void_p
+    L.o3_create_leaves.argtypes = [C.c_int, C.c_double, C.c_int, C.c_int, C.c_int, dp, C.c_int, C.POINTER(C.c_int8),
+                                   ip, ip, ip, ip, dp, C.POINTER(C.c_int)]
+    L.o3_n_mortars.restype = C.c_int
+    L.o3_n_mortars.argtypes = [C.c_void_p]
+    L.o3_set_mortar_out.argtypes = [dp, dp]
+    L.o3_mortar_table.argtypes = [C.c_void_p, ip]
     L.o3_destroy.argtypes = [C.c_void_p]
     L.o3_n_nodes.restype = C.c_int
     L.o3_n_nodes.argtypes = [C.c_void_p]
@@ -103,8 +110,9 @@ def _d(a):
 
 
 class Oracle3D:
-    """The 3D oracle on a grid with the attributes nx, ny, nz, box, bc,
-    bc_prim and n_elems (workloads.Grid3)."""
+    """The 3D oracle on a uniform grid (attributes nx, ny, nz, box, bc,
+    bc_prim, n_elems: workloads.Grid3) or on a 2:1 octree (attributes nx0,
+    ny0, nz0, box, level, ix, iy, iz, bc, bc_prim: workloads.Mesh3)."""
 
     def __init__(self, grid, N: int, gamma: float = 1.4):
         self.grid, self.N, self.np, self.gamma = grid, N, N + 1, gamma
@@ -113,11 +121,22 @@ class Oracle3D:
         box = np.ascontiguousarray(grid.box, dtype=np.float64)
         bc = np.ascontiguousarray(grid.bc, dtype=np.int32)
         bcp = np.ascontiguousarray(grid.bc_prim, dtype=np.float64).reshape(30)
-        self._h = self._L.o3_create(N, gamma, grid.nx, grid.ny, grid.nz, _d(box),
-                                    bc.ctypes.data_as(C.POINTER(C.c_int32)), _d(bcp), C.byref(err))
+        ip = C.POINTER(C.c_int32)
+        if hasattr(grid, "level"):
+            lev = np.ascontiguousarray(grid.level, dtype=np.int8)
+            ix, iy, iz = (np.ascontiguousarray(a, dtype=np.int32) for a in (grid.ix, grid.iy, grid.iz))
+            self._keep = (lev, ix, iy, iz)
+            self._h = self._L.o3_create_leaves(N, gamma, grid.nx0, grid.ny0, grid.nz0, _d(box), int(lev.size),
+                                               lev.ctypes.data_as(C.POINTER(C.c_int8)), ix.ctypes.data_as(ip),
+                                               iy.ctypes.data_as(ip), iz.ctypes.data_as(ip), bc.ctypes.data_as(ip),
+                                               _d(bcp), C.byref(err))
+        else:
+            self._h = self._L.o3_create(N, gamma, grid.nx, grid.ny, grid.nz, _d(box), bc.ctypes.data_as(ip), _d(bcp),
+                                        C.byref(err))
         if not self._h:
             raise ValueError(f"o3_create failed ({err.value})")
         self.nn = self._L.o3_n_nodes(self._h)
+        self.M = self._L.o3_n_mortars(self._h)
 
     def __del__(self):
         if getattr(self, "_h", None):
@@ -158,19 +177,28 @@ class Oracle3D:
         rho_max, p_min, R+, R-) and iface [nif][12] (left node, right node,
         exempt, Zalesak factor, theta_left, theta_right, factor, A (5))."""
         nif = self.grid.n_elems * 3 * self.np * self.np * self.N
-        node, iface = np.zeros((self.nn, 10)), np.zeros((nif, 12))
+        node, iface, mell = np.zeros((self.nn, 10)), np.zeros((nif, 12)), np.zeros(max(self.M, 1))
+        mrec = np.zeros((max(self.M, 1), 5 * self.np * self.np, 20))
         st = np.zeros(16)
         self._L.o3_stats_init(_d(st))
         self._L.o3_set_dbg_out(_d(node), _d(iface))
+        self._L.o3_set_mortar_out(_d(mell), _d(mrec))
         if force_ell is not None:
             self._L.o3_set_force_ell(float(force_ell))
         try:
             res, ut = self.stage(u, dt, limiting=limiting, beta=beta, stats=st)
         finally:
             self._L.o3_set_dbg_out(None, None)
+            self._L.o3_set_mortar_out(None, None)
             self._L.o3_set_force_ell(-1.0)
         return {"res": res, "ut": ut, "stats": {k: float(st[i]) for i, k in enumerate(ST_NAMES)},
-                "node": node, "iface": iface}
+                "node": node, "iface": iface, "mortar_ell": mell[:self.M], "mortar": mrec[:self.M]}
+
+    def mortars(self):
+        """[M][7]: d, large element, large on the low side, small elements p = p1 + 2 p2."""
+        t = np.zeros((max(self.M, 1), 7), np.int32)
+        self._L.o3_mortar_table(self._h, t.ctypes.data_as(C.POINTER(C.c_int32)))
+        return t[:self.M]
 
     def dt(self, u, cfl=0.5):
         return self._L.o3_dt(self._h, _d(self._u(u)), cfl)

@@ -512,8 +512,11 @@ class Grid3:
         return self.nx * self.ny * self.nz
 
 
-def node_coords3(grid: Grid3, N: int):
-    """x, y, z of every node, shape [K][N+1][N+1][N+1] indexed [e][k][j][i]."""
+def node_coords3(grid, N: int):
+    """x, y, z of every node of a Grid3 or a Mesh3, shape [K][N+1][N+1][N+1]
+    indexed [e][k][j][i]."""
+    if hasattr(grid, "level"):
+        return node_coords_mesh3(grid, N)
     x0, y0, z0, x1, y1, z1 = grid.box
     hx, hy, hz = (x1 - x0) / grid.nx, (y1 - y0) / grid.ny, (z1 - z0) / grid.nz
     ez, ey, ex = np.meshgrid(np.arange(grid.nz), np.arange(grid.ny), np.arange(grid.nx), indexing="ij")
@@ -591,3 +594,93 @@ def slab_from_2d(u2, mesh, N: int, nz: int):
         out[2, :, k] = src[2][e2]
         out[4, :, k] = src[3][e2]
     return out, e2
+
+
+@dataclasses.dataclass
+class Mesh3:
+    """Leaves of a 2:1 octree over a box with an nx0 x ny0 x nz0 level-0 grid:
+    leaf e at level level[e], index (ix, iy, iz)[e] on its level's grid."""
+
+    nx0: int
+    ny0: int
+    nz0: int
+    box: tuple  # (x0, y0, z0, x1, y1, z1)
+    level: np.ndarray  # int8 [K]
+    ix: np.ndarray     # int32 [K]
+    iy: np.ndarray
+    iz: np.ndarray
+    bc: tuple = (BC_PERIODIC,) * 6
+    bc_prim: np.ndarray = dataclasses.field(default_factory=lambda: np.zeros((6, 5)))
+
+    @property
+    def n_elems(self) -> int:
+        return int(self.level.shape[0])
+
+
+def box_refined_mesh3(nx0, ny0, nz0, box, rbox, bc=(BC_PERIODIC,) * 6, base_level=0, inside=True):
+    """A uniform octree at base_level with the leaves whose centre lies in
+    rbox = (x0, y0, z0, x1, y1, z1) (outside it, with inside=False) refined
+    once (one level jump: 2:1)."""
+    lev, ix, iy, iz = [], [], [], []
+    n = 1 << base_level
+    x0, y0, z0, x1, y1, z1 = box
+    hx, hy, hz = (x1 - x0) / (nx0 * n), (y1 - y0) / (ny0 * n), (z1 - z0) / (nz0 * n)
+    for c in range(nz0 * n):
+        for b in range(ny0 * n):
+            for a in range(nx0 * n):
+                cx, cy, cz = x0 + (a + 0.5) * hx, y0 + (b + 0.5) * hy, z0 + (c + 0.5) * hz
+                hit = rbox[0] < cx < rbox[3] and rbox[1] < cy < rbox[4] and rbox[2] < cz < rbox[5]
+                if hit == inside:
+                    for q in range(8):
+                        lev.append(base_level + 1)
+                        ix.append(2 * a + (q & 1)); iy.append(2 * b + ((q >> 1) & 1)); iz.append(2 * c + (q >> 2))
+                else:
+                    lev.append(base_level); ix.append(a); iy.append(b); iz.append(c)
+    return Mesh3(nx0, ny0, nz0, box, np.array(lev, np.int8), np.array(ix, np.int32), np.array(iy, np.int32),
+                 np.array(iz, np.int32), bc=bc)
+
+
+def extruded_mesh3(mesh2: Mesh, z0=0.0, z1=1.0, bcz=(BC_PERIODIC, BC_PERIODIC)):
+    """The octree that extrudes a quadtree mesh in z over one level-0 cell:
+    2D leaf (l, ix, iy) becomes the 2^l leaves (l, ix, iy, iz); with states
+    that do not depend on z the 3D scheme reduces to the 2D one on it. Also
+    returns, per 3D leaf, its 2D leaf."""
+    lev, ix, iy, iz, e2 = [], [], [], [], []
+    for e in range(mesh2.n_elems):
+        l = int(mesh2.level[e])
+        for c in range(1 << l):
+            lev.append(l); ix.append(int(mesh2.ix[e])); iy.append(int(mesh2.iy[e])); iz.append(c); e2.append(e)
+    x0, y0, x1, y1 = mesh2.box
+    m3 = Mesh3(mesh2.nx0, mesh2.ny0, 1, (x0, y0, z0, x1, y1, z1), np.array(lev, np.int8), np.array(ix, np.int32),
+               np.array(iy, np.int32), np.array(iz, np.int32), bc=tuple(mesh2.bc) + tuple(bcz))
+    return m3, np.array(e2, np.int64)
+
+
+def node_coords_mesh3(mesh: Mesh3, N: int):
+    """x, y, z of every node of an octree, [K][N+1][N+1][N+1] indexed [e][k][j][i]."""
+    x0, y0, z0, x1, y1, z1 = mesh.box
+    lv = mesh.level.astype(np.int64)
+    hx = (x1 - x0) / (mesh.nx0 * (1 << lv))
+    hy = (y1 - y0) / (mesh.ny0 * (1 << lv))
+    hz = (z1 - z0) / (mesh.nz0 * (1 << lv))
+    s = lgl_points(N)
+    cx = (x0 + (mesh.ix + 0.5) * hx)[:, None, None, None]
+    cy = (y0 + (mesh.iy + 0.5) * hy)[:, None, None, None]
+    cz = (z0 + (mesh.iz + 0.5) * hz)[:, None, None, None]
+    shape = (mesh.n_elems, N + 1, N + 1, N + 1)
+    X = np.broadcast_to(cx + 0.5 * hx[:, None, None, None] * s[None, None, None, :], shape).copy()
+    Y = np.broadcast_to(cy + 0.5 * hy[:, None, None, None] * s[None, None, :, None], shape).copy()
+    Z = np.broadcast_to(cz + 0.5 * hz[:, None, None, None] * s[None, :, None, None], shape).copy()
+    return X, Y, Z
+
+
+def extrude_state(u2, e2, N: int):
+    """The 3D state on extruded_mesh3 that repeats the 2D state in z (v3 = 0)."""
+    src = np.asarray(u2).reshape(4, -1, N + 1, N + 1)
+    out = np.zeros((5, len(e2), N + 1, N + 1, N + 1))
+    for k in range(N + 1):
+        out[0, :, k] = src[0][e2]
+        out[1, :, k] = src[1][e2]
+        out[2, :, k] = src[2][e2]
+        out[4, :, k] = src[3][e2]
+    return out
