@@ -1,7 +1,8 @@
 /*
  * idp_dgsem3d.h -- C ABI of the 3D IDP-limited LGL-DGSEM (arXiv 2607.06045,
- * Sec. 2 with d = 3) on a conforming Cartesian grid of hexahedra, in the same
- * library as idp_dgsem.h (libidpdgsem.so, CUDA, sm_103a).
+ * Sec. 2 with d = 3) on Cartesian grids and 2:1-balanced octrees of
+ * hexahedra, in the same library as idp_dgsem.h (libidpdgsem.so, CUDA,
+ * sm_103a).
  *
  * The method per stage: the flux-differencing volume terms of
  * Eq. evolutionformula along x, y and z with Ranocha's two-point flux and
@@ -9,12 +10,21 @@
  * Eq. LowOrderScheme_globalIndices; bar-state density bounds and positivity
  * (Eqs. Bounds_Positivity, Bounds_Barstates); Zalesak density limiting and
  * the pressure factor with Gamma = 2d = 6 (Sec. 2.3); the IDP time step
- * (Eq. timestep_restriction) and SSP-RK3 (Sec. 3). FP64 throughout.
+ * (Eq. timestep_restriction) and SSP-RK3 (Sec. 3). FP64 throughout. On an
+ * octree a face between a leaf and four finer ones is a mortar with 2 x 2
+ * small faces (Sec. 2.2 in 3D): the L2 mortar flux as the tensor product of
+ * the 1D interpolation and exact L2 projection, the sparse low-order mortar
+ * flux of Eq. interfaceflux_local with products of the 1D overlap weights
+ * (App. A), the bar states of its pairs in the density bounds, and one
+ * factor per mortar after the volume correction with each node's share
+ * scaled by its number of mortars n_i (Sec. 2.3); a mortar whose
+ * interpolated states leave the admissible set keeps its low-order flux.
  *
  * State layout (caller-owned device memory): u[5][K][N+1][N+1][N+1] doubles,
  * variables (rho, rho v1, rho v2, rho v3, rho e), then element, then node
- * (k, j, i) with the x index i fastest; elements e = (ez ny + ey) nx + ex.
- * Degrees N = 1..4. Errors: the idp_status codes of idp_dgsem.h.
+ * (k, j, i) with the x index i fastest; on a grid e = (ez ny + ey) nx + ex,
+ * on an octree the caller's leaf order. Degrees N = 1..4. Errors: the
+ * idp_status codes of idp_dgsem.h.
  */
 #ifndef IDP_DGSEM3D_H
 #define IDP_DGSEM3D_H
@@ -59,8 +69,22 @@ idp_status idp3d_options_default(idp3d_options *o);
 idp_status idp3d_create(const idp3d_grid_desc *grid, int32_t N, double gamma, const idp3d_options *opts,
                         idp3d_ctx **out);
 
+/* Context for the leaves of a 2:1-balanced octree over the box of `base`,
+ * whose nx, ny, nz give the level-0 grid: leaf e (0 <= e < n_leaves) is cell
+ * (ix[e], iy[e], iz[e]) of the (nx 2^l) x (ny 2^l) x (nz 2^l) grid of its
+ * level l = level[e] (0..18). Host arrays, read during the call only. The
+ * leaves must tile the box, and leaves sharing a face differ by at most one
+ * level (across periodic sides too): IDP_E_ARG otherwise, as for the
+ * arguments of idp3d_create. */
+idp_status idp3d_create_octree(const idp3d_grid_desc *base, int64_t n_leaves, const int8_t *level, const int32_t *ix,
+                               const int32_t *iy, const int32_t *iz, int32_t N, double gamma,
+                               const idp3d_options *opts, idp3d_ctx **out);
+
 /* n_elems and nodes per element (N+1)^3; either may be NULL. */
 idp_status idp3d_layout(const idp3d_ctx *ctx, int64_t *n_elems, int32_t *nodes_per_elem);
+
+/* the number of mortars and of nodes on mortars; either may be NULL */
+idp_status idp3d_mesh_info(const idp3d_ctx *ctx, int64_t *n_mortars, int64_t *n_mortar_nodes);
 
 /* rhs = the limited residual per unit mass of u for a stage of length dt
  * (dt = 0: the unlimited high-order residual), device arrays in the layout
@@ -88,11 +112,15 @@ idp_status idp3d_integrals(idp3d_ctx *ctx, const double *u, double *out_host, vo
  * mass-weighted mean of 1 - (the node's smallest interface factor), nodes
  * with a factor below one, violations of the density bounds and of the
  * pressure bound (beyond 1e-13 relative), non-admissible results, the
- * smallest density and pressure seen, and the stage count. */
+ * smallest density and pressure seen, and the stage count; on octrees the
+ * area-weighted mean of 1 - l_S over the mortars, the mortars with l_S < 1
+ * and those that kept their low-order flux (counted per stage). */
 typedef struct {
     double alpha_mean;
     int64_t n_active, n_viol_density, n_viol_pressure, n_nonpositive, n_stages;
     double min_rho, min_p;
+    double alpha_mortar;
+    int64_t n_mortar_active, n_mortar_fallback;
 } idp3d_stats;
 
 idp_status idp3d_limiter_stats(idp3d_ctx *ctx, idp3d_stats *out, void *stream);

@@ -1,6 +1,7 @@
 // idp3d.cuh -- the IDP-limited LGL-DGSEM stage for the 3D Euler equations
-// (d = 3 of arXiv 2607.06045, Sec. 2) on a conforming Cartesian grid of
-// hexahedra: one fused element kernel per stage and the IDP time step.
+// (d = 3 of arXiv 2607.06045, Sec. 2) on 2:1-balanced Cartesian octrees of
+// hexahedra: one fused element kernel per stage and the IDP time step (the
+// mortar kernels of the nonconforming faces are in idp3d_mortar.cuh).
 //
 // The stage is the 2D one with the third direction (Sec. 2.1-2.3 for
 // d = 3): Ranocha's two-point fluxes along x, y and z within each element,
@@ -10,7 +11,10 @@
 // and positivity (Eqs. Bounds_Positivity, Bounds_Barstates), Zalesak density
 // limiting and the pressure factor with Gamma = 2d = 6, then the SSP-RK3
 // combination. State u[5][K][N+1]^3 FP64 (rho, rho v1, rho v2, rho v3, rho e),
-// x index fastest; element e = (ez ny + ey) nx + ex.
+// x index fastest, leaves in the caller's order. At a mortar side the element
+// takes its low-order face terms and bar-state ranges from the mortar's slots
+// and hands the node's volume-corrected state to the mortar kernels, which
+// finish it.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -30,14 +34,48 @@ constexpr double kGamma3 = 6.0;       // Gamma = 2d (Sec. 2.3)
 enum : int { B_PERIODIC = 0, B_WALL = 1, B_DIRICHLET = 2, B_OUTFLOW = 3 };
 enum : unsigned { S_BAD_INPUT = 1u, S_VIOLATION = 2u };
 
-// the grid, its boundary kinds per side (-x, +x, -y, +y, -z, +z) and the
-// conserved Dirichlet states
+// Mortars (a face between a leaf and four finer ones, 2 x 2 small faces p =
+// p1 + 2 p2 by their offsets along the face's tangential directions (d+1) mod
+// 3 and (d+2) mod 3). Each mortar has Q = 5 (N+1)^2 slots, one per node on
+// it: the large face's nodes, then each small face's, node t = a + (N+1) b
+// of a face with a along (d+1) mod 3. A "mortar node" is a node on at least
+// one mortar (up to three); the element kernel hands it off and the mortar
+// kernels finish it.
+struct Mort3 {
+    int M, S, MN;                    // mortars, slots (M Q), mortar nodes
+    const int *info;                 // [M][7]: d, large element, large on the low side, small elements p = 0..3
+    double *chi, *clo;               // [NV][S]: high- and low-order contribution to the node's mass-weighted residual
+    double *rbmin, *rbmax, *dsum;    // [S]: bar-state density range over the slot's pairs and their sum of 2 d_ij
+    int *bad;                        // [M]: the interpolated states left the admissible set (R16)
+    double *ell;                     // [M]: the mortar's factor l_S
+    const int *slot_mn;              // [S]: the slot's mortar node
+    const int *mn_node;              // [MN]: its global node (e (N+1)^3 + n)
+    const int *mn_slot;              // [3][MN]: its slots in mortar order, -1 past n_i
+    const int *mn_cnt;               // [MN]: n_i, its number of mortars
+    double *h_uvol, *h_res;          // [NV][MN]: u_vol and the residual before the mortar corrections (mass-weighted)
+    double *h_b;                     // [5][MN]: rho_min, rho_max, p_min, rho_FV, 1 / m
+};
+
+// The mesh: K leaves, leaf e at level lev[e] with extents (dx, dy, dz) 2^-lev
+// (dx, dy, dz of a level-0 cell); per side (-x, +x, -y, +y, -z, +z) of each
+// leaf nbr[6 e + s]: the conforming neighbour (>= 0), -1 at a boundary, or
+// -2 - (the first slot of the mortar face); boundary kinds per side of the
+// box and the conserved Dirichlet states.
 struct Grid3 {
     int nx, ny, nz, K;
     double dx, dy, dz;
     int bc[6];
     double bc_cons[6][NV];
+    const int *nbr;
+    const signed char *lev;
+    Mort3 mort;
 };
+
+// extents of leaf e
+__device__ __forceinline__ void extents3(const Grid3 &G, int e, double *h) {
+    const double sc = __int_as_float((127 - (int)G.lev[e]) << 23);   // 2^-lev, exact
+    h[0] = G.dx * sc; h[1] = G.dy * sc; h[2] = G.dz * sc;
+}
 
 // LGL nodes and weights, Sbar (Sec. 2.1), 1 / w
 struct Ops3 {
@@ -50,6 +88,8 @@ struct Stats3 {
     unsigned long long n_active;    // nodes with a factor below one
     unsigned long long n_vrho, n_vp, n_nonpos;
     unsigned long long min_rho_bits, min_p_bits;
+    double alpha_mort_a, mort_area;          // sum over mortars of area (1 - l_S), of area
+    unsigned long long n_mort, n_mort_fallback;   // mortars with l_S < 1; with an inadmissible interpolation
 };
 
 struct Stage3 {
@@ -198,20 +238,6 @@ __device__ __forceinline__ void ghost3(const Grid3 &G, int s, const double *in, 
     }
 }
 
-// neighbour element across side s of element e, or -1 at a non-periodic boundary
-__device__ __forceinline__ int nbr3(const Grid3 &G, int e, int s) {
-    int ex = e % G.nx, ey = (e / G.nx) % G.ny, ez = e / (G.nx * G.ny);
-    const int d = s / 2, step = (s & 1) ? 1 : -1;
-    int c[3] = {ex, ey, ez};
-    const int n[3] = {G.nx, G.ny, G.nz};
-    c[d] += step;
-    if (c[d] < 0 || c[d] >= n[d]) {
-        if (G.bc[s] != B_PERIODIC) return -1;
-        c[d] = (c[d] + n[d]) % n[d];
-    }
-    return (c[2] * G.ny + c[1]) * G.nx + c[0];
-}
-
 template <int NP>
 struct El3 {
     static constexpr int N = NP - 1, NR = NP * NP, NN = NP * NP * NP, NPAIR = NP * (NP - 1) / 2;
@@ -253,7 +279,8 @@ struct Sm3 {
     union {
         struct {                     // P1 - P2
             double ff[6][NR][NV];    // face fluxes, mass-weighted, along +d
-            double fbar[6][NR];      // bar-state density across the face
+            double fbl[6][NR];       // bar-state density range across the face (one value
+            double fbh[6][NR];       // at a conforming face, a mortar slot's range at a mortar)
             double ibar[NIF];        // bar-state density of the interior interfaces
         };
         double A[NIF][NV];           // P2b - P5: antidiffusive fluxes (mass-weighted)
@@ -263,6 +290,8 @@ struct Sm3 {
     double rmin[NN], rmax[NN], pmin[NN];
     double c0[NN];             // P2 - P4: g(0) = (gamma-1)(rho E - |m|^2/2) - p_min rho at u_FV
     double im[NN];             // P2 - P5: 1 / m
+    double q[3], J, iJ;        // quarter face areas, dx dy dz / 8 and its inverse
+    int nb[6];                 // the sides' neighbour entries (Grid3::nbr)
 };
 
 // threads of a block of EPB elements: one per node, rounded up to whole warps
@@ -325,13 +354,19 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     const size_t KN = (size_t)G.K * NN;
     const double g = A.gamma, gm1 = g - 1.0;
     const double dt = stage_dt3(A);
-    const double q[3] = {G.dy * G.dz / 4.0, G.dx * G.dz / 4.0, G.dx * G.dy / 4.0};   // quarter face areas
-    const double iJ = 8.0 / (G.dx * G.dy * G.dz);
     const int e0 = blockIdx.x * EPB;
+    const Mort3 &MO = G.mort;
     // ---- P0: state, primitives, logarithms, wave speeds; outside states
     for (int k = tid; k < EPB * NN; k += NT) {
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
+        if (n == 0) {
+            double h[3];
+            extents3(G, e, h);
+            S[le].q[0] = h[1] * h[2] / 4.0; S[le].q[1] = h[0] * h[2] / 4.0; S[le].q[2] = h[0] * h[1] / 4.0;
+            S[le].J = h[0] * h[1] * h[2] / 8.0;
+            S[le].iJ = 8.0 / (h[0] * h[1] * h[2]);
+        }
         double uv[NV];
         for (int v = 0; v < NV; ++v) { uv[v] = A.u[v * KN + (size_t)e * NN + n]; S[le].u[v][n] = uv[v]; }
         const double ir = idp::fast_rcp(uv[0]);
@@ -355,7 +390,9 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / (6 * NR), r0 = k - le * 6 * NR, s = r0 / NR, t = r0 - s * NR, e = e0 + le;
         if (e >= G.K) continue;
         const int d = s / 2, side = s & 1;
-        const int nb = nbr3(G, e, s);
+        const int nb = G.nbr[6 * e + s];
+        if (t == 0) S[le].nb[s] = nb;
+        if (nb < -1) continue;   // a mortar: its slots carry the face terms
         const int nin = node_of<NP>(d, t, side ? N : 0);
         double o[NV];
         if (nb >= 0) {
@@ -406,8 +443,22 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / (6 * NR), r0 = k - le * 6 * NR, s = r0 / NR, t = r0 - s * NR;
         if (e0 + le >= G.K) continue;
         const int d = s / 2, side = s & 1;
+        const int nbv = S[le].nb[s];
+        if (nbv < -1) {
+            // mortar: the slot's low-order contribution to the node (ff enters
+            // a low face with +, a high face with -) and its bar-state range
+            const int slot = -2 - nbv + t;
+            for (int v = 0; v < NV; ++v) {
+                const double c = MO.clo[(size_t)v * MO.S + slot];
+                S[le].ff[s][t][v] = side ? -c : c;
+            }
+            S[le].fbl[s][t] = MO.rbmin[slot];
+            S[le].fbh[s][t] = MO.rbmax[slot];
+            continue;
+        }
         const int nin = node_of<NP>(d, t, side ? N : 0);
         const SM &X = S[le];
+        const double *q = X.q;
         double ui[NV], uo[NV], fi[NV], fo[NV];
         for (int v = 0; v < NV; ++v) { ui[v] = X.u[v][nin]; uo[v] = X.outs[s][t][v]; }
         flux_p(ui, X.pr[d][nin], X.pr[3][nin], d, fi);
@@ -419,7 +470,9 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         for (int v = 0; v < NV; ++v) S[le].ff[s][t][v] = cw * (0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]));
         // ubar = (u_i + u_o)/2 - c.(f_o - f_i)/(2 |c| lambda), c along the outward normal
         const double sg = side ? 0.5 : -0.5;
-        S[le].fbar[s][t] = 0.5 * (ui[0] + uo[0]) - sg * (fo[0] - fi[0]) * idp::fast_rcp(lam);
+        const double fb = 0.5 * (ui[0] + uo[0]) - sg * (fo[0] - fi[0]) * idp::fast_rcp(lam);
+        S[le].fbl[s][t] = fb;
+        S[le].fbh[s][t] = fb;
     }
     // ---- P1c: low-order subcell fluxes at the interior interfaces
     for (int k = tid; k < EPB * NIF; k += NT) {
@@ -433,7 +486,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         flux_p(ul, X.pr[d][nl], X.pr[3][nl], d, fl);
         flux_p(ur, X.pr[d][nr], X.pr[3][nr], d, fr);
         const double lam = fmax(X.lam[d][nl], X.lam[d][nr]);
-        const double cc = ops.w[r % NP] * ops.w[r / NP] * q[d] / 2.0;
+        const double cc = ops.w[r % NP] * ops.w[r / NP] * X.q[d] / 2.0;
         for (int v = 0; v < NV; ++v) S[le].fvf[id][v] = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
         S[le].ibar[id] = 0.5 * (ul[0] + ur[0]) - 0.5 * (fr[0] - fl[0]) * idp::fast_rcp(lam);
     }
@@ -443,32 +496,34 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / NN, n = k - le * NN;
         if (e0 + le >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
-        const double im = ops.iw[idx[0]] * ops.iw[idx[1]] * ops.iw[idx[2]] * iJ;
+        const double im = ops.iw[idx[0]] * ops.iw[idx[1]] * ops.iw[idx[2]] * S[le].iJ;
         double r[NV] = {0, 0, 0, 0, 0}, uv[NV];
         for (int v = 0; v < NV; ++v) uv[v] = S[le].u[v][n];
         double lo = uv[0], hi = uv[0];
         for (int d = 0; d < 3; ++d) {
             const int pos = idx[d], row = idx[(d + 1) % 3] + NP * idx[(d + 2) % 3];
             // low side: the interface (pos-1, pos) or the low face
-            double b0, b1;
+            double b0l, b0h, b1l, b1h;
             if (pos > 0) {
                 const int id = (d * NR + row) * N + pos - 1;
                 for (int v = 0; v < NV; ++v) r[v] += S[le].fvf[id][v];
-                b0 = S[le].ibar[id];
+                b0l = b0h = S[le].ibar[id];
             } else {
                 for (int v = 0; v < NV; ++v) r[v] += S[le].ff[2 * d][row][v];
-                b0 = S[le].fbar[2 * d][row];
+                b0l = S[le].fbl[2 * d][row];
+                b0h = S[le].fbh[2 * d][row];
             }
             if (pos < N) {
                 const int id = (d * NR + row) * N + pos;
                 for (int v = 0; v < NV; ++v) r[v] -= S[le].fvf[id][v];
-                b1 = S[le].ibar[id];
+                b1l = b1h = S[le].ibar[id];
             } else {
                 for (int v = 0; v < NV; ++v) r[v] -= S[le].ff[2 * d + 1][row][v];
-                b1 = S[le].fbar[2 * d + 1][row];
+                b1l = S[le].fbl[2 * d + 1][row];
+                b1h = S[le].fbh[2 * d + 1][row];
             }
-            lo = idp::dmin(lo, idp::dmin(b0, b1));
-            hi = idp::dmax(hi, idp::dmax(b0, b1));
+            lo = idp::dmin(lo, idp::dmin(b0l, b1l));
+            hi = idp::dmax(hi, idp::dmax(b0h, b1h));
         }
         double uf[NV];
         for (int v = 0; v < NV; ++v) {
@@ -501,7 +556,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
                 if (mm == l) continue;   // Sbar has a zero diagonal
                 const int lo_ = l < mm ? l : mm, hi_ = l < mm ? mm : l;
                 const int pp = lo_ * (2 * NP - lo_ - 1) / 2 + (hi_ - lo_ - 1);
-                const double sq = ops.S[l][mm] * q[d];
+                const double sq = ops.S[l][mm] * S[le].q[d];
                 for (int v = 0; v < NV; ++v) acc[v] += sq * S[le].pair[d][r][pp][v];
             }
             const int id = (d * NR + r) * N + l;
@@ -518,7 +573,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / NN, n = k - le * NN;
         if (e0 + le >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
-        const double m = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * (G.dx * G.dy * G.dz / 8.0);
+        const double m = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * S[le].J;
         double Pp = 0.0, Pm = 0.0;
         for (int d = 0; d < 3; ++d) {
             const int pos = idx[d], row = idx[(d + 1) % 3] + NP * idx[(d + 2) % 3];
@@ -591,29 +646,54 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
                 for (int v = 0; v < NV; ++v) s[v] -= l * S[le].A[id][v];
             }
         }
+        // a node on a mortar side: its first mortar slot (x, y, z order)
+        int mslot = -1;
+        for (int d = 0; d < 3 && mslot < 0; ++d) {
+            const int pos = idx[d], row = idx[(d + 1) % 3] + NP * idx[(d + 2) % 3];
+            const int nbv = pos == 0 ? S[le].nb[2 * d] : (pos == N ? S[le].nb[2 * d + 1] : 0);
+            if (nbv < -1) mslot = -2 - nbv + row;
+        }
         const size_t gi = (size_t)e * NN + n;
         double ut[NV];
-        for (int v = 0; v < NV; ++v) {
-            const double res = S[le].rfv[v][n] + s[v];
-            ut[v] = S[le].ufv[v][n] + dt * im * s[v];
-            double o;
-            if (A.mode == 0) o = res * im;
-            else if (A.comb == 1) o = 0.75 * A.un[v * KN + gi] + 0.25 * ut[v];
-            else if (A.comb == 2) o = A.un[v * KN + gi] * (1.0 / 3.0) + 2.0 / 3.0 * ut[v];
-            else o = ut[v];
-            A.out[v * KN + gi] = o;
+        if (mslot >= 0) {
+            // hand-off: the mortar kernels add the limited mortar corrections
+            // and write the node
+            const int mn = MO.slot_mn[mslot];
+            for (int v = 0; v < NV; ++v) {
+                ut[v] = S[le].ufv[v][n] + dt * im * s[v];
+                MO.h_uvol[(size_t)v * MO.MN + mn] = ut[v];
+                MO.h_res[(size_t)v * MO.MN + mn] = S[le].rfv[v][n] + s[v];
+            }
+            MO.h_b[0 * (size_t)MO.MN + mn] = S[le].rmin[n];
+            MO.h_b[1 * (size_t)MO.MN + mn] = S[le].rmax[n];
+            MO.h_b[2 * (size_t)MO.MN + mn] = S[le].pmin[n];
+            MO.h_b[3 * (size_t)MO.MN + mn] = S[le].ufv[0][n];
+            MO.h_b[4 * (size_t)MO.MN + mn] = im;
+        } else {
+            for (int v = 0; v < NV; ++v) {
+                const double res = S[le].rfv[v][n] + s[v];
+                ut[v] = S[le].ufv[v][n] + dt * im * s[v];
+                double o;
+                if (A.mode == 0) o = res * im;
+                else if (A.comb == 1) o = 0.75 * A.un[v * KN + gi] + 0.25 * ut[v];
+                else if (A.comb == 2) o = A.un[v * KN + gi] * (1.0 / 3.0) + 2.0 / 3.0 * ut[v];
+                else o = ut[v];
+                A.out[v * KN + gi] = o;
+            }
         }
         if (A.collect && A.limiting > 0) {
-            const double p = pres3(g, ut);
-            const double rl = S[le].rmin[n], rh = S[le].rmax[n], pl = S[le].pmin[n];
-            if (ut[0] < rl - kViol3 * fabs(rl) || ut[0] > rh + kViol3 * fabs(rh)) vr++;
-            if (p < pl - kViol3 * fabs(pl)) vp++;
-            if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
-            const double mm_ = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * (G.dx * G.dy * G.dz / 8.0);
+            const double mm_ = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * S[le].J;
             am += mm_ * (1.0 - lm);
             if (lm < 1.0) nact++;
-            rmin_st = idp::dmin(rmin_st, ut[0]);
-            pmin_st = idp::dmin(pmin_st, p);
+            if (mslot < 0) {
+                const double p = pres3(g, ut);
+                const double rl = S[le].rmin[n], rh = S[le].rmax[n], pl = S[le].pmin[n];
+                if (ut[0] < rl - kViol3 * fabs(rl) || ut[0] > rh + kViol3 * fabs(rh)) vr++;
+                if (p < pl - kViol3 * fabs(pl)) vp++;
+                if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
+                rmin_st = idp::dmin(rmin_st, ut[0]);
+                pmin_st = idp::dmin(pmin_st, p);
+            }
         }
     }
     if (A.collect && A.limiting > 0) {
@@ -641,7 +721,9 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
 }
 
 // IDP time step (Eq. timestep_restriction): per node m_i / sum_j 2 d_ij over
-// its subcell and face neighbours; minimum per block, one atomic per block
+// its subcell and face neighbours (at a mortar side the slot's sum over its
+// pairs, formed by the mortar flux kernel from the same state); minimum per
+// block, one atomic per block
 template <int NP, int EPB>
 __global__ void __launch_bounds__(Launch3<NP, EPB>::threads)
 k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, double gamma,
@@ -663,13 +745,15 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
         for (int d = 0; d < 3; ++d) lam[le][d][n] = wave3(gamma, uv, d);
     }
     __syncthreads();
-    const double q[3] = {G.dy * G.dz / 4.0, G.dx * G.dz / 4.0, G.dx * G.dy / 4.0};
-    const double J = G.dx * G.dy * G.dz / 8.0;
     unsigned long long best = (unsigned long long)__double_as_longlong(INFINITY);
     for (int k = tid; k < EPB * NN; k += NT) {
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
+        double h[3];
+        extents3(G, e, h);
+        const double q[3] = {h[1] * h[2] / 4.0, h[0] * h[2] / 4.0, h[0] * h[1] / 4.0};
+        const double J = h[0] * h[1] * h[2] / 8.0;
         double s2d = 0.0;
         for (int d = 0; d < 3; ++d) {
             const double cd = w[idx[(d + 1) % 3]] * w[idx[(d + 2) % 3]] * q[d] / 2.0;
@@ -681,7 +765,11 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
                     const int nn2 = n + (side == 0 ? -1 : 1) * (d == 0 ? 1 : (d == 1 ? NP : NP * NP));
                     lo = lam[le][d][nn2];
                 } else {
-                    const int s = 2 * d + side, nb = nbr3(G, e, s);
+                    const int s = 2 * d + side, nb = G.nbr[6 * e + s];
+                    if (nb < -1) {
+                        s2d += G.mort.dsum[-2 - nb + idx[(d + 1) % 3] + NP * idx[(d + 2) % 3]];
+                        continue;
+                    }
                     double o[NV];
                     if (nb >= 0) {
                         int jdx[3] = {idx[0], idx[1], idx[2]};

@@ -1,13 +1,15 @@
 // idp3d_host.cu -- host runtime and C ABI of the 3D IDP-limited LGL-DGSEM
-// (include/idp_dgsem3d.h): the grid and operators on the device, the
-// SSP-RK3 step as one CUDA graph (time step, three limited stages, time
-// advance), right-hand sides, time steps, conservation totals and limiter
-// statistics.
+// (include/idp_dgsem3d.h): the octree's connectivity (face neighbours,
+// mortars, their slots and nodes) and the operators on the device, the
+// SSP-RK3 step as one CUDA graph (mortar fluxes, time step, three limited
+// stages with their mortar factors, time advance), right-hand sides, time
+// steps, conservation totals and limiter statistics.
 #include <cuda_runtime.h>
 
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/idp_dgsem3d.h"
@@ -15,6 +17,7 @@
 
 namespace idp {
 void host_lgl_sbar(int N, double *x, double *w, double *S);
+void host_lgl_mortar(int N, double *I, double *P, double *wt);
 }
 
 using namespace idp3;
@@ -27,6 +30,11 @@ struct idp3d_ctx {
     Launchers3 L;
     int grid_el = 1;               // element-kernel blocks
     Ops3 *d_ops = nullptr;
+    MOps3 *d_mops = nullptr;
+    int *d_nbr = nullptr, *d_minfo = nullptr, *d_slot_mn = nullptr, *d_mn_node = nullptr, *d_mn_slot = nullptr;
+    int *d_mn_cnt = nullptr, *d_mbad = nullptr;
+    signed char *d_lev = nullptr;
+    double *d_mslot = nullptr, *d_hand = nullptr, *d_ell = nullptr;
     double *d_buf1 = nullptr, *d_buf2 = nullptr, *d_part = nullptr, *d_tot = nullptr;
     unsigned long long *d_dtmin = nullptr, *d_dtmin2 = nullptr;
     double *d_t = nullptr, *d_dtlast = nullptr;
@@ -78,16 +86,29 @@ Stage3 stage_args(idp3d_ctx *c, const double *u, const double *un, double *out, 
 
 int dt_grid(const idp3d_ctx *c) { return (c->grid.K + c->L.epb - 1) / c->L.epb; }
 
+bool has_mortars(const idp3d_ctx *c) { return c->grid.mort.M > 0; }
+
+// one limited stage: the mortar fluxes of its input (unless already formed),
+// the element kernel, then the mortar factors and the mortar nodes
+void enqueue_stage(idp3d_ctx *c, cudaStream_t st, const Stage3 &A, bool mflux) {
+    if (has_mortars(c) && mflux) c->L.mflux(st, c->grid, c->d_mops, A.u, c->gamma);
+    c->L.element(c->grid_el, st, c->grid, c->d_ops, A);
+    if (has_mortars(c)) {
+        c->L.mfactor(st, c->grid, A);
+        c->L.mapply(st, c->grid, A);
+    }
+}
+
 // one SSP-RK3 step of u in place (Shu-Osher): u1 = u~(u), u2 = 3/4 u + 1/4 u~(u1),
-// u = 1/3 u + 2/3 u~(u2); dt from u^n
+// u = 1/3 u + 2/3 u~(u2); dt from u^n (its mortar 2 d sums from the first
+// stage's mortar fluxes)
 void enqueue_step(idp3d_ctx *c, cudaStream_t st, double *u) {
+    if (has_mortars(c)) c->L.mflux(st, c->grid, c->d_mops, u, c->gamma);
     c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, c->d_dtmin, c->d_status);
-    Stage3 A = stage_args(c, u, u, c->d_buf1, 1, 0);
-    c->L.element(c->grid_el, st, c->grid, c->d_ops, A);
-    A = stage_args(c, c->d_buf1, u, c->d_buf2, 1, 1);
-    c->L.element(c->grid_el, st, c->grid, c->d_ops, A);
-    A = stage_args(c, c->d_buf2, u, u, 1, 2);   // each node reads its own u^n, then writes it
-    c->L.element(c->grid_el, st, c->grid, c->d_ops, A);
+    enqueue_stage(c, st, stage_args(c, u, u, c->d_buf1, 1, 0), false);
+    enqueue_stage(c, st, stage_args(c, c->d_buf1, u, c->d_buf2, 1, 1), true);
+    // each node reads its own u^n, then writes it
+    enqueue_stage(c, st, stage_args(c, c->d_buf2, u, u, 1, 2), true);
     k_advance3d<<<1, 32, 0, st>>>(c->d_t, c->d_dtmin, c->opt.cfl, c->d_dtlast);
 }
 
@@ -114,8 +135,10 @@ cudaError_t reset_stats3(idp3d_ctx *c, cudaStream_t st) {
 __global__ void k_part3(Grid3 G, const Ops3 *ops, const double *u, int NP, double *part) {
     const int NN = NP * NP * NP;
     const size_t KN = (size_t)G.K * NN;
-    const double J = G.dx * G.dy * G.dz / 8.0;
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < G.K; e += gridDim.x * blockDim.x) {
+        double h[3];
+        extents3(G, e, h);
+        const double J = h[0] * h[1] * h[2] / 8.0;
         double s[NV] = {0, 0, 0, 0, 0};
         for (int n = 0; n < NN; ++n) {
             const int i = n % NP, j = (n / NP) % NP, k = n / (NP * NP);
@@ -142,26 +165,170 @@ __global__ void __launch_bounds__(1024) k_sum3(const double *part, int K, double
     }
 }
 
-}  // namespace
+// ---------------------------------------------------------------------------
+// octree connectivity
+// ---------------------------------------------------------------------------
 
-extern "C" {
+struct Octree3 {
+    std::vector<int> nbr;            // [K][6] (Grid3::nbr)
+    std::vector<signed char> lev;    // [K]
+    std::vector<int> info;           // [M][7]
+    std::vector<int> slot_mn;        // [S]
+    std::vector<int> mn_node, mn_cnt;   // [MN]
+    std::vector<int> mn_slot;        // [3][MN]
+    int M = 0, MN = 0;
+};
 
-idp_status idp3d_options_default(idp3d_options *o) {
-    if (!o) return IDP_E_ARG;
-    o->limiting = 2;
-    o->beta = 0.1;
-    o->cfl = 0.5;
+uint64_t leaf_key(int l, int64_t x, int64_t y, int64_t z) {
+    return ((uint64_t)l << 57) | ((uint64_t)x << 38) | ((uint64_t)y << 19) | (uint64_t)z;
+}
+
+int node_of_host(int NP, int d, int t, int a) {
+    int idx[3];
+    idx[d] = a; idx[(d + 1) % 3] = t % NP; idx[(d + 2) % 3] = t / NP;
+    return (idx[2] * NP + idx[1]) * NP + idx[0];
+}
+
+// Face neighbours (same level), mortars (a leaf whose side faces four finer
+// leaves: mortars numbered in the order of their large leaf and side) and
+// their slots and nodes. IDP_E_ARG for leaves outside their level's grid,
+// duplicates, a gap or overlap, or a level jump above one across a face.
+idp_status build_octree3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, const int32_t *ix,
+                         const int32_t *iy, const int32_t *iz, int NP, Octree3 &T) {
+    const int64_t n0[3] = {gd->nx, gd->ny, gd->nz};
+    std::unordered_map<uint64_t, int> tab;
+    tab.reserve((size_t)K * 2);
+    int lmax = 0;
+    for (int64_t e = 0; e < K; ++e) {
+        const int l = level[e];
+        if (l < 0 || l > 18) return IDP_E_ARG;
+        const int64_t c[3] = {ix[e], iy[e], iz[e]};
+        for (int a = 0; a < 3; ++a)
+            if (c[a] < 0 || c[a] >= (n0[a] << l)) return IDP_E_ARG;
+        if (!tab.emplace(leaf_key(l, c[0], c[1], c[2]), (int)e).second) return IDP_E_ARG;
+        lmax = l > lmax ? l : lmax;
+    }
+    // the leaves' volumes in finest cells add up to the box's (with the face
+    // checks below, no gap and no overlap)
+    unsigned __int128 vol = 0, box = (unsigned __int128)(n0[0] * n0[1] * n0[2]) << (3 * lmax);
+    for (int64_t e = 0; e < K; ++e) vol += (unsigned __int128)1 << (3 * (lmax - level[e]));
+    if (vol != box) return IDP_E_ARG;
+    auto find = [&](int l, int64_t x, int64_t y, int64_t z) -> int {
+        if (l < 0) return -1;
+        auto it = tab.find(leaf_key(l, x, y, z));
+        return it == tab.end() ? -1 : it->second;
+    };
+    const int NR = NP * NP, Q = 5 * NR;
+    T.nbr.assign((size_t)K * 6, -1);
+    T.lev.resize((size_t)K);
+    std::vector<char> small((size_t)K * 6, 0);
+    for (int64_t e = 0; e < K; ++e) {
+        const int l = level[e];
+        T.lev[e] = (signed char)l;
+        for (int s = 0; s < 6; ++s) {
+            const int d = s / 2, side = s & 1, a1 = (d + 1) % 3, a2 = (d + 2) % 3;
+            int64_t q[3] = {ix[e], iy[e], iz[e]};
+            const int64_t nl = n0[d] << l;
+            q[d] += side ? 1 : -1;
+            if (q[d] < 0 || q[d] >= nl) {
+                if (gd->bc[s] != IDP_BC_PERIODIC) { T.nbr[6 * e + s] = -1; continue; }
+                q[d] = (q[d] + nl) % nl;
+            }
+            const int f = find(l, q[0], q[1], q[2]);
+            if (f >= 0) { T.nbr[6 * e + s] = f; continue; }
+            if (find(l - 1, q[0] >> 1, q[1] >> 1, q[2] >> 1) >= 0) { small[6 * e + s] = 1; continue; }
+            // four finer leaves across the face: a mortar with e as its large leaf
+            int sm[4];
+            for (int p = 0; p < 4; ++p) {
+                int64_t r[3];
+                r[d] = 2 * q[d] + (side ? 0 : 1);
+                r[a1] = 2 * q[a1] + (p & 1);
+                r[a2] = 2 * q[a2] + (p >> 1);
+                sm[p] = find(l + 1, r[0], r[1], r[2]);
+                if (sm[p] < 0) return IDP_E_ARG;
+            }
+            const int m = T.M++;
+            T.info.insert(T.info.end(), {d, (int)e, side, sm[0], sm[1], sm[2], sm[3]});
+            T.nbr[6 * e + s] = -2 - m * Q;
+        }
+    }
+    // the small sides
+    for (int m = 0; m < T.M; ++m) {
+        const int *inf = &T.info[7 * m];
+        const int sS = 2 * inf[0] + (inf[2] ? 0 : 1);
+        for (int p = 0; p < 4; ++p) {
+            const int e = inf[3 + p];
+            if (!small[6 * e + sS]) return IDP_E_ARG;
+            small[6 * e + sS] = 2;
+            T.nbr[6 * e + sS] = -2 - (m * Q + (1 + p) * NR);
+        }
+    }
+    for (size_t k = 0; k < small.size(); ++k)
+        if (small[k] == 1) return IDP_E_ARG;
+    // slots and mortar nodes (first appearance in slot order)
+    const int NN = NR * NP, N = NP - 1;
+    std::unordered_map<int, int> mn_of;
+    T.slot_mn.resize((size_t)T.M * Q);
+    std::vector<int> slots;   // [MN][3]
+    for (int m = 0; m < T.M; ++m) {
+        const int *inf = &T.info[7 * m];
+        const int d = inf[0], low = inf[2];
+        for (int q = 0; q < Q; ++q) {
+            const int f = q / NR, t = q - f * NR;
+            const int e = f == 0 ? inf[1] : inf[3 + f - 1];
+            const int pos = (f == 0) == (low != 0) ? N : 0;
+            const int g = e * NN + node_of_host(NP, d, t, pos);
+            auto it = mn_of.find(g);
+            int mn;
+            if (it == mn_of.end()) {
+                mn = T.MN++;
+                mn_of.emplace(g, mn);
+                T.mn_node.push_back(g);
+                T.mn_cnt.push_back(0);
+                slots.insert(slots.end(), {-1, -1, -1});
+            } else {
+                mn = it->second;
+            }
+            if (T.mn_cnt[mn] >= 3) return IDP_E_ARG;   // not reached on a 2:1 octree
+            slots[3 * mn + T.mn_cnt[mn]++] = m * Q + q;
+            T.slot_mn[(size_t)m * Q + q] = mn;
+        }
+    }
+    T.mn_slot.resize((size_t)3 * T.MN);
+    for (int mn = 0; mn < T.MN; ++mn)
+        for (int c = 0; c < 3; ++c) T.mn_slot[(size_t)c * T.MN + mn] = slots[3 * mn + c];
     return IDP_OK;
 }
 
-idp_status idp3d_create(const idp3d_grid_desc *gd, int32_t N, double gamma, const idp3d_options *opts,
-                        idp3d_ctx **out) {
-    if (!out) return IDP_E_ARG;
-    *out = nullptr;
-    if (!gd || N < 1 || N > 4 || !(gamma > 1.0)) return IDP_E_ARG;
-    if (gd->nx < 1 || gd->ny < 1 || gd->nz < 1 || !(gd->x1 > gd->x0) || !(gd->y1 > gd->y0) || !(gd->z1 > gd->z0))
-        return IDP_E_ARG;
-    if ((long long)gd->nx * gd->ny * gd->nz > (1LL << 24)) return IDP_E_ARG;
+// the mortar operators of degree N and their 1D pair lists; false if the
+// overlap pattern exceeds the kernels' fixed sizes
+bool build_mops3(int N, MOps3 &mo) {
+    const int np = N + 1;
+    double I[2 * NPMAX3 * NPMAX3], P[NPMAX3 * 2 * NPMAX3], wt[NPMAX3 * 2 * NPMAX3], x[NPMAX3], S[NPMAX3 * NPMAX3];
+    std::memset(&mo, 0, sizeof(mo));
+    idp::host_lgl_mortar(N, I, P, wt);
+    idp::host_lgl_sbar(N, x, mo.w, S);
+    for (int r = 0; r < 2 * np; ++r)
+        for (int k = 0; k < np; ++k) mo.I[r][k] = I[r * np + k];
+    for (int k = 0; k < np; ++k)
+        for (int r = 0; r < 2 * np; ++r) { mo.P[k][r] = P[k * 2 * np + r]; mo.wt[k][r] = wt[k * 2 * np + r]; }
+    mo.n1 = 0;
+    for (int k = 0; k < np; ++k)
+        for (int r = 0; r < 2 * np; ++r)
+            if (mo.wt[k][r] != 0.0) {
+                if (mo.n1 >= 3 * np - 1 || mo.sn[k] >= 2 * np || mo.sn[np + r] >= 2 * np) return false;
+                const int p = mo.n1++;
+                mo.pk[p] = k; mo.pr[p] = r;
+                mo.sp[k][mo.sn[k]++] = p;
+                mo.sp[np + r][mo.sn[np + r]++] = p;
+            }
+    return true;
+}
+
+idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, const int32_t *ix, const int32_t *iy,
+                   const int32_t *iz, int32_t N, double gamma, const idp3d_options *opts, idp3d_ctx **out) {
+    if (N < 1 || N > 4 || !(gamma > 1.0)) return IDP_E_ARG;
+    if (!(gd->x1 > gd->x0) || !(gd->y1 > gd->y0) || !(gd->z1 > gd->z0)) return IDP_E_ARG;
     for (int s = 0; s < 6; ++s)
         if (gd->bc[s] < IDP_BC_PERIODIC || gd->bc[s] > IDP_BC_OUTFLOW) return IDP_E_ARG;
     for (int d = 0; d < 3; ++d)
@@ -170,11 +337,16 @@ idp_status idp3d_create(const idp3d_grid_desc *gd, int32_t N, double gamma, cons
     idp3d_options_default(&o);
     if (opts) o = *opts;
     if (o.limiting < 0 || o.limiting > 2 || !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0)) return IDP_E_ARG;
+    Octree3 T;
+    idp_status rs = build_octree3(gd, K, level, ix, iy, iz, N + 1, T);
+    if (rs != IDP_OK) return rs;
+    MOps3 mops;
+    if (!build_mops3(N, mops)) return IDP_E_ARG;
     idp3d_ctx *c = new (std::nothrow) idp3d_ctx();
     if (!c) return IDP_E_ARG;
     c->N = N; c->NP = N + 1; c->gamma = gamma; c->opt = o;
     Grid3 &G = c->grid;
-    G.nx = gd->nx; G.ny = gd->ny; G.nz = gd->nz; G.K = gd->nx * gd->ny * gd->nz;
+    G.nx = gd->nx; G.ny = gd->ny; G.nz = gd->nz; G.K = (int)K;
     G.dx = (gd->x1 - gd->x0) / gd->nx; G.dy = (gd->y1 - gd->y0) / gd->ny; G.dz = (gd->z1 - gd->z0) / gd->nz;
     for (int s = 0; s < 6; ++s) {
         G.bc[s] = gd->bc[s];
@@ -193,10 +365,42 @@ idp_status idp3d_create(const idp3d_grid_desc *gd, int32_t N, double gamma, cons
     }
     bool ok = true;
     auto chk = [&](cudaError_t e) { if (e != cudaSuccess) ok = false; };
+    auto upload = [&](auto **dst, const auto *src, size_t n) {
+        if (!ok) return;
+        chk(cudaMalloc((void **)dst, sizeof(*src) * n));
+        if (ok) chk(cudaMemcpy(*dst, src, sizeof(*src) * n, cudaMemcpyHostToDevice));
+    };
     const size_t kn = nodes_of(c);
     chk(c->L.prepare());
-    if (ok) chk(cudaMalloc(&c->d_ops, sizeof(Ops3)));
-    if (ok) chk(cudaMemcpy(c->d_ops, &ops, sizeof(Ops3), cudaMemcpyHostToDevice));
+    upload(&c->d_ops, &ops, 1);
+    upload(&c->d_nbr, T.nbr.data(), T.nbr.size());
+    upload(&c->d_lev, T.lev.data(), T.lev.size());
+    G.nbr = c->d_nbr;
+    G.lev = c->d_lev;
+    Mort3 &MO = G.mort;
+    std::memset(&MO, 0, sizeof(MO));
+    if (T.M > 0 && ok) {
+        const size_t S = (size_t)T.M * 5 * c->NP * c->NP, MN = (size_t)T.MN;
+        MO.M = T.M; MO.S = (int)S; MO.MN = T.MN;
+        upload(&c->d_mops, &mops, 1);
+        upload(&c->d_minfo, T.info.data(), T.info.size());
+        upload(&c->d_slot_mn, T.slot_mn.data(), T.slot_mn.size());
+        upload(&c->d_mn_node, T.mn_node.data(), T.mn_node.size());
+        upload(&c->d_mn_slot, T.mn_slot.data(), T.mn_slot.size());
+        upload(&c->d_mn_cnt, T.mn_cnt.data(), T.mn_cnt.size());
+        if (ok) chk(cudaMalloc(&c->d_mslot, sizeof(double) * 13 * S));
+        if (ok) chk(cudaMalloc(&c->d_hand, sizeof(double) * 15 * MN));
+        if (ok) chk(cudaMalloc(&c->d_ell, sizeof(double) * (size_t)T.M));
+        if (ok) chk(cudaMalloc(&c->d_mbad, sizeof(int) * (size_t)T.M));
+        if (ok) {
+            MO.info = c->d_minfo;
+            MO.chi = c->d_mslot; MO.clo = c->d_mslot + 5 * S;
+            MO.rbmin = c->d_mslot + 10 * S; MO.rbmax = c->d_mslot + 11 * S; MO.dsum = c->d_mslot + 12 * S;
+            MO.bad = c->d_mbad; MO.ell = c->d_ell;
+            MO.slot_mn = c->d_slot_mn; MO.mn_node = c->d_mn_node; MO.mn_slot = c->d_mn_slot; MO.mn_cnt = c->d_mn_cnt;
+            MO.h_uvol = c->d_hand; MO.h_res = c->d_hand + 5 * MN; MO.h_b = c->d_hand + 10 * MN;
+        }
+    }
     if (ok) chk(cudaMalloc(&c->d_buf1, sizeof(double) * NV * kn));
     if (ok) chk(cudaMalloc(&c->d_buf2, sizeof(double) * NV * kn));
     if (ok) chk(cudaMalloc(&c->d_part, sizeof(double) * NV * (size_t)G.K));
@@ -218,10 +422,56 @@ idp_status idp3d_create(const idp3d_grid_desc *gd, int32_t N, double gamma, cons
     return IDP_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+idp_status idp3d_options_default(idp3d_options *o) {
+    if (!o) return IDP_E_ARG;
+    o->limiting = 2;
+    o->beta = 0.1;
+    o->cfl = 0.5;
+    return IDP_OK;
+}
+
+idp_status idp3d_create(const idp3d_grid_desc *gd, int32_t N, double gamma, const idp3d_options *opts,
+                        idp3d_ctx **out) {
+    if (!out) return IDP_E_ARG;
+    *out = nullptr;
+    if (!gd || gd->nx < 1 || gd->ny < 1 || gd->nz < 1) return IDP_E_ARG;
+    const long long K = (long long)gd->nx * gd->ny * gd->nz;
+    if (K > (1LL << 24)) return IDP_E_ARG;
+    // the grid as level-0 leaves, e = (ez ny + ey) nx + ex
+    std::vector<int8_t> lev((size_t)K, 0);
+    std::vector<int32_t> ix((size_t)K), iy((size_t)K), iz((size_t)K);
+    for (long long e = 0; e < K; ++e) {
+        ix[e] = (int32_t)(e % gd->nx);
+        iy[e] = (int32_t)((e / gd->nx) % gd->ny);
+        iz[e] = (int32_t)(e / ((long long)gd->nx * gd->ny));
+    }
+    return create3(gd, K, lev.data(), ix.data(), iy.data(), iz.data(), N, gamma, opts, out);
+}
+
+idp_status idp3d_create_octree(const idp3d_grid_desc *base, int64_t n_leaves, const int8_t *level, const int32_t *ix,
+                               const int32_t *iy, const int32_t *iz, int32_t N, double gamma,
+                               const idp3d_options *opts, idp3d_ctx **out) {
+    if (!out) return IDP_E_ARG;
+    *out = nullptr;
+    if (!base || !level || !ix || !iy || !iz || n_leaves < 1 || n_leaves > (1LL << 24)) return IDP_E_ARG;
+    return create3(base, n_leaves, level, ix, iy, iz, N, gamma, opts, out);
+}
+
 idp_status idp3d_layout(const idp3d_ctx *c, int64_t *n_elems, int32_t *nodes_per_elem) {
     if (!c) return IDP_E_ARG;
     if (n_elems) *n_elems = c->grid.K;
     if (nodes_per_elem) *nodes_per_elem = c->NP * c->NP * c->NP;
+    return IDP_OK;
+}
+
+idp_status idp3d_mesh_info(const idp3d_ctx *c, int64_t *n_mortars, int64_t *n_mortar_nodes) {
+    if (!c) return IDP_E_ARG;
+    if (n_mortars) *n_mortars = c->grid.mort.M;
+    if (n_mortar_nodes) *n_mortar_nodes = c->grid.mort.MN;
     return IDP_OK;
 }
 
@@ -233,7 +483,7 @@ idp_status idp3d_rhs(idp3d_ctx *c, const double *u, double dt, double *rhs, void
     A.dt_host = dt;
     A.collect = 0;
     if (dt == 0.0) A.limiting = 0;   // the unlimited high-order residual
-    c->L.element(c->grid_el, st, c->grid, c->d_ops, A);
+    enqueue_stage(c, st, A, true);
     return cuda_ok(cudaGetLastError());
 }
 
@@ -243,6 +493,7 @@ idp_status idp3d_dt(idp3d_ctx *c, const double *u, double *dt_host, void *stream
     unsigned long long b = kInfBits;
     if (cudaMemcpyAsync(c->d_dtmin2, &kInfBits, sizeof(kInfBits), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return IDP_E_CUDA;
+    if (has_mortars(c)) c->L.mflux(st, c->grid, c->d_mops, u, c->gamma);
     c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, c->d_dtmin2, c->d_status);
     if (cudaMemcpyAsync(&b, c->d_dtmin2, sizeof(b), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
@@ -319,6 +570,9 @@ idp_status idp3d_limiter_stats(idp3d_ctx *c, idp3d_stats *out, void *stream) {
     out->n_stages = c->n_stages;
     std::memcpy(&out->min_rho, &a.min_rho_bits, sizeof(double));
     std::memcpy(&out->min_p, &a.min_p_bits, sizeof(double));
+    out->alpha_mortar = a.mort_area > 0.0 ? a.alpha_mort_a / a.mort_area : 0.0;
+    out->n_mortar_active = (int64_t)a.n_mort;
+    out->n_mortar_fallback = (int64_t)a.n_mort_fallback;
     c->n_stages = 0;
     if (reset_stats3(c, c->stream) != cudaSuccess) return IDP_E_CUDA;
     return read_status3(c);
@@ -328,7 +582,9 @@ void idp3d_destroy(idp3d_ctx *c) {
     if (!c) return;
     if (c->graph) cudaGraphExecDestroy(c->graph);
     void *ptrs[] = {c->d_ops, c->d_buf1, c->d_buf2, c->d_part, c->d_tot, c->d_dtmin, c->d_dtmin2, c->d_t,
-                    c->d_dtlast, c->d_status, c->d_stats};
+                    c->d_dtlast, c->d_status, c->d_stats, c->d_mops, c->d_nbr, c->d_lev, c->d_minfo,
+                    c->d_slot_mn, c->d_mn_node, c->d_mn_slot, c->d_mn_cnt, c->d_mbad, c->d_mslot, c->d_hand,
+                    c->d_ell};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_in) cudaEventDestroy(c->ev_in);

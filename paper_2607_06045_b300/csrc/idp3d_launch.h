@@ -6,7 +6,7 @@
 
 #include <cstddef>
 
-#include "idp3d.cuh"
+#include "idp3d_mortar.cuh"
 
 namespace idp3 {
 
@@ -17,6 +17,10 @@ struct Launchers3 {
     void (*element)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) = nullptr;
     void (*dt)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
                unsigned long long *dtmin, unsigned *status) = nullptr;
+    // the mortar kernels (grid: one block per mortar; apply: its own grid)
+    void (*mflux)(cudaStream_t st, const Grid3 &G, const MOps3 *mo, const double *u, double gamma) = nullptr;
+    void (*mfactor)(cudaStream_t st, const Grid3 &G, const Stage3 &A) = nullptr;
+    void (*mapply)(cudaStream_t st, const Grid3 &G, const Stage3 &A) = nullptr;
 };
 
 Launchers3 launchers3_np2();

@@ -484,6 +484,20 @@ void host_lgl_weights(int N, double *w) {
     lgl_nodes(N, x, w);
 }
 
+// the 1D mortar operators of degree N (the 3D contexts take their tensor
+// products): interpolation I[2(N+1)][N+1] to the two half-faces' nodes, the
+// exact L2 projection P[N+1][2(N+1)] back and the local overlap weights
+// wt[N+1][2(N+1)] (App. A), row-major, as the 2D contexts build them
+void host_lgl_mortar(int N, double *I, double *P, double *wt) {
+    Ops o;
+    build_ops(N, 1, 0, o);
+    const int np = N + 1;
+    for (int r = 0; r < 2 * np; ++r)
+        for (int k = 0; k < np; ++k) I[r * np + k] = o.I[r][k];
+    for (int k = 0; k < np; ++k)
+        for (int r = 0; r < 2 * np; ++r) { P[k * 2 * np + r] = o.P[k][r]; wt[k * 2 * np + r] = o.wt[k][r]; }
+}
+
 // LGL nodes and weights and Sbar (row-major, (N+1)^2) for degree N (the 3D
 // contexts), the operators the 2D contexts use
 void host_lgl_sbar(int N, double *x, double *w, double *S) {

@@ -31,6 +31,19 @@ void dt(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double
     k_dt3d<NP, EPB><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status);
 }
 
+void mflux(cudaStream_t st, const Grid3 &G, const MOps3 *mo, const double *u, double gamma) {
+    k_mflux3<NP><<<G.mort.M, kMortThreads3, 0, st>>>(G, mo, u, gamma);
+}
+
+void mfactor(cudaStream_t st, const Grid3 &G, const Stage3 &A) {
+    k_mfactor3<NP><<<G.mort.M, kMortThreads3, 0, st>>>(G, A);
+}
+
+void mapply(cudaStream_t st, const Grid3 &G, const Stage3 &A) {
+    const int blocks = (G.mort.MN + 255) / 256;
+    k_mapply3<NP><<<blocks < 1184 ? blocks : 1184, 256, 0, st>>>(G, A);
+}
+
 }  // namespace
 
 Launchers3 IDP3_CAT(launchers3_np, IDP3_NP)() {
@@ -42,6 +55,9 @@ Launchers3 IDP3_CAT(launchers3_np, IDP3_NP)() {
     L.prepare = prepare;
     L.element = element;
     L.dt = dt;
+    L.mflux = mflux;
+    L.mfactor = mfactor;
+    L.mapply = mapply;
     return L;
 }
 

@@ -65,8 +65,8 @@ EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", 
            "idp_amr_transfer", "idp_dgsem_adapt", "idp_dgsem_leaves", "idp_dgsem_mesh_tables"]
 
 
-EXPORTS3 = ["idp3d_options_default", "idp3d_create", "idp3d_layout", "idp3d_rhs", "idp3d_dt", "idp3d_step",
-            "idp3d_integrals", "idp3d_limiter_stats", "idp3d_destroy"]
+EXPORTS3 = ["idp3d_options_default", "idp3d_create", "idp3d_create_octree", "idp3d_layout", "idp3d_mesh_info",
+            "idp3d_rhs", "idp3d_dt", "idp3d_step", "idp3d_integrals", "idp3d_limiter_stats", "idp3d_destroy"]
 
 
 class GridDesc3(C.Structure):
@@ -83,7 +83,8 @@ class Options3(C.Structure):
 class LimiterStats3(C.Structure):
     _fields_ = [("alpha_mean", C.c_double), ("n_active", C.c_int64), ("n_viol_density", C.c_int64),
                 ("n_viol_pressure", C.c_int64), ("n_nonpositive", C.c_int64), ("n_stages", C.c_int64),
-                ("min_rho", C.c_double), ("min_p", C.c_double)]
+                ("min_rho", C.c_double), ("min_p", C.c_double), ("alpha_mortar", C.c_double),
+                ("n_mortar_active", C.c_int64), ("n_mortar_fallback", C.c_int64)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -135,7 +136,10 @@ def lib():
         L.idp_dgsem_mesh_tables.argtypes = [vp, i64p, ip, C.POINTER(C.c_uint8), ip, ip, ip, ip, ip, ip, ip, ip]
         L.idp3d_options_default.argtypes = [C.POINTER(Options3)]
         L.idp3d_create.argtypes = [C.POINTER(GridDesc3), C.c_int32, C.c_double, C.POINTER(Options3), C.POINTER(vp)]
+        L.idp3d_create_octree.argtypes = [C.POINTER(GridDesc3), C.c_int64, i8p, ip, ip, ip, C.c_int32, C.c_double,
+                                          C.POINTER(Options3), C.POINTER(vp)]
         L.idp3d_layout.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        L.idp3d_mesh_info.argtypes = [vp, i64p, i64p]
         L.idp3d_rhs.argtypes = [vp, vp, C.c_double, vp, vp]
         L.idp3d_dt.argtypes = [vp, vp, dp, vp]
         L.idp3d_step.argtypes = [vp, vp, C.c_int32, dp, dp, vp]
@@ -545,26 +549,40 @@ def options3(**kw) -> Options3:
 
 
 class Context3D:
-    """idp3d context for a conforming grid of hexahedra (a workloads.Grid3-like
-    object: nx, ny, nz, box, bc, bc_prim) and degree N (1..4)."""
+    """idp3d context for a grid of hexahedra (a workloads.Grid3-like object:
+    nx, ny, nz, box, bc, bc_prim) or the leaves of a 2:1 octree (a
+    workloads.Mesh3-like object: nx0, ny0, nz0, box, level, ix, iy, iz, bc,
+    bc_prim) and degree N (1..4)."""
 
     def __init__(self, grid, N: int, gamma: float = 1.4, opts: Optional[Options3] = None, **kw):
         if opts is None:
             opts = options3(**kw)
         self.grid, self.N, self.np, self.gamma, self.opts = grid, N, N + 1, gamma, opts
+        octree = hasattr(grid, "level")
         d = GridDesc3()
-        d.nx, d.ny, d.nz = grid.nx, grid.ny, grid.nz
+        d.nx, d.ny, d.nz = (grid.nx0, grid.ny0, grid.nz0) if octree else (grid.nx, grid.ny, grid.nz)
         d.x0, d.y0, d.z0, d.x1, d.y1, d.z1 = (float(v) for v in grid.box)
         for s in range(6):
             d.bc[s] = int(grid.bc[s])
             for v in range(5):
                 d.bc_prim[s][v] = float(np.asarray(grid.bc_prim)[s, v])
         h = C.c_void_p()
-        _check(lib().idp3d_create(C.byref(d), N, gamma, C.byref(opts), C.byref(h)), "idp3d_create")
+        if octree:
+            lev = np.ascontiguousarray(grid.level, dtype=np.int8)
+            ix, iy, iz = (np.ascontiguousarray(a, dtype=np.int32) for a in (grid.ix, grid.iy, grid.iz))
+            ip = C.POINTER(C.c_int32)
+            _check(lib().idp3d_create_octree(C.byref(d), C.c_int64(lev.size), lev.ctypes.data_as(C.POINTER(C.c_int8)),
+                                             ix.ctypes.data_as(ip), iy.ctypes.data_as(ip), iz.ctypes.data_as(ip), N,
+                                             C.c_double(gamma), C.byref(opts), C.byref(h)), "idp3d_create_octree")
+        else:
+            _check(lib().idp3d_create(C.byref(d), N, gamma, C.byref(opts), C.byref(h)), "idp3d_create")
         self._h = h
         K, npe = C.c_int64(), C.c_int32()
         lib().idp3d_layout(h, C.byref(K), C.byref(npe))
         self.K, self.nodes_per_elem = K.value, npe.value
+        M, MN = C.c_int64(), C.c_int64()
+        lib().idp3d_mesh_info(h, C.byref(M), C.byref(MN))
+        self.n_mortars, self.n_mortar_nodes = M.value, MN.value
 
     def close(self):
         if getattr(self, "_h", None):

@@ -163,3 +163,155 @@ def test_bad_arguments():
     bad = W.Grid3(2, 2, 2, bc=(o3d.BC_PERIODIC, o3d.BC_WALL) + (o3d.BC_PERIODIC,) * 4)
     with pytest.raises(idp.IdpError):
         idp.Context3D(bad, 2)
+
+
+# ----------------------------------------------------------------------------
+# 2:1 octrees with mortars
+# ----------------------------------------------------------------------------
+
+UNIT = (0.0, 0.0, 0.0, 1.0, 1.0, 1.0)
+MID = (0.34, 0.34, 0.34, 0.66, 0.66, 0.66)
+
+
+def octree(kind):
+    """small: the centre of a 3^3 periodic grid refined (six mortars, small
+    elements inside); large: everything but the centre refined (the centre
+    is the large element of six mortars), walls in x, Dirichlet and outflow
+    in y, periodic in z; extruded: a 2:1 quadtree extruded in z (levels 1
+    and 2, mortars normal to x and y)."""
+    if kind == "small":
+        return W.box_refined_mesh3(3, 3, 3, UNIT, MID)
+    if kind == "large":
+        bcp = np.zeros((6, 5))
+        bcp[:] = [1.2, 0.3, -0.2, 0.1, 1.5]
+        m = W.box_refined_mesh3(3, 3, 3, UNIT, MID, inside=False,
+                                bc=(o3d.BC_WALL, o3d.BC_WALL, o3d.BC_DIRICHLET, o3d.BC_OUTFLOW, o3d.BC_PERIODIC,
+                                    o3d.BC_PERIODIC))
+        m.bc_prim = bcp
+        return m
+    m2 = W.box_refined_mesh(3, 2, (0.0, 0.0, 0.9, 0.6), (0.25, 0.2, 0.6, 0.45), base_level=1)
+    return W.extruded_mesh3(m2, 0.0, 0.4)[0]
+
+
+def sphere3(m, N, centre=(1 / 3, 0.4, 0.45), r0=0.15):
+    X, Y, Z = W.node_coords3(m, N)
+    inside = ((X - centre[0]) ** 2 + (Y - centre[1]) ** 2 + (Z - centre[2]) ** 2) < r0 ** 2
+    rho = 1.0 + 0.5 * np.sin(2 * np.pi * X) * np.sin(2 * np.pi * Y) * np.cos(2 * np.pi * Z) + 2.0 * inside
+    one = np.ones_like(X)
+    return W.conserved3(rho, 0.3 * one, -0.2 * one, 0.25 * one, 1.0 + 4.0 * inside, G)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+@pytest.mark.parametrize("kind", ["small", "large", "extruded"])
+def test_octree_rhs(N, kind):
+    m = octree(kind)
+    o = o3d.Oracle3D(m, N)
+    for state in ("random", "sphere"):
+        if state == "random":
+            u = W.random3_state(m, N, seed=10 * N + len(kind), rho_range=(0.3, 3.0), p_range=(0.3, 3.0), vmax=1.0)
+        else:
+            u = sphere3(m, N)
+        dt_idp = o.dt(u, cfl=1.0)
+        sc = scale(u, dt_idp)
+        for lim in (0, 1, 2):
+            ctx = idp.Context3D(m, N, limiting=lim)
+            assert ctx.n_mortars == o.M > 0
+            dt = 0.0 if lim == 0 else 0.5 * dt_idp
+            e = rel(gpu_rhs(ctx, u, dt), o.rhs(u, dt=dt, limiting=lim), sc)
+            assert e <= 1e-12, (state, lim, e)
+            ctx.close()
+
+
+def test_octree_rhs_with_inadmissible_interpolation():
+    """A rough state whose large-side interpolation leaves the admissible set
+    on some mortars: those keep their low-order flux (R16)."""
+    m, N = octree("large"), 2
+    u = W.random3_state(m, N, seed=6, rho_range=(0.1, 10.0), p_range=(0.1, 10.0), vmax=2.0)
+    o = o3d.Oracle3D(m, N)
+    dt_idp = o.dt(u, cfl=1.0)
+    sc = scale(u, dt_idp)
+    for lim, dt in ((0, 0.0), (2, 0.5 * dt_idp)):
+        ctx = idp.Context3D(m, N, limiting=lim)
+        e = rel(gpu_rhs(ctx, u, dt), o.rhs(u, dt=dt, limiting=lim), sc)
+        assert e <= 1e-12, (lim, e)
+        ctx.close()
+
+
+@pytest.mark.parametrize("N", [1, 3, 4])
+@pytest.mark.parametrize("kind", ["small", "large"])
+def test_octree_dt(N, kind):
+    m = octree(kind)
+    u = W.random3_state(m, N, seed=3)
+    o = o3d.Oracle3D(m, N)
+    ctx = idp.Context3D(m, N, cfl=0.7)
+    d_g, d_o = ctx.idp3d_dt(dev(u)), o.dt(u, cfl=0.7)
+    assert abs(d_g - d_o) <= 1e-13 * d_o
+    ctx.close()
+
+
+@pytest.mark.parametrize("N,lim,kind", [(2, 2, "small"), (3, 1, "large"), (3, 2, "large"), (4, 2, "small"),
+                                        (3, 2, "extruded")])
+def test_octree_steps(N, lim, kind):
+    import torch
+    m = octree(kind)
+    u = sphere3(m, N) if kind != "extruded" else W.random3_state(m, N, seed=N)
+    o = o3d.Oracle3D(m, N)
+    u_o, t_o, _, st_o = o.step(u, 20, cfl=0.5, limiting=lim)
+    ctx = idp.Context3D(m, N, limiting=lim, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    rc, _ = ctx.idp3d_step(ud, 20, t)
+    assert rc == idp.IDP_OK
+    torch.cuda.synchronize()
+    sc = np.abs(u_o).reshape(5, -1).max(axis=1)
+    err = (np.abs(ud.cpu().numpy() - u_o).reshape(5, -1).max(axis=1) / sc).max()
+    assert err <= 1e-10, err
+    assert abs(t[0] - t_o) <= 1e-12 * t_o
+    rc, st = ctx.idp3d_limiter_stats()
+    assert rc == idp.IDP_OK
+    assert st["n_viol_density"] == 0 and st["n_viol_pressure"] == 0 and st["n_nonpositive"] == 0
+    assert st["n_stages"] == 60
+    assert (st["n_mortar_active"] > 0) == (st_o["n_mort_active"] > 0)
+    ctx.close()
+
+
+def test_octree_blast_conservation_and_positivity():
+    import torch
+    N = 3
+    m = W.box_refined_mesh3(4, 4, 4, UNIT, (0.3, 0.3, 0.3, 0.7, 0.7, 0.7))
+    u = W.blast3_state(m, N, rho_bg=1e-5, p_bg=1e-6, rho_in=1.0, p_in=1e2, centre=(0.45, 0.5, 0.55), r0=0.2)
+    ctx = idp.Context3D(m, N, limiting=1, cfl=0.9)
+    assert ctx.n_mortars > 0
+    ud = dev(u)
+    I0 = ctx.idp3d_integrals(ud)
+    t = np.zeros(1)
+    rc, _ = ctx.idp3d_step(ud, 40, t)
+    assert rc == idp.IDP_OK
+    I1 = ctx.idp3d_integrals(ud)
+    assert np.abs(I1 - I0).max() <= 1e-12 * np.abs(I0).max()
+    q = ud.cpu().numpy().reshape(5, -1)
+    p = (G - 1.0) * (q[4] - 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / q[0])
+    assert q[0].min() > 0.0 and p.min() > 0.0
+    rc, st = ctx.idp3d_limiter_stats()
+    assert st["n_nonpositive"] == 0 and st["n_viol_pressure"] == 0 and st["n_mortar_active"] > 0
+    torch.cuda.synchronize()
+    ctx.close()
+
+
+def test_octree_bad_meshes():
+    m = octree("small")
+    # a level jump of two across a face: one small child refined again
+    k = int(np.flatnonzero(m.level == 1)[0])
+    lev, ix, iy, iz = (list(a) for a in (m.level, m.ix, m.iy, m.iz))
+    a, b, c = ix.pop(k), iy.pop(k), iz.pop(k)
+    lev.pop(k)
+    for q in range(8):
+        lev.append(2); ix.append(2 * a + (q & 1)); iy.append(2 * b + ((q >> 1) & 1)); iz.append(2 * c + (q >> 2))
+    bad = W.Mesh3(3, 3, 3, UNIT, np.array(lev, np.int8), np.array(ix, np.int32), np.array(iy, np.int32),
+                  np.array(iz, np.int32))
+    with pytest.raises(idp.IdpError):
+        idp.Context3D(bad, 2)
+    # a gap: one leaf left out
+    gap = W.Mesh3(3, 3, 3, UNIT, m.level[1:], m.ix[1:], m.iy[1:], m.iz[1:])
+    with pytest.raises(idp.IdpError):
+        idp.Context3D(gap, 2)
