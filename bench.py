@@ -396,10 +396,16 @@ def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn):
     return step_ms * 1e-3, el_ms, el_n, kern
 
 
-def bench_3d(idp, flush, stream, args, n=40, N=3):
+def bench_3d(idp, flush, stream, args, n=40, N=3, octree=False):
+    """The 3D blast on an n^3 grid, or (octree) on an n^3 base grid with the
+    leaves in [1/4, 3/4]^3 refined once: 2:1 mortars around the block."""
     import torch
     from paper_2607_06045_b300 import workloads as W
-    g = W.Grid3(n, n, n, bc=(3,) * 6)
+    if octree:
+        g = W.box_refined_mesh3(n, n, n, (0.0, 0.0, 0.0, 1.0, 1.0, 1.0), (0.25, 0.25, 0.25, 0.75, 0.75, 0.75),
+                                bc=(3,) * 6)
+    else:
+        g = W.Grid3(n, n, n, bc=(3,) * 6)
     u = W.blast3_state(g, N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0)
     ctx = idp.Context3D(g, N, limiting=2, cfl=0.5)
     ud = torch.from_numpy(u).cuda()
@@ -421,11 +427,18 @@ def bench_3d(idp, flush, stream, args, n=40, N=3):
     rc, st = ctx.idp3d_limiter_stats()
     dofs = g.n_elems * (N + 1) ** 3
     ms = float(np.mean(times))
+    mesh_text = (f"{n}^3 base hexahedra with [1/4, 3/4]^3 refined once ({g.n_elems} leaves, {ctx.n_mortars} "
+                 f"mortars)" if octree else f"{n}^3 hexahedra")
+    launches = 5 + (10 if octree else 0)   # dt, 3 stages, advance; mortar flux, factor, apply per stage
     out = dict(value=dofs * 3 / (ms * 1e-3), unit=UNIT, ms_per_step=ms, ms_per_step_median=float(np.median(times)),
-               steps=steps, elements=g.n_elems, dofs=dofs, gpu_launches=5 * steps,
-               workload=f"3D blast: [0,1]^3, {n}^3 hexahedra, N={N}, sphere r < 0.15 at p = 10 in a gas at "
+               steps=steps, elements=g.n_elems, dofs=dofs, gpu_launches=launches * steps,
+               workload=f"3D blast: [0,1]^3, {mesh_text}, N={N}, sphere r < 0.15 at p = 10 in a gas at "
                         "rho = 1, p = 0.1, outflow, local limiting (d = 3, Gamma = 6), FP64",
-               stats={k: st[k] for k in ("alpha_mean", "n_viol_density", "n_viol_pressure", "n_nonpositive")})
+               stats={k: st[k] for k in ("alpha_mean", "n_viol_density", "n_viol_pressure", "n_nonpositive",
+                                         "alpha_mortar", "n_mortar_active", "n_mortar_fallback")})
+    if octree:
+        out["mortars"] = ctx.n_mortars
+        out["mortar_nodes"] = ctx.n_mortar_nodes
     ctx.close()
     return out
 
@@ -658,6 +671,9 @@ def run_ours(args):
     # (4.1M DOFs), local limiting, FP64; per-step CUDA events on the
     # launching stream, L2 flushed between steps
     variants["blast3d"] = bench_3d(idp, flush, stream, args)
+    # the same blast on a 2:1 octree: 32^3 base, [1/4, 3/4]^3 refined once
+    # (61,440 leaves, 1,536 mortars, 3.9M DOFs)
+    variants["blast3d_octree"] = bench_3d(idp, flush, stream, args, n=32, octree=True)
     variants["dt_rules"] = {"idp": dts[0], "low_order_cfl": dts[1], "ratio": dts[1] / dts[0],
                             "note": "cfl = 1 on the initial state; steps to a fixed time scale with 1 / dt"}
     # near-vacuum blast (512 x 512 base + 2 levels, N = 5), FP32 form
@@ -717,6 +733,16 @@ def run_ours(args):
                                flops_per_node_stage=f3,
                                flops_source="oracle op-counting build, 3D (method_work.json: 3d), one flop per "
                                             "operation; the whole step (time step, three stages, advance)")
+    # 3D octree: the method's work per node (all rows but the mortars') and
+    # per mortar, from the counting build on the same mesh at 1/64 size
+    bo = variants["blast3d_octree"]
+    to = json.load(open(os.path.join(ROOT, "paper_2607_06045_b300", "method_work.json")))["3d_octree"]["degrees"]["3"]
+    fo = to["node_flops_per_node_stage"] * bo["dofs"] + to["mortar_flops_per_mortar_stage"] * bo["mortars"]
+    acho = fo * 3 / (bo["ms_per_step"] * 1e-3) * 1e-12
+    bo["step_roofline"] = dict(bound="alu", achieved=acho, peak=peak, unit="TFLOP/s", frac=acho / peak,
+                               flops_per_stage=fo,
+                               flops_source="oracle op-counting build, 3D octree (method_work.json: 3d_octree): "
+                                            "per node and per mortar; the whole step")
     bval = bnodes_all * 3 * bsteps / btot   # the whole batch over the slowest rank
     hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0

@@ -256,6 +256,8 @@ static void o3_count_node_prep(const o3_ctx *c, const cdbl *u) {
 
 /* One counted SSP-RK3 step of the 3D oracle (conforming grid, as o3_create
    takes it); counts[row][class] as for opc_count_step; u advanced in place. */
+static int count_step3_ctx(o3_ctx *c, double *u_io, double cfl, int limiting, long long *counts);
+
 extern "C" int opc_count_step3(int N, double gamma, int nx, int ny, int nz, const double *box, const int32_t *bc,
                                const double *bc_prim, double *u_io, double cfl, int limiting, long long *counts) {
     std::vector<cdbl> bx(6), bcp(30);
@@ -264,6 +266,24 @@ extern "C" int opc_count_step3(int N, double gamma, int nx, int ny, int nz, cons
     int err = 0;
     o3_ctx *c = o3_create(N, gamma, nx, ny, nz, bx.data(), bc, bcp.data(), &err);
     if (!c) return 1;
+    return count_step3_ctx(c, u_io, cfl, limiting, counts);
+}
+
+/* the same on the leaves of a 2:1 octree */
+extern "C" int opc_count_step3_leaves(int N, double gamma, int nx0, int ny0, int nz0, const double *box, int K,
+                                      const int8_t *level, const int32_t *ix, const int32_t *iy, const int32_t *iz,
+                                      const int32_t *bc, const double *bc_prim, double *u_io, double cfl,
+                                      int limiting, long long *counts) {
+    std::vector<cdbl> bx(6), bcp(30);
+    for (int k = 0; k < 6; ++k) bx[k] = box[k];
+    for (int k = 0; k < 30; ++k) bcp[k] = bc_prim[k];
+    int err = 0;
+    o3_ctx *c = o3_create_leaves(N, gamma, nx0, ny0, nz0, bx.data(), K, level, ix, iy, iz, bc, bcp.data(), &err);
+    if (!c) return 1;
+    return count_step3_ctx(c, u_io, cfl, limiting, counts);
+}
+
+static int count_step3_ctx(o3_ctx *c, double *u_io, double cfl, int limiting, long long *counts) {
     size_t n = 5 * (size_t)c->nn;
     std::vector<cdbl> u(n);
     for (size_t k = 0; k < n; ++k) u[k] = cdbl::mk(u_io[k], true);

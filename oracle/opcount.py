@@ -92,8 +92,9 @@ def count_step(mesh, N, u, cfl=0.5, limiting=2, gamma=1.4, vflux=0, t0=0.0):
 
 
 def count_step3(grid, N, u, cfl=0.5, limiting=2, gamma=1.4):
-    """One counted SSP-RK3 step of the 3D oracle on a conforming grid.
-    Returns (counts[row][class], u after the step)."""
+    """One counted SSP-RK3 step of the 3D oracle on a grid (workloads.Grid3)
+    or an octree (workloads.Mesh3). Returns (counts[row][class], u after the
+    step)."""
     L = lib()
     nrow = L.opc_n_rows()
     box = np.ascontiguousarray(grid.box, dtype=np.float64)
@@ -101,10 +102,19 @@ def count_step3(grid, N, u, cfl=0.5, limiting=2, gamma=1.4):
     bcp = np.ascontiguousarray(grid.bc_prim, dtype=np.float64).reshape(30)
     uu = np.ascontiguousarray(u, dtype=np.float64).copy()
     out = np.zeros(nrow * len(CLASSES), dtype=np.int64)
-    dp = C.POINTER(C.c_double)
-    rc = L.opc_count_step3(N, gamma, grid.nx, grid.ny, grid.nz, box.ctypes.data_as(dp),
-                           bc.ctypes.data_as(C.POINTER(C.c_int32)), bcp.ctypes.data_as(dp), uu.ctypes.data_as(dp),
-                           cfl, limiting, out.ctypes.data_as(C.POINTER(C.c_longlong)))
+    dp, ip = C.POINTER(C.c_double), C.POINTER(C.c_int32)
+    if hasattr(grid, "level"):
+        lev = np.ascontiguousarray(grid.level, dtype=np.int8)
+        ix, iy, iz = (np.ascontiguousarray(a, dtype=np.int32) for a in (grid.ix, grid.iy, grid.iz))
+        rc = L.opc_count_step3_leaves(N, C.c_double(gamma), grid.nx0, grid.ny0, grid.nz0, box.ctypes.data_as(dp),
+                                      int(lev.size), lev.ctypes.data_as(C.POINTER(C.c_int8)), ix.ctypes.data_as(ip),
+                                      iy.ctypes.data_as(ip), iz.ctypes.data_as(ip), bc.ctypes.data_as(ip),
+                                      bcp.ctypes.data_as(dp), uu.ctypes.data_as(dp), C.c_double(cfl), limiting,
+                                      out.ctypes.data_as(C.POINTER(C.c_longlong)))
+    else:
+        rc = L.opc_count_step3(N, gamma, grid.nx, grid.ny, grid.nz, box.ctypes.data_as(dp), bc.ctypes.data_as(ip),
+                               bcp.ctypes.data_as(dp), uu.ctypes.data_as(dp), cfl, limiting,
+                               out.ctypes.data_as(C.POINTER(C.c_longlong)))
     if rc != 0:
         raise ValueError("counting build rejected the grid")
     cnt = out.reshape(nrow, len(CLASSES))
@@ -164,11 +174,46 @@ def work_table3(degrees=(1, 2, 3, 4), n=10):
     return out
 
 
+MORTAR_ROWS = ["mortar_flux", "mortar_limit"]
+
+
+def work_table3_octree(degrees=(1, 2, 3, 4), n=8):
+    """The 3D scheme's work on a 2:1 octree, split into a part per node and a
+    part per mortar: a counted step of the 3D blast on an n^3 base grid with
+    [1/4, 3/4]^3 refined once (the octree benchmark's mesh at 1/64 of its
+    size); per node and stage the method rows other than the mortar rows, per
+    mortar and stage the mortar rows (mortar fluxes and their graph terms,
+    mortar limiting)."""
+    sys.path.insert(0, os.path.dirname(_HERE))
+    from paper_2607_06045_b300 import workloads as W
+    from oracle import o3d
+    g = W.box_refined_mesh3(n, n, n, (0.0, 0.0, 0.0, 1.0, 1.0, 1.0), (0.25, 0.25, 0.25, 0.75, 0.75, 0.75),
+                            bc=(3,) * 6)
+    out = {"workload": f"3D blast, {n}^3 base hexahedra over [0,1]^3 with [1/4, 3/4]^3 refined once "
+                       f"({g.n_elems} leaves), one SSP-RK3 step, local limiting, CFL 0.5",
+           "elements": int(g.n_elems), "degrees": {}}
+    for N in degrees:
+        M = o3d.Oracle3D(g, N).M
+        u = W.blast3_state(g, N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0)
+        c, _ = count_step3(g, N, u)
+        nodes = g.n_elems * (N + 1) ** 3
+        pn = per_node_stage(c, nodes)
+        pm = {r: {k: v / (3.0 * M) for k, v in c[r].items()} for r in MORTAR_ROWS}
+        node_rows = [r for r in METHOD_ROWS if r not in MORTAR_ROWS]
+        out["degrees"][str(N)] = {
+            "nodes": nodes, "mortars": M,
+            "node_flops_per_node_stage": round(sum(flops(pn[r]) for r in node_rows), 3),
+            "mortar_flops_per_mortar_stage": round(sum(flops(pm[r]) for r in MORTAR_ROWS), 3),
+            "mortar_rows": {r: round(flops(pm[r]), 3) for r in MORTAR_ROWS}}
+    return out
+
+
 TABLE = os.path.join(os.path.dirname(_HERE), "paper_2607_06045_b300", "method_work.json")
 
 if __name__ == "__main__":
     t = work_table()
     t["3d"] = work_table3()
+    t["3d_octree"] = work_table3_octree()
     with open(TABLE, "w") as f:
         json.dump(t, f, indent=1, sort_keys=True)
         f.write("\n")

@@ -98,3 +98,23 @@ def test_stored_3d_table_matches_the_counting_build():
     stored = t3["degrees"][str(N)]["rows"]
     for r in OC.ROWS:
         assert stored[r]["flops"] == pytest.approx(round(OC.flops(pn[r]), 3), abs=1e-3), r
+
+
+def test_counted_3d_octree_step_is_the_oracle():
+    from oracle import o3d
+    m = W.box_refined_mesh3(4, 4, 4, (0.0, 0.0, 0.0, 1.0, 1.0, 1.0), (0.25, 0.25, 0.25, 0.75, 0.75, 0.75),
+                            bc=(3,) * 6)
+    N = 2
+    u = W.blast3_state(m, N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0, centre=(0.4, 0.5, 0.5), r0=0.3)
+    _, u1 = OC.count_step3(m, N, u)
+    u2, *_ = o3d.Oracle3D(m, N).step(u, 1, cfl=0.5, limiting=2)
+    assert np.array_equal(u1.reshape(u2.shape), u2)
+
+
+def test_stored_3d_octree_table_matches_the_counting_build():
+    t = R.method_table()["3d_octree"]
+    fresh = OC.work_table3_octree(degrees=(1,))
+    assert fresh["elements"] == t["elements"]
+    a, b = t["degrees"]["1"], fresh["degrees"]["1"]
+    for k in ("node_flops_per_node_stage", "mortar_flops_per_mortar_stage", "mortars", "nodes"):
+        assert a[k] == pytest.approx(b[k], abs=1e-3), k
