@@ -11,7 +11,8 @@ import numpy as np
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("--workload", default="dmr", choices=["dmr", "square", "blast", "batched", "blast3d"])
+    ap.add_argument("--workload", default="dmr",
+                    choices=["dmr", "square", "blast", "batched", "blast3d", "blast3d_octree"])
     ap.add_argument("--n3", type=int, default=40, help="3D: elements per direction")
     ap.add_argument("--precision", type=int, default=0)
     ap.add_argument("--steps", type=int, default=3)
@@ -25,15 +26,19 @@ def main(argv=None):
     from paper_2607_06045_b300 import build, idp
     from paper_2607_06045_b300 import workloads as W
     build.build()
-    if a.workload == "blast3d":
-        g = W.Grid3(a.n3, a.n3, a.n3, bc=(3,) * 6)
+    if a.workload in ("blast3d", "blast3d_octree"):
+        if a.workload == "blast3d":
+            g = W.Grid3(a.n3, a.n3, a.n3, bc=(3,) * 6)
+        else:   # the n3^3 base grid with [1/4, 3/4]^3 refined once
+            g = W.box_refined_mesh3(a.n3, a.n3, a.n3, (0.0, 0.0, 0.0, 1.0, 1.0, 1.0),
+                                    (0.25, 0.25, 0.25, 0.75, 0.75, 0.75), bc=(3,) * 6)
         u = W.blast3_state(g, a.N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0)
         ctx = idp.Context3D(g, a.N, limiting=a.limiting, cfl=0.5)
         ud = torch.from_numpy(u).cuda()
         t = np.zeros(1)
         ctx.idp3d_step(ud, a.steps, t)
         torch.cuda.synchronize()
-        print(f"ok: blast3d K={ctx.K} steps={a.steps} t={t[0]}")
+        print(f"ok: {a.workload} K={ctx.K} mortars={ctx.n_mortars} steps={a.steps} t={t[0]}")
         return
     if a.workload == "dmr":
         meshes = W.dmr_mesh(); u = W.dmr_state(meshes, a.N)
