@@ -68,6 +68,7 @@ struct Grid3 {
     double bc_cons[6][NV];
     const int *nbr;
     const signed char *lev;
+    const idp::LogTab *lg;           // table of the FP64 logarithm
     Mort3 mort;
 };
 
@@ -114,38 +115,6 @@ __device__ __forceinline__ double stage_dt3(const Stage3 &A) {
 
 __device__ __forceinline__ double pres3(double g, const double *u) {
     return (g - 1.0) * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * idp::fast_rcp(u[0]));
-}
-
-__device__ __forceinline__ void flux3(double g, const double *u, int d, double *f) {
-    const double p = pres3(g, u), vn = u[1 + d] / u[0];
-    f[0] = u[1 + d];
-    f[1] = u[1] * vn + (d == 0 ? p : 0.0);
-    f[2] = u[2] * vn + (d == 1 ? p : 0.0);
-    f[3] = u[3] * vn + (d == 2 ? p : 0.0);
-    f[4] = (u[4] + p) * vn;
-}
-
-__device__ __forceinline__ double wave3(double g, const double *u, int d) {
-    return fabs(u[1 + d] / u[0]) + sqrt(g * pres3(g, u) / u[0]);
-}
-
-// R2: logarithmic mean, Ismail-Roe series below u = 1e-4
-__device__ __forceinline__ double logmean3(double a, double b) {
-    const double f = (a - b) / (a + b), uu = f * f;
-    if (uu < 1e-4) return (a + b) / (2.0 * (1.0 + uu / 3.0 + uu * uu / 5.0 + uu * uu * uu / 7.0));
-    return (a - b) / log(a / b);
-}
-
-// R1 along axis d from the two states and their primitives (v, p)
-__device__ __forceinline__ void ranocha3(double g, const double *uL, const double *vL, double pL,
-                                         const double *uR, const double *vR, double pR, int d, double *f) {
-    const double rho_ln = logmean3(uL[0], uR[0]);
-    const double bet_ln = logmean3(uL[0] / pL, uR[0] / pR);
-    const double vdot = vL[0] * vR[0] + vL[1] * vR[1] + vL[2] * vR[2];
-    const double fr = rho_ln * 0.5 * (vL[d] + vR[d]);
-    f[0] = fr;
-    for (int a = 0; a < 3; ++a) f[1 + a] = fr * 0.5 * (vL[a] + vR[a]) + (a == d ? 0.5 * (pL + pR) : 0.0);
-    f[4] = fr * (0.5 * vdot + 1.0 / ((g - 1.0) * bet_ln)) + 0.5 * (pL * vR[d] + pR * vL[d]);
 }
 
 // R8 with 5 variables: the largest theta <= hi with rho(u0 + theta a) > 0
@@ -300,30 +269,33 @@ struct Launch3 {
     static constexpr int items = EPB * NP * NP * NP, threads = (items + 31) / 32 * 32;
 };
 
-// logarithmic mean of a and b from their logarithms (R2): (a - b) / (la - lb),
-// and the Ismail-Roe series where ((a - b)/(a + b))^2 < 1e-4 (the branch
-// test taken in FP32: the two forms agree to rounding near the threshold)
-__device__ __forceinline__ double logmean_l(double a, double b, double la, double lb) {
-    const double x = a + b, y = a - b;
-    const float yf = (float)y, xf = (float)x;
-    if (yf * yf < 1e-4f * xf * xf) {
-        const double ix = idp::fast_rcp(x), uu = (y * ix) * (y * ix);
-        // x / (2 F(u)) with 1/F = 1 - u/3 - 4u^2/45 - 44u^3/945
-        return 0.5 * x * (1.0 - uu * (1.0 / 3.0 + uu * (4.0 / 45.0 + uu * (44.0 / 945.0))));
+// Both logarithmic means of a pair (R2) from the node logarithms, with one
+// reciprocal: rho_ln = (ra - rb) / (ln ra - ln rb) and 1 / beta_ln = (ln ba -
+// ln bb) / (ba - bb), each by the Ismail-Roe series where ((a - b)/(a + b))^2
+// <= 1e-4 (the test in FP32, converted on the integer pipe: the two forms
+// agree to rounding near the threshold).
+__device__ __forceinline__ void log_means3(double ra, double rb, double lra, double lrb, double ba, double bb,
+                                           double lba, double lbb, double &rho_ln, double &ibeta) {
+    const double dr = ra - rb, sr = ra + rb, db = ba - bb, sb = ba + bb;
+    const float drf = idp::d2f(dr), srf = idp::d2f(sr), dbf = idp::d2f(db), sbf = idp::d2f(sb);
+    const bool nr = drf * drf <= 1e-4f * (srf * srf), nb = dbf * dbf <= 1e-4f * (sbf * sbf);
+    const double Xr = nr ? sr : lra - lrb, Xb = nb ? sb : db;
+    const double R = idp::fast_rcp(Xr * Xb);
+    const double ixr = Xb * R, ixb = Xr * R;   // 1 / Xr, 1 / Xb
+    if (nr) {
+        const double f = dr * ixr, u = f * f;
+        // sr / (2 F(u)) with 1/F = 1 - u/3 - 4u^2/45 - 44u^3/945
+        rho_ln = 0.5 * sr * (1.0 - u * (1.0 / 3.0 + u * (4.0 / 45.0 + u * (44.0 / 945.0))));
+    } else {
+        rho_ln = dr * ixr;
     }
-    return y * idp::fast_rcp(la - lb);
-}
-
-// 1 / (logarithmic mean) of a and b from their logarithms
-__device__ __forceinline__ double inv_logmean_l(double a, double b, double la, double lb) {
-    const double x = a + b, y = a - b;
-    const float yf = (float)y, xf = (float)x;
-    if (yf * yf < 1e-4f * xf * xf) {
-        const double ix = idp::fast_rcp(x), uu = (y * ix) * (y * ix);
-        // 2 F(u) / x with F = 1 + u/3 + u^2/5 + u^3/7
-        return 2.0 * ix * (1.0 + uu * (1.0 / 3.0 + uu * (1.0 / 5.0 + uu * (1.0 / 7.0))));
+    if (nb) {
+        const double f = db * ixb, u = f * f;
+        // 2 F(u) / sb with F = 1 + u/3 + u^2/5 + u^3/7
+        ibeta = 2.0 * ixb * (1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0))));
+    } else {
+        ibeta = (lba - lbb) * ixb;
     }
-    return (la - lb) * idp::fast_rcp(y);
 }
 
 // physical flux along d from the state and its velocity along d and pressure
@@ -381,8 +353,8 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         }
         const double c = idp::fast_sqrt(g * p * ir);
         const double bet = uv[0] * idp::fast_rcp(p);
-        S[le].pr[4][n] = log(uv[0]);
-        S[le].pr[5][n] = log(bet);
+        S[le].pr[4][n] = idp::fast_log(uv[0], G.lg);
+        S[le].pr[5][n] = idp::fast_log(bet, G.lg);
         S[le].pr[6][n] = bet;
         S[le].lam[0][n] = fabs(v1) + c; S[le].lam[1][n] = fabs(v2) + c; S[le].lam[2][n] = fabs(v3) + c;
     }
@@ -424,9 +396,10 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int b = a + 1 + rem;
         const int na = node_of<NP>(d, r, a), nb = node_of<NP>(d, r, b);
         const SM &X = S[le];
-        const double rho_ln = logmean_l(X.u[0][na], X.u[0][nb], X.pr[4][na], X.pr[4][nb]);
+        double rho_ln, iba;
+        log_means3(X.u[0][na], X.u[0][nb], X.pr[4][na], X.pr[4][nb], X.pr[6][na], X.pr[6][nb], X.pr[5][na],
+                   X.pr[5][nb], rho_ln, iba);
         const double pa = X.pr[3][na], pb = X.pr[3][nb];
-        const double iba = inv_logmean_l(X.pr[6][na], X.pr[6][nb], X.pr[5][na], X.pr[5][nb]);
         double va[3], vb[3];
         for (int cc = 0; cc < 3; ++cc) { va[cc] = X.pr[cc][na]; vb[cc] = X.pr[cc][nb]; }
         // R1 (Ranocha) along d
@@ -463,7 +436,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         for (int v = 0; v < NV; ++v) { ui[v] = X.u[v][nin]; uo[v] = X.outs[s][t][v]; }
         flux_p(ui, X.pr[d][nin], X.pr[3][nin], d, fi);
         flux_p(uo, X.outp[s][t][0], X.outp[s][t][1], d, fo);
-        const double lam = fmax(X.lam[d][nin], X.outp[s][t][2]);
+        const double lam = idp::dmax(X.lam[d][nin], X.outp[s][t][2]);
         const double wt = ops.w[t % NP] * ops.w[t / NP], cw = wt * q[d];
         // left state first: the outside is on the left of a low face
         const double *uL = side ? ui : uo, *uR = side ? uo : ui, *fL = side ? fi : fo, *fR = side ? fo : fi;
@@ -485,7 +458,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         for (int v = 0; v < NV; ++v) { ul[v] = X.u[v][nl]; ur[v] = X.u[v][nr]; }
         flux_p(ul, X.pr[d][nl], X.pr[3][nl], d, fl);
         flux_p(ur, X.pr[d][nr], X.pr[3][nr], d, fr);
-        const double lam = fmax(X.lam[d][nl], X.lam[d][nr]);
+        const double lam = idp::dmax(X.lam[d][nl], X.lam[d][nr]);
         const double cc = ops.w[r % NP] * ops.w[r / NP] * X.q[d] / 2.0;
         for (int v = 0; v < NV; ++v) S[le].fvf[id][v] = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
         S[le].ibar[id] = 0.5 * (ul[0] + ur[0]) - 0.5 * (fr[0] - fl[0]) * idp::fast_rcp(lam);
@@ -590,9 +563,11 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         }
         const double rf = S[le].ufv[0][n];
         const double Qp = m / dt * (S[le].rmax[n] - rf), Qm = m / dt * (S[le].rmin[n] - rf);
-        double Rp = (Pp > 0.0) ? fmin(Qp / Pp, 1.0) : 1.0, Rm = (Pm < 0.0) ? fmin(Qm / Pm, 1.0) : 1.0;
-        S[le].Rp[n] = Rp > 0.0 ? Rp : 0.0;
-        S[le].Rm[n] = Rm > 0.0 ? Rm : 0.0;
+        // the quotients only where the bound has room (R < 1)
+        double Rp = (idp::dpos(Pp) && idp::dlt(Qp, Pp)) ? Qp * idp::fast_rcp(Pp) : 1.0;
+        double Rm = (idp::dneg(Pm) && idp::dlt(Pm, Qm)) ? Qm * idp::fast_rcp(Pm) : 1.0;
+        S[le].Rp[n] = idp::dpos(Rp) ? Rp : 0.0;
+        S[le].Rm[n] = idp::dpos(Rm) ? Rm : 0.0;
     }
     __syncthreads();
     // ---- P4: interface factors: Zalesak, then the pressure factor of both
@@ -606,7 +581,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             const int nl = node_of<NP>(d, r, a), nr = node_of<NP>(d, r, a + 1);
             const double *Ai = S[le].A[id];
             const double lr = S[le].ex[id] ? 1.0
-                            : (-Ai[0] > 0.0) ? fmin(S[le].Rp[nl], S[le].Rm[nr]) : fmin(S[le].Rm[nl], S[le].Rp[nr]);
+                            : idp::dneg(Ai[0]) ? idp::dmin(S[le].Rp[nl], S[le].Rm[nr]) : idp::dmin(S[le].Rm[nl], S[le].Rp[nr]);
             const double gl = -kGamma3 * dt * S[le].im[nl], gr = kGamma3 * dt * S[le].im[nr];
             double u0[NV], av[NV];
             // each end: certified in FP32 at lr, else the FP64 solve (R8)
@@ -616,7 +591,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             for (int v = 0; v < NV; ++v) { u0[v] = S[le].ufv[v][nr]; av[v] = gr * Ai[v]; }
             const double thr = admissible3_f32(gm1, u0, av, S[le].pmin[nr], S[le].c0[nr], lr)
                              ? lr : theta3(g, u0, av, S[le].pmin[nr], lr);
-            l = fmin(thl, thr);
+            l = idp::dmin(thl, thr);
         }
         S[le].ell[id] = l;
     }
@@ -720,6 +695,20 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     if (A.collect && (vr | vp | np_) != 0u && (tid & 31) == 0) atomicOr(A.status, S_VIOLATION);
 }
 
+// |v_d| + c of a state along the three axes, with one fast reciprocal and
+// square root; false for a non-admissible state
+__device__ __forceinline__ bool wave_speeds3(double g, const double *u, double *lam) {
+    const double ir = idp::fast_rcp(u[0]);
+    const double p = (g - 1.0) * (u[4] - 0.5 * (u[1] * u[1] + u[2] * u[2] + u[3] * u[3]) * ir);
+    if (!idp::dpos(u[0]) || !idp::dpos(p)) {
+        lam[0] = lam[1] = lam[2] = 0.0;
+        return false;
+    }
+    const double c = idp::fast_sqrt(g * p * ir);
+    for (int d = 0; d < 3; ++d) lam[d] = fabs(u[1 + d] * ir) + c;
+    return true;
+}
+
 // IDP time step (Eq. timestep_restriction): per node m_i / sum_j 2 d_ij over
 // its subcell and face neighbours (at a mortar side the slot's sum over its
 // pairs, formed by the mortar flux kernel from the same state); minimum per
@@ -739,10 +728,10 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
     for (int k = tid; k < EPB * NN; k += NT) {
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
-        double uv[NV];
+        double uv[NV], l3[3];
         for (int v = 0; v < NV; ++v) uv[v] = u[v * KN + (size_t)e * NN + n];
-        if (!(uv[0] > 0.0) || !(pres3(gamma, uv) > 0.0)) atomicOr(status, S_BAD_INPUT);
-        for (int d = 0; d < 3; ++d) lam[le][d][n] = wave3(gamma, uv, d);
+        if (!wave_speeds3(gamma, uv, l3)) atomicOr(status, S_BAD_INPUT);
+        for (int d = 0; d < 3; ++d) lam[le][d][n] = l3[d];
     }
     __syncthreads();
     unsigned long long best = (unsigned long long)__double_as_longlong(INFINITY);
@@ -781,13 +770,15 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
                         for (int v = 0; v < NV; ++v) in[v] = u[v * KN + (size_t)e * NN + n];
                         ghost3(G, s, in, o);
                     }
-                    lo = wave3(gamma, o, d);
+                    double l3[3];
+                    wave_speeds3(gamma, o, l3);
+                    lo = l3[d];
                 }
-                s2d += 2.0 * cd * fmax(li, lo);
+                s2d += 2.0 * cd * idp::dmax(li, lo);
             }
         }
         const double m = w[idx[0]] * w[idx[1]] * w[idx[2]] * J;
-        const double val = m / s2d;
+        const double val = m * idp::fast_rcp(s2d);
         const unsigned long long vb = (unsigned long long)__double_as_longlong(val);
         if (val > 0.0 && vb < best) best = vb;
     }

@@ -18,6 +18,7 @@
 namespace idp {
 void host_lgl_sbar(int N, double *x, double *w, double *S);
 void host_lgl_mortar(int N, double *I, double *P, double *wt);
+void host_log_table(LogTab &T);
 }
 
 using namespace idp3;
@@ -31,6 +32,7 @@ struct idp3d_ctx {
     int grid_el = 1;               // element-kernel blocks
     Ops3 *d_ops = nullptr;
     MOps3 *d_mops = nullptr;
+    idp::LogTab *d_lg = nullptr;
     int *d_nbr = nullptr, *d_minfo = nullptr, *d_slot_mn = nullptr, *d_mn_node = nullptr, *d_mn_slot = nullptr;
     int *d_mn_cnt = nullptr, *d_mbad = nullptr;
     signed char *d_lev = nullptr;
@@ -373,6 +375,12 @@ idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, co
     const size_t kn = nodes_of(c);
     chk(c->L.prepare());
     upload(&c->d_ops, &ops, 1);
+    {
+        idp::LogTab lt;
+        idp::host_log_table(lt);
+        upload(&c->d_lg, &lt, 1);
+    }
+    G.lg = c->d_lg;
     upload(&c->d_nbr, T.nbr.data(), T.nbr.size());
     upload(&c->d_lev, T.lev.data(), T.lev.size());
     G.nbr = c->d_nbr;
@@ -584,7 +592,7 @@ void idp3d_destroy(idp3d_ctx *c) {
     void *ptrs[] = {c->d_ops, c->d_buf1, c->d_buf2, c->d_part, c->d_tot, c->d_dtmin, c->d_dtmin2, c->d_t,
                     c->d_dtlast, c->d_status, c->d_stats, c->d_mops, c->d_nbr, c->d_lev, c->d_minfo,
                     c->d_slot_mn, c->d_mn_node, c->d_mn_slot, c->d_mn_cnt, c->d_mbad, c->d_mslot, c->d_hand,
-                    c->d_ell};
+                    c->d_ell, c->d_lg};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_in) cudaEventDestroy(c->ev_in);
