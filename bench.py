@@ -396,9 +396,10 @@ def time_steps(ctx, u_dev, steps, warmup, flush, stream, sync_fn):
     return step_ms * 1e-3, el_ms, el_n, kern
 
 
-def bench_3d(idp, flush, stream, args, n=40, N=3, octree=False):
+def bench_3d(idp, flush, stream, args, n=40, N=3, octree=False, precision=0):
     """The 3D blast on an n^3 grid, or (octree) on an n^3 base grid with the
-    leaves in [1/4, 3/4]^3 refined once: 2:1 mortars around the block."""
+    leaves in [1/4, 3/4]^3 refined once: 2:1 mortars around the block;
+    precision 1: the FP32 form."""
     import torch
     from paper_2607_06045_b300 import workloads as W
     if octree:
@@ -407,7 +408,7 @@ def bench_3d(idp, flush, stream, args, n=40, N=3, octree=False):
     else:
         g = W.Grid3(n, n, n, bc=(3,) * 6)
     u = W.blast3_state(g, N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0)
-    ctx = idp.Context3D(g, N, limiting=2, cfl=0.5)
+    ctx = idp.Context3D(g, N, limiting=2, cfl=0.5, precision=precision)
     ud = torch.from_numpy(u).cuda()
     del u
     t = np.zeros(1)
@@ -433,7 +434,8 @@ def bench_3d(idp, flush, stream, args, n=40, N=3, octree=False):
     out = dict(value=dofs * 3 / (ms * 1e-3), unit=UNIT, ms_per_step=ms, ms_per_step_median=float(np.median(times)),
                steps=steps, elements=g.n_elems, dofs=dofs, gpu_launches=launches * steps,
                workload=f"3D blast: [0,1]^3, {mesh_text}, N={N}, sphere r < 0.15 at p = 10 in a gas at "
-                        "rho = 1, p = 0.1, outflow, local limiting (d = 3, Gamma = 6), FP64",
+                        "rho = 1, p = 0.1, outflow, local limiting (d = 3, Gamma = 6), "
+                        + ("FP32 form" if precision else "FP64"),
                stats={k: st[k] for k in ("alpha_mean", "n_viol_density", "n_viol_pressure", "n_nonpositive",
                                          "alpha_mortar", "n_mortar_active", "n_mortar_fallback")})
     if octree:
@@ -674,6 +676,9 @@ def run_ours(args):
     # the same blast on a 2:1 octree: 32^3 base, [1/4, 3/4]^3 refined once
     # (61,440 leaves, 1,536 mortars, 3.9M DOFs)
     variants["blast3d_octree"] = bench_3d(idp, flush, stream, args, n=32, octree=True)
+    # the FP32 form of the 3D path on both meshes
+    variants["blast3d_fp32"] = bench_3d(idp, flush, stream, args, precision=1)
+    variants["blast3d_octree_fp32"] = bench_3d(idp, flush, stream, args, n=32, octree=True, precision=1)
     variants["dt_rules"] = {"idp": dts[0], "low_order_cfl": dts[1], "ratio": dts[1] / dts[0],
                             "note": "cfl = 1 on the initial state; steps to a fixed time scale with 1 / dt"}
     # near-vacuum blast (512 x 512 base + 2 levels, N = 5), FP32 form
@@ -743,6 +748,24 @@ def run_ours(args):
                                flops_per_stage=fo,
                                flops_source="oracle op-counting build, 3D octree (method_work.json: 3d_octree): "
                                             "per node and per mortar; the whole step")
+    # 3D FP32 form: its FP32 rows over the FP32 peak plus the rest over the
+    # FP64 peak give the roofline time of a step
+    f32rows = ("node_prep", "volume_flux", "subcell_fv", "face_flux")
+    for key, base in (("blast3d_fp32", t3), ("blast3d_octree_fp32", None)):
+        bf = variants[key]
+        rows3 = t3["rows"]
+        f32 = sum(rows3[r]["flops"] for r in f32rows)
+        if base is None:
+            f64 = (to["node_flops_per_node_stage"] - f32) * bf["dofs"] + to["mortar_flops_per_mortar_stage"] * bf["mortars"]
+        else:
+            f64 = (f3 - f32) * bf["dofs"]
+        t_roof = 3 * (f64 / (peak * 1e12) + f32 * bf["dofs"] / (peak32 * 1e12))
+        bf["step_roofline"] = dict(bound="alu", roofline_ms=t_roof * 1e3, frac=t_roof / (bf["ms_per_step"] * 1e-3),
+                                   flops_fp64_per_stage=f64, flops_fp32_per_stage=f32 * bf["dofs"],
+                                   peak_fp64=peak, peak_fp32=peak32, unit="TFLOP/s",
+                                   flops_source="3D counting build; rows node_prep, volume_flux, subcell_fv and "
+                                                "face_flux in FP32, the rest in FP64")
+        bf["speedup_vs_fp64"] = variants[key.replace("_fp32", "")]["ms_per_step"] / bf["ms_per_step"]
     bval = bnodes_all * 3 * bsteps / btot   # the whole batch over the slowest rank
     hbm = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"] \
         if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6400.0

@@ -53,14 +53,19 @@ typedef struct {
 
 /* limiting: 0 none (the high-order scheme), 1 positivity, 2 local (density
  * bounds from the bar states, with positivity); beta the positivity factor
- * of Eq. Bounds_Positivity (0.1); cfl the factor on the IDP time step. */
+ * of Eq. Bounds_Positivity (0.1); cfl the factor on the IDP time step;
+ * precision 0 FP64 throughout, 1 the FP32 form: node primitives and the
+ * two-point, face and subcell fluxes of the element pass in FP32, the bar
+ * states, bounds, limiter, sums, stage update, mortars and time step in
+ * FP64. */
 typedef struct {
     int32_t limiting;
     double beta;
     double cfl;
+    int32_t precision;
 } idp3d_options;
 
-/* limiting 2, beta 0.1, cfl 0.5 */
+/* limiting 2, beta 0.1, cfl 0.5, precision 0 */
 idp_status idp3d_options_default(idp3d_options *o);
 
 /* Context for one grid and degree N (1..4); *out receives it. IDP_E_ARG for

@@ -223,9 +223,28 @@ __device__ __forceinline__ int node_of(int d, int r, int a) {
     return (idx[2] * NP + idx[1]) * NP + idx[0];
 }
 
-// shared memory of one element; arrays whose lifetimes do not overlap share
-// storage (phases P0..P5 of k_element3d)
+// per-node flux data of the element kernel: in the FP64 path v1, v2, v3, p,
+// ln rho, ln beta, beta = rho / p and |v_d| + c; in the FP32 form the state
+// rounded to FP32, v1, v2, v3, p, beta and |v_d| + c in FP32
+template <int NP, bool F32>
+struct Node3 {
+    static constexpr int NN = NP * NP * NP;
+    double pr[7][NN];
+    double lam[3][NN];
+};
 template <int NP>
+struct Node3<NP, true> {
+    static constexpr int NN = NP * NP * NP;
+    float uf[NV][NN];
+    float pr[5][NN];
+    float lam[3][NN];
+};
+
+// shared memory of one element; arrays whose lifetimes do not overlap share
+// storage (phases P0..P5 of k_element3d). FT: the flux type (float in the
+// FP32 form): the per-node flux data, pair fluxes, outside primitives and
+// low-order subcell fluxes; everything else is FP64.
+template <int NP, typename FT = double>
 struct Sm3 {
     using E = El3<NP>;
     static constexpr int NN = E::NN, NR = E::NR, NIF = E::NIF, NPAIR = E::NPAIR;
@@ -233,9 +252,8 @@ struct Sm3 {
         double u[NV][NN];      // P0 - P2: the stage input
         double rfv[NV][NN];    // P2 - P5: low-order residual (each node overwrites only its own u)
     };
-    double pr[7][NN];          // P0 - P1: v1, v2, v3, p, ln rho, ln (rho / p), rho / p
-    double lam[3][NN];         // P0 - P1: |v_d| + c
-    double outp[6][NR][3];     // P0 - P1: outside states' normal velocity, pressure, wave speed
+    Node3<NP, sizeof(FT) == 4> nd;   // P0 - P1
+    FT outp[6][NR][3];         // P0 - P1: outside states' normal velocity, pressure, wave speed
     union {
         double outs[6][NR][NV];   // P0 - P1: outside states of the six faces
         struct {                  // P2b - P5
@@ -244,7 +262,7 @@ struct Sm3 {
             unsigned char ex[NIF];       // R15 exemption (P2b - P4)
         };
     };
-    double pair[3][NR][NPAIR][NV];   // P1 - P2b: two-point fluxes of every row
+    FT pair[3][NR][NPAIR][NV];       // P1 - P2b: two-point fluxes of every row
     union {
         struct {                     // P1 - P2
             double ff[6][NR][NV];    // face fluxes, mass-weighted, along +d
@@ -254,7 +272,7 @@ struct Sm3 {
         };
         double A[NIF][NV];           // P2b - P5: antidiffusive fluxes (mass-weighted)
     };
-    double fvf[NIF][NV];       // P1 - P2b: low-order subcell fluxes, mass-weighted, along +d
+    FT fvf[NIF][NV];           // P1 - P2b: low-order subcell fluxes, mass-weighted, along +d
     double ufv[NV][NN];        // P2 - P5
     double rmin[NN], rmax[NN], pmin[NN];
     double c0[NN];             // P2 - P4: g(0) = (gamma-1)(rho E - |m|^2/2) - p_min rho at u_FV
@@ -262,6 +280,59 @@ struct Sm3 {
     double q[3], J, iJ;        // quarter face areas, dx dy dz / 8 and its inverse
     int nb[6];                 // the sides' neighbour entries (Grid3::nbr)
 };
+
+// a flux-type value in FP64 (FP32 converted on the integer pipe)
+__device__ __forceinline__ double to_d3(double x) { return x; }
+__device__ __forceinline__ double to_d3(float x) { return idp::f2d(x); }
+
+// FP32 primitives of a state (the FP32 form): the state rounded to FP32 (on
+// the integer pipe), v, p and 1 / rho. When E - |m|^2/2rho keeps at least an
+// eighth of E the pressure is formed in FP32 (within 2e-6 of the rounded
+// state's and positive for sure, as in 2D); otherwise v, p and 1/rho are
+// formed in FP64 and rounded. False for a non-admissible state.
+__device__ __forceinline__ bool prim3_f32(double gm1, const double *u, float *uf, float *v, float &p, float &ir) {
+    for (int k = 0; k < NV; ++k) uf[k] = idp::d2f(u[k]);
+    ir = __frcp_rn(uf[0]);
+    for (int c = 0; c < 3; ++c) v[c] = __fmul_rn(uf[1 + c], ir);
+    const float ke = 0.5f * (uf[1] * v[0] + uf[2] * v[1] + uf[3] * v[2]);
+    const float pe = uf[4] - ke;
+    if (uf[0] > 0.0f && uf[4] > 0.0f && pe >= 0.125f * uf[4]) {
+        p = idp::d2f(gm1) * pe;
+        return true;
+    }
+    const double ird = idp::fast_rcp(u[0]);
+    double vd[3];
+    for (int c = 0; c < 3; ++c) vd[c] = u[1 + c] * ird;
+    const double pd = gm1 * (u[4] - 0.5 * (u[1] * vd[0] + u[2] * vd[1] + u[3] * vd[2]));
+    for (int c = 0; c < 3; ++c) v[c] = idp::d2f(vd[c]);
+    p = idp::d2f(pd);
+    ir = idp::d2f(ird);
+    return idp::dpos(u[0]) && idp::dpos(pd) && p > 0.0f;
+}
+
+// both logarithmic means of a pair in FP32 (the FP32 form): logarithms of
+// the ratios, the Ismail-Roe series where ((a - b)/(a + b))^2 < 1e-2 (its
+// truncation is below FP32 rounding there), one reciprocal for both
+__device__ __forceinline__ void log_means3_f32(float ra, float rb, float ba, float bb, float &rho_ln, float &ibeta) {
+    const float dr = ra - rb, sr = ra + rb, db = ba - bb, sb = ba + bb;
+    const bool nr = dr * dr < 1e-2f * (sr * sr), nb = db * db < 1e-2f * (sb * sb);
+    const float lr = nr ? 0.0f : logf(__fdiv_rn(ra, rb)), lb = nb ? 0.0f : logf(__fdiv_rn(ba, bb));
+    const float Xr = nr ? sr : lr, Xb = nb ? sb : db;
+    const float R = __frcp_rn(Xr * Xb);
+    const float ixr = Xb * R, ixb = Xr * R;
+    if (nr) {
+        const float f = dr * ixr, uu = f * f;
+        rho_ln = 0.5f * sr * (1.0f - uu * (1.0f / 3.0f + uu * (4.0f / 45.0f + uu * (44.0f / 945.0f))));
+    } else {
+        rho_ln = dr * ixr;
+    }
+    if (nb) {
+        const float f = db * ixb, uu = f * f;
+        ibeta = 2.0f * ixb * (1.0f + uu * (1.0f / 3.0f + uu * (1.0f / 5.0f + uu * (1.0f / 7.0f))));
+    } else {
+        ibeta = lb * ixb;
+    }
+}
 
 // threads of a block of EPB elements: one per node, rounded up to whole warps
 template <int NP, int EPB>
@@ -299,23 +370,27 @@ __device__ __forceinline__ void log_means3(double ra, double rb, double lra, dou
 }
 
 // physical flux along d from the state and its velocity along d and pressure
-__device__ __forceinline__ void flux_p(const double *u, double vd, double p, int d, double *f) {
+template <typename T>
+__device__ __forceinline__ void flux_p(const T *u, T vd, T p, int d, T *f) {
     f[0] = u[1 + d];
-    f[1] = u[1] * vd + (d == 0 ? p : 0.0);
-    f[2] = u[2] * vd + (d == 1 ? p : 0.0);
-    f[3] = u[3] * vd + (d == 2 ? p : 0.0);
+    f[1] = u[1] * vd + (d == 0 ? p : T(0));
+    f[2] = u[2] * vd + (d == 1 ? p : T(0));
+    f[3] = u[3] * vd + (d == 2 ? p : T(0));
     f[4] = (u[4] + p) * vd;
 }
 
 // One block of EPB elements, one thread per node; items of each phase are
 // spread over the block. Per node, its primitives, logarithms and wave
 // speeds are formed once (P0); the pair, face and subcell fluxes take them
-// from shared memory.
-template <int NP, int EPB>
+// from shared memory. FT = float: the FP32 form (R18): node primitives, the
+// two-point, face and subcell fluxes in FP32; bar states, bounds, sums,
+// limiting and the stage update in FP64.
+template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(Launch3<NP, EPB>::threads)
 k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     using E = El3<NP>;
-    using SM = Sm3<NP>;
+    using SM = Sm3<NP, FT>;
+    constexpr bool F32 = sizeof(FT) == 4;
     constexpr int N = E::N, NN = E::NN, NR = E::NR, NPAIR = E::NPAIR, NIF = E::NIF, NT = Launch3<NP, EPB>::threads;
     extern __shared__ __align__(16) unsigned char sm3_raw[];
     SM *S = reinterpret_cast<SM *>(sm3_raw);
@@ -324,7 +399,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     for (int k = tid; k < (int)(sizeof(Ops3) / sizeof(double)); k += NT)
         reinterpret_cast<double *>(&ops)[k] = reinterpret_cast<const double *>(ops_g)[k];
     const size_t KN = (size_t)G.K * NN;
-    const double g = A.gamma, gm1 = g - 1.0;
+    const double g = A.gamma, gm1 = g - 1.0, igm1 = 1.0 / gm1;
     const double dt = stage_dt3(A);
     const int e0 = blockIdx.x * EPB;
     const Mort3 &MO = G.mort;
@@ -341,22 +416,40 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         }
         double uv[NV];
         for (int v = 0; v < NV; ++v) { uv[v] = A.u[v * KN + (size_t)e * NN + n]; S[le].u[v][n] = uv[v]; }
-        const double ir = idp::fast_rcp(uv[0]);
-        const double v1 = uv[1] * ir, v2 = uv[2] * ir, v3 = uv[3] * ir;
-        const double p = gm1 * (uv[4] - 0.5 * (uv[1] * v1 + uv[2] * v2 + uv[3] * v3));
-        S[le].pr[0][n] = v1; S[le].pr[1][n] = v2; S[le].pr[2][n] = v3; S[le].pr[3][n] = p;
-        if (!(uv[0] > 0.0) || !(p > 0.0)) {
-            atomicOr(A.status, S_BAD_INPUT);
-            S[le].pr[4][n] = 0.0; S[le].pr[5][n] = 0.0; S[le].pr[6][n] = 1.0;
-            for (int d = 0; d < 3; ++d) S[le].lam[d][n] = 0.0;
-            continue;
+        auto &nd = S[le].nd;
+        if constexpr (F32) {
+            float uf[NV], vf[3], pf, irf;
+            const bool ok = prim3_f32(gm1, uv, uf, vf, pf, irf);
+            for (int v = 0; v < NV; ++v) nd.uf[v][n] = uf[v];
+            for (int c = 0; c < 3; ++c) nd.pr[c][n] = vf[c];
+            nd.pr[3][n] = pf;
+            if (!ok) {
+                atomicOr(A.status, S_BAD_INPUT);
+                nd.pr[4][n] = 1.0f;
+                for (int d = 0; d < 3; ++d) nd.lam[d][n] = 0.0f;
+                continue;
+            }
+            const float c = sqrtf(idp::d2f(g) * pf * irf);
+            nd.pr[4][n] = uf[0] * __frcp_rn(pf);
+            for (int d = 0; d < 3; ++d) nd.lam[d][n] = fabsf(vf[d]) + c;
+        } else {
+            const double ir = idp::fast_rcp(uv[0]);
+            const double v1 = uv[1] * ir, v2 = uv[2] * ir, v3 = uv[3] * ir;
+            const double p = gm1 * (uv[4] - 0.5 * (uv[1] * v1 + uv[2] * v2 + uv[3] * v3));
+            nd.pr[0][n] = v1; nd.pr[1][n] = v2; nd.pr[2][n] = v3; nd.pr[3][n] = p;
+            if (!(uv[0] > 0.0) || !(p > 0.0)) {
+                atomicOr(A.status, S_BAD_INPUT);
+                nd.pr[4][n] = 0.0; nd.pr[5][n] = 0.0; nd.pr[6][n] = 1.0;
+                for (int d = 0; d < 3; ++d) nd.lam[d][n] = 0.0;
+                continue;
+            }
+            const double c = idp::fast_sqrt(g * p * ir);
+            const double bet = uv[0] * idp::fast_rcp(p);
+            nd.pr[4][n] = idp::fast_log(uv[0], G.lg);
+            nd.pr[5][n] = idp::fast_log(bet, G.lg);
+            nd.pr[6][n] = bet;
+            nd.lam[0][n] = fabs(v1) + c; nd.lam[1][n] = fabs(v2) + c; nd.lam[2][n] = fabs(v3) + c;
         }
-        const double c = idp::fast_sqrt(g * p * ir);
-        const double bet = uv[0] * idp::fast_rcp(p);
-        S[le].pr[4][n] = idp::fast_log(uv[0], G.lg);
-        S[le].pr[5][n] = idp::fast_log(bet, G.lg);
-        S[le].pr[6][n] = bet;
-        S[le].lam[0][n] = fabs(v1) + c; S[le].lam[1][n] = fabs(v2) + c; S[le].lam[2][n] = fabs(v3) + c;
     }
     for (int k = tid; k < EPB * 6 * NR; k += NT) {
         const int le = k / (6 * NR), r0 = k - le * 6 * NR, s = r0 / NR, t = r0 - s * NR, e = e0 + le;
@@ -377,12 +470,20 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         }
         for (int v = 0; v < NV; ++v) S[le].outs[s][t][v] = o[v];
         // the outside state's normal velocity, pressure and wave speed
-        const double ir = idp::fast_rcp(o[0]);
-        const double vd = o[1 + d] * ir;
-        const double po = gm1 * (o[4] - 0.5 * (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) * ir);
-        S[le].outp[s][t][0] = vd;
-        S[le].outp[s][t][1] = po;
-        S[le].outp[s][t][2] = (o[0] > 0.0 && po > 0.0) ? fabs(vd) + idp::fast_sqrt(g * po * ir) : 0.0;
+        if constexpr (F32) {
+            float of[NV], vf[3], pf, irf;
+            const bool ok = prim3_f32(gm1, o, of, vf, pf, irf);
+            S[le].outp[s][t][0] = vf[d];
+            S[le].outp[s][t][1] = pf;
+            S[le].outp[s][t][2] = ok ? fabsf(vf[d]) + sqrtf(idp::d2f(g) * pf * irf) : 0.0f;
+        } else {
+            const double ir = idp::fast_rcp(o[0]);
+            const double vd = o[1 + d] * ir;
+            const double po = gm1 * (o[4] - 0.5 * (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) * ir);
+            S[le].outp[s][t][0] = vd;
+            S[le].outp[s][t][1] = po;
+            S[le].outp[s][t][2] = (o[0] > 0.0 && po > 0.0) ? fabs(vd) + idp::fast_sqrt(g * po * ir) : 0.0;
+        }
     }
     __syncthreads();
     // ---- P1a: two-point fluxes of every row, each unordered pair once
@@ -396,19 +497,26 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int b = a + 1 + rem;
         const int na = node_of<NP>(d, r, a), nb = node_of<NP>(d, r, b);
         const SM &X = S[le];
-        double rho_ln, iba;
-        log_means3(X.u[0][na], X.u[0][nb], X.pr[4][na], X.pr[4][nb], X.pr[6][na], X.pr[6][nb], X.pr[5][na],
-                   X.pr[5][nb], rho_ln, iba);
-        const double pa = X.pr[3][na], pb = X.pr[3][nb];
-        double va[3], vb[3];
-        for (int cc = 0; cc < 3; ++cc) { va[cc] = X.pr[cc][na]; vb[cc] = X.pr[cc][nb]; }
+        FT rho_ln, iba, igm;
+        if constexpr (F32) {
+            log_means3_f32(X.nd.uf[0][na], X.nd.uf[0][nb], X.nd.pr[4][na], X.nd.pr[4][nb], rho_ln, iba);
+            igm = idp::d2f(igm1);
+        } else {
+            log_means3(X.u[0][na], X.u[0][nb], X.nd.pr[4][na], X.nd.pr[4][nb], X.nd.pr[6][na], X.nd.pr[6][nb],
+                       X.nd.pr[5][na], X.nd.pr[5][nb], rho_ln, iba);
+            igm = igm1;
+        }
+        const FT pa = X.nd.pr[3][na], pb = X.nd.pr[3][nb];
+        FT va[3], vb[3];
+        for (int cc = 0; cc < 3; ++cc) { va[cc] = X.nd.pr[cc][na]; vb[cc] = X.nd.pr[cc][nb]; }
         // R1 (Ranocha) along d
-        const double vdot = va[0] * vb[0] + va[1] * vb[1] + va[2] * vb[2];
-        const double fr = rho_ln * 0.5 * (va[d] + vb[d]);
-        double f[NV];
+        const FT h = FT(0.5);
+        const FT vdot = va[0] * vb[0] + va[1] * vb[1] + va[2] * vb[2];
+        const FT fr = rho_ln * h * (va[d] + vb[d]);
+        FT f[NV];
         f[0] = fr;
-        for (int cc = 0; cc < 3; ++cc) f[1 + cc] = fr * 0.5 * (va[cc] + vb[cc]) + (cc == d ? 0.5 * (pa + pb) : 0.0);
-        f[4] = fr * (0.5 * vdot + iba * (1.0 / gm1)) + 0.5 * (pa * vb[d] + pb * va[d]);
+        for (int cc = 0; cc < 3; ++cc) f[1 + cc] = fr * h * (va[cc] + vb[cc]) + (cc == d ? h * (pa + pb) : FT(0));
+        f[4] = fr * (h * vdot + iba * igm) + h * (pa * vb[d] + pb * va[d]);
         for (int v = 0; v < NV; ++v) S[le].pair[d][r][pp][v] = f[v];
     }
     // ---- P1b: LLF faces (mass-weighted, along +d) and their bar-state densities
@@ -432,18 +540,26 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int nin = node_of<NP>(d, t, side ? N : 0);
         const SM &X = S[le];
         const double *q = X.q;
-        double ui[NV], uo[NV], fi[NV], fo[NV];
-        for (int v = 0; v < NV; ++v) { ui[v] = X.u[v][nin]; uo[v] = X.outs[s][t][v]; }
-        flux_p(ui, X.pr[d][nin], X.pr[3][nin], d, fi);
-        flux_p(uo, X.outp[s][t][0], X.outp[s][t][1], d, fo);
-        const double lam = idp::dmax(X.lam[d][nin], X.outp[s][t][2]);
         const double wt = ops.w[t % NP] * ops.w[t / NP], cw = wt * q[d];
+        FT ui[NV], uo[NV], fi[NV], fo[NV];
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (F32) { ui[v] = X.nd.uf[v][nin]; uo[v] = idp::d2f(X.outs[s][t][v]); }
+            else { ui[v] = X.u[v][nin]; uo[v] = X.outs[s][t][v]; }
+        }
+        flux_p<FT>(ui, X.nd.pr[d][nin], X.nd.pr[3][nin], d, fi);
+        flux_p<FT>(uo, X.outp[s][t][0], X.outp[s][t][1], d, fo);
+        FT lam;
+        if constexpr (F32) lam = fmaxf(X.nd.lam[d][nin], X.outp[s][t][2]);
+        else lam = idp::dmax(X.nd.lam[d][nin], X.outp[s][t][2]);
+        const FT cwf = (FT)(F32 ? (double)idp::d2f(cw) : cw);
         // left state first: the outside is on the left of a low face
-        const double *uL = side ? ui : uo, *uR = side ? uo : ui, *fL = side ? fi : fo, *fR = side ? fo : fi;
-        for (int v = 0; v < NV; ++v) S[le].ff[s][t][v] = cw * (0.5 * (fL[v] + fR[v]) - 0.5 * lam * (uR[v] - uL[v]));
-        // ubar = (u_i + u_o)/2 - c.(f_o - f_i)/(2 |c| lambda), c along the outward normal
+        const FT *uL = side ? ui : uo, *uR = side ? uo : ui, *fL = side ? fi : fo, *fR = side ? fo : fi;
+        for (int v = 0; v < NV; ++v)
+            S[le].ff[s][t][v] = to_d3(cwf * (FT(0.5) * (fL[v] + fR[v]) - FT(0.5) * lam * (uR[v] - uL[v])));
+        // ubar = (u_i + u_o)/2 - c.(f_o - f_i)/(2 |c| lambda), c along the outward normal (FP64)
         const double sg = side ? 0.5 : -0.5;
-        const double fb = 0.5 * (ui[0] + uo[0]) - sg * (fo[0] - fi[0]) * idp::fast_rcp(lam);
+        const double fb = 0.5 * (X.u[0][nin] + X.outs[s][t][0]) -
+                          sg * (X.outs[s][t][1 + d] - X.u[1 + d][nin]) * idp::fast_rcp(to_d3(lam));
         S[le].fbl[s][t] = fb;
         S[le].fbh[s][t] = fb;
     }
@@ -454,14 +570,20 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int d = id / (NR * N), r1 = id - d * NR * N, r = r1 / N, a = r1 - r * N;
         const int nl = node_of<NP>(d, r, a), nr = node_of<NP>(d, r, a + 1);
         const SM &X = S[le];
-        double ul[NV], ur[NV], fl[NV], fr[NV];
-        for (int v = 0; v < NV; ++v) { ul[v] = X.u[v][nl]; ur[v] = X.u[v][nr]; }
-        flux_p(ul, X.pr[d][nl], X.pr[3][nl], d, fl);
-        flux_p(ur, X.pr[d][nr], X.pr[3][nr], d, fr);
-        const double lam = idp::dmax(X.lam[d][nl], X.lam[d][nr]);
-        const double cc = ops.w[r % NP] * ops.w[r / NP] * X.q[d] / 2.0;
+        FT ul[NV], ur[NV], fl[NV], fr[NV];
+        for (int v = 0; v < NV; ++v) {
+            if constexpr (F32) { ul[v] = X.nd.uf[v][nl]; ur[v] = X.nd.uf[v][nr]; }
+            else { ul[v] = X.u[v][nl]; ur[v] = X.u[v][nr]; }
+        }
+        flux_p<FT>(ul, X.nd.pr[d][nl], X.nd.pr[3][nl], d, fl);
+        flux_p<FT>(ur, X.nd.pr[d][nr], X.nd.pr[3][nr], d, fr);
+        FT lam;
+        if constexpr (F32) lam = fmaxf(X.nd.lam[d][nl], X.nd.lam[d][nr]);
+        else lam = idp::dmax(X.nd.lam[d][nl], X.nd.lam[d][nr]);
+        const double ccd = ops.w[r % NP] * ops.w[r / NP] * X.q[d] / 2.0;
+        const FT cc = (FT)(F32 ? (double)idp::d2f(ccd) : ccd);
         for (int v = 0; v < NV; ++v) S[le].fvf[id][v] = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
-        S[le].ibar[id] = 0.5 * (ul[0] + ur[0]) - 0.5 * (fr[0] - fl[0]) * idp::fast_rcp(lam);
+        S[le].ibar[id] = 0.5 * (X.u[0][nl] + X.u[0][nr]) - 0.5 * (X.u[1 + d][nr] - X.u[1 + d][nl]) * idp::fast_rcp(to_d3(lam));
     }
     __syncthreads();
     // ---- P2: low-order residual, low-order update and bounds per node
@@ -479,7 +601,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             double b0l, b0h, b1l, b1h;
             if (pos > 0) {
                 const int id = (d * NR + row) * N + pos - 1;
-                for (int v = 0; v < NV; ++v) r[v] += S[le].fvf[id][v];
+                for (int v = 0; v < NV; ++v) r[v] += to_d3(S[le].fvf[id][v]);
                 b0l = b0h = S[le].ibar[id];
             } else {
                 for (int v = 0; v < NV; ++v) r[v] += S[le].ff[2 * d][row][v];
@@ -488,7 +610,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             }
             if (pos < N) {
                 const int id = (d * NR + row) * N + pos;
-                for (int v = 0; v < NV; ++v) r[v] -= S[le].fvf[id][v];
+                for (int v = 0; v < NV; ++v) r[v] -= to_d3(S[le].fvf[id][v]);
                 b1l = b1h = S[le].ibar[id];
             } else {
                 for (int v = 0; v < NV; ++v) r[v] -= S[le].ff[2 * d + 1][row][v];
@@ -516,9 +638,9 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         S[le].im[n] = im;
     }
     __syncthreads();
-    // ---- P2b: telescoped high-order subcell fluxes per row, then A = F_DG - F_FV
-    // (A takes the storage of the face data, the exemption flags that of the
-    // outside states: both dead after P2)
+    // ---- P2b: telescoped high-order subcell fluxes per row (summed in FP64),
+    // then A = F_DG - F_FV (A takes the storage of the face data, the
+    // exemption flags that of the outside states: both dead after P2)
     for (int k = tid; k < EPB * 3 * NR; k += NT) {
         const int le = k / (3 * NR), r0 = k - le * 3 * NR, d = r0 / NR, r = r0 - d * NR;
         if (e0 + le >= G.K) continue;
@@ -530,12 +652,12 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
                 const int lo_ = l < mm ? l : mm, hi_ = l < mm ? mm : l;
                 const int pp = lo_ * (2 * NP - lo_ - 1) / 2 + (hi_ - lo_ - 1);
                 const double sq = ops.S[l][mm] * S[le].q[d];
-                for (int v = 0; v < NV; ++v) acc[v] += sq * S[le].pair[d][r][pp][v];
+                for (int v = 0; v < NV; ++v) acc[v] += sq * to_d3(S[le].pair[d][r][pp][v]);
             }
             const int id = (d * NR + r) * N + l;
             const int nl = node_of<NP>(d, r, l), nr = node_of<NP>(d, r, l + 1);
             const double iml = S[le].im[nl], imr = S[le].im[nr];
-            for (int v = 0; v < NV; ++v) S[le].A[id][v] = wt * acc[v] - S[le].fvf[id][v];
+            for (int v = 0; v < NV; ++v) S[le].A[id][v] = wt * acc[v] - to_d3(S[le].fvf[id][v]);
             const double Ar = fabs(S[le].A[id][0]);
             S[le].ex[id] = (dt * iml * Ar <= kTol3 * fabs(S[le].ufv[0][nl])) && (dt * imr * Ar <= kTol3 * fabs(S[le].ufv[0][nr]));
         }

@@ -94,7 +94,8 @@ bool has_mortars(const idp3d_ctx *c) { return c->grid.mort.M > 0; }
 // the element kernel, then the mortar factors and the mortar nodes
 void enqueue_stage(idp3d_ctx *c, cudaStream_t st, const Stage3 &A, bool mflux) {
     if (has_mortars(c) && mflux) c->L.mflux(st, c->grid, c->d_mops, A.u, c->gamma);
-    c->L.element(c->grid_el, st, c->grid, c->d_ops, A);
+    if (c->opt.precision == 1) c->L.element32(c->grid_el, st, c->grid, c->d_ops, A);
+    else c->L.element(c->grid_el, st, c->grid, c->d_ops, A);
     if (has_mortars(c)) {
         c->L.mfactor(st, c->grid, A);
         c->L.mapply(st, c->grid, A);
@@ -339,6 +340,7 @@ idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, co
     idp3d_options_default(&o);
     if (opts) o = *opts;
     if (o.limiting < 0 || o.limiting > 2 || !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0)) return IDP_E_ARG;
+    if (o.precision < 0 || o.precision > 1) return IDP_E_ARG;
     Octree3 T;
     idp_status rs = build_octree3(gd, K, level, ix, iy, iz, N + 1, T);
     if (rs != IDP_OK) return rs;
@@ -439,6 +441,7 @@ idp_status idp3d_options_default(idp3d_options *o) {
     o->limiting = 2;
     o->beta = 0.1;
     o->cfl = 0.5;
+    o->precision = 0;
     return IDP_OK;
 }
 

@@ -12,9 +12,11 @@ namespace idp3 {
 
 struct Launchers3 {
     int np = 0, epb = 0, threads = 0;
-    size_t smem = 0;   // dynamic shared memory of one element-kernel block
+    size_t smem = 0, smem32 = 0;   // dynamic shared memory of one element-kernel block (FP64 path, FP32 form)
     cudaError_t (*prepare)() = nullptr;
+    // the element kernel: FP64 path, FP32 form
     void (*element)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) = nullptr;
+    void (*element32)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) = nullptr;
     void (*dt)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
                unsigned long long *dtmin, unsigned *status) = nullptr;
     // the mortar kernels (grid: one block per mortar; apply: its own grid)

@@ -18,12 +18,19 @@ constexpr int EPB = NP == 2 ? 16 : (NP == 3 ? 4 : (NP == 4 ? 2 : 1));
 using L3 = Launch3<NP, EPB>;
 
 cudaError_t prepare() {
-    return cudaFuncSetAttribute(k_element3d<NP, EPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)(sizeof(Sm3<NP>) * EPB));
+    cudaError_t e = cudaFuncSetAttribute(k_element3d<NP, EPB, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(Sm3<NP, double>) * EPB));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_element3d<NP, EPB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(Sm3<NP, float>) * EPB));
 }
 
 void element(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) {
-    k_element3d<NP, EPB><<<grid, L3::threads, sizeof(Sm3<NP>) * EPB, st>>>(G, ops, A);
+    k_element3d<NP, EPB, double><<<grid, L3::threads, sizeof(Sm3<NP, double>) * EPB, st>>>(G, ops, A);
+}
+
+void element32(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) {
+    k_element3d<NP, EPB, float><<<grid, L3::threads, sizeof(Sm3<NP, float>) * EPB, st>>>(G, ops, A);
 }
 
 void dt(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
@@ -51,9 +58,11 @@ Launchers3 IDP3_CAT(launchers3_np, IDP3_NP)() {
     L.np = NP;
     L.epb = EPB;
     L.threads = L3::threads;
-    L.smem = sizeof(Sm3<NP>) * EPB;
+    L.smem = sizeof(Sm3<NP, double>) * EPB;
+    L.smem32 = sizeof(Sm3<NP, float>) * EPB;
     L.prepare = prepare;
     L.element = element;
+    L.element32 = element32;
     L.dt = dt;
     L.mflux = mflux;
     L.mfactor = mfactor;

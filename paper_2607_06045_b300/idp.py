@@ -77,7 +77,7 @@ class GridDesc3(C.Structure):
 
 
 class Options3(C.Structure):
-    _fields_ = [("limiting", C.c_int32), ("beta", C.c_double), ("cfl", C.c_double)]
+    _fields_ = [("limiting", C.c_int32), ("beta", C.c_double), ("cfl", C.c_double), ("precision", C.c_int32)]
 
 
 class LimiterStats3(C.Structure):

@@ -33,7 +33,7 @@ def main(argv=None):
             g = W.box_refined_mesh3(a.n3, a.n3, a.n3, (0.0, 0.0, 0.0, 1.0, 1.0, 1.0),
                                     (0.25, 0.25, 0.25, 0.75, 0.75, 0.75), bc=(3,) * 6)
         u = W.blast3_state(g, a.N, rho_bg=1.0, p_bg=0.1, rho_in=1.0, p_in=10.0)
-        ctx = idp.Context3D(g, a.N, limiting=a.limiting, cfl=0.5)
+        ctx = idp.Context3D(g, a.N, limiting=a.limiting, cfl=0.5, precision=a.precision)
         ud = torch.from_numpy(u).cuda()
         t = np.zeros(1)
         ctx.idp3d_step(ud, a.steps, t)

@@ -3,7 +3,9 @@
 
 Tolerances: right-hand sides (unlimited and limited) 1e-12 relative to the
 residual scale max|u_v| / dt_idp, as in 2D; the time step 1e-13; SSP-RK3
-steps 1e-10 relative to max|u_v| after 20 steps.
+steps 1e-10 relative to max|u_v| after 20 steps. The FP32 form against the
+FP64 oracle: mass-weighted L1 of the density within 1e-5 and of the other
+fields within 3e-5 after 20 steps, right-hand sides within 1e-5.
 """
 import numpy as np
 import pytest
@@ -315,3 +317,84 @@ def test_octree_bad_meshes():
     gap = W.Mesh3(3, 3, 3, UNIT, m.level[1:], m.ix[1:], m.iy[1:], m.iz[1:])
     with pytest.raises(idp.IdpError):
         idp.Context3D(gap, 2)
+
+
+# ----------------------------------------------------------------------------
+# the FP32 form (precision 1): fluxes in FP32, limiter and sums in FP64
+# ----------------------------------------------------------------------------
+
+def l1_fields3(u, ref, m):
+    """Mass-weighted L1 difference per conserved field relative to the
+    reference (momenta against sum m (|ref| + sqrt(rho E)))."""
+    u, ref = np.asarray(u).reshape(5, -1), np.asarray(ref).reshape(5, -1)
+    ps = np.sqrt(np.abs(ref[0] * ref[4]))
+    out = []
+    for v in range(5):
+        den = (m * np.abs(ref[v])).sum() + ((m * ps).sum() if v in (1, 2, 3) else 0.0)
+        out.append(float((m * np.abs(u[v] - ref[v])).sum() / den))
+    return out
+
+
+@pytest.mark.parametrize("N,kind,lim", [(2, "grid", 2), (3, "grid", 2), (4, "grid", 1), (3, "small", 2),
+                                        (3, "large", 2), (2, "extruded", 2)])
+def test_fp32_form_steps(N, kind, lim):
+    """20 SSP-RK3 steps of the FP32 form against the FP64 oracle: density L1
+    within 1e-5 and the other fields within 3e-5 (as the 2D FP32 form), no
+    bound violation, the time within 1e-6."""
+    import torch
+    if kind == "grid":
+        m = grid("walls", n=(3, 3, 2))
+        u = W.random3_state(m, N, seed=N, rho_range=(0.5, 2.0), p_range=(0.5, 2.0), vmax=0.5)
+    else:
+        m = octree(kind)
+        u = sphere3(m, N) if kind != "extruded" else W.random3_state(m, N, seed=N)
+    o = o3d.Oracle3D(m, N)
+    u_o, t_o, _, _ = o.step(u, 20, cfl=0.5, limiting=lim)
+    ctx = idp.Context3D(m, N, limiting=lim, cfl=0.5, precision=1)
+    ud = dev(u)
+    t = np.zeros(1)
+    rc, _ = ctx.idp3d_step(ud, 20, t)
+    assert rc == idp.IDP_OK
+    torch.cuda.synchronize()
+    e = l1_fields3(ud.cpu().numpy(), u_o, o.masses())
+    assert e[0] <= 1e-5 and max(e[1:]) <= 3e-5, e
+    assert abs(t[0] - t_o) <= 1e-6 * t_o
+    rc, st = ctx.idp3d_limiter_stats()
+    assert st["n_viol_density"] == 0 and st["n_viol_pressure"] == 0 and st["n_nonpositive"] == 0
+    ctx.close()
+
+
+def test_fp32_form_rhs():
+    """One limited right-hand side of the FP32 form within 1e-5 of the
+    oracle's, relative to the residual scale."""
+    m, N = octree("small"), 3
+    u = sphere3(m, N)
+    o = o3d.Oracle3D(m, N)
+    dt_idp = o.dt(u, cfl=1.0)
+    sc = scale(u, dt_idp)
+    for lim in (0, 2):
+        ctx = idp.Context3D(m, N, limiting=lim, precision=1)
+        dt = 0.0 if lim == 0 else 0.5 * dt_idp
+        e = rel(gpu_rhs(ctx, u, dt), o.rhs(u, dt=dt, limiting=lim), sc)
+        assert e <= 1e-5, (lim, e)
+        ctx.close()
+
+
+def test_fp32_form_near_vacuum_blast():
+    import torch
+    N = 3
+    m = W.box_refined_mesh3(4, 4, 4, UNIT, (0.3, 0.3, 0.3, 0.7, 0.7, 0.7))
+    u = W.blast3_state(m, N, rho_bg=1e-5, p_bg=1e-6, rho_in=1.0, p_in=1e2, centre=(0.45, 0.5, 0.55), r0=0.2)
+    ctx = idp.Context3D(m, N, limiting=1, cfl=0.9, precision=1)
+    ud = dev(u)
+    I0 = ctx.idp3d_integrals(ud)
+    t = np.zeros(1)
+    rc, _ = ctx.idp3d_step(ud, 40, t)
+    assert rc == idp.IDP_OK
+    I1 = ctx.idp3d_integrals(ud)
+    assert np.abs(I1 - I0).max() <= 1e-12 * np.abs(I0).max()
+    q = ud.cpu().numpy().reshape(5, -1)
+    p = (G - 1.0) * (q[4] - 0.5 * (q[1] ** 2 + q[2] ** 2 + q[3] ** 2) / q[0])
+    assert q[0].min() > 0.0 and p.min() > 0.0
+    torch.cuda.synchronize()
+    ctx.close()
