@@ -395,12 +395,15 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     extern __shared__ __align__(16) unsigned char sm3_raw[];
     SM *S = reinterpret_cast<SM *>(sm3_raw);
     __shared__ Ops3 ops;
+    __shared__ float Sf[NP][NP];   // Sbar in FP32 (the FP32 form)
     const int tid = threadIdx.x;
     for (int k = tid; k < (int)(sizeof(Ops3) / sizeof(double)); k += NT)
         reinterpret_cast<double *>(&ops)[k] = reinterpret_cast<const double *>(ops_g)[k];
+    if (F32)
+        for (int k = tid; k < NP * NP; k += NT) Sf[k / NP][k % NP] = idp::d2f(ops_g->S[k / NP][k % NP]);
     const size_t KN = (size_t)G.K * NN;
     const double g = A.gamma, gm1 = g - 1.0, igm1 = 1.0 / gm1;
-    const double dt = stage_dt3(A);
+    const double dt = stage_dt3(A), idt = 1.0 / dt;
     const int e0 = blockIdx.x * EPB;
     const Mort3 &MO = G.mort;
     // ---- P0: state, primitives, logarithms, wave speeds; outside states
@@ -556,10 +559,15 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const FT *uL = side ? ui : uo, *uR = side ? uo : ui, *fL = side ? fi : fo, *fR = side ? fo : fi;
         for (int v = 0; v < NV; ++v)
             S[le].ff[s][t][v] = to_d3(cwf * (FT(0.5) * (fL[v] + fR[v]) - FT(0.5) * lam * (uR[v] - uL[v])));
-        // ubar = (u_i + u_o)/2 - c.(f_o - f_i)/(2 |c| lambda), c along the outward normal (FP64)
-        const double sg = side ? 0.5 : -0.5;
-        const double fb = 0.5 * (X.u[0][nin] + X.outs[s][t][0]) -
-                          sg * (X.outs[s][t][1 + d] - X.u[1 + d][nin]) * idp::fast_rcp(to_d3(lam));
+        // ubar = (u_i + u_o)/2 - c.(f_o - f_i)/(2 |c| lambda), c along the outward normal
+        double fb;
+        if constexpr (F32) {
+            const float sgf = side ? 0.5f : -0.5f;
+            fb = idp::f2d(0.5f * (ui[0] + uo[0]) - sgf * (uo[1 + d] - ui[1 + d]) * __frcp_rn(lam));
+        } else {
+            const double sg = side ? 0.5 : -0.5;
+            fb = 0.5 * (ui[0] + uo[0]) - sg * (uo[1 + d] - ui[1 + d]) * idp::fast_rcp(lam);
+        }
         S[le].fbl[s][t] = fb;
         S[le].fbh[s][t] = fb;
     }
@@ -583,7 +591,8 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const double ccd = ops.w[r % NP] * ops.w[r / NP] * X.q[d] / 2.0;
         const FT cc = (FT)(F32 ? (double)idp::d2f(ccd) : ccd);
         for (int v = 0; v < NV; ++v) S[le].fvf[id][v] = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
-        S[le].ibar[id] = 0.5 * (X.u[0][nl] + X.u[0][nr]) - 0.5 * (X.u[1 + d][nr] - X.u[1 + d][nl]) * idp::fast_rcp(to_d3(lam));
+        if constexpr (F32) S[le].ibar[id] = idp::f2d(0.5f * (ul[0] + ur[0]) - 0.5f * (ur[1 + d] - ul[1 + d]) * __frcp_rn(lam));
+        else S[le].ibar[id] = 0.5 * (ul[0] + ur[0]) - 0.5 * (ur[1 + d] - ul[1 + d]) * idp::fast_rcp(lam);
     }
     __syncthreads();
     // ---- P2: low-order residual, low-order update and bounds per node
@@ -645,19 +654,31 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / (3 * NR), r0 = k - le * 3 * NR, d = r0 / NR, r = r0 - d * NR;
         if (e0 + le >= G.K) continue;
         const double wt = ops.w[r % NP] * ops.w[r / NP];
+        // FP32 form: the contraction in FP32 (each interface's A is formed
+        // once and enters both its nodes, so conservation is untouched)
+        const float wqf = F32 ? idp::d2f(wt * S[le].q[d]) : 0.0f;
         double acc[NV] = {0, 0, 0, 0, 0};
+        float accf[NV] = {0, 0, 0, 0, 0};
         for (int l = 0; l < N; ++l) {
             for (int mm = 0; mm < NP; ++mm) {
                 if (mm == l) continue;   // Sbar has a zero diagonal
                 const int lo_ = l < mm ? l : mm, hi_ = l < mm ? mm : l;
                 const int pp = lo_ * (2 * NP - lo_ - 1) / 2 + (hi_ - lo_ - 1);
-                const double sq = ops.S[l][mm] * S[le].q[d];
-                for (int v = 0; v < NV; ++v) acc[v] += sq * to_d3(S[le].pair[d][r][pp][v]);
+                if constexpr (F32) {
+                    const float sf = Sf[l][mm];
+                    for (int v = 0; v < NV; ++v) accf[v] += sf * S[le].pair[d][r][pp][v];
+                } else {
+                    const double sq = ops.S[l][mm] * S[le].q[d];
+                    for (int v = 0; v < NV; ++v) acc[v] += sq * to_d3(S[le].pair[d][r][pp][v]);
+                }
             }
             const int id = (d * NR + r) * N + l;
             const int nl = node_of<NP>(d, r, l), nr = node_of<NP>(d, r, l + 1);
             const double iml = S[le].im[nl], imr = S[le].im[nr];
-            for (int v = 0; v < NV; ++v) S[le].A[id][v] = wt * acc[v] - to_d3(S[le].fvf[id][v]);
+            for (int v = 0; v < NV; ++v) {
+                if constexpr (F32) S[le].A[id][v] = idp::f2d(wqf * accf[v] - S[le].fvf[id][v]);
+                else S[le].A[id][v] = wt * acc[v] - S[le].fvf[id][v];
+            }
             const double Ar = fabs(S[le].A[id][0]);
             S[le].ex[id] = (dt * iml * Ar <= kTol3 * fabs(S[le].ufv[0][nl])) && (dt * imr * Ar <= kTol3 * fabs(S[le].ufv[0][nr]));
         }
@@ -684,7 +705,8 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             }
         }
         const double rf = S[le].ufv[0][n];
-        const double Qp = m / dt * (S[le].rmax[n] - rf), Qm = m / dt * (S[le].rmin[n] - rf);
+        const double mdt = m * idt;
+        const double Qp = mdt * (S[le].rmax[n] - rf), Qm = mdt * (S[le].rmin[n] - rf);
         // the quotients only where the bound has room (R < 1)
         double Rp = (idp::dpos(Pp) && idp::dlt(Qp, Pp)) ? Qp * idp::fast_rcp(Pp) : 1.0;
         double Rm = (idp::dneg(Pm) && idp::dlt(Pm, Qm)) ? Qm * idp::fast_rcp(Pm) : 1.0;
@@ -831,26 +853,52 @@ __device__ __forceinline__ bool wave_speeds3(double g, const double *u, double *
     return true;
 }
 
+// the same in FP32 from the certified FP32 primitives (the FP32 form)
+__device__ __forceinline__ bool wave_speeds3(double g, const double *u, float *lam) {
+    float uf[NV], v[3], p, ir;
+    const bool ok = prim3_f32(g - 1.0, u, uf, v, p, ir);
+    const float c = ok ? sqrtf(idp::d2f(g) * p * ir) : 0.0f;
+    for (int d = 0; d < 3; ++d) lam[d] = ok ? fabsf(v[d]) + c : 0.0f;
+    return ok;
+}
+
+// The FP32 form's time step is formed in FP32 and scaled by (1 - 8e-6):
+// its wave speeds carry the certified FP32 pressure (within 2.5e-6 of the
+// rounded state's), a square root and a few roundings, so the scaled
+// quotient stays below the FP64 one.
+constexpr double kDtSafe32 = 1.0 - 8e-6;
+
 // IDP time step (Eq. timestep_restriction): per node m_i / sum_j 2 d_ij over
 // its subcell and face neighbours (at a mortar side the slot's sum over its
 // pairs, formed by the mortar flux kernel from the same state); minimum per
-// block, one atomic per block
-template <int NP, int EPB>
+// block, one atomic per block. 2 d_ij of a subcell or conforming pair is
+// w_t1 w_t2 (A_d / 4) max(lambda_i, lambda_j). FT = float: wave speeds, sums
+// and the quotient in FP32 (the FP32 form).
+template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(Launch3<NP, EPB>::threads)
 k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, double gamma,
        unsigned long long *dtmin, unsigned *status) {
     using E = El3<NP>;
+    constexpr bool F32 = sizeof(FT) == 4;
     constexpr int N = E::N, NN = E::NN, NT = Launch3<NP, EPB>::threads;
-    __shared__ double lam[EPB][3][NN];
-    __shared__ double w[NP];
+    __shared__ FT lam[EPB][3][NN];
+    __shared__ FT w[NP];
+    __shared__ FT geo[EPB][4];   // quarter face areas, dx dy dz / 8
     __shared__ unsigned long long best_s[NT / 32];
-    if (threadIdx.x < NP) w[threadIdx.x] = ops_g->w[threadIdx.x];
+    if (threadIdx.x < NP) w[threadIdx.x] = (FT)(F32 ? (double)idp::d2f(ops_g->w[threadIdx.x]) : ops_g->w[threadIdx.x]);
     const size_t KN = (size_t)G.K * NN;
     const int e0 = blockIdx.x * EPB, tid = threadIdx.x;
     for (int k = tid; k < EPB * NN; k += NT) {
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
-        double uv[NV], l3[3];
+        if (n == 0) {
+            double h[3];
+            extents3(G, e, h);
+            const double gd[4] = {h[1] * h[2] / 4.0, h[0] * h[2] / 4.0, h[0] * h[1] / 4.0, h[0] * h[1] * h[2] / 8.0};
+            for (int c = 0; c < 4; ++c) geo[le][c] = (FT)(F32 ? (double)idp::d2f(gd[c]) : gd[c]);
+        }
+        double uv[NV];
+        FT l3[3];
         for (int v = 0; v < NV; ++v) uv[v] = u[v * KN + (size_t)e * NN + n];
         if (!wave_speeds3(gamma, uv, l3)) atomicOr(status, S_BAD_INPUT);
         for (int d = 0; d < 3; ++d) lam[le][d][n] = l3[d];
@@ -861,24 +909,21 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
-        double h[3];
-        extents3(G, e, h);
-        const double q[3] = {h[1] * h[2] / 4.0, h[0] * h[2] / 4.0, h[0] * h[1] / 4.0};
-        const double J = h[0] * h[1] * h[2] / 8.0;
-        double s2d = 0.0;
+        FT s2d = FT(0);
+        double smort = 0.0;   // the mortar slots' sums (FP64)
         for (int d = 0; d < 3; ++d) {
-            const double cd = w[idx[(d + 1) % 3]] * w[idx[(d + 2) % 3]] * q[d] / 2.0;
-            const double li = lam[le][d][n];
+            const int pos = idx[d];
+            const FT li = lam[le][d][n];
+            FT lsum = FT(0);
             for (int side = 0; side < 2; ++side) {
-                const int pos = idx[d];
-                double lo;
+                FT lo;
                 if (side == 0 ? pos > 0 : pos < N) {
                     const int nn2 = n + (side == 0 ? -1 : 1) * (d == 0 ? 1 : (d == 1 ? NP : NP * NP));
                     lo = lam[le][d][nn2];
                 } else {
                     const int s = 2 * d + side, nb = G.nbr[6 * e + s];
                     if (nb < -1) {
-                        s2d += G.mort.dsum[-2 - nb + idx[(d + 1) % 3] + NP * idx[(d + 2) % 3]];
+                        smort += G.mort.dsum[-2 - nb + idx[(d + 1) % 3] + NP * idx[(d + 2) % 3]];
                         continue;
                     }
                     double o[NV];
@@ -892,15 +937,23 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
                         for (int v = 0; v < NV; ++v) in[v] = u[v * KN + (size_t)e * NN + n];
                         ghost3(G, s, in, o);
                     }
-                    double l3[3];
+                    FT l3[3];
                     wave_speeds3(gamma, o, l3);
                     lo = l3[d];
                 }
-                s2d += 2.0 * cd * idp::dmax(li, lo);
+                if constexpr (F32) lsum += fmaxf(li, lo);
+                else lsum += idp::dmax(li, lo);
             }
+            s2d += w[idx[(d + 1) % 3]] * w[idx[(d + 2) % 3]] * geo[le][d] * lsum;
         }
-        const double m = w[idx[0]] * w[idx[1]] * w[idx[2]] * J;
-        const double val = m * idp::fast_rcp(s2d);
+        const FT m = w[idx[0]] * w[idx[1]] * w[idx[2]] * geo[le][3];
+        double val;
+        if constexpr (F32) {
+            const float tot = smort == 0.0 ? s2d : (float)(idp::f2d(s2d) + smort) ;
+            val = idp::f2d(__fdiv_rn(m, tot)) * kDtSafe32;
+        } else {
+            val = m * idp::fast_rcp(s2d + smort);
+        }
         const unsigned long long vb = (unsigned long long)__double_as_longlong(val);
         if (val > 0.0 && vb < best) best = vb;
     }

@@ -90,6 +90,12 @@ int dt_grid(const idp3d_ctx *c) { return (c->grid.K + c->L.epb - 1) / c->L.epb; 
 
 bool has_mortars(const idp3d_ctx *c) { return c->grid.mort.M > 0; }
 
+// the time-step kernel of the context's precision
+void launch_dt(idp3d_ctx *c, cudaStream_t st, const double *u, unsigned long long *dtmin) {
+    if (c->opt.precision == 1) c->L.dt32(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status);
+    else c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status);
+}
+
 // one limited stage: the mortar fluxes of its input (unless already formed),
 // the element kernel, then the mortar factors and the mortar nodes
 void enqueue_stage(idp3d_ctx *c, cudaStream_t st, const Stage3 &A, bool mflux) {
@@ -107,7 +113,7 @@ void enqueue_stage(idp3d_ctx *c, cudaStream_t st, const Stage3 &A, bool mflux) {
 // stage's mortar fluxes)
 void enqueue_step(idp3d_ctx *c, cudaStream_t st, double *u) {
     if (has_mortars(c)) c->L.mflux(st, c->grid, c->d_mops, u, c->gamma);
-    c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, c->d_dtmin, c->d_status);
+    launch_dt(c, st, u, c->d_dtmin);
     enqueue_stage(c, st, stage_args(c, u, u, c->d_buf1, 1, 0), false);
     enqueue_stage(c, st, stage_args(c, c->d_buf1, u, c->d_buf2, 1, 1), true);
     // each node reads its own u^n, then writes it
@@ -505,7 +511,7 @@ idp_status idp3d_dt(idp3d_ctx *c, const double *u, double *dt_host, void *stream
     if (cudaMemcpyAsync(c->d_dtmin2, &kInfBits, sizeof(kInfBits), cudaMemcpyHostToDevice, st) != cudaSuccess)
         return IDP_E_CUDA;
     if (has_mortars(c)) c->L.mflux(st, c->grid, c->d_mops, u, c->gamma);
-    c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, c->d_dtmin2, c->d_status);
+    launch_dt(c, st, u, c->d_dtmin2);
     if (cudaMemcpyAsync(&b, c->d_dtmin2, sizeof(b), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return IDP_E_CUDA;

@@ -35,7 +35,12 @@ void element32(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const
 
 void dt(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
         unsigned long long *dtmin, unsigned *status) {
-    k_dt3d<NP, EPB><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status);
+    k_dt3d<NP, EPB, double><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status);
+}
+
+void dt32(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
+          unsigned long long *dtmin, unsigned *status) {
+    k_dt3d<NP, EPB, float><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status);
 }
 
 void mflux(cudaStream_t st, const Grid3 &G, const MOps3 *mo, const double *u, double gamma) {
@@ -64,6 +69,7 @@ Launchers3 IDP3_CAT(launchers3_np, IDP3_NP)() {
     L.element = element;
     L.element32 = element32;
     L.dt = dt;
+    L.dt32 = dt32;
     L.mflux = mflux;
     L.mfactor = mfactor;
     L.mapply = mapply;

@@ -340,7 +340,8 @@ def l1_fields3(u, ref, m):
 def test_fp32_form_steps(N, kind, lim):
     """20 SSP-RK3 steps of the FP32 form against the FP64 oracle: density L1
     within 1e-5 and the other fields within 3e-5 (as the 2D FP32 form), no
-    bound violation, the time within 1e-6."""
+    bound violation, the time within 2e-5 (its time step is FP32, scaled
+    down by 8e-6)."""
     import torch
     if kind == "grid":
         m = grid("walls", n=(3, 3, 2))
@@ -358,9 +359,24 @@ def test_fp32_form_steps(N, kind, lim):
     torch.cuda.synchronize()
     e = l1_fields3(ud.cpu().numpy(), u_o, o.masses())
     assert e[0] <= 1e-5 and max(e[1:]) <= 3e-5, e
-    assert abs(t[0] - t_o) <= 1e-6 * t_o
+    assert abs(t[0] - t_o) <= 2e-5 * t_o
     rc, st = ctx.idp3d_limiter_stats()
     assert st["n_viol_density"] == 0 and st["n_viol_pressure"] == 0 and st["n_nonpositive"] == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("N", [1, 3, 4])
+@pytest.mark.parametrize("kind", ["grid", "small", "large"])
+def test_fp32_form_dt_is_safe_and_tight(N, kind):
+    """The FP32 form's time step never exceeds the FP64 oracle's and is
+    within 2e-5 of it, on random and sphere states."""
+    m = grid("dirichlet") if kind == "grid" else octree(kind)
+    o = o3d.Oracle3D(m, N)
+    ctx = idp.Context3D(m, N, cfl=0.7, precision=1)
+    for u in (W.random3_state(m, N, seed=3, rho_range=(0.1, 10.0), p_range=(0.1, 10.0), vmax=2.0),
+              sphere3(m, N) if kind != "grid" else W.random3_state(m, N, seed=4)):
+        d32, d64 = ctx.idp3d_dt(dev(u)), o.dt(u, cfl=0.7)
+        assert d32 <= d64 and d32 >= d64 * (1.0 - 2e-5), (d32, d64)
     ctx.close()
 
 
