@@ -109,6 +109,11 @@ struct Stage3 {
     unsigned *status;
 };
 
+// a statistic's running minimum (positive doubles order like their bits)
+__device__ __forceinline__ void stat_min(unsigned long long *slot, double v) {
+    if (v > 0.0 && v < INFINITY) atomicMin(slot, (unsigned long long)__double_as_longlong(v));
+}
+
 __device__ __forceinline__ double stage_dt3(const Stage3 &A) {
     return A.dtmin ? A.cfl * __longlong_as_double((long long)*A.dtmin) : A.dt_host;
 }
@@ -252,20 +257,30 @@ struct Sm3 {
         double u[NV][NN];      // P0 - P2: the stage input
         double rfv[NV][NN];    // P2 - P5: low-order residual (each node overwrites only its own u)
     };
-    Node3<NP, sizeof(FT) == 4> nd;   // P0 - P1
-    FT outp[6][NR][3];         // P0 - P1: outside states' normal velocity, pressure, wave speed
     union {
-        double outs[6][NR][NV];   // P0 - P1: outside states of the six faces
-        struct {                  // P2b - P5
-            double Rp[NN], Rm[NN];       // Zalesak factors (P3 - P4)
-            double ell[NIF];             // interface factors (P4 - P5)
-            unsigned char ex[NIF];       // R15 exemption (P2b - P4)
+        struct {                          // P0 - P1
+            Node3<NP, sizeof(FT) == 4> nd;
+            FT outp[6][NR][3];            // outside states' normal velocity, pressure, wave speed
         };
+        struct {                          // P2 - P5
+            double ufv[NV][NN];           // the low-order update u_FV
+            double rmin[NN], rmax[NN], pmin[NN];
+            double c0[NN];                // g(0) = (gamma-1)(rho E - |m|^2/2) - p_min rho at u_FV (P2 - P4)
+            double im[NN];                // 1 / m
+        };
+    };
+    struct {                      // P2b - P5
+        double Rp[NN], Rm[NN];       // Zalesak factors (P3 - P4)
+        double ell[NIF];             // interface factors (P4 - P5)
+        unsigned char ex[NIF];       // R15 exemption (P2b - P4)
     };
     FT pair[3][NR][NPAIR][NV];       // P1 - P2b: two-point fluxes of every row
     union {
-        struct {                     // P1 - P2
-            double ff[6][NR][NV];    // face fluxes, mass-weighted, along +d
+        struct {                     // P0 - P2
+            union {
+                double outs[6][NR][NV];   // P0 - P1b: outside states of the six faces
+                double ff[6][NR][NV];     // P1b - P2: face fluxes, mass-weighted, along +d (each
+            };                            // P1b item reads its outside state, then writes its flux)
             double fbl[6][NR];       // bar-state density range across the face (one value
             double fbh[6][NR];       // at a conforming face, a mortar slot's range at a mortar)
             double ibar[NIF];        // bar-state density of the interior interfaces
@@ -273,10 +288,6 @@ struct Sm3 {
         double A[NIF][NV];           // P2b - P5: antidiffusive fluxes (mass-weighted)
     };
     FT fvf[NIF][NV];           // P1 - P2b: low-order subcell fluxes, mass-weighted, along +d
-    double ufv[NV][NN];        // P2 - P5
-    double rmin[NN], rmax[NN], pmin[NN];
-    double c0[NN];             // P2 - P4: g(0) = (gamma-1)(rho E - |m|^2/2) - p_min rho at u_FV
-    double im[NN];             // P2 - P5: 1 / m
     double q[3], J, iJ;        // quarter face areas, dx dy dz / 8 and its inverse
     int nb[6];                 // the sides' neighbour entries (Grid3::nbr)
 };
@@ -396,9 +407,15 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     SM *S = reinterpret_cast<SM *>(sm3_raw);
     __shared__ Ops3 ops;
     __shared__ float Sf[NP][NP];   // Sbar in FP32 (the FP32 form)
+    __shared__ double w3[NN], iw3[NN];   // w_i w_j w_k and its inverse per node of an element
     const int tid = threadIdx.x;
     for (int k = tid; k < (int)(sizeof(Ops3) / sizeof(double)); k += NT)
         reinterpret_cast<double *>(&ops)[k] = reinterpret_cast<const double *>(ops_g)[k];
+    for (int k = tid; k < NN; k += NT) {
+        const int i = k % NP, j = (k / NP) % NP, l = k / (NP * NP);
+        w3[k] = ops_g->w[i] * ops_g->w[j] * ops_g->w[l];
+        iw3[k] = (1.0 / ops_g->w[i]) * (1.0 / ops_g->w[j]) * (1.0 / ops_g->w[l]);
+    }
     if (F32)
         for (int k = tid; k < NP * NP; k += NT) Sf[k / NP][k % NP] = idp::d2f(ops_g->S[k / NP][k % NP]);
     const size_t KN = (size_t)G.K * NN;
@@ -600,7 +617,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / NN, n = k - le * NN;
         if (e0 + le >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
-        const double im = ops.iw[idx[0]] * ops.iw[idx[1]] * ops.iw[idx[2]] * S[le].iJ;
+        const double im = iw3[n] * S[le].iJ;
         double r[NV] = {0, 0, 0, 0, 0}, uv[NV];
         for (int v = 0; v < NV; ++v) uv[v] = S[le].u[v][n];
         double lo = uv[0], hi = uv[0];
@@ -689,7 +706,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const int le = k / NN, n = k - le * NN;
         if (e0 + le >= G.K) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
-        const double m = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * S[le].J;
+        const double m = w3[n] * S[le].J;
         double Pp = 0.0, Pm = 0.0;
         for (int d = 0; d < 3; ++d) {
             const int pos = idx[d], row = idx[(d + 1) % 3] + NP * idx[(d + 2) % 3];
@@ -801,17 +818,32 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             }
         }
         if (A.collect && A.limiting > 0) {
-            const double mm_ = ops.w[idx[0]] * ops.w[idx[1]] * ops.w[idx[2]] * S[le].J;
-            am += mm_ * (1.0 - lm);
-            if (lm < 1.0) nact++;
+            if (idp::dlt(lm, 1.0)) {
+                am += w3[n] * S[le].J * (1.0 - lm);
+                nact++;
+            }
             if (mslot < 0) {
-                const double p = pres3(g, ut);
                 const double rl = S[le].rmin[n], rh = S[le].rmax[n], pl = S[le].pmin[n];
-                if (ut[0] < rl - kViol3 * fabs(rl) || ut[0] > rh + kViol3 * fabs(rh)) vr++;
-                if (p < pl - kViol3 * fabs(pl)) vp++;
-                if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;
+                // the density bounds: the exact comparison first, the tolerance only past a bound
+                if ((idp::dlt(ut[0], rl) && idp::dlt(ut[0], rl - kViol3 * fabs(rl))) ||
+                    (idp::dlt(rh, ut[0]) && idp::dlt(rh + kViol3 * fabs(rh), ut[0])))
+                    vr++;
+                // rho p = (gamma-1)(rho E - |m|^2/2) against p_min rho: certified in
+                // FP32 when it clears the bound by 1e-5 of its terms (far above the
+                // FP32 rounding of these few operations), else decided in FP64
+                float q[NV];
+                for (int v = 0; v < NV; ++v) q[v] = idp::d2f(ut[v]);
+                const float kef = 0.5f * (q[1] * q[1] + q[2] * q[2] + q[3] * q[3]), ref = q[0] * q[4];
+                const float gf = idp::d2f(gm1), rpf = gf * (ref - kef), lim = idp::d2f(pl) * q[0];
+                if (q[0] > 0.0f && rpf - lim > 1e-5f * (gf * (fabsf(ref) + kef) + fabsf(lim))) {
+                    pmin_st = idp::dmin(pmin_st, idp::f2d(__fdiv_rn(rpf, q[0])));
+                } else {
+                    const double rp = gm1 * (ut[0] * ut[4] - 0.5 * (ut[1] * ut[1] + ut[2] * ut[2] + ut[3] * ut[3]));
+                    if (idp::dlt(rp, (pl - kViol3 * fabs(pl)) * ut[0])) vp++;
+                    if (!idp::dpos(ut[0]) || !idp::dpos(rp)) np_++;
+                    else pmin_st = idp::dmin(pmin_st, idp::f2d(__fdiv_rn(idp::d2f(rp), q[0])));
+                }
                 rmin_st = idp::dmin(rmin_st, ut[0]);
-                pmin_st = idp::dmin(pmin_st, p);
             }
         }
     }
@@ -832,8 +864,8 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             if (vr) atomicAdd(&A.stats->n_vrho, (unsigned long long)vr);
             if (vp) atomicAdd(&A.stats->n_vp, (unsigned long long)vp);
             if (np_) atomicAdd(&A.stats->n_nonpos, (unsigned long long)np_);
-            if (rmin_st > 0.0 && rmin_st < INFINITY) atomicMin(&A.stats->min_rho_bits, (unsigned long long)__double_as_longlong(rmin_st));
-            if (pmin_st > 0.0 && pmin_st < INFINITY) atomicMin(&A.stats->min_p_bits, (unsigned long long)__double_as_longlong(pmin_st));
+            stat_min(&A.stats->min_rho_bits, rmin_st);
+            stat_min(&A.stats->min_p_bits, pmin_st);
         }
     }
     if (A.collect && (vr | vp | np_) != 0u && (tid & 31) == 0) atomicOr(A.status, S_VIOLATION);

@@ -29,7 +29,7 @@ struct idp3d_ctx {
     idp3d_options opt{};
     Grid3 grid{};
     Launchers3 L;
-    int grid_el = 1;               // element-kernel blocks
+    int grid_el = 1, grid_el64 = 1;   // element-kernel blocks: FP32 form, FP64 path
     Ops3 *d_ops = nullptr;
     MOps3 *d_mops = nullptr;
     idp::LogTab *d_lg = nullptr;
@@ -101,7 +101,7 @@ void launch_dt(idp3d_ctx *c, cudaStream_t st, const double *u, unsigned long lon
 void enqueue_stage(idp3d_ctx *c, cudaStream_t st, const Stage3 &A, bool mflux) {
     if (has_mortars(c) && mflux) c->L.mflux(st, c->grid, c->d_mops, A.u, c->gamma);
     if (c->opt.precision == 1) c->L.element32(c->grid_el, st, c->grid, c->d_ops, A);
-    else c->L.element(c->grid_el, st, c->grid, c->d_ops, A);
+    else c->L.element(c->grid_el64, st, c->grid, c->d_ops, A);
     if (has_mortars(c)) {
         c->L.mfactor(st, c->grid, A);
         c->L.mapply(st, c->grid, A);
@@ -365,6 +365,7 @@ idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, co
     c->volume = (gd->x1 - gd->x0) * (gd->y1 - gd->y0) * (gd->z1 - gd->z0);
     c->L = get3(c->NP);
     c->grid_el = (G.K + c->L.epb - 1) / c->L.epb;
+    c->grid_el64 = (G.K + c->L.epb64 - 1) / c->L.epb64;
     Ops3 ops;
     std::memset(&ops, 0, sizeof(ops));
     {

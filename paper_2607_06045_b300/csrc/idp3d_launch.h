@@ -11,7 +11,7 @@
 namespace idp3 {
 
 struct Launchers3 {
-    int np = 0, epb = 0, threads = 0;
+    int np = 0, epb = 0, epb64 = 0, threads = 0;   // elements per block: time step and FP32 form; FP64 element kernel
     size_t smem = 0, smem32 = 0;   // dynamic shared memory of one element-kernel block (FP64 path, FP32 form)
     cudaError_t (*prepare)() = nullptr;
     // the element kernel: FP64 path, FP32 form

@@ -319,8 +319,8 @@ __global__ void __launch_bounds__(256) k_mapply3(Grid3 G, Stage3 A) {
             if (vr) atomicAdd(&A.stats->n_vrho, (unsigned long long)vr);
             if (vp) atomicAdd(&A.stats->n_vp, (unsigned long long)vp);
             if (np_) atomicAdd(&A.stats->n_nonpos, (unsigned long long)np_);
-            if (rmin_st > 0.0 && rmin_st < INFINITY) atomicMin(&A.stats->min_rho_bits, (unsigned long long)__double_as_longlong(rmin_st));
-            if (pmin_st > 0.0 && pmin_st < INFINITY) atomicMin(&A.stats->min_p_bits, (unsigned long long)__double_as_longlong(pmin_st));
+            stat_min(&A.stats->min_rho_bits, rmin_st);
+            stat_min(&A.stats->min_p_bits, pmin_st);
         }
         if ((vr | vp | np_) != 0u && (threadIdx.x & 31) == 0) atomicOr(A.status, S_VIOLATION);
     }

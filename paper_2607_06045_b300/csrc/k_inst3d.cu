@@ -14,19 +14,21 @@ namespace {
 
 constexpr int NP = IDP3_NP;
 // elements per block: about 128 threads, one per node
-constexpr int EPB = NP == 2 ? 16 : (NP == 3 ? 4 : (NP == 4 ? 2 : 1));
+constexpr int EPB = NP == 2 ? 16 : (NP == 3 ? 4 : (NP == 4 ? 2 : 1));   // time step, FP32 form
+constexpr int EPB64 = EPB;                                              // FP64 element kernel
 using L3 = Launch3<NP, EPB>;
+using L64 = Launch3<NP, EPB64>;
 
 cudaError_t prepare() {
-    cudaError_t e = cudaFuncSetAttribute(k_element3d<NP, EPB, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(Sm3<NP, double>) * EPB));
+    cudaError_t e = cudaFuncSetAttribute(k_element3d<NP, EPB64, double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(Sm3<NP, double>) * EPB64));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_element3d<NP, EPB, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)(sizeof(Sm3<NP, float>) * EPB));
 }
 
 void element(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) {
-    k_element3d<NP, EPB, double><<<grid, L3::threads, sizeof(Sm3<NP, double>) * EPB, st>>>(G, ops, A);
+    k_element3d<NP, EPB64, double><<<grid, L64::threads, sizeof(Sm3<NP, double>) * EPB64, st>>>(G, ops, A);
 }
 
 void element32(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) {
@@ -62,8 +64,9 @@ Launchers3 IDP3_CAT(launchers3_np, IDP3_NP)() {
     Launchers3 L;
     L.np = NP;
     L.epb = EPB;
+    L.epb64 = EPB64;
     L.threads = L3::threads;
-    L.smem = sizeof(Sm3<NP, double>) * EPB;
+    L.smem = sizeof(Sm3<NP, double>) * EPB64;
     L.smem32 = sizeof(Sm3<NP, float>) * EPB;
     L.prepare = prepare;
     L.element = element;
