@@ -267,6 +267,7 @@ struct Sm3 {
             double rmin[NN], rmax[NN], pmin[NN];
             double c0[NN];                // g(0) = (gamma-1)(rho E - |m|^2/2) - p_min rho at u_FV (P2 - P4)
             double im[NN];                // 1 / m
+            float dtimf[NN], tolf[NN];    // dt / m and 1e-14 |rho_FV| in FP32 (P2 - P2b: the R15 pre-test)
         };
     };
     struct {                      // P2b - P5
@@ -662,6 +663,8 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         S[le].pmin[n] = pm;
         S[le].c0[n] = gm1 * rhoe - pm * uf[0];
         S[le].im[n] = im;
+        S[le].dtimf[n] = idp::d2f(dt * im);
+        S[le].tolf[n] = idp::d2f(kTol3 * fabs(uf[0]));
     }
     __syncthreads();
     // ---- P2b: telescoped high-order subcell fluxes per row (summed in FP64),
@@ -696,8 +699,24 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
                 if constexpr (F32) S[le].A[id][v] = idp::f2d(wqf * accf[v] - S[le].fvf[id][v]);
                 else S[le].A[id][v] = wt * acc[v] - S[le].fvf[id][v];
             }
+            // R15 at both ends: decided in FP32 where the two sides differ by more
+            // than 1e-3 (far above the few FP32 roundings), else in FP64
             const double Ar = fabs(S[le].A[id][0]);
-            S[le].ex[id] = (dt * iml * Ar <= kTol3 * fabs(S[le].ufv[0][nl])) && (dt * imr * Ar <= kTol3 * fabs(S[le].ufv[0][nr]));
+            const float af = fabsf(idp::d2f(Ar));
+            bool exl, exr;
+            {
+                const float lf = S[le].dtimf[nl] * af, tf = S[le].tolf[nl];
+                if (lf < 0.999f * tf) exl = true;
+                else if (lf > 1.001f * tf) exl = false;
+                else exl = dt * iml * Ar <= kTol3 * fabs(S[le].ufv[0][nl]);
+            }
+            {
+                const float lf = S[le].dtimf[nr] * af, tf = S[le].tolf[nr];
+                if (lf < 0.999f * tf) exr = true;
+                else if (lf > 1.001f * tf) exr = false;
+                else exr = dt * imr * Ar <= kTol3 * fabs(S[le].ufv[0][nr]);
+            }
+            S[le].ex[id] = exl && exr;
         }
     }
     __syncthreads();
