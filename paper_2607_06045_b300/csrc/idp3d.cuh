@@ -201,6 +201,33 @@ __device__ __forceinline__ bool admissible3_f32(double gm1, const double *u0, co
     return rh > 4e-6f * (r0 + hf * fabsf(ar));
 }
 
+// The same certificate from FP32 inputs that carry at most three roundings
+// each (u_FV rounded once, a = Gamma dt/m A from two rounded factors): every
+// product and sum below then stays within 20 unit roundings of S, as above.
+__device__ __forceinline__ bool admissible3_f32f(float gm, const float *u0, const float *a, float pm, float c0f,
+                                                 float hf) {
+    if (!(c0f > 0.0f) || !(u0[0] > 0.0f) || !(hf > 0.0f)) return false;
+    const float t1 = u0[0] * a[4], t2 = a[0] * u0[4], t5 = pm * a[0];
+    float tm = 0.0f, sm = 0.0f, q2 = 0.0f;
+    for (int c = 1; c <= 3; ++c) {
+        const float t = u0[c] * a[c];
+        tm += t;
+        sm += fabsf(t);
+        q2 += a[c] * a[c];
+    }
+    const float c1 = gm * (t1 + t2 - tm) - t5;
+    const float s1 = gm * (fabsf(t1) + fabsf(t2) + sm) + fabsf(t5);
+    const float q1 = a[0] * a[4];
+    const float c2 = gm * (q1 - 0.5f * q2);
+    const float s2 = gm * (fabsf(q1) + 0.5f * q2);
+    const float S = fabsf(c0f) + hf * (s1 + hf * s2);
+    if (!(S > 1e-30f) || !(S < 1e30f)) return false;
+    const float gh = c0f + hf * (c1 + hf * c2);
+    if (!(gh > 4e-6f * S)) return false;
+    const float rh = u0[0] + hf * a[0];
+    return rh > 4e-6f * (u0[0] + hf * fabsf(a[0]));
+}
+
 // the ghost state across boundary side s (R4: wall, Dirichlet, outflow)
 __device__ __forceinline__ void ghost3(const Grid3 &G, int s, const double *in, double *q) {
     const int kind = G.bc[s];
@@ -265,9 +292,10 @@ struct Sm3 {
         struct {                          // P2 - P5
             double ufv[NV][NN];           // the low-order update u_FV
             double rmin[NN], rmax[NN], pmin[NN];
-            double c0[NN];                // g(0) = (gamma-1)(rho E - |m|^2/2) - p_min rho at u_FV (P2 - P4)
             double im[NN];                // 1 / m
-            float dtimf[NN], tolf[NN];    // dt / m and 1e-14 |rho_FV| in FP32 (P2 - P2b: the R15 pre-test)
+            // FP32 copies for the certificates (P2 - P4): u_FV, Gamma dt / m,
+            // p_min and g(0) = (gamma-1)(rho E - |m|^2/2) - p_min rho at u_FV
+            float ufvf[NV][NN], gdtf[NN], pmf[NN], c0f[NN];
         };
     };
     struct {                      // P2b - P5
@@ -275,7 +303,13 @@ struct Sm3 {
         double ell[NIF];             // interface factors (P4 - P5)
         unsigned char ex[NIF];       // R15 exemption (P2b - P4)
     };
-    FT pair[3][NR][NPAIR][NV];       // P1 - P2b: two-point fluxes of every row
+    union {
+        FT pair[3][NR][NPAIR][NV];       // P1 - P2b: two-point fluxes of every row
+        struct {                          // P3 - P4: interface ends whose FP32 certificate
+            unsigned short pend[NIF];     // did not decide (interface id | end << 15), for
+            int npend;                    // the FP64 solve by whole warps
+        };
+    };
     union {
         struct {                     // P0 - P2
             union {
@@ -661,10 +695,11 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const double rhoe = uf[0] * uf[4] - 0.5 * (uf[1] * uf[1] + uf[2] * uf[2] + uf[3] * uf[3]);
         const double pm = A.beta * gm1 * rhoe * idp::fast_rcp(uf[0]);
         S[le].pmin[n] = pm;
-        S[le].c0[n] = gm1 * rhoe - pm * uf[0];
         S[le].im[n] = im;
-        S[le].dtimf[n] = idp::d2f(dt * im);
-        S[le].tolf[n] = idp::d2f(kTol3 * fabs(uf[0]));
+        for (int v = 0; v < NV; ++v) S[le].ufvf[v][n] = idp::d2f(uf[v]);
+        S[le].gdtf[n] = idp::d2f(kGamma3 * dt * im);
+        S[le].pmf[n] = idp::d2f(pm);
+        S[le].c0f[n] = idp::d2f(gm1 * rhoe - pm * uf[0]);
     }
     __syncthreads();
     // ---- P2b: telescoped high-order subcell fluxes per row (summed in FP64),
@@ -699,19 +734,21 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
                 if constexpr (F32) S[le].A[id][v] = idp::f2d(wqf * accf[v] - S[le].fvf[id][v]);
                 else S[le].A[id][v] = wt * acc[v] - S[le].fvf[id][v];
             }
-            // R15 at both ends: decided in FP32 where the two sides differ by more
-            // than 1e-3 (far above the few FP32 roundings), else in FP64
+            // R15 at both ends (dt/m |A| <= 1e-14 |rho_FV|, both sides times Gamma):
+            // decided in FP32 where the two sides differ by more than 1e-3 (far
+            // above the few FP32 roundings), else in FP64
             const double Ar = fabs(S[le].A[id][0]);
             const float af = fabsf(idp::d2f(Ar));
+            constexpr float kTolG = (float)(kTol3 * kGamma3);
             bool exl, exr;
             {
-                const float lf = S[le].dtimf[nl] * af, tf = S[le].tolf[nl];
+                const float lf = S[le].gdtf[nl] * af, tf = kTolG * fabsf(S[le].ufvf[0][nl]);
                 if (lf < 0.999f * tf) exl = true;
                 else if (lf > 1.001f * tf) exl = false;
                 else exl = dt * iml * Ar <= kTol3 * fabs(S[le].ufv[0][nl]);
             }
             {
-                const float lf = S[le].dtimf[nr] * af, tf = S[le].tolf[nr];
+                const float lf = S[le].gdtf[nr] * af, tf = kTolG * fabsf(S[le].ufvf[0][nr]);
                 if (lf < 0.999f * tf) exr = true;
                 else if (lf > 1.001f * tf) exr = false;
                 else exr = dt * imr * Ar <= kTol3 * fabs(S[le].ufv[0][nr]);
@@ -724,6 +761,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     for (int k = tid; k < EPB * NN; k += NT) {
         const int le = k / NN, n = k - le * NN;
         if (e0 + le >= G.K) continue;
+        if (n == 0) S[le].npend = 0;   // the pair fluxes are dead: P4's list takes their storage
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
         const double m = w3[n] * S[le].J;
         double Pp = 0.0, Pm = 0.0;
@@ -751,29 +789,64 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     }
     __syncthreads();
     // ---- P4: interface factors: Zalesak, then the pressure factor of both
-    // ends with Gamma = 6
+    // ends with Gamma = 6, each end searched below the other's result. Pass 1
+    // certifies the ends in FP32 from the per-node FP32 copies; the first end
+    // it leaves undecided goes to its element's list with the factor reached
+    // so far, and pass 2 runs those FP64 solves (R8) by whole warps.
+    // the FP32 certificate of end `side` of interface id at th
+    auto cert_end = [&](const SM &X, int id, int side, const float *af, double th) {
+        const int d = id / (NR * N), r1 = id - d * NR * N, r = r1 / N, a = r1 - r * N;
+        const int nd = node_of<NP>(d, r, side ? a + 1 : a);
+        float u0f[NV], avf[NV];
+        const float sg = side ? X.gdtf[nd] : -X.gdtf[nd];
+        for (int v = 0; v < NV; ++v) { u0f[v] = X.ufvf[v][nd]; avf[v] = sg * af[v]; }
+        return admissible3_f32f(idp::d2f(gm1), u0f, avf, X.pmf[nd], X.c0f[nd], idp::d2f(th));
+    };
+    // the FP64 solve of end `side` of interface id below th
+    auto solve_end = [&](const SM &X, int id, int side, double th) {
+        const int d = id / (NR * N), r1 = id - d * NR * N, r = r1 / N, a = r1 - r * N;
+        const int nd = node_of<NP>(d, r, side ? a + 1 : a);
+        double u0[NV], av[NV];
+        const double sg = (side ? kGamma3 : -kGamma3) * dt * X.im[nd];
+        for (int v = 0; v < NV; ++v) { u0[v] = X.ufv[v][nd]; av[v] = sg * X.A[id][v]; }
+        return theta3(g, u0, av, X.pmin[nd], th);
+    };
     for (int k = tid; k < EPB * NIF; k += NT) {
         const int le = k / NIF, id = k - le * NIF;
         if (e0 + le >= G.K) continue;
-        double l = 1.0;
+        double th = 1.0;
         if (A.limiting > 0) {
             const int d = id / (NR * N), r1 = id - d * NR * N, r = r1 / N, a = r1 - r * N;
             const int nl = node_of<NP>(d, r, a), nr = node_of<NP>(d, r, a + 1);
             const double *Ai = S[le].A[id];
-            const double lr = S[le].ex[id] ? 1.0
-                            : idp::dneg(Ai[0]) ? idp::dmin(S[le].Rp[nl], S[le].Rm[nr]) : idp::dmin(S[le].Rm[nl], S[le].Rp[nr]);
-            const double gl = -kGamma3 * dt * S[le].im[nl], gr = kGamma3 * dt * S[le].im[nr];
-            double u0[NV], av[NV];
-            // each end: certified in FP32 at lr, else the FP64 solve (R8)
-            for (int v = 0; v < NV; ++v) { u0[v] = S[le].ufv[v][nl]; av[v] = gl * Ai[v]; }
-            const double thl = admissible3_f32(gm1, u0, av, S[le].pmin[nl], S[le].c0[nl], lr)
-                             ? lr : theta3(g, u0, av, S[le].pmin[nl], lr);
-            for (int v = 0; v < NV; ++v) { u0[v] = S[le].ufv[v][nr]; av[v] = gr * Ai[v]; }
-            const double thr = admissible3_f32(gm1, u0, av, S[le].pmin[nr], S[le].c0[nr], lr)
-                             ? lr : theta3(g, u0, av, S[le].pmin[nr], lr);
-            l = idp::dmin(thl, thr);
+            th = S[le].ex[id] ? 1.0
+               : idp::dneg(Ai[0]) ? idp::dmin(S[le].Rp[nl], S[le].Rm[nr]) : idp::dmin(S[le].Rm[nl], S[le].Rp[nr]);
+            float af[NV];
+            for (int v = 0; v < NV; ++v) af[v] = idp::d2f(Ai[v]);
+            int pend = -1;
+            for (int side = 0; side < 2 && idp::dpos(th); ++side)
+                if (!cert_end(S[le], id, side, af, th)) { pend = side; break; }
+            if (pend >= 0) S[le].pend[atomicAdd(&S[le].npend, 1)] = (unsigned short)(id | (pend << 15));
         }
-        S[le].ell[id] = l;
+        S[le].ell[id] = th;
+    }
+    __syncthreads();
+    if (A.limiting > 0) {
+        int tot = 0;
+        for (int le = 0; le < EPB; ++le) tot += (e0 + le < G.K) ? S[le].npend : 0;
+        for (int k = tid; k < tot; k += NT) {
+            int le = 0, j = k;
+            while (j >= S[le].npend) { j -= S[le].npend; ++le; }
+            const SM &X = S[le];
+            const int item = X.pend[j], id = item & 0x7fff, side0 = item >> 15;
+            double th = solve_end(X, id, side0, X.ell[id]);
+            if (side0 == 0 && idp::dpos(th)) {
+                float af[NV];
+                for (int v = 0; v < NV; ++v) af[v] = idp::d2f(X.A[id][v]);
+                if (!cert_end(X, id, 1, af, th)) th = solve_end(X, id, 1, th);
+            }
+            S[le].ell[id] = th;
+        }
     }
     __syncthreads();
     // ---- P5: limited update, stage combination, statistics
