@@ -767,15 +767,16 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         double Pp = 0.0, Pm = 0.0;
         for (int d = 0; d < 3; ++d) {
             const int pos = idx[d], row = idx[(d + 1) % 3] + NP * idx[(d + 2) % 3];
+            // the signs on the integer pipe: each inflow adds to one of the two sums
             if (pos > 0) {
                 const int id = (d * NR + row) * N + pos - 1;
                 const double Gv = S[le].A[id][0];
-                if (!S[le].ex[id]) { Pp += Gv > 0 ? Gv : 0.0; Pm += Gv < 0 ? Gv : 0.0; }
+                if (!S[le].ex[id]) { if (idp::dpos(Gv)) Pp += Gv; else if (idp::dneg(Gv)) Pm += Gv; }
             }
             if (pos < N) {
                 const int id = (d * NR + row) * N + pos;
                 const double Gv = -S[le].A[id][0];
-                if (!S[le].ex[id]) { Pp += Gv > 0 ? Gv : 0.0; Pm += Gv < 0 ? Gv : 0.0; }
+                if (!S[le].ex[id]) { if (idp::dpos(Gv)) Pp += Gv; else if (idp::dneg(Gv)) Pm += Gv; }
             }
         }
         const double rf = S[le].ufv[0][n];
