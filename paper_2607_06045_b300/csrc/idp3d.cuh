@@ -993,16 +993,32 @@ __device__ __forceinline__ bool wave_speeds3(double g, const double *u, float *l
 // quotient stays below the FP64 one.
 constexpr double kDtSafe32 = 1.0 - 8e-6;
 
+// per node |v_d| + c of u, lam[d][K (N+1)^3] (the FP64 time step's first
+// pass, so that the time step reads the outside nodes' wave speeds instead
+// of forming them again)
+template <int NP>
+__global__ void __launch_bounds__(256) k_wave3d(Grid3 G, const double *__restrict__ u, double gamma,
+                                                double *__restrict__ lam, unsigned *status) {
+    const size_t KN = (size_t)G.K * NP * NP * NP;
+    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < KN; i += (size_t)gridDim.x * 256) {
+        double uv[NV], l3[3];
+        for (int v = 0; v < NV; ++v) uv[v] = u[v * KN + i];
+        if (!wave_speeds3(gamma, uv, l3)) atomicOr(status, S_BAD_INPUT);
+        for (int d = 0; d < 3; ++d) lam[d * KN + i] = l3[d];
+    }
+}
+
 // IDP time step (Eq. timestep_restriction): per node m_i / sum_j 2 d_ij over
 // its subcell and face neighbours (at a mortar side the slot's sum over its
 // pairs, formed by the mortar flux kernel from the same state); minimum per
 // block, one atomic per block. 2 d_ij of a subcell or conforming pair is
 // w_t1 w_t2 (A_d / 4) max(lambda_i, lambda_j). FT = float: wave speeds, sums
-// and the quotient in FP32 (the FP32 form).
+// and the quotient in FP32 (the FP32 form). lamg (FP64 path): the wave
+// speeds of every node from k_wave3d.
 template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(Launch3<NP, EPB>::threads)
 k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, double gamma,
-       unsigned long long *dtmin, unsigned *status) {
+       unsigned long long *dtmin, unsigned *status, const double *__restrict__ lamg) {
     using E = El3<NP>;
     constexpr bool F32 = sizeof(FT) == 4;
     constexpr int N = E::N, NN = E::NN, NT = Launch3<NP, EPB>::threads;
@@ -1021,6 +1037,10 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
             extents3(G, e, h);
             const double gd[4] = {h[1] * h[2] / 4.0, h[0] * h[2] / 4.0, h[0] * h[1] / 4.0, h[0] * h[1] * h[2] / 8.0};
             for (int c = 0; c < 4; ++c) geo[le][c] = (FT)(F32 ? (double)idp::d2f(gd[c]) : gd[c]);
+        }
+        if (!F32 && lamg) {
+            for (int d = 0; d < 3; ++d) lam[le][d][n] = (FT)lamg[d * KN + (size_t)e * NN + n];
+            continue;
         }
         double uv[NV];
         FT l3[3];
@@ -1052,6 +1072,19 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
                         continue;
                     }
                     double o[NV];
+                    if (!F32 && lamg && (nb >= 0 || G.bc[s] != B_DIRICHLET)) {
+                        // a conforming neighbour's wave speed, or a wall or outflow ghost's (the own one)
+                        if (nb >= 0) {
+                            int jdx[3] = {idx[0], idx[1], idx[2]};
+                            jdx[d] = side ? 0 : N;
+                            lo = (FT)lamg[d * KN + (size_t)nb * NN + (jdx[2] * NP + jdx[1]) * NP + jdx[0]];
+                        } else {
+                            lo = li;
+                        }
+                        if constexpr (F32) lsum += fmaxf(li, lo);
+                        else lsum += idp::dmax(li, lo);
+                        continue;
+                    }
                     if (nb >= 0) {
                         int jdx[3] = {idx[0], idx[1], idx[2]};
                         jdx[d] = side ? 0 : N;

@@ -38,6 +38,7 @@ struct idp3d_ctx {
     signed char *d_lev = nullptr;
     double *d_mslot = nullptr, *d_hand = nullptr, *d_ell = nullptr;
     double *d_buf1 = nullptr, *d_buf2 = nullptr, *d_part = nullptr, *d_tot = nullptr;
+    double *d_lam = nullptr;       // FP64 time step: the nodes' wave speeds [3][K (N+1)^3]
     unsigned long long *d_dtmin = nullptr, *d_dtmin2 = nullptr;
     double *d_t = nullptr, *d_dtlast = nullptr;
     unsigned *d_status = nullptr;
@@ -92,8 +93,8 @@ bool has_mortars(const idp3d_ctx *c) { return c->grid.mort.M > 0; }
 
 // the time-step kernel of the context's precision
 void launch_dt(idp3d_ctx *c, cudaStream_t st, const double *u, unsigned long long *dtmin) {
-    if (c->opt.precision == 1) c->L.dt32(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status);
-    else c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status);
+    if (c->opt.precision == 1) c->L.dt32(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status, nullptr);
+    else c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status, c->d_lam);
 }
 
 // one limited stage: the mortar fluxes of its input (unless already formed),
@@ -420,6 +421,7 @@ idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, co
     }
     if (ok) chk(cudaMalloc(&c->d_buf1, sizeof(double) * NV * kn));
     if (ok) chk(cudaMalloc(&c->d_buf2, sizeof(double) * NV * kn));
+    if (ok && o.precision == 0) chk(cudaMalloc(&c->d_lam, sizeof(double) * 3 * kn));
     if (ok) chk(cudaMalloc(&c->d_part, sizeof(double) * NV * (size_t)G.K));
     if (ok) chk(cudaMalloc(&c->d_tot, sizeof(double) * NV));
     if (ok) chk(cudaMalloc(&c->d_dtmin, sizeof(unsigned long long)));
@@ -602,7 +604,7 @@ void idp3d_destroy(idp3d_ctx *c) {
     void *ptrs[] = {c->d_ops, c->d_buf1, c->d_buf2, c->d_part, c->d_tot, c->d_dtmin, c->d_dtmin2, c->d_t,
                     c->d_dtlast, c->d_status, c->d_stats, c->d_mops, c->d_nbr, c->d_lev, c->d_minfo,
                     c->d_slot_mn, c->d_mn_node, c->d_mn_slot, c->d_mn_cnt, c->d_mbad, c->d_mslot, c->d_hand,
-                    c->d_ell, c->d_lg};
+                    c->d_ell, c->d_lg, c->d_lam};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_in) cudaEventDestroy(c->ev_in);

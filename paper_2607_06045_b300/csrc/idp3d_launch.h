@@ -17,11 +17,11 @@ struct Launchers3 {
     // the element kernel: FP64 path, FP32 form
     void (*element)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) = nullptr;
     void (*element32)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) = nullptr;
-    // the time step: FP64 path, FP32 form
+    // the time step: FP64 path (its wave speeds first, into lam[3][K (N+1)^3]), FP32 form
     void (*dt)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
-               unsigned long long *dtmin, unsigned *status) = nullptr;
+               unsigned long long *dtmin, unsigned *status, double *lam) = nullptr;
     void (*dt32)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
-                 unsigned long long *dtmin, unsigned *status) = nullptr;
+                 unsigned long long *dtmin, unsigned *status, double *lam) = nullptr;
     // the mortar kernels (grid: one block per mortar; apply: its own grid)
     void (*mflux)(cudaStream_t st, const Grid3 &G, const MOps3 *mo, const double *u, double gamma) = nullptr;
     void (*mfactor)(cudaStream_t st, const Grid3 &G, const Stage3 &A) = nullptr;

@@ -36,13 +36,16 @@ void element32(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const
 }
 
 void dt(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
-        unsigned long long *dtmin, unsigned *status) {
-    k_dt3d<NP, EPB, double><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status);
+        unsigned long long *dtmin, unsigned *status, double *lam) {
+    const size_t KN = (size_t)G.K * NP * NP * NP;
+    const size_t wb = (KN + 255) / 256;
+    k_wave3d<NP><<<(unsigned)(wb < 148 * 16 ? wb : 148 * 16), 256, 0, st>>>(G, u, gamma, lam, status);
+    k_dt3d<NP, EPB, double><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status, lam);
 }
 
 void dt32(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
-          unsigned long long *dtmin, unsigned *status) {
-    k_dt3d<NP, EPB, float><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status);
+          unsigned long long *dtmin, unsigned *status, double *) {
+    k_dt3d<NP, EPB, float><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status, nullptr);
 }
 
 void mflux(cudaStream_t st, const Grid3 &G, const MOps3 *mo, const double *u, double gamma) {
