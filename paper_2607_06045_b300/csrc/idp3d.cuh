@@ -782,9 +782,11 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         const double rf = S[le].ufv[0][n];
         const double mdt = m * idt;
         const double Qp = mdt * (S[le].rmax[n] - rf), Qm = mdt * (S[le].rmin[n] - rf);
-        // the quotients only where the bound has room (R < 1)
-        double Rp = (idp::dpos(Pp) && idp::dlt(Qp, Pp)) ? Qp * idp::fast_rcp(Pp) : 1.0;
-        double Rm = (idp::dneg(Pm) && idp::dlt(Pm, Qm)) ? Qm * idp::fast_rcp(Pm) : 1.0;
+        // the quotients only where the bound has some room but less than the
+        // inflow (0 < R < 1); a node on its bound takes R = 0 without one
+        double Rp = 1.0, Rm = 1.0;
+        if (idp::dpos(Pp) && idp::dlt(Qp, Pp)) Rp = idp::dpos(Qp) ? Qp * idp::fast_rcp(Pp) : 0.0;
+        if (idp::dneg(Pm) && idp::dlt(Pm, Qm)) Rm = idp::dneg(Qm) ? Qm * idp::fast_rcp(Pm) : 0.0;
         S[le].Rp[n] = idp::dpos(Rp) ? Rp : 0.0;
         S[le].Rm[n] = idp::dpos(Rm) ? Rm : 0.0;
     }
