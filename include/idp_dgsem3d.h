@@ -91,6 +91,20 @@ idp_status idp3d_layout(const idp3d_ctx *ctx, int64_t *n_elems, int32_t *nodes_p
 /* the number of mortars and of nodes on mortars; either may be NULL */
 idp_status idp3d_mesh_info(const idp3d_ctx *ctx, int64_t *n_mortars, int64_t *n_mortar_nodes);
 
+/* The connectivity idp3d_create_octree builds, on the host only (no device
+ * memory, no CUDA call): the number of mortars and mortar nodes, and, where
+ * the arrays are not NULL, mortar_info[7 M] (per mortar: direction d, large
+ * leaf, 1 if the large leaf is on the low side of the face, the four small
+ * leaves p = p1 + 2 p2 by their offsets along (d+1) mod 3 and (d+2) mod 3)
+ * and nbr[6 n_leaves] (per leaf side -x, +x, -y, +y, -z, +z: the conforming
+ * neighbour, -1 at a boundary, or -2 minus the side's first mortar slot,
+ * slot = mortar * 5 (N+1)^2 + face * (N+1)^2, face 0 the large one).
+ * Call with NULL arrays for the counts first. IDP_E_ARG as for
+ * idp3d_create_octree. */
+idp_status idp3d_octree_tables(const idp3d_grid_desc *base, int64_t n_leaves, const int8_t *level, const int32_t *ix,
+                               const int32_t *iy, const int32_t *iz, int32_t N, int64_t *n_mortars,
+                               int64_t *n_mortar_nodes, int32_t *mortar_info, int32_t *nbr);
+
 /* rhs = the limited residual per unit mass of u for a stage of length dt
  * (dt = 0: the unlimited high-order residual), device arrays in the layout
  * above. Asynchronous on `stream`. */

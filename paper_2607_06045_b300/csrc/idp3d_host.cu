@@ -488,6 +488,24 @@ idp_status idp3d_layout(const idp3d_ctx *c, int64_t *n_elems, int32_t *nodes_per
     return IDP_OK;
 }
 
+idp_status idp3d_octree_tables(const idp3d_grid_desc *base, int64_t n_leaves, const int8_t *level, const int32_t *ix,
+                               const int32_t *iy, const int32_t *iz, int32_t N, int64_t *n_mortars,
+                               int64_t *n_mortar_nodes, int32_t *mortar_info, int32_t *nbr) {
+    if (!base || !level || !ix || !iy || !iz || n_leaves < 1 || n_leaves > (1LL << 24) || N < 1 || N > 4)
+        return IDP_E_ARG;
+    if (base->nx < 1 || base->ny < 1 || base->nz < 1) return IDP_E_ARG;
+    for (int d = 0; d < 3; ++d)
+        if ((base->bc[2 * d] == IDP_BC_PERIODIC) != (base->bc[2 * d + 1] == IDP_BC_PERIODIC)) return IDP_E_ARG;
+    Octree3 T;
+    const idp_status rs = build_octree3(base, n_leaves, level, ix, iy, iz, N + 1, T);
+    if (rs != IDP_OK) return rs;
+    if (n_mortars) *n_mortars = T.M;
+    if (n_mortar_nodes) *n_mortar_nodes = T.MN;
+    if (mortar_info) std::memcpy(mortar_info, T.info.data(), sizeof(int32_t) * T.info.size());
+    if (nbr) std::memcpy(nbr, T.nbr.data(), sizeof(int32_t) * T.nbr.size());
+    return IDP_OK;
+}
+
 idp_status idp3d_mesh_info(const idp3d_ctx *c, int64_t *n_mortars, int64_t *n_mortar_nodes) {
     if (!c) return IDP_E_ARG;
     if (n_mortars) *n_mortars = c->grid.mort.M;

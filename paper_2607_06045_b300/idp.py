@@ -66,6 +66,7 @@ EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", 
 
 
 EXPORTS3 = ["idp3d_options_default", "idp3d_create", "idp3d_create_octree", "idp3d_layout", "idp3d_mesh_info",
+            "idp3d_octree_tables",
             "idp3d_rhs", "idp3d_dt", "idp3d_step", "idp3d_integrals", "idp3d_limiter_stats", "idp3d_destroy"]
 
 
@@ -140,6 +141,8 @@ def lib():
                                           C.POINTER(Options3), C.POINTER(vp)]
         L.idp3d_layout.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.idp3d_mesh_info.argtypes = [vp, i64p, i64p]
+        L.idp3d_octree_tables.argtypes = [C.POINTER(GridDesc3), C.c_int64, i8p, ip, ip, ip, C.c_int32, i64p, i64p, ip,
+                                          ip]
         L.idp3d_rhs.argtypes = [vp, vp, C.c_double, vp, vp]
         L.idp3d_dt.argtypes = [vp, vp, dp, vp]
         L.idp3d_step.argtypes = [vp, vp, C.c_int32, dp, dp, vp]
@@ -540,6 +543,36 @@ def idp_amr_transfer(N, gamma, u_old, kind, src, zs_threshold=1e-10, stream=None
 
 # ---- 3D (include/idp_dgsem3d.h) ----------------------------------------------
 
+def _grid_desc3(mesh) -> GridDesc3:
+    octree = hasattr(mesh, "level")
+    d = GridDesc3()
+    d.nx, d.ny, d.nz = (mesh.nx0, mesh.ny0, mesh.nz0) if octree else (mesh.nx, mesh.ny, mesh.nz)
+    d.x0, d.y0, d.z0, d.x1, d.y1, d.z1 = (float(v) for v in mesh.box)
+    for s in range(6):
+        d.bc[s] = int(mesh.bc[s])
+        for v in range(5):
+            d.bc_prim[s][v] = float(np.asarray(mesh.bc_prim)[s, v])
+    return d
+
+
+def octree_tables3(mesh, N: int):
+    """idp3d_octree_tables on the host (no GPU): (mortar_info [M][7],
+    nbr [K][6], number of mortar nodes) of a workloads.Mesh3-like octree."""
+    d = _grid_desc3(mesh)
+    lev = np.ascontiguousarray(mesh.level, dtype=np.int8)
+    ix, iy, iz = (np.ascontiguousarray(a, dtype=np.int32) for a in (mesh.ix, mesh.iy, mesh.iz))
+    ip, i8 = C.POINTER(C.c_int32), C.POINTER(C.c_int8)
+    args = (C.byref(d), C.c_int64(lev.size), lev.ctypes.data_as(i8), ix.ctypes.data_as(ip), iy.ctypes.data_as(ip),
+            iz.ctypes.data_as(ip), N)
+    M, MN = C.c_int64(), C.c_int64()
+    _check(lib().idp3d_octree_tables(*args, C.byref(M), C.byref(MN), None, None), "idp3d_octree_tables")
+    info = np.zeros((max(M.value, 1), 7), np.int32)
+    nbr = np.zeros((lev.size, 6), np.int32)
+    _check(lib().idp3d_octree_tables(*args, None, None, info.ctypes.data_as(ip), nbr.ctypes.data_as(ip)),
+           "idp3d_octree_tables")
+    return info[:M.value], nbr, MN.value
+
+
 def options3(**kw) -> Options3:
     o = Options3()
     lib().idp3d_options_default(C.byref(o))
@@ -559,13 +592,7 @@ class Context3D:
             opts = options3(**kw)
         self.grid, self.N, self.np, self.gamma, self.opts = grid, N, N + 1, gamma, opts
         octree = hasattr(grid, "level")
-        d = GridDesc3()
-        d.nx, d.ny, d.nz = (grid.nx0, grid.ny0, grid.nz0) if octree else (grid.nx, grid.ny, grid.nz)
-        d.x0, d.y0, d.z0, d.x1, d.y1, d.z1 = (float(v) for v in grid.box)
-        for s in range(6):
-            d.bc[s] = int(grid.bc[s])
-            for v in range(5):
-                d.bc_prim[s][v] = float(np.asarray(grid.bc_prim)[s, v])
+        d = _grid_desc3(grid)
         h = C.c_void_p()
         if octree:
             lev = np.ascontiguousarray(grid.level, dtype=np.int8)

@@ -684,3 +684,64 @@ def extrude_state(u2, e2, N: int):
         out[2, :, k] = src[2][e2]
         out[4, :, k] = src[3][e2]
     return out
+
+
+def random_octree3(nx0, ny0, nz0, box=(0.0, 0.0, 0.0, 1.0, 1.0, 1.0), seed=0, n_refine=6, max_level=2,
+                   bc=(BC_PERIODIC,) * 6):
+    """A seeded 2:1-balanced octree: n_refine times a random leaf below
+    max_level is refined, then leaves are refined until face neighbours
+    (across periodic sides too) differ by at most one level. Kept as a level
+    map over the finest cells, as the 2D meshes."""
+    rng = np.random.default_rng(seed)
+    L = max_level
+    lmap = np.zeros((nx0 << L, ny0 << L, nz0 << L), dtype=np.int16)
+    per = [bc[2 * d] == BC_PERIODIC for d in range(3)]
+
+    def leaves():
+        f = np.indices(lmap.shape).reshape(3, -1)
+        lv = lmap.reshape(-1).astype(np.int64)
+        sh = L - lv
+        anchor = np.all((f & ((1 << sh) - 1)) == 0, axis=0)
+        return lv[anchor], f[:, anchor] >> sh[anchor]
+
+    def refine(l, c):
+        s = L - l
+        x, y, z = (int(v) << s for v in c)
+        lmap[x:x + (1 << s), y:y + (1 << s), z:z + (1 << s)] += 1
+
+    for _ in range(n_refine):
+        lv, c = leaves()
+        cand = np.flatnonzero(lv < max_level)
+        if cand.size == 0:
+            break
+        k = int(rng.choice(cand))
+        refine(int(lv[k]), c[:, k])
+    while True:
+        nbm = np.full(lmap.shape, -1, dtype=np.int32)
+        a = lmap.astype(np.int32)
+        for d in range(3):
+            for sh in (1, -1):
+                if per[d]:
+                    nb = np.roll(a, sh, axis=d)
+                else:
+                    nb = np.full_like(a, -1)
+                    src = [slice(None)] * 3
+                    dst = [slice(None)] * 3
+                    if sh == 1:
+                        dst[d], src[d] = slice(1, None), slice(None, -1)
+                    else:
+                        dst[d], src[d] = slice(None, -1), slice(1, None)
+                    nb[tuple(dst)] = a[tuple(src)]
+                nbm = np.maximum(nbm, nb)
+        need = nbm >= a + 2
+        if not need.any():
+            break
+        lv, c = leaves()
+        for k in range(lv.size):
+            s = L - int(lv[k])
+            x, y, z = (int(v) << s for v in c[:, k])
+            if need[x:x + (1 << s), y:y + (1 << s), z:z + (1 << s)].any():
+                refine(int(lv[k]), c[:, k])
+    lv, c = leaves()
+    return Mesh3(nx0, ny0, nz0, tuple(float(b) for b in box), lv.astype(np.int8), c[0].astype(np.int32),
+                 c[1].astype(np.int32), c[2].astype(np.int32), bc=tuple(bc))

@@ -414,3 +414,32 @@ def test_fp32_form_near_vacuum_blast():
     assert q[0].min() > 0.0 and p.min() > 0.0
     torch.cuda.synchronize()
     ctx.close()
+
+
+@pytest.mark.parametrize("seed,N", [(1, 2), (3, 3), (5, 4)])
+def test_random_octree_rhs_and_steps(seed, N):
+    """Seeded random 2:1 octrees (levels 0..2, level jumps on every face
+    orientation): right-hand sides at 1e-12 and 10 steps at 1e-10."""
+    import torch
+    bc = (o3d.BC_OUTFLOW, o3d.BC_OUTFLOW, o3d.BC_PERIODIC, o3d.BC_PERIODIC, o3d.BC_WALL, o3d.BC_WALL)
+    m = W.random_octree3(2, 3, 2, seed=seed, n_refine=4, max_level=2, bc=bc if seed == 5 else (o3d.BC_PERIODIC,) * 6)
+    u = W.random3_state(m, N, seed=seed, rho_range=(0.5, 2.0), p_range=(0.5, 2.0), vmax=0.5)
+    o = o3d.Oracle3D(m, N)
+    dt_idp = o.dt(u, cfl=1.0)
+    sc = scale(u, dt_idp)
+    for lim in (0, 2):
+        ctx = idp.Context3D(m, N, limiting=lim)
+        dt = 0.0 if lim == 0 else 0.5 * dt_idp
+        e = rel(gpu_rhs(ctx, u, dt), o.rhs(u, dt=dt, limiting=lim), sc)
+        assert e <= 1e-12, (lim, e)
+        ctx.close()
+    u_o, t_o, _, _ = o.step(u, 10, cfl=0.5, limiting=2)
+    ctx = idp.Context3D(m, N, limiting=2, cfl=0.5)
+    ud = dev(u)
+    t = np.zeros(1)
+    rc, _ = ctx.idp3d_step(ud, 10, t)
+    assert rc == idp.IDP_OK
+    torch.cuda.synchronize()
+    sc2 = np.abs(u_o).reshape(5, -1).max(axis=1)
+    assert (np.abs(ud.cpu().numpy() - u_o).reshape(5, -1).max(axis=1) / sc2).max() <= 1e-10
+    ctx.close()
