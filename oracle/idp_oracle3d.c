@@ -31,8 +31,14 @@
  *     Zalesak density limiting and the pressure factor with Gamma = 2d = 6
  *     (Sec. 2.3), and one factor per mortar after the volume correction with
  *     the n_i budget (R9);
+ *   - the combined limiting (limiting 3, Sec. 3.5, Eq.
+ *     combination_posLim_local): per interface and per mortar the factor
+ *     (1 - a) l_positivity + a l_local with a the element's shock indicator
+ *     (the largest of the mortar's five elements), the indicator the
+ *     modal-energy one of the pressure in the tensor-product Legendre basis
+ *     (reading R34);
  *   - the IDP time step (Eq. timestep_restriction) and SSP-RK3.
- * Readings as in idp_oracle.c (R1-R3, R5-R10, R13, R15-R17), with the
+ * Readings as in idp_oracle.c (R1-R3, R5-R10, R13, R15-R17, R20), with the
  * states u = (rho, rho v1, rho v2, rho v3, rho e) and
  * p = (gamma - 1)(rho e - |m|^2 / (2 rho)); the boundary kinds of R4 without
  * the 2D problem-specific ones (periodic, wall, Dirichlet, outflow).
@@ -756,7 +762,92 @@ double o3_dt(const o3_ctx *c, const double *u, double cfl) {
 /* one limited stage (Sec. 2.3 with Gamma = 2d = 6)                          */
 /* ------------------------------------------------------------------------ */
 
-static double g_force3 = -1.0;
+/* ------------------------------------------------------------------------ */
+/* shock indicator of the combined limiting (Sec. 3.5, Eq.                   */
+/* combination_posLim_local) in 3D: Hennemann et al.'s modal-energy indicator */
+/* of the pressure with the tensor-product Legendre modes (reading R34)      */
+/* ------------------------------------------------------------------------ */
+
+/* P_k(x) by the three-term recurrence */
+static double legendre3(int k, double x) {
+    double p0 = 1.0, p1 = x;
+    if (k == 0) return p0;
+    for (int n = 1; n < k; ++n) {
+        double p2 = ((2.0 * n + 1.0) * x * p1 - n * p0) / (n + 1.0);
+        p0 = p1; p1 = p2;
+    }
+    return p1;
+}
+
+/* alpha in [0, 1] from the nodal pressures p[(k np + j) np + i] of one
+   element: the modal coefficients m = (V^-1 x V^-1 x V^-1) p in the
+   orthonormal Legendre tensor basis, V_ik = sqrt((2k+1)/2) P_k(xi_i); e1 the
+   energy of the modes with max(k1, k2, k3) = N, e2 of max = N - 1, e0 the
+   rest; E = max(e1 / (e0 + e1 + e2), e2 / (e0 + e2)); alpha the logistic map
+   1 / (1 + exp(-(s / T)(E - T))), T = 0.5 10^(-1.8 (N+1)^(1/4)),
+   s = ln((1 - 1e-4) / 1e-4), snapped to 0 or 1 within 1e-3 of them. */
+double o3_indicator(int N, const double *xi, const double *p) {
+    int np = N + 1;
+    double V[NP3][NP3], Vi[NP3][NP3];
+    for (int i = 0; i < np; ++i)
+        for (int k = 0; k < np; ++k) { V[i][k] = sqrt((2.0 * k + 1.0) / 2.0) * legendre3(k, xi[i]); Vi[i][k] = i == k; }
+    /* Vi = V^-1 by Gauss-Jordan elimination with partial pivoting */
+    for (int c = 0; c < np; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < np; ++r) if (fabs(V[r][c]) > fabs(V[piv][c])) piv = r;
+        for (int k = 0; k < np; ++k) {
+            double t = V[c][k]; V[c][k] = V[piv][k]; V[piv][k] = t;
+            t = Vi[c][k]; Vi[c][k] = Vi[piv][k]; Vi[piv][k] = t;
+        }
+        double d = V[c][c];
+        for (int k = 0; k < np; ++k) { V[c][k] /= d; Vi[c][k] /= d; }
+        for (int r = 0; r < np; ++r) {
+            if (r == c) continue;
+            double f = V[r][c];
+            for (int k = 0; k < np; ++k) { V[r][k] -= f * V[c][k]; Vi[r][k] -= f * Vi[c][k]; }
+        }
+    }
+    double a[NP3 * NP3 * NP3], b[NP3 * NP3 * NP3];
+    for (int n = 0; n < np * np * np; ++n) a[n] = p[n];
+    /* along x, then y, then z */
+    for (int k = 0; k < np; ++k) for (int j = 0; j < np; ++j) for (int m = 0; m < np; ++m) {
+        double s = 0.0;
+        for (int i = 0; i < np; ++i) s += Vi[m][i] * a[(k * np + j) * np + i];
+        b[(k * np + j) * np + m] = s;
+    }
+    for (int k = 0; k < np; ++k) for (int m = 0; m < np; ++m) for (int i = 0; i < np; ++i) {
+        double s = 0.0;
+        for (int j = 0; j < np; ++j) s += Vi[m][j] * b[(k * np + j) * np + i];
+        a[(k * np + m) * np + i] = s;
+    }
+    for (int m = 0; m < np; ++m) for (int j = 0; j < np; ++j) for (int i = 0; i < np; ++i) {
+        double s = 0.0;
+        for (int k = 0; k < np; ++k) s += Vi[m][k] * a[(k * np + j) * np + i];
+        b[(m * np + j) * np + i] = s;
+    }
+    double e0 = 0.0, e1 = 0.0, e2 = 0.0;
+    for (int k = 0; k < np; ++k) for (int j = 0; j < np; ++j) for (int i = 0; i < np; ++i) {
+        double m2 = b[(k * np + j) * np + i] * b[(k * np + j) * np + i];
+        int top = i > j ? i : j;
+        if (k > top) top = k;
+        if (top == N) e1 += m2;
+        else if (top == N - 1) e2 += m2;
+        else e0 += m2;
+    }
+    double E = 0.0;
+    if (e0 + e1 + e2 > 0.0) E = e1 / (e0 + e1 + e2);
+    if (e0 + e2 > 0.0 && e2 / (e0 + e2) > E) E = e2 / (e0 + e2);
+    double T = 0.5 * pow(10.0, -1.8 * pow(N + 1.0, 0.25));
+    double sh = log((1.0 - 1e-4) / 1e-4);
+    double al = 1.0 / (1.0 + exp(-sh / T * (E - T)));
+    if (al < 1e-3) al = 0.0;
+    if (al > 1.0 - 1e-3) al = 1.0;
+    return al;
+}
+
+static double g_force3 = -1.0, g_force_alpha3 = -1.0;
+/* test hook: every element's indicator replaced by v in [0, 1] (v < 0: off) */
+void o3_set_force_alpha(double v) { g_force_alpha3 = v; }
 /* test hook: every factor replaced by v in [0, 1] (v < 0: off) */
 void o3_set_force_ell(double v) { g_force3 = v; }
 /* test hooks: per node [u_FV (5), rho_min, rho_max, p_min, R+, R-] and per
@@ -817,6 +908,16 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
     /* bounds (R6): bar states of every graph neighbour, the node itself
        included; positivity bounds beta rho_FV, beta p_FV */
     double *rmin = malloc(sizeof(double) * nn), *rmax = malloc(sizeof(double) * nn), *pmin = malloc(sizeof(double) * nn);
+    /* combined limiting (limiting 3): the positivity density bound beside the
+       local ones, and the indicator per element from the stage input */
+    const int comb = limiting == 3;
+    double *rmin2 = malloc(sizeof(double) * nn), *aind = calloc((size_t)K, sizeof(double));
+    if (comb)
+        for (int e = 0; e < K; ++e) {
+            double pe[NP3 * NP3 * NP3], q[NV];
+            for (int n = 0; n < np * np * np; ++n) { get3(c, u, e * np * np * np + n, q); pe[n] = pressure3(gm, q); }
+            aind[e] = g_force_alpha3 >= 0.0 ? g_force_alpha3 : o3_indicator(N, c->xi, pe);
+        }
     ORC_ROW(ROW_BOUNDS);
     for (int i = 0; i < nn; ++i) {
         double ui[NV], q[NV];
@@ -834,6 +935,7 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
         else { rmin[i] = beta * q[0]; rmax[i] = INFINITY; }
         if (q[0] < rmin[i]) rmin[i] = q[0];
         if (q[0] > rmax[i]) rmax[i] = q[0];
+        rmin2[i] = beta * q[0] < q[0] ? beta * q[0] : q[0];
         pmin[i] = beta * pressure3(gm, q);
     }
     /* antidiffusive fluxes A = F_DG - F_FV at the interior subcell
@@ -886,7 +988,7 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
                     exempt[id] = (dt / mass3(c, gl) * Ar <= TOL3 * fabs(ufv[gl])) &&
                                  (dt / mass3(c, gr) * Ar <= TOL3 * fabs(ufv[gr]));
                 }
-    double *Rp = malloc(sizeof(double) * nn), *Rm = malloc(sizeof(double) * nn);
+    double *Rp = malloc(sizeof(double) * nn), *Rm = malloc(sizeof(double) * nn), *Rm2 = malloc(sizeof(double) * nn);
     for (int i = 0; i < nn; ++i) {
         int e = i / (np * np * np), rr = i % (np * np * np);
         int idx[3] = {rr % np, (rr / np) % np, rr / (np * np)};
@@ -908,6 +1010,10 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
         Rm[i] = (Pm < 0.0) ? (Qm / Pm < 1.0 ? Qm / Pm : 1.0) : 1.0;
         if (Rp[i] < 0.0) Rp[i] = 0.0;
         if (Rm[i] < 0.0) Rm[i] = 0.0;
+        /* the positivity bounds alone (no upper density bound: R+ = 1) */
+        double Qm2 = m / dt * (rmin2[i] - rf);
+        Rm2[i] = (Pm < 0.0) ? (Qm2 / Pm < 1.0 ? Qm2 / Pm : 1.0) : 1.0;
+        if (Rm2[i] < 0.0) Rm2[i] = 0.0;
     }
     /* R8 with Gamma = 2d = 6: per interface the largest factor keeping both
        end nodes admissible for the Gamma-scaled single-interface update */
@@ -933,6 +1039,17 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
                     for (int v = 0; v < NV; ++v) { u0[v] = ufv[(size_t)v * nn + gr]; av[v] = Gam * dt / mr * Ai[v]; }
                     double thr = o3_theta(gm, u0, av, pmin[gr], lr);
                     double l = thl < thr ? thl : thr;
+                    if (comb) {
+                        /* the positivity-only factor of the same interface, blended
+                           (Eq. combination_posLim_local) */
+                        double lr2 = exempt[id] ? 1.0 : (-Ai[0] > 0.0) ? Rm2[gr] : Rm2[gl];
+                        for (int v = 0; v < NV; ++v) { u0[v] = ufv[(size_t)v * nn + gl]; av[v] = -Gam * dt / ml * Ai[v]; }
+                        double t2l = o3_theta(gm, u0, av, pmin[gl], lr2);
+                        for (int v = 0; v < NV; ++v) { u0[v] = ufv[(size_t)v * nn + gr]; av[v] = Gam * dt / mr * Ai[v]; }
+                        double t2r = o3_theta(gm, u0, av, pmin[gr], lr2);
+                        double l2 = t2l < t2r ? t2l : t2r;
+                        l = (1.0 - aind[e]) * l2 + aind[e] * l;
+                    }
                     if (g_iface3) {
                         double *o = g_iface3 + (size_t)id * 12;
                         o[0] = gl; o[1] = gr; o[2] = exempt[id]; o[3] = lr; o[4] = thl; o[5] = thr; o[6] = l;
@@ -1002,7 +1119,11 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
                     H[NR + p * NR + t][v] = -(FL2 - Flo[NR + p * NR + t][v]);
                 }
         }
-        double lS = 1.0;
+        double lS = 1.0, lS2 = 1.0, am = 0.0;
+        if (comb) {
+            am = aind[L];
+            for (int p = 0; p < 4; ++p) if (aind[mr[3 + p]] > am) am = aind[mr[3 + p]];
+        }
         if (mbad[m]) {
             /* R16: no admissible high-order flux, pure low order */
             for (int q = 0; q < 5 * NR; ++q) for (int v = 0; v < NV; ++v) H[q][v] = 0.0;
@@ -1019,7 +1140,15 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
             if (lr < 0.0) lr = 0.0;
             double th = o3_theta(gm, u0, av, pmin[i] - TOL3 * fabs(pmin[i]), lr);
             if (th < lS) lS = th;
+            if (comb) {
+                double lr2 = 1.0;
+                if (av[0] < 0.0) { double t = (rmin2[i] - tolr - u0[0]) / av[0]; if (t < lr2) lr2 = t; }
+                if (lr2 < 0.0) lr2 = 0.0;
+                double th2 = o3_theta(gm, u0, av, pmin[i] - TOL3 * fabs(pmin[i]), lr2);
+                if (th2 < lS2) lS2 = th2;
+            }
         }
+        if (comb && !mbad[m]) lS = (1.0 - am) * lS2 + am * lS;
         for (int q = 0; q < 5 * NR && g_mrec3; ++q) {
             int i = gnode[q];
             double ni = (double)c->mcount[i], *o = g_mrec3 + ((size_t)m * 5 * NR + q) * 20;
@@ -1057,7 +1186,8 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
         ORC_ROW(ROW_STATS);
         if (stats) {
             double p = pressure3(gm, q);
-            if (q[0] < rmin[i] - 1e-13 * fabs(rmin[i]) || q[0] > rmax[i] + 1e-13 * fabs(rmax[i])) stats[S3_VRHO] += 1;
+            double lo_ = comb ? rmin2[i] : rmin[i], hi_ = comb ? INFINITY : rmax[i];
+            if (q[0] < lo_ - 1e-13 * fabs(lo_) || q[0] > hi_ + 1e-13 * fabs(hi_)) stats[S3_VRHO] += 1;
             if (p < pmin[i] - 1e-13 * fabs(pmin[i])) stats[S3_VP] += 1;
             if (!(q[0] > 0.0) || !(p > 0.0)) stats[S3_NONPOS] += 1;
             if (q[0] < stats[S3_MINRHO]) stats[S3_MINRHO] = q[0];
@@ -1066,7 +1196,7 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
     }
     free(uvol); free(acc); free(corr); free(sf); free(mbad);
     free(rfv); free(ds); free(ufv); free(rmin); free(rmax); free(pmin); free(A); free(exempt);
-    free(Rp); free(Rm); free(ell); free(lmin);
+    free(Rp); free(Rm); free(ell); free(lmin); free(Rm2); free(rmin2); free(aind);
     return 0;
 }
 

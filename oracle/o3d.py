@@ -57,6 +57,9 @@ def load(path: str):
     L.o3_n_mortars.restype = C.c_int
     L.o3_n_mortars.argtypes = [C.c_void_p]
     L.o3_set_mortar_out.argtypes = [dp, dp]
+    L.o3_indicator.restype = C.c_double
+    L.o3_indicator.argtypes = [C.c_int, dp, dp]
+    L.o3_set_force_alpha.argtypes = [C.c_double]
     L.o3_mortar_table.argtypes = [C.c_void_p, ip]
     L.o3_destroy.argtypes = [C.c_void_p]
     L.o3_n_nodes.restype = C.c_int
@@ -253,3 +256,22 @@ def llf(gamma, uL, uR, d):
     lib().o3_llf(gamma, _d(np.ascontiguousarray(uL, dtype=np.float64)),
                  _d(np.ascontiguousarray(uR, dtype=np.float64)), d, _d(f))
     return f
+
+
+def indicator3(N, p):
+    """The 3D shock indicator alpha in [0, 1] of one element from its nodal
+    pressures p[k][j][i] (the combined limiting's, reading R34)."""
+    xi = np.asarray(oracle_lgl_nodes(N), dtype=np.float64)
+    pp = np.ascontiguousarray(p, dtype=np.float64).reshape(-1)
+    return float(lib().o3_indicator(N, _d(xi), _d(pp)))
+
+
+def oracle_lgl_nodes(N):
+    """The LGL nodes of the 2D oracle's operators (shared by the 3D one)."""
+    import oracle as _o
+    return _o.lgl(N)[0]
+
+
+def set_force_alpha(v):
+    """Every element's shock indicator replaced by v (v < 0: off); test hook."""
+    lib().o3_set_force_alpha(float(v))
