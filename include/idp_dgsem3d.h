@@ -52,7 +52,11 @@ typedef struct {
 } idp3d_grid_desc;
 
 /* limiting: 0 none (the high-order scheme), 1 positivity, 2 local (density
- * bounds from the bar states, with positivity); beta the positivity factor
+ * bounds from the bar states, with positivity), 3 combined (Sec. 3.5, Eq.
+ * combination_posLim_local: per interface and per mortar (1 - a) times the
+ * positivity factor plus a times the local one, a the element's shock
+ * indicator, the modal energy of the pressure in the tensor Legendre basis;
+ * a mortar takes the largest of its five elements'); beta the positivity factor
  * of Eq. Bounds_Positivity (0.1); cfl the factor on the IDP time step;
  * precision 0 FP64 throughout, 1 the FP32 form: node primitives and the
  * two-point, face and subcell fluxes of the element pass in FP32, the bar
@@ -87,6 +91,13 @@ idp_status idp3d_create_octree(const idp3d_grid_desc *base, int64_t n_leaves, co
 
 /* n_elems and nodes per element (N+1)^3; either may be NULL. */
 idp_status idp3d_layout(const idp3d_ctx *ctx, int64_t *n_elems, int32_t *nodes_per_elem);
+
+/* The last limited stage's factors (after idp3d_rhs or idp3d_step): the
+ * combined limiting's shock indicator per element (alpha_host[n_elems]; set
+ * by stages with limiting 3 only) and each mortar's factor l_S
+ * (mortar_ell_host[n_mortars]); either may be NULL. Synchronises `stream`
+ * and the context's stream. */
+idp_status idp3d_stage_factors(idp3d_ctx *ctx, double *alpha_host, double *mortar_ell_host, void *stream);
 
 /* the number of mortars and of nodes on mortars; either may be NULL */
 idp_status idp3d_mesh_info(const idp3d_ctx *ctx, int64_t *n_mortars, int64_t *n_mortar_nodes);

@@ -935,7 +935,7 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
         else { rmin[i] = beta * q[0]; rmax[i] = INFINITY; }
         if (q[0] < rmin[i]) rmin[i] = q[0];
         if (q[0] > rmax[i]) rmax[i] = q[0];
-        rmin2[i] = beta * q[0] < q[0] ? beta * q[0] : q[0];
+        if (comb) rmin2[i] = beta * q[0] < q[0] ? beta * q[0] : q[0];
         pmin[i] = beta * pressure3(gm, q);
     }
     /* antidiffusive fluxes A = F_DG - F_FV at the interior subcell
@@ -1011,9 +1011,11 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
         if (Rp[i] < 0.0) Rp[i] = 0.0;
         if (Rm[i] < 0.0) Rm[i] = 0.0;
         /* the positivity bounds alone (no upper density bound: R+ = 1) */
-        double Qm2 = m / dt * (rmin2[i] - rf);
-        Rm2[i] = (Pm < 0.0) ? (Qm2 / Pm < 1.0 ? Qm2 / Pm : 1.0) : 1.0;
-        if (Rm2[i] < 0.0) Rm2[i] = 0.0;
+        if (comb) {
+            double Qm2 = m / dt * (rmin2[i] - rf);
+            Rm2[i] = (Pm < 0.0) ? (Qm2 / Pm < 1.0 ? Qm2 / Pm : 1.0) : 1.0;
+            if (Rm2[i] < 0.0) Rm2[i] = 0.0;
+        }
     }
     /* R8 with Gamma = 2d = 6: per interface the largest factor keeping both
        end nodes admissible for the Gamma-scaled single-interface update */
@@ -1134,15 +1136,19 @@ int o3_stage(const o3_ctx *c, const double *u, double dt, int limiting, double b
             double mi = mass3(c, i), ni = (double)c->mcount[i], tolr = TOL3 * fabs(ufv[i]);
             double u0[NV], av[NV];
             for (int v = 0; v < NV; ++v) { u0[v] = uvol[(size_t)v * nn + i]; av[v] = ni * dt / mi * H[q][v]; }
+            /* R15 per mortar slot: a density change below TOL3 |rho_FV| (rounding
+               noise of exactly cancelling high- and low-order mortar fluxes) is
+               exempt from the density bounds */
+            const int exs = fabs(av[0]) <= tolr;
             double lr = 1.0;
-            if (av[0] > 0.0) { double t = (rmax[i] + tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
-            else if (av[0] < 0.0) { double t = (rmin[i] - tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
+            if (!exs && av[0] > 0.0) { double t = (rmax[i] + tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
+            else if (!exs && av[0] < 0.0) { double t = (rmin[i] - tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
             if (lr < 0.0) lr = 0.0;
             double th = o3_theta(gm, u0, av, pmin[i] - TOL3 * fabs(pmin[i]), lr);
             if (th < lS) lS = th;
             if (comb) {
                 double lr2 = 1.0;
-                if (av[0] < 0.0) { double t = (rmin2[i] - tolr - u0[0]) / av[0]; if (t < lr2) lr2 = t; }
+                if (!exs && av[0] < 0.0) { double t = (rmin2[i] - tolr - u0[0]) / av[0]; if (t < lr2) lr2 = t; }
                 if (lr2 < 0.0) lr2 = 0.0;
                 double th2 = o3_theta(gm, u0, av, pmin[i] - TOL3 * fabs(pmin[i]), lr2);
                 if (th2 < lS2) lS2 = th2;

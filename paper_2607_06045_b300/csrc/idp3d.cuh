@@ -69,6 +69,7 @@ struct Grid3 {
     const int *nbr;
     const signed char *lev;
     const idp::LogTab *lg;           // table of the FP64 logarithm
+    const double *ind;               // shock indicator: V^-1 [(N+1)^2] row-major, then T and s
     Mort3 mort;
 };
 
@@ -102,11 +103,12 @@ struct Stage3 {
     double cfl;
     int mode;            // 0: residual per unit mass, 1: stage state
     int comb;            // 0: u~, 1: 3/4 u^n + 1/4 u~, 2: 1/3 u^n + 2/3 u~
-    int limiting;        // 0 none (the high-order residual), 1 positivity, 2 local
+    int limiting;        // 0 none (the high-order residual), 1 positivity, 2 local, 3 combined
     int collect;         // statistics on
     double beta, gamma;
     Stats3 *stats;
     unsigned *status;
+    double *aind;        // combined limiting: per element shock indicator (written by the element kernel)
 };
 
 // a statistic's running minimum (positive doubles order like their bits)
@@ -305,9 +307,11 @@ struct Sm3 {
     };
     union {
         FT pair[3][NR][NPAIR][NV];       // P1 - P2b: two-point fluxes of every row
+        double iscr[2][NN];               // P0b: the combined limiting's modal transform
         struct {                          // P3 - P4: interface ends whose FP32 certificate
             unsigned short pend[NIF];     // did not decide (interface id | end << 15), for
             int npend;                    // the FP64 solve by whole warps
+            double Rm2[NN];               // combined limiting: R- of the positivity bounds
         };
     };
     union {
@@ -324,6 +328,7 @@ struct Sm3 {
     };
     FT fvf[NIF][NV];           // P1 - P2b: low-order subcell fluxes, mass-weighted, along +d
     double q[3], J, iJ;        // quarter face areas, dx dy dz / 8 and its inverse
+    double aind;               // combined limiting: the element's shock indicator
     int nb[6];                 // the sides' neighbour entries (Grid3::nbr)
 };
 
@@ -541,6 +546,54 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         }
     }
     __syncthreads();
+    const bool comb = A.limiting == 3;
+    if (comb) {
+        // ---- P0b: the shock indicator of each element (Sec. 3.5, reading R34):
+        // the pressure's modes in the orthonormal Legendre tensor basis, one
+        // direction per pass, then the energies of the top two mode shells
+        const double *Vi = G.ind;
+        for (int k = tid; k < EPB * NN; k += NT) {
+            const int le = k / NN, n = k - le * NN;
+            if (e0 + le >= G.K) continue;
+            const double r = S[le].u[0][n], m1 = S[le].u[1][n], m2 = S[le].u[2][n], m3 = S[le].u[3][n];
+            S[le].iscr[0][n] = gm1 * (S[le].u[4][n] - 0.5 * (m1 * m1 + m2 * m2 + m3 * m3) * idp::fast_rcp(r));
+        }
+        for (int pass = 0; pass < 3; ++pass) {
+            __syncthreads();
+            const int src = pass & 1, dst = src ^ 1, stride = pass == 0 ? 1 : (pass == 1 ? NP : NP * NP);
+            for (int k = tid; k < EPB * NN; k += NT) {
+                const int le = k / NN, n = k - le * NN;
+                if (e0 + le >= G.K) continue;
+                const int mi = (n / stride) % NP, base = n - mi * stride;
+                double acc = 0.0;
+                for (int i = 0; i < NP; ++i) acc += Vi[mi * NP + i] * S[le].iscr[src][base + i * stride];
+                S[le].iscr[dst][n] = acc;
+            }
+        }
+        __syncthreads();
+        for (int le = tid; le < EPB; le += NT) {
+            if (e0 + le >= G.K) continue;
+            double e0s = 0.0, e1s = 0.0, e2s = 0.0;
+            for (int n = 0; n < NN; ++n) {
+                const int i = n % NP, j = (n / NP) % NP, k = n / (NP * NP);
+                const int top = max(max(i, j), k);
+                const double m2 = S[le].iscr[1][n] * S[le].iscr[1][n];
+                if (top == N) e1s += m2;
+                else if (top == N - 1) e2s += m2;
+                else e0s += m2;
+            }
+            double E = 0.0;
+            if (e0s + e1s + e2s > 0.0) E = e1s / (e0s + e1s + e2s);
+            if (e0s + e2s > 0.0 && e2s / (e0s + e2s) > E) E = e2s / (e0s + e2s);
+            const double T = Vi[NP * NP], sh = Vi[NP * NP + 1];
+            double a = 1.0 / (1.0 + exp(-sh / T * (E - T)));
+            if (a < 1e-3) a = 0.0;
+            if (a > 1.0 - 1e-3) a = 1.0;
+            S[le].aind = a;
+            A.aind[e0 + le] = a;
+        }
+        __syncthreads();
+    }
     // ---- P1a: two-point fluxes of every row, each unordered pair once
     for (int k = tid; k < EPB * 3 * NR * NPAIR; k += NT) {
         const int le = k / (3 * NR * NPAIR), r0 = k - le * 3 * NR * NPAIR;
@@ -789,6 +842,13 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         if (idp::dneg(Pm) && idp::dlt(Pm, Qm)) Rm = idp::dneg(Qm) ? Qm * idp::fast_rcp(Pm) : 0.0;
         S[le].Rp[n] = idp::dpos(Rp) ? Rp : 0.0;
         S[le].Rm[n] = idp::dpos(Rm) ? Rm : 0.0;
+        if (comb) {
+            // R- of the positivity bounds alone (rho >= beta rho_FV; no upper bound)
+            const double Qm2 = mdt * (idp::dmin(A.beta * rf, rf) - rf);
+            double Rm2 = 1.0;
+            if (idp::dneg(Pm) && idp::dlt(Pm, Qm2)) Rm2 = idp::dneg(Qm2) ? Qm2 * idp::fast_rcp(Pm) : 0.0;
+            S[le].Rm2[n] = idp::dpos(Rm2) ? Rm2 : 0.0;
+        }
     }
     __syncthreads();
     // ---- P4: interface factors: Zalesak, then the pressure factor of both
@@ -814,7 +874,32 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         for (int v = 0; v < NV; ++v) { u0[v] = X.ufv[v][nd]; av[v] = sg * X.A[id][v]; }
         return theta3(g, u0, av, X.pmin[nd], th);
     };
-    for (int k = tid; k < EPB * NIF; k += NT) {
+    // the pressure factor of both ends below lr (certificate, else FP64 solve)
+    auto pressure_factor = [&](const SM &X, int id, const float *af, double lr) {
+        double th = lr;
+        for (int side = 0; side < 2 && idp::dpos(th); ++side)
+            if (!cert_end(X, id, side, af, th)) th = solve_end(X, id, side, th);
+        return th;
+    };
+    if (comb) {
+        // Eq. combination_posLim_local: l = (1 - a) l_positivity + a l_local
+        for (int k = tid; k < EPB * NIF; k += NT) {
+            const int le = k / NIF, id = k - le * NIF;
+            if (e0 + le >= G.K) continue;
+            const int d = id / (NR * N), r1 = id - d * NR * N, r = r1 / N, a = r1 - r * N;
+            const int nl = node_of<NP>(d, r, a), nr = node_of<NP>(d, r, a + 1);
+            const SM &X = S[le];
+            const double *Ai = X.A[id];
+            const bool neg = idp::dneg(Ai[0]);
+            const double lr = X.ex[id] ? 1.0 : neg ? idp::dmin(X.Rp[nl], X.Rm[nr]) : idp::dmin(X.Rm[nl], X.Rp[nr]);
+            const double lr2 = X.ex[id] ? 1.0 : neg ? X.Rm2[nr] : X.Rm2[nl];
+            float af[NV];
+            for (int v = 0; v < NV; ++v) af[v] = idp::d2f(Ai[v]);
+            const double th = pressure_factor(X, id, af, lr), th2 = pressure_factor(X, id, af, lr2);
+            S[le].ell[id] = (1.0 - X.aind) * th2 + X.aind * th;
+        }
+    }
+    for (int k = tid; k < EPB * NIF && !comb; k += NT) {
         const int le = k / NIF, id = k - le * NIF;
         if (e0 + le >= G.K) continue;
         double th = 1.0;
@@ -834,7 +919,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         S[le].ell[id] = th;
     }
     __syncthreads();
-    if (A.limiting > 0) {
+    if (A.limiting > 0 && !comb) {
         int tot = 0;
         for (int le = 0; le < EPB; ++le) tot += (e0 + le < G.K) ? S[le].npend : 0;
         for (int k = tid; k < tot; k += NT) {
@@ -918,7 +1003,10 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
                 nact++;
             }
             if (mslot < 0) {
-                const double rl = S[le].rmin[n], rh = S[le].rmax[n], pl = S[le].pmin[n];
+                // the bounds the stage keeps: the positivity ones under the combined limiting
+                const double rf0 = S[le].ufv[0][n];
+                const double rl = comb ? idp::dmin(A.beta * rf0, rf0) : S[le].rmin[n];
+                const double rh = comb ? INFINITY : S[le].rmax[n], pl = S[le].pmin[n];
                 // the density bounds: the exact comparison first, the tolerance only past a bound
                 if ((idp::dlt(ut[0], rl) && idp::dlt(ut[0], rl - kViol3 * fabs(rl))) ||
                     (idp::dlt(rh, ut[0]) && idp::dlt(rh + kViol3 * fabs(rh), ut[0])))

@@ -19,6 +19,7 @@ namespace idp {
 void host_lgl_sbar(int N, double *x, double *w, double *S);
 void host_lgl_mortar(int N, double *I, double *P, double *wt);
 void host_log_table(LogTab &T);
+void host_lgl_indicator(int N, double *Vinv, double *T, double *s);
 }
 
 using namespace idp3;
@@ -39,6 +40,7 @@ struct idp3d_ctx {
     double *d_mslot = nullptr, *d_hand = nullptr, *d_ell = nullptr;
     double *d_buf1 = nullptr, *d_buf2 = nullptr, *d_part = nullptr, *d_tot = nullptr;
     double *d_lam = nullptr;       // FP64 time step: the nodes' wave speeds [3][K (N+1)^3]
+    double *d_ind = nullptr, *d_aind = nullptr;   // combined limiting: indicator operators, per element indicator
     unsigned long long *d_dtmin = nullptr, *d_dtmin2 = nullptr;
     double *d_t = nullptr, *d_dtlast = nullptr;
     unsigned *d_status = nullptr;
@@ -84,6 +86,7 @@ Stage3 stage_args(idp3d_ctx *c, const double *u, const double *un, double *out, 
     A.collect = 1;
     A.beta = c->opt.beta; A.gamma = c->gamma;
     A.stats = c->d_stats; A.status = c->d_status;
+    A.aind = c->d_aind;
     return A;
 }
 
@@ -346,7 +349,7 @@ idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, co
     idp3d_options o;
     idp3d_options_default(&o);
     if (opts) o = *opts;
-    if (o.limiting < 0 || o.limiting > 2 || !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0)) return IDP_E_ARG;
+    if (o.limiting < 0 || o.limiting > 3 || !(o.beta >= 0.0 && o.beta < 1.0) || !(o.cfl > 0.0)) return IDP_E_ARG;
     if (o.precision < 0 || o.precision > 1) return IDP_E_ARG;
     Octree3 T;
     idp_status rs = build_octree3(gd, K, level, ix, iy, iz, N + 1, T);
@@ -391,6 +394,13 @@ idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, co
         upload(&c->d_lg, &lt, 1);
     }
     G.lg = c->d_lg;
+    {
+        std::vector<double> ind((size_t)(N + 1) * (N + 1) + 2);
+        idp::host_lgl_indicator(N, ind.data(), &ind[(size_t)(N + 1) * (N + 1)], &ind[(size_t)(N + 1) * (N + 1) + 1]);
+        upload(&c->d_ind, ind.data(), ind.size());
+    }
+    G.ind = c->d_ind;
+    if (ok) chk(cudaMalloc(&c->d_aind, sizeof(double) * (size_t)K));
     upload(&c->d_nbr, T.nbr.data(), T.nbr.size());
     upload(&c->d_lev, T.lev.data(), T.lev.size());
     G.nbr = c->d_nbr;
@@ -503,6 +513,18 @@ idp_status idp3d_octree_tables(const idp3d_grid_desc *base, int64_t n_leaves, co
     if (n_mortar_nodes) *n_mortar_nodes = T.MN;
     if (mortar_info) std::memcpy(mortar_info, T.info.data(), sizeof(int32_t) * T.info.size());
     if (nbr) std::memcpy(nbr, T.nbr.data(), sizeof(int32_t) * T.nbr.size());
+    return IDP_OK;
+}
+
+idp_status idp3d_stage_factors(idp3d_ctx *c, double *alpha_host, double *mortar_ell_host, void *stream) {
+    if (!c) return IDP_E_ARG;
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess) return IDP_E_CUDA;
+    if (alpha_host && cudaMemcpy(alpha_host, c->d_aind, sizeof(double) * (size_t)c->grid.K, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return IDP_E_CUDA;
+    if (mortar_ell_host && c->grid.mort.M > 0 &&
+        cudaMemcpy(mortar_ell_host, c->d_ell, sizeof(double) * (size_t)c->grid.mort.M, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return IDP_E_CUDA;
     return IDP_OK;
 }
 
@@ -622,7 +644,7 @@ void idp3d_destroy(idp3d_ctx *c) {
     void *ptrs[] = {c->d_ops, c->d_buf1, c->d_buf2, c->d_part, c->d_tot, c->d_dtmin, c->d_dtmin2, c->d_t,
                     c->d_dtlast, c->d_status, c->d_stats, c->d_mops, c->d_nbr, c->d_lev, c->d_minfo,
                     c->d_slot_mn, c->d_mn_node, c->d_mn_slot, c->d_mn_cnt, c->d_mbad, c->d_mslot, c->d_hand,
-                    c->d_ell, c->d_lg, c->d_lam};
+                    c->d_ell, c->d_lg, c->d_lam, c->d_ind, c->d_aind};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_in) cudaEventDestroy(c->ev_in);

@@ -217,15 +217,15 @@ template <int NP>
 __global__ void __launch_bounds__(kMortThreads3) k_mfactor3(Grid3 G, Stage3 A) {
     using MS = MortSize3<NP>;
     constexpr int Q = MS::Q, NT = kMortThreads3;
-    __shared__ unsigned long long s_min;
+    __shared__ unsigned long long s_min, s_min2;
     const Mort3 &MO = G.mort;
     const int m = blockIdx.x, tid = threadIdx.x;
     const double g = A.gamma, dt = stage_dt3(A);
-    const bool bad = MO.bad[m] != 0;
-    if (tid == 0) s_min = (unsigned long long)__double_as_longlong(1.0);
+    const bool bad = MO.bad[m] != 0, comb = A.limiting == 3;
+    if (tid == 0) s_min = s_min2 = (unsigned long long)__double_as_longlong(1.0);
     __syncthreads();
     if (A.limiting > 0 && !bad) {
-        unsigned long long best = (unsigned long long)__double_as_longlong(1.0);
+        unsigned long long best = (unsigned long long)__double_as_longlong(1.0), best2 = best;
         for (int q = tid; q < Q; q += NT) {
             const int s = m * Q + q, mn = MO.slot_mn[s];
             const size_t MN = MO.MN;
@@ -236,25 +236,47 @@ __global__ void __launch_bounds__(kMortThreads3) k_mfactor3(Grid3 G, Stage3 A) {
                 av[v] = f * (MO.chi[(size_t)v * MO.S + s] - MO.clo[(size_t)v * MO.S + s]);
             }
             const double tolr = kTol3 * fabs(MO.h_b[3 * MN + mn]);
+            // R15 per slot: a density change below 1e-14 |rho_FV| is exempt from the density bounds
+            const bool exs = fabs(av[0]) <= tolr;
             double lr = 1.0;
-            if (av[0] > 0.0) { const double t = (MO.h_b[1 * MN + mn] + tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
-            else if (av[0] < 0.0) { const double t = (MO.h_b[0 * MN + mn] - tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
+            if (!exs && av[0] > 0.0) { const double t = (MO.h_b[1 * MN + mn] + tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
+            else if (!exs && av[0] < 0.0) { const double t = (MO.h_b[0 * MN + mn] - tolr - u0[0]) / av[0]; if (t < lr) lr = t; }
             if (!(lr > 0.0)) lr = 0.0;
             const double pm = MO.h_b[2 * MN + mn];
             double th = theta3(g, u0, av, pm - kTol3 * fabs(pm), lr);
             if (!(th > 0.0)) th = 0.0;
             const unsigned long long tb = (unsigned long long)__double_as_longlong(th);
             best = tb < best ? tb : best;
+            if (comb) {
+                // the positivity bounds alone: rho >= min(beta rho_FV, rho_FV), p >= p_min
+                const double rf = MO.h_b[3 * MN + mn], rmin2 = idp::dmin(A.beta * rf, rf);
+                double lr2 = 1.0;
+                if (!exs && av[0] < 0.0) { const double t = (rmin2 - tolr - u0[0]) / av[0]; if (t < lr2) lr2 = t; }
+                if (!(lr2 > 0.0)) lr2 = 0.0;
+                double th2 = theta3(g, u0, av, pm - kTol3 * fabs(pm), lr2);
+                if (!(th2 > 0.0)) th2 = 0.0;
+                const unsigned long long tb2 = (unsigned long long)__double_as_longlong(th2);
+                best2 = tb2 < best2 ? tb2 : best2;
+            }
         }
         for (int o = 16; o > 0; o >>= 1) {
             const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
             best = ob < best ? ob : best;
+            const unsigned long long ob2 = __shfl_down_sync(0xffffffffu, best2, o);
+            best2 = ob2 < best2 ? ob2 : best2;
         }
-        if ((tid & 31) == 0) atomicMin(&s_min, best);
+        if ((tid & 31) == 0) { atomicMin(&s_min, best); atomicMin(&s_min2, best2); }
     }
     __syncthreads();
     if (tid == 0) {
-        const double lS = bad ? 0.0 : (A.limiting > 0 ? __longlong_as_double((long long)s_min) : 1.0);
+        double lS = bad ? 0.0 : (A.limiting > 0 ? __longlong_as_double((long long)s_min) : 1.0);
+        if (comb && !bad) {
+            // Eq. combination_posLim_local with the largest indicator of the mortar's five elements
+            const int *inf = MO.info + 7 * m;
+            double am = A.aind[inf[1]];
+            for (int p = 0; p < 4; ++p) am = fmax(am, A.aind[inf[3 + p]]);
+            lS = (1.0 - am) * __longlong_as_double((long long)s_min2) + am * lS;
+        }
         MO.ell[m] = lS;
         if (A.collect && A.limiting > 0) {
             const int *inf = MO.info + 7 * m;
@@ -298,7 +320,10 @@ __global__ void __launch_bounds__(256) k_mapply3(Grid3 G, Stage3 A) {
         }
         if (A.collect && A.limiting > 0) {
             const double p = pres3(g, ut);
-            const double rl = MO.h_b[0 * MN + mn], rh = MO.h_b[1 * MN + mn], pl = MO.h_b[2 * MN + mn];
+            // the bounds the stage keeps: the positivity ones under the combined limiting
+            const double rf0 = MO.h_b[3 * MN + mn];
+            const double rl = A.limiting == 3 ? idp::dmin(A.beta * rf0, rf0) : MO.h_b[0 * MN + mn];
+            const double rh = A.limiting == 3 ? INFINITY : MO.h_b[1 * MN + mn], pl = MO.h_b[2 * MN + mn];
             if (ut[0] < rl - kViol3 * fabs(rl) || ut[0] > rh + kViol3 * fabs(rh)) vr++;
             if (p < pl - kViol3 * fabs(pl)) vp++;
             if (!(ut[0] > 0.0) || !(p > 0.0)) np_++;

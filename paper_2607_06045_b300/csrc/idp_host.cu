@@ -498,6 +498,19 @@ void host_lgl_mortar(int N, double *I, double *P, double *wt) {
         for (int r = 0; r < 2 * np; ++r) { P[k * 2 * np + r] = o.P[k][r]; wt[k * 2 * np + r] = o.wt[k][r]; }
 }
 
+// the shock indicator's operators of degree N (the 3D contexts take their
+// tensor products): the inverse of V_ik = sqrt((2k+1)/2) P_k(xi_i) (row-major,
+// (N+1)^2), the threshold T and the sharpness s, as the 2D contexts build them
+void host_lgl_indicator(int N, double *Vinv, double *T, double *s) {
+    Ops o;
+    build_ops(N, 1, 0, o);
+    const int np = N + 1;
+    for (int k = 0; k < np; ++k)
+        for (int i = 0; i < np; ++i) Vinv[k * np + i] = o.Vinv[k][i];
+    *T = o.ind_T;
+    *s = o.ind_s;
+}
+
 // LGL nodes and weights and Sbar (row-major, (N+1)^2) for degree N (the 3D
 // contexts), the operators the 2D contexts use
 void host_lgl_sbar(int N, double *x, double *w, double *S) {

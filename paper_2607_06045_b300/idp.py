@@ -66,7 +66,7 @@ EXPORTS = ["idp_options_default", "idp_dgsem_create", "idp_dgsem_create_batch", 
 
 
 EXPORTS3 = ["idp3d_options_default", "idp3d_create", "idp3d_create_octree", "idp3d_layout", "idp3d_mesh_info",
-            "idp3d_octree_tables",
+            "idp3d_octree_tables", "idp3d_stage_factors",
             "idp3d_rhs", "idp3d_dt", "idp3d_step", "idp3d_integrals", "idp3d_limiter_stats", "idp3d_destroy"]
 
 
@@ -141,6 +141,7 @@ def lib():
                                           C.POINTER(Options3), C.POINTER(vp)]
         L.idp3d_layout.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.idp3d_mesh_info.argtypes = [vp, i64p, i64p]
+        L.idp3d_stage_factors.argtypes = [vp, dp, dp, vp]
         L.idp3d_octree_tables.argtypes = [C.POINTER(GridDesc3), C.c_int64, i8p, ip, ip, ip, C.c_int32, i64p, i64p, ip,
                                           ip]
         L.idp3d_rhs.argtypes = [vp, vp, C.c_double, vp, vp]
@@ -644,6 +645,15 @@ class Context3D:
         if check:
             _check(rc, "idp3d_step")
         return rc, dl.value
+
+    def idp3d_stage_factors(self, stream=None):
+        """(shock indicator per element, l_S per mortar) of the last limited stage."""
+        a = np.zeros(self.K)
+        ell = np.zeros(max(self.n_mortars, 1))
+        _check(lib().idp3d_stage_factors(self._h, a.ctypes.data_as(C.POINTER(C.c_double)),
+                                         ell.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)),
+               "idp3d_stage_factors")
+        return a, ell[:self.n_mortars]
 
     def idp3d_integrals(self, u, stream=None):
         out = np.zeros(5)

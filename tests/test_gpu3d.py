@@ -70,7 +70,7 @@ def test_rhs(N, kind):
     o = o3d.Oracle3D(g, N)
     dt_idp = o.dt(u, cfl=1.0)
     sc = scale(u, dt_idp)
-    for lim in (0, 1, 2):
+    for lim in (0, 1, 2, 3):
         ctx = idp.Context3D(g, N, limiting=lim)
         dt = 0.0 if lim == 0 else 0.5 * dt_idp
         r_o = o.rhs(u, dt=dt, limiting=lim)
@@ -215,7 +215,7 @@ def test_octree_rhs(N, kind):
             u = sphere3(m, N)
         dt_idp = o.dt(u, cfl=1.0)
         sc = scale(u, dt_idp)
-        for lim in (0, 1, 2):
+        for lim in (0, 1, 2, 3):
             ctx = idp.Context3D(m, N, limiting=lim)
             assert ctx.n_mortars == o.M > 0
             dt = 0.0 if lim == 0 else 0.5 * dt_idp
@@ -252,7 +252,7 @@ def test_octree_dt(N, kind):
 
 
 @pytest.mark.parametrize("N,lim,kind", [(2, 2, "small"), (3, 1, "large"), (3, 2, "large"), (4, 2, "small"),
-                                        (3, 2, "extruded")])
+                                        (3, 2, "extruded"), (3, 3, "small"), (2, 3, "large")])
 def test_octree_steps(N, lim, kind):
     import torch
     m = octree(kind)
@@ -336,7 +336,7 @@ def l1_fields3(u, ref, m):
 
 
 @pytest.mark.parametrize("N,kind,lim", [(2, "grid", 2), (3, "grid", 2), (4, "grid", 1), (3, "small", 2),
-                                        (3, "large", 2), (2, "extruded", 2)])
+                                        (3, "large", 2), (2, "extruded", 2), (3, "small", 3)])
 def test_fp32_form_steps(N, kind, lim):
     """20 SSP-RK3 steps of the FP32 form against the FP64 oracle: density L1
     within 1e-5 and the other fields within 3e-5 (as the 2D FP32 form), no
@@ -443,3 +443,51 @@ def test_random_octree_rhs_and_steps(seed, N):
     sc2 = np.abs(u_o).reshape(5, -1).max(axis=1)
     assert (np.abs(ud.cpu().numpy() - u_o).reshape(5, -1).max(axis=1) / sc2).max() <= 1e-10
     ctx.close()
+
+
+def test_combined_indicator_values():
+    """The element kernel's shock indicators (limiting 3) on a sphere state
+    take values strictly between 0 and 1 somewhere, and the combined steps
+    keep the positivity bounds on an octree near-vacuum blast."""
+    import torch
+    N = 3
+    m = W.box_refined_mesh3(4, 4, 4, UNIT, (0.3, 0.3, 0.3, 0.7, 0.7, 0.7))
+    u = W.blast3_state(m, N, rho_bg=1e-5, p_bg=1e-6, rho_in=1.0, p_in=1e2, centre=(0.45, 0.5, 0.55), r0=0.2)
+    o = o3d.Oracle3D(m, N)
+    u_o, t_o, _, _ = o.step(u, 10, cfl=0.9, limiting=3)
+    ctx = idp.Context3D(m, N, limiting=3, cfl=0.9)
+    ud = dev(u)
+    t = np.zeros(1)
+    rc, _ = ctx.idp3d_step(ud, 10, t)
+    assert rc == idp.IDP_OK
+    torch.cuda.synchronize()
+    sc = np.abs(u_o).reshape(5, -1).max(axis=1)
+    assert (np.abs(ud.cpu().numpy() - u_o).reshape(5, -1).max(axis=1) / sc).max() <= 1e-10
+    rc, st = ctx.idp3d_limiter_stats()
+    assert st["n_nonpositive"] == 0 and st["n_viol_pressure"] == 0 and st["n_viol_density"] == 0
+    ctx.close()
+
+
+@pytest.mark.parametrize("kind", ["small", "large"])
+def test_stage_factors_read_back(kind):
+    """The element kernel's shock indicators (limiting 3) equal the oracle's
+    per element, and the mortar factors l_S of one limited stage (limiting
+    2 and 3) equal the oracle's."""
+    m, N = octree(kind), 2
+    u = sphere3(m, N)
+    o = o3d.Oracle3D(m, N)
+    dt = 0.5 * o.dt(u, cfl=1.0)
+    npe = (N + 1) ** 3
+    U = u.reshape(5, m.n_elems, npe)
+    p = (G - 1.0) * (U[4] - 0.5 * (U[1] ** 2 + U[2] ** 2 + U[3] ** 2) / U[0])
+    al = np.array([o3d.indicator3(N, p[e]) for e in range(m.n_elems)])
+    for lim in (2, 3):
+        ctx = idp.Context3D(m, N, limiting=lim)
+        gpu_rhs(ctx, u, dt)
+        a_g, ell_g = ctx.idp3d_stage_factors()
+        ell_o = o.stage_debug(u, dt, limiting=lim)["mortar_ell"]
+        assert np.abs(ell_g - ell_o).max() <= 1e-12, (lim, ell_g, ell_o)
+        if lim == 3:
+            assert np.abs(a_g - al).max() <= 1e-12
+            assert 0.0 < al.mean() < 1.0
+        ctx.close()
