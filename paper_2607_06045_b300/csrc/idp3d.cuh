@@ -168,44 +168,14 @@ __device__ __forceinline__ double theta3(double g, const double *u0, const doubl
 }
 
 // Certifies in FP32 that theta = h is admissible for u0 + theta a (rho > 0 and
-// g(h) = (gamma-1)(rho E - |m|^2/2) - pmin rho >= 0 in exact arithmetic),
-// given c0 = g(0) formed in FP64: every FP32 product and sum below stays
-// within 20 unit roundings (2^-24) of the sum S of the absolute terms, so
-// g_f32 > 4e-6 S (67 unit roundings) implies g(h) > 0 with a threefold
-// margin, and the same holds for the density. h rounded to FP32 moves g by
-// less than 2 unit roundings of S. Returns false when it cannot decide (near
-// the bound, or magnitudes outside the FP32 range); the FP64 solve then runs.
-__device__ __forceinline__ bool admissible3_f32(double gm1, const double *u0, const double *a, double pmin, double c0,
-                                                double h) {
-    if (!(c0 > 0.0) || !(u0[0] > 0.0) || !(h > 0.0)) return false;
-    float r0 = idp::d2f(u0[0]), E0 = idp::d2f(u0[4]), ar = idp::d2f(a[0]), aE = idp::d2f(a[4]);
-    float gm = idp::d2f(gm1), pm = idp::d2f(pmin), hf = idp::d2f(h);
-    float t1 = r0 * aE, t2 = ar * E0, t5 = pm * ar;
-    float tm = 0.0f, sm = 0.0f, q2 = 0.0f;
-    for (int c = 1; c <= 3; ++c) {
-        const float mc = idp::d2f(u0[c]), ac = idp::d2f(a[c]);
-        const float t = mc * ac;
-        tm += t;
-        sm += fabsf(t);
-        q2 += ac * ac;
-    }
-    float c1 = gm * (t1 + t2 - tm) - t5;
-    float s1 = gm * (fabsf(t1) + fabsf(t2) + sm) + fabsf(t5);
-    float q1 = ar * aE;
-    float c2 = gm * (q1 - 0.5f * q2);
-    float s2 = gm * (fabsf(q1) + 0.5f * q2);
-    float c0f = idp::d2f(c0);
-    float S = fabsf(c0f) + hf * (s1 + hf * s2);
-    if (!(S > 1e-30f) || !(S < 1e30f)) return false;
-    float gh = c0f + hf * (c1 + hf * c2);
-    if (!(gh > 4e-6f * S)) return false;
-    float rh = r0 + hf * ar;
-    return rh > 4e-6f * (r0 + hf * fabsf(ar));
-}
-
-// The same certificate from FP32 inputs that carry at most three roundings
-// each (u_FV rounded once, a = Gamma dt/m A from two rounded factors): every
-// product and sum below then stays within 20 unit roundings of S, as above.
+// g(h) = (gamma-1)(rho E - |m|^2/2) - pmin rho >= 0 in exact arithmetic) from
+// FP32 inputs that carry at most three roundings each (u_FV rounded once,
+// a = Gamma dt/m A from two rounded factors, c0 = g(0) formed in FP64 and
+// rounded): every FP32 product and sum below stays within 20 unit roundings
+// (2^-24) of the sum S of the absolute terms, so g_f32 > 4e-6 S (67 unit
+// roundings) implies g(h) > 0 with a threefold margin, and the same holds for
+// the density. Returns false when it cannot decide (near the bound, or
+// magnitudes outside the FP32 range); the FP64 solve then runs.
 __device__ __forceinline__ bool admissible3_f32f(float gm, const float *u0, const float *a, float pm, float c0f,
                                                  float hf) {
     if (!(c0f > 0.0f) || !(u0[0] > 0.0f) || !(hf > 0.0f)) return false;
