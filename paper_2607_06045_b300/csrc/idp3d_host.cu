@@ -401,6 +401,7 @@ idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, co
     }
     G.ind = c->d_ind;
     if (ok) chk(cudaMalloc(&c->d_aind, sizeof(double) * (size_t)K));
+    if (ok) chk(cudaMemset(c->d_aind, 0, sizeof(double) * (size_t)K));
     upload(&c->d_nbr, T.nbr.data(), T.nbr.size());
     upload(&c->d_lev, T.lev.data(), T.lev.size());
     G.nbr = c->d_nbr;
