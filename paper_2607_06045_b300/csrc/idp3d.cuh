@@ -227,9 +227,12 @@ __device__ __forceinline__ int node_of(int d, int r, int a) {
     return (idx[2] * NP + idx[1]) * NP + idx[0];
 }
 
-// per-node flux data of the element kernel: in the FP64 path v1, v2, v3, p,
-// ln rho, ln beta, beta = rho / p and |v_d| + c; in the FP32 form the state
-// rounded to FP32, v1, v2, v3, p, beta and |v_d| + c in FP32
+// per-node flux data of the element kernel: in the FP64 path v1/2, v2/2,
+// v3/2, p/2, ln rho, ln beta', beta' = (gamma - 1) rho / p = rho / (rho e) and
+// |v_d| + c (the halves and beta' are exact or rounding-level rescalings that
+// fold the means' factors 1/2 and the 1/(gamma - 1) of the two-point flux into
+// the node data); in the FP32 form the state rounded to FP32, v1, v2, v3, p,
+// beta = rho / p and |v_d| + c in FP32
 template <int NP, bool F32>
 struct Node3 {
     static constexpr int NN = NP * NP * NP;
@@ -390,6 +393,16 @@ __device__ __forceinline__ void log_means3(double ra, double rb, double lra, dou
     }
 }
 
+// half the physical flux along d (the mass flux m_d whole) from the state,
+// half its velocity along d and half its pressure (the FP64 node data)
+__device__ __forceinline__ void flux_h(const double *u, double hv, double hp, int d, double *f) {
+    f[0] = u[1 + d];
+    f[1] = u[1] * hv + (d == 0 ? hp : 0.0);
+    f[2] = u[2] * hv + (d == 1 ? hp : 0.0);
+    f[3] = u[3] * hv + (d == 2 ? hp : 0.0);
+    f[4] = (u[4] + 2.0 * hp) * hv;
+}
+
 // physical flux along d from the state and its velocity along d and pressure
 template <typename T>
 __device__ __forceinline__ void flux_p(const T *u, T vd, T p, int d, T *f) {
@@ -429,7 +442,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
     if (F32)
         for (int k = tid; k < NP * NP; k += NT) Sf[k / NP][k % NP] = idp::d2f(ops_g->S[k / NP][k % NP]);
     const size_t KN = (size_t)G.K * NN;
-    const double g = A.gamma, gm1 = g - 1.0, igm1 = 1.0 / gm1;
+    const double g = A.gamma, gm1 = g - 1.0, igm1 = 1.0 / gm1, hgm1 = 0.5 * gm1, g2 = 2.0 * g;
     const double dt = stage_dt3(A), idt = 1.0 / dt;
     const int e0 = blockIdx.x * EPB;
     const Mort3 &MO = G.mort;
@@ -463,22 +476,24 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             nd.pr[4][n] = uf[0] * __frcp_rn(pf);
             for (int d = 0; d < 3; ++d) nd.lam[d][n] = fabsf(vf[d]) + c;
         } else {
-            const double ir = idp::fast_rcp(uv[0]);
-            const double v1 = uv[1] * ir, v2 = uv[2] * ir, v3 = uv[3] * ir;
-            const double p = gm1 * (uv[4] - 0.5 * (uv[1] * v1 + uv[2] * v2 + uv[3] * v3));
-            nd.pr[0][n] = v1; nd.pr[1][n] = v2; nd.pr[2][n] = v3; nd.pr[3][n] = p;
-            if (!(uv[0] > 0.0) || !(p > 0.0)) {
+            // halves of v and p; rho e = E - |m|^2 / 2 rho = p / (gamma - 1)
+            const double ir = idp::fast_rcp(uv[0]), hir = 0.5 * ir;
+            const double h1 = uv[1] * hir, h2 = uv[2] * hir, h3 = uv[3] * hir;
+            const double re = uv[4] - (uv[1] * h1 + uv[2] * h2 + uv[3] * h3);
+            const double hp = hgm1 * re;
+            nd.pr[0][n] = h1; nd.pr[1][n] = h2; nd.pr[2][n] = h3; nd.pr[3][n] = hp;
+            if (!(uv[0] > 0.0) || !(re > 0.0)) {
                 atomicOr(A.status, S_BAD_INPUT);
                 nd.pr[4][n] = 0.0; nd.pr[5][n] = 0.0; nd.pr[6][n] = 1.0;
                 for (int d = 0; d < 3; ++d) nd.lam[d][n] = 0.0;
                 continue;
             }
-            const double c = idp::fast_sqrt(g * p * ir);
-            const double bet = uv[0] * idp::fast_rcp(p);
+            const double c = idp::fast_sqrt(g2 * hp * ir);
+            const double bet = uv[0] * idp::fast_rcp(re);
             nd.pr[4][n] = idp::fast_log(uv[0], G.lg);
             nd.pr[5][n] = idp::fast_log(bet, G.lg);
             nd.pr[6][n] = bet;
-            nd.lam[0][n] = fabs(v1) + c; nd.lam[1][n] = fabs(v2) + c; nd.lam[2][n] = fabs(v3) + c;
+            nd.lam[0][n] = 2.0 * fabs(h1) + c; nd.lam[1][n] = 2.0 * fabs(h2) + c; nd.lam[2][n] = 2.0 * fabs(h3) + c;
         }
     }
     for (int k = tid; k < EPB * 6 * NR; k += NT) {
@@ -507,12 +522,14 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             S[le].outp[s][t][1] = pf;
             S[le].outp[s][t][2] = ok ? fabsf(vf[d]) + sqrtf(idp::d2f(g) * pf * irf) : 0.0f;
         } else {
-            const double ir = idp::fast_rcp(o[0]);
-            const double vd = o[1 + d] * ir;
-            const double po = gm1 * (o[4] - 0.5 * (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) * ir);
-            S[le].outp[s][t][0] = vd;
-            S[le].outp[s][t][1] = po;
-            S[le].outp[s][t][2] = (o[0] > 0.0 && po > 0.0) ? fabs(vd) + idp::fast_sqrt(g * po * ir) : 0.0;
+            // halves of v_d and p, as the node data
+            const double ir = idp::fast_rcp(o[0]), hir = 0.5 * ir;
+            const double hvd = o[1 + d] * hir;
+            const double re = o[4] - (o[1] * o[1] + o[2] * o[2] + o[3] * o[3]) * hir;
+            const double hpo = hgm1 * re;
+            S[le].outp[s][t][0] = hvd;
+            S[le].outp[s][t][1] = hpo;
+            S[le].outp[s][t][2] = (o[0] > 0.0 && re > 0.0) ? 2.0 * fabs(hvd) + idp::fast_sqrt(g2 * hpo * ir) : 0.0;
         }
     }
     __syncthreads();
@@ -588,13 +605,23 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         FT va[3], vb[3];
         for (int cc = 0; cc < 3; ++cc) { va[cc] = X.nd.pr[cc][na]; vb[cc] = X.nd.pr[cc][nb]; }
         // R1 (Ranocha) along d
-        const FT h = FT(0.5);
-        const FT vdot = va[0] * vb[0] + va[1] * vb[1] + va[2] * vb[2];
-        const FT fr = rho_ln * h * (va[d] + vb[d]);
         FT f[NV];
-        f[0] = fr;
-        for (int cc = 0; cc < 3; ++cc) f[1 + cc] = fr * h * (va[cc] + vb[cc]) + (cc == d ? h * (pa + pb) : FT(0));
-        f[4] = fr * (h * vdot + iba * igm) + h * (pa * vb[d] + pb * va[d]);
+        if constexpr (F32) {
+            const FT h = FT(0.5);
+            const FT vdot = va[0] * vb[0] + va[1] * vb[1] + va[2] * vb[2];
+            const FT fr = rho_ln * h * (va[d] + vb[d]);
+            f[0] = fr;
+            for (int cc = 0; cc < 3; ++cc) f[1 + cc] = fr * h * (va[cc] + vb[cc]) + (cc == d ? h * (pa + pb) : FT(0));
+            f[4] = fr * (h * vdot + iba * igm) + h * (pa * vb[d] + pb * va[d]);
+        } else {
+            // halves of v and p: the means are sums; iba is already 1 / ((gamma - 1) beta_ln)
+            (void)igm;
+            const double hdot = va[0] * vb[0] + va[1] * vb[1] + va[2] * vb[2];
+            const double fr = rho_ln * (va[d] + vb[d]);
+            f[0] = fr;
+            for (int cc = 0; cc < 3; ++cc) f[1 + cc] = fr * (va[cc] + vb[cc]) + (cc == d ? pa + pb : 0.0);
+            f[4] = fr * (2.0 * hdot + iba) + 2.0 * (pa * vb[d] + pb * va[d]);
+        }
         for (int v = 0; v < NV; ++v) S[le].pair[d][r][pp][v] = f[v];
     }
     // ---- P1b: LLF faces (mass-weighted, along +d) and their bar-state densities
@@ -624,16 +651,25 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             if constexpr (F32) { ui[v] = X.nd.uf[v][nin]; uo[v] = idp::d2f(X.outs[s][t][v]); }
             else { ui[v] = X.u[v][nin]; uo[v] = X.outs[s][t][v]; }
         }
-        flux_p<FT>(ui, X.nd.pr[d][nin], X.nd.pr[3][nin], d, fi);
-        flux_p<FT>(uo, X.outp[s][t][0], X.outp[s][t][1], d, fo);
         FT lam;
-        if constexpr (F32) lam = fmaxf(X.nd.lam[d][nin], X.outp[s][t][2]);
-        else lam = idp::dmax(X.nd.lam[d][nin], X.outp[s][t][2]);
+        if constexpr (F32) {
+            flux_p<FT>(ui, X.nd.pr[d][nin], X.nd.pr[3][nin], d, fi);
+            flux_p<FT>(uo, X.outp[s][t][0], X.outp[s][t][1], d, fo);
+            lam = fmaxf(X.nd.lam[d][nin], X.outp[s][t][2]);
+        } else {
+            // half fluxes (the mass flux whole) from the halves of v_d and p
+            flux_h(ui, X.nd.pr[d][nin], X.nd.pr[3][nin], d, fi);
+            flux_h(uo, X.outp[s][t][0], X.outp[s][t][1], d, fo);
+            lam = idp::dmax(X.nd.lam[d][nin], X.outp[s][t][2]);
+        }
         const FT cwf = (FT)(F32 ? (double)idp::d2f(cw) : cw);
         // left state first: the outside is on the left of a low face
         const FT *uL = side ? ui : uo, *uR = side ? uo : ui, *fL = side ? fi : fo, *fR = side ? fo : fi;
-        for (int v = 0; v < NV; ++v)
-            S[le].ff[s][t][v] = to_d3(cwf * (FT(0.5) * (fL[v] + fR[v]) - FT(0.5) * lam * (uR[v] - uL[v])));
+        const FT hl = FT(0.5) * lam;
+        for (int v = 0; v < NV; ++v) {
+            const FT fm = (F32 || v == 0) ? FT(0.5) * (fL[v] + fR[v]) : fL[v] + fR[v];
+            S[le].ff[s][t][v] = to_d3(cwf * (fm - hl * (uR[v] - uL[v])));
+        }
         // ubar = (u_i + u_o)/2 - c.(f_o - f_i)/(2 |c| lambda), c along the outward normal
         double fb;
         if constexpr (F32) {
@@ -658,14 +694,22 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             if constexpr (F32) { ul[v] = X.nd.uf[v][nl]; ur[v] = X.nd.uf[v][nr]; }
             else { ul[v] = X.u[v][nl]; ur[v] = X.u[v][nr]; }
         }
-        flux_p<FT>(ul, X.nd.pr[d][nl], X.nd.pr[3][nl], d, fl);
-        flux_p<FT>(ur, X.nd.pr[d][nr], X.nd.pr[3][nr], d, fr);
         FT lam;
-        if constexpr (F32) lam = fmaxf(X.nd.lam[d][nl], X.nd.lam[d][nr]);
-        else lam = idp::dmax(X.nd.lam[d][nl], X.nd.lam[d][nr]);
-        const double ccd = ops.w[r % NP] * ops.w[r / NP] * X.q[d] / 2.0;
+        if constexpr (F32) {
+            flux_p<FT>(ul, X.nd.pr[d][nl], X.nd.pr[3][nl], d, fl);
+            flux_p<FT>(ur, X.nd.pr[d][nr], X.nd.pr[3][nr], d, fr);
+            lam = fmaxf(X.nd.lam[d][nl], X.nd.lam[d][nr]);
+        } else {
+            flux_h(ul, X.nd.pr[d][nl], X.nd.pr[3][nl], d, fl);
+            flux_h(ur, X.nd.pr[d][nr], X.nd.pr[3][nr], d, fr);
+            lam = idp::dmax(X.nd.lam[d][nl], X.nd.lam[d][nr]);
+        }
+        const double cc2d = ops.w[r % NP] * ops.w[r / NP] * X.q[d], ccd = 0.5 * cc2d;
         const FT cc = (FT)(F32 ? (double)idp::d2f(ccd) : ccd);
-        for (int v = 0; v < NV; ++v) S[le].fvf[id][v] = cc * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
+        // FP64 path: half fluxes for v >= 1, so 2 cc multiplies their sum
+        const FT cc2 = (FT)(F32 ? 0.0 : cc2d);
+        for (int v = 0; v < NV; ++v)
+            S[le].fvf[id][v] = ((F32 || v == 0) ? cc : cc2) * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
         if constexpr (F32) S[le].ibar[id] = idp::f2d(0.5f * (ul[0] + ur[0]) - 0.5f * (ur[1 + d] - ul[1 + d]) * __frcp_rn(lam));
         else S[le].ibar[id] = 0.5 * (ul[0] + ur[0]) - 0.5 * (ur[1 + d] - ul[1 + d]) * idp::fast_rcp(lam);
     }
