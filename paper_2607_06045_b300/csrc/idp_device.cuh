@@ -289,6 +289,50 @@ __device__ __forceinline__ Prim<FT> make_prim(const Gas &G, double r, double m1,
     return q;
 }
 
+// Node data of the FP64 element pass in halves: v1/2, v2/2 and p/2 (the
+// same bits as make_prim's v1, v2, p scaled by 1/2, which is exact) and
+// beta' = rho / (rho e) = (gamma - 1) rho / p with ln beta' (a rescaling of
+// beta at rounding level; the logarithmic mean's quotient is homogeneous of
+// degree -1 in beta, so 1/{beta'}_ln = 1/((gamma - 1) {beta}_ln)). The
+// two-point flux's means become sums of halves and its factor 1/(gamma - 1)
+// sits in beta'; c is make_prim's.
+__device__ __forceinline__ Prim<double> make_prim_half(const Gas &G, double r, double m1, double m2, double E) {
+    Prim<double> q;
+    const double ri = fast_rcp(r), hri = 0.5 * ri;
+    const double h1 = __dmul_rn(m1, hri), h2 = __dmul_rn(m2, hri);
+    const double re = __dadd_rn(E, -__dadd_rn(__dmul_rn(m1, h1), __dmul_rn(m2, h2)));   // rho e
+    const double hp = __dmul_rn(0.5 * G.gm1, re);
+    q.rho = r; q.v1 = h1; q.v2 = h2; q.p = hp; q.E = E;
+    q.c = fast_sqrt(__dmul_rn(__dmul_rn(2.0 * G.g, hp), ri));
+    q.beta = __dmul_rn(r, fast_rcp(re));
+    q.lr = fast_log(r, G.lg);
+    q.lb = q.lr - fast_log(re, G.lg);
+    return q;
+}
+
+// Half the physical flux along d (the mass flux m_d whole) from half the
+// normal velocity and half the pressure.
+__device__ __forceinline__ void phys_flux_half(double m1, double m2, double E, double hp, double hvn, int d,
+                                               double f[4]) {
+    f[0] = (d == 0 ? m1 : m2);
+    f[1] = m1 * hvn + (d == 0 ? hp : 0.0);
+    f[2] = m2 * hvn + (d == 1 ? hp : 0.0);
+    f[3] = (E + 2.0 * hp) * hvn;
+}
+
+// Ranocha's flux (R1) from the halved node data of make_prim_half.
+__device__ __forceinline__ void ranocha_half(const Prim<double> &a, const Prim<double> &b, int d, double f[4]) {
+    double rho_ln, ibeta;
+    log_means<double>(a, b, rho_ln, ibeta);
+    const double v1m = a.v1 + b.v1, v2m = a.v2 + b.v2, pm = a.p + b.p;
+    const double vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
+    const double fr = rho_ln * (d == 0 ? v1m : v2m);
+    f[0] = fr;
+    f[1] = fr * v1m + (d == 0 ? pm : 0.0);
+    f[2] = fr * v2m + (d == 1 ? pm : 0.0);
+    f[3] = fr * (2.0 * (a.v1 * b.v1 + a.v2 * b.v2) + ibeta) + 2.0 * (a.p * vnb + b.p * vna);
+}
+
 // FP32 primitives of the FP32 form. When E - |m|^2/2rho keeps at least an
 // eighth of E the pressure is formed in FP32: with the state rounded once,
 // the kinetic energy carries at most 4 unit roundings and E one half, so the

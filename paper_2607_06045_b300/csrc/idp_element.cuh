@@ -282,8 +282,10 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
     constexpr int NN = NP * NP, N = NP - 1, NPAIR = SM::NPAIR, NIF = SM::NIF;
     constexpr int NT = ElemLaunch<NP, EPB>::threads;
     constexpr bool F32 = sizeof(FT) == 4;
-    // FP64 default kernel: conforming faces come from k_face
+    // FP64 default kernel: conforming faces come from k_face, and the node
+    // data holds halves of v and p and beta' (make_prim_half)
     constexpr bool FACEBUF = !F32 && !EXT;
+    constexpr bool HALF = !F32 && !EXT;
     extern __shared__ __align__(16) unsigned char smraw[];
     SM *sm = reinterpret_cast<SM *>(smraw);
     // reference tables: w, 1/w, Sbar, w_i w_j, 1/(w_i w_j) and FP32 copies
@@ -334,6 +336,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 q = make_prim_f32(G, r, m1, m2, E, true, m1f, m2f);
                 S.uf[0][n] = q.rho; S.uf[1][n] = m1f; S.uf[2][n] = m2f; S.uf[3][n] = q.E;
                 okp = q.p > 0.0f;
+            } else if constexpr (HALF) {
+                q = make_prim_half(G, r, m1, m2, E);
+                okp = dpos(q.p);
             } else {
                 q = make_prim<FT>(G, r, m1, m2, E, true);
                 okp = dpos(q.p);
@@ -398,7 +403,8 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             PairTab<NP>::ab(pi, a, b);
             Prim<FT> pa = load_prim<NP, FT, EXT>(S, nodeid<NP>(d, r, a)), pb = load_prim<NP, FT, EXT>(S, nodeid<NP>(d, r, b));
             FT f[4];
-            if (EXT && A.vflux == 1) chandrashekar<FT>(pa, pb, d, ginv1, f);
+            if constexpr (HALF) ranocha_half(pa, pb, d, f);
+            else if (EXT && A.vflux == 1) chandrashekar<FT>(pa, pb, d, ginv1, f);
             else ranocha<FT>(pa, pb, d, ginv1, f);
             for (int v = 0; v < 4; ++v) S.pair[d][r][pi][v] = f[v];
         }
@@ -449,6 +455,7 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
             int d = s >> 1, n = face_node<NP>(s, t);
             const double *out = S.outs[s][t];
             Prim<FT> pi = load_prim<NP, FT, EXT>(S, n);
+            if constexpr (HALF) { pi.v1 *= 2.0; pi.v2 *= 2.0; pi.p *= 2.0; }   // make_prim's values
             FT f[4], lam;
             double i2l;
             // left/bottom state first, so that both elements of a face form
@@ -529,7 +536,9 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 int na = nodeid<NP>(d, r, a), nb = nodeid<NP>(d, r, a + 1);
                 Prim<FT> pa = load_prim<NP, FT, EXT>(S, na), pb = load_prim<NP, FT, EXT>(S, nb);
                 FT vna = d == 0 ? pa.v1 : pa.v2, vnb = d == 0 ? pb.v1 : pb.v2;
-                FT la = fabs(vna) + pa.c, lb = fabs(vnb) + pb.c;
+                // (FP64 default kernel: halves of v_n, so |v_n| = 2 |v_n / 2|)
+                const FT vs = HALF ? FT(2) : FT(1);
+                FT la = vs * fabs(vna) + pa.c, lb = vs * fabs(vnb) + pb.c;
                 FT lam = speed_max(la, lb);
                 FT ua[4], ub[4];
                 for (int v = 0; v < 4; ++v) {
@@ -537,13 +546,22 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                     else { ua[v] = S.u[v][na]; ub[v] = S.u[v][nb]; }
                 }
                 FT fa[4], fb[4];
-                phys_flux<FT>(ua[1], ua[2], ua[3], pa.p, vna, d, fa);
-                phys_flux<FT>(ub[1], ub[2], ub[3], pb.p, vnb, d, fb);
-                FT cc;
-                if constexpr (F32) cc = s_wf[r] * (d == 0 ? S.qyf : S.qxf);
-                else cc = s_w[r] * (d == 0 ? S.qy : S.qx);
+                FT cc, cc2;
+                if constexpr (HALF) {
+                    // half fluxes (the mass flux whole): 2 cc = w_r |face| / 2 multiplies their sums
+                    phys_flux_half(ua[1], ua[2], ua[3], pa.p, vna, d, fa);
+                    phys_flux_half(ub[1], ub[2], ub[3], pb.p, vnb, d, fb);
+                    cc = s_w[r] * (d == 0 ? S.qy : S.qx);
+                    cc2 = s_w[r] * (d == 0 ? S.hy : S.hx);
+                } else {
+                    phys_flux<FT>(ua[1], ua[2], ua[3], pa.p, vna, d, fa);
+                    phys_flux<FT>(ub[1], ub[2], ub[3], pb.p, vnb, d, fb);
+                    if constexpr (F32) cc = s_wf[r] * (d == 0 ? S.qyf : S.qxf);
+                    else cc = s_w[r] * (d == 0 ? S.qy : S.qx);
+                    cc2 = cc;
+                }
                 for (int v = 0; v < 4; ++v) {
-                    FT fv = cc * (fa[v] + fb[v]) - cc * lam * (ub[v] - ua[v]);
+                    FT fv = (v == 0 ? cc : cc2) * (fa[v] + fb[v]) - cc * lam * (ub[v] - ua[v]);
                     if constexpr (F32) S.Ffv[id][v] = fv;
                     else S.Fv[id][v] = fv;
                 }
