@@ -257,7 +257,10 @@ enum {
     IDP_K_MORTAR_LOB = 8,   /* low-order bounds across mortars (bounds 1) */
     IDP_K_FACE = 9,         /* conforming-face fluxes of the FP64 element pass (part of it) */
     IDP_K_DT_SPEED = 10,    /* wave speeds of every node for the time step (no face buffer) */
-    IDP_NKERNELS = 11
+    IDP_K_DT_FILTER = 11,   /* FP64 path with the face buffer: the time step's FP32 pass,
+                               which picks the elements whose quotients IDP_K_DT forms
+                               in FP64 */
+    IDP_NKERNELS = 12
 };
 
 /* Measurement support (the paper has no counterpart). mode 1: each step's

@@ -583,6 +583,7 @@ struct idp_ctx {
     int facebuf = 0;           // FP64 default kernel: conforming faces from k_face
     double *d_fbuf = nullptr;  // k_face output: [6][2 K (N+1)] doubles + [2 K (N+1)] floats
     void *d_lam = nullptr;     // wave speeds of every node for the time step (no face buffer)
+    unsigned *d_emin = nullptr;   // with the face buffer: per element, the FP32 pass's time-step minimum
     // adaptation on the device (single-mesh contexts): the leaves' level and
     // indices, the level-0 grid, the transfer's operators, the buffer sizes
     // in elements and mortars, and a scratch area that only grows
@@ -732,7 +733,7 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux, 
     int k;
     if (reset) {
         k = kt_begin(c, st, IDP_K_DT_INIT);
-        k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
+        k_dt_init<<<(2 * c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
         kt_end(c, st, k);
     }
     // the mortar fluxes of u^n beside the face or wave-speed kernel; the time
@@ -766,15 +767,30 @@ void enqueue_dt(idp_ctx *c, cudaStream_t st, const double *u, bool mortar_flux, 
         kt_end(c, st, k);
     }
     if (fork) cudaStreamWaitEvent(st, c->ev_join, 0);   // the mortars' 2d sums
-    k = kt_begin(c, st, IDP_K_DT);
-    c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, make_gas(c->gamma, &c->d_ops->lg), c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
-            c->d_status, faces ? c->d_fbuf : nullptr, lam);
-    kt_end(c, st, k);
+    const Gas gas = make_gas(c->gamma, &c->d_ops->lg);
+    if (faces && c->d_emin) {
+        // FP64 path: the FP32 pass over every node, then the FP64 quotients
+        // of the elements within its margin (the same minimum as one FP64
+        // pass over every node)
+        k = kt_begin(c, st, IDP_K_DT_FILTER);
+        c->L.dt(0, g, st, c->mesh, c->slots, u, gas, c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin, c->d_status,
+                c->d_fbuf, nullptr, 1, c->d_emin);
+        kt_end(c, st, k);
+        k = kt_begin(c, st, IDP_K_DT);
+        c->L.dt(0, g, st, c->mesh, c->slots, u, gas, c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin, c->d_status,
+                c->d_fbuf, nullptr, 2, c->d_emin);
+        kt_end(c, st, k);
+    } else {
+        k = kt_begin(c, st, IDP_K_DT);
+        c->L.dt(c->opt.precision, g, st, c->mesh, c->slots, u, gas, c->opt.dt_rule, c->d_ops, c->d_tsim, c->d_dtmin,
+                c->d_status, faces ? c->d_fbuf : nullptr, lam, 0, nullptr);
+        kt_end(c, st, k);
+    }
 }
 
 // one SSP-RK3 step on u (in place), using the ctx stage buffers
 static void dt_restore(idp_ctx *c, cudaStream_t st) {
-    k_dt_init<<<(c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
+    k_dt_init<<<(2 * c->n_sims + 255) / 256, 256, 0, st>>>(c->d_dtmin, c->n_sims);
 }
 
 void enqueue_step(idp_ctx *c, cudaStream_t st, double *u) {
@@ -1056,10 +1072,12 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     const size_t kn = KN(c);
     if (ok) chk(cudaMalloc(&c->d_buf1, sizeof(double) * 4 * kn));
     if (ok) chk(cudaMalloc(&c->d_buf2, sizeof(double) * 4 * kn));
-    if (ok) chk(cudaMalloc(&c->d_dtmin, sizeof(unsigned long long) * n_sims));
+    // the time-step minimum per simulation, then the FP32 pass's minimum of
+    // the two-pass time step (k_dt)
+    if (ok) chk(cudaMalloc(&c->d_dtmin, sizeof(unsigned long long) * 2 * n_sims));
     if (ok) {
-        const std::vector<unsigned long long> inf(n_sims, 0x7FF0000000000000ull);   // +inf: no step formed yet
-        chk(cudaMemcpy(c->d_dtmin, inf.data(), sizeof(unsigned long long) * n_sims, cudaMemcpyHostToDevice));
+        const std::vector<unsigned long long> inf(2 * n_sims, 0x7FF0000000000000ull);   // +inf: no step formed yet
+        chk(cudaMemcpy(c->d_dtmin, inf.data(), sizeof(unsigned long long) * 2 * n_sims, cudaMemcpyHostToDevice));
     }
     if (ok) chk(cudaMalloc(&c->d_tsim, sizeof(double) * n_sims));
     if (ok) chk(cudaMalloc(&c->d_dtlast, sizeof(double) * n_sims));
@@ -1075,6 +1093,7 @@ idp_status create_impl(const idp_mesh_desc *meshes, int n_sims, int N, double ga
     }
     if (ok && (!c->facebuf || o.dt_rule != 0))
         chk(cudaMalloc(&c->d_lam, (o.precision ? sizeof(float) : sizeof(double)) * 2 * kn));
+    if (ok && c->facebuf && o.dt_rule == 0) chk(cudaMalloc(&c->d_emin, sizeof(unsigned) * (size_t)c->K));
     if (ok && c->lob) chk(cudaMalloc(&c->d_lofv, sizeof(double) * 2 * kn));
     if (ok && c->lob) chk(cudaMemset(c->d_lofv, 0, sizeof(double) * 2 * kn));
     if (ok) chk(cudaMalloc(&c->d_intout, sizeof(double) * 4 * n_sims));
@@ -1729,6 +1748,7 @@ idp_status idp_dgsem_adapt(idp_ctx *c, const double *u_old, const idp_amr_params
             c->d_lam = nullptr;
             chk(cudaMalloc(&c->d_lam, (c->opt.precision ? sizeof(float) : sizeof(double)) * 2 * (size_t)nK * NN));
         }
+        if (c->d_emin) chk(ensure(&c->d_emin, nK, 0));
         if (c->d_lofv) chk(ensure(&c->d_lofv, 2 * nK * NN, 0));
         if (c->d_hostbuf) { cudaFree(c->d_hostbuf); c->d_hostbuf = nullptr; }
         if (ce != cudaSuccess) { note(ce, "adapt alloc"); return IDP_E_CUDA; }
@@ -1875,7 +1895,7 @@ void idp_dgsem_destroy(idp_ctx *c) {
     if (!c) return;
     if (c->stream) cudaStreamSynchronize(c->stream);
     if (c->graph) cudaGraphExecDestroy(c->graph);
-    void *ptrs[] = {c->d_lev, c->d_ix, c->d_iy, c->d_ops_amr, c->d_rm, c->d_fbuf, c->d_lam, c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
+    void *ptrs[] = {c->d_lev, c->d_ix, c->d_iy, c->d_ops_amr, c->d_rm, c->d_fbuf, c->d_lam, c->d_emin, c->d_lofv, c->d_aind, c->d_ops, c->d_geom, c->d_geoc, c->d_sim, c->d_mlarge, c->d_minfo, c->d_mnnode, c->d_fnbr, c->d_ftype,
                     c->d_mbnode, c->d_mbfor, c->d_mbforeign,
                     c->d_msmall, c->d_mnslot, c->d_siminfo, c->d_slot_block, c->d_buf1, c->d_buf2, c->d_hostbuf,
                     c->d_dtmin, c->d_tsim, c->d_dtlast, c->d_status, c->d_stats, c->d_part, c->d_intout, c->d_off};

@@ -32,10 +32,13 @@ struct Launchers {
     void (*mortar_limit)(int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const StageArgs &a);
     int mortar_w;
     // time step; lam (when not null): the wave speeds of every node,
-    // 2 K (N+1)^2 values in the flux type, written by dt_speed first
+    // 2 K (N+1)^2 values in the flux type, written by dt_speed first; filt
+    // 1 and 2: the two passes of the FP64 path's time step with the face
+    // buffer (k_dt's DtFilter; emin: one value per element; dtmin: 2 n_sims
+    // entries)
     void (*dt)(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u,
                const Gas &gas, int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin,
-               unsigned *status, const double *fbuf, const void *lam);
+               unsigned *status, const double *fbuf, const void *lam, int filt, unsigned *emin);
     void (*dt_speed)(int fp32, cudaStream_t st, const MeshDev &m, const double *u, const Gas &gas,
                      unsigned *status, void *lam, int num_sms);
     void (*integrals)(int grid, cudaStream_t st, const MeshDev &m, const double *u, const Ops *ops, double *part);

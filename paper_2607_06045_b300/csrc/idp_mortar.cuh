@@ -512,11 +512,27 @@ __global__ void __launch_bounds__(256) k_dt_speed(MeshDev mesh, const double *__
     }
 }
 
+// The FP64 path's time step in two passes. The first (FT = float, mode 1)
+// forms every node's quotient in FP32 from the FP32 primitives and the face
+// buffer's wave speeds and writes each element's minimum (emin) and, into
+// its own dtmin array, each simulation's minimum; its quotients are within
+// a relative 1e-5 of the FP64 ones (the FP32 form's scaling margin is 4e-6).
+// The second (FT = double, mode 2) forms the FP64 quotients only in the
+// elements whose FP32 minimum is within a relative 1e-4 of their
+// simulation's, which hold the FP64 minimiser, so its minimum is the one-pass
+// FP64 minimum bit for bit.
+struct DtFilter {
+    int mode;                          // 0: one pass; 1: FP32 pass; 2: FP64 pass over the candidates
+    unsigned *emin;                    // per element: the FP32 pass's minimum (bits of a positive float)
+    const unsigned long long *smin;    // mode 2: per simulation, the FP32 pass's minimum (bits of a double)
+};
+constexpr double kDtFilterMargin = 1e-4;
+
 template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(ElemLaunch<NP, EPB>::threads)
 k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule, const Ops *ops,
      const double *t_sim, unsigned long long *dtmin, unsigned *status, const double *__restrict__ fbuf,
-     const FT *__restrict__ lam) {
+     const FT *__restrict__ lam, DtFilter flt) {
     constexpr int NN = NP * NP, N = NP - 1, NT = ElemLaunch<NP, EPB>::threads;
     constexpr bool F32 = sizeof(FT) == 4;
     __shared__ FT s_l[EPB][2][NN];       // |v_x| + c, |v_y| + c per node
@@ -524,13 +540,31 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
     __shared__ double s_w[NP];
     __shared__ int s_wsim[NT / 32];                 // per warp: its lane 0's simulation
     __shared__ unsigned long long s_wbest[NT / 32];  // and that simulation's minimum
+    __shared__ unsigned s_emin[EPB];                 // mode 1: per element minimum (float bits)
+    __shared__ unsigned char s_cand[EPB];            // mode 2: the element is a candidate
     if (threadIdx.x < NP) s_w[threadIdx.x] = ops->w[threadIdx.x];
     const size_t KN = (size_t)mesh.K * NN;
     const Gas &g = gas;
     for (int e0 = blockIdx.x * EPB; e0 < mesh.K; e0 += gridDim.x * EPB) {
+        if (flt.mode != 0) {
+            // (EPB * NN <= NT: one node per thread)
+            const int le = threadIdx.x / NN, e = e0 + le;
+            bool cd = false;
+            if (le < EPB && threadIdx.x % NN == 0) {
+                if (flt.mode == 1) s_emin[le] = 0x7f800000u;   // +inf
+                if (e < mesh.K && flt.mode == 2) {
+                    const double smin = __longlong_as_double((long long)flt.smin[mesh.sim[e]]);
+                    cd = (double)__uint_as_float(flt.emin[e]) <= smin * (1.0 + kDtFilterMargin);
+                }
+                s_cand[le] = cd;
+            }
+            // mode 2: a block without candidates has nothing to do (uniform)
+            if (!__syncthreads_or(cd) && flt.mode == 2) continue;
+        }
         for (int k = threadIdx.x; k < EPB * NN; k += NT) {
             int le = k / NN, n = k - le * NN, e = e0 + le;
             if (e >= mesh.K) continue;
+            if (flt.mode == 2 && !s_cand[le]) continue;
             size_t gi = (size_t)e * NN + n;
             if (lam) {
                 // from k_dt_speed
@@ -551,6 +585,7 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
             for (int k = threadIdx.x; k < EPB * 4 * NP; k += NT) {
                 int le = k / (4 * NP), s = (k / NP) % 4, t = k % NP, e = e0 + le;
                 if (e >= mesh.K) continue;
+                if (flt.mode == 2 && !s_cand[le]) continue;
                 const uchar4 ftv = mesh.ftype[e];
                 const int4 nb4 = mesh.fnbr[e];
                 const int ft = s == 0 ? ftv.x : (s == 1 ? ftv.y : (s == 2 ? ftv.z : ftv.w));
@@ -593,6 +628,7 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
         for (int k = threadIdx.x; k < EPB * NN; k += NT) {
             int le = k / NN, n = k - le * NN, e = e0 + le;
             if (e >= mesh.K) continue;
+            if (flt.mode == 2 && !s_cand[le]) continue;
             const int i = n % NP, j = n / NP;
             const GeoC gc = mesh.geoc[e];
             const int sim = mesh.sim[e];
@@ -635,6 +671,7 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
                 best = dbits(INFINITY);
             }
             if (dpos(val) && vb < best) best = vb;
+            if (flt.mode == 1 && dpos(val)) atomicMin(&s_emin[le], __float_as_uint((float)val));
         }
         // warp minimum among the lanes that share lane 0's simulation (other
         // simulations: one atomic per lane), then the block's warps of the
@@ -661,17 +698,21 @@ k_dt(MeshDev mesh, SlotsDev sl, const double *__restrict__ u, Gas gas, int rule,
                     if (bm < dbits(INFINITY)) atomicMin(&dtmin[sw], bm);
                 }
             }
+            if (flt.mode == 1 && threadIdx.x < EPB && e0 + (int)threadIdx.x < mesh.K)
+                flt.emin[e0 + threadIdx.x] = s_emin[threadIdx.x];
         }
         __syncthreads();
     }
 }
 
+// dtmin holds 2 n entries: the time-step minimum per simulation, then the
+// FP32 pass's minimum of the two-pass time step
 static __global__ void k_dt_init(unsigned long long *dtmin, int n) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) dtmin[k] = dbits(INFINITY);
+    if (k < 2 * n) dtmin[k] = dbits(INFINITY);
 }
 
-// The step's end: t += dt per simulation, and the time-step minimum reset to
+// The step's end: t += dt per simulation, and both time-step minima reset to
 // +inf for the next step (which then needs no reset launch of its own).
 static __global__ void k_time_advance(double *t_sim, unsigned long long *dtmin, double cfl, double *dt_last, int n) {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -680,6 +721,7 @@ static __global__ void k_time_advance(double *t_sim, unsigned long long *dtmin, 
         t_sim[k] += dt;
         dt_last[k] = dt;
         dtmin[k] = dbits(INFINITY);
+        dtmin[n + k] = dbits(INFINITY);
     }
 }
 

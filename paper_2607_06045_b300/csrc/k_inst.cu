@@ -116,15 +116,25 @@ void dt_speed(int fp32, cudaStream_t st, const MeshDev &m, const double *u, cons
 
 void dt(int fp32, int grid, cudaStream_t st, const MeshDev &m, const SlotsDev &s, const double *u, const Gas &gamma,
         int rule, const Ops *ops, const double *t_sim, unsigned long long *dtmin, unsigned *status,
-        const double *fbuf, const void *lam) {
+        const double *fbuf, const void *lam, int filt, unsigned *emin) {
     constexpr int EPB = NP * NP >= 64 ? 2 : (NP * NP >= 25 ? 4 : 8);
     int blocks = (m.K + EPB - 1) / EPB;
-    if (fp32)
-        k_dt<NP, EPB, float><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
-                                                                             dtmin, status, nullptr, (const float *)lam);
-    else
-        k_dt<NP, EPB, double><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(m, s, u, gamma, rule, ops, t_sim,
-                                                                              dtmin, status, fbuf, (const double *)lam);
+    const int n = m.n_sims;
+    if (filt == 1) {
+        // the FP64 path's two passes: FP32 minima into dtmin[n..2n) and emin,
+        k_dt<NP, EPB, float><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(
+            m, s, u, gamma, rule, ops, t_sim, dtmin + n, status, fbuf, nullptr, DtFilter{1, emin, nullptr});
+    } else if (filt == 2) {
+        // then the FP64 quotients of the candidate elements into dtmin[0..n)
+        k_dt<NP, EPB, double><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(
+            m, s, u, gamma, rule, ops, t_sim, dtmin, status, fbuf, nullptr, DtFilter{2, emin, dtmin + n});
+    } else if (fp32) {
+        k_dt<NP, EPB, float><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(
+            m, s, u, gamma, rule, ops, t_sim, dtmin, status, nullptr, (const float *)lam, DtFilter{0, nullptr, nullptr});
+    } else {
+        k_dt<NP, EPB, double><<<blocks, ElemLaunch<NP, EPB>::threads, 0, st>>>(
+            m, s, u, gamma, rule, ops, t_sim, dtmin, status, fbuf, (const double *)lam, DtFilter{0, nullptr, nullptr});
+    }
     (void)grid;
 }
 

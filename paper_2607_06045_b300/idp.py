@@ -193,7 +193,7 @@ def idp_eval_math(fn, x, y, stream=None):
 
 # kernel kinds of one step, in the order of the IDP_K_* constants
 KERNELS = ["dt_init", "mortar_flux", "dt", "element", "mortar_limit", "mortar_apply", "time_advance",
-           "element_lo", "mortar_lob", "face", "dt_speed"]
+           "element_lo", "mortar_lob", "face", "dt_speed", "dt_filter"]
 
 NOALLOC_MAX_ELEMS = 1 << 19
 
@@ -380,6 +380,8 @@ class Context:
         # time-step minimum needs no reset launch in a step
         ext_or_f32 = o.precision == 1 or ext
         n = (1 if (M and self.opts.dt_rule == 0) else 0) + 1 + (1 if ext_or_f32 or o.dt_rule != 0 else 0)
+        # FP64 path with the face buffer: the time step's FP32 pass before its FP64 pass
+        n += 1 if (not ext_or_f32 and o.dt_rule == 0) else 0
         # per stage with mortars and limiting: one mortar limiting-and-apply launch
         n += (1 if (M and self.opts.dt_rule != 0) else 0) + el + lob + (1 if (M and lim) else 0)   # stage 1
         n += 2 * ((1 if M else 0) + el + lob + (1 if (M and lim) else 0))   # stages 2, 3

@@ -90,6 +90,12 @@ def method_kernel_work(N: int, precision: int, K: int, face_kernel=None) -> dict
             rows = tuple(r for r in rows if r != "face_flux")
         a, b = method_flops(N, rows, precision)
         out[name] = (a * nodes, b * nodes)
+    if face_kernel:
+        # the two-pass time step: its FP32 pass forms the row's quotients at
+        # every node, the FP64 pass only in the few elements it picks
+        a, b = out.pop("dt")
+        out["dt_filter"] = (0.0, a + b)
+        out["dt"] = (0.0, 0.0)
     return out
 
 
@@ -238,8 +244,13 @@ def kernel_work(N: int, precision: int, K: int, M: int, n_mnodes: int, w_div: fl
         # without the face kernel the time step reads the wave speeds that its
         # pre-pass wrote from the state (two values per node in the flux type)
         **({} if face_kernel else {"dt_speed": (0.0, (32.0 + 2.0 * (4 if precision else 8)) * nodes)}),
-        "dt": (2.0 * dt_ops_per_node(N, precision, face_kernel).dfma_eq(*w) * nodes,
-               (32.0 + 8.0 * 4.0 / (N + 1) if face_kernel else 2.0 * (4 if precision else 8)) * nodes),
+        # with the face kernel the time step's FP32 pass reads the state and
+        # the faces' wave speeds and writes one minimum per element; its FP64
+        # pass reads those minima (and the few picked elements' data)
+        **({"dt_filter": (0.0, (32.0 + 8.0 * 4.0 / (N + 1)) * nodes + 4.0 * K),
+            "dt": (0.0, 4.0 * K)} if face_kernel else
+           {"dt": (2.0 * dt_ops_per_node(N, precision, face_kernel).dfma_eq(*w) * nodes,
+                   2.0 * (4 if precision else 8) * nodes)}),
         "mortar_flux": (2.0 * mortar_flux_ops_per_mortar(N, precision).dfma_eq(*w) * M, (96.0 + 264.0) * (N + 1) * M),
         "mortar_limit": (2.0 * mortar_limit_ops_per_slot(precision).dfma_eq(*w) * Q * M, 112.0 * Q * M),
         "mortar_apply": (2.0 * mortar_apply_ops_per_node(precision).dfma_eq(*w) * n_mnodes, 136.0 * n_mnodes),

@@ -139,6 +139,41 @@ def test_fp32_form_dt_is_safe_and_tight():
             assert d32[k] >= d64 * (1.0 - 2e-5), (N, k, d32[k], d64)
 
 
+def test_fp64_two_pass_dt_is_the_one_pass_dt():
+    """The FP64 path's time step runs an FP32 pass that picks the elements
+    whose quotients the FP64 pass forms. Its result equals, bit for bit, the
+    one-pass FP64 time step of the extended kernel's context (which forms
+    every node's FP64 quotient), and the oracle's to 1e-13: with mortars,
+    walls, inflow and outflow, a uniform state (every element ties), several
+    simulations and the full DMR mesh."""
+    cases = []
+    sq = W.square_mesh()
+    cases.append(([sq], 3, [W.disc_wave_state(sq, 3)]))
+    cases.append(([sq], 3, [W.random_state(sq, 3, seed=1, rho_range=(1.0, 1.0), p_range=(1.0, 1.0), vmax=0.0)]))
+    dm = W.dmr_sample_mesh()
+    cases.append(([dm], 3, [W.dmr_state(dm, 3)]))
+    cases.append(([sq], 5, [W.random_state(sq, 5, seed=3, rho_range=(0.1, 10.0), p_range=(0.1, 10.0), vmax=2.0)]))
+    ms = W.batch_meshes(256, seed=0)
+    small = np.argsort([mm.n_elems for mm in ms])[:3].tolist()
+    rng = np.random.default_rng(1)
+    us = [W.riemann4_state(mm, 3, rng) for mm in ms]
+    cases.append(([ms[k] for k in small], 3, [us[k] for k in small]))
+    full = W.dmr_mesh()
+    cases.append(([full], 3, [W.dmr_state(full, 3)]))
+    for meshes, N, states in cases:
+        mesh = meshes if len(meshes) > 1 else meshes[0]
+        ud = dev(W.concat_states(states))
+        two = idp.Context(mesh, N, cfl=0.5, limiting=2)
+        one = idp.Context(mesh, N, cfl=0.5, limiting=2, entropy_bound=1)   # no face buffer: one FP64 pass
+        d2, d1 = two.idp_dgsem_dt(ud), one.idp_dgsem_dt(ud)
+        assert np.array_equal(d2, d1), (N, len(meshes), d2, d1)
+        two.close()
+        one.close()
+        for k, (m, u) in enumerate(zip(meshes, states)):
+            d64 = oracle.Oracle(m, N).dt(u, cfl=0.5)
+            assert abs(d2[k] - d64) <= 1e-13 * d64, (N, k, d2[k], d64)
+
+
 @pytest.mark.parametrize("limiting", [1, 2])
 def test_square_100_steps(limiting):
     m = W.square_mesh()

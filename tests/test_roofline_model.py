@@ -43,3 +43,21 @@ def test_pair_fluxes_scale_with_the_degree():
 def test_bytes_per_node_stage():
     # read u^(s), read u^n in two of three stages, write u^(s+1)
     assert R.BYTES_PER_NODE_STAGE == pytest.approx(32 + 64 / 3 + 32)
+
+
+def test_fp64_time_step_in_two_passes():
+    # with the face kernel the time step's FP32 pass reads the state and the
+    # faces' wave speeds and carries the method's time-step row (as FP32
+    # work); its FP64 pass over the picked elements is not method work
+    N, K = 3, 1000
+    nodes = K * (N + 1) ** 2
+    work = R.kernel_work(N, 0, K, 50, 600, *W)
+    assert work["dt_filter"] == (0.0, pytest.approx((32.0 + 8.0) * nodes + 4.0 * K))
+    assert work["dt"] == (0.0, pytest.approx(4.0 * K))
+    mk = R.method_kernel_work(N, 0, K)
+    assert mk["dt"] == (0.0, 0.0)
+    assert mk["dt_filter"][0] == 0.0
+    assert mk["dt_filter"][1] == pytest.approx(R.method_rows(N)["dt"] * nodes, rel=1e-12)
+    # the FP32 form's one-pass time step keeps the row
+    assert "dt_filter" not in R.kernel_work(N, 1, K, 50, 600, *W)
+    assert "dt_filter" not in R.method_kernel_work(N, 1, K)
