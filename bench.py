@@ -289,7 +289,7 @@ def method_work(roofline, N, precision, K, M, n_mnodes, w):
     """Per kernel and launch: (FP64 flops, FP32 flops, HBM bytes), the flops
     from the method's work table (the oracle's counting build), the bytes
     from the kernels' algorithmic traffic."""
-    fl = roofline.method_kernel_work(N, precision, K)
+    fl = roofline.method_kernel_work(N, precision, K, M=M)
     by = {name: b for name, (_, b) in roofline.kernel_work(N, precision, K, M, n_mnodes, *w).items()}
     # one kernel limits the mortars and applies their corrections
     by["mortar_limit"] += by.pop("mortar_apply")

@@ -137,9 +137,11 @@ def work_table(degrees=(1, 2, 3, 4, 5, 6, 7)):
     sys.path.insert(0, os.path.dirname(_HERE))
     from paper_2607_06045_b300 import workloads as W
     m = W.dmr_sample_mesh()
+    from oracle import Oracle
     table = {"workload": "double Mach reflection, 64x16 base + 3 levels (dmr_sample_mesh), one SSP-RK3 step "
                          "from the initial state, local + positivity limiting, CFL 0.5",
-             "elements": int(m.n_elems), "weights": WEIGHTS, "method_rows": METHOD_ROWS, "degrees": {}}
+             "elements": int(m.n_elems), "mortars": int(Oracle(m, 1).n_mortars),
+             "weights": WEIGHTS, "method_rows": METHOD_ROWS, "degrees": {}}
     for N in degrees:
         u = W.dmr_state(m, N)
         c, _ = count_step(m, N, u)

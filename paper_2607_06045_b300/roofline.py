@@ -74,14 +74,20 @@ def method_flops(N: int, rows, precision: int = 0):
     return f64, f32
 
 
-def method_kernel_work(N: int, precision: int, K: int, face_kernel=None) -> dict:
+MORTAR_KERNELS = ("mortar_flux", "mortar_limit")
+
+
+def method_kernel_work(N: int, precision: int, K: int, face_kernel=None, M=None) -> dict:
     """Per launch: (FP64 flops, FP32 flops) of each kernel's rows over the K
-    elements of one launch (the mortar rows are per node of the whole mesh,
-    as the table normalises them). With the face kernel the face row is its
-    work and the rest the element kernel's."""
+    elements of one launch. The table normalises the mortar rows per node of
+    its own mesh; with M (the launch's mortars) they are taken per mortar of
+    that mesh and scaled to M, else per node of the K elements. With the face
+    kernel the face row is its work and the rest the element kernel's."""
     nodes = K * (N + 1) ** 2
     if face_kernel is None:
         face_kernel = precision == 0
+    t = method_table()
+    per_mortar = t["degrees"][str(N)]["nodes"] / t["mortars"]
     out = {}
     for name, rows in KERNEL_ROWS.items():
         if name == "face" and not face_kernel:
@@ -89,7 +95,8 @@ def method_kernel_work(N: int, precision: int, K: int, face_kernel=None) -> dict
         if name == "element" and face_kernel:
             rows = tuple(r for r in rows if r != "face_flux")
         a, b = method_flops(N, rows, precision)
-        out[name] = (a * nodes, b * nodes)
+        scale = per_mortar * M if (M is not None and name in MORTAR_KERNELS) else nodes
+        out[name] = (a * scale, b * scale)
     if face_kernel:
         # the two-pass time step: its FP32 pass forms the row's quotients at
         # every node, the FP64 pass only in the few elements it picks

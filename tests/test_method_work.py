@@ -118,3 +118,20 @@ def test_stored_3d_octree_table_matches_the_counting_build():
     a, b = t["degrees"]["1"], fresh["degrees"]["1"]
     for k in ("node_flops_per_node_stage", "mortar_flops_per_mortar_stage", "mortars", "nodes"):
         assert a[k] == pytest.approx(b[k], abs=1e-3), k
+
+
+def test_mortar_rows_scale_with_the_mortar_count():
+    # the table's mortar rows are per node of its own mesh: on that mesh
+    # (its elements and mortars) the per-mortar form gives the same work, and
+    # on another mesh it follows the mortar count, not the node count
+    t = R.method_table()
+    assert t["mortars"] == oracle.Oracle(W.dmr_sample_mesh(), 1).n_mortars
+    N, Kt, Mt = 3, t["elements"], t["mortars"]
+    a = R.method_kernel_work(N, 0, Kt)
+    b = R.method_kernel_work(N, 0, Kt, M=Mt)
+    for k in a:
+        assert b[k] == pytest.approx(a[k], rel=1e-12), k
+    c = R.method_kernel_work(N, 0, 10 * Kt, M=Mt)
+    for k in R.MORTAR_KERNELS:
+        assert c[k] == pytest.approx(a[k], rel=1e-12), k
+    assert c["element"][0] == pytest.approx(10 * a["element"][0], rel=1e-12)
