@@ -35,13 +35,15 @@ if ROOT not in sys.path:
 METRIC = "IDP-DGSEM DOF-updates/s per RK stage (FP64 vs FP32 form, batched); % roofline"
 UNIT = "DOF-updates/s"
 L2_BYTES = 126 * 2 ** 20
-# element-pass launch of the timed DMR contexts: 8 elements per block, one
-# block per batch. A sweep of every (elements per block, grid) pair on a B300
-# found it the fastest for both precisions (FP64 path 2.89 ms/step, FP32 form
-# 0.975; the next best within 0.5% and 1.5%). It is fixed rather than left to
+# element-pass launch of the timed DMR contexts, per precision. A sweep of
+# (elements per block, grid) pairs on a B300: the FP64 path is fastest with 4
+# elements per block on a persistent grid of resident blocks (2.591 ms per
+# step against 2.616 with 8 per block, one block per batch), the FP32 form
+# with 8 per block, one block per batch (0.958 ms against 0.959 with 4 per
+# block and 0.978 on the persistent grid). It is fixed rather than left to
 # the autotuner so that a profiler run, whose serialised launches make the
 # tuner's timings meaningless, launches the same grid as the timed run.
-DMR_ELEMS_PER_BLOCK = 8
+DMR_LAUNCH = {0: dict(elems_per_block=4, grid_mode=2), 1: dict(elems_per_block=8, grid_mode=1)}
 # B300: 148 SMs, each retiring 2 FP64 fused multiply-adds per clock (the
 # nominal 1.25 TFLOP/s FP64 rate at the maximum SM clock).
 SMS, DFMA_PER_CLK_SM = 148, 2
@@ -469,7 +471,7 @@ def run_ours(args):
     results = {}
     clocks = Clocks(local)
     for prec in (0, 1):
-        ctx = idp.Context(meshes[0], 3, precision=prec, limiting=2, cfl=0.5, elems_per_block=DMR_ELEMS_PER_BLOCK)
+        ctx = idp.Context(meshes[0], 3, precision=prec, limiting=2, cfl=0.5, **DMR_LAUNCH[prec])
         u_dev = torch.from_numpy(u0).cuda()
         barrier_sync()
         if prec == 0:

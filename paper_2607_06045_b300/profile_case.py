@@ -18,6 +18,9 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--N", type=int, default=3)
     ap.add_argument("--epb", type=int, default=0, help="elements per block (0: autotune)")
+    ap.add_argument("--grid-mode", type=int, default=0,
+                    help="element-pass grid: 0 autotune (one block per batch with --epb), 1 one block per batch, "
+                         "2 persistent")
     ap.add_argument("--limiting", type=int, default=2)
     ap.add_argument("--bounds", type=int, default=0, help="0 bar states, 1 low-order solution")
     ap.add_argument("--entropy", type=int, default=0, help="1: entropy bound")
@@ -51,7 +54,7 @@ def main(argv=None):
         rng = np.random.default_rng(1)
         u = W.concat_states([W.riemann4_state(m, a.N, rng) for m in meshes])
     ctx = idp.Context(meshes, a.N, precision=a.precision, limiting=a.limiting, bounds=a.bounds,
-                      entropy_bound=a.entropy, cfl=0.5, elems_per_block=a.epb)
+                      entropy_bound=a.entropy, cfl=0.5, elems_per_block=a.epb, grid_mode=a.grid_mode)
     ud = torch.from_numpy(u).cuda()
     t = np.zeros(ctx.n_sims)
     stream = torch.cuda.Stream()
