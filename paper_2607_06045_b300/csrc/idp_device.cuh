@@ -296,7 +296,9 @@ __device__ __forceinline__ Prim<FT> make_prim(const Gas &G, double r, double m1,
 // degree -1 in beta, so 1/{beta'}_ln = 1/((gamma - 1) {beta}_ln)). The
 // two-point flux's means become sums of halves and its factor 1/(gamma - 1)
 // sits in beta'; c is make_prim's.
-__device__ __forceinline__ Prim<double> make_prim_half(const Gas &G, double r, double m1, double m2, double E) {
+// (full = false: v/2, p/2 and c only; re receives rho e)
+__device__ __forceinline__ Prim<double> make_prim_half(const Gas &G, double r, double m1, double m2, double E,
+                                                       bool full = true) {
     Prim<double> q;
     const double ri = fast_rcp(r), hri = 0.5 * ri;
     const double h1 = __dmul_rn(m1, hri), h2 = __dmul_rn(m2, hri);
@@ -304,9 +306,12 @@ __device__ __forceinline__ Prim<double> make_prim_half(const Gas &G, double r, d
     const double hp = __dmul_rn(0.5 * G.gm1, re);
     q.rho = r; q.v1 = h1; q.v2 = h2; q.p = hp; q.E = E;
     q.c = fast_sqrt(__dmul_rn(__dmul_rn(2.0 * G.g, hp), ri));
-    q.beta = __dmul_rn(r, fast_rcp(re));
-    q.lr = fast_log(r, G.lg);
-    q.lb = q.lr - fast_log(re, G.lg);
+    q.beta = q.lr = q.lb = 0.0;
+    if (full) {
+        q.beta = __dmul_rn(r, fast_rcp(re));
+        q.lr = fast_log(r, G.lg);
+        q.lb = q.lr - fast_log(re, G.lg);
+    }
     return q;
 }
 
@@ -318,6 +323,21 @@ __device__ __forceinline__ void phys_flux_half(double m1, double m2, double E, d
     f[1] = m1 * hvn + (d == 0 ? hp : 0.0);
     f[2] = m2 * hvn + (d == 1 ? hp : 0.0);
     f[3] = (E + 2.0 * hp) * hvn;
+}
+
+// Local Lax-Friedrichs flux along axis d (Davis wave speed, R3) from the
+// conserved states and the halved data of make_prim_half; returns lambda.
+__device__ __forceinline__ double llf_half(const double uL[4], const Prim<double> &a, const double uR[4],
+                                           const Prim<double> &b, int d, double f[4]) {
+    const double vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
+    const double lam = speed_max(2.0 * fabs(vna) + a.c, 2.0 * fabs(vnb) + b.c);
+    double fa[4], fb[4];
+    phys_flux_half(uL[1], uL[2], uL[3], a.p, vna, d, fa);
+    phys_flux_half(uR[1], uR[2], uR[3], b.p, vnb, d, fb);
+    const double hl = 0.5 * lam;
+    f[0] = 0.5 * (fa[0] + fb[0]) - hl * (uR[0] - uL[0]);
+    for (int v = 1; v < 4; ++v) f[v] = (fa[v] + fb[v]) - hl * (uR[v] - uL[v]);
+    return lam;
 }
 
 // Ranocha's flux (R1) from the halved node data of make_prim_half.

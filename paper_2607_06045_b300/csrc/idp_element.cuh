@@ -84,16 +84,15 @@ __global__ void __launch_bounds__(256) k_face(MeshDev mesh, const double *__rest
         const size_t gr = (size_t)nb * NP * NP + face_node<NP>(s ^ 1, t);
         double uL[4], uR[4];
         for (int v = 0; v < 4; ++v) { uL[v] = u[v * KN + gl]; uR[v] = u[v * KN + gr]; }
-        const Prim<double> pL = make_prim<double>(G, uL[0], uL[1], uL[2], uL[3], false);
-        const Prim<double> pR = make_prim<double>(G, uR[0], uR[1], uR[2], uR[3], false);
+        const Prim<double> pL = make_prim_half(G, uL[0], uL[1], uL[2], uL[3], false);
+        const Prim<double> pR = make_prim_half(G, uR[0], uR[1], uR[2], uR[3], false);
         double f[4];
-        const double lam = llf_prim<double, double>(uL, pL, uR, pR, d, f);
+        const double lam = llf_half(uL, pL, uR, pR, d, f);
         const GeoC gc = mesh.geoc[e];
         const double wh = ops->w[t] * (d == 0 ? gc.hy : gc.hx);
         for (int v = 0; v < 4; ++v) fb[v * F + k] = wh * f[v];
-        const double i2l = 0.5 * fast_rcp(lam);
         const double mL = d == 0 ? uL[1] : uL[2], mR = d == 0 ? uR[1] : uR[2];
-        fb[4 * F + k] = 0.5 * (uL[0] + uR[0]) - (mR - mL) * i2l;
+        fb[4 * F + k] = 0.5 * ((uL[0] + uR[0]) - (mR - mL) * fast_rcp(lam));
         fb[5 * F + k] = lam;
         fl[k] = d2f(ops->w[t]) * (d == 0 ? gc.hyf : gc.hxf) * d2f(lam);
     }
@@ -569,9 +568,14 @@ k_element(MeshDev mesh, SlotsDev sl, StageArgs A) {
                 else S.i2d[id] = 2.0f * (s_wf[r] * (d == 0 ? S.qyf : S.qxf)) * d2f(lam);
                 double i2l;
                 FT i2lt;
-                if constexpr (F32) { i2lt = 0.5f / lam; i2l = f2d(i2lt); }
-                else { i2l = 0.5 * fast_rcp(lam); i2lt = i2l; }
-                S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * i2l;
+                if constexpr (F32) {
+                    i2lt = 0.5f / lam; i2l = f2d(i2lt);
+                    S.ibar[id] = 0.5 * (S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * i2l;
+                } else {
+                    const double rl = fast_rcp(lam);
+                    i2l = 0.5 * rl; i2lt = i2l;
+                    S.ibar[id] = 0.5 * ((S.u[0][na] + S.u[0][nb]) - (S.u[1 + d][nb] - S.u[1 + d][na]) * rl);
+                }
                 if (EXT && ent && !lob && !pre) S.xs[NN + id] = bar_entropy<FT>(G, ua, fa, ub, fb, i2lt);
             }
             if (EXT && ent && !lob && !pre) {
