@@ -184,8 +184,10 @@ __device__ __forceinline__ Prim<FT> pick_prim(bool c, const Prim<FT> &a, const P
 // ln(a/b) (FP32); for u = ((a-b)/(a+b))^2 below 1e-4 (FP64) or 1e-2 (FP32)
 // the Ismail-Roe series (a+b)/(2 F(u)), F = 1 + u/3 + u^2/5 + u^3/7, with
 // 1/F from the inverted series 1 - u/3 - 4u^2/45 - 44u^3/945. The two
-// denominators share one reciprocal.
-template <typename FT>
+// denominators share one reciprocal. HALVES: rho, beta and their logarithms
+// are given halved (make_prim_half), which scales every quotient exactly and
+// leaves the series' factors 1/2 and 2 to the data.
+template <typename FT, bool HALVES = false>
 __device__ __forceinline__ void log_means(const Prim<FT> &a, const Prim<FT> &b, FT &rho_ln, FT &ibeta) {
     constexpr bool dbl = sizeof(FT) == 8;
     const FT thr = dbl ? FT(1e-4) : FT(1e-2);
@@ -218,14 +220,14 @@ __device__ __forceinline__ void log_means(const Prim<FT> &a, const Prim<FT> &b, 
     if (nr) {
         FT f = dr * ixr, u = f * f;
         FT invF = FT(1) - u * (FT(1.0 / 3.0) + u * (FT(4.0 / 45.0) + u * FT(44.0 / 945.0)));
-        rho_ln = FT(0.5) * sr * invF;
+        rho_ln = HALVES ? sr * invF : FT(0.5) * sr * invF;
     } else {
         rho_ln = dr * ixr;
     }
     if (nb) {
         FT f = db * ixb, u = f * f;
         FT F = FT(1) + u * (FT(1.0 / 3.0) + u * (FT(1.0 / 5.0) + u * FT(1.0 / 7.0)));
-        ibeta = FT(2) * F * ixb;
+        ibeta = HALVES ? F * ixb : FT(2) * F * ixb;
     } else {
         ibeta = lb * ixb;
     }
@@ -290,13 +292,14 @@ __device__ __forceinline__ Prim<FT> make_prim(const Gas &G, double r, double m1,
 }
 
 // Node data of the FP64 element pass in halves: v1/2, v2/2 and p/2 (the
-// same bits as make_prim's v1, v2, p scaled by 1/2, which is exact) and
-// beta' = rho / (rho e) = (gamma - 1) rho / p with ln beta' (a rescaling of
-// beta at rounding level; the logarithmic mean's quotient is homogeneous of
-// degree -1 in beta, so 1/{beta'}_ln = 1/((gamma - 1) {beta}_ln)). The
-// two-point flux's means become sums of halves and its factor 1/(gamma - 1)
-// sits in beta'; c is make_prim's.
-// (full = false: v/2, p/2 and c only; re receives rho e)
+// same bits as make_prim's v1, v2, p scaled by 1/2, which is exact), rho/2,
+// and beta'/2 with beta' = rho / (rho e) = (gamma - 1) rho / p, and the
+// halves of ln rho and ln beta' (beta' rescales beta at rounding level; the
+// logarithmic mean's quotient is homogeneous of degree -1 in beta, so
+// 1/{beta'}_ln = 1/((gamma - 1) {beta}_ln)). The two-point flux's means
+// become sums of halves, the logarithmic means lose their factors 1/2 and 2
+// and the factor 1/(gamma - 1) sits in beta'; c is make_prim's.
+// (full = false: v/2, p/2 and c only, rho whole)
 __device__ __forceinline__ Prim<double> make_prim_half(const Gas &G, double r, double m1, double m2, double E,
                                                        bool full = true) {
     Prim<double> q;
@@ -308,9 +311,10 @@ __device__ __forceinline__ Prim<double> make_prim_half(const Gas &G, double r, d
     q.c = fast_sqrt(__dmul_rn(__dmul_rn(2.0 * G.g, hp), ri));
     q.beta = q.lr = q.lb = 0.0;
     if (full) {
-        q.beta = __dmul_rn(r, fast_rcp(re));
-        q.lr = fast_log(r, G.lg);
-        q.lb = q.lr - fast_log(re, G.lg);
+        q.rho = 0.5 * r;
+        q.beta = q.rho * fast_rcp(re);
+        q.lr = 0.5 * fast_log(r, G.lg);
+        q.lb = q.lr - 0.5 * fast_log(re, G.lg);
     }
     return q;
 }
@@ -343,7 +347,7 @@ __device__ __forceinline__ double llf_half(const double uL[4], const Prim<double
 // Ranocha's flux (R1) from the halved node data of make_prim_half.
 __device__ __forceinline__ void ranocha_half(const Prim<double> &a, const Prim<double> &b, int d, double f[4]) {
     double rho_ln, ibeta;
-    log_means<double>(a, b, rho_ln, ibeta);
+    log_means<double, true>(a, b, rho_ln, ibeta);
     const double v1m = a.v1 + b.v1, v2m = a.v2 + b.v2, pm = a.p + b.p;
     const double vna = d == 0 ? a.v1 : a.v2, vnb = d == 0 ? b.v1 : b.v2;
     const double fr = rho_ln * (d == 0 ? v1m : v2m);
