@@ -228,10 +228,10 @@ __device__ __forceinline__ int node_of(int d, int r, int a) {
 }
 
 // per-node flux data of the element kernel: in the FP64 path v1/2, v2/2,
-// v3/2, p/2, ln rho, ln beta', beta' = (gamma - 1) rho / p = rho / (rho e) and
-// |v_d| + c (the halves and beta' are exact or rounding-level rescalings that
-// fold the means' factors 1/2 and the 1/(gamma - 1) of the two-point flux into
-// the node data); in the FP32 form the state rounded to FP32, v1, v2, v3, p,
+// v3/2, p/2, ln rho, (ln beta')/2, beta'/2 with beta' = (gamma - 1) rho / p =
+// rho / (rho e), and |v_d| + c (the halves and beta' are exact or
+// rounding-level rescalings that fold the means' factors 1/2 and 2 and the
+// 1/(gamma - 1) of the two-point flux into the node data); in the FP32 form the state rounded to FP32, v1, v2, v3, p,
 // beta = rho / p and |v_d| + c in FP32
 template <int NP, bool F32>
 struct Node3 {
@@ -368,7 +368,9 @@ struct Launch3 {
 // reciprocal: rho_ln = (ra - rb) / (ln ra - ln rb) and 1 / beta_ln = (ln ba -
 // ln bb) / (ba - bb), each by the Ismail-Roe series where ((a - b)/(a + b))^2
 // <= 1e-4 (the test in FP32, converted on the integer pipe: the two forms
-// agree to rounding near the threshold).
+// agree to rounding near the threshold). ba, bb and their logarithms come
+// halved (the FP64 node data), which scales the quotient exactly and drops
+// the series' factor 2.
 __device__ __forceinline__ void log_means3(double ra, double rb, double lra, double lrb, double ba, double bb,
                                            double lba, double lbb, double &rho_ln, double &ibeta) {
     const double dr = ra - rb, sr = ra + rb, db = ba - bb, sb = ba + bb;
@@ -387,7 +389,7 @@ __device__ __forceinline__ void log_means3(double ra, double rb, double lra, dou
     if (nb) {
         const double f = db * ixb, u = f * f;
         // 2 F(u) / sb with F = 1 + u/3 + u^2/5 + u^3/7
-        ibeta = 2.0 * ixb * (1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0))));
+        ibeta = ixb * (1.0 + u * (1.0 / 3.0 + u * (1.0 / 5.0 + u * (1.0 / 7.0))));
     } else {
         ibeta = (lba - lbb) * ixb;
     }
@@ -491,8 +493,8 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             const double c = idp::fast_sqrt(g2 * hp * ir);
             const double bet = uv[0] * idp::fast_rcp(re);
             nd.pr[4][n] = idp::fast_log(uv[0], G.lg);
-            nd.pr[5][n] = idp::fast_log(bet, G.lg);
-            nd.pr[6][n] = bet;
+            nd.pr[5][n] = 0.5 * idp::fast_log(bet, G.lg);
+            nd.pr[6][n] = 0.5 * bet;
             nd.lam[0][n] = 2.0 * fabs(h1) + c; nd.lam[1][n] = 2.0 * fabs(h2) + c; nd.lam[2][n] = 2.0 * fabs(h3) + c;
         }
     }
@@ -676,8 +678,8 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
             const float sgf = side ? 0.5f : -0.5f;
             fb = idp::f2d(0.5f * (ui[0] + uo[0]) - sgf * (uo[1 + d] - ui[1 + d]) * __frcp_rn(lam));
         } else {
-            const double sg = side ? 0.5 : -0.5;
-            fb = 0.5 * (ui[0] + uo[0]) - sg * (uo[1 + d] - ui[1 + d]) * idp::fast_rcp(lam);
+            const double dm = side ? uo[1 + d] - ui[1 + d] : ui[1 + d] - uo[1 + d];
+            fb = 0.5 * ((ui[0] + uo[0]) - dm * idp::fast_rcp(lam));
         }
         S[le].fbl[s][t] = fb;
         S[le].fbh[s][t] = fb;
@@ -711,7 +713,7 @@ k_element3d(Grid3 G, const Ops3 *__restrict__ ops_g, Stage3 A) {
         for (int v = 0; v < NV; ++v)
             S[le].fvf[id][v] = ((F32 || v == 0) ? cc : cc2) * (fl[v] + fr[v]) - cc * lam * (ur[v] - ul[v]);
         if constexpr (F32) S[le].ibar[id] = idp::f2d(0.5f * (ul[0] + ur[0]) - 0.5f * (ur[1 + d] - ul[1 + d]) * __frcp_rn(lam));
-        else S[le].ibar[id] = 0.5 * (ul[0] + ur[0]) - 0.5 * (ur[1 + d] - ul[1 + d]) * idp::fast_rcp(lam);
+        else S[le].ibar[id] = 0.5 * ((ul[0] + ur[0]) - (ur[1 + d] - ul[1 + d]) * idp::fast_rcp(lam));
     }
     __syncthreads();
     // ---- P2: low-order residual, low-order update and bounds per node
