@@ -432,9 +432,9 @@ def bench_3d(idp, flush, stream, args, n=40, N=3, octree=False, precision=0):
     ms = float(np.mean(times))
     mesh_text = (f"{n}^3 base hexahedra with [1/4, 3/4]^3 refined once ({g.n_elems} leaves, {ctx.n_mortars} "
                  f"mortars)" if octree else f"{n}^3 hexahedra")
-    # per step: the time step (FP64 path: wave speeds and sums), three element
+    # per step: the time step (FP64 path: a reset and its FP32 and FP64 passes), three element
     # launches, the advance; on octrees mortar flux, factor and apply per stage
-    launches = (5 if precision else 6) + (9 if octree else 0)
+    launches = (5 if precision else 7) + (9 if octree else 0)
     out = dict(value=dofs * 3 / (ms * 1e-3), unit=UNIT, ms_per_step=ms, ms_per_step_median=float(np.median(times)),
                steps=steps, elements=g.n_elems, dofs=dofs, gpu_launches=launches * steps,
                workload=f"3D blast: [0,1]^3, {mesh_text}, N={N}, sphere r < 0.15 at p = 10 in a gas at "

@@ -1099,32 +1099,35 @@ __device__ __forceinline__ bool wave_speeds3(double g, const double *u, float *l
 // quotient stays below the FP64 one.
 constexpr double kDtSafe32 = 1.0 - 8e-6;
 
-// per node |v_d| + c of u, lam[d][K (N+1)^3] (the FP64 time step's first
-// pass, so that the time step reads the outside nodes' wave speeds instead
-// of forming them again)
-template <int NP>
-__global__ void __launch_bounds__(256) k_wave3d(Grid3 G, const double *__restrict__ u, double gamma,
-                                                double *__restrict__ lam, unsigned *status) {
-    const size_t KN = (size_t)G.K * NP * NP * NP;
-    for (size_t i = (size_t)blockIdx.x * 256 + threadIdx.x; i < KN; i += (size_t)gridDim.x * 256) {
-        double uv[NV], l3[3];
-        for (int v = 0; v < NV; ++v) uv[v] = u[v * KN + i];
-        if (!wave_speeds3(gamma, uv, l3)) atomicOr(status, S_BAD_INPUT);
-        for (int d = 0; d < 3; ++d) lam[d * KN + i] = l3[d];
-    }
-}
-
 // IDP time step (Eq. timestep_restriction): per node m_i / sum_j 2 d_ij over
 // its subcell and face neighbours (at a mortar side the slot's sum over its
 // pairs, formed by the mortar flux kernel from the same state); minimum per
 // block, one atomic per block. 2 d_ij of a subcell or conforming pair is
 // w_t1 w_t2 (A_d / 4) max(lambda_i, lambda_j). FT = float: wave speeds, sums
-// and the quotient in FP32 (the FP32 form). lamg (FP64 path): the wave
-// speeds of every node from k_wave3d.
+// and the quotient in FP32 (the FP32 form).
+// The FP64 path's time step in two passes (pk): the FP32 kernel (mode 1)
+// also writes each element's minimum (emin, bits of a positive float); the
+// FP64 kernel (mode 2) then forms the FP64 quotients only in the
+// elements whose FP32 minimum lies within a relative 1e-4 of the FP32
+// pass's overall minimum (smin). The FP32 quotients are within about 1e-5
+// of the FP64 ones (the FP32 form's margin kDtSafe32 is 8e-6), so the FP64
+// minimiser's element is always formed and the result is the one-pass FP64
+// minimum bit for bit.
+struct DtPick3 {
+    int mode;                          // 0: one pass; 1: FP32 pass; 2: FP64 pass over the picked elements
+    unsigned *emin;                    // per element: the FP32 pass's minimum
+    const unsigned long long *smin;    // mode 2: the FP32 pass's minimum (bits of a double)
+};
+constexpr double kPickMargin3 = 1e-4;
+
+static __global__ void k_inf3d(unsigned long long *p) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = (unsigned long long)__double_as_longlong(INFINITY);
+}
+
 template <int NP, int EPB, typename FT>
 __global__ void __launch_bounds__(Launch3<NP, EPB>::threads)
 k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, double gamma,
-       unsigned long long *dtmin, unsigned *status, const double *__restrict__ lamg) {
+       unsigned long long *dtmin, unsigned *status, DtPick3 pk) {
     using E = El3<NP>;
     constexpr bool F32 = sizeof(FT) == 4;
     constexpr int N = E::N, NN = E::NN, NT = Launch3<NP, EPB>::threads;
@@ -1132,21 +1135,33 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
     __shared__ FT w[NP];
     __shared__ FT geo[EPB][4];   // quarter face areas, dx dy dz / 8
     __shared__ unsigned long long best_s[NT / 32];
+    __shared__ unsigned s_emin[EPB];
+    __shared__ unsigned char s_cand[EPB];
     if (threadIdx.x < NP) w[threadIdx.x] = (FT)(F32 ? (double)idp::d2f(ops_g->w[threadIdx.x]) : ops_g->w[threadIdx.x]);
     const size_t KN = (size_t)G.K * NN;
     const int e0 = blockIdx.x * EPB, tid = threadIdx.x;
+    if (pk.mode != 0) {
+        // (EPB * NN <= NT: one node per thread)
+        const int le = tid / NN, e = e0 + le;
+        bool cd = false;
+        if (le < EPB && tid % NN == 0) {
+            if (pk.mode == 1) s_emin[le] = 0x7f800000u;   // +inf
+            if (pk.mode == 2 && e < G.K)
+                cd = (double)__uint_as_float(pk.emin[e]) <= __longlong_as_double((long long)*pk.smin) * (1.0 + kPickMargin3);
+            s_cand[le] = cd;
+        }
+        // mode 2: a block without picked elements has nothing to do (uniform)
+        if (!__syncthreads_or(cd) && pk.mode == 2) return;
+    }
     for (int k = tid; k < EPB * NN; k += NT) {
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
+        if (pk.mode == 2 && !s_cand[le]) continue;
         if (n == 0) {
             double h[3];
             extents3(G, e, h);
             const double gd[4] = {h[1] * h[2] / 4.0, h[0] * h[2] / 4.0, h[0] * h[1] / 4.0, h[0] * h[1] * h[2] / 8.0};
             for (int c = 0; c < 4; ++c) geo[le][c] = (FT)(F32 ? (double)idp::d2f(gd[c]) : gd[c]);
-        }
-        if (!F32 && lamg) {
-            for (int d = 0; d < 3; ++d) lam[le][d][n] = (FT)lamg[d * KN + (size_t)e * NN + n];
-            continue;
         }
         double uv[NV];
         FT l3[3];
@@ -1159,6 +1174,7 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
     for (int k = tid; k < EPB * NN; k += NT) {
         const int le = k / NN, n = k - le * NN, e = e0 + le;
         if (e >= G.K) continue;
+        if (pk.mode == 2 && !s_cand[le]) continue;
         const int idx[3] = {n % NP, (n / NP) % NP, n / (NP * NP)};
         FT s2d = FT(0);
         double smort = 0.0;   // the mortar slots' sums (FP64)
@@ -1178,19 +1194,6 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
                         continue;
                     }
                     double o[NV];
-                    if (!F32 && lamg && (nb >= 0 || G.bc[s] != B_DIRICHLET)) {
-                        // a conforming neighbour's wave speed, or a wall or outflow ghost's (the own one)
-                        if (nb >= 0) {
-                            int jdx[3] = {idx[0], idx[1], idx[2]};
-                            jdx[d] = side ? 0 : N;
-                            lo = (FT)lamg[d * KN + (size_t)nb * NN + (jdx[2] * NP + jdx[1]) * NP + jdx[0]];
-                        } else {
-                            lo = li;
-                        }
-                        if constexpr (F32) lsum += fmaxf(li, lo);
-                        else lsum += idp::dmax(li, lo);
-                        continue;
-                    }
                     if (nb >= 0) {
                         int jdx[3] = {idx[0], idx[1], idx[2]};
                         jdx[d] = side ? 0 : N;
@@ -1220,6 +1223,7 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
         }
         const unsigned long long vb = (unsigned long long)__double_as_longlong(val);
         if (val > 0.0 && vb < best) best = vb;
+        if (pk.mode == 1 && val > 0.0) atomicMin(&s_emin[le], __float_as_uint((float)val));
     }
     for (int o = 16; o > 0; o >>= 1) {
         const unsigned long long ob = __shfl_down_sync(0xffffffffu, best, o);
@@ -1232,6 +1236,7 @@ k_dt3d(Grid3 G, const Ops3 *__restrict__ ops_g, const double *__restrict__ u, do
         for (int k = 1; k < NT / 32; ++k) b = best_s[k] < b ? best_s[k] : b;
         if (b < (unsigned long long)__double_as_longlong(INFINITY)) atomicMin(dtmin, b);
     }
+    if (pk.mode == 1 && tid < EPB && e0 + tid < G.K) pk.emin[e0 + tid] = s_emin[tid];
 }
 
 // the step's end: t += cfl * min, the minimum reset to +inf for the next step

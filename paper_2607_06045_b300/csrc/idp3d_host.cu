@@ -39,7 +39,7 @@ struct idp3d_ctx {
     signed char *d_lev = nullptr;
     double *d_mslot = nullptr, *d_hand = nullptr, *d_ell = nullptr;
     double *d_buf1 = nullptr, *d_buf2 = nullptr, *d_part = nullptr, *d_tot = nullptr;
-    double *d_lam = nullptr;       // FP64 time step: the nodes' wave speeds [3][K (N+1)^3]
+    unsigned *d_emin = nullptr;    // FP64 time step: per element, its FP32 pass's minimum
     double *d_ind = nullptr, *d_aind = nullptr;   // combined limiting: indicator operators, per element indicator
     unsigned long long *d_dtmin = nullptr, *d_dtmin2 = nullptr;
     double *d_t = nullptr, *d_dtlast = nullptr;
@@ -97,7 +97,7 @@ bool has_mortars(const idp3d_ctx *c) { return c->grid.mort.M > 0; }
 // the time-step kernel of the context's precision
 void launch_dt(idp3d_ctx *c, cudaStream_t st, const double *u, unsigned long long *dtmin) {
     if (c->opt.precision == 1) c->L.dt32(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status, nullptr);
-    else c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status, c->d_lam);
+    else c->L.dt(dt_grid(c), st, c->grid, c->d_ops, u, c->gamma, dtmin, c->d_status, c->d_emin);
 }
 
 // one limited stage: the mortar fluxes of its input (unless already formed),
@@ -432,11 +432,12 @@ idp_status create3(const idp3d_grid_desc *gd, int64_t K, const int8_t *level, co
     }
     if (ok) chk(cudaMalloc(&c->d_buf1, sizeof(double) * NV * kn));
     if (ok) chk(cudaMalloc(&c->d_buf2, sizeof(double) * NV * kn));
-    if (ok && o.precision == 0) chk(cudaMalloc(&c->d_lam, sizeof(double) * 3 * kn));
+    if (ok && o.precision == 0) chk(cudaMalloc(&c->d_emin, sizeof(unsigned) * (size_t)G.K));
     if (ok) chk(cudaMalloc(&c->d_part, sizeof(double) * NV * (size_t)G.K));
     if (ok) chk(cudaMalloc(&c->d_tot, sizeof(double) * NV));
-    if (ok) chk(cudaMalloc(&c->d_dtmin, sizeof(unsigned long long)));
-    if (ok) chk(cudaMalloc(&c->d_dtmin2, sizeof(unsigned long long)));
+    // each: the minimum, then the FP32 pass's minimum of the two-pass time step
+    if (ok) chk(cudaMalloc(&c->d_dtmin, 2 * sizeof(unsigned long long)));
+    if (ok) chk(cudaMalloc(&c->d_dtmin2, 2 * sizeof(unsigned long long)));
     if (ok) chk(cudaMemcpy(c->d_dtmin, &kInfBits, sizeof(kInfBits), cudaMemcpyHostToDevice));
     if (ok) chk(cudaMalloc(&c->d_t, sizeof(double)));
     if (ok) chk(cudaMalloc(&c->d_dtlast, sizeof(double)));
@@ -645,7 +646,7 @@ void idp3d_destroy(idp3d_ctx *c) {
     void *ptrs[] = {c->d_ops, c->d_buf1, c->d_buf2, c->d_part, c->d_tot, c->d_dtmin, c->d_dtmin2, c->d_t,
                     c->d_dtlast, c->d_status, c->d_stats, c->d_mops, c->d_nbr, c->d_lev, c->d_minfo,
                     c->d_slot_mn, c->d_mn_node, c->d_mn_slot, c->d_mn_cnt, c->d_mbad, c->d_mslot, c->d_hand,
-                    c->d_ell, c->d_lg, c->d_lam, c->d_ind, c->d_aind};
+                    c->d_ell, c->d_lg, c->d_emin, c->d_ind, c->d_aind};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (c->ev_in) cudaEventDestroy(c->ev_in);

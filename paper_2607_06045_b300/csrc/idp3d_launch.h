@@ -18,10 +18,12 @@ struct Launchers3 {
     void (*element)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) = nullptr;
     void (*element32)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const Stage3 &A) = nullptr;
     // the time step: FP64 path (its wave speeds first, into lam[3][K (N+1)^3]), FP32 form
+    // dt: the FP64 path's two passes (dtmin: 2 entries, the minimum and the
+    // FP32 pass's; emin: one value per element); dt32: the FP32 form
     void (*dt)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
-               unsigned long long *dtmin, unsigned *status, double *lam) = nullptr;
+               unsigned long long *dtmin, unsigned *status, unsigned *emin) = nullptr;
     void (*dt32)(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
-                 unsigned long long *dtmin, unsigned *status, double *lam) = nullptr;
+                 unsigned long long *dtmin, unsigned *status, unsigned *emin) = nullptr;
     // the mortar kernels (grid: one block per mortar; apply: its own grid)
     void (*mflux)(cudaStream_t st, const Grid3 &G, const MOps3 *mo, const double *u, double gamma) = nullptr;
     void (*mfactor)(cudaStream_t st, const Grid3 &G, const Stage3 &A) = nullptr;

@@ -35,17 +35,21 @@ void element32(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const
     k_element3d<NP, EPB, float><<<grid, L3::threads, sizeof(Sm3<NP, float>) * EPB, st>>>(G, ops, A);
 }
 
+// FP64 path: the FP32 pass into dtmin[1] (reset first) and the elements'
+// minima, then the FP64 quotients of the picked elements into dtmin[0]
 void dt(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
-        unsigned long long *dtmin, unsigned *status, double *lam) {
-    const size_t KN = (size_t)G.K * NP * NP * NP;
-    const size_t wb = (KN + 255) / 256;
-    k_wave3d<NP><<<(unsigned)(wb < 148 * 16 ? wb : 148 * 16), 256, 0, st>>>(G, u, gamma, lam, status);
-    k_dt3d<NP, EPB, double><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status, lam);
+        unsigned long long *dtmin, unsigned *status, unsigned *emin) {
+    k_inf3d<<<1, 32, 0, st>>>(dtmin + 1);
+    k_dt3d<NP, EPB, float><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin + 1, status,
+                                                          DtPick3{1, emin, nullptr});
+    k_dt3d<NP, EPB, double><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status,
+                                                           DtPick3{2, emin, dtmin + 1});
 }
 
 void dt32(int grid, cudaStream_t st, const Grid3 &G, const Ops3 *ops, const double *u, double gamma,
-          unsigned long long *dtmin, unsigned *status, double *) {
-    k_dt3d<NP, EPB, float><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status, nullptr);
+          unsigned long long *dtmin, unsigned *status, unsigned *) {
+    k_dt3d<NP, EPB, float><<<grid, L3::threads, 0, st>>>(G, ops, u, gamma, dtmin, status,
+                                                          DtPick3{0, nullptr, nullptr});
 }
 
 void mflux(cudaStream_t st, const Grid3 &G, const MOps3 *mo, const double *u, double gamma) {
